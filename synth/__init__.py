@@ -1,0 +1,216 @@
+"""Seeded synthetic LiDAR inputs shared by the oracle tests, the GPU tests and the bench.
+
+The ray caster lives in ``lidar_synth.c`` (compiled on first use with gcc).  It
+holds none of the compression method's arithmetic: it only produces point
+clouds shaped like HDL-64E / KITTI scans and the exact sensor poses of a
+sequence.  Workload presets mirror the five benchmark configurations:
+
+* ``frame_cfg1``  16x512 key frame, elevation -15..+15 deg, 4 walls closing a
+  courtyard 10-40 m away, 6 boxes, 10 poles, sigma 2 cm, 5 % dropout, max
+  range 80 m.
+* ``sequence_cfg2``  64x2048 frames (elevation -24.8..+2 deg), 20 walls,
+  40 boxes, 60 poles, 2 % clutter, sigma 2 cm, 1 m/frame forward, 0.5 deg/frame
+  yaw, 10 frames with the key frame in the middle.
+
+Seeds follow ``seed = 1000003*config + 1009*sequence + frame``.
+"""
+from __future__ import annotations
+
+import ctypes
+import math
+import os
+import subprocess
+import threading
+from dataclasses import dataclass
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "lidar_synth.c")
+_LIB_PATH = os.path.join(_HERE, "liblidar_synth.so")
+_lock = threading.Lock()
+_lib = None
+
+
+class _Obj(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int32), ("pad", ctypes.c_int32), ("p", ctypes.c_double * 6)]
+
+
+def build(force: bool = False) -> str:
+    """Compile the generator shared library (gcc, OpenMP not needed)."""
+    if force or not os.path.exists(_LIB_PATH) or os.path.getmtime(_LIB_PATH) < os.path.getmtime(_SRC):
+        tmp = _LIB_PATH + f".tmp{os.getpid()}"
+        subprocess.check_call(["gcc", "-O2", "-fPIC", "-shared", "-ffp-contract=off",
+                               "-o", tmp, _SRC, "-lm"])
+        os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is None:
+            build()
+            lib = ctypes.CDLL(_LIB_PATH)
+            lib.syn_make_scene.restype = ctypes.c_int
+            lib.syn_make_scene.argtypes = [ctypes.c_uint64, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                           ctypes.c_double, ctypes.c_double, ctypes.c_int, ctypes.c_void_p,
+                                           ctypes.c_int]
+            lib.syn_render.restype = ctypes.c_int64
+            lib.syn_render.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                       ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                                       ctypes.c_void_p, ctypes.c_void_p, ctypes.c_double,
+                                       ctypes.c_double, ctypes.c_double, ctypes.c_uint64,
+                                       ctypes.c_void_p, ctypes.c_int64]
+            _lib = lib
+    return _lib
+
+
+@dataclass(frozen=True)
+class Sensor:
+    rows: int
+    cols: int
+    elev_min_deg: float
+    elev_max_deg: float
+    max_range_m: float
+
+
+CFG1_SENSOR = Sensor(16, 512, -15.0, 15.0, 80.0)
+HDL64_SENSOR = Sensor(64, 2048, -24.8, 2.0, 80.0)
+
+
+def config_seed(config: int, sequence: int, frame: int) -> int:
+    return 1000003 * config + 1009 * sequence + frame
+
+
+class Scene:
+    def __init__(self, seed: int, n_walls: int, n_boxes: int, n_poles: int,
+                 ground_z: float = -1.7, path_len: float = 0.0, enclose: bool = False):
+        lib = _load()
+        cap = 1 + n_walls + n_boxes + n_poles
+        self._objs = (_Obj * cap)()
+        n = lib.syn_make_scene(seed, n_walls, n_boxes, n_poles, ground_z, path_len, int(enclose),
+                               ctypes.cast(self._objs, ctypes.c_void_p), cap)
+        if n < 0:
+            raise RuntimeError("scene generation failed")
+        self.n = n
+
+    def objects(self):
+        return [(o.kind, tuple(o.p)) for o in self._objs[: self.n]]
+
+    def render(self, sensor: Sensor, R=None, t=None, sigma=0.02, dropout=0.0, clutter=0.0,
+               seed=0) -> np.ndarray:
+        """One frame as float32 (n, 4) = (x, y, z, 0) in sensor coordinates."""
+        lib = _load()
+        R = np.eye(3) if R is None else np.asarray(R, dtype=np.float64)
+        t = np.zeros(3) if t is None else np.asarray(t, dtype=np.float64)
+        R = np.ascontiguousarray(R, dtype=np.float64).reshape(9)
+        t = np.ascontiguousarray(t, dtype=np.float64).reshape(3)
+        cap = sensor.rows * sensor.cols
+        out = np.empty((cap, 4), dtype=np.float32)
+        n = lib.syn_render(ctypes.cast(self._objs, ctypes.c_void_p), self.n, sensor.rows, sensor.cols,
+                           sensor.elev_min_deg, sensor.elev_max_deg, sensor.max_range_m,
+                           R.ctypes.data, t.ctypes.data, sigma, dropout, clutter, seed,
+                           out.ctypes.data, cap)
+        if n < 0:
+            raise RuntimeError("render failed")
+        return out[:n].copy()
+
+
+def yaw_matrix(psi: float) -> np.ndarray:
+    c, s = math.cos(psi), math.sin(psi)
+    return np.array([[c, -s, 0.0], [s, c, 0.0], [0.0, 0.0, 1.0]])
+
+
+def ego_poses(n_frames: int, step_m: float, yaw_deg_per_frame: float):
+    """World poses (R, t) of a sensor that drives forward along its heading and yaws
+    by a fixed angle per frame (frame 0 at the origin, heading +x)."""
+    poses = []
+    pos = np.zeros(3)
+    for f in range(n_frames):
+        psi = math.radians(yaw_deg_per_frame * f)
+        poses.append((yaw_matrix(psi), pos.copy()))
+        pos = pos + step_m * np.array([math.cos(psi), math.sin(psi), 0.0])
+    return poses
+
+
+def relative_pose(pose_f, pose_k) -> np.ndarray:
+    """4x4 row-major matrix M with p_K = R p_f + T (frame f coordinates to frame k)."""
+    Rf, tf = pose_f
+    Rk, tk = pose_k
+    M = np.eye(4)
+    M[:3, :3] = Rk.T @ Rf
+    M[:3, 3] = Rk.T @ (tf - tk)
+    return M
+
+
+def perturb_pose(M: np.ndarray, sigma_t: float, sigma_rot_deg: float, seed: int) -> np.ndarray:
+    """Add Gaussian noise (translation sigma_t metres, small rotation sigma_rot_deg about
+    each axis) to a 4x4 pose; models an IMU-derived pose."""
+    rng = np.random.default_rng(seed)
+    a = np.radians(rng.normal(0.0, sigma_rot_deg, 3))
+    cx, sx, cy, sy, cz, sz = math.cos(a[0]), math.sin(a[0]), math.cos(a[1]), math.sin(a[1]), \
+        math.cos(a[2]), math.sin(a[2])
+    Rx = np.array([[1, 0, 0], [0, cx, -sx], [0, sx, cx]])
+    Ry = np.array([[cy, 0, sy], [0, 1, 0], [-sy, 0, cy]])
+    Rz = np.array([[cz, -sz, 0], [sz, cz, 0], [0, 0, 1]])
+    out = M.copy()
+    out[:3, :3] = Rz @ Ry @ Rx @ M[:3, :3]
+    out[:3, 3] = M[:3, 3] + rng.normal(0.0, sigma_t, 3)
+    return out
+
+
+def frame_cfg1(sequence: int = 0) -> tuple[Sensor, np.ndarray]:
+    """Single 16x512 key frame of the small workload."""
+    seed = config_seed(1, sequence, 0)
+    scene = Scene(seed, n_walls=4, n_boxes=6, n_poles=10, enclose=True)
+    pts = scene.render(CFG1_SENSOR, sigma=0.02, dropout=0.05, clutter=0.0, seed=seed)
+    return CFG1_SENSOR, pts
+
+
+@dataclass
+class Sequence:
+    sensor: Sensor
+    frames: list          # list of float32 (n_i, 4)
+    key_index: int
+    poses: np.ndarray     # (n_frames, 4, 4): frame i coordinates -> key frame coordinates
+
+
+def sequence(sensor: Sensor, n_frames: int, seed: int, n_walls: int, n_boxes: int, n_poles: int,
+             step_m: float, yaw_deg: float, sigma: float = 0.02, dropout: float = 0.0,
+             clutter: float = 0.0, pose_noise=None, key_index=None) -> Sequence:
+    """A sequence in one scene; the key frame is the middle one (floor(n/2))."""
+    world = ego_poses(n_frames, step_m, yaw_deg)
+    path_len = step_m * max(n_frames - 1, 0)
+    scene = Scene(seed, n_walls, n_boxes, n_poles, path_len=path_len)
+    k = n_frames // 2 if key_index is None else key_index
+    frames, poses = [], []
+    for f in range(n_frames):
+        Rw, tw = world[f]
+        frames.append(scene.render(sensor, Rw, tw, sigma=sigma, dropout=dropout, clutter=clutter,
+                                   seed=seed * 131 + f))
+        M = relative_pose(world[f], world[k])
+        if pose_noise is not None and f != k:
+            M = perturb_pose(M, pose_noise[0], pose_noise[1], seed * 7 + f)
+        poses.append(M)
+    return Sequence(sensor, frames, k, np.stack(poses))
+
+
+def sequence_cfg2(sequence_id: int = 0, n_frames: int = 10) -> Sequence:
+    """HDL-64E-shaped urban sequence: 1 key frame (the middle one) + 9 P-frames."""
+    seed = config_seed(2, sequence_id, 0)
+    return sequence(HDL64_SENSOR, n_frames, seed, n_walls=20, n_boxes=40, n_poles=60,
+                    step_m=1.0, yaw_deg=0.5, sigma=0.02, dropout=0.0, clutter=0.02)
+
+
+def offgrid_points(n: int, seed: int, r_lo=0.5, r_hi=90.0, elev_lo_deg=-40.0, elev_hi_deg=40.0):
+    """Random points anywhere (not on beam centres): binning and collision tests."""
+    rng = np.random.default_rng(seed)
+    r = rng.uniform(r_lo, r_hi, n)
+    az = rng.uniform(-math.pi, math.pi, n)
+    el = np.radians(rng.uniform(elev_lo_deg, elev_hi_deg, n))
+    pts = np.zeros((n, 4), dtype=np.float32)
+    pts[:, 0] = r * np.cos(el) * np.cos(az)
+    pts[:, 1] = r * np.cos(el) * np.sin(az)
+    pts[:, 2] = r * np.sin(el)
+    return pts

@@ -1,0 +1,451 @@
+"""Pins of the CPU oracle against things other than itself.
+
+Every test here checks the oracle against a closed form, a library routine, a
+brute-force search or an invariant that the paper's definitions fix, so that a
+dropped term, a wrong sign or index, or a transposed operand in the oracle
+fails at least one of them.  No GPU is needed.
+"""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+
+import oracle as O
+import synth
+from tests import streamfmt
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _sensor(rows=16, cols=64, lo=-15.0, hi=15.0, rmax=80.0):
+    return O.Sensor(rows, cols, lo, hi, rmax)
+
+
+def _centre_dirs(s):
+    """fp64 pixel-centre beam directions from the grid definition (Sec. III-B)."""
+    de = (s.elev_max_deg - s.elev_min_deg) / s.rows
+    el = np.radians(s.elev_max_deg - (np.arange(s.rows) + 0.5) * de)
+    az = -math.pi + (np.arange(s.cols) + 0.5) * 2 * math.pi / s.cols
+    E, A = np.meshgrid(el, az, indexing="ij")
+    return np.stack([np.cos(E) * np.cos(A), np.cos(E) * np.sin(A), np.sin(E)], -1)
+
+
+# ---------------------------------------------------------------- Eq. 1-2 --
+
+def test_beam_table_is_unit_and_matches_pixel_centres():
+    s = _sensor(32, 1024, -24.8, 2.0)
+    u = O.beams(s).astype(np.float64)
+    ref = _centre_dirs(s)
+    assert np.abs(np.linalg.norm(u, axis=-1) - 1).max() < 3e-7
+    assert np.abs(u - ref).max() < 2e-7
+
+
+def test_pixel_centre_points_land_in_their_pixel():
+    s = _sensor(16, 512)
+    d = _centre_dirs(s).reshape(-1, 3)
+    r = np.random.default_rng(1).uniform(0.5, 79.0, len(d))
+    pts = np.zeros((len(d), 4), np.float32)
+    pts[:, :3] = (d * r[:, None]).astype(np.float32)
+    img, pix, st = O.range_image(s, pts)
+    assert (pix == np.arange(len(d))).all()
+    assert st[3] == len(d)
+    # Eq. 1: the stored value is the point's range
+    r32 = np.sqrt((pts[:, :3].astype(np.float64) ** 2).sum(1))
+    assert np.abs(img.reshape(-1) - r32).max() < 1e-5
+
+
+def test_binning_matches_eq2_in_fp64_away_from_boundaries():
+    s = _sensor(64, 2048, -24.8, 2.0)
+    pts = synth.offgrid_points(60000, seed=3, r_hi=79.0, elev_lo_deg=-30, elev_hi_deg=8)
+    img, pix, st = O.range_image(s, pts)
+    p = pts[:, :3].astype(np.float64)
+    az = np.arctan2(p[:, 1], p[:, 0])
+    el = np.degrees(np.arctan2(p[:, 2], np.hypot(p[:, 0], p[:, 1])))
+    de = (s.elev_max_deg - s.elev_min_deg) / s.rows
+    rowf = (s.elev_max_deg - el) / de
+    colf = (az + math.pi) / (2 * math.pi / s.cols)
+    infov = (el < s.elev_max_deg) & (el > s.elev_min_deg)
+    far_row = np.abs(rowf - np.round(rowf)) * de > 1e-4      # > 1e-4 deg from a row edge
+    far_col = np.abs(colf - np.round(colf)) * 360 / s.cols > 1e-4
+    sel = far_row & far_col
+    exp = np.where(infov, np.floor(rowf).astype(np.int64) * s.cols + np.floor(colf).astype(np.int64) % s.cols, -1)
+    assert sel.sum() > 50000
+    assert (pix[sel] == exp[sel]).all()
+
+
+def test_boundary_convention_and_azimuth_wrap():
+    s = _sensor(8, 16, -10.0, 10.0)
+    de = 20.0 / 8
+    eps = 1e-4
+    pts, want = [], []
+    for k in range(1, 8):                 # row boundaries b_k between rows k-1 and k
+        b = math.radians(10.0 - k * de)
+        for sgn, row in ((+1, k - 1), (-1, k)):
+            e = b + sgn * math.radians(eps)
+            a = math.radians(-180 + 360 / 16 * 3.5)
+            pts.append([10 * math.cos(e) * math.cos(a), 10 * math.cos(e) * math.sin(a), 10 * math.sin(e), 0])
+            want.append(row * 16 + 3)
+    for j in range(16):                   # column boundaries a_j between cols j-1 and j
+        a = -math.pi + j * 2 * math.pi / 16
+        for sgn, col in ((+1, j), (-1, (j - 1) % 16)):
+            aa = a + sgn * math.radians(eps)
+            e = math.radians(10.0 - 4.5 * de)
+            pts.append([10 * math.cos(e) * math.cos(aa), 10 * math.cos(e) * math.sin(aa), 10 * math.sin(e), 0])
+            want.append(4 * 16 + col)
+    # outside the vertical field of view
+    for e in (10.0 + eps, -10.0 - eps, 45.0, -60.0):
+        er = math.radians(e)
+        pts.append([10 * math.cos(er), 0, 10 * math.sin(er), 0])
+        want.append(-1)
+    _, pix, st = O.range_image(s, np.array(pts, np.float32))
+    assert pix.tolist() == want
+    assert st[2] == 4
+
+
+def test_collision_keeps_nearest_and_drops_invalid():
+    s = _sensor(16, 64)
+    d = _centre_dirs(s).reshape(-1, 3)
+    rng = np.random.default_rng(5)
+    sel = rng.choice(len(d), 200, replace=False)
+    ranges = rng.uniform(1, 70, (200, 4))
+    pts = []
+    for i, k in enumerate(sel):
+        for r in ranges[i]:
+            pts.append(np.append(d[k] * r, 0))
+    pts = np.array(pts, np.float32)
+    perm = rng.permutation(len(pts))
+    img, pix, st = O.range_image(s, pts[perm])
+    got = img.reshape(-1)[sel]
+    want = np.sqrt((pts[:, :3].astype(np.float64) ** 2).sum(1)).reshape(200, 4).min(1)
+    assert np.abs(got - want).max() < 1e-5
+    assert st[0] == 800 and st[3] == 200
+    bad = np.array([[np.nan, 1, 1, 0], [np.inf, 0, 0, 0], [0, 0, 0, 0], [100, 0, 0, 0]], np.float32)
+    _, pix, st = O.range_image(s, bad)
+    assert (pix == -1).all() and st[1] == 4
+
+
+# --------------------------------------------------------- TLS plane fit --
+
+def _cov(p):
+    c = p.mean(0)
+    q = p - c
+    return q.T @ q / len(p), c
+
+
+def test_tls_matches_numpy_eigh():
+    rng = np.random.default_rng(7)
+    for trial in range(300):
+        n = int(rng.integers(3, 40))
+        p = rng.normal(0, 1, (n, 3)) * rng.uniform(0.01, 3, 3) + rng.uniform(-40, 40, 3)
+        nrm, d, lam = O.tls_fit(p)
+        C, c = _cov(p)
+        w, V = np.linalg.eigh(C)
+        assert np.allclose(lam, w, rtol=1e-9, atol=1e-12 * w.max())
+        if w[1] - w[0] > 1e-6 * w[2]:
+            assert abs(abs(nrm @ V[:, 0]) - 1) < 1e-10
+        assert abs(d - nrm @ c) < 1e-9 * max(1, abs(d))
+        assert d >= 0 or abs(d) < 1e-9
+        assert abs(np.linalg.norm(nrm) - 1) < 1e-12
+
+
+def test_tls_matches_brute_force_search():
+    from scipy.optimize import minimize
+    rng = np.random.default_rng(11)
+    th, ph = np.meshgrid(np.linspace(0, math.pi, 181), np.linspace(0, 2 * math.pi, 361), indexing="ij")
+    grid = np.stack([np.sin(th) * np.cos(ph), np.sin(th) * np.sin(ph), np.cos(th)], -1).reshape(-1, 3)
+    for trial in range(12):
+        n = int(rng.integers(3, 7))
+        p = rng.normal(0, 1, (n, 3)) * np.array([2.0, 1.0, 0.2]) + rng.uniform(-5, 5, 3)
+        q = p - p.mean(0)
+        cost = ((q @ grid.T) ** 2).sum(0)
+        g = grid[np.argmin(cost)]
+        t0, p0 = math.acos(np.clip(g[2], -1, 1)), math.atan2(g[1], g[0])
+
+        def f(x):
+            v = np.array([math.sin(x[0]) * math.cos(x[1]), math.sin(x[0]) * math.sin(x[1]), math.cos(x[0])])
+            return ((q @ v) ** 2).sum()
+
+        res = minimize(f, [t0, p0], method="Nelder-Mead", options={"xatol": 1e-12, "fatol": 1e-20,
+                                                                   "maxiter": 20000})
+        v = np.array([math.sin(res.x[0]) * math.cos(res.x[1]), math.sin(res.x[0]) * math.sin(res.x[1]),
+                      math.cos(res.x[0])])
+        nrm, d, lam = O.tls_fit(p)
+        assert abs(abs(nrm @ v) - 1) < 1e-10
+        assert f([math.acos(np.clip(nrm[2], -1, 1)), math.atan2(nrm[1], nrm[0])]) <= res.fun * (1 + 1e-9) + 1e-18
+
+
+def test_tls_recovers_exact_planes_with_canonical_sign():
+    rng = np.random.default_rng(13)
+    for trial in range(100):
+        n = rng.normal(size=3)
+        n /= np.linalg.norm(n)
+        d = rng.uniform(-30, 30)
+        a = np.cross(n, [1, 0, 0] if abs(n[0]) < 0.9 else [0, 1, 0])
+        a /= np.linalg.norm(a)
+        b = np.cross(n, a)
+        uv = rng.uniform(-1, 1, (10, 2))
+        p = d * n + uv[:, :1] * a + uv[:, 1:] * b
+        nrm, dd, lam = O.tls_fit(p)
+        s = 1 if d >= 0 else -1
+        assert np.abs(nrm - s * n).max() < 1e-10
+        assert abs(dd - abs(d)) < 1e-10
+        assert lam[0] <= 1e-14 * lam[2]
+
+
+def test_tile_golden_examples():
+    """Hand-built tiles (tests/golden/tile_examples.json) with closed-form planes (Eq. 3)."""
+    with open(os.path.join(GOLDEN, "tile_examples.json")) as fh:
+        cases = json.load(fh)["cases"]
+    for case in cases:
+        p = np.array(case["points"], np.float64)
+        nrm, d, lam = O.tls_fit(p)
+        want = np.array(case["normal"], np.float64)
+        assert np.abs(nrm - want).max() < 1e-9, case["name"]
+        assert abs(d - case["d"]) < 1e-9, case["name"]
+
+
+# -------------------------------------------------- iterative tile fit --
+
+def test_noise_free_ground_tiles_fit_exactly_in_one_round():
+    sen = synth.Sensor(64, 2048, -24.8, 2.0, 80.0)
+    s = O.sensor(sen)
+    p = O.params()
+    pts = synth.Scene(5, 0, 0, 0).render(sen, sigma=0.0)
+    bits, kft, fits, modes = O.encode_keyframe(s, p, pts)
+    has = fits["n_valid"] >= 3
+    assert (fits["status"][has] == O.FIT_OK).all()
+    assert (fits["rounds"][has] == 1).all()
+    assert np.abs(fits["plane"][has] - np.array([0, 0, -1, 1.7], np.float32)).max() < 1e-5
+    rng, _, _ = O.range_image(s, pts)
+    dec, _, _ = O.decode(s, bits)
+    m = rng > 0
+    # every point is fitted with residual code 0: the decoded range is the ray-cast plane range
+    h = streamfmt.header(bits)
+    assert h["n_fitted"] == m.sum() and h["n_raw"] == 0
+    assert (streamfmt.residual_codes(bits) == 0).all()
+    assert np.abs(dec[m] - rng[m]).max() < 0.01
+
+
+def test_planted_outlier_is_dropped_and_plane_refit():
+    """One pixel of a noise-free planar tile moved 0.5 m along its ray: the
+    rounds must drop it, refit on the 15 others and recover the exact plane."""
+    s = O.Sensor(4, 256, -10.0, 10.0, 80.0)
+    p = O.params(min_inlier_frac=0.75)
+    u = O.beams(s).astype(np.float64)
+    n = np.array([0.9, 0.3, 0.1])
+    n /= np.linalg.norm(n)
+    d = 12.0
+    dots = u @ n
+    rng_img = np.where(dots > 0.1, d / np.where(dots > 0.1, dots, 1), 0).astype(np.float32)
+    tc = int(np.argmax(dots[1])) // 4
+    rng_img[1, 4 * tc + 2] -= 0.5
+    fits = O.fit_tiles(s, p, rng_img)
+    tile = fits[tc]
+    assert tile["status"] == O.FIT_OK
+    assert tile["n_valid"] == 16 and tile["n_inlier"] == 15
+    assert tile["rounds"] in (2, 3)
+    assert np.abs(tile["plane"] - np.array([*n, d], np.float32)).max() < 2e-5
+    # the moved pixel is raw-coded, the others are fitted
+    bits, kft, modes = O.pack(s, p, 0, rng_img, fits["plane"], fits["status"] == O.FIT_OK)
+    dec, _, _ = O.decode(s, bits)
+    assert abs(dec[1, 4 * tc + 2] - rng_img[1, 4 * tc + 2]) <= 0.01 + 1e-5
+    # its neighbours (no outlier) fit in one round
+    assert fits[tc - 2]["rounds"] == 1 and fits[tc - 2]["n_inlier"] == 16
+
+
+def test_all_points_reading_rejects_tile_with_outlier():
+    s = O.Sensor(4, 256, -10.0, 10.0, 80.0)
+    u = O.beams(s).astype(np.float64)
+    n = np.array([1.0, 0.0, 0.0])
+    rng_img = (10.0 / (u @ n)).astype(np.float32)
+    rng_img[rng_img < 0] = 0
+    rng_img[2, 129] += 0.3
+    fits_all = O.fit_tiles(s, O.params(min_inlier_frac=1.0), rng_img)
+    fits_75 = O.fit_tiles(s, O.params(min_inlier_frac=0.75), rng_img)
+    t = 128 // 4  # the tile covering azimuth 0 (x axis)
+    assert fits_all[t]["status"] == O.FIT_FAIL
+    assert fits_75[t]["status"] == O.FIT_OK
+
+
+# ------------------------------------------------------- coding, decode --
+
+@pytest.mark.parametrize("tile,thr", [((4, 4), 0.05), ((8, 8), 0.05), ((4, 4), 0.02), ((4, 8), 0.10),
+                                      ((8, 16), 0.05)])
+def test_decode_error_within_half_step(cfg1, tile, thr):
+    sen, pts = cfg1
+    s = O.sensor(sen)
+    p = O.params(tile[0], tile[1], fit_thr_m=thr)
+    bits, kft, fits, modes = O.encode_keyframe(s, p, pts)
+    rng, _, _ = O.range_image(s, pts)
+    dec, xyz, valid = O.decode(s, bits)
+    m = rng > 0
+    assert ((dec > 0) == m).all()
+    assert np.abs(dec[m] - rng[m]).max() <= 0.01 + 1e-5
+    # Eq. 1-2 inverted: the decoded point lies on the pixel's beam at the decoded range
+    u = O.beams(s)
+    assert np.abs(xyz[..., :3] - dec[..., None] * u).max() == 0
+
+
+def test_partial_edge_tiles_round_trip():
+    sen = synth.Sensor(18, 515, -15.0, 15.0, 80.0)
+    pts = synth.Scene(9, 4, 6, 10, enclose=True).render(sen, sigma=0.02, dropout=0.05, seed=9)
+    s = O.sensor(sen)
+    for tile in ((4, 4), (8, 16)):
+        p = O.params(*tile)
+        bits, kft, fits, modes = O.encode_keyframe(s, p, pts)
+        rng, _, _ = O.range_image(s, pts)
+        dec, _, _ = O.decode(s, bits)
+        m = rng > 0
+        assert np.abs(dec[m] - rng[m]).max() <= 0.01 + 1e-5
+
+
+def test_raw_round_trip_and_reencode_identity(cfg1):
+    sen, pts = cfg1
+    s = O.sensor(sen)
+    p = O.params(min_inlier_frac=2.0)       # no plane can qualify: every tile is raw
+    bits, kft, fits, modes = O.encode_keyframe(s, p, pts)
+    assert set(np.unique(modes)) <= {O.T_RAW, O.T_EMPTY}
+    rng, _, _ = O.range_image(s, pts)
+    dec, xyz, _ = O.decode(s, bits)
+    m = rng > 0
+    q = np.float32(0.02)
+    want = (np.floor(rng[m] / q + np.float32(0.5)) * q).astype(np.float32)
+    assert (dec[m] == want).all()
+    pts2 = xyz.reshape(-1, 4)[m.reshape(-1)]
+    bits2, _, _, _ = O.encode_keyframe(s, p, pts2)
+    assert bits2.tobytes() == bits.tobytes()
+
+
+def test_greedy_run_invariants(cfg2_seq):
+    seq = cfg2_seq
+    s = O.sensor(seq.sensor)
+    p = O.params()
+    pts = seq.frames[seq.key_index]
+    bits, kft, fits, modes = O.encode_keyframe(s, p, pts)
+    rng, _, _ = O.range_image(s, pts)
+    u = O.beams(s).astype(np.float64)
+    TW = s.cols // p.tile_w
+
+    def passes(t, plane):
+        tr, tc = divmod(t, TW)
+        r = rng[tr * 4:(tr + 1) * 4, tc * 4:(tc + 1) * 4].astype(np.float64).reshape(-1)
+        uu = u[tr * 4:(tr + 1) * 4, tc * 4:(tc + 1) * 4].reshape(-1, 3)
+        v = r > 0
+        if v.sum() < 3:
+            return False, False
+        dot = uu[v] @ plane[:3].astype(np.float64)
+        e = np.where(dot > 1e-3, r[v] - plane[3] / np.where(dot > 1e-3, dot, 1), np.inf)
+        near = np.any(np.abs(np.abs(e) - 0.05) < 1e-4)
+        need = max(3, math.ceil(0.75 * v.sum()))
+        return (np.abs(e) <= 0.05).sum() >= need, near
+
+    ok = fits["status"] == O.FIT_OK
+    assert ((modes == O.T_RUN_START) <= ok).all()          # a run starts at an own-fit tile
+    assert ((modes == O.T_RAW) <= ~ok).all()               # raw tiles failed their own fit
+    checked = 0
+    for t in range(len(modes)):
+        if modes[t] == O.T_RUN_START:
+            plane = kft[t]
+            k = t + 1
+            while k % TW and modes[k] == O.T_RUN_CONT:
+                assert (kft[k] == plane).all()
+                good, near = passes(k, plane)
+                assert good or near
+                k += 1
+            if k % TW:
+                good, near = passes(k, plane)
+                assert (not good) or near
+                checked += 1
+    assert checked > 500
+
+
+def test_corrupt_streams_are_rejected(cfg1):
+    sen, pts = cfg1
+    s = O.sensor(sen)
+    p = O.params()
+    bits, kft, fits, modes = O.encode_keyframe(s, p, pts)
+    assert O.decode_status(s, bits[:-4]) == O.ERR_CORRUPT
+    bad = bits.copy()
+    bad[0] ^= 1
+    assert O.decode_status(s, bad) == O.ERR_CORRUPT
+    bad = bits.copy()
+    bad[64 + (16 * 512 // 8) + 0] = 0x33       # first tile codes: RUN_CONT at the row start
+    assert O.decode_status(s, bad) == O.ERR_CORRUPT
+    assert O.decode_status(s, bits[:40]) == O.ERR_CORRUPT
+
+
+def test_empty_frame():
+    s = _sensor(16, 512)
+    p = O.params()
+    bits, kft, fits, modes = O.encode_keyframe(s, p, np.zeros((0, 4), np.float32))
+    assert (modes == O.T_EMPTY).all()
+    assert len(bits) == 64 + 4 * (16 * 512 // 32 + 512 // 8)
+    dec, _, valid = O.decode(s, bits)
+    assert (dec == 0).all() and (valid == 0).all()
+
+
+# ----------------------------------------------------------- temporal --
+
+def _pitch(deg):
+    a = math.radians(deg)
+    return np.array([[math.cos(a), 0, math.sin(a)], [0, 1, 0], [-math.sin(a), 0, math.cos(a)]])
+
+
+@pytest.mark.parametrize("R", [np.eye(3), synth.yaw_matrix(math.radians(3.0)) @ _pitch(1.5)])
+def test_temporal_offset_is_exact_under_known_motion(R):
+    """Ground plane only: every P tile whose anchor lands in the K image is
+    temporally coded with n' = R^T n and c' = d - n.T."""
+    sen = synth.HDL64_SENSOR
+    s = O.sensor(sen)
+    p = O.params()
+    scene = synth.Scene(5, 0, 0, 0)
+    kpts = scene.render(sen, sigma=0.0)
+    T = np.array([1.0, 0.4, 0.05])
+    ppts = scene.render(sen, R=R, t=T, sigma=0.0)
+    M = np.eye(4)
+    M[:3, :3] = R
+    M[:3, 3] = T
+    _, kft, _, _ = O.encode_keyframe(s, p, kpts)
+    bits, fits, tmp, modes = O.encode_pframe(s, p, kft, M, ppts)
+    found = tmp["kref"] >= 0
+    assert (tmp["status"][found & (tmp["n_valid"] >= 3)] == 2).all()
+    assert found.sum() > 0.9 * (tmp["n_valid"] > 0).sum()
+    sel = tmp["status"] == 2
+    assert (modes[sel] == O.T_TEMPORAL).all()
+    n = np.array([0, 0, -1.0])
+    assert np.abs(tmp["plane"][sel][:, :3] - (R.T @ n).astype(np.float32)).max() < 1e-6
+    assert np.abs(tmp["plane"][sel][:, 3] - (1.7 - n @ T)).max() < 2e-5
+    rng, _, _ = O.range_image(s, ppts)
+    dec, _, _ = O.decode(s, bits, kft, M)
+    m = rng > 0
+    assert np.abs(dec[m] - rng[m]).max() <= 0.01 + 1e-5
+
+
+def test_identity_pose_makes_every_plane_tile_temporal():
+    sen = synth.HDL64_SENSOR
+    s = O.sensor(sen)
+    p = O.params()
+    pts = synth.Scene(7, 4, 0, 0, enclose=True).render(sen, sigma=0.0)
+    _, kft, kfits, kmodes = O.encode_keyframe(s, p, pts)
+    bits, fits, tmp, modes = O.encode_pframe(s, p, kft, np.eye(4), pts)
+    plane = (kmodes == O.T_RUN_START) | (kmodes == O.T_RUN_CONT)
+    assert (tmp["kref"][plane] == np.nonzero(plane)[0]).all()
+    assert (modes[plane] == O.T_TEMPORAL).mean() > 0.99
+
+
+def test_pframe_decode_error_and_kf_table_from_stream(cfg2_seq):
+    seq = cfg2_seq
+    s = O.sensor(seq.sensor)
+    p = O.params()
+    kbits, kft, _, _ = O.encode_keyframe(s, p, seq.frames[seq.key_index])
+    kft2 = O.kf_table_from_stream(s, kbits, len(kft))
+    assert (kft2 == kft).all()
+    for f in (0, seq.key_index + 1, len(seq.frames) - 1):
+        bits, fits, tmp, modes = O.encode_pframe(s, p, kft, seq.poses[f], seq.frames[f])
+        assert (modes == O.T_TEMPORAL).sum() > 1000
+        rng, _, _ = O.range_image(s, seq.frames[f])
+        dec, _, _ = O.decode(s, bits, kft2, seq.poses[f])
+        m = rng > 0
+        assert np.abs(dec[m] - rng[m]).max() <= 0.01 + 1e-5
