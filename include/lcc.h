@@ -1,0 +1,199 @@
+/*
+ * lcc — GB300-native spatio-temporal LiDAR point-cloud compression.
+ *
+ * C ABI of the encoder/decoder described in "Real-Time Spatio-Temporal LiDAR
+ * Point Cloud Compression" (Feng, Liu, Zhu): a key frame (K) is spatially
+ * encoded by iterative plane fitting over range-image tiles (Sec. III-B,
+ * III-C); predicted frames (P) are encoded against the key frame's planes
+ * moved by the inter-frame pose, with the leftover tiles spatially encoded
+ * (Sec. III-D).  All compute runs as CUDA kernels for sm_103a.
+ *
+ * Conventions
+ *  - Pointers named d_* are device pointers; the caller owns them.  Host
+ *    arrays are named h_* or are plain C arrays (poses, pointer tables).
+ *  - Every call is asynchronous on the context's CUDA stream unless stated.
+ *    Argument errors are returned at once.  Errors found on the device
+ *    (output capacity, corrupt stream) are latched in the context and
+ *    returned by lcc_sync().
+ *  - One context per stream; a context is not thread-safe.
+ *  - Points are float4 (x, y, z, unused), metres, sensor coordinates.
+ *  - Poses are row-major 4x4 doubles M with p_K = R p + T (Eq. 6), mapping a
+ *    P frame's coordinates into the key frame's.
+ */
+#ifndef LCC_H
+#define LCC_H
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    LCC_OK = 0,
+    LCC_ERR_INVALID_ARG = 1,  /* bad pointer, size or parameter */
+    LCC_ERR_CAPACITY = 2,     /* an output buffer is too small; the needed size is reported */
+    LCC_ERR_CUDA = 3,         /* a CUDA runtime call failed */
+    LCC_ERR_TIMEOUT = 4,      /* a bounded device wait gave up */
+    LCC_ERR_CORRUPT = 5,      /* a stream failed validation while decoding */
+    LCC_ERR_UNSUPPORTED = 6,  /* valid request this build does not handle */
+    LCC_ERR_NO_DEVICE = 7     /* no usable sm_103 GPU */
+} lcc_status;
+
+/* Range-image geometry (Sec. III-B): rows = beams (row 0 = top), cols =
+ * azimuth steps over 360 degrees starting at -180.  Row i spans elevations
+ * (b_{i+1}, b_i], b_k = elev_max - k (elev_max - elev_min) / rows; column j
+ * spans azimuths [-pi + j 2pi/cols, -pi + (j+1) 2pi/cols). */
+typedef struct {
+    int32_t rows, cols;
+    double elev_min_deg, elev_max_deg;
+    double max_range_m;
+} lcc_sensor;
+
+/* Encoder parameters. */
+typedef struct {
+    int32_t tile_h, tile_w;   /* unit tile (Sec. III-C); supported: 4x4, 4x8, 8x8, 8x16 */
+    float fit_thr_m;          /* threshold on the along-ray residual |r - d/(n.u)| */
+    float quant_m;            /* quantisation step q of residual and raw codes (decode error <= q/2) */
+    int32_t max_refits;       /* refit rounds after the first plane fit (0..7) */
+    float min_inlier_frac;    /* share of a tile's points a plane must keep (1.0 = all, the paper's rule) */
+    int32_t merge_runs;       /* 1: grow runs of tiles horizontally with the run's plane (Sec. III-C) */
+    int32_t max_batch;        /* frames per batched launch the context reserves scratch for (1..64) */
+    int32_t lookahead;        /* tiles ahead the fit kernel pre-tests for run growth (0..16) */
+} lcc_params;
+
+/* Per-frame statistics of the last encode (Fig. 11's categories and more). */
+typedef struct {
+    int64_t points_in;        /* points passed in */
+    int64_t points_invalid;   /* non-finite, r <= 0 or r > max range */
+    int64_t points_fov;       /* outside the vertical field of view */
+    int64_t points_binned;    /* binned (before collisions) */
+    int64_t pixels_valid;     /* occupied pixels; binned - valid = points lost to collisions */
+    int64_t tiles_empty, tiles_raw, tiles_run_start, tiles_run_cont, tiles_temporal;
+    int64_t fit_rounds[8];    /* tiles by number of plane fits (index = fits, 0..7) */
+    int64_t tiles_borderline; /* tiles with a residual within 1e-6 m of the threshold in some round */
+    int64_t cand, fitted, raw;/* candidate, plane-coded and raw-coded pixels */
+    uint64_t bytes;           /* stream size */
+} lcc_stats;
+
+/* Per-tile record (debug and parity checks): the tile's own fit results. */
+typedef struct {
+    float plane[4];           /* own spatial plane n.p = d, or (n', c') for a temporal tile */
+    float tplane[4];          /* temporal test plane (n', c') if a K tile was found */
+    uint32_t kref;            /* K tile the anchor maps to, 0xFFFFFFFF if none */
+    uint32_t ahead_mask;      /* run pre-test bits: bit k-1 = tile +k passes this tile's plane */
+    uint8_t status;           /* 0 empty, 1 fit failed, 2 fit ok, 3 temporal */
+    uint8_t rounds;           /* spatial plane fits performed */
+    uint8_t flags;            /* bit0 borderline, bit1 degenerate scatter, bit2 temporal tested */
+    uint8_t n_valid;          /* valid pixels */
+    uint8_t n_inlier;         /* inliers of the final spatial (or temporal) plane */
+    uint8_t t_rounds;         /* temporal offset fits */
+    uint8_t t_inlier;         /* inliers of the temporal plane */
+    uint8_t t_status;         /* 0 no K plane, 1 failed, 2 passed */
+    uint8_t ahead_cnt[16];    /* inlier counts of the pre-tested tiles */
+} lcc_tile_info;
+
+typedef struct lcc_ctx lcc_ctx;
+typedef struct lcc_keyframe lcc_keyframe;
+
+/* Human-readable name of a status. */
+const char *lcc_status_string(lcc_status s);
+
+/* Default parameters: 4x4 tiles, thr 0.05 m, q 0.02 m, 3 refits, f_min 0.75,
+ * runs on, max_batch 16, lookahead 8. */
+void lcc_default_params(lcc_params *p);
+
+/* Create a context on the current device bound to cuda_stream (a
+ * cudaStream_t, NULL = default stream).  Allocates device scratch for
+ * max_batch frames.  Fails with LCC_ERR_NO_DEVICE without an sm_103 GPU. */
+lcc_status lcc_create(lcc_ctx **out, const lcc_sensor *sensor, const lcc_params *params, void *cuda_stream);
+lcc_status lcc_destroy(lcc_ctx *ctx);
+
+/* Upper bound of one frame's stream size in bytes (for output buffers). */
+uint64_t lcc_max_encoded_bytes(const lcc_ctx *ctx);
+
+/* Number of tiles of one frame. */
+int64_t lcc_num_tiles(const lcc_ctx *ctx);
+
+/* Beam and boundary tables of the sensor (host copies, fp32): ce/se [rows]
+ * (cos/sin of row-centre elevation), ct/st [cols] (column-centre azimuth),
+ * rbc/rbs [rows+1] (row boundaries), cbc/cbs [cols] (column boundaries).
+ * Beam of pixel (i,j) = (ce_i ct_j, ce_i st_j, se_i) in fp32.  Synchronous. */
+lcc_status lcc_tables(const lcc_ctx *ctx, float *ce, float *se, float *ct, float *st,
+                      float *rbc, float *rbs, float *cbc, float *cbs);
+
+/* Eq. 1-2: range image of one frame.  d_range [rows*cols] fp32 (0 = empty,
+ * nearest point wins on collision, Sec. III-D); d_valid [ceil(rows*cols/32)]
+ * occupancy bitmap, raster order, LSB first.  Either output may be NULL. */
+lcc_status lcc_range_image(lcc_ctx *ctx, const float *d_pts, int64_t n, float *d_range, uint32_t *d_valid);
+
+/* Key-frame handles hold a frame's per-tile coding planes on the device. */
+lcc_status lcc_keyframe_create(lcc_ctx *ctx, lcc_keyframe **out);
+void lcc_keyframe_free(lcc_keyframe *kf);
+
+/* Spatial encode of a key frame (Sec. III-B, III-C).  d_out receives up to
+ * cap bytes; *out_bytes (host or device uint64, caller-owned) receives the
+ * stream size once the stream syncs (the needed size if cap was too small;
+ * lcc_sync then returns LCC_ERR_CAPACITY).  kf (nullable) receives the coding
+ * planes for later P frames. */
+lcc_status lcc_encode_keyframe(lcc_ctx *ctx, const float *d_pts, int64_t n, lcc_keyframe *kf,
+                               uint8_t *d_out, uint64_t cap, uint64_t *out_bytes);
+
+/* Temporal + spatial encode of one P frame against kf (Sec. III-D). */
+lcc_status lcc_encode_pframe(lcc_ctx *ctx, const lcc_keyframe *kf, const double pose[16],
+                             const float *d_pts, int64_t n, uint8_t *d_out, uint64_t cap,
+                             uint64_t *out_bytes);
+
+/* Batched: nframes P frames against one key frame in one launch per kernel.
+ * poses: nframes x 16 doubles; d_pts, n, d_out, cap: per-frame host arrays;
+ * out_bytes: nframes uint64 (host or device).  nframes <= max_batch. */
+lcc_status lcc_encode_pframes(lcc_ctx *ctx, const lcc_keyframe *kf, int32_t nframes, const double *poses,
+                              const float *const *d_pts, const int64_t *n, uint8_t *const *d_out,
+                              const uint64_t *cap, uint64_t *out_bytes);
+
+/* A whole sequence (Fig. 1): frame key_index is the K frame, all others are P
+ * frames; poses[f] maps frame f to the key frame (poses[key_index] unused).
+ * Bins all frames in one launch, encodes K, then all P frames batched.
+ * nframes <= max_batch.  kf (nullable) receives the key frame's planes. */
+lcc_status lcc_encode_sequence(lcc_ctx *ctx, int32_t nframes, int32_t key_index, const double *poses,
+                               const float *const *d_pts, const int64_t *n, uint8_t *const *d_out,
+                               const uint64_t *cap, uint64_t *out_bytes, lcc_keyframe *kf);
+
+/* End-to-end variant with HOST buffers: copies the points host->device,
+ * encodes the sequence and copies each stream device->host.  h_out[f] must
+ * hold cap[f] bytes; out_bytes is a host array.  Synchronous. */
+lcc_status lcc_encode_sequence_host(lcc_ctx *ctx, int32_t nframes, int32_t key_index, const double *poses,
+                                    const float *const *h_pts, const int64_t *n, uint8_t *const *h_out,
+                                    const uint64_t *cap, uint64_t *out_bytes);
+
+/* Rebuild a key frame's planes from its stream (for decoding P frames). */
+lcc_status lcc_keyframe_from_stream(lcc_ctx *ctx, const uint8_t *d_bits, uint64_t nbytes, lcc_keyframe *kf);
+
+/* Decode one stream (ray casting, Sec. III-C).  kf and pose are required for
+ * P-frame streams (NULL for K).  Outputs (any may be NULL): d_range
+ * [rows*cols] fp32 (0 = empty), d_xyz4 [rows*cols] float4 (x, y, z, 0),
+ * d_valid occupancy bitmap.  A corrupt stream latches LCC_ERR_CORRUPT. */
+lcc_status lcc_decode(lcc_ctx *ctx, const uint8_t *d_bits, uint64_t nbytes, const lcc_keyframe *kf,
+                      const double pose[16], float *d_range, float *d_xyz4, uint32_t *d_valid);
+
+/* Wait for the context's stream and return (then clear) any latched device error. */
+lcc_status lcc_sync(lcc_ctx *ctx);
+
+/* Statistics of frame `frame` (batch position) of the last encode call.  Synchronous. */
+lcc_status lcc_last_stats(lcc_ctx *ctx, int32_t frame, lcc_stats *out);
+
+/* Per-tile records of frame `frame` of the last encode call (host array of
+ * at least lcc_num_tiles entries).  Synchronous. */
+lcc_status lcc_tile_records(lcc_ctx *ctx, int32_t frame, lcc_tile_info *h_out, int64_t cap);
+
+/* Kernel timing: when enabled, every kernel launch is bracketed by CUDA events
+ * on the context stream.  lcc_kernel_times returns, per kernel name, the
+ * number of launches and summed milliseconds since the last reset
+ * (synchronous).  Names: "bin", "fit", "merge", "scan", "pack", "decode_prep",
+ * "decode_px".  Returns the number of entries written. */
+lcc_status lcc_set_profiling(lcc_ctx *ctx, int32_t enable);
+int32_t lcc_kernel_times(lcc_ctx *ctx, char names[][16], int64_t *launches, double *ms, int32_t cap);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

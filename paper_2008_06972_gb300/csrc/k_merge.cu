@@ -1,0 +1,153 @@
+// Greedy horizontal run growth (Sec. III-C) — one warp per tile row.
+//
+// The paper grows a run of tiles to the right while the plane "fit so far"
+// (the run's first plane) still codes the next tile under the threshold, and
+// restarts at the first tile that fails.  The walk is sequential along a row,
+// so each step is made warp-wide: the 32 lanes look at 32 consecutive tiles,
+// a ballot finds the first candidate run start, the start's precomputed
+// look-ahead bits (from the fit kernel) decide the first `lookahead` joins,
+// and only runs longer than that test further tiles explicitly, 32 tiles per
+// step with one lane per tile.  Temporal tiles of P frames are already coded
+// (Sec. III-D) and end a run.
+//
+// Output per tile: its stream mode, the tile whose plane codes it, and its
+// counts of candidate / plane-coded / raw-coded pixels.
+#include "lcc_internal.cuh"
+
+namespace lcc {
+
+constexpr int kMergeWarps = 4;
+
+struct RecHead {
+    uint8_t status, n_valid, n_inlier;
+};
+
+__device__ __forceinline__ RecHead load_head(const TileRec *r) {
+    const uint2 w = *reinterpret_cast<const uint2 *>(reinterpret_cast<const uint8_t *>(r) + 40);
+    return {(uint8_t)(w.x & 0xff), (uint8_t)(w.x >> 24), (uint8_t)(w.y & 0xff)};
+}
+
+__device__ __forceinline__ void put_code(TileCode *codes, int t, uint8_t mode, int cand, int fitted, int raw,
+                                         uint32_t plane_tile) {
+    const uint32_t w0 = (uint32_t)mode | ((uint32_t)cand << 8) | ((uint32_t)fitted << 16) | ((uint32_t)raw << 24);
+    *reinterpret_cast<uint2 *>(codes + t) = make_uint2(w0, plane_tile);
+}
+
+// Code of a tile that is not part of a spatial run.
+__device__ __forceinline__ void put_plain(TileCode *codes, float4 *kfo, int t, RecHead h) {
+    if (h.status == S_TEMPORAL)
+        put_code(codes, t, T_TEMPORAL, h.n_valid, h.n_inlier, h.n_valid - h.n_inlier, (uint32_t)t);
+    else
+        put_code(codes, t, h.n_valid ? T_RAW : T_EMPTY, 0, 0, h.n_valid, (uint32_t)t);
+    if (kfo) kfo[t] = make_float4(0.f, 0.f, 0.f, 0.f);
+}
+
+template <int TH_, int TW_>
+__global__ void __launch_bounds__(kMergeWarps * 32) k_merge(Geometry g, Scratch s, Batch b) {
+    const unsigned FULL = 0xffffffffu;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int f = blockIdx.y;
+    const int tr = blockIdx.x * kMergeWarps + warp;
+    if (tr >= g.TR) return;  // whole warp
+    const size_t slot = (size_t)b.slot[f];
+    const TileRec *recs = s.tiles + slot * g.NT;
+    TileCode *codes = s.codes + slot * g.NT;
+    const uint32_t *rimg = s.rimg + slot * g.H * g.W;
+    float4 *kfo = (b.kind == 0) ? b.kf_out : nullptr;
+    const int row0 = tr * g.TC;
+
+    int j = 0;
+    while (j < g.TC) {
+        const int c = j + lane;
+        RecHead h = {S_EMPTY, 0, 0};
+        if (c < g.TC) h = load_head(recs + row0 + c);
+        const uint32_t fitb = __ballot_sync(FULL, c < g.TC && h.status == S_FIT);
+        const int first = fitb ? __ffs(fitb) - 1 : 32;
+        if (c < g.TC && lane < first) put_plain(codes, kfo, row0 + c, h);
+        if (!fitb) {
+            j += 32;
+            continue;
+        }
+        const int s0 = j + first;
+        const TileRec *start = recs + row0 + s0;
+        const float4 pl = start->plane;
+        if (lane == first) {
+            put_code(codes, row0 + s0, T_RUN_START, h.n_valid, h.n_inlier, h.n_valid - h.n_inlier, (uint32_t)(row0 + s0));
+            if (kfo) kfo[row0 + s0] = pl;
+        }
+        int k = s0 + 1;
+        bool open = g.merge && k < g.TC;
+        // phase 1: joins decided by the fit kernel's look-ahead bits
+        const int hz = g.merge ? min(g.lookahead, g.TC - 1 - s0) : 0;
+        if (hz > 0) {
+            const uint32_t amask = start->ahead_mask;
+            const int c1 = s0 + 1 + lane;
+            bool pass = false;
+            RecHead h1 = {S_EMPTY, 0, 0};
+            int cnt = 0;
+            if (lane < hz) {
+                h1 = load_head(recs + row0 + c1);
+                pass = ((amask >> lane) & 1u) && h1.status != S_TEMPORAL;
+                cnt = start->ahead_cnt[lane];
+            }
+            const uint32_t failb = __ballot_sync(FULL, lane < hz && !pass);
+            const int nj = failb ? __ffs(failb) - 1 : hz;
+            if (lane < nj) {
+                put_code(codes, row0 + c1, T_RUN_CONT, h1.n_valid, cnt, h1.n_valid - cnt, (uint32_t)(row0 + s0));
+                if (kfo) kfo[row0 + c1] = pl;
+            }
+            k = s0 + 1 + nj;
+            open = (failb == 0) && k < g.TC;
+        }
+        // phase 2: explicit tests, one tile per lane, 32 tiles per step
+        while (open) {
+            const int c2 = k + lane;
+            bool pass = false;
+            int nvv = 0, nin = 0;
+            RecHead h2 = {S_EMPTY, 0, 0};
+            if (c2 < g.TC) {
+                h2 = load_head(recs + row0 + c2);
+                if (h2.status != S_TEMPORAL) {
+                    for (int q = 0; q < TH_ * TW_; q++) {
+                        const int i = tr * TH_ + q / TW_, jj = c2 * TW_ + q % TW_;
+                        if (i >= g.H || jj >= g.W) continue;
+                        const uint32_t bits = __ldg(rimg + (size_t)i * g.W + jj);
+                        if (!bits_valid(bits)) continue;
+                        nvv++;
+                        float ux, uy, uz, e;
+                        beam(g, i, jj, ux, uy, uz);
+                        nin += residual(pl, ux, uy, uz, __uint_as_float(bits), g.thr, e) ? 1 : 0;
+                    }
+                    pass = nvv >= 3 && nin >= need_inliers(g.fmin, nvv);
+                }
+            }
+            const uint32_t failb = __ballot_sync(FULL, !pass);
+            const int nj = failb ? __ffs(failb) - 1 : 32;
+            if (lane < nj) {
+                put_code(codes, row0 + c2, T_RUN_CONT, nvv, nin, nvv - nin, (uint32_t)(row0 + s0));
+                if (kfo) kfo[row0 + c2] = pl;
+            }
+            k += nj;
+            open = (failb == 0) && k < g.TC;
+        }
+        j = k;
+    }
+}
+
+template <int TH_, int TW_>
+static cudaError_t launch_merge_t(const Geometry &g, const Scratch &s, const Batch &b, cudaStream_t st) {
+    dim3 grid((g.TR + kMergeWarps - 1) / kMergeWarps, b.nframes);
+    k_merge<TH_, TW_><<<grid, kMergeWarps * 32, 0, st>>>(g, s, b);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_merge(const Geometry &g, const Scratch &s, const Batch &b, cudaStream_t st) {
+    if (b.nframes <= 0) return cudaSuccess;
+    if (g.th == 4 && g.tw == 4) return launch_merge_t<4, 4>(g, s, b, st);
+    if (g.th == 4 && g.tw == 8) return launch_merge_t<4, 8>(g, s, b, st);
+    if (g.th == 8 && g.tw == 8) return launch_merge_t<8, 8>(g, s, b, st);
+    if (g.th == 8 && g.tw == 16) return launch_merge_t<8, 16>(g, s, b, st);
+    return cudaErrorInvalidValue;
+}
+
+}  // namespace lcc

@@ -1,0 +1,168 @@
+// Stream layout of one frame: exclusive prefix sums of the per-tile counts
+// (candidates, plane-coded pixels, raw pixels, run starts, temporal tiles)
+// give every tile its position in each stream section; the totals give the
+// section offsets, the header and the capacity check.  One CTA per frame; the
+// CTA then zeroes the frame's output words so the packer can OR bits in.
+#include "lcc_internal.cuh"
+
+namespace lcc {
+
+constexpr int kScanThreads = 1024;
+constexpr int kScanVals = 6;
+
+__device__ __forceinline__ uint32_t words_for(uint64_t bits) { return (uint32_t)((bits + 31) >> 5); }
+
+__global__ void __launch_bounds__(kScanThreads) k_scan(Geometry g, Scratch s, Batch b) {
+    const int f = blockIdx.x;
+    const size_t slot = (size_t)b.slot[f];
+    const TileCode *codes = s.codes + slot * g.NT;
+    const TileRec *recs = s.tiles + slot * g.NT;
+    TileOff *offs = s.offs + slot * g.NT;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+
+    __shared__ uint32_t s_warp[32][kScanVals];
+    __shared__ uint32_t s_carry[kScanVals];
+    __shared__ unsigned long long s_hist[16];
+    __shared__ uint32_t s_ok, s_total;
+    if (tid < kScanVals) s_carry[tid] = 0;
+    if (tid < 16) s_hist[tid] = 0;
+    __syncthreads();
+
+    for (int base = 0; base < g.NT; base += kScanThreads) {
+        const int t = base + tid;
+        uint32_t v[kScanVals] = {0, 0, 0, 0, 0, 0};
+        uint8_t mode = T_EMPTY;
+        if (t < g.NT) {
+            const uint2 c = *reinterpret_cast<const uint2 *>(codes + t);
+            mode = (uint8_t)(c.x & 0xff);
+            const uint32_t cand = (c.x >> 8) & 0xff, fitted = (c.x >> 16) & 0xff, raw = c.x >> 24;
+            v[0] = cand;
+            v[1] = fitted;
+            v[2] = raw;
+            v[3] = mode == T_RUN_START;
+            v[4] = mode == T_TEMPORAL;
+            v[5] = mode >= T_RUN_START ? cand : raw;   // valid pixels
+            const uint32_t w0 = *reinterpret_cast<const uint32_t *>(reinterpret_cast<const uint8_t *>(recs + t) + 40);
+            const uint32_t rounds = (w0 >> 8) & 0xff, flags = (w0 >> 16) & 0xff;
+            atomicAdd(&s_hist[mode], 1ull);                 // [0..4] tiles by mode
+            atomicAdd(&s_hist[5 + min(rounds, 7u)], 1ull);  // [5..12] fit rounds
+            if (flags & 1) atomicAdd(&s_hist[13], 1ull);
+        }
+        // warp inclusive scans
+        uint32_t inc[kScanVals];
+#pragma unroll
+        for (int q = 0; q < kScanVals; q++) {
+            uint32_t x = v[q];
+#pragma unroll
+            for (int off = 1; off < 32; off <<= 1) {
+                const uint32_t y = __shfl_up_sync(0xffffffffu, x, off);
+                if (lane >= off) x += y;
+            }
+            inc[q] = x;
+        }
+        if (lane == 31)
+#pragma unroll
+            for (int q = 0; q < kScanVals; q++) s_warp[warp][q] = inc[q];
+        __syncthreads();
+        if (warp == 0) {
+#pragma unroll
+            for (int q = 0; q < kScanVals; q++) {
+                uint32_t x = s_warp[lane][q];
+#pragma unroll
+                for (int off = 1; off < 32; off <<= 1) {
+                    const uint32_t y = __shfl_up_sync(0xffffffffu, x, off);
+                    if (lane >= off) x += y;
+                }
+                s_warp[lane][q] = x;  // inclusive over warps
+            }
+        }
+        __syncthreads();
+        if (t < g.NT) {
+            uint32_t o[kScanVals];
+#pragma unroll
+            for (int q = 0; q < kScanVals; q++)
+                o[q] = s_carry[q] + (warp ? s_warp[warp - 1][q] : 0u) + inc[q] - v[q];
+            uint4 *dst = reinterpret_cast<uint4 *>(offs + t);
+            dst[0] = make_uint4(o[0], o[1], o[2], o[3]);
+            dst[1] = make_uint4(o[4], 0u, 0u, 0u);
+        }
+        __syncthreads();
+        if (tid < kScanVals) s_carry[tid] += s_warp[31][tid];
+        __syncthreads();
+    }
+
+    if (tid == 0) {
+        const uint32_t cand = s_carry[0], fitted = s_carry[1], raw = s_carry[2], runs = s_carry[3],
+                       temporal = s_carry[4], valid = s_carry[5];
+        FrameLayout L;
+        L.sec[0] = 0;
+        L.sec[1] = L.sec[0] + words_for((uint64_t)g.H * g.W);
+        L.sec[2] = L.sec[1] + words_for((uint64_t)g.NT * 4);
+        L.sec[3] = L.sec[2] + 4u * runs;
+        L.sec[4] = L.sec[3] + 2u * temporal;
+        L.sec[5] = L.sec[4] + words_for(cand);
+        L.sec[6] = L.sec[5] + words_for((uint64_t)fitted * g.w_res);
+        L.sec[7] = L.sec[6] + words_for((uint64_t)raw * g.w_raw);
+        const unsigned long long total = (unsigned long long)kHeaderBytes + 4ull * L.sec[7];
+        L.total_bytes = (uint32_t)total;
+        L.ok = total <= b.cap[f] ? 1u : 0u;
+        L.n_valid = valid;
+        L.pad = 0;
+        s.layout[slot] = L;
+        s.bytes[slot] = total;
+        if (!L.ok) atomicOr(s.err, E_CAPACITY);
+        s_ok = L.ok;
+        s_total = L.total_bytes;
+        if (L.ok) {
+            uint32_t hw[16];
+            hw[0] = kMagic;
+            hw[1] = (uint32_t)kVersion | ((uint32_t)b.kind << 16) | ((uint32_t)(g.merge ? 1 : 0) << 24);
+            hw[2] = (uint32_t)g.H | ((uint32_t)g.W << 16);
+            hw[3] = (uint32_t)g.th | ((uint32_t)g.tw << 8) | ((uint32_t)g.w_res << 16) | ((uint32_t)g.w_raw << 24);
+            hw[4] = __float_as_uint(g.thr);
+            hw[5] = __float_as_uint(g.q);
+            hw[6] = (uint32_t)g.NT;
+            hw[7] = valid;
+            hw[8] = runs;
+            hw[9] = temporal;
+            hw[10] = cand;
+            hw[11] = fitted;
+            hw[12] = raw;
+            hw[13] = (uint32_t)g.k_max;
+            hw[14] = L.total_bytes;
+            hw[15] = 0;
+            uint4 *o = reinterpret_cast<uint4 *>(b.out[f]);
+            for (int q = 0; q < 4; q++) o[q] = make_uint4(hw[4 * q], hw[4 * q + 1], hw[4 * q + 2], hw[4 * q + 3]);
+        }
+        DevStats *st = s.stats + slot;
+        st->valid = valid;
+        st->empty = s_hist[T_EMPTY];
+        st->raw_tiles = s_hist[T_RAW];
+        st->run_start = s_hist[T_RUN_START];
+        st->run_cont = s_hist[T_RUN_CONT];
+        st->temporal = s_hist[T_TEMPORAL];
+        for (int q = 0; q < 8; q++) st->rounds[q] = s_hist[5 + q];
+        st->borderline = s_hist[13];
+        st->cand = cand;
+        st->fitted = fitted;
+        st->raw = raw;
+        st->bytes = total;
+    }
+    __syncthreads();
+    if (s_ok) {
+        // zero everything after the header: 16-byte stores then the tail words
+        const uint32_t nw = (s_total - kHeaderBytes) / 4;
+        uint4 *o4 = reinterpret_cast<uint4 *>(b.out[f] + kHeaderBytes);
+        for (uint32_t q = tid; q < nw / 4; q += kScanThreads) o4[q] = make_uint4(0u, 0u, 0u, 0u);
+        uint32_t *o1 = reinterpret_cast<uint32_t *>(b.out[f] + kHeaderBytes);
+        for (uint32_t q = (nw / 4) * 4 + tid; q < nw; q += kScanThreads) o1[q] = 0u;
+    }
+}
+
+cudaError_t launch_scan(const Geometry &g, const Scratch &s, const Batch &b, cudaStream_t st) {
+    if (b.nframes <= 0) return cudaSuccess;
+    k_scan<<<b.nframes, kScanThreads, 0, st>>>(g, s, b);
+    return cudaGetLastError();
+}
+
+}  // namespace lcc

@@ -1,0 +1,666 @@
+// C ABI of the lcc library: context and scratch management, argument
+// checks, batched launches of the encode/decode kernels on the context
+// stream, statistics and per-kernel timing.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "lcc.h"
+#include "lcc_internal.cuh"
+
+using namespace lcc;
+
+namespace {
+
+struct ProfRec {
+    int name;
+    cudaEvent_t a, b;
+};
+
+const char *kKernelNames[] = {"bin", "fit", "merge", "scan", "pack", "decode_prep", "decode_px", "range_export"};
+constexpr int kNumKernels = 8;
+
+size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
+
+}  // namespace
+
+struct lcc_keyframe {
+    lcc_ctx *ctx;
+    float4 *planes;
+    int64_t nt;
+};
+
+struct lcc_ctx {
+    lcc_sensor sensor;
+    lcc_params prm;
+    cudaStream_t stream = nullptr;
+    Geometry g{};
+    Scratch s{};
+    void *d_tables = nullptr;
+    void *d_scratch = nullptr;
+    DecTile *d_dec = nullptr;
+    std::vector<float> h_tables;  // ce, se, ct, st, rbc, rbs, cbc, cbs
+    int slots = 0;
+    uint64_t max_bytes = 0;
+    int last_nframes = 0;
+    // profiling
+    bool prof = false;
+    std::vector<ProfRec> pending;
+    std::vector<cudaEvent_t> pool;
+    int64_t launches[kNumKernels] = {};
+    double ms[kNumKernels] = {};
+    // host-buffer staging
+    void *d_stage_pts = nullptr;
+    size_t stage_pts_cap = 0;
+    uint8_t *d_stage_out = nullptr;
+    size_t stage_out_cap = 0;
+    unsigned long long *d_stage_bytes = nullptr;
+};
+
+namespace {
+
+cudaEvent_t get_event(lcc_ctx *c) {
+    if (!c->pool.empty()) {
+        cudaEvent_t e = c->pool.back();
+        c->pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+}
+
+int prof_begin(lcc_ctx *c, int name) {
+    if (!c->prof) return -1;
+    ProfRec r{name, get_event(c), get_event(c)};
+    cudaEventRecord(r.a, c->stream);
+    c->pending.push_back(r);
+    return (int)c->pending.size() - 1;
+}
+
+void prof_end(lcc_ctx *c, int idx) {
+    if (idx < 0) return;
+    cudaEventRecord(c->pending[idx].b, c->stream);
+}
+
+void prof_collect(lcc_ctx *c) {
+    for (auto &r : c->pending) {
+        float ms = 0.f;
+        if (cudaEventSynchronize(r.b) == cudaSuccess && cudaEventElapsedTime(&ms, r.a, r.b) == cudaSuccess) {
+            c->launches[r.name]++;
+            c->ms[r.name] += ms;
+        }
+        c->pool.push_back(r.a);
+        c->pool.push_back(r.b);
+    }
+    c->pending.clear();
+}
+
+#define LCC_LAUNCH(ctx, id, call)                   \
+    do {                                            \
+        const int _pi = prof_begin(ctx, id);        \
+        const cudaError_t _e = (call);              \
+        prof_end(ctx, _pi);                         \
+        if (_e != cudaSuccess) return LCC_ERR_CUDA; \
+    } while (0)
+
+#define LCC_CUDA(call)                                   \
+    do {                                                 \
+        if ((call) != cudaSuccess) return LCC_ERR_CUDA;  \
+    } while (0)
+
+bool tile_supported(int th, int tw) {
+    return (th == 4 && tw == 4) || (th == 4 && tw == 8) || (th == 8 && tw == 8) || (th == 8 && tw == 16);
+}
+
+// Sensor tables from the grid definition of Sec. III-B, fp64 libm rounded to fp32.
+void make_tables(const lcc_sensor &s, std::vector<float> &t) {
+    const int H = s.rows, W = s.cols;
+    t.assign((size_t)4 * H + 2 + (size_t)4 * W, 0.f);
+    float *ce = t.data(), *se = ce + H, *ct = se + H, *st = ct + W, *rbc = st + W, *rbs = rbc + H + 1,
+          *cbc = rbs + H + 1, *cbs = cbc + W;
+    const double deg = M_PI / 180.0;
+    const double d_el = (s.elev_max_deg - s.elev_min_deg) / H;
+    const double d_az = 2.0 * M_PI / W;
+    for (int i = 0; i < H; i++) {
+        const double e = (s.elev_max_deg - (i + 0.5) * d_el) * deg;
+        ce[i] = (float)std::cos(e);
+        se[i] = (float)std::sin(e);
+    }
+    for (int k = 0; k <= H; k++) {
+        const double e = (s.elev_max_deg - k * d_el) * deg;
+        rbc[k] = (float)std::cos(e);
+        rbs[k] = (float)std::sin(e);
+    }
+    for (int j = 0; j < W; j++) {
+        const double a = -M_PI + (j + 0.5) * d_az;
+        ct[j] = (float)std::cos(a);
+        st[j] = (float)std::sin(a);
+        const double b = -M_PI + j * d_az;
+        cbc[j] = (float)std::cos(b);
+        cbs[j] = (float)std::sin(b);
+    }
+}
+
+int bits_for(int max_value) {
+    int w = 1;
+    while ((1 << w) < max_value + 1) w++;
+    return w;
+}
+
+bool aligned16(const void *p) { return ((uintptr_t)p & 15u) == 0; }
+
+lcc_status latched(lcc_ctx *c) {
+    uint32_t e = 0;
+    if (cudaMemcpy(&e, c->s.err, 4, cudaMemcpyDeviceToHost) != cudaSuccess) return LCC_ERR_CUDA;
+    if (e) cudaMemset(c->s.err, 0, 4);
+    if (e & E_CORRUPT) return LCC_ERR_CORRUPT;
+    if (e & E_CAPACITY) return LCC_ERR_CAPACITY;
+    if (e & E_TIMEOUT) return LCC_ERR_TIMEOUT;
+    if (e) return LCC_ERR_CUDA;
+    return LCC_OK;
+}
+
+// One batched encode pass over frames that are already binned (slots 0..n-1
+// hold their range images): fit, merge, scan, pack.
+lcc_status encode_batch(lcc_ctx *c, int kind, int nframes, const int *slots, uint8_t *const *d_out,
+                        const uint64_t *cap, const double *poses, const lcc_keyframe *kf, lcc_keyframe *kf_out) {
+    if (nframes <= 0) return LCC_OK;
+    Batch b;
+    memset(&b, 0, sizeof(b));
+    b.nframes = nframes;
+    b.kind = kind;
+    for (int f = 0; f < nframes; f++) {
+        b.slot[f] = slots[f];
+        b.out[f] = d_out[f];
+        b.cap[f] = cap[f];
+    }
+    b.kf = kf ? kf->planes : nullptr;
+    b.kf_out = kf_out ? kf_out->planes : nullptr;
+    Poses p;
+    memset(&p, 0, sizeof(p));
+    if (poses)
+        for (int f = 0; f < nframes; f++) memcpy(p.m[f], poses + 16 * f, 16 * sizeof(double));
+    LCC_LAUNCH(c, 1, launch_fit(c->g, c->s, b, p, c->stream));
+    LCC_LAUNCH(c, 2, launch_merge(c->g, c->s, b, c->stream));
+    LCC_LAUNCH(c, 3, launch_scan(c->g, c->s, b, c->stream));
+    LCC_LAUNCH(c, 4, launch_pack(c->g, c->s, b, c->stream));
+    return LCC_OK;
+}
+
+// Bin frames into slots[f] (stats of those slots are reset first).
+lcc_status bin_frames(lcc_ctx *c, int nframes, const int *slots, const float *const *d_pts, const int64_t *n) {
+    Batch b;
+    memset(&b, 0, sizeof(b));
+    b.nframes = nframes;
+    long long blocks = 0;
+    const long long per_block = 256 * 4;
+    for (int f = 0; f < nframes; f++) {
+        b.slot[f] = slots[f];
+        b.pts[f] = reinterpret_cast<const float4 *>(d_pts[f]);
+        b.n[f] = n[f];
+        b.blk_prefix[f] = blocks;
+        blocks += (n[f] + per_block - 1) / per_block;
+        LCC_CUDA(cudaMemsetAsync(c->s.stats + slots[f], 0, sizeof(DevStats), c->stream));
+    }
+    b.blk_prefix[nframes] = blocks;
+    LCC_LAUNCH(c, 0, launch_bin(c->g, c->s, b, blocks, c->stream));
+    return LCC_OK;
+}
+
+lcc_status copy_bytes(lcc_ctx *c, int nframes, const int *slots, uint64_t *out_bytes) {
+    if (!out_bytes) return LCC_OK;
+    bool contiguous = true;
+    for (int f = 0; f < nframes; f++) contiguous = contiguous && slots[f] == slots[0] + f;
+    if (contiguous) {
+        LCC_CUDA(cudaMemcpyAsync(out_bytes, c->s.bytes + slots[0], sizeof(uint64_t) * nframes, cudaMemcpyDefault,
+                                 c->stream));
+    } else {
+        for (int f = 0; f < nframes; f++)
+            LCC_CUDA(cudaMemcpyAsync(out_bytes + f, c->s.bytes + slots[f], sizeof(uint64_t), cudaMemcpyDefault,
+                                     c->stream));
+    }
+    return LCC_OK;
+}
+
+lcc_status check_frames(lcc_ctx *c, int nframes, const float *const *d_pts, const int64_t *n,
+                        uint8_t *const *d_out, const uint64_t *cap) {
+    if (nframes < 1 || nframes > c->slots || !d_pts || !n || !d_out || !cap) return LCC_ERR_INVALID_ARG;
+    for (int f = 0; f < nframes; f++) {
+        if (n[f] < 0 || n[f] > (int64_t)1 << 31) return LCC_ERR_INVALID_ARG;
+        if (n[f] > 0 && (!d_pts[f] || !aligned16(d_pts[f]))) return LCC_ERR_INVALID_ARG;
+        if (!d_out[f] || !aligned16(d_out[f]) || cap[f] < (uint64_t)kHeaderBytes) return LCC_ERR_INVALID_ARG;
+    }
+    return LCC_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *lcc_status_string(lcc_status s) {
+    switch (s) {
+    case LCC_OK: return "ok";
+    case LCC_ERR_INVALID_ARG: return "invalid argument";
+    case LCC_ERR_CAPACITY: return "output buffer too small";
+    case LCC_ERR_CUDA: return "CUDA runtime error";
+    case LCC_ERR_TIMEOUT: return "device wait timed out";
+    case LCC_ERR_CORRUPT: return "corrupt stream";
+    case LCC_ERR_UNSUPPORTED: return "unsupported";
+    case LCC_ERR_NO_DEVICE: return "no sm_103 GPU";
+    }
+    return "unknown";
+}
+
+void lcc_default_params(lcc_params *p) {
+    if (!p) return;
+    p->tile_h = 4;
+    p->tile_w = 4;
+    p->fit_thr_m = 0.05f;
+    p->quant_m = 0.02f;
+    p->max_refits = 3;
+    p->min_inlier_frac = 0.75f;
+    p->merge_runs = 1;
+    p->max_batch = 16;
+    p->lookahead = 8;
+}
+
+lcc_status lcc_create(lcc_ctx **out, const lcc_sensor *sensor, const lcc_params *params, void *cuda_stream) {
+    if (!out || !sensor || !params) return LCC_ERR_INVALID_ARG;
+    *out = nullptr;
+    const lcc_sensor &s = *sensor;
+    const lcc_params &p = *params;
+    if (s.rows < 1 || s.cols < 2 || s.rows > 65535 || s.cols > 65535 || !(s.elev_max_deg > s.elev_min_deg) ||
+        s.elev_max_deg > 90.0 || s.elev_min_deg < -90.0 || !(s.max_range_m > 0))
+        return LCC_ERR_INVALID_ARG;
+    if (!tile_supported(p.tile_h, p.tile_w)) return LCC_ERR_UNSUPPORTED;
+    if (!(p.fit_thr_m >= 0) || !(p.quant_m > 0) || p.max_refits < 0 || p.max_refits > 6 ||
+        !(p.min_inlier_frac >= 0) || p.max_batch < 1 || p.max_batch > kMaxBatch || p.lookahead < 0 ||
+        p.lookahead > 16)
+        return LCC_ERR_INVALID_ARG;
+    int dev = 0;
+    cudaDeviceProp prop;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaGetDeviceProperties(&prop, dev) != cudaSuccess)
+        return LCC_ERR_NO_DEVICE;
+    if (!(prop.major == 10 && prop.minor == 3)) return LCC_ERR_NO_DEVICE;
+
+    lcc_ctx *c = new (std::nothrow) lcc_ctx();
+    if (!c) return LCC_ERR_CUDA;
+    c->sensor = s;
+    c->prm = p;
+    c->stream = (cudaStream_t)cuda_stream;
+    Geometry &g = c->g;
+    g.H = s.rows;
+    g.W = s.cols;
+    g.th = p.tile_h;
+    g.tw = p.tile_w;
+    g.tpx = p.tile_h * p.tile_w;
+    g.TR = (s.rows + p.tile_h - 1) / p.tile_h;
+    g.TC = (s.cols + p.tile_w - 1) / p.tile_w;
+    g.NT = g.TR * g.TC;
+    g.thr = p.fit_thr_m;
+    g.q = p.quant_m;
+    g.rmax = (float)s.max_range_m;
+    g.fmin = p.min_inlier_frac;
+    g.R = p.max_refits;
+    g.merge = p.merge_runs ? 1 : 0;
+    g.lookahead = p.merge_runs ? p.lookahead : 0;
+    g.k_max = (int)floorf(p.fit_thr_m / p.quant_m + 0.5f) + 1;
+    g.w_res = bits_for(2 * g.k_max);
+    const int m_max = (int)floorf((float)s.max_range_m / p.quant_m + 0.5f) + 1;
+    g.w_raw = bits_for(m_max);
+    g.elev_max_deg = (float)s.elev_max_deg;
+    g.d_el_deg = (float)((s.elev_max_deg - s.elev_min_deg) / s.rows);
+    g.d_az = (float)(2.0 * M_PI / s.cols);
+    if (g.w_res > 16 || g.w_raw > 24) {
+        delete c;
+        return LCC_ERR_UNSUPPORTED;
+    }
+    make_tables(s, c->h_tables);
+    const int H = s.rows, W = s.cols;
+    if (cudaMalloc(&c->d_tables, c->h_tables.size() * sizeof(float)) != cudaSuccess) {
+        delete c;
+        return LCC_ERR_CUDA;
+    }
+    cudaMemcpy(c->d_tables, c->h_tables.data(), c->h_tables.size() * sizeof(float), cudaMemcpyHostToDevice);
+    const float *tb = (const float *)c->d_tables;
+    g.ce = tb;
+    g.se = g.ce + H;
+    g.ct = g.se + H;
+    g.st = g.ct + W;
+    g.rbc = g.st + W;
+    g.rbs = g.rbc + H + 1;
+    g.cbc = g.rbs + H + 1;
+    g.cbs = g.cbc + W;
+
+    c->slots = p.max_batch;
+    const size_t npx = (size_t)H * W, nt = (size_t)g.NT, sl = (size_t)c->slots;
+    const size_t o_rimg = 0;
+    const size_t o_tiles = o_rimg + align256(sl * npx * 4);
+    const size_t o_codes = o_tiles + align256(sl * nt * sizeof(TileRec));
+    const size_t o_offs = o_codes + align256(sl * nt * sizeof(TileCode));
+    const size_t o_layout = o_offs + align256(sl * nt * sizeof(TileOff));
+    const size_t o_stats = o_layout + align256(sl * sizeof(FrameLayout));
+    const size_t o_bytes = o_stats + align256(sl * sizeof(DevStats));
+    const size_t o_err = o_bytes + align256(sl * 8);
+    const size_t o_dec = o_err + 256;
+    const size_t total = o_dec + align256((nt + 4) * sizeof(DecTile));
+    if (cudaMalloc(&c->d_scratch, total) != cudaSuccess) {
+        cudaFree(c->d_tables);
+        delete c;
+        return LCC_ERR_CUDA;
+    }
+    char *base = (char *)c->d_scratch;
+    c->s.rimg = (uint32_t *)(base + o_rimg);
+    c->s.tiles = (TileRec *)(base + o_tiles);
+    c->s.codes = (TileCode *)(base + o_codes);
+    c->s.offs = (TileOff *)(base + o_offs);
+    c->s.layout = (FrameLayout *)(base + o_layout);
+    c->s.stats = (DevStats *)(base + o_stats);
+    c->s.bytes = (unsigned long long *)(base + o_bytes);
+    c->s.err = (uint32_t *)(base + o_err);
+    c->d_dec = (DecTile *)(base + o_dec);
+    cudaMemset(c->d_scratch, 0, total);
+    cudaMemset(c->s.rimg, 0xFF, sl * npx * 4);
+    c->max_bytes = (uint64_t)kHeaderBytes +
+                   4ull * ((npx + 31) / 32 + (nt * 4 + 31) / 32 + 4 * nt + 2 * nt + (npx + 31) / 32 +
+                           (npx * g.w_res + 31) / 32 + (npx * g.w_raw + 31) / 32 + 4);
+    if (cudaDeviceSynchronize() != cudaSuccess) {
+        lcc_destroy(c);
+        return LCC_ERR_CUDA;
+    }
+    *out = c;
+    return LCC_OK;
+}
+
+lcc_status lcc_destroy(lcc_ctx *c) {
+    if (!c) return LCC_ERR_INVALID_ARG;
+    cudaStreamSynchronize(c->stream);
+    for (auto &r : c->pending) {
+        cudaEventDestroy(r.a);
+        cudaEventDestroy(r.b);
+    }
+    for (auto e : c->pool) cudaEventDestroy(e);
+    cudaFree(c->d_tables);
+    cudaFree(c->d_scratch);
+    cudaFree(c->d_stage_pts);
+    cudaFree(c->d_stage_out);
+    cudaFree(c->d_stage_bytes);
+    delete c;
+    return LCC_OK;
+}
+
+uint64_t lcc_max_encoded_bytes(const lcc_ctx *c) { return c ? c->max_bytes : 0; }
+
+int64_t lcc_num_tiles(const lcc_ctx *c) { return c ? c->g.NT : 0; }
+
+lcc_status lcc_tables(const lcc_ctx *c, float *ce, float *se, float *ct, float *st, float *rbc, float *rbs,
+                      float *cbc, float *cbs) {
+    if (!c) return LCC_ERR_INVALID_ARG;
+    const int H = c->g.H, W = c->g.W;
+    const float *t = c->h_tables.data();
+    float *dst[8] = {ce, se, ct, st, rbc, rbs, cbc, cbs};
+    const int len[8] = {H, H, W, W, H + 1, H + 1, W, W};
+    for (int k = 0; k < 8; k++) {
+        if (dst[k]) memcpy(dst[k], t, sizeof(float) * len[k]);
+        t += len[k];
+    }
+    return LCC_OK;
+}
+
+lcc_status lcc_range_image(lcc_ctx *c, const float *d_pts, int64_t n, float *d_range, uint32_t *d_valid) {
+    if (!c || n < 0 || (n > 0 && (!d_pts || !aligned16(d_pts)))) return LCC_ERR_INVALID_ARG;
+    const int slot = 0;
+    lcc_status st = bin_frames(c, 1, &slot, &d_pts, &n);
+    if (st != LCC_OK) return st;
+    LCC_LAUNCH(c, 7, launch_range_image(c->g, c->s.rimg, d_range, d_valid, c->stream));
+    c->last_nframes = 1;
+    return LCC_OK;
+}
+
+lcc_status lcc_keyframe_create(lcc_ctx *c, lcc_keyframe **out) {
+    if (!c || !out) return LCC_ERR_INVALID_ARG;
+    lcc_keyframe *k = new (std::nothrow) lcc_keyframe();
+    if (!k) return LCC_ERR_CUDA;
+    k->ctx = c;
+    k->nt = c->g.NT;
+    if (cudaMalloc(&k->planes, sizeof(float4) * k->nt) != cudaSuccess) {
+        delete k;
+        return LCC_ERR_CUDA;
+    }
+    cudaMemsetAsync(k->planes, 0, sizeof(float4) * k->nt, c->stream);
+    *out = k;
+    return LCC_OK;
+}
+
+void lcc_keyframe_free(lcc_keyframe *k) {
+    if (!k) return;
+    cudaStreamSynchronize(k->ctx->stream);
+    cudaFree(k->planes);
+    delete k;
+}
+
+lcc_status lcc_encode_keyframe(lcc_ctx *c, const float *d_pts, int64_t n, lcc_keyframe *kf, uint8_t *d_out,
+                               uint64_t cap, uint64_t *out_bytes) {
+    if (!c) return LCC_ERR_INVALID_ARG;
+    if (kf && kf->ctx != c) return LCC_ERR_INVALID_ARG;
+    lcc_status st = check_frames(c, 1, &d_pts, &n, &d_out, &cap);
+    if (st != LCC_OK) return st;
+    const int slot = 0;
+    if ((st = bin_frames(c, 1, &slot, &d_pts, &n)) != LCC_OK) return st;
+    if ((st = encode_batch(c, 0, 1, &slot, &d_out, &cap, nullptr, nullptr, kf)) != LCC_OK) return st;
+    c->last_nframes = 1;
+    return copy_bytes(c, 1, &slot, out_bytes);
+}
+
+lcc_status lcc_encode_pframes(lcc_ctx *c, const lcc_keyframe *kf, int32_t nframes, const double *poses,
+                              const float *const *d_pts, const int64_t *n, uint8_t *const *d_out,
+                              const uint64_t *cap, uint64_t *out_bytes) {
+    if (!c || !kf || kf->ctx != c || !poses) return LCC_ERR_INVALID_ARG;
+    lcc_status st = check_frames(c, nframes, d_pts, n, d_out, cap);
+    if (st != LCC_OK) return st;
+    int slots[kMaxBatch];
+    for (int f = 0; f < nframes; f++) slots[f] = f;
+    if ((st = bin_frames(c, nframes, slots, d_pts, n)) != LCC_OK) return st;
+    if ((st = encode_batch(c, 1, nframes, slots, d_out, cap, poses, kf, nullptr)) != LCC_OK) return st;
+    c->last_nframes = nframes;
+    return copy_bytes(c, nframes, slots, out_bytes);
+}
+
+lcc_status lcc_encode_pframe(lcc_ctx *c, const lcc_keyframe *kf, const double pose[16], const float *d_pts,
+                             int64_t n, uint8_t *d_out, uint64_t cap, uint64_t *out_bytes) {
+    return lcc_encode_pframes(c, kf, 1, pose, &d_pts, &n, &d_out, &cap, out_bytes);
+}
+
+lcc_status lcc_encode_sequence(lcc_ctx *c, int32_t nframes, int32_t key_index, const double *poses,
+                               const float *const *d_pts, const int64_t *n, uint8_t *const *d_out,
+                               const uint64_t *cap, uint64_t *out_bytes, lcc_keyframe *kf) {
+    if (!c || !poses || key_index < 0 || key_index >= nframes) return LCC_ERR_INVALID_ARG;
+    if (kf && kf->ctx != c) return LCC_ERR_INVALID_ARG;
+    lcc_status st = check_frames(c, nframes, d_pts, n, d_out, cap);
+    if (st != LCC_OK) return st;
+    lcc_keyframe local;
+    lcc_keyframe *k = kf;
+    if (!k) {
+        // the key frame's planes must outlive the P pass: use the decoder scratch
+        static_assert(sizeof(DecTile) >= sizeof(float4), "scratch size");
+        local.ctx = c;
+        local.nt = c->g.NT;
+        local.planes = reinterpret_cast<float4 *>(c->d_dec);
+        k = &local;
+    }
+    int slots[kMaxBatch];
+    for (int f = 0; f < nframes; f++) slots[f] = f;
+    if ((st = bin_frames(c, nframes, slots, d_pts, n)) != LCC_OK) return st;
+    const int kslot = key_index;
+    uint8_t *kout = d_out[key_index];
+    const uint64_t kcap = cap[key_index];
+    if ((st = encode_batch(c, 0, 1, &kslot, &kout, &kcap, nullptr, nullptr, k)) != LCC_OK) return st;
+    int pslots[kMaxBatch];
+    uint8_t *pout[kMaxBatch];
+    uint64_t pcap[kMaxBatch];
+    std::vector<double> pposes;
+    int np = 0;
+    for (int f = 0; f < nframes; f++) {
+        if (f == key_index) continue;
+        pslots[np] = f;
+        pout[np] = d_out[f];
+        pcap[np] = cap[f];
+        pposes.insert(pposes.end(), poses + 16 * f, poses + 16 * f + 16);
+        np++;
+    }
+    if ((st = encode_batch(c, 1, np, pslots, pout, pcap, pposes.data(), k, nullptr)) != LCC_OK) return st;
+    c->last_nframes = nframes;
+    return copy_bytes(c, nframes, slots, out_bytes);
+}
+
+lcc_status lcc_encode_sequence_host(lcc_ctx *c, int32_t nframes, int32_t key_index, const double *poses,
+                                    const float *const *h_pts, const int64_t *n, uint8_t *const *h_out,
+                                    const uint64_t *cap, uint64_t *out_bytes) {
+    if (!c || !h_pts || !n || !h_out || !cap || !out_bytes || nframes < 1 || nframes > c->slots)
+        return LCC_ERR_INVALID_ARG;
+    size_t pts_total = 0, out_total = 0;
+    for (int f = 0; f < nframes; f++) {
+        if (n[f] < 0) return LCC_ERR_INVALID_ARG;
+        pts_total += align256((size_t)n[f] * 16);
+        out_total += align256((size_t)cap[f]);
+    }
+    if (pts_total > c->stage_pts_cap) {
+        cudaFree(c->d_stage_pts);
+        c->d_stage_pts = nullptr;
+        LCC_CUDA(cudaMalloc(&c->d_stage_pts, pts_total));
+        c->stage_pts_cap = pts_total;
+    }
+    if (out_total > c->stage_out_cap) {
+        cudaFree(c->d_stage_out);
+        c->d_stage_out = nullptr;
+        LCC_CUDA(cudaMalloc(&c->d_stage_out, out_total));
+        c->stage_out_cap = out_total;
+    }
+    if (!c->d_stage_bytes) LCC_CUDA(cudaMalloc(&c->d_stage_bytes, sizeof(unsigned long long) * kMaxBatch));
+    const float *dp[kMaxBatch];
+    uint8_t *dout[kMaxBatch];
+    char *pp = (char *)c->d_stage_pts;
+    uint8_t *po = c->d_stage_out;
+    for (int f = 0; f < nframes; f++) {
+        dp[f] = (const float *)pp;
+        if (n[f]) LCC_CUDA(cudaMemcpyAsync(pp, h_pts[f], (size_t)n[f] * 16, cudaMemcpyHostToDevice, c->stream));
+        pp += align256((size_t)n[f] * 16);
+        dout[f] = po;
+        po += align256((size_t)cap[f]);
+    }
+    lcc_status st = lcc_encode_sequence(c, nframes, key_index, poses, dp, n, dout, cap,
+                                        (uint64_t *)c->d_stage_bytes, nullptr);
+    if (st != LCC_OK) return st;
+    LCC_CUDA(cudaMemcpyAsync(out_bytes, c->d_stage_bytes, sizeof(uint64_t) * nframes, cudaMemcpyDeviceToHost,
+                             c->stream));
+    LCC_CUDA(cudaStreamSynchronize(c->stream));
+    for (int f = 0; f < nframes; f++) {
+        const uint64_t nb = out_bytes[f] <= cap[f] ? out_bytes[f] : 0;
+        if (nb) LCC_CUDA(cudaMemcpyAsync(h_out[f], dout[f], nb, cudaMemcpyDeviceToHost, c->stream));
+    }
+    LCC_CUDA(cudaStreamSynchronize(c->stream));
+    return latched(c);
+}
+
+lcc_status lcc_keyframe_from_stream(lcc_ctx *c, const uint8_t *d_bits, uint64_t nbytes, lcc_keyframe *kf) {
+    if (!c || !kf || kf->ctx != c || !d_bits || !aligned16(d_bits)) return LCC_ERR_INVALID_ARG;
+    Poses p;
+    memset(&p, 0, sizeof(p));
+    LCC_LAUNCH(c, 5, launch_decode_prep(c->g, d_bits, nbytes, nullptr, nullptr, c->d_dec, kf->planes, c->s.err, 0,
+                                        &p, c->stream));
+    return LCC_OK;
+}
+
+lcc_status lcc_decode(lcc_ctx *c, const uint8_t *d_bits, uint64_t nbytes, const lcc_keyframe *kf,
+                      const double pose[16], float *d_range, float *d_xyz4, uint32_t *d_valid) {
+    if (!c || !d_bits || !aligned16(d_bits)) return LCC_ERR_INVALID_ARG;
+    if (kf && (kf->ctx != c || !pose)) return LCC_ERR_INVALID_ARG;
+    if (d_xyz4 && !aligned16(d_xyz4)) return LCC_ERR_INVALID_ARG;
+    Poses p;
+    memset(&p, 0, sizeof(p));
+    if (pose) memcpy(p.m[0], pose, 16 * sizeof(double));
+    LCC_LAUNCH(c, 5, launch_decode_prep(c->g, d_bits, nbytes, kf ? kf->planes : nullptr, nullptr, c->d_dec, nullptr,
+                                        c->s.err, kf ? 1 : 0, &p, c->stream));
+    LCC_LAUNCH(c, 6, launch_decode_px(c->g, d_bits, c->d_dec, d_range, reinterpret_cast<float4 *>(d_xyz4), c->s.err,
+                                      c->stream));
+    if (d_valid) {
+        const size_t words = ((size_t)c->g.H * c->g.W + 31) / 32;
+        if (nbytes < (uint64_t)kHeaderBytes + 4 * words) return LCC_ERR_CORRUPT;
+        LCC_CUDA(cudaMemcpyAsync(d_valid, d_bits + kHeaderBytes, 4 * words, cudaMemcpyDeviceToDevice, c->stream));
+    }
+    return LCC_OK;
+}
+
+lcc_status lcc_sync(lcc_ctx *c) {
+    if (!c) return LCC_ERR_INVALID_ARG;
+    if (cudaStreamSynchronize(c->stream) != cudaSuccess) return LCC_ERR_CUDA;
+    return latched(c);
+}
+
+lcc_status lcc_last_stats(lcc_ctx *c, int32_t frame, lcc_stats *out) {
+    if (!c || !out || frame < 0 || frame >= c->last_nframes) return LCC_ERR_INVALID_ARG;
+    if (cudaStreamSynchronize(c->stream) != cudaSuccess) return LCC_ERR_CUDA;
+    DevStats d;
+    LCC_CUDA(cudaMemcpy(&d, c->s.stats + frame, sizeof(d), cudaMemcpyDeviceToHost));
+    out->points_in = (int64_t)d.points_in;
+    out->points_invalid = (int64_t)d.invalid;
+    out->points_fov = (int64_t)d.fov;
+    out->points_binned = (int64_t)d.binned;
+    out->pixels_valid = (int64_t)d.valid;
+    out->tiles_empty = (int64_t)d.empty;
+    out->tiles_raw = (int64_t)d.raw_tiles;
+    out->tiles_run_start = (int64_t)d.run_start;
+    out->tiles_run_cont = (int64_t)d.run_cont;
+    out->tiles_temporal = (int64_t)d.temporal;
+    for (int q = 0; q < 8; q++) out->fit_rounds[q] = (int64_t)d.rounds[q];
+    out->tiles_borderline = (int64_t)d.borderline;
+    out->cand = (int64_t)d.cand;
+    out->fitted = (int64_t)d.fitted;
+    out->raw = (int64_t)d.raw;
+    out->bytes = d.bytes;
+    return LCC_OK;
+}
+
+lcc_status lcc_tile_records(lcc_ctx *c, int32_t frame, lcc_tile_info *h_out, int64_t cap) {
+    if (!c || !h_out || frame < 0 || frame >= c->last_nframes || cap < c->g.NT) return LCC_ERR_INVALID_ARG;
+    if (cudaStreamSynchronize(c->stream) != cudaSuccess) return LCC_ERR_CUDA;
+    LCC_CUDA(cudaMemcpy(h_out, c->s.tiles + (size_t)frame * c->g.NT, sizeof(TileRec) * c->g.NT,
+                        cudaMemcpyDeviceToHost));
+    return LCC_OK;
+}
+
+lcc_status lcc_set_profiling(lcc_ctx *c, int32_t enable) {
+    if (!c) return LCC_ERR_INVALID_ARG;
+    c->prof = enable != 0;
+    prof_collect(c);
+    for (int k = 0; k < kNumKernels; k++) {
+        c->launches[k] = 0;
+        c->ms[k] = 0.0;
+    }
+    return LCC_OK;
+}
+
+int32_t lcc_kernel_times(lcc_ctx *c, char names[][16], int64_t *launches, double *ms, int32_t cap) {
+    if (!c) return 0;
+    prof_collect(c);
+    int w = 0;
+    for (int k = 0; k < kNumKernels && w < cap; k++) {
+        if (!c->launches[k]) continue;
+        if (names) {
+            strncpy(names[w], kKernelNames[k], 15);
+            names[w][15] = 0;
+        }
+        if (launches) launches[w] = c->launches[k];
+        if (ms) ms[w] = c->ms[k];
+        w++;
+    }
+    return w;
+}
+
+}  // extern "C"

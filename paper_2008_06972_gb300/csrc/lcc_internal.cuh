@@ -1,0 +1,293 @@
+// Internal types and device helpers of the lcc CUDA library (sm_103a).
+//
+// Arithmetic contract shared with any independent implementation of the
+// method: every per-point fp32 expression below is written with explicit
+// IEEE-rounded intrinsics (__fmul_rn, __fadd_rn, __fdiv_rn, fmaf, sqrtf) and
+// the library is compiled with -fmad=false, so no multiply-add is fused
+// behind our back.  Binning, residual tests and quantised codes are therefore
+// bit-reproducible given the same fp32 plane.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "lcc.h"
+
+namespace lcc {
+
+constexpr int kMaxBatch = 64;          // frames per batched launch
+constexpr uint32_t kEmptyBits = 0xFFFFFFFFu;  // range-image pixel with no point
+constexpr int kHeaderBytes = 64;
+constexpr uint32_t kMagic = 0x3143434Cu;     // "LCC1"
+constexpr int kVersion = 1;
+constexpr int kMaxTilePx = 128;
+
+// tile codes in the stream
+enum : uint8_t { T_EMPTY = 0, T_RAW = 1, T_RUN_START = 2, T_RUN_CONT = 3, T_TEMPORAL = 4 };
+// own-fit status of a tile
+enum : uint8_t { S_EMPTY = 0, S_FAIL = 1, S_FIT = 2, S_TEMPORAL = 3 };
+// latched device error bits
+enum : uint32_t { E_CAPACITY = 1u, E_CORRUPT = 2u, E_TIMEOUT = 4u, E_INTERNAL = 8u };
+
+// Per-tile fit record; layout identical to lcc_tile_info.
+struct alignas(16) TileRec {
+    float4 plane;        // own spatial plane (n, d) or (n', c') if temporal
+    float4 tplane;       // temporal test plane
+    uint32_t kref;       // K tile of the anchor, ~0u if none
+    uint32_t ahead_mask; // bit k-1: tile +k passes this plane
+    uint8_t status, rounds, flags, n_valid;
+    uint8_t n_inlier, t_rounds, t_inlier, t_status;
+    uint8_t ahead_cnt[16];
+};
+static_assert(sizeof(TileRec) == 64, "TileRec layout");
+static_assert(sizeof(TileRec) == sizeof(lcc_tile_info), "TileRec matches lcc_tile_info");
+
+// Output of the run merge: how the tile is coded and its stream counts.
+struct TileCode {
+    uint8_t mode, cand, fitted, raw;
+    uint32_t plane_tile;  // tile whose plane codes this one (run start)
+};
+
+// Exclusive stream offsets of a tile (in codes) from the per-frame scan.
+struct TileOff {
+    uint32_t cand, fitted, raw, run, temporal, pad0, pad1, pad2;
+};
+
+// Word offsets of the stream sections of one frame (written by the scan).
+struct FrameLayout {
+    uint32_t sec[8];     // word offsets after the header: bitmap, tiles, runs, temporal, fitted, res, raw, end
+    uint32_t total_bytes;
+    uint32_t ok;         // 1 if the stream fits the output buffer
+    uint32_t n_valid, pad;
+};
+
+// Per-frame device counters (atomics).
+struct DevStats {
+    unsigned long long points_in, invalid, fov, binned, valid;
+    unsigned long long empty, raw_tiles, run_start, run_cont, temporal;
+    unsigned long long rounds[8];
+    unsigned long long borderline, cand, fitted, raw;
+    unsigned long long bytes;
+};
+
+// Decoder per-tile state.
+struct alignas(16) DecTile {
+    float4 plane;
+    uint32_t off_cand, off_fit, off_raw;
+    uint8_t mode, n_valid, pad0, pad1;
+};
+
+// Sensor geometry and parameters, passed by value to every kernel.
+struct Geometry {
+    int H, W;            // image rows, cols
+    int th, tw, tpx;     // tile shape and pixels per tile
+    int TR, TC, NT;      // tile rows, tile cols, tiles per frame
+    float thr, q, rmax, fmin;
+    int R;               // refit rounds after the first fit
+    int merge, lookahead;
+    int k_max, w_res, w_raw;
+    float elev_max_deg, d_el_deg, d_az;   // first guesses only; the tables decide
+    const float *ce, *se, *ct, *st;       // beam tables
+    const float *rbc, *rbs, *cbc, *cbs;   // boundary tables
+};
+
+// Per-slot scratch pointers (slot = batch position's scratch area).
+struct Scratch {
+    uint32_t *rimg;      // [slots][H*W]
+    TileRec *tiles;      // [slots][NT]
+    TileCode *codes;     // [slots][NT]
+    TileOff *offs;       // [slots][NT]
+    FrameLayout *layout; // [slots]
+    DevStats *stats;     // [slots]
+    unsigned long long *bytes;  // [slots] stream size (or needed size)
+    uint32_t *err;       // latched error bits
+};
+
+// One batched launch over up to kMaxBatch frames of the same sensor.
+struct Batch {
+    int nframes;
+    int kind;                      // 0 key frames, 1 P frames
+    int slot[kMaxBatch];
+    const float4 *pts[kMaxBatch];
+    long long n[kMaxBatch];
+    uint8_t *out[kMaxBatch];
+    unsigned long long cap[kMaxBatch];
+    long long blk_prefix[kMaxBatch + 1];  // binning blocks before each frame
+    const float4 *kf;              // key-frame planes (P frames) or NULL
+    float4 *kf_out;                // key-frame plane table to fill (K frames) or NULL
+};
+
+struct Poses {
+    double m[kMaxBatch][16];
+};
+
+// ------------------------------------------------------------------------
+// device helpers
+// ------------------------------------------------------------------------
+
+__device__ __forceinline__ bool bits_valid(uint32_t b) { return b < 0x7F800000u && b != 0u; }
+
+// Beam of pixel (i, j): fp32 products of the row and column tables.
+__device__ __forceinline__ void beam(const Geometry &g, int i, int j, float &ux, float &uy, float &uz) {
+    const float ce = __ldg(g.ce + i), se = __ldg(g.se + i);
+    ux = __fmul_rn(ce, __ldg(g.ct + j));
+    uy = __fmul_rn(ce, __ldg(g.st + j));
+    uz = se;
+}
+
+// Along-ray residual against an fp32 plane; true if |e| <= thr.
+__device__ __forceinline__ bool residual(const float4 &pl, float ux, float uy, float uz, float r, float thr,
+                                         float &e) {
+    const float dot = fmaf(pl.x, ux, fmaf(pl.y, uy, __fmul_rn(pl.z, uz)));
+    if (!(dot > 1e-3f)) {
+        e = __int_as_float(0x7f800000);
+        return false;
+    }
+    const float rhat = __fdiv_rn(pl.w, dot);
+    e = __fsub_rn(r, rhat);
+    return fabsf(e) <= thr;
+}
+
+__device__ __forceinline__ int quant_res(float e, float q) {
+    const float k = floorf(__fadd_rn(__fdiv_rn(fabsf(e), q), 0.5f));
+    return e < 0.0f ? -(int)k : (int)k;
+}
+
+__device__ __forceinline__ uint32_t quant_raw(float r, float q) {
+    return (uint32_t)floorf(__fadd_rn(__fdiv_rn(r, q), 0.5f));
+}
+
+__device__ __forceinline__ int need_inliers(float fmin, int nv) {
+    const int need = (int)ceilf(__fmul_rn(fmin, (float)nv));
+    return need < 3 ? 3 : need;
+}
+
+// Sign tests against the boundary tables.
+__device__ __forceinline__ float row_side(const Geometry &g, int k, float z, float rho) {
+    return fmaf(z, __ldg(g.rbc + k), -__fmul_rn(rho, __ldg(g.rbs + k)));
+}
+__device__ __forceinline__ float col_side(const Geometry &g, int j, float x, float y) {
+    return fmaf(y, __ldg(g.cbc + j), -__fmul_rn(x, __ldg(g.cbs + j)));
+}
+
+// Eq. 1-2 for one point: 0 binned (r, pix set), 1 invalid, 2 out of FOV.
+// The pixel is the unique one whose boundary sign tests hold; atan2f only
+// gives the starting guess of a bounded walk.
+__device__ __forceinline__ int bin_point(const Geometry &g, float x, float y, float z, float &r, int &pix) {
+    if (!isfinite(x) || !isfinite(y) || !isfinite(z)) return 1;
+    r = sqrtf(fmaf(x, x, fmaf(y, y, __fmul_rn(z, z))));
+    if (!(r > 0.0f) || !(r <= g.rmax)) return 1;
+    const float rho = sqrtf(fmaf(x, x, __fmul_rn(y, y)));
+    if (row_side(g, 0, z, rho) > 0.0f) return 2;
+    if (!(row_side(g, g.H, z, rho) > 0.0f)) return 2;
+    const float el = atan2f(z, rho) * 57.29577951308232f;
+    int i = (int)floorf((g.elev_max_deg - el) / g.d_el_deg);
+    i = min(max(i, 0), g.H - 1);
+    for (int it = 0; it < g.H && i > 0 && row_side(g, i, z, rho) > 0.0f; it++) i--;
+    for (int it = 0; it < g.H && i < g.H - 1 && !(row_side(g, i + 1, z, rho) > 0.0f); it++) i++;
+    if (row_side(g, i, z, rho) > 0.0f || !(row_side(g, i + 1, z, rho) > 0.0f)) return 2;
+    const float az = atan2f(y, x);
+    int j = (int)floorf((az + 3.14159265358979f) / g.d_az);
+    j = ((j % g.W) + g.W) % g.W;
+    for (int it = 0; it < g.W && !(col_side(g, j, x, y) >= 0.0f); it++) j = (j == 0) ? g.W - 1 : j - 1;
+    for (int it = 0; it < g.W && col_side(g, (j + 1 == g.W) ? 0 : j + 1, x, y) >= 0.0f; it++)
+        j = (j + 1 == g.W) ? 0 : j + 1;
+    if (!(col_side(g, j, x, y) >= 0.0f) || col_side(g, (j + 1 == g.W) ? 0 : j + 1, x, y) >= 0.0f) return 2;
+    pix = i * g.W + j;
+    return 0;
+}
+
+// n' = R^T n in fp64 with a fixed operation order, rounded to fp32.
+__device__ __forceinline__ void rotate_normal(const double *M, float nx, float ny, float nz, float *o) {
+#pragma unroll
+    for (int j = 0; j < 3; j++) {
+        double t = __dmul_rn(M[0 * 4 + j], (double)nx);
+        t = fma(M[1 * 4 + j], (double)ny, t);
+        t = fma(M[2 * 4 + j], (double)nz, t);
+        o[j] = (float)t;
+    }
+}
+
+// Eq. 6: p' = R p + T in fp64, rounded to fp32.
+__device__ __forceinline__ void transform_point(const double *M, float px, float py, float pz, float *o) {
+#pragma unroll
+    for (int i = 0; i < 3; i++) {
+        double t = __dmul_rn(M[i * 4 + 0], (double)px);
+        t = fma(M[i * 4 + 1], (double)py, t);
+        t = fma(M[i * 4 + 2], (double)pz, t);
+        o[i] = (float)__dadd_rn(t, M[i * 4 + 3]);
+    }
+}
+
+// ---- float-float (double-single) arithmetic for compensated moments ----
+
+struct ff {
+    float hi, lo;
+};
+
+__device__ __forceinline__ ff two_sum(float a, float b) {
+    const float s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    const float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+    return {s, e};
+}
+
+__device__ __forceinline__ ff fast_two_sum(float a, float b) {
+    const float s = __fadd_rn(a, b);
+    return {s, __fsub_rn(b, __fsub_rn(s, a))};
+}
+
+__device__ __forceinline__ ff ff_add(ff a, ff b) {
+    ff s = two_sum(a.hi, b.hi);
+    const float lo = __fadd_rn(s.lo, __fadd_rn(a.lo, b.lo));
+    return fast_two_sum(s.hi, lo);
+}
+
+// Exact product of two floats as an unevaluated sum.
+__device__ __forceinline__ ff two_prod(float a, float b) {
+    const float p = __fmul_rn(a, b);
+    return {p, fmaf(a, b, -p)};
+}
+
+// (a.hi + a.lo) * (b.hi + b.lo) ~ exact product of the hi parts plus cross terms.
+__device__ __forceinline__ ff ff_mul(ff a, ff b) {
+    const float p = __fmul_rn(a.hi, b.hi);
+    const float e = fmaf(a.hi, b.hi, -p);
+    const float c = fmaf(a.hi, b.lo, __fmul_rn(a.lo, b.hi));
+    return fast_two_sum(p, __fadd_rn(e, c));
+}
+
+__device__ __forceinline__ double ff_to_d(ff a) { return (double)a.hi + (double)a.lo; }
+
+__device__ __forceinline__ ff shfl_xor_ff(ff v, int off) {
+    return {__shfl_xor_sync(0xffffffffu, v.hi, off), __shfl_xor_sync(0xffffffffu, v.lo, off)};
+}
+
+// Read `width` bits (<= 25) at bit position pos from little-endian words.
+__device__ __forceinline__ uint32_t get_bits(const uint32_t *w, uint64_t pos, int width) {
+    const uint64_t wi = pos >> 5;
+    const int sh = (int)(pos & 31);
+    uint64_t v = w[wi];
+    if (sh + width > 32) v |= (uint64_t)w[wi + 1] << 32;
+    return (uint32_t)((v >> sh) & ((1ull << width) - 1));
+}
+
+// ------------------------------------------------------------------------
+// host-side launchers (one per kernel file)
+// ------------------------------------------------------------------------
+
+cudaError_t launch_bin(const Geometry &g, const Scratch &s, const Batch &b, long long total_blocks,
+                       cudaStream_t st);
+cudaError_t launch_range_image(const Geometry &g, const uint32_t *rimg, float *range, uint32_t *valid,
+                               cudaStream_t st);
+cudaError_t launch_fit(const Geometry &g, const Scratch &s, const Batch &b, const Poses &p, cudaStream_t st);
+cudaError_t launch_merge(const Geometry &g, const Scratch &s, const Batch &b, cudaStream_t st);
+cudaError_t launch_scan(const Geometry &g, const Scratch &s, const Batch &b, cudaStream_t st);
+cudaError_t launch_pack(const Geometry &g, const Scratch &s, const Batch &b, cudaStream_t st);
+cudaError_t launch_decode_prep(const Geometry &g, const uint8_t *bits, unsigned long long nbytes,
+                               const float4 *kf, const double *pose, DecTile *dt, float4 *kf_out,
+                               uint32_t *err, int expect_kind, const Poses *poses, cudaStream_t st);
+cudaError_t launch_decode_px(const Geometry &g, const uint8_t *bits, const DecTile *dt, float *range,
+                             float4 *xyz, uint32_t *err, cudaStream_t st);
+
+}  // namespace lcc

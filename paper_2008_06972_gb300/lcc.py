@@ -1,0 +1,304 @@
+"""ctypes binding of the lcc C ABI (include/lcc.h) — argument marshalling only.
+
+Function names mirror the C entry points.  Device buffers are passed as torch
+CUDA tensors (their ``data_ptr()``) or raw integer addresses; every step of the
+encoder and decoder runs in the CUDA kernels of ``liblcc.so``.  There is no CPU
+fallback: loading fails loudly if the library has not been built.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "liblcc.so")
+
+OK, ERR_INVALID_ARG, ERR_CAPACITY, ERR_CUDA, ERR_TIMEOUT, ERR_CORRUPT, ERR_UNSUPPORTED, ERR_NO_DEVICE = range(8)
+T_EMPTY, T_RAW, T_RUN_START, T_RUN_CONT, T_TEMPORAL = range(5)
+S_EMPTY, S_FAIL, S_FIT, S_TEMPORAL = range(4)
+
+
+class LccError(RuntimeError):
+    def __init__(self, status: int, what: str):
+        super().__init__(f"{what}: {status_string(status)} ({status})")
+        self.status = status
+
+
+class lcc_sensor(ctypes.Structure):
+    _fields_ = [("rows", ctypes.c_int32), ("cols", ctypes.c_int32), ("elev_min_deg", ctypes.c_double),
+                ("elev_max_deg", ctypes.c_double), ("max_range_m", ctypes.c_double)]
+
+
+class lcc_params(ctypes.Structure):
+    _fields_ = [("tile_h", ctypes.c_int32), ("tile_w", ctypes.c_int32), ("fit_thr_m", ctypes.c_float),
+                ("quant_m", ctypes.c_float), ("max_refits", ctypes.c_int32), ("min_inlier_frac", ctypes.c_float),
+                ("merge_runs", ctypes.c_int32), ("max_batch", ctypes.c_int32), ("lookahead", ctypes.c_int32)]
+
+
+class lcc_stats(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_int64) for n in ("points_in", "points_invalid", "points_fov", "points_binned",
+                                               "pixels_valid", "tiles_empty", "tiles_raw", "tiles_run_start",
+                                               "tiles_run_cont", "tiles_temporal")] + \
+               [("fit_rounds", ctypes.c_int64 * 8), ("tiles_borderline", ctypes.c_int64),
+                ("cand", ctypes.c_int64), ("fitted", ctypes.c_int64), ("raw", ctypes.c_int64),
+                ("bytes", ctypes.c_uint64)]
+
+
+TILE_INFO_DTYPE = np.dtype([("plane", "<f4", 4), ("tplane", "<f4", 4), ("kref", "<u4"), ("ahead_mask", "<u4"),
+                            ("status", "u1"), ("rounds", "u1"), ("flags", "u1"), ("n_valid", "u1"),
+                            ("n_inlier", "u1"), ("t_rounds", "u1"), ("t_inlier", "u1"), ("t_status", "u1"),
+                            ("ahead_cnt", "u1", 16)])
+assert TILE_INFO_DTYPE.itemsize == 64
+
+_lib = None
+KERNEL_NAMES = ("bin", "fit", "merge", "scan", "pack", "decode_prep", "decode_px", "range_export")
+
+
+def load(path: str = LIB_PATH):
+    """Load liblcc.so (built by paper_2008_06972_gb300.build)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"{path} is missing: build the CUDA library first (__graft_entry__.build())")
+    L = ctypes.CDLL(path)
+    vp, i32, i64, u64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_uint64
+    sig = {
+        "lcc_status_string": (ctypes.c_char_p, [i32]),
+        "lcc_default_params": (None, [vp]),
+        "lcc_create": (i32, [vp, vp, vp, vp]),
+        "lcc_destroy": (i32, [vp]),
+        "lcc_max_encoded_bytes": (u64, [vp]),
+        "lcc_num_tiles": (i64, [vp]),
+        "lcc_tables": (i32, [vp] * 9),
+        "lcc_range_image": (i32, [vp, vp, i64, vp, vp]),
+        "lcc_keyframe_create": (i32, [vp, vp]),
+        "lcc_keyframe_free": (None, [vp]),
+        "lcc_encode_keyframe": (i32, [vp, vp, i64, vp, vp, u64, vp]),
+        "lcc_encode_pframe": (i32, [vp, vp, vp, vp, i64, vp, u64, vp]),
+        "lcc_encode_pframes": (i32, [vp, vp, i32, vp, vp, vp, vp, vp, vp]),
+        "lcc_encode_sequence": (i32, [vp, i32, i32, vp, vp, vp, vp, vp, vp, vp]),
+        "lcc_encode_sequence_host": (i32, [vp, i32, i32, vp, vp, vp, vp, vp, vp]),
+        "lcc_keyframe_from_stream": (i32, [vp, vp, u64, vp]),
+        "lcc_decode": (i32, [vp, vp, u64, vp, vp, vp, vp, vp]),
+        "lcc_sync": (i32, [vp]),
+        "lcc_last_stats": (i32, [vp, i32, vp]),
+        "lcc_tile_records": (i32, [vp, i32, vp, i64]),
+        "lcc_set_profiling": (i32, [vp, i32]),
+        "lcc_kernel_times": (i32, [vp, vp, vp, vp, i32]),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(L, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = L
+    return L
+
+
+def exported_symbols() -> list[str]:
+    """Entry points this binding expects liblcc.so to export."""
+    return ["lcc_status_string", "lcc_default_params", "lcc_create", "lcc_destroy", "lcc_max_encoded_bytes",
+            "lcc_num_tiles", "lcc_tables", "lcc_range_image", "lcc_keyframe_create", "lcc_keyframe_free",
+            "lcc_encode_keyframe", "lcc_encode_pframe", "lcc_encode_pframes", "lcc_encode_sequence",
+            "lcc_encode_sequence_host", "lcc_keyframe_from_stream", "lcc_decode", "lcc_sync", "lcc_last_stats",
+            "lcc_tile_records", "lcc_set_profiling", "lcc_kernel_times"]
+
+
+def status_string(s: int) -> str:
+    try:
+        return load().lcc_status_string(s).decode()
+    except Exception:
+        return str(s)
+
+
+def _check(st: int, what: str):
+    if st != OK:
+        raise LccError(st, what)
+
+
+def _ptr(x) -> int | None:
+    """Device address of a torch tensor, or an int address, or None."""
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    if hasattr(x, "data_ptr"):
+        if hasattr(x, "is_cuda") and not x.is_cuda:
+            raise ValueError("expected a CUDA tensor")
+        return x.data_ptr()
+    raise TypeError(f"cannot take a device address of {type(x)}")
+
+
+def _arr(ctype, values):
+    return (ctype * len(values))(*values)
+
+
+def default_params(**kw) -> lcc_params:
+    p = lcc_params()
+    load().lcc_default_params(ctypes.byref(p))
+    for k, v in kw.items():
+        setattr(p, k, v)
+    return p
+
+
+def sensor(s) -> lcc_sensor:
+    return lcc_sensor(s.rows, s.cols, s.elev_min_deg, s.elev_max_deg, s.max_range_m)
+
+
+class Keyframe:
+    def __init__(self, ctx: "Context"):
+        self.ctx = ctx
+        h = ctypes.c_void_p()
+        _check(load().lcc_keyframe_create(ctx.h, ctypes.byref(h)), "lcc_keyframe_create")
+        self.h = h
+
+    def free(self):
+        if self.h:
+            load().lcc_keyframe_free(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+class Context:
+    """An lcc context bound to a CUDA stream (torch stream or raw handle)."""
+
+    def __init__(self, sensor_, params: lcc_params | None = None, stream=None):
+        self.lib = load()
+        self.sensor = sensor(sensor_) if not isinstance(sensor_, lcc_sensor) else sensor_
+        self.params = params or default_params()
+        if stream is None:
+            handle = None
+        elif isinstance(stream, int):
+            handle = stream
+        else:
+            handle = stream.cuda_stream
+        self.stream_handle = handle
+        h = ctypes.c_void_p()
+        _check(self.lib.lcc_create(ctypes.byref(h), ctypes.byref(self.sensor), ctypes.byref(self.params), handle),
+               "lcc_create")
+        self.h = h
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.lcc_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # --- queries ---
+    @property
+    def max_encoded_bytes(self) -> int:
+        return int(self.lib.lcc_max_encoded_bytes(self.h))
+
+    @property
+    def num_tiles(self) -> int:
+        return int(self.lib.lcc_num_tiles(self.h))
+
+    def tables(self) -> dict:
+        H, W = self.sensor.rows, self.sensor.cols
+        out = {k: np.zeros(n, np.float32) for k, n in
+               [("ce", H), ("se", H), ("ct", W), ("st", W), ("rbc", H + 1), ("rbs", H + 1), ("cbc", W), ("cbs", W)]}
+        _check(self.lib.lcc_tables(self.h, *[out[k].ctypes.data for k in
+                                             ("ce", "se", "ct", "st", "rbc", "rbs", "cbc", "cbs")]), "lcc_tables")
+        return out
+
+    # --- calls (async on the context stream) ---
+    def lcc_range_image(self, d_pts, n: int, d_range=None, d_valid=None):
+        _check(self.lib.lcc_range_image(self.h, _ptr(d_pts), n, _ptr(d_range), _ptr(d_valid)), "lcc_range_image")
+
+    def lcc_encode_keyframe(self, d_pts, n: int, kf: Keyframe | None, d_out, cap: int, out_bytes):
+        _check(self.lib.lcc_encode_keyframe(self.h, _ptr(d_pts), n, kf.h if kf else None, _ptr(d_out), cap,
+                                            _ptr(out_bytes)), "lcc_encode_keyframe")
+
+    def lcc_encode_pframe(self, kf: Keyframe, pose: np.ndarray, d_pts, n: int, d_out, cap: int, out_bytes):
+        pose = np.ascontiguousarray(pose, dtype=np.float64).reshape(16)
+        _check(self.lib.lcc_encode_pframe(self.h, kf.h, pose.ctypes.data, _ptr(d_pts), n, _ptr(d_out), cap,
+                                          _ptr(out_bytes)), "lcc_encode_pframe")
+
+    def lcc_encode_pframes(self, kf: Keyframe, poses, d_pts: list, n: list, d_out: list, cap: list, out_bytes):
+        poses = np.ascontiguousarray(poses, dtype=np.float64).reshape(-1)
+        nf = len(d_pts)
+        _check(self.lib.lcc_encode_pframes(self.h, kf.h, nf, poses.ctypes.data,
+                                           _arr(ctypes.c_void_p, [_ptr(x) for x in d_pts]),
+                                           _arr(ctypes.c_int64, n), _arr(ctypes.c_void_p, [_ptr(x) for x in d_out]),
+                                           _arr(ctypes.c_uint64, cap), _ptr(out_bytes)), "lcc_encode_pframes")
+
+    def lcc_encode_sequence(self, key_index: int, poses, d_pts: list, n: list, d_out: list, cap: list, out_bytes,
+                            kf: Keyframe | None = None):
+        poses = np.ascontiguousarray(poses, dtype=np.float64).reshape(-1)
+        nf = len(d_pts)
+        _check(self.lib.lcc_encode_sequence(self.h, nf, key_index, poses.ctypes.data,
+                                            _arr(ctypes.c_void_p, [_ptr(x) for x in d_pts]),
+                                            _arr(ctypes.c_int64, n), _arr(ctypes.c_void_p, [_ptr(x) for x in d_out]),
+                                            _arr(ctypes.c_uint64, cap), _ptr(out_bytes), kf.h if kf else None),
+               "lcc_encode_sequence")
+
+    def lcc_encode_sequence_host(self, key_index: int, poses, h_pts: list, h_out: list, cap: list) -> np.ndarray:
+        """HOST buffers: h_pts numpy float32 (n,4) arrays, h_out numpy uint8 arrays.  Synchronous."""
+        poses = np.ascontiguousarray(poses, dtype=np.float64).reshape(-1)
+        nf = len(h_pts)
+        nbytes = np.zeros(nf, np.uint64)
+        _check(self.lib.lcc_encode_sequence_host(self.h, nf, key_index, poses.ctypes.data,
+                                                 _arr(ctypes.c_void_p, [_host_ptr(a) for a in h_pts]),
+                                                 _arr(ctypes.c_int64, [len(a) for a in h_pts]),
+                                                 _arr(ctypes.c_void_p, [_host_ptr(a) for a in h_out]),
+                                                 _arr(ctypes.c_uint64, cap), nbytes.ctypes.data),
+               "lcc_encode_sequence_host")
+        return nbytes
+
+    def lcc_keyframe_from_stream(self, d_bits, nbytes: int, kf: Keyframe):
+        _check(self.lib.lcc_keyframe_from_stream(self.h, _ptr(d_bits), nbytes, kf.h), "lcc_keyframe_from_stream")
+
+    def lcc_decode(self, d_bits, nbytes: int, kf: Keyframe | None, pose, d_range=None, d_xyz4=None, d_valid=None):
+        pose_p = None
+        if pose is not None:
+            pose = np.ascontiguousarray(pose, dtype=np.float64).reshape(16)
+            pose_p = pose.ctypes.data
+        _check(self.lib.lcc_decode(self.h, _ptr(d_bits), nbytes, kf.h if kf else None, pose_p, _ptr(d_range),
+                                   _ptr(d_xyz4), _ptr(d_valid)), "lcc_decode")
+
+    def lcc_sync(self) -> int:
+        return int(self.lib.lcc_sync(self.h))
+
+    def lcc_last_stats(self, frame: int = 0) -> dict:
+        st = lcc_stats()
+        _check(self.lib.lcc_last_stats(self.h, frame, ctypes.byref(st)), "lcc_last_stats")
+        out = {n: getattr(st, n) for n, _ in lcc_stats._fields_}
+        out["fit_rounds"] = list(st.fit_rounds)
+        return out
+
+    def lcc_tile_records(self, frame: int = 0) -> np.ndarray:
+        out = np.zeros(self.num_tiles, TILE_INFO_DTYPE)
+        _check(self.lib.lcc_tile_records(self.h, frame, out.ctypes.data, len(out)), "lcc_tile_records")
+        return out
+
+    def lcc_set_profiling(self, enable: bool):
+        _check(self.lib.lcc_set_profiling(self.h, 1 if enable else 0), "lcc_set_profiling")
+
+    def lcc_kernel_times(self) -> dict:
+        names = (ctypes.c_char * 16 * 16)()
+        launches = np.zeros(16, np.int64)
+        ms = np.zeros(16, np.float64)
+        n = self.lib.lcc_kernel_times(self.h, names, launches.ctypes.data, ms.ctypes.data, 16)
+        return {bytes(names[i]).split(b"\0")[0].decode(): (int(launches[i]), float(ms[i])) for i in range(n)}
+
+
+def _host_ptr(a) -> int:
+    if isinstance(a, np.ndarray):
+        if not a.flags.c_contiguous:
+            raise ValueError("host arrays must be contiguous")
+        return a.ctypes.data
+    if hasattr(a, "data_ptr"):
+        return a.data_ptr()
+    raise TypeError(type(a))

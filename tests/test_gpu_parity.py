@@ -1,0 +1,364 @@
+"""GPU path vs the CPU oracle, through the C ABI.
+
+Layered parity (the contract):
+* bit-exact: range-image binning, tile membership and occupancy, the K-tile
+  lookup of the temporal test, and — given the GPU's own fp32 planes and fit
+  decisions — the whole packed stream (modes, runs, fitted bits, residual and
+  raw codes);  decoding is bit-exact on both sides;
+* tolerance: independently fitted planes agree within 1e-5 relative; a tile's
+  fit decision or inlier count may differ only where a residual lies within
+  1e-6 m of the threshold (the borderline tiles, counted and reported).
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle as O
+import synth
+from tests import harness as H
+from tests import streamfmt
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    from paper_2008_06972_gb300 import lcc
+    lcc.load()
+
+
+def _oparams(tile=(4, 4), thr=0.05, q=0.02, R=3, fmin=0.75, merge=1):
+    return O.params(tile[0], tile[1], thr, q, R, fmin, merge)
+
+
+def _gparams(tile=(4, 4), thr=0.05, q=0.02, R=3, fmin=0.75, merge=1, **kw):
+    return dict(tile_h=tile[0], tile_w=tile[1], fit_thr_m=thr, quant_m=q, max_refits=R, min_inlier_frac=fmin,
+                merge_runs=merge, **kw)
+
+
+def _compare_spatial(s, p, rng, recs, ofits, thr, skip=None):
+    """Layer-2 comparison of own spatial fits.  Returns (n_compared, n_borderline)."""
+    from paper_2008_06972_gb300 import lcc
+    assert (recs["n_valid"] == ofits["n_valid"]).all(), "tile membership differs"
+    g_ok = recs["status"] == lcc.S_FIT
+    o_ok = ofits["status"] == O.FIT_OK
+    border = 0
+    compared = 0
+    for t in range(len(recs)):
+        if skip is not None and skip[t]:
+            continue
+        if ofits["n_valid"][t] < 3:
+            assert recs["status"][t] in (lcc.S_EMPTY, lcc.S_FAIL)
+            continue
+        compared += 1
+        same = (g_ok[t] == o_ok[t]) and (recs["n_inlier"][t] == ofits["n_inlier"][t] or not (g_ok[t] or o_ok[t]))
+        close = True
+        if g_ok[t] and o_ok[t]:
+            close = H.plane_close(recs["plane"][t], ofits["plane"][t])
+        if same and close and (not g_ok[t] or recs["rounds"][t] == ofits["rounds"][t]):
+            continue
+        is_border = bool(ofits["borderline"][t]) or bool(recs["flags"][t] & 1) or \
+            H.borderline_tile(s, p, rng, recs["plane"][t], ofits["plane"][t], t, thr)
+        assert is_border, f"tile {t}: gpu status {recs['status'][t]} inl {recs['n_inlier'][t]} " \
+                          f"plane {recs['plane'][t]} rounds {recs['rounds'][t]} | oracle status " \
+                          f"{ofits['status'][t]} inl {ofits['n_inlier'][t]} plane {ofits['plane'][t]} " \
+                          f"rounds {ofits['rounds'][t]}"
+        border += 1
+    return compared, border
+
+
+def _check_decode(c, s, bits, rng, q, kf_gpu=None, kft=None, pose=None):
+    st, drng, dxyz, dvalid = H.decode(c, bits, kf_gpu, pose)
+    assert st == 0
+    orng, oxyz, ovalid = O.decode(s, bits, kft, pose)
+    assert np.array_equal(drng.view(np.uint32), orng.view(np.uint32))
+    assert np.array_equal(dxyz.view(np.uint32), oxyz.view(np.uint32))
+    assert np.array_equal(dvalid, ovalid)
+    m = rng > 0
+    assert ((drng > 0) == m).all()
+    err = np.abs(drng[m] - rng[m]).max() if m.any() else 0.0
+    assert err <= q / 2 + 1e-5
+    return err
+
+
+def _keyframe_case(sensor_, pts, **kw):
+    from paper_2008_06972_gb300 import lcc
+    s = O.sensor(sensor_)
+    p = _oparams(**kw)
+    c = H.ctx(sensor_, **_gparams(**kw))
+    gbits, recs = H.encode_keyframe(c, pts)
+    rng, _, _ = O.range_image(s, pts)
+    ofits = O.fit_tiles(s, p, rng)
+    compared, border = _compare_spatial(s, p, rng, recs, ofits, p.fit_thr_m)
+    assert border <= max(2, 0.005 * compared), f"{border} borderline tiles of {compared}"
+    # Layer 1: the oracle's merge + code + pack on the GPU's planes reproduces the GPU stream
+    planes, ok = H.gpu_planes(recs)
+    cbits, _, _ = O.pack(s, p, 0, rng, planes, ok)
+    assert cbits.tobytes() == gbits.tobytes()
+    # with identical planes the streams are identical outright
+    obits, _, _, _ = O.encode_keyframe(s, p, pts)
+    same_planes = np.array_equal(recs["plane"][ok.astype(bool)].view(np.uint32),
+                                 ofits["plane"][ok.astype(bool)].view(np.uint32)) and \
+        np.array_equal(ok, (ofits["status"] == O.FIT_OK).astype(np.uint8))
+    if same_planes:
+        assert obits.tobytes() == gbits.tobytes()
+    err = _check_decode(c, s, gbits, rng, p.quant_m)
+    stats = c.lcc_last_stats(0) if False else None
+    return dict(bytes=len(gbits), border=border, compared=compared, err=err, same_planes=same_planes, ctx=c,
+                recs=recs, bits=gbits)
+
+
+# ------------------------------------------------------------------ tables, binning --
+
+def test_sensor_tables_match_oracle():
+    for sen in (synth.CFG1_SENSOR, synth.HDL64_SENSOR, synth.Sensor(18, 515, -15, 15, 80.0)):
+        c = H.ctx(sen)
+        g = c.tables()
+        o = O.tables(O.sensor(sen))
+        for k in g:
+            assert np.array_equal(g[k].view(np.uint32), o[k].view(np.uint32)), k
+
+
+@pytest.mark.parametrize("case", ["cfg1", "cfg2", "offgrid", "ragged"])
+def test_range_image_bit_exact(case, cfg1, cfg2_seq):
+    if case == "cfg1":
+        sen, pts = cfg1
+    elif case == "cfg2":
+        sen, pts = cfg2_seq.sensor, cfg2_seq.frames[0]
+    elif case == "offgrid":
+        sen = synth.HDL64_SENSOR
+        pts = synth.offgrid_points(300000, seed=17, r_hi=95.0, elev_lo_deg=-40, elev_hi_deg=10)
+        pts[::997, 0] = np.nan
+        pts[::1009, :3] = 0.0
+        pts[::1013, 1] = np.inf
+    else:
+        sen = synth.Sensor(18, 515, -15.0, 15.0, 80.0)
+        pts = synth.Scene(9, 4, 6, 10, enclose=True).render(sen, sigma=0.02, dropout=0.05, seed=9)
+        pts = np.concatenate([pts, pts[::3] * np.float32(1.01), pts[::5]])   # collisions, exact duplicates
+    s = O.sensor(sen)
+    c = H.ctx(sen)
+    d = H.to_dev(pts)
+    npx = sen.rows * sen.cols
+    rng = torch.empty(npx, dtype=torch.float32, device="cuda")
+    valid = torch.empty((npx + 31) // 32, dtype=torch.int32, device="cuda")
+    c.lcc_range_image(d, len(pts), rng, valid)
+    assert c.lcc_sync() == 0
+    orng, _, ost = O.range_image(s, pts)
+    assert np.array_equal(rng.cpu().numpy().view(np.uint32), orng.reshape(-1).view(np.uint32))
+    obits = np.packbits((orng.reshape(-1) > 0).astype(np.uint8), bitorder="little")
+    obits = np.concatenate([obits, np.zeros((-len(obits)) % 4, np.uint8)]).view(np.uint32)
+    assert np.array_equal(valid.cpu().numpy().view(np.uint32), obits)
+    st = c.lcc_last_stats(0)
+    assert st["points_in"] == len(pts)
+    assert (st["points_binned"], st["points_invalid"], st["points_fov"]) == (ost[0], ost[1], ost[2])
+
+
+# -------------------------------------------------------------------- key frames --
+
+@pytest.mark.parametrize("tile,thr", [((4, 4), 0.05), ((4, 8), 0.05), ((8, 8), 0.05), ((8, 16), 0.05),
+                                      ((4, 4), 0.02), ((8, 8), 0.10)])
+def test_keyframe_parity_cfg1(cfg1, tile, thr):
+    sen, pts = cfg1
+    r = _keyframe_case(sen, pts, tile=tile, thr=thr)
+    assert r["err"] <= 0.01 + 1e-5
+
+
+@pytest.mark.parametrize("merge,fmin,R", [(0, 0.75, 3), (1, 1.0, 3), (1, 0.75, 0), (1, 0.5, 6)])
+def test_keyframe_parity_variants(cfg1, merge, fmin, R):
+    sen, pts = cfg1
+    _keyframe_case(sen, pts, merge=merge, fmin=fmin, R=R)
+
+
+@pytest.mark.parametrize("tile", [(4, 4), (8, 16)])
+def test_keyframe_parity_ragged_sensor(tile):
+    sen = synth.Sensor(18, 515, -15.0, 15.0, 80.0)   # partial edge tiles in both directions
+    pts = synth.Scene(21, 4, 6, 10, enclose=True).render(sen, sigma=0.02, dropout=0.05, seed=21)
+    _keyframe_case(sen, pts, tile=tile)
+
+
+def test_keyframe_parity_full_size_hdl64(cfg2_seq):
+    """The bench's workload size: a 64x2048 key frame."""
+    seq = cfg2_seq
+    r = _keyframe_case(seq.sensor, seq.frames[seq.key_index])
+    recs = r["recs"]
+    assert (recs["status"] == 2).sum() > 4000
+
+
+def test_empty_and_tiny_frames():
+    sen = synth.CFG1_SENSOR
+    for pts in (np.zeros((0, 4), np.float32), np.array([[10, 0, 0, 0]], np.float32)):
+        r = _keyframe_case(sen, pts)
+        assert r["bytes"] == len(O.encode_keyframe(O.sensor(sen), _oparams(), pts)[0])
+
+
+def test_schedule_invariance_and_determinism(cfg1):
+    sen, pts = cfg1
+    ref = None
+    for la in (0, 1, 8, 16):
+        c = H.ctx(sen, lookahead=la)
+        b1, _ = H.encode_keyframe(c, pts)
+        b2, _ = H.encode_keyframe(c, pts)
+        assert b1.tobytes() == b2.tobytes()
+        ref = b1 if ref is None else ref
+        assert b1.tobytes() == ref.tobytes()
+
+
+# ------------------------------------------------------------------- P frames --
+
+def _pframe_case(seq, frames, tile=(4, 4), thr=0.05, poses=None):
+    from paper_2008_06972_gb300 import lcc
+    s = O.sensor(seq.sensor)
+    p = _oparams(tile=tile, thr=thr)
+    c = H.ctx(seq.sensor, **_gparams(tile=tile, thr=thr, max_batch=max(16, len(frames))))
+    kf = lcc.Keyframe(c)
+    kbits, krecs = H.encode_keyframe(c, seq.frames[seq.key_index], kf)
+    okft = O.kf_table_from_stream(s, kbits, c.num_tiles)
+    poses = [seq.poses[f] for f in frames] if poses is None else poses
+    pbits, precs = H.encode_pframes(c, kf, poses, [seq.frames[f] for f in frames])
+    kf2 = lcc.Keyframe(c)
+    c.lcc_keyframe_from_stream(torch.from_numpy(kbits).cuda(), len(kbits), kf2)
+    assert c.lcc_sync() == 0
+    total_border = 0
+    for i, f in enumerate(frames):
+        pts = seq.frames[f]
+        rng, _, _ = O.range_image(s, pts)
+        recs = precs[i]
+        otmp = O.temporal_tiles(s, p, rng, okft, poses[i])
+        # the K tile of every anchor is found identically (FP64 transform + exact binning)
+        found = otmp["status"] > 0
+        assert np.array_equal(recs["t_status"] > 0, found)
+        assert np.array_equal(recs["kref"][found].astype(np.int64), otmp["kref"][found].astype(np.int64))
+        assert np.array_equal(recs["tplane"][found][:, :3].view(np.uint32),
+                              otmp["plane"][found][:, :3].view(np.uint32))
+        border = 0
+        for t in np.nonzero(found)[0]:
+            same = recs["t_status"][t] == otmp["status"][t] and recs["t_inlier"][t] == otmp["n_inlier"][t]
+            cg, co = float(recs["tplane"][t][3]), float(otmp["plane"][t][3])
+            close = abs(cg - co) <= H.PLANE_TOL * max(abs(co), 1.0)
+            if same and close:
+                continue
+            assert otmp["borderline"][t] or (recs["flags"][t] & 1) or \
+                H.borderline_tile(s, p, rng, recs["tplane"][t], otmp["plane"][t], t, p.fit_thr_m), \
+                f"frame {f} tile {t}: gpu {recs['t_status'][t]} {recs['t_inlier'][t]} {cg} | " \
+                f"oracle {otmp['status'][t]} {otmp['n_inlier'][t]} {co}"
+            border += 1
+        ofits = O.fit_tiles(s, p, rng)
+        temporal = recs["status"] == lcc.S_TEMPORAL
+        _, b2 = _compare_spatial(s, p, rng, recs, ofits, p.fit_thr_m,
+                                 skip=temporal | (otmp["status"] == 2))
+        total_border += border + b2
+        planes, ok = H.gpu_planes(recs)
+        tplanes, kref = H.gpu_temporal(recs)
+        cbits, _, _ = O.pack(s, p, 1, rng, planes, ok, tplanes, kref)
+        assert cbits.tobytes() == pbits[i].tobytes(), f"frame {f}: stream differs from the oracle's packing"
+        assert (streamfmt.tile_codes(pbits[i]) == 4).sum() == temporal.sum()
+        _check_decode(c, s, pbits[i], rng, p.quant_m, kf_gpu=kf2, kft=okft, pose=poses[i])
+    return total_border
+
+
+def test_pframe_parity_cfg2(cfg2_seq):
+    seq = cfg2_seq
+    frames = [f for f in range(len(seq.frames)) if f != seq.key_index]
+    border = _pframe_case(seq, frames)
+    assert border <= 20
+
+
+@pytest.mark.parametrize("tile,thr", [((8, 8), 0.05), ((4, 4), 0.10), ((8, 16), 0.02)])
+def test_pframe_parity_tiles(cfg2_seq, tile, thr):
+    seq = cfg2_seq
+    _pframe_case(seq, [0, seq.key_index + 1], tile=tile, thr=thr)
+
+
+def test_pframe_noisy_pose(cfg2_seq):
+    seq = cfg2_seq
+    poses = [synth.perturb_pose(seq.poses[f], 0.01, 0.05, 100 + f) for f in (2, 8)]
+    _pframe_case(seq, [2, 8], poses=poses)
+
+
+def test_sequence_call_matches_separate_calls(cfg2_seq):
+    from paper_2008_06972_gb300 import lcc
+    seq = cfg2_seq
+    n = len(seq.frames)
+    c = H.ctx(seq.sensor, max_batch=16)
+    ds = [H.to_dev(p) for p in seq.frames]
+    outs = [H.out_buf(c) for _ in range(n)]
+    nb = torch.zeros(n, dtype=torch.int64, device="cuda")
+    kf = lcc.Keyframe(c)
+    c.lcc_encode_sequence(seq.key_index, seq.poses, ds, [len(p) for p in seq.frames], outs,
+                          [o.numel() for o in outs], nb, kf)
+    assert c.lcc_sync() == 0
+    nbs = nb.cpu().numpy()
+    seq_bits = [outs[i][:nbs[i]].cpu().numpy() for i in range(n)]
+    c2 = H.ctx(seq.sensor, max_batch=16)
+    kf2 = lcc.Keyframe(c2)
+    kbits, _ = H.encode_keyframe(c2, seq.frames[seq.key_index], kf2)
+    assert kbits.tobytes() == seq_bits[seq.key_index].tobytes()
+    others = [f for f in range(n) if f != seq.key_index]
+    pb, _ = H.encode_pframes(c2, kf2, [seq.poses[f] for f in others], [seq.frames[f] for f in others])
+    for i, f in enumerate(others):
+        assert pb[i].tobytes() == seq_bits[f].tobytes()
+    # host-buffer variant (end-to-end path of the bench)
+    h_out = [np.zeros(c.max_encoded_bytes, np.uint8) for _ in range(n)]
+    nbh = c.lcc_encode_sequence_host(seq.key_index, seq.poses, [np.ascontiguousarray(p) for p in seq.frames], h_out,
+                                     [len(h) for h in h_out])
+    for f in range(n):
+        assert h_out[f][:nbh[f]].tobytes() == seq_bits[f].tobytes()
+
+
+# ------------------------------------------------------------------ errors --
+
+def test_capacity_error_reports_needed_size(cfg1):
+    from paper_2008_06972_gb300 import lcc
+    sen, pts = cfg1
+    c = H.ctx(sen)
+    need = len(H.encode_keyframe(c, pts)[0])
+    out = torch.zeros(256, dtype=torch.uint8, device="cuda")
+    nb = torch.zeros(1, dtype=torch.int64, device="cuda")
+    c.lcc_encode_keyframe(H.to_dev(pts), len(pts), None, out, 256, nb)
+    assert c.lcc_sync() == lcc.ERR_CAPACITY
+    assert int(nb.item()) == need
+    assert c.lcc_sync() == lcc.OK     # the error is cleared once reported
+    b, _ = H.encode_keyframe(c, pts)  # the context stays usable
+    assert len(b) == need
+
+
+def test_corrupt_streams_are_rejected(cfg1):
+    from paper_2008_06972_gb300 import lcc
+    sen, pts = cfg1
+    c = H.ctx(sen)
+    bits, _ = H.encode_keyframe(c, pts)
+    cases = [bits[:-4], bits[:40]]
+    bad = bits.copy()
+    bad[0] ^= 1
+    cases.append(bad)
+    bad = bits.copy()
+    bad[64 + (16 * 512 // 8)] = 0x33     # first tile codes: a run continuation at the row start
+    cases.append(bad)
+    bad = bits.copy()
+    bad[44] ^= 0x10                       # fitted count no longer matches the fitted bits
+    cases.append(bad)
+    for b in cases:
+        padded = np.concatenate([b, np.zeros(64, np.uint8)])
+        st, _, _, _ = H.decode(c, padded[:max(len(b), 1)] if len(b) >= 64 else padded[:len(b)])
+        assert st == lcc.ERR_CORRUPT
+        assert O.decode_status(O.sensor(sen), b) == O.ERR_CORRUPT
+    st, _, _, _ = H.decode(c, bits)
+    assert st == lcc.OK
+
+
+def test_invalid_arguments_fail_fast(cfg1):
+    from paper_2008_06972_gb300 import lcc
+    sen, pts = cfg1
+    with pytest.raises(lcc.LccError) as e:
+        H.ctx(sen, tile_h=3, tile_w=5)
+    assert e.value.status == lcc.ERR_UNSUPPORTED
+    c = H.ctx(sen)
+    d = H.to_dev(pts)
+    out = H.out_buf(c)
+    with pytest.raises(lcc.LccError) as e:
+        c.lcc_encode_keyframe(d, len(pts), None, out[1:], out.numel() - 1, None)   # misaligned output
+    assert e.value.status == lcc.ERR_INVALID_ARG
