@@ -321,7 +321,8 @@ __global__ void __launch_bounds__(kDecWarps * 32) k_decode_px(Geometry g, const 
             }
         }
         if (range) range[p] = r;
-        if (xyz) xyz[p] = make_float4(__fmul_rn(r, ux), __fmul_rn(r, uy), __fmul_rn(r, uz), 0.f);
+        if (xyz) xyz[p] = v[m] ? make_float4(__fmul_rn(r, ux), __fmul_rn(r, uy), __fmul_rn(r, uz), 0.f)
+                               : make_float4(0.f, 0.f, 0.f, 0.f);
     }
     if (bad) atomicOr(err, E_CORRUPT);
 }

@@ -10,9 +10,9 @@
 // first valid point) are accumulated in float-float (TwoSum / exact products),
 // reduced across the segment with xor shuffles (every lane ends with the same
 // bits), then one lane forms the covariance in FP64 and solves for the
-// smallest eigenvector: an fp32 trigonometric seed, FP64 Newton steps on
-// det(C - lambda I), and the eigenvector as the largest cross product of two
-// rows of C - lambda I.  The fp32 plane is broadcast and every lane tests its
+// smallest eigenvector (largest eigenpair by Newton + cross products, then an
+// exact 2x2 Jacobi rotation in its orthogonal complement; see solve_plane).
+// The fp32 plane is broadcast and every lane tests its
 // pixels with the along-ray residual; ballots give the inlier set.
 //
 // Temporal test (P frames, before the spatial fit): the anchor is moved to
@@ -45,6 +45,16 @@ __device__ __forceinline__ ff seg_sum(ff v) {
 }
 
 // FP64 plane of the moments: returns true if the scatter matrix is degenerate.
+//
+// The smallest eigenvector of C is found without ever resolving the smallest
+// eigenvalue from the characteristic polynomial (whose root is only accurate
+// to eps*lambda_max^2/lambda_mid): the largest eigenpair is well conditioned,
+// so lambda_max comes from Newton steps on det(C - l I) started above it from
+// an fp32 trigonometric seed, and its eigenvector from the largest cross
+// product of two rows of C - lambda_max I.  C is then projected onto the plane
+// orthogonal to that vector and the 2x2 problem is solved by one exact Jacobi
+// rotation, which gives lambda_min, lambda_mid and the normal with absolute
+// accuracy ~eps*lambda_max, like a full Jacobi sweep.
 __device__ __noinline__ bool solve_plane(const double m1[3], const double m2[6], int n, float ax, float ay,
                                          float az, float4 &pl, float &ratio) {
     const double inv = 1.0 / (double)n;
@@ -52,12 +62,10 @@ __device__ __noinline__ bool solve_plane(const double m1[3], const double m2[6],
     const double cxx = m2[0] * inv - mx * mx, cxy = m2[1] * inv - mx * my, cxz = m2[2] * inv - mx * mz;
     const double cyy = m2[3] * inv - my * my, cyz = m2[4] * inv - my * mz, czz = m2[5] * inv - mz * mz;
     const double tr = cxx + cyy + czz;
-    if (!(tr > 0.0)) {
-        pl = make_float4(0.f, 0.f, 0.f, 0.f);
-        ratio = 0.f;
-        return true;
-    }
-    // fp32 seed of the smallest eigenvalue (trigonometric closed form)
+    pl = make_float4(0.f, 0.f, 0.f, 0.f);
+    ratio = 0.f;
+    if (!(tr > 0.0)) return true;
+    // fp32 seed of the largest eigenvalue (trigonometric closed form)
     const float fxx = (float)cxx, fyy = (float)cyy, fzz = (float)czz;
     const float fxy = (float)cxy, fxz = (float)cxz, fyz = (float)cyz;
     const float q = (fxx + fyy + fzz) * (1.0f / 3.0f);
@@ -71,55 +79,107 @@ __device__ __noinline__ bool solve_plane(const double m1[3], const double m2[6],
         const float bxx = dx * ip, byy = dy * ip, bzz = dz * ip, bxy = fxy * ip, bxz = fxz * ip, byz = fyz * ip;
         const float detb = bxx * (byy * bzz - byz * byz) - bxy * (bxy * bzz - byz * bxz) + bxz * (bxy * byz - byy * bxz);
         const float rr = fminf(fmaxf(0.5f * detb, -1.0f), 1.0f);
-        const float phi = acosf(rr) * (1.0f / 3.0f);
-        seed = q + 2.0f * pp * cosf(phi + 2.09439510239f);
+        seed = q + 2.0f * pp * cosf(acosf(rr) * (1.0f / 3.0f));
         spread = pp;
     }
-    // FP64 Newton on f(l) = det(C - l I) from below (f is convex and
-    // decreasing left of the smallest root, so the iterates rise to it).
-    const double scale = (double)spread + 1e-30;
-    double lam = (double)seed - 3e-5 * scale;
-    for (int it = 0; it < 5; it++) {
+    // Newton on f(l) = det(C - l I) from above lambda_max: f is concave and
+    // decreasing there, so the iterates fall monotonically onto the root.
+    const double scale = (double)spread + 1e-30 * tr;
+    double lam = (double)seed + 3e-5 * scale;
+    for (int it = 0; it < 6; it++) {
         const double a = cxx - lam, b = cyy - lam, c = czz - lam;
         const double myz = b * c - cyz * cyz, mxz = a * c - cxz * cxz, mxy = a * b - cxy * cxy;
         const double det = a * myz - cxy * (cxy * c - cyz * cxz) + cxz * (cxy * cyz - b * cxz);
-        const double dsum = myz + mxz + mxy;  // -f'(l)
+        const double dsum = myz + mxz + mxy;  // -f'(l) > 0 above the largest root
         if (!(dsum > 0.0)) break;
         const double step = det * (double)__frcp_rn((float)dsum);
         lam += step;
-        if (fabs(step) <= 1e-16 * scale) break;
+        if (fabs(step) <= 1e-17 * scale) break;
     }
-    // the two other eigenvalues from the trace and the sum of principal minors
-    const double c1 = (cyy * czz - cyz * cyz) + (cxx * czz - cxz * cxz) + (cxx * cyy - cxy * cxy);
-    const double s = tr - lam;
-    const double prod = c1 - lam * s;
-    double disc = s * s - 4.0 * prod;
-    disc = disc > 0.0 ? disc : 0.0;
-    const double l2 = 0.5 * (s + sqrt(disc));
-    const bool degenerate = !(prod > 1e-12 * l2 * l2);   // lambda_mid <= 1e-12 lambda_max
-    ratio = l2 > 0.0 ? (float)(prod / (l2 * l2)) : 0.0f;
-    // eigenvector: largest cross product of two rows of C - lam I
-    const double a = cxx - lam, b = cyy - lam, c = czz - lam;
-    const double v0x = cxy * cyz - b * cxz, v0y = cxz * cxy - cyz * a, v0z = b * a - cxy * cxy;     // r0 x r1
-    const double v1x = cxy * c - cxz * cyz, v1y = cxz * cxz - a * c, v1z = a * cyz - cxy * cxz;     // r0 x r2
-    const double v2x = b * c - cyz * cyz, v2y = cyz * cxz - cxy * c, v2z = cxy * cyz - b * cxz;     // r1 x r2
-    const double n0 = v0x * v0x + v0y * v0y + v0z * v0z;
-    const double n1 = v1x * v1x + v1y * v1y + v1z * v1z;
-    const double n2 = v2x * v2x + v2y * v2y + v2z * v2z;
-    double vx = v2x, vy = v2y, vz = v2z, nn = n2;
-    if (n1 > nn) { vx = v1x; vy = v1y; vz = v1z; nn = n1; }
-    if (n0 > nn) { vx = v0x; vy = v0y; vz = v0z; nn = n0; }
-    if (!(nn > 0.0)) {
-        pl = make_float4(0.f, 0.f, 0.f, 0.f);
-        return true;
+    // eigenvector of lambda_max: largest cross product of two rows of C - lam I
+    double v2x, v2y, v2z;
+    {
+        const double a = cxx - lam, b = cyy - lam, c = czz - lam;
+        const double x0 = cxy * cyz - b * cxz, y0 = cxz * cxy - cyz * a, z0 = b * a - cxy * cxy;   // r0 x r1
+        const double x1 = cxy * c - cxz * cyz, y1 = cxz * cxz - a * c, z1 = a * cyz - cxy * cxz;   // r0 x r2
+        const double x2 = b * c - cyz * cyz, y2 = cyz * cxz - cxy * c, z2 = cxy * cyz - b * cxz;   // r1 x r2
+        const double n0 = x0 * x0 + y0 * y0 + z0 * z0, n1 = x1 * x1 + y1 * y1 + z1 * z1,
+                     n2 = x2 * x2 + y2 * y2 + z2 * z2;
+        v2x = x2; v2y = y2; v2z = z2;
+        double nn = n2;
+        if (n1 > nn) { v2x = x1; v2y = y1; v2z = z1; nn = n1; }
+        if (n0 > nn) { v2x = x0; v2y = y0; v2z = z0; nn = n0; }
+        if (!(nn > 1e-24 * tr * tr * tr * tr)) {
+            // C - lam I has rank <= 1 (lambda_mid ~ lambda_max): its largest row
+            // is the normal direction; take any unit vector orthogonal to it.
+            const double r0 = a * a + cxy * cxy + cxz * cxz, r1 = cxy * cxy + b * b + cyz * cyz,
+                         r2 = cxz * cxz + cyz * cyz + c * c;
+            double wx = a, wy = cxy, wz = cxz;
+            if (r1 > r0 && r1 >= r2) { wx = cxy; wy = b; wz = cyz; }
+            else if (r2 > r0 && r2 > r1) { wx = cxz; wy = cyz; wz = c; }
+            const double aw = fabs(wx), bw = fabs(wy), cw = fabs(wz);
+            // w x e_k with e_k the axis least aligned with w
+            if (aw <= bw && aw <= cw) { v2x = 0.0; v2y = wz; v2z = -wy; }
+            else if (bw <= cw) { v2x = -wz; v2y = 0.0; v2z = wx; }
+            else { v2x = wy; v2y = -wx; v2z = 0.0; }
+            nn = v2x * v2x + v2y * v2y + v2z * v2z;
+            if (!(nn > 0.0)) return true;
+        }
+        const double in = rsqrt(nn);
+        v2x *= in; v2y *= in; v2z *= in;
     }
-    const double in = rsqrt(nn);
-    double nx = vx * in, ny = vy * in, nz = vz * in;
+    // orthonormal basis (u, w) of the plane orthogonal to v2
+    double ux, uy, uz;
+    {
+        const double ax2 = fabs(v2x), ay2 = fabs(v2y), az2 = fabs(v2z);
+        if (ax2 <= ay2 && ax2 <= az2) { ux = 0.0; uy = v2z; uz = -v2y; }
+        else if (ay2 <= az2) { ux = -v2z; uy = 0.0; uz = v2x; }
+        else { ux = v2y; uy = -v2x; uz = 0.0; }
+        const double in = rsqrt(ux * ux + uy * uy + uz * uz);
+        ux *= in; uy *= in; uz *= in;
+    }
+    const double wx = v2y * uz - v2z * uy, wy = v2z * ux - v2x * uz, wz = v2x * uy - v2y * ux;
+    // B = [u w]^T C [u w]
+    const double cux = cxx * ux + cxy * uy + cxz * uz, cuy = cxy * ux + cyy * uy + cyz * uz,
+                 cuz = cxz * ux + cyz * uy + czz * uz;
+    const double cwx = cxx * wx + cxy * wy + cxz * wz, cwy = cxy * wx + cyy * wy + cyz * wz,
+                 cwz = cxz * wx + cyz * wy + czz * wz;
+    const double b00 = ux * cux + uy * cuy + uz * cuz;
+    const double b01 = ux * cwx + uy * cwy + uz * cwz;
+    const double b11 = wx * cwx + wy * cwy + wz * cwz;
+    // one Jacobi rotation diagonalises the 2x2 block
+    double e0, e1, c0 = 1.0, s0 = 0.0;
+    if (b01 != 0.0) {
+        const double tau = (b11 - b00) / (2.0 * b01);
+        const double t = (tau >= 0.0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(tau * tau + 1.0));
+        c0 = rsqrt(t * t + 1.0);
+        s0 = t * c0;
+        e0 = b00 - t * b01;
+        e1 = b11 + t * b01;
+    } else {
+        e0 = b00;
+        e1 = b11;
+    }
+    // eigenvectors in the (u, w) basis: (c, -s) for e0 and (s, c) for e1
+    double nx, ny, nz, lmin, lmid;
+    if (e0 <= e1) {
+        nx = c0 * ux - s0 * wx; ny = c0 * uy - s0 * wy; nz = c0 * uz - s0 * wz;
+        lmin = e0; lmid = e1;
+    } else {
+        nx = s0 * ux + c0 * wx; ny = s0 * uy + c0 * wy; nz = s0 * uz + c0 * wz;
+        lmin = e1; lmid = e0;
+    }
+    (void)lmin;
+    const double lmax = lam;
+    const bool degenerate = !(lmid > 1e-12 * lmax);   // lambda_mid <= 1e-12 lambda_max
+    ratio = lmax > 0.0 ? (float)(lmid / lmax) : 0.0f;
+    const double in = rsqrt(nx * nx + ny * ny + nz * nz);
+    nx *= in; ny *= in; nz *= in;
     double d = nx * ((double)ax + mx) + ny * ((double)ay + my) + nz * ((double)az + mz);
     bool flip;
     if (fabs(d) < 1e-9) {
-        const double ux = fabs(nx), uy = fabs(ny), uz = fabs(nz);
-        const double big = (ux >= uy && ux >= uz) ? nx : ((uy >= uz) ? ny : nz);
+        const double ux3 = fabs(nx), uy3 = fabs(ny), uz3 = fabs(nz);
+        const double big = (ux3 >= uy3 && ux3 >= uz3) ? nx : ((uy3 >= uz3) ? ny : nz);
         flip = big < 0.0;
     } else {
         flip = d < 0.0;

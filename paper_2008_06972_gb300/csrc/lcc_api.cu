@@ -590,9 +590,11 @@ lcc_status lcc_decode(lcc_ctx *c, const uint8_t *d_bits, uint64_t nbytes, const 
     LCC_LAUNCH(c, 6, launch_decode_px(c->g, d_bits, c->d_dec, d_range, reinterpret_cast<float4 *>(d_xyz4), c->s.err,
                                       c->stream));
     if (d_valid) {
+        // a stream too short to hold the bitmap is latched as corrupt by the prep kernel
         const size_t words = ((size_t)c->g.H * c->g.W + 31) / 32;
-        if (nbytes < (uint64_t)kHeaderBytes + 4 * words) return LCC_ERR_CORRUPT;
-        LCC_CUDA(cudaMemcpyAsync(d_valid, d_bits + kHeaderBytes, 4 * words, cudaMemcpyDeviceToDevice, c->stream));
+        if (nbytes >= (uint64_t)kHeaderBytes + 4 * words)
+            LCC_CUDA(cudaMemcpyAsync(d_valid, d_bits + kHeaderBytes, 4 * words, cudaMemcpyDeviceToDevice,
+                                     c->stream));
     }
     return LCC_OK;
 }
