@@ -1,0 +1,326 @@
+"""Throughput of the spatio-temporal LiDAR encoder on one synthetic HDL-64E sequence.
+
+Workload (one step): a 10-frame sequence of 64x2048 range images (about 1.3 M
+points), the middle frame spatially encoded as the key frame and the nine
+others temporally + spatially encoded against it (Sec. III), tiles 4x4,
+threshold 0.05 m, quantisation 0.02 m (max decode error 0.01 m <= 2 cm).
+Inputs are resident in HBM; L2 is flushed (256 MiB write) between timed steps
+and the flush is outside the per-step CUDA-event timing.
+
+Prints one JSON line.  --impl reference times the CPU oracle (plain C, one
+core) on a bounded sample of the same workload instead.
+Multi-GPU: one process per GPU (torchrun); each rank encodes its own sequence
+(no data-path collective; weak scaling); timing is the max over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Mpoints/s encoded at ≤2 cm max error: plain vs batched+learned, % HBM roofline"
+WORKLOAD = "HDL-64E sequence: 10 frames of 64x2048 (1 key frame + 9 P-frames), tiles 4x4, thr 0.05 m, q 0.02 m"
+UNIT = "Mpoints/s"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="lcc", choices=["lcc", "reference"])
+    ap.add_argument("--tile", default="4x4")
+    ap.add_argument("--thr", type=float, default=0.05)
+    ap.add_argument("--cpu-seconds", type=float, default=12.0, help="bounded oracle sample length")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def make_workload(rank: int):
+    import synth
+    seq = synth.sequence_cfg2(sequence_id=rank)
+    return seq
+
+
+def oracle_sample(seq, th, tw, thr, seconds):
+    """Time the oracle (as it stands) on whole sequences until `seconds` pass."""
+    import oracle as O
+    s = O.sensor(seq.sensor)
+    p = O.params(th, tw, thr, 0.02)
+    pts_per_seq = sum(len(f) for f in seq.frames)
+    t0 = time.perf_counter()
+    nseq = 0
+    while True:
+        _, kft, _, _ = O.encode_keyframe(s, p, seq.frames[seq.key_index])
+        for f in range(len(seq.frames)):
+            if f != seq.key_index:
+                O.encode_pframe(s, p, kft, seq.poses[f], seq.frames[f])
+        nseq += 1
+        el = time.perf_counter() - t0
+        if el >= seconds:
+            break
+    return pts_per_seq * nseq / el / 1e6, nseq, el
+
+
+class Clocks:
+    def __init__(self, path):
+        self.path = path
+        self.proc = None
+
+    def __enter__(self):
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={q}", "--format=csv,noheader,nounits",
+                                          "-lms", "100", "-i", str(int(os.environ.get("LOCAL_RANK", "0")))],
+                                         stdout=self.fh, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.fh.close()
+
+    def summary(self):
+        try:
+            rows = [r.split(",") for r in open(self.path).read().strip().splitlines()]
+            rows = [[c.strip() for c in r] for r in rows if len(r) >= 9]
+        except Exception:
+            rows = []
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k].lower() == "active"})
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def run_reference(args, rank, world):
+    th, tw = (int(x) for x in args.tile.split("x"))
+    if world > 1 and rank != 0:
+        return
+    seq = make_workload(0)
+    pts = sum(len(f) for f in seq.frames)
+    per_step = max(args.cpu_seconds / max(args.steps + args.warmup, 1), 0.5)
+    for _ in range(args.warmup):
+        oracle_sample(seq, th, tw, args.thr, 0.0)
+    vals, secs = [], 0.0
+    for _ in range(args.steps):
+        v, nseq, el = oracle_sample(seq, th, tw, args.thr, per_step)
+        vals.append(v)
+        secs += el
+    value = float(np.mean(vals))
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * pts / (value * 1e6),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "points_per_step": pts, "tile": args.tile, "thr_m": args.thr},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": f"whole sequences repeated for >= {per_step:.1f} s per step"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+    th, tw = (int(x) for x in args.tile.split("x"))
+    seq = make_workload(rank)
+    import torch
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    from paper_2008_06972_gb300 import build as B
+    B.build()
+    from paper_2008_06972_gb300 import lcc
+
+    n_frames = len(seq.frames)
+    stream = torch.cuda.current_stream()
+    params = lcc.default_params(tile_h=th, tile_w=tw, fit_thr_m=args.thr, max_batch=max(16, n_frames))
+    ctx = lcc.Context(seq.sensor, params, stream=stream)
+    kf = lcc.Keyframe(ctx)
+    d_pts = [torch.from_numpy(f).cuda() for f in seq.frames]
+    n = [len(f) for f in seq.frames]
+    cap = ctx.max_encoded_bytes
+    d_out = [torch.zeros(cap, dtype=torch.uint8, device="cuda") for _ in range(n_frames)]
+    nbytes = torch.zeros(n_frames, dtype=torch.int64, device="cuda")
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    pts_step = sum(n)
+
+    def step():
+        ctx.lcc_encode_sequence(seq.key_index, seq.poses, d_pts, n, d_out, [cap] * n_frames, nbytes, kf)
+
+    for _ in range(max(args.warmup, 3)):
+        step()
+    assert ctx.lcc_sync() == lcc.OK
+    # ---- timed region: K steps, each bracketed by CUDA events on the context stream ----
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    clocks = Clocks(os.path.join(ROOT, "gpurun_out", f"clocks_rank{rank}.csv") if os.path.isdir(
+        os.path.join(ROOT, "gpurun_out")) else f"/tmp/lcc_clocks_{os.getpid()}.csv")
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with clocks:
+        t_wall = time.perf_counter()
+        for k in range(args.steps):
+            flush.zero_()
+            evs[k][0].record(stream)
+            step()
+            evs[k][1].record(stream)
+        torch.cuda.synchronize()
+        t_wall = time.perf_counter() - t_wall
+    if dist:
+        dist.barrier()
+    st = ctx.lcc_sync()
+    assert st == lcc.OK, lcc.status_string(st)
+    ms = np.array([a.elapsed_time(b) for a, b in evs])
+    ms_step = float(ms.mean())
+    if dist:
+        t = torch.tensor([ms_step], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_step = float(t.item())
+    value = pts_step * world / (ms_step * 1e-3) / 1e6
+
+    # ---- per-kernel times (same workload, profiling events around each launch) ----
+    ctx.lcc_set_profiling(True)
+    for k in range(args.steps):
+        flush.zero_()
+        step()
+    ktimes = ctx.lcc_kernel_times()
+    ctx.lcc_set_profiling(False)
+    launches_per_step = sum(v[0] for v in ktimes.values()) / args.steps
+
+    # ---- correctness of what was timed: decode every frame, max error vs the range image ----
+    out_sizes = nbytes.cpu().numpy()
+    H, W = seq.sensor.rows, seq.sensor.cols
+    max_err = 0.0
+    ref = torch.empty(H * W, dtype=torch.float32, device="cuda")
+    dec = torch.empty(H * W, dtype=torch.float32, device="cuda")
+    kfd = lcc.Keyframe(ctx)
+    ctx.lcc_keyframe_from_stream(d_out[seq.key_index], int(out_sizes[seq.key_index]), kfd)
+    for f in range(n_frames):
+        ctx.lcc_range_image(d_pts[f], n[f], ref, None)
+        isk = f == seq.key_index
+        ctx.lcc_decode(d_out[f], int(out_sizes[f]), None if isk else kfd, None if isk else seq.poses[f], dec,
+                       None, None)
+        assert ctx.lcc_sync() == lcc.OK
+        m = ref > 0
+        if bool(m.any()):
+            max_err = max(max_err, float((dec[m] - ref[m]).abs().max().item()))
+    total_bytes = int(out_sizes.sum())
+
+    # ---- end to end through the C ABI with HOST buffers (pinned) ----
+    h_pts = [torch.from_numpy(f).pin_memory() for f in seq.frames]
+    h_out = [torch.zeros(cap, dtype=torch.uint8).pin_memory() for _ in range(n_frames)]
+    for _ in range(2):
+        ctx.lcc_encode_sequence_host(seq.key_index, seq.poses, h_pts, h_out, [cap] * n_frames)
+    torch.cuda.synchronize()
+    e2e_steps = max(3, args.steps // 2)
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        nb = ctx.lcc_encode_sequence_host(seq.key_index, seq.poses, h_pts, h_out, [cap] * n_frames)
+    e2e_s = (time.perf_counter() - t0) / e2e_steps
+    if dist:
+        t = torch.tensor([e2e_s], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    e2e_value = pts_step * world / e2e_s / 1e6
+
+    # ---- roofline of the dominant kernel ----
+    hbm, src = peaks()
+    dom = max(ktimes.items(), key=lambda kv: kv[1][1])
+    dname, (dl, dms) = dom
+    per_launch_ms = dms / dl
+    # algorithmic bytes per launch (per-unit figures):
+    #   bin:   16 B per input point (float4 read) + 4 B per point atomic into the range image
+    #   fit:   4 B per pixel (range image read) + 64 B per tile record written
+    #   merge: 64 B per tile record read + 8 B per tile code written
+    #   scan:  8 B per tile code read + 32 B per tile offset written + stream bytes zeroed
+    #   pack:  4 B per pixel read + 4 B per pixel reset + stream bytes written
+    npx = H * W
+    nt = ctx.num_tiles
+    per_step_units = {
+        "bin": 20.0 * pts_step,
+        "fit": n_frames * (4.0 * npx + 64.0 * nt),
+        "merge": n_frames * (64.0 * nt + 8.0 * nt),
+        "scan": n_frames * (8.0 * nt + 32.0 * nt) + total_bytes,
+        "pack": n_frames * 8.0 * npx + total_bytes,
+    }
+    launches_of = {k: v[0] / args.steps for k, v in ktimes.items()}
+    alg_bytes = per_step_units.get(dname, 0.0) / max(launches_of.get(dname, 1.0), 1e-9)
+    achieved = alg_bytes / (per_launch_ms * 1e-3) / 1e9
+    path_bytes = 16.0 * pts_step + total_bytes
+    roof = {"bound": "hbm", "kernel": dname, "achieved": achieved, "peak": hbm, "unit": "GB/s",
+            "frac": achieved / hbm, "traffic": None, "peak_source": src,
+            "path": {"alg_bytes_per_step": path_bytes, "achieved": path_bytes / (ms_step * 1e-3) / 1e9,
+                     "frac": path_bytes / (ms_step * 1e-3) / 1e9 / hbm}}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        v, nseq, el = oracle_sample(seq, th, tw, args.thr, args.cpu_seconds)
+        cpu = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": f"{nseq} whole sequences (10 frames each) in {el:.1f} s on one host core"}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "frames": n_frames, "points_per_step": pts_step, "tile": args.tile,
+                       "thr_m": args.thr, "q_m": 0.02, "l2": "flushed between steps (256 MiB write, untimed)",
+                       "parallelism": f"replicas x{world}"},
+            "max_decode_error_m": max_err,
+            "compression_ratio": 12.0 * pts_step / total_bytes,
+            "bytes_per_step": total_bytes,
+            "kernel_ms_per_step": {k: v[1] / args.steps for k, v in ktimes.items()},
+            "roofline": roof,
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(16 * pts_step),
+                    "d2h_bytes_per_step": int(total_bytes + 8 * n_frames)},
+            "gpu_launches": int(round(launches_per_step * args.steps)),
+            "cpu_baseline": cpu,
+            "clocks": clocks.summary(),
+            "wall_s_timed": t_wall,
+        }
+        assert max_err <= 0.02, max_err
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

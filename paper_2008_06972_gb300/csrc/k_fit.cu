@@ -1,19 +1,18 @@
 // Per-tile plane fitting (Sec. III-C) and the relaxed-plane temporal test
 // (Sec. III-D).
 //
-// A tile is processed by a segment of LPT lanes (16 lanes for 4x4 tiles, two
-// tiles per warp; 32 lanes for larger tiles with 1-4 pixels per lane).  The
-// range image is read straight from L2 (each pixel once, plus the look-ahead
-// tiles), the point of pixel (i,j) is p = r * u_ij in fp32.
+// One thread owns one tile: it reads the tile's pixels from the range image
+// (L2/L1), forms the points p = r * u_ij in fp32, and runs the whole iterative
+// fit itself, so every FP64 instruction of the plane solve carries up to 32
+// tiles (GB300's FP64 pipe is the scarce resource of this kernel).
 //
 // Spatial fit, per round: anchor-shifted moments q = p - a (a = the tile's
 // first valid point) are accumulated in float-float (TwoSum / exact products),
-// reduced across the segment with xor shuffles (every lane ends with the same
-// bits), then one lane forms the covariance in FP64 and solves for the
-// smallest eigenvector (largest eigenpair by Newton + cross products, then an
-// exact 2x2 Jacobi rotation in its orthogonal complement; see solve_plane).
-// The fp32 plane is broadcast and every lane tests its
-// pixels with the along-ray residual; ballots give the inlier set.
+// then the covariance is formed in FP64 and the smallest eigenvector found
+// (largest eigenpair by Newton + cross products, then an exact 2x2 Jacobi
+// rotation in its orthogonal complement; see solve_plane).  The fp32 plane is
+// tested on every valid pixel with the along-ray residual to give the next
+// inlier set.
 //
 // Temporal test (P frames, before the spatial fit): the anchor is moved to
 // key-frame coordinates (Eq. 6), binned (Eq. 1-2) into the key frame's grid,
@@ -27,22 +26,7 @@
 
 namespace lcc {
 
-constexpr int kFitWarps = 8;
-
-template <int TH_, int TW_>
-struct Shape {
-    static constexpr int PX = TH_ * TW_;
-    static constexpr int LPT = PX < 32 ? PX : 32;  // lanes per tile
-    static constexpr int PPL = PX / LPT;           // pixels per lane
-    static constexpr int TPW = 32 / LPT;           // tiles per warp
-};
-
-template <int LPT>
-__device__ __forceinline__ ff seg_sum(ff v) {
-#pragma unroll
-    for (int off = LPT / 2; off >= 1; off >>= 1) v = ff_add(v, shfl_xor_ff(v, off));
-    return v;
-}
+constexpr int kFitThreads = 128;
 
 // FP64 plane of the moments: returns true if the scatter matrix is degenerate.
 //
@@ -190,280 +174,220 @@ __device__ __noinline__ bool solve_plane(const double m1[3], const double m2[6],
 }
 
 template <int TH_, int TW_>
-__global__ void __launch_bounds__(kFitWarps * 32) k_fit(Geometry g, Scratch s, Batch b, Poses ps) {
-    using S = Shape<TH_, TW_>;
-    constexpr int LPT = S::LPT, PPL = S::PPL, TPW = S::TPW;
-    const unsigned FULL = 0xffffffffu;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int seg = lane / LPT, sl = lane % LPT;
-    const int leader = seg * LPT;
+__global__ void __launch_bounds__(kFitThreads) k_fit(Geometry g, Scratch s, Batch b, Poses ps) {
+    constexpr int PX = TH_ * TW_;
+    constexpr int MW = (PX + 63) / 64;   // mask words
     const int f = blockIdx.y;
-    const int t = (blockIdx.x * kFitWarps + warp) * TPW + seg;
-    const bool tile_ok = t < g.NT;
-    const int tr = tile_ok ? t / g.TC : 0, tc = tile_ok ? t % g.TC : 0;
+    const int t = blockIdx.x * kFitThreads + threadIdx.x;
+    if (t >= g.NT) return;
+    const int tr = t / g.TC, tc = t % g.TC;
+    const int i0 = tr * TH_, j0 = tc * TW_;
     const uint32_t *rimg = s.rimg + (size_t)b.slot[f] * g.H * g.W;
     TileRec *recs = s.tiles + (size_t)b.slot[f] * g.NT;
-    const uint32_t segmask = (LPT == 32) ? FULL : (((1u << LPT) - 1u) << (seg * LPT));
     const float thr = g.thr;
 
-    // ---- load the tile's pixels ----
-    float r[PPL], px[PPL], py[PPL], pz[PPL], ux[PPL], uy[PPL], uz[PPL];
-    bool v[PPL];
+    // range of pixel k of this tile (0 if empty or outside the image)
+    auto rng = [&](int k) -> float {
+        const int i = i0 + k / TW_, j = j0 + k % TW_;
+        if (i >= g.H || j >= g.W) return 0.0f;
+        const uint32_t bits = __ldg(rimg + (size_t)i * g.W + j);
+        return bits_valid(bits) ? __uint_as_float(bits) : 0.0f;
+    };
+    auto ubeam = [&](int k, float &ux, float &uy, float &uz) {
+        beam(g, i0 + k / TW_, j0 + k % TW_, ux, uy, uz);
+    };
+
+    // valid mask and anchor (first valid pixel in raster order)
+    unsigned long long V[MW];
+    int nv = 0, first = -1;
 #pragma unroll
-    for (int m = 0; m < PPL; m++) {
-        const int k = sl + LPT * m;
-        const int i = tr * TH_ + k / TW_, j = tc * TW_ + k % TW_;
-        const bool in = tile_ok && i < g.H && j < g.W;
-        const uint32_t bits = in ? __ldg(rimg + (size_t)i * g.W + j) : kEmptyBits;
-        v[m] = bits_valid(bits);
-        r[m] = v[m] ? __uint_as_float(bits) : 0.0f;
-        if (in) beam(g, i, j, ux[m], uy[m], uz[m]);
-        else ux[m] = uy[m] = uz[m] = 0.0f;
-        px[m] = __fmul_rn(r[m], ux[m]);
-        py[m] = __fmul_rn(r[m], uy[m]);
-        pz[m] = __fmul_rn(r[m], uz[m]);
+    for (int w = 0; w < MW; w++) V[w] = 0ull;
+#pragma unroll 4
+    for (int k = 0; k < PX; k++) {
+        if (rng(k) > 0.0f) {
+            V[k >> 6] |= 1ull << (k & 63);
+            nv++;
+            if (first < 0) first = k;
+        }
     }
-    uint32_t vb[PPL];
-    int nv = 0;
-#pragma unroll
-    for (int m = 0; m < PPL; m++) {
-        vb[m] = __ballot_sync(FULL, v[m]) & segmask;
-        nv += __popc(vb[m]);
+    float ax = 0.f, ay = 0.f, az = 0.f;
+    if (first >= 0) {
+        float ux, uy, uz;
+        ubeam(first, ux, uy, uz);
+        const float r0 = rng(first);
+        ax = __fmul_rn(r0, ux);
+        ay = __fmul_rn(r0, uy);
+        az = __fmul_rn(r0, uz);
     }
-    // anchor = first valid pixel in raster order (raster index k = sl + LPT*m)
-    int am = -1, al = leader;
-#pragma unroll
-    for (int m = 0; m < PPL; m++)
-        if (am < 0 && vb[m]) { am = m; al = __ffs(vb[m]) - 1; }
-    float sx = px[0], sy = py[0], sz = pz[0];
-#pragma unroll
-    for (int m = 1; m < PPL; m++)
-        if (m == am) { sx = px[m]; sy = py[m]; sz = pz[m]; }
-    const float ax = __shfl_sync(FULL, sx, al), ay = __shfl_sync(FULL, sy, al), az = __shfl_sync(FULL, sz, al);
 
     uint8_t status = nv == 0 ? S_EMPTY : S_FAIL;
     uint8_t flags = 0, t_status = 0, t_rounds = 0, t_inl = 0, rounds = 0, n_inl = 0;
     uint32_t kref = 0xFFFFFFFFu;
     float4 tpl = make_float4(0.f, 0.f, 0.f, 0.f), pl = tpl;
-    int nI = 0;
-    uint32_t Sb[PPL];
+    unsigned long long Sm[MW], Im[MW];
+
+    // inlier set of a plane over the valid pixels; returns its size
+    auto inliers = [&](const float4 &q4, unsigned long long (&I)[MW], bool &border) -> int {
+        int cnt = 0;
+#pragma unroll
+        for (int w = 0; w < MW; w++) I[w] = 0ull;
+#pragma unroll 4
+        for (int k = 0; k < PX; k++) {
+            if (!((V[k >> 6] >> (k & 63)) & 1ull)) continue;
+            float ux, uy, uz, e;
+            ubeam(k, ux, uy, uz);
+            if (residual(q4, ux, uy, uz, rng(k), thr, e)) {
+                I[k >> 6] |= 1ull << (k & 63);
+                cnt++;
+            }
+            if (isfinite(e) && fabsf(fabsf(e) - thr) <= 1e-6f) border = true;
+        }
+        return cnt;
+    };
 
     // ---- temporal test (P frames) ----
-    if (b.kind == 1) {
-        int kt = -1;
-        float nxp = 0.f, nyp = 0.f, nzp = 0.f;
-        if (sl == 0 && tile_ok && nv > 0) {
-            float aK[3];
-            transform_point(ps.m[f], ax, ay, az, aK);
-            float rK;
-            int pixK;
-            if (bin_point(g, aK[0], aK[1], aK[2], rK, pixK) == 0) {
-                const int kti = (pixK / g.W / g.th) * g.TC + (pixK % g.W) / g.tw;
-                const float4 kp = __ldg(b.kf + kti);
-                if (!(kp.x == 0.f && kp.y == 0.f && kp.z == 0.f)) {
-                    float o[3];
-                    rotate_normal(ps.m[f], kp.x, kp.y, kp.z, o);
-                    nxp = o[0]; nyp = o[1]; nzp = o[2];
-                    kt = kti;
+    if (b.kind == 1 && nv > 0) {
+        float aK[3];
+        transform_point(ps.m[f], ax, ay, az, aK);
+        float rK;
+        int pixK;
+        if (bin_point(g, aK[0], aK[1], aK[2], rK, pixK) == 0) {
+            const int kti = (pixK / g.W / g.th) * g.TC + (pixK % g.W) / g.tw;
+            const float4 kp = __ldg(b.kf + kti);
+            if (!(kp.x == 0.f && kp.y == 0.f && kp.z == 0.f)) {
+                float o[3];
+                rotate_normal(ps.m[f], kp.x, kp.y, kp.z, o);
+                kref = (uint32_t)kti;
+#pragma unroll
+                for (int w = 0; w < MW; w++) Sm[w] = V[w];
+                int nS = nv, nI = 0;
+                float c = 0.f;
+                bool border = false;
+                for (;;) {
+                    ff acc = {0.f, 0.f};
+#pragma unroll 4
+                    for (int k = 0; k < PX; k++) {
+                        if (!((Sm[k >> 6] >> (k & 63)) & 1ull)) continue;
+                        float ux, uy, uz;
+                        ubeam(k, ux, uy, uz);
+                        const float r = rng(k);
+                        const ff dp = ff_add(ff_add(two_prod(o[0], __fmul_rn(r, ux)), two_prod(o[1], __fmul_rn(r, uy))),
+                                             two_prod(o[2], __fmul_rn(r, uz)));
+                        acc = ff_add(acc, dp);
+                    }
+                    c = (float)(ff_to_d(acc) / (double)nS);
+                    t_rounds++;
+                    nI = inliers(make_float4(o[0], o[1], o[2], c), Im, border);
+                    bool same = nI == nS;
+#pragma unroll
+                    for (int w = 0; w < MW; w++) same = same && Im[w] == Sm[w];
+                    if (same || t_rounds == g.R + 1 || nI < 3) break;
+#pragma unroll
+                    for (int w = 0; w < MW; w++) Sm[w] = Im[w];
+                    nS = nI;
                 }
-            }
-        }
-        kt = __shfl_sync(FULL, kt, leader);
-        nxp = __shfl_sync(FULL, nxp, leader);
-        nyp = __shfl_sync(FULL, nyp, leader);
-        nzp = __shfl_sync(FULL, nzp, leader);
-        bool act = tile_ok && kt >= 0;
-        int nS = nv;
-#pragma unroll
-        for (int m = 0; m < PPL; m++) Sb[m] = vb[m];
-        float c = 0.f;
-        while (__any_sync(FULL, act)) {
-            ff acc = {0.f, 0.f};
-#pragma unroll
-            for (int m = 0; m < PPL; m++) {
-                const bool inS = (Sb[m] >> lane) & 1u;
-                if (act && inS) {
-                    const ff dp = ff_add(ff_add(two_prod(nxp, px[m]), two_prod(nyp, py[m])), two_prod(nzp, pz[m]));
-                    acc = ff_add(acc, dp);
+                if (border) flags |= 1;
+                flags |= 4;
+                tpl = make_float4(o[0], o[1], o[2], c);
+                t_inl = (uint8_t)nI;
+                t_status = (nv >= 3 && nI >= need_inliers(g.fmin, nv)) ? 2 : 1;
+                if (t_status == 2) {
+                    status = S_TEMPORAL;
+                    pl = tpl;
+                    n_inl = (uint8_t)nI;
                 }
-            }
-            acc = seg_sum<LPT>(acc);
-            float cl = 0.f;
-            if (act && sl == 0) cl = (float)(ff_to_d(acc) / (double)nS);
-            cl = __shfl_sync(FULL, cl, leader);
-            if (act) {
-                c = cl;
-                t_rounds++;
-            }
-            const float4 tp = make_float4(nxp, nyp, nzp, c);
-            uint32_t Ib[PPL];
-            int ni = 0;
-            bool same = true, border = false;
-#pragma unroll
-            for (int m = 0; m < PPL; m++) {
-                float e = 0.f;
-                const bool in = act && v[m] && residual(tp, ux[m], uy[m], uz[m], r[m], thr, e);
-                if (act && v[m] && isfinite(e) && fabsf(fabsf(e) - thr) <= 1e-6f) border = true;
-                Ib[m] = __ballot_sync(FULL, in) & segmask;
-                ni += __popc(Ib[m]);
-                same = same && (Ib[m] == Sb[m]);
-            }
-            if (__ballot_sync(FULL, border) & segmask) flags |= act ? 1 : 0;
-            if (act) {
-                nI = ni;
-                if (same || t_rounds == g.R + 1 || ni < 3) {
-                    act = false;
-                } else {
-#pragma unroll
-                    for (int m = 0; m < PPL; m++) Sb[m] = Ib[m];
-                    nS = ni;
-                }
-            }
-        }
-        if (kt >= 0) {
-            kref = (uint32_t)kt;
-            tpl = make_float4(nxp, nyp, nzp, c);
-            t_inl = (uint8_t)nI;
-            flags |= 4;
-            t_status = (nv >= 3 && nI >= need_inliers(g.fmin, nv)) ? 2 : 1;
-            if (t_status == 2) {
-                status = S_TEMPORAL;
-                pl = tpl;
-                n_inl = (uint8_t)nI;
             }
         }
     }
 
     // ---- spatial fit with drop-and-refit rounds ----
-    {
-        bool act = tile_ok && status != S_TEMPORAL && nv >= 3;
-        bool degen = false;
-        int nS = nv;
+    if (status != S_TEMPORAL && nv >= 3) {
 #pragma unroll
-        for (int m = 0; m < PPL; m++) Sb[m] = vb[m];
-        nI = 0;
+        for (int w = 0; w < MW; w++) Sm[w] = V[w];
+        int nS = nv, nI = 0;
+        bool degen = false, border = false;
         float4 cur = make_float4(0.f, 0.f, 0.f, 0.f);
-        while (__any_sync(FULL, act)) {
+        for (;;) {
             ff s1x = {0.f, 0.f}, s1y = s1x, s1z = s1x, sxx = s1x, sxy = s1x, sxz = s1x, syy = s1x, syz = s1x, szz = s1x;
-#pragma unroll
-            for (int m = 0; m < PPL; m++) {
-                const bool inS = (Sb[m] >> lane) & 1u;
-                if (act && inS) {
-                    const ff qx = two_sum(px[m], -ax), qy = two_sum(py[m], -ay), qz = two_sum(pz[m], -az);
-                    s1x = ff_add(s1x, qx);
-                    s1y = ff_add(s1y, qy);
-                    s1z = ff_add(s1z, qz);
-                    sxx = ff_add(sxx, ff_mul(qx, qx));
-                    sxy = ff_add(sxy, ff_mul(qx, qy));
-                    sxz = ff_add(sxz, ff_mul(qx, qz));
-                    syy = ff_add(syy, ff_mul(qy, qy));
-                    syz = ff_add(syz, ff_mul(qy, qz));
-                    szz = ff_add(szz, ff_mul(qz, qz));
-                }
+#pragma unroll 4
+            for (int k = 0; k < PX; k++) {
+                if (!((Sm[k >> 6] >> (k & 63)) & 1ull)) continue;
+                float ux, uy, uz;
+                ubeam(k, ux, uy, uz);
+                const float r = rng(k);
+                const ff qx = two_sum(__fmul_rn(r, ux), -ax), qy = two_sum(__fmul_rn(r, uy), -ay),
+                         qz = two_sum(__fmul_rn(r, uz), -az);
+                s1x = ff_add(s1x, qx);
+                s1y = ff_add(s1y, qy);
+                s1z = ff_add(s1z, qz);
+                sxx = ff_add(sxx, ff_mul(qx, qx));
+                sxy = ff_add(sxy, ff_mul(qx, qy));
+                sxz = ff_add(sxz, ff_mul(qx, qz));
+                syy = ff_add(syy, ff_mul(qy, qy));
+                syz = ff_add(syz, ff_mul(qy, qz));
+                szz = ff_add(szz, ff_mul(qz, qz));
             }
-            s1x = seg_sum<LPT>(s1x); s1y = seg_sum<LPT>(s1y); s1z = seg_sum<LPT>(s1z);
-            sxx = seg_sum<LPT>(sxx); sxy = seg_sum<LPT>(sxy); sxz = seg_sum<LPT>(sxz);
-            syy = seg_sum<LPT>(syy); syz = seg_sum<LPT>(syz); szz = seg_sum<LPT>(szz);
-            float4 np = make_float4(0.f, 0.f, 0.f, 0.f);
-            int dg = 0;
+            const double m1[3] = {ff_to_d(s1x), ff_to_d(s1y), ff_to_d(s1z)};
+            const double m2[6] = {ff_to_d(sxx), ff_to_d(sxy), ff_to_d(sxz), ff_to_d(syy), ff_to_d(syz), ff_to_d(szz)};
             float ratio = 0.f;
-            if (act && sl == 0) {
-                const double m1[3] = {ff_to_d(s1x), ff_to_d(s1y), ff_to_d(s1z)};
-                const double m2[6] = {ff_to_d(sxx), ff_to_d(sxy), ff_to_d(sxz), ff_to_d(syy), ff_to_d(syz), ff_to_d(szz)};
-                dg = solve_plane(m1, m2, nS, ax, ay, az, np, ratio) ? 1 : 0;
-                if (ratio >= 0.999e-12f && ratio <= 1.001e-12f) dg |= 2;
+            degen = solve_plane(m1, m2, nS, ax, ay, az, cur, ratio);
+            if (ratio >= 0.999e-12f && ratio <= 1.001e-12f) flags |= 1;
+            rounds++;
+            if (degen) {
+                nI = 0;
+                break;
             }
-            np.x = __shfl_sync(FULL, np.x, leader);
-            np.y = __shfl_sync(FULL, np.y, leader);
-            np.z = __shfl_sync(FULL, np.z, leader);
-            np.w = __shfl_sync(FULL, np.w, leader);
-            dg = __shfl_sync(FULL, dg, leader);
-            if (act) {
-                rounds++;
-                cur = np;
-                if (dg & 2) flags |= 1;
-                if (dg & 1) degen = true;
-            }
-            uint32_t Ib[PPL];
-            int ni = 0;
-            bool same = true, border = false;
-            const bool test = act && !degen;
+            nI = inliers(cur, Im, border);
+            bool same = nI == nS;
 #pragma unroll
-            for (int m = 0; m < PPL; m++) {
-                float e = 0.f;
-                const bool in = test && v[m] && residual(cur, ux[m], uy[m], uz[m], r[m], thr, e);
-                if (test && v[m] && isfinite(e) && fabsf(fabsf(e) - thr) <= 1e-6f) border = true;
-                Ib[m] = __ballot_sync(FULL, in) & segmask;
-                ni += __popc(Ib[m]);
-                same = same && (Ib[m] == Sb[m]);
-            }
-            if ((__ballot_sync(FULL, border) & segmask) && test) flags |= 1;
-            if (act) {
-                nI = degen ? 0 : ni;
-                if (degen || same || rounds == g.R + 1 || ni < 3) {
-                    act = false;
-                } else {
+            for (int w = 0; w < MW; w++) same = same && Im[w] == Sm[w];
+            if (same || rounds == g.R + 1 || nI < 3) break;
 #pragma unroll
-                    for (int m = 0; m < PPL; m++) Sb[m] = Ib[m];
-                    nS = ni;
-                }
-            }
+            for (int w = 0; w < MW; w++) Sm[w] = Im[w];
+            nS = nI;
         }
-        if (status != S_TEMPORAL && nv >= 3) {
-            pl = cur;
-            n_inl = (uint8_t)nI;
-            if (degen) flags |= 2;
-            if (!degen && nI >= need_inliers(g.fmin, nv)) status = S_FIT;
-        }
+        if (border) flags |= 1;
+        pl = cur;
+        n_inl = (uint8_t)nI;
+        if (degen) flags |= 2;
+        if (!degen && nI >= need_inliers(g.fmin, nv)) status = S_FIT;
     }
 
     // ---- look-ahead tests of the next tiles of the row against this plane ----
     uint32_t amask = 0, acnt[4] = {0u, 0u, 0u, 0u};
-    {
-        bool la = tile_ok && status == S_FIT && g.merge;
-        for (int k = 1; k <= g.lookahead; k++) {
-            if (!__any_sync(FULL, la)) break;
-            const bool inrow = la && tc + k < g.TC;
+    if (status == S_FIT && g.merge) {
+        for (int k = 1; k <= g.lookahead && tc + k < g.TC; k++) {
+            const int jn = j0 + k * TW_;
             int nvn = 0, nin = 0;
-#pragma unroll
-            for (int m = 0; m < PPL; m++) {
-                const int kk = sl + LPT * m;
-                const int i = tr * TH_ + kk / TW_, j = (tc + k) * TW_ + kk % TW_;
-                const bool in = inrow && i < g.H && j < g.W;
-                const uint32_t bits = in ? __ldg(rimg + (size_t)i * g.W + j) : kEmptyBits;
-                const bool vv = bits_valid(bits);
-                float e = 0.f, qx = 0.f, qy = 0.f, qz = 0.f;
-                if (vv) beam(g, i, j, qx, qy, qz);
-                const bool ok = vv && residual(pl, qx, qy, qz, __uint_as_float(bits), thr, e);
-                nvn += __popc(__ballot_sync(FULL, vv) & segmask);
-                nin += __popc(__ballot_sync(FULL, ok) & segmask);
+#pragma unroll 4
+            for (int q = 0; q < PX; q++) {
+                const int i = i0 + q / TW_, j = jn + q % TW_;
+                if (i >= g.H || j >= g.W) continue;
+                const uint32_t bits = __ldg(rimg + (size_t)i * g.W + j);
+                if (!bits_valid(bits)) continue;
+                nvn++;
+                float ux, uy, uz, e;
+                beam(g, i, j, ux, uy, uz);
+                nin += residual(pl, ux, uy, uz, __uint_as_float(bits), thr, e) ? 1 : 0;
             }
-            if (inrow) {
-                if (nvn >= 3 && nin >= need_inliers(g.fmin, nvn)) amask |= 1u << (k - 1);
-                acnt[(k - 1) >> 2] |= (uint32_t)nin << (8 * ((k - 1) & 3));
-            } else {
-                la = false;
-            }
+            if (nvn >= 3 && nin >= need_inliers(g.fmin, nvn)) amask |= 1u << (k - 1);
+            acnt[(k - 1) >> 2] |= (uint32_t)nin << (8 * ((k - 1) & 3));
         }
     }
 
-    if (tile_ok && sl == 0) {
-        uint4 *dst = reinterpret_cast<uint4 *>(recs + t);
-        dst[0] = make_uint4(__float_as_uint(pl.x), __float_as_uint(pl.y), __float_as_uint(pl.z), __float_as_uint(pl.w));
-        dst[1] = make_uint4(__float_as_uint(tpl.x), __float_as_uint(tpl.y), __float_as_uint(tpl.z), __float_as_uint(tpl.w));
-        const uint32_t w0 = (uint32_t)status | ((uint32_t)rounds << 8) | ((uint32_t)flags << 16) | ((uint32_t)nv << 24);
-        const uint32_t w1 = (uint32_t)n_inl | ((uint32_t)t_rounds << 8) | ((uint32_t)t_inl << 16) | ((uint32_t)t_status << 24);
-        dst[2] = make_uint4(kref, amask, w0, w1);
-        dst[3] = make_uint4(acnt[0], acnt[1], acnt[2], acnt[3]);
-    }
+    uint4 *dst = reinterpret_cast<uint4 *>(recs + t);
+    dst[0] = make_uint4(__float_as_uint(pl.x), __float_as_uint(pl.y), __float_as_uint(pl.z), __float_as_uint(pl.w));
+    dst[1] = make_uint4(__float_as_uint(tpl.x), __float_as_uint(tpl.y), __float_as_uint(tpl.z), __float_as_uint(tpl.w));
+    const uint32_t w0 = (uint32_t)status | ((uint32_t)rounds << 8) | ((uint32_t)flags << 16) | ((uint32_t)nv << 24);
+    const uint32_t w1 = (uint32_t)n_inl | ((uint32_t)t_rounds << 8) | ((uint32_t)t_inl << 16) | ((uint32_t)t_status << 24);
+    dst[2] = make_uint4(kref, amask, w0, w1);
+    dst[3] = make_uint4(acnt[0], acnt[1], acnt[2], acnt[3]);
 }
 
 template <int TH_, int TW_>
 static cudaError_t launch_fit_t(const Geometry &g, const Scratch &s, const Batch &b, const Poses &p, cudaStream_t st) {
-    using S = Shape<TH_, TW_>;
-    const int tiles_per_block = kFitWarps * S::TPW;
-    dim3 grid((g.NT + tiles_per_block - 1) / tiles_per_block, b.nframes);
-    k_fit<TH_, TW_><<<grid, kFitWarps * 32, 0, st>>>(g, s, b, p);
+    dim3 grid((g.NT + kFitThreads - 1) / kFitThreads, b.nframes);
+    k_fit<TH_, TW_><<<grid, kFitThreads, 0, st>>>(g, s, b, p);
     return cudaGetLastError();
 }
 

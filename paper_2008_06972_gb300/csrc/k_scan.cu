@@ -22,7 +22,7 @@ __global__ void __launch_bounds__(kScanThreads) k_scan(Geometry g, Scratch s, Ba
 
     __shared__ uint32_t s_warp[32][kScanVals];
     __shared__ uint32_t s_carry[kScanVals];
-    __shared__ unsigned long long s_hist[16];
+    __shared__ unsigned int s_hist[16];
     __shared__ uint32_t s_ok, s_total;
     if (tid < kScanVals) s_carry[tid] = 0;
     if (tid < 16) s_hist[tid] = 0;
@@ -42,11 +42,28 @@ __global__ void __launch_bounds__(kScanThreads) k_scan(Geometry g, Scratch s, Ba
             v[3] = mode == T_RUN_START;
             v[4] = mode == T_TEMPORAL;
             v[5] = mode >= T_RUN_START ? cand : raw;   // valid pixels
-            const uint32_t w0 = *reinterpret_cast<const uint32_t *>(reinterpret_cast<const uint8_t *>(recs + t) + 40);
-            const uint32_t rounds = (w0 >> 8) & 0xff, flags = (w0 >> 16) & 0xff;
-            atomicAdd(&s_hist[mode], 1ull);                 // [0..4] tiles by mode
-            atomicAdd(&s_hist[5 + min(rounds, 7u)], 1ull);  // [5..12] fit rounds
-            if (flags & 1) atomicAdd(&s_hist[13], 1ull);
+        }
+        // histograms: one ballot per bin and warp, then one shared atomic per warp
+        {
+            uint32_t rounds = 0, flags = 0;
+            if (t < g.NT) {
+                const uint32_t w0 = *reinterpret_cast<const uint32_t *>(reinterpret_cast<const uint8_t *>(recs + t) + 40);
+                rounds = min((w0 >> 8) & 0xffu, 7u);
+                flags = (w0 >> 16) & 0xffu;
+            }
+            const bool in = t < g.NT;
+#pragma unroll
+            for (int q = 0; q < 5; q++) {
+                const uint32_t c = __popc(__ballot_sync(0xffffffffu, in && mode == q));
+                if (lane == 0 && c) atomicAdd(&s_hist[q], c);           // [0..4] tiles by mode
+            }
+#pragma unroll
+            for (int q = 0; q < 8; q++) {
+                const uint32_t c = __popc(__ballot_sync(0xffffffffu, in && rounds == (uint32_t)q));
+                if (lane == 0 && c) atomicAdd(&s_hist[5 + q], c);       // [5..12] fit rounds
+            }
+            const uint32_t c = __popc(__ballot_sync(0xffffffffu, in && (flags & 1u)));
+            if (lane == 0 && c) atomicAdd(&s_hist[13], c);              // borderline tiles
         }
         // warp inclusive scans
         uint32_t inc[kScanVals];
