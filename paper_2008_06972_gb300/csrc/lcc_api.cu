@@ -317,7 +317,8 @@ lcc_status lcc_create(lcc_ctx **out, const lcc_sensor *sensor, const lcc_params 
     g.elev_max_deg = (float)s.elev_max_deg;
     g.d_el_deg = (float)((s.elev_max_deg - s.elev_min_deg) / s.rows);
     g.d_az = (float)(2.0 * M_PI / s.cols);
-    if (g.w_res > 16 || g.w_raw > 24) {
+    // the run walker keeps one tile row (48 B per tile) in shared memory
+    if (g.w_res > 16 || g.w_raw > 24 || (size_t)g.TC * 48 > 200 * 1024) {
         delete c;
         return LCC_ERR_UNSUPPORTED;
     }
