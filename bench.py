@@ -40,8 +40,10 @@ def parse():
     ap.add_argument("--impl", default="lcc", choices=["lcc", "reference"])
     ap.add_argument("--tile", default="4x4")
     ap.add_argument("--thr", type=float, default=0.05)
-    ap.add_argument("--lookahead", type=int, default=8)
+    ap.add_argument("--lookahead", type=int, default=16)
     ap.add_argument("--refits", type=int, default=3)
+    ap.add_argument("--solver", default="ff", choices=["ff", "fp64"])
+    ap.add_argument("--schedule", type=int, default=0)
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="bounded oracle sample length")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     return ap.parse_args()
@@ -173,7 +175,8 @@ def main():
     n_frames = len(seq.frames)
     stream = torch.cuda.current_stream()
     params = lcc.default_params(tile_h=th, tile_w=tw, fit_thr_m=args.thr, max_batch=max(16, n_frames),
-                                lookahead=args.lookahead, max_refits=args.refits)
+                                lookahead=args.lookahead, max_refits=args.refits,
+                                solver=0 if args.solver == "ff" else 1, fit_schedule=args.schedule)
     ctx = lcc.Context(seq.sensor, params, stream=stream)
     kf = lcc.Keyframe(ctx)
     d_pts = [torch.from_numpy(f).cuda() for f in seq.frames]
@@ -304,7 +307,9 @@ def main():
             "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": WORKLOAD, "frames": n_frames, "points_per_step": pts_step, "tile": args.tile,
-                       "thr_m": args.thr, "q_m": 0.02, "lookahead": args.lookahead, "max_refits": args.refits, "l2": "flushed between steps (256 MiB write, untimed)",
+                       "thr_m": args.thr, "q_m": 0.02, "lookahead": args.lookahead, "max_refits": args.refits,
+                       "plane_solver": "float-float" if args.solver == "ff" else "fp64",
+                       "fit_schedule": args.schedule, "l2": "flushed between steps (256 MiB write, untimed)",
                        "parallelism": f"replicas x{world}"},
             "max_decode_error_m": max_err,
             "compression_ratio": 12.0 * pts_step / total_bytes,

@@ -58,7 +58,10 @@ typedef struct {
     float min_inlier_frac;    /* share of a tile's points a plane must keep (1.0 = all, the paper's rule) */
     int32_t merge_runs;       /* 1: grow runs of tiles horizontally with the run's plane (Sec. III-C) */
     int32_t max_batch;        /* frames per batched launch the context reserves scratch for (1..64) */
-    int32_t lookahead;        /* tiles ahead the fit kernel pre-tests for run growth (0..16) */
+    int32_t lookahead;        /* run pre-test span: tiles to the left each tile is tested against (0..16) */
+    int32_t solver;           /* 3x3 plane solve: 0 float-float on the FP32 pipes (default), 1 FP64 */
+    int32_t fit_schedule;     /* 0: a thread runs all refit rounds of its tile; 1: tiles needing another
+                                 round are queued and re-run in dense warps, one kernel per round */
 } lcc_params;
 
 /* Per-frame statistics of the last encode (Fig. 11's categories and more). */
@@ -80,7 +83,7 @@ typedef struct {
     float plane[4];           /* own spatial plane n.p = d, or (n', c') for a temporal tile */
     float tplane[4];          /* temporal test plane (n', c') if a K tile was found */
     uint32_t kref;            /* K tile the anchor maps to, 0xFFFFFFFF if none */
-    uint32_t ahead_mask;      /* run pre-test bits: bit k-1 = tile +k passes this tile's plane */
+    uint32_t ahead_mask;      /* run pre-test bits: bit j = this tile passes the plane of tile t-1-j */
     uint8_t status;           /* 0 empty, 1 fit failed, 2 fit ok, 3 temporal */
     uint8_t rounds;           /* spatial plane fits performed */
     uint8_t flags;            /* bit0 borderline, bit1 degenerate scatter, bit2 temporal tested */
@@ -89,7 +92,7 @@ typedef struct {
     uint8_t t_rounds;         /* temporal offset fits */
     uint8_t t_inlier;         /* inliers of the temporal plane */
     uint8_t t_status;         /* 0 no K plane, 1 failed, 2 passed */
-    uint8_t ahead_cnt[16];    /* inlier counts of the pre-tested tiles */
+    uint8_t ahead_cnt[16];    /* inlier counts of those pre-tests */
 } lcc_tile_info;
 
 typedef struct lcc_ctx lcc_ctx;
@@ -99,7 +102,7 @@ typedef struct lcc_keyframe lcc_keyframe;
 const char *lcc_status_string(lcc_status s);
 
 /* Default parameters: 4x4 tiles, thr 0.05 m, q 0.02 m, 3 refits, f_min 0.75,
- * runs on, max_batch 16, lookahead 8. */
+ * runs on, max_batch 16, lookahead 16, float-float solver. */
 void lcc_default_params(lcc_params *p);
 
 /* Create a context on the current device bound to cuda_stream (a
@@ -188,8 +191,8 @@ lcc_status lcc_tile_records(lcc_ctx *ctx, int32_t frame, lcc_tile_info *h_out, i
 /* Kernel timing: when enabled, every kernel launch is bracketed by CUDA events
  * on the context stream.  lcc_kernel_times returns, per kernel name, the
  * number of launches and summed milliseconds since the last reset
- * (synchronous).  Names: "bin", "fit", "merge", "scan", "pack", "decode_prep",
- * "decode_px".  Returns the number of entries written. */
+ * (synchronous).  Names: "bin", "fit", "refit", "merge", "scan", "pack",
+ * "decode_prep", "decode_px", "range_export".  Returns the number of entries written. */
 lcc_status lcc_set_profiling(lcc_ctx *ctx, int32_t enable);
 int32_t lcc_kernel_times(lcc_ctx *ctx, char names[][16], int64_t *launches, double *ms, int32_t cap);
 

@@ -8,25 +8,67 @@
 //
 // Spatial fit, per round: anchor-shifted moments q = p - a (a = the tile's
 // first valid point) are accumulated in float-float (TwoSum / exact products),
-// then the covariance is formed in FP64 and the smallest eigenvector found
-// (largest eigenpair by Newton + cross products, then an exact 2x2 Jacobi
-// rotation in its orthogonal complement; see solve_plane).  The fp32 plane is
-// tested on every valid pixel with the along-ray residual to give the next
-// inlier set.
+// then the covariance is formed and the smallest eigenvector found (largest
+// eigenpair by Newton + cross products, then an exact 2x2 Jacobi rotation in
+// its orthogonal complement).  The solve runs in float-float on the FP32 pipes
+// (ffmath.cuh, ~48-bit); params.solver = 1 selects the same method in FP64
+// (solve_plane below), which GB300's FP64 latency makes ~10x slower per tile.
+// The fp32 plane is tested on every valid pixel with the along-ray residual to
+// give the next inlier set.
 //
 // Temporal test (P frames, before the spatial fit): the anchor is moved to
 // key-frame coordinates (Eq. 6), binned (Eq. 1-2) into the key frame's grid,
 // and the K tile's coding plane normal is rotated into P coordinates; the
 // offset c' = mean(n'.p) is refit over the current set with the same rounds.
 //
-// Look-ahead: a tile whose own fit succeeded also tests the next `lookahead`
-// tiles of its row against its plane, so the run-growth walker rarely has to
-// touch pixels.
+// Run pre-test (k_lookbehind): each tile tests itself against the planes of
+// the fitted tiles to its left, so the run-growth walker rarely has to touch
+// pixels.
+//
+// Work is split so the FP64 solves run in dense warps: a first pass over all
+// tiles does the temporal test (P frames) or the first spatial round (key
+// frames); tiles that need a (further) spatial round are queued and each
+// round kernel processes only the queue.
+#include <algorithm>
+
+#include "ffmath.cuh"
 #include "lcc_internal.cuh"
 
 namespace lcc {
 
 constexpr int kFitThreads = 128;
+
+// FP64 reciprocal and reciprocal square root for the solver.  GB300 runs a
+// dependent FP64 FMA in ~64 cycles but a correctly rounded FP64 division or
+// square root in ~430-680 cycles, so these take the fp32 hardware estimate
+// and refine it with Newton steps in FP64: relative error ~1e-15 (rcp64, two
+// steps) and ~1.5e-14 (rsqrt64, one step), far below the fp32 rounding of
+// the plane.  Arguments must be positive normal fp32 numbers after the cast.
+__device__ __forceinline__ double rcp64(double x) {
+    double y = (double)__frcp_rn((float)x);
+    double e = fma(-x, y, 1.0);
+    y = fma(y, e, y);
+    e = fma(-x, y, 1.0);
+    return fma(y, e, y);
+}
+
+__device__ __forceinline__ double rsqrt64(double x) {
+    const double y = (double)__frsqrt_rn((float)x);
+    const double h = x * y;
+    const double r = fma(-h, y, 1.0);   // 1 - x y^2
+    return fma(0.5 * y, r, y);
+}
+
+// Scale a vector by roughly 1/max|v_i| so that its squared norm is fp32-safe.
+__device__ __forceinline__ bool prescale(double &x, double &y, double &z) {
+    const double m = fmax(fabs(x), fmax(fabs(y), fabs(z)));
+    if (!(m > 1e-300)) return false;
+    const double s = (double)__frcp_rn((float)fmin(fmax(m, 1e-30), 1e30));
+    x *= s;
+    y *= s;
+    z *= s;
+    return true;
+}
 
 // FP64 plane of the moments: returns true if the scatter matrix is degenerate.
 //
@@ -38,17 +80,18 @@ constexpr int kFitThreads = 128;
 // product of two rows of C - lambda_max I.  C is then projected onto the plane
 // orthogonal to that vector and the 2x2 problem is solved by one exact Jacobi
 // rotation, which gives lambda_min, lambda_mid and the normal with absolute
-// accuracy ~eps*lambda_max, like a full Jacobi sweep.
+// accuracy ~eps*lambda_max, like a full Jacobi sweep.  The dependency chain is
+// kept short (fixed Newton counts, no FP64 division or square root).
 __device__ __noinline__ bool solve_plane(const double m1[3], const double m2[6], int n, float ax, float ay,
                                          float az, float4 &pl, float &ratio) {
-    const double inv = 1.0 / (double)n;
+    const double inv = rcp64((double)n);
     const double mx = m1[0] * inv, my = m1[1] * inv, mz = m1[2] * inv;
-    const double cxx = m2[0] * inv - mx * mx, cxy = m2[1] * inv - mx * my, cxz = m2[2] * inv - mx * mz;
-    const double cyy = m2[3] * inv - my * my, cyz = m2[4] * inv - my * mz, czz = m2[5] * inv - mz * mz;
+    const double cxx = fma(m2[0], inv, -mx * mx), cxy = fma(m2[1], inv, -mx * my), cxz = fma(m2[2], inv, -mx * mz);
+    const double cyy = fma(m2[3], inv, -my * my), cyz = fma(m2[4], inv, -my * mz), czz = fma(m2[5], inv, -mz * mz);
     const double tr = cxx + cyy + czz;
     pl = make_float4(0.f, 0.f, 0.f, 0.f);
     ratio = 0.f;
-    if (!(tr > 0.0)) return true;
+    if (!(tr > 1e-30)) return true;
     // fp32 seed of the largest eigenvalue (trigonometric closed form)
     const float fxx = (float)cxx, fyy = (float)cyy, fzz = (float)czz;
     const float fxy = (float)cxy, fxz = (float)cxz, fyz = (float)cyz;
@@ -67,26 +110,25 @@ __device__ __noinline__ bool solve_plane(const double m1[3], const double m2[6],
         spread = pp;
     }
     // Newton on f(l) = det(C - l I) from above lambda_max: f is concave and
-    // decreasing there, so the iterates fall monotonically onto the root.
+    // decreasing there, so the iterates fall onto the root; three steps take
+    // the 3e-5 start offset to full precision (quadratic convergence).
     const double scale = (double)spread + 1e-30 * tr;
     double lam = (double)seed + 3e-5 * scale;
-    for (int it = 0; it < 6; it++) {
+#pragma unroll
+    for (int it = 0; it < 3; it++) {
         const double a = cxx - lam, b = cyy - lam, c = czz - lam;
-        const double myz = b * c - cyz * cyz, mxz = a * c - cxz * cxz, mxy = a * b - cxy * cxy;
-        const double det = a * myz - cxy * (cxy * c - cyz * cxz) + cxz * (cxy * cyz - b * cxz);
+        const double myz = fma(b, c, -cyz * cyz), mxz = fma(a, c, -cxz * cxz), mxy = fma(a, b, -cxy * cxy);
+        const double det = fma(a, myz, fma(-cxy, fma(cxy, c, -cyz * cxz), cxz * fma(cxy, cyz, -b * cxz)));
         const double dsum = myz + mxz + mxy;  // -f'(l) > 0 above the largest root
-        if (!(dsum > 0.0)) break;
-        const double step = det * (double)__frcp_rn((float)dsum);
-        lam += step;
-        if (fabs(step) <= 1e-17 * scale) break;
+        if (dsum > 0.0) lam = fma(det, (double)__frcp_rn((float)dsum), lam);
     }
     // eigenvector of lambda_max: largest cross product of two rows of C - lam I
     double v2x, v2y, v2z;
     {
         const double a = cxx - lam, b = cyy - lam, c = czz - lam;
-        const double x0 = cxy * cyz - b * cxz, y0 = cxz * cxy - cyz * a, z0 = b * a - cxy * cxy;   // r0 x r1
-        const double x1 = cxy * c - cxz * cyz, y1 = cxz * cxz - a * c, z1 = a * cyz - cxy * cxz;   // r0 x r2
-        const double x2 = b * c - cyz * cyz, y2 = cyz * cxz - cxy * c, z2 = cxy * cyz - b * cxz;   // r1 x r2
+        const double x0 = fma(cxy, cyz, -b * cxz), y0 = fma(cxz, cxy, -cyz * a), z0 = fma(b, a, -cxy * cxy);   // r0 x r1
+        const double x1 = fma(cxy, c, -cxz * cyz), y1 = fma(cxz, cxz, -a * c), z1 = fma(a, cyz, -cxy * cxz);   // r0 x r2
+        const double x2 = fma(b, c, -cyz * cyz), y2 = fma(cyz, cxz, -cxy * c), z2 = fma(cxy, cyz, -b * cxz);   // r1 x r2
         const double n0 = x0 * x0 + y0 * y0 + z0 * z0, n1 = x1 * x1 + y1 * y1 + z1 * z1,
                      n2 = x2 * x2 + y2 * y2 + z2 * z2;
         v2x = x2; v2y = y2; v2z = z2;
@@ -102,14 +144,12 @@ __device__ __noinline__ bool solve_plane(const double m1[3], const double m2[6],
             if (r1 > r0 && r1 >= r2) { wx = cxy; wy = b; wz = cyz; }
             else if (r2 > r0 && r2 > r1) { wx = cxz; wy = cyz; wz = c; }
             const double aw = fabs(wx), bw = fabs(wy), cw = fabs(wz);
-            // w x e_k with e_k the axis least aligned with w
             if (aw <= bw && aw <= cw) { v2x = 0.0; v2y = wz; v2z = -wy; }
             else if (bw <= cw) { v2x = -wz; v2y = 0.0; v2z = wx; }
             else { v2x = wy; v2y = -wx; v2z = 0.0; }
-            nn = v2x * v2x + v2y * v2y + v2z * v2z;
-            if (!(nn > 0.0)) return true;
         }
-        const double in = rsqrt(nn);
+        if (!prescale(v2x, v2y, v2z)) return true;
+        const double in = rsqrt64(v2x * v2x + v2y * v2y + v2z * v2z);
         v2x *= in; v2y *= in; v2z *= in;
     }
     // orthonormal basis (u, w) of the plane orthogonal to v2
@@ -119,10 +159,10 @@ __device__ __noinline__ bool solve_plane(const double m1[3], const double m2[6],
         if (ax2 <= ay2 && ax2 <= az2) { ux = 0.0; uy = v2z; uz = -v2y; }
         else if (ay2 <= az2) { ux = -v2z; uy = 0.0; uz = v2x; }
         else { ux = v2y; uy = -v2x; uz = 0.0; }
-        const double in = rsqrt(ux * ux + uy * uy + uz * uz);
+        const double in = rsqrt64(ux * ux + uy * uy + uz * uz);   // in [1/2, 1]: fp32-safe
         ux *= in; uy *= in; uz *= in;
     }
-    const double wx = v2y * uz - v2z * uy, wy = v2z * ux - v2x * uz, wz = v2x * uy - v2y * ux;
+    const double wx = fma(v2y, uz, -v2z * uy), wy = fma(v2z, ux, -v2x * uz), wz = fma(v2x, uy, -v2y * ux);
     // B = [u w]^T C [u w]
     const double cux = cxx * ux + cxy * uy + cxz * uz, cuy = cxy * ux + cyy * uy + cyz * uz,
                  cuz = cxz * ux + cyz * uy + czz * uz;
@@ -132,33 +172,41 @@ __device__ __noinline__ bool solve_plane(const double m1[3], const double m2[6],
     const double b01 = ux * cwx + uy * cwy + uz * cwz;
     const double b11 = wx * cwx + wy * cwy + wz * cwz;
     // one Jacobi rotation diagonalises the 2x2 block
-    double e0, e1, c0 = 1.0, s0 = 0.0;
-    if (b01 != 0.0) {
-        const double tau = (b11 - b00) / (2.0 * b01);
-        const double t = (tau >= 0.0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(tau * tau + 1.0));
-        c0 = rsqrt(t * t + 1.0);
+    double e0 = b00, e1 = b11, c0 = 1.0, s0 = 0.0;
+    if (fabs(b01) > 1e-30 * tr) {
+        const double tau = (b11 - b00) * (0.5 * rcp64(b01));
+        const double at = fabs(tau);
+        double t;
+        if (at > 1e4) {
+            // t = 1 / (|tau| + sqrt(tau^2 + 1)) = (1 - 1/(4 tau^2) + O(tau^-4)) / (2 |tau|)
+            const double r = rcp64(at);
+            t = 0.5 * r * fma(-0.25 * r, r, 1.0);
+        } else {
+            const double x = fma(at, at, 1.0);
+            t = rcp64(at + x * rsqrt64(x));
+        }
+        if (tau < 0.0) t = -t;
+        c0 = rsqrt64(fma(t, t, 1.0));
         s0 = t * c0;
-        e0 = b00 - t * b01;
-        e1 = b11 + t * b01;
-    } else {
-        e0 = b00;
-        e1 = b11;
+        e0 = fma(-t, b01, b00);
+        e1 = fma(t, b01, b11);
     }
     // eigenvectors in the (u, w) basis: (c, -s) for e0 and (s, c) for e1
-    double nx, ny, nz, lmin, lmid;
+    double nx, ny, nz, lmid;
     if (e0 <= e1) {
         nx = c0 * ux - s0 * wx; ny = c0 * uy - s0 * wy; nz = c0 * uz - s0 * wz;
-        lmin = e0; lmid = e1;
+        lmid = e1;
     } else {
         nx = s0 * ux + c0 * wx; ny = s0 * uy + c0 * wy; nz = s0 * uz + c0 * wz;
-        lmin = e1; lmid = e0;
+        lmid = e0;
     }
-    (void)lmin;
     const double lmax = lam;
     const bool degenerate = !(lmid > 1e-12 * lmax);   // lambda_mid <= 1e-12 lambda_max
-    ratio = lmax > 0.0 ? (float)(lmid / lmax) : 0.0f;
-    const double in = rsqrt(nx * nx + ny * ny + nz * nz);
-    nx *= in; ny *= in; nz *= in;
+    ratio = lmax > 0.0 ? (float)lmid / (float)lmax : 0.0f;
+    {
+        const double in = rsqrt64(nx * nx + ny * ny + nz * nz);   // ~1 already
+        nx *= in; ny *= in; nz *= in;
+    }
     double d = nx * ((double)ax + mx) + ny * ((double)ay + my) + nz * ((double)az + mz);
     bool flip;
     if (fabs(d) < 1e-9) {
@@ -173,230 +221,420 @@ __device__ __noinline__ bool solve_plane(const double m1[3], const double m2[6],
     return degenerate;
 }
 
-template <int TH_, int TW_>
-__global__ void __launch_bounds__(kFitThreads) k_fit(Geometry g, Scratch s, Batch b, Poses ps) {
-    constexpr int PX = TH_ * TW_;
-    constexpr int MW = (PX + 63) / 64;   // mask words
-    const int f = blockIdx.y;
-    const int t = blockIdx.x * kFitThreads + threadIdx.x;
-    if (t >= g.NT) return;
-    const int tr = t / g.TC, tc = t % g.TC;
-    const int i0 = tr * TH_, j0 = tc * TW_;
-    const uint32_t *rimg = s.rimg + (size_t)b.slot[f] * g.H * g.W;
-    TileRec *recs = s.tiles + (size_t)b.slot[f] * g.NT;
-    const float thr = g.thr;
+// Moments of a point set (float-float), anchor and count: the solver input.
+struct Moments {
+    ff s1x, s1y, s1z, sxx, sxy, sxz, syy, syz, szz;
+};
 
-    // range of pixel k of this tile (0 if empty or outside the image)
-    auto rng = [&](int k) -> float {
+// One plane solve; a single out-of-line copy keeps the instruction footprint
+// of the kernels small (the kernels run few warps per SM, so cold instruction
+// fetches, not arithmetic, bound them when code is duplicated).
+__device__ __noinline__ bool solve_moments(const Moments m, int n, float ax, float ay, float az, int solver,
+                                           float4 *pl, float *ratio) {
+    if (solver == 1) {
+        const double m1[3] = {ff_to_d(m.s1x), ff_to_d(m.s1y), ff_to_d(m.s1z)};
+        const double m2[6] = {ff_to_d(m.sxx), ff_to_d(m.sxy), ff_to_d(m.sxz),
+                              ff_to_d(m.syy), ff_to_d(m.syz), ff_to_d(m.szz)};
+        return solve_plane(m1, m2, n, ax, ay, az, *pl, *ratio);
+    }
+    const ffm::f2 f1[3] = {{m.s1x.hi, m.s1x.lo}, {m.s1y.hi, m.s1y.lo}, {m.s1z.hi, m.s1z.lo}};
+    const ffm::f2 f2m[6] = {{m.sxx.hi, m.sxx.lo}, {m.sxy.hi, m.sxy.lo}, {m.sxz.hi, m.sxz.lo},
+                            {m.syy.hi, m.syy.lo}, {m.syz.hi, m.syz.lo}, {m.szz.hi, m.szz.lo}};
+    float o4[4];
+    const bool dg = ffm::solve_plane_ff(f1, f2m, n, ax, ay, az, o4, ratio);
+    *pl = make_float4(o4[0], o4[1], o4[2], o4[3]);
+    return dg;
+}
+
+// Pixel masks of a tile (up to 128 pixels).
+struct Mask {
+    unsigned long long w0, w1;
+    __device__ __forceinline__ bool get(int k) const { return ((k < 64 ? w0 : w1) >> (k & 63)) & 1ull; }
+    __device__ __forceinline__ void set(int k) {
+        if (k < 64) w0 |= 1ull << k;
+        else w1 |= 1ull << (k & 63);
+    }
+    __device__ __forceinline__ bool operator==(const Mask &o) const { return w0 == o.w0 && w1 == o.w1; }
+};
+
+// One tile seen by one thread: geometry, valid mask and anchor.  Pixel
+// ranges are re-read from the range image (L1 hits) on each pass.
+template <int TH_, int TW_>
+struct TileView {
+    static constexpr int PX = TH_ * TW_;
+    const Geometry &g;
+    const uint32_t *rimg;
+    int t, tc, i0, j0;
+    Mask V;
+    int nv, first;
+    float ax, ay, az;
+
+    __device__ __forceinline__ TileView(const Geometry &g_, const uint32_t *rimg_, int t_)
+        : g(g_), rimg(rimg_), t(t_) {
+        const int tr = t / g.TC;
+        tc = t % g.TC;
+        i0 = tr * TH_;
+        j0 = tc * TW_;
+        nv = 0;
+        first = -1;
+        V.w0 = V.w1 = 0ull;
+#pragma unroll 4
+        for (int k = 0; k < PX; k++) {
+            if (r(k) > 0.0f) {
+                V.set(k);
+                nv++;
+                if (first < 0) first = k;
+            }
+        }
+        ax = ay = az = 0.f;
+        if (first >= 0) {
+            float ux, uy, uz;
+            u(first, ux, uy, uz);
+            const float r0 = r(first);
+            ax = __fmul_rn(r0, ux);
+            ay = __fmul_rn(r0, uy);
+            az = __fmul_rn(r0, uz);
+        }
+    }
+    // range of pixel k (0 if empty or outside the image)
+    __device__ __forceinline__ float r(int k) const {
         const int i = i0 + k / TW_, j = j0 + k % TW_;
         if (i >= g.H || j >= g.W) return 0.0f;
         const uint32_t bits = __ldg(rimg + (size_t)i * g.W + j);
         return bits_valid(bits) ? __uint_as_float(bits) : 0.0f;
-    };
-    auto ubeam = [&](int k, float &ux, float &uy, float &uz) {
+    }
+    __device__ __forceinline__ void u(int k, float &ux, float &uy, float &uz) const {
         beam(g, i0 + k / TW_, j0 + k % TW_, ux, uy, uz);
-    };
-
-    // valid mask and anchor (first valid pixel in raster order)
-    unsigned long long V[MW];
-    int nv = 0, first = -1;
-#pragma unroll
-    for (int w = 0; w < MW; w++) V[w] = 0ull;
-#pragma unroll 4
-    for (int k = 0; k < PX; k++) {
-        if (rng(k) > 0.0f) {
-            V[k >> 6] |= 1ull << (k & 63);
-            nv++;
-            if (first < 0) first = k;
-        }
     }
-    float ax = 0.f, ay = 0.f, az = 0.f;
-    if (first >= 0) {
-        float ux, uy, uz;
-        ubeam(first, ux, uy, uz);
-        const float r0 = rng(first);
-        ax = __fmul_rn(r0, ux);
-        ay = __fmul_rn(r0, uy);
-        az = __fmul_rn(r0, uz);
-    }
-
-    uint8_t status = nv == 0 ? S_EMPTY : S_FAIL;
-    uint8_t flags = 0, t_status = 0, t_rounds = 0, t_inl = 0, rounds = 0, n_inl = 0;
-    uint32_t kref = 0xFFFFFFFFu;
-    float4 tpl = make_float4(0.f, 0.f, 0.f, 0.f), pl = tpl;
-    unsigned long long Sm[MW], Im[MW];
-
     // inlier set of a plane over the valid pixels; returns its size
-    auto inliers = [&](const float4 &q4, unsigned long long (&I)[MW], bool &border) -> int {
+    __device__ __forceinline__ int inliers(const float4 &pl, Mask &I, bool &border) const {
         int cnt = 0;
-#pragma unroll
-        for (int w = 0; w < MW; w++) I[w] = 0ull;
-#pragma unroll 4
+        I.w0 = I.w1 = 0ull;
+#pragma unroll 2
         for (int k = 0; k < PX; k++) {
-            if (!((V[k >> 6] >> (k & 63)) & 1ull)) continue;
+            if (!V.get(k)) continue;
             float ux, uy, uz, e;
-            ubeam(k, ux, uy, uz);
-            if (residual(q4, ux, uy, uz, rng(k), thr, e)) {
-                I[k >> 6] |= 1ull << (k & 63);
+            u(k, ux, uy, uz);
+            if (residual(pl, ux, uy, uz, r(k), g.thr, e)) {
+                I.set(k);
                 cnt++;
             }
-            if (isfinite(e) && fabsf(fabsf(e) - thr) <= 1e-6f) border = true;
+            if (isfinite(e) && fabsf(fabsf(e) - g.thr) <= 1e-6f) border = true;
         }
         return cnt;
-    };
+    }
+    // one total-least-squares fit over the set S (float-float moments)
+    __device__ __forceinline__ bool fit(const Mask &S, int nS, float4 &pl, float &ratio) const {
+        Moments m;
+        m.s1x = m.s1y = m.s1z = m.sxx = m.sxy = m.sxz = m.syy = m.syz = m.szz = {0.f, 0.f};
+#pragma unroll 2
+        for (int k = 0; k < PX; k++) {
+            if (!S.get(k)) continue;
+            float ux, uy, uz;
+            u(k, ux, uy, uz);
+            const float rr = r(k);
+            const ff qx = two_sum(__fmul_rn(rr, ux), -ax), qy = two_sum(__fmul_rn(rr, uy), -ay),
+                     qz = two_sum(__fmul_rn(rr, uz), -az);
+            m.s1x = ff_add(m.s1x, qx);
+            m.s1y = ff_add(m.s1y, qy);
+            m.s1z = ff_add(m.s1z, qz);
+            m.sxx = ff_add(m.sxx, ff_mul(qx, qx));
+            m.sxy = ff_add(m.sxy, ff_mul(qx, qy));
+            m.sxz = ff_add(m.sxz, ff_mul(qx, qz));
+            m.syy = ff_add(m.syy, ff_mul(qy, qy));
+            m.syz = ff_add(m.syz, ff_mul(qy, qz));
+            m.szz = ff_add(m.szz, ff_mul(qz, qz));
+        }
+        return solve_moments(m, nS, ax, ay, az, g.solver, &pl, &ratio);
+    }
+};
 
-    // ---- temporal test (P frames) ----
-    if (b.kind == 1 && nv > 0) {
-        float aK[3];
-        transform_point(ps.m[f], ax, ay, az, aK);
-        float rK;
-        int pixK;
-        if (bin_point(g, aK[0], aK[1], aK[2], rK, pixK) == 0) {
-            const int kti = (pixK / g.W / g.th) * g.TC + (pixK % g.W) / g.tw;
-            const float4 kp = __ldg(b.kf + kti);
-            if (!(kp.x == 0.f && kp.y == 0.f && kp.z == 0.f)) {
-                float o[3];
-                rotate_normal(ps.m[f], kp.x, kp.y, kp.z, o);
-                kref = (uint32_t)kti;
-#pragma unroll
-                for (int w = 0; w < MW; w++) Sm[w] = V[w];
-                int nS = nv, nI = 0;
-                float c = 0.f;
-                bool border = false;
-                for (;;) {
-                    ff acc = {0.f, 0.f};
-#pragma unroll 4
-                    for (int k = 0; k < PX; k++) {
-                        if (!((Sm[k >> 6] >> (k & 63)) & 1ull)) continue;
-                        float ux, uy, uz;
-                        ubeam(k, ux, uy, uz);
-                        const float r = rng(k);
-                        const ff dp = ff_add(ff_add(two_prod(o[0], __fmul_rn(r, ux)), two_prod(o[1], __fmul_rn(r, uy))),
-                                             two_prod(o[2], __fmul_rn(r, uz)));
-                        acc = ff_add(acc, dp);
-                    }
-                    c = (float)(ff_to_d(acc) / (double)nS);
-                    t_rounds++;
-                    nI = inliers(make_float4(o[0], o[1], o[2], c), Im, border);
-                    bool same = nI == nS;
-#pragma unroll
-                    for (int w = 0; w < MW; w++) same = same && Im[w] == Sm[w];
-                    if (same || t_rounds == g.R + 1 || nI < 3) break;
-#pragma unroll
-                    for (int w = 0; w < MW; w++) Sm[w] = Im[w];
-                    nS = nI;
-                }
-                if (border) flags |= 1;
-                flags |= 4;
-                tpl = make_float4(o[0], o[1], o[2], c);
-                t_inl = (uint8_t)nI;
-                t_status = (nv >= 3 && nI >= need_inliers(g.fmin, nv)) ? 2 : 1;
-                if (t_status == 2) {
-                    status = S_TEMPORAL;
-                    pl = tpl;
-                    n_inl = (uint8_t)nI;
-                }
-            }
+struct RecOut {
+    float4 plane, tplane;
+    uint32_t kref, amask;
+    uint8_t status, rounds, flags, nv, n_inl, t_rounds, t_inl, t_status;
+    uint32_t acnt[4];
+};
+
+__device__ __forceinline__ void write_rec(TileRec *dst_rec, const RecOut &o) {
+    uint4 *dst = reinterpret_cast<uint4 *>(dst_rec);
+    dst[0] = make_uint4(__float_as_uint(o.plane.x), __float_as_uint(o.plane.y), __float_as_uint(o.plane.z),
+                        __float_as_uint(o.plane.w));
+    dst[1] = make_uint4(__float_as_uint(o.tplane.x), __float_as_uint(o.tplane.y), __float_as_uint(o.tplane.z),
+                        __float_as_uint(o.tplane.w));
+    const uint32_t w0 = (uint32_t)o.status | ((uint32_t)o.rounds << 8) | ((uint32_t)o.flags << 16) | ((uint32_t)o.nv << 24);
+    const uint32_t w1 = (uint32_t)o.n_inl | ((uint32_t)o.t_rounds << 8) | ((uint32_t)o.t_inl << 16) |
+                        ((uint32_t)o.t_status << 24);
+    dst[2] = make_uint4(o.kref, o.amask, w0, w1);
+    dst[3] = make_uint4(o.acnt[0], o.acnt[1], o.acnt[2], o.acnt[3]);
+}
+
+__device__ __forceinline__ RecOut read_rec(const TileRec *src_rec) {
+    const uint4 *src = reinterpret_cast<const uint4 *>(src_rec);
+    const uint4 q0 = src[0], q1 = src[1], q2 = src[2];
+    RecOut o;
+    o.plane = make_float4(__uint_as_float(q0.x), __uint_as_float(q0.y), __uint_as_float(q0.z), __uint_as_float(q0.w));
+    o.tplane = make_float4(__uint_as_float(q1.x), __uint_as_float(q1.y), __uint_as_float(q1.z), __uint_as_float(q1.w));
+    o.kref = q2.x;
+    o.amask = 0;
+    o.status = q2.z & 0xff; o.rounds = (q2.z >> 8) & 0xff; o.flags = (q2.z >> 16) & 0xff; o.nv = q2.z >> 24;
+    o.n_inl = q2.w & 0xff; o.t_rounds = (q2.w >> 8) & 0xff; o.t_inl = (q2.w >> 16) & 0xff; o.t_status = q2.w >> 24;
+    o.acnt[0] = o.acnt[1] = o.acnt[2] = o.acnt[3] = 0;
+    return o;
+}
+
+// Warp-aggregated push of (frame, tile) onto a work queue.
+__device__ __forceinline__ void queue_push(bool push, uint32_t item, uint32_t *queue, uint32_t *count) {
+    const unsigned mask = __ballot_sync(__activemask(), push);
+    if (!push) return;
+    const int lane = threadIdx.x & 31;
+    const int leader = __ffs(mask) - 1;
+    uint32_t base = 0;
+    if (lane == leader) base = atomicAdd(count, (uint32_t)__popc(mask));
+    base = __shfl_sync(mask, base, leader);
+    queue[base + __popc(mask & ((1u << lane) - 1u))] = item;
+}
+
+// Spatial rounds of one tile from its current state (o.rounds fits done, the
+// last plane in o.plane).  Runs at most `max_rounds` more fits; returns true
+// if the tile is finished (o fully updated), false if it needs more rounds.
+template <int TH_, int TW_>
+__device__ __forceinline__ bool spatial_rounds(const TileView<TH_, TW_> &tv, RecOut &o, int max_rounds) {
+    const Geometry &g = tv.g;
+    Mask S, I;
+    int nS;
+    bool border = false;
+    if (o.rounds == 0) {
+        S = tv.V;
+        nS = tv.nv;
+    } else {
+        nS = tv.inliers(o.plane, S, border);   // the set the previous plane kept
+    }
+    bool done = false;
+    for (int r = 0; r < max_rounds; r++) {
+        float ratio = 0.f;
+        const bool degen = tv.fit(S, nS, o.plane, ratio);
+        if (ratio >= 0.999e-12f && ratio <= 1.001e-12f) o.flags |= 1;
+        o.rounds++;
+        const int nI = degen ? 0 : tv.inliers(o.plane, I, border);
+        done = degen || nI < 3 || o.rounds == g.R + 1 || (nI == nS && I == S);
+        if (done) {
+            o.n_inl = (uint8_t)nI;
+            if (degen) o.flags |= 2;
+            if (!degen && nI >= need_inliers(g.fmin, tv.nv)) o.status = S_FIT;
+            break;
+        }
+        S = I;
+        nS = nI;
+    }
+    if (border) o.flags |= 1;
+    return done;
+}
+
+// Temporal test of a P tile (Sec. III-D): anchor to key-frame coordinates,
+// K tile lookup, rotated normal, offset refit rounds.  Updates o.
+template <int TH_, int TW_>
+__device__ __forceinline__ void temporal_test(const TileView<TH_, TW_> &tv, const double *M, const float4 *kf,
+                                              RecOut &o) {
+    const Geometry &g = tv.g;
+    float aK[3];
+    transform_point(M, tv.ax, tv.ay, tv.az, aK);
+    float rK;
+    int pixK;
+    if (bin_point(g, aK[0], aK[1], aK[2], rK, pixK) != 0) return;
+    const int kti = (pixK / g.W / g.th) * g.TC + (pixK % g.W) / g.tw;
+    const float4 kp = __ldg(kf + kti);
+    if (kp.x == 0.f && kp.y == 0.f && kp.z == 0.f) return;
+    float n[3];
+    rotate_normal(M, kp.x, kp.y, kp.z, n);
+    o.kref = (uint32_t)kti;
+    Mask S = tv.V, I;
+    int nS = tv.nv, nI = 0;
+    float c = 0.f;
+    bool border = false;
+    for (;;) {
+        ff acc = {0.f, 0.f};
+#pragma unroll 2
+        for (int k = 0; k < TileView<TH_, TW_>::PX; k++) {
+            if (!S.get(k)) continue;
+            float ux, uy, uz;
+            tv.u(k, ux, uy, uz);
+            const float rr = tv.r(k);
+            const ff dp = ff_add(ff_add(two_prod(n[0], __fmul_rn(rr, ux)), two_prod(n[1], __fmul_rn(rr, uy))),
+                                 two_prod(n[2], __fmul_rn(rr, uz)));
+            acc = ff_add(acc, dp);
+        }
+        c = ffm::mul({acc.hi, acc.lo}, ffm::rcp(ffm::mk((float)nS))).hi;   // mean of n'.p
+        o.t_rounds++;
+        nI = tv.inliers(make_float4(n[0], n[1], n[2], c), I, border);
+        if ((nI == nS && I == S) || o.t_rounds == g.R + 1 || nI < 3) break;
+        S = I;
+        nS = nI;
+    }
+    if (border) o.flags |= 1;
+    o.flags |= 4;
+    o.tplane = make_float4(n[0], n[1], n[2], c);
+    o.t_inl = (uint8_t)nI;
+    o.t_status = (tv.nv >= 3 && nI >= need_inliers(g.fmin, tv.nv)) ? 2 : 1;
+    if (o.t_status == 2) {
+        o.status = S_TEMPORAL;
+        o.plane = o.tplane;
+        o.n_inl = (uint8_t)nI;
+    }
+}
+
+// First pass over every tile: temporal test (P frames), then the spatial fit.
+// Schedule 0 runs all of a tile's rounds in its thread; schedule 1 runs at
+// most the first spatial round here and queues the tile for dense round
+// kernels (k_fit_round), so that tiles needing more rounds do not hold
+// whole warps.
+template <int TH_, int TW_, bool kQueue>
+__global__ void __launch_bounds__(kFitThreads) k_fit_first(Geometry g, Scratch s, Batch b, Poses ps) {
+    using TV = TileView<TH_, TW_>;
+    const int f = blockIdx.y;
+    const int t = blockIdx.x * kFitThreads + threadIdx.x;
+    if (t >= g.NT) return;
+    const uint32_t *rimg = s.rimg + (size_t)b.slot[f] * g.H * g.W;
+    TileRec *recs = s.tiles + (size_t)b.slot[f] * g.NT;
+    const TV tv(g, rimg, t);
+    RecOut o;
+    o.plane = o.tplane = make_float4(0.f, 0.f, 0.f, 0.f);
+    o.kref = 0xFFFFFFFFu;
+    o.amask = 0;
+    o.acnt[0] = o.acnt[1] = o.acnt[2] = o.acnt[3] = 0;
+    o.status = tv.nv == 0 ? S_EMPTY : S_FAIL;
+    o.rounds = o.flags = o.n_inl = o.t_rounds = o.t_inl = o.t_status = 0;
+    o.nv = (uint8_t)tv.nv;
+    if (b.kind == 1 && tv.nv > 0) temporal_test<TH_, TW_>(tv, ps.m[f], b.kf, o);
+    bool queued = false;
+    if (o.status != S_TEMPORAL && tv.nv >= 3) {
+        if (!kQueue) {
+            spatial_rounds<TH_, TW_>(tv, o, g.R + 1);
+        } else if (b.kind == 1) {
+            queued = true;   // P-frame spatial fallback from its first round, in the dense pass
+        } else {
+            queued = !spatial_rounds<TH_, TW_>(tv, o, 1);
         }
     }
+    if (kQueue) queue_push(queued, ((uint32_t)f << 26) | (uint32_t)t, s.queue, s.qcount);
+    write_rec(recs + t, o);
+}
 
-    // ---- spatial fit with drop-and-refit rounds ----
-    if (status != S_TEMPORAL && nv >= 3) {
-#pragma unroll
-        for (int w = 0; w < MW; w++) Sm[w] = V[w];
-        int nS = nv, nI = 0;
-        bool degen = false, border = false;
-        float4 cur = make_float4(0.f, 0.f, 0.f, 0.f);
-        for (;;) {
-            ff s1x = {0.f, 0.f}, s1y = s1x, s1z = s1x, sxx = s1x, sxy = s1x, sxz = s1x, syy = s1x, syz = s1x, szz = s1x;
-#pragma unroll 4
-            for (int k = 0; k < PX; k++) {
-                if (!((Sm[k >> 6] >> (k & 63)) & 1ull)) continue;
-                float ux, uy, uz;
-                ubeam(k, ux, uy, uz);
-                const float r = rng(k);
-                const ff qx = two_sum(__fmul_rn(r, ux), -ax), qy = two_sum(__fmul_rn(r, uy), -ay),
-                         qz = two_sum(__fmul_rn(r, uz), -az);
-                s1x = ff_add(s1x, qx);
-                s1y = ff_add(s1y, qy);
-                s1z = ff_add(s1z, qz);
-                sxx = ff_add(sxx, ff_mul(qx, qx));
-                sxy = ff_add(sxy, ff_mul(qx, qy));
-                sxz = ff_add(sxz, ff_mul(qx, qz));
-                syy = ff_add(syy, ff_mul(qy, qy));
-                syz = ff_add(syz, ff_mul(qy, qz));
-                szz = ff_add(szz, ff_mul(qz, qz));
-            }
-            const double m1[3] = {ff_to_d(s1x), ff_to_d(s1y), ff_to_d(s1z)};
-            const double m2[6] = {ff_to_d(sxx), ff_to_d(sxy), ff_to_d(sxz), ff_to_d(syy), ff_to_d(syz), ff_to_d(szz)};
-            float ratio = 0.f;
-            degen = solve_plane(m1, m2, nS, ax, ay, az, cur, ratio);
-            if (ratio >= 0.999e-12f && ratio <= 1.001e-12f) flags |= 1;
-            rounds++;
-            if (degen) {
-                nI = 0;
-                break;
-            }
-            nI = inliers(cur, Im, border);
-            bool same = nI == nS;
-#pragma unroll
-            for (int w = 0; w < MW; w++) same = same && Im[w] == Sm[w];
-            if (same || rounds == g.R + 1 || nI < 3) break;
-#pragma unroll
-            for (int w = 0; w < MW; w++) Sm[w] = Im[w];
-            nS = nI;
-        }
-        if (border) flags |= 1;
-        pl = cur;
-        n_inl = (uint8_t)nI;
-        if (degen) flags |= 2;
-        if (!degen && nI >= need_inliers(g.fmin, nv)) status = S_FIT;
+// One more spatial round for every queued tile; tiles that still need one
+// are pushed onto the next queue.
+template <int TH_, int TW_>
+__global__ void __launch_bounds__(kFitThreads) k_fit_round(Geometry g, Scratch s, Batch b, int in_q, int out_q) {
+    using TV = TileView<TH_, TW_>;
+    const uint32_t n_in = s.qcount[in_q];
+    const uint32_t *qin = s.queue + (size_t)(in_q & 1) * s.qcap;
+    uint32_t *qout = s.queue + (size_t)(out_q & 1) * s.qcap;
+    for (uint32_t idx = blockIdx.x * kFitThreads + threadIdx.x; idx < n_in; idx += gridDim.x * kFitThreads) {
+        const uint32_t item = qin[idx];
+        const int f = (int)(item >> 26), t = (int)(item & 0x3FFFFFFu);
+        const uint32_t *rimg = s.rimg + (size_t)b.slot[f] * g.H * g.W;
+        TileRec *recs = s.tiles + (size_t)b.slot[f] * g.NT;
+        const TV tv(g, rimg, t);
+        RecOut o = read_rec(recs + t);
+        const bool done = spatial_rounds<TH_, TW_>(tv, o, 1);
+        queue_push(!done, item, qout, s.qcount + out_q);
+        write_rec(recs + t, o);
     }
+}
 
-    // ---- look-ahead tests of the next tiles of the row against this plane ----
-    uint32_t amask = 0, acnt[4] = {0u, 0u, 0u, 0u};
-    if (status == S_FIT && g.merge) {
-        for (int k = 1; k <= g.lookahead && tc + k < g.TC; k++) {
-            const int jn = j0 + k * TW_;
-            int nvn = 0, nin = 0;
-#pragma unroll 4
-            for (int q = 0; q < PX; q++) {
-                const int i = i0 + q / TW_, j = jn + q % TW_;
-                if (i >= g.H || j >= g.W) continue;
-                const uint32_t bits = __ldg(rimg + (size_t)i * g.W + j);
-                if (!bits_valid(bits)) continue;
-                nvn++;
+// Run pre-test, after every tile's own fit is final: tile t tests its own
+// pixels against the planes of the (up to `lookahead`) tiles to its left in
+// the row whose fit succeeded.  Bit j of the result (and count byte j) says
+// whether tile t would join a run started at tile t-1-j, i.e. passes that
+// plane under the acceptance rule (Sec. III-C run growth).  Working from the
+// tested tile keeps every pixel load in the tile's own (cached) range.
+template <int TH_, int TW_>
+__global__ void __launch_bounds__(kFitThreads) k_lookbehind(Geometry g, Scratch s, Batch b) {
+    using TV = TileView<TH_, TW_>;
+    const int f = blockIdx.y;
+    const int t = blockIdx.x * kFitThreads + threadIdx.x;
+    if (t >= g.NT) return;
+    const uint32_t *rimg = s.rimg + (size_t)b.slot[f] * g.H * g.W;
+    TileRec *recs = s.tiles + (size_t)b.slot[f] * g.NT;
+    const TV tv(g, rimg, t);
+    uint32_t bmask = 0, bcnt[4] = {0u, 0u, 0u, 0u};
+    const int need = need_inliers(g.fmin, tv.nv);
+    const int span = min(g.lookahead, tv.tc);
+    if (tv.nv >= 3) {
+        for (int j = 0; j < span; j++) {
+            const TileRec *src = recs + (t - 1 - j);
+            const uint32_t w0 = *reinterpret_cast<const uint32_t *>(reinterpret_cast<const uint8_t *>(src) + 40);
+            if ((w0 & 0xff) != S_FIT) continue;
+            const float4 pl = src->plane;
+            int nin = 0;
+#pragma unroll 2
+            for (int k = 0; k < TV::PX; k++) {
+                if (!tv.V.get(k)) continue;
                 float ux, uy, uz, e;
-                beam(g, i, j, ux, uy, uz);
-                nin += residual(pl, ux, uy, uz, __uint_as_float(bits), thr, e) ? 1 : 0;
+                tv.u(k, ux, uy, uz);
+                nin += residual(pl, ux, uy, uz, tv.r(k), g.thr, e) ? 1 : 0;
             }
-            if (nvn >= 3 && nin >= need_inliers(g.fmin, nvn)) amask |= 1u << (k - 1);
-            acnt[(k - 1) >> 2] |= (uint32_t)nin << (8 * ((k - 1) & 3));
+            if (nin >= need) bmask |= 1u << j;
+            bcnt[j >> 2] |= (uint32_t)nin << (8 * (j & 3));
         }
     }
-
-    uint4 *dst = reinterpret_cast<uint4 *>(recs + t);
-    dst[0] = make_uint4(__float_as_uint(pl.x), __float_as_uint(pl.y), __float_as_uint(pl.z), __float_as_uint(pl.w));
-    dst[1] = make_uint4(__float_as_uint(tpl.x), __float_as_uint(tpl.y), __float_as_uint(tpl.z), __float_as_uint(tpl.w));
-    const uint32_t w0 = (uint32_t)status | ((uint32_t)rounds << 8) | ((uint32_t)flags << 16) | ((uint32_t)nv << 24);
-    const uint32_t w1 = (uint32_t)n_inl | ((uint32_t)t_rounds << 8) | ((uint32_t)t_inl << 16) | ((uint32_t)t_status << 24);
-    dst[2] = make_uint4(kref, amask, w0, w1);
-    dst[3] = make_uint4(acnt[0], acnt[1], acnt[2], acnt[3]);
+    uint8_t *base = reinterpret_cast<uint8_t *>(recs + t);
+    *reinterpret_cast<uint32_t *>(base + 36) = bmask;
+    *reinterpret_cast<uint4 *>(base + 48) = make_uint4(bcnt[0], bcnt[1], bcnt[2], bcnt[3]);
 }
 
 template <int TH_, int TW_>
-static cudaError_t launch_fit_t(const Geometry &g, const Scratch &s, const Batch &b, const Poses &p, cudaStream_t st) {
+static cudaError_t launch_fit_first_t(const Geometry &g, const Scratch &s, const Batch &b, const Poses &p,
+                                     cudaStream_t st) {
     dim3 grid((g.NT + kFitThreads - 1) / kFitThreads, b.nframes);
-    k_fit<TH_, TW_><<<grid, kFitThreads, 0, st>>>(g, s, b, p);
+    if (g.schedule == 1) {
+        cudaError_t e = cudaMemsetAsync(s.qcount, 0, sizeof(uint32_t) * 8, st);
+        if (e != cudaSuccess) return e;
+        k_fit_first<TH_, TW_, true><<<grid, kFitThreads, 0, st>>>(g, s, b, p);
+    } else {
+        k_fit_first<TH_, TW_, false><<<grid, kFitThreads, 0, st>>>(g, s, b, p);
+    }
     return cudaGetLastError();
+}
+
+template <int TH_, int TW_>
+static cudaError_t launch_lookbehind_t(const Geometry &g, const Scratch &s, const Batch &b, cudaStream_t st) {
+    if (!g.merge || g.lookahead <= 0) return cudaSuccess;
+    dim3 grid((g.NT + kFitThreads - 1) / kFitThreads, b.nframes);
+    k_lookbehind<TH_, TW_><<<grid, kFitThreads, 0, st>>>(g, s, b);
+    return cudaGetLastError();
+}
+
+template <int TH_, int TW_>
+static cudaError_t launch_fit_rounds_t(const Geometry &g, const Scratch &s, const Batch &b, cudaStream_t st) {
+    if (g.schedule == 1) {
+        // key frames did round 1 already; P frames start their spatial rounds here
+        const int rounds_left = g.R + (b.kind == 1 ? 1 : 0);
+        const long long worst = (long long)g.NT * b.nframes;
+        const int blocks = (int)std::min<long long>((worst + kFitThreads - 1) / kFitThreads, 152 * 8);
+        for (int r = 0; r < rounds_left; r++) {
+            k_fit_round<TH_, TW_><<<blocks, kFitThreads, 0, st>>>(g, s, b, r, r + 1);
+            const cudaError_t e = cudaGetLastError();
+            if (e != cudaSuccess) return e;
+        }
+    }
+    return launch_lookbehind_t<TH_, TW_>(g, s, b, st);
 }
 
 cudaError_t launch_fit(const Geometry &g, const Scratch &s, const Batch &b, const Poses &p, cudaStream_t st) {
     if (b.nframes <= 0) return cudaSuccess;
-    if (g.th == 4 && g.tw == 4) return launch_fit_t<4, 4>(g, s, b, p, st);
-    if (g.th == 4 && g.tw == 8) return launch_fit_t<4, 8>(g, s, b, p, st);
-    if (g.th == 8 && g.tw == 8) return launch_fit_t<8, 8>(g, s, b, p, st);
-    if (g.th == 8 && g.tw == 16) return launch_fit_t<8, 16>(g, s, b, p, st);
+    if (g.th == 4 && g.tw == 4) return launch_fit_first_t<4, 4>(g, s, b, p, st);
+    if (g.th == 4 && g.tw == 8) return launch_fit_first_t<4, 8>(g, s, b, p, st);
+    if (g.th == 8 && g.tw == 8) return launch_fit_first_t<8, 8>(g, s, b, p, st);
+    if (g.th == 8 && g.tw == 16) return launch_fit_first_t<8, 16>(g, s, b, p, st);
+    return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_fit_rounds(const Geometry &g, const Scratch &s, const Batch &b, cudaStream_t st) {
+    if (b.nframes <= 0) return cudaSuccess;
+    if (g.th == 4 && g.tw == 4) return launch_fit_rounds_t<4, 4>(g, s, b, st);
+    if (g.th == 4 && g.tw == 8) return launch_fit_rounds_t<4, 8>(g, s, b, st);
+    if (g.th == 8 && g.tw == 8) return launch_fit_rounds_t<8, 8>(g, s, b, st);
+    if (g.th == 8 && g.tw == 16) return launch_fit_rounds_t<8, 16>(g, s, b, st);
     return cudaErrorInvalidValue;
 }
 

@@ -4,8 +4,9 @@
 // (the run's first plane) still codes the next tile under the threshold, and
 // restarts at the first tile that fails.  The walk is sequential along a row,
 // so each step is made warp-wide: the 32 lanes look at 32 consecutive tiles,
-// a ballot finds the first candidate run start, the start's precomputed
-// look-ahead bits (from the fit kernel) decide the first `lookahead` joins,
+// a ballot finds the first candidate run start, the precomputed look-behind
+// bits of the following tiles (from the fit stage) decide the first
+// `lookahead` joins,
 // and only runs longer than that test further tiles explicitly, 32 tiles per
 // step with one lane per tile.  Temporal tiles of P frames are already coded
 // (Sec. III-D) and end a run.
@@ -93,17 +94,18 @@ __global__ void __launch_bounds__(32) k_merge(Geometry g, Scratch s, Batch b) {
         }
         int k = s0 + 1;
         bool open = g.merge && k < g.TC;
-        // phase 1: joins decided by the fit kernel's look-ahead bits
+        // phase 1: joins decided by the precomputed look-behind bits
         const int hz = g.merge ? min(g.lookahead, g.TC - 1 - s0) : 0;
         if (hz > 0) {
-            const uint32_t amask = start.amask;
             const int c1 = s0 + 1 + lane;
             bool pass = false;
             int cnt = 0, nv1 = 0;
             if (lane < hz) {
-                pass = ((amask >> lane) & 1u) && row[c1].status != S_TEMPORAL;
-                cnt = (start.acnt[lane >> 2] >> (8 * (lane & 3))) & 0xff;
-                nv1 = row[c1].n_valid;
+                // tile c1's look-behind bit `lane` refers to the plane of tile c1-1-lane = s0
+                const RowRec &h1 = row[c1];
+                pass = ((h1.amask >> lane) & 1u) && h1.status != S_TEMPORAL;
+                cnt = (h1.acnt[lane >> 2] >> (8 * (lane & 3))) & 0xff;
+                nv1 = h1.n_valid;
             }
             const uint32_t failb = __ballot_sync(FULL, lane < hz && !pass);
             const int nj = failb ? __ffs(failb) - 1 : hz;

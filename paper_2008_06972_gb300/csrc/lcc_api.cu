@@ -22,8 +22,8 @@ struct ProfRec {
     cudaEvent_t a, b;
 };
 
-const char *kKernelNames[] = {"bin", "fit", "merge", "scan", "pack", "decode_prep", "decode_px", "range_export"};
-constexpr int kNumKernels = 8;
+const char *kKernelNames[] = {"bin", "fit", "merge", "scan", "pack", "decode_prep", "decode_px", "range_export", "refit"};
+constexpr int kNumKernels = 9;
 
 size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
@@ -187,6 +187,7 @@ lcc_status encode_batch(lcc_ctx *c, int kind, int nframes, const int *slots, uin
     if (poses)
         for (int f = 0; f < nframes; f++) memcpy(p.m[f], poses + 16 * f, 16 * sizeof(double));
     LCC_LAUNCH(c, 1, launch_fit(c->g, c->s, b, p, c->stream));
+    LCC_LAUNCH(c, 8, launch_fit_rounds(c->g, c->s, b, c->stream));
     LCC_LAUNCH(c, 2, launch_merge(c->g, c->s, b, c->stream));
     LCC_LAUNCH(c, 3, launch_scan(c->g, c->s, b, c->stream));
     LCC_LAUNCH(c, 4, launch_pack(c->g, c->s, b, c->stream));
@@ -267,7 +268,9 @@ void lcc_default_params(lcc_params *p) {
     p->min_inlier_frac = 0.75f;
     p->merge_runs = 1;
     p->max_batch = 16;
-    p->lookahead = 8;
+    p->lookahead = 16;
+    p->solver = 0;
+    p->fit_schedule = 0;
 }
 
 lcc_status lcc_create(lcc_ctx **out, const lcc_sensor *sensor, const lcc_params *params, void *cuda_stream) {
@@ -276,12 +279,14 @@ lcc_status lcc_create(lcc_ctx **out, const lcc_sensor *sensor, const lcc_params 
     const lcc_sensor &s = *sensor;
     const lcc_params &p = *params;
     if (s.rows < 1 || s.cols < 2 || s.rows > 65535 || s.cols > 65535 || !(s.elev_max_deg > s.elev_min_deg) ||
+        (int64_t)s.rows * s.cols > (1 << 26) ||
         s.elev_max_deg > 90.0 || s.elev_min_deg < -90.0 || !(s.max_range_m > 0))
         return LCC_ERR_INVALID_ARG;
     if (!tile_supported(p.tile_h, p.tile_w)) return LCC_ERR_UNSUPPORTED;
     if (!(p.fit_thr_m >= 0) || !(p.quant_m > 0) || p.max_refits < 0 || p.max_refits > 6 ||
         !(p.min_inlier_frac >= 0) || p.max_batch < 1 || p.max_batch > kMaxBatch || p.lookahead < 0 ||
-        p.lookahead > 16)
+        p.lookahead > 16 || p.solver < 0 || p.solver > 1 || p.fit_schedule < 0 ||
+        p.fit_schedule > 1)
         return LCC_ERR_INVALID_ARG;
     int dev = 0;
     cudaDeviceProp prop;
@@ -310,6 +315,8 @@ lcc_status lcc_create(lcc_ctx **out, const lcc_sensor *sensor, const lcc_params 
     g.R = p.max_refits;
     g.merge = p.merge_runs ? 1 : 0;
     g.lookahead = p.merge_runs ? p.lookahead : 0;
+    g.solver = p.solver;
+    g.schedule = p.fit_schedule;
     g.k_max = (int)floorf(p.fit_thr_m / p.quant_m + 0.5f) + 1;
     g.w_res = bits_for(2 * g.k_max);
     const int m_max = (int)floorf((float)s.max_range_m / p.quant_m + 0.5f) + 1;
@@ -350,7 +357,9 @@ lcc_status lcc_create(lcc_ctx **out, const lcc_sensor *sensor, const lcc_params 
     const size_t o_bytes = o_stats + align256(sl * sizeof(DevStats));
     const size_t o_err = o_bytes + align256(sl * 8);
     const size_t o_dec = o_err + 256;
-    const size_t total = o_dec + align256((nt + 4) * sizeof(DecTile));
+    const size_t o_queue = o_dec + align256((nt + 4) * sizeof(DecTile));
+    const size_t o_qcount = o_queue + align256(2 * sl * nt * 4);
+    const size_t total = o_qcount + 256;
     if (cudaMalloc(&c->d_scratch, total) != cudaSuccess) {
         cudaFree(c->d_tables);
         delete c;
@@ -366,6 +375,9 @@ lcc_status lcc_create(lcc_ctx **out, const lcc_sensor *sensor, const lcc_params 
     c->s.bytes = (unsigned long long *)(base + o_bytes);
     c->s.err = (uint32_t *)(base + o_err);
     c->d_dec = (DecTile *)(base + o_dec);
+    c->s.queue = (uint32_t *)(base + o_queue);
+    c->s.qcount = (uint32_t *)(base + o_qcount);
+    c->s.qcap = (uint32_t)(sl * nt);
     cudaMemset(c->d_scratch, 0, total);
     cudaMemset(c->s.rimg, 0xFF, sl * npx * 4);
     c->max_bytes = (uint64_t)kHeaderBytes +

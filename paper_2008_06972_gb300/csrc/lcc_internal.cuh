@@ -34,10 +34,10 @@ struct alignas(16) TileRec {
     float4 plane;        // own spatial plane (n, d) or (n', c') if temporal
     float4 tplane;       // temporal test plane
     uint32_t kref;       // K tile of the anchor, ~0u if none
-    uint32_t ahead_mask; // bit k-1: tile +k passes this plane
+    uint32_t ahead_mask; // bit j: this tile passes the plane of tile t-1-j (run pre-test)
     uint8_t status, rounds, flags, n_valid;
     uint8_t n_inlier, t_rounds, t_inlier, t_status;
-    uint8_t ahead_cnt[16];
+    uint8_t ahead_cnt[16];  // inlier counts of those tests
 };
 static_assert(sizeof(TileRec) == 64, "TileRec layout");
 static_assert(sizeof(TileRec) == sizeof(lcc_tile_info), "TileRec matches lcc_tile_info");
@@ -85,6 +85,8 @@ struct Geometry {
     float thr, q, rmax, fmin;
     int R;               // refit rounds after the first fit
     int merge, lookahead;
+    int solver;          // 0 float-float plane solve, 1 FP64
+    int schedule;        // 0 per-thread fit rounds, 1 queued dense rounds
     int k_max, w_res, w_raw;
     float elev_max_deg, d_el_deg, d_az;   // first guesses only; the tables decide
     const float *ce, *se, *ct, *st;       // beam tables
@@ -101,6 +103,9 @@ struct Scratch {
     DevStats *stats;     // [slots]
     unsigned long long *bytes;  // [slots] stream size (or needed size)
     uint32_t *err;       // latched error bits
+    uint32_t *queue;     // [2][qcap] fit work queues (frame << 26 | tile)
+    uint32_t *qcount;    // [8] items pushed per fit round
+    uint32_t qcap;       // entries per queue (slots * tiles)
 };
 
 // One batched launch over up to kMaxBatch frames of the same sensor.
@@ -281,6 +286,7 @@ cudaError_t launch_bin(const Geometry &g, const Scratch &s, const Batch &b, long
 cudaError_t launch_range_image(const Geometry &g, const uint32_t *rimg, float *range, uint32_t *valid,
                                cudaStream_t st);
 cudaError_t launch_fit(const Geometry &g, const Scratch &s, const Batch &b, const Poses &p, cudaStream_t st);
+cudaError_t launch_fit_rounds(const Geometry &g, const Scratch &s, const Batch &b, cudaStream_t st);
 cudaError_t launch_merge(const Geometry &g, const Scratch &s, const Batch &b, cudaStream_t st);
 cudaError_t launch_scan(const Geometry &g, const Scratch &s, const Batch &b, cudaStream_t st);
 cudaError_t launch_pack(const Geometry &g, const Scratch &s, const Batch &b, cudaStream_t st);

@@ -34,7 +34,8 @@ class lcc_sensor(ctypes.Structure):
 class lcc_params(ctypes.Structure):
     _fields_ = [("tile_h", ctypes.c_int32), ("tile_w", ctypes.c_int32), ("fit_thr_m", ctypes.c_float),
                 ("quant_m", ctypes.c_float), ("max_refits", ctypes.c_int32), ("min_inlier_frac", ctypes.c_float),
-                ("merge_runs", ctypes.c_int32), ("max_batch", ctypes.c_int32), ("lookahead", ctypes.c_int32)]
+                ("merge_runs", ctypes.c_int32), ("max_batch", ctypes.c_int32), ("lookahead", ctypes.c_int32),
+                ("solver", ctypes.c_int32), ("fit_schedule", ctypes.c_int32)]
 
 
 class lcc_stats(ctypes.Structure):
@@ -53,7 +54,7 @@ TILE_INFO_DTYPE = np.dtype([("plane", "<f4", 4), ("tplane", "<f4", 4), ("kref", 
 assert TILE_INFO_DTYPE.itemsize == 64
 
 _lib = None
-KERNEL_NAMES = ("bin", "fit", "merge", "scan", "pack", "decode_prep", "decode_px", "range_export")
+KERNEL_NAMES = ("bin", "fit", "merge", "scan", "pack", "decode_prep", "decode_px", "range_export", "refit")
 
 
 def load(path: str = LIB_PATH):

@@ -35,9 +35,9 @@ def _oparams(tile=(4, 4), thr=0.05, q=0.02, R=3, fmin=0.75, merge=1):
     return O.params(tile[0], tile[1], thr, q, R, fmin, merge)
 
 
-def _gparams(tile=(4, 4), thr=0.05, q=0.02, R=3, fmin=0.75, merge=1, **kw):
+def _gparams(tile=(4, 4), thr=0.05, q=0.02, R=3, fmin=0.75, merge=1, solver=0, **kw):
     return dict(tile_h=tile[0], tile_w=tile[1], fit_thr_m=thr, quant_m=q, max_refits=R, min_inlier_frac=fmin,
-                merge_runs=merge, **kw)
+                merge_runs=merge, solver=solver, **kw)
 
 
 def _compare_spatial(s, p, rng, recs, ofits, thr, skip=None):
@@ -88,7 +88,7 @@ def _check_decode(c, s, bits, rng, q, kf_gpu=None, kft=None, pose=None):
 def _keyframe_case(sensor_, pts, **kw):
     from paper_2008_06972_gb300 import lcc
     s = O.sensor(sensor_)
-    p = _oparams(**kw)
+    p = _oparams(**{k: v for k, v in kw.items() if k not in ("solver", "fit_schedule")})
     c = H.ctx(sensor_, **_gparams(**kw))
     gbits, recs = H.encode_keyframe(c, pts)
     rng, _, _ = O.range_image(s, pts)
@@ -107,7 +107,6 @@ def _keyframe_case(sensor_, pts, **kw):
     if same_planes:
         assert obits.tobytes() == gbits.tobytes()
     err = _check_decode(c, s, gbits, rng, p.quant_m)
-    stats = c.lcc_last_stats(0) if False else None
     return dict(bytes=len(gbits), border=border, compared=compared, err=err, same_planes=same_planes, ctx=c,
                 recs=recs, bits=gbits)
 
@@ -173,6 +172,13 @@ def test_keyframe_parity_variants(cfg1, merge, fmin, R):
     _keyframe_case(sen, pts, merge=merge, fmin=fmin, R=R)
 
 
+@pytest.mark.parametrize("solver,schedule", [(0, 0), (1, 0), (0, 1), (1, 1)])
+def test_keyframe_parity_solvers_and_schedules(cfg2_seq, solver, schedule):
+    """Both plane solvers (float-float, FP64) and both fit schedules meet the parity contract."""
+    seq = cfg2_seq
+    _keyframe_case(seq.sensor, seq.frames[seq.key_index], solver=solver, fit_schedule=schedule)
+
+
 @pytest.mark.parametrize("tile", [(4, 4), (8, 16)])
 def test_keyframe_parity_ragged_sensor(tile):
     sen = synth.Sensor(18, 515, -15.0, 15.0, 80.0)   # partial edge tiles in both directions
@@ -209,11 +215,11 @@ def test_schedule_invariance_and_determinism(cfg1):
 
 # ------------------------------------------------------------------- P frames --
 
-def _pframe_case(seq, frames, tile=(4, 4), thr=0.05, poses=None):
+def _pframe_case(seq, frames, tile=(4, 4), thr=0.05, poses=None, schedule=0):
     from paper_2008_06972_gb300 import lcc
     s = O.sensor(seq.sensor)
     p = _oparams(tile=tile, thr=thr)
-    c = H.ctx(seq.sensor, **_gparams(tile=tile, thr=thr, max_batch=max(16, len(frames))))
+    c = H.ctx(seq.sensor, **_gparams(tile=tile, thr=thr, max_batch=max(16, len(frames)), fit_schedule=schedule))
     kf = lcc.Keyframe(c)
     kbits, krecs = H.encode_keyframe(c, seq.frames[seq.key_index], kf)
     okft = O.kf_table_from_stream(s, kbits, c.num_tiles)
@@ -271,6 +277,11 @@ def test_pframe_parity_cfg2(cfg2_seq):
 def test_pframe_parity_tiles(cfg2_seq, tile, thr):
     seq = cfg2_seq
     _pframe_case(seq, [0, seq.key_index + 1], tile=tile, thr=thr)
+
+
+def test_pframe_parity_queued_schedule(cfg2_seq):
+    seq = cfg2_seq
+    _pframe_case(seq, [1, 7], schedule=1)
 
 
 def test_pframe_noisy_pose(cfg2_seq):
