@@ -1,18 +1,17 @@
-// Greedy horizontal run growth (Sec. III-C) — one warp per tile row.
+// Greedy horizontal run growth (Sec. III-C) — one block per tile row.
 //
 // The paper grows a run of tiles to the right while the plane "fit so far"
 // (the run's first plane) still codes the next tile under the threshold, and
-// restarts at the first tile that fails.  The walk is sequential along a row,
-// so each step is made warp-wide: the 32 lanes look at 32 consecutive tiles,
-// a ballot finds the first candidate run start, the precomputed look-behind
-// bits of the following tiles (from the fit stage) decide the first
-// `lookahead` joins,
-// and only runs longer than that test further tiles explicitly, 32 tiles per
-// step with one lane per tile.  Temporal tiles of P frames are already coded
-// (Sec. III-D) and end a run.
+// restarts at the first tile that fails.  The walk is inherently sequential
+// along a row, so everything around it is parallel: the followers'
+// look-behind bits (from the fit stage) decide the first `lookahead` joins of
+// a run in one ballot, and the walk itself is a pointer chase in shared
+// memory.  Temporal tiles of P frames are already coded (Sec. III-D) and end
+// a run.
 //
-// Output per tile: its stream mode, the tile whose plane codes it, and its
-// counts of candidate / plane-coded / raw-coded pixels.
+// Output per tile: its stream mode, the tile whose plane codes it, its counts
+// of candidate / plane-coded / raw-coded pixels and their offsets within the
+// tile row; per row: the totals.
 #include "lcc_internal.cuh"
 
 namespace lcc {
@@ -21,9 +20,10 @@ namespace lcc {
 // step costs shared-memory latency instead of a dependent L2 round trip.
 struct alignas(16) RowRec {
     float4 plane;
-    uint32_t amask;
-    uint8_t status, n_valid, n_inlier, pad;
-    uint32_t acnt[4];
+    uint32_t amask;          // look-behind bits: bit j = this tile passes the plane of tile c-1-j
+    uint8_t status, n_valid, n_inlier, rounds;
+    uint32_t acnt[4];        // look-behind inlier counts (byte j)
+    uint8_t flags, pad0, pad1, pad2;
 };
 
 __device__ __forceinline__ void put_code(TileCode *codes, int t, uint8_t mode, int cand, int fitted, int raw,
@@ -32,131 +32,262 @@ __device__ __forceinline__ void put_code(TileCode *codes, int t, uint8_t mode, i
     *reinterpret_cast<uint2 *>(codes + t) = make_uint2(w0, plane_tile);
 }
 
-// Code of a tile that is not part of a spatial run.
-__device__ __forceinline__ void put_plain(TileCode *codes, float4 *kfo, int t, const RowRec &h) {
-    if (h.status == S_TEMPORAL)
-        put_code(codes, t, T_TEMPORAL, h.n_valid, h.n_inlier, h.n_valid - h.n_inlier, (uint32_t)t);
-    else
-        put_code(codes, t, h.n_valid ? T_RAW : T_EMPTY, 0, 0, h.n_valid, (uint32_t)t);
-    if (kfo) kfo[t] = make_float4(0.f, 0.f, 0.f, 0.f);
+__device__ __forceinline__ uint32_t warp_incl_sum(uint32_t x, int lane) {
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, x, off);
+        if (lane >= off) x += y;
+    }
+    return x;
 }
 
-// One warp per tile row (one warp per block; the row lives in dynamic shared memory).
+constexpr int kMergeThreads = 128;
+
+// One block per tile row (the row lives in dynamic shared memory).  Stages:
+// (A) all threads stage the row's fit records; (B) the next fitted tile at or
+// after every position (suffix scan, warp 0) and, for every fitted tile, how
+// far its run would reach by the followers' look-behind bits (all threads);
+// (C) warp 0 walks the greedy chain: a run starts at the next fitted tile,
+// ends where its precomputed reach ends (explicit tests with one lane per
+// tile only past the look-behind horizon), and the walk resumes at the next
+// fitted tile after it; (D) all threads assign codes and counts, then a block
+// scan gives the intra-row stream offsets and the row totals.
 template <int TH_, int TW_>
-__global__ void __launch_bounds__(32) k_merge(Geometry g, Scratch s, Batch b) {
-    extern __shared__ RowRec row[];
+__global__ void __launch_bounds__(kMergeThreads) k_merge(Geometry g, Scratch s, Batch b) {
+    extern __shared__ __align__(16) uint8_t smem[];
+    const int TC = g.TC;
+    RowRec *row = reinterpret_cast<RowRec *>(smem);
+    uint16_t *nextfit = reinterpret_cast<uint16_t *>(row + TC);   // TC + 1 entries
+    uint16_t *runend = nextfit + (TC + 1);                         // end of the run started at c, 0 if none
+    uint16_t *reach = runend + TC;                                 // look-behind reach of a fitted tile
+    uint8_t *extcnt = reinterpret_cast<uint8_t *>(reach + TC);     // counts of explicitly tested joins
+    __shared__ uint32_t s_warp[kMergeThreads / 32][6];
+    __shared__ uint32_t s_carry[6];
     const unsigned FULL = 0xffffffffu;
-    const int lane = threadIdx.x;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int f = blockIdx.y;
     const int tr = blockIdx.x;
     const size_t slot = (size_t)b.slot[f];
     const TileRec *recs = s.tiles + slot * g.NT;
     TileCode *codes = s.codes + slot * g.NT;
+    TileOff *offs = s.offs + slot * g.NT;
     const uint32_t *rimg = s.rimg + slot * g.H * g.W;
     float4 *kfo = (b.kind == 0) ? b.kf_out : nullptr;
-    const int row0 = tr * g.TC;
+    const int row0 = tr * TC;
+    const int hzmax = g.merge ? g.lookahead : 0;
 
-    // stage the row's records (coalesced 16-byte loads)
-    for (int c = lane; c < g.TC; c += 32) {
+    // (A) stage the row's records (coalesced 16-byte loads)
+    for (int c = tid; c < TC; c += kMergeThreads) {
         const uint4 *src = reinterpret_cast<const uint4 *>(recs + row0 + c);
         const uint4 q0 = src[0], q2 = src[2], q3 = src[3];
         RowRec h;
         h.plane = make_float4(__uint_as_float(q0.x), __uint_as_float(q0.y), __uint_as_float(q0.z), __uint_as_float(q0.w));
         h.amask = q2.y;
         h.status = (uint8_t)(q2.z & 0xff);
+        h.rounds = (uint8_t)((q2.z >> 8) & 0xff);
+        h.flags = (uint8_t)((q2.z >> 16) & 0xff);
         h.n_valid = (uint8_t)(q2.z >> 24);
         h.n_inlier = (uint8_t)(q2.w & 0xff);
-        h.pad = 0;
+        h.pad0 = h.pad1 = h.pad2 = 0;
         h.acnt[0] = q3.x; h.acnt[1] = q3.y; h.acnt[2] = q3.z; h.acnt[3] = q3.w;
         row[c] = h;
+        runend[c] = 0;
+        extcnt[c] = 0;
     }
-    __syncwarp();
-
-    int j = 0;
-    while (j < g.TC) {
-        const int c = j + lane;
-        const bool inrow = c < g.TC;
-        const uint8_t st = inrow ? row[c].status : (uint8_t)S_EMPTY;
-        const uint32_t fitb = __ballot_sync(FULL, inrow && st == S_FIT);
-        const int first = fitb ? __ffs(fitb) - 1 : 32;
-        if (inrow && lane < first) put_plain(codes, kfo, row0 + c, row[c]);
-        if (!fitb) {
-            j += 32;
-            continue;
-        }
-        const int s0 = j + first;
-        const RowRec &start = row[s0];
-        const float4 pl = start.plane;
-        if (lane == first) {
-            put_code(codes, row0 + s0, T_RUN_START, start.n_valid, start.n_inlier, start.n_valid - start.n_inlier,
-                     (uint32_t)(row0 + s0));
-            if (kfo) kfo[row0 + s0] = pl;
-        }
-        int k = s0 + 1;
-        bool open = g.merge && k < g.TC;
-        // phase 1: joins decided by the precomputed look-behind bits
-        const int hz = g.merge ? min(g.lookahead, g.TC - 1 - s0) : 0;
-        if (hz > 0) {
-            const int c1 = s0 + 1 + lane;
-            bool pass = false;
-            int cnt = 0, nv1 = 0;
-            if (lane < hz) {
-                // tile c1's look-behind bit `lane` refers to the plane of tile c1-1-lane = s0
-                const RowRec &h1 = row[c1];
-                pass = ((h1.amask >> lane) & 1u) && h1.status != S_TEMPORAL;
-                cnt = (h1.acnt[lane >> 2] >> (8 * (lane & 3))) & 0xff;
-                nv1 = h1.n_valid;
+    if (tid < 6) s_carry[tid] = 0;
+    __syncthreads();
+    // (B) reach of every fitted tile; next fitted tile at or after c
+    for (int c = tid; c < TC; c += kMergeThreads) {
+        int k = c + 1;
+        if (row[c].status == S_FIT) {
+            const int hz = min(hzmax, TC - 1 - c);
+            for (int j = 0; j < hz; j++) {
+                const RowRec &h1 = row[c + 1 + j];
+                if (!((h1.amask >> j) & 1u) || h1.status == S_TEMPORAL) break;
+                k++;
             }
-            const uint32_t failb = __ballot_sync(FULL, lane < hz && !pass);
-            const int nj = failb ? __ffs(failb) - 1 : hz;
-            if (lane < nj) {
-                put_code(codes, row0 + c1, T_RUN_CONT, nv1, cnt, nv1 - cnt, (uint32_t)(row0 + s0));
-                if (kfo) kfo[row0 + c1] = pl;
-            }
-            k = s0 + 1 + nj;
-            open = (failb == 0) && k < g.TC;
         }
-        // phase 2: explicit tests, one tile per lane, 32 tiles per step
-        while (open) {
-            const int c2 = k + lane;
-            bool pass = false;
-            int nvv = 0, nin = 0;
-            if (c2 < g.TC && row[c2].status != S_TEMPORAL) {
-                for (int q = 0; q < TH_ * TW_; q++) {
-                    const int i = tr * TH_ + q / TW_, jj = c2 * TW_ + q % TW_;
-                    if (i >= g.H || jj >= g.W) continue;
-                    const uint32_t bits = __ldg(rimg + (size_t)i * g.W + jj);
-                    if (!bits_valid(bits)) continue;
-                    nvv++;
-                    float ux, uy, uz, e;
-                    beam(g, i, jj, ux, uy, uz);
-                    nin += residual(pl, ux, uy, uz, __uint_as_float(bits), g.thr, e) ? 1 : 0;
+        reach[c] = (uint16_t)k;
+    }
+    if (warp == 0) {
+        uint32_t carry = (uint32_t)TC;
+        if (lane == 0) nextfit[TC] = (uint16_t)TC;
+        for (int base = ((TC - 1) / 32) * 32; base >= 0; base -= 32) {
+            const int c = base + lane;
+            uint32_t v = (c < TC && row[c].status == S_FIT) ? (uint32_t)c : 0xFFFFu;
+#pragma unroll
+            for (int off = 1; off < 32; off <<= 1) {
+                const uint32_t y = __shfl_down_sync(FULL, v, off);
+                if (lane + off < 32) v = min(v, y);
+            }
+            v = min(v, carry);
+            if (c < TC) nextfit[c] = (uint16_t)v;
+            carry = __shfl_sync(FULL, v, 0);
+        }
+    }
+    __syncthreads();
+    // (C) the greedy walk (warp 0)
+    if (warp == 0) {
+        int st = nextfit[0];
+        while (st < TC) {
+            int k = reach[st];
+            // every pre-tested follower joined and the row goes on: test further tiles explicitly
+            bool open = g.merge && k < TC && k - st - 1 >= hzmax;
+            if (open) {
+                const float4 pl = row[st].plane;
+                while (open) {
+                    const int c2 = k + lane;
+                    bool pass = false;
+                    int nvv = 0, nin = 0;
+                    if (c2 < TC && row[c2].status != S_TEMPORAL) {
+                        uint32_t bits[TH_ * TW_];
+#pragma unroll
+                        for (int q = 0; q < TH_ * TW_; q++) {
+                            const int i = tr * TH_ + q / TW_, jj = c2 * TW_ + q % TW_;
+                            bits[q] = (i < g.H && jj < g.W) ? __ldg(rimg + (size_t)i * g.W + jj) : kEmptyBits;
+                        }
+#pragma unroll 4
+                        for (int q = 0; q < TH_ * TW_; q++) {
+                            if (!bits_valid(bits[q])) continue;
+                            nvv++;
+                            float ux, uy, uz, e;
+                            beam(g, tr * TH_ + q / TW_, c2 * TW_ + q % TW_, ux, uy, uz);
+                            nin += residual(pl, ux, uy, uz, __uint_as_float(bits[q]), g.thr, e) ? 1 : 0;
+                        }
+                        pass = nvv >= 3 && nin >= need_inliers(g.fmin, nvv);
+                    }
+                    const uint32_t failb = __ballot_sync(FULL, !pass);
+                    const int nj = failb ? __ffs(failb) - 1 : 32;
+                    if (lane < nj) extcnt[c2] = (uint8_t)nin;
+                    k += nj;
+                    open = (failb == 0) && k < TC;
                 }
-                pass = nvv >= 3 && nin >= need_inliers(g.fmin, nvv);
             }
-            const uint32_t failb = __ballot_sync(FULL, !pass);
-            const int nj = failb ? __ffs(failb) - 1 : 32;
-            if (lane < nj) {
-                put_code(codes, row0 + c2, T_RUN_CONT, nvv, nin, nvv - nin, (uint32_t)(row0 + s0));
-                if (kfo) kfo[row0 + c2] = pl;
-            }
-            k += nj;
-            open = (failb == 0) && k < g.TC;
+            if (lane == 0) runend[st] = (uint16_t)k;
+            st = k < TC ? nextfit[k] : TC;
         }
-        j = k;
     }
+    __syncthreads();
+    // (D) codes, counts and intra-row offsets (block scan in chunks of the block size)
+    uint32_t hist[5] = {0u, 0u, 0u, 0u, 0u}, rhist[8] = {0u, 0u, 0u, 0u, 0u, 0u, 0u, 0u}, border = 0;
+    __shared__ int s_wmax[kMergeThreads / 32];
+    __shared__ int s_last;
+    if (tid == 0) s_last = -1;
+    __syncthreads();
+    for (int base = 0; base < TC; base += kMergeThreads) {
+        const int c = base + tid;
+        uint32_t v[6] = {0u, 0u, 0u, 0u, 0u, 0u};   // cand, fitted, raw, run, temporal, valid
+        // the run covering c (if any) starts at the last run start at or before c:
+        // block-wide inclusive max-scan of the start positions, carried across chunks
+        const bool isstart = c < TC && runend[c] != 0;
+        int stc = isstart ? c : -1;
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+            const int y = __shfl_up_sync(FULL, stc, off);
+            if (lane >= off) stc = max(stc, y);
+        }
+        if (lane == 31) s_wmax[warp] = stc;
+        __syncthreads();
+        int pre = s_last;
+        for (int w = 0; w < warp; w++) pre = max(pre, s_wmax[w]);
+        stc = max(stc, pre);
+        if (c < TC) {
+            const RowRec &h = row[c];
+            if (!isstart && (stc < 0 || c >= (int)runend[stc])) stc = -1;
+            uint32_t cand = 0, fit = 0, raw = 0, ptile = (uint32_t)(row0 + c);
+            uint8_t mode;
+            if (isstart) {
+                mode = T_RUN_START;
+                cand = h.n_valid;
+                fit = h.n_inlier;
+            } else if (stc >= 0) {
+                mode = T_RUN_CONT;
+                const int j = c - stc - 1;
+                cand = h.n_valid;
+                fit = j < hzmax ? (h.acnt[j >> 2] >> (8 * (j & 3))) & 0xffu : extcnt[c];
+                ptile = (uint32_t)(row0 + stc);
+            } else if (h.status == S_TEMPORAL) {
+                mode = T_TEMPORAL;
+                cand = h.n_valid;
+                fit = h.n_inlier;
+            } else {
+                mode = h.n_valid ? T_RAW : T_EMPTY;
+                raw = h.n_valid;
+            }
+            if (mode >= T_RUN_START) raw = cand - fit;
+            put_code(codes, row0 + c, mode, (int)cand, (int)fit, (int)raw, ptile);
+            if (kfo) kfo[row0 + c] = (mode == T_RUN_START || mode == T_RUN_CONT) ? row[stc].plane
+                                                                                : make_float4(0.f, 0.f, 0.f, 0.f);
+            v[0] = cand; v[1] = fit; v[2] = raw; v[3] = isstart; v[4] = mode == T_TEMPORAL; v[5] = h.n_valid;
+            hist[mode]++;
+            rhist[min((uint32_t)h.rounds, 7u)]++;
+            border += h.flags & 1u;
+        }
+        uint32_t inc[6];
+#pragma unroll
+        for (int q = 0; q < 6; q++) inc[q] = warp_incl_sum(v[q], lane);
+        if (lane == 31)
+#pragma unroll
+            for (int q = 0; q < 6; q++) s_warp[warp][q] = inc[q];
+        __syncthreads();
+        uint32_t wb[6] = {0u, 0u, 0u, 0u, 0u, 0u};
+        for (int w = 0; w < warp; w++)
+#pragma unroll
+            for (int q = 0; q < 6; q++) wb[q] += s_warp[w][q];
+        if (c < TC) {
+            uint4 *dst = reinterpret_cast<uint4 *>(offs + row0 + c);
+            dst[0] = make_uint4(s_carry[0] + wb[0] + inc[0] - v[0], s_carry[1] + wb[1] + inc[1] - v[1],
+                                s_carry[2] + wb[2] + inc[2] - v[2], s_carry[3] + wb[3] + inc[3] - v[3]);
+            dst[1] = make_uint4(s_carry[4] + wb[4] + inc[4] - v[4], 0u, 0u, 0u);
+        }
+        __syncthreads();
+        if (tid < 6) {
+            uint32_t t6 = 0;
+            for (int w = 0; w < kMergeThreads / 32; w++) t6 += s_warp[w][tid];
+            s_carry[tid] += t6;
+        }
+        if (tid == kMergeThreads - 1) {
+            int m = s_last;
+            for (int w = 0; w < kMergeThreads / 32; w++) m = max(m, s_wmax[w]);
+            s_last = m;
+        }
+        __syncthreads();
+    }
+    uint32_t *tot = s.rowtot + (slot * g.TR + tr) * 8;
+    if (tid < 6) tot[tid] = s_carry[tid];
+    // tile statistics (A11): warp reductions, one atomic per counter and warp
+#pragma unroll
+    for (int off = 16; off; off >>= 1) {
+#pragma unroll
+        for (int q = 0; q < 5; q++) hist[q] += __shfl_xor_sync(FULL, hist[q], off);
+#pragma unroll
+        for (int q = 0; q < 8; q++) rhist[q] += __shfl_xor_sync(FULL, rhist[q], off);
+        border += __shfl_xor_sync(FULL, border, off);
+    }
+    if (lane == 0) {
+        DevStats *stt = s.stats + slot;
+        for (int q = 0; q < 5; q++)
+            if (hist[q]) atomicAdd(&(&stt->empty)[q], (unsigned long long)hist[q]);
+        for (int q = 0; q < 8; q++)
+            if (rhist[q]) atomicAdd(&stt->rounds[q], (unsigned long long)rhist[q]);
+        if (border) atomicAdd(&stt->borderline, (unsigned long long)border);
+    }
+}
+
+size_t merge_smem_bytes(int TC) {
+    return sizeof(RowRec) * (size_t)TC + 2 * (size_t)(TC + 1) + 4 * (size_t)TC + (size_t)TC + 16;
 }
 
 template <int TH_, int TW_>
 static cudaError_t launch_merge_t(const Geometry &g, const Scratch &s, const Batch &b, cudaStream_t st) {
-    const size_t smem = sizeof(RowRec) * (size_t)g.TC;
+    const size_t smem = merge_smem_bytes(g.TC);
     if (smem > 48 * 1024) {
         const cudaError_t e = cudaFuncSetAttribute(k_merge<TH_, TW_>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                    (int)smem);
         if (e != cudaSuccess) return e;
     }
     dim3 grid(g.TR, b.nframes);
-    k_merge<TH_, TW_><<<grid, 32, smem, st>>>(g, s, b);
+    k_merge<TH_, TW_><<<grid, kMergeThreads, smem, st>>>(g, s, b);
     return cudaGetLastError();
 }
 

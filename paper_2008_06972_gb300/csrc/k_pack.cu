@@ -91,7 +91,9 @@ __global__ void __launch_bounds__(kPackWarps * 32) k_pack(Geometry g, Scratch s,
         plane_tile = c.y < (uint32_t)g.NT ? c.y : 0u;
         const uint4 o0 = *reinterpret_cast<const uint4 *>(s.offs + slot * g.NT + t);
         const uint4 o1 = *(reinterpret_cast<const uint4 *>(s.offs + slot * g.NT + t) + 1);
-        off.cand = o0.x; off.fitted = o0.y; off.raw = o0.z; off.run = o0.w; off.temporal = o1.x;
+        const uint32_t *rb = s.rowbase + (slot * g.TR + tr) * 8;   // the tile row's base offsets
+        off.cand = o0.x + rb[0]; off.fitted = o0.y + rb[1]; off.raw = o0.z + rb[2]; off.run = o0.w + rb[3];
+        off.temporal = o1.x + rb[4];
         if (mode >= T_RUN_START) pl = recs[plane_tile].plane;
     }
     const bool coded = mode >= T_RUN_START;

@@ -1,71 +1,38 @@
-// Stream layout of one frame: exclusive prefix sums of the per-tile counts
-// (candidates, plane-coded pixels, raw pixels, run starts, temporal tiles)
-// give every tile its position in each stream section; the totals give the
-// section offsets, the header and the capacity check.  One CTA per frame; the
-// CTA then zeroes the frame's output words so the packer can OR bits in.
+// Stream layout of one frame (one CTA per frame).
 #include "lcc_internal.cuh"
 
 namespace lcc {
 
-constexpr int kScanThreads = 1024;
+constexpr int kScanThreads = 512;
 constexpr int kScanVals = 6;
 
 __device__ __forceinline__ uint32_t words_for(uint64_t bits) { return (uint32_t)((bits + 31) >> 5); }
 
+// Per frame: exclusive prefix of the tile-row totals (cand, fitted, raw, run
+// starts, temporal tiles, valid pixels) gives every row its base offset in
+// each section; the frame totals give the section layout, the header and the
+// capacity check.  The CTA then zeroes the frame's output words so the packer
+// can OR bits in.
 __global__ void __launch_bounds__(kScanThreads) k_scan(Geometry g, Scratch s, Batch b) {
     const int f = blockIdx.x;
     const size_t slot = (size_t)b.slot[f];
-    const TileCode *codes = s.codes + slot * g.NT;
-    const TileRec *recs = s.tiles + slot * g.NT;
-    TileOff *offs = s.offs + slot * g.NT;
+    const uint32_t *rowtot = s.rowtot + slot * g.TR * 8;
+    uint32_t *rowbase = s.rowbase + slot * g.TR * 8;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    constexpr int NW = kScanThreads / 32;
 
-    __shared__ uint32_t s_warp[32][kScanVals];
+    __shared__ uint32_t s_warp[NW][kScanVals];
     __shared__ uint32_t s_carry[kScanVals];
-    __shared__ unsigned int s_hist[16];
     __shared__ uint32_t s_ok, s_total;
     if (tid < kScanVals) s_carry[tid] = 0;
-    if (tid < 16) s_hist[tid] = 0;
     __syncthreads();
 
-    for (int base = 0; base < g.NT; base += kScanThreads) {
-        const int t = base + tid;
+    for (int base = 0; base < g.TR; base += kScanThreads) {
+        const int r = base + tid;
         uint32_t v[kScanVals] = {0, 0, 0, 0, 0, 0};
-        uint8_t mode = T_EMPTY;
-        if (t < g.NT) {
-            const uint2 c = *reinterpret_cast<const uint2 *>(codes + t);
-            mode = (uint8_t)(c.x & 0xff);
-            const uint32_t cand = (c.x >> 8) & 0xff, fitted = (c.x >> 16) & 0xff, raw = c.x >> 24;
-            v[0] = cand;
-            v[1] = fitted;
-            v[2] = raw;
-            v[3] = mode == T_RUN_START;
-            v[4] = mode == T_TEMPORAL;
-            v[5] = mode >= T_RUN_START ? cand : raw;   // valid pixels
-        }
-        // histograms: one ballot per bin and warp, then one shared atomic per warp
-        {
-            uint32_t rounds = 0, flags = 0;
-            if (t < g.NT) {
-                const uint32_t w0 = *reinterpret_cast<const uint32_t *>(reinterpret_cast<const uint8_t *>(recs + t) + 40);
-                rounds = min((w0 >> 8) & 0xffu, 7u);
-                flags = (w0 >> 16) & 0xffu;
-            }
-            const bool in = t < g.NT;
+        if (r < g.TR)
 #pragma unroll
-            for (int q = 0; q < 5; q++) {
-                const uint32_t c = __popc(__ballot_sync(0xffffffffu, in && mode == q));
-                if (lane == 0 && c) atomicAdd(&s_hist[q], c);           // [0..4] tiles by mode
-            }
-#pragma unroll
-            for (int q = 0; q < 8; q++) {
-                const uint32_t c = __popc(__ballot_sync(0xffffffffu, in && rounds == (uint32_t)q));
-                if (lane == 0 && c) atomicAdd(&s_hist[5 + q], c);       // [5..12] fit rounds
-            }
-            const uint32_t c = __popc(__ballot_sync(0xffffffffu, in && (flags & 1u)));
-            if (lane == 0 && c) atomicAdd(&s_hist[13], c);              // borderline tiles
-        }
-        // warp inclusive scans
+            for (int q = 0; q < kScanVals; q++) v[q] = rowtot[r * 8 + q];
         uint32_t inc[kScanVals];
 #pragma unroll
         for (int q = 0; q < kScanVals; q++) {
@@ -84,27 +51,22 @@ __global__ void __launch_bounds__(kScanThreads) k_scan(Geometry g, Scratch s, Ba
         if (warp == 0) {
 #pragma unroll
             for (int q = 0; q < kScanVals; q++) {
-                uint32_t x = s_warp[lane][q];
+                uint32_t x = lane < NW ? s_warp[lane][q] : 0u;
 #pragma unroll
                 for (int off = 1; off < 32; off <<= 1) {
                     const uint32_t y = __shfl_up_sync(0xffffffffu, x, off);
                     if (lane >= off) x += y;
                 }
-                s_warp[lane][q] = x;  // inclusive over warps
+                if (lane < NW) s_warp[lane][q] = x;   // inclusive over warps
             }
         }
         __syncthreads();
-        if (t < g.NT) {
-            uint32_t o[kScanVals];
+        if (r < g.TR)
 #pragma unroll
             for (int q = 0; q < kScanVals; q++)
-                o[q] = s_carry[q] + (warp ? s_warp[warp - 1][q] : 0u) + inc[q] - v[q];
-            uint4 *dst = reinterpret_cast<uint4 *>(offs + t);
-            dst[0] = make_uint4(o[0], o[1], o[2], o[3]);
-            dst[1] = make_uint4(o[4], 0u, 0u, 0u);
-        }
+                rowbase[r * 8 + q] = s_carry[q] + (warp ? s_warp[warp - 1][q] : 0u) + inc[q] - v[q];
         __syncthreads();
-        if (tid < kScanVals) s_carry[tid] += s_warp[31][tid];
+        if (tid < kScanVals) s_carry[tid] += s_warp[NW - 1][tid];
         __syncthreads();
     }
 
@@ -153,13 +115,6 @@ __global__ void __launch_bounds__(kScanThreads) k_scan(Geometry g, Scratch s, Ba
         }
         DevStats *st = s.stats + slot;
         st->valid = valid;
-        st->empty = s_hist[T_EMPTY];
-        st->raw_tiles = s_hist[T_RAW];
-        st->run_start = s_hist[T_RUN_START];
-        st->run_cont = s_hist[T_RUN_CONT];
-        st->temporal = s_hist[T_TEMPORAL];
-        for (int q = 0; q < 8; q++) st->rounds[q] = s_hist[5 + q];
-        st->borderline = s_hist[13];
         st->cand = cand;
         st->fitted = fitted;
         st->raw = raw;

@@ -324,8 +324,8 @@ lcc_status lcc_create(lcc_ctx **out, const lcc_sensor *sensor, const lcc_params 
     g.elev_max_deg = (float)s.elev_max_deg;
     g.d_el_deg = (float)((s.elev_max_deg - s.elev_min_deg) / s.rows);
     g.d_az = (float)(2.0 * M_PI / s.cols);
-    // the run walker keeps one tile row (48 B per tile) in shared memory
-    if (g.w_res > 16 || g.w_raw > 24 || (size_t)g.TC * 48 > 200 * 1024) {
+    // the run walker keeps one tile row in shared memory
+    if (g.w_res > 16 || g.w_raw > 24 || merge_smem_bytes(g.TC) > 200 * 1024 || g.TC > 65535) {
         delete c;
         return LCC_ERR_UNSUPPORTED;
     }
@@ -357,7 +357,9 @@ lcc_status lcc_create(lcc_ctx **out, const lcc_sensor *sensor, const lcc_params 
     const size_t o_bytes = o_stats + align256(sl * sizeof(DevStats));
     const size_t o_err = o_bytes + align256(sl * 8);
     const size_t o_dec = o_err + 256;
-    const size_t o_queue = o_dec + align256((nt + 4) * sizeof(DecTile));
+    const size_t o_rowtot = o_dec + align256((nt + 4) * sizeof(DecTile));
+    const size_t o_rowbase = o_rowtot + align256(sl * (size_t)g.TR * 32);
+    const size_t o_queue = o_rowbase + align256(sl * (size_t)g.TR * 32);
     const size_t o_qcount = o_queue + align256(2 * sl * nt * 4);
     const size_t total = o_qcount + 256;
     if (cudaMalloc(&c->d_scratch, total) != cudaSuccess) {
@@ -375,6 +377,8 @@ lcc_status lcc_create(lcc_ctx **out, const lcc_sensor *sensor, const lcc_params 
     c->s.bytes = (unsigned long long *)(base + o_bytes);
     c->s.err = (uint32_t *)(base + o_err);
     c->d_dec = (DecTile *)(base + o_dec);
+    c->s.rowtot = (uint32_t *)(base + o_rowtot);
+    c->s.rowbase = (uint32_t *)(base + o_rowbase);
     c->s.queue = (uint32_t *)(base + o_queue);
     c->s.qcount = (uint32_t *)(base + o_qcount);
     c->s.qcap = (uint32_t)(sl * nt);

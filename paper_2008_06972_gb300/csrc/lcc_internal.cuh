@@ -48,7 +48,7 @@ struct TileCode {
     uint32_t plane_tile;  // tile whose plane codes this one (run start)
 };
 
-// Exclusive stream offsets of a tile (in codes) from the per-frame scan.
+// Exclusive stream offsets of a tile (in codes) within its tile row.
 struct TileOff {
     uint32_t cand, fitted, raw, run, temporal, pad0, pad1, pad2;
 };
@@ -103,6 +103,8 @@ struct Scratch {
     DevStats *stats;     // [slots]
     unsigned long long *bytes;  // [slots] stream size (or needed size)
     uint32_t *err;       // latched error bits
+    uint32_t *rowtot;    // [slots][TR][8] per tile-row totals: cand, fitted, raw, run, temporal, valid
+    uint32_t *rowbase;   // [slots][TR][8] exclusive prefix of rowtot over the frame's rows
     uint32_t *queue;     // [2][qcap] fit work queues (frame << 26 | tile)
     uint32_t *qcount;    // [8] items pushed per fit round
     uint32_t qcap;       // entries per queue (slots * tiles)
@@ -288,6 +290,7 @@ cudaError_t launch_range_image(const Geometry &g, const uint32_t *rimg, float *r
 cudaError_t launch_fit(const Geometry &g, const Scratch &s, const Batch &b, const Poses &p, cudaStream_t st);
 cudaError_t launch_fit_rounds(const Geometry &g, const Scratch &s, const Batch &b, cudaStream_t st);
 cudaError_t launch_merge(const Geometry &g, const Scratch &s, const Batch &b, cudaStream_t st);
+size_t merge_smem_bytes(int TC);
 cudaError_t launch_scan(const Geometry &g, const Scratch &s, const Batch &b, cudaStream_t st);
 cudaError_t launch_pack(const Geometry &g, const Scratch &s, const Batch &b, cudaStream_t st);
 cudaError_t launch_decode_prep(const Geometry &g, const uint8_t *bits, unsigned long long nbytes,
