@@ -58,7 +58,7 @@ typedef struct {
     float min_inlier_frac;    /* share of a tile's points a plane must keep (1.0 = all, the paper's rule) */
     int32_t merge_runs;       /* 1: grow runs of tiles horizontally with the run's plane (Sec. III-C) */
     int32_t max_batch;        /* frames per batched launch the context reserves scratch for (1..64) */
-    int32_t lookahead;        /* run pre-test span: tiles to the left each tile is tested against (0..16) */
+    int32_t lookahead;        /* run pre-test span: tiles to the left each tile is tested against (0..32) */
     int32_t solver;           /* 3x3 plane solve: 0 float-float on the FP32 pipes (default), 1 FP64 */
     int32_t fit_schedule;     /* 0: a thread runs all refit rounds of its tile; 1: tiles needing another
                                  round are queued and re-run in dense warps, one kernel per round */
@@ -92,7 +92,7 @@ typedef struct {
     uint8_t t_rounds;         /* temporal offset fits */
     uint8_t t_inlier;         /* inliers of the temporal plane */
     uint8_t t_status;         /* 0 no K plane, 1 failed, 2 passed */
-    uint8_t ahead_cnt[16];    /* inlier counts of those pre-tests */
+    uint8_t ahead_cnt[16];    /* inlier counts of the first 16 of those pre-tests */
 } lcc_tile_info;
 
 typedef struct lcc_ctx lcc_ctx;
@@ -102,7 +102,7 @@ typedef struct lcc_keyframe lcc_keyframe;
 const char *lcc_status_string(lcc_status s);
 
 /* Default parameters: 4x4 tiles, thr 0.05 m, q 0.02 m, 3 refits, f_min 0.75,
- * runs on, max_batch 16, lookahead 16, float-float solver. */
+ * runs on, max_batch 16, lookahead 16, float-float solver, per-thread fit rounds. */
 void lcc_default_params(lcc_params *p);
 
 /* Create a context on the current device bound to cuda_stream (a

@@ -313,13 +313,12 @@ struct TileView {
 #pragma unroll 2
         for (int k = 0; k < PX; k++) {
             if (!V.get(k)) continue;
-            float ux, uy, uz, e;
+            float ux, uy, uz;
             u(k, ux, uy, uz);
-            if (residual(pl, ux, uy, uz, r(k), g.thr, e)) {
+            if (inlier_screened(pl, ux, uy, uz, r(k), g.thr, border)) {
                 I.set(k);
                 cnt++;
             }
-            if (isfinite(e) && fabsf(fabsf(e) - g.thr) <= 1e-6f) border = true;
         }
         return cnt;
     }
@@ -550,15 +549,30 @@ __global__ void __launch_bounds__(kFitThreads) k_fit_round(Geometry g, Scratch s
 template <int TH_, int TW_>
 __global__ void __launch_bounds__(kFitThreads) k_lookbehind(Geometry g, Scratch s, Batch b) {
     using TV = TileView<TH_, TW_>;
+    constexpr int PX = TV::PX;
+    constexpr bool kRegs = PX <= 16;   // small tiles keep their points in registers
+    __shared__ __align__(16) uint8_t s_cnt[kFitThreads][32];
     const int f = blockIdx.y;
     const int t = blockIdx.x * kFitThreads + threadIdx.x;
     if (t >= g.NT) return;
     const uint32_t *rimg = s.rimg + (size_t)b.slot[f] * g.H * g.W;
     TileRec *recs = s.tiles + (size_t)b.slot[f] * g.NT;
     const TV tv(g, rimg, t);
-    uint32_t bmask = 0, bcnt[4] = {0u, 0u, 0u, 0u};
+    float pr[kRegs ? PX : 1], pux[kRegs ? PX : 1], puy[kRegs ? PX : 1], puz[kRegs ? PX : 1];
+    if (kRegs) {
+#pragma unroll
+        for (int k = 0; k < (kRegs ? PX : 1); k++) {
+            pr[k] = tv.r(k);
+            tv.u(k, pux[k], puy[k], puz[k]);
+        }
+    }
+    uint32_t bmask = 0;
+    uint32_t *cw = reinterpret_cast<uint32_t *>(s_cnt[threadIdx.x]);
+#pragma unroll
+    for (int q = 0; q < 8; q++) cw[q] = 0u;
     const int need = need_inliers(g.fmin, tv.nv);
     const int span = min(g.lookahead, tv.tc);
+    bool border = false;
     if (tv.nv >= 3) {
         for (int j = 0; j < span; j++) {
             const TileRec *src = recs + (t - 1 - j);
@@ -566,20 +580,31 @@ __global__ void __launch_bounds__(kFitThreads) k_lookbehind(Geometry g, Scratch 
             if ((w0 & 0xff) != S_FIT) continue;
             const float4 pl = src->plane;
             int nin = 0;
+            if (kRegs) {
+#pragma unroll
+                for (int k = 0; k < (kRegs ? PX : 1); k++)
+                    if (pr[k] > 0.0f) nin += inlier_screened(pl, pux[k], puy[k], puz[k], pr[k], g.thr, border) ? 1 : 0;
+            } else {
 #pragma unroll 2
-            for (int k = 0; k < TV::PX; k++) {
-                if (!tv.V.get(k)) continue;
-                float ux, uy, uz, e;
-                tv.u(k, ux, uy, uz);
-                nin += residual(pl, ux, uy, uz, tv.r(k), g.thr, e) ? 1 : 0;
+                for (int k = 0; k < PX; k++) {
+                    const float rr = tv.r(k);
+                    if (!(rr > 0.0f)) continue;
+                    float ux, uy, uz;
+                    tv.u(k, ux, uy, uz);
+                    nin += inlier_screened(pl, ux, uy, uz, rr, g.thr, border) ? 1 : 0;
+                }
             }
             if (nin >= need) bmask |= 1u << j;
-            bcnt[j >> 2] |= (uint32_t)nin << (8 * (j & 3));
+            s_cnt[threadIdx.x][j] = (uint8_t)nin;
         }
     }
     uint8_t *base = reinterpret_cast<uint8_t *>(recs + t);
     *reinterpret_cast<uint32_t *>(base + 36) = bmask;
-    *reinterpret_cast<uint4 *>(base + 48) = make_uint4(bcnt[0], bcnt[1], bcnt[2], bcnt[3]);
+    const uint4 c0 = make_uint4(cw[0], cw[1], cw[2], cw[3]), c1 = make_uint4(cw[4], cw[5], cw[6], cw[7]);
+    *reinterpret_cast<uint4 *>(base + 48) = c0;
+    uint4 *dst = reinterpret_cast<uint4 *>(s.lbcnt + ((size_t)b.slot[f] * g.NT + t) * 32);
+    dst[0] = c0;
+    dst[1] = c1;
 }
 
 template <int TH_, int TW_>

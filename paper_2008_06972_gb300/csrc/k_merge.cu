@@ -150,9 +150,10 @@ __global__ void __launch_bounds__(kMergeThreads) k_merge(Geometry g, Scratch s, 
                         for (int q = 0; q < TH_ * TW_; q++) {
                             if (!bits_valid(bits[q])) continue;
                             nvv++;
-                            float ux, uy, uz, e;
+                            float ux, uy, uz;
+                            bool border = false;
                             beam(g, tr * TH_ + q / TW_, c2 * TW_ + q % TW_, ux, uy, uz);
-                            nin += residual(pl, ux, uy, uz, __uint_as_float(bits[q]), g.thr, e) ? 1 : 0;
+                            nin += inlier_screened(pl, ux, uy, uz, __uint_as_float(bits[q]), g.thr, border) ? 1 : 0;
                         }
                         pass = nvv >= 3 && nin >= need_inliers(g.fmin, nvv);
                     }
@@ -204,7 +205,7 @@ __global__ void __launch_bounds__(kMergeThreads) k_merge(Geometry g, Scratch s, 
                 mode = T_RUN_CONT;
                 const int j = c - stc - 1;
                 cand = h.n_valid;
-                fit = j < hzmax ? (h.acnt[j >> 2] >> (8 * (j & 3))) & 0xffu : extcnt[c];
+                fit = j < hzmax ? (uint32_t)s.lbcnt[(slot * g.NT + row0 + c) * 32 + j] : extcnt[c];
                 ptile = (uint32_t)(row0 + stc);
             } else if (h.status == S_TEMPORAL) {
                 mode = T_TEMPORAL;

@@ -285,7 +285,7 @@ lcc_status lcc_create(lcc_ctx **out, const lcc_sensor *sensor, const lcc_params 
     if (!tile_supported(p.tile_h, p.tile_w)) return LCC_ERR_UNSUPPORTED;
     if (!(p.fit_thr_m >= 0) || !(p.quant_m > 0) || p.max_refits < 0 || p.max_refits > 6 ||
         !(p.min_inlier_frac >= 0) || p.max_batch < 1 || p.max_batch > kMaxBatch || p.lookahead < 0 ||
-        p.lookahead > 16 || p.solver < 0 || p.solver > 1 || p.fit_schedule < 0 ||
+        p.lookahead > 32 || p.solver < 0 || p.solver > 1 || p.fit_schedule < 0 ||
         p.fit_schedule > 1)
         return LCC_ERR_INVALID_ARG;
     int dev = 0;
@@ -357,7 +357,8 @@ lcc_status lcc_create(lcc_ctx **out, const lcc_sensor *sensor, const lcc_params 
     const size_t o_bytes = o_stats + align256(sl * sizeof(DevStats));
     const size_t o_err = o_bytes + align256(sl * 8);
     const size_t o_dec = o_err + 256;
-    const size_t o_rowtot = o_dec + align256((nt + 4) * sizeof(DecTile));
+    const size_t o_lbcnt = o_dec + align256((nt + 4) * sizeof(DecTile));
+    const size_t o_rowtot = o_lbcnt + align256(sl * nt * 32);
     const size_t o_rowbase = o_rowtot + align256(sl * (size_t)g.TR * 32);
     const size_t o_queue = o_rowbase + align256(sl * (size_t)g.TR * 32);
     const size_t o_qcount = o_queue + align256(2 * sl * nt * 4);
@@ -377,6 +378,7 @@ lcc_status lcc_create(lcc_ctx **out, const lcc_sensor *sensor, const lcc_params 
     c->s.bytes = (unsigned long long *)(base + o_bytes);
     c->s.err = (uint32_t *)(base + o_err);
     c->d_dec = (DecTile *)(base + o_dec);
+    c->s.lbcnt = (uint8_t *)(base + o_lbcnt);
     c->s.rowtot = (uint32_t *)(base + o_rowtot);
     c->s.rowbase = (uint32_t *)(base + o_rowbase);
     c->s.queue = (uint32_t *)(base + o_queue);

@@ -34,10 +34,10 @@ struct alignas(16) TileRec {
     float4 plane;        // own spatial plane (n, d) or (n', c') if temporal
     float4 tplane;       // temporal test plane
     uint32_t kref;       // K tile of the anchor, ~0u if none
-    uint32_t ahead_mask; // bit j: this tile passes the plane of tile t-1-j (run pre-test)
+    uint32_t ahead_mask; // bit j: this tile passes the plane of tile t-1-j (run pre-test, j < 32)
     uint8_t status, rounds, flags, n_valid;
     uint8_t n_inlier, t_rounds, t_inlier, t_status;
-    uint8_t ahead_cnt[16];  // inlier counts of those tests
+    uint8_t ahead_cnt[16];  // inlier counts of the first 16 of those tests
 };
 static_assert(sizeof(TileRec) == 64, "TileRec layout");
 static_assert(sizeof(TileRec) == sizeof(lcc_tile_info), "TileRec matches lcc_tile_info");
@@ -103,6 +103,7 @@ struct Scratch {
     DevStats *stats;     // [slots]
     unsigned long long *bytes;  // [slots] stream size (or needed size)
     uint32_t *err;       // latched error bits
+    uint8_t *lbcnt;      // [slots][NT][32] run pre-test inlier counts (byte j: vs the plane of tile t-1-j)
     uint32_t *rowtot;    // [slots][TR][8] per tile-row totals: cand, fitted, raw, run, temporal, valid
     uint32_t *rowbase;   // [slots][TR][8] exclusive prefix of rowtot over the frame's rows
     uint32_t *queue;     // [2][qcap] fit work queues (frame << 26 | tile)
@@ -153,6 +154,27 @@ __device__ __forceinline__ bool residual(const float4 &pl, float ux, float uy, f
     const float rhat = __fdiv_rn(pl.w, dot);
     e = __fsub_rn(r, rhat);
     return fabsf(e) <= thr;
+}
+
+// The same decision as residual() (|r - d/(n.u)| <= thr with an IEEE
+// division), reached without the division for all but the pixels near the
+// threshold: the quotient from the fast reciprocal is within 2 ulp of the
+// exact one, so when the approximate residual is farther than a safe margin
+// from thr the exact test cannot decide differently.  Pixels inside the margin
+// (which always includes |e| within 1e-6 m of thr) take the exact path.
+__device__ __forceinline__ bool inlier_screened(const float4 &pl, float ux, float uy, float uz, float r, float thr,
+                                                bool &border) {
+    const float dot = fmaf(pl.x, ux, fmaf(pl.y, uy, __fmul_rn(pl.z, uz)));
+    if (!(dot > 1e-3f)) return false;
+    const float rh = __fdividef(pl.w, dot);
+    const float ea = fabsf(__fsub_rn(r, rh));
+    const float margin = fmaxf(3.0e-6f * (fabsf(rh) + fabsf(r)), 2.0e-6f);
+    if (ea < thr - margin) return true;
+    if (ea > thr + margin) return false;
+    float e;
+    const bool in = residual(pl, ux, uy, uz, r, thr, e);
+    if (isfinite(e) && fabsf(fabsf(e) - thr) <= 1e-6f) border = true;
+    return in;
 }
 
 __device__ __forceinline__ int quant_res(float e, float q) {

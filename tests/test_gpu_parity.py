@@ -204,7 +204,7 @@ def test_empty_and_tiny_frames():
 def test_schedule_invariance_and_determinism(cfg1):
     sen, pts = cfg1
     ref = None
-    for la in (0, 1, 8, 16):
+    for la in (0, 1, 8, 16, 32):
         c = H.ctx(sen, lookahead=la)
         b1, _ = H.encode_keyframe(c, pts)
         b2, _ = H.encode_keyframe(c, pts)
