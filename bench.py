@@ -84,6 +84,38 @@ def oracle_sample(seq, th, tw, thr, seconds):
     return pts_per_seq * nseq / el / 1e6, nseq, el
 
 
+KERNEL_SOURCES = {"bin": "k_bin.cu", "fit": "k_fit.cu", "refit": "k_fit.cu", "merge": "k_merge.cu",
+                  "scan": "k_scan.cu", "pack": "k_pack.cu"}
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "dram_traffic_hdl64_sequence.txt")
+
+
+def source_digest(kernel: str) -> str:
+    """Digest of the sources a kernel is compiled from (its .cu plus the shared headers)."""
+    import hashlib
+    csrc = os.path.join(ROOT, "paper_2008_06972_gb300", "csrc")
+    h = hashlib.sha256()
+    for name in (KERNEL_SOURCES[kernel], "lcc_internal.cuh", "ffmath.cuh"):
+        with open(os.path.join(csrc, name), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def measured_traffic(kernel: str):
+    """DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum, averaged over one
+    step's launches) from the committed ncu summary, or None when the kernel's sources changed
+    after the counters were taken."""
+    if kernel not in KERNEL_SOURCES:
+        return None
+    try:
+        for line in open(TRAFFIC_FILE):
+            f = line.split()
+            if len(f) == 3 and f[0] == kernel and not line.startswith("#"):
+                return float(f[1]) if f[2] == source_digest(kernel) else None
+    except OSError:
+        pass
+    return None
+
+
 class Clocks:
     def __init__(self, path):
         self.path = path
@@ -277,11 +309,14 @@ def main():
     #   merge: 64 B per tile record read + 8 B per tile code written
     #   scan:  8 B per tile code read + 32 B per tile offset written + stream bytes zeroed
     #   pack:  4 B per pixel read + 4 B per pixel reset + stream bytes written
+    #   refit: 4 B per pixel (range image read) + 64 B per tile record read + 32 B per tile of
+    #          look-behind counts written (extra refit rounds, when scheduled, reuse the same data)
     npx = H * W
     nt = ctx.num_tiles
     per_step_units = {
         "bin": 20.0 * pts_step,
         "fit": n_frames * (4.0 * npx + 64.0 * nt),
+        "refit": n_frames * (4.0 * npx + 96.0 * nt),
         "merge": n_frames * (64.0 * nt + 8.0 * nt),
         "scan": n_frames * (8.0 * nt + 32.0 * nt) + total_bytes,
         "pack": n_frames * 8.0 * npx + total_bytes,
@@ -290,8 +325,11 @@ def main():
     alg_bytes = per_step_units.get(dname, 0.0) / max(launches_of.get(dname, 1.0), 1e-9)
     achieved = alg_bytes / (per_launch_ms * 1e-3) / 1e9
     path_bytes = 16.0 * pts_step + total_bytes
+    traffic = measured_traffic(dname) if (args.tile, args.thr, args.lookahead, args.schedule) == (
+        "4x4", 0.05, 16, 0) else None
     roof = {"bound": "hbm", "kernel": dname, "achieved": achieved, "peak": hbm, "unit": "GB/s",
-            "frac": achieved / hbm, "traffic": None, "peak_source": src,
+            "frac": achieved / hbm, "traffic": traffic, "alg_bytes_per_launch": alg_bytes,
+            "peak_source": src,
             "path": {"alg_bytes_per_step": path_bytes, "achieved": path_bytes / (ms_step * 1e-3) / 1e9,
                      "frac": path_bytes / (ms_step * 1e-3) / 1e9 / hbm}}
 
