@@ -196,6 +196,104 @@ lcc_status lcc_tile_records(lcc_ctx *ctx, int32_t frame, lcc_tile_info *h_out, i
 lcc_status lcc_set_profiling(lcc_ctx *ctx, int32_t enable);
 int32_t lcc_kernel_times(lcc_ctx *ctx, char names[][16], int64_t *launches, double *ms, int32_t cap);
 
+/* ---- Batched encode of many sequences, replayed as a CUDA graph ----
+ *
+ * The paper encodes one sequence at a time (Sec. III-C: frames are grouped,
+ * the middle frame of each group is the key frame K, the others are P frames
+ * coded against K's planes).  A plan applies that grouping to a whole table
+ * of sequences of possibly different sensors: every sequence is bound to one
+ * of up to 8 contexts (one per resolution / tile-shape class).  Per class,
+ * all key frames are encoded first, then all P frames, in chunks of the
+ * context's max_batch frames, each chunk one batched launch set.  With more
+ * than one class, each class runs on its own stream between a fork and a
+ * join, so the classes overlap on the GPU.
+ *
+ * Key-frame groups: group g of a sequence covers frames [g*I, min((g+1)*I, n))
+ * with I = key_interval; its key frame is the group's frame start + floor(len/2).
+ * poses[f] (4x4 row-major doubles) maps frame f into the coordinates of its
+ * group's key frame (p_K = R p + T, Eq. 6); the key frames' own entries are
+ * ignored.  Stream f of a sequence is bit-identical to what
+ * lcc_encode_sequence makes for that group (same params).
+ *
+ * Every context must have been created on the same stream.  The plan copies
+ * the descriptors (pointer arrays, counts, poses) at create/update time; the
+ * device buffers they point to must stay allocated while the plan is used.
+ * The plan owns, per class, one key-frame plane table per group.  While a
+ * plan call runs, its contexts must not be used by other calls. */
+typedef struct lcc_seq_desc {
+    int32_t ctx;              /* index into the plan's context array */
+    int32_t nframes;          /* >= 1 */
+    int32_t key_interval;     /* frames per key-frame group, >= 1 */
+    int32_t reserved;
+    const double *poses;      /* host, nframes x 16 */
+    const float *const *d_pts;/* host array of nframes device pointers to float4 (x, y, z, unused), 16-B aligned */
+    const int64_t *n;         /* host array: points per frame */
+    uint8_t *const *d_out;    /* host array of nframes device output buffers, 16-B aligned */
+    const uint64_t *cap;      /* host array: capacity of each output buffer (bytes) */
+    uint64_t *d_nbytes;       /* DEVICE array of nframes: stream size of each frame, written by the encode */
+} lcc_seq_desc;
+
+typedef struct lcc_plan lcc_plan;
+
+typedef struct lcc_plan_info {
+    int64_t frames, key_frames, points;
+    int64_t launches;         /* kernel launches of one encode (after the first encode or capture) */
+    int64_t graph_nodes;      /* nodes of the captured graph (0 before capture) */
+    int32_t classes, captured;
+} lcc_plan_info;
+
+/* Validates the table and allocates the key-frame plane tables (synchronous).
+ * LCC_ERR_INVALID_ARG: bad descriptor, contexts on different streams, a context listed twice. */
+lcc_status lcc_plan_create(lcc_plan **out, int32_t nctx, lcc_ctx *const *ctxs, int32_t nseq,
+                           const lcc_seq_desc *seqs);
+/* Replaces pointers, counts and poses; the structure (per sequence: ctx, nframes,
+ * key_interval) must be unchanged.  A captured plan is re-recorded and its
+ * executable graph updated in place. */
+lcc_status lcc_plan_update(lcc_plan *plan, int32_t nseq, const lcc_seq_desc *seqs);
+/* Enqueues one encode of the whole table (asynchronous, no graph). */
+lcc_status lcc_plan_encode(lcc_plan *plan);
+/* Records one encode of the table as a CUDA graph (nothing runs).  Not allowed while
+ * profiling is enabled on one of the contexts (LCC_ERR_INVALID_ARG). */
+lcc_status lcc_plan_capture(lcc_plan *plan);
+/* Launches the captured graph on the contexts' stream (asynchronous). */
+lcc_status lcc_plan_replay(lcc_plan *plan);
+/* Waits for the stream, then returns (and clears) the first error latched by any context. */
+lcc_status lcc_plan_sync(lcc_plan *plan);
+lcc_status lcc_plan_get_info(const lcc_plan *plan, lcc_plan_info *out);
+void lcc_plan_destroy(lcc_plan *plan);
+
+/* ---- Autotuner ----
+ *
+ * Not in the paper (its tile size is a fixed parameter).  Encodes a sample
+ * sequence (nframes <= 64 device frames, key frame key_index, poses as in
+ * lcc_encode_sequence) with every candidate of tile shape {4x4, 4x8, 8x8,
+ * 8x16} x run-test horizon {8, 16, 32} (only 0 when base->merge_runs is 0) x
+ * fit schedule {0, 1}, each on a context of its own, `reps` timed encodes per
+ * candidate (CUDA events on cuda_stream).  Every frame is then decoded and
+ * compared with its binned input: candidates whose max range error exceeds
+ * max_err_m are rejected.  Of the rest, those whose total stream size is at
+ * most (1 + bytes_slack) x the smallest are eligible, and the fastest of
+ * them is written to *best (base with tile_h, tile_w, lookahead and
+ * fit_schedule replaced).  results (cap entries, may be NULL when cap is 0)
+ * receives every candidate, *nresults their number.  Synchronous; allocates
+ * and frees its own buffers.  LCC_ERR_UNSUPPORTED when no candidate is
+ * eligible. */
+typedef struct lcc_tune_result {
+    int32_t tile_h, tile_w, lookahead, fit_schedule;
+    int32_t status;           /* LCC_OK, or why the candidate could not be measured */
+    int32_t chosen;           /* 1 for the candidate written to *best */
+    double ms;                /* mean device time of one encode of the sample */
+    double mpts_per_s;
+    uint64_t bytes;           /* total stream bytes of the sample */
+    float max_err_m;          /* max |decoded range - binned input range| over occupied pixels */
+    float reserved;
+} lcc_tune_result;
+
+lcc_status lcc_autotune(const lcc_sensor *sensor, const lcc_params *base, int32_t nframes, int32_t key_index,
+                        const double *poses, const float *const *d_pts, const int64_t *n, int32_t reps,
+                        float max_err_m, float bytes_slack, void *cuda_stream, lcc_tune_result *results,
+                        int32_t cap, int32_t *nresults, lcc_params *best);
+
 #ifdef __cplusplus
 }
 #endif

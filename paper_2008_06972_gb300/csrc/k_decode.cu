@@ -3,6 +3,8 @@
 // (Sec. III-C): r = d / (n.u) + k q for plane-coded pixels, r = m q for raw
 // ones, and the point is r * u.  A corrupt stream latches E_CORRUPT and leaves
 // the outputs unspecified; no read leaves the stream's declared sections.
+#include <algorithm>
+
 #include "lcc_internal.cuh"
 
 namespace lcc {
@@ -354,6 +356,25 @@ cudaError_t launch_decode_px(const Geometry &g, const uint8_t *bits, const DecTi
     if (g.th == 8 && g.tw == 8) return launch_px_t<8, 8>(g, bits, dt, range, xyz, err, st);
     if (g.th == 8 && g.tw == 16) return launch_px_t<8, 16>(g, bits, dt, range, xyz, err, st);
     return cudaErrorInvalidValue;
+}
+
+// Largest |a - b| over pixels occupied in either image; a pixel occupied in only one of them
+// counts as +inf.  Non-negative floats order like their bit patterns, so an unsigned atomicMax
+// on the bits is a float max.
+__global__ void __launch_bounds__(256) k_maxdiff(const float *a, const float *b, long long n, uint32_t *out) {
+    float m = 0.f;
+    for (long long i = blockIdx.x * 256ll + threadIdx.x; i < n; i += (long long)gridDim.x * 256) {
+        const float x = a[i], y = b[i];
+        if (x > 0.f || y > 0.f) m = fmaxf(m, (x > 0.f && y > 0.f) ? fabsf(x - y) : __int_as_float(0x7f800000));
+    }
+    for (int o = 16; o; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0 && m > 0.f) atomicMax(out, __float_as_uint(m));
+}
+
+cudaError_t launch_maxdiff(const float *a, const float *b, long long n, uint32_t *out, cudaStream_t st) {
+    const long long blocks = std::min<long long>((n + 255) / 256, 152 * 8);
+    if (blocks > 0) k_maxdiff<<<(unsigned)blocks, 256, 0, st>>>(a, b, n, out);
+    return cudaGetLastError();
 }
 
 }  // namespace lcc

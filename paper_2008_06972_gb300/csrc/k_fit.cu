@@ -504,7 +504,7 @@ __global__ void __launch_bounds__(kFitThreads) k_fit_first(Geometry g, Scratch s
     o.status = tv.nv == 0 ? S_EMPTY : S_FAIL;
     o.rounds = o.flags = o.n_inl = o.t_rounds = o.t_inl = o.t_status = 0;
     o.nv = (uint8_t)tv.nv;
-    if (b.kind == 1 && tv.nv > 0) temporal_test<TH_, TW_>(tv, ps.m[f], b.kf, o);
+    if (b.kind == 1 && tv.nv > 0 && b.kf[f]) temporal_test<TH_, TW_>(tv, ps.m[f], b.kf[f], o);
     bool queued = false;
     if (o.status != S_TEMPORAL && tv.nv >= 3) {
         if (!kQueue) {

@@ -72,7 +72,7 @@ __global__ void __launch_bounds__(kMergeThreads) k_merge(Geometry g, Scratch s, 
     TileCode *codes = s.codes + slot * g.NT;
     TileOff *offs = s.offs + slot * g.NT;
     const uint32_t *rimg = s.rimg + slot * g.H * g.W;
-    float4 *kfo = (b.kind == 0) ? b.kf_out : nullptr;
+    float4 *kfo = (b.kind == 0) ? b.kf_out[f] : nullptr;
     const int row0 = tr * TC;
     const int hzmax = g.merge ? g.lookahead : 0;
 

@@ -89,6 +89,7 @@ __global__ void __launch_bounds__(kScanThreads) k_scan(Geometry g, Scratch s, Ba
         L.pad = 0;
         s.layout[slot] = L;
         s.bytes[slot] = total;
+        if (b.nbytes_out[f]) *b.nbytes_out[f] = total;
         if (!L.ok) atomicOr(s.err, E_CAPACITY);
         s_ok = L.ok;
         s_total = L.total_bytes;

@@ -11,58 +11,14 @@
 #include <vector>
 
 #include "lcc.h"
-#include "lcc_internal.cuh"
+#include "lcc_ctx.cuh"
 
 using namespace lcc;
 
-namespace {
-
-struct ProfRec {
-    int name;
-    cudaEvent_t a, b;
-};
+namespace lcc {
+namespace api {
 
 const char *kKernelNames[] = {"bin", "fit", "merge", "scan", "pack", "decode_prep", "decode_px", "range_export", "refit"};
-constexpr int kNumKernels = 9;
-
-size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
-
-}  // namespace
-
-struct lcc_keyframe {
-    lcc_ctx *ctx;
-    float4 *planes;
-    int64_t nt;
-};
-
-struct lcc_ctx {
-    lcc_sensor sensor;
-    lcc_params prm;
-    cudaStream_t stream = nullptr;
-    Geometry g{};
-    Scratch s{};
-    void *d_tables = nullptr;
-    void *d_scratch = nullptr;
-    DecTile *d_dec = nullptr;
-    std::vector<float> h_tables;  // ce, se, ct, st, rbc, rbs, cbc, cbs
-    int slots = 0;
-    uint64_t max_bytes = 0;
-    int last_nframes = 0;
-    // profiling
-    bool prof = false;
-    std::vector<ProfRec> pending;
-    std::vector<cudaEvent_t> pool;
-    int64_t launches[kNumKernels] = {};
-    double ms[kNumKernels] = {};
-    // host-buffer staging
-    void *d_stage_pts = nullptr;
-    size_t stage_pts_cap = 0;
-    uint8_t *d_stage_out = nullptr;
-    size_t stage_out_cap = 0;
-    unsigned long long *d_stage_bytes = nullptr;
-};
-
-namespace {
 
 cudaEvent_t get_event(lcc_ctx *c) {
     if (!c->pool.empty()) {
@@ -101,19 +57,6 @@ void prof_collect(lcc_ctx *c) {
     c->pending.clear();
 }
 
-#define LCC_LAUNCH(ctx, id, call)                   \
-    do {                                            \
-        const int _pi = prof_begin(ctx, id);        \
-        const cudaError_t _e = (call);              \
-        prof_end(ctx, _pi);                         \
-        if (_e != cudaSuccess) return LCC_ERR_CUDA; \
-    } while (0)
-
-#define LCC_CUDA(call)                                   \
-    do {                                                 \
-        if ((call) != cudaSuccess) return LCC_ERR_CUDA;  \
-    } while (0)
-
 bool tile_supported(int th, int tw) {
     return (th == 4 && tw == 4) || (th == 4 && tw == 8) || (th == 8 && tw == 8) || (th == 8 && tw == 16);
 }
@@ -132,18 +75,12 @@ void make_tables(const lcc_sensor &s, std::vector<float> &t) {
         ce[i] = (float)std::cos(e);
         se[i] = (float)std::sin(e);
     }
-    for (int k = 0; k <= H; k++) {
-        const double e = (s.elev_max_deg - k * d_el) * deg;
-        rbc[k] = (float)std::cos(e);
-        rbs[k] = (float)std::sin(e);
-    }
+    for (int k = 0; k <= H; k++) row_boundary(s, k, rbc + k, rbs + k);
     for (int j = 0; j < W; j++) {
         const double a = -M_PI + (j + 0.5) * d_az;
         ct[j] = (float)std::cos(a);
         st[j] = (float)std::sin(a);
-        const double b = -M_PI + j * d_az;
-        cbc[j] = (float)std::cos(b);
-        cbs[j] = (float)std::sin(b);
+        col_boundary(s, j, cbc + j, cbs + j);
     }
 }
 
@@ -166,10 +103,9 @@ lcc_status latched(lcc_ctx *c) {
     return LCC_OK;
 }
 
-// One batched encode pass over frames that are already binned (slots 0..n-1
-// hold their range images): fit, merge, scan, pack.
 lcc_status encode_batch(lcc_ctx *c, int kind, int nframes, const int *slots, uint8_t *const *d_out,
-                        const uint64_t *cap, const double *poses, const lcc_keyframe *kf, lcc_keyframe *kf_out) {
+                        const uint64_t *cap, const double *poses, const float4 *const *kf, float4 *const *kf_out,
+                        unsigned long long *const *nbytes_out) {
     if (nframes <= 0) return LCC_OK;
     Batch b;
     memset(&b, 0, sizeof(b));
@@ -179,9 +115,10 @@ lcc_status encode_batch(lcc_ctx *c, int kind, int nframes, const int *slots, uin
         b.slot[f] = slots[f];
         b.out[f] = d_out[f];
         b.cap[f] = cap[f];
+        b.kf[f] = kf ? kf[f] : nullptr;
+        b.kf_out[f] = kf_out ? kf_out[f] : nullptr;
+        b.nbytes_out[f] = nbytes_out ? nbytes_out[f] : nullptr;
     }
-    b.kf = kf ? kf->planes : nullptr;
-    b.kf_out = kf_out ? kf_out->planes : nullptr;
     Poses p;
     memset(&p, 0, sizeof(p));
     if (poses)
@@ -194,7 +131,6 @@ lcc_status encode_batch(lcc_ctx *c, int kind, int nframes, const int *slots, uin
     return LCC_OK;
 }
 
-// Bin frames into slots[f] (stats of those slots are reset first).
 lcc_status bin_frames(lcc_ctx *c, int nframes, const int *slots, const float *const *d_pts, const int64_t *n) {
     Batch b;
     memset(&b, 0, sizeof(b));
@@ -207,7 +143,14 @@ lcc_status bin_frames(lcc_ctx *c, int nframes, const int *slots, const float *co
         b.n[f] = n[f];
         b.blk_prefix[f] = blocks;
         blocks += (n[f] + per_block - 1) / per_block;
-        LCC_CUDA(cudaMemsetAsync(c->s.stats + slots[f], 0, sizeof(DevStats), c->stream));
+    }
+    bool contiguous = true;
+    for (int f = 0; f < nframes; f++) contiguous = contiguous && slots[f] == slots[0] + f;
+    if (contiguous) {
+        LCC_CUDA(cudaMemsetAsync(c->s.stats + slots[0], 0, sizeof(DevStats) * nframes, c->stream));
+    } else {
+        for (int f = 0; f < nframes; f++)
+            LCC_CUDA(cudaMemsetAsync(c->s.stats + slots[f], 0, sizeof(DevStats), c->stream));
     }
     b.blk_prefix[nframes] = blocks;
     LCC_LAUNCH(c, 0, launch_bin(c->g, c->s, b, blocks, c->stream));
@@ -240,7 +183,10 @@ lcc_status check_frames(lcc_ctx *c, int nframes, const float *const *d_pts, cons
     return LCC_OK;
 }
 
-}  // namespace
+}  // namespace api
+}  // namespace lcc
+
+using namespace lcc::api;
 
 extern "C" {
 
@@ -472,7 +418,8 @@ lcc_status lcc_encode_keyframe(lcc_ctx *c, const float *d_pts, int64_t n, lcc_ke
     if (st != LCC_OK) return st;
     const int slot = 0;
     if ((st = bin_frames(c, 1, &slot, &d_pts, &n)) != LCC_OK) return st;
-    if ((st = encode_batch(c, 0, 1, &slot, &d_out, &cap, nullptr, nullptr, kf)) != LCC_OK) return st;
+    float4 *kfo = kf ? kf->planes : nullptr;
+    if ((st = encode_batch(c, 0, 1, &slot, &d_out, &cap, nullptr, nullptr, &kfo)) != LCC_OK) return st;
     c->last_nframes = 1;
     return copy_bytes(c, 1, &slot, out_bytes);
 }
@@ -484,9 +431,13 @@ lcc_status lcc_encode_pframes(lcc_ctx *c, const lcc_keyframe *kf, int32_t nframe
     lcc_status st = check_frames(c, nframes, d_pts, n, d_out, cap);
     if (st != LCC_OK) return st;
     int slots[kMaxBatch];
-    for (int f = 0; f < nframes; f++) slots[f] = f;
+    const float4 *kfi[kMaxBatch];
+    for (int f = 0; f < nframes; f++) {
+        slots[f] = f;
+        kfi[f] = kf->planes;
+    }
     if ((st = bin_frames(c, nframes, slots, d_pts, n)) != LCC_OK) return st;
-    if ((st = encode_batch(c, 1, nframes, slots, d_out, cap, poses, kf, nullptr)) != LCC_OK) return st;
+    if ((st = encode_batch(c, 1, nframes, slots, d_out, cap, poses, kfi, nullptr)) != LCC_OK) return st;
     c->last_nframes = nframes;
     return copy_bytes(c, nframes, slots, out_bytes);
 }
@@ -519,10 +470,12 @@ lcc_status lcc_encode_sequence(lcc_ctx *c, int32_t nframes, int32_t key_index, c
     const int kslot = key_index;
     uint8_t *kout = d_out[key_index];
     const uint64_t kcap = cap[key_index];
-    if ((st = encode_batch(c, 0, 1, &kslot, &kout, &kcap, nullptr, nullptr, k)) != LCC_OK) return st;
+    float4 *kfo = k->planes;
+    if ((st = encode_batch(c, 0, 1, &kslot, &kout, &kcap, nullptr, nullptr, &kfo)) != LCC_OK) return st;
     int pslots[kMaxBatch];
     uint8_t *pout[kMaxBatch];
     uint64_t pcap[kMaxBatch];
+    const float4 *kfi[kMaxBatch];
     std::vector<double> pposes;
     int np = 0;
     for (int f = 0; f < nframes; f++) {
@@ -530,10 +483,11 @@ lcc_status lcc_encode_sequence(lcc_ctx *c, int32_t nframes, int32_t key_index, c
         pslots[np] = f;
         pout[np] = d_out[f];
         pcap[np] = cap[f];
+        kfi[np] = k->planes;
         pposes.insert(pposes.end(), poses + 16 * f, poses + 16 * f + 16);
         np++;
     }
-    if ((st = encode_batch(c, 1, np, pslots, pout, pcap, pposes.data(), k, nullptr)) != LCC_OK) return st;
+    if ((st = encode_batch(c, 1, np, pslots, pout, pcap, pposes.data(), kfi, nullptr)) != LCC_OK) return st;
     c->last_nframes = nframes;
     return copy_bytes(c, nframes, slots, out_bytes);
 }

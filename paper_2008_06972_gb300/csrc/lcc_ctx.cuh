@@ -1,0 +1,96 @@
+// Host-side state of an lcc context shared by the translation units of the
+// C ABI (single-sequence calls in lcc_api.cu, the batch planner in
+// lcc_plan.cu).  Not part of the public interface.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <vector>
+
+#include "lcc.h"
+#include "lcc_internal.cuh"
+
+namespace lcc {
+namespace api {
+
+struct ProfRec {
+    int name;
+    cudaEvent_t a, b;
+};
+
+constexpr int kNumKernels = 9;
+extern const char *kKernelNames[];
+
+inline size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
+
+}  // namespace api
+}  // namespace lcc
+
+struct lcc_keyframe {
+    lcc_ctx *ctx;
+    float4 *planes;
+    int64_t nt;
+};
+
+struct lcc_ctx {
+    lcc_sensor sensor;
+    lcc_params prm;
+    cudaStream_t stream = nullptr;
+    lcc::Geometry g{};
+    lcc::Scratch s{};
+    void *d_tables = nullptr;
+    void *d_scratch = nullptr;
+    lcc::DecTile *d_dec = nullptr;
+    std::vector<float> h_tables;  // ce, se, ct, st, rbc, rbs, cbc, cbs
+    int slots = 0;
+    uint64_t max_bytes = 0;
+    int last_nframes = 0;
+    // profiling
+    bool prof = false;
+    std::vector<lcc::api::ProfRec> pending;
+    std::vector<cudaEvent_t> pool;
+    int64_t launches[lcc::api::kNumKernels] = {};
+    double ms[lcc::api::kNumKernels] = {};
+    // host-buffer staging
+    void *d_stage_pts = nullptr;
+    size_t stage_pts_cap = 0;
+    uint8_t *d_stage_out = nullptr;
+    size_t stage_out_cap = 0;
+    unsigned long long *d_stage_bytes = nullptr;
+};
+
+namespace lcc {
+namespace api {
+
+int prof_begin(lcc_ctx *c, int name);
+void prof_end(lcc_ctx *c, int idx);
+bool aligned16(const void *p);
+// Reads and clears the device error word (synchronous).
+lcc_status latched(lcc_ctx *c);
+// Bin frames d_pts[f] into slots[f] (their stats are reset first).
+lcc_status bin_frames(lcc_ctx *c, int nframes, const int *slots, const float *const *d_pts, const int64_t *n);
+// Fit, merge, scan and pack frames already binned into slots[f].  kf[f] (P frames) is the key-frame
+// plane table frame f is coded against; kf_out[f] (key frames) receives frame f's coding planes;
+// nbytes_out[f], when given, receives frame f's stream size in device memory.
+lcc_status encode_batch(lcc_ctx *c, int kind, int nframes, const int *slots, uint8_t *const *d_out,
+                        const uint64_t *cap, const double *poses, const float4 *const *kf, float4 *const *kf_out,
+                        unsigned long long *const *nbytes_out = nullptr);
+lcc_status check_frames(lcc_ctx *c, int nframes, const float *const *d_pts, const int64_t *n,
+                        uint8_t *const *d_out, const uint64_t *cap);
+
+}  // namespace api
+}  // namespace lcc
+
+#define LCC_LAUNCH(ctx, id, call)                                  \
+    do {                                                           \
+        const int _pi = lcc::api::prof_begin(ctx, id);             \
+        const cudaError_t _e = (call);                             \
+        lcc::api::prof_end(ctx, _pi);                              \
+        if (_e != cudaSuccess) return LCC_ERR_CUDA;                \
+    } while (0)
+
+#define LCC_CUDA(call)                                   \
+    do {                                                 \
+        if ((call) != cudaSuccess) return LCC_ERR_CUDA;  \
+    } while (0)

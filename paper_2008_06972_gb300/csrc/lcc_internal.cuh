@@ -11,9 +11,26 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <cmath>
+
 #include "lcc.h"
 
 namespace lcc {
+
+// Pixel-boundary directions of the grid of Sec. III-B, fp64 libm rounded to fp32 (host).
+// Row boundary k in 0..rows (k = 0 is the top edge); column boundary j in 0..cols-1 (j = 0
+// is azimuth -pi).
+inline void row_boundary(const lcc_sensor &s, int k, float *c, float *sn) {
+    const double d_el = (s.elev_max_deg - s.elev_min_deg) / s.rows;
+    const double e = (s.elev_max_deg - k * d_el) * (M_PI / 180.0);
+    *c = (float)cos(e);
+    *sn = (float)sin(e);
+}
+inline void col_boundary(const lcc_sensor &s, int j, float *c, float *sn) {
+    const double b = -M_PI + j * (2.0 * M_PI / s.cols);
+    *c = (float)cos(b);
+    *sn = (float)sin(b);
+}
 
 constexpr int kMaxBatch = 64;          // frames per batched launch
 constexpr uint32_t kEmptyBits = 0xFFFFFFFFu;  // range-image pixel with no point
@@ -121,8 +138,9 @@ struct Batch {
     uint8_t *out[kMaxBatch];
     unsigned long long cap[kMaxBatch];
     long long blk_prefix[kMaxBatch + 1];  // binning blocks before each frame
-    const float4 *kf;              // key-frame planes (P frames) or NULL
-    float4 *kf_out;                // key-frame plane table to fill (K frames) or NULL
+    const float4 *kf[kMaxBatch];   // per frame: key-frame planes (P frames) or NULL
+    float4 *kf_out[kMaxBatch];     // per frame: key-frame plane table to fill (K frames) or NULL
+    unsigned long long *nbytes_out[kMaxBatch];  // per frame: extra copy of the stream size, or NULL
 };
 
 struct Poses {
@@ -318,6 +336,7 @@ cudaError_t launch_pack(const Geometry &g, const Scratch &s, const Batch &b, cud
 cudaError_t launch_decode_prep(const Geometry &g, const uint8_t *bits, unsigned long long nbytes,
                                const float4 *kf, const double *pose, DecTile *dt, float4 *kf_out,
                                uint32_t *err, int expect_kind, const Poses *poses, cudaStream_t st);
+cudaError_t launch_maxdiff(const float *a, const float *b, long long n, uint32_t *out, cudaStream_t st);
 cudaError_t launch_decode_px(const Geometry &g, const uint8_t *bits, const DecTile *dt, float *range,
                              float4 *xyz, uint32_t *err, cudaStream_t st);
 

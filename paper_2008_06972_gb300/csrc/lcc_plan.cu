@@ -1,0 +1,327 @@
+// Batched encode of a table of sequences (lcc_plan_*): key-frame grouping,
+// chunking of frames into the contexts' slots, fork/join of resolution
+// classes onto side streams, and capture of the whole enqueue as one CUDA
+// graph that is replayed.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "lcc.h"
+#include "lcc_ctx.cuh"
+
+using namespace lcc;
+using namespace lcc::api;
+
+namespace {
+
+constexpr int kMaxPlanContexts = 8;
+
+// One frame of the table, in the order the planner enqueues it.
+struct PlanFrame {
+    int seq, frame;       // position in the caller's table
+    int table;            // key-frame plane table (index into the context's tables)
+    const float *pts;
+    int64_t n;
+    uint8_t *out;
+    uint64_t cap;
+    unsigned long long *nbytes;
+    double pose[16];
+};
+
+struct PlanClass {
+    lcc_ctx *ctx = nullptr;
+    cudaStream_t side = nullptr;     // side stream when the plan has several classes
+    cudaEvent_t done = nullptr;
+    float4 *tables = nullptr;        // ngroups x NT key-frame planes
+    int ngroups = 0;
+    std::vector<PlanFrame> keys, pframes;
+};
+
+}  // namespace
+
+struct lcc_plan {
+    cudaStream_t stream = nullptr;   // the stream every context was created on (replays run here)
+    cudaStream_t cap = nullptr;      // private stream the graph is recorded on (the legacy default
+                                     // stream cannot be captured)
+    cudaEvent_t fork = nullptr;
+    std::vector<PlanClass> cls;
+    std::vector<lcc_seq_desc> shape;  // nframes / key_interval / ctx per sequence (structure check)
+    int64_t frames = 0, key_frames = 0, points = 0;
+    int64_t launches = 0;            // kernel launches of one encode
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+};
+
+namespace {
+
+// Group g of a sequence covers frames [g*I, min((g+1)*I, nframes)); its key frame is the
+// group's middle frame start + floor(len/2) (Sec. III-C: K is the middle frame of the group).
+int key_of(int frame, int nframes, int interval, int *group) {
+    const int g = frame / interval, start = g * interval;
+    const int len = std::min(interval, nframes - start);
+    *group = g;
+    return start + len / 2;
+}
+
+// Builds the frame lists of every class from the sequence table; the plan is left untouched
+// unless the whole table is valid (and, for check_only, has the plan's group structure).
+lcc_status fill(lcc_plan *p, int32_t nseq, const lcc_seq_desc *seqs, bool check_only) {
+    const size_t ncls = p->cls.size();
+    std::vector<std::vector<PlanFrame>> keys_of(ncls), pfr_of(ncls);
+    std::vector<int> group_base(ncls, 0);
+    int64_t frames = 0, keys = 0, points = 0;
+    for (int s = 0; s < nseq; s++) {
+        const lcc_seq_desc &d = seqs[s];
+        if (d.ctx < 0 || d.ctx >= (int)p->cls.size() || d.nframes < 1 || d.key_interval < 1 || !d.poses ||
+            !d.d_pts || !d.n || !d.d_out || !d.cap || !d.d_nbytes)
+            return LCC_ERR_INVALID_ARG;
+        for (int f = 0; f < d.nframes; f++) {
+            if (d.n[f] < 0 || d.n[f] > (int64_t)1 << 31) return LCC_ERR_INVALID_ARG;
+            if (d.n[f] > 0 && (!d.d_pts[f] || !aligned16(d.d_pts[f]))) return LCC_ERR_INVALID_ARG;
+            if (!d.d_out[f] || !aligned16(d.d_out[f]) || d.cap[f] < (uint64_t)kHeaderBytes)
+                return LCC_ERR_INVALID_ARG;
+            int grp = 0;
+            const int k = key_of(f, d.nframes, d.key_interval, &grp);
+            PlanFrame pf;
+            pf.seq = s;
+            pf.frame = f;
+            pf.table = group_base[d.ctx] + grp;
+            pf.pts = d.d_pts[f];
+            pf.n = d.n[f];
+            pf.out = d.d_out[f];
+            pf.cap = d.cap[f];
+            pf.nbytes = reinterpret_cast<unsigned long long *>(d.d_nbytes + f);
+            memcpy(pf.pose, d.poses + 16 * (size_t)f, sizeof(pf.pose));
+            (k == f ? keys_of[d.ctx] : pfr_of[d.ctx]).push_back(pf);
+            keys += k == f;
+            points += d.n[f];
+            frames++;
+        }
+        group_base[d.ctx] += (d.nframes + d.key_interval - 1) / d.key_interval;
+    }
+    if (check_only)
+        for (size_t k = 0; k < ncls; k++)
+            if (group_base[k] != p->cls[k].ngroups) return LCC_ERR_INVALID_ARG;
+    for (size_t k = 0; k < ncls; k++) {
+        p->cls[k].ngroups = group_base[k];
+        p->cls[k].keys.swap(keys_of[k]);
+        p->cls[k].pframes.swap(pfr_of[k]);
+    }
+    p->frames = frames;
+    p->key_frames = keys;
+    p->points = points;
+    return LCC_OK;
+}
+
+// Enqueue one class: its key frames chunk by chunk, then its P frames, each chunk binned into
+// slots 0..m-1 of the class context and encoded as one batch.
+lcc_status enqueue_class(PlanClass &pc, int64_t *launches) {
+    lcc_ctx *c = pc.ctx;
+    const int NT = c->g.NT;
+    for (int kind = 0; kind < 2; kind++) {
+        const std::vector<PlanFrame> &list = kind == 0 ? pc.keys : pc.pframes;
+        for (size_t base = 0; base < list.size(); base += (size_t)c->slots) {
+            const int m = (int)std::min<size_t>((size_t)c->slots, list.size() - base);
+            int slots[kMaxBatch];
+            const float *pts[kMaxBatch];
+            int64_t n[kMaxBatch];
+            uint8_t *out[kMaxBatch];
+            uint64_t cap[kMaxBatch];
+            const float4 *kf[kMaxBatch];
+            float4 *kfo[kMaxBatch];
+            unsigned long long *nb[kMaxBatch];
+            std::vector<double> poses((size_t)m * 16);
+            for (int f = 0; f < m; f++) {
+                const PlanFrame &pf = list[base + f];
+                slots[f] = f;
+                pts[f] = pf.pts;
+                n[f] = pf.n;
+                out[f] = pf.out;
+                cap[f] = pf.cap;
+                float4 *tab = pc.tables + (size_t)pf.table * NT;
+                kf[f] = tab;
+                kfo[f] = tab;
+                nb[f] = pf.nbytes;
+                memcpy(poses.data() + 16 * (size_t)f, pf.pose, sizeof(pf.pose));
+            }
+            lcc_status st = bin_frames(c, m, slots, pts, n);
+            if (st != LCC_OK) return st;
+            st = encode_batch(c, kind, m, slots, out, cap, kind ? poses.data() : nullptr, kind ? kf : nullptr,
+                              kind ? nullptr : kfo, nb);
+            if (st != LCC_OK) return st;
+            c->last_nframes = m;
+            *launches += 1 + 4 + (c->g.lookahead > 0 ? 1 : 0) +
+                         (c->g.schedule == 1 ? c->g.R + (kind == 1 ? 1 : 0) : 0);
+        }
+    }
+    return LCC_OK;
+}
+
+// Every launch of the plan, ordered after earlier work on `main`.  With several classes each
+// class runs on its own side stream between a fork and a join event, so classes overlap on the
+// GPU.  The contexts' launches go to the chosen stream for the duration of the call.
+lcc_status enqueue(lcc_plan *p, cudaStream_t main) {
+    int64_t launches = 0;
+    const bool forked = p->cls.size() > 1;
+    if (forked) LCC_CUDA(cudaEventRecord(p->fork, main));
+    lcc_status st = LCC_OK;
+    for (auto &pc : p->cls) {
+        if (forked && cudaStreamWaitEvent(pc.side, p->fork, 0) != cudaSuccess) return LCC_ERR_CUDA;
+        pc.ctx->stream = forked ? pc.side : main;
+        st = enqueue_class(pc, &launches);
+        pc.ctx->stream = p->stream;
+        if (forked && (cudaEventRecord(pc.done, pc.side) != cudaSuccess ||
+                       cudaStreamWaitEvent(main, pc.done, 0) != cudaSuccess))
+            return LCC_ERR_CUDA;
+        if (st != LCC_OK) return st;
+    }
+    p->launches = launches;
+    return LCC_OK;
+}
+
+void release(lcc_plan *p) {
+    if (p->exec) cudaGraphExecDestroy(p->exec);
+    if (p->graph) cudaGraphDestroy(p->graph);
+    for (auto &pc : p->cls) {
+        if (pc.side) cudaStreamDestroy(pc.side);
+        if (pc.done) cudaEventDestroy(pc.done);
+        cudaFree(pc.tables);
+    }
+    if (p->fork) cudaEventDestroy(p->fork);
+    if (p->cap) cudaStreamDestroy(p->cap);
+    delete p;
+}
+
+}  // namespace
+
+extern "C" {
+
+lcc_status lcc_plan_create(lcc_plan **out, int32_t nctx, lcc_ctx *const *ctxs, int32_t nseq,
+                           const lcc_seq_desc *seqs) {
+    if (!out || !ctxs || !seqs || nctx < 1 || nctx > kMaxPlanContexts || nseq < 1) return LCC_ERR_INVALID_ARG;
+    *out = nullptr;
+    for (int k = 0; k < nctx; k++) {
+        if (!ctxs[k] || ctxs[k]->stream != ctxs[0]->stream) return LCC_ERR_INVALID_ARG;
+        for (int j = 0; j < k; j++)
+            if (ctxs[j] == ctxs[k]) return LCC_ERR_INVALID_ARG;
+    }
+    lcc_plan *p = new (std::nothrow) lcc_plan();
+    if (!p) return LCC_ERR_CUDA;
+    p->stream = ctxs[0]->stream;
+    p->cls.resize(nctx);
+    for (int k = 0; k < nctx; k++) p->cls[k].ctx = ctxs[k];
+    lcc_status st = fill(p, nseq, seqs, false);
+    if (st != LCC_OK) {
+        release(p);
+        return st;
+    }
+    p->shape.assign(seqs, seqs + nseq);
+    bool ok = cudaEventCreateWithFlags(&p->fork, cudaEventDisableTiming) == cudaSuccess &&
+              cudaStreamCreateWithFlags(&p->cap, cudaStreamNonBlocking) == cudaSuccess;
+    for (auto &pc : p->cls) {
+        ok = ok && cudaMalloc(&pc.tables, sizeof(float4) * (size_t)std::max(pc.ngroups, 1) * pc.ctx->g.NT) ==
+                       cudaSuccess;
+        ok = ok && cudaMemset(pc.tables, 0, sizeof(float4) * (size_t)std::max(pc.ngroups, 1) * pc.ctx->g.NT) ==
+                       cudaSuccess;
+        if (nctx > 1) {
+            ok = ok && cudaStreamCreateWithFlags(&pc.side, cudaStreamNonBlocking) == cudaSuccess;
+            ok = ok && cudaEventCreateWithFlags(&pc.done, cudaEventDisableTiming) == cudaSuccess;
+        }
+    }
+    if (!ok || cudaDeviceSynchronize() != cudaSuccess) {
+        release(p);
+        return LCC_ERR_CUDA;
+    }
+    *out = p;
+    return LCC_OK;
+}
+
+lcc_status lcc_plan_update(lcc_plan *p, int32_t nseq, const lcc_seq_desc *seqs) {
+    if (!p || !seqs || nseq != (int32_t)p->shape.size()) return LCC_ERR_INVALID_ARG;
+    for (int s = 0; s < nseq; s++)
+        if (seqs[s].ctx != p->shape[s].ctx || seqs[s].nframes != p->shape[s].nframes ||
+            seqs[s].key_interval != p->shape[s].key_interval)
+            return LCC_ERR_INVALID_ARG;
+    lcc_status st = fill(p, nseq, seqs, true);
+    if (st != LCC_OK) return st;
+    if (!p->exec) return LCC_OK;
+    // re-record with the new pointers, counts and poses and update the executable graph in place
+    return lcc_plan_capture(p);
+}
+
+lcc_status lcc_plan_encode(lcc_plan *p) {
+    if (!p) return LCC_ERR_INVALID_ARG;
+    return enqueue(p, p->stream);
+}
+
+lcc_status lcc_plan_capture(lcc_plan *p) {
+    if (!p) return LCC_ERR_INVALID_ARG;
+    for (auto &pc : p->cls)
+        if (pc.ctx->prof) return LCC_ERR_INVALID_ARG;  // profiling events cannot be collected from a graph
+    LCC_CUDA(cudaStreamBeginCapture(p->cap, cudaStreamCaptureModeThreadLocal));
+    const lcc_status st = enqueue(p, p->cap);
+    cudaGraph_t g = nullptr;
+    const cudaError_t e = cudaStreamEndCapture(p->cap, &g);
+    if (st != LCC_OK || e != cudaSuccess) {
+        if (g) cudaGraphDestroy(g);
+        return st != LCC_OK ? st : LCC_ERR_CUDA;
+    }
+    if (p->exec) {
+        cudaGraphExecUpdateResultInfo info;
+        if (cudaGraphExecUpdate(p->exec, g, &info) != cudaSuccess) {
+            cudaGetLastError();
+            cudaGraphExecDestroy(p->exec);
+            p->exec = nullptr;
+        }
+    }
+    if (!p->exec && cudaGraphInstantiate(&p->exec, g, 0) != cudaSuccess) {
+        cudaGraphDestroy(g);
+        return LCC_ERR_CUDA;
+    }
+    if (p->graph) cudaGraphDestroy(p->graph);
+    p->graph = g;
+    return LCC_OK;
+}
+
+lcc_status lcc_plan_replay(lcc_plan *p) {
+    if (!p || !p->exec) return LCC_ERR_INVALID_ARG;
+    LCC_CUDA(cudaGraphLaunch(p->exec, p->stream));
+    return LCC_OK;
+}
+
+lcc_status lcc_plan_sync(lcc_plan *p) {
+    if (!p) return LCC_ERR_INVALID_ARG;
+    LCC_CUDA(cudaStreamSynchronize(p->stream));
+    lcc_status first = LCC_OK;
+    for (auto &pc : p->cls) {
+        const lcc_status st = latched(pc.ctx);
+        if (first == LCC_OK) first = st;
+    }
+    return first;
+}
+
+lcc_status lcc_plan_get_info(const lcc_plan *p, lcc_plan_info *out) {
+    if (!p || !out) return LCC_ERR_INVALID_ARG;
+    memset(out, 0, sizeof(*out));
+    out->frames = p->frames;
+    out->key_frames = p->key_frames;
+    out->points = p->points;
+    out->launches = p->launches;
+    out->classes = (int32_t)p->cls.size();
+    out->captured = p->exec ? 1 : 0;
+    size_t nodes = 0;
+    if (p->graph && cudaGraphGetNodes(p->graph, nullptr, &nodes) != cudaSuccess) nodes = 0;
+    out->graph_nodes = (int64_t)nodes;
+    return LCC_OK;
+}
+
+void lcc_plan_destroy(lcc_plan *p) {
+    if (!p) return;
+    cudaStreamSynchronize(p->stream);
+    release(p);
+}
+
+}  // extern "C"

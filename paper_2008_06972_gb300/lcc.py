@@ -47,6 +47,26 @@ class lcc_stats(ctypes.Structure):
                 ("bytes", ctypes.c_uint64)]
 
 
+class lcc_seq_desc(ctypes.Structure):
+    _fields_ = [("ctx", ctypes.c_int32), ("nframes", ctypes.c_int32), ("key_interval", ctypes.c_int32),
+                ("reserved", ctypes.c_int32), ("poses", ctypes.c_void_p), ("d_pts", ctypes.c_void_p),
+                ("n", ctypes.c_void_p), ("d_out", ctypes.c_void_p), ("cap", ctypes.c_void_p),
+                ("d_nbytes", ctypes.c_void_p)]
+
+
+class lcc_plan_info(ctypes.Structure):
+    _fields_ = [("frames", ctypes.c_int64), ("key_frames", ctypes.c_int64), ("points", ctypes.c_int64),
+                ("launches", ctypes.c_int64), ("graph_nodes", ctypes.c_int64), ("classes", ctypes.c_int32),
+                ("captured", ctypes.c_int32)]
+
+
+class lcc_tune_result(ctypes.Structure):
+    _fields_ = [("tile_h", ctypes.c_int32), ("tile_w", ctypes.c_int32), ("lookahead", ctypes.c_int32),
+                ("fit_schedule", ctypes.c_int32), ("status", ctypes.c_int32), ("chosen", ctypes.c_int32),
+                ("ms", ctypes.c_double), ("mpts_per_s", ctypes.c_double), ("bytes", ctypes.c_uint64),
+                ("max_err_m", ctypes.c_float), ("reserved", ctypes.c_float)]
+
+
 TILE_INFO_DTYPE = np.dtype([("plane", "<f4", 4), ("tplane", "<f4", 4), ("kref", "<u4"), ("ahead_mask", "<u4"),
                             ("status", "u1"), ("rounds", "u1"), ("flags", "u1"), ("n_valid", "u1"),
                             ("n_inlier", "u1"), ("t_rounds", "u1"), ("t_inlier", "u1"), ("t_status", "u1"),
@@ -89,6 +109,16 @@ def load(path: str = LIB_PATH):
         "lcc_tile_records": (i32, [vp, i32, vp, i64]),
         "lcc_set_profiling": (i32, [vp, i32]),
         "lcc_kernel_times": (i32, [vp, vp, vp, vp, i32]),
+        "lcc_plan_create": (i32, [vp, i32, vp, i32, vp]),
+        "lcc_plan_update": (i32, [vp, i32, vp]),
+        "lcc_plan_encode": (i32, [vp]),
+        "lcc_plan_capture": (i32, [vp]),
+        "lcc_plan_replay": (i32, [vp]),
+        "lcc_plan_sync": (i32, [vp]),
+        "lcc_plan_get_info": (i32, [vp, vp]),
+        "lcc_plan_destroy": (None, [vp]),
+        "lcc_autotune": (i32, [vp, vp, i32, i32, vp, vp, vp, i32, ctypes.c_float, ctypes.c_float, vp, vp, i32,
+                               vp, vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
@@ -104,7 +134,9 @@ def exported_symbols() -> list[str]:
             "lcc_num_tiles", "lcc_tables", "lcc_range_image", "lcc_keyframe_create", "lcc_keyframe_free",
             "lcc_encode_keyframe", "lcc_encode_pframe", "lcc_encode_pframes", "lcc_encode_sequence",
             "lcc_encode_sequence_host", "lcc_keyframe_from_stream", "lcc_decode", "lcc_sync", "lcc_last_stats",
-            "lcc_tile_records", "lcc_set_profiling", "lcc_kernel_times"]
+            "lcc_tile_records", "lcc_set_profiling", "lcc_kernel_times", "lcc_plan_create", "lcc_plan_update",
+            "lcc_plan_encode", "lcc_plan_capture", "lcc_plan_replay", "lcc_plan_sync", "lcc_plan_get_info",
+            "lcc_plan_destroy", "lcc_autotune"]
 
 
 def status_string(s: int) -> str:
@@ -303,3 +335,87 @@ def _host_ptr(a) -> int:
     if hasattr(a, "data_ptr"):
         return a.data_ptr()
     raise TypeError(type(a))
+
+
+class Plan:
+    """A table of sequences encoded together (lcc_plan_*).
+
+    ``seqs`` is a list of dicts with keys ``ctx`` (index into ``contexts``),
+    ``key_interval``, ``poses`` ((nframes, 4, 4) float64, frame -> its group's key frame),
+    ``d_pts`` (list of CUDA float4 tensors), ``n``, ``d_out`` (list of CUDA uint8 tensors),
+    ``cap`` and ``d_nbytes`` (CUDA int64 tensor of nframes)."""
+
+    def __init__(self, contexts: list, seqs: list):
+        self.lib = load()
+        self.contexts = contexts
+        self._keep = []
+        descs = self._descs(seqs)
+        h = ctypes.c_void_p()
+        ctxs = _arr(ctypes.c_void_p, [c.h for c in contexts])
+        _check(self.lib.lcc_plan_create(ctypes.byref(h), len(contexts), ctxs, len(seqs), descs), "lcc_plan_create")
+        self.h = h
+
+    def _descs(self, seqs):
+        keep = []
+        descs = (lcc_seq_desc * len(seqs))()
+        for i, q in enumerate(seqs):
+            nf = len(q["d_pts"])
+            poses = np.ascontiguousarray(q["poses"], dtype=np.float64).reshape(-1)
+            arrs = (poses, _arr(ctypes.c_void_p, [_ptr(x) for x in q["d_pts"]]), _arr(ctypes.c_int64, q["n"]),
+                    _arr(ctypes.c_void_p, [_ptr(x) for x in q["d_out"]]), _arr(ctypes.c_uint64, q["cap"]))
+            keep.append(arrs)
+            descs[i] = lcc_seq_desc(q["ctx"], nf, q["key_interval"], 0, poses.ctypes.data,
+                                    ctypes.addressof(arrs[1]), ctypes.addressof(arrs[2]), ctypes.addressof(arrs[3]),
+                                    ctypes.addressof(arrs[4]), _ptr(q["d_nbytes"]))
+        self._keep = keep
+        return descs
+
+    def update(self, seqs: list):
+        _check(self.lib.lcc_plan_update(self.h, len(seqs), self._descs(seqs)), "lcc_plan_update")
+
+    def encode(self):
+        _check(self.lib.lcc_plan_encode(self.h), "lcc_plan_encode")
+
+    def capture(self):
+        _check(self.lib.lcc_plan_capture(self.h), "lcc_plan_capture")
+
+    def replay(self):
+        _check(self.lib.lcc_plan_replay(self.h), "lcc_plan_replay")
+
+    def sync(self) -> int:
+        return int(self.lib.lcc_plan_sync(self.h))
+
+    def info(self) -> dict:
+        i = lcc_plan_info()
+        _check(self.lib.lcc_plan_get_info(self.h, ctypes.byref(i)), "lcc_plan_get_info")
+        return {n: getattr(i, n) for n, _ in lcc_plan_info._fields_}
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.lcc_plan_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def autotune(sensor_, base: lcc_params, key_index: int, poses, d_pts: list, n: list, reps: int = 3,
+             max_err_m: float = 0.02, bytes_slack: float = 0.05, stream=None):
+    """lcc_autotune: returns (best lcc_params, list of candidate dicts)."""
+    lib = load()
+    sn = sensor(sensor_) if not isinstance(sensor_, lcc_sensor) else sensor_
+    poses = np.ascontiguousarray(poses, dtype=np.float64).reshape(-1)
+    res = (lcc_tune_result * 64)()
+    nres = ctypes.c_int32()
+    best = lcc_params()
+    sp = stream.cuda_stream if stream is not None and hasattr(stream, "cuda_stream") else stream
+    st = lib.lcc_autotune(ctypes.byref(sn), ctypes.byref(base), len(d_pts), key_index, poses.ctypes.data,
+                          _arr(ctypes.c_void_p, [_ptr(x) for x in d_pts]), _arr(ctypes.c_int64, n), reps,
+                          max_err_m, bytes_slack, sp, res, 64, ctypes.byref(nres), ctypes.byref(best))
+    _check(st, "lcc_autotune")
+    rows = [{k: getattr(res[i], k) for k, _ in lcc_tune_result._fields_ if k != "reserved"}
+            for i in range(min(nres.value, 64))]
+    return best, rows

@@ -11,6 +11,10 @@ sequence.  Workload presets mirror the five benchmark configurations:
 * ``sequence_cfg2``  64x2048 frames (elevation -24.8..+2 deg), 20 walls,
   40 boxes, 60 poles, 2 % clutter, sigma 2 cm, 1 m/frame forward, 0.5 deg/frame
   yaw, 10 frames with the key frame in the middle.
+* ``batch_cfg3``  64 sequences of U{5..40} frames, each at one of the
+  resolutions 16x1024, 32x1024, 64x2048, 128x2048 (elevation -15..+15 deg),
+  the frame-1 scene family and noise, the cfg2 ego motion, key-frame groups of
+  10 frames with the key frame in the middle of each group.
 
 Seeds follow ``seed = 1000003*config + 1009*sequence + frame``.
 """
@@ -214,3 +218,56 @@ def offgrid_points(n: int, seed: int, r_lo=0.5, r_hi=90.0, elev_lo_deg=-40.0, el
     pts[:, 1] = r * np.cos(el) * np.sin(az)
     pts[:, 2] = r * np.sin(el)
     return pts
+
+
+CFG3_SENSORS = (Sensor(16, 1024, -15.0, 15.0, 80.0), Sensor(32, 1024, -15.0, 15.0, 80.0),
+                Sensor(64, 2048, -15.0, 15.0, 80.0), Sensor(128, 2048, -15.0, 15.0, 80.0))
+
+
+def group_key(frame: int, n_frames: int, interval: int) -> int:
+    """Key frame of the group holding `frame`: groups are [g*I, min((g+1)*I, n)), the key is the
+    group's middle frame (start + floor(len/2))."""
+    start = (frame // interval) * interval
+    return start + min(interval, n_frames - start) // 2
+
+
+@dataclass
+class GroupedSequence:
+    sensor: Sensor
+    sensor_class: int
+    frames: list          # list of float32 (n_i, 4)
+    key_interval: int
+    poses: np.ndarray     # (n_frames, 4, 4): frame i coordinates -> its group's key frame coordinates
+
+
+def grouped_sequence(sensor: Sensor, sensor_class: int, n_frames: int, seed: int, key_interval: int,
+                     n_walls=4, n_boxes=6, n_poles=10, step_m=1.0, yaw_deg=0.5, sigma=0.02, dropout=0.05,
+                     clutter=0.0, pool=None) -> GroupedSequence:
+    world = ego_poses(n_frames, step_m, yaw_deg)
+    scene = Scene(seed, n_walls, n_boxes, n_poles, path_len=step_m * max(n_frames - 1, 0), enclose=True)
+
+    def one(f):
+        Rw, tw = world[f]
+        return scene.render(sensor, Rw, tw, sigma=sigma, dropout=dropout, clutter=clutter, seed=seed * 131 + f)
+
+    frames = list(pool.map(one, range(n_frames))) if pool else [one(f) for f in range(n_frames)]
+    poses = np.stack([relative_pose(world[f], world[group_key(f, n_frames, key_interval)])
+                      for f in range(n_frames)])
+    return GroupedSequence(sensor, sensor_class, frames, key_interval, poses)
+
+
+def batch_cfg3(n_seq: int = 64, min_len: int = 5, max_len: int = 40, key_interval: int = 10,
+               classes=None, threads: int = 0) -> list:
+    """Uneven batch: per sequence a length U{min_len..max_len} and a resolution class drawn with a
+    generator seeded by config 3; frames rendered in parallel threads (the ray caster releases
+    the GIL)."""
+    import concurrent.futures as cf
+    rng = np.random.default_rng(config_seed(3, 0, 0))
+    lens = rng.integers(min_len, max_len + 1, n_seq)
+    cls = rng.integers(0, len(CFG3_SENSORS), n_seq)
+    if classes is not None:
+        cls = np.asarray([classes[i % len(classes)] for i in range(n_seq)])
+    threads = threads or min(16, os.cpu_count() or 4)
+    with cf.ThreadPoolExecutor(threads) as pool:
+        return [grouped_sequence(CFG3_SENSORS[int(c)], int(c), int(L), config_seed(3, i, 0), key_interval,
+                                 pool=pool) for i, (L, c) in enumerate(zip(lens, cls))]
