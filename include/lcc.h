@@ -196,6 +196,39 @@ lcc_status lcc_tile_records(lcc_ctx *ctx, int32_t frame, lcc_tile_info *h_out, i
 lcc_status lcc_set_profiling(lcc_ctx *ctx, int32_t enable);
 int32_t lcc_kernel_times(lcc_ctx *ctx, char names[][16], int64_t *launches, double *ms, int32_t cap);
 
+/* ---- Range image without a context or any allocation ----
+ *
+ * The paper has no counterpart: this is an implementation entry point.  It
+ * computes what lcc_range_image computes (Sec. III-B, Eq. 1-2: one pixel per
+ * point by exact boundary sign tests, nearest point per pixel) for callers
+ * that must not allocate device memory: a process whose device memory is
+ * fully reserved up front by its own pool, or a latency-critical thread that
+ * cannot take the implicit device-wide synchronisation of cudaFree or the
+ * cost of a first allocation.  It makes no cudaMalloc, cudaFree or other
+ * allocating call; its scratch is one fixed device array of about 1.2 MB
+ * (range image, boundary tables, counters) in the library.
+ *
+ * Limits: rows <= 512, cols <= 8192, rows * cols <= 262144 (e.g. 128 x 2048);
+ * larger sensors return LCC_ERR_UNSUPPORTED.  Invalid sensor or pointers
+ * return LCC_ERR_INVALID_ARG.
+ *
+ * d_pts: n device float4 (x, y, z, unused), 16-byte aligned (may be NULL when
+ * n = 0).  Outputs (either may be NULL): d_range [rows*cols] fp32 (0 =
+ * empty), d_valid occupancy bitmap of ceil(rows*cols/32) words, bit p of word
+ * p/32 set when pixel p holds a point.  Asynchronous on cuda_stream (the
+ * boundary tables are copied from a small host stack buffer by pageable
+ * cudaMemcpyAsync, which returns once each chunk is staged).
+ *
+ * Set-up: the first call on each device, with that device current, resolves
+ * the array's address with cudaGetSymbolAddress (checked) and caches it;
+ * make that first call before any stream capture on that device.
+ * The array is shared by every call on a device: calls that overlap in time
+ * (other streams, other threads) race on it and must be serialised by the
+ * caller.  Each call clears what must start cleared (range image to empty,
+ * counters to zero) on its stream before binning. */
+lcc_status lcc_range_image_static(const lcc_sensor *sensor, const float *d_pts, int64_t n, float *d_range,
+                                  uint32_t *d_valid, void *cuda_stream);
+
 /* ---- Batched encode of many sequences, replayed as a CUDA graph ----
  *
  * The paper encodes one sequence at a time (Sec. III-C: frames are grouped,

@@ -109,6 +109,7 @@ def load(path: str = LIB_PATH):
         "lcc_tile_records": (i32, [vp, i32, vp, i64]),
         "lcc_set_profiling": (i32, [vp, i32]),
         "lcc_kernel_times": (i32, [vp, vp, vp, vp, i32]),
+        "lcc_range_image_static": (i32, [vp, vp, i64, vp, vp, vp]),
         "lcc_plan_create": (i32, [vp, i32, vp, i32, vp]),
         "lcc_plan_update": (i32, [vp, i32, vp]),
         "lcc_plan_encode": (i32, [vp]),
@@ -134,7 +135,7 @@ def exported_symbols() -> list[str]:
             "lcc_num_tiles", "lcc_tables", "lcc_range_image", "lcc_keyframe_create", "lcc_keyframe_free",
             "lcc_encode_keyframe", "lcc_encode_pframe", "lcc_encode_pframes", "lcc_encode_sequence",
             "lcc_encode_sequence_host", "lcc_keyframe_from_stream", "lcc_decode", "lcc_sync", "lcc_last_stats",
-            "lcc_tile_records", "lcc_set_profiling", "lcc_kernel_times", "lcc_plan_create", "lcc_plan_update",
+            "lcc_tile_records", "lcc_set_profiling", "lcc_kernel_times", "lcc_range_image_static", "lcc_plan_create", "lcc_plan_update",
             "lcc_plan_encode", "lcc_plan_capture", "lcc_plan_replay", "lcc_plan_sync", "lcc_plan_get_info",
             "lcc_plan_destroy", "lcc_autotune"]
 
@@ -335,6 +336,14 @@ def _host_ptr(a) -> int:
     if hasattr(a, "data_ptr"):
         return a.data_ptr()
     raise TypeError(type(a))
+
+
+def lcc_range_image_static(sensor_, d_pts, n: int, d_range=None, d_valid=None, stream=None):
+    """Range image with the library's fixed scratch (no context, no allocation).  Asynchronous on
+    `stream` (torch stream, raw handle or None for the default stream); returns the status."""
+    sn = sensor(sensor_) if not isinstance(sensor_, lcc_sensor) else sensor_
+    sp = stream.cuda_stream if stream is not None and hasattr(stream, "cuda_stream") else stream
+    return int(load().lcc_range_image_static(ctypes.byref(sn), _ptr(d_pts), n, _ptr(d_range), _ptr(d_valid), sp))
 
 
 class Plan:
