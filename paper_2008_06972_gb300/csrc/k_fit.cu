@@ -544,67 +544,69 @@ __global__ void __launch_bounds__(kFitThreads) k_fit_round(Geometry g, Scratch s
 // pixels against the planes of the (up to `lookahead`) tiles to its left in
 // the row whose fit succeeded.  Bit j of the result (and count byte j) says
 // whether tile t would join a run started at tile t-1-j, i.e. passes that
-// plane under the acceptance rule (Sec. III-C run growth).  Working from the
-// tested tile keeps every pixel load in the tile's own (cached) range.
-template <int TH_, int TW_>
+// plane under the acceptance rule (Sec. III-C run growth).
+//
+// LPT lanes per tile (16 for horizons up to 16, else 32): the lanes stage the
+// tile's pixels (unit ray and range) in shared memory, one pixel each, then
+// lane j tests all of them against the plane of tile t-1-j.  The tests of
+// one tile run side by side instead of one after the other, which is what a
+// single key frame (8192 tiles at 64x2048) needs to fill the GPU.
+template <int TH_, int TW_, int LPT>
 __global__ void __launch_bounds__(kFitThreads) k_lookbehind(Geometry g, Scratch s, Batch b) {
-    using TV = TileView<TH_, TW_>;
-    constexpr int PX = TV::PX;
-    constexpr bool kRegs = PX <= 16;   // small tiles keep their points in registers
-    __shared__ __align__(16) uint8_t s_cnt[kFitThreads][32];
+    constexpr int PX = TH_ * TW_;
+    constexpr int TPB = kFitThreads / LPT;
+    __shared__ float4 s_px[TPB][PX + 1];   // +1: tiles of one warp start in different banks
+    const unsigned FULL = 0xffffffffu;
     const int f = blockIdx.y;
-    const int t = blockIdx.x * kFitThreads + threadIdx.x;
-    if (t >= g.NT) return;
+    const int lt = threadIdx.x / LPT, j = threadIdx.x % LPT;
+    const int t = blockIdx.x * TPB + lt;
+    const bool live = t < g.NT;
     const uint32_t *rimg = s.rimg + (size_t)b.slot[f] * g.H * g.W;
     TileRec *recs = s.tiles + (size_t)b.slot[f] * g.NT;
-    const TV tv(g, rimg, t);
-    float pr[kRegs ? PX : 1], pux[kRegs ? PX : 1], puy[kRegs ? PX : 1], puz[kRegs ? PX : 1];
-    if (kRegs) {
-#pragma unroll
-        for (int k = 0; k < (kRegs ? PX : 1); k++) {
-            pr[k] = tv.r(k);
-            tv.u(k, pux[k], puy[k], puz[k]);
-        }
-    }
-    uint32_t bmask = 0;
-    uint32_t *cw = reinterpret_cast<uint32_t *>(s_cnt[threadIdx.x]);
-#pragma unroll
-    for (int q = 0; q < 8; q++) cw[q] = 0u;
-    const int need = need_inliers(g.fmin, tv.nv);
-    const int span = min(g.lookahead, tv.tc);
-    bool border = false;
-    if (tv.nv >= 3) {
-        for (int j = 0; j < span; j++) {
-            const TileRec *src = recs + (t - 1 - j);
-            const uint32_t w0 = *reinterpret_cast<const uint32_t *>(reinterpret_cast<const uint8_t *>(src) + 40);
-            if ((w0 & 0xff) != S_FIT) continue;
-            const float4 pl = src->plane;
-            int nin = 0;
-            if (kRegs) {
-#pragma unroll
-                for (int k = 0; k < (kRegs ? PX : 1); k++)
-                    if (pr[k] > 0.0f) nin += inlier_screened(pl, pux[k], puy[k], puz[k], pr[k], g.thr, border) ? 1 : 0;
-            } else {
-#pragma unroll 2
-                for (int k = 0; k < PX; k++) {
-                    const float rr = tv.r(k);
-                    if (!(rr > 0.0f)) continue;
-                    float ux, uy, uz;
-                    tv.u(k, ux, uy, uz);
-                    nin += inlier_screened(pl, ux, uy, uz, rr, g.thr, border) ? 1 : 0;
-                }
+    const int tc = live ? t % g.TC : 0;
+    const int i0 = live ? (t / g.TC) * TH_ : 0, j0 = tc * TW_;
+    int nv = 0;
+    for (int k = j; k < PX; k += LPT) {
+        float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+        const int i = i0 + k / TW_, jj = j0 + k % TW_;
+        if (live && i < g.H && jj < g.W) {
+            const uint32_t bits = __ldg(rimg + (size_t)i * g.W + jj);
+            if (bits_valid(bits)) {
+                beam(g, i, jj, v.x, v.y, v.z);
+                v.w = __uint_as_float(bits);
+                nv++;
             }
-            if (nin >= need) bmask |= 1u << j;
-            s_cnt[threadIdx.x][j] = (uint8_t)nin;
+        }
+        s_px[lt][k] = v;
+    }
+#pragma unroll
+    for (int off = LPT / 2; off; off >>= 1) nv += __shfl_xor_sync(FULL, nv, off);
+    __syncwarp();
+    int nin = 0;
+    bool pass = false, border = false;
+    if (live && nv >= 3 && j < min(g.lookahead, tc)) {
+        const TileRec *src = recs + (t - 1 - j);
+        const uint32_t w0 = *reinterpret_cast<const uint32_t *>(reinterpret_cast<const uint8_t *>(src) + 40);
+        if ((w0 & 0xff) == S_FIT) {
+            const float4 pl = src->plane;
+#pragma unroll 4
+            for (int k = 0; k < PX; k++) {
+                const float4 v = s_px[lt][k];
+                if (v.w > 0.0f) nin += inlier_screened(pl, v.x, v.y, v.z, v.w, g.thr, border) ? 1 : 0;
+            }
+            pass = nin >= need_inliers(g.fmin, nv);
         }
     }
-    uint8_t *base = reinterpret_cast<uint8_t *>(recs + t);
-    *reinterpret_cast<uint32_t *>(base + 36) = bmask;
-    const uint4 c0 = make_uint4(cw[0], cw[1], cw[2], cw[3]), c1 = make_uint4(cw[4], cw[5], cw[6], cw[7]);
-    *reinterpret_cast<uint4 *>(base + 48) = c0;
-    uint4 *dst = reinterpret_cast<uint4 *>(s.lbcnt + ((size_t)b.slot[f] * g.NT + t) * 32);
-    dst[0] = c0;
-    dst[1] = c1;
+    const uint32_t bal = __ballot_sync(FULL, pass);
+    const uint32_t bmask = LPT == 32 ? bal : (bal >> ((threadIdx.x & 31) & ~(LPT - 1))) & ((1u << LPT) - 1u);
+    if (live) {
+        uint8_t *lb = s.lbcnt + ((size_t)b.slot[f] * g.NT + t) * 32;
+        lb[j] = (uint8_t)nin;
+        if (LPT == 16) lb[j + 16] = 0;
+        uint8_t *base = reinterpret_cast<uint8_t *>(recs + t);
+        if (j < 16) base[48 + j] = (uint8_t)nin;
+        if (j == 0) *reinterpret_cast<uint32_t *>(base + 36) = bmask;
+    }
 }
 
 template <int TH_, int TW_>
@@ -624,8 +626,13 @@ static cudaError_t launch_fit_first_t(const Geometry &g, const Scratch &s, const
 template <int TH_, int TW_>
 static cudaError_t launch_lookbehind_t(const Geometry &g, const Scratch &s, const Batch &b, cudaStream_t st) {
     if (!g.merge || g.lookahead <= 0) return cudaSuccess;
-    dim3 grid((g.NT + kFitThreads - 1) / kFitThreads, b.nframes);
-    k_lookbehind<TH_, TW_><<<grid, kFitThreads, 0, st>>>(g, s, b);
+    if (g.lookahead <= 16) {
+        constexpr int TPB = kFitThreads / 16;
+        k_lookbehind<TH_, TW_, 16><<<dim3((g.NT + TPB - 1) / TPB, b.nframes), kFitThreads, 0, st>>>(g, s, b);
+    } else {
+        constexpr int TPB = kFitThreads / 32;
+        k_lookbehind<TH_, TW_, 32><<<dim3((g.NT + TPB - 1) / TPB, b.nframes), kFitThreads, 0, st>>>(g, s, b);
+    }
     return cudaGetLastError();
 }
 

@@ -41,16 +41,16 @@ __device__ __forceinline__ uint32_t warp_incl_sum(uint32_t x, int lane) {
     return x;
 }
 
-constexpr int kMergeThreads = 128;
+constexpr int kMergeThreads = 256;
 
 // One block per tile row (the row lives in dynamic shared memory).  Stages:
 // (A) all threads stage the row's fit records; (B) the next fitted tile at or
 // after every position (suffix scan, warp 0) and, for every fitted tile, how
 // far its run would reach by the followers' look-behind bits (all threads);
-// (C) warp 0 walks the greedy chain: a run starts at the next fitted tile,
-// ends where its precomputed reach ends (explicit tests with one lane per
-// tile only past the look-behind horizon), and the walk resumes at the next
-// fitted tile after it; (D) all threads assign codes and counts, then a block
+// (C) all threads walk the greedy chain together: a run starts at the next
+// fitted tile, ends where its precomputed reach ends (past the look-behind
+// horizon, block-wide steps test one tile per thread), and the walk resumes
+// at the next fitted tile after it; (D) all threads assign codes and counts, then a block
 // scan gives the intra-row stream offsets and the row totals.
 template <int TH_, int TW_>
 __global__ void __launch_bounds__(kMergeThreads) k_merge(Geometry g, Scratch s, Batch b) {
@@ -126,17 +126,19 @@ __global__ void __launch_bounds__(kMergeThreads) k_merge(Geometry g, Scratch s, 
         }
     }
     __syncthreads();
-    // (C) the greedy walk (warp 0)
-    if (warp == 0) {
+    // (C) the greedy walk.  Every thread follows the same chain (uniform values read from
+    // shared memory); past the look-behind horizon the whole block tests the next
+    // kMergeThreads tiles against the run's plane in one step.
+    {
+        __shared__ uint32_t s_fail[kMergeThreads / 32];
         int st = nextfit[0];
         while (st < TC) {
             int k = reach[st];
-            // every pre-tested follower joined and the row goes on: test further tiles explicitly
             bool open = g.merge && k < TC && k - st - 1 >= hzmax;
             if (open) {
                 const float4 pl = row[st].plane;
                 while (open) {
-                    const int c2 = k + lane;
+                    const int c2 = k + tid;
                     bool pass = false;
                     int nvv = 0, nin = 0;
                     if (c2 < TC && row[c2].status != S_TEMPORAL) {
@@ -158,13 +160,19 @@ __global__ void __launch_bounds__(kMergeThreads) k_merge(Geometry g, Scratch s, 
                         pass = nvv >= 3 && nin >= need_inliers(g.fmin, nvv);
                     }
                     const uint32_t failb = __ballot_sync(FULL, !pass);
-                    const int nj = failb ? __ffs(failb) - 1 : 32;
-                    if (lane < nj) extcnt[c2] = (uint8_t)nin;
+                    if (lane == 0) s_fail[warp] = failb;
+                    __syncthreads();
+                    int nj = kMergeThreads;
+#pragma unroll
+                    for (int w = kMergeThreads / 32 - 1; w >= 0; w--)
+                        if (s_fail[w]) nj = w * 32 + __ffs(s_fail[w]) - 1;
+                    __syncthreads();   // s_fail is rewritten by the next step
+                    if (tid < nj) extcnt[c2] = (uint8_t)nin;
                     k += nj;
-                    open = (failb == 0) && k < TC;
+                    open = nj == kMergeThreads && k < TC;
                 }
             }
-            if (lane == 0) runend[st] = (uint16_t)k;
+            if (tid == 0) runend[st] = (uint16_t)k;
             st = k < TC ? nextfit[k] : TC;
         }
     }
