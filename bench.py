@@ -85,7 +85,8 @@ def oracle_sample(seq, th, tw, thr, seconds):
     return pts_per_seq * nseq / el / 1e6, nseq, el
 
 
-KERNEL_SOURCES = {"bin": "k_bin.cu", "fit": "k_fit.cu", "refit": "k_fit.cu", "merge": "k_merge.cu",
+KERNEL_SOURCES = {"bin": "k_bin.cu", "fit": "k_fit.cu", "refit": "k_fit.cu", "temporal": "k_fit.cu",
+                  "merge": "k_merge.cu",
                   "scan": "k_scan.cu", "pack": "k_pack.cu"}
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "dram_traffic_hdl64_sequence.txt")
 
@@ -436,6 +437,7 @@ def main():
     #   merge: 64 B per tile record read + 8 B per tile code written
     #   scan:  8 B per tile code read + 32 B per tile offset written + stream bytes zeroed
     #   pack:  4 B per pixel read + 4 B per pixel reset + stream bytes written
+    #   temporal: (P frames) 4 B per pixel + 64 B per tile record read and written
     #   refit: 4 B per pixel (range image read) + 64 B per tile record read + 32 B per tile of
     #          look-behind counts written (extra refit rounds, when scheduled, reuse the same data)
     npx = H * W
@@ -444,6 +446,7 @@ def main():
         "bin": 20.0 * pts_step,
         "fit": n_frames * (4.0 * npx + 64.0 * nt),
         "refit": n_frames * (4.0 * npx + 96.0 * nt),
+        "temporal": (n_frames - 1) * (4.0 * npx + 128.0 * nt),
         "merge": n_frames * (64.0 * nt + 8.0 * nt),
         "scan": n_frames * (8.0 * nt + 32.0 * nt) + total_bytes,
         "pack": n_frames * 8.0 * npx + total_bytes,

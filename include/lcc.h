@@ -155,7 +155,10 @@ lcc_status lcc_encode_pframes(lcc_ctx *ctx, const lcc_keyframe *kf, int32_t nfra
 
 /* A whole sequence (Fig. 1): frame key_index is the K frame, all others are P
  * frames; poses[f] maps frame f to the key frame (poses[key_index] unused).
- * Bins all frames in one launch, encodes K, then all P frames batched.
+ * Bins all frames in one launch, encodes K, then all P frames batched.  With
+ * fit_schedule 0 the P frames' spatial fits run on a second stream of the
+ * context while K is encoded (they do not need K), and their temporal test
+ * runs after; the streams are the same as with the sequential order.
  * nframes <= max_batch.  kf (nullable) receives the key frame's planes. */
 lcc_status lcc_encode_sequence(lcc_ctx *ctx, int32_t nframes, int32_t key_index, const double *poses,
                                const float *const *d_pts, const int64_t *n, uint8_t *const *d_out,
@@ -189,10 +192,11 @@ lcc_status lcc_last_stats(lcc_ctx *ctx, int32_t frame, lcc_stats *out);
 lcc_status lcc_tile_records(lcc_ctx *ctx, int32_t frame, lcc_tile_info *h_out, int64_t cap);
 
 /* Kernel timing: when enabled, every kernel launch is bracketed by CUDA events
- * on the context stream.  lcc_kernel_times returns, per kernel name, the
+ * on the stream it runs on.  lcc_kernel_times returns, per kernel name, the
  * number of launches and summed milliseconds since the last reset
- * (synchronous).  Names: "bin", "fit", "refit", "merge", "scan", "pack",
- * "decode_prep", "decode_px", "range_export".  Returns the number of entries written. */
+ * (synchronous; launches that overlap are each timed in full).  Names: "bin",
+ * "fit", "refit", "temporal", "merge", "scan", "pack", "decode_prep",
+ * "decode_px", "range_export".  Returns the number of entries written. */
 lcc_status lcc_set_profiling(lcc_ctx *ctx, int32_t enable);
 int32_t lcc_kernel_times(lcc_ctx *ctx, char names[][16], int64_t *launches, double *ms, int32_t cap);
 

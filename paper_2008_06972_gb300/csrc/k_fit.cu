@@ -540,6 +540,39 @@ __global__ void __launch_bounds__(kFitThreads) k_fit_round(Geometry g, Scratch s
     }
 }
 
+// Temporal pass over P tiles whose spatial fit already ran (k_fit_first
+// without a key-frame table): the temporal test of Sec. III-D against the
+// key frame's planes, and the same per-tile decision as the fused pass — a
+// tile that passes becomes TEMPORAL exactly as if its spatial fit had never
+// run; otherwise the spatial result stands and the temporal fields are added.
+template <int TH_, int TW_>
+__global__ void __launch_bounds__(kFitThreads) k_temporal(Geometry g, Scratch s, Batch b, Poses ps) {
+    using TV = TileView<TH_, TW_>;
+    const int f = blockIdx.y;
+    const int t = blockIdx.x * kFitThreads + threadIdx.x;
+    if (t >= g.NT || !b.kf[f]) return;
+    const uint32_t *rimg = s.rimg + (size_t)b.slot[f] * g.H * g.W;
+    TileRec *recs = s.tiles + (size_t)b.slot[f] * g.NT;
+    const TV tv(g, rimg, t);
+    if (tv.nv == 0) return;
+    RecOut o = read_rec(recs + t);
+    RecOut ot = o;
+    ot.flags = 0;
+    temporal_test<TH_, TW_>(tv, ps.m[f], b.kf[f], ot);
+    if (ot.status == S_TEMPORAL) {
+        ot.rounds = 0;
+        write_rec(recs + t, ot);
+    } else if (ot.flags) {
+        o.kref = ot.kref;
+        o.tplane = ot.tplane;
+        o.t_rounds = ot.t_rounds;
+        o.t_inl = ot.t_inl;
+        o.t_status = ot.t_status;
+        o.flags |= ot.flags;
+        write_rec(recs + t, o);
+    }
+}
+
 // Run pre-test, after every tile's own fit is final: tile t tests its own
 // pixels against the planes of the (up to `lookahead`) tiles to its left in
 // the row whose fit succeeded.  Bit j of the result (and count byte j) says
@@ -650,6 +683,22 @@ static cudaError_t launch_fit_rounds_t(const Geometry &g, const Scratch &s, cons
         }
     }
     return launch_lookbehind_t<TH_, TW_>(g, s, b, st);
+}
+
+template <int TH_, int TW_>
+static cudaError_t launch_temporal_t(const Geometry &g, const Scratch &s, const Batch &b, const Poses &p,
+                                     cudaStream_t st) {
+    k_temporal<TH_, TW_><<<dim3((g.NT + kFitThreads - 1) / kFitThreads, b.nframes), kFitThreads, 0, st>>>(g, s, b, p);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_temporal(const Geometry &g, const Scratch &s, const Batch &b, const Poses &p, cudaStream_t st) {
+    if (b.nframes <= 0) return cudaSuccess;
+    if (g.th == 4 && g.tw == 4) return launch_temporal_t<4, 4>(g, s, b, p, st);
+    if (g.th == 4 && g.tw == 8) return launch_temporal_t<4, 8>(g, s, b, p, st);
+    if (g.th == 8 && g.tw == 8) return launch_temporal_t<8, 8>(g, s, b, p, st);
+    if (g.th == 8 && g.tw == 16) return launch_temporal_t<8, 16>(g, s, b, p, st);
+    return cudaErrorInvalidValue;
 }
 
 cudaError_t launch_fit(const Geometry &g, const Scratch &s, const Batch &b, const Poses &p, cudaStream_t st) {

@@ -18,7 +18,8 @@ using namespace lcc;
 namespace lcc {
 namespace api {
 
-const char *kKernelNames[] = {"bin", "fit", "merge", "scan", "pack", "decode_prep", "decode_px", "range_export", "refit"};
+const char *kKernelNames[] = {"bin",          "fit",   "merge", "scan",    "pack", "decode_prep",
+                              "decode_px",    "range_export",   "refit",   "temporal"};
 
 cudaEvent_t get_event(lcc_ctx *c) {
     if (!c->pool.empty()) {
@@ -103,11 +104,9 @@ lcc_status latched(lcc_ctx *c) {
     return LCC_OK;
 }
 
-lcc_status encode_batch(lcc_ctx *c, int kind, int nframes, const int *slots, uint8_t *const *d_out,
-                        const uint64_t *cap, const double *poses, const float4 *const *kf, float4 *const *kf_out,
-                        unsigned long long *const *nbytes_out) {
-    if (nframes <= 0) return LCC_OK;
-    Batch b;
+void prepare_batch(Batch &b, Poses &p, int kind, int nframes, const int *slots, uint8_t *const *d_out,
+                   const uint64_t *cap, const double *poses, const float4 *const *kf, float4 *const *kf_out,
+                   unsigned long long *const *nbytes_out) {
     memset(&b, 0, sizeof(b));
     b.nframes = nframes;
     b.kind = kind;
@@ -119,16 +118,29 @@ lcc_status encode_batch(lcc_ctx *c, int kind, int nframes, const int *slots, uin
         b.kf_out[f] = kf_out ? kf_out[f] : nullptr;
         b.nbytes_out[f] = nbytes_out ? nbytes_out[f] : nullptr;
     }
-    Poses p;
     memset(&p, 0, sizeof(p));
     if (poses)
         for (int f = 0; f < nframes; f++) memcpy(p.m[f], poses + 16 * f, 16 * sizeof(double));
-    LCC_LAUNCH(c, 1, launch_fit(c->g, c->s, b, p, c->stream));
+}
+
+// Everything after the first fit pass: further rounds and the run pre-test, merge, scan, pack.
+lcc_status encode_tail(lcc_ctx *c, const Batch &b) {
     LCC_LAUNCH(c, 8, launch_fit_rounds(c->g, c->s, b, c->stream));
     LCC_LAUNCH(c, 2, launch_merge(c->g, c->s, b, c->stream));
     LCC_LAUNCH(c, 3, launch_scan(c->g, c->s, b, c->stream));
     LCC_LAUNCH(c, 4, launch_pack(c->g, c->s, b, c->stream));
     return LCC_OK;
+}
+
+lcc_status encode_batch(lcc_ctx *c, int kind, int nframes, const int *slots, uint8_t *const *d_out,
+                        const uint64_t *cap, const double *poses, const float4 *const *kf, float4 *const *kf_out,
+                        unsigned long long *const *nbytes_out) {
+    if (nframes <= 0) return LCC_OK;
+    Batch b;
+    Poses p;
+    prepare_batch(b, p, kind, nframes, slots, d_out, cap, poses, kf, kf_out, nbytes_out);
+    LCC_LAUNCH(c, 1, launch_fit(c->g, c->s, b, p, c->stream));
+    return encode_tail(c, b);
 }
 
 lcc_status bin_frames(lcc_ctx *c, int nframes, const int *slots, const float *const *d_pts, const int64_t *n) {
@@ -332,6 +344,12 @@ lcc_status lcc_create(lcc_ctx **out, const lcc_sensor *sensor, const lcc_params 
     c->s.qcap = (uint32_t)(sl * nt);
     cudaMemset(c->d_scratch, 0, total);
     cudaMemset(c->s.rimg, 0xFF, sl * npx * 4);
+    if (cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming) != cudaSuccess) {
+        lcc_destroy(c);
+        return LCC_ERR_CUDA;
+    }
     c->max_bytes = (uint64_t)kHeaderBytes +
                    4ull * ((npx + 31) / 32 + (nt * 4 + 31) / 32 + 4 * nt + 2 * nt + (npx + 31) / 32 +
                            (npx * g.w_res + 31) / 32 + (npx * g.w_raw + 31) / 32 + 4);
@@ -351,6 +369,12 @@ lcc_status lcc_destroy(lcc_ctx *c) {
         cudaEventDestroy(r.b);
     }
     for (auto e : c->pool) cudaEventDestroy(e);
+    if (c->side) {
+        cudaStreamSynchronize(c->side);
+        cudaStreamDestroy(c->side);
+    }
+    if (c->ev_fork) cudaEventDestroy(c->ev_fork);
+    if (c->ev_join) cudaEventDestroy(c->ev_join);
     cudaFree(c->d_tables);
     cudaFree(c->d_scratch);
     cudaFree(c->d_stage_pts);
@@ -470,8 +494,6 @@ lcc_status lcc_encode_sequence(lcc_ctx *c, int32_t nframes, int32_t key_index, c
     const int kslot = key_index;
     uint8_t *kout = d_out[key_index];
     const uint64_t kcap = cap[key_index];
-    float4 *kfo = k->planes;
-    if ((st = encode_batch(c, 0, 1, &kslot, &kout, &kcap, nullptr, nullptr, &kfo)) != LCC_OK) return st;
     int pslots[kMaxBatch];
     uint8_t *pout[kMaxBatch];
     uint64_t pcap[kMaxBatch];
@@ -487,7 +509,34 @@ lcc_status lcc_encode_sequence(lcc_ctx *c, int32_t nframes, int32_t key_index, c
         pposes.insert(pposes.end(), poses + 16 * f, poses + 16 * f + 16);
         np++;
     }
-    if ((st = encode_batch(c, 1, np, pslots, pout, pcap, pposes.data(), kfi, nullptr)) != LCC_OK) return st;
+    float4 *kfo = k->planes;
+    if (np == 0 || c->g.schedule != 0) {
+        if ((st = encode_batch(c, 0, 1, &kslot, &kout, &kcap, nullptr, nullptr, &kfo)) != LCC_OK) return st;
+        if ((st = encode_batch(c, 1, np, pslots, pout, pcap, pposes.data(), kfi, nullptr)) != LCC_OK) return st;
+    } else {
+        // The P frames' spatial fits do not need the key frame: they run on the side stream while
+        // the key frame is encoded, and the temporal test (which needs its planes) runs after.
+        Batch bk, bp;
+        Poses pk, pp;
+        prepare_batch(bk, pk, 0, 1, &kslot, &kout, &kcap, nullptr, nullptr, &kfo, nullptr);
+        prepare_batch(bp, pp, 1, np, pslots, pout, pcap, pposes.data(), nullptr, nullptr, nullptr);
+        LCC_CUDA(cudaEventRecord(c->ev_fork, c->stream));
+        LCC_CUDA(cudaStreamWaitEvent(c->side, c->ev_fork, 0));
+        cudaStream_t main = c->stream;
+        c->stream = c->side;   // profiling events of this launch go to the side stream too
+        const int pi = prof_begin(c, 1);
+        const cudaError_t e = launch_fit(c->g, c->s, bp, pp, c->side);
+        prof_end(c, pi);
+        c->stream = main;
+        if (e != cudaSuccess) return LCC_ERR_CUDA;
+        LCC_CUDA(cudaEventRecord(c->ev_join, c->side));
+        LCC_LAUNCH(c, 1, launch_fit(c->g, c->s, bk, pk, c->stream));
+        if ((st = encode_tail(c, bk)) != LCC_OK) return st;
+        LCC_CUDA(cudaStreamWaitEvent(c->stream, c->ev_join, 0));
+        for (int f = 0; f < np; f++) bp.kf[f] = k->planes;
+        LCC_LAUNCH(c, 9, launch_temporal(c->g, c->s, bp, pp, c->stream));
+        if ((st = encode_tail(c, bp)) != LCC_OK) return st;
+    }
     c->last_nframes = nframes;
     return copy_bytes(c, nframes, slots, out_bytes);
 }

@@ -19,7 +19,7 @@ struct ProfRec {
     cudaEvent_t a, b;
 };
 
-constexpr int kNumKernels = 9;
+constexpr int kNumKernels = 10;
 extern const char *kKernelNames[];
 
 inline size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
@@ -37,6 +37,8 @@ struct lcc_ctx {
     lcc_sensor sensor;
     lcc_params prm;
     cudaStream_t stream = nullptr;
+    cudaStream_t side = nullptr;          // second stream for work that overlaps the key frame
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     lcc::Geometry g{};
     lcc::Scratch s{};
     void *d_tables = nullptr;

@@ -329,6 +329,7 @@ cudaError_t launch_range_image(const Geometry &g, const uint32_t *rimg, float *r
                                cudaStream_t st);
 cudaError_t launch_fit(const Geometry &g, const Scratch &s, const Batch &b, const Poses &p, cudaStream_t st);
 cudaError_t launch_fit_rounds(const Geometry &g, const Scratch &s, const Batch &b, cudaStream_t st);
+cudaError_t launch_temporal(const Geometry &g, const Scratch &s, const Batch &b, const Poses &p, cudaStream_t st);
 cudaError_t launch_merge(const Geometry &g, const Scratch &s, const Batch &b, cudaStream_t st);
 size_t merge_smem_bytes(int TC);
 cudaError_t launch_scan(const Geometry &g, const Scratch &s, const Batch &b, cudaStream_t st);

@@ -304,14 +304,28 @@ def test_sequence_call_matches_separate_calls(cfg2_seq):
     assert c.lcc_sync() == 0
     nbs = nb.cpu().numpy()
     seq_bits = [outs[i][:nbs[i]].cpu().numpy() for i in range(n)]
+    seq_recs = [c.lcc_tile_records(i) for i in range(n)]
     c2 = H.ctx(seq.sensor, max_batch=16)
     kf2 = lcc.Keyframe(c2)
-    kbits, _ = H.encode_keyframe(c2, seq.frames[seq.key_index], kf2)
+    kbits, krecs = H.encode_keyframe(c2, seq.frames[seq.key_index], kf2)
     assert kbits.tobytes() == seq_bits[seq.key_index].tobytes()
+    assert krecs.tobytes() == seq_recs[seq.key_index].tobytes()
     others = [f for f in range(n) if f != seq.key_index]
-    pb, _ = H.encode_pframes(c2, kf2, [seq.poses[f] for f in others], [seq.frames[f] for f in others])
+    pb, precs = H.encode_pframes(c2, kf2, [seq.poses[f] for f in others], [seq.frames[f] for f in others])
     for i, f in enumerate(others):
         assert pb[i].tobytes() == seq_bits[f].tobytes()
+        # the sequence call fits P tiles spatially while the key frame is encoded and tests them
+        # temporally afterwards; every tile record (rounds and flags included) is as if fused
+        assert precs[i].tobytes() == seq_recs[f].tobytes(), f"frame {f}: tile records differ"
+    # the same with the queued fit schedule (sequential order inside the sequence call)
+    cq = H.ctx(seq.sensor, max_batch=16, fit_schedule=1)
+    outs_q = [H.out_buf(cq) for _ in range(n)]
+    cq.lcc_encode_sequence(seq.key_index, seq.poses, ds, [len(p) for p in seq.frames], outs_q,
+                           [o.numel() for o in outs_q], nb, None)
+    assert cq.lcc_sync() == 0
+    nbq = nb.cpu().numpy()
+    for f in range(n):
+        assert outs_q[f][:nbq[f]].cpu().numpy().tobytes() == seq_bits[f].tobytes()
     # host-buffer variant (end-to-end path of the bench)
     h_out = [np.zeros(c.max_encoded_bytes, np.uint8) for _ in range(n)]
     nbh = c.lcc_encode_sequence_host(seq.key_index, seq.poses, [np.ascontiguousarray(p) for p in seq.frames], h_out,
