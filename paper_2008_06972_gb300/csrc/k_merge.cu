@@ -26,6 +26,15 @@ struct alignas(16) RowRec {
     uint8_t flags, pad0, pad1, pad2;
 };
 
+// Byte offset of the staged row in the merge kernel's dynamic shared memory (after the row
+// records, the next-fitted / run-end / reach tables and the explicit-join counts).
+__host__ __device__ __forceinline__ size_t merge_stage_offset(int TC) {
+    const size_t raw = sizeof(RowRec) * (size_t)TC + 2 * (size_t)(TC + 1) + 4 * (size_t)TC + (size_t)TC + 16;
+    return (raw + 15) & ~size_t(15);
+}
+
+constexpr size_t kMergeStageMaxSmem = 200 * 1024;
+
 __device__ __forceinline__ void put_code(TileCode *codes, int t, uint8_t mode, int cand, int fitted, int raw,
                                          uint32_t plane_tile) {
     const uint32_t w0 = (uint32_t)mode | ((uint32_t)cand << 8) | ((uint32_t)fitted << 16) | ((uint32_t)raw << 24);
@@ -52,15 +61,25 @@ constexpr int kMergeThreads = 256;
 // horizon, block-wide steps test one tile per thread), and the walk resumes
 // at the next fitted tile after it; (D) all threads assign codes and counts, then a block
 // scan gives the intra-row stream offsets and the row totals.
-template <int TH_, int TW_>
+template <int TH_, int TW_, bool kStage>
 __global__ void __launch_bounds__(kMergeThreads) k_merge(Geometry g, Scratch s, Batch b) {
     extern __shared__ __align__(16) uint8_t smem[];
+    constexpr int PX = TH_ * TW_;
+    constexpr int kEL = PX >= 64 ? 8 : 4;              // lanes per tile in an extension step
+    constexpr int kStepTiles = kMergeThreads / kEL;    // tiles tested per extension step
     const int TC = g.TC;
     RowRec *row = reinterpret_cast<RowRec *>(smem);
     uint16_t *nextfit = reinterpret_cast<uint16_t *>(row + TC);   // TC + 1 entries
     uint16_t *runend = nextfit + (TC + 1);                         // end of the run started at c, 0 if none
     uint16_t *reach = runend + TC;                                 // look-behind reach of a fitted tile
     uint8_t *extcnt = reinterpret_cast<uint8_t *>(reach + TC);     // counts of explicitly tested joins
+    // staged tile row for extension steps (kStage): range bits per tile (stride PX + 1), the
+    // row's column directions and its TH_ row directions
+    uint32_t *s_r = reinterpret_cast<uint32_t *>(smem + merge_stage_offset(TC));
+    float *s_ct = reinterpret_cast<float *>(s_r + (size_t)TC * (PX + 1));
+    float *s_st = s_ct + (size_t)TC * TW_;
+    float *s_ce = s_st + (size_t)TC * TW_;
+    float *s_se = s_ce + TH_;
     __shared__ uint32_t s_warp[kMergeThreads / 32][6];
     __shared__ uint32_t s_carry[6];
     const unsigned FULL = 0xffffffffu;
@@ -127,49 +146,78 @@ __global__ void __launch_bounds__(kMergeThreads) k_merge(Geometry g, Scratch s, 
     }
     __syncthreads();
     // (C) the greedy walk.  Every thread follows the same chain (uniform values read from
-    // shared memory); past the look-behind horizon the whole block tests the next
-    // kMergeThreads tiles against the run's plane in one step.
+    // shared memory); past the look-behind horizon the whole block tests the next kStepTiles
+    // tiles against the run's plane in one step, kEL lanes per tile.  The first such step of
+    // a row stages the row's ranges and ray directions in shared memory (kStage).
     {
         __shared__ uint32_t s_fail[kMergeThreads / 32];
+        bool staged = false;
         int st = nextfit[0];
         while (st < TC) {
             int k = reach[st];
             bool open = g.merge && k < TC && k - st - 1 >= hzmax;
             if (open) {
+                if (kStage && !staged) {
+                    for (int idx = tid; idx < TH_ * TC * TW_; idx += kMergeThreads) {
+                        const int ii = idx / (TC * TW_), jj = idx % (TC * TW_);
+                        const int i = tr * TH_ + ii;
+                        const uint32_t bits = (i < g.H && jj < g.W) ? __ldg(rimg + (size_t)i * g.W + jj) : kEmptyBits;
+                        s_r[(jj / TW_) * (PX + 1) + ii * TW_ + jj % TW_] = bits;
+                        if (ii == 0) {
+                            s_ct[jj] = jj < g.W ? __ldg(g.ct + jj) : 0.f;
+                            s_st[jj] = jj < g.W ? __ldg(g.st + jj) : 0.f;
+                        }
+                    }
+                    if (tid < TH_) {
+                        const int i = tr * TH_ + tid;
+                        s_ce[tid] = i < g.H ? __ldg(g.ce + i) : 0.f;
+                        s_se[tid] = i < g.H ? __ldg(g.se + i) : 0.f;
+                    }
+                    __syncthreads();
+                    staged = true;
+                }
                 const float4 pl = row[st].plane;
                 while (open) {
-                    const int c2 = k + tid;
-                    bool pass = false;
-                    int nvv = 0, nin = 0;
-                    if (c2 < TC && row[c2].status != S_TEMPORAL) {
-                        uint32_t bits[TH_ * TW_];
-#pragma unroll
-                        for (int q = 0; q < TH_ * TW_; q++) {
-                            const int i = tr * TH_ + q / TW_, jj = c2 * TW_ + q % TW_;
-                            bits[q] = (i < g.H && jj < g.W) ? __ldg(rimg + (size_t)i * g.W + jj) : kEmptyBits;
-                        }
+                    const int c2 = k + tid / kEL, l = tid % kEL;
+                    const bool cand = c2 < TC && row[c2].status != S_TEMPORAL;
+                    int nin = 0;
+                    if (cand) {
+                        bool border = false;
 #pragma unroll 4
-                        for (int q = 0; q < TH_ * TW_; q++) {
-                            if (!bits_valid(bits[q])) continue;
-                            nvv++;
+                        for (int q = l; q < PX; q += kEL) {
+                            const int ii = q / TW_, jj = c2 * TW_ + q % TW_;
+                            uint32_t bits;
                             float ux, uy, uz;
-                            bool border = false;
-                            beam(g, tr * TH_ + q / TW_, c2 * TW_ + q % TW_, ux, uy, uz);
-                            nin += inlier_screened(pl, ux, uy, uz, __uint_as_float(bits[q]), g.thr, border) ? 1 : 0;
+                            if (kStage) {
+                                bits = s_r[c2 * (PX + 1) + q];
+                                const float ce = s_ce[ii];
+                                ux = __fmul_rn(ce, s_ct[jj]);
+                                uy = __fmul_rn(ce, s_st[jj]);
+                                uz = s_se[ii];
+                            } else {
+                                const int i = tr * TH_ + ii;
+                                bits = (i < g.H && jj < g.W) ? __ldg(rimg + (size_t)i * g.W + jj) : kEmptyBits;
+                                if (bits_valid(bits)) beam(g, i, jj, ux, uy, uz);
+                            }
+                            if (bits_valid(bits))
+                                nin += inlier_screened(pl, ux, uy, uz, __uint_as_float(bits), g.thr, border) ? 1 : 0;
                         }
-                        pass = nvv >= 3 && nin >= need_inliers(g.fmin, nvv);
                     }
+#pragma unroll
+                    for (int off = kEL / 2; off; off >>= 1) nin += __shfl_xor_sync(FULL, nin, off);
+                    const int nvv = cand ? (int)row[c2].n_valid : 0;
+                    const bool pass = cand && nvv >= 3 && nin >= need_inliers(g.fmin, nvv);
                     const uint32_t failb = __ballot_sync(FULL, !pass);
                     if (lane == 0) s_fail[warp] = failb;
                     __syncthreads();
-                    int nj = kMergeThreads;
+                    int nj = kStepTiles;
 #pragma unroll
                     for (int w = kMergeThreads / 32 - 1; w >= 0; w--)
-                        if (s_fail[w]) nj = w * 32 + __ffs(s_fail[w]) - 1;
+                        if (s_fail[w]) nj = (w * 32 + __ffs(s_fail[w]) - 1) / kEL;
                     __syncthreads();   // s_fail is rewritten by the next step
-                    if (tid < nj) extcnt[c2] = (uint8_t)nin;
+                    if (l == 0 && tid / kEL < nj) extcnt[c2] = (uint8_t)nin;
                     k += nj;
-                    open = nj == kMergeThreads && k < TC;
+                    open = nj == kStepTiles && k < TC;
                 }
             }
             if (tid == 0) runend[st] = (uint16_t)k;
@@ -283,21 +331,31 @@ __global__ void __launch_bounds__(kMergeThreads) k_merge(Geometry g, Scratch s, 
     }
 }
 
-size_t merge_smem_bytes(int TC) {
-    return sizeof(RowRec) * (size_t)TC + 2 * (size_t)(TC + 1) + 4 * (size_t)TC + (size_t)TC + 16;
+size_t merge_smem_bytes(int TC) { return merge_stage_offset(TC); }
+
+size_t merge_stage_bytes(int TC, int th, int tw) {
+    return 4 * ((size_t)TC * (th * tw + 1) + 2 * (size_t)TC * tw + 2 * (size_t)th);
 }
 
-template <int TH_, int TW_>
-static cudaError_t launch_merge_t(const Geometry &g, const Scratch &s, const Batch &b, cudaStream_t st) {
-    const size_t smem = merge_smem_bytes(g.TC);
+template <int TH_, int TW_, bool kStage>
+static cudaError_t launch_merge_v(const Geometry &g, const Scratch &s, const Batch &b, size_t smem, cudaStream_t st) {
     if (smem > 48 * 1024) {
-        const cudaError_t e = cudaFuncSetAttribute(k_merge<TH_, TW_>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                   (int)smem);
+        const cudaError_t e = cudaFuncSetAttribute(k_merge<TH_, TW_, kStage>,
+                                                   cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
     }
-    dim3 grid(g.TR, b.nframes);
-    k_merge<TH_, TW_><<<grid, kMergeThreads, smem, st>>>(g, s, b);
+    k_merge<TH_, TW_, kStage><<<dim3(g.TR, b.nframes), kMergeThreads, smem, st>>>(g, s, b);
     return cudaGetLastError();
+}
+
+// The staged variant keeps the tile row's ranges and directions in shared memory for the
+// extension steps; rows too wide for that read them from L2 instead.
+template <int TH_, int TW_>
+static cudaError_t launch_merge_t(const Geometry &g, const Scratch &s, const Batch &b, cudaStream_t st) {
+    const size_t base = merge_stage_offset(g.TC);
+    const size_t staged = base + merge_stage_bytes(g.TC, TH_, TW_);
+    if (staged <= kMergeStageMaxSmem) return launch_merge_v<TH_, TW_, true>(g, s, b, staged, st);
+    return launch_merge_v<TH_, TW_, false>(g, s, b, base, st);
 }
 
 cudaError_t launch_merge(const Geometry &g, const Scratch &s, const Batch &b, cudaStream_t st) {
