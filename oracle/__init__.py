@@ -89,6 +89,8 @@ def lib():
             L.orc_tls_fit.argtypes = [vp, i32, vp, vp, vp]
             L.orc_fit_tiles.restype = i32
             L.orc_fit_tiles.argtypes = [vp, vp, vp, vp]
+            L.orc_fit_tiles_seeded.restype = i32
+            L.orc_fit_tiles_seeded.argtypes = [vp, vp, vp, vp, ctypes.c_float, vp]
             L.orc_temporal_tiles.restype = i32
             L.orc_temporal_tiles.argtypes = [vp, vp, vp, vp, vp, vp]
             L.orc_pack.restype = i64
@@ -165,6 +167,18 @@ def fit_tiles(s: Sensor, p: Params, rng: np.ndarray) -> np.ndarray:
     rc = lib().orc_fit_tiles(ctypes.byref(s), ctypes.byref(p), _p(rng), _p(out))
     if rc != OK:
         raise ValueError(f"orc_fit_tiles: {rc}")
+    return out
+
+
+def fit_tiles_seeded(s: Sensor, p: Params, rng: np.ndarray, prop: np.ndarray, skip_logit: float) -> np.ndarray:
+    """Fit of every tile seeded by a proposal (T, 5) float32 per tile: (logit, v0, v1, v2, d_rel)."""
+    rng = np.ascontiguousarray(rng, dtype=np.float32)
+    prop = np.ascontiguousarray(prop, dtype=np.float32)
+    out = np.zeros(n_tiles(s, p), FIT_DTYPE)
+    assert prop.shape == (len(out), 5)
+    rc = lib().orc_fit_tiles_seeded(ctypes.byref(s), ctypes.byref(p), _p(rng), _p(prop), skip_logit, _p(out))
+    if rc != OK:
+        raise ValueError(f"orc_fit_tiles_seeded: {rc}")
     return out
 
 

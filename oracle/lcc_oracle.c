@@ -386,6 +386,69 @@ static void fit_one(const orc_params *prm, const tile_px_t *tp, orc_tile_fit *f)
     if (!f->degenerate && nI >= need_inliers(prm, tp->n_valid)) f->status = ORC_FIT_OK;
 }
 
+/*
+ * Seeded fit (a learned proposal per tile; not in the paper).  prop = (logit,
+ * v0, v1, v2, d_rel): a planarity logit, an unnormalised normal and the plane
+ * offset relative to the tile's anchor (its first valid pixel's point).
+ *   - logit < skip_logit: the tile is not fitted (status FAIL, no round).
+ *   - Otherwise the proposed plane, in fp32: n = v / |v| (sqrtf of an fma sum,
+ *     IEEE divisions), d = d_rel + n.anchor (fma chain), both negated if d < 0.
+ *     The first set S is the valid pixels within the threshold of that plane;
+ *     with fewer than 3 of them (or |v| = 0) S is all valid pixels, as in the
+ *     plain fit.  From S on, the rounds and the FIT rule are those of fit_one.
+ */
+static void fit_one_seeded(const orc_params *prm, const tile_px_t *tp, const float prop[5], float skip_logit,
+                           orc_tile_fit *f) {
+    memset(f, 0, sizeof(*f));
+    f->n_valid = tp->n_valid;
+    if (tp->n_valid == 0) { f->status = ORC_FIT_EMPTY; return; }
+    f->status = ORC_FIT_FAIL;
+    if (tp->n_valid < 3) return;
+    if (prop[0] < skip_logit) return;
+    int S[MAX_TILE_PX], I[MAX_TILE_PX];
+    double buf[3 * MAX_TILE_PX];
+    int nS = 0, nI = 0;
+    const float nn = sqrtf(fmaf(prop[1], prop[1], fmaf(prop[2], prop[2], prop[3] * prop[3])));
+    if (nn > 0.0f && isfinite(nn)) {
+        int a0 = 0;
+        while (!tp->valid[a0]) a0++;
+        float pl[4] = {prop[1] / nn, prop[2] / nn, prop[3] / nn, 0.0f};
+        pl[3] = prop[4] + fmaf(pl[0], tp->p[a0][0], fmaf(pl[1], tp->p[a0][1], pl[2] * tp->p[a0][2]));
+        if (pl[3] < 0.0f)
+            for (int a = 0; a < 4; a++) pl[a] = -pl[a];
+        nS = inliers(tp, pl, prm->fit_thr_m, S, &f->borderline);
+    }
+    if (nS < 3) {
+        for (int k = 0; k < tp->n; k++) S[k] = tp->valid[k];
+        nS = tp->n_valid;
+    }
+    for (;;) {
+        int m = 0;
+        for (int k = 0; k < tp->n; k++)
+            if (S[k]) {
+                for (int a = 0; a < 3; a++) buf[3 * m + a] = (double)tp->p[k][a];
+                m++;
+            }
+        double nrm[3], d, lam[3];
+        orc_tls_fit(buf, m, nrm, &d, lam);
+        f->rounds++;
+        for (int a = 0; a < 3; a++) f->lam[a] = lam[a];
+        f->plane64[0] = nrm[0]; f->plane64[1] = nrm[1]; f->plane64[2] = nrm[2]; f->plane64[3] = d;
+        for (int a = 0; a < 3; a++) f->plane[a] = (float)nrm[a];
+        f->plane[3] = (float)d;
+        if (lam[1] >= 0.999e-12 * lam[2] && lam[1] <= 1.001e-12 * lam[2]) f->borderline = 1;
+        if (!(lam[1] > 1e-12 * lam[2])) { f->degenerate = 1; nI = 0; break; }
+        nI = inliers(tp, f->plane, prm->fit_thr_m, I, &f->borderline);
+        int same = (nI == nS);
+        for (int k = 0; k < tp->n && same; k++) same = (I[k] == S[k]);
+        if (same || f->rounds == prm->max_refits + 1 || nI < 3) break;
+        memcpy(S, I, sizeof(int) * tp->n);
+        nS = nI;
+    }
+    f->n_inlier = nI;
+    if (!f->degenerate && nI >= need_inliers(prm, tp->n_valid)) f->status = ORC_FIT_OK;
+}
+
 static int params_ok(const orc_sensor *s, const orc_params *p) {
     return sensor_ok(s) && p && p->tile_h >= 1 && p->tile_w >= 1 &&
            p->tile_h * p->tile_w <= MAX_TILE_PX && p->tile_h <= 255 && p->tile_w <= 255 &&
@@ -402,6 +465,23 @@ int orc_fit_tiles(const orc_sensor *s, const orc_params *prm, const float *range
     for (int t = 0; t < TW * TH; t++) {
         tile_gather(s, prm, &T, range, t, tp);
         fit_one(prm, tp, &out[t]);
+    }
+    free(tp);
+    tables_free(&T);
+    return ORC_OK;
+}
+
+int orc_fit_tiles_seeded(const orc_sensor *s, const orc_params *prm, const float *range, const float *prop,
+                         float skip_logit, orc_tile_fit *out) {
+    if (!params_ok(s, prm) || !prop) return ORC_ERR_ARG;
+    tables_t T;
+    tables_make(s, &T);
+    const int TW = (s->cols + prm->tile_w - 1) / prm->tile_w;
+    const int TH = (s->rows + prm->tile_h - 1) / prm->tile_h;
+    tile_px_t *tp = malloc(sizeof(tile_px_t));
+    for (int t = 0; t < TW * TH; t++) {
+        tile_gather(s, prm, &T, range, t, tp);
+        fit_one_seeded(prm, tp, prop + 5 * (size_t)t, skip_logit, &out[t]);
     }
     free(tp);
     tables_free(&T);

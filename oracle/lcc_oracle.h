@@ -86,6 +86,11 @@ int orc_tls_fit(const double *p, int n, double normal[3], double *d, double lam[
 /* Per-tile iterative plane fit of the whole image (tiles row-major). */
 int orc_fit_tiles(const orc_sensor *s, const orc_params *prm, const float *range, orc_tile_fit *out);
 
+/* Per-tile fit seeded by a proposal per tile, prop[t] = (logit, v0, v1, v2,
+ * d_rel) (the learned proposal; not in the paper): see fit_one_seeded. */
+int orc_fit_tiles_seeded(const orc_sensor *s, const orc_params *prm, const float *range, const float *prop,
+                         float skip_logit, orc_tile_fit *out);
+
 /* Temporal test of every P tile against the warped K planes (Sec. III-D). */
 int orc_temporal_tiles(const orc_sensor *s, const orc_params *prm, const float *range,
                        const float *kf_table, const double pose[16], orc_tile_temporal *out);

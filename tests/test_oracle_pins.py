@@ -449,3 +449,71 @@ def test_pframe_decode_error_and_kf_table_from_stream(cfg2_seq):
         dec, _, _ = O.decode(s, bits, kft2, seq.poses[f])
         m = rng > 0
         assert np.abs(dec[m] - rng[m]).max() <= 0.01 + 1e-5
+
+
+# ------------------------------------------------------------------ seeded fit (learned proposal) --
+
+def _planar_tile_with_outlier():
+    s = O.Sensor(8, 256, -10.0, 10.0, 80.0)
+    p = O.params(tile_h=8, tile_w=8, min_inlier_frac=0.75)
+    u = O.beams(s).astype(np.float64)
+    n = np.array([0.9, 0.3, 0.1])
+    n /= np.linalg.norm(n)
+    d = 12.0
+    dots = u @ n
+    rng_img = np.where(dots > 0.1, d / np.where(dots > 0.1, dots, 1), 0).astype(np.float32)
+    tc = int(np.argmax(dots[3])) // 8
+    rng_img[3, 8 * tc + 2] -= 0.5
+    return s, p, rng_img, tc, n, d
+
+
+def _prop_for(s, p, rng_img, n, d, logit=3.0):
+    """Proposal rows for every tile: the true plane relative to each tile's anchor."""
+    u = O.beams(s)
+    nt = O.n_tiles(s, p)
+    TC = (s.cols + p.tile_w - 1) // p.tile_w
+    prop = np.zeros((nt, 5), np.float32)
+    for t in range(nt):
+        tr, tc = divmod(t, TC)
+        r = rng_img[tr * 8:(tr + 1) * 8, tc * 8:(tc + 1) * 8]
+        idx = np.flatnonzero(r.reshape(-1) > 0)
+        if len(idx) == 0:
+            continue
+        k = idx[0]
+        pa = (r.reshape(-1)[k] * u[tr * 8:(tr + 1) * 8, tc * 8:(tc + 1) * 8].reshape(-1, 3)[k]).astype(np.float32)
+        prop[t] = [logit, n[0], n[1], n[2], d - float(np.dot(n, pa))]
+    return prop
+
+
+def test_seeded_fit_starts_from_the_proposal_inliers():
+    """A proposal equal to the true plane puts the moved pixel out of the first set, so the
+    seeded fit reaches the plain fit's final plane in one round (the plain fit needs two)."""
+    s, p, rng_img, tc, n, d = _planar_tile_with_outlier()
+    plain = O.fit_tiles(s, p, rng_img)
+    prop = _prop_for(s, p, rng_img, n, d)
+    seeded = O.fit_tiles_seeded(s, p, rng_img, prop, -2.944)
+    assert plain[tc]["rounds"] >= 2 and seeded[tc]["rounds"] == 1
+    assert seeded[tc]["status"] == O.FIT_OK and seeded[tc]["n_inlier"] == plain[tc]["n_inlier"] == 63
+    assert np.abs(seeded[tc]["plane"] - np.array([*n, d], np.float32)).max() < 2e-5
+    # the proposal's sign does not matter (the plane is made canonical, d >= 0)
+    neg = prop.copy()
+    neg[:, 1:] = -neg[:, 1:]
+    seeded2 = O.fit_tiles_seeded(s, p, rng_img, neg, -2.944)
+    assert seeded2.tobytes() == seeded.tobytes()
+
+
+def test_seeded_fit_skip_and_fallbacks():
+    s, p, rng_img, tc, n, d = _planar_tile_with_outlier()
+    plain = O.fit_tiles(s, p, rng_img)
+    has = plain["n_valid"] >= 3
+    # below the skip logit: no fit at all
+    prop = _prop_for(s, p, rng_img, n, d, logit=-5.0)
+    skipped = O.fit_tiles_seeded(s, p, rng_img, prop, -2.944)
+    assert (skipped["status"][has] == O.FIT_FAIL).all() and (skipped["rounds"] == 0).all()
+    # a zero normal, or a plane with fewer than 3 pixels near it, falls back to the plain fit
+    zero = np.zeros((O.n_tiles(s, p), 5), np.float32)
+    zero[:, 0] = 3.0
+    assert O.fit_tiles_seeded(s, p, rng_img, zero, -2.944).tobytes() == plain.tobytes()
+    far = _prop_for(s, p, rng_img, n, d)
+    far[:, 4] += 5.0
+    assert O.fit_tiles_seeded(s, p, rng_img, far, -2.944).tobytes() == plain.tobytes()
