@@ -86,7 +86,8 @@ typedef struct {
     uint32_t ahead_mask;      /* run pre-test bits: bit j = this tile passes the plane of tile t-1-j */
     uint8_t status;           /* 0 empty, 1 fit failed, 2 fit ok, 3 temporal */
     uint8_t rounds;           /* spatial plane fits performed */
-    uint8_t flags;            /* bit0 borderline, bit1 degenerate scatter, bit2 temporal tested */
+    uint8_t flags;            /* bit0 borderline, bit1 degenerate scatter, bit2 temporal tested,
+                                 bit3 not fitted: its proposal logit was below the skip logit */
     uint8_t n_valid;          /* valid pixels */
     uint8_t n_inlier;         /* inliers of the final spatial (or temporal) plane */
     uint8_t t_rounds;         /* temporal offset fits */
@@ -146,6 +147,19 @@ lcc_status lcc_encode_pframe(lcc_ctx *ctx, const lcc_keyframe *kf, const double 
                              const float *d_pts, int64_t n, uint8_t *d_out, uint64_t cap,
                              uint64_t *out_bytes);
 
+/* A key frame whose tile fits are seeded by proposals (the learned proposal of
+ * the net below; not in the paper).  d_prop: device float [num_tiles][5] per
+ * tile: planarity logit, unnormalised normal (3), plane offset relative to the
+ * tile's anchor (its first valid pixel's point r*u).  A tile whose logit is
+ * below skip_logit is not fitted (raw-coded); otherwise its first round fits
+ * the pixels within fit_thr_m of the proposed plane (all valid pixels if fewer
+ * than 3), and the rounds and the FIT rule are the plain ones, so every plane
+ * that codes points passes the same threshold test.  Streams are in the same
+ * format and decode with lcc_decode. */
+lcc_status lcc_encode_keyframe_seeded(lcc_ctx *ctx, const float *d_pts, int64_t n, const float *d_prop,
+                                      float skip_logit, lcc_keyframe *kf, uint8_t *d_out, uint64_t cap,
+                                      uint64_t *out_bytes);
+
 /* Batched: nframes P frames against one key frame in one launch per kernel.
  * poses: nframes x 16 doubles; d_pts, n, d_out, cap: per-frame host arrays;
  * out_bytes: nframes uint64 (host or device).  nframes <= max_batch. */
@@ -199,6 +213,45 @@ lcc_status lcc_tile_records(lcc_ctx *ctx, int32_t frame, lcc_tile_info *h_out, i
  * "decode_px", "range_export".  Returns the number of entries written. */
 lcc_status lcc_set_profiling(lcc_ctx *ctx, int32_t enable);
 int32_t lcc_kernel_times(lcc_ctx *ctx, char names[][16], int64_t *launches, double *ms, int32_t cap);
+
+/* ---- Learned tile proposal (net over 8x8 tiles) ----
+ *
+ * Not in the paper: a small convolutional net that predicts, for an 8x8 tile,
+ * whether the iterative fit will succeed (logit) and the plane it will find
+ * (unnormalised normal, offset relative to the tile's anchor = its first valid
+ * pixel's point), used by lcc_encode_keyframe_seeded.  Input per tile: 64
+ * pixels x 4 bf16 channels (r - r_anchor, p - p_anchor in metres, empty
+ * pixels 0), pixel-major.  Layers: conv3x3 pad 1 4->32, 32->64, 64->64 (ReLU),
+ * global average pool, linear 64->32 (ReLU), linear 32->5.  BF16 operands,
+ * FP32 accumulation on the tensor cores.  Parameters: one fp32 vector of
+ * lcc_net_num_params() = 58853 values, in the order W1[32,4,3,3], b1,
+ * W2[64,32,3,3], b2, W3[64,64,3,3], b3, F1[32,64], c1, F2[5,32], c2.
+ * Loss (mean over tiles): BCE-with-logits(logit, fit) + fit*(1 - |n_hat.n|) +
+ * fit*SmoothL1_0.02m(offset - d_rel); labels per tile (fit, n[3], d_rel).
+ * Optimiser: Adam (0.9, 0.999, 1e-8) on fp32 master weights. */
+typedef struct lcc_net lcc_net;
+
+int64_t lcc_net_num_params(void);
+/* max_tiles bounds the tiles of one lcc_net_gradient / lcc_net_train_step call
+ * (activations are kept per tile, about 41 KB each).  Synchronous. */
+lcc_status lcc_net_create(lcc_net **out, const float *h_params, int64_t max_tiles, void *cuda_stream);
+void lcc_net_destroy(lcc_net *net);
+lcc_status lcc_net_get_params(lcc_net *net, float *h_params);   /* synchronous */
+lcc_status lcc_net_set_params(lcc_net *net, const float *h_params);   /* also resets Adam moments */
+/* Bins a frame (slot 0 of a context with 8x8 tiles) and writes the net input of
+ * every tile: d_x [num_tiles][64][4] bf16 (as uint16), d_anchor [num_tiles]
+ * float4 (anchor x, y, z, r).  LCC_ERR_UNSUPPORTED for other tile shapes. */
+lcc_status lcc_net_tile_inputs(lcc_ctx *ctx, const float *d_pts, int64_t n, uint16_t *d_x, float *d_anchor);
+/* Outputs d_out [ntiles][5] fp32 (logit, v[3], d_rel), on the net's stream. */
+lcc_status lcc_net_forward(lcc_net *net, const uint16_t *d_x, int64_t ntiles, float *d_out);
+/* Gradient of the mean loss w.r.t. the parameters (d_grad: 58853 fp32, may be
+ * NULL) and the loss (d_loss: 1 fp32, may be NULL); d_labels [ntiles][5]. */
+lcc_status lcc_net_gradient(lcc_net *net, const uint16_t *d_x, const float *d_labels, int64_t ntiles, float *d_grad,
+                            float *d_loss);
+/* One training step: gradient, then an Adam update with learning rate lr at
+ * step number `step` (from 1, for the bias correction). */
+lcc_status lcc_net_train_step(lcc_net *net, const uint16_t *d_x, const float *d_labels, int64_t ntiles, float lr,
+                              int32_t step, float *d_loss);
 
 /* ---- Range image without a context or any allocation ----
  *

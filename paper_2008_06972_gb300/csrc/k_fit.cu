@@ -397,15 +397,40 @@ __device__ __forceinline__ void queue_push(bool push, uint32_t item, uint32_t *q
 // Spatial rounds of one tile from its current state (o.rounds fits done, the
 // last plane in o.plane).  Runs at most `max_rounds` more fits; returns true
 // if the tile is finished (o fully updated), false if it needs more rounds.
+//
+// With a proposal (logit, v, d_rel) for the tile, the first round starts from
+// the pixels within the threshold of the proposed plane instead of all valid
+// pixels (fewer than 3 of them: all valid pixels), and a logit below the skip
+// threshold leaves the tile unfitted (flag 8).  The proposed plane is formed by
+// fixed fp32 operations: n = v / sqrtf(fma sum of squares), d = d_rel + n.anchor
+// (fma chain), both negated when d < 0.
 template <int TH_, int TW_>
-__device__ __forceinline__ bool spatial_rounds(const TileView<TH_, TW_> &tv, RecOut &o, int max_rounds) {
+__device__ __forceinline__ bool spatial_rounds(const TileView<TH_, TW_> &tv, RecOut &o, int max_rounds,
+                                               const float *prop = nullptr, float skip_logit = 0.f) {
     const Geometry &g = tv.g;
     Mask S, I;
     int nS;
     bool border = false;
     if (o.rounds == 0) {
-        S = tv.V;
-        nS = tv.nv;
+        nS = 0;
+        if (prop) {
+            const float lg = prop[0], v0 = prop[1], v1 = prop[2], v2 = prop[3], drel = prop[4];
+            if (lg < skip_logit) {
+                o.flags |= 8;
+                return true;
+            }
+            const float nn = sqrtf(fmaf(v0, v0, fmaf(v1, v1, __fmul_rn(v2, v2))));
+            if (nn > 0.0f && isfinite(nn)) {
+                float4 pl = make_float4(__fdiv_rn(v0, nn), __fdiv_rn(v1, nn), __fdiv_rn(v2, nn), 0.f);
+                pl.w = __fadd_rn(drel, fmaf(pl.x, tv.ax, fmaf(pl.y, tv.ay, __fmul_rn(pl.z, tv.az))));
+                if (pl.w < 0.0f) pl = make_float4(-pl.x, -pl.y, -pl.z, -pl.w);
+                nS = tv.inliers(pl, S, border);
+            }
+        }
+        if (nS < 3) {
+            S = tv.V;
+            nS = tv.nv;
+        }
     } else {
         nS = tv.inliers(o.plane, S, border);   // the set the previous plane kept
     }
@@ -507,12 +532,13 @@ __global__ void __launch_bounds__(kFitThreads) k_fit_first(Geometry g, Scratch s
     if (b.kind == 1 && tv.nv > 0 && b.kf[f]) temporal_test<TH_, TW_>(tv, ps.m[f], b.kf[f], o);
     bool queued = false;
     if (o.status != S_TEMPORAL && tv.nv >= 3) {
+        const float *prop = b.prop[f] ? b.prop[f] + 5 * (size_t)t : nullptr;
         if (!kQueue) {
-            spatial_rounds<TH_, TW_>(tv, o, g.R + 1);
+            spatial_rounds<TH_, TW_>(tv, o, g.R + 1, prop, b.skip_logit);
         } else if (b.kind == 1) {
             queued = true;   // P-frame spatial fallback from its first round, in the dense pass
         } else {
-            queued = !spatial_rounds<TH_, TW_>(tv, o, 1);
+            queued = !spatial_rounds<TH_, TW_>(tv, o, 1, prop, b.skip_logit);
         }
     }
     if (kQueue) queue_push(queued, ((uint32_t)f << 26) | (uint32_t)t, s.queue, s.qcount);

@@ -1,0 +1,888 @@
+// Learned tile proposal (not in the paper): a small convolutional net that
+// predicts, for an 8x8 tile of the range image, whether the iterative plane
+// fit of Sec. III-C will succeed and which plane it will find.  The encoder
+// uses the prediction to seed its first fit round and to skip tiles that will
+// not fit; the plain fit still decides every plane that codes points.
+//
+// Net: input 4x8x8 (r - r_anchor, p - p_anchor; empty pixels 0), conv3x3
+// pad 1 4->32, ReLU, 32->64, ReLU, 64->64, ReLU, global average pool, linear
+// 64->32, ReLU, linear 32->5 (logit, normal, offset relative to the anchor).
+// BF16 operands with FP32 accumulation on the tensor cores (mma.sync
+// m16n8k16); activations are rounded to BF16 after each ReLU, as are the
+// pooled vector, the hidden head activation and the convolution gradients.
+//
+// Every convolution is an implicit GEMM per tile: rows are the 64 pixels,
+// columns the output channels, and the reduction runs over the 9 taps x input
+// channels, read straight from a zero-bordered 10x10 copy of the tile in
+// shared memory (no im2col buffer).  The input-gradient convolution is the
+// same GEMM with the taps mirrored and the weights transposed.  The weight
+// gradient is a GEMM over (tile, pixel) split across CTAs.
+#include <cuda_bf16.h>
+
+#include <algorithm>
+#include <cstdint>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "lcc.h"
+#include "lcc_ctx.cuh"
+
+using namespace lcc;
+using namespace lcc::api;
+
+namespace {
+
+typedef __nv_bfloat16 bf16;
+
+constexpr int kPX = 64;                       // pixels of an 8x8 tile
+constexpr int C0 = 4, C1 = 32, C2 = 64, C3 = 64, HID = 32, NOUT = 5;
+constexpr int XS = 8;                         // padded channel stride of the input copy
+constexpr int A1S = C1 + 8, A2S = C2 + 8;     // padded channel strides (bank spread)
+constexpr int K1 = 48, B1S = 56;              // conv1: 9 taps x 4 channels = 36, padded to 3 k-steps
+constexpr int B2S = 9 * C1 + 8, B3S = 9 * C2 + 8, BTS = 9 * 64 + 8;
+constexpr int kNetWarps = 4;
+
+// offsets of the flat parameter vector: W1[32,4,3,3] b1 W2[64,32,3,3] b2 W3[64,64,3,3] b3 F1[32,64] c1 F2[5,32] c2
+constexpr int OW1 = 0, OB1 = OW1 + C1 * C0 * 9, OW2 = OB1 + C1, OB2 = OW2 + C2 * C1 * 9, OW3 = OB2 + C2,
+              OB3 = OW3 + C3 * C2 * 9, OF1 = OB3 + C3, OC1 = OF1 + HID * C3, OF2 = OC1 + HID, OC2 = OF2 + NOUT * HID,
+              NPARAM = OC2 + NOUT;
+static_assert(NPARAM == 58853, "parameter count");
+
+// device copies of the weights in the layouts the kernels read
+struct NetDev {
+    const float *theta;                      // fp32 master parameters
+    bf16 *B1f, *B2f, *B3f;                   // forward GEMM B: [cout][k = tap*cin + ci]
+    bf16 *B2t, *B3t;                         // input-gradient GEMM B: [ci][k = tap*cout + co]
+    float *F1b, *F2b;                        // head weights rounded to bf16 values
+};
+
+struct NetAct {                              // per-tile training activations
+    bf16 *a1, *a2, *a3;                      // [T][64][C]
+    float *g, *h, *o;                        // [T][64], [T][32], [T][5]
+    float *da3c;                             // [T][64]  dL/d(pooled input) / 64
+    bf16 *dz1t, *dz2t, *dz3t;                // [T][C][64] pre-activation gradients, pixel-contiguous
+};
+
+__device__ __forceinline__ uint32_t ld32(const bf16 *p) { return *reinterpret_cast<const uint32_t *>(p); }
+__device__ __forceinline__ void st32(bf16 *p, float a, float b) {
+    __nv_bfloat162 v = __floats2bfloat162_rn(a, b);
+    *reinterpret_cast<__nv_bfloat162 *>(p) = v;
+}
+__device__ __forceinline__ float bfround(float x) { return __bfloat162float(__float2bfloat16_rn(x)); }
+__device__ __forceinline__ uint32_t pack2(bf16 lo, bf16 hi) {
+    return (uint32_t)__bfloat16_as_ushort(lo) | ((uint32_t)__bfloat16_as_ushort(hi) << 16);
+}
+
+__device__ __forceinline__ void mma_bf16(float c[4], uint32_t a0, uint32_t a1, uint32_t a2, uint32_t a3, uint32_t b0,
+                                         uint32_t b1) {
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+        "{%0,%1,%2,%3};\n"
+        : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+        : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
+}
+
+// One warp: acc[m][n] (+)= conv of the padded tile `ap` (stride AS) with B rows
+// [COUT][9*CIN (+pad)] (stride BS).  Row block m covers pixels 16m..16m+15,
+// i.e. tile rows 2m and 2m+1; lane (g, t) holds rows g and g+8 of each block.
+// MIRROR reads tap (ky, kx) at offset (2-ky, 2-kx): the input-gradient form.
+template <int CIN, int COUT, int AS, int BS, bool MIRROR>
+__device__ __forceinline__ void conv_tile(const bf16 *ap, const bf16 *B, float (&acc)[4][COUT / 8][4]) {
+    const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+#pragma unroll 1
+    for (int tap = 0; tap < 9; tap++) {
+        const int ky = tap / 3, kx = tap % 3;
+        const int oy = MIRROR ? 2 - ky : ky, ox = MIRROR ? 2 - kx : kx;
+#pragma unroll 1
+        for (int c0 = 0; c0 < CIN; c0 += 16) {
+            uint32_t a[4][4];
+#pragma unroll
+            for (int m = 0; m < 4; m++) {
+                const bf16 *r0 = ap + ((2 * m + oy) * 10 + g + ox) * AS + c0 + 2 * t;
+                const bf16 *r1 = r0 + 10 * AS;
+                a[m][0] = ld32(r0);
+                a[m][1] = ld32(r1);
+                a[m][2] = ld32(r0 + 8);
+                a[m][3] = ld32(r1 + 8);
+            }
+#pragma unroll
+            for (int n = 0; n < COUT / 8; n++) {
+                const bf16 *bp = B + (n * 8 + g) * BS + tap * CIN + c0 + 2 * t;
+                const uint32_t b0 = ld32(bp), b1 = ld32(bp + 8);
+#pragma unroll
+                for (int m = 0; m < 4; m++) mma_bf16(acc[m][n], a[m][0], a[m][1], a[m][2], a[m][3], b0, b1);
+            }
+        }
+    }
+}
+
+template <int COUT>
+__device__ __forceinline__ void zero_acc(float (&acc)[4][COUT / 8][4]) {
+#pragma unroll
+    for (int m = 0; m < 4; m++)
+#pragma unroll
+        for (int n = 0; n < COUT / 8; n++) acc[m][n][0] = acc[m][n][1] = acc[m][n][2] = acc[m][n][3] = 0.f;
+}
+
+// conv1: the reduction index is k = tap*4 + ci (36 real values, 3 k-steps of 16).
+__device__ __forceinline__ uint32_t conv1_a(const bf16 *xp, int py, int px, int k) {
+    if (k >= 36) return 0u;
+    const int tap = k >> 2, ci = k & 3;
+    return ld32(xp + ((py + tap / 3) * 10 + px + tap % 3) * XS + ci);
+}
+
+__device__ __forceinline__ void conv1_tile(const bf16 *xp, const bf16 *B1, float (&acc)[4][C1 / 8][4]) {
+    const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+#pragma unroll
+    for (int ks = 0; ks < K1 / 16; ks++) {
+        const int k0 = ks * 16 + 2 * t;
+        uint32_t a[4][4];
+#pragma unroll
+        for (int m = 0; m < 4; m++) {
+            a[m][0] = conv1_a(xp, 2 * m, g, k0);
+            a[m][1] = conv1_a(xp, 2 * m + 1, g, k0);
+            a[m][2] = conv1_a(xp, 2 * m, g, k0 + 8);
+            a[m][3] = conv1_a(xp, 2 * m + 1, g, k0 + 8);
+        }
+#pragma unroll
+        for (int n = 0; n < C1 / 8; n++) {
+            const bf16 *bp = B1 + (n * 8 + g) * B1S + ks * 16 + 2 * t;
+            const uint32_t b0 = ld32(bp), b1 = ld32(bp + 8);
+#pragma unroll
+            for (int m = 0; m < 4; m++) mma_bf16(acc[m][n], a[m][0], a[m][1], a[m][2], a[m][3], b0, b1);
+        }
+    }
+}
+
+// bias + ReLU + bf16 into the next padded copy (and the training copy [64][C] when given)
+template <int COUT, int AS>
+__device__ __forceinline__ void epilogue(float (&acc)[4][COUT / 8][4], const float *bias, bf16 *ap_next,
+                                         bf16 *act_out) {
+    const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+#pragma unroll
+    for (int m = 0; m < 4; m++)
+#pragma unroll
+        for (int n = 0; n < COUT / 8; n++) {
+            const int co = n * 8 + 2 * t;
+            const float b0 = __ldg(bias + co), b1 = __ldg(bias + co + 1);
+#pragma unroll
+            for (int h = 0; h < 2; h++) {
+                const int py = 2 * m + h, px = g;
+                const float v0 = fmaxf(acc[m][n][2 * h] + b0, 0.f), v1 = fmaxf(acc[m][n][2 * h + 1] + b1, 0.f);
+                if (ap_next) st32(ap_next + ((py + 1) * 10 + px + 1) * AS + co, v0, v1);
+                if (act_out) st32(act_out + (py * 8 + px) * COUT + co, v0, v1);
+            }
+        }
+}
+
+// ------------------------------------------------------------------ weights --
+
+__global__ void k_net_prep(NetDev nd) {
+    const float *th = nd.theta;
+    const int n1 = C1 * B1S, n2 = C2 * B2S, n3 = C3 * B3S, n2t = C1 * BTS, n3t = C2 * BTS;
+    const int total = n1 + n2 + n3 + n2t + n3t + HID * C3 + NOUT * HID;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < total; i += gridDim.x * blockDim.x) {
+        int j = i;
+        if (j < n1) {
+            const int co = j / B1S, k = j % B1S;
+            nd.B1f[j] = __float2bfloat16_rn(k < 36 ? th[OW1 + co * 36 + (k & 3) * 9 + (k >> 2)] : 0.f);
+            continue;
+        }
+        j -= n1;
+        if (j < n2) {
+            const int co = j / B2S, k = j % B2S;
+            nd.B2f[j] = __float2bfloat16_rn(k < 9 * C1 ? th[OW2 + co * 9 * C1 + (k % C1) * 9 + k / C1] : 0.f);
+            continue;
+        }
+        j -= n2;
+        if (j < n3) {
+            const int co = j / B3S, k = j % B3S;
+            nd.B3f[j] = __float2bfloat16_rn(k < 9 * C2 ? th[OW3 + co * 9 * C2 + (k % C2) * 9 + k / C2] : 0.f);
+            continue;
+        }
+        j -= n3;
+        if (j < n2t) {   // conv2 input gradient: rows ci (32), k = tap*64 + co
+            const int ci = j / BTS, k = j % BTS;
+            nd.B2t[j] = __float2bfloat16_rn(k < 9 * C2 ? th[OW2 + (k % C2) * 9 * C1 + ci * 9 + k / C2] : 0.f);
+            continue;
+        }
+        j -= n2t;
+        if (j < n3t) {   // conv3 input gradient: rows ci (64), k = tap*64 + co
+            const int ci = j / BTS, k = j % BTS;
+            nd.B3t[j] = __float2bfloat16_rn(k < 9 * C3 ? th[OW3 + (k % C3) * 9 * C2 + ci * 9 + k / C3] : 0.f);
+            continue;
+        }
+        j -= n3t;
+        if (j < HID * C3) {
+            nd.F1b[j] = bfround(th[OF1 + j]);
+            continue;
+        }
+        j -= HID * C3;
+        nd.F2b[j] = bfround(th[OF2 + j]);
+    }
+}
+
+// ------------------------------------------------------------------ inputs --
+
+// Net input of every 8x8 tile of the frame binned into slot 0; the range image
+// is reset to empty afterwards.  One warp per tile, two pixels per lane.
+__global__ void k_net_inputs(Geometry g, uint32_t *rimg, bf16 *x, float4 *anchor) {
+    const int lane = threadIdx.x & 31;
+    const int tile = blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5);
+    if (tile >= g.NT) return;
+    const int i0 = (tile / g.TC) * 8, j0 = (tile % g.TC) * 8;
+    float r[2], p[2][3];
+    bool v[2];
+#pragma unroll
+    for (int h = 0; h < 2; h++) {
+        const int q = lane + 32 * h, i = i0 + q / 8, j = j0 + q % 8;
+        const bool in = i < g.H && j < g.W;
+        const uint32_t bits = in ? rimg[(size_t)i * g.W + j] : kEmptyBits;
+        v[h] = bits_valid(bits);
+        r[h] = v[h] ? __uint_as_float(bits) : 0.f;
+        p[h][0] = p[h][1] = p[h][2] = 0.f;
+        if (v[h]) {
+            float ux, uy, uz;
+            beam(g, i, j, ux, uy, uz);
+            p[h][0] = __fmul_rn(r[h], ux);
+            p[h][1] = __fmul_rn(r[h], uy);
+            p[h][2] = __fmul_rn(r[h], uz);
+        }
+        if (in) rimg[(size_t)i * g.W + j] = kEmptyBits;
+    }
+    const unsigned b0 = __ballot_sync(0xffffffffu, v[0]), b1 = __ballot_sync(0xffffffffu, v[1]);
+    float ra = 0.f, pa0 = 0.f, pa1 = 0.f, pa2 = 0.f;
+    if (b0 | b1) {
+        const int first = b0 ? __ffs(b0) - 1 : 32 + __ffs(b1) - 1;
+        const int src = first & 31, hh = first >> 5;
+        ra = __shfl_sync(0xffffffffu, hh ? r[1] : r[0], src);
+        pa0 = __shfl_sync(0xffffffffu, hh ? p[1][0] : p[0][0], src);
+        pa1 = __shfl_sync(0xffffffffu, hh ? p[1][1] : p[0][1], src);
+        pa2 = __shfl_sync(0xffffffffu, hh ? p[1][2] : p[0][2], src);
+    }
+#pragma unroll
+    for (int h = 0; h < 2; h++) {
+        const int q = lane + 32 * h;
+        bf16 c[4];
+        if (v[h]) {
+            c[0] = __float2bfloat16_rn(__fsub_rn(r[h], ra));
+            c[1] = __float2bfloat16_rn(__fsub_rn(p[h][0], pa0));
+            c[2] = __float2bfloat16_rn(__fsub_rn(p[h][1], pa1));
+            c[3] = __float2bfloat16_rn(__fsub_rn(p[h][2], pa2));
+        } else {
+            c[0] = c[1] = c[2] = c[3] = __float2bfloat16_rn(0.f);
+        }
+        *reinterpret_cast<uint2 *>(x + ((size_t)tile * kPX + q) * C0) = make_uint2(pack2(c[0], c[1]), pack2(c[2], c[3]));
+    }
+    if (lane == 0) anchor[tile] = make_float4(pa0, pa1, pa2, ra);
+}
+
+// ------------------------------------------------------------------ forward --
+
+constexpr size_t kFwdWeightBytes = sizeof(bf16) * (size_t)(C1 * B1S + C2 * B2S + C3 * B3S);
+constexpr size_t kFwdWarpBytes = sizeof(bf16) * (size_t)(100 * XS + 100 * A1S + 100 * A2S) + sizeof(float) * (C3 + HID);
+constexpr size_t kFwdSmem = kFwdWeightBytes + kNetWarps * kFwdWarpBytes;
+
+// Persistent: the CTA stages the weights once, each warp runs one tile at a time.
+template <bool kTrain>
+__global__ void __launch_bounds__(kNetWarps * 32, 1) k_net_fwd(NetDev nd, const bf16 *x, long long T, float *out,
+                                                               NetAct act) {
+    extern __shared__ __align__(16) uint8_t sm[];
+    bf16 *sB1 = reinterpret_cast<bf16 *>(sm);
+    bf16 *sB2 = sB1 + C1 * B1S;
+    bf16 *sB3 = sB2 + C2 * B2S;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    uint8_t *wbase = sm + kFwdWeightBytes + warp * kFwdWarpBytes;
+    bf16 *xp = reinterpret_cast<bf16 *>(wbase);
+    bf16 *a1p = xp + 100 * XS;
+    bf16 *a2p = a1p + 100 * A1S;
+    float *gs = reinterpret_cast<float *>(a2p + 100 * A2S);
+    float *hs = gs + C3;
+    {
+        const uint4 *src[3] = {reinterpret_cast<const uint4 *>(nd.B1f), reinterpret_cast<const uint4 *>(nd.B2f),
+                               reinterpret_cast<const uint4 *>(nd.B3f)};
+        uint4 *dst[3] = {reinterpret_cast<uint4 *>(sB1), reinterpret_cast<uint4 *>(sB2), reinterpret_cast<uint4 *>(sB3)};
+        const int cnt[3] = {C1 * B1S / 8, C2 * B2S / 8, C3 * B3S / 8};
+        for (int q = 0; q < 3; q++)
+            for (int i = threadIdx.x; i < cnt[q]; i += blockDim.x) dst[q][i] = src[q][i];
+        // zero this warp's padded copies once: borders stay zero, interiors are rewritten per tile
+        uint32_t *z = reinterpret_cast<uint32_t *>(wbase);
+        for (int i = lane; i < (int)(kFwdWarpBytes / 4); i += 32) z[i] = 0u;
+    }
+    __syncthreads();
+    const float *th = nd.theta;
+    for (long long tile = (long long)blockIdx.x * kNetWarps + warp; tile < T; tile += (long long)gridDim.x * kNetWarps) {
+        // input into the padded copy (4 channels, stride 8)
+#pragma unroll
+        for (int h = 0; h < 2; h++) {
+            const int q = lane + 32 * h, py = q / 8, px = q % 8;
+            const uint2 v = *reinterpret_cast<const uint2 *>(x + ((size_t)tile * kPX + q) * C0);
+            *reinterpret_cast<uint2 *>(xp + ((py + 1) * 10 + px + 1) * XS) = v;
+        }
+        __syncwarp();
+        {
+            float acc[4][C1 / 8][4];
+            zero_acc<C1>(acc);
+            conv1_tile(xp, sB1, acc);
+            epilogue<C1, A1S>(acc, th + OB1, a1p, kTrain ? act.a1 + (size_t)tile * kPX * C1 : nullptr);
+        }
+        __syncwarp();
+        {
+            float acc[4][C2 / 8][4];
+            zero_acc<C2>(acc);
+            conv_tile<C1, C2, A1S, B2S, false>(a1p, sB2, acc);
+            epilogue<C2, A2S>(acc, th + OB2, a2p, kTrain ? act.a2 + (size_t)tile * kPX * C2 : nullptr);
+        }
+        __syncwarp();
+        {
+            float acc[4][C3 / 8][4];
+            zero_acc<C3>(acc);
+            conv_tile<C2, C3, A2S, B3S, false>(a2p, sB3, acc);
+            const int g = lane >> 2, t = lane & 3;
+            bf16 *a3 = kTrain ? act.a3 + (size_t)tile * kPX * C3 : nullptr;
+#pragma unroll
+            for (int n = 0; n < C3 / 8; n++) {
+                const int co = n * 8 + 2 * t;
+                const float b0 = __ldg(th + OB3 + co), b1 = __ldg(th + OB3 + co + 1);
+                float s0 = 0.f, s1 = 0.f;
+#pragma unroll
+                for (int m = 0; m < 4; m++)
+#pragma unroll
+                    for (int h = 0; h < 2; h++) {
+                        const float v0 = bfround(fmaxf(acc[m][n][2 * h] + b0, 0.f));
+                        const float v1 = bfround(fmaxf(acc[m][n][2 * h + 1] + b1, 0.f));
+                        s0 += v0;
+                        s1 += v1;
+                        if (a3) st32(a3 + ((2 * m + h) * 8 + g) * C3 + co, v0, v1);
+                    }
+#pragma unroll
+                for (int off = 4; off < 32; off <<= 1) {
+                    s0 += __shfl_xor_sync(0xffffffffu, s0, off);
+                    s1 += __shfl_xor_sync(0xffffffffu, s1, off);
+                }
+                if (g == 0) {
+                    gs[co] = bfround(s0 * (1.0f / kPX));
+                    gs[co + 1] = bfround(s1 * (1.0f / kPX));
+                }
+            }
+        }
+        __syncwarp();
+        // head: lane j computes hidden unit j, then the 5 outputs by warp sums
+        float y = __ldg(th + OC1 + lane);
+        for (int c = 0; c < C3; c++) y = fmaf(__ldg(nd.F1b + lane * C3 + c), gs[c], y);
+        const float hj = bfround(fmaxf(y, 0.f));
+        float o[NOUT];
+#pragma unroll
+        for (int i = 0; i < NOUT; i++) {
+            float s = __ldg(nd.F2b + i * HID + lane) * hj;
+#pragma unroll
+            for (int off = 16; off; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
+            o[i] = s + __ldg(th + OC2 + i);
+        }
+        if (lane < NOUT) out[(size_t)tile * NOUT + lane] = o[lane];
+        if (kTrain) {
+            act.h[(size_t)tile * HID + lane] = hj;
+            act.g[(size_t)tile * C3 + lane] = gs[lane];
+            act.g[(size_t)tile * C3 + lane + 32] = gs[lane + 32];
+            if (lane < NOUT) act.o[(size_t)tile * NOUT + lane] = o[lane];
+        }
+        (void)hs;
+        __syncwarp();
+    }
+}
+
+// ------------------------------------------------------------------ backward: loss and head --
+
+constexpr float kBeta = 0.02f, kNormEps = 1e-12f;
+
+// One warp per tile (persistent): loss terms, head gradients (accumulated per
+// warp, one atomic per value at the end), and dL/d(pooled) / 64 per channel.
+__global__ void __launch_bounds__(kNetWarps * 32) k_net_head_bwd(NetDev nd, const float *labels, long long T,
+                                                                  NetAct act, float *grad, float *loss) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const float invT = 1.0f / (float)T;
+    float dF1[C3], dF2[NOUT], dc1 = 0.f, dc2 = 0.f, lsum = 0.f;
+#pragma unroll
+    for (int c = 0; c < C3; c++) dF1[c] = 0.f;
+#pragma unroll
+    for (int i = 0; i < NOUT; i++) dF2[i] = 0.f;
+    for (long long tile = (long long)blockIdx.x * kNetWarps + warp; tile < T; tile += (long long)gridDim.x * kNetWarps) {
+        const float *o = act.o + (size_t)tile * NOUT;
+        const float *y = labels + (size_t)tile * NOUT;
+        const float lg = o[0], v0 = o[1], v1 = o[2], v2 = o[3], dd = o[4];
+        const float fit = y[0], n0 = y[1], n1 = y[2], n2 = y[3], drel = y[4];
+        const float s = sqrtf(v0 * v0 + v1 * v1 + v2 * v2 + kNormEps);
+        const float vn = v0 * n0 + v1 * n1 + v2 * n2;
+        const float cs = vn / s;
+        const float xd = dd - drel, ax = fabsf(xd);
+        const float sl1 = ax < kBeta ? 0.5f * xd * xd / kBeta : ax - 0.5f * kBeta;
+        const float bce = fmaxf(lg, 0.f) - fit * lg + log1pf(expf(-fabsf(lg)));
+        lsum += bce + fit * (1.f - fabsf(cs)) + fit * sl1;
+        float dout[NOUT];
+        dout[0] = (1.f / (1.f + expf(-lg)) - fit) * invT;
+        const float sg = cs > 0.f ? 1.f : (cs < 0.f ? -1.f : 0.f);
+        const float k3 = vn / (s * s * s);
+        dout[1] = -fit * sg * (n0 / s - k3 * v0) * invT;
+        dout[2] = -fit * sg * (n1 / s - k3 * v1) * invT;
+        dout[3] = -fit * sg * (n2 / s - k3 * v2) * invT;
+        dout[4] = fit * fminf(fmaxf(xd / kBeta, -1.f), 1.f) * invT;
+        const float hj = act.h[(size_t)tile * HID + lane];
+        float dh = 0.f;
+#pragma unroll
+        for (int i = 0; i < NOUT; i++) {
+            dF2[i] = fmaf(dout[i], hj, dF2[i]);
+            dh = fmaf(__ldg(nd.F2b + i * HID + lane), dout[i], dh);
+        }
+        if (lane < NOUT) dc2 += dout[lane];
+        const float dy = hj > 0.f ? dh : 0.f;
+        dc1 += dy;
+        const float *gv = act.g + (size_t)tile * C3;
+#pragma unroll
+        for (int c = 0; c < C3; c++) dF1[c] = fmaf(dy, gv[c], dF1[c]);
+        // dg[c] = sum_j F1b[j][c] dy_j: lane c and c + 32 gather the 32 hidden units
+        float dg0 = 0.f, dg1 = 0.f;
+        for (int j = 0; j < HID; j++) {
+            const float dyj = __shfl_sync(0xffffffffu, dy, j);
+            dg0 = fmaf(__ldg(nd.F1b + j * C3 + lane), dyj, dg0);
+            dg1 = fmaf(__ldg(nd.F1b + j * C3 + lane + 32), dyj, dg1);
+        }
+        act.da3c[(size_t)tile * C3 + lane] = dg0 * (1.0f / kPX);
+        act.da3c[(size_t)tile * C3 + lane + 32] = dg1 * (1.0f / kPX);
+    }
+#pragma unroll
+    for (int c = 0; c < C3; c++)
+        if (dF1[c] != 0.f) atomicAdd(grad + OF1 + lane * C3 + c, dF1[c]);
+#pragma unroll
+    for (int i = 0; i < NOUT; i++)
+        if (dF2[i] != 0.f) atomicAdd(grad + OF2 + i * HID + lane, dF2[i]);
+    if (dc1 != 0.f) atomicAdd(grad + OC1 + lane, dc1);
+    if (lane < NOUT && dc2 != 0.f) atomicAdd(grad + OC2 + lane, dc2);
+    // every lane of a warp evaluated the same tiles' loss: count it once
+    if (lane == 0 && lsum != 0.f) atomicAdd(loss, lsum * invT);
+}
+
+// ------------------------------------------------------------------ backward: convolution inputs --
+
+constexpr size_t kBwdWeightBytes = sizeof(bf16) * (size_t)(C3 * BTS + C1 * BTS);
+constexpr size_t kBwdWarpBytes = sizeof(bf16) * (size_t)(100 * A2S);
+constexpr size_t kBwdSmem = kBwdWeightBytes + kNetWarps * kBwdWarpBytes;
+
+// column sums over the 64 pixel rows of an accumulator set (bias gradients);
+// lanes with g == 0 end up holding the sums of channels 8n + 2t + {0, 1}
+template <int COUT>
+__device__ __forceinline__ void colsum_add(const float (&v)[4][COUT / 8][4], float (&bsum)[COUT / 8][2]) {
+#pragma unroll
+    for (int n = 0; n < COUT / 8; n++) {
+        float s0 = 0.f, s1 = 0.f;
+#pragma unroll
+        for (int m = 0; m < 4; m++) {
+            s0 += v[m][n][0] + v[m][n][2];
+            s1 += v[m][n][1] + v[m][n][3];
+        }
+#pragma unroll
+        for (int off = 4; off < 32; off <<= 1) {
+            s0 += __shfl_xor_sync(0xffffffffu, s0, off);
+            s1 += __shfl_xor_sync(0xffffffffu, s1, off);
+        }
+        bsum[n][0] += s0;
+        bsum[n][1] += s1;
+    }
+}
+
+// dz = bf16(da * [a > 0]) from an accumulator set: into the padded copy (for the next
+// input-gradient convolution), the pixel-contiguous global copy, and back into acc.
+template <int C, bool kPad>
+__device__ __forceinline__ void relu_grad(float (&acc)[4][C / 8][4], const bf16 *a, bf16 *pad, bf16 *dzt) {
+    const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+#pragma unroll
+    for (int m = 0; m < 4; m++)
+#pragma unroll
+        for (int n = 0; n < C / 8; n++) {
+            const int c = n * 8 + 2 * t;
+#pragma unroll
+            for (int h = 0; h < 2; h++) {
+                const int p = (2 * m + h) * 8 + g;
+                const __nv_bfloat162 av = *reinterpret_cast<const __nv_bfloat162 *>(a + p * C + c);
+                const float d0 = bfround(__bfloat162float(av.x) > 0.f ? acc[m][n][2 * h] : 0.f);
+                const float d1 = bfround(__bfloat162float(av.y) > 0.f ? acc[m][n][2 * h + 1] : 0.f);
+                acc[m][n][2 * h] = d0;
+                acc[m][n][2 * h + 1] = d1;
+                if (kPad) st32(pad + ((2 * m + h + 1) * 10 + g + 1) * A2S + c, d0, d1);
+                dzt[c * kPX + p] = __float2bfloat16_rn(d0);
+                dzt[(c + 1) * kPX + p] = __float2bfloat16_rn(d1);
+            }
+        }
+}
+
+__global__ void __launch_bounds__(kNetWarps * 32, 1) k_net_conv_bwd(NetDev nd, long long T, NetAct act, float *grad) {
+    extern __shared__ __align__(16) uint8_t sm[];
+    bf16 *sB3t = reinterpret_cast<bf16 *>(sm);
+    bf16 *sB2t = sB3t + C3 * BTS;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    bf16 *dp = reinterpret_cast<bf16 *>(sm + kBwdWeightBytes + warp * kBwdWarpBytes);
+    {
+        const uint4 *s3 = reinterpret_cast<const uint4 *>(nd.B3t), *s2 = reinterpret_cast<const uint4 *>(nd.B2t);
+        uint4 *d3 = reinterpret_cast<uint4 *>(sB3t), *d2 = reinterpret_cast<uint4 *>(sB2t);
+        for (int i = threadIdx.x; i < C3 * BTS / 8; i += blockDim.x) d3[i] = s3[i];
+        for (int i = threadIdx.x; i < C1 * BTS / 8; i += blockDim.x) d2[i] = s2[i];
+        uint32_t *z = reinterpret_cast<uint32_t *>(dp);
+        for (int i = lane; i < (int)(kBwdWarpBytes / 4); i += 32) z[i] = 0u;
+    }
+    __syncthreads();
+    float db3[C3 / 8][2], db2[C2 / 8][2], db1[C1 / 8][2];
+#pragma unroll
+    for (int n = 0; n < C3 / 8; n++) db3[n][0] = db3[n][1] = db2[n][0] = db2[n][1] = 0.f;
+#pragma unroll
+    for (int n = 0; n < C1 / 8; n++) db1[n][0] = db1[n][1] = 0.f;
+    const int g = lane >> 2, t = lane & 3;
+    for (long long tile = (long long)blockIdx.x * kNetWarps + warp; tile < T; tile += (long long)gridDim.x * kNetWarps) {
+        const bf16 *a1 = act.a1 + (size_t)tile * kPX * C1;
+        const bf16 *a2 = act.a2 + (size_t)tile * kPX * C2;
+        const bf16 *a3 = act.a3 + (size_t)tile * kPX * C3;
+        const float *da3 = act.da3c + (size_t)tile * C3;
+        {   // dz3 from the pooled gradient and the ReLU mask
+            float acc[4][C3 / 8][4];
+#pragma unroll
+            for (int m = 0; m < 4; m++)
+#pragma unroll
+                for (int n = 0; n < C3 / 8; n++) {
+                    const int c = n * 8 + 2 * t;
+                    acc[m][n][0] = acc[m][n][2] = da3[c];
+                    acc[m][n][1] = acc[m][n][3] = da3[c + 1];
+                }
+            relu_grad<C3, true>(acc, a3, dp, act.dz3t + (size_t)tile * C3 * kPX);
+            colsum_add<C3>(acc, db3);
+        }
+        __syncwarp();
+        {   // da2 = conv3 input gradient; dz2
+            float acc[4][C2 / 8][4];
+            zero_acc<C2>(acc);
+            conv_tile<C3, C2, A2S, BTS, true>(dp, sB3t, acc);
+            __syncwarp();
+            relu_grad<C2, true>(acc, a2, dp, act.dz2t + (size_t)tile * C2 * kPX);
+            colsum_add<C2>(acc, db2);
+        }
+        __syncwarp();
+        {   // da1 = conv2 input gradient; dz1
+            float acc[4][C1 / 8][4];
+            zero_acc<C1>(acc);
+            conv_tile<C2, C1, A2S, BTS, true>(dp, sB2t, acc);
+            relu_grad<C1, false>(acc, a1, nullptr, act.dz1t + (size_t)tile * C1 * kPX);
+            colsum_add<C1>(acc, db1);
+        }
+        __syncwarp();
+    }
+    if (g == 0) {
+#pragma unroll
+        for (int n = 0; n < C3 / 8; n++)
+#pragma unroll
+            for (int j = 0; j < 2; j++) {
+                atomicAdd(grad + OB3 + n * 8 + 2 * t + j, db3[n][j]);
+                atomicAdd(grad + OB2 + n * 8 + 2 * t + j, db2[n][j]);
+            }
+#pragma unroll
+        for (int n = 0; n < C1 / 8; n++)
+#pragma unroll
+            for (int j = 0; j < 2; j++) atomicAdd(grad + OB1 + n * 8 + 2 * t + j, db1[n][j]);
+    }
+}
+
+// ------------------------------------------------------------------ backward: weight gradients --
+
+// dW[co][k = tap*CIN + ci] = sum over tiles and pixels of dz[co][p] * a_pad[p + tap][ci].
+// CTA (x: a chunk of KCH reduction columns, y: a slice of tiles); each warp runs its
+// own tiles of the slice with the tile's input staged in a padded shared copy.
+template <int CIN, int COUT, int KCH, int AS>
+__global__ void __launch_bounds__(kNetWarps * 32) k_net_wgrad(const bf16 *a, const bf16 *dzt, long long T, float *grad,
+                                                               int wofs) {
+    extern __shared__ __align__(16) uint8_t sm[];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+    bf16 *ap = reinterpret_cast<bf16 *>(sm) + warp * 100 * AS;
+    for (int i = lane; i < 100 * AS / 2; i += 32) reinterpret_cast<uint32_t *>(ap)[i] = 0u;
+    __syncwarp();
+    const int k0 = blockIdx.x * KCH;
+    constexpr int MT = COUT / 16, NT = KCH / 8;
+    float acc[MT][NT][4];
+#pragma unroll
+    for (int m = 0; m < MT; m++)
+#pragma unroll
+        for (int n = 0; n < NT; n++) acc[m][n][0] = acc[m][n][1] = acc[m][n][2] = acc[m][n][3] = 0.f;
+    // column k -> (tap, ci) of the padded copy, per lane for its two B columns
+    int koff[NT];
+#pragma unroll
+    for (int n = 0; n < NT; n++) {
+        const int k = k0 + n * 8 + g;
+        koff[n] = k < 9 * CIN ? ((k / CIN) / 3 * 10 + (k / CIN) % 3) * AS + k % CIN : -1;
+    }
+    for (long long tile = (long long)blockIdx.y * kNetWarps + warp; tile < T; tile += (long long)gridDim.y * kNetWarps) {
+        const bf16 *at = a + (size_t)tile * kPX * CIN;
+        for (int i = lane; i < kPX * CIN / 2; i += 32) {
+            const int p = (2 * i) / CIN, c = (2 * i) % CIN;
+            *reinterpret_cast<uint32_t *>(ap + ((p / 8 + 1) * 10 + p % 8 + 1) * AS + c) =
+                reinterpret_cast<const uint32_t *>(at)[i];
+        }
+        __syncwarp();
+        const bf16 *dz = dzt + (size_t)tile * COUT * kPX;
+#pragma unroll
+        for (int ks = 0; ks < kPX / 16; ks++) {
+            const int p0 = ks * 16 + 2 * t;     // this lane's pixel pairs: p0, p0+1 and p0+8, p0+9
+            uint32_t b[NT][2];
+#pragma unroll
+            for (int n = 0; n < NT; n++) {
+#pragma unroll
+                for (int hh = 0; hh < 2; hh++) {
+                    const int pa = p0 + 8 * hh;
+                    if (koff[n] < 0) {
+                        b[n][hh] = 0u;
+                    } else {
+                        const bf16 lo = ap[koff[n] + ((pa / 8) * 10 + pa % 8) * AS];
+                        const bf16 hi = ap[koff[n] + (((pa + 1) / 8) * 10 + (pa + 1) % 8) * AS];
+                        b[n][hh] = pack2(lo, hi);
+                    }
+                }
+            }
+#pragma unroll
+            for (int m = 0; m < MT; m++) {
+                const bf16 *r0 = dz + (m * 16 + g) * kPX + p0;
+                const bf16 *r1 = r0 + 8 * kPX;
+                const uint32_t a0 = ld32(r0), a1 = ld32(r1), a2 = ld32(r0 + 8), a3 = ld32(r1 + 8);
+#pragma unroll
+                for (int n = 0; n < NT; n++) mma_bf16(acc[m][n], a0, a1, a2, a3, b[n][0], b[n][1]);
+            }
+        }
+        __syncwarp();
+    }
+#pragma unroll
+    for (int m = 0; m < MT; m++)
+#pragma unroll
+        for (int n = 0; n < NT; n++)
+#pragma unroll
+            for (int q = 0; q < 4; q++) {
+                const int co = m * 16 + g + (q >> 1) * 8, k = k0 + n * 8 + 2 * t + (q & 1);
+                if (k < 9 * CIN && acc[m][n][q] != 0.f)
+                    atomicAdd(grad + wofs + co * 9 * CIN + (k % CIN) * 9 + k / CIN, acc[m][n][q]);
+            }
+}
+
+// ------------------------------------------------------------------ optimiser --
+
+__global__ void k_net_adam(float *theta, const float *grad, float *m, float *v, int n, float lr, float bc1, float bc2) {
+    const float b1 = 0.9f, b2 = 0.999f, eps = 1e-8f;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const float gi = grad[i];
+        const float mi = b1 * m[i] + (1.f - b1) * gi;
+        const float vi = b2 * v[i] + (1.f - b2) * gi * gi;
+        m[i] = mi;
+        v[i] = vi;
+        theta[i] -= lr * (mi / bc1) / (sqrtf(vi / bc2) + eps);
+    }
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------ C ABI --
+
+struct lcc_net {
+    cudaStream_t stream = nullptr;
+    int64_t max_tiles = 0;
+    int sms = 0;
+    float *theta = nullptr, *grad = nullptr, *m = nullptr, *v = nullptr, *loss = nullptr;
+    NetDev nd{};
+    NetAct act{};
+    void *wbuf = nullptr, *abuf = nullptr;
+};
+
+namespace {
+
+lcc_status net_prep(lcc_net *net) {
+    k_net_prep<<<152, 256, 0, net->stream>>>(net->nd);
+    return cudaGetLastError() == cudaSuccess ? LCC_OK : LCC_ERR_CUDA;
+}
+
+template <typename K>
+lcc_status smem_attr(K kernel, size_t bytes) {
+    return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes) == cudaSuccess
+               ? LCC_OK
+               : LCC_ERR_CUDA;
+}
+
+constexpr size_t wgrad_smem(int as) { return sizeof(bf16) * (size_t)kNetWarps * 100 * as; }
+
+int grid_for(const lcc_net *net, int64_t tiles) {
+    const int64_t want = (tiles + kNetWarps - 1) / kNetWarps;
+    return (int)std::max<int64_t>(1, std::min<int64_t>(want, net->sms));
+}
+
+lcc_status forward(lcc_net *net, const uint16_t *d_x, int64_t ntiles, float *d_out, bool train) {
+    const bf16 *x = reinterpret_cast<const bf16 *>(d_x);
+    if (train) {
+        k_net_fwd<true><<<grid_for(net, ntiles), kNetWarps * 32, kFwdSmem, net->stream>>>(net->nd, x, ntiles, d_out,
+                                                                                        net->act);
+    } else {
+        k_net_fwd<false><<<grid_for(net, ntiles), kNetWarps * 32, kFwdSmem, net->stream>>>(net->nd, x, ntiles, d_out,
+                                                                                         net->act);
+    }
+    return cudaGetLastError() == cudaSuccess ? LCC_OK : LCC_ERR_CUDA;
+}
+
+lcc_status backward(lcc_net *net, const uint16_t *d_x, const float *d_labels, int64_t ntiles) {
+    cudaStream_t st = net->stream;
+    LCC_CUDA(cudaMemsetAsync(net->grad, 0, sizeof(float) * NPARAM, st));
+    LCC_CUDA(cudaMemsetAsync(net->loss, 0, sizeof(float), st));
+    lcc_status s = forward(net, d_x, ntiles, net->act.o, true);
+    if (s != LCC_OK) return s;
+    k_net_head_bwd<<<grid_for(net, ntiles), kNetWarps * 32, 0, st>>>(net->nd, d_labels, ntiles, net->act, net->grad,
+                                                                     net->loss);
+    k_net_conv_bwd<<<grid_for(net, ntiles), kNetWarps * 32, kBwdSmem, st>>>(net->nd, ntiles, net->act, net->grad);
+    const int slices = (int)std::max<int64_t>(1, std::min<int64_t>((ntiles + kNetWarps - 1) / kNetWarps, 64));
+    k_net_wgrad<C2, C3, 64, A2S><<<dim3(9 * C2 / 64, slices), kNetWarps * 32, wgrad_smem(A2S), st>>>(
+        net->act.a2, net->act.dz3t, ntiles, net->grad, OW3);
+    k_net_wgrad<C1, C2, 32, A1S><<<dim3(9 * C1 / 32, slices), kNetWarps * 32, wgrad_smem(A1S), st>>>(
+        net->act.a1, net->act.dz2t, ntiles, net->grad, OW2);
+    k_net_wgrad<C0, C1, 40, XS><<<dim3(1, slices), kNetWarps * 32, wgrad_smem(XS), st>>>(
+        reinterpret_cast<const bf16 *>(d_x), net->act.dz1t, ntiles, net->grad, OW1);
+    return cudaGetLastError() == cudaSuccess ? LCC_OK : LCC_ERR_CUDA;
+}
+
+}  // namespace
+
+extern "C" {
+
+lcc_status lcc_net_create(lcc_net **out, const float *h_params, int64_t max_tiles, void *cuda_stream) {
+    if (!out || !h_params || max_tiles < 1 || max_tiles > ((int64_t)1 << 24)) return LCC_ERR_INVALID_ARG;
+    *out = nullptr;
+    int dev = 0;
+    cudaDeviceProp prop;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaGetDeviceProperties(&prop, dev) != cudaSuccess)
+        return LCC_ERR_NO_DEVICE;
+    if (!(prop.major == 10 && prop.minor == 3)) return LCC_ERR_NO_DEVICE;
+    lcc_net *net = new (std::nothrow) lcc_net();
+    if (!net) return LCC_ERR_CUDA;
+    net->stream = (cudaStream_t)cuda_stream;
+    net->max_tiles = max_tiles;
+    net->sms = prop.multiProcessorCount;
+    const size_t wb[] = {sizeof(float) * NPARAM * 4 + 256,   // theta, grad, m, v
+                         sizeof(bf16) * (C1 * B1S + C2 * B2S + C3 * B3S + C1 * BTS + C3 * BTS),
+                         sizeof(float) * (HID * C3 + NOUT * HID), 256};
+    size_t wtotal = 0;
+    for (size_t b : wb) wtotal += align256(b);
+    const size_t T = (size_t)max_tiles;
+    const size_t ab[] = {sizeof(bf16) * T * kPX * C1, sizeof(bf16) * T * kPX * C2, sizeof(bf16) * T * kPX * C3,
+                         sizeof(float) * T * C3,      sizeof(float) * T * HID,      sizeof(float) * T * NOUT,
+                         sizeof(float) * T * C3,      sizeof(bf16) * T * C1 * kPX,  sizeof(bf16) * T * C2 * kPX,
+                         sizeof(bf16) * T * C3 * kPX};
+    size_t atotal = 0;
+    for (size_t b : ab) atotal += align256(b);
+    if (cudaMalloc(&net->wbuf, wtotal) != cudaSuccess || cudaMalloc(&net->abuf, atotal) != cudaSuccess) {
+        lcc_net_destroy(net);
+        return LCC_ERR_CUDA;
+    }
+    char *w = (char *)net->wbuf;
+    net->theta = (float *)w;
+    net->grad = net->theta + NPARAM;
+    net->m = net->grad + NPARAM;
+    net->v = net->m + NPARAM;
+    w += align256(wb[0]);
+    net->nd.theta = net->theta;
+    net->nd.B1f = (bf16 *)w;
+    net->nd.B2f = net->nd.B1f + C1 * B1S;
+    net->nd.B3f = net->nd.B2f + C2 * B2S;
+    net->nd.B2t = net->nd.B3f + C3 * B3S;
+    net->nd.B3t = net->nd.B2t + C1 * BTS;
+    w += align256(wb[1]);
+    net->nd.F1b = (float *)w;
+    net->nd.F2b = net->nd.F1b + HID * C3;
+    w += align256(wb[2]);
+    net->loss = (float *)w;
+    char *a = (char *)net->abuf;
+    void **slots[] = {(void **)&net->act.a1, (void **)&net->act.a2, (void **)&net->act.a3, (void **)&net->act.g,
+                      (void **)&net->act.h,  (void **)&net->act.o,  (void **)&net->act.da3c, (void **)&net->act.dz1t,
+                      (void **)&net->act.dz2t, (void **)&net->act.dz3t};
+    for (int i = 0; i < 10; i++) {
+        *slots[i] = a;
+        a += align256(ab[i]);
+    }
+    if (smem_attr(k_net_fwd<true>, kFwdSmem) != LCC_OK || smem_attr(k_net_fwd<false>, kFwdSmem) != LCC_OK ||
+        smem_attr(k_net_conv_bwd, kBwdSmem) != LCC_OK ||
+        smem_attr(k_net_wgrad<C2, C3, 64, A2S>, wgrad_smem(A2S)) != LCC_OK ||
+        cudaMemcpy(net->theta, h_params, sizeof(float) * NPARAM, cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemset(net->m, 0, sizeof(float) * 2 * NPARAM) != cudaSuccess || net_prep(net) != LCC_OK ||
+        cudaDeviceSynchronize() != cudaSuccess) {
+        lcc_net_destroy(net);
+        return LCC_ERR_CUDA;
+    }
+    *out = net;
+    return LCC_OK;
+}
+
+void lcc_net_destroy(lcc_net *net) {
+    if (!net) return;
+    cudaStreamSynchronize(net->stream);
+    cudaFree(net->wbuf);
+    cudaFree(net->abuf);
+    delete net;
+}
+
+int64_t lcc_net_num_params(void) { return NPARAM; }
+
+lcc_status lcc_net_get_params(lcc_net *net, float *h_params) {
+    if (!net || !h_params) return LCC_ERR_INVALID_ARG;
+    LCC_CUDA(cudaMemcpyAsync(h_params, net->theta, sizeof(float) * NPARAM, cudaMemcpyDeviceToHost, net->stream));
+    LCC_CUDA(cudaStreamSynchronize(net->stream));
+    return LCC_OK;
+}
+
+lcc_status lcc_net_set_params(lcc_net *net, const float *h_params) {
+    if (!net || !h_params) return LCC_ERR_INVALID_ARG;
+    LCC_CUDA(cudaMemcpyAsync(net->theta, h_params, sizeof(float) * NPARAM, cudaMemcpyHostToDevice, net->stream));
+    LCC_CUDA(cudaMemsetAsync(net->m, 0, sizeof(float) * 2 * NPARAM, net->stream));
+    lcc_status s = net_prep(net);
+    if (s != LCC_OK) return s;
+    LCC_CUDA(cudaStreamSynchronize(net->stream));
+    return LCC_OK;
+}
+
+lcc_status lcc_net_tile_inputs(lcc_ctx *c, const float *d_pts, int64_t n, uint16_t *d_x, float *d_anchor) {
+    if (!c || !d_x || !d_anchor || c->g.th != 8 || c->g.tw != 8) return !c ? LCC_ERR_INVALID_ARG : LCC_ERR_UNSUPPORTED;
+    if (((uintptr_t)d_x & 7u) || ((uintptr_t)d_anchor & 15u)) return LCC_ERR_INVALID_ARG;
+    if (n < 0 || (n > 0 && (!d_pts || ((uintptr_t)d_pts & 15u)))) return LCC_ERR_INVALID_ARG;
+    const int slot = 0;
+    lcc_status st = bin_frames(c, 1, &slot, &d_pts, &n);
+    if (st != LCC_OK) return st;
+    const int wpb = 8;
+    k_net_inputs<<<(c->g.NT + wpb - 1) / wpb, wpb * 32, 0, c->stream>>>(c->g, c->s.rimg, reinterpret_cast<bf16 *>(d_x),
+                                                                         reinterpret_cast<float4 *>(d_anchor));
+    return cudaGetLastError() == cudaSuccess ? LCC_OK : LCC_ERR_CUDA;
+}
+
+lcc_status lcc_net_forward(lcc_net *net, const uint16_t *d_x, int64_t ntiles, float *d_out) {
+    if (!net || !d_x || !d_out || ntiles < 0 || ((uintptr_t)d_x & 7u)) return LCC_ERR_INVALID_ARG;
+    if (ntiles == 0) return LCC_OK;
+    return forward(net, d_x, ntiles, d_out, false);
+}
+
+lcc_status lcc_net_gradient(lcc_net *net, const uint16_t *d_x, const float *d_labels, int64_t ntiles, float *d_grad,
+                            float *d_loss) {
+    if (!net || !d_x || !d_labels || ntiles < 1 || ntiles > net->max_tiles || ((uintptr_t)d_x & 7u))
+        return LCC_ERR_INVALID_ARG;
+    lcc_status s = backward(net, d_x, d_labels, ntiles);
+    if (s != LCC_OK) return s;
+    if (d_grad)
+        LCC_CUDA(cudaMemcpyAsync(d_grad, net->grad, sizeof(float) * NPARAM, cudaMemcpyDeviceToDevice, net->stream));
+    if (d_loss) LCC_CUDA(cudaMemcpyAsync(d_loss, net->loss, sizeof(float), cudaMemcpyDeviceToDevice, net->stream));
+    return LCC_OK;
+}
+
+lcc_status lcc_net_train_step(lcc_net *net, const uint16_t *d_x, const float *d_labels, int64_t ntiles, float lr,
+                              int32_t step, float *d_loss) {
+    if (!net || step < 1 || !(lr > 0)) return LCC_ERR_INVALID_ARG;
+    lcc_status s = lcc_net_gradient(net, d_x, d_labels, ntiles, nullptr, d_loss);
+    if (s != LCC_OK) return s;
+    const float bc1 = 1.f - powf(0.9f, (float)step), bc2 = 1.f - powf(0.999f, (float)step);
+    k_net_adam<<<64, 256, 0, net->stream>>>(net->theta, net->grad, net->m, net->v, NPARAM, lr, bc1, bc2);
+    if (cudaGetLastError() != cudaSuccess) return LCC_ERR_CUDA;
+    return net_prep(net);
+}
+
+}  // extern "C"

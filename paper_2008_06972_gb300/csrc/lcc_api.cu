@@ -106,8 +106,10 @@ lcc_status latched(lcc_ctx *c) {
 
 void prepare_batch(Batch &b, Poses &p, int kind, int nframes, const int *slots, uint8_t *const *d_out,
                    const uint64_t *cap, const double *poses, const float4 *const *kf, float4 *const *kf_out,
-                   unsigned long long *const *nbytes_out) {
+                   unsigned long long *const *nbytes_out, const float *const *prop = nullptr,
+                   float skip_logit = 0.f) {
     memset(&b, 0, sizeof(b));
+    b.skip_logit = skip_logit;
     b.nframes = nframes;
     b.kind = kind;
     for (int f = 0; f < nframes; f++) {
@@ -117,6 +119,7 @@ void prepare_batch(Batch &b, Poses &p, int kind, int nframes, const int *slots, 
         b.kf[f] = kf ? kf[f] : nullptr;
         b.kf_out[f] = kf_out ? kf_out[f] : nullptr;
         b.nbytes_out[f] = nbytes_out ? nbytes_out[f] : nullptr;
+        b.prop[f] = prop ? prop[f] : nullptr;
     }
     memset(&p, 0, sizeof(p));
     if (poses)
@@ -134,11 +137,11 @@ lcc_status encode_tail(lcc_ctx *c, const Batch &b) {
 
 lcc_status encode_batch(lcc_ctx *c, int kind, int nframes, const int *slots, uint8_t *const *d_out,
                         const uint64_t *cap, const double *poses, const float4 *const *kf, float4 *const *kf_out,
-                        unsigned long long *const *nbytes_out) {
+                        unsigned long long *const *nbytes_out, const float *const *prop, float skip_logit) {
     if (nframes <= 0) return LCC_OK;
     Batch b;
     Poses p;
-    prepare_batch(b, p, kind, nframes, slots, d_out, cap, poses, kf, kf_out, nbytes_out);
+    prepare_batch(b, p, kind, nframes, slots, d_out, cap, poses, kf, kf_out, nbytes_out, prop, skip_logit);
     LCC_LAUNCH(c, 1, launch_fit(c->g, c->s, b, p, c->stream));
     return encode_tail(c, b);
 }
@@ -444,6 +447,23 @@ lcc_status lcc_encode_keyframe(lcc_ctx *c, const float *d_pts, int64_t n, lcc_ke
     if ((st = bin_frames(c, 1, &slot, &d_pts, &n)) != LCC_OK) return st;
     float4 *kfo = kf ? kf->planes : nullptr;
     if ((st = encode_batch(c, 0, 1, &slot, &d_out, &cap, nullptr, nullptr, &kfo)) != LCC_OK) return st;
+    c->last_nframes = 1;
+    return copy_bytes(c, 1, &slot, out_bytes);
+}
+
+lcc_status lcc_encode_keyframe_seeded(lcc_ctx *c, const float *d_pts, int64_t n, const float *d_prop,
+                                      float skip_logit, lcc_keyframe *kf, uint8_t *d_out, uint64_t cap,
+                                      uint64_t *out_bytes) {
+    if (!c || !d_prop || ((uintptr_t)d_prop & 3u) || !(skip_logit == skip_logit)) return LCC_ERR_INVALID_ARG;
+    if (kf && kf->ctx != c) return LCC_ERR_INVALID_ARG;
+    lcc_status st = check_frames(c, 1, &d_pts, &n, &d_out, &cap);
+    if (st != LCC_OK) return st;
+    const int slot = 0;
+    if ((st = bin_frames(c, 1, &slot, &d_pts, &n)) != LCC_OK) return st;
+    float4 *kfo = kf ? kf->planes : nullptr;
+    if ((st = encode_batch(c, 0, 1, &slot, &d_out, &cap, nullptr, nullptr, &kfo, nullptr, &d_prop, skip_logit)) !=
+        LCC_OK)
+        return st;
     c->last_nframes = 1;
     return copy_bytes(c, 1, &slot, out_bytes);
 }

@@ -74,10 +74,12 @@ lcc_status latched(lcc_ctx *c);
 lcc_status bin_frames(lcc_ctx *c, int nframes, const int *slots, const float *const *d_pts, const int64_t *n);
 // Fit, merge, scan and pack frames already binned into slots[f].  kf[f] (P frames) is the key-frame
 // plane table frame f is coded against; kf_out[f] (key frames) receives frame f's coding planes;
-// nbytes_out[f], when given, receives frame f's stream size in device memory.
+// nbytes_out[f], when given, receives frame f's stream size in device memory; prop[f], when given,
+// seeds frame f's tile fits (with skip_logit).
 lcc_status encode_batch(lcc_ctx *c, int kind, int nframes, const int *slots, uint8_t *const *d_out,
                         const uint64_t *cap, const double *poses, const float4 *const *kf, float4 *const *kf_out,
-                        unsigned long long *const *nbytes_out = nullptr);
+                        unsigned long long *const *nbytes_out = nullptr, const float *const *prop = nullptr,
+                        float skip_logit = 0.f);
 lcc_status check_frames(lcc_ctx *c, int nframes, const float *const *d_pts, const int64_t *n,
                         uint8_t *const *d_out, const uint64_t *cap);
 

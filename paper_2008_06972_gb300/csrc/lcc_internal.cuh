@@ -141,6 +141,8 @@ struct Batch {
     const float4 *kf[kMaxBatch];   // per frame: key-frame planes (P frames) or NULL
     float4 *kf_out[kMaxBatch];     // per frame: key-frame plane table to fill (K frames) or NULL
     unsigned long long *nbytes_out[kMaxBatch];  // per frame: extra copy of the stream size, or NULL
+    const float *prop[kMaxBatch];  // per frame: fit proposals [NT][5] (logit, v, d_rel), or NULL
+    float skip_logit;              // tiles whose proposal logit is below this are not fitted
 };
 
 struct Poses {

@@ -101,6 +101,7 @@ def load(path: str = LIB_PATH):
         "lcc_encode_keyframe": (i32, [vp, vp, i64, vp, vp, u64, vp]),
         "lcc_encode_pframe": (i32, [vp, vp, vp, vp, i64, vp, u64, vp]),
         "lcc_encode_pframes": (i32, [vp, vp, i32, vp, vp, vp, vp, vp, vp]),
+        "lcc_encode_keyframe_seeded": (i32, [vp, vp, i64, vp, ctypes.c_float, vp, vp, u64, vp]),
         "lcc_encode_sequence": (i32, [vp, i32, i32, vp, vp, vp, vp, vp, vp, vp]),
         "lcc_encode_sequence_host": (i32, [vp, i32, i32, vp, vp, vp, vp, vp, vp]),
         "lcc_keyframe_from_stream": (i32, [vp, vp, u64, vp]),
@@ -111,6 +112,15 @@ def load(path: str = LIB_PATH):
         "lcc_set_profiling": (i32, [vp, i32]),
         "lcc_kernel_times": (i32, [vp, vp, vp, vp, i32]),
         "lcc_range_image_static": (i32, [vp, vp, i64, vp, vp, vp]),
+        "lcc_net_num_params": (i64, []),
+        "lcc_net_create": (i32, [vp, vp, i64, vp]),
+        "lcc_net_destroy": (None, [vp]),
+        "lcc_net_get_params": (i32, [vp, vp]),
+        "lcc_net_set_params": (i32, [vp, vp]),
+        "lcc_net_tile_inputs": (i32, [vp, vp, i64, vp, vp]),
+        "lcc_net_forward": (i32, [vp, vp, i64, vp]),
+        "lcc_net_gradient": (i32, [vp, vp, vp, i64, vp, vp]),
+        "lcc_net_train_step": (i32, [vp, vp, vp, i64, ctypes.c_float, i32, vp]),
         "lcc_plan_create": (i32, [vp, i32, vp, i32, vp]),
         "lcc_plan_update": (i32, [vp, i32, vp]),
         "lcc_plan_encode": (i32, [vp]),
@@ -134,9 +144,11 @@ def exported_symbols() -> list[str]:
     """Entry points this binding expects liblcc.so to export."""
     return ["lcc_status_string", "lcc_default_params", "lcc_create", "lcc_destroy", "lcc_max_encoded_bytes",
             "lcc_num_tiles", "lcc_tables", "lcc_range_image", "lcc_keyframe_create", "lcc_keyframe_free",
-            "lcc_encode_keyframe", "lcc_encode_pframe", "lcc_encode_pframes", "lcc_encode_sequence",
+            "lcc_encode_keyframe", "lcc_encode_keyframe_seeded", "lcc_encode_pframe", "lcc_encode_pframes", "lcc_encode_sequence",
             "lcc_encode_sequence_host", "lcc_keyframe_from_stream", "lcc_decode", "lcc_sync", "lcc_last_stats",
-            "lcc_tile_records", "lcc_set_profiling", "lcc_kernel_times", "lcc_range_image_static", "lcc_plan_create", "lcc_plan_update",
+            "lcc_tile_records", "lcc_set_profiling", "lcc_kernel_times", "lcc_range_image_static", "lcc_net_num_params", "lcc_net_create", "lcc_net_destroy",
+            "lcc_net_get_params", "lcc_net_set_params", "lcc_net_tile_inputs", "lcc_net_forward", "lcc_net_gradient",
+            "lcc_net_train_step", "lcc_plan_create", "lcc_plan_update",
             "lcc_plan_encode", "lcc_plan_capture", "lcc_plan_replay", "lcc_plan_sync", "lcc_plan_get_info",
             "lcc_plan_destroy", "lcc_autotune"]
 
@@ -255,6 +267,12 @@ class Context:
     def lcc_encode_keyframe(self, d_pts, n: int, kf: Keyframe | None, d_out, cap: int, out_bytes):
         _check(self.lib.lcc_encode_keyframe(self.h, _ptr(d_pts), n, kf.h if kf else None, _ptr(d_out), cap,
                                             _ptr(out_bytes)), "lcc_encode_keyframe")
+
+    def lcc_encode_keyframe_seeded(self, d_pts, n: int, d_prop, skip_logit: float, kf: Keyframe | None, d_out,
+                                   cap: int, out_bytes):
+        _check(self.lib.lcc_encode_keyframe_seeded(self.h, _ptr(d_pts), n, _ptr(d_prop), skip_logit,
+                                                   kf.h if kf else None, _ptr(d_out), cap, _ptr(out_bytes)),
+               "lcc_encode_keyframe_seeded")
 
     def lcc_encode_pframe(self, kf: Keyframe, pose: np.ndarray, d_pts, n: int, d_out, cap: int, out_bytes):
         pose = np.ascontiguousarray(pose, dtype=np.float64).reshape(16)
@@ -429,3 +447,56 @@ def autotune(sensor_, base: lcc_params, key_index: int, poses, d_pts: list, n: l
     rows = [{k: getattr(res[i], k) for k, _ in lcc_tune_result._fields_ if k != "reserved"}
             for i in range(min(nres.value, 64))]
     return best, rows
+
+
+class Net:
+    """The learned tile proposal net (lcc_net_*): fp32 master parameters on the device."""
+
+    def __init__(self, params: np.ndarray, max_tiles: int, stream=None):
+        self.lib = load()
+        params = np.ascontiguousarray(params, dtype=np.float32)
+        assert params.size == self.lib.lcc_net_num_params()
+        sp = stream.cuda_stream if stream is not None and hasattr(stream, "cuda_stream") else stream
+        h = ctypes.c_void_p()
+        _check(self.lib.lcc_net_create(ctypes.byref(h), params.ctypes.data, max_tiles, sp), "lcc_net_create")
+        self.h = h
+        self.max_tiles = max_tiles
+
+    @staticmethod
+    def num_params() -> int:
+        return int(load().lcc_net_num_params())
+
+    def params(self) -> np.ndarray:
+        out = np.zeros(self.num_params(), np.float32)
+        _check(self.lib.lcc_net_get_params(self.h, out.ctypes.data), "lcc_net_get_params")
+        return out
+
+    def set_params(self, params: np.ndarray):
+        params = np.ascontiguousarray(params, dtype=np.float32)
+        _check(self.lib.lcc_net_set_params(self.h, params.ctypes.data), "lcc_net_set_params")
+
+    def forward(self, d_x, ntiles: int, d_out):
+        _check(self.lib.lcc_net_forward(self.h, _ptr(d_x), ntiles, _ptr(d_out)), "lcc_net_forward")
+
+    def gradient(self, d_x, d_labels, ntiles: int, d_grad=None, d_loss=None):
+        _check(self.lib.lcc_net_gradient(self.h, _ptr(d_x), _ptr(d_labels), ntiles, _ptr(d_grad), _ptr(d_loss)),
+               "lcc_net_gradient")
+
+    def train_step(self, d_x, d_labels, ntiles: int, lr: float, step: int, d_loss=None):
+        _check(self.lib.lcc_net_train_step(self.h, _ptr(d_x), _ptr(d_labels), ntiles, lr, step, _ptr(d_loss)),
+               "lcc_net_train_step")
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.lcc_net_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def net_tile_inputs(ctx: "Context", d_pts, n: int, d_x, d_anchor):
+    _check(load().lcc_net_tile_inputs(ctx.h, _ptr(d_pts), n, _ptr(d_x), _ptr(d_anchor)), "lcc_net_tile_inputs")

@@ -1,0 +1,228 @@
+"""The learned tile proposal on the GPU against the oracle (oracle/net.py, oracle fit_tiles_seeded).
+
+- tile inputs: bit-exact (fp32 differences rounded to BF16 on both sides);
+- forward outputs and parameter gradients: BF16 operands with FP32 accumulation against the
+  oracle's BF16 operands with FP64 accumulation; a BF16 activation can round to the other
+  neighbour when the two sums straddle a rounding boundary, so the bar is a relative error
+  (per output, per gradient block) rather than equality;
+- the seeded fit: the same two-layer parity as the plain fit (decisions identical except on
+  borderline tiles, planes within 1e-5, the stream equal to the oracle's packing of the GPU
+  planes)."""
+from __future__ import annotations
+
+import numpy as np
+import pytest
+
+import oracle as O
+import synth
+from oracle import net as N
+from tests import harness as H
+from tests.test_gpu_parity import _compare_spatial
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+SKIP_LOGIT = -2.944   # sigma(-2.944) = 0.05
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    from paper_2008_06972_gb300 import lcc
+    lcc.load()
+
+
+@pytest.fixture(scope="module")
+def frame():
+    seq = synth.sequence_cfg2()
+    return seq.sensor, seq.frames[seq.key_index]
+
+
+def _params(seed):
+    P = N.unflatten(N.init_params(seed))
+    rng = np.random.default_rng(seed + 1)
+    for k in ("b1", "b2", "b3", "c1", "c2"):
+        P[k][:] = rng.normal(0, 0.05, P[k].shape)
+    return N.flatten(P).astype(np.float32)
+
+
+def _gpu_inputs(sensor, pts):
+    from paper_2008_06972_gb300 import lcc
+    c = H.ctx(sensor, tile_h=8, tile_w=8)
+    nt = c.num_tiles
+    x = torch.zeros((nt, 64, 4), dtype=torch.int16, device="cuda")
+    anc = torch.zeros((nt, 4), dtype=torch.float32, device="cuda")
+    lcc.net_tile_inputs(c, H.to_dev(pts), len(pts), x, anc)
+    assert c.lcc_sync() == lcc.OK
+    return c, x, anc
+
+
+def _as_float(x16: np.ndarray) -> np.ndarray:
+    return (x16.astype(np.uint16).astype(np.uint32) << 16).view(np.float32)
+
+
+def _oracle_x(xg: np.ndarray) -> np.ndarray:
+    """GPU input layout [T][64][4] -> oracle layout [T][4][8][8]."""
+    return _as_float(xg).reshape(-1, 8, 8, 4).transpose(0, 3, 1, 2).astype(np.float64)
+
+
+def _sample(nv, k, seed):
+    rng = np.random.default_rng(seed)
+    has = np.flatnonzero(nv >= 3)
+    emp = np.flatnonzero(nv < 3)
+    return np.sort(np.concatenate([rng.choice(has, k - 4, replace=False), emp[:4]]))
+
+
+def test_tile_inputs_bit_exact(frame):
+    sensor, pts = frame
+    c, x, anc = _gpu_inputs(sensor, pts)
+    s = O.sensor(sensor)
+    rng, _, _ = O.range_image(s, pts)
+    X, anchors, nv = N.tile_inputs(rng, O.beams(s))
+    xg = x.cpu().numpy()
+    assert np.array_equal(_as_float(xg).reshape(-1, 8, 8, 4).transpose(0, 3, 1, 2),
+                          N.bf16(X).astype(np.float32))
+    ag = anc.cpu().numpy()
+    assert np.array_equal(ag[:, :3].view(np.uint32), anchors.view(np.uint32))
+
+
+def test_forward_matches_oracle(frame):
+    from paper_2008_06972_gb300 import lcc
+    sensor, pts = frame
+    c, x, _ = _gpu_inputs(sensor, pts)
+    s = O.sensor(sensor)
+    rng, _, _ = O.range_image(s, pts)
+    _, _, nv = N.tile_inputs(rng, O.beams(s))
+    idx = _sample(nv, 96, 1)
+    theta = _params(21)
+    net = lcc.Net(theta, max_tiles=256)
+    xs = x[torch.from_numpy(idx).cuda()].contiguous()
+    out = torch.zeros((len(idx), 5), dtype=torch.float32, device="cuda")
+    net.forward(xs, len(idx), out)
+    torch.cuda.synchronize()
+    og = out.cpu().numpy()
+    oo, _ = N.forward(theta.astype(np.float64), _oracle_x(xs.cpu().numpy()), rounding=True)
+    err = np.abs(og - oo)
+    assert (err <= 1e-2 * (1.0 + np.abs(oo))).all(), err.max()
+    assert np.median(err) <= 1e-3
+    # the full frame runs too (persistent kernel over 2048 tiles)
+    full = torch.zeros((c.num_tiles, 5), dtype=torch.float32, device="cuda")
+    net.forward(x, c.num_tiles, full)
+    torch.cuda.synchronize()
+    assert np.array_equal(full.cpu().numpy()[idx], og)
+
+
+def _labels(nt, seed):
+    rng = np.random.default_rng(seed)
+    y = np.zeros((nt, 5), np.float32)
+    y[:, 0] = rng.integers(0, 2, nt)
+    n = rng.normal(0, 1, (nt, 3))
+    y[:, 1:4] = n / np.linalg.norm(n, axis=1, keepdims=True)
+    y[:, 4] = rng.normal(0, 0.03, nt)
+    y[y[:, 0] == 0, 1:] = 0
+    return y
+
+
+def test_gradient_matches_oracle(frame):
+    from paper_2008_06972_gb300 import lcc
+    sensor, pts = frame
+    _, x, _ = _gpu_inputs(sensor, pts)
+    s = O.sensor(sensor)
+    rng, _, _ = O.range_image(s, pts)
+    _, _, nv = N.tile_inputs(rng, O.beams(s))
+    idx = _sample(nv, 64, 2)
+    theta = _params(33)
+    net = lcc.Net(theta, max_tiles=64)
+    xs = x[torch.from_numpy(idx).cuda()].contiguous()
+    y = _labels(len(idx), 5)
+    yd = torch.from_numpy(y).cuda()
+    grad = torch.zeros(N.N_PARAMS, dtype=torch.float32, device="cuda")
+    loss = torch.zeros(1, dtype=torch.float32, device="cuda")
+    net.gradient(xs, yd, len(idx), grad, loss)
+    torch.cuda.synchronize()
+    gg = grad.cpu().numpy().astype(np.float64)
+    lo, go, _ = N.loss_and_grad(theta.astype(np.float64), _oracle_x(xs.cpu().numpy()), y.astype(np.float64),
+                                rounding=True)
+    assert abs(float(loss.item()) - lo) <= 1e-3 * max(1.0, abs(lo))
+    o = 0
+    for name, shp in N.SHAPES:
+        n = int(np.prod(shp))
+        a, b = gg[o:o + n], go[o:o + n]
+        rel = np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-12)
+        assert rel <= 3e-2, (name, rel)
+        o += n
+    # an Adam step from that gradient (step 1: theta - lr * g / (|g| + eps))
+    net.train_step(xs, yd, len(idx), 1e-3, 1)
+    t1 = net.params().astype(np.float64)
+    net.set_params(theta)
+    grad2 = torch.zeros_like(grad)
+    net.gradient(xs, yd, len(idx), grad2, None)
+    torch.cuda.synchronize()
+    g2 = grad2.cpu().numpy().astype(np.float64)
+    ref, _, _ = N.adam(theta.astype(np.float64), g2, np.zeros_like(g2), np.zeros_like(g2), 1, 1e-3)
+    big = np.abs(g2) > 1e-6   # where |g| is tiny the atomics' summation order decides the sign
+    assert np.abs(t1 - ref)[big].max() <= 1e-6
+
+
+def test_training_lowers_the_loss(frame):
+    """Labels from the plain GPU encoder (fit flag and plane per 8x8 tile); Adam on one frame."""
+    from paper_2008_06972_gb300 import lcc
+    sensor, pts = frame
+    c, x, anc = _gpu_inputs(sensor, pts)
+    bits, recs = H.encode_keyframe(c, pts)
+    planes, ok = H.gpu_planes(recs)
+    y = N.labels(ok, planes, anc.cpu().numpy()[:, :3]).astype(np.float32)
+    nt = c.num_tiles
+    net = lcc.Net(N.init_params(5).astype(np.float32), max_tiles=nt)
+    yd = torch.from_numpy(y).cuda()
+    loss = torch.zeros(1, dtype=torch.float32, device="cuda")
+    hist = []
+    for step in range(1, 151):
+        net.train_step(x, yd, nt, 2e-3, step, loss)
+        if step in (1, 150):
+            torch.cuda.synchronize()
+            hist.append(float(loss.item()))
+    assert np.isfinite(hist).all() and hist[1] < 0.7 * hist[0], hist
+
+
+def test_seeded_keyframe_parity(frame):
+    """Proposals built from the plain fit (some perturbed, some below the skip logit): the
+    GPU's seeded fit agrees with the oracle's seeded fit and its stream with the oracle's
+    packing of the GPU planes."""
+    from paper_2008_06972_gb300 import lcc
+    sensor, pts = frame
+    s = O.sensor(sensor)
+    p = O.params(8, 8, 0.05, 0.02)
+    c, x, anc = _gpu_inputs(sensor, pts)
+    _, recs = H.encode_keyframe(c, pts)
+    planes, ok = H.gpu_planes(recs)
+    y = N.labels(ok, planes, anc.cpu().numpy()[:, :3])
+    rng_ = np.random.default_rng(8)
+    prop = np.zeros((c.num_tiles, 5), np.float32)
+    prop[:, 0] = np.where(ok, 3.0, -1.0)
+    prop[:, 1:4] = y[:, 1:4] + rng_.normal(0, 0.02, (c.num_tiles, 3))
+    prop[:, 4] = y[:, 4] + rng_.normal(0, 0.01, c.num_tiles)
+    prop[rng_.random(c.num_tiles) < 0.1, 0] = -4.0          # skipped
+    prop[rng_.random(c.num_tiles) < 0.05, 1:4] = 0.0        # zero normal: plain first round
+    d_prop = torch.from_numpy(prop).cuda()
+    out = H.out_buf(c)
+    nb = torch.zeros(1, dtype=torch.int64, device="cuda")
+    c.lcc_encode_keyframe_seeded(H.to_dev(pts), len(pts), d_prop, SKIP_LOGIT, None, out, out.numel(), nb)
+    assert c.lcc_sync() == lcc.OK
+    gbits = out[:int(nb.item())].cpu().numpy()
+    grecs = c.lcc_tile_records(0)
+    rng, _, _ = O.range_image(s, pts)
+    ofits = O.fit_tiles_seeded(s, p, rng, prop, SKIP_LOGIT)
+    skipped = (prop[:, 0] < SKIP_LOGIT) & (ofits["n_valid"] >= 3)
+    assert (grecs["status"][skipped] == lcc.S_FAIL).all() and (grecs["rounds"][skipped] == 0).all()
+    assert ((grecs["flags"][skipped] & 8) != 0).all()
+    compared, border = _compare_spatial(s, p, rng, grecs, ofits, p.fit_thr_m)
+    assert border <= max(2, 0.005 * compared)
+    gp, gok = H.gpu_planes(grecs)
+    cbits, _, _ = O.pack(s, p, 0, rng, gp, gok)
+    assert cbits.tobytes() == gbits.tobytes()
+    st, drng, _, _ = H.decode(c, gbits)
+    assert st == lcc.OK
+    m = rng > 0
+    assert np.abs(drng[m] - rng[m]).max() <= 0.01 + 1e-5
