@@ -47,6 +47,9 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="bounded oracle sample length")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batched", action="store_true", help="skip the uneven multi-sequence batch")
+    ap.add_argument("--no-learned", action="store_true", help="skip the learned-proposal section")
+    ap.add_argument("--train-steps", type=int, default=300)
+    ap.add_argument("--train-seqs", type=int, default=6)
     return ap.parse_args()
 
 
@@ -312,6 +315,130 @@ def run_batched(args, stream, hbm):
     }
 
 
+def run_learned(args, stream):
+    """Learned tile proposal on 64x2048 key frames with 8x8 tiles: the net is trained on the GPU
+    (its own forward/backward/Adam kernels) on tiles the plain encoder labels, then the seeded
+    encode (net inputs + inference + seeded fit) is compared with the plain encode on held-out
+    frames: time, fit rounds, bytes, max decode error."""
+    import torch
+    import synth
+    from paper_2008_06972_gb300 import lcc
+    from paper_2008_06972_gb300 import train as TR
+    sensor = synth.HDL64_SENSOR
+
+    def frames(ids, n):
+        out = []
+        for i in ids:
+            q = synth.sequence(sensor, n, synth.config_seed(4, i, 0), n_walls=20, n_boxes=40, n_poles=60,
+                               step_m=1.0, yaw_deg=0.5, sigma=0.02, clutter=0.02)
+            out += q.frames
+        return out
+
+    t0 = time.perf_counter()
+    train_f = frames(range(args.train_seqs), 8)
+    eval_f = frames(range(1000, 1002), 8)
+    gen_s = time.perf_counter() - t0
+    ctx = lcc.Context(sensor, lcc.default_params(tile_h=8, tile_w=8, fit_thr_m=0.05), stream=stream)
+    X, Y = [], []
+    for f in train_f:
+        x, _, y, _ = TR.frame_examples(ctx, torch.from_numpy(f).cuda(), len(f))
+        X.append(x)
+        Y.append(y)
+    X, Y = torch.cat(X), torch.cat(Y)
+    batch = 4096
+    net = lcc.Net(TR.he_uniform_params(4), max_tiles=batch, stream=stream)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    losses = TR.train(net, X, Y, args.train_steps, batch, 2e-3, seed=1, lr_final=2e-4)
+    torch.cuda.synchronize()
+    train_s = time.perf_counter() - t0
+    nt = ctx.num_tiles
+    xin = torch.zeros((nt, 64, 4), dtype=torch.int16, device="cuda")
+    anc = torch.zeros((nt, 4), dtype=torch.float32, device="cuda")
+    prop = torch.zeros((nt, 5), dtype=torch.float32, device="cuda")
+    out = torch.empty(ctx.max_encoded_bytes, dtype=torch.uint8, device="cuda")
+    nb = torch.zeros(1, dtype=torch.int64, device="cuda")
+    ref = torch.empty(sensor.rows * sensor.cols, dtype=torch.float32, device="cuda")
+    dec = torch.empty_like(ref)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+    stats = {"plain": dict(ms=0.0, bytes=0, rounds=0, fitted_tiles=0, err=0.0),
+             "learned": dict(ms=0.0, net_ms=0.0, bytes=0, rounds=0, fitted_tiles=0, skipped=0, err=0.0)}
+    pts_total = 0
+    for rep in range(2):      # the first pass warms up; the second is measured
+        for f in eval_f:
+            d = torch.from_numpy(f).cuda()
+            torch.cuda.synchronize()
+            ev[0].record(stream)
+            ctx.lcc_encode_keyframe(d, len(f), None, out, out.numel(), nb)
+            ev[1].record(stream)
+            assert ctx.lcc_sync() == lcc.OK
+            recs = ctx.lcc_tile_records(0)
+            nbytes = int(nb.item())
+            ctx.lcc_range_image(d, len(f), ref, None)
+            ctx.lcc_decode(out, nbytes, None, None, dec, None, None)
+            assert ctx.lcc_sync() == lcc.OK
+            m = ref > 0
+            err_p = float((dec[m] - ref[m]).abs().max().item())
+            torch.cuda.synchronize()
+            ev[0].record(stream)
+            lcc.net_tile_inputs(ctx, d, len(f), xin, anc)
+            net.forward(xin, nt, prop)
+            ev[2].record(stream)
+            ctx.lcc_encode_keyframe_seeded(d, len(f), prop, TR.SKIP_LOGIT, None, out, out.numel(), nb)
+            ev[3].record(stream)
+            assert ctx.lcc_sync() == lcc.OK
+            srecs = ctx.lcc_tile_records(0)
+            sbytes = int(nb.item())
+            ctx.lcc_range_image(d, len(f), ref, None)
+            ctx.lcc_decode(out, sbytes, None, None, dec, None, None)
+            assert ctx.lcc_sync() == lcc.OK
+            err_l = float((dec[m] - ref[m]).abs().max().item())
+            if rep == 0:
+                continue
+            pts_total += len(f)
+            P, L = stats["plain"], stats["learned"]
+            P["bytes"] += nbytes
+            P["rounds"] += int(recs["rounds"].sum())
+            P["fitted_tiles"] += int((recs["status"] == lcc.S_FIT).sum())
+            P["err"] = max(P["err"], err_p)
+            L["net_ms"] += ev[0].elapsed_time(ev[2])
+            L["ms"] += ev[0].elapsed_time(ev[3])
+            L["bytes"] += sbytes
+            L["rounds"] += int(srecs["rounds"].sum())
+            L["fitted_tiles"] += int((srecs["status"] == lcc.S_FIT).sum())
+            L["skipped"] += int(((srecs["flags"] & 8) != 0).sum())
+            L["err"] = max(L["err"], err_l)
+    # the plain encode timed on its own (same frames, same warm-up)
+    plain_ms = 0.0
+    for rep in range(2):
+        for f in eval_f:
+            d = torch.from_numpy(f).cuda()
+            torch.cuda.synchronize()
+            ev[0].record(stream)
+            ctx.lcc_encode_keyframe(d, len(f), None, out, out.numel(), nb)
+            ev[1].record(stream)
+            torch.cuda.synchronize()
+            if rep:
+                plain_ms += ev[0].elapsed_time(ev[1])
+    stats["plain"]["ms"] = plain_ms
+    for k in stats:
+        stats[k]["mpts_per_s"] = pts_total / (stats[k]["ms"] * 1e-3) / 1e6
+        stats[k]["ms_per_frame"] = stats[k]["ms"] / len(eval_f)
+    return {
+        "workload": "HDL-64E key frames 64x2048, tiles 8x8, thr 0.05 m; net trained on "
+                    f"{len(train_f)} frames ({X.shape[0]} tiles) of the same scene family, evaluated on "
+                    f"{len(eval_f)} held-out frames",
+        "train": {"steps": args.train_steps, "batch_tiles": batch, "seconds": train_s,
+                  "loss_first": float(losses[0]), "loss_last": float(np.mean(losses[-10:])),
+                  "tflops": 3 * 7.2e6 * batch * args.train_steps / train_s / 1e12},
+        "net_flops_per_tile": 7.2e6,
+        "plain": stats["plain"], "learned": stats["learned"],
+        "rounds_saved_frac": 1.0 - stats["learned"]["rounds"] / max(stats["plain"]["rounds"], 1),
+        "bytes_ratio_learned_vs_plain": stats["learned"]["bytes"] / max(stats["plain"]["bytes"], 1),
+        "setup_s": {"generate": gen_s},
+    }
+
+
 def main():
     args = parse()
     rank = int(os.environ.get("RANK", "0"))
@@ -464,6 +591,7 @@ def main():
                      "frac": path_bytes / (ms_step * 1e-3) / 1e9 / hbm}}
 
     batched = None if args.no_batched else run_batched(args, stream, hbm)
+    learned = None if args.no_learned else run_learned(args, stream)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -487,6 +615,7 @@ def main():
             "kernel_ms_per_step": {k: v[1] / args.steps for k, v in ktimes.items()},
             "roofline": roof,
             "batched": batched,
+            "learned": learned,
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(16 * pts_step),
                     "d2h_bytes_per_step": int(total_bytes + 8 * n_frames)},
             "gpu_launches": int(round(launches_per_step * args.steps)),

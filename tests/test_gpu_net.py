@@ -226,3 +226,58 @@ def test_seeded_keyframe_parity(frame):
     assert st == lcc.OK
     m = rng > 0
     assert np.abs(drng[m] - rng[m]).max() <= 0.01 + 1e-5
+
+
+def test_trained_net_saves_fit_rounds_on_held_out_frames():
+    """What the trained net gains: trained on frames of one set of sequences, the seeded encode
+    of frames from other sequences needs fewer fit rounds than the plain encode, with streams no
+    larger (within 2%) and the same decode bound."""
+    from paper_2008_06972_gb300 import lcc
+    from paper_2008_06972_gb300 import train as TR
+    sensor = synth.HDL64_SENSOR
+
+    def frames(ids, n):
+        out = []
+        for i in ids:
+            q = synth.sequence(sensor, n, synth.config_seed(4, i, 0), n_walls=20, n_boxes=40, n_poles=60,
+                               step_m=1.0, yaw_deg=0.5, sigma=0.02, clutter=0.02)
+            out += q.frames
+        return out
+
+    ctx = H.ctx(sensor, tile_h=8, tile_w=8)
+    X, Y = [], []
+    for f in frames(range(2), 6):
+        x, _, y, _ = TR.frame_examples(ctx, H.to_dev(f), len(f))
+        X.append(x)
+        Y.append(y)
+    X, Y = torch.cat(X), torch.cat(Y)
+    net = lcc.Net(TR.he_uniform_params(4), max_tiles=2048)
+    losses = TR.train(net, X, Y, 150, 2048, 2e-3, seed=1, lr_final=2e-4)
+    assert losses[-10:].mean() < 0.5 * losses[0]
+    nt = ctx.num_tiles
+    xin = torch.zeros((nt, 64, 4), dtype=torch.int16, device="cuda")
+    anc = torch.zeros((nt, 4), dtype=torch.float32, device="cuda")
+    prop = torch.zeros((nt, 5), dtype=torch.float32, device="cuda")
+    tot = {"plain": [0, 0], "seeded": [0, 0]}
+    for f in frames([1000], 3):
+        d = H.to_dev(f)
+        bits, recs = H.encode_keyframe(ctx, f)
+        lcc.net_tile_inputs(ctx, d, len(f), xin, anc)
+        net.forward(xin, nt, prop)
+        out = H.out_buf(ctx)
+        nb = torch.zeros(1, dtype=torch.int64, device="cuda")
+        ctx.lcc_encode_keyframe_seeded(d, len(f), prop, TR.SKIP_LOGIT, None, out, out.numel(), nb)
+        assert ctx.lcc_sync() == lcc.OK
+        sbits = out[:int(nb.item())].cpu().numpy()
+        srecs = ctx.lcc_tile_records(0)
+        tot["plain"][0] += int(recs["rounds"].sum())
+        tot["plain"][1] += len(bits)
+        tot["seeded"][0] += int(srecs["rounds"].sum())
+        tot["seeded"][1] += len(sbits)
+        rng, _, _ = O.range_image(O.sensor(sensor), f)
+        st, drng, _, _ = H.decode(ctx, sbits)
+        assert st == lcc.OK
+        m = rng > 0
+        assert np.abs(drng[m] - rng[m]).max() <= 0.01 + 1e-5
+    assert tot["seeded"][0] < 0.9 * tot["plain"][0], tot
+    assert tot["seeded"][1] <= 1.02 * tot["plain"][1], tot
