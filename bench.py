@@ -7,8 +7,12 @@ threshold 0.05 m, quantisation 0.02 m (max decode error 0.01 m <= 2 cm).
 Inputs are resident in HBM; L2 is flushed (256 MiB write) between timed steps
 and the flush is outside the per-step CUDA-event timing.
 
-Prints one JSON line.  --impl reference times the CPU oracle (plain C, one
-core) on a bounded sample of the same workload instead.
+Prints one JSON line.  Besides the headline sequence it carries two sections:
+"batched" (64 uneven sequences of four resolutions in one plan replayed as a
+CUDA graph, against one call per key-frame group) and "learned" (the proposal
+net trained on the GPU, then the seeded encode against the plain one on
+held-out 64x2048 frames with 8x8 tiles).  --impl reference times the CPU
+oracle (plain C, one core) on a bounded sample of the headline workload.
 Multi-GPU: one process per GPU (torchrun); each rank encodes its own sequence
 (no data-path collective; weak scaling); timing is the max over ranks.
 """

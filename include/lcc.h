@@ -242,8 +242,12 @@ lcc_status lcc_net_set_params(lcc_net *net, const float *h_params);   /* also re
  * every tile: d_x [num_tiles][64][4] bf16 (as uint16), d_anchor [num_tiles]
  * float4 (anchor x, y, z, r).  LCC_ERR_UNSUPPORTED for other tile shapes. */
 lcc_status lcc_net_tile_inputs(lcc_ctx *ctx, const float *d_pts, int64_t n, uint16_t *d_x, float *d_anchor);
-/* Outputs d_out [ntiles][5] fp32 (logit, v[3], d_rel), on the net's stream. */
+/* Outputs d_out [ntiles][5] fp32 (logit, v[3], d_rel), on the net's stream.
+ * Inference runs on tcgen05 (TMEM accumulators, two tiles per MMA); its
+ * waits are bounded, and one that ran out is reported by lcc_net_sync. */
 lcc_status lcc_net_forward(lcc_net *net, const uint16_t *d_x, int64_t ntiles, float *d_out);
+/* Waits for the net's stream; LCC_ERR_TIMEOUT if a kernel's bounded wait ran out (then cleared). */
+lcc_status lcc_net_sync(lcc_net *net);
 /* Gradient of the mean loss w.r.t. the parameters (d_grad: 58853 fp32, may be
  * NULL) and the loss (d_loss: 1 fp32, may be NULL); d_labels [ntiles][5]. */
 lcc_status lcc_net_gradient(lcc_net *net, const uint16_t *d_x, const float *d_labels, int64_t ntiles, float *d_grad,

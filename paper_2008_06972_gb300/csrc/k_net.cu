@@ -55,6 +55,7 @@ struct NetDev {
     bf16 *B1f, *B2f, *B3f;                   // forward GEMM B: [cout][k = tap*cin + ci]
     bf16 *B2t, *B3t;                         // input-gradient GEMM B: [ci][k = tap*cout + co]
     float *F1b, *F2b;                        // head weights rounded to bf16 values
+    bf16 *T1, *T2, *T3;                      // tcgen05 B operands: [tap][ci/8][cout][8], core-matrix order
 };
 
 struct NetAct {                              // per-tile training activations
@@ -220,6 +221,26 @@ __global__ void k_net_prep(NetDev nd) {
         }
         j -= HID * C3;
         nd.F2b[j] = bfround(th[OF2 + j]);
+    }
+    // tcgen05 layouts: element (tap, c8, co, e) = W[co][ci = 8 c8 + e][tap] (conv1: ci >= 4 is zero)
+    const int m1 = 9 * 2 * C1 * 8, m2 = 9 * (C1 / 8) * C2 * 8, m3 = 9 * (C2 / 8) * C3 * 8;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < m1 + m2 + m3; i += gridDim.x * blockDim.x) {
+        int j = i;
+        if (j < m1) {
+            const int e = j % 8, co = (j / 8) % C1, c8 = (j / (8 * C1)) % 2, tap = j / (8 * C1 * 2);
+            const int ci = 8 * c8 + e;
+            nd.T1[j] = __float2bfloat16_rn(ci < C0 ? th[OW1 + co * C0 * 9 + ci * 9 + tap] : 0.f);
+            continue;
+        }
+        j -= m1;
+        if (j < m2) {
+            const int e = j % 8, co = (j / 8) % C2, c8 = (j / (8 * C2)) % (C1 / 8), tap = j / (8 * C2 * (C1 / 8));
+            nd.T2[j] = __float2bfloat16_rn(th[OW2 + co * C1 * 9 + (8 * c8 + e) * 9 + tap]);
+            continue;
+        }
+        j -= m2;
+        const int e = j % 8, co = (j / 8) % C3, c8 = (j / (8 * C3)) % (C2 / 8), tap = j / (8 * C3 * (C2 / 8));
+        nd.T3[j] = __float2bfloat16_rn(th[OW3 + co * C2 * 9 + (8 * c8 + e) * 9 + tap]);
     }
 }
 
@@ -390,6 +411,249 @@ __global__ void __launch_bounds__(kNetWarps * 32, 1) k_net_fwd(NetDev nd, const 
         (void)hs;
         __syncwarp();
     }
+}
+
+// ------------------------------------------------------------------ forward on tcgen05 (inference) --
+//
+// Two tiles per step: M = 128 GEMM rows ordered (tile row y, tile, pixel x),
+// so that every 8-row core matrix of A is 8 consecutive pixels of one row of
+// one tile.  Activations live in shared memory as [channel/8][y 0..9][tile][x
+// 0..9][8 channels] with a zero border, i.e. K-major core matrices whose
+// 8-row groups are 160 B apart; the 3x3 tap (ky, kx) is then the same
+// descriptor started (ky*20 + kx)*16 bytes further, so the nine taps of a
+// convolution are nine accumulating MMAs per 16 input channels, with no im2col.
+// One thread issues tcgen05.mma into a 128-lane x 64-column fp32 TMEM
+// accumulator; the four warps read their 32 lanes back (tcgen05.ld) for the
+// bias/ReLU/BF16 epilogue into the next layer's copy.
+
+constexpr int TPOS = 10 * 2 * 10;              // padded positions per 8-channel chunk
+constexpr int TCHUNK = TPOS * 16;              // bytes per chunk (3200)
+constexpr int TW1 = 9 * 2 * C1 * 16, TW2 = 9 * (C1 / 8) * C2 * 16, TW3 = 9 * (C2 / 8) * C3 * 16;
+constexpr int TX = 2 * TCHUNK, TA1 = (C1 / 8) * TCHUNK, TA2 = (C2 / 8) * TCHUNK;
+constexpr int TGP = kNetWarps * 2 * C3 * 4, TG = 2 * C3 * 4;
+constexpr size_t kTcSmem = (size_t)TW1 + TW2 + TW3 + TX + TA1 + TA2 + TGP + TG + 64;
+constexpr uint32_t kTmemCols = 64;
+constexpr long long kSpinLimit = 1ll << 22;
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+// shared-memory matrix descriptor: K-major, no swizzle (start, leading = K-direction
+// core-matrix stride, stride = M/N-direction 8-row group stride, version 1)
+__device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
+    return (uint64_t)((addr & 0x3FFFFu) >> 4) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
+           ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46);
+}
+
+// instruction descriptor, kind::f16: fp32 accumulator, bf16 A and B, both K-major
+__host__ __device__ constexpr uint32_t mma_idesc(int M, int N) {
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void tc_mma(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n"
+        :
+        : "r"(d_tmem), "l"(a), "l"(b), "r"(idesc), "r"(acc));
+}
+
+__device__ __forceinline__ void tc_commit(uint32_t mbar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(mbar)
+                 : "memory");
+}
+
+// bounded wait on an mbarrier phase; false if the limit was reached
+__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity) {
+    for (long long it = 0; it < kSpinLimit; it++) {
+        uint32_t done;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+            "selp.u32 %0, 1, 0, p;\n\t}\n"
+            : "=r"(done)
+            : "r"(mbar), "r"(parity)
+            : "memory");
+        if (done) return true;
+    }
+    return false;
+}
+
+__device__ __forceinline__ void tc_ld16(uint32_t taddr, float (&v)[16]) {
+    uint32_t r[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];\n"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+#pragma unroll
+    for (int i = 0; i < 16; i++) v[i] = __uint_as_float(r[i]);
+}
+
+__device__ __forceinline__ void tc_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory"); }
+__device__ __forceinline__ void tc_before_sync() { asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory"); }
+__device__ __forceinline__ void tc_after_sync() { asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory"); }
+__device__ __forceinline__ void proxy_fence() { asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory"); }
+
+// byte offset of (chunk, y, tile, x) in an activation copy
+__device__ __forceinline__ int tpos(int c8, int y, int tile, int x) { return c8 * TCHUNK + ((y * 2 + tile) * 10 + x) * 16; }
+
+// One convolution: nine taps x (CIN/16) k-steps of M=128, N=COUT MMAs (one thread).
+template <int CIN, int COUT>
+__device__ __forceinline__ void tc_conv(uint32_t tmem, uint32_t act, uint32_t wts) {
+    constexpr uint32_t idesc = mma_idesc(128, COUT);
+    constexpr int KCH = CIN < 16 ? 16 : CIN;   // conv1: 4 real channels padded to one k-step
+    uint32_t acc = 0;
+#pragma unroll 1
+    for (int tap = 0; tap < 9; tap++) {
+        const int ky = tap / 3, kx = tap % 3;
+#pragma unroll 1
+        for (int ks = 0; ks < KCH / 16; ks++) {
+            const uint64_t a = smem_desc(act + (uint32_t)((ky * 20 + kx) * 16 + 2 * ks * TCHUNK), TCHUNK, 160);
+            const uint64_t b = smem_desc(wts + (uint32_t)(tap * (KCH / 8) * COUT * 16 + 2 * ks * COUT * 16),
+                                         COUT * 16, 128);
+            tc_mma(tmem, a, b, idesc, acc);
+            acc = 1;
+        }
+    }
+}
+
+__global__ void __launch_bounds__(kNetWarps * 32, 1) k_net_fwd_tc(NetDev nd, const bf16 *x, long long T, float *out,
+                                                                  int *err) {
+    extern __shared__ __align__(1024) uint8_t sm[];
+    uint8_t *sW1 = sm, *sW2 = sW1 + TW1, *sW3 = sW2 + TW2;
+    uint8_t *sX = sW3 + TW3, *sA1 = sX + TX, *sA2 = sA1 + TA1;
+    float *sGP = reinterpret_cast<float *>(sA2 + TA2);     // [warp][tile][64]
+    float *sG = sGP + kNetWarps * 2 * C3;                 // [tile][64]
+    uint64_t *bar = reinterpret_cast<uint64_t *>(sG + 2 * C3);
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bar + 1);
+    int *s_fail = reinterpret_cast<int *>(tmem_slot + 1);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    // stage weights, zero the activation copies (borders stay zero)
+    {
+        const uint4 *src[3] = {reinterpret_cast<const uint4 *>(nd.T1), reinterpret_cast<const uint4 *>(nd.T2),
+                               reinterpret_cast<const uint4 *>(nd.T3)};
+        uint4 *dst[3] = {reinterpret_cast<uint4 *>(sW1), reinterpret_cast<uint4 *>(sW2), reinterpret_cast<uint4 *>(sW3)};
+        const int cnt[3] = {TW1 / 16, TW2 / 16, TW3 / 16};
+        for (int q = 0; q < 3; q++)
+            for (int i = tid; i < cnt[q]; i += blockDim.x) dst[q][i] = src[q][i];
+        uint4 *z = reinterpret_cast<uint4 *>(sX);
+        for (int i = tid; i < (TX + TA1 + TA2) / 16; i += blockDim.x) z[i] = make_uint4(0u, 0u, 0u, 0u);
+    }
+    if (tid == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(bar)) : "memory");
+        *s_fail = 0;
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(smem_u32(tmem_slot)),
+                     "r"(kTmemCols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::: "memory");
+    }
+    proxy_fence();
+    tc_before_sync();
+    __syncthreads();
+    tc_after_sync();
+    const uint32_t tmem = *tmem_slot;
+    const uint32_t mbar = smem_u32(bar);
+    const uint32_t aX = smem_u32(sX), aA1 = smem_u32(sA1), aA2 = smem_u32(sA2);
+    const uint32_t aW1 = smem_u32(sW1), aW2 = smem_u32(sW2), aW3 = smem_u32(sW3);
+    const float *th = nd.theta;
+    // this thread's GEMM row: r = 32 warp + lane -> (y, tile, x)
+    const int r = tid, grp = r >> 3, px = r & 7, py = grp >> 1, tl = grp & 1;
+    const uint32_t trow = tmem + ((uint32_t)(warp * 32) << 16);
+    uint32_t phase = 0;
+    for (long long pair = blockIdx.x; pair * 2 < T; pair += gridDim.x) {
+        const long long tile = pair * 2 + tl;
+        {   // input row (4 channels + 4 zero) of this thread's pixel
+            uint2 v = make_uint2(0u, 0u);
+            if (tile < T) v = *reinterpret_cast<const uint2 *>(x + ((size_t)tile * kPX + py * 8 + px) * C0);
+            *reinterpret_cast<uint4 *>(sX + tpos(0, py + 1, tl, px + 1)) = make_uint4(v.x, v.y, 0u, 0u);
+        }
+        // conv1 -> a1, conv2 -> a2, conv3 -> pooled sums
+#pragma unroll 1
+        for (int layer = 0; layer < 3; layer++) {
+            proxy_fence();
+            tc_before_sync();
+            __syncthreads();
+            tc_after_sync();
+            if (tid == 0) {
+                if (layer == 0) tc_conv<C0, C1>(tmem, aX, aW1);
+                else if (layer == 1) tc_conv<C1, C2>(tmem, aA1, aW2);
+                else tc_conv<C2, C3>(tmem, aA2, aW3);
+                tc_commit(mbar);
+            }
+            if (!mbar_wait(mbar, phase)) {
+                atomicExch(s_fail, 1);
+                if (err) atomicExch(err, 1);
+            }
+            phase ^= 1u;
+            tc_after_sync();
+            const int cout = layer == 0 ? C1 : C2;
+            const float *bias = th + (layer == 0 ? OB1 : layer == 1 ? OB2 : OB3);
+#pragma unroll 1
+            for (int c0 = 0; c0 < cout; c0 += 16) {
+                float v[16];
+                tc_ld16(trow + (uint32_t)c0, v);
+                tc_wait_ld();
+#pragma unroll
+                for (int i = 0; i < 16; i++) v[i] = fmaxf(v[i] + __ldg(bias + c0 + i), 0.f);
+                if (layer < 2) {
+                    uint8_t *dst = layer == 0 ? sA1 : sA2;
+#pragma unroll
+                    for (int h = 0; h < 2; h++) {
+                        uint32_t w[4];
+#pragma unroll
+                        for (int q = 0; q < 4; q++) {
+                            const __nv_bfloat162 b2 = __floats2bfloat162_rn(v[8 * h + 2 * q], v[8 * h + 2 * q + 1]);
+                            w[q] = *reinterpret_cast<const uint32_t *>(&b2);
+                        }
+                        *reinterpret_cast<uint4 *>(dst + tpos(c0 / 8 + h, py + 1, tl, px + 1)) =
+                            make_uint4(w[0], w[1], w[2], w[3]);
+                    }
+                } else {
+#pragma unroll
+                    for (int i = 0; i < 16; i++) {
+                        float s2 = bfround(v[i]);
+                        s2 += __shfl_xor_sync(0xffffffffu, s2, 1);
+                        s2 += __shfl_xor_sync(0xffffffffu, s2, 2);
+                        s2 += __shfl_xor_sync(0xffffffffu, s2, 4);
+                        s2 += __shfl_xor_sync(0xffffffffu, s2, 16);
+                        if (lane == 0 || lane == 8) sGP[(warp * 2 + tl) * C3 + c0 + i] = s2;
+                    }
+                }
+            }
+        }
+        tc_before_sync();
+        __syncthreads();
+        tc_after_sync();
+        if (*s_fail) break;   // read after the barrier: the same decision in every thread
+        {   // pooled vector of both tiles (fixed summation order over the warps)
+            const int t2 = tid >> 6, c = tid & 63;
+            float s2 = 0.f;
+            for (int w = 0; w < kNetWarps; w++) s2 += sGP[(w * 2 + t2) * C3 + c];
+            sG[t2 * C3 + c] = bfround(s2 * (1.0f / kPX));
+        }
+        __syncthreads();
+        if (warp < 2 && pair * 2 + warp < T) {   // head: warp w takes tile w of the pair
+            const float *gs = sG + warp * C3;
+            float yv = __ldg(th + OC1 + lane);
+            for (int c = 0; c < C3; c++) yv = fmaf(__ldg(nd.F1b + lane * C3 + c), gs[c], yv);
+            const float hj = bfround(fmaxf(yv, 0.f));
+            float o[NOUT];
+#pragma unroll
+            for (int i = 0; i < NOUT; i++) {
+                float sacc = __ldg(nd.F2b + i * HID + lane) * hj;
+#pragma unroll
+                for (int off = 16; off; off >>= 1) sacc += __shfl_xor_sync(0xffffffffu, sacc, off);
+                o[i] = sacc + __ldg(th + OC2 + i);
+            }
+            if (lane < NOUT) out[(size_t)(pair * 2 + warp) * NOUT + lane] = o[lane];
+        }
+    }
+    tc_before_sync();
+    __syncthreads();
+    tc_after_sync();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(kTmemCols) : "memory");
 }
 
 // ------------------------------------------------------------------ backward: loss and head --
@@ -688,6 +952,7 @@ struct lcc_net {
     int64_t max_tiles = 0;
     int sms = 0;
     float *theta = nullptr, *grad = nullptr, *m = nullptr, *v = nullptr, *loss = nullptr;
+    int *err = nullptr;                      // set by a kernel whose bounded wait ran out
     NetDev nd{};
     NetAct act{};
     void *wbuf = nullptr, *abuf = nullptr;
@@ -763,7 +1028,7 @@ lcc_status lcc_net_create(lcc_net **out, const float *h_params, int64_t max_tile
     net->max_tiles = max_tiles;
     net->sms = prop.multiProcessorCount;
     const size_t wb[] = {sizeof(float) * NPARAM * 4 + 256,   // theta, grad, m, v
-                         sizeof(bf16) * (C1 * B1S + C2 * B2S + C3 * B3S + C1 * BTS + C3 * BTS),
+                         sizeof(bf16) * (C1 * B1S + C2 * B2S + C3 * B3S + C1 * BTS + C3 * BTS) + TW1 + TW2 + TW3,
                          sizeof(float) * (HID * C3 + NOUT * HID), 256};
     size_t wtotal = 0;
     for (size_t b : wb) wtotal += align256(b);
@@ -790,11 +1055,15 @@ lcc_status lcc_net_create(lcc_net **out, const float *h_params, int64_t max_tile
     net->nd.B3f = net->nd.B2f + C2 * B2S;
     net->nd.B2t = net->nd.B3f + C3 * B3S;
     net->nd.B3t = net->nd.B2t + C1 * BTS;
+    net->nd.T1 = net->nd.B3t + C3 * BTS;
+    net->nd.T2 = net->nd.T1 + TW1 / 2;
+    net->nd.T3 = net->nd.T2 + TW2 / 2;
     w += align256(wb[1]);
     net->nd.F1b = (float *)w;
     net->nd.F2b = net->nd.F1b + HID * C3;
     w += align256(wb[2]);
     net->loss = (float *)w;
+    net->err = (int *)(w + 64);
     char *a = (char *)net->abuf;
     void **slots[] = {(void **)&net->act.a1, (void **)&net->act.a2, (void **)&net->act.a3, (void **)&net->act.g,
                       (void **)&net->act.h,  (void **)&net->act.o,  (void **)&net->act.da3c, (void **)&net->act.dz1t,
@@ -804,10 +1073,11 @@ lcc_status lcc_net_create(lcc_net **out, const float *h_params, int64_t max_tile
         a += align256(ab[i]);
     }
     if (smem_attr(k_net_fwd<true>, kFwdSmem) != LCC_OK || smem_attr(k_net_fwd<false>, kFwdSmem) != LCC_OK ||
-        smem_attr(k_net_conv_bwd, kBwdSmem) != LCC_OK ||
+        smem_attr(k_net_conv_bwd, kBwdSmem) != LCC_OK || smem_attr(k_net_fwd_tc, kTcSmem) != LCC_OK ||
         smem_attr(k_net_wgrad<C2, C3, 64, A2S>, wgrad_smem(A2S)) != LCC_OK ||
         cudaMemcpy(net->theta, h_params, sizeof(float) * NPARAM, cudaMemcpyHostToDevice) != cudaSuccess ||
-        cudaMemset(net->m, 0, sizeof(float) * 2 * NPARAM) != cudaSuccess || net_prep(net) != LCC_OK ||
+        cudaMemset(net->m, 0, sizeof(float) * 2 * NPARAM) != cudaSuccess ||
+        cudaMemset(net->err, 0, sizeof(int)) != cudaSuccess || net_prep(net) != LCC_OK ||
         cudaDeviceSynchronize() != cudaSuccess) {
         lcc_net_destroy(net);
         return LCC_ERR_CUDA;
@@ -859,7 +1129,23 @@ lcc_status lcc_net_tile_inputs(lcc_ctx *c, const float *d_pts, int64_t n, uint16
 lcc_status lcc_net_forward(lcc_net *net, const uint16_t *d_x, int64_t ntiles, float *d_out) {
     if (!net || !d_x || !d_out || ntiles < 0 || ((uintptr_t)d_x & 7u)) return LCC_ERR_INVALID_ARG;
     if (ntiles == 0) return LCC_OK;
-    return forward(net, d_x, ntiles, d_out, false);
+    const int64_t pairs = (ntiles + 1) / 2;
+    const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(pairs, net->sms));
+    k_net_fwd_tc<<<grid, kNetWarps * 32, kTcSmem, net->stream>>>(net->nd, reinterpret_cast<const bf16 *>(d_x), ntiles,
+                                                                  d_out, net->err);
+    return cudaGetLastError() == cudaSuccess ? LCC_OK : LCC_ERR_CUDA;
+}
+
+lcc_status lcc_net_sync(lcc_net *net) {
+    if (!net) return LCC_ERR_INVALID_ARG;
+    LCC_CUDA(cudaStreamSynchronize(net->stream));
+    int e = 0;
+    LCC_CUDA(cudaMemcpy(&e, net->err, sizeof(int), cudaMemcpyDeviceToHost));
+    if (e) {
+        cudaMemset(net->err, 0, sizeof(int));
+        return LCC_ERR_TIMEOUT;
+    }
+    return LCC_OK;
 }
 
 lcc_status lcc_net_gradient(lcc_net *net, const uint16_t *d_x, const float *d_labels, int64_t ntiles, float *d_grad,

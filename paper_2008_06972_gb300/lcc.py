@@ -119,6 +119,7 @@ def load(path: str = LIB_PATH):
         "lcc_net_set_params": (i32, [vp, vp]),
         "lcc_net_tile_inputs": (i32, [vp, vp, i64, vp, vp]),
         "lcc_net_forward": (i32, [vp, vp, i64, vp]),
+        "lcc_net_sync": (i32, [vp]),
         "lcc_net_gradient": (i32, [vp, vp, vp, i64, vp, vp]),
         "lcc_net_train_step": (i32, [vp, vp, vp, i64, ctypes.c_float, i32, vp]),
         "lcc_plan_create": (i32, [vp, i32, vp, i32, vp]),
@@ -147,7 +148,7 @@ def exported_symbols() -> list[str]:
             "lcc_encode_keyframe", "lcc_encode_keyframe_seeded", "lcc_encode_pframe", "lcc_encode_pframes", "lcc_encode_sequence",
             "lcc_encode_sequence_host", "lcc_keyframe_from_stream", "lcc_decode", "lcc_sync", "lcc_last_stats",
             "lcc_tile_records", "lcc_set_profiling", "lcc_kernel_times", "lcc_range_image_static", "lcc_net_num_params", "lcc_net_create", "lcc_net_destroy",
-            "lcc_net_get_params", "lcc_net_set_params", "lcc_net_tile_inputs", "lcc_net_forward", "lcc_net_gradient",
+            "lcc_net_get_params", "lcc_net_set_params", "lcc_net_tile_inputs", "lcc_net_forward", "lcc_net_sync", "lcc_net_gradient",
             "lcc_net_train_step", "lcc_plan_create", "lcc_plan_update",
             "lcc_plan_encode", "lcc_plan_capture", "lcc_plan_replay", "lcc_plan_sync", "lcc_plan_get_info",
             "lcc_plan_destroy", "lcc_autotune"]
@@ -477,6 +478,9 @@ class Net:
 
     def forward(self, d_x, ntiles: int, d_out):
         _check(self.lib.lcc_net_forward(self.h, _ptr(d_x), ntiles, _ptr(d_out)), "lcc_net_forward")
+
+    def sync(self) -> int:
+        return int(self.lib.lcc_net_sync(self.h))
 
     def gradient(self, d_x, d_labels, ntiles: int, d_grad=None, d_loss=None):
         _check(self.lib.lcc_net_gradient(self.h, _ptr(d_x), _ptr(d_labels), ntiles, _ptr(d_grad), _ptr(d_loss)),

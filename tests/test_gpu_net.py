@@ -100,7 +100,7 @@ def test_forward_matches_oracle(frame):
     xs = x[torch.from_numpy(idx).cuda()].contiguous()
     out = torch.zeros((len(idx), 5), dtype=torch.float32, device="cuda")
     net.forward(xs, len(idx), out)
-    torch.cuda.synchronize()
+    assert net.sync() == lcc.OK
     og = out.cpu().numpy()
     oo, _ = N.forward(theta.astype(np.float64), _oracle_x(xs.cpu().numpy()), rounding=True)
     err = np.abs(og - oo)
@@ -109,7 +109,7 @@ def test_forward_matches_oracle(frame):
     # the full frame runs too (persistent kernel over 2048 tiles)
     full = torch.zeros((c.num_tiles, 5), dtype=torch.float32, device="cuda")
     net.forward(x, c.num_tiles, full)
-    torch.cuda.synchronize()
+    assert net.sync() == lcc.OK
     assert np.array_equal(full.cpu().numpy()[idx], og)
 
 
