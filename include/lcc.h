@@ -160,6 +160,14 @@ lcc_status lcc_encode_keyframe_seeded(lcc_ctx *ctx, const float *d_pts, int64_t 
                                       float skip_logit, lcc_keyframe *kf, uint8_t *d_out, uint64_t cap,
                                       uint64_t *out_bytes);
 
+/* Batched key frames: nframes independent frames, each spatially coded (its own
+ * key frame), in one launch per kernel.  d_prop: NULL for the plain fit, or a
+ * host array of nframes device proposal tables as in lcc_encode_keyframe_seeded.
+ * nframes <= max_batch; out_bytes: nframes uint64 (host or device). */
+lcc_status lcc_encode_keyframes(lcc_ctx *ctx, int32_t nframes, const float *const *d_pts, const int64_t *n,
+                                const float *const *d_prop, float skip_logit, uint8_t *const *d_out,
+                                const uint64_t *cap, uint64_t *out_bytes);
+
 /* Batched: nframes P frames against one key frame in one launch per kernel.
  * poses: nframes x 16 doubles; d_pts, n, d_out, cap: per-frame host arrays;
  * out_bytes: nframes uint64 (host or device).  nframes <= max_batch. */

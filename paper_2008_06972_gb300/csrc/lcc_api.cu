@@ -468,6 +468,25 @@ lcc_status lcc_encode_keyframe_seeded(lcc_ctx *c, const float *d_pts, int64_t n,
     return copy_bytes(c, 1, &slot, out_bytes);
 }
 
+lcc_status lcc_encode_keyframes(lcc_ctx *c, int32_t nframes, const float *const *d_pts, const int64_t *n,
+                                const float *const *d_prop, float skip_logit, uint8_t *const *d_out,
+                                const uint64_t *cap, uint64_t *out_bytes) {
+    if (!c || !(skip_logit == skip_logit)) return LCC_ERR_INVALID_ARG;
+    lcc_status st = check_frames(c, nframes, d_pts, n, d_out, cap);
+    if (st != LCC_OK) return st;
+    if (d_prop)
+        for (int f = 0; f < nframes; f++)
+            if (!d_prop[f] || ((uintptr_t)d_prop[f] & 3u)) return LCC_ERR_INVALID_ARG;
+    int slots[kMaxBatch];
+    for (int f = 0; f < nframes; f++) slots[f] = f;
+    if ((st = bin_frames(c, nframes, slots, d_pts, n)) != LCC_OK) return st;
+    if ((st = encode_batch(c, 0, nframes, slots, d_out, cap, nullptr, nullptr, nullptr, nullptr, d_prop,
+                           skip_logit)) != LCC_OK)
+        return st;
+    c->last_nframes = nframes;
+    return copy_bytes(c, nframes, slots, out_bytes);
+}
+
 lcc_status lcc_encode_pframes(lcc_ctx *c, const lcc_keyframe *kf, int32_t nframes, const double *poses,
                               const float *const *d_pts, const int64_t *n, uint8_t *const *d_out,
                               const uint64_t *cap, uint64_t *out_bytes) {

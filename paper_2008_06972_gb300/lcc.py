@@ -102,6 +102,7 @@ def load(path: str = LIB_PATH):
         "lcc_encode_pframe": (i32, [vp, vp, vp, vp, i64, vp, u64, vp]),
         "lcc_encode_pframes": (i32, [vp, vp, i32, vp, vp, vp, vp, vp, vp]),
         "lcc_encode_keyframe_seeded": (i32, [vp, vp, i64, vp, ctypes.c_float, vp, vp, u64, vp]),
+        "lcc_encode_keyframes": (i32, [vp, i32, vp, vp, vp, ctypes.c_float, vp, vp, vp]),
         "lcc_encode_sequence": (i32, [vp, i32, i32, vp, vp, vp, vp, vp, vp, vp]),
         "lcc_encode_sequence_host": (i32, [vp, i32, i32, vp, vp, vp, vp, vp, vp]),
         "lcc_keyframe_from_stream": (i32, [vp, vp, u64, vp]),
@@ -145,7 +146,7 @@ def exported_symbols() -> list[str]:
     """Entry points this binding expects liblcc.so to export."""
     return ["lcc_status_string", "lcc_default_params", "lcc_create", "lcc_destroy", "lcc_max_encoded_bytes",
             "lcc_num_tiles", "lcc_tables", "lcc_range_image", "lcc_keyframe_create", "lcc_keyframe_free",
-            "lcc_encode_keyframe", "lcc_encode_keyframe_seeded", "lcc_encode_pframe", "lcc_encode_pframes", "lcc_encode_sequence",
+            "lcc_encode_keyframe", "lcc_encode_keyframe_seeded", "lcc_encode_keyframes", "lcc_encode_pframe", "lcc_encode_pframes", "lcc_encode_sequence",
             "lcc_encode_sequence_host", "lcc_keyframe_from_stream", "lcc_decode", "lcc_sync", "lcc_last_stats",
             "lcc_tile_records", "lcc_set_profiling", "lcc_kernel_times", "lcc_range_image_static", "lcc_net_num_params", "lcc_net_create", "lcc_net_destroy",
             "lcc_net_get_params", "lcc_net_set_params", "lcc_net_tile_inputs", "lcc_net_forward", "lcc_net_sync", "lcc_net_gradient",
@@ -274,6 +275,15 @@ class Context:
         _check(self.lib.lcc_encode_keyframe_seeded(self.h, _ptr(d_pts), n, _ptr(d_prop), skip_logit,
                                                    kf.h if kf else None, _ptr(d_out), cap, _ptr(out_bytes)),
                "lcc_encode_keyframe_seeded")
+
+    def lcc_encode_keyframes(self, d_pts: list, n: list, d_prop: list | None, skip_logit: float, d_out: list,
+                             cap: list, out_bytes):
+        nf = len(d_pts)
+        props = _arr(ctypes.c_void_p, [_ptr(x) for x in d_prop]) if d_prop is not None else None
+        _check(self.lib.lcc_encode_keyframes(self.h, nf, _arr(ctypes.c_void_p, [_ptr(x) for x in d_pts]),
+                                             _arr(ctypes.c_int64, n), props, skip_logit,
+                                             _arr(ctypes.c_void_p, [_ptr(x) for x in d_out]),
+                                             _arr(ctypes.c_uint64, cap), _ptr(out_bytes)), "lcc_encode_keyframes")
 
     def lcc_encode_pframe(self, kf: Keyframe, pose: np.ndarray, d_pts, n: int, d_out, cap: int, out_bytes):
         pose = np.ascontiguousarray(pose, dtype=np.float64).reshape(16)

@@ -281,3 +281,32 @@ def test_trained_net_saves_fit_rounds_on_held_out_frames():
         assert np.abs(drng[m] - rng[m]).max() <= 0.01 + 1e-5
     assert tot["seeded"][0] < 0.9 * tot["plain"][0], tot
     assert tot["seeded"][1] <= 1.02 * tot["plain"][1], tot
+
+
+def test_batched_keyframes_match_single_calls(frame):
+    """lcc_encode_keyframes (several key frames per launch, plain or seeded) writes the same
+    streams as one call per frame."""
+    from paper_2008_06972_gb300 import lcc
+    seq = synth.sequence_cfg2()
+    c = H.ctx(seq.sensor, tile_h=8, tile_w=8, max_batch=4)
+    frames = [seq.frames[i] for i in (0, 3, 5)]
+    ds = [H.to_dev(f) for f in frames]
+    n = [len(f) for f in frames]
+    rng = np.random.default_rng(3)
+    props = [torch.from_numpy(np.concatenate([rng.normal(0, 3, (c.num_tiles, 1)), rng.normal(0, 1, (c.num_tiles, 4))],
+                                             axis=1).astype(np.float32)).cuda() for _ in frames]
+    for seeded in (False, True):
+        outs = [H.out_buf(c) for _ in frames]
+        nb = torch.zeros(len(frames), dtype=torch.int64, device="cuda")
+        c.lcc_encode_keyframes(ds, n, props if seeded else None, SKIP_LOGIT, outs, [o.numel() for o in outs], nb)
+        assert c.lcc_sync() == lcc.OK
+        nbs = nb.cpu().numpy()
+        for i, f in enumerate(frames):
+            one = H.out_buf(c)
+            nb1 = torch.zeros(1, dtype=torch.int64, device="cuda")
+            if seeded:
+                c.lcc_encode_keyframe_seeded(ds[i], n[i], props[i], SKIP_LOGIT, None, one, one.numel(), nb1)
+            else:
+                c.lcc_encode_keyframe(ds[i], n[i], None, one, one.numel(), nb1)
+            assert c.lcc_sync() == lcc.OK
+            assert one[:int(nb1.item())].cpu().numpy().tobytes() == outs[i][:nbs[i]].cpu().numpy().tobytes()
