@@ -599,6 +599,19 @@ def main():
     ktimes = ctx.lcc_kernel_times()
     ctx.lcc_set_profiling(False)
     launches_per_step = sum(v[0] for v in ktimes.values()) / args.steps
+    # tile-mode split and fit rounds of the last step (library statistics, all frames)
+    modes = {"empty": 0, "raw": 0, "run_start": 0, "run_cont": 0, "temporal": 0}
+    rounds_hist = [0] * 8
+    border = 0
+    for f in range(n_frames):
+        st_f = ctx.lcc_last_stats(f)
+        modes["empty"] += st_f["tiles_empty"]
+        modes["raw"] += st_f["tiles_raw"]
+        modes["run_start"] += st_f["tiles_run_start"]
+        modes["run_cont"] += st_f["tiles_run_cont"]
+        modes["temporal"] += st_f["tiles_temporal"]
+        rounds_hist = [a + b for a, b in zip(rounds_hist, st_f["fit_rounds"])]
+        border += st_f["tiles_borderline"]
 
     # ---- correctness of what was timed: decode every frame, max error vs the range image ----
     out_sizes = nbytes.cpu().numpy()
@@ -695,6 +708,7 @@ def main():
                        "fit_schedule": args.schedule, "l2": "flushed between steps (256 MiB write, untimed)",
                        "parallelism": f"replicas x{world}"},
             "max_decode_error_m": max_err,
+            "tile_modes": modes, "fit_rounds_hist": rounds_hist, "tiles_borderline": border,
             "compression_ratio": 12.0 * pts_step / total_bytes,
             "bytes_per_step": total_bytes,
             "kernel_ms_per_step": {k: v[1] / args.steps for k, v in ktimes.items()},

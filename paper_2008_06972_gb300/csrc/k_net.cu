@@ -430,9 +430,11 @@ constexpr int TPOS = 10 * 2 * 10;              // padded positions per 8-channel
 constexpr int TCHUNK = TPOS * 16;              // bytes per chunk (3200)
 constexpr int TW1 = 9 * 2 * C1 * 16, TW2 = 9 * (C1 / 8) * C2 * 16, TW3 = 9 * (C2 / 8) * C3 * 16;
 constexpr int TX = 2 * TCHUNK, TA1 = (C1 / 8) * TCHUNK, TA2 = (C2 / 8) * TCHUNK;
+constexpr int TSLOT = TX + TA1 + TA2;           // activation copies of one pair of tiles
 constexpr int TGP = kNetWarps * 2 * C3 * 4, TG = 2 * C3 * 4;
-constexpr size_t kTcSmem = (size_t)TW1 + TW2 + TW3 + TX + TA1 + TA2 + TGP + TG + 64;
-constexpr uint32_t kTmemCols = 64;
+constexpr int TPAR = (C1 + C2 + C3 + HID * C3 + HID + NOUT * HID + NOUT + 3) / 4 * 16;   // biases, head (fp32)
+constexpr size_t kTcSmem = (size_t)TW1 + TW2 + TW3 + 2 * (size_t)(TSLOT + TGP + TG) + TPAR + 64;
+constexpr uint32_t kTmemCols = 128;             // two 64-column accumulators, one per pair in flight
 constexpr long long kSpinLimit = 1ll << 22;
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -516,31 +518,46 @@ __device__ __forceinline__ void tc_conv(uint32_t tmem, uint32_t act, uint32_t wt
     }
 }
 
+// bulk copy global -> shared (TMA engine), completion counted on an mbarrier
+__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void *src, uint32_t bytes, uint32_t mbar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(dst),
+                 "l"(src), "r"(bytes), "r"(mbar)
+                 : "memory");
+}
+
+// Two pairs of tiles are in flight: while the warps run one pair's epilogue, the tensor
+// cores run the other pair's MMAs (separate activation copies, TMEM columns and mbarriers).
 __global__ void __launch_bounds__(kNetWarps * 32, 1) k_net_fwd_tc(NetDev nd, const bf16 *x, long long T, float *out,
                                                                   int *err) {
     extern __shared__ __align__(1024) uint8_t sm[];
     uint8_t *sW1 = sm, *sW2 = sW1 + TW1, *sW3 = sW2 + TW2;
-    uint8_t *sX = sW3 + TW3, *sA1 = sX + TX, *sA2 = sA1 + TA1;
-    float *sGP = reinterpret_cast<float *>(sA2 + TA2);     // [warp][tile][64]
-    float *sG = sGP + kNetWarps * 2 * C3;                 // [tile][64]
-    uint64_t *bar = reinterpret_cast<uint64_t *>(sG + 2 * C3);
-    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bar + 1);
+    uint8_t *sSlot = sW3 + TW3;                                        // [2][TSLOT]
+    float *sGP = reinterpret_cast<float *>(sSlot + 2 * TSLOT);         // [2][warp][tile][64]
+    float *sG = sGP + 2 * kNetWarps * 2 * C3;                          // [2][tile][64]
+    float *sPar = sG + 2 * 2 * C3;                                     // b1 b2 b3 F1b c1 F2b c2
+    float *sB1 = sPar, *sB2 = sB1 + C1, *sB3 = sB2 + C2, *sF1 = sB3 + C3, *sC1 = sF1 + HID * C3;
+    float *sF2 = sC1 + HID, *sC2 = sF2 + NOUT * HID;
+    uint64_t *bar = reinterpret_cast<uint64_t *>(reinterpret_cast<uint8_t *>(sPar) + TPAR);   // [0] weights, [1..2] slots
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bar + 3);
     int *s_fail = reinterpret_cast<int *>(tmem_slot + 1);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    // stage weights, zero the activation copies (borders stay zero)
-    {
-        const uint4 *src[3] = {reinterpret_cast<const uint4 *>(nd.T1), reinterpret_cast<const uint4 *>(nd.T2),
-                               reinterpret_cast<const uint4 *>(nd.T3)};
-        uint4 *dst[3] = {reinterpret_cast<uint4 *>(sW1), reinterpret_cast<uint4 *>(sW2), reinterpret_cast<uint4 *>(sW3)};
-        const int cnt[3] = {TW1 / 16, TW2 / 16, TW3 / 16};
-        for (int q = 0; q < 3; q++)
-            for (int i = tid; i < cnt[q]; i += blockDim.x) dst[q][i] = src[q][i];
-        uint4 *z = reinterpret_cast<uint4 *>(sX);
-        for (int i = tid; i < (TX + TA1 + TA2) / 16; i += blockDim.x) z[i] = make_uint4(0u, 0u, 0u, 0u);
-    }
+    const float *th = nd.theta;
     if (tid == 0) {
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(bar)) : "memory");
+        for (int i = 0; i < 3; i++)
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(bar + i)) : "memory");
         *s_fail = 0;
+    }
+    // zero both pairs' activation copies (borders stay zero); parameters of the epilogues
+    {
+        uint4 *z = reinterpret_cast<uint4 *>(sSlot);
+        for (int i = tid; i < 2 * TSLOT / 16; i += blockDim.x) z[i] = make_uint4(0u, 0u, 0u, 0u);
+        for (int i = tid; i < C1; i += blockDim.x) sB1[i] = th[OB1 + i];
+        for (int i = tid; i < C2; i += blockDim.x) sB2[i] = th[OB2 + i];
+        for (int i = tid; i < C3; i += blockDim.x) sB3[i] = th[OB3 + i];
+        for (int i = tid; i < HID * C3; i += blockDim.x) sF1[i] = nd.F1b[i];
+        for (int i = tid; i < HID; i += blockDim.x) sC1[i] = th[OC1 + i];
+        for (int i = tid; i < NOUT * HID; i += blockDim.x) sF2[i] = nd.F2b[i];
+        for (int i = tid; i < NOUT; i += blockDim.x) sC2[i] = th[OC2 + i];
     }
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(smem_u32(tmem_slot)),
@@ -548,106 +565,144 @@ __global__ void __launch_bounds__(kNetWarps * 32, 1) k_net_fwd_tc(NetDev nd, con
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::: "memory");
     }
+    __syncthreads();
+    // weights by the TMA engine: three bulk copies counted on barrier 0
+    if (tid == 0) {
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_u32(bar)),
+                     "r"((uint32_t)(TW1 + TW2 + TW3))
+                     : "memory");
+        bulk_g2s(smem_u32(sW1), nd.T1, TW1, smem_u32(bar));
+        bulk_g2s(smem_u32(sW2), nd.T2, TW2, smem_u32(bar));
+        bulk_g2s(smem_u32(sW3), nd.T3, TW3, smem_u32(bar));
+    }
+    if (!mbar_wait(smem_u32(bar), 0)) {
+        atomicExch(s_fail, 1);
+        if (err) atomicExch(err, 1);
+    }
     proxy_fence();
     tc_before_sync();
     __syncthreads();
     tc_after_sync();
     const uint32_t tmem = *tmem_slot;
-    const uint32_t mbar = smem_u32(bar);
-    const uint32_t aX = smem_u32(sX), aA1 = smem_u32(sA1), aA2 = smem_u32(sA2);
     const uint32_t aW1 = smem_u32(sW1), aW2 = smem_u32(sW2), aW3 = smem_u32(sW3);
-    const float *th = nd.theta;
     // this thread's GEMM row: r = 32 warp + lane -> (y, tile, x)
-    const int r = tid, grp = r >> 3, px = r & 7, py = grp >> 1, tl = grp & 1;
-    const uint32_t trow = tmem + ((uint32_t)(warp * 32) << 16);
-    uint32_t phase = 0;
-    for (long long pair = blockIdx.x; pair * 2 < T; pair += gridDim.x) {
-        const long long tile = pair * 2 + tl;
-        {   // input row (4 channels + 4 zero) of this thread's pixel
-            uint2 v = make_uint2(0u, 0u);
-            if (tile < T) v = *reinterpret_cast<const uint2 *>(x + ((size_t)tile * kPX + py * 8 + px) * C0);
-            *reinterpret_cast<uint4 *>(sX + tpos(0, py + 1, tl, px + 1)) = make_uint4(v.x, v.y, 0u, 0u);
+    const int grp = tid >> 3, px = tid & 7, py = grp >> 1, tl = grp & 1;
+    uint32_t phase[2] = {0u, 0u};
+    auto slot_x = [&](int sl) { return sSlot + sl * TSLOT; };
+    auto issue = [&](int sl, int layer) {   // thread 0: one convolution of pair slot sl
+        const uint32_t base = smem_u32(slot_x(sl));
+        const uint32_t d = tmem + (uint32_t)(sl * 64);
+        if (layer == 0) tc_conv<C0, C1>(d, base, aW1);
+        else if (layer == 1) tc_conv<C1, C2>(d, base + TX, aW2);
+        else tc_conv<C2, C3>(d, base + TX + TA1, aW3);
+        tc_commit(smem_u32(bar + 1 + sl));
+    };
+    auto epilogue_tc = [&](int sl, int layer) {   // all threads: wait, read TMEM, write the next copy
+        if (!mbar_wait(smem_u32(bar + 1 + sl), phase[sl])) {
+            atomicExch(s_fail, 1);
+            if (err) atomicExch(err, 1);
         }
-        // conv1 -> a1, conv2 -> a2, conv3 -> pooled sums
+        phase[sl] ^= 1u;
+        tc_after_sync();
+        const int cout = layer == 0 ? C1 : C2;
+        const float *bias = layer == 0 ? sB1 : layer == 1 ? sB2 : sB3;
+        uint8_t *dst = slot_x(sl) + (layer == 0 ? TX : TX + TA1);
+        const uint32_t trow = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(sl * 64);
+        float *gp = sGP + sl * kNetWarps * 2 * C3;
 #pragma unroll 1
-        for (int layer = 0; layer < 3; layer++) {
-            proxy_fence();
-            tc_before_sync();
-            __syncthreads();
-            tc_after_sync();
-            if (tid == 0) {
-                if (layer == 0) tc_conv<C0, C1>(tmem, aX, aW1);
-                else if (layer == 1) tc_conv<C1, C2>(tmem, aA1, aW2);
-                else tc_conv<C2, C3>(tmem, aA2, aW3);
-                tc_commit(mbar);
-            }
-            if (!mbar_wait(mbar, phase)) {
-                atomicExch(s_fail, 1);
-                if (err) atomicExch(err, 1);
-            }
-            phase ^= 1u;
-            tc_after_sync();
-            const int cout = layer == 0 ? C1 : C2;
-            const float *bias = th + (layer == 0 ? OB1 : layer == 1 ? OB2 : OB3);
-#pragma unroll 1
-            for (int c0 = 0; c0 < cout; c0 += 16) {
-                float v[16];
-                tc_ld16(trow + (uint32_t)c0, v);
-                tc_wait_ld();
+        for (int c0 = 0; c0 < cout; c0 += 16) {
+            float v[16];
+            tc_ld16(trow + (uint32_t)c0, v);
+            tc_wait_ld();
 #pragma unroll
-                for (int i = 0; i < 16; i++) v[i] = fmaxf(v[i] + __ldg(bias + c0 + i), 0.f);
-                if (layer < 2) {
-                    uint8_t *dst = layer == 0 ? sA1 : sA2;
+            for (int i = 0; i < 16; i++) v[i] = fmaxf(v[i] + bias[c0 + i], 0.f);
+            if (layer < 2) {
 #pragma unroll
-                    for (int h = 0; h < 2; h++) {
-                        uint32_t w[4];
+                for (int h = 0; h < 2; h++) {
+                    uint32_t w[4];
 #pragma unroll
-                        for (int q = 0; q < 4; q++) {
-                            const __nv_bfloat162 b2 = __floats2bfloat162_rn(v[8 * h + 2 * q], v[8 * h + 2 * q + 1]);
-                            w[q] = *reinterpret_cast<const uint32_t *>(&b2);
-                        }
-                        *reinterpret_cast<uint4 *>(dst + tpos(c0 / 8 + h, py + 1, tl, px + 1)) =
-                            make_uint4(w[0], w[1], w[2], w[3]);
+                    for (int q = 0; q < 4; q++) {
+                        const __nv_bfloat162 b2 = __floats2bfloat162_rn(v[8 * h + 2 * q], v[8 * h + 2 * q + 1]);
+                        w[q] = *reinterpret_cast<const uint32_t *>(&b2);
                     }
-                } else {
+                    *reinterpret_cast<uint4 *>(dst + tpos(c0 / 8 + h, py + 1, tl, px + 1)) =
+                        make_uint4(w[0], w[1], w[2], w[3]);
+                }
+            } else {
 #pragma unroll
-                    for (int i = 0; i < 16; i++) {
-                        float s2 = bfround(v[i]);
-                        s2 += __shfl_xor_sync(0xffffffffu, s2, 1);
-                        s2 += __shfl_xor_sync(0xffffffffu, s2, 2);
-                        s2 += __shfl_xor_sync(0xffffffffu, s2, 4);
-                        s2 += __shfl_xor_sync(0xffffffffu, s2, 16);
-                        if (lane == 0 || lane == 8) sGP[(warp * 2 + tl) * C3 + c0 + i] = s2;
-                    }
+                for (int i = 0; i < 16; i++) {
+                    float s2 = bfround(v[i]);
+                    s2 += __shfl_xor_sync(0xffffffffu, s2, 1);
+                    s2 += __shfl_xor_sync(0xffffffffu, s2, 2);
+                    s2 += __shfl_xor_sync(0xffffffffu, s2, 4);
+                    s2 += __shfl_xor_sync(0xffffffffu, s2, 16);
+                    if (lane == 0 || lane == 8) gp[(warp * 2 + tl) * C3 + c0 + i] = s2;
                 }
             }
         }
+        proxy_fence();
         tc_before_sync();
         __syncthreads();
         tc_after_sync();
-        if (*s_fail) break;   // read after the barrier: the same decision in every thread
-        {   // pooled vector of both tiles (fixed summation order over the warps)
+    };
+    for (long long pa = blockIdx.x; pa * 2 < T; pa += 2ll * gridDim.x) {
+        if (*s_fail) break;   // uniform: read after a barrier
+        const long long pb = pa + gridDim.x;
+        const bool hasB = pb * 2 < T;
+        const long long pr[2] = {pa, pb};
+        for (int sl = 0; sl < (hasB ? 2 : 1); sl++) {   // inputs (4 channels + 4 zero) of this thread's pixel
+            const long long tile = pr[sl] * 2 + tl;
+            uint2 v = make_uint2(0u, 0u);
+            if (tile < T) v = *reinterpret_cast<const uint2 *>(x + ((size_t)tile * kPX + py * 8 + px) * C0);
+            *reinterpret_cast<uint4 *>(slot_x(sl) + tpos(0, py + 1, tl, px + 1)) = make_uint4(v.x, v.y, 0u, 0u);
+        }
+        proxy_fence();
+        tc_before_sync();
+        __syncthreads();
+        tc_after_sync();
+        if (tid == 0) {
+            issue(0, 0);
+            if (hasB) issue(1, 0);
+        }
+#pragma unroll 1
+        for (int layer = 0; layer < 3; layer++) {
+            epilogue_tc(0, layer);
+            if (layer < 2 && tid == 0) issue(0, layer + 1);
+            if (hasB) {
+                epilogue_tc(1, layer);
+                if (layer < 2 && tid == 0) issue(1, layer + 1);
+            }
+        }
+        {   // pooled vectors (fixed summation order over the warps)
             const int t2 = tid >> 6, c = tid & 63;
-            float s2 = 0.f;
-            for (int w = 0; w < kNetWarps; w++) s2 += sGP[(w * 2 + t2) * C3 + c];
-            sG[t2 * C3 + c] = bfround(s2 * (1.0f / kPX));
+            for (int sl = 0; sl < (hasB ? 2 : 1); sl++) {
+                const float *gp = sGP + sl * kNetWarps * 2 * C3;
+                float s2 = 0.f;
+                for (int w = 0; w < kNetWarps; w++) s2 += gp[(w * 2 + t2) * C3 + c];
+                sG[(sl * 2 + t2) * C3 + c] = bfround(s2 * (1.0f / kPX));
+            }
         }
         __syncthreads();
-        if (warp < 2 && pair * 2 + warp < T) {   // head: warp w takes tile w of the pair
-            const float *gs = sG + warp * C3;
-            float yv = __ldg(th + OC1 + lane);
-            for (int c = 0; c < C3; c++) yv = fmaf(__ldg(nd.F1b + lane * C3 + c), gs[c], yv);
-            const float hj = bfround(fmaxf(yv, 0.f));
-            float o[NOUT];
+        {   // head: warp w takes tile (w & 1) of pair slot (w >> 1)
+            const int sl = warp >> 1, t2 = warp & 1;
+            const long long tile = pr[sl] * 2 + t2;
+            if ((sl == 0 || hasB) && tile < T) {
+                const float *gs = sG + (sl * 2 + t2) * C3;
+                float yv = sC1[lane];
+                for (int c = 0; c < C3; c++) yv = fmaf(sF1[lane * C3 + c], gs[c], yv);
+                const float hj = bfround(fmaxf(yv, 0.f));
+                float o[NOUT];
 #pragma unroll
-            for (int i = 0; i < NOUT; i++) {
-                float sacc = __ldg(nd.F2b + i * HID + lane) * hj;
+                for (int i = 0; i < NOUT; i++) {
+                    float sacc = sF2[i * HID + lane] * hj;
 #pragma unroll
-                for (int off = 16; off; off >>= 1) sacc += __shfl_xor_sync(0xffffffffu, sacc, off);
-                o[i] = sacc + __ldg(th + OC2 + i);
+                    for (int off = 16; off; off >>= 1) sacc += __shfl_xor_sync(0xffffffffu, sacc, off);
+                    o[i] = sacc + sC2[i];
+                }
+                if (lane < NOUT) out[(size_t)tile * NOUT + lane] = o[lane];
             }
-            if (lane < NOUT) out[(size_t)(pair * 2 + warp) * NOUT + lane] = o[lane];
         }
+        __syncthreads();
     }
     tc_before_sync();
     __syncthreads();
