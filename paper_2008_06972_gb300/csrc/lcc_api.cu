@@ -510,13 +510,26 @@ lcc_status lcc_encode_pframe(lcc_ctx *c, const lcc_keyframe *kf, const double po
     return lcc_encode_pframes(c, kf, 1, pose, &d_pts, &n, &d_out, &cap, out_bytes);
 }
 
-lcc_status lcc_encode_sequence(lcc_ctx *c, int32_t nframes, int32_t key_index, const double *poses,
-                               const float *const *d_pts, const int64_t *n, uint8_t *const *d_out,
-                               const uint64_t *cap, uint64_t *out_bytes, lcc_keyframe *kf) {
+}  // extern "C"
+
+namespace {
+
+// The sequence encode.  With h_pts, frame f's points are first copied from host memory into
+// d_pts[f]: the key frame's copy on the context stream, the P frames' copies on the side stream
+// where their binning and first fit pass follow, so the copies overlap the key frame's encode.
+lcc_status encode_sequence(lcc_ctx *c, int32_t nframes, int32_t key_index, const double *poses,
+                           const float *const *d_pts, const int64_t *n, uint8_t *const *d_out, const uint64_t *cap,
+                           uint64_t *out_bytes, lcc_keyframe *kf, const float *const *h_pts) {
     if (!c || !poses || key_index < 0 || key_index >= nframes) return LCC_ERR_INVALID_ARG;
     if (kf && kf->ctx != c) return LCC_ERR_INVALID_ARG;
     lcc_status st = check_frames(c, nframes, d_pts, n, d_out, cap);
     if (st != LCC_OK) return st;
+    const bool overlap = c->g.schedule == 0 && nframes > 1;
+    auto h2d = [&](int f, cudaStream_t sm) -> bool {
+        return !h_pts || n[f] == 0 ||
+               cudaMemcpyAsync(const_cast<float *>(d_pts[f]), h_pts[f], (size_t)n[f] * 16, cudaMemcpyHostToDevice,
+                               sm) == cudaSuccess;
+    };
     lcc_keyframe local;
     lcc_keyframe *k = kf;
     if (!k) {
@@ -529,7 +542,11 @@ lcc_status lcc_encode_sequence(lcc_ctx *c, int32_t nframes, int32_t key_index, c
     }
     int slots[kMaxBatch];
     for (int f = 0; f < nframes; f++) slots[f] = f;
-    if ((st = bin_frames(c, nframes, slots, d_pts, n)) != LCC_OK) return st;
+    if (!overlap) {
+        for (int f = 0; f < nframes; f++)
+            if (!h2d(f, c->stream)) return LCC_ERR_CUDA;
+        if ((st = bin_frames(c, nframes, slots, d_pts, n)) != LCC_OK) return st;
+    }
     const int kslot = key_index;
     uint8_t *kout = d_out[key_index];
     const uint64_t kcap = cap[key_index];
@@ -549,7 +566,7 @@ lcc_status lcc_encode_sequence(lcc_ctx *c, int32_t nframes, int32_t key_index, c
         np++;
     }
     float4 *kfo = k->planes;
-    if (np == 0 || c->g.schedule != 0) {
+    if (!overlap) {
         if ((st = encode_batch(c, 0, 1, &kslot, &kout, &kcap, nullptr, nullptr, &kfo)) != LCC_OK) return st;
         if ((st = encode_batch(c, 1, np, pslots, pout, pcap, pposes.data(), kfi, nullptr)) != LCC_OK) return st;
     } else {
@@ -559,16 +576,30 @@ lcc_status lcc_encode_sequence(lcc_ctx *c, int32_t nframes, int32_t key_index, c
         Poses pk, pp;
         prepare_batch(bk, pk, 0, 1, &kslot, &kout, &kcap, nullptr, nullptr, &kfo, nullptr);
         prepare_batch(bp, pp, 1, np, pslots, pout, pcap, pposes.data(), nullptr, nullptr, nullptr);
+        const float *pdp[kMaxBatch];
+        int64_t pn[kMaxBatch];
+        for (int q = 0; q < np; q++) {
+            pdp[q] = d_pts[pslots[q]];
+            pn[q] = n[pslots[q]];
+        }
         LCC_CUDA(cudaEventRecord(c->ev_fork, c->stream));
         LCC_CUDA(cudaStreamWaitEvent(c->side, c->ev_fork, 0));
         cudaStream_t main = c->stream;
-        c->stream = c->side;   // profiling events of this launch go to the side stream too
-        const int pi = prof_begin(c, 1);
-        const cudaError_t e = launch_fit(c->g, c->s, bp, pp, c->side);
-        prof_end(c, pi);
+        c->stream = c->side;   // launches (and their profiling events) on the side stream
+        lcc_status sst = LCC_OK;
+        for (int q = 0; q < np && sst == LCC_OK; q++)
+            if (!h2d(pslots[q], c->side)) sst = LCC_ERR_CUDA;
+        if (sst == LCC_OK) sst = bin_frames(c, np, pslots, pdp, pn);
+        if (sst == LCC_OK) {
+            const int pi = prof_begin(c, 1);
+            if (launch_fit(c->g, c->s, bp, pp, c->side) != cudaSuccess) sst = LCC_ERR_CUDA;
+            prof_end(c, pi);
+        }
         c->stream = main;
-        if (e != cudaSuccess) return LCC_ERR_CUDA;
+        if (sst != LCC_OK) return sst;
         LCC_CUDA(cudaEventRecord(c->ev_join, c->side));
+        if (!h2d(key_index, main)) return LCC_ERR_CUDA;
+        if ((st = bin_frames(c, 1, &kslot, &d_pts[key_index], &n[key_index])) != LCC_OK) return st;
         LCC_LAUNCH(c, 1, launch_fit(c->g, c->s, bk, pk, c->stream));
         if ((st = encode_tail(c, bk)) != LCC_OK) return st;
         LCC_CUDA(cudaStreamWaitEvent(c->stream, c->ev_join, 0));
@@ -578,6 +609,16 @@ lcc_status lcc_encode_sequence(lcc_ctx *c, int32_t nframes, int32_t key_index, c
     }
     c->last_nframes = nframes;
     return copy_bytes(c, nframes, slots, out_bytes);
+}
+
+}  // namespace
+
+extern "C" {
+
+lcc_status lcc_encode_sequence(lcc_ctx *c, int32_t nframes, int32_t key_index, const double *poses,
+                               const float *const *d_pts, const int64_t *n, uint8_t *const *d_out,
+                               const uint64_t *cap, uint64_t *out_bytes, lcc_keyframe *kf) {
+    return encode_sequence(c, nframes, key_index, poses, d_pts, n, d_out, cap, out_bytes, kf, nullptr);
 }
 
 lcc_status lcc_encode_sequence_host(lcc_ctx *c, int32_t nframes, int32_t key_index, const double *poses,
@@ -610,13 +651,12 @@ lcc_status lcc_encode_sequence_host(lcc_ctx *c, int32_t nframes, int32_t key_ind
     uint8_t *po = c->d_stage_out;
     for (int f = 0; f < nframes; f++) {
         dp[f] = (const float *)pp;
-        if (n[f]) LCC_CUDA(cudaMemcpyAsync(pp, h_pts[f], (size_t)n[f] * 16, cudaMemcpyHostToDevice, c->stream));
         pp += align256((size_t)n[f] * 16);
         dout[f] = po;
         po += align256((size_t)cap[f]);
     }
-    lcc_status st = lcc_encode_sequence(c, nframes, key_index, poses, dp, n, dout, cap,
-                                        (uint64_t *)c->d_stage_bytes, nullptr);
+    lcc_status st = encode_sequence(c, nframes, key_index, poses, dp, n, dout, cap, (uint64_t *)c->d_stage_bytes,
+                                    nullptr, h_pts);
     if (st != LCC_OK) return st;
     LCC_CUDA(cudaMemcpyAsync(out_bytes, c->d_stage_bytes, sizeof(uint64_t) * nframes, cudaMemcpyDeviceToHost,
                              c->stream));
