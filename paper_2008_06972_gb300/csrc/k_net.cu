@@ -431,7 +431,8 @@ constexpr int TCHUNK = TPOS * 16;              // bytes per chunk (3200)
 constexpr int TW1 = 9 * 2 * C1 * 16, TW2 = 9 * (C1 / 8) * C2 * 16, TW3 = 9 * (C2 / 8) * C3 * 16;
 constexpr int TX = 2 * TCHUNK, TA1 = (C1 / 8) * TCHUNK, TA2 = (C2 / 8) * TCHUNK;
 constexpr int TSLOT = TX + TA1 + TA2;           // activation copies of one pair of tiles
-constexpr int TGP = kNetWarps * 2 * C3 * 4, TG = 2 * C3 * 4;
+constexpr int kTcWarps = 8;                     // two warps per TMEM lane quadrant (column halves)
+constexpr int TGP = 4 * 2 * C3 * 4, TG = 2 * C3 * 4;
 constexpr int TPAR = (C1 + C2 + C3 + HID * C3 + HID + NOUT * HID + NOUT + 3) / 4 * 16;   // biases, head (fp32)
 constexpr size_t kTcSmem = (size_t)TW1 + TW2 + TW3 + 2 * (size_t)(TSLOT + TGP + TG) + TPAR + 64;
 constexpr uint32_t kTmemCols = 128;             // two 64-column accumulators, one per pair in flight
@@ -527,13 +528,13 @@ __device__ __forceinline__ void bulk_g2s(uint32_t dst, const void *src, uint32_t
 
 // Two pairs of tiles are in flight: while the warps run one pair's epilogue, the tensor
 // cores run the other pair's MMAs (separate activation copies, TMEM columns and mbarriers).
-__global__ void __launch_bounds__(kNetWarps * 32, 1) k_net_fwd_tc(NetDev nd, const bf16 *x, long long T, float *out,
+__global__ void __launch_bounds__(kTcWarps * 32, 1) k_net_fwd_tc(NetDev nd, const bf16 *x, long long T, float *out,
                                                                   int *err) {
     extern __shared__ __align__(1024) uint8_t sm[];
     uint8_t *sW1 = sm, *sW2 = sW1 + TW1, *sW3 = sW2 + TW2;
     uint8_t *sSlot = sW3 + TW3;                                        // [2][TSLOT]
     float *sGP = reinterpret_cast<float *>(sSlot + 2 * TSLOT);         // [2][warp][tile][64]
-    float *sG = sGP + 2 * kNetWarps * 2 * C3;                          // [2][tile][64]
+    float *sG = sGP + 2 * 4 * 2 * C3;                                  // [2][tile][64]
     float *sPar = sG + 2 * 2 * C3;                                     // b1 b2 b3 F1b c1 F2b c2
     float *sB1 = sPar, *sB2 = sB1 + C1, *sB3 = sB2 + C2, *sF1 = sB3 + C3, *sC1 = sF1 + HID * C3;
     float *sF2 = sC1 + HID, *sC2 = sF2 + NOUT * HID;
@@ -585,8 +586,9 @@ __global__ void __launch_bounds__(kNetWarps * 32, 1) k_net_fwd_tc(NetDev nd, con
     tc_after_sync();
     const uint32_t tmem = *tmem_slot;
     const uint32_t aW1 = smem_u32(sW1), aW2 = smem_u32(sW2), aW3 = smem_u32(sW3);
-    // this thread's GEMM row: r = 32 warp + lane -> (y, tile, x)
-    const int grp = tid >> 3, px = tid & 7, py = grp >> 1, tl = grp & 1;
+    // this thread's GEMM row: r = 32 (warp % 4) + lane -> (y, tile, x); its column half: warp / 4
+    const int quad = warp & 3, half = warp >> 2;
+    const int row = quad * 32 + lane, grp = row >> 3, px = row & 7, py = grp >> 1, tl = grp & 1;
     uint32_t phase[2] = {0u, 0u};
     auto slot_x = [&](int sl) { return sSlot + sl * TSLOT; };
     auto issue = [&](int sl, int layer) {   // thread 0: one convolution of pair slot sl
@@ -607,10 +609,11 @@ __global__ void __launch_bounds__(kNetWarps * 32, 1) k_net_fwd_tc(NetDev nd, con
         const int cout = layer == 0 ? C1 : C2;
         const float *bias = layer == 0 ? sB1 : layer == 1 ? sB2 : sB3;
         uint8_t *dst = slot_x(sl) + (layer == 0 ? TX : TX + TA1);
-        const uint32_t trow = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(sl * 64);
-        float *gp = sGP + sl * kNetWarps * 2 * C3;
+        const uint32_t trow = tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(sl * 64);
+        float *gp = sGP + sl * 4 * 2 * C3;
+        const int cbeg = half * (cout / 2), cend = cbeg + cout / 2;
 #pragma unroll 1
-        for (int c0 = 0; c0 < cout; c0 += 16) {
+        for (int c0 = cbeg; c0 < cend; c0 += 16) {
             float v[16];
             tc_ld16(trow + (uint32_t)c0, v);
             tc_wait_ld();
@@ -636,7 +639,7 @@ __global__ void __launch_bounds__(kNetWarps * 32, 1) k_net_fwd_tc(NetDev nd, con
                     s2 += __shfl_xor_sync(0xffffffffu, s2, 2);
                     s2 += __shfl_xor_sync(0xffffffffu, s2, 4);
                     s2 += __shfl_xor_sync(0xffffffffu, s2, 16);
-                    if (lane == 0 || lane == 8) gp[(warp * 2 + tl) * C3 + c0 + i] = s2;
+                    if (lane == 0 || lane == 8) gp[(quad * 2 + tl) * C3 + c0 + i] = s2;
                 }
             }
         }
@@ -650,7 +653,7 @@ __global__ void __launch_bounds__(kNetWarps * 32, 1) k_net_fwd_tc(NetDev nd, con
         const long long pb = pa + gridDim.x;
         const bool hasB = pb * 2 < T;
         const long long pr[2] = {pa, pb};
-        for (int sl = 0; sl < (hasB ? 2 : 1); sl++) {   // inputs (4 channels + 4 zero) of this thread's pixel
+        for (int sl = half; sl < (hasB ? 2 : 1); sl += 2) {   // inputs (4 channels + 4 zero): warps 4-7 fill slot 1
             const long long tile = pr[sl] * 2 + tl;
             uint2 v = make_uint2(0u, 0u);
             if (tile < T) v = *reinterpret_cast<const uint2 *>(x + ((size_t)tile * kPX + py * 8 + px) * C0);
@@ -673,17 +676,17 @@ __global__ void __launch_bounds__(kNetWarps * 32, 1) k_net_fwd_tc(NetDev nd, con
                 if (layer < 2 && tid == 0) issue(1, layer + 1);
             }
         }
-        {   // pooled vectors (fixed summation order over the warps)
-            const int t2 = tid >> 6, c = tid & 63;
-            for (int sl = 0; sl < (hasB ? 2 : 1); sl++) {
-                const float *gp = sGP + sl * kNetWarps * 2 * C3;
+        {   // pooled vectors (fixed summation order over the lane quadrants): thread -> (slot, tile, channel)
+            const int sl = tid >> 7, t2 = (tid >> 6) & 1, c = tid & 63;
+            if (sl == 0 || hasB) {
+                const float *gp = sGP + sl * 4 * 2 * C3;
                 float s2 = 0.f;
-                for (int w = 0; w < kNetWarps; w++) s2 += gp[(w * 2 + t2) * C3 + c];
+                for (int w = 0; w < 4; w++) s2 += gp[(w * 2 + t2) * C3 + c];
                 sG[(sl * 2 + t2) * C3 + c] = bfround(s2 * (1.0f / kPX));
             }
         }
         __syncthreads();
-        {   // head: warp w takes tile (w & 1) of pair slot (w >> 1)
+        if (warp < 4) {   // head: warp w < 4 takes tile (w & 1) of pair slot (w >> 1)
             const int sl = warp >> 1, t2 = warp & 1;
             const long long tile = pr[sl] * 2 + t2;
             if ((sl == 0 || hasB) && tile < T) {
@@ -1186,7 +1189,7 @@ lcc_status lcc_net_forward(lcc_net *net, const uint16_t *d_x, int64_t ntiles, fl
     if (ntiles == 0) return LCC_OK;
     const int64_t pairs = (ntiles + 1) / 2;
     const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(pairs, net->sms));
-    k_net_fwd_tc<<<grid, kNetWarps * 32, kTcSmem, net->stream>>>(net->nd, reinterpret_cast<const bf16 *>(d_x), ntiles,
+    k_net_fwd_tc<<<grid, kTcWarps * 32, kTcSmem, net->stream>>>(net->nd, reinterpret_cast<const bf16 *>(d_x), ntiles,
                                                                   d_out, net->err);
     return cudaGetLastError() == cudaSuccess ? LCC_OK : LCC_ERR_CUDA;
 }
