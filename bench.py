@@ -67,6 +67,7 @@ def peaks():
 
 
 def make_workload(rank: int):
+    """Each rank encodes its own sequence (weak scaling): sequence id = rank."""
     import synth
     seq = synth.sequence_cfg2(sequence_id=rank)
     return seq
@@ -584,12 +585,10 @@ def main():
     st = ctx.lcc_sync()
     assert st == lcc.OK, lcc.status_string(st)
     ms = np.array([a.elapsed_time(b) for a, b in evs])
-    ms_step = float(ms.mean())
-    if dist:
-        t = torch.tensor([ms_step], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_step = float(t.item())
-    value = pts_step * world / (ms_step * 1e-3) / 1e6
+    from paper_2008_06972_gb300 import multi
+    # whole job: all ranks' points over the slowest rank's mean step time
+    value, sec_step, pts_job = multi.job_value(pts_step, float(ms.mean()) * 1e-3, dist, "cuda")
+    ms_step = sec_step * 1e3
 
     # ---- per-kernel times (same workload, profiling events around each launch) ----
     ctx.lcc_set_profiling(True)
@@ -643,11 +642,7 @@ def main():
     for _ in range(e2e_steps):
         nb = ctx.lcc_encode_sequence_host(seq.key_index, seq.poses, h_pts, h_out, [cap] * n_frames)
     e2e_s = (time.perf_counter() - t0) / e2e_steps
-    if dist:
-        t = torch.tensor([e2e_s], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
-    e2e_value = pts_step * world / e2e_s / 1e6
+    e2e_value, e2e_s, _ = multi.job_value(pts_step, e2e_s, dist, "cuda")
 
     # ---- roofline of the dominant kernel ----
     hbm, src = peaks()

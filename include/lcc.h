@@ -265,6 +265,13 @@ lcc_status lcc_net_gradient(lcc_net *net, const uint16_t *d_x, const float *d_la
 lcc_status lcc_net_train_step(lcc_net *net, const uint16_t *d_x, const float *d_labels, int64_t ntiles, float lr,
                               int32_t step, float *d_loss);
 
+/* Self-test of the bounded device waits (failure detection without a fault):
+ * one kernel waits, at most `limit` polls, on an mbarrier that nothing
+ * arrives on, the same bounded wait the tcgen05 kernels use.  Returns
+ * LCC_ERR_TIMEOUT when the wait expired as it must, the context stays usable.
+ * Synchronous.  Not in the paper. */
+lcc_status lcc_selftest_bounded_wait(int64_t limit, void *cuda_stream);
+
 /* ---- Range image without a context or any allocation ----
  *
  * The paper has no counterpart: this is an implementation entry point.  It

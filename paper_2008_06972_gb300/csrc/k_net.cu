@@ -466,8 +466,8 @@ __device__ __forceinline__ void tc_commit(uint32_t mbar) {
 }
 
 // bounded wait on an mbarrier phase; false if the limit was reached
-__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity) {
-    for (long long it = 0; it < kSpinLimit; it++) {
+__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity, long long limit = kSpinLimit) {
+    for (long long it = 0; it < limit; it++) {
         uint32_t done;
         asm volatile(
             "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
@@ -712,6 +712,16 @@ __global__ void __launch_bounds__(kTcWarps * 32, 1) k_net_fwd_tc(NetDev nd, cons
     tc_after_sync();
     if (warp == 0)
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(kTmemCols) : "memory");
+}
+
+// Failure detection without a fault: an mbarrier that nothing arrives on, waited on with the
+// same bounded wait the tcgen05 kernels use; the expired wait sets the error word and the
+// kernel returns normally.
+__global__ void k_bounded_wait_selftest(long long limit, int *err) {
+    __shared__ uint64_t bar;
+    if (threadIdx.x == 0) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(&bar)) : "memory");
+    __syncthreads();
+    if (!mbar_wait(smem_u32(&bar), 0, limit) && threadIdx.x == 0) atomicExch(err, 1);
 }
 
 // ------------------------------------------------------------------ backward: loss and head --
@@ -1192,6 +1202,21 @@ lcc_status lcc_net_forward(lcc_net *net, const uint16_t *d_x, int64_t ntiles, fl
     k_net_fwd_tc<<<grid, kTcWarps * 32, kTcSmem, net->stream>>>(net->nd, reinterpret_cast<const bf16 *>(d_x), ntiles,
                                                                   d_out, net->err);
     return cudaGetLastError() == cudaSuccess ? LCC_OK : LCC_ERR_CUDA;
+}
+
+lcc_status lcc_selftest_bounded_wait(int64_t limit, void *cuda_stream) {
+    if (limit < 1 || limit > ((int64_t)1 << 30)) return LCC_ERR_INVALID_ARG;
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    int *d_err = nullptr;
+    LCC_CUDA(cudaMalloc(&d_err, sizeof(int)));
+    int e = 0;
+    const bool ok = cudaMemsetAsync(d_err, 0, sizeof(int), st) == cudaSuccess &&
+                    (k_bounded_wait_selftest<<<1, 32, 0, st>>>(limit, d_err), cudaGetLastError() == cudaSuccess) &&
+                    cudaMemcpyAsync(&e, d_err, sizeof(int), cudaMemcpyDeviceToHost, st) == cudaSuccess &&
+                    cudaStreamSynchronize(st) == cudaSuccess;
+    cudaFree(d_err);
+    if (!ok) return LCC_ERR_CUDA;
+    return e ? LCC_ERR_TIMEOUT : LCC_OK;
 }
 
 lcc_status lcc_net_sync(lcc_net *net) {

@@ -121,6 +121,7 @@ def load(path: str = LIB_PATH):
         "lcc_net_tile_inputs": (i32, [vp, vp, i64, vp, vp]),
         "lcc_net_forward": (i32, [vp, vp, i64, vp]),
         "lcc_net_sync": (i32, [vp]),
+        "lcc_selftest_bounded_wait": (i32, [i64, vp]),
         "lcc_net_gradient": (i32, [vp, vp, vp, i64, vp, vp]),
         "lcc_net_train_step": (i32, [vp, vp, vp, i64, ctypes.c_float, i32, vp]),
         "lcc_plan_create": (i32, [vp, i32, vp, i32, vp]),
@@ -150,7 +151,7 @@ def exported_symbols() -> list[str]:
             "lcc_encode_sequence_host", "lcc_keyframe_from_stream", "lcc_decode", "lcc_sync", "lcc_last_stats",
             "lcc_tile_records", "lcc_set_profiling", "lcc_kernel_times", "lcc_range_image_static", "lcc_net_num_params", "lcc_net_create", "lcc_net_destroy",
             "lcc_net_get_params", "lcc_net_set_params", "lcc_net_tile_inputs", "lcc_net_forward", "lcc_net_sync", "lcc_net_gradient",
-            "lcc_net_train_step", "lcc_plan_create", "lcc_plan_update",
+            "lcc_net_train_step", "lcc_selftest_bounded_wait", "lcc_plan_create", "lcc_plan_update",
             "lcc_plan_encode", "lcc_plan_capture", "lcc_plan_replay", "lcc_plan_sync", "lcc_plan_get_info",
             "lcc_plan_destroy", "lcc_autotune"]
 

@@ -387,3 +387,14 @@ def test_invalid_arguments_fail_fast(cfg1):
     with pytest.raises(lcc.LccError) as e:
         c.lcc_encode_keyframe(d, len(pts), None, out[1:], out.numel() - 1, None)   # misaligned output
     assert e.value.status == lcc.ERR_INVALID_ARG
+
+
+def test_bounded_wait_expires_and_reports_timeout(cfg1):
+    """Failure detection without a fault: a device wait on a barrier nothing arrives on gives up
+    after its limit, the host sees LCC_ERR_TIMEOUT, and the GPU keeps working."""
+    from paper_2008_06972_gb300 import lcc
+    assert lcc.load().lcc_selftest_bounded_wait(1 << 12, None) == lcc.ERR_TIMEOUT
+    sensor, pts = cfg1
+    c = H.ctx(sensor)
+    bits, _ = H.encode_keyframe(c, pts)
+    assert len(bits) > 64
