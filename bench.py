@@ -39,7 +39,7 @@ UNIT = "Mpoints/s"
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="lcc", choices=["lcc", "reference"])
     ap.add_argument("--tile", default="4x4")
@@ -158,8 +158,20 @@ class Clocks:
         try:
             self.fh = open(self.path, "w")
             self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={q}", "--format=csv,noheader,nounits",
-                                          "-lms", "100", "-i", str(int(os.environ.get("LOCAL_RANK", "0")))],
+                                          "-lms", "10", "-i", str(int(os.environ.get("LOCAL_RANK", "0")))],
                                          stdout=self.fh, stderr=subprocess.DEVNULL)
+            # enter the timed region only once the sampler is producing samples
+            t0 = time.perf_counter()
+            while time.perf_counter() - t0 < 10.0:
+                self.fh.flush()
+                if os.path.getsize(self.path) > 0:
+                    break
+                time.sleep(0.01)
+            self.skip = 0
+            try:
+                self.skip = len(open(self.path).read().strip().splitlines())   # samples before the region
+            except Exception:
+                pass
         except Exception:
             self.proc = None
         return self
@@ -176,6 +188,7 @@ class Clocks:
     def summary(self):
         try:
             rows = [r.split(",") for r in open(self.path).read().strip().splitlines()]
+            rows = rows[getattr(self, "skip", 0):] or rows[-1:]
             rows = [[c.strip() for c in r] for r in rows if len(r) >= 9]
         except Exception:
             rows = []

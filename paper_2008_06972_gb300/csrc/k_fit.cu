@@ -535,13 +535,15 @@ __global__ void __launch_bounds__(kFitThreads) k_fit_first(Geometry g, Scratch s
         const float *prop = b.prop[f] ? b.prop[f] + 5 * (size_t)t : nullptr;
         if (!kQueue) {
             spatial_rounds<TH_, TW_>(tv, o, g.R + 1, prop, b.skip_logit);
-        } else if (b.kind == 1) {
-            queued = true;   // P-frame spatial fallback from its first round, in the dense pass
+        } else if (b.kind == 1 && b.kf[f]) {
+            queued = true;   // P-frame spatial fallback after its temporal test: from its first round, dense
         } else {
             queued = !spatial_rounds<TH_, TW_>(tv, o, 1, prop, b.skip_logit);
         }
     }
-    if (kQueue) queue_push(queued, ((uint32_t)f << 26) | (uint32_t)t, s.queue, s.qcount);
+    if (kQueue)
+        queue_push(queued, ((uint32_t)f << 26) | (uint32_t)t, s.queue + (size_t)b.qset * 2 * s.qcap,
+                   s.qcount + 8 * b.qset);
     write_rec(recs + t, o);
 }
 
@@ -550,9 +552,11 @@ __global__ void __launch_bounds__(kFitThreads) k_fit_first(Geometry g, Scratch s
 template <int TH_, int TW_>
 __global__ void __launch_bounds__(kFitThreads) k_fit_round(Geometry g, Scratch s, Batch b, int in_q, int out_q) {
     using TV = TileView<TH_, TW_>;
-    const uint32_t n_in = s.qcount[in_q];
-    const uint32_t *qin = s.queue + (size_t)(in_q & 1) * s.qcap;
-    uint32_t *qout = s.queue + (size_t)(out_q & 1) * s.qcap;
+    uint32_t *queue = s.queue + (size_t)b.qset * 2 * s.qcap;
+    uint32_t *qcount = s.qcount + 8 * b.qset;
+    const uint32_t n_in = qcount[in_q];
+    const uint32_t *qin = queue + (size_t)(in_q & 1) * s.qcap;
+    uint32_t *qout = queue + (size_t)(out_q & 1) * s.qcap;
     for (uint32_t idx = blockIdx.x * kFitThreads + threadIdx.x; idx < n_in; idx += gridDim.x * kFitThreads) {
         const uint32_t item = qin[idx];
         const int f = (int)(item >> 26), t = (int)(item & 0x3FFFFFFu);
@@ -561,7 +565,7 @@ __global__ void __launch_bounds__(kFitThreads) k_fit_round(Geometry g, Scratch s
         const TV tv(g, rimg, t);
         RecOut o = read_rec(recs + t);
         const bool done = spatial_rounds<TH_, TW_>(tv, o, 1);
-        queue_push(!done, item, qout, s.qcount + out_q);
+        queue_push(!done, item, qout, qcount + out_q);
         write_rec(recs + t, o);
     }
 }
@@ -673,7 +677,7 @@ static cudaError_t launch_fit_first_t(const Geometry &g, const Scratch &s, const
                                      cudaStream_t st) {
     dim3 grid((g.NT + kFitThreads - 1) / kFitThreads, b.nframes);
     if (g.schedule == 1) {
-        cudaError_t e = cudaMemsetAsync(s.qcount, 0, sizeof(uint32_t) * 8, st);
+        cudaError_t e = cudaMemsetAsync(s.qcount + 8 * b.qset, 0, sizeof(uint32_t) * 8, st);
         if (e != cudaSuccess) return e;
         k_fit_first<TH_, TW_, true><<<grid, kFitThreads, 0, st>>>(g, s, b, p);
     } else {
@@ -696,10 +700,11 @@ static cudaError_t launch_lookbehind_t(const Geometry &g, const Scratch &s, cons
 }
 
 template <int TH_, int TW_>
-static cudaError_t launch_fit_rounds_t(const Geometry &g, const Scratch &s, const Batch &b, cudaStream_t st) {
+static cudaError_t launch_queued_rounds_t(const Geometry &g, const Scratch &s, const Batch &b, cudaStream_t st) {
     if (g.schedule == 1) {
-        // key frames did round 1 already; P frames start their spatial rounds here
-        const int rounds_left = g.R + (b.kind == 1 ? 1 : 0);
+        // round 1 ran in the first pass, except for P frames whose first pass was their temporal
+        // test: their spatial rounds all run here
+        const int rounds_left = g.R + ((b.kind == 1 && b.kf[0]) ? 1 : 0);
         const long long worst = (long long)g.NT * b.nframes;
         const int blocks = (int)std::min<long long>((worst + kFitThreads - 1) / kFitThreads, 152 * 8);
         for (int r = 0; r < rounds_left; r++) {
@@ -708,6 +713,13 @@ static cudaError_t launch_fit_rounds_t(const Geometry &g, const Scratch &s, cons
             if (e != cudaSuccess) return e;
         }
     }
+    return cudaSuccess;
+}
+
+template <int TH_, int TW_>
+static cudaError_t launch_fit_rounds_t(const Geometry &g, const Scratch &s, const Batch &b, cudaStream_t st) {
+    const cudaError_t e = launch_queued_rounds_t<TH_, TW_>(g, s, b, st);
+    if (e != cudaSuccess) return e;
     return launch_lookbehind_t<TH_, TW_>(g, s, b, st);
 }
 
@@ -733,6 +745,24 @@ cudaError_t launch_fit(const Geometry &g, const Scratch &s, const Batch &b, cons
     if (g.th == 4 && g.tw == 8) return launch_fit_first_t<4, 8>(g, s, b, p, st);
     if (g.th == 8 && g.tw == 8) return launch_fit_first_t<8, 8>(g, s, b, p, st);
     if (g.th == 8 && g.tw == 16) return launch_fit_first_t<8, 16>(g, s, b, p, st);
+    return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_queued_rounds(const Geometry &g, const Scratch &s, const Batch &b, cudaStream_t st) {
+    if (b.nframes <= 0) return cudaSuccess;
+    if (g.th == 4 && g.tw == 4) return launch_queued_rounds_t<4, 4>(g, s, b, st);
+    if (g.th == 4 && g.tw == 8) return launch_queued_rounds_t<4, 8>(g, s, b, st);
+    if (g.th == 8 && g.tw == 8) return launch_queued_rounds_t<8, 8>(g, s, b, st);
+    if (g.th == 8 && g.tw == 16) return launch_queued_rounds_t<8, 16>(g, s, b, st);
+    return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_lookbehind(const Geometry &g, const Scratch &s, const Batch &b, cudaStream_t st) {
+    if (b.nframes <= 0) return cudaSuccess;
+    if (g.th == 4 && g.tw == 4) return launch_lookbehind_t<4, 4>(g, s, b, st);
+    if (g.th == 4 && g.tw == 8) return launch_lookbehind_t<4, 8>(g, s, b, st);
+    if (g.th == 8 && g.tw == 8) return launch_lookbehind_t<8, 8>(g, s, b, st);
+    if (g.th == 8 && g.tw == 16) return launch_lookbehind_t<8, 16>(g, s, b, st);
     return cudaErrorInvalidValue;
 }
 

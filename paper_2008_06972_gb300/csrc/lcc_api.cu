@@ -126,9 +126,14 @@ void prepare_batch(Batch &b, Poses &p, int kind, int nframes, const int *slots, 
         for (int f = 0; f < nframes; f++) memcpy(p.m[f], poses + 16 * f, 16 * sizeof(double));
 }
 
-// Everything after the first fit pass: further rounds and the run pre-test, merge, scan, pack.
-lcc_status encode_tail(lcc_ctx *c, const Batch &b) {
-    LCC_LAUNCH(c, 8, launch_fit_rounds(c->g, c->s, b, c->stream));
+// Everything after the first fit pass: further rounds (unless already run) and the run
+// pre-test, merge, scan, pack.
+lcc_status encode_tail(lcc_ctx *c, const Batch &b, bool rounds_done = false) {
+    if (rounds_done) {
+        LCC_LAUNCH(c, 8, launch_lookbehind(c->g, c->s, b, c->stream));
+    } else {
+        LCC_LAUNCH(c, 8, launch_fit_rounds(c->g, c->s, b, c->stream));
+    }
     LCC_LAUNCH(c, 2, launch_merge(c->g, c->s, b, c->stream));
     LCC_LAUNCH(c, 3, launch_scan(c->g, c->s, b, c->stream));
     LCC_LAUNCH(c, 4, launch_pack(c->g, c->s, b, c->stream));
@@ -322,7 +327,7 @@ lcc_status lcc_create(lcc_ctx **out, const lcc_sensor *sensor, const lcc_params 
     const size_t o_rowtot = o_lbcnt + align256(sl * nt * 32);
     const size_t o_rowbase = o_rowtot + align256(sl * (size_t)g.TR * 32);
     const size_t o_queue = o_rowbase + align256(sl * (size_t)g.TR * 32);
-    const size_t o_qcount = o_queue + align256(2 * sl * nt * 4);
+    const size_t o_qcount = o_queue + align256(4 * sl * nt * 4);
     const size_t total = o_qcount + 256;
     if (cudaMalloc(&c->d_scratch, total) != cudaSuccess) {
         cudaFree(c->d_tables);
@@ -524,7 +529,7 @@ lcc_status encode_sequence(lcc_ctx *c, int32_t nframes, int32_t key_index, const
     if (kf && kf->ctx != c) return LCC_ERR_INVALID_ARG;
     lcc_status st = check_frames(c, nframes, d_pts, n, d_out, cap);
     if (st != LCC_OK) return st;
-    const bool overlap = c->g.schedule == 0 && nframes > 1;
+    const bool overlap = nframes > 1;
     auto h2d = [&](int f, cudaStream_t sm) -> bool {
         return !h_pts || n[f] == 0 ||
                cudaMemcpyAsync(const_cast<float *>(d_pts[f]), h_pts[f], (size_t)n[f] * 16, cudaMemcpyHostToDevice,
@@ -576,6 +581,7 @@ lcc_status encode_sequence(lcc_ctx *c, int32_t nframes, int32_t key_index, const
         Poses pk, pp;
         prepare_batch(bk, pk, 0, 1, &kslot, &kout, &kcap, nullptr, nullptr, &kfo, nullptr);
         prepare_batch(bp, pp, 1, np, pslots, pout, pcap, pposes.data(), nullptr, nullptr, nullptr);
+        bp.qset = 1;   // the P frames' queued rounds run beside the key frame's: their own queues
         const float *pdp[kMaxBatch];
         int64_t pn[kMaxBatch];
         for (int q = 0; q < np; q++) {
@@ -595,6 +601,11 @@ lcc_status encode_sequence(lcc_ctx *c, int32_t nframes, int32_t key_index, const
             if (launch_fit(c->g, c->s, bp, pp, c->side) != cudaSuccess) sst = LCC_ERR_CUDA;
             prof_end(c, pi);
         }
+        if (sst == LCC_OK && c->g.schedule == 1) {   // the rest of their spatial rounds, still beside K
+            const int pi = prof_begin(c, 8);
+            if (launch_queued_rounds(c->g, c->s, bp, c->side) != cudaSuccess) sst = LCC_ERR_CUDA;
+            prof_end(c, pi);
+        }
         c->stream = main;
         if (sst != LCC_OK) return sst;
         LCC_CUDA(cudaEventRecord(c->ev_join, c->side));
@@ -605,7 +616,7 @@ lcc_status encode_sequence(lcc_ctx *c, int32_t nframes, int32_t key_index, const
         LCC_CUDA(cudaStreamWaitEvent(c->stream, c->ev_join, 0));
         for (int f = 0; f < np; f++) bp.kf[f] = k->planes;
         LCC_LAUNCH(c, 9, launch_temporal(c->g, c->s, bp, pp, c->stream));
-        if ((st = encode_tail(c, bp)) != LCC_OK) return st;
+        if ((st = encode_tail(c, bp, true)) != LCC_OK) return st;
     }
     c->last_nframes = nframes;
     return copy_bytes(c, nframes, slots, out_bytes);

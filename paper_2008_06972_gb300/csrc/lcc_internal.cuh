@@ -123,8 +123,8 @@ struct Scratch {
     uint8_t *lbcnt;      // [slots][NT][32] run pre-test inlier counts (byte j: vs the plane of tile t-1-j)
     uint32_t *rowtot;    // [slots][TR][8] per tile-row totals: cand, fitted, raw, run, temporal, valid
     uint32_t *rowbase;   // [slots][TR][8] exclusive prefix of rowtot over the frame's rows
-    uint32_t *queue;     // [2][qcap] fit work queues (frame << 26 | tile)
-    uint32_t *qcount;    // [8] items pushed per fit round
+    uint32_t *queue;     // [2 sets][2][qcap] fit work queues (frame << 26 | tile)
+    uint32_t *qcount;    // [2 sets][8] items pushed per fit round
     uint32_t qcap;       // entries per queue (slots * tiles)
 };
 
@@ -142,6 +142,7 @@ struct Batch {
     float4 *kf_out[kMaxBatch];     // per frame: key-frame plane table to fill (K frames) or NULL
     unsigned long long *nbytes_out[kMaxBatch];  // per frame: extra copy of the stream size, or NULL
     const float *prop[kMaxBatch];  // per frame: fit proposals [NT][5] (logit, v, d_rel), or NULL
+    int qset;                      // queue set of the queued fit schedule (batches that overlap use different sets)
     float skip_logit;              // tiles whose proposal logit is below this are not fitted
 };
 
@@ -332,6 +333,8 @@ cudaError_t launch_range_image(const Geometry &g, const uint32_t *rimg, float *r
 cudaError_t launch_fit(const Geometry &g, const Scratch &s, const Batch &b, const Poses &p, cudaStream_t st);
 cudaError_t launch_fit_rounds(const Geometry &g, const Scratch &s, const Batch &b, cudaStream_t st);
 cudaError_t launch_temporal(const Geometry &g, const Scratch &s, const Batch &b, const Poses &p, cudaStream_t st);
+cudaError_t launch_lookbehind(const Geometry &g, const Scratch &s, const Batch &b, cudaStream_t st);
+cudaError_t launch_queued_rounds(const Geometry &g, const Scratch &s, const Batch &b, cudaStream_t st);
 cudaError_t launch_merge(const Geometry &g, const Scratch &s, const Batch &b, cudaStream_t st);
 size_t merge_smem_bytes(int TC);
 cudaError_t launch_scan(const Geometry &g, const Scratch &s, const Batch &b, cudaStream_t st);
