@@ -508,10 +508,10 @@ __device__ __forceinline__ void temporal_test(const TileView<TH_, TW_> &tv, cons
 }
 
 // First pass over every tile: temporal test (P frames), then the spatial fit.
-// Schedule 0 runs all of a tile's rounds in its thread; schedule 1 runs at
-// most the first spatial round here and queues the tile for dense round
-// kernels (k_fit_round), so that tiles needing more rounds do not hold
-// whole warps.
+// Schedule 0 runs all of a tile's rounds in its thread; schedules 1 and 2 run
+// at most that many spatial rounds here and queue the tile for dense round
+// kernels (k_fit_round), so that the few tiles needing more rounds do not
+// hold whole warps.
 template <int TH_, int TW_, bool kQueue>
 __global__ void __launch_bounds__(kFitThreads) k_fit_first(Geometry g, Scratch s, Batch b, Poses ps) {
     using TV = TileView<TH_, TW_>;
@@ -538,7 +538,7 @@ __global__ void __launch_bounds__(kFitThreads) k_fit_first(Geometry g, Scratch s
         } else if (b.kind == 1 && b.kf[f]) {
             queued = true;   // P-frame spatial fallback after its temporal test: from its first round, dense
         } else {
-            queued = !spatial_rounds<TH_, TW_>(tv, o, 1, prop, b.skip_logit);
+            queued = !spatial_rounds<TH_, TW_>(tv, o, g.first_rounds, prop, b.skip_logit);
         }
     }
     if (kQueue)
@@ -676,7 +676,7 @@ template <int TH_, int TW_>
 static cudaError_t launch_fit_first_t(const Geometry &g, const Scratch &s, const Batch &b, const Poses &p,
                                      cudaStream_t st) {
     dim3 grid((g.NT + kFitThreads - 1) / kFitThreads, b.nframes);
-    if (g.schedule == 1) {
+    if (g.schedule >= 1) {
         cudaError_t e = cudaMemsetAsync(s.qcount + 8 * b.qset, 0, sizeof(uint32_t) * 8, st);
         if (e != cudaSuccess) return e;
         k_fit_first<TH_, TW_, true><<<grid, kFitThreads, 0, st>>>(g, s, b, p);
@@ -701,10 +701,10 @@ static cudaError_t launch_lookbehind_t(const Geometry &g, const Scratch &s, cons
 
 template <int TH_, int TW_>
 static cudaError_t launch_queued_rounds_t(const Geometry &g, const Scratch &s, const Batch &b, cudaStream_t st) {
-    if (g.schedule == 1) {
-        // round 1 ran in the first pass, except for P frames whose first pass was their temporal
-        // test: their spatial rounds all run here
-        const int rounds_left = g.R + ((b.kind == 1 && b.kf[0]) ? 1 : 0);
+    if (g.schedule >= 1) {
+        // the first pass ran the first rounds, except for P frames whose first pass was their
+        // temporal test: their spatial rounds all run here
+        const int rounds_left = (b.kind == 1 && b.kf[0]) ? g.R + 1 : g.R + 1 - g.first_rounds;
         const long long worst = (long long)g.NT * b.nframes;
         const int blocks = (int)std::min<long long>((worst + kFitThreads - 1) / kFitThreads, 152 * 8);
         for (int r = 0; r < rounds_left; r++) {

@@ -103,7 +103,8 @@ struct Geometry {
     int R;               // refit rounds after the first fit
     int merge, lookahead;
     int solver;          // 0 float-float plane solve, 1 FP64
-    int schedule;        // 0 per-thread fit rounds, 1 queued dense rounds
+    int schedule;        // 0 per-thread fit rounds; 1, 2: that many rounds per thread, the rest queued
+    int first_rounds;    // fit rounds of the first pass under a queued schedule
     int k_max, w_res, w_raw;
     float elev_max_deg, d_el_deg, d_az;   // first guesses only; the tables decide
     const float *ce, *se, *ct, *st;       // beam tables

@@ -204,13 +204,19 @@ def test_empty_and_tiny_frames():
 def test_schedule_invariance_and_determinism(cfg1):
     sen, pts = cfg1
     ref = None
-    for la in (0, 1, 8, 16, 32):
-        c = H.ctx(sen, lookahead=la)
-        b1, _ = H.encode_keyframe(c, pts)
+    ref_recs = None
+    for la, sched in ((0, 0), (1, 0), (8, 0), (16, 0), (32, 0), (16, 1), (16, 2), (0, 2)):
+        c = H.ctx(sen, lookahead=la, fit_schedule=sched)
+        b1, r1 = H.encode_keyframe(c, pts)
         b2, _ = H.encode_keyframe(c, pts)
         assert b1.tobytes() == b2.tobytes()
         ref = b1 if ref is None else ref
         assert b1.tobytes() == ref.tobytes()
+        fields = ("plane", "status", "rounds", "n_inlier", "n_valid")
+        if ref_recs is None:
+            ref_recs = r1
+        for k in fields:   # every fit schedule runs the same rounds on every tile
+            assert np.array_equal(r1[k], ref_recs[k]), (la, sched, k)
 
 
 # ------------------------------------------------------------------- P frames --
@@ -317,15 +323,16 @@ def test_sequence_call_matches_separate_calls(cfg2_seq):
         # the sequence call fits P tiles spatially while the key frame is encoded and tests them
         # temporally afterwards; every tile record (rounds and flags included) is as if fused
         assert precs[i].tobytes() == seq_recs[f].tobytes(), f"frame {f}: tile records differ"
-    # the same with the queued fit schedule (sequential order inside the sequence call)
-    cq = H.ctx(seq.sensor, max_batch=16, fit_schedule=1)
-    outs_q = [H.out_buf(cq) for _ in range(n)]
-    cq.lcc_encode_sequence(seq.key_index, seq.poses, ds, [len(p) for p in seq.frames], outs_q,
-                           [o.numel() for o in outs_q], nb, None)
-    assert cq.lcc_sync() == 0
-    nbq = nb.cpu().numpy()
-    for f in range(n):
-        assert outs_q[f][:nbq[f]].cpu().numpy().tobytes() == seq_bits[f].tobytes()
+    # the same with the queued fit schedules (their P rounds also run beside the key frame)
+    for sched in (1, 2):
+        cq = H.ctx(seq.sensor, max_batch=16, fit_schedule=sched)
+        outs_q = [H.out_buf(cq) for _ in range(n)]
+        cq.lcc_encode_sequence(seq.key_index, seq.poses, ds, [len(p) for p in seq.frames], outs_q,
+                               [o.numel() for o in outs_q], nb, None)
+        assert cq.lcc_sync() == 0
+        nbq = nb.cpu().numpy()
+        for f in range(n):
+            assert outs_q[f][:nbq[f]].cpu().numpy().tobytes() == seq_bits[f].tobytes(), (sched, f)
     # host-buffer variant (end-to-end path of the bench)
     h_out = [np.zeros(c.max_encoded_bytes, np.uint8) for _ in range(n)]
     nbh = c.lcc_encode_sequence_host(seq.key_index, seq.poses, [np.ascontiguousarray(p) for p in seq.frames], h_out,
