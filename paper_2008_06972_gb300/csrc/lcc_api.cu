@@ -633,6 +633,48 @@ lcc_status lcc_encode_sequence(lcc_ctx *c, int32_t nframes, int32_t key_index, c
     return encode_sequence(c, nframes, key_index, poses, d_pts, n, d_out, cap, out_bytes, kf, nullptr);
 }
 
+}  // extern "C"
+
+namespace {
+
+// Device address of page-locked host memory (mapped into the device's address space under
+// unified addressing), or NULL for memory the device cannot address.
+void *device_view(const void *p) {
+    cudaPointerAttributes a;
+    if (!p || cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    if (a.type != cudaMemoryTypeHost || !a.devicePointer) return nullptr;
+    return a.devicePointer;
+}
+
+struct CopyOut {
+    const uint8_t *src[kMaxBatch];
+    uint8_t *dst[kMaxBatch];
+    unsigned long long cap[kMaxBatch];
+    const unsigned long long *nbytes;
+};
+
+// Every frame's stream from the device staging buffer straight into the caller's page-locked
+// host buffer (16-byte stores over the host link), sized by the stream length on the device.
+__global__ void __launch_bounds__(256) k_copy_out(CopyOut co) {
+    const int f = blockIdx.y;
+    const unsigned long long nb = co.nbytes[f] <= co.cap[f] ? co.nbytes[f] : 0ull;
+    const uint4 *src = reinterpret_cast<const uint4 *>(co.src[f]);
+    uint4 *dst = reinterpret_cast<uint4 *>(co.dst[f]);
+    const unsigned long long n16 = nb / 16;
+    for (unsigned long long i = blockIdx.x * 256ull + threadIdx.x; i < n16; i += gridDim.x * 256ull) dst[i] = src[i];
+    const unsigned long long tail = nb - n16 * 16;   // streams are whole 32-bit words
+    if (blockIdx.x == 0 && threadIdx.x < tail / 4)
+        reinterpret_cast<uint32_t *>(co.dst[f] + n16 * 16)[threadIdx.x] =
+            reinterpret_cast<const uint32_t *>(co.src[f] + n16 * 16)[threadIdx.x];
+}
+
+}  // namespace
+
+extern "C" {
+
 lcc_status lcc_encode_sequence_host(lcc_ctx *c, int32_t nframes, int32_t key_index, const double *poses,
                                     const float *const *h_pts, const int64_t *n, uint8_t *const *h_out,
                                     const uint64_t *cap, uint64_t *out_bytes) {
@@ -657,27 +699,53 @@ lcc_status lcc_encode_sequence_host(lcc_ctx *c, int32_t nframes, int32_t key_ind
         c->stage_out_cap = out_total;
     }
     if (!c->d_stage_bytes) LCC_CUDA(cudaMalloc(&c->d_stage_bytes, sizeof(unsigned long long) * kMaxBatch));
+    // Page-locked inputs are read by the binning kernel in place, over the host link (no staging
+    // copy); page-locked outputs are written by one copy-out kernel (no second host round trip).
+    bool in_mapped = true, out_mapped = true;
+    const float *hv[kMaxBatch];
+    uint8_t *ov[kMaxBatch];
+    for (int f = 0; f < nframes; f++) {
+        hv[f] = n[f] ? (const float *)device_view(h_pts[f]) : nullptr;
+        in_mapped = in_mapped && (!n[f] || (hv[f] && aligned16(hv[f])));
+        ov[f] = (uint8_t *)device_view(h_out[f]);
+        out_mapped = out_mapped && ov[f] && aligned16(ov[f]);
+    }
     const float *dp[kMaxBatch];
     uint8_t *dout[kMaxBatch];
     char *pp = (char *)c->d_stage_pts;
     uint8_t *po = c->d_stage_out;
     for (int f = 0; f < nframes; f++) {
-        dp[f] = (const float *)pp;
+        dp[f] = in_mapped ? hv[f] : (const float *)pp;
         pp += align256((size_t)n[f] * 16);
         dout[f] = po;
         po += align256((size_t)cap[f]);
     }
     lcc_status st = encode_sequence(c, nframes, key_index, poses, dp, n, dout, cap, (uint64_t *)c->d_stage_bytes,
-                                    nullptr, h_pts);
+                                    nullptr, in_mapped ? nullptr : h_pts);
     if (st != LCC_OK) return st;
-    LCC_CUDA(cudaMemcpyAsync(out_bytes, c->d_stage_bytes, sizeof(uint64_t) * nframes, cudaMemcpyDeviceToHost,
-                             c->stream));
-    LCC_CUDA(cudaStreamSynchronize(c->stream));
-    for (int f = 0; f < nframes; f++) {
-        const uint64_t nb = out_bytes[f] <= cap[f] ? out_bytes[f] : 0;
-        if (nb) LCC_CUDA(cudaMemcpyAsync(h_out[f], dout[f], nb, cudaMemcpyDeviceToHost, c->stream));
+    if (out_mapped) {
+        CopyOut co;
+        for (int f = 0; f < nframes; f++) {
+            co.src[f] = dout[f];
+            co.dst[f] = ov[f];
+            co.cap[f] = cap[f];
+        }
+        co.nbytes = c->d_stage_bytes;
+        k_copy_out<<<dim3(16, nframes), 256, 0, c->stream>>>(co);
+        LCC_CUDA(cudaGetLastError());
+        LCC_CUDA(cudaMemcpyAsync(out_bytes, c->d_stage_bytes, sizeof(uint64_t) * nframes, cudaMemcpyDeviceToHost,
+                                 c->stream));
+        LCC_CUDA(cudaStreamSynchronize(c->stream));
+    } else {
+        LCC_CUDA(cudaMemcpyAsync(out_bytes, c->d_stage_bytes, sizeof(uint64_t) * nframes, cudaMemcpyDeviceToHost,
+                                 c->stream));
+        LCC_CUDA(cudaStreamSynchronize(c->stream));
+        for (int f = 0; f < nframes; f++) {
+            const uint64_t nb = out_bytes[f] <= cap[f] ? out_bytes[f] : 0;
+            if (nb) LCC_CUDA(cudaMemcpyAsync(h_out[f], dout[f], nb, cudaMemcpyDeviceToHost, c->stream));
+        }
+        LCC_CUDA(cudaStreamSynchronize(c->stream));
     }
-    LCC_CUDA(cudaStreamSynchronize(c->stream));
     return latched(c);
 }
 

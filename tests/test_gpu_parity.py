@@ -339,6 +339,13 @@ def test_sequence_call_matches_separate_calls(cfg2_seq):
                                      [len(h) for h in h_out])
     for f in range(n):
         assert h_out[f][:nbh[f]].tobytes() == seq_bits[f].tobytes()
+    # page-locked host buffers: points read in place over the host link, streams written by the
+    # copy-out kernel
+    hp = [torch.from_numpy(np.ascontiguousarray(p)).pin_memory() for p in seq.frames]
+    ho = [torch.zeros(c.max_encoded_bytes, dtype=torch.uint8).pin_memory() for _ in range(n)]
+    nbp = c.lcc_encode_sequence_host(seq.key_index, seq.poses, hp, ho, [o.numel() for o in ho])
+    for f in range(n):
+        assert ho[f][:int(nbp[f])].numpy().tobytes() == seq_bits[f].tobytes()
 
 
 # ------------------------------------------------------------------ errors --
