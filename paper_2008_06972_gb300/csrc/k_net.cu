@@ -434,7 +434,7 @@ constexpr int TSLOT = TX + TA1 + TA2;           // activation copies of one pair
 constexpr int kTcWarps = 8;                     // two warps per TMEM lane quadrant (column halves)
 constexpr int TGP = 4 * 2 * C3 * 4, TG = 2 * C3 * 4;
 constexpr int TPAR = (C1 + C2 + C3 + HID * C3 + HID + NOUT * HID + NOUT + 3) / 4 * 16;   // biases, head (fp32)
-constexpr size_t kTcSmem = (size_t)TW1 + TW2 + TW3 + 2 * (size_t)(TSLOT + TGP + TG) + TPAR + 64;
+constexpr size_t kTcSmem = (size_t)TW1 + TW2 + TW3 + 2 * (size_t)(TSLOT + TGP + TG) + TPAR + 64;   // + 5 barriers
 constexpr uint32_t kTmemCols = 128;             // two 64-column accumulators, one per pair in flight
 constexpr long long kSpinLimit = 1ll << 22;
 
@@ -499,22 +499,22 @@ __device__ __forceinline__ void proxy_fence() { asm volatile("fence.proxy.async.
 // byte offset of (chunk, y, tile, x) in an activation copy
 __device__ __forceinline__ int tpos(int c8, int y, int tile, int x) { return c8 * TCHUNK + ((y * 2 + tile) * 10 + x) * 16; }
 
-// One convolution: nine taps x (CIN/16) k-steps of M=128, N=COUT MMAs (one thread).
+// One convolution: nine taps x (CIN/16) k-steps of M=128, N=COUT MMAs (one thread).  The
+// descriptors differ only in their start-address field, so each MMA's pair is the base pair
+// plus compile-time offsets (all addresses stay below 256 KB: no carry out of the field).
 template <int CIN, int COUT>
 __device__ __forceinline__ void tc_conv(uint32_t tmem, uint32_t act, uint32_t wts) {
     constexpr uint32_t idesc = mma_idesc(128, COUT);
     constexpr int KCH = CIN < 16 ? 16 : CIN;   // conv1: 4 real channels padded to one k-step
-    uint32_t acc = 0;
-#pragma unroll 1
+    const uint64_t a0 = smem_desc(act, TCHUNK, 160);
+    const uint64_t b0 = smem_desc(wts, COUT * 16, 128);
+#pragma unroll
     for (int tap = 0; tap < 9; tap++) {
-        const int ky = tap / 3, kx = tap % 3;
-#pragma unroll 1
+#pragma unroll
         for (int ks = 0; ks < KCH / 16; ks++) {
-            const uint64_t a = smem_desc(act + (uint32_t)((ky * 20 + kx) * 16 + 2 * ks * TCHUNK), TCHUNK, 160);
-            const uint64_t b = smem_desc(wts + (uint32_t)(tap * (KCH / 8) * COUT * 16 + 2 * ks * COUT * 16),
-                                         COUT * 16, 128);
-            tc_mma(tmem, a, b, idesc, acc);
-            acc = 1;
+            const uint64_t a = a0 + (uint64_t)((((tap / 3) * 20 + tap % 3) * 16 + 2 * ks * TCHUNK) >> 4);
+            const uint64_t b = b0 + (uint64_t)((tap * (KCH / 8) * COUT * 16 + 2 * ks * COUT * 16) >> 4);
+            tc_mma(tmem, a, b, idesc, (tap | ks) ? 1u : 0u);
         }
     }
 }
@@ -526,29 +526,46 @@ __device__ __forceinline__ void bulk_g2s(uint32_t dst, const void *src, uint32_t
                  : "memory");
 }
 
-// Two pairs of tiles are in flight: while the warps run one pair's epilogue, the tensor
-// cores run the other pair's MMAs (separate activation copies, TMEM columns and mbarriers).
-__global__ void __launch_bounds__(kTcWarps * 32, 1) k_net_fwd_tc(NetDev nd, const bf16 *x, long long T, float *out,
-                                                                  int *err) {
+// Warp-specialised: eight epilogue warps (two per TMEM lane quadrant, one column half each)
+// and one MMA warp.  Two pairs of tiles are in flight in separate activation copies and TMEM
+// accumulators; for each pair slot, an mbarrier armed by tcgen05.commit hands a finished
+// layer to the epilogue warps, and an mbarrier the eight epilogue warps arrive on hands the
+// next layer's input (and the emptied accumulator) back to the MMA warp.  No CTA-wide
+// barrier sits between layers, so the tensor cores run one pair's layer while the epilogue
+// warps finish the other's.
+constexpr int kTcEpiWarps = 8;
+constexpr int kTcThreads = (kTcEpiWarps + 1) * 32;
+
+__device__ __forceinline__ void mbar_arrive(uint32_t mbar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(mbar) : "memory");
+}
+__device__ __forceinline__ void epi_sync() { asm volatile("bar.sync 1, %0;\n" ::"n"(kTcEpiWarps * 32) : "memory"); }
+
+__global__ void __launch_bounds__(kTcThreads, 1) k_net_fwd_tc(NetDev nd, const bf16 *x, long long T, float *out,
+                                                              int *err) {
     extern __shared__ __align__(1024) uint8_t sm[];
     uint8_t *sW1 = sm, *sW2 = sW1 + TW1, *sW3 = sW2 + TW2;
     uint8_t *sSlot = sW3 + TW3;                                        // [2][TSLOT]
-    float *sGP = reinterpret_cast<float *>(sSlot + 2 * TSLOT);         // [2][warp][tile][64]
+    float *sGP = reinterpret_cast<float *>(sSlot + 2 * TSLOT);         // [2][quadrant][tile][64]
     float *sG = sGP + 2 * 4 * 2 * C3;                                  // [2][tile][64]
     float *sPar = sG + 2 * 2 * C3;                                     // b1 b2 b3 F1b c1 F2b c2
     float *sB1 = sPar, *sB2 = sB1 + C1, *sB3 = sB2 + C2, *sF1 = sB3 + C3, *sC1 = sF1 + HID * C3;
     float *sF2 = sC1 + HID, *sC2 = sF2 + NOUT * HID;
-    uint64_t *bar = reinterpret_cast<uint64_t *>(reinterpret_cast<uint8_t *>(sPar) + TPAR);   // [0] weights, [1..2] slots
-    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bar + 3);
+    // barriers: [0] weights, [1 + s] layer done (tcgen05.commit), [3 + s] layer input ready (epilogue)
+    uint64_t *bar = reinterpret_cast<uint64_t *>(reinterpret_cast<uint8_t *>(sPar) + TPAR);
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bar + 5);
     int *s_fail = reinterpret_cast<int *>(tmem_slot + 1);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const float *th = nd.theta;
     if (tid == 0) {
-        for (int i = 0; i < 3; i++)
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(bar)) : "memory");
+        for (int i = 1; i < 3; i++)
             asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(bar + i)) : "memory");
+        for (int i = 3; i < 5; i++)
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_u32(bar + i)), "n"(kTcEpiWarps)
+                         : "memory");
         *s_fail = 0;
     }
-    // zero both pairs' activation copies (borders stay zero); parameters of the epilogues
     {
         uint4 *z = reinterpret_cast<uint4 *>(sSlot);
         for (int i = tid; i < 2 * TSLOT / 16; i += blockDim.x) z[i] = make_uint4(0u, 0u, 0u, 0u);
@@ -567,8 +584,7 @@ __global__ void __launch_bounds__(kTcWarps * 32, 1) k_net_fwd_tc(NetDev nd, cons
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::: "memory");
     }
     __syncthreads();
-    // weights by the TMA engine: three bulk copies counted on barrier 0
-    if (tid == 0) {
+    if (tid == 0) {   // weights by the TMA engine, counted on barrier 0
         asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_u32(bar)),
                      "r"((uint32_t)(TW1 + TW2 + TW3))
                      : "memory");
@@ -585,127 +601,143 @@ __global__ void __launch_bounds__(kTcWarps * 32, 1) k_net_fwd_tc(NetDev nd, cons
     __syncthreads();
     tc_after_sync();
     const uint32_t tmem = *tmem_slot;
-    const uint32_t aW1 = smem_u32(sW1), aW2 = smem_u32(sW2), aW3 = smem_u32(sW3);
-    // this thread's GEMM row: r = 32 (warp % 4) + lane -> (y, tile, x); its column half: warp / 4
-    const int quad = warp & 3, half = warp >> 2;
-    const int row = quad * 32 + lane, grp = row >> 3, px = row & 7, py = grp >> 1, tl = grp & 1;
-    uint32_t phase[2] = {0u, 0u};
     auto slot_x = [&](int sl) { return sSlot + sl * TSLOT; };
-    auto issue = [&](int sl, int layer) {   // thread 0: one convolution of pair slot sl
-        const uint32_t base = smem_u32(slot_x(sl));
-        const uint32_t d = tmem + (uint32_t)(sl * 64);
-        if (layer == 0) tc_conv<C0, C1>(d, base, aW1);
-        else if (layer == 1) tc_conv<C1, C2>(d, base + TX, aW2);
-        else tc_conv<C2, C3>(d, base + TX + TA1, aW3);
-        tc_commit(smem_u32(bar + 1 + sl));
-    };
-    auto epilogue_tc = [&](int sl, int layer) {   // all threads: wait, read TMEM, write the next copy
-        if (!mbar_wait(smem_u32(bar + 1 + sl), phase[sl])) {
+    // a bounded wait that gives up at once after any earlier wait expired
+    auto wait = [&](uint32_t mbar, uint32_t parity) {
+        if (*(volatile int *)s_fail) return;
+        if (!mbar_wait(mbar, parity)) {
             atomicExch(s_fail, 1);
             if (err) atomicExch(err, 1);
         }
-        phase[sl] ^= 1u;
-        tc_after_sync();
-        const int cout = layer == 0 ? C1 : C2;
-        const float *bias = layer == 0 ? sB1 : layer == 1 ? sB2 : sB3;
-        uint8_t *dst = slot_x(sl) + (layer == 0 ? TX : TX + TA1);
-        const uint32_t trow = tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(sl * 64);
-        float *gp = sGP + sl * 4 * 2 * C3;
-        const int cbeg = half * (cout / 2), cend = cbeg + cout / 2;
-#pragma unroll 1
-        for (int c0 = cbeg; c0 < cend; c0 += 16) {
-            float v[16];
-            tc_ld16(trow + (uint32_t)c0, v);
-            tc_wait_ld();
-#pragma unroll
-            for (int i = 0; i < 16; i++) v[i] = fmaxf(v[i] + bias[c0 + i], 0.f);
-            if (layer < 2) {
-#pragma unroll
-                for (int h = 0; h < 2; h++) {
-                    uint32_t w[4];
-#pragma unroll
-                    for (int q = 0; q < 4; q++) {
-                        const __nv_bfloat162 b2 = __floats2bfloat162_rn(v[8 * h + 2 * q], v[8 * h + 2 * q + 1]);
-                        w[q] = *reinterpret_cast<const uint32_t *>(&b2);
-                    }
-                    *reinterpret_cast<uint4 *>(dst + tpos(c0 / 8 + h, py + 1, tl, px + 1)) =
-                        make_uint4(w[0], w[1], w[2], w[3]);
-                }
-            } else {
-#pragma unroll
-                for (int i = 0; i < 16; i++) {
-                    float s2 = bfround(v[i]);
-                    s2 += __shfl_xor_sync(0xffffffffu, s2, 1);
-                    s2 += __shfl_xor_sync(0xffffffffu, s2, 2);
-                    s2 += __shfl_xor_sync(0xffffffffu, s2, 4);
-                    s2 += __shfl_xor_sync(0xffffffffu, s2, 16);
-                    if (lane == 0 || lane == 8) gp[(quad * 2 + tl) * C3 + c0 + i] = s2;
-                }
-            }
-        }
-        proxy_fence();
-        tc_before_sync();
-        __syncthreads();
-        tc_after_sync();
     };
-    for (long long pa = blockIdx.x; pa * 2 < T; pa += 2ll * gridDim.x) {
-        if (*s_fail) break;   // uniform: read after a barrier
-        const long long pb = pa + gridDim.x;
-        const bool hasB = pb * 2 < T;
-        const long long pr[2] = {pa, pb};
-        for (int sl = half; sl < (hasB ? 2 : 1); sl += 2) {   // inputs (4 channels + 4 zero): warps 4-7 fill slot 1
-            const long long tile = pr[sl] * 2 + tl;
-            uint2 v = make_uint2(0u, 0u);
-            if (tile < T) v = *reinterpret_cast<const uint2 *>(x + ((size_t)tile * kPX + py * 8 + px) * C0);
-            *reinterpret_cast<uint4 *>(slot_x(sl) + tpos(0, py + 1, tl, px + 1)) = make_uint4(v.x, v.y, 0u, 0u);
-        }
-        proxy_fence();
-        tc_before_sync();
-        __syncthreads();
-        tc_after_sync();
-        if (tid == 0) {
-            issue(0, 0);
-            if (hasB) issue(1, 0);
-        }
+    const long long G = gridDim.x;
+    if (warp == kTcEpiWarps) {
+        // ---- MMA warp: one lane issues every convolution of both pair slots ----
+        uint32_t ph[2] = {0u, 0u};
+        const uint32_t aW1 = smem_u32(sW1), aW2 = smem_u32(sW2), aW3 = smem_u32(sW3);
+        for (long long pa = blockIdx.x; pa * 2 < T; pa += 2 * G) {
+            const bool hasB = (pa + G) * 2 < T;
 #pragma unroll 1
-        for (int layer = 0; layer < 3; layer++) {
-            epilogue_tc(0, layer);
-            if (layer < 2 && tid == 0) issue(0, layer + 1);
-            if (hasB) {
-                epilogue_tc(1, layer);
-                if (layer < 2 && tid == 0) issue(1, layer + 1);
-            }
-        }
-        {   // pooled vectors (fixed summation order over the lane quadrants): thread -> (slot, tile, channel)
-            const int sl = tid >> 7, t2 = (tid >> 6) & 1, c = tid & 63;
-            if (sl == 0 || hasB) {
-                const float *gp = sGP + sl * 4 * 2 * C3;
-                float s2 = 0.f;
-                for (int w = 0; w < 4; w++) s2 += gp[(w * 2 + t2) * C3 + c];
-                sG[(sl * 2 + t2) * C3 + c] = bfround(s2 * (1.0f / kPX));
-            }
-        }
-        __syncthreads();
-        if (warp < 4) {   // head: warp w < 4 takes tile (w & 1) of pair slot (w >> 1)
-            const int sl = warp >> 1, t2 = warp & 1;
-            const long long tile = pr[sl] * 2 + t2;
-            if ((sl == 0 || hasB) && tile < T) {
-                const float *gs = sG + (sl * 2 + t2) * C3;
-                float yv = sC1[lane];
-                for (int c = 0; c < C3; c++) yv = fmaf(sF1[lane * C3 + c], gs[c], yv);
-                const float hj = bfround(fmaxf(yv, 0.f));
-                float o[NOUT];
-#pragma unroll
-                for (int i = 0; i < NOUT; i++) {
-                    float sacc = sF2[i * HID + lane] * hj;
-#pragma unroll
-                    for (int off = 16; off; off >>= 1) sacc += __shfl_xor_sync(0xffffffffu, sacc, off);
-                    o[i] = sacc + sC2[i];
+            for (int layer = 0; layer < 3; layer++) {
+#pragma unroll 1
+                for (int sl = 0; sl < (hasB ? 2 : 1); sl++) {
+                    if (lane == 0) {
+                        wait(smem_u32(bar + 3 + sl), ph[sl]);
+                        tc_after_sync();
+                        const uint32_t base = smem_u32(slot_x(sl));
+                        const uint32_t d = tmem + (uint32_t)(sl * 64);
+                        if (layer == 0) tc_conv<C0, C1>(d, base, aW1);
+                        else if (layer == 1) tc_conv<C1, C2>(d, base + TX, aW2);
+                        else tc_conv<C2, C3>(d, base + TX + TA1, aW3);
+                        tc_commit(smem_u32(bar + 1 + sl));
+                    }
+                    ph[sl] ^= 1u;
+                    __syncwarp();
                 }
-                if (lane < NOUT) out[(size_t)tile * NOUT + lane] = o[lane];
             }
         }
-        __syncthreads();
+    } else {
+        // ---- epilogue warps: row = 32 (warp % 4) + lane -> (y, tile, x); column half = warp / 4 ----
+        const int quad = warp & 3, half = warp >> 2;
+        const int row = quad * 32 + lane, grp = row >> 3, px = row & 7, py = grp >> 1, tl = grp & 1;
+        uint32_t ph[2] = {0u, 0u};
+        auto handoff = [&](int sl) {   // this warp's part of slot sl is written: hand it to the MMA warp
+            proxy_fence();
+            tc_before_sync();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(smem_u32(bar + 3 + sl));
+        };
+        for (long long pa = blockIdx.x; pa * 2 < T; pa += 2 * G) {
+            const long long pb = pa + G;
+            const bool hasB = pb * 2 < T;
+            const long long pr[2] = {pa, pb};
+            if (half == 0 || hasB) {   // inputs (4 channels + 4 zero): warps 0-3 fill slot 0, warps 4-7 slot 1
+                const long long tile = pr[half] * 2 + tl;
+                uint2 v = make_uint2(0u, 0u);
+                if (tile < T) v = *reinterpret_cast<const uint2 *>(x + ((size_t)tile * kPX + py * 8 + px) * C0);
+                *reinterpret_cast<uint4 *>(slot_x(half) + tpos(0, py + 1, tl, px + 1)) = make_uint4(v.x, v.y, 0u, 0u);
+            }
+            for (int sl = 0; sl < (hasB ? 2 : 1); sl++) handoff(sl);
+#pragma unroll 1
+            for (int layer = 0; layer < 3; layer++) {
+#pragma unroll 1
+                for (int sl = 0; sl < (hasB ? 2 : 1); sl++) {
+                    wait(smem_u32(bar + 1 + sl), ph[sl]);
+                    ph[sl] ^= 1u;
+                    tc_after_sync();
+                    const int cout = layer == 0 ? C1 : C2;
+                    const float *bias = layer == 0 ? sB1 : layer == 1 ? sB2 : sB3;
+                    uint8_t *dst = slot_x(sl) + (layer == 0 ? TX : TX + TA1);
+                    const uint32_t trow = tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(sl * 64);
+                    float *gp = sGP + sl * 4 * 2 * C3;
+                    const int cbeg = half * (cout / 2), cend = cbeg + cout / 2;
+#pragma unroll 1
+                    for (int c0 = cbeg; c0 < cend; c0 += 16) {
+                        float v[16];
+                        tc_ld16(trow + (uint32_t)c0, v);
+                        tc_wait_ld();
+#pragma unroll
+                        for (int i = 0; i < 16; i++) v[i] = fmaxf(v[i] + bias[c0 + i], 0.f);
+                        if (layer < 2) {
+#pragma unroll
+                            for (int h = 0; h < 2; h++) {
+                                uint32_t w[4];
+#pragma unroll
+                                for (int q = 0; q < 4; q++) {
+                                    const __nv_bfloat162 b2 =
+                                        __floats2bfloat162_rn(v[8 * h + 2 * q], v[8 * h + 2 * q + 1]);
+                                    w[q] = *reinterpret_cast<const uint32_t *>(&b2);
+                                }
+                                *reinterpret_cast<uint4 *>(dst + tpos(c0 / 8 + h, py + 1, tl, px + 1)) =
+                                    make_uint4(w[0], w[1], w[2], w[3]);
+                            }
+                        } else {
+#pragma unroll
+                            for (int i = 0; i < 16; i++) {
+                                float s2 = bfround(v[i]);
+                                s2 += __shfl_xor_sync(0xffffffffu, s2, 1);
+                                s2 += __shfl_xor_sync(0xffffffffu, s2, 2);
+                                s2 += __shfl_xor_sync(0xffffffffu, s2, 4);
+                                s2 += __shfl_xor_sync(0xffffffffu, s2, 16);
+                                if (lane == 0 || lane == 8) gp[(quad * 2 + tl) * C3 + c0 + i] = s2;
+                            }
+                        }
+                    }
+                    if (layer < 2) handoff(sl);   // the next layer's input is in place, the accumulator is read
+                    else tc_before_sync();
+                }
+            }
+            epi_sync();
+            {   // pooled vectors (fixed summation order over the lane quadrants): thread -> (slot, tile, channel)
+                const int sl = tid >> 7, t2 = (tid >> 6) & 1, c = tid & 63;
+                if (sl == 0 || hasB) {
+                    const float *gp = sGP + sl * 4 * 2 * C3;
+                    float s2 = 0.f;
+                    for (int w = 0; w < 4; w++) s2 += gp[(w * 2 + t2) * C3 + c];
+                    sG[(sl * 2 + t2) * C3 + c] = bfround(s2 * (1.0f / kPX));
+                }
+            }
+            epi_sync();
+            if (warp < 4) {   // head: warp w < 4 takes tile (w & 1) of pair slot (w >> 1)
+                const int sl = warp >> 1, t2 = warp & 1;
+                const long long tile = pr[sl] * 2 + t2;
+                if ((sl == 0 || hasB) && tile < T) {
+                    const float *gs = sG + (sl * 2 + t2) * C3;
+                    float yv = sC1[lane];
+                    for (int c = 0; c < C3; c++) yv = fmaf(sF1[lane * C3 + c], gs[c], yv);
+                    const float hj = bfround(fmaxf(yv, 0.f));
+                    float o[NOUT];
+#pragma unroll
+                    for (int i = 0; i < NOUT; i++) {
+                        float sacc = sF2[i * HID + lane] * hj;
+#pragma unroll
+                        for (int off = 16; off; off >>= 1) sacc += __shfl_xor_sync(0xffffffffu, sacc, off);
+                        o[i] = sacc + sC2[i];
+                    }
+                    if (lane < NOUT) out[(size_t)tile * NOUT + lane] = o[lane];
+                }
+            }
+        }
     }
     tc_before_sync();
     __syncthreads();
@@ -1199,7 +1231,7 @@ lcc_status lcc_net_forward(lcc_net *net, const uint16_t *d_x, int64_t ntiles, fl
     if (ntiles == 0) return LCC_OK;
     const int64_t pairs = (ntiles + 1) / 2;
     const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(pairs, net->sms));
-    k_net_fwd_tc<<<grid, kTcWarps * 32, kTcSmem, net->stream>>>(net->nd, reinterpret_cast<const bf16 *>(d_x), ntiles,
+    k_net_fwd_tc<<<grid, kTcThreads, kTcSmem, net->stream>>>(net->nd, reinterpret_cast<const bf16 *>(d_x), ntiles,
                                                                   d_out, net->err);
     return cudaGetLastError() == cudaSuccess ? LCC_OK : LCC_ERR_CUDA;
 }

@@ -353,7 +353,9 @@ lcc_status lcc_create(lcc_ctx **out, const lcc_sensor *sensor, const lcc_params 
     c->s.qcap = (uint32_t)(sl * nt);
     cudaMemset(c->d_scratch, 0, total);
     cudaMemset(c->s.rimg, 0xFF, sl * npx * 4);
-    if (cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking) != cudaSuccess ||
+    if (cudaHostAlloc(&c->h_pinned, sizeof(unsigned long long) * (kMaxBatch + 1), cudaHostAllocDefault) !=
+            cudaSuccess ||
+        cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking) != cudaSuccess ||
         cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
         cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming) != cudaSuccess) {
         lcc_destroy(c);
@@ -389,6 +391,7 @@ lcc_status lcc_destroy(lcc_ctx *c) {
     cudaFree(c->d_stage_pts);
     cudaFree(c->d_stage_out);
     cudaFree(c->d_stage_bytes);
+    if (c->h_pinned) cudaFreeHost(c->h_pinned);
     delete c;
     return LCC_OK;
 }
@@ -733,9 +736,15 @@ lcc_status lcc_encode_sequence_host(lcc_ctx *c, int32_t nframes, int32_t key_ind
         co.nbytes = c->d_stage_bytes;
         k_copy_out<<<dim3(16, nframes), 256, 0, c->stream>>>(co);
         LCC_CUDA(cudaGetLastError());
-        LCC_CUDA(cudaMemcpyAsync(out_bytes, c->d_stage_bytes, sizeof(uint64_t) * nframes, cudaMemcpyDeviceToHost,
+        // sizes and the error word into page-locked memory, then the one host round trip
+        LCC_CUDA(cudaMemcpyAsync(c->h_pinned, c->d_stage_bytes, sizeof(uint64_t) * nframes, cudaMemcpyDeviceToHost,
                                  c->stream));
+        LCC_CUDA(cudaMemcpyAsync(c->h_pinned + kMaxBatch, c->s.err, 4, cudaMemcpyDeviceToHost, c->stream));
         LCC_CUDA(cudaStreamSynchronize(c->stream));
+        memcpy(out_bytes, c->h_pinned, sizeof(uint64_t) * nframes);
+        const uint32_t e = (uint32_t)(c->h_pinned[kMaxBatch] & 0xFFFFFFFFull);
+        if (!e) return LCC_OK;
+        return latched(c);   // reads and clears the error word
     } else {
         LCC_CUDA(cudaMemcpyAsync(out_bytes, c->d_stage_bytes, sizeof(uint64_t) * nframes, cudaMemcpyDeviceToHost,
                                  c->stream));

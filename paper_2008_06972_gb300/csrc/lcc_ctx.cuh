@@ -60,6 +60,7 @@ struct lcc_ctx {
     uint8_t *d_stage_out = nullptr;
     size_t stage_out_cap = 0;
     unsigned long long *d_stage_bytes = nullptr;
+    unsigned long long *h_pinned = nullptr;   // page-locked: stream sizes (kMaxBatch) + error word
 };
 
 namespace lcc {
