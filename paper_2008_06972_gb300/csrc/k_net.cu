@@ -526,14 +526,15 @@ __device__ __forceinline__ void bulk_g2s(uint32_t dst, const void *src, uint32_t
                  : "memory");
 }
 
-// Warp-specialised: eight epilogue warps (two per TMEM lane quadrant, one column half each)
+// Warp-specialised: eight epilogue warps (two per TMEM lane quadrant, a column half each)
 // and one MMA warp.  Two pairs of tiles are in flight in separate activation copies and TMEM
 // accumulators; for each pair slot, an mbarrier armed by tcgen05.commit hands a finished
-// layer to the epilogue warps, and an mbarrier the eight epilogue warps arrive on hands the
+// layer to the epilogue warps, and an mbarrier the epilogue warps arrive on hands the
 // next layer's input (and the emptied accumulator) back to the MMA warp.  No CTA-wide
 // barrier sits between layers, so the tensor cores run one pair's layer while the epilogue
 // warps finish the other's.
-constexpr int kTcEpiWarps = 8;
+constexpr int kTcParts = 2;                       // epilogue warps per TMEM lane quadrant (column parts)
+constexpr int kTcEpiWarps = 4 * kTcParts;
 constexpr int kTcThreads = (kTcEpiWarps + 1) * 32;
 
 __device__ __forceinline__ void mbar_arrive(uint32_t mbar) {
@@ -637,8 +638,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_net_fwd_tc(NetDev nd, const b
             }
         }
     } else {
-        // ---- epilogue warps: row = 32 (warp % 4) + lane -> (y, tile, x); column half = warp / 4 ----
-        const int quad = warp & 3, half = warp >> 2;
+        // ---- epilogue warps: row = 32 (warp % 4) + lane -> (y, tile, x); column part = warp / 4 ----
+        const int quad = warp & 3, part = warp >> 2;
         const int row = quad * 32 + lane, grp = row >> 3, px = row & 7, py = grp >> 1, tl = grp & 1;
         uint32_t ph[2] = {0u, 0u};
         auto handoff = [&](int sl) {   // this warp's part of slot sl is written: hand it to the MMA warp
@@ -651,11 +652,11 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_net_fwd_tc(NetDev nd, const b
             const long long pb = pa + G;
             const bool hasB = pb * 2 < T;
             const long long pr[2] = {pa, pb};
-            if (half == 0 || hasB) {   // inputs (4 channels + 4 zero): warps 0-3 fill slot 0, warps 4-7 slot 1
-                const long long tile = pr[half] * 2 + tl;
+            if (part < 2 && (part == 0 || hasB)) {   // inputs (4 channels + 4 zero): part p fills slot p
+                const long long tile = pr[part] * 2 + tl;
                 uint2 v = make_uint2(0u, 0u);
                 if (tile < T) v = *reinterpret_cast<const uint2 *>(x + ((size_t)tile * kPX + py * 8 + px) * C0);
-                *reinterpret_cast<uint4 *>(slot_x(half) + tpos(0, py + 1, tl, px + 1)) = make_uint4(v.x, v.y, 0u, 0u);
+                *reinterpret_cast<uint4 *>(slot_x(part) + tpos(0, py + 1, tl, px + 1)) = make_uint4(v.x, v.y, 0u, 0u);
             }
             for (int sl = 0; sl < (hasB ? 2 : 1); sl++) handoff(sl);
 #pragma unroll 1
@@ -670,7 +671,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_net_fwd_tc(NetDev nd, const b
                     uint8_t *dst = slot_x(sl) + (layer == 0 ? TX : TX + TA1);
                     const uint32_t trow = tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(sl * 64);
                     float *gp = sGP + sl * 4 * 2 * C3;
-                    const int cbeg = half * (cout / 2), cend = cbeg + cout / 2;
+                    const int cw = cout / kTcParts < 16 ? 16 : cout / kTcParts;   // 16-column loads
+                    const int cbeg = part * cw, cend = cbeg + cw < cout ? cbeg + cw : cout;
 #pragma unroll 1
                     for (int c0 = cbeg; c0 < cend; c0 += 16) {
                         float v[16];
@@ -708,7 +710,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_net_fwd_tc(NetDev nd, const b
                 }
             }
             epi_sync();
-            {   // pooled vectors (fixed summation order over the lane quadrants): thread -> (slot, tile, channel)
+            if (tid < 256) {   // pooled vectors (fixed order over the lane quadrants): thread -> (slot, tile, channel)
                 const int sl = tid >> 7, t2 = (tid >> 6) & 1, c = tid & 63;
                 if (sl == 0 || hasB) {
                     const float *gp = sGP + sl * 4 * 2 * C3;
