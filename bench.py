@@ -479,8 +479,7 @@ def run_learned(args, stream):
         ctx.lcc_encode_keyframes(d_eval, n_eval, None, 0.0, outs, caps, nbs)
 
     def batched_learned():
-        for i in range(nf):
-            lcc.net_tile_inputs(ctx, d_eval[i], n_eval[i], xall[i * nt:(i + 1) * nt], aall[i * nt:(i + 1) * nt])
+        lcc.net_tile_inputs_batch(ctx, d_eval, n_eval, xall, aall)
         net.forward(xall, nf * nt, pall)
         ctx.lcc_encode_keyframes(d_eval, n_eval, props, TR.SKIP_LOGIT, outs, caps, nbs)
 

@@ -251,6 +251,10 @@ lcc_status lcc_net_set_params(lcc_net *net, const float *h_params);   /* also re
  * every tile: d_x [num_tiles][64][4] bf16 (as uint16), d_anchor [num_tiles]
  * float4 (anchor x, y, z, r).  LCC_ERR_UNSUPPORTED for other tile shapes. */
 lcc_status lcc_net_tile_inputs(lcc_ctx *ctx, const float *d_pts, int64_t n, uint16_t *d_x, float *d_anchor);
+/* The same for nframes frames (<= max_batch) in one binning launch and one input launch: frame f's
+ * tiles are rows [f*num_tiles, (f+1)*num_tiles) of d_x and d_anchor. */
+lcc_status lcc_net_tile_inputs_batch(lcc_ctx *ctx, int32_t nframes, const float *const *d_pts, const int64_t *n,
+                                     uint16_t *d_x, float *d_anchor);
 /* Outputs d_out [ntiles][5] fp32 (logit, v[3], d_rel), on the net's stream.
  * Inference runs on tcgen05 (TMEM accumulators, two tiles per MMA); its
  * waits are bounded, and one that ran out is reported by lcc_net_sync. */

@@ -248,10 +248,14 @@ __global__ void k_net_prep(NetDev nd) {
 
 // Net input of every 8x8 tile of the frame binned into slot 0; the range image
 // is reset to empty afterwards.  One warp per tile, two pixels per lane.
-__global__ void k_net_inputs(Geometry g, uint32_t *rimg, bf16 *x, float4 *anchor) {
+__global__ void k_net_inputs(Geometry g, uint32_t *rimg0, bf16 *x0, float4 *anchor0) {
     const int lane = threadIdx.x & 31;
     const int tile = blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5);
     if (tile >= g.NT) return;
+    // frame blockIdx.y: its range image is slot blockIdx.y, its tiles follow the previous frames'
+    uint32_t *rimg = rimg0 + (size_t)blockIdx.y * g.H * g.W;
+    bf16 *x = x0 + (size_t)blockIdx.y * g.NT * kPX * C0;
+    float4 *anchor = anchor0 + (size_t)blockIdx.y * g.NT;
     const int i0 = (tile / g.TC) * 8, j0 = (tile % g.TC) * 8;
     float r[2], p[2][3];
     bool v[2];
@@ -1215,17 +1219,26 @@ lcc_status lcc_net_set_params(lcc_net *net, const float *h_params) {
     return LCC_OK;
 }
 
-lcc_status lcc_net_tile_inputs(lcc_ctx *c, const float *d_pts, int64_t n, uint16_t *d_x, float *d_anchor) {
-    if (!c || !d_x || !d_anchor || c->g.th != 8 || c->g.tw != 8) return !c ? LCC_ERR_INVALID_ARG : LCC_ERR_UNSUPPORTED;
-    if (((uintptr_t)d_x & 7u) || ((uintptr_t)d_anchor & 15u)) return LCC_ERR_INVALID_ARG;
-    if (n < 0 || (n > 0 && (!d_pts || ((uintptr_t)d_pts & 15u)))) return LCC_ERR_INVALID_ARG;
-    const int slot = 0;
-    lcc_status st = bin_frames(c, 1, &slot, &d_pts, &n);
+lcc_status lcc_net_tile_inputs_batch(lcc_ctx *c, int32_t nframes, const float *const *d_pts, const int64_t *n,
+                                     uint16_t *d_x, float *d_anchor) {
+    if (!c || !d_x || !d_anchor || !d_pts || !n) return LCC_ERR_INVALID_ARG;
+    if (c->g.th != 8 || c->g.tw != 8) return LCC_ERR_UNSUPPORTED;
+    if (nframes < 1 || nframes > c->slots || ((uintptr_t)d_x & 7u) || ((uintptr_t)d_anchor & 15u))
+        return LCC_ERR_INVALID_ARG;
+    for (int f = 0; f < nframes; f++)
+        if (n[f] < 0 || (n[f] > 0 && (!d_pts[f] || ((uintptr_t)d_pts[f] & 15u)))) return LCC_ERR_INVALID_ARG;
+    int slots[kMaxBatch];
+    for (int f = 0; f < nframes; f++) slots[f] = f;
+    lcc_status st = bin_frames(c, nframes, slots, d_pts, n);
     if (st != LCC_OK) return st;
     const int wpb = 8;
-    k_net_inputs<<<(c->g.NT + wpb - 1) / wpb, wpb * 32, 0, c->stream>>>(c->g, c->s.rimg, reinterpret_cast<bf16 *>(d_x),
-                                                                         reinterpret_cast<float4 *>(d_anchor));
+    k_net_inputs<<<dim3((c->g.NT + wpb - 1) / wpb, nframes), wpb * 32, 0, c->stream>>>(
+        c->g, c->s.rimg, reinterpret_cast<bf16 *>(d_x), reinterpret_cast<float4 *>(d_anchor));
     return cudaGetLastError() == cudaSuccess ? LCC_OK : LCC_ERR_CUDA;
+}
+
+lcc_status lcc_net_tile_inputs(lcc_ctx *c, const float *d_pts, int64_t n, uint16_t *d_x, float *d_anchor) {
+    return lcc_net_tile_inputs_batch(c, 1, &d_pts, &n, d_x, d_anchor);
 }
 
 lcc_status lcc_net_forward(lcc_net *net, const uint16_t *d_x, int64_t ntiles, float *d_out) {

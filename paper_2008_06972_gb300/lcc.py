@@ -119,6 +119,7 @@ def load(path: str = LIB_PATH):
         "lcc_net_get_params": (i32, [vp, vp]),
         "lcc_net_set_params": (i32, [vp, vp]),
         "lcc_net_tile_inputs": (i32, [vp, vp, i64, vp, vp]),
+        "lcc_net_tile_inputs_batch": (i32, [vp, i32, vp, vp, vp, vp]),
         "lcc_net_forward": (i32, [vp, vp, i64, vp]),
         "lcc_net_sync": (i32, [vp]),
         "lcc_selftest_bounded_wait": (i32, [i64, vp]),
@@ -150,7 +151,7 @@ def exported_symbols() -> list[str]:
             "lcc_encode_keyframe", "lcc_encode_keyframe_seeded", "lcc_encode_keyframes", "lcc_encode_pframe", "lcc_encode_pframes", "lcc_encode_sequence",
             "lcc_encode_sequence_host", "lcc_keyframe_from_stream", "lcc_decode", "lcc_sync", "lcc_last_stats",
             "lcc_tile_records", "lcc_set_profiling", "lcc_kernel_times", "lcc_range_image_static", "lcc_net_num_params", "lcc_net_create", "lcc_net_destroy",
-            "lcc_net_get_params", "lcc_net_set_params", "lcc_net_tile_inputs", "lcc_net_forward", "lcc_net_sync", "lcc_net_gradient",
+            "lcc_net_get_params", "lcc_net_set_params", "lcc_net_tile_inputs", "lcc_net_tile_inputs_batch", "lcc_net_forward", "lcc_net_sync", "lcc_net_gradient",
             "lcc_net_train_step", "lcc_selftest_bounded_wait", "lcc_plan_create", "lcc_plan_update",
             "lcc_plan_encode", "lcc_plan_capture", "lcc_plan_replay", "lcc_plan_sync", "lcc_plan_get_info",
             "lcc_plan_destroy", "lcc_autotune"]
@@ -515,3 +516,9 @@ class Net:
 
 def net_tile_inputs(ctx: "Context", d_pts, n: int, d_x, d_anchor):
     _check(load().lcc_net_tile_inputs(ctx.h, _ptr(d_pts), n, _ptr(d_x), _ptr(d_anchor)), "lcc_net_tile_inputs")
+
+
+def net_tile_inputs_batch(ctx: "Context", d_pts: list, n: list, d_x, d_anchor):
+    _check(load().lcc_net_tile_inputs_batch(ctx.h, len(d_pts), _arr(ctypes.c_void_p, [_ptr(x) for x in d_pts]),
+                                            _arr(ctypes.c_int64, n), _ptr(d_x), _ptr(d_anchor)),
+           "lcc_net_tile_inputs_batch")

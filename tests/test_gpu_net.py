@@ -312,3 +312,20 @@ def test_batched_keyframes_match_single_calls(frame):
                 c.lcc_encode_keyframe(ds[i], n[i], None, one, one.numel(), nb1)
             assert c.lcc_sync() == lcc.OK
             assert one[:int(nb1.item())].cpu().numpy().tobytes() == outs[i][:nbs[i]].cpu().numpy().tobytes()
+
+
+def test_batched_inputs_match_single_frames():
+    from paper_2008_06972_gb300 import lcc
+    seq = synth.sequence_cfg2()
+    c = H.ctx(seq.sensor, tile_h=8, tile_w=8, max_batch=4)
+    frames = [seq.frames[i] for i in (1, 4, 6)]
+    nt = c.num_tiles
+    xb = torch.zeros((3 * nt, 64, 4), dtype=torch.int16, device="cuda")
+    ab = torch.zeros((3 * nt, 4), dtype=torch.float32, device="cuda")
+    lcc.net_tile_inputs_batch(c, [H.to_dev(f) for f in frames], [len(f) for f in frames], xb, ab)
+    for i, f in enumerate(frames):
+        x1 = torch.zeros((nt, 64, 4), dtype=torch.int16, device="cuda")
+        a1 = torch.zeros((nt, 4), dtype=torch.float32, device="cuda")
+        lcc.net_tile_inputs(c, H.to_dev(f), len(f), x1, a1)
+        assert c.lcc_sync() == lcc.OK
+        assert torch.equal(x1, xb[i * nt:(i + 1) * nt]) and torch.equal(a1, ab[i * nt:(i + 1) * nt])
