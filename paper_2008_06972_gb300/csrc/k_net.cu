@@ -618,7 +618,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_net_fwd_tc(NetDev nd, const b
     const long long G = gridDim.x;
     if (warp == kTcEpiWarps) {
         // ---- MMA warp: one lane issues every convolution of both pair slots ----
-        uint32_t ph[2] = {0u, 0u};
+        uint32_t ph = 0u;   // bit s: parity of slot s's next wait (no per-thread arrays: no local memory)
         const uint32_t aW1 = smem_u32(sW1), aW2 = smem_u32(sW2), aW3 = smem_u32(sW3);
         for (long long pa = blockIdx.x; pa * 2 < T; pa += 2 * G) {
             const bool hasB = (pa + G) * 2 < T;
@@ -627,7 +627,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_net_fwd_tc(NetDev nd, const b
 #pragma unroll 1
                 for (int sl = 0; sl < (hasB ? 2 : 1); sl++) {
                     if (lane == 0) {
-                        wait(smem_u32(bar + 3 + sl), ph[sl]);
+                        wait(smem_u32(bar + 3 + sl), (ph >> sl) & 1u);
                         tc_after_sync();
                         const uint32_t base = smem_u32(slot_x(sl));
                         const uint32_t d = tmem + (uint32_t)(sl * 64);
@@ -636,7 +636,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_net_fwd_tc(NetDev nd, const b
                         else tc_conv<C2, C3>(d, base + TX + TA1, aW3);
                         tc_commit(smem_u32(bar + 1 + sl));
                     }
-                    ph[sl] ^= 1u;
+                    ph ^= 1u << sl;
                     __syncwarp();
                 }
             }
@@ -645,7 +645,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_net_fwd_tc(NetDev nd, const b
         // ---- epilogue warps: row = 32 (warp % 4) + lane -> (y, tile, x); column part = warp / 4 ----
         const int quad = warp & 3, part = warp >> 2;
         const int row = quad * 32 + lane, grp = row >> 3, px = row & 7, py = grp >> 1, tl = grp & 1;
-        uint32_t ph[2] = {0u, 0u};
+        uint32_t ph = 0u;
         auto handoff = [&](int sl) {   // this warp's part of slot sl is written: hand it to the MMA warp
             proxy_fence();
             tc_before_sync();
@@ -653,11 +653,9 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_net_fwd_tc(NetDev nd, const b
             if (lane == 0) mbar_arrive(smem_u32(bar + 3 + sl));
         };
         for (long long pa = blockIdx.x; pa * 2 < T; pa += 2 * G) {
-            const long long pb = pa + G;
-            const bool hasB = pb * 2 < T;
-            const long long pr[2] = {pa, pb};
+            const bool hasB = (pa + G) * 2 < T;
             if (part < 2 && (part == 0 || hasB)) {   // inputs (4 channels + 4 zero): part p fills slot p
-                const long long tile = pr[part] * 2 + tl;
+                const long long tile = (pa + part * G) * 2 + tl;
                 uint2 v = make_uint2(0u, 0u);
                 if (tile < T) v = *reinterpret_cast<const uint2 *>(x + ((size_t)tile * kPX + py * 8 + px) * C0);
                 *reinterpret_cast<uint4 *>(slot_x(part) + tpos(0, py + 1, tl, px + 1)) = make_uint4(v.x, v.y, 0u, 0u);
@@ -667,8 +665,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_net_fwd_tc(NetDev nd, const b
             for (int layer = 0; layer < 3; layer++) {
 #pragma unroll 1
                 for (int sl = 0; sl < (hasB ? 2 : 1); sl++) {
-                    wait(smem_u32(bar + 1 + sl), ph[sl]);
-                    ph[sl] ^= 1u;
+                    wait(smem_u32(bar + 1 + sl), (ph >> sl) & 1u);
+                    ph ^= 1u << sl;
                     tc_after_sync();
                     const int cout = layer == 0 ? C1 : C2;
                     const float *bias = layer == 0 ? sB1 : layer == 1 ? sB2 : sB3;
@@ -726,7 +724,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_net_fwd_tc(NetDev nd, const b
             epi_sync();
             if (warp < 4) {   // head: warp w < 4 takes tile (w & 1) of pair slot (w >> 1)
                 const int sl = warp >> 1, t2 = warp & 1;
-                const long long tile = pr[sl] * 2 + t2;
+                const long long tile = (pa + sl * G) * 2 + t2;
                 if ((sl == 0 || hasB) && tile < T) {
                     const float *gs = sG + (sl * 2 + t2) * C3;
                     float yv = sC1[lane];
