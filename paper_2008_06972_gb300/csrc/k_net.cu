@@ -7,16 +7,18 @@
 // Net: input 4x8x8 (r - r_anchor, p - p_anchor; empty pixels 0), conv3x3
 // pad 1 4->32, ReLU, 32->64, ReLU, 64->64, ReLU, global average pool, linear
 // 64->32, ReLU, linear 32->5 (logit, normal, offset relative to the anchor).
-// BF16 operands with FP32 accumulation on the tensor cores (mma.sync
-// m16n8k16); activations are rounded to BF16 after each ReLU, as are the
-// pooled vector, the hidden head activation and the convolution gradients.
+// BF16 operands with FP32 accumulation on the tensor cores; activations are
+// rounded to BF16 after each ReLU, as are the pooled vector, the hidden head
+// activation and the convolution gradients.
 //
-// Every convolution is an implicit GEMM per tile: rows are the 64 pixels,
-// columns the output channels, and the reduction runs over the 9 taps x input
-// channels, read straight from a zero-bordered 10x10 copy of the tile in
-// shared memory (no im2col buffer).  The input-gradient convolution is the
-// same GEMM with the taps mirrored and the weights transposed.  The weight
-// gradient is a GEMM over (tile, pixel) split across CTAs.
+// Every convolution is an implicit GEMM: rows are pixels, columns output
+// channels, and the reduction runs over the 9 taps x input channels, read
+// straight from a zero-bordered 10x10 copy of the tile in shared memory (no
+// im2col buffer).  The forward pass (inference and training) runs on tcgen05
+// with TMEM accumulators, two tiles per 128-row MMA.  The backward pass runs
+// on the warp-level mma.sync m16n8k16 instruction: the input-gradient
+// convolution is the same GEMM with the taps mirrored and the weights
+// transposed, the weight gradient a GEMM over (tile, pixel) split across CTAs.
 #include <cuda_bf16.h>
 
 #include <algorithm>
@@ -39,8 +41,7 @@ constexpr int kPX = 64;                       // pixels of an 8x8 tile
 constexpr int C0 = 4, C1 = 32, C2 = 64, C3 = 64, HID = 32, NOUT = 5;
 constexpr int XS = 8;                         // padded channel stride of the input copy
 constexpr int A1S = C1 + 8, A2S = C2 + 8;     // padded channel strides (bank spread)
-constexpr int K1 = 48, B1S = 56;              // conv1: 9 taps x 4 channels = 36, padded to 3 k-steps
-constexpr int B2S = 9 * C1 + 8, B3S = 9 * C2 + 8, BTS = 9 * 64 + 8;
+constexpr int BTS = 9 * 64 + 8;               // input-gradient weight rows (9 taps x 64 channels + bank pad)
 constexpr int kNetWarps = 4;
 
 // offsets of the flat parameter vector: W1[32,4,3,3] b1 W2[64,32,3,3] b2 W3[64,64,3,3] b3 F1[32,64] c1 F2[5,32] c2
@@ -52,7 +53,6 @@ static_assert(NPARAM == 58853, "parameter count");
 // device copies of the weights in the layouts the kernels read
 struct NetDev {
     const float *theta;                      // fp32 master parameters
-    bf16 *B1f, *B2f, *B3f;                   // forward GEMM B: [cout][k = tap*cin + ci]
     bf16 *B2t, *B3t;                         // input-gradient GEMM B: [ci][k = tap*cout + co]
     float *F1b, *F2b;                        // head weights rounded to bf16 values
     bf16 *T1, *T2, *T3;                      // tcgen05 B operands: [tap][ci/8][cout][8], core-matrix order
@@ -126,83 +126,14 @@ __device__ __forceinline__ void zero_acc(float (&acc)[4][COUT / 8][4]) {
         for (int n = 0; n < COUT / 8; n++) acc[m][n][0] = acc[m][n][1] = acc[m][n][2] = acc[m][n][3] = 0.f;
 }
 
-// conv1: the reduction index is k = tap*4 + ci (36 real values, 3 k-steps of 16).
-__device__ __forceinline__ uint32_t conv1_a(const bf16 *xp, int py, int px, int k) {
-    if (k >= 36) return 0u;
-    const int tap = k >> 2, ci = k & 3;
-    return ld32(xp + ((py + tap / 3) * 10 + px + tap % 3) * XS + ci);
-}
-
-__device__ __forceinline__ void conv1_tile(const bf16 *xp, const bf16 *B1, float (&acc)[4][C1 / 8][4]) {
-    const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
-#pragma unroll
-    for (int ks = 0; ks < K1 / 16; ks++) {
-        const int k0 = ks * 16 + 2 * t;
-        uint32_t a[4][4];
-#pragma unroll
-        for (int m = 0; m < 4; m++) {
-            a[m][0] = conv1_a(xp, 2 * m, g, k0);
-            a[m][1] = conv1_a(xp, 2 * m + 1, g, k0);
-            a[m][2] = conv1_a(xp, 2 * m, g, k0 + 8);
-            a[m][3] = conv1_a(xp, 2 * m + 1, g, k0 + 8);
-        }
-#pragma unroll
-        for (int n = 0; n < C1 / 8; n++) {
-            const bf16 *bp = B1 + (n * 8 + g) * B1S + ks * 16 + 2 * t;
-            const uint32_t b0 = ld32(bp), b1 = ld32(bp + 8);
-#pragma unroll
-            for (int m = 0; m < 4; m++) mma_bf16(acc[m][n], a[m][0], a[m][1], a[m][2], a[m][3], b0, b1);
-        }
-    }
-}
-
-// bias + ReLU + bf16 into the next padded copy (and the training copy [64][C] when given)
-template <int COUT, int AS>
-__device__ __forceinline__ void epilogue(float (&acc)[4][COUT / 8][4], const float *bias, bf16 *ap_next,
-                                         bf16 *act_out) {
-    const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
-#pragma unroll
-    for (int m = 0; m < 4; m++)
-#pragma unroll
-        for (int n = 0; n < COUT / 8; n++) {
-            const int co = n * 8 + 2 * t;
-            const float b0 = __ldg(bias + co), b1 = __ldg(bias + co + 1);
-#pragma unroll
-            for (int h = 0; h < 2; h++) {
-                const int py = 2 * m + h, px = g;
-                const float v0 = fmaxf(acc[m][n][2 * h] + b0, 0.f), v1 = fmaxf(acc[m][n][2 * h + 1] + b1, 0.f);
-                if (ap_next) st32(ap_next + ((py + 1) * 10 + px + 1) * AS + co, v0, v1);
-                if (act_out) st32(act_out + (py * 8 + px) * COUT + co, v0, v1);
-            }
-        }
-}
-
 // ------------------------------------------------------------------ weights --
 
 __global__ void k_net_prep(NetDev nd) {
     const float *th = nd.theta;
-    const int n1 = C1 * B1S, n2 = C2 * B2S, n3 = C3 * B3S, n2t = C1 * BTS, n3t = C2 * BTS;
-    const int total = n1 + n2 + n3 + n2t + n3t + HID * C3 + NOUT * HID;
+    const int n2t = C1 * BTS, n3t = C2 * BTS;
+    const int total = n2t + n3t + HID * C3 + NOUT * HID;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < total; i += gridDim.x * blockDim.x) {
         int j = i;
-        if (j < n1) {
-            const int co = j / B1S, k = j % B1S;
-            nd.B1f[j] = __float2bfloat16_rn(k < 36 ? th[OW1 + co * 36 + (k & 3) * 9 + (k >> 2)] : 0.f);
-            continue;
-        }
-        j -= n1;
-        if (j < n2) {
-            const int co = j / B2S, k = j % B2S;
-            nd.B2f[j] = __float2bfloat16_rn(k < 9 * C1 ? th[OW2 + co * 9 * C1 + (k % C1) * 9 + k / C1] : 0.f);
-            continue;
-        }
-        j -= n2;
-        if (j < n3) {
-            const int co = j / B3S, k = j % B3S;
-            nd.B3f[j] = __float2bfloat16_rn(k < 9 * C2 ? th[OW3 + co * 9 * C2 + (k % C2) * 9 + k / C2] : 0.f);
-            continue;
-        }
-        j -= n3;
         if (j < n2t) {   // conv2 input gradient: rows ci (32), k = tap*64 + co
             const int ci = j / BTS, k = j % BTS;
             nd.B2t[j] = __float2bfloat16_rn(k < 9 * C2 ? th[OW2 + (k % C2) * 9 * C1 + ci * 9 + k / C2] : 0.f);
@@ -303,121 +234,7 @@ __global__ void k_net_inputs(Geometry g, uint32_t *rimg0, bf16 *x0, float4 *anch
     if (lane == 0) anchor[tile] = make_float4(pa0, pa1, pa2, ra);
 }
 
-// ------------------------------------------------------------------ forward --
-
-constexpr size_t kFwdWeightBytes = sizeof(bf16) * (size_t)(C1 * B1S + C2 * B2S + C3 * B3S);
-constexpr size_t kFwdWarpBytes = sizeof(bf16) * (size_t)(100 * XS + 100 * A1S + 100 * A2S) + sizeof(float) * (C3 + HID);
-constexpr size_t kFwdSmem = kFwdWeightBytes + kNetWarps * kFwdWarpBytes;
-
-// Persistent: the CTA stages the weights once, each warp runs one tile at a time.
-template <bool kTrain>
-__global__ void __launch_bounds__(kNetWarps * 32, 1) k_net_fwd(NetDev nd, const bf16 *x, long long T, float *out,
-                                                               NetAct act) {
-    extern __shared__ __align__(16) uint8_t sm[];
-    bf16 *sB1 = reinterpret_cast<bf16 *>(sm);
-    bf16 *sB2 = sB1 + C1 * B1S;
-    bf16 *sB3 = sB2 + C2 * B2S;
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    uint8_t *wbase = sm + kFwdWeightBytes + warp * kFwdWarpBytes;
-    bf16 *xp = reinterpret_cast<bf16 *>(wbase);
-    bf16 *a1p = xp + 100 * XS;
-    bf16 *a2p = a1p + 100 * A1S;
-    float *gs = reinterpret_cast<float *>(a2p + 100 * A2S);
-    float *hs = gs + C3;
-    {
-        const uint4 *src[3] = {reinterpret_cast<const uint4 *>(nd.B1f), reinterpret_cast<const uint4 *>(nd.B2f),
-                               reinterpret_cast<const uint4 *>(nd.B3f)};
-        uint4 *dst[3] = {reinterpret_cast<uint4 *>(sB1), reinterpret_cast<uint4 *>(sB2), reinterpret_cast<uint4 *>(sB3)};
-        const int cnt[3] = {C1 * B1S / 8, C2 * B2S / 8, C3 * B3S / 8};
-        for (int q = 0; q < 3; q++)
-            for (int i = threadIdx.x; i < cnt[q]; i += blockDim.x) dst[q][i] = src[q][i];
-        // zero this warp's padded copies once: borders stay zero, interiors are rewritten per tile
-        uint32_t *z = reinterpret_cast<uint32_t *>(wbase);
-        for (int i = lane; i < (int)(kFwdWarpBytes / 4); i += 32) z[i] = 0u;
-    }
-    __syncthreads();
-    const float *th = nd.theta;
-    for (long long tile = (long long)blockIdx.x * kNetWarps + warp; tile < T; tile += (long long)gridDim.x * kNetWarps) {
-        // input into the padded copy (4 channels, stride 8)
-#pragma unroll
-        for (int h = 0; h < 2; h++) {
-            const int q = lane + 32 * h, py = q / 8, px = q % 8;
-            const uint2 v = *reinterpret_cast<const uint2 *>(x + ((size_t)tile * kPX + q) * C0);
-            *reinterpret_cast<uint2 *>(xp + ((py + 1) * 10 + px + 1) * XS) = v;
-        }
-        __syncwarp();
-        {
-            float acc[4][C1 / 8][4];
-            zero_acc<C1>(acc);
-            conv1_tile(xp, sB1, acc);
-            epilogue<C1, A1S>(acc, th + OB1, a1p, kTrain ? act.a1 + (size_t)tile * kPX * C1 : nullptr);
-        }
-        __syncwarp();
-        {
-            float acc[4][C2 / 8][4];
-            zero_acc<C2>(acc);
-            conv_tile<C1, C2, A1S, B2S, false>(a1p, sB2, acc);
-            epilogue<C2, A2S>(acc, th + OB2, a2p, kTrain ? act.a2 + (size_t)tile * kPX * C2 : nullptr);
-        }
-        __syncwarp();
-        {
-            float acc[4][C3 / 8][4];
-            zero_acc<C3>(acc);
-            conv_tile<C2, C3, A2S, B3S, false>(a2p, sB3, acc);
-            const int g = lane >> 2, t = lane & 3;
-            bf16 *a3 = kTrain ? act.a3 + (size_t)tile * kPX * C3 : nullptr;
-#pragma unroll
-            for (int n = 0; n < C3 / 8; n++) {
-                const int co = n * 8 + 2 * t;
-                const float b0 = __ldg(th + OB3 + co), b1 = __ldg(th + OB3 + co + 1);
-                float s0 = 0.f, s1 = 0.f;
-#pragma unroll
-                for (int m = 0; m < 4; m++)
-#pragma unroll
-                    for (int h = 0; h < 2; h++) {
-                        const float v0 = bfround(fmaxf(acc[m][n][2 * h] + b0, 0.f));
-                        const float v1 = bfround(fmaxf(acc[m][n][2 * h + 1] + b1, 0.f));
-                        s0 += v0;
-                        s1 += v1;
-                        if (a3) st32(a3 + ((2 * m + h) * 8 + g) * C3 + co, v0, v1);
-                    }
-#pragma unroll
-                for (int off = 4; off < 32; off <<= 1) {
-                    s0 += __shfl_xor_sync(0xffffffffu, s0, off);
-                    s1 += __shfl_xor_sync(0xffffffffu, s1, off);
-                }
-                if (g == 0) {
-                    gs[co] = bfround(s0 * (1.0f / kPX));
-                    gs[co + 1] = bfround(s1 * (1.0f / kPX));
-                }
-            }
-        }
-        __syncwarp();
-        // head: lane j computes hidden unit j, then the 5 outputs by warp sums
-        float y = __ldg(th + OC1 + lane);
-        for (int c = 0; c < C3; c++) y = fmaf(__ldg(nd.F1b + lane * C3 + c), gs[c], y);
-        const float hj = bfround(fmaxf(y, 0.f));
-        float o[NOUT];
-#pragma unroll
-        for (int i = 0; i < NOUT; i++) {
-            float s = __ldg(nd.F2b + i * HID + lane) * hj;
-#pragma unroll
-            for (int off = 16; off; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
-            o[i] = s + __ldg(th + OC2 + i);
-        }
-        if (lane < NOUT) out[(size_t)tile * NOUT + lane] = o[lane];
-        if (kTrain) {
-            act.h[(size_t)tile * HID + lane] = hj;
-            act.g[(size_t)tile * C3 + lane] = gs[lane];
-            act.g[(size_t)tile * C3 + lane + 32] = gs[lane + 32];
-            if (lane < NOUT) act.o[(size_t)tile * NOUT + lane] = o[lane];
-        }
-        (void)hs;
-        __syncwarp();
-    }
-}
-
-// ------------------------------------------------------------------ forward on tcgen05 (inference) --
+// ------------------------------------------------------------------ forward on tcgen05 --
 //
 // Two tiles per step: M = 128 GEMM rows ordered (tile row y, tile, pixel x),
 // so that every 8-row core matrix of A is 8 consecutive pixels of one row of
@@ -546,8 +363,9 @@ __device__ __forceinline__ void mbar_arrive(uint32_t mbar) {
 }
 __device__ __forceinline__ void epi_sync() { asm volatile("bar.sync 1, %0;\n" ::"n"(kTcEpiWarps * 32) : "memory"); }
 
+template <bool kTrain>
 __global__ void __launch_bounds__(kTcThreads, 1) k_net_fwd_tc(NetDev nd, const bf16 *x, long long T, float *out,
-                                                              int *err) {
+                                                              int *err, NetAct act) {
     extern __shared__ __align__(1024) uint8_t sm[];
     uint8_t *sW1 = sm, *sW2 = sW1 + TW1, *sW3 = sW2 + TW2;
     uint8_t *sSlot = sW3 + TW3;                                        // [2][TSLOT]
@@ -682,6 +500,19 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_net_fwd_tc(NetDev nd, const b
                         tc_wait_ld();
 #pragma unroll
                         for (int i = 0; i < 16; i++) v[i] = fmaxf(v[i] + bias[c0 + i], 0.f);
+                        const long long tile = (pa + sl * G) * 2 + tl;
+                        if (kTrain && tile < T) {   // activations for the backward pass: [tile][pixel][channel]
+                            bf16 *ao = layer == 0 ? act.a1 + ((size_t)tile * kPX + py * 8 + px) * C1
+                                                  : (layer == 1 ? act.a2 : act.a3) + ((size_t)tile * kPX + py * 8 + px) * C2;
+                            uint32_t w[8];
+#pragma unroll
+                            for (int q = 0; q < 8; q++) {
+                                const __nv_bfloat162 b2 = __floats2bfloat162_rn(v[2 * q], v[2 * q + 1]);
+                                w[q] = *reinterpret_cast<const uint32_t *>(&b2);
+                            }
+                            *reinterpret_cast<uint4 *>(ao + c0) = make_uint4(w[0], w[1], w[2], w[3]);
+                            *reinterpret_cast<uint4 *>(ao + c0 + 8) = make_uint4(w[4], w[5], w[6], w[7]);
+                        }
                         if (layer < 2) {
 #pragma unroll
                             for (int h = 0; h < 2; h++) {
@@ -739,6 +570,12 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_net_fwd_tc(NetDev nd, const b
                         o[i] = sacc + sC2[i];
                     }
                     if (lane < NOUT) out[(size_t)tile * NOUT + lane] = o[lane];
+                    if (kTrain) {
+                        act.h[(size_t)tile * HID + lane] = hj;
+                        act.g[(size_t)tile * C3 + lane] = gs[lane];
+                        act.g[(size_t)tile * C3 + lane + 32] = gs[lane + 32];
+                        if (lane < NOUT) act.o[(size_t)tile * NOUT + lane] = o[lane];
+                    }
                 }
             }
         }
@@ -1083,15 +920,15 @@ int grid_for(const lcc_net *net, int64_t tiles) {
     return (int)std::max<int64_t>(1, std::min<int64_t>(want, net->sms));
 }
 
-lcc_status forward(lcc_net *net, const uint16_t *d_x, int64_t ntiles, float *d_out, bool train) {
+// tcgen05 forward; with `train` it also keeps the activations the backward pass reads
+lcc_status forward_tc(lcc_net *net, const uint16_t *d_x, int64_t ntiles, float *d_out, bool train) {
+    const int64_t pairs = (ntiles + 1) / 2;
+    const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(pairs, net->sms));
     const bf16 *x = reinterpret_cast<const bf16 *>(d_x);
-    if (train) {
-        k_net_fwd<true><<<grid_for(net, ntiles), kNetWarps * 32, kFwdSmem, net->stream>>>(net->nd, x, ntiles, d_out,
-                                                                                        net->act);
-    } else {
-        k_net_fwd<false><<<grid_for(net, ntiles), kNetWarps * 32, kFwdSmem, net->stream>>>(net->nd, x, ntiles, d_out,
-                                                                                         net->act);
-    }
+    if (train)
+        k_net_fwd_tc<true><<<grid, kTcThreads, kTcSmem, net->stream>>>(net->nd, x, ntiles, d_out, net->err, net->act);
+    else
+        k_net_fwd_tc<false><<<grid, kTcThreads, kTcSmem, net->stream>>>(net->nd, x, ntiles, d_out, net->err, net->act);
     return cudaGetLastError() == cudaSuccess ? LCC_OK : LCC_ERR_CUDA;
 }
 
@@ -1099,7 +936,7 @@ lcc_status backward(lcc_net *net, const uint16_t *d_x, const float *d_labels, in
     cudaStream_t st = net->stream;
     LCC_CUDA(cudaMemsetAsync(net->grad, 0, sizeof(float) * NPARAM, st));
     LCC_CUDA(cudaMemsetAsync(net->loss, 0, sizeof(float), st));
-    lcc_status s = forward(net, d_x, ntiles, net->act.o, true);
+    lcc_status s = forward_tc(net, d_x, ntiles, net->act.o, true);
     if (s != LCC_OK) return s;
     k_net_head_bwd<<<grid_for(net, ntiles), kNetWarps * 32, 0, st>>>(net->nd, d_labels, ntiles, net->act, net->grad,
                                                                      net->loss);
@@ -1132,7 +969,7 @@ lcc_status lcc_net_create(lcc_net **out, const float *h_params, int64_t max_tile
     net->max_tiles = max_tiles;
     net->sms = prop.multiProcessorCount;
     const size_t wb[] = {sizeof(float) * NPARAM * 4 + 256,   // theta, grad, m, v
-                         sizeof(bf16) * (C1 * B1S + C2 * B2S + C3 * B3S + C1 * BTS + C3 * BTS) + TW1 + TW2 + TW3,
+                         sizeof(bf16) * (C1 * BTS + C3 * BTS) + TW1 + TW2 + TW3,
                          sizeof(float) * (HID * C3 + NOUT * HID), 256};
     size_t wtotal = 0;
     for (size_t b : wb) wtotal += align256(b);
@@ -1154,10 +991,7 @@ lcc_status lcc_net_create(lcc_net **out, const float *h_params, int64_t max_tile
     net->v = net->m + NPARAM;
     w += align256(wb[0]);
     net->nd.theta = net->theta;
-    net->nd.B1f = (bf16 *)w;
-    net->nd.B2f = net->nd.B1f + C1 * B1S;
-    net->nd.B3f = net->nd.B2f + C2 * B2S;
-    net->nd.B2t = net->nd.B3f + C3 * B3S;
+    net->nd.B2t = (bf16 *)w;
     net->nd.B3t = net->nd.B2t + C1 * BTS;
     net->nd.T1 = net->nd.B3t + C3 * BTS;
     net->nd.T2 = net->nd.T1 + TW1 / 2;
@@ -1176,8 +1010,8 @@ lcc_status lcc_net_create(lcc_net **out, const float *h_params, int64_t max_tile
         *slots[i] = a;
         a += align256(ab[i]);
     }
-    if (smem_attr(k_net_fwd<true>, kFwdSmem) != LCC_OK || smem_attr(k_net_fwd<false>, kFwdSmem) != LCC_OK ||
-        smem_attr(k_net_conv_bwd, kBwdSmem) != LCC_OK || smem_attr(k_net_fwd_tc, kTcSmem) != LCC_OK ||
+    if (smem_attr(k_net_conv_bwd, kBwdSmem) != LCC_OK || smem_attr(k_net_fwd_tc<false>, kTcSmem) != LCC_OK ||
+        smem_attr(k_net_fwd_tc<true>, kTcSmem) != LCC_OK ||
         smem_attr(k_net_wgrad<C2, C3, 64, A2S>, wgrad_smem(A2S)) != LCC_OK ||
         cudaMemcpy(net->theta, h_params, sizeof(float) * NPARAM, cudaMemcpyHostToDevice) != cudaSuccess ||
         cudaMemset(net->m, 0, sizeof(float) * 2 * NPARAM) != cudaSuccess ||
@@ -1242,11 +1076,7 @@ lcc_status lcc_net_tile_inputs(lcc_ctx *c, const float *d_pts, int64_t n, uint16
 lcc_status lcc_net_forward(lcc_net *net, const uint16_t *d_x, int64_t ntiles, float *d_out) {
     if (!net || !d_x || !d_out || ntiles < 0 || ((uintptr_t)d_x & 7u)) return LCC_ERR_INVALID_ARG;
     if (ntiles == 0) return LCC_OK;
-    const int64_t pairs = (ntiles + 1) / 2;
-    const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(pairs, net->sms));
-    k_net_fwd_tc<<<grid, kTcThreads, kTcSmem, net->stream>>>(net->nd, reinterpret_cast<const bf16 *>(d_x), ntiles,
-                                                                  d_out, net->err);
-    return cudaGetLastError() == cudaSuccess ? LCC_OK : LCC_ERR_CUDA;
+    return forward_tc(net, d_x, ntiles, d_out, false);
 }
 
 lcc_status lcc_selftest_bounded_wait(int64_t limit, void *cuda_stream) {
