@@ -11,6 +11,8 @@ sequence.  Workload presets mirror the five benchmark configurations:
 * ``sequence_cfg2``  64x2048 frames (elevation -24.8..+2 deg), 20 walls,
   40 boxes, 60 poles, 2 % clutter, sigma 2 cm, 1 m/frame forward, 0.5 deg/frame
   yaw, 10 frames with the key frame in the middle.
+* ``sequence_cfg5``  128x4096 frames, twice the frame-1 density, 5% clutter,
+  1.5 m and 1 deg per frame, noisy poses.
 * ``batch_cfg3``  64 sequences of U{5..40} frames, each at one of the
   resolutions 16x1024, 32x1024, 64x2048, 128x2048 (elevation -15..+15 deg),
   the frame-1 scene family and noise, the cfg2 ego motion, key-frame groups of
@@ -205,6 +207,18 @@ def sequence_cfg2(sequence_id: int = 0, n_frames: int = 10) -> Sequence:
     seed = config_seed(2, sequence_id, 0)
     return sequence(HDL64_SENSOR, n_frames, seed, n_walls=20, n_boxes=40, n_poles=60,
                     step_m=1.0, yaw_deg=0.5, sigma=0.02, dropout=0.0, clutter=0.02)
+
+
+CFG5_SENSOR = Sensor(128, 4096, -15.0, 15.0, 80.0)
+
+
+def sequence_cfg5(sequence_id: int = 0, n_frames: int = 10) -> Sequence:
+    """128x4096 frames (524,288 beams): twice the frame-1 scene density (8 walls, 12 boxes, 20 poles),
+    5% clutter, sigma 2 cm, 1.5 m/frame forward and 1 deg/frame yaw, the given poses perturbed
+    by 1 cm / 0.05 deg (an IMU-like pose); the key frame is the middle one."""
+    seed = config_seed(5, sequence_id, 0)
+    return sequence(CFG5_SENSOR, n_frames, seed, n_walls=8, n_boxes=12, n_poles=20, step_m=1.5, yaw_deg=1.0,
+                    sigma=0.02, dropout=0.0, clutter=0.05, pose_noise=(0.01, 0.05))
 
 
 def offgrid_points(n: int, seed: int, r_lo=0.5, r_hi=90.0, elev_lo_deg=-40.0, elev_hi_deg=40.0):

@@ -412,3 +412,13 @@ def test_bounded_wait_expires_and_reports_timeout(cfg1):
     c = H.ctx(sensor)
     bits, _ = H.encode_keyframe(c, pts)
     assert len(bits) > 64
+
+
+def test_largest_resolution_sequence_with_noisy_poses():
+    """128x4096 frames (the largest configuration's resolution, 524k beams, 32,768 4x4 tiles per
+    frame) with IMU-like pose noise: key-frame and P-frame parity with the oracle, tile by tile."""
+    seq = synth.sequence_cfg5(0, 3)
+    info = _keyframe_case(seq.sensor, seq.frames[seq.key_index])
+    assert info["border"] <= max(2, 0.005 * info["compared"])
+    border = _pframe_case(seq, [f for f in range(3) if f != seq.key_index])
+    assert border <= 40
