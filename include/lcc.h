@@ -62,7 +62,9 @@ typedef struct {
     int32_t solver;           /* 3x3 plane solve: 0 float-float on the FP32 pipes (default), 1 FP64 */
     int32_t fit_schedule;     /* 0: a thread runs all refit rounds of its tile; 1 or 2: a thread runs that
                                  many rounds, tiles needing another round are queued and re-run in
-                                 dense warps, one kernel per round (same results for every value) */
+                                 dense warps, one kernel per round; 3: one round per thread, then the
+                                 queued tiles' remaining rounds in one dense kernel (same results for
+                                 every value) */
 } lcc_params;
 
 /* Per-frame statistics of the last encode (Fig. 11's categories and more). */

@@ -510,8 +510,9 @@ __device__ __forceinline__ void temporal_test(const TileView<TH_, TW_> &tv, cons
 // First pass over every tile: temporal test (P frames), then the spatial fit.
 // Schedule 0 runs all of a tile's rounds in its thread; schedules 1 and 2 run
 // at most that many spatial rounds here and queue the tile for dense round
-// kernels (k_fit_round), so that the few tiles needing more rounds do not
-// hold whole warps.
+// kernels (k_fit_round, one launch per round), schedule 3 runs one round here
+// and the queued tiles' remaining rounds in a single dense launch, so that the
+// few tiles needing more rounds do not hold whole warps.
 template <int TH_, int TW_, bool kQueue>
 __global__ void __launch_bounds__(kFitThreads) k_fit_first(Geometry g, Scratch s, Batch b, Poses ps) {
     using TV = TileView<TH_, TW_>;
@@ -550,7 +551,8 @@ __global__ void __launch_bounds__(kFitThreads) k_fit_first(Geometry g, Scratch s
 // One more spatial round for every queued tile; tiles that still need one
 // are pushed onto the next queue.
 template <int TH_, int TW_>
-__global__ void __launch_bounds__(kFitThreads) k_fit_round(Geometry g, Scratch s, Batch b, int in_q, int out_q) {
+__global__ void __launch_bounds__(kFitThreads) k_fit_round(Geometry g, Scratch s, Batch b, int in_q, int out_q,
+                                                             int max_rounds) {
     using TV = TileView<TH_, TW_>;
     uint32_t *queue = s.queue + (size_t)b.qset * 2 * s.qcap;
     uint32_t *qcount = s.qcount + 8 * b.qset;
@@ -564,7 +566,7 @@ __global__ void __launch_bounds__(kFitThreads) k_fit_round(Geometry g, Scratch s
         TileRec *recs = s.tiles + (size_t)b.slot[f] * g.NT;
         const TV tv(g, rimg, t);
         RecOut o = read_rec(recs + t);
-        const bool done = spatial_rounds<TH_, TW_>(tv, o, 1);
+        const bool done = spatial_rounds<TH_, TW_>(tv, o, max_rounds);
         queue_push(!done, item, qout, qcount + out_q);
         write_rec(recs + t, o);
     }
@@ -707,8 +709,12 @@ static cudaError_t launch_queued_rounds_t(const Geometry &g, const Scratch &s, c
         const int rounds_left = (b.kind == 1 && b.kf[0]) ? g.R + 1 : g.R + 1 - g.first_rounds;
         const long long worst = (long long)g.NT * b.nframes;
         const int blocks = (int)std::min<long long>((worst + kFitThreads - 1) / kFitThreads, 152 * 8);
+        if (g.schedule == 3) {   // the queued tiles run all their remaining rounds in one dense launch
+            k_fit_round<TH_, TW_><<<blocks, kFitThreads, 0, st>>>(g, s, b, 0, 1, rounds_left);
+            return cudaGetLastError();
+        }
         for (int r = 0; r < rounds_left; r++) {
-            k_fit_round<TH_, TW_><<<blocks, kFitThreads, 0, st>>>(g, s, b, r, r + 1);
+            k_fit_round<TH_, TW_><<<blocks, kFitThreads, 0, st>>>(g, s, b, r, r + 1, 1);
             const cudaError_t e = cudaGetLastError();
             if (e != cudaSuccess) return e;
         }

@@ -205,7 +205,7 @@ def test_schedule_invariance_and_determinism(cfg1):
     sen, pts = cfg1
     ref = None
     ref_recs = None
-    for la, sched in ((0, 0), (1, 0), (8, 0), (16, 0), (32, 0), (16, 1), (16, 2), (0, 2)):
+    for la, sched in ((0, 0), (1, 0), (8, 0), (16, 0), (32, 0), (16, 1), (16, 2), (0, 2), (16, 3)):
         c = H.ctx(sen, lookahead=la, fit_schedule=sched)
         b1, r1 = H.encode_keyframe(c, pts)
         b2, _ = H.encode_keyframe(c, pts)
@@ -324,7 +324,7 @@ def test_sequence_call_matches_separate_calls(cfg2_seq):
         # temporally afterwards; every tile record (rounds and flags included) is as if fused
         assert precs[i].tobytes() == seq_recs[f].tobytes(), f"frame {f}: tile records differ"
     # the same with the queued fit schedules (their P rounds also run beside the key frame)
-    for sched in (1, 2):
+    for sched in (1, 2, 3):
         cq = H.ctx(seq.sensor, max_batch=16, fit_schedule=sched)
         outs_q = [H.out_buf(cq) for _ in range(n)]
         cq.lcc_encode_sequence(seq.key_index, seq.poses, ds, [len(p) for p in seq.frames], outs_q,
