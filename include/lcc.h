@@ -86,7 +86,10 @@ typedef struct {
     float plane[4];           /* own spatial plane n.p = d, or (n', c') for a temporal tile */
     float tplane[4];          /* temporal test plane (n', c') if a K tile was found */
     uint32_t kref;            /* K tile the anchor maps to, 0xFFFFFFFF if none */
-    uint32_t ahead_mask;      /* run pre-test bits: bit j = this tile passes the plane of tile t-1-j */
+    uint32_t ahead_mask;      /* run pre-test bits: bit j = this tile passes the plane of tile t-1-j
+                                 (bit j and ahead_cnt[j] are meaningful where tile t-1-j has status 2;
+                                 otherwise they are 0, or in lcc_encode_sequence's P frames may hold
+                                 the test against that tile's spatial plane before it became temporal) */
     uint8_t status;           /* 0 empty, 1 fit failed, 2 fit ok, 3 temporal */
     uint8_t rounds;           /* spatial plane fits performed */
     uint8_t flags;            /* bit0 borderline, bit1 degenerate scatter, bit2 temporal tested,
@@ -224,6 +227,14 @@ lcc_status lcc_tile_records(lcc_ctx *ctx, int32_t frame, lcc_tile_info *h_out, i
  * "decode_px", "range_export".  Returns the number of entries written. */
 lcc_status lcc_set_profiling(lcc_ctx *ctx, int32_t enable);
 int32_t lcc_kernel_times(lcc_ctx *ctx, char names[][16], int64_t *launches, double *ms, int32_t cap);
+
+/* Launch timeline: for each timed launch since profiling was last enabled
+ * (in the order the launches were issued, up to 65536), its name and its
+ * start and end in milliseconds after the start of the first timed launch,
+ * across all the streams the context uses, so overlapping launches show as
+ * overlapping intervals.  Synchronous; writes at most cap entries (names,
+ * t0_ms and t1_ms may each be NULL) and returns the number written. */
+int32_t lcc_kernel_timeline(lcc_ctx *ctx, char names[][16], float *t0_ms, float *t1_ms, int32_t cap);
 
 /* ---- Learned tile proposal (net over 8x8 tiles) ----
  *

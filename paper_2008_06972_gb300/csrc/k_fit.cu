@@ -588,6 +588,12 @@ __global__ void __launch_bounds__(kFitThreads) k_temporal(Geometry g, Scratch s,
     const TV tv(g, rimg, t);
     if (tv.nv == 0) return;
     RecOut o = read_rec(recs + t);
+    {   // keep the run pre-test results when it ran first (they refer to other tiles' spatial planes)
+        const uint4 *src = reinterpret_cast<const uint4 *>(recs + t);
+        const uint4 q3 = src[3];
+        o.amask = src[2].y;
+        o.acnt[0] = q3.x; o.acnt[1] = q3.y; o.acnt[2] = q3.z; o.acnt[3] = q3.w;
+    }
     RecOut ot = o;
     ot.flags = 0;
     temporal_test<TH_, TW_>(tv, ps.m[f], b.kf[f], ot);

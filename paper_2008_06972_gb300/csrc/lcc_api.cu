@@ -48,14 +48,33 @@ void prof_end(lcc_ctx *c, int idx) {
 void prof_collect(lcc_ctx *c) {
     for (auto &r : c->pending) {
         float ms = 0.f;
+        bool base = false;
         if (cudaEventSynchronize(r.b) == cudaSuccess && cudaEventElapsedTime(&ms, r.a, r.b) == cudaSuccess) {
             c->launches[r.name]++;
             c->ms[r.name] += ms;
+            if (!c->prof_base) {
+                c->prof_base = r.a;
+                base = true;
+            }
+            float t0 = 0.f, t1 = 0.f;
+            if (c->timeline.size() < kMaxTimeline && cudaEventElapsedTime(&t0, c->prof_base, r.a) == cudaSuccess &&
+                cudaEventElapsedTime(&t1, c->prof_base, r.b) == cudaSuccess)
+                c->timeline.push_back(TimelineRec{r.name, t0, t1});
         }
-        c->pool.push_back(r.a);
+        if (!base) c->pool.push_back(r.a);
         c->pool.push_back(r.b);
     }
     c->pending.clear();
+}
+
+void prof_reset(lcc_ctx *c) {
+    for (int k = 0; k < kNumKernels; k++) {
+        c->launches[k] = 0;
+        c->ms[k] = 0.0;
+    }
+    if (c->prof_base) c->pool.push_back(c->prof_base);
+    c->prof_base = nullptr;
+    c->timeline.clear();
 }
 
 bool tile_supported(int th, int tw) {
@@ -357,7 +376,8 @@ lcc_status lcc_create(lcc_ctx **out, const lcc_sensor *sensor, const lcc_params 
             cudaSuccess ||
         cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking) != cudaSuccess ||
         cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
-        cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming) != cudaSuccess) {
+        cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&c->ev_kplanes, cudaEventDisableTiming) != cudaSuccess) {
         lcc_destroy(c);
         return LCC_ERR_CUDA;
     }
@@ -379,6 +399,7 @@ lcc_status lcc_destroy(lcc_ctx *c) {
         cudaEventDestroy(r.a);
         cudaEventDestroy(r.b);
     }
+    if (c->prof_base) cudaEventDestroy(c->prof_base);
     for (auto e : c->pool) cudaEventDestroy(e);
     if (c->side) {
         cudaStreamSynchronize(c->side);
@@ -386,6 +407,7 @@ lcc_status lcc_destroy(lcc_ctx *c) {
     }
     if (c->ev_fork) cudaEventDestroy(c->ev_fork);
     if (c->ev_join) cudaEventDestroy(c->ev_join);
+    if (c->ev_kplanes) cudaEventDestroy(c->ev_kplanes);
     cudaFree(c->d_tables);
     cudaFree(c->d_scratch);
     cudaFree(c->d_stage_pts);
@@ -579,8 +601,11 @@ lcc_status encode_sequence(lcc_ctx *c, int32_t nframes, int32_t key_index, const
         if ((st = encode_batch(c, 0, 1, &kslot, &kout, &kcap, nullptr, nullptr, &kfo)) != LCC_OK) return st;
         if ((st = encode_batch(c, 1, np, pslots, pout, pcap, pposes.data(), kfi, nullptr)) != LCC_OK) return st;
     } else {
-        // The P frames' spatial fits do not need the key frame: they run on the side stream while
-        // the key frame is encoded, and the temporal test (which needs its planes) runs after.
+        // The P frames' spatial fits and their run pre-test do not need the key frame: they run on
+        // the side stream while the key frame is fitted and merged.  The temporal test needs the
+        // key frame's coding planes, which its merge writes: the P frames' temporal test, merge,
+        // scan and pack follow on the side stream while the key frame's scan and pack finish on
+        // the main one.
         Batch bk, bp;
         Poses pk, pp;
         prepare_batch(bk, pk, 0, 1, &kslot, &kout, &kcap, nullptr, nullptr, &kfo, nullptr);
@@ -610,17 +635,47 @@ lcc_status encode_sequence(lcc_ctx *c, int32_t nframes, int32_t key_index, const
             if (launch_queued_rounds(c->g, c->s, bp, c->side) != cudaSuccess) sst = LCC_ERR_CUDA;
             prof_end(c, pi);
         }
+        if (sst == LCC_OK) {
+            const int pi = prof_begin(c, 8);
+            if (launch_lookbehind(c->g, c->s, bp, c->side) != cudaSuccess) sst = LCC_ERR_CUDA;
+            prof_end(c, pi);
+        }
         c->stream = main;
         if (sst != LCC_OK) return sst;
-        LCC_CUDA(cudaEventRecord(c->ev_join, c->side));
         if (!h2d(key_index, main)) return LCC_ERR_CUDA;
         if ((st = bin_frames(c, 1, &kslot, &d_pts[key_index], &n[key_index])) != LCC_OK) return st;
         LCC_LAUNCH(c, 1, launch_fit(c->g, c->s, bk, pk, c->stream));
-        if ((st = encode_tail(c, bk)) != LCC_OK) return st;
-        LCC_CUDA(cudaStreamWaitEvent(c->stream, c->ev_join, 0));
+        LCC_LAUNCH(c, 8, launch_fit_rounds(c->g, c->s, bk, c->stream));
+        LCC_LAUNCH(c, 2, launch_merge(c->g, c->s, bk, c->stream));
+        LCC_CUDA(cudaEventRecord(c->ev_kplanes, main));
+        LCC_LAUNCH(c, 3, launch_scan(c->g, c->s, bk, c->stream));
+        LCC_LAUNCH(c, 4, launch_pack(c->g, c->s, bk, c->stream));
+        // the P frames' temporal test and tail, on the side stream once the key planes exist
+        LCC_CUDA(cudaStreamWaitEvent(c->side, c->ev_kplanes, 0));
         for (int f = 0; f < np; f++) bp.kf[f] = k->planes;
-        LCC_LAUNCH(c, 9, launch_temporal(c->g, c->s, bp, pp, c->stream));
-        if ((st = encode_tail(c, bp, true)) != LCC_OK) return st;
+        c->stream = c->side;
+        const int pt = prof_begin(c, 9);
+        if (launch_temporal(c->g, c->s, bp, pp, c->side) != cudaSuccess) sst = LCC_ERR_CUDA;
+        prof_end(c, pt);
+        if (sst == LCC_OK) {
+            const int pm = prof_begin(c, 2);
+            if (launch_merge(c->g, c->s, bp, c->side) != cudaSuccess) sst = LCC_ERR_CUDA;
+            prof_end(c, pm);
+        }
+        if (sst == LCC_OK) {
+            const int ps2 = prof_begin(c, 3);
+            if (launch_scan(c->g, c->s, bp, c->side) != cudaSuccess) sst = LCC_ERR_CUDA;
+            prof_end(c, ps2);
+        }
+        if (sst == LCC_OK) {
+            const int pk2 = prof_begin(c, 4);
+            if (launch_pack(c->g, c->s, bp, c->side) != cudaSuccess) sst = LCC_ERR_CUDA;
+            prof_end(c, pk2);
+        }
+        c->stream = main;
+        if (sst != LCC_OK) return sst;
+        LCC_CUDA(cudaEventRecord(c->ev_join, c->side));
+        LCC_CUDA(cudaStreamWaitEvent(main, c->ev_join, 0));
     }
     c->last_nframes = nframes;
     return copy_bytes(c, nframes, slots, out_bytes);
@@ -831,11 +886,24 @@ lcc_status lcc_set_profiling(lcc_ctx *c, int32_t enable) {
     if (!c) return LCC_ERR_INVALID_ARG;
     c->prof = enable != 0;
     prof_collect(c);
-    for (int k = 0; k < kNumKernels; k++) {
-        c->launches[k] = 0;
-        c->ms[k] = 0.0;
-    }
+    prof_reset(c);
     return LCC_OK;
+}
+
+int32_t lcc_kernel_timeline(lcc_ctx *c, char names[][16], float *t0_ms, float *t1_ms, int32_t cap) {
+    if (!c || cap < 0) return 0;
+    prof_collect(c);
+    const int32_t w = (int32_t)std::min<size_t>((size_t)cap, c->timeline.size());
+    for (int32_t k = 0; k < w; k++) {
+        const TimelineRec &r = c->timeline[k];
+        if (names) {
+            strncpy(names[k], kKernelNames[r.name], 15);
+            names[k][15] = 0;
+        }
+        if (t0_ms) t0_ms[k] = r.t0;
+        if (t1_ms) t1_ms[k] = r.t1;
+    }
+    return w;
 }
 
 int32_t lcc_kernel_times(lcc_ctx *c, char names[][16], int64_t *launches, double *ms, int32_t cap) {

@@ -19,6 +19,12 @@ struct ProfRec {
     cudaEvent_t a, b;
 };
 
+struct TimelineRec {
+    int name;
+    float t0, t1;   // ms after the first launch timed since profiling was (re)enabled
+};
+constexpr size_t kMaxTimeline = 65536;
+
 constexpr int kNumKernels = 10;
 extern const char *kKernelNames[];
 
@@ -38,7 +44,7 @@ struct lcc_ctx {
     lcc_params prm;
     cudaStream_t stream = nullptr;
     cudaStream_t side = nullptr;          // second stream for work that overlaps the key frame
-    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr, ev_kplanes = nullptr;
     lcc::Geometry g{};
     lcc::Scratch s{};
     void *d_tables = nullptr;
@@ -54,6 +60,8 @@ struct lcc_ctx {
     std::vector<cudaEvent_t> pool;
     int64_t launches[lcc::api::kNumKernels] = {};
     double ms[lcc::api::kNumKernels] = {};
+    cudaEvent_t prof_base = nullptr;   // start event of the first timed launch
+    std::vector<lcc::api::TimelineRec> timeline;
     // host-buffer staging
     void *d_stage_pts = nullptr;
     size_t stage_pts_cap = 0;

@@ -112,6 +112,7 @@ def load(path: str = LIB_PATH):
         "lcc_tile_records": (i32, [vp, i32, vp, i64]),
         "lcc_set_profiling": (i32, [vp, i32]),
         "lcc_kernel_times": (i32, [vp, vp, vp, vp, i32]),
+        "lcc_kernel_timeline": (i32, [vp, vp, vp, vp, i32]),
         "lcc_range_image_static": (i32, [vp, vp, i64, vp, vp, vp]),
         "lcc_net_num_params": (i64, []),
         "lcc_net_create": (i32, [vp, vp, i64, vp]),
@@ -150,7 +151,7 @@ def exported_symbols() -> list[str]:
             "lcc_num_tiles", "lcc_tables", "lcc_range_image", "lcc_keyframe_create", "lcc_keyframe_free",
             "lcc_encode_keyframe", "lcc_encode_keyframe_seeded", "lcc_encode_keyframes", "lcc_encode_pframe", "lcc_encode_pframes", "lcc_encode_sequence",
             "lcc_encode_sequence_host", "lcc_keyframe_from_stream", "lcc_decode", "lcc_sync", "lcc_last_stats",
-            "lcc_tile_records", "lcc_set_profiling", "lcc_kernel_times", "lcc_range_image_static", "lcc_net_num_params", "lcc_net_create", "lcc_net_destroy",
+            "lcc_tile_records", "lcc_set_profiling", "lcc_kernel_times", "lcc_kernel_timeline", "lcc_range_image_static", "lcc_net_num_params", "lcc_net_create", "lcc_net_destroy",
             "lcc_net_get_params", "lcc_net_set_params", "lcc_net_tile_inputs", "lcc_net_tile_inputs_batch", "lcc_net_forward", "lcc_net_sync", "lcc_net_gradient",
             "lcc_net_train_step", "lcc_selftest_bounded_wait", "lcc_plan_create", "lcc_plan_update",
             "lcc_plan_encode", "lcc_plan_capture", "lcc_plan_replay", "lcc_plan_sync", "lcc_plan_get_info",
@@ -358,6 +359,14 @@ class Context:
         ms = np.zeros(16, np.float64)
         n = self.lib.lcc_kernel_times(self.h, names, launches.ctypes.data, ms.ctypes.data, 16)
         return {bytes(names[i]).split(b"\0")[0].decode(): (int(launches[i]), float(ms[i])) for i in range(n)}
+
+    def lcc_kernel_timeline(self, cap: int = 4096) -> list:
+        """[(name, start_ms, end_ms)] of the launches timed since profiling was enabled."""
+        names = (ctypes.c_char * 16 * cap)()
+        t0 = np.zeros(cap, np.float32)
+        t1 = np.zeros(cap, np.float32)
+        n = self.lib.lcc_kernel_timeline(self.h, names, t0.ctypes.data, t1.ctypes.data, cap)
+        return [(bytes(names[i]).split(b"\0")[0].decode(), float(t0[i]), float(t1[i])) for i in range(n)]
 
 
 def _host_ptr(a) -> int:
