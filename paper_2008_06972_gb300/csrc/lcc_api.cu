@@ -372,12 +372,16 @@ lcc_status lcc_create(lcc_ctx **out, const lcc_sensor *sensor, const lcc_params 
     c->s.qcap = (uint32_t)(sl * nt);
     cudaMemset(c->d_scratch, 0, total);
     cudaMemset(c->s.rimg, 0xFF, sl * npx * 4);
+    int prio_hi = 0;
     if (cudaHostAlloc(&c->h_pinned, sizeof(unsigned long long) * (kMaxBatch + 1), cudaHostAllocDefault) !=
             cudaSuccess ||
         cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaDeviceGetStreamPriorityRange(nullptr, &prio_hi) != cudaSuccess ||
+        cudaStreamCreateWithPriority(&c->kstream, cudaStreamNonBlocking, prio_hi) != cudaSuccess ||
         cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
         cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming) != cudaSuccess ||
-        cudaEventCreateWithFlags(&c->ev_kplanes, cudaEventDisableTiming) != cudaSuccess) {
+        cudaEventCreateWithFlags(&c->ev_kplanes, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&c->ev_kdone, cudaEventDisableTiming) != cudaSuccess) {
         lcc_destroy(c);
         return LCC_ERR_CUDA;
     }
@@ -405,9 +409,14 @@ lcc_status lcc_destroy(lcc_ctx *c) {
         cudaStreamSynchronize(c->side);
         cudaStreamDestroy(c->side);
     }
+    if (c->kstream) {
+        cudaStreamSynchronize(c->kstream);
+        cudaStreamDestroy(c->kstream);
+    }
     if (c->ev_fork) cudaEventDestroy(c->ev_fork);
     if (c->ev_join) cudaEventDestroy(c->ev_join);
     if (c->ev_kplanes) cudaEventDestroy(c->ev_kplanes);
+    if (c->ev_kdone) cudaEventDestroy(c->ev_kdone);
     cudaFree(c->d_tables);
     cudaFree(c->d_scratch);
     cudaFree(c->d_stage_pts);
@@ -601,11 +610,13 @@ lcc_status encode_sequence(lcc_ctx *c, int32_t nframes, int32_t key_index, const
         if ((st = encode_batch(c, 0, 1, &kslot, &kout, &kcap, nullptr, nullptr, &kfo)) != LCC_OK) return st;
         if ((st = encode_batch(c, 1, np, pslots, pout, pcap, pposes.data(), kfi, nullptr)) != LCC_OK) return st;
     } else {
-        // The P frames' spatial fits and their run pre-test do not need the key frame: they run on
-        // the side stream while the key frame is fitted and merged.  The temporal test needs the
-        // key frame's coding planes, which its merge writes: the P frames' temporal test, merge,
-        // scan and pack follow on the side stream while the key frame's scan and pack finish on
-        // the main one.
+        // The key frame's chain (binning, fit, run pre-test, merge, scan, pack) runs on a private
+        // stream of the highest priority, issued first, so that its blocks are dispatched ahead of
+        // the P frames' whenever both wait for room on the SMs.  The P frames' binning, spatial fits
+        // and run pre-test do not need the key frame and run on the side stream beside it.  Their
+        // temporal test needs the key frame's coding planes, which its merge writes: the P frames'
+        // temporal test, merge, scan and pack follow on the side stream while the key frame's scan
+        // and pack finish.  The calling stream then waits for both.
         Batch bk, bp;
         Poses pk, pp;
         prepare_batch(bk, pk, 0, 1, &kslot, &kout, &kcap, nullptr, nullptr, &kfo, nullptr);
@@ -617,64 +628,46 @@ lcc_status encode_sequence(lcc_ctx *c, int32_t nframes, int32_t key_index, const
             pdp[q] = d_pts[pslots[q]];
             pn[q] = n[pslots[q]];
         }
-        LCC_CUDA(cudaEventRecord(c->ev_fork, c->stream));
+        struct StreamGuard {   // launches (and their profiling events) go to c->stream
+            lcc_ctx *c;
+            cudaStream_t saved;
+            ~StreamGuard() { c->stream = saved; }
+        } guard{c, c->stream};
+        const cudaStream_t main = c->stream;
+        LCC_CUDA(cudaEventRecord(c->ev_fork, main));
+        LCC_CUDA(cudaStreamWaitEvent(c->kstream, c->ev_fork, 0));
         LCC_CUDA(cudaStreamWaitEvent(c->side, c->ev_fork, 0));
-        cudaStream_t main = c->stream;
-        c->stream = c->side;   // launches (and their profiling events) on the side stream
-        lcc_status sst = LCC_OK;
-        for (int q = 0; q < np && sst == LCC_OK; q++)
-            if (!h2d(pslots[q], c->side)) sst = LCC_ERR_CUDA;
-        if (sst == LCC_OK) sst = bin_frames(c, np, pslots, pdp, pn);
-        if (sst == LCC_OK) {
-            const int pi = prof_begin(c, 1);
-            if (launch_fit(c->g, c->s, bp, pp, c->side) != cudaSuccess) sst = LCC_ERR_CUDA;
-            prof_end(c, pi);
-        }
-        if (sst == LCC_OK && c->g.schedule >= 1) {   // the rest of their spatial rounds, still beside K
-            const int pi = prof_begin(c, 8);
-            if (launch_queued_rounds(c->g, c->s, bp, c->side) != cudaSuccess) sst = LCC_ERR_CUDA;
-            prof_end(c, pi);
-        }
-        if (sst == LCC_OK) {
-            const int pi = prof_begin(c, 8);
-            if (launch_lookbehind(c->g, c->s, bp, c->side) != cudaSuccess) sst = LCC_ERR_CUDA;
-            prof_end(c, pi);
-        }
-        c->stream = main;
-        if (sst != LCC_OK) return sst;
-        if (!h2d(key_index, main)) return LCC_ERR_CUDA;
+        // key frame: binning and fit
+        c->stream = c->kstream;
+        if (!h2d(key_index, c->kstream)) return LCC_ERR_CUDA;
         if ((st = bin_frames(c, 1, &kslot, &d_pts[key_index], &n[key_index])) != LCC_OK) return st;
         LCC_LAUNCH(c, 1, launch_fit(c->g, c->s, bk, pk, c->stream));
+        // P frames: binning, spatial fits (and the rest of their rounds), run pre-test
+        c->stream = c->side;
+        for (int q = 0; q < np; q++)
+            if (!h2d(pslots[q], c->side)) return LCC_ERR_CUDA;
+        if ((st = bin_frames(c, np, pslots, pdp, pn)) != LCC_OK) return st;
+        LCC_LAUNCH(c, 1, launch_fit(c->g, c->s, bp, pp, c->stream));
+        if (c->g.schedule >= 1) LCC_LAUNCH(c, 8, launch_queued_rounds(c->g, c->s, bp, c->stream));
+        LCC_LAUNCH(c, 8, launch_lookbehind(c->g, c->s, bp, c->stream));
+        // key frame: the rest of its rounds and its pre-test, merge (its coding planes), scan, pack
+        c->stream = c->kstream;
         LCC_LAUNCH(c, 8, launch_fit_rounds(c->g, c->s, bk, c->stream));
         LCC_LAUNCH(c, 2, launch_merge(c->g, c->s, bk, c->stream));
-        LCC_CUDA(cudaEventRecord(c->ev_kplanes, main));
+        LCC_CUDA(cudaEventRecord(c->ev_kplanes, c->kstream));
         LCC_LAUNCH(c, 3, launch_scan(c->g, c->s, bk, c->stream));
         LCC_LAUNCH(c, 4, launch_pack(c->g, c->s, bk, c->stream));
-        // the P frames' temporal test and tail, on the side stream once the key planes exist
+        LCC_CUDA(cudaEventRecord(c->ev_kdone, c->kstream));
+        // P frames: temporal test against the key planes, merge, scan, pack
+        c->stream = c->side;
         LCC_CUDA(cudaStreamWaitEvent(c->side, c->ev_kplanes, 0));
         for (int f = 0; f < np; f++) bp.kf[f] = k->planes;
-        c->stream = c->side;
-        const int pt = prof_begin(c, 9);
-        if (launch_temporal(c->g, c->s, bp, pp, c->side) != cudaSuccess) sst = LCC_ERR_CUDA;
-        prof_end(c, pt);
-        if (sst == LCC_OK) {
-            const int pm = prof_begin(c, 2);
-            if (launch_merge(c->g, c->s, bp, c->side) != cudaSuccess) sst = LCC_ERR_CUDA;
-            prof_end(c, pm);
-        }
-        if (sst == LCC_OK) {
-            const int ps2 = prof_begin(c, 3);
-            if (launch_scan(c->g, c->s, bp, c->side) != cudaSuccess) sst = LCC_ERR_CUDA;
-            prof_end(c, ps2);
-        }
-        if (sst == LCC_OK) {
-            const int pk2 = prof_begin(c, 4);
-            if (launch_pack(c->g, c->s, bp, c->side) != cudaSuccess) sst = LCC_ERR_CUDA;
-            prof_end(c, pk2);
-        }
-        c->stream = main;
-        if (sst != LCC_OK) return sst;
+        LCC_LAUNCH(c, 9, launch_temporal(c->g, c->s, bp, pp, c->stream));
+        LCC_LAUNCH(c, 2, launch_merge(c->g, c->s, bp, c->stream));
+        LCC_LAUNCH(c, 3, launch_scan(c->g, c->s, bp, c->stream));
+        LCC_LAUNCH(c, 4, launch_pack(c->g, c->s, bp, c->stream));
         LCC_CUDA(cudaEventRecord(c->ev_join, c->side));
+        LCC_CUDA(cudaStreamWaitEvent(main, c->ev_kdone, 0));
         LCC_CUDA(cudaStreamWaitEvent(main, c->ev_join, 0));
     }
     c->last_nframes = nframes;

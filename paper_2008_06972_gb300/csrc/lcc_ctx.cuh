@@ -44,7 +44,8 @@ struct lcc_ctx {
     lcc_params prm;
     cudaStream_t stream = nullptr;
     cudaStream_t side = nullptr;          // second stream for work that overlaps the key frame
-    cudaEvent_t ev_fork = nullptr, ev_join = nullptr, ev_kplanes = nullptr;
+    cudaStream_t kstream = nullptr;   // key-frame chain of a sequence call (highest priority)
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr, ev_kplanes = nullptr, ev_kdone = nullptr;
     lcc::Geometry g{};
     lcc::Scratch s{};
     void *d_tables = nullptr;
