@@ -455,8 +455,51 @@ __device__ __forceinline__ bool spatial_rounds(const TileView<TH_, TW_> &tv, Rec
     return done;
 }
 
+// Lanes per tile of the lane-parallel temporal test (k_temporal): lane l of a
+// tile's group owns pixels k = l, l + L, l + 2L, ... (PX / L of them).
+template <int TH_, int TW_>
+struct TLanes {
+    static constexpr int PX = TH_ * TW_;
+    static constexpr int L = PX <= 16 ? 4 : (PX <= 64 ? 8 : 16);
+    static constexpr int PPL = PX / L;
+};
+
+// n'.p of pixel k in float-float (the terms of the temporal offset's mean).
+__device__ __forceinline__ ff dot_term(const float n[3], float rr, float ux, float uy, float uz) {
+    return ff_add(ff_add(two_prod(n[0], __fmul_rn(rr, ux)), two_prod(n[1], __fmul_rn(rr, uy))),
+                  two_prod(n[2], __fmul_rn(rr, uz)));
+}
+
+// Sum over the pixels of set S of a tile in the order the L lanes of k_temporal form it:
+// pixel class l = k mod L summed in increasing k, then the class sums pairwise,
+// ((0+1)+(2+3))+..., which is the order of an xor-butterfly over the lanes (float-float
+// addition is commutative bit for bit, so both halves of every butterfly step agree).
+template <int TH_, int TW_>
+__device__ __forceinline__ ff class_tree_sum(const TileView<TH_, TW_> &tv, const Mask &S, const float n[3]) {
+    constexpr int PX = TH_ * TW_, L = TLanes<TH_, TW_>::L;
+    ff stk[6];
+    int depth = 0;
+#pragma unroll
+    for (int l = 0; l < L; l++) {
+        ff p = {0.f, 0.f};
+#pragma unroll 2
+        for (int k = l; k < PX; k += L) {
+            if (!S.get(k)) continue;
+            float ux, uy, uz;
+            tv.u(k, ux, uy, uz);
+            p = ff_add(p, dot_term(n, tv.r(k), ux, uy, uz));
+        }
+#pragma unroll
+        for (int cnt = l + 1; (cnt & 1) == 0; cnt >>= 1) p = ff_add(stk[--depth], p);
+        stk[depth++] = p;
+    }
+    return stk[0];
+}
+
 // Temporal test of a P tile (Sec. III-D): anchor to key-frame coordinates,
-// K tile lookup, rotated normal, offset refit rounds.  Updates o.
+// K tile lookup, rotated normal, offset refit rounds.  Updates o.  One thread
+// per tile; k_temporal runs the same test with a group of lanes per tile and
+// sums in the same order (class_tree_sum), so both give the same bits.
 template <int TH_, int TW_>
 __device__ __forceinline__ void temporal_test(const TileView<TH_, TW_> &tv, const double *M, const float4 *kf,
                                               RecOut &o) {
@@ -477,17 +520,7 @@ __device__ __forceinline__ void temporal_test(const TileView<TH_, TW_> &tv, cons
     float c = 0.f;
     bool border = false;
     for (;;) {
-        ff acc = {0.f, 0.f};
-#pragma unroll 2
-        for (int k = 0; k < TileView<TH_, TW_>::PX; k++) {
-            if (!S.get(k)) continue;
-            float ux, uy, uz;
-            tv.u(k, ux, uy, uz);
-            const float rr = tv.r(k);
-            const ff dp = ff_add(ff_add(two_prod(n[0], __fmul_rn(rr, ux)), two_prod(n[1], __fmul_rn(rr, uy))),
-                                 two_prod(n[2], __fmul_rn(rr, uz)));
-            acc = ff_add(acc, dp);
-        }
+        const ff acc = class_tree_sum<TH_, TW_>(tv, S, n);
         c = ffm::mul({acc.hi, acc.lo}, ffm::rcp(ffm::mk((float)nS))).hi;   // mean of n'.p
         o.t_rounds++;
         nI = tv.inliers(make_float4(n[0], n[1], n[2], c), I, border);
@@ -577,16 +610,59 @@ __global__ void __launch_bounds__(kFitThreads) k_fit_round(Geometry g, Scratch s
 // key frame's planes, and the same per-tile decision as the fused pass — a
 // tile that passes becomes TEMPORAL exactly as if its spatial fit had never
 // run; otherwise the spatial result stands and the temporal fields are added.
+// Temporal test of the P frames after their spatial fits (lcc_encode_sequence):
+// a group of L lanes per tile (TLanes), each lane holding its PX / L pixels in
+// registers; sums and inlier sets are combined by xor-butterflies inside the
+// group.  A tile that passes becomes temporal; otherwise only the temporal
+// fields and flags of its record change (its spatial fit and run pre-test stay).
 template <int TH_, int TW_>
 __global__ void __launch_bounds__(kFitThreads) k_temporal(Geometry g, Scratch s, Batch b, Poses ps) {
-    using TV = TileView<TH_, TW_>;
+    constexpr int PX = TH_ * TW_, L = TLanes<TH_, TW_>::L, PPL = TLanes<TH_, TW_>::PPL;
+    static_assert(PX % L == 0 && kFitThreads % L == 0 && 32 % L == 0, "lane groups");
     const int f = blockIdx.y;
-    const int t = blockIdx.x * kFitThreads + threadIdx.x;
-    if (t >= g.NT || !b.kf[f]) return;
+    const int lane = threadIdx.x & 31, l = lane % L;
+    const int t = (blockIdx.x * kFitThreads + (int)threadIdx.x) / L;
+    const unsigned gmask = ((1u << L) - 1u) << (lane - l);
+    if (t >= g.NT || !b.kf[f]) return;   // whole groups leave together
     const uint32_t *rimg = s.rimg + (size_t)b.slot[f] * g.H * g.W;
     TileRec *recs = s.tiles + (size_t)b.slot[f] * g.NT;
-    const TV tv(g, rimg, t);
-    if (tv.nv == 0) return;
+    const int i0 = (t / g.TC) * TH_, j0 = (t % g.TC) * TW_;
+    // this lane's pixels: range (0 if empty) and unit ray
+    float pr[PPL], pux[PPL], puy[PPL], puz[PPL];
+    Mask V;
+    V.w0 = V.w1 = 0ull;
+#pragma unroll
+    for (int m = 0; m < PPL; m++) {
+        const int k = l + L * m, i = i0 + k / TW_, j = j0 + k % TW_;
+        pr[m] = 0.f;
+        pux[m] = puy[m] = puz[m] = 0.f;
+        if (i < g.H && j < g.W) {
+            const uint32_t bits = __ldg(rimg + (size_t)i * g.W + j);
+            if (bits_valid(bits)) {
+                pr[m] = __uint_as_float(bits);
+                beam(g, i, j, pux[m], puy[m], puz[m]);
+                V.set(k);
+            }
+        }
+    }
+#pragma unroll
+    for (int off = 1; off < L; off <<= 1) {
+        V.w0 |= __shfl_xor_sync(gmask, V.w0, off);
+        V.w1 |= __shfl_xor_sync(gmask, V.w1, off);
+    }
+    const int nv = __popcll(V.w0) + __popcll(V.w1);
+    if (nv == 0) return;
+    const int first = V.w0 ? __ffsll((long long)V.w0) - 1 : 64 + __ffsll((long long)V.w1) - 1;
+    float ax, ay, az;
+    {
+        const int i = i0 + first / TW_, j = j0 + first % TW_;
+        float ux, uy, uz;
+        beam(g, i, j, ux, uy, uz);
+        const float r0 = __uint_as_float(__ldg(rimg + (size_t)i * g.W + j));
+        ax = __fmul_rn(r0, ux);
+        ay = __fmul_rn(r0, uy);
+        az = __fmul_rn(r0, uz);
+    }
     RecOut o = read_rec(recs + t);
     {   // keep the run pre-test results when it ran first (they refer to other tiles' spatial planes)
         const uint4 *src = reinterpret_cast<const uint4 *>(recs + t);
@@ -594,21 +670,82 @@ __global__ void __launch_bounds__(kFitThreads) k_temporal(Geometry g, Scratch s,
         o.amask = src[2].y;
         o.acnt[0] = q3.x; o.acnt[1] = q3.y; o.acnt[2] = q3.z; o.acnt[3] = q3.w;
     }
-    RecOut ot = o;
-    ot.flags = 0;
-    temporal_test<TH_, TW_>(tv, ps.m[f], b.kf[f], ot);
-    if (ot.status == S_TEMPORAL) {
-        ot.rounds = 0;
-        write_rec(recs + t, ot);
-    } else if (ot.flags) {
-        o.kref = ot.kref;
-        o.tplane = ot.tplane;
-        o.t_rounds = ot.t_rounds;
-        o.t_inl = ot.t_inl;
-        o.t_status = ot.t_status;
-        o.flags |= ot.flags;
-        write_rec(recs + t, o);
+    // anchor in key-frame coordinates, key tile, rotated normal: the FP64 products of
+    // transform_point and rotate_normal (same operations, same order), one output coordinate
+    // per lane (GB300's FP64 rate is low), gathered by shuffles
+    const double *M = ps.m[f];
+    const int cl = l < 3 ? l : 2, g0 = lane - l;
+    float aK[3];
+    {
+        double tt = __dmul_rn(M[cl * 4 + 0], (double)ax);
+        tt = fma(M[cl * 4 + 1], (double)ay, tt);
+        tt = fma(M[cl * 4 + 2], (double)az, tt);
+        const float v = (float)__dadd_rn(tt, M[cl * 4 + 3]);
+#pragma unroll
+        for (int q = 0; q < 3; q++) aK[q] = __shfl_sync(gmask, v, g0 + q);
     }
+    float rK;
+    int pixK;
+    if (bin_point(g, aK[0], aK[1], aK[2], rK, pixK) != 0) return;
+    const int kti = (pixK / g.W / g.th) * g.TC + (pixK % g.W) / g.tw;
+    const float4 kp = __ldg(b.kf[f] + kti);
+    if (kp.x == 0.f && kp.y == 0.f && kp.z == 0.f) return;
+    float n[3];
+    {
+        double tt = __dmul_rn(M[0 * 4 + cl], (double)kp.x);
+        tt = fma(M[1 * 4 + cl], (double)kp.y, tt);
+        tt = fma(M[2 * 4 + cl], (double)kp.z, tt);
+        const float v = (float)tt;
+#pragma unroll
+        for (int q = 0; q < 3; q++) n[q] = __shfl_sync(gmask, v, g0 + q);
+    }
+    Mask S = V, I;
+    int nS = nv, nI = 0;
+    float c = 0.f;
+    bool border = false;
+    uint8_t t_rounds = 0;
+    for (;;) {
+        ff acc = {0.f, 0.f};
+#pragma unroll
+        for (int m = 0; m < PPL; m++)
+            if (S.get(l + L * m)) acc = ff_add(acc, dot_term(n, pr[m], pux[m], puy[m], puz[m]));
+#pragma unroll
+        for (int off = 1; off < L; off <<= 1) acc = ff_add(acc, shfl_xor_ff_m(gmask, acc, off));
+        c = ffm::mul({acc.hi, acc.lo}, ffm::rcp(ffm::mk((float)nS))).hi;   // mean of n'.p
+        t_rounds++;
+        const float4 pl = make_float4(n[0], n[1], n[2], c);
+        I.w0 = I.w1 = 0ull;
+#pragma unroll
+        for (int m = 0; m < PPL; m++)
+            if (pr[m] > 0.0f && inlier_screened(pl, pux[m], puy[m], puz[m], pr[m], g.thr, border)) I.set(l + L * m);
+#pragma unroll
+        for (int off = 1; off < L; off <<= 1) {
+            I.w0 |= __shfl_xor_sync(gmask, I.w0, off);
+            I.w1 |= __shfl_xor_sync(gmask, I.w1, off);
+        }
+        nI = __popcll(I.w0) + __popcll(I.w1);
+        if ((nI == nS && I == S) || t_rounds == g.R + 1 || nI < 3) break;
+        S = I;
+        nS = nI;
+    }
+    border = __any_sync(gmask, border);
+    if (l != 0) return;
+    o.kref = (uint32_t)kti;
+    const uint8_t tflags = (uint8_t)((border ? 1 : 0) | 4);
+    o.tplane = make_float4(n[0], n[1], n[2], c);
+    o.t_rounds = t_rounds;
+    o.t_inl = (uint8_t)nI;
+    o.t_status = (nv >= 3 && nI >= need_inliers(g.fmin, nv)) ? 2 : 1;
+    if (o.t_status == 2) {
+        o.status = S_TEMPORAL;
+        o.plane = o.tplane;
+        o.n_inl = (uint8_t)nI;
+        o.rounds = 0;
+        o.flags = tflags;
+    } else {
+        o.flags |= tflags;
+    }
+    write_rec(recs + t, o);
 }
 
 // Run pre-test, after every tile's own fit is final: tile t tests its own
@@ -738,7 +875,8 @@ static cudaError_t launch_fit_rounds_t(const Geometry &g, const Scratch &s, cons
 template <int TH_, int TW_>
 static cudaError_t launch_temporal_t(const Geometry &g, const Scratch &s, const Batch &b, const Poses &p,
                                      cudaStream_t st) {
-    k_temporal<TH_, TW_><<<dim3((g.NT + kFitThreads - 1) / kFitThreads, b.nframes), kFitThreads, 0, st>>>(g, s, b, p);
+    constexpr int TPB = kFitThreads / TLanes<TH_, TW_>::L;   // tiles per block
+    k_temporal<TH_, TW_><<<dim3((g.NT + TPB - 1) / TPB, b.nframes), kFitThreads, 0, st>>>(g, s, b, p);
     return cudaGetLastError();
 }
 

@@ -24,21 +24,26 @@ struct alignas(16) RowRec {
     uint8_t status, n_valid, n_inlier, rounds;
     uint32_t acnt[4];        // look-behind inlier counts (byte j)
     uint8_t flags, pad0, pad1, pad2;
+    uint32_t kref;           // key-frame tile (temporal tiles)
 };
+static_assert(sizeof(RowRec) == 48, "RowRec layout");
 
 // Byte offset of the staged row in the merge kernel's dynamic shared memory (after the row
 // records, the next-fitted / run-end / reach tables and the explicit-join counts).
 __host__ __device__ __forceinline__ size_t merge_stage_offset(int TC) {
-    const size_t raw = sizeof(RowRec) * (size_t)TC + 2 * (size_t)(TC + 1) + 4 * (size_t)TC + (size_t)TC + 16;
+    const size_t raw = sizeof(RowRec) * (size_t)TC + 2 * (size_t)(TC + 1) + 6 * (size_t)TC + (size_t)TC + 16;
     return (raw + 15) & ~size_t(15);
 }
 
 constexpr size_t kMergeStageMaxSmem = 200 * 1024;
 
 __device__ __forceinline__ void put_code(TileCode *codes, int t, uint8_t mode, int cand, int fitted, int raw,
-                                         uint32_t plane_tile) {
+                                         uint32_t plane_tile, uint32_t kref, float4 plane) {
     const uint32_t w0 = (uint32_t)mode | ((uint32_t)cand << 8) | ((uint32_t)fitted << 16) | ((uint32_t)raw << 24);
-    *reinterpret_cast<uint2 *>(codes + t) = make_uint2(w0, plane_tile);
+    uint4 *dst = reinterpret_cast<uint4 *>(codes + t);
+    dst[0] = make_uint4(w0, plane_tile, kref, 0u);
+    dst[1] = make_uint4(__float_as_uint(plane.x), __float_as_uint(plane.y), __float_as_uint(plane.z),
+                        __float_as_uint(plane.w));
 }
 
 __device__ __forceinline__ uint32_t warp_incl_sum(uint32_t x, int lane) {
@@ -53,14 +58,17 @@ __device__ __forceinline__ uint32_t warp_incl_sum(uint32_t x, int lane) {
 constexpr int kMergeThreads = 256;
 
 // One block per tile row (the row lives in dynamic shared memory).  Stages:
-// (A) all threads stage the row's fit records; (B) the next fitted tile at or
-// after every position (suffix scan, warp 0) and, for every fitted tile, how
-// far its run would reach by the followers' look-behind bits (all threads);
-// (C) all threads walk the greedy chain together: a run starts at the next
-// fitted tile, ends where its precomputed reach ends (past the look-behind
-// horizon, block-wide steps test one tile per thread), and the walk resumes
-// at the next fitted tile after it; (D) all threads assign codes and counts, then a block
-// scan gives the intra-row stream offsets and the row totals.
+// (A) all threads stage the row's fit records (and, for the staged variant,
+// the row's ranges and ray directions, loaded up front so that their latency
+// overlaps the rest); (B) the next fitted tile at or after every position
+// (suffix scan, warp 0), for every fitted tile how far its run would reach by
+// the followers' look-behind bits (all threads, branch-free), and where the
+// walk goes next from it when that run ends inside the look-behind horizon;
+// (C) all threads walk the greedy chain together: one shared-memory load per
+// run that ends inside the horizon; past it, block-wide steps test one tile
+// per kEL lanes against the run's plane; (D) all threads assign codes and
+// counts, then a block scan gives the intra-row stream offsets and the row
+// totals.
 template <int TH_, int TW_, bool kStage>
 __global__ void __launch_bounds__(kMergeThreads) k_merge(Geometry g, Scratch s, Batch b) {
     extern __shared__ __align__(16) uint8_t smem[];
@@ -72,7 +80,8 @@ __global__ void __launch_bounds__(kMergeThreads) k_merge(Geometry g, Scratch s, 
     uint16_t *nextfit = reinterpret_cast<uint16_t *>(row + TC);   // TC + 1 entries
     uint16_t *runend = nextfit + (TC + 1);                         // end of the run started at c, 0 if none
     uint16_t *reach = runend + TC;                                 // look-behind reach of a fitted tile
-    uint8_t *extcnt = reinterpret_cast<uint8_t *>(reach + TC);     // counts of explicitly tested joins
+    uint16_t *jmp = reach + TC;                                    // walk successor of a fitted tile (below)
+    uint8_t *extcnt = reinterpret_cast<uint8_t *>(jmp + TC);       // counts of explicitly tested joins
     // staged tile row for extension steps (kStage): range bits per tile (stride PX + 1), the
     // row's column directions and its TH_ row directions
     uint32_t *s_r = reinterpret_cast<uint32_t *>(smem + merge_stage_offset(TC));
@@ -95,6 +104,52 @@ __global__ void __launch_bounds__(kMergeThreads) k_merge(Geometry g, Scratch s, 
     const int row0 = tr * TC;
     const int hzmax = g.merge ? g.lookahead : 0;
 
+    if (kStage) {
+        // the tile row's ranges, per tile in raster order (stride PX + 1), and its ray directions;
+        // 16-byte loads, eight in flight per thread, when image rows are whole 16-byte groups
+        const int rowpx = TC * TW_;   // TW_ is a multiple of 4
+        if ((g.W & 3) == 0) {
+            const int q4 = rowpx / 4, nvec = TH_ * q4;
+            constexpr int U = 8;
+            for (int v0 = tid; v0 < nvec; v0 += kMergeThreads * U) {
+                uint4 q[U];
+#pragma unroll
+                for (int u = 0; u < U; u++) {
+                    const int v = v0 + u * kMergeThreads;
+                    q[u] = make_uint4(kEmptyBits, kEmptyBits, kEmptyBits, kEmptyBits);
+                    if (v < nvec) {
+                        const int i = tr * TH_ + v / q4, jj = (v % q4) * 4;
+                        if (i < g.H && jj < g.W) q[u] = __ldg(reinterpret_cast<const uint4 *>(rimg + (size_t)i * g.W + jj));
+                    }
+                }
+#pragma unroll
+                for (int u = 0; u < U; u++) {
+                    const int v = v0 + u * kMergeThreads;
+                    if (v < nvec) {
+                        const int ii = v / q4, jj = (v % q4) * 4;
+                        uint32_t *d = s_r + (jj / TW_) * (PX + 1) + ii * TW_ + jj % TW_;
+                        d[0] = q[u].x; d[1] = q[u].y; d[2] = q[u].z; d[3] = q[u].w;
+                    }
+                }
+            }
+        } else {
+            for (int idx = tid; idx < TH_ * rowpx; idx += kMergeThreads) {
+                const int ii = idx / rowpx, jj = idx % rowpx;
+                const int i = tr * TH_ + ii;
+                s_r[(jj / TW_) * (PX + 1) + ii * TW_ + jj % TW_] =
+                    (i < g.H && jj < g.W) ? __ldg(rimg + (size_t)i * g.W + jj) : kEmptyBits;
+            }
+        }
+        for (int jj = tid; jj < rowpx; jj += kMergeThreads) {
+            s_ct[jj] = jj < g.W ? __ldg(g.ct + jj) : 0.f;
+            s_st[jj] = jj < g.W ? __ldg(g.st + jj) : 0.f;
+        }
+        if (tid < TH_) {
+            const int i = tr * TH_ + tid;
+            s_ce[tid] = i < g.H ? __ldg(g.ce + i) : 0.f;
+            s_se[tid] = i < g.H ? __ldg(g.se + i) : 0.f;
+        }
+    }
     // (A) stage the row's records (coalesced 16-byte loads)
     for (int c = tid; c < TC; c += kMergeThreads) {
         const uint4 *src = reinterpret_cast<const uint4 *>(recs + row0 + c);
@@ -108,6 +163,7 @@ __global__ void __launch_bounds__(kMergeThreads) k_merge(Geometry g, Scratch s, 
         h.n_valid = (uint8_t)(q2.z >> 24);
         h.n_inlier = (uint8_t)(q2.w & 0xff);
         h.pad0 = h.pad1 = h.pad2 = 0;
+        h.kref = q2.x;
         h.acnt[0] = q3.x; h.acnt[1] = q3.y; h.acnt[2] = q3.z; h.acnt[3] = q3.w;
         row[c] = h;
         runend[c] = 0;
@@ -115,16 +171,22 @@ __global__ void __launch_bounds__(kMergeThreads) k_merge(Geometry g, Scratch s, 
     }
     if (tid < 6) s_carry[tid] = 0;
     __syncthreads();
-    // (B) reach of every fitted tile; next fitted tile at or after c
+    // (B) reach of every fitted tile: 1 + the number of its followers, from the next one on,
+    // whose look-behind bit for it is set (and that are not temporal); next fitted tile at or
+    // after c
     for (int c = tid; c < TC; c += kMergeThreads) {
         int k = c + 1;
         if (row[c].status == S_FIT) {
             const int hz = min(hzmax, TC - 1 - c);
-            for (int j = 0; j < hz; j++) {
-                const RowRec &h1 = row[c + 1 + j];
-                if (!((h1.amask >> j) & 1u) || h1.status == S_TEMPORAL) break;
-                k++;
+            uint32_t m = 0u;
+#pragma unroll 8
+            for (int j = 0; j < 32; j++) {
+                if (j < hz) {
+                    const RowRec &h1 = row[c + 1 + j];
+                    if (((h1.amask >> j) & 1u) && h1.status != S_TEMPORAL) m |= 1u << j;
+                }
             }
+            k += (m == 0xFFFFFFFFu) ? 32 : __ffs(~m) - 1;   // consecutive joins from j = 0
         }
         reach[c] = (uint16_t)k;
     }
@@ -145,37 +207,33 @@ __global__ void __launch_bounds__(kMergeThreads) k_merge(Geometry g, Scratch s, 
         }
     }
     __syncthreads();
+    // walk successor of every fitted tile c: where the walk goes after a run started at c that
+    // ends inside the look-behind horizon (the next fitted tile at or after its reach, TC at the
+    // row end), or the reach itself with bit 15 set when the run reaches past the horizon and
+    // must be extended by explicit tests (TC < 32768: the row records fit in shared memory)
+    for (int c = tid; c < TC; c += kMergeThreads) {
+        if (row[c].status != S_FIT) continue;
+        const int k = reach[c];
+        const bool open = g.merge && k < TC && k - c - 1 >= hzmax;
+        jmp[c] = open ? (uint16_t)(0x8000 | k) : (uint16_t)(k < TC ? nextfit[k] : TC);
+    }
+    __syncthreads();
     // (C) the greedy walk.  Every thread follows the same chain (uniform values read from
     // shared memory); past the look-behind horizon the whole block tests the next kStepTiles
-    // tiles against the run's plane in one step, kEL lanes per tile.  The first such step of
-    // a row stages the row's ranges and ray directions in shared memory (kStage).
+    // tiles against the run's plane in one step, kEL lanes per tile.
     {
         __shared__ uint32_t s_fail[kMergeThreads / 32];
-        bool staged = false;
         int st = nextfit[0];
         while (st < TC) {
-            int k = reach[st];
-            bool open = g.merge && k < TC && k - st - 1 >= hzmax;
-            if (open) {
-                if (kStage && !staged) {
-                    for (int idx = tid; idx < TH_ * TC * TW_; idx += kMergeThreads) {
-                        const int ii = idx / (TC * TW_), jj = idx % (TC * TW_);
-                        const int i = tr * TH_ + ii;
-                        const uint32_t bits = (i < g.H && jj < g.W) ? __ldg(rimg + (size_t)i * g.W + jj) : kEmptyBits;
-                        s_r[(jj / TW_) * (PX + 1) + ii * TW_ + jj % TW_] = bits;
-                        if (ii == 0) {
-                            s_ct[jj] = jj < g.W ? __ldg(g.ct + jj) : 0.f;
-                            s_st[jj] = jj < g.W ? __ldg(g.st + jj) : 0.f;
-                        }
-                    }
-                    if (tid < TH_) {
-                        const int i = tr * TH_ + tid;
-                        s_ce[tid] = i < g.H ? __ldg(g.ce + i) : 0.f;
-                        s_se[tid] = i < g.H ? __ldg(g.se + i) : 0.f;
-                    }
-                    __syncthreads();
-                    staged = true;
-                }
+            const uint32_t jv = jmp[st];
+            if (!(jv & 0x8000u)) {
+                if (tid == 0) runend[st] = reach[st];
+                st = (int)jv;
+                continue;
+            }
+            int k = (int)(jv & 0x7FFFu);
+            bool open = true;
+            {
                 const float4 pl = row[st].plane;
                 while (open) {
                     const int c2 = k + tid / kEL, l = tid % kEL;
@@ -272,9 +330,10 @@ __global__ void __launch_bounds__(kMergeThreads) k_merge(Geometry g, Scratch s, 
                 raw = h.n_valid;
             }
             if (mode >= T_RUN_START) raw = cand - fit;
-            put_code(codes, row0 + c, mode, (int)cand, (int)fit, (int)raw, ptile);
-            if (kfo) kfo[row0 + c] = (mode == T_RUN_START || mode == T_RUN_CONT) ? row[stc].plane
-                                                                                : make_float4(0.f, 0.f, 0.f, 0.f);
+            const float4 cpl = (mode == T_RUN_START || mode == T_RUN_CONT) ? row[stc].plane
+                               : (mode == T_TEMPORAL ? h.plane : make_float4(0.f, 0.f, 0.f, 0.f));
+            put_code(codes, row0 + c, mode, (int)cand, (int)fit, (int)raw, ptile, h.kref, cpl);
+            if (kfo) kfo[row0 + c] = mode == T_TEMPORAL ? make_float4(0.f, 0.f, 0.f, 0.f) : cpl;
             v[0] = cand; v[1] = fit; v[2] = raw; v[3] = isstart; v[4] = mode == T_TEMPORAL; v[5] = h.n_valid;
             hist[mode]++;
             rhist[min((uint32_t)h.rounds, 7u)]++;

@@ -74,27 +74,32 @@ __global__ void __launch_bounds__(kPackWarps * 32) k_pack(Geometry g, Scratch s,
     const bool tile_ok = t < g.NT;
     const int tr = tile_ok ? t / g.TC : 0, tc = tile_ok ? t % g.TC : 0;
     uint32_t *rimg = s.rimg + slot * g.H * g.W;
-    const TileRec *recs = s.tiles + slot * g.NT;
     const uint32_t segmask = (LPT == 32) ? FULL : (((1u << LPT) - 1u) << (seg * LPT));
     const uint32_t below = segmask & ((1u << lane) - 1u);
 
+    // every load of the tile is independent of the others: one round trip
+    const FrameLayout L = s.layout[slot];
     uint8_t mode = T_EMPTY;
     TileOff off = {0, 0, 0, 0, 0, 0, 0, 0};
     float4 pl = make_float4(0.f, 0.f, 0.f, 0.f);
-    uint32_t plane_tile = 0, want_cand = 0, want_fit = 0, want_raw = 0;
+    uint32_t kref = 0, want_cand = 0, want_fit = 0, want_raw = 0;
     if (tile_ok) {
-        const uint2 c = *reinterpret_cast<const uint2 *>(s.codes + slot * g.NT + t);
+        const uint4 *cp = reinterpret_cast<const uint4 *>(s.codes + slot * g.NT + t);
+        const uint4 c = cp[0], cpl = cp[1];
         mode = (uint8_t)(c.x & 0xff);
         want_cand = (c.x >> 8) & 0xff;
         want_fit = (c.x >> 16) & 0xff;
         want_raw = c.x >> 24;
-        plane_tile = c.y < (uint32_t)g.NT ? c.y : 0u;
+        kref = c.z;
         const uint4 o0 = *reinterpret_cast<const uint4 *>(s.offs + slot * g.NT + t);
         const uint4 o1 = *(reinterpret_cast<const uint4 *>(s.offs + slot * g.NT + t) + 1);
-        const uint32_t *rb = s.rowbase + (slot * g.TR + tr) * 8;   // the tile row's base offsets
-        off.cand = o0.x + rb[0]; off.fitted = o0.y + rb[1]; off.raw = o0.z + rb[2]; off.run = o0.w + rb[3];
-        off.temporal = o1.x + rb[4];
-        if (mode >= T_RUN_START) pl = recs[plane_tile].plane;
+        const uint4 *rb = reinterpret_cast<const uint4 *>(s.rowbase + (slot * g.TR + tr) * 8);   // row base offsets
+        const uint4 rb0 = rb[0], rb1 = rb[1];
+        off.cand = o0.x + rb0.x; off.fitted = o0.y + rb0.y; off.raw = o0.z + rb0.z; off.run = o0.w + rb0.w;
+        off.temporal = o1.x + rb1.x;
+        if (mode >= T_RUN_START)
+            pl = make_float4(__uint_as_float(cpl.x), __uint_as_float(cpl.y), __uint_as_float(cpl.z),
+                             __uint_as_float(cpl.w));
     }
     const bool coded = mode >= T_RUN_START;
 
@@ -124,7 +129,6 @@ __global__ void __launch_bounds__(kPackWarps * 32) k_pack(Geometry g, Scratch s,
             else mc[m] = quant_raw(r, g.q);
         }
     }
-    const FrameLayout L = s.layout[slot];
     if (!L.ok) return;
     uint32_t *words = reinterpret_cast<uint32_t *>(b.out[f] + kHeaderBytes);
 
@@ -179,7 +183,7 @@ __global__ void __launch_bounds__(kPackWarps * 32) k_pack(Geometry g, Scratch s,
         }
         if (mode == T_TEMPORAL) {
             uint32_t *d = words + L.sec[3] + 2u * off.temporal;
-            d[0] = recs[t].kref;
+            d[0] = kref;
             d[1] = __float_as_uint(pl.w);
         }
     }

@@ -59,11 +59,16 @@ struct alignas(16) TileRec {
 static_assert(sizeof(TileRec) == 64, "TileRec layout");
 static_assert(sizeof(TileRec) == sizeof(lcc_tile_info), "TileRec matches lcc_tile_info");
 
-// Output of the run merge: how the tile is coded and its stream counts.
-struct TileCode {
+// Output of the run merge: how the tile is coded, its stream counts and everything the
+// packer needs about its plane, so that the packer's loads do not depend on one another.
+struct alignas(16) TileCode {
     uint8_t mode, cand, fitted, raw;
     uint32_t plane_tile;  // tile whose plane codes this one (run start)
+    uint32_t kref;        // key-frame tile of a temporal tile
+    uint32_t pad;
+    float4 plane;         // coding plane: the run's plane, or (n', c') of a temporal tile
 };
+static_assert(sizeof(TileCode) == 32, "TileCode layout");
 
 // Exclusive stream offsets of a tile (in codes) within its tile row.
 struct TileOff {
@@ -312,6 +317,10 @@ __device__ __forceinline__ double ff_to_d(ff a) { return (double)a.hi + (double)
 
 __device__ __forceinline__ ff shfl_xor_ff(ff v, int off) {
     return {__shfl_xor_sync(0xffffffffu, v.hi, off), __shfl_xor_sync(0xffffffffu, v.lo, off)};
+}
+
+__device__ __forceinline__ ff shfl_xor_ff_m(unsigned mask, ff v, int off) {
+    return {__shfl_xor_sync(mask, v.hi, off), __shfl_xor_sync(mask, v.lo, off)};
 }
 
 // Read `width` bits (<= 25) at bit position pos from little-endian words.
