@@ -307,9 +307,9 @@ lcc_status lcc_create(lcc_ctx **out, const lcc_sensor *sensor, const lcc_params 
     g.w_res = bits_for(2 * g.k_max);
     const int m_max = (int)floorf((float)s.max_range_m / p.quant_m + 0.5f) + 1;
     g.w_raw = bits_for(m_max);
-    g.elev_max_deg = (float)s.elev_max_deg;
-    g.d_el_deg = (float)((s.elev_max_deg - s.elev_min_deg) / s.rows);
-    g.d_az = (float)(2.0 * M_PI / s.cols);
+    g.elev_max_rad = (float)(s.elev_max_deg * (M_PI / 180.0));
+    g.inv_d_el = (float)(s.rows / ((s.elev_max_deg - s.elev_min_deg) * (M_PI / 180.0)));
+    g.inv_d_az = (float)(s.cols / (2.0 * M_PI));
     // the run walker keeps one tile row in shared memory
     if (g.w_res > 16 || g.w_raw > 24 || merge_smem_bytes(g.TC) > 200 * 1024 || g.TC > 65535) {
         delete c;

@@ -111,7 +111,7 @@ struct Geometry {
     int schedule;        // 0 per-thread fit rounds; 1, 2: that many rounds per thread, the rest queued
     int first_rounds;    // fit rounds of the first pass under a queued schedule
     int k_max, w_res, w_raw;
-    float elev_max_deg, d_el_deg, d_az;   // first guesses only; the tables decide
+    float elev_max_rad, inv_d_el, inv_d_az;   // first guesses only (1/row and 1/column pitch, rad); the tables decide
     const float *ce, *se, *ct, *st;       // beam tables
     const float *rbc, *rbs, *cbc, *cbs;   // boundary tables
 };
@@ -226,9 +226,28 @@ __device__ __forceinline__ float col_side(const Geometry &g, int j, float x, flo
     return fmaf(y, __ldg(g.cbc + j), -__fmul_rn(x, __ldg(g.cbs + j)));
 }
 
+// Starting guess of atan(a) for a in [0, 1]: an odd polynomial of degree 7 whose
+// coefficients were fitted to atan on [0, 1] by iteratively reweighted least squares
+// (maximum error 8.2e-5 rad).  It only picks where the boundary walks below start.
+__device__ __forceinline__ float atan01_guess(float a) {
+    const float a2 = __fmul_rn(a, a);
+    return __fmul_rn(a, fmaf(fmaf(fmaf(-0.03898929f, a2, 0.14626859f), a2, -0.32117667f), a2, 0.99921398f));
+}
+
+// Starting guess of atan2(y, x) in [-pi, pi] (octant reduction of atan01_guess).
+__device__ __forceinline__ float atan2_guess(float y, float x) {
+    const float ax = fabsf(x), ay = fabsf(y);
+    const float mx = fmaxf(ax, ay), mn = fminf(ax, ay);
+    float t = mx > 0.0f ? atan01_guess(__fdividef(mn, mx)) : 0.0f;
+    if (ay > ax) t = 1.5707963f - t;
+    if (x < 0.0f) t = 3.1415927f - t;
+    return y < 0.0f ? -t : t;
+}
+
 // Eq. 1-2 for one point: 0 binned (r, pix set), 1 invalid, 2 out of FOV.
-// The pixel is the unique one whose boundary sign tests hold; atan2f only
-// gives the starting guess of a bounded walk.
+// The pixel is the unique one whose boundary sign tests hold (the signs are
+// monotone along the rows and around the columns, so the result does not
+// depend on the starting guess, which only sets how many steps the walks take).
 __device__ __forceinline__ int bin_point(const Geometry &g, float x, float y, float z, float &r, int &pix) {
     if (!isfinite(x) || !isfinite(y) || !isfinite(z)) return 1;
     r = sqrtf(fmaf(x, x, fmaf(y, y, __fmul_rn(z, z))));
@@ -236,19 +255,37 @@ __device__ __forceinline__ int bin_point(const Geometry &g, float x, float y, fl
     const float rho = sqrtf(fmaf(x, x, __fmul_rn(y, y)));
     if (row_side(g, 0, z, rho) > 0.0f) return 2;
     if (!(row_side(g, g.H, z, rho) > 0.0f)) return 2;
-    const float el = atan2f(z, rho) * 57.29577951308232f;
-    int i = (int)floorf((g.elev_max_deg - el) / g.d_el_deg);
+    int i = (int)floorf(__fmul_rn(g.elev_max_rad - atan2_guess(z, rho), g.inv_d_el));
     i = min(max(i, 0), g.H - 1);
-    for (int it = 0; it < g.H && i > 0 && row_side(g, i, z, rho) > 0.0f; it++) i--;
-    for (int it = 0; it < g.H && i < g.H - 1 && !(row_side(g, i + 1, z, rho) > 0.0f); it++) i++;
-    if (row_side(g, i, z, rho) > 0.0f || !(row_side(g, i + 1, z, rho) > 0.0f)) return 2;
-    const float az = atan2f(y, x);
-    int j = (int)floorf((az + 3.14159265358979f) / g.d_az);
-    j = ((j % g.W) + g.W) % g.W;
-    for (int it = 0; it < g.W && !(col_side(g, j, x, y) >= 0.0f); it++) j = (j == 0) ? g.W - 1 : j - 1;
-    for (int it = 0; it < g.W && col_side(g, (j + 1 == g.W) ? 0 : j + 1, x, y) >= 0.0f; it++)
+    // row i: !(side(i) > 0) and side(i + 1) > 0
+    float lo = row_side(g, i, z, rho), hi = row_side(g, i + 1, z, rho);
+    for (int it = 0; it < g.H && i > 0 && lo > 0.0f; it++) {
+        i--;
+        hi = lo;
+        lo = row_side(g, i, z, rho);
+    }
+    for (int it = 0; it < g.H && i < g.H - 1 && !(hi > 0.0f); it++) {
+        i++;
+        lo = hi;
+        hi = row_side(g, i + 1, z, rho);
+    }
+    if (lo > 0.0f || !(hi > 0.0f)) return 2;
+    int j = (int)floorf(__fmul_rn(atan2_guess(y, x) + 3.1415927f, g.inv_d_az));
+    j = j < 0 ? j + g.W : (j >= g.W ? j - g.W : j);
+    j = min(max(j, 0), g.W - 1);
+    // column j: side(j) >= 0 and !(side(j + 1) >= 0), indices modulo W
+    float cl = col_side(g, j, x, y), ch = col_side(g, (j + 1 == g.W) ? 0 : j + 1, x, y);
+    for (int it = 0; it < g.W && !(cl >= 0.0f); it++) {
+        j = (j == 0) ? g.W - 1 : j - 1;
+        ch = cl;
+        cl = col_side(g, j, x, y);
+    }
+    for (int it = 0; it < g.W && ch >= 0.0f; it++) {
         j = (j + 1 == g.W) ? 0 : j + 1;
-    if (!(col_side(g, j, x, y) >= 0.0f) || col_side(g, (j + 1 == g.W) ? 0 : j + 1, x, y) >= 0.0f) return 2;
+        cl = ch;
+        ch = col_side(g, (j + 1 == g.W) ? 0 : j + 1, x, y);
+    }
+    if (!(cl >= 0.0f) || ch >= 0.0f) return 2;
     pix = i * g.W + j;
     return 0;
 }

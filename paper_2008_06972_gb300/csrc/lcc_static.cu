@@ -106,9 +106,9 @@ extern "C" lcc_status lcc_range_image_static(const lcc_sensor *sensor, const flo
     g.H = H;
     g.W = W;
     g.rmax = (float)s.max_range_m;
-    g.elev_max_deg = (float)s.elev_max_deg;
-    g.d_el_deg = (float)((s.elev_max_deg - s.elev_min_deg) / s.rows);
-    g.d_az = (float)(2.0 * M_PI / s.cols);
+    g.elev_max_rad = (float)(s.elev_max_deg * (M_PI / 180.0));
+    g.inv_d_el = (float)(s.rows / ((s.elev_max_deg - s.elev_min_deg) * (M_PI / 180.0)));
+    g.inv_d_az = (float)(s.cols / (2.0 * M_PI));
     g.rbc = tab;
     g.rbs = tab + (H + 1);
     g.cbc = tab + 2 * (H + 1);
