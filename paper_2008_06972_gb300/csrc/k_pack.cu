@@ -18,10 +18,12 @@ namespace lcc {
 constexpr int kPackWarps = 8;
 constexpr int kStageWords = 128;   // shared staging words per warp
 
+// Lanes per tile: half the tile's pixels up to a warp, so every lane codes at least two
+// pixels whose loads are in flight together (and the launch has half the warps).
 template <int TH_, int TW_>
 struct PShape {
     static constexpr int PX = TH_ * TW_;
-    static constexpr int LPT = PX < 32 ? PX : 32;
+    static constexpr int LPT = PX / 2 < 32 ? PX / 2 : 32;
     static constexpr int PPL = PX / LPT;
     static constexpr int TPW = 32 / LPT;
     static constexpr int SW = kStageWords / TPW;   // staging words per segment
