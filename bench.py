@@ -113,9 +113,8 @@ def oracle_all_cores(seq, th, tw, thr, seconds):
     return pts * nseq / wall / 1e6, nseq, wall, cores
 
 
-KERNEL_SOURCES = {"bin": "k_bin.cu", "fit": "k_fit.cu", "refit": "k_fit.cu", "temporal": "k_fit.cu",
-                  "merge": "k_merge.cu",
-                  "scan": "k_scan.cu", "pack": "k_pack.cu"}
+KERNEL_SOURCES = {"bin": ("k_bin.cu",), "fit": ("k_fit.cu",), "refit": ("k_fit.cu",), "temporal": ("k_fit.cu",),
+                  "merge": ("k_merge.cu", "scan_frame.cuh"), "pack": ("k_pack.cu",)}
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "dram_traffic_hdl64_sequence.txt")
 
 
@@ -124,7 +123,7 @@ def source_digest(kernel: str) -> str:
     import hashlib
     csrc = os.path.join(ROOT, "paper_2008_06972_gb300", "csrc")
     h = hashlib.sha256()
-    for name in (KERNEL_SOURCES[kernel], "lcc_internal.cuh", "ffmath.cuh"):
+    for name in KERNEL_SOURCES[kernel] + ("lcc_internal.cuh", "ffmath.cuh"):
         with open(os.path.join(csrc, name), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -664,8 +663,8 @@ def main():
     # algorithmic bytes per launch (per-unit figures):
     #   bin:   16 B per input point (float4 read) + 4 B per point atomic into the range image
     #   fit:   4 B per pixel (range image read) + 64 B per tile record written
-    #   merge: 64 B per tile record read + 8 B per tile code written
-    #   scan:  8 B per tile code read + 32 B per tile offset written + stream bytes zeroed
+    #   merge: 64 B per tile record read + 32 B tile code and 32 B tile offsets written per tile
+    #          + the stream bytes zeroed by the frame's layout step
     #   pack:  4 B per pixel read + 4 B per pixel reset + stream bytes written
     #   temporal: (P frames) 4 B per pixel + 64 B per tile record read and written
     #   refit: 4 B per pixel (range image read) + 64 B per tile record read + 32 B per tile of
@@ -677,8 +676,7 @@ def main():
         "fit": n_frames * (4.0 * npx + 64.0 * nt),
         "refit": n_frames * (4.0 * npx + 96.0 * nt),
         "temporal": (n_frames - 1) * (4.0 * npx + 128.0 * nt),
-        "merge": n_frames * (64.0 * nt + 8.0 * nt),
-        "scan": n_frames * (8.0 * nt + 32.0 * nt) + total_bytes,
+        "merge": n_frames * (64.0 * nt + 32.0 * nt + 32.0 * nt) + total_bytes,
         "pack": n_frames * 8.0 * npx + total_bytes,
     }
     launches_of = {k: v[0] / args.steps for k, v in ktimes.items()}

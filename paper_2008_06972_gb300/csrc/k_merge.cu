@@ -13,6 +13,7 @@
 // of candidate / plane-coded / raw-coded pixels and their offsets within the
 // tile row; per row: the totals.
 #include "lcc_internal.cuh"
+#include "scan_frame.cuh"
 
 namespace lcc {
 
@@ -68,7 +69,8 @@ constexpr int kMergeThreads = 256;
 // run that ends inside the horizon; past it, block-wide steps test one tile
 // per kEL lanes against the run's plane; (D) all threads assign codes and
 // counts, then a block scan gives the intra-row stream offsets and the row
-// totals.
+// totals; (E) the last block of a frame to finish lays out the frame's
+// stream from the row totals (scan_frame).
 template <int TH_, int TW_, bool kStage>
 __global__ void __launch_bounds__(kMergeThreads) k_merge(Geometry g, Scratch s, Batch b) {
     extern __shared__ __align__(16) uint8_t smem[];
@@ -387,6 +389,17 @@ __global__ void __launch_bounds__(kMergeThreads) k_merge(Geometry g, Scratch s, 
         for (int q = 0; q < 8; q++)
             if (rhist[q]) atomicAdd(&stt->rounds[q], (unsigned long long)rhist[q]);
         if (border) atomicAdd(&stt->borderline, (unsigned long long)border);
+    }
+    // (E) the last tile row of the frame to finish (the classic fence + counter pattern)
+    __shared__ int s_lastrow;
+    __threadfence();
+    __syncthreads();
+    if (tid == 0) s_lastrow = atomicAdd(s.rowdone + slot, 1u) == (unsigned)g.TR - 1u;
+    __syncthreads();
+    if (s_lastrow) {
+        __threadfence();
+        scan_frame<kMergeThreads>(g, s, b, f);
+        if (tid == 0) s.rowdone[slot] = 0u;   // ready for the next frame in this slot
     }
 }
 

@@ -146,7 +146,7 @@ void prepare_batch(Batch &b, Poses &p, int kind, int nframes, const int *slots, 
 }
 
 // Everything after the first fit pass: further rounds (unless already run) and the run
-// pre-test, merge, scan, pack.
+// pre-test, merge (which also lays out each frame's stream), pack.
 lcc_status encode_tail(lcc_ctx *c, const Batch &b, bool rounds_done = false) {
     if (rounds_done) {
         LCC_LAUNCH(c, 8, launch_lookbehind(c->g, c->s, b, c->stream));
@@ -154,7 +154,6 @@ lcc_status encode_tail(lcc_ctx *c, const Batch &b, bool rounds_done = false) {
         LCC_LAUNCH(c, 8, launch_fit_rounds(c->g, c->s, b, c->stream));
     }
     LCC_LAUNCH(c, 2, launch_merge(c->g, c->s, b, c->stream));
-    LCC_LAUNCH(c, 3, launch_scan(c->g, c->s, b, c->stream));
     LCC_LAUNCH(c, 4, launch_pack(c->g, c->s, b, c->stream));
     return LCC_OK;
 }
@@ -348,7 +347,8 @@ lcc_status lcc_create(lcc_ctx **out, const lcc_sensor *sensor, const lcc_params 
     const size_t o_rowbase = o_rowtot + align256(sl * (size_t)g.TR * 32);
     const size_t o_queue = o_rowbase + align256(sl * (size_t)g.TR * 32);
     const size_t o_qcount = o_queue + align256(4 * sl * nt * 4);
-    const size_t total = o_qcount + 256;
+    const size_t o_rowdone = o_qcount + 256;
+    const size_t total = o_rowdone + align256(sl * 4);
     if (cudaMalloc(&c->d_scratch, total) != cudaSuccess) {
         cudaFree(c->d_tables);
         delete c;
@@ -369,6 +369,7 @@ lcc_status lcc_create(lcc_ctx **out, const lcc_sensor *sensor, const lcc_params 
     c->s.rowbase = (uint32_t *)(base + o_rowbase);
     c->s.queue = (uint32_t *)(base + o_queue);
     c->s.qcount = (uint32_t *)(base + o_qcount);
+    c->s.rowdone = (uint32_t *)(base + o_rowdone);
     c->s.qcap = (uint32_t)(sl * nt);
     cudaMemset(c->d_scratch, 0, total);
     cudaMemset(c->s.rimg, 0xFF, sl * npx * 4);
@@ -610,13 +611,13 @@ lcc_status encode_sequence(lcc_ctx *c, int32_t nframes, int32_t key_index, const
         if ((st = encode_batch(c, 0, 1, &kslot, &kout, &kcap, nullptr, nullptr, &kfo)) != LCC_OK) return st;
         if ((st = encode_batch(c, 1, np, pslots, pout, pcap, pposes.data(), kfi, nullptr)) != LCC_OK) return st;
     } else {
-        // The key frame's chain (binning, fit, run pre-test, merge, scan, pack) runs on a private
+        // The key frame's chain (binning, fit, run pre-test, merge, pack) runs on a private
         // stream of the highest priority, issued first, so that its blocks are dispatched ahead of
         // the P frames' whenever both wait for room on the SMs.  The P frames' binning, spatial fits
         // and run pre-test do not need the key frame and run on the side stream beside it.  Their
         // temporal test needs the key frame's coding planes, which its merge writes: the P frames'
-        // temporal test, merge, scan and pack follow on the side stream while the key frame's scan
-        // and pack finish.  The calling stream then waits for both.
+        // temporal test, merge and pack follow on the side stream while the key frame's pack
+        // finishes.  The calling stream then waits for both.
         Batch bk, bp;
         Poses pk, pp;
         prepare_batch(bk, pk, 0, 1, &kslot, &kout, &kcap, nullptr, nullptr, &kfo, nullptr);
@@ -650,21 +651,19 @@ lcc_status encode_sequence(lcc_ctx *c, int32_t nframes, int32_t key_index, const
         LCC_LAUNCH(c, 1, launch_fit(c->g, c->s, bp, pp, c->stream));
         if (c->g.schedule >= 1) LCC_LAUNCH(c, 8, launch_queued_rounds(c->g, c->s, bp, c->stream));
         LCC_LAUNCH(c, 8, launch_lookbehind(c->g, c->s, bp, c->stream));
-        // key frame: the rest of its rounds and its pre-test, merge (its coding planes), scan, pack
+        // key frame: the rest of its rounds and its pre-test, merge (its coding planes), pack
         c->stream = c->kstream;
         LCC_LAUNCH(c, 8, launch_fit_rounds(c->g, c->s, bk, c->stream));
-        LCC_LAUNCH(c, 2, launch_merge(c->g, c->s, bk, c->stream));
+        LCC_LAUNCH(c, 2, launch_merge(c->g, c->s, bk, c->stream));   // with the frame's stream layout
         LCC_CUDA(cudaEventRecord(c->ev_kplanes, c->kstream));
-        LCC_LAUNCH(c, 3, launch_scan(c->g, c->s, bk, c->stream));
         LCC_LAUNCH(c, 4, launch_pack(c->g, c->s, bk, c->stream));
         LCC_CUDA(cudaEventRecord(c->ev_kdone, c->kstream));
-        // P frames: temporal test against the key planes, merge, scan, pack
+        // P frames: temporal test against the key planes, merge, pack
         c->stream = c->side;
         LCC_CUDA(cudaStreamWaitEvent(c->side, c->ev_kplanes, 0));
         for (int f = 0; f < np; f++) bp.kf[f] = k->planes;
         LCC_LAUNCH(c, 9, launch_temporal(c->g, c->s, bp, pp, c->stream));
         LCC_LAUNCH(c, 2, launch_merge(c->g, c->s, bp, c->stream));
-        LCC_LAUNCH(c, 3, launch_scan(c->g, c->s, bp, c->stream));
         LCC_LAUNCH(c, 4, launch_pack(c->g, c->s, bp, c->stream));
         LCC_CUDA(cudaEventRecord(c->ev_join, c->side));
         LCC_CUDA(cudaStreamWaitEvent(main, c->ev_kdone, 0));

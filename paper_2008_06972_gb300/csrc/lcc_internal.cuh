@@ -131,6 +131,7 @@ struct Scratch {
     uint32_t *rowbase;   // [slots][TR][8] exclusive prefix of rowtot over the frame's rows
     uint32_t *queue;     // [2 sets][2][qcap] fit work queues (frame << 26 | tile)
     uint32_t *qcount;    // [2 sets][8] items pushed per fit round
+    uint32_t *rowdone;   // [slots] tile rows of the frame merged so far (0 between launches)
     uint32_t qcap;       // entries per queue (slots * tiles)
 };
 
@@ -384,7 +385,6 @@ cudaError_t launch_lookbehind(const Geometry &g, const Scratch &s, const Batch &
 cudaError_t launch_queued_rounds(const Geometry &g, const Scratch &s, const Batch &b, cudaStream_t st);
 cudaError_t launch_merge(const Geometry &g, const Scratch &s, const Batch &b, cudaStream_t st);
 size_t merge_smem_bytes(int TC);
-cudaError_t launch_scan(const Geometry &g, const Scratch &s, const Batch &b, cudaStream_t st);
 cudaError_t launch_pack(const Geometry &g, const Scratch &s, const Batch &b, cudaStream_t st);
 cudaError_t launch_decode_prep(const Geometry &g, const uint8_t *bits, unsigned long long nbytes,
                                const float4 *kf, const double *pose, DecTile *dt, float4 *kf_out,

@@ -153,7 +153,7 @@ lcc_status enqueue_class(PlanClass &pc, int64_t *launches) {
                               kind ? nullptr : kfo, nb);
             if (st != LCC_OK) return st;
             c->last_nframes = m;
-            *launches += 1 + 4 + (c->g.lookahead > 0 ? 1 : 0) +
+            *launches += 1 + 3 + (c->g.lookahead > 0 ? 1 : 0) +
                          (c->g.schedule == 3 ? 1
                           : c->g.schedule >= 1 ? c->g.R + 1 - (kind == 1 ? 0 : c->g.first_rounds) : 0);
         }

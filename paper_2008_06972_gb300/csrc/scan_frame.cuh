@@ -1,9 +1,11 @@
-// Stream layout of one frame (one CTA per frame).
+// Stream layout of one frame, run by the last block of the run merge to finish
+// a frame (the rows' totals are final then).
+#pragma once
+
 #include "lcc_internal.cuh"
 
 namespace lcc {
 
-constexpr int kScanThreads = 512;
 constexpr int kScanVals = 6;
 
 __device__ __forceinline__ uint32_t words_for(uint64_t bits) { return (uint32_t)((bits + 31) >> 5); }
@@ -11,10 +13,10 @@ __device__ __forceinline__ uint32_t words_for(uint64_t bits) { return (uint32_t)
 // Per frame: exclusive prefix of the tile-row totals (cand, fitted, raw, run
 // starts, temporal tiles, valid pixels) gives every row its base offset in
 // each section; the frame totals give the section layout, the header and the
-// capacity check.  The CTA then zeroes the frame's output words so the packer
-// can OR bits in.
-__global__ void __launch_bounds__(kScanThreads) k_scan(Geometry g, Scratch s, Batch b) {
-    const int f = blockIdx.x;
+// capacity check.  The block then zeroes the frame's output words so the packer
+// can OR bits in.  Called by all kScanThreads threads of one block.
+template <int kScanThreads>
+__device__ __forceinline__ void scan_frame(const Geometry &g, const Scratch &s, const Batch &b, int f) {
     const size_t slot = (size_t)b.slot[f];
     const uint32_t *rowtot = s.rowtot + slot * g.TR * 8;
     uint32_t *rowbase = s.rowbase + slot * g.TR * 8;
@@ -32,7 +34,7 @@ __global__ void __launch_bounds__(kScanThreads) k_scan(Geometry g, Scratch s, Ba
         uint32_t v[kScanVals] = {0, 0, 0, 0, 0, 0};
         if (r < g.TR)
 #pragma unroll
-            for (int q = 0; q < kScanVals; q++) v[q] = rowtot[r * 8 + q];
+            for (int q = 0; q < kScanVals; q++) v[q] = __ldcg(rowtot + r * 8 + q);   // written by other blocks
         uint32_t inc[kScanVals];
 #pragma unroll
         for (int q = 0; q < kScanVals; q++) {
@@ -130,12 +132,6 @@ __global__ void __launch_bounds__(kScanThreads) k_scan(Geometry g, Scratch s, Ba
         uint32_t *o1 = reinterpret_cast<uint32_t *>(b.out[f] + kHeaderBytes);
         for (uint32_t q = (nw / 4) * 4 + tid; q < nw; q += kScanThreads) o1[q] = 0u;
     }
-}
-
-cudaError_t launch_scan(const Geometry &g, const Scratch &s, const Batch &b, cudaStream_t st) {
-    if (b.nframes <= 0) return cudaSuccess;
-    k_scan<<<b.nframes, kScanThreads, 0, st>>>(g, s, b);
-    return cudaGetLastError();
 }
 
 }  // namespace lcc
