@@ -47,7 +47,7 @@ def parse():
     ap.add_argument("--lookahead", type=int, default=16)
     ap.add_argument("--refits", type=int, default=3)
     ap.add_argument("--solver", default="ff", choices=["ff", "fp64"])
-    ap.add_argument("--schedule", type=int, default=0)
+    ap.add_argument("--schedule", type=int, default=3)
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="bounded oracle sample length")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batched", action="store_true", help="skip the uneven multi-sequence batch")
@@ -684,7 +684,7 @@ def main():
     achieved = alg_bytes / (per_launch_ms * 1e-3) / 1e9
     path_bytes = 16.0 * pts_step + total_bytes
     traffic = measured_traffic(dname) if (args.tile, args.thr, args.lookahead, args.schedule) == (
-        "4x4", 0.05, 16, 0) else None
+        "4x4", 0.05, 16, 3) else None
     roof = {"bound": "hbm", "kernel": dname, "achieved": achieved, "peak": hbm, "unit": "GB/s",
             "frac": achieved / hbm, "traffic": traffic, "alg_bytes_per_launch": alg_bytes,
             "peak_source": src,

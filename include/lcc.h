@@ -109,7 +109,8 @@ typedef struct lcc_keyframe lcc_keyframe;
 const char *lcc_status_string(lcc_status s);
 
 /* Default parameters: 4x4 tiles, thr 0.05 m, q 0.02 m, 3 refits, f_min 0.75,
- * runs on, max_batch 16, lookahead 16, float-float solver, per-thread fit rounds. */
+ * runs on, max_batch 16, lookahead 16, float-float solver, fit schedule 3 (one
+ * round per thread, the few tiles needing more finish in one dense launch). */
 void lcc_default_params(lcc_params *p);
 
 /* Create a context on the current device bound to cuda_stream (a
@@ -183,10 +184,11 @@ lcc_status lcc_encode_pframes(lcc_ctx *ctx, const lcc_keyframe *kf, int32_t nfra
 
 /* A whole sequence (Fig. 1): frame key_index is the K frame, all others are P
  * frames; poses[f] maps frame f to the key frame (poses[key_index] unused).
- * Bins all frames in one launch, encodes K, then all P frames batched.  With
- * fit_schedule 0 the P frames' spatial fits run on a second stream of the
- * context while K is encoded (they do not need K), and their temporal test
- * runs after; the streams are the same as with the sequential order.
+ * The key frame's chain runs on a private high-priority stream; the P frames'
+ * binning, spatial fits and run pre-test run on a second stream of the context
+ * beside it (they do not need K), and their temporal test, merge and pack
+ * follow once the key frame's merge has written its planes.  The streams are
+ * byte-identical to encoding K and then the P frames in sequence.
  * nframes <= max_batch.  kf (nullable) receives the key frame's planes. */
 lcc_status lcc_encode_sequence(lcc_ctx *ctx, int32_t nframes, int32_t key_index, const double *poses,
                                const float *const *d_pts, const int64_t *n, uint8_t *const *d_out,
@@ -395,7 +397,7 @@ void lcc_plan_destroy(lcc_plan *plan);
  * sequence (nframes <= 64 device frames, key frame key_index, poses as in
  * lcc_encode_sequence) with every candidate of tile shape {4x4, 4x8, 8x8,
  * 8x16} x run-test horizon {8, 16, 32} (only 0 when base->merge_runs is 0) x
- * fit schedule {0, 1}, each on a context of its own, `reps` timed encodes per
+ * fit schedule {0, 3}, each on a context of its own, `reps` timed encodes per
  * candidate (CUDA events on cuda_stream).  Every frame is then decoded and
  * compared with its binned input: candidates whose max range error exceeds
  * max_err_m are rejected.  Of the rest, those whose total stream size is at

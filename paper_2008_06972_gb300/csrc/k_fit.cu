@@ -477,9 +477,9 @@ __device__ __forceinline__ ff dot_term(const float n[3], float rr, float ux, flo
 template <int TH_, int TW_>
 __device__ __forceinline__ ff class_tree_sum(const TileView<TH_, TW_> &tv, const Mask &S, const float n[3]) {
     constexpr int PX = TH_ * TW_, L = TLanes<TH_, TW_>::L;
-    ff stk[6];
+    ff stk[6];   // pending class sums of the pairwise tree (rolled loop: one code copy)
     int depth = 0;
-#pragma unroll
+#pragma unroll 1
     for (int l = 0; l < L; l++) {
         ff p = {0.f, 0.f};
 #pragma unroll 2
@@ -489,7 +489,6 @@ __device__ __forceinline__ ff class_tree_sum(const TileView<TH_, TW_> &tv, const
             tv.u(k, ux, uy, uz);
             p = ff_add(p, dot_term(n, tv.r(k), ux, uy, uz));
         }
-#pragma unroll
         for (int cnt = l + 1; (cnt & 1) == 0; cnt >>= 1) p = ff_add(stk[--depth], p);
         stk[depth++] = p;
     }

@@ -59,15 +59,14 @@ __device__ __forceinline__ uint32_t warp_incl_sum(uint32_t x, int lane) {
 constexpr int kMergeThreads = 256;
 
 // One block per tile row (the row lives in dynamic shared memory).  Stages:
-// (A) all threads stage the row's fit records (and, for the staged variant,
-// the row's ranges and ray directions, loaded up front so that their latency
-// overlaps the rest); (B) the next fitted tile at or after every position
+// (A) all threads stage the row's fit records; (B) the next fitted tile at or after every position
 // (suffix scan, warp 0), for every fitted tile how far its run would reach by
 // the followers' look-behind bits (all threads, branch-free), and where the
 // walk goes next from it when that run ends inside the look-behind horizon;
 // (C) all threads walk the greedy chain together: one shared-memory load per
 // run that ends inside the horizon; past it, block-wide steps test one tile
-// per kEL lanes against the run's plane; (D) all threads assign codes and
+// per kEL lanes against the run's plane (the staged variant loads the row's
+// ranges and ray directions into shared memory on the first such step); (D) all threads assign codes and
 // counts, then a block scan gives the intra-row stream offsets and the row
 // totals; (E) the last block of a frame to finish lays out the frame's
 // stream from the row totals (scan_frame).
@@ -106,52 +105,6 @@ __global__ void __launch_bounds__(kMergeThreads) k_merge(Geometry g, Scratch s, 
     const int row0 = tr * TC;
     const int hzmax = g.merge ? g.lookahead : 0;
 
-    if (kStage) {
-        // the tile row's ranges, per tile in raster order (stride PX + 1), and its ray directions;
-        // 16-byte loads, eight in flight per thread, when image rows are whole 16-byte groups
-        const int rowpx = TC * TW_;   // TW_ is a multiple of 4
-        if ((g.W & 3) == 0) {
-            const int q4 = rowpx / 4, nvec = TH_ * q4;
-            constexpr int U = 8;
-            for (int v0 = tid; v0 < nvec; v0 += kMergeThreads * U) {
-                uint4 q[U];
-#pragma unroll
-                for (int u = 0; u < U; u++) {
-                    const int v = v0 + u * kMergeThreads;
-                    q[u] = make_uint4(kEmptyBits, kEmptyBits, kEmptyBits, kEmptyBits);
-                    if (v < nvec) {
-                        const int i = tr * TH_ + v / q4, jj = (v % q4) * 4;
-                        if (i < g.H && jj < g.W) q[u] = __ldg(reinterpret_cast<const uint4 *>(rimg + (size_t)i * g.W + jj));
-                    }
-                }
-#pragma unroll
-                for (int u = 0; u < U; u++) {
-                    const int v = v0 + u * kMergeThreads;
-                    if (v < nvec) {
-                        const int ii = v / q4, jj = (v % q4) * 4;
-                        uint32_t *d = s_r + (jj / TW_) * (PX + 1) + ii * TW_ + jj % TW_;
-                        d[0] = q[u].x; d[1] = q[u].y; d[2] = q[u].z; d[3] = q[u].w;
-                    }
-                }
-            }
-        } else {
-            for (int idx = tid; idx < TH_ * rowpx; idx += kMergeThreads) {
-                const int ii = idx / rowpx, jj = idx % rowpx;
-                const int i = tr * TH_ + ii;
-                s_r[(jj / TW_) * (PX + 1) + ii * TW_ + jj % TW_] =
-                    (i < g.H && jj < g.W) ? __ldg(rimg + (size_t)i * g.W + jj) : kEmptyBits;
-            }
-        }
-        for (int jj = tid; jj < rowpx; jj += kMergeThreads) {
-            s_ct[jj] = jj < g.W ? __ldg(g.ct + jj) : 0.f;
-            s_st[jj] = jj < g.W ? __ldg(g.st + jj) : 0.f;
-        }
-        if (tid < TH_) {
-            const int i = tr * TH_ + tid;
-            s_ce[tid] = i < g.H ? __ldg(g.ce + i) : 0.f;
-            s_se[tid] = i < g.H ? __ldg(g.se + i) : 0.f;
-        }
-    }
     // (A) stage the row's records (coalesced 16-byte loads)
     for (int c = tid; c < TC; c += kMergeThreads) {
         const uint4 *src = reinterpret_cast<const uint4 *>(recs + row0 + c);
@@ -225,6 +178,7 @@ __global__ void __launch_bounds__(kMergeThreads) k_merge(Geometry g, Scratch s, 
     // tiles against the run's plane in one step, kEL lanes per tile.
     {
         __shared__ uint32_t s_fail[kMergeThreads / 32];
+        bool staged = false;
         int st = nextfit[0];
         while (st < TC) {
             const uint32_t jv = jmp[st];
@@ -235,6 +189,55 @@ __global__ void __launch_bounds__(kMergeThreads) k_merge(Geometry g, Scratch s, 
             }
             int k = (int)(jv & 0x7FFFu);
             bool open = true;
+            if (kStage && !staged) {
+                // the tile row's ranges, per tile in raster order (stride PX + 1), and its ray directions;
+                // 16-byte loads, eight in flight per thread, when image rows are whole 16-byte groups
+                // (loaded once per row, by the first run that reaches past the look-behind horizon)
+                const int rowpx = TC * TW_;   // TW_ is a multiple of 4
+                if ((g.W & 3) == 0) {
+                    const int q4 = rowpx / 4, nvec = TH_ * q4;
+                    constexpr int U = 8;
+                    for (int v0 = tid; v0 < nvec; v0 += kMergeThreads * U) {
+                        uint4 q[U];
+#pragma unroll
+                        for (int u = 0; u < U; u++) {
+                            const int v = v0 + u * kMergeThreads;
+                            q[u] = make_uint4(kEmptyBits, kEmptyBits, kEmptyBits, kEmptyBits);
+                            if (v < nvec) {
+                                const int i = tr * TH_ + v / q4, jj = (v % q4) * 4;
+                                if (i < g.H && jj < g.W) q[u] = __ldg(reinterpret_cast<const uint4 *>(rimg + (size_t)i * g.W + jj));
+                            }
+                        }
+#pragma unroll
+                        for (int u = 0; u < U; u++) {
+                            const int v = v0 + u * kMergeThreads;
+                            if (v < nvec) {
+                                const int ii = v / q4, jj = (v % q4) * 4;
+                                uint32_t *d = s_r + (jj / TW_) * (PX + 1) + ii * TW_ + jj % TW_;
+                                d[0] = q[u].x; d[1] = q[u].y; d[2] = q[u].z; d[3] = q[u].w;
+                            }
+                        }
+                    }
+                } else {
+                    for (int idx = tid; idx < TH_ * rowpx; idx += kMergeThreads) {
+                        const int ii = idx / rowpx, jj = idx % rowpx;
+                        const int i = tr * TH_ + ii;
+                        s_r[(jj / TW_) * (PX + 1) + ii * TW_ + jj % TW_] =
+                            (i < g.H && jj < g.W) ? __ldg(rimg + (size_t)i * g.W + jj) : kEmptyBits;
+                    }
+                }
+                for (int jj = tid; jj < rowpx; jj += kMergeThreads) {
+                    s_ct[jj] = jj < g.W ? __ldg(g.ct + jj) : 0.f;
+                    s_st[jj] = jj < g.W ? __ldg(g.st + jj) : 0.f;
+                }
+                if (tid < TH_) {
+                    const int i = tr * TH_ + tid;
+                    s_ce[tid] = i < g.H ? __ldg(g.ce + i) : 0.f;
+                    s_se[tid] = i < g.H ? __ldg(g.se + i) : 0.f;
+                }
+                __syncthreads();
+                staged = true;
+            }
             {
                 const float4 pl = row[st].plane;
                 while (open) {
@@ -411,7 +414,9 @@ size_t merge_stage_bytes(int TC, int th, int tw) {
 
 template <int TH_, int TW_, bool kStage>
 static cudaError_t launch_merge_v(const Geometry &g, const Scratch &s, const Batch &b, size_t smem, cudaStream_t st) {
-    if (smem > 48 * 1024) {
+    // above 48 KB of shared memory per block, counting the kernel's own static arrays (a few
+    // hundred bytes) with the dynamic part, a launch needs the opt-in
+    if (smem + 4096 > 48 * 1024) {
         const cudaError_t e = cudaFuncSetAttribute(k_merge<TH_, TW_, kStage>,
                                                    cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;

@@ -254,7 +254,7 @@ void lcc_default_params(lcc_params *p) {
     p->max_batch = 16;
     p->lookahead = 16;
     p->solver = 0;
-    p->fit_schedule = 0;
+    p->fit_schedule = 3;
 }
 
 lcc_status lcc_create(lcc_ctx **out, const lcc_sensor *sensor, const lcc_params *params, void *cuda_stream) {

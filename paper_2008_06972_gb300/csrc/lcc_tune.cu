@@ -114,7 +114,7 @@ lcc_status lcc_autotune(const lcc_sensor *sensor, const lcc_params *base, int32_
     static const int kHorizon[3] = {8, 16, 32};
     std::vector<lcc_tune_result> all;
     for (const auto &t : kTiles)
-        for (int sched = 0; sched < 2; sched++)
+        for (int sched : {0, 3})
             for (int h = 0; h < (base->merge_runs ? 3 : 1); h++) {
                 lcc_params prm = *base;
                 prm.tile_h = t[0];

@@ -172,7 +172,7 @@ def test_keyframe_parity_variants(cfg1, merge, fmin, R):
     _keyframe_case(sen, pts, merge=merge, fmin=fmin, R=R)
 
 
-@pytest.mark.parametrize("solver,schedule", [(0, 0), (1, 0), (0, 1), (1, 1)])
+@pytest.mark.parametrize("solver,schedule", [(0, 0), (1, 0), (0, 1), (1, 1), (0, 3)])
 def test_keyframe_parity_solvers_and_schedules(cfg2_seq, solver, schedule):
     """Both plane solvers (float-float, FP64) and both fit schedules meet the parity contract."""
     seq = cfg2_seq
