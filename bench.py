@@ -113,7 +113,8 @@ def oracle_all_cores(seq, th, tw, thr, seconds):
     return pts * nseq / wall / 1e6, nseq, wall, cores
 
 
-KERNEL_SOURCES = {"bin": ("k_bin.cu",), "fit": ("k_fit.cu",), "refit": ("k_fit.cu",), "temporal": ("k_fit.cu",),
+KERNEL_SOURCES = {"bin": ("k_bin.cu",), "fit": ("k_fit.cu",), "rounds": ("k_fit.cu",), "lookbehind": ("k_fit.cu",),
+                  "temporal": ("k_fit.cu",),
                   "merge": ("k_merge.cu", "scan_frame.cuh"), "pack": ("k_pack.cu",)}
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "dram_traffic_hdl64_sequence.txt")
 
@@ -667,14 +668,19 @@ def main():
     #          + the stream bytes zeroed by the frame's layout step
     #   pack:  4 B per pixel read + 4 B per pixel reset + stream bytes written
     #   temporal: (P frames) 4 B per pixel + 64 B per tile record read and written
-    #   refit: 4 B per pixel (range image read) + 64 B per tile record read + 32 B per tile of
-    #          look-behind counts written (extra refit rounds, when scheduled, reuse the same data)
+    #   lookbehind: 4 B per pixel (range image read) + 64 B per tile record read + 32 B per tile
+    #          of look-behind counts written
+    #   rounds: per queued tile its record read and written (128 B), and 4 B per pixel per
+    #          further round (the fit rounds after the first pass, from the rounds histogram)
     npx = H * W
     nt = ctx.num_tiles
+    queued_tiles = sum(rounds_hist[r] for r in range(2, 8))
+    extra_rounds = sum((r - 1) * rounds_hist[r] for r in range(2, 8))
     per_step_units = {
         "bin": 20.0 * pts_step,
         "fit": n_frames * (4.0 * npx + 64.0 * nt),
-        "refit": n_frames * (4.0 * npx + 96.0 * nt),
+        "rounds": 128.0 * queued_tiles + 4.0 * th * tw * extra_rounds,
+        "lookbehind": n_frames * (4.0 * npx + 96.0 * nt),
         "temporal": (n_frames - 1) * (4.0 * npx + 128.0 * nt),
         "merge": n_frames * (64.0 * nt + 32.0 * nt + 32.0 * nt) + total_bytes,
         "pack": n_frames * 8.0 * npx + total_bytes,

@@ -225,8 +225,10 @@ lcc_status lcc_tile_records(lcc_ctx *ctx, int32_t frame, lcc_tile_info *h_out, i
  * on the stream it runs on.  lcc_kernel_times returns, per kernel name, the
  * number of launches and summed milliseconds since the last reset
  * (synchronous; launches that overlap are each timed in full).  Names: "bin",
- * "fit", "refit", "temporal", "merge", "scan", "pack", "decode_prep",
- * "decode_px", "range_export".  Returns the number of entries written. */
+ * "fit" (first fit pass), "rounds" (queued fit rounds), "lookbehind" (run
+ * pre-test), "temporal", "merge" (with the frame's stream layout), "pack",
+ * "decode_prep", "decode_px", "range_export".  Returns the number of entries
+ * written. */
 lcc_status lcc_set_profiling(lcc_ctx *ctx, int32_t enable);
 int32_t lcc_kernel_times(lcc_ctx *ctx, char names[][16], int64_t *launches, double *ms, int32_t cap);
 

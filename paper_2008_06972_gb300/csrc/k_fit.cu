@@ -226,6 +226,67 @@ struct Moments {
     ff s1x, s1y, s1z, sxx, sxy, sxz, syy, syz, szz;
 };
 
+__device__ __forceinline__ Moments moments_zero() {
+    Moments m;
+    m.s1x = m.s1y = m.s1z = m.sxx = m.sxy = m.sxz = m.syy = m.syz = m.szz = {0.f, 0.f};
+    return m;
+}
+
+// Adds the point p = r u, shifted by the anchor a, to m.
+__device__ __forceinline__ void moments_point(Moments &m, float rr, float ux, float uy, float uz, float ax, float ay,
+                                              float az) {
+    const ff qx = two_sum(__fmul_rn(rr, ux), -ax), qy = two_sum(__fmul_rn(rr, uy), -ay),
+             qz = two_sum(__fmul_rn(rr, uz), -az);
+    m.s1x = ff_add(m.s1x, qx);
+    m.s1y = ff_add(m.s1y, qy);
+    m.s1z = ff_add(m.s1z, qz);
+    m.sxx = ff_add(m.sxx, ff_mul(qx, qx));
+    m.sxy = ff_add(m.sxy, ff_mul(qx, qy));
+    m.sxz = ff_add(m.sxz, ff_mul(qx, qz));
+    m.syy = ff_add(m.syy, ff_mul(qy, qy));
+    m.syz = ff_add(m.syz, ff_mul(qy, qz));
+    m.szz = ff_add(m.szz, ff_mul(qz, qz));
+}
+
+__device__ __forceinline__ Moments moments_add(const Moments &a, const Moments &b) {
+    Moments m;
+    m.s1x = ff_add(a.s1x, b.s1x);
+    m.s1y = ff_add(a.s1y, b.s1y);
+    m.s1z = ff_add(a.s1z, b.s1z);
+    m.sxx = ff_add(a.sxx, b.sxx);
+    m.sxy = ff_add(a.sxy, b.sxy);
+    m.sxz = ff_add(a.sxz, b.sxz);
+    m.syy = ff_add(a.syy, b.syy);
+    m.syz = ff_add(a.syz, b.syz);
+    m.szz = ff_add(a.szz, b.szz);
+    return m;
+}
+
+__device__ __forceinline__ Moments moments_shfl(unsigned mask, const Moments &m, int src) {
+    Moments o;
+    o.s1x = {__shfl_sync(mask, m.s1x.hi, src), __shfl_sync(mask, m.s1x.lo, src)};
+    o.s1y = {__shfl_sync(mask, m.s1y.hi, src), __shfl_sync(mask, m.s1y.lo, src)};
+    o.s1z = {__shfl_sync(mask, m.s1z.hi, src), __shfl_sync(mask, m.s1z.lo, src)};
+    o.sxx = {__shfl_sync(mask, m.sxx.hi, src), __shfl_sync(mask, m.sxx.lo, src)};
+    o.sxy = {__shfl_sync(mask, m.sxy.hi, src), __shfl_sync(mask, m.sxy.lo, src)};
+    o.sxz = {__shfl_sync(mask, m.sxz.hi, src), __shfl_sync(mask, m.sxz.lo, src)};
+    o.syy = {__shfl_sync(mask, m.syy.hi, src), __shfl_sync(mask, m.syy.lo, src)};
+    o.syz = {__shfl_sync(mask, m.syz.hi, src), __shfl_sync(mask, m.syz.lo, src)};
+    o.szz = {__shfl_sync(mask, m.szz.hi, src), __shfl_sync(mask, m.szz.lo, src)};
+    return o;
+}
+
+// Order of a tile's moment sums, shared by the per-thread fit (TileView) and the
+// lane-group fit of the queued rounds (TileLanes), so both give the same bits:
+// the pixels are split into L chunks of CH consecutive pixels (raster order),
+// each chunk is summed in pixel order, and the chunk sums are added left to right.
+template <int TH_, int TW_>
+struct FitLanes {
+    static constexpr int PX = TH_ * TW_;
+    static constexpr int L = PX / 4 < 8 ? PX / 4 : 8;
+    static constexpr int CH = PX / L;
+};
+
 // One plane solve; a single out-of-line copy keeps the instruction footprint
 // of the kernels small (the kernels run few warps per SM, so cold instruction
 // fetches, not arithmetic, bound them when code is duplicated).
@@ -322,28 +383,109 @@ struct TileView {
         }
         return cnt;
     }
-    // one total-least-squares fit over the set S (float-float moments)
+    // one total-least-squares fit over the set S (float-float moments, in the chunk order
+    // of FitLanes)
     __device__ __forceinline__ bool fit(const Mask &S, int nS, float4 &pl, float &ratio) const {
-        Moments m;
-        m.s1x = m.s1y = m.s1z = m.sxx = m.sxy = m.sxz = m.syy = m.syz = m.szz = {0.f, 0.f};
+        constexpr int L = FitLanes<TH_, TW_>::L, CH = FitLanes<TH_, TW_>::CH;
+        Moments m = moments_zero();
+#pragma unroll 1
+        for (int c = 0; c < L; c++) {
+            Moments part = moments_zero();
 #pragma unroll 2
-        for (int k = 0; k < PX; k++) {
+            for (int k = c * CH; k < (c + 1) * CH; k++) {
+                if (!S.get(k)) continue;
+                float ux, uy, uz;
+                u(k, ux, uy, uz);
+                moments_point(part, r(k), ux, uy, uz, ax, ay, az);
+            }
+            m = c == 0 ? part : moments_add(m, part);
+        }
+        return solve_moments(m, nS, ax, ay, az, g.solver, &pl, &ratio);
+    }
+};
+
+// One tile seen by a group of L lanes (FitLanes; an aligned group of a warp):
+// lane l owns the pixel chunk [l CH, (l + 1) CH).  Every member function is
+// collective over the group and returns the same value on every lane.
+template <int TH_, int TW_>
+struct TileLanes {
+    static constexpr int PX = TH_ * TW_;
+    static constexpr int L = FitLanes<TH_, TW_>::L, CH = FitLanes<TH_, TW_>::CH;
+    const Geometry &g;
+    const uint32_t *rimg;
+    int t, i0, j0, l, g0;
+    unsigned gmask;
+    Mask V;
+    int nv, first;
+    float ax, ay, az;
+
+    __device__ __forceinline__ TileLanes(const Geometry &g_, const uint32_t *rimg_, int t_, int lane)
+        : g(g_), rimg(rimg_), t(t_) {
+        l = lane % L;
+        g0 = lane - l;
+        gmask = ((1u << L) - 1u) << g0;
+        i0 = (t / g.TC) * TH_;
+        j0 = (t % g.TC) * TW_;
+        V.w0 = V.w1 = 0ull;
+#pragma unroll 4
+        for (int k = l * CH; k < (l + 1) * CH; k++)
+            if (r(k) > 0.0f) V.set(k);
+#pragma unroll
+        for (int off = 1; off < L; off <<= 1) {
+            V.w0 |= __shfl_xor_sync(gmask, V.w0, off);
+            V.w1 |= __shfl_xor_sync(gmask, V.w1, off);
+        }
+        nv = __popcll(V.w0) + __popcll(V.w1);
+        first = V.w0 ? __ffsll((long long)V.w0) - 1 : (V.w1 ? 64 + __ffsll((long long)V.w1) - 1 : -1);
+        ax = ay = az = 0.f;
+        if (first >= 0) {
+            float ux, uy, uz;
+            u(first, ux, uy, uz);
+            const float r0 = r(first);
+            ax = __fmul_rn(r0, ux);
+            ay = __fmul_rn(r0, uy);
+            az = __fmul_rn(r0, uz);
+        }
+    }
+    __device__ __forceinline__ float r(int k) const {
+        const int i = i0 + k / TW_, j = j0 + k % TW_;
+        if (i >= g.H || j >= g.W) return 0.0f;
+        const uint32_t bits = __ldg(rimg + (size_t)i * g.W + j);
+        return bits_valid(bits) ? __uint_as_float(bits) : 0.0f;
+    }
+    __device__ __forceinline__ void u(int k, float &ux, float &uy, float &uz) const {
+        beam(g, i0 + k / TW_, j0 + k % TW_, ux, uy, uz);
+    }
+    __device__ __forceinline__ int inliers(const float4 &pl, Mask &I, bool &border) const {
+        I.w0 = I.w1 = 0ull;
+        bool bd = false;
+#pragma unroll 2
+        for (int k = l * CH; k < (l + 1) * CH; k++) {
+            if (!V.get(k)) continue;
+            float ux, uy, uz;
+            u(k, ux, uy, uz);
+            if (inlier_screened(pl, ux, uy, uz, r(k), g.thr, bd)) I.set(k);
+        }
+#pragma unroll
+        for (int off = 1; off < L; off <<= 1) {
+            I.w0 |= __shfl_xor_sync(gmask, I.w0, off);
+            I.w1 |= __shfl_xor_sync(gmask, I.w1, off);
+        }
+        if (__any_sync(gmask, bd)) border = true;
+        return __popcll(I.w0) + __popcll(I.w1);
+    }
+    __device__ __forceinline__ bool fit(const Mask &S, int nS, float4 &pl, float &ratio) const {
+        Moments part = moments_zero();
+#pragma unroll 2
+        for (int k = l * CH; k < (l + 1) * CH; k++) {
             if (!S.get(k)) continue;
             float ux, uy, uz;
             u(k, ux, uy, uz);
-            const float rr = r(k);
-            const ff qx = two_sum(__fmul_rn(rr, ux), -ax), qy = two_sum(__fmul_rn(rr, uy), -ay),
-                     qz = two_sum(__fmul_rn(rr, uz), -az);
-            m.s1x = ff_add(m.s1x, qx);
-            m.s1y = ff_add(m.s1y, qy);
-            m.s1z = ff_add(m.s1z, qz);
-            m.sxx = ff_add(m.sxx, ff_mul(qx, qx));
-            m.sxy = ff_add(m.sxy, ff_mul(qx, qy));
-            m.sxz = ff_add(m.sxz, ff_mul(qx, qz));
-            m.syy = ff_add(m.syy, ff_mul(qy, qy));
-            m.syz = ff_add(m.syz, ff_mul(qy, qz));
-            m.szz = ff_add(m.szz, ff_mul(qz, qz));
+            moments_point(part, r(k), ux, uy, uz, ax, ay, az);
         }
+        Moments m = moments_shfl(gmask, part, g0);
+#pragma unroll
+        for (int c = 1; c < L; c++) m = moments_add(m, moments_shfl(gmask, part, g0 + c));
         return solve_moments(m, nS, ax, ay, az, g.solver, &pl, &ratio);
     }
 };
@@ -404,8 +546,8 @@ __device__ __forceinline__ void queue_push(bool push, uint32_t item, uint32_t *q
 // threshold leaves the tile unfitted (flag 8).  The proposed plane is formed by
 // fixed fp32 operations: n = v / sqrtf(fma sum of squares), d = d_rel + n.anchor
 // (fma chain), both negated when d < 0.
-template <int TH_, int TW_>
-__device__ __forceinline__ bool spatial_rounds(const TileView<TH_, TW_> &tv, RecOut &o, int max_rounds,
+template <class TV>
+__device__ __forceinline__ bool spatial_rounds(const TV &tv, RecOut &o, int max_rounds,
                                                const float *prop = nullptr, float skip_logit = 0.f) {
     const Geometry &g = tv.g;
     Mask S, I;
@@ -567,11 +709,11 @@ __global__ void __launch_bounds__(kFitThreads) k_fit_first(Geometry g, Scratch s
     if (o.status != S_TEMPORAL && tv.nv >= 3) {
         const float *prop = b.prop[f] ? b.prop[f] + 5 * (size_t)t : nullptr;
         if (!kQueue) {
-            spatial_rounds<TH_, TW_>(tv, o, g.R + 1, prop, b.skip_logit);
+            spatial_rounds(tv, o, g.R + 1, prop, b.skip_logit);
         } else if (b.kind == 1 && b.kf[f]) {
             queued = true;   // P-frame spatial fallback after its temporal test: from its first round, dense
         } else {
-            queued = !spatial_rounds<TH_, TW_>(tv, o, g.first_rounds, prop, b.skip_logit);
+            queued = !spatial_rounds(tv, o, g.first_rounds, prop, b.skip_logit);
         }
     }
     if (kQueue)
@@ -580,36 +722,40 @@ __global__ void __launch_bounds__(kFitThreads) k_fit_first(Geometry g, Scratch s
     write_rec(recs + t, o);
 }
 
-// One more spatial round for every queued tile; tiles that still need one
-// are pushed onto the next queue.
+// Further spatial rounds (at most max_rounds) for every queued tile, a group of
+// FitLanes::L lanes per tile (the few tiles that need them are latency-bound:
+// the group splits each round's pixel work); tiles that still need a round are
+// pushed onto the next queue.
 template <int TH_, int TW_>
 __global__ void __launch_bounds__(kFitThreads) k_fit_round(Geometry g, Scratch s, Batch b, int in_q, int out_q,
                                                              int max_rounds) {
-    using TV = TileView<TH_, TW_>;
+    using TV = TileLanes<TH_, TW_>;
+    constexpr int L = FitLanes<TH_, TW_>::L;
+    static_assert(kFitThreads % L == 0 && 32 % L == 0, "lane groups");
     uint32_t *queue = s.queue + (size_t)b.qset * 2 * s.qcap;
     uint32_t *qcount = s.qcount + 8 * b.qset;
     const uint32_t n_in = qcount[in_q];
     const uint32_t *qin = queue + (size_t)(in_q & 1) * s.qcap;
     uint32_t *qout = queue + (size_t)(out_q & 1) * s.qcap;
-    for (uint32_t idx = blockIdx.x * kFitThreads + threadIdx.x; idx < n_in; idx += gridDim.x * kFitThreads) {
+    const int lane = threadIdx.x & 31;
+    const uint32_t stride = gridDim.x * (kFitThreads / L);
+    for (uint32_t idx = (blockIdx.x * kFitThreads + threadIdx.x) / L; idx < n_in; idx += stride) {
         const uint32_t item = qin[idx];
         const int f = (int)(item >> 26), t = (int)(item & 0x3FFFFFFu);
         const uint32_t *rimg = s.rimg + (size_t)b.slot[f] * g.H * g.W;
         TileRec *recs = s.tiles + (size_t)b.slot[f] * g.NT;
-        const TV tv(g, rimg, t);
+        const TV tv(g, rimg, t, lane);
         RecOut o = read_rec(recs + t);
-        const bool done = spatial_rounds<TH_, TW_>(tv, o, max_rounds);
-        queue_push(!done, item, qout, qcount + out_q);
-        write_rec(recs + t, o);
+        const bool done = spatial_rounds(tv, o, max_rounds);
+        const bool leader = tv.l == 0;
+        queue_push(!done && leader, item, qout, qcount + out_q);
+        if (leader) write_rec(recs + t, o);
     }
 }
 
-// Temporal pass over P tiles whose spatial fit already ran (k_fit_first
-// without a key-frame table): the temporal test of Sec. III-D against the
-// key frame's planes, and the same per-tile decision as the fused pass — a
-// tile that passes becomes TEMPORAL exactly as if its spatial fit had never
-// run; otherwise the spatial result stands and the temporal fields are added.
-// Temporal test of the P frames after their spatial fits (lcc_encode_sequence):
+// Temporal test of the P frames after their spatial fits (lcc_encode_sequence), with the
+// same per-tile decision as the fused pass (a tile that passes becomes temporal exactly as
+// if its spatial fit had never run):
 // a group of L lanes per tile (TLanes), each lane holding its PX / L pixels in
 // registers; sums and inlier sets are combined by xor-butterflies inside the
 // group.  A tile that passes becomes temporal; otherwise only the temporal
@@ -848,9 +994,10 @@ static cudaError_t launch_queued_rounds_t(const Geometry &g, const Scratch &s, c
     if (g.schedule >= 1) {
         // the first pass ran the first rounds, except for P frames whose first pass was their
         // temporal test: their spatial rounds all run here
-        const int rounds_left = (b.kind == 1 && b.kf[0]) ? g.R + 1 : g.R + 1 - g.first_rounds;
+        const int rounds_left = queued_rounds_left(g, b);
         const long long worst = (long long)g.NT * b.nframes;
-        const int blocks = (int)std::min<long long>((worst + kFitThreads - 1) / kFitThreads, 152 * 8);
+        constexpr int L = FitLanes<TH_, TW_>::L;   // lanes per queued tile
+        const int blocks = (int)std::min<long long>((worst * L + kFitThreads - 1) / kFitThreads, 152 * 8);
         if (g.schedule == 3) {   // the queued tiles run all their remaining rounds in one dense launch
             k_fit_round<TH_, TW_><<<blocks, kFitThreads, 0, st>>>(g, s, b, 0, 1, rounds_left);
             return cudaGetLastError();
@@ -862,13 +1009,6 @@ static cudaError_t launch_queued_rounds_t(const Geometry &g, const Scratch &s, c
         }
     }
     return cudaSuccess;
-}
-
-template <int TH_, int TW_>
-static cudaError_t launch_fit_rounds_t(const Geometry &g, const Scratch &s, const Batch &b, cudaStream_t st) {
-    const cudaError_t e = launch_queued_rounds_t<TH_, TW_>(g, s, b, st);
-    if (e != cudaSuccess) return e;
-    return launch_lookbehind_t<TH_, TW_>(g, s, b, st);
 }
 
 template <int TH_, int TW_>
@@ -912,15 +1052,6 @@ cudaError_t launch_lookbehind(const Geometry &g, const Scratch &s, const Batch &
     if (g.th == 4 && g.tw == 8) return launch_lookbehind_t<4, 8>(g, s, b, st);
     if (g.th == 8 && g.tw == 8) return launch_lookbehind_t<8, 8>(g, s, b, st);
     if (g.th == 8 && g.tw == 16) return launch_lookbehind_t<8, 16>(g, s, b, st);
-    return cudaErrorInvalidValue;
-}
-
-cudaError_t launch_fit_rounds(const Geometry &g, const Scratch &s, const Batch &b, cudaStream_t st) {
-    if (b.nframes <= 0) return cudaSuccess;
-    if (g.th == 4 && g.tw == 4) return launch_fit_rounds_t<4, 4>(g, s, b, st);
-    if (g.th == 4 && g.tw == 8) return launch_fit_rounds_t<4, 8>(g, s, b, st);
-    if (g.th == 8 && g.tw == 8) return launch_fit_rounds_t<8, 8>(g, s, b, st);
-    if (g.th == 8 && g.tw == 16) return launch_fit_rounds_t<8, 16>(g, s, b, st);
     return cudaErrorInvalidValue;
 }
 

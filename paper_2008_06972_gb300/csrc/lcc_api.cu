@@ -18,8 +18,8 @@ using namespace lcc;
 namespace lcc {
 namespace api {
 
-const char *kKernelNames[] = {"bin",          "fit",   "merge", "scan",    "pack", "decode_prep",
-                              "decode_px",    "range_export",   "refit",   "temporal"};
+const char *kKernelNames[] = {"bin",          "fit",   "merge", "rounds",  "pack", "decode_prep",
+                              "decode_px",    "range_export",   "lookbehind",   "temporal"};
 
 cudaEvent_t get_event(lcc_ctx *c) {
     if (!c->pool.empty()) {
@@ -32,9 +32,9 @@ cudaEvent_t get_event(lcc_ctx *c) {
     return e;
 }
 
-int prof_begin(lcc_ctx *c, int name) {
+int prof_begin(lcc_ctx *c, int name, int count) {
     if (!c->prof) return -1;
-    ProfRec r{name, get_event(c), get_event(c)};
+    ProfRec r{name, get_event(c), get_event(c), count};
     cudaEventRecord(r.a, c->stream);
     c->pending.push_back(r);
     return (int)c->pending.size() - 1;
@@ -50,7 +50,7 @@ void prof_collect(lcc_ctx *c) {
         float ms = 0.f;
         bool base = false;
         if (cudaEventSynchronize(r.b) == cudaSuccess && cudaEventElapsedTime(&ms, r.a, r.b) == cudaSuccess) {
-            c->launches[r.name]++;
+            c->launches[r.name] += r.count;
             c->ms[r.name] += ms;
             if (!c->prof_base) {
                 c->prof_base = r.a;
@@ -148,11 +148,9 @@ void prepare_batch(Batch &b, Poses &p, int kind, int nframes, const int *slots, 
 // Everything after the first fit pass: further rounds (unless already run) and the run
 // pre-test, merge (which also lays out each frame's stream), pack.
 lcc_status encode_tail(lcc_ctx *c, const Batch &b, bool rounds_done = false) {
-    if (rounds_done) {
-        LCC_LAUNCH(c, 8, launch_lookbehind(c->g, c->s, b, c->stream));
-    } else {
-        LCC_LAUNCH(c, 8, launch_fit_rounds(c->g, c->s, b, c->stream));
-    }
+    if (!rounds_done && c->g.schedule >= 1)
+        LCC_LAUNCH_N(c, 3, queued_round_kernels(c->g, b), launch_queued_rounds(c->g, c->s, b, c->stream));
+    if (c->g.merge && c->g.lookahead > 0) LCC_LAUNCH(c, 8, launch_lookbehind(c->g, c->s, b, c->stream));
     LCC_LAUNCH(c, 2, launch_merge(c->g, c->s, b, c->stream));
     LCC_LAUNCH(c, 4, launch_pack(c->g, c->s, b, c->stream));
     return LCC_OK;
@@ -649,11 +647,14 @@ lcc_status encode_sequence(lcc_ctx *c, int32_t nframes, int32_t key_index, const
             if (!h2d(pslots[q], c->side)) return LCC_ERR_CUDA;
         if ((st = bin_frames(c, np, pslots, pdp, pn)) != LCC_OK) return st;
         LCC_LAUNCH(c, 1, launch_fit(c->g, c->s, bp, pp, c->stream));
-        if (c->g.schedule >= 1) LCC_LAUNCH(c, 8, launch_queued_rounds(c->g, c->s, bp, c->stream));
-        LCC_LAUNCH(c, 8, launch_lookbehind(c->g, c->s, bp, c->stream));
+        if (c->g.schedule >= 1)
+            LCC_LAUNCH_N(c, 3, queued_round_kernels(c->g, bp), launch_queued_rounds(c->g, c->s, bp, c->stream));
+        if (c->g.merge && c->g.lookahead > 0) LCC_LAUNCH(c, 8, launch_lookbehind(c->g, c->s, bp, c->stream));
         // key frame: the rest of its rounds and its pre-test, merge (its coding planes), pack
         c->stream = c->kstream;
-        LCC_LAUNCH(c, 8, launch_fit_rounds(c->g, c->s, bk, c->stream));
+        if (c->g.schedule >= 1)
+            LCC_LAUNCH_N(c, 3, queued_round_kernels(c->g, bk), launch_queued_rounds(c->g, c->s, bk, c->stream));
+        if (c->g.merge && c->g.lookahead > 0) LCC_LAUNCH(c, 8, launch_lookbehind(c->g, c->s, bk, c->stream));
         LCC_LAUNCH(c, 2, launch_merge(c->g, c->s, bk, c->stream));   // with the frame's stream layout
         LCC_CUDA(cudaEventRecord(c->ev_kplanes, c->kstream));
         LCC_LAUNCH(c, 4, launch_pack(c->g, c->s, bk, c->stream));

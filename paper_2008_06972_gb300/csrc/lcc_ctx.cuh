@@ -17,6 +17,7 @@ namespace api {
 struct ProfRec {
     int name;
     cudaEvent_t a, b;
+    int count;   // kernels launched between the two events
 };
 
 struct TimelineRec {
@@ -75,7 +76,7 @@ struct lcc_ctx {
 namespace lcc {
 namespace api {
 
-int prof_begin(lcc_ctx *c, int name);
+int prof_begin(lcc_ctx *c, int name, int count = 1);
 void prof_end(lcc_ctx *c, int idx);
 bool aligned16(const void *p);
 // Reads and clears the device error word (synchronous).
@@ -99,6 +100,15 @@ lcc_status check_frames(lcc_ctx *c, int nframes, const float *const *d_pts, cons
 #define LCC_LAUNCH(ctx, id, call)                                  \
     do {                                                           \
         const int _pi = lcc::api::prof_begin(ctx, id);             \
+        const cudaError_t _e = (call);                             \
+        lcc::api::prof_end(ctx, _pi);                              \
+        if (_e != cudaSuccess) return LCC_ERR_CUDA;                \
+    } while (0)
+
+// The same for a call that launches n kernels (n = 0: timed, not counted).
+#define LCC_LAUNCH_N(ctx, id, n, call)                             \
+    do {                                                           \
+        const int _pi = lcc::api::prof_begin(ctx, id, n);          \
         const cudaError_t _e = (call);                             \
         lcc::api::prof_end(ctx, _pi);                              \
         if (_e != cudaSuccess) return LCC_ERR_CUDA;                \

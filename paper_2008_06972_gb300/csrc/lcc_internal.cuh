@@ -379,10 +379,21 @@ cudaError_t launch_bin(const Geometry &g, const Scratch &s, const Batch &b, long
 cudaError_t launch_range_image(const Geometry &g, const uint32_t *rimg, float *range, uint32_t *valid,
                                cudaStream_t st);
 cudaError_t launch_fit(const Geometry &g, const Scratch &s, const Batch &b, const Poses &p, cudaStream_t st);
-cudaError_t launch_fit_rounds(const Geometry &g, const Scratch &s, const Batch &b, cudaStream_t st);
 cudaError_t launch_temporal(const Geometry &g, const Scratch &s, const Batch &b, const Poses &p, cudaStream_t st);
 cudaError_t launch_lookbehind(const Geometry &g, const Scratch &s, const Batch &b, cudaStream_t st);
 cudaError_t launch_queued_rounds(const Geometry &g, const Scratch &s, const Batch &b, cudaStream_t st);
+
+// Spatial rounds still to run after a batch's first fit pass under a queued schedule: all of
+// them for P frames whose first pass was their temporal test, else those the pass left.
+inline int queued_rounds_left(const Geometry &g, const Batch &b) {
+    return (b.kind == 1 && b.kf[0]) ? g.R + 1 : g.R + 1 - g.first_rounds;
+}
+
+// Kernels launch_queued_rounds launches for a batch (one per round, or one under schedule 3).
+inline int queued_round_kernels(const Geometry &g, const Batch &b) {
+    if (g.schedule < 1 || b.nframes <= 0) return 0;
+    return g.schedule == 3 ? 1 : queued_rounds_left(g, b);
+}
 cudaError_t launch_merge(const Geometry &g, const Scratch &s, const Batch &b, cudaStream_t st);
 size_t merge_smem_bytes(int TC);
 cudaError_t launch_pack(const Geometry &g, const Scratch &s, const Batch &b, cudaStream_t st);

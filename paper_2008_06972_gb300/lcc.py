@@ -74,7 +74,7 @@ TILE_INFO_DTYPE = np.dtype([("plane", "<f4", 4), ("tplane", "<f4", 4), ("kref", 
 assert TILE_INFO_DTYPE.itemsize == 64
 
 _lib = None
-KERNEL_NAMES = ("bin", "fit", "merge", "scan", "pack", "decode_prep", "decode_px", "range_export", "refit",
+KERNEL_NAMES = ("bin", "fit", "merge", "rounds", "pack", "decode_prep", "decode_px", "range_export", "lookbehind",
                 "temporal")
 
 
