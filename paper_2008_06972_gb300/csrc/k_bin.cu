@@ -13,57 +13,64 @@ namespace lcc {
 constexpr int kBinThreads = 256;
 constexpr int kBinPerThread = 4;
 
-__global__ void __launch_bounds__(kBinThreads) k_bin(Geometry g, Scratch s, Batch b) {
+// Chunk cb of kBinThreads * kBinPerThread points (chunks are numbered over the batch's
+// frames, blk_prefix[f] = first chunk of frame f); a CTA takes chunks blockIdx.x,
+// blockIdx.x + gridDim.x, ... so that a capped grid covers them all.
+__global__ void __launch_bounds__(kBinThreads) k_bin(Geometry g, Scratch s, Batch b, long long chunks) {
     __shared__ int s_frame;
-    if (threadIdx.x == 0) {
-        int f = 0;
-        while (f + 1 < b.nframes && b.blk_prefix[f + 1] <= (long long)blockIdx.x) f++;
-        s_frame = f;
-    }
-    __syncthreads();
-    const int f = s_frame;
-    const long long n = b.n[f];
-    const long long base = ((long long)blockIdx.x - b.blk_prefix[f]) * (kBinThreads * kBinPerThread);
-    uint32_t *rimg = s.rimg + (size_t)b.slot[f] * g.H * g.W;
-    const float4 *pts = b.pts[f];
-    unsigned invalid = 0, fov = 0, binned = 0;
+    for (long long cb = blockIdx.x; cb < chunks; cb += gridDim.x) {
+        __syncthreads();   // s_frame of the previous chunk has been read by every thread
+        if (threadIdx.x == 0) {
+            int f = 0;
+            while (f + 1 < b.nframes && b.blk_prefix[f + 1] <= cb) f++;
+            s_frame = f;
+        }
+        __syncthreads();
+        const int f = s_frame;
+        const long long n = b.n[f];
+        const long long base = (cb - b.blk_prefix[f]) * (kBinThreads * kBinPerThread);
+        uint32_t *rimg = s.rimg + (size_t)b.slot[f] * g.H * g.W;
+        const float4 *pts = b.pts[f];
+        unsigned invalid = 0, fov = 0, binned = 0;
 #pragma unroll
-    for (int k = 0; k < kBinPerThread; k++) {
-        const long long idx = base + (long long)k * kBinThreads + threadIdx.x;
-        if (idx < n) {
-            const float4 p = __ldcs(pts + idx);
-            float r;
-            int pix;
-            const int res = bin_point(g, p.x, p.y, p.z, r, pix);
-            if (res == 0) {
-                atomicMin(rimg + pix, __float_as_uint(r));
-                binned++;
-            } else if (res == 1) {
-                invalid++;
-            } else {
-                fov++;
+        for (int k = 0; k < kBinPerThread; k++) {
+            const long long idx = base + (long long)k * kBinThreads + threadIdx.x;
+            if (idx < n) {
+                const float4 p = __ldcs(pts + idx);
+                float r;
+                int pix;
+                const int res = bin_point(g, p.x, p.y, p.z, r, pix);
+                if (res == 0) {
+                    atomicMin(rimg + pix, __float_as_uint(r));
+                    binned++;
+                } else if (res == 1) {
+                    invalid++;
+                } else {
+                    fov++;
+                }
             }
         }
-    }
 #pragma unroll
-    for (int off = 16; off; off >>= 1) {
-        invalid += __shfl_xor_sync(0xffffffffu, invalid, off);
-        fov += __shfl_xor_sync(0xffffffffu, fov, off);
-        binned += __shfl_xor_sync(0xffffffffu, binned, off);
+        for (int off = 16; off; off >>= 1) {
+            invalid += __shfl_xor_sync(0xffffffffu, invalid, off);
+            fov += __shfl_xor_sync(0xffffffffu, fov, off);
+            binned += __shfl_xor_sync(0xffffffffu, binned, off);
+        }
+        DevStats *st = s.stats + b.slot[f];
+        if ((threadIdx.x & 31) == 0 && (invalid | fov | binned)) {
+            if (invalid) atomicAdd(&st->invalid, (unsigned long long)invalid);
+            if (fov) atomicAdd(&st->fov, (unsigned long long)fov);
+            if (binned) atomicAdd(&st->binned, (unsigned long long)binned);
+        }
+        if (threadIdx.x == 0 && base == 0) atomicAdd(&st->points_in, (unsigned long long)n);
     }
-    DevStats *st = s.stats + b.slot[f];
-    if ((threadIdx.x & 31) == 0 && (invalid | fov | binned)) {
-        if (invalid) atomicAdd(&st->invalid, (unsigned long long)invalid);
-        if (fov) atomicAdd(&st->fov, (unsigned long long)fov);
-        if (binned) atomicAdd(&st->binned, (unsigned long long)binned);
-    }
-    if (threadIdx.x == 0 && base == 0) atomicAdd(&st->points_in, (unsigned long long)n);
 }
 
 cudaError_t launch_bin(const Geometry &g, const Scratch &s, const Batch &b, long long total_blocks,
-                       cudaStream_t st) {
+                       cudaStream_t st, long long max_blocks) {
     if (total_blocks <= 0) return cudaSuccess;
-    k_bin<<<(unsigned)total_blocks, kBinThreads, 0, st>>>(g, s, b);
+    const long long grid = max_blocks > 0 && total_blocks > max_blocks ? max_blocks : total_blocks;
+    k_bin<<<(unsigned)grid, kBinThreads, 0, st>>>(g, s, b, total_blocks);
     return cudaGetLastError();
 }
 

@@ -167,7 +167,8 @@ lcc_status encode_batch(lcc_ctx *c, int kind, int nframes, const int *slots, uin
     return encode_tail(c, b);
 }
 
-lcc_status bin_frames(lcc_ctx *c, int nframes, const int *slots, const float *const *d_pts, const int64_t *n) {
+lcc_status bin_frames(lcc_ctx *c, int nframes, const int *slots, const float *const *d_pts, const int64_t *n,
+                      long long max_blocks) {
     Batch b;
     memset(&b, 0, sizeof(b));
     b.nframes = nframes;
@@ -189,7 +190,7 @@ lcc_status bin_frames(lcc_ctx *c, int nframes, const int *slots, const float *co
             LCC_CUDA(cudaMemsetAsync(c->s.stats + slots[f], 0, sizeof(DevStats), c->stream));
     }
     b.blk_prefix[nframes] = blocks;
-    LCC_LAUNCH(c, 0, launch_bin(c->g, c->s, b, blocks, c->stream));
+    LCC_LAUNCH(c, 0, launch_bin(c->g, c->s, b, blocks, c->stream, max_blocks));
     return LCC_OK;
 }
 
@@ -280,6 +281,7 @@ lcc_status lcc_create(lcc_ctx **out, const lcc_sensor *sensor, const lcc_params 
     if (!c) return LCC_ERR_CUDA;
     c->sensor = s;
     c->prm = p;
+    c->num_sms = prop.multiProcessorCount;
     c->stream = (cudaStream_t)cuda_stream;
     Geometry &g = c->g;
     g.H = s.rows;
@@ -558,8 +560,12 @@ namespace {
 // where their binning and first fit pass follow, so the copies overlap the key frame's encode.
 lcc_status encode_sequence(lcc_ctx *c, int32_t nframes, int32_t key_index, const double *poses,
                            const float *const *d_pts, const int64_t *n, uint8_t *const *d_out, const uint64_t *cap,
-                           uint64_t *out_bytes, lcc_keyframe *kf, const float *const *h_pts) {
+                           uint64_t *out_bytes, lcc_keyframe *kf, const float *const *h_pts,
+                           bool via_link = false) {
     if (!c || !poses || key_index < 0 || key_index >= nframes) return LCC_ERR_INVALID_ARG;
+    // points read in place over the host link: a binning grid of two CTAs per SM keeps enough
+    // reads in flight for the link and leaves the rest of the SMs to the key frame's kernels
+    const long long bin_cap = via_link ? 2LL * c->num_sms : 0LL;
     if (kf && kf->ctx != c) return LCC_ERR_INVALID_ARG;
     lcc_status st = check_frames(c, nframes, d_pts, n, d_out, cap);
     if (st != LCC_OK) return st;
@@ -639,13 +645,13 @@ lcc_status encode_sequence(lcc_ctx *c, int32_t nframes, int32_t key_index, const
         // key frame: binning and fit
         c->stream = c->kstream;
         if (!h2d(key_index, c->kstream)) return LCC_ERR_CUDA;
-        if ((st = bin_frames(c, 1, &kslot, &d_pts[key_index], &n[key_index])) != LCC_OK) return st;
+        if ((st = bin_frames(c, 1, &kslot, &d_pts[key_index], &n[key_index], bin_cap)) != LCC_OK) return st;
         LCC_LAUNCH(c, 1, launch_fit(c->g, c->s, bk, pk, c->stream));
         // P frames: binning, spatial fits (and the rest of their rounds), run pre-test
         c->stream = c->side;
         for (int q = 0; q < np; q++)
             if (!h2d(pslots[q], c->side)) return LCC_ERR_CUDA;
-        if ((st = bin_frames(c, np, pslots, pdp, pn)) != LCC_OK) return st;
+        if ((st = bin_frames(c, np, pslots, pdp, pn, bin_cap)) != LCC_OK) return st;
         LCC_LAUNCH(c, 1, launch_fit(c->g, c->s, bp, pp, c->stream));
         if (c->g.schedule >= 1)
             LCC_LAUNCH_N(c, 3, queued_round_kernels(c->g, bp), launch_queued_rounds(c->g, c->s, bp, c->stream));
@@ -772,7 +778,7 @@ lcc_status lcc_encode_sequence_host(lcc_ctx *c, int32_t nframes, int32_t key_ind
         po += align256((size_t)cap[f]);
     }
     lcc_status st = encode_sequence(c, nframes, key_index, poses, dp, n, dout, cap, (uint64_t *)c->d_stage_bytes,
-                                    nullptr, in_mapped ? nullptr : h_pts);
+                                    nullptr, in_mapped ? nullptr : h_pts, in_mapped);
     if (st != LCC_OK) return st;
     if (out_mapped) {
         CopyOut co;

@@ -54,6 +54,7 @@ struct lcc_ctx {
     lcc::DecTile *d_dec = nullptr;
     std::vector<float> h_tables;  // ce, se, ct, st, rbc, rbs, cbc, cbs
     int slots = 0;
+    int num_sms = 0;   // SMs of the context's device
     uint64_t max_bytes = 0;
     int last_nframes = 0;
     // profiling
@@ -82,7 +83,8 @@ bool aligned16(const void *p);
 // Reads and clears the device error word (synchronous).
 lcc_status latched(lcc_ctx *c);
 // Bin frames d_pts[f] into slots[f] (their stats are reset first).
-lcc_status bin_frames(lcc_ctx *c, int nframes, const int *slots, const float *const *d_pts, const int64_t *n);
+lcc_status bin_frames(lcc_ctx *c, int nframes, const int *slots, const float *const *d_pts, const int64_t *n,
+                      long long max_blocks = 0);
 // Fit, merge, scan and pack frames already binned into slots[f].  kf[f] (P frames) is the key-frame
 // plane table frame f is coded against; kf_out[f] (key frames) receives frame f's coding planes;
 // nbytes_out[f], when given, receives frame f's stream size in device memory; prop[f], when given,

@@ -374,8 +374,11 @@ __device__ __forceinline__ uint32_t get_bits(const uint32_t *w, uint64_t pos, in
 // host-side launchers (one per kernel file)
 // ------------------------------------------------------------------------
 
+// max_blocks > 0 caps the grid (a CTA then takes several chunks of points): for points read
+// over the host link, whose reads are link-bound, so that the binning does not occupy every
+// SM's thread slots while other kernels wait for them.
 cudaError_t launch_bin(const Geometry &g, const Scratch &s, const Batch &b, long long total_blocks,
-                       cudaStream_t st);
+                       cudaStream_t st, long long max_blocks = 0);
 cudaError_t launch_range_image(const Geometry &g, const uint32_t *rimg, float *range, uint32_t *valid,
                                cudaStream_t st);
 cudaError_t launch_fit(const Geometry &g, const Scratch &s, const Batch &b, const Poses &p, cudaStream_t st);
