@@ -134,12 +134,11 @@ __global__ void __launch_bounds__(kMergeThreads) k_merge(Geometry g, Scratch s, 
         if (row[c].status == S_FIT) {
             const int hz = min(hzmax, TC - 1 - c);
             uint32_t m = 0u;
-#pragma unroll 8
-            for (int j = 0; j < 32; j++) {
-                if (j < hz) {
-                    const RowRec &h1 = row[c + 1 + j];
-                    if (((h1.amask >> j) & 1u) && h1.status != S_TEMPORAL) m |= 1u << j;
-                }
+#pragma unroll 4
+            for (int j = 0; j < hz; j++) {
+                // amask and the status byte of follower c + 1 + j in one 8-byte load
+                const uint2 w = *reinterpret_cast<const uint2 *>(&row[c + 1 + j].amask);
+                if (((w.x >> j) & 1u) && (w.y & 0xffu) != S_TEMPORAL) m |= 1u << j;
             }
             k += (m == 0xFFFFFFFFu) ? 32 : __ffs(~m) - 1;   // consecutive joins from j = 0
         }
@@ -173,21 +172,29 @@ __global__ void __launch_bounds__(kMergeThreads) k_merge(Geometry g, Scratch s, 
         jmp[c] = open ? (uint16_t)(0x8000 | k) : (uint16_t)(k < TC ? nextfit[k] : TC);
     }
     __syncthreads();
-    // (C) the greedy walk.  Every thread follows the same chain (uniform values read from
-    // shared memory); past the look-behind horizon the whole block tests the next kStepTiles
-    // tiles against the run's plane in one step, kEL lanes per tile.
+    // (C) the greedy walk.  Warp 0 follows the chain through the runs that end inside the
+    // look-behind horizon (one shared-memory load per run) and hands the block the first run
+    // that reaches past it; there the whole block tests the next kStepTiles tiles against the
+    // run's plane in one step, kEL lanes per tile, and the walk resumes after the run.
     {
         __shared__ uint32_t s_fail[kMergeThreads / 32];
+        __shared__ int s_walk;   // walk position handed from warp 0 to the block
         bool staged = false;
         int st = nextfit[0];
-        while (st < TC) {
-            const uint32_t jv = jmp[st];
-            if (!(jv & 0x8000u)) {
-                if (tid == 0) runend[st] = reach[st];
-                st = (int)jv;
-                continue;
+        for (;;) {
+            if (warp == 0) {
+                while (st < TC) {
+                    const uint32_t jv = jmp[st];
+                    if (jv & 0x8000u) break;
+                    if (lane == 0) runend[st] = reach[st];
+                    st = (int)jv;
+                }
+                if (lane == 0) s_walk = st;
             }
-            int k = (int)(jv & 0x7FFFu);
+            __syncthreads();
+            st = s_walk;
+            if (st >= TC) break;
+            int k = (int)(jmp[st] & 0x7FFFu);
             bool open = true;
             if (kStage && !staged) {
                 // the tile row's ranges, per tile in raster order (stride PX + 1), and its ray directions;
@@ -285,6 +292,7 @@ __global__ void __launch_bounds__(kMergeThreads) k_merge(Geometry g, Scratch s, 
             }
             if (tid == 0) runend[st] = (uint16_t)k;
             st = k < TC ? nextfit[k] : TC;
+            __syncthreads();   // every thread has read s_walk before warp 0 writes it again
         }
     }
     __syncthreads();
