@@ -779,15 +779,13 @@ __global__ void __launch_bounds__(kFitThreads) k_temporal(Geometry g, Scratch s,
 #pragma unroll
     for (int m = 0; m < PPL; m++) {
         const int k = l + L * m, i = i0 + k / TW_, j = j0 + k % TW_;
+        const bool in = i < g.H && j < g.W;
+        const uint32_t bits = in ? __ldg(rimg + (size_t)i * g.W + j) : kEmptyBits;
+        beam(g, in ? i : 0, in ? j : 0, pux[m], puy[m], puz[m]);   // issued beside the range load
         pr[m] = 0.f;
-        pux[m] = puy[m] = puz[m] = 0.f;
-        if (i < g.H && j < g.W) {
-            const uint32_t bits = __ldg(rimg + (size_t)i * g.W + j);
-            if (bits_valid(bits)) {
-                pr[m] = __uint_as_float(bits);
-                beam(g, i, j, pux[m], puy[m], puz[m]);
-                V.set(k);
-            }
+        if (bits_valid(bits)) {
+            pr[m] = __uint_as_float(bits);
+            V.set(k);
         }
     }
 #pragma unroll
@@ -922,13 +920,14 @@ __global__ void __launch_bounds__(kFitThreads) k_lookbehind(Geometry g, Scratch 
     for (int k = j; k < PX; k += LPT) {
         float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
         const int i = i0 + k / TW_, jj = j0 + k % TW_;
-        if (live && i < g.H && jj < g.W) {
-            const uint32_t bits = __ldg(rimg + (size_t)i * g.W + jj);
-            if (bits_valid(bits)) {
-                beam(g, i, jj, v.x, v.y, v.z);
-                v.w = __uint_as_float(bits);
-                nv++;
-            }
+        const bool in = live && i < g.H && jj < g.W;
+        const uint32_t bits = in ? __ldg(rimg + (size_t)i * g.W + jj) : kEmptyBits;
+        beam(g, in ? i : 0, in ? jj : 0, v.x, v.y, v.z);   // issued beside the range load
+        if (bits_valid(bits)) {
+            v.w = __uint_as_float(bits);
+            nv++;
+        } else {
+            v = make_float4(0.f, 0.f, 0.f, 0.f);
         }
         s_px[lt][k] = v;
     }

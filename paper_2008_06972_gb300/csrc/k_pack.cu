@@ -107,26 +107,33 @@ __global__ void __launch_bounds__(kPackWarps * 32) k_pack(Geometry g, Scratch s,
 
     bool v[PPL], fit[PPL];
     uint32_t kc[PPL], mc[PPL];
+    // the pixels' ranges and rays: every load issued before any is used (one round trip)
+    uint32_t bits[PPL];
+    float ux[PPL], uy[PPL], uz[PPL];
 #pragma unroll
     for (int m = 0; m < PPL; m++) {
         const int k = sl + LPT * m;
         const int i = tr * TH_ + k / TW_, j = tc * TW_ + k % TW_;
         const bool in = tile_ok && i < g.H && j < g.W;
-        uint32_t bits = kEmptyBits;
-        if (in) {
-            uint32_t *px = rimg + (size_t)i * g.W + j;
-            bits = *px;
-            *px = kEmptyBits;   // ready for the next frame
-        }
-        v[m] = bits_valid(bits);
-        const float r = __uint_as_float(bits);
+        bits[m] = in ? __ldcg(rimg + (size_t)i * g.W + j) : kEmptyBits;
+        beam(g, in ? i : 0, in ? j : 0, ux[m], uy[m], uz[m]);
+    }
+#pragma unroll
+    for (int m = 0; m < PPL; m++) {
+        const int k = sl + LPT * m;
+        const int i = tr * TH_ + k / TW_, j = tc * TW_ + k % TW_;
+        if (tile_ok && i < g.H && j < g.W) rimg[(size_t)i * g.W + j] = kEmptyBits;   // ready for the next frame
+    }
+#pragma unroll
+    for (int m = 0; m < PPL; m++) {
+        v[m] = bits_valid(bits[m]);
+        const float r = __uint_as_float(bits[m]);
         fit[m] = false;
         kc[m] = 0;
         mc[m] = 0;
         if (v[m]) {
-            float ux, uy, uz, e = 0.f;
-            beam(g, i, j, ux, uy, uz);
-            fit[m] = coded && residual(pl, ux, uy, uz, r, g.thr, e);
+            float e = 0.f;
+            fit[m] = coded && residual(pl, ux[m], uy[m], uz[m], r, g.thr, e);
             if (fit[m]) kc[m] = (uint32_t)(quant_res(e, g.q) + g.k_max);
             else mc[m] = quant_raw(r, g.q);
         }
