@@ -443,3 +443,41 @@ def test_largest_resolution_sequence_with_noisy_poses():
     assert info["border"] <= max(2, 0.005 * info["compared"])
     border = _pframe_case(seq, [f for f in range(3) if f != seq.key_index])
     assert border <= 40
+
+
+def test_profiler_counts_every_kernel_and_orders_the_timeline(cfg2_seq):
+    """The profiler's launch counts (what bench.py reports as gpu_launches) are the kernels a
+    sequence call launches: per call, two binnings, two first fit passes, two queued-round
+    launches (fit schedule 3), two run pre-tests, two merges, two packs and one temporal test;
+    the timeline lists the same launches, each ending after it starts."""
+    from paper_2008_06972_gb300 import lcc
+    seq = cfg2_seq
+    n = len(seq.frames)
+    c = H.ctx(seq.sensor, max_batch=16, fit_schedule=3)
+    ds = [H.to_dev(p) for p in seq.frames]
+    outs = [H.out_buf(c) for _ in range(n)]
+    nb = torch.zeros(n, dtype=torch.int64, device="cuda")
+    call = lambda: c.lcc_encode_sequence(seq.key_index, seq.poses, ds, [len(p) for p in seq.frames], outs,
+                                         [o.numel() for o in outs], nb, None)
+    call()
+    assert c.lcc_sync() == 0
+    c.lcc_set_profiling(True)
+    for _ in range(3):
+        call()
+    assert c.lcc_sync() == 0
+    times = c.lcc_kernel_times()
+    tl = c.lcc_kernel_timeline()
+    c.lcc_set_profiling(False)
+    per_call = {"bin": 2, "fit": 2, "rounds": 2, "lookbehind": 2, "merge": 2, "pack": 2, "temporal": 1}
+    assert {k: v[0] for k, v in times.items()} == {k: 3 * v for k, v in per_call.items()}
+    assert len(tl) == 3 * sum(per_call.values())
+    assert all(t1 >= t0 >= 0.0 for _, t0, t1 in tl)
+    # in issue order per call; the P frames' merge and pack follow their temporal test on one stream
+    k = sum(per_call.values())
+    for i in range(3):
+        chunk = tl[i * k:(i + 1) * k]
+        names = [nm for nm, _, _ in chunk]
+        assert names[0] == "bin" and names.count("temporal") == 1
+        it = names.index("temporal")
+        assert names[it + 1:] == ["merge", "pack"]
+        assert chunk[it + 1][1] >= chunk[it][2] - 1e-3 and chunk[it + 2][1] >= chunk[it + 1][2] - 1e-3
