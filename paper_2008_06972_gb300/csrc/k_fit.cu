@@ -1,10 +1,15 @@
 // Per-tile plane fitting (Sec. III-C) and the relaxed-plane temporal test
 // (Sec. III-D).
 //
-// One thread owns one tile: it reads the tile's pixels from the range image
-// (L2/L1), forms the points p = r * u_ij in fp32, and runs the whole iterative
-// fit itself, so every FP64 instruction of the plane solve carries up to 32
-// tiles (GB300's FP64 pipe is the scarce resource of this kernel).
+// First pass (k_fit_first): one thread owns one tile: it reads the tile's
+// pixels from the range image (L2/L1), forms the points p = r * u_ij in fp32,
+// and runs the fit itself, so every instruction of the plane solve carries up
+// to 32 tiles.  Under the default schedule the pass runs one round; the few
+// tiles that need more (5% on an HDL-64E frame) are queued and finish in one
+// launch of k_fit_round with a group of lanes per tile, which splits each
+// round's pixel work.  Both sum a tile's moments in the same order (pixel
+// chunks summed left to right, FitLanes), so every schedule gives the same
+// records.
 //
 // Spatial fit, per round: anchor-shifted moments q = p - a (a = the tile's
 // first valid point) are accumulated in float-float (TwoSum / exact products),
@@ -16,19 +21,17 @@
 // The fp32 plane is tested on every valid pixel with the along-ray residual to
 // give the next inlier set.
 //
-// Temporal test (P frames, before the spatial fit): the anchor is moved to
-// key-frame coordinates (Eq. 6), binned (Eq. 1-2) into the key frame's grid,
-// and the K tile's coding plane normal is rotated into P coordinates; the
-// offset c' = mean(n'.p) is refit over the current set with the same rounds.
+// Temporal test (P frames): the anchor is moved to key-frame coordinates
+// (Eq. 6), binned (Eq. 1-2) into the key frame's grid, and the K tile's coding
+// plane normal is rotated into P coordinates; the offset c' = mean(n'.p) is
+// refit over the current set with the same rounds.  It runs before the
+// spatial fit in the first pass (per thread), or after the spatial fits in
+// k_temporal (a lane group per tile) when lcc_encode_sequence has fitted the P
+// frames beside the key frame.
 //
 // Run pre-test (k_lookbehind): each tile tests itself against the planes of
 // the fitted tiles to its left, so the run-growth walker rarely has to touch
 // pixels.
-//
-// Work is split so the FP64 solves run in dense warps: a first pass over all
-// tiles does the temporal test (P frames) or the first spatial round (key
-// frames); tiles that need a (further) spatial round are queued and each
-// round kernel processes only the queue.
 #include <algorithm>
 
 #include "ffmath.cuh"
