@@ -52,6 +52,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batched", action="store_true", help="skip the uneven multi-sequence batch")
     ap.add_argument("--no-learned", action="store_true", help="skip the learned-proposal section")
+    ap.add_argument("--no-sweep", action="store_true", help="skip the tile / threshold sweep")
     ap.add_argument("--train-steps", type=int, default=300)
     ap.add_argument("--train-seqs", type=int, default=6)
     return ap.parse_args()
@@ -360,6 +361,71 @@ def run_batched(args, stream, hbm):
         "speedup_vs_plain": plain_ms / ms,
         "l2": "inputs (2.3 GB) larger than L2", "setup_s": {"generate": gen_s, "autotune": tune_s},
     }
+
+
+def run_sweep(args, stream, seq, d_pts, flush):
+    """The HDL-64E sequence under the swept parameters (tiles 4x4 and 8x8, fit thresholds 0.02,
+    0.05 and 0.10 m, q 0.02 m): device throughput (CUDA events, L2 flushed between steps),
+    compression ratio, tile modes and the max decode error of every frame."""
+    import torch
+    from paper_2008_06972_gb300 import lcc
+    n_frames = len(seq.frames)
+    n = [len(f) for f in seq.frames]
+    pts = sum(n)
+    H, W = seq.sensor.rows, seq.sensor.cols
+    steps = max(10, min(args.steps, 50))
+    rows = []
+    for th, tw in ((4, 4), (8, 8)):
+        for thr in (0.02, 0.05, 0.10):
+            ctx = lcc.Context(seq.sensor, lcc.default_params(tile_h=th, tile_w=tw, fit_thr_m=thr,
+                                                            max_batch=max(16, n_frames)), stream=stream)
+            cap = ctx.max_encoded_bytes
+            outs = [torch.zeros(cap, dtype=torch.uint8, device="cuda") for _ in range(n_frames)]
+            nb = torch.zeros(n_frames, dtype=torch.int64, device="cuda")
+            kf = lcc.Keyframe(ctx)
+
+            def step():
+                ctx.lcc_encode_sequence(seq.key_index, seq.poses, d_pts, n, outs, [cap] * n_frames, nb, kf)
+
+            for _ in range(3):
+                step()
+            evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+            torch.cuda.synchronize()
+            for k in range(steps):
+                flush.zero_()
+                evs[k][0].record(stream)
+                step()
+                evs[k][1].record(stream)
+            torch.cuda.synchronize()
+            assert ctx.lcc_sync() == lcc.OK
+            ms = float(np.mean([a.elapsed_time(b) for a, b in evs]))
+            sizes = nb.cpu().numpy()
+            modes = {"raw": 0, "run": 0, "temporal": 0}
+            for f in range(n_frames):
+                st_f = ctx.lcc_last_stats(f)
+                modes["raw"] += st_f["tiles_raw"]
+                modes["run"] += st_f["tiles_run_start"] + st_f["tiles_run_cont"]
+                modes["temporal"] += st_f["tiles_temporal"]
+            ref = torch.empty(H * W, dtype=torch.float32, device="cuda")
+            dec = torch.empty(H * W, dtype=torch.float32, device="cuda")
+            kfd = lcc.Keyframe(ctx)
+            ctx.lcc_keyframe_from_stream(outs[seq.key_index], int(sizes[seq.key_index]), kfd)
+            err = 0.0
+            for f in range(n_frames):
+                ctx.lcc_range_image(d_pts[f], n[f], ref, None)
+                isk = f == seq.key_index
+                ctx.lcc_decode(outs[f], int(sizes[f]), None if isk else kfd, None if isk else seq.poses[f], dec,
+                               None, None)
+                assert ctx.lcc_sync() == lcc.OK
+                m = ref > 0
+                if bool(m.any()):
+                    err = max(err, float((dec[m] - ref[m]).abs().max().item()))
+            rows.append({"tile": f"{th}x{tw}", "thr_m": thr, "mpts_per_s": round(pts / (ms * 1e-3) / 1e6, 1),
+                         "ms_per_step": round(ms, 4), "compression_ratio": round(12.0 * pts / float(sizes.sum()), 3),
+                         "max_decode_error_m": err, "tile_modes": modes})
+            del kf, kfd, ctx
+    return {"workload": WORKLOAD.split(",")[0] + ", swept tiles and thresholds, q 0.02 m", "steps": steps,
+            "rows": rows}
 
 
 def run_learned(args, stream):
@@ -706,6 +772,7 @@ def main():
             "path": {"alg_bytes_per_step": path_bytes, "achieved": path_bytes / (ms_step * 1e-3) / 1e9,
                      "frac": path_bytes / (ms_step * 1e-3) / 1e9 / hbm}}
 
+    sweep = None if args.no_sweep or world > 1 else run_sweep(args, stream, seq, d_pts, flush)
     batched = None if args.no_batched else run_batched(args, stream, hbm)
     learned = None if args.no_learned else run_learned(args, stream)
 
@@ -733,6 +800,7 @@ def main():
             "bytes_per_step": total_bytes,
             "kernel_ms_per_step": {k: v[1] / args.steps for k, v in ktimes.items()},
             "roofline": roof,
+            "sweep": sweep,
             "batched": batched,
             "learned": learned,
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(16 * pts_step),
