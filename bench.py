@@ -718,6 +718,34 @@ def main():
             max_err = max(max_err, float((dec[m] - ref[m]).abs().max().item()))
     total_bytes = int(out_sizes.sum())
 
+    # ---- decode throughput: the step's streams back to ranges, points and occupancy bitmaps ----
+    xyz = torch.empty(H * W * 4, dtype=torch.float32, device="cuda")
+    valid = torch.empty((H * W + 31) // 32, dtype=torch.int32, device="cuda")
+    sizes = [int(x) for x in out_sizes]
+
+    def decode_step():
+        ctx.lcc_keyframe_from_stream(d_out[seq.key_index], sizes[seq.key_index], kfd)
+        for f in range(n_frames):
+            isk = f == seq.key_index
+            ctx.lcc_decode(d_out[f], sizes[f], None if isk else kfd, None if isk else seq.poses[f], dec, xyz, valid)
+
+    for _ in range(3):
+        decode_step()
+    assert ctx.lcc_sync() == lcc.OK
+    dec_steps = max(5, min(args.steps, 50))
+    dev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(dec_steps)]
+    for k in range(dec_steps):
+        flush.zero_()
+        dev[k][0].record(stream)
+        decode_step()
+        dev[k][1].record(stream)
+    torch.cuda.synchronize()
+    assert ctx.lcc_sync() == lcc.OK
+    dec_ms = float(np.mean([a.elapsed_time(b) for a, b in dev]))
+    decode = {"workload": "the step's 10 streams: key-frame planes from its stream, then every frame decoded to "
+                          "range, xyz and occupancy bitmap", "steps": dec_steps, "ms_per_step": dec_ms,
+              "mpts_per_s": pts_step / (dec_ms * 1e-3) / 1e6}
+
     # ---- end to end through the C ABI with HOST buffers (pinned) ----
     h_pts = [torch.from_numpy(f).pin_memory() for f in seq.frames]
     h_out = [torch.zeros(cap, dtype=torch.uint8).pin_memory() for _ in range(n_frames)]
@@ -800,6 +828,7 @@ def main():
             "bytes_per_step": total_bytes,
             "kernel_ms_per_step": {k: v[1] / args.steps for k, v in ktimes.items()},
             "roofline": roof,
+            "decode": decode,
             "sweep": sweep,
             "batched": batched,
             "learned": learned,

@@ -26,6 +26,19 @@ __device__ __forceinline__ uint32_t rd_u32(const uint8_t *p) {
 
 __device__ __forceinline__ uint32_t dwords(uint64_t bits) { return (uint32_t)((bits + 31) >> 5); }
 
+// Set bits of the LSB-first bit string w in [pos, pos + len).
+__device__ __forceinline__ uint32_t popc_range(const uint32_t *w, uint64_t pos, uint32_t len) {
+    uint32_t n = 0;
+    while (len) {
+        const uint32_t sh = (uint32_t)(pos & 31), take = min(32u - sh, len);
+        const uint32_t m = take == 32 ? 0xFFFFFFFFu : ((1u << take) - 1u);
+        n += __popc((w[pos >> 5] >> sh) & m);
+        pos += take;
+        len -= take;
+    }
+    return n;
+}
+
 template <int N>
 __device__ __forceinline__ void block_scan(uint32_t (&v)[N], uint32_t (&excl)[N], uint32_t (&tot)[N],
                                            uint32_t (*s_warp)[N]) {
@@ -127,15 +140,11 @@ __global__ void __launch_bounds__(kPrepThreads) k_decode_prep(Geometry g, const 
         const int tr = t / g.TC, tc = t % g.TC;
         if (t < g.NT) {
             mode = (tcw[t >> 3] >> (4 * (t & 7))) & 15u;
+            const int j0 = tc * g.tw, wdt = min(g.tw, g.W - j0);
             for (int rr = 0; rr < g.th; rr++) {
                 const int i = tr * g.th + rr;
                 if (i >= g.H) break;
-                for (int cc = 0; cc < g.tw; cc++) {
-                    const int j = tc * g.tw + cc;
-                    if (j >= g.W) break;
-                    const uint64_t p = (uint64_t)i * g.W + j;
-                    nv += (bm[p >> 5] >> (p & 31)) & 1u;
-                }
+                nv += popc_range(bm, (uint64_t)i * g.W + j0, (uint32_t)wdt);
             }
             if (mode > T_TEMPORAL) bad = 1;
             if (mode == T_EMPTY && nv) bad = 1;
@@ -158,10 +167,7 @@ __global__ void __launch_bounds__(kPrepThreads) k_decode_prep(Geometry g, const 
             if (off_cand + nv > n_cand) {
                 bad = 1;
             } else {
-                for (uint32_t q = 0; q < nv; q++) {
-                    const uint32_t pos = off_cand + q;
-                    fitted += (fitw[pos >> 5] >> (pos & 31)) & 1u;
-                }
+                fitted = popc_range(fitw, off_cand, nv);
             }
         }
         uint32_t v2[2] = {fitted, v5[3] + (coded ? nv - fitted : 0u)};
