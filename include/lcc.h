@@ -211,6 +211,20 @@ lcc_status lcc_keyframe_from_stream(lcc_ctx *ctx, const uint8_t *d_bits, uint64_
 lcc_status lcc_decode(lcc_ctx *ctx, const uint8_t *d_bits, uint64_t nbytes, const lcc_keyframe *kf,
                       const double pose[16], float *d_range, float *d_xyz4, uint32_t *d_valid);
 
+/* Decode a whole sequence encoded by lcc_encode_sequence (frame key_index is
+ * its key frame, poses[16 f] the pose of frame f, as given to the encoder):
+ * the key frame's stream is resolved first (its coding planes), then every P
+ * stream against them, all P streams in one launch (one CTA each), and every
+ * frame is reconstructed.  The same outputs as lcc_keyframe_from_stream plus
+ * lcc_decode per frame.  d_range, d_xyz4 and d_valid are arrays of nframes
+ * device pointers (each array, and each entry, may be NULL); nframes <=
+ * max_batch.  The decoder's per-frame state lives in the context, so a
+ * context decodes one sequence at a time.  Not in the paper as a call: its
+ * decoder is per frame. */
+lcc_status lcc_decode_sequence(lcc_ctx *ctx, int32_t nframes, int32_t key_index, const double *poses,
+                               const uint8_t *const *d_bits, const uint64_t *nbytes, float *const *d_range,
+                               float *const *d_xyz4, uint32_t *const *d_valid);
+
 /* Wait for the context's stream and return (then clear) any latched device error. */
 lcc_status lcc_sync(lcc_ctx *ctx);
 

@@ -79,10 +79,14 @@ __device__ __forceinline__ void block_scan(uint32_t (&v)[N], uint32_t (&excl)[N]
     __syncthreads();
 }
 
-__global__ void __launch_bounds__(kPrepThreads) k_decode_prep(Geometry g, const uint8_t *bits,
-                                                               unsigned long long nbytes, const float4 *kf,
-                                                               Poses ps, DecTile *dt, float4 *kf_out,
-                                                               DecState *state, uint32_t *err, int expect_kind) {
+// One CTA per stream (frame f = blockIdx.y of the batch).
+__global__ void __launch_bounds__(kPrepThreads) k_decode_prep(Geometry g, DecBatch db, const float4 *kf, Poses ps,
+                                                               float4 *kf_out, uint32_t *err, int expect_kind) {
+    const int frame = blockIdx.y;
+    const uint8_t *bits = db.bits[frame];
+    const unsigned long long nbytes = db.nbytes[frame];
+    DecTile *dt = db.dt[frame];
+    DecState *state = reinterpret_cast<DecState *>(dt + g.NT);
     __shared__ uint32_t s_warp5[32][5];
     __shared__ uint32_t s_warp2[32][2];
     __shared__ uint32_t s_h[16];
@@ -191,7 +195,7 @@ __global__ void __launch_bounds__(kPrepThreads) k_decode_prep(Geometry g, const 
                         const float4 kp = kf[kref];
                         if (kp.x == 0.f && kp.y == 0.f && kp.z == 0.f) bad = 1;
                         float o[3];
-                        rotate_normal(ps.m[0], kp.x, kp.y, kp.z, o);
+                        rotate_normal(ps.m[frame], kp.x, kp.y, kp.z, o);
                         pl = make_float4(o[0], o[1], o[2], c);
                     }
                 }
@@ -263,9 +267,13 @@ __global__ void __launch_bounds__(kPrepThreads) k_decode_prep(Geometry g, const 
 }
 
 template <int TH_, int TW_>
-__global__ void __launch_bounds__(kDecWarps * 32) k_decode_px(Geometry g, const uint8_t *bits, const DecTile *dt,
-                                                               const DecState *state, float *range, float4 *xyz,
-                                                               uint32_t *err) {
+__global__ void __launch_bounds__(kDecWarps * 32) k_decode_px(Geometry g, DecBatch db, uint32_t *err) {
+    const int frame = blockIdx.y;
+    const uint8_t *bits = db.bits[frame];
+    const DecTile *dt = db.dt[frame];
+    const DecState *state = reinterpret_cast<const DecState *>(dt + g.NT);
+    float *range = db.range[frame];
+    float4 *xyz = db.xyz[frame];
     constexpr int PX = TH_ * TW_;
     constexpr int LPT = PX < 32 ? PX : 32, PPL = PX / LPT, TPW = 32 / LPT;
     const unsigned FULL = 0xffffffffu;
@@ -335,32 +343,28 @@ __global__ void __launch_bounds__(kDecWarps * 32) k_decode_px(Geometry g, const 
     if (bad) atomicOr(err, E_CORRUPT);
 }
 
-cudaError_t launch_decode_prep(const Geometry &g, const uint8_t *bits, unsigned long long nbytes,
-                               const float4 *kf, const double *pose, DecTile *dt, float4 *kf_out,
-                               uint32_t *err, int expect_kind, const Poses *poses, cudaStream_t st) {
-    (void)pose;
-    k_decode_prep<<<1, kPrepThreads, 0, st>>>(g, bits, nbytes, kf, *poses, dt, kf_out,
-                                              reinterpret_cast<DecState *>(dt + g.NT), err, expect_kind);
+cudaError_t launch_decode_prep(const Geometry &g, const DecBatch &db, int nframes, const float4 *kf,
+                               const Poses &poses, float4 *kf_out, uint32_t *err, int expect_kind, cudaStream_t st) {
+    if (nframes <= 0) return cudaSuccess;
+    k_decode_prep<<<dim3(1, nframes), kPrepThreads, 0, st>>>(g, db, kf, poses, kf_out, err, expect_kind);
     return cudaGetLastError();
 }
 
 template <int TH_, int TW_>
-static cudaError_t launch_px_t(const Geometry &g, const uint8_t *bits, const DecTile *dt, float *range,
-                               float4 *xyz, uint32_t *err, cudaStream_t st) {
+static cudaError_t launch_px_t(const Geometry &g, const DecBatch &db, int nframes, uint32_t *err, cudaStream_t st) {
     constexpr int PX = TH_ * TW_;
     constexpr int TPW = 32 / (PX < 32 ? PX : 32);
     const int tpb = kDecWarps * TPW;
-    k_decode_px<TH_, TW_><<<(g.NT + tpb - 1) / tpb, kDecWarps * 32, 0, st>>>(
-        g, bits, dt, reinterpret_cast<const DecState *>(dt + g.NT), range, xyz, err);
+    k_decode_px<TH_, TW_><<<dim3((g.NT + tpb - 1) / tpb, nframes), kDecWarps * 32, 0, st>>>(g, db, err);
     return cudaGetLastError();
 }
 
-cudaError_t launch_decode_px(const Geometry &g, const uint8_t *bits, const DecTile *dt, float *range,
-                             float4 *xyz, uint32_t *err, cudaStream_t st) {
-    if (g.th == 4 && g.tw == 4) return launch_px_t<4, 4>(g, bits, dt, range, xyz, err, st);
-    if (g.th == 4 && g.tw == 8) return launch_px_t<4, 8>(g, bits, dt, range, xyz, err, st);
-    if (g.th == 8 && g.tw == 8) return launch_px_t<8, 8>(g, bits, dt, range, xyz, err, st);
-    if (g.th == 8 && g.tw == 16) return launch_px_t<8, 16>(g, bits, dt, range, xyz, err, st);
+cudaError_t launch_decode_px(const Geometry &g, const DecBatch &db, int nframes, uint32_t *err, cudaStream_t st) {
+    if (nframes <= 0) return cudaSuccess;
+    if (g.th == 4 && g.tw == 4) return launch_px_t<4, 4>(g, db, nframes, err, st);
+    if (g.th == 4 && g.tw == 8) return launch_px_t<4, 8>(g, db, nframes, err, st);
+    if (g.th == 8 && g.tw == 8) return launch_px_t<8, 8>(g, db, nframes, err, st);
+    if (g.th == 8 && g.tw == 16) return launch_px_t<8, 16>(g, db, nframes, err, st);
     return cudaErrorInvalidValue;
 }
 

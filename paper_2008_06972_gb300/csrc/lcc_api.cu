@@ -342,13 +342,14 @@ lcc_status lcc_create(lcc_ctx **out, const lcc_sensor *sensor, const lcc_params 
     const size_t o_bytes = o_stats + align256(sl * sizeof(DevStats));
     const size_t o_err = o_bytes + align256(sl * 8);
     const size_t o_dec = o_err + 256;
-    const size_t o_lbcnt = o_dec + align256((nt + 4) * sizeof(DecTile));
+    const size_t o_lbcnt = o_dec + align256(sl * (nt + 4) * sizeof(DecTile));   // decoder state per slot
     const size_t o_rowtot = o_lbcnt + align256(sl * nt * 32);
     const size_t o_rowbase = o_rowtot + align256(sl * (size_t)g.TR * 32);
     const size_t o_queue = o_rowbase + align256(sl * (size_t)g.TR * 32);
     const size_t o_qcount = o_queue + align256(4 * sl * nt * 4);
     const size_t o_rowdone = o_qcount + 256;
-    const size_t total = o_rowdone + align256(sl * 4);
+    const size_t o_kplanes = o_rowdone + align256(sl * 4);
+    const size_t total = o_kplanes + align256(nt * sizeof(float4));
     if (cudaMalloc(&c->d_scratch, total) != cudaSuccess) {
         cudaFree(c->d_tables);
         delete c;
@@ -370,6 +371,7 @@ lcc_status lcc_create(lcc_ctx **out, const lcc_sensor *sensor, const lcc_params 
     c->s.queue = (uint32_t *)(base + o_queue);
     c->s.qcount = (uint32_t *)(base + o_qcount);
     c->s.rowdone = (uint32_t *)(base + o_rowdone);
+    c->d_kplanes = (float4 *)(base + o_kplanes);
     c->s.qcap = (uint32_t)(sl * nt);
     cudaMemset(c->d_scratch, 0, total);
     cudaMemset(c->s.rimg, 0xFF, sl * npx * 4);
@@ -816,10 +818,28 @@ lcc_status lcc_keyframe_from_stream(lcc_ctx *c, const uint8_t *d_bits, uint64_t 
     if (!c || !kf || kf->ctx != c || !d_bits || !aligned16(d_bits)) return LCC_ERR_INVALID_ARG;
     Poses p;
     memset(&p, 0, sizeof(p));
-    LCC_LAUNCH(c, 5, launch_decode_prep(c->g, d_bits, nbytes, nullptr, nullptr, c->d_dec, kf->planes, c->s.err, 0,
-                                        &p, c->stream));
+    DecBatch db;
+    memset(&db, 0, sizeof(db));
+    db.bits[0] = d_bits;
+    db.nbytes[0] = nbytes;
+    db.dt[0] = dec_slot(c, 0);
+    LCC_LAUNCH(c, 5, launch_decode_prep(c->g, db, 1, nullptr, p, kf->planes, c->s.err, 0, c->stream));
     return LCC_OK;
 }
+
+namespace {
+
+// The occupancy bitmap of a stream is its first section: copied as it is (a stream too short to
+// hold it is latched as corrupt by the prep kernel).
+lcc_status copy_valid(lcc_ctx *c, const uint8_t *d_bits, uint64_t nbytes, uint32_t *d_valid) {
+    if (!d_valid) return LCC_OK;
+    const size_t words = ((size_t)c->g.H * c->g.W + 31) / 32;
+    if (nbytes >= (uint64_t)kHeaderBytes + 4 * words)
+        LCC_CUDA(cudaMemcpyAsync(d_valid, d_bits + kHeaderBytes, 4 * words, cudaMemcpyDeviceToDevice, c->stream));
+    return LCC_OK;
+}
+
+}  // namespace
 
 lcc_status lcc_decode(lcc_ctx *c, const uint8_t *d_bits, uint64_t nbytes, const lcc_keyframe *kf,
                       const double pose[16], float *d_range, float *d_xyz4, uint32_t *d_valid) {
@@ -829,17 +849,63 @@ lcc_status lcc_decode(lcc_ctx *c, const uint8_t *d_bits, uint64_t nbytes, const 
     Poses p;
     memset(&p, 0, sizeof(p));
     if (pose) memcpy(p.m[0], pose, 16 * sizeof(double));
-    LCC_LAUNCH(c, 5, launch_decode_prep(c->g, d_bits, nbytes, kf ? kf->planes : nullptr, nullptr, c->d_dec, nullptr,
-                                        c->s.err, kf ? 1 : 0, &p, c->stream));
-    LCC_LAUNCH(c, 6, launch_decode_px(c->g, d_bits, c->d_dec, d_range, reinterpret_cast<float4 *>(d_xyz4), c->s.err,
-                                      c->stream));
-    if (d_valid) {
-        // a stream too short to hold the bitmap is latched as corrupt by the prep kernel
-        const size_t words = ((size_t)c->g.H * c->g.W + 31) / 32;
-        if (nbytes >= (uint64_t)kHeaderBytes + 4 * words)
-            LCC_CUDA(cudaMemcpyAsync(d_valid, d_bits + kHeaderBytes, 4 * words, cudaMemcpyDeviceToDevice,
-                                     c->stream));
+    DecBatch db;
+    memset(&db, 0, sizeof(db));
+    db.bits[0] = d_bits;
+    db.nbytes[0] = nbytes;
+    db.dt[0] = dec_slot(c, 0);
+    db.range[0] = d_range;
+    db.xyz[0] = reinterpret_cast<float4 *>(d_xyz4);
+    LCC_LAUNCH(c, 5, launch_decode_prep(c->g, db, 1, kf ? kf->planes : nullptr, p, nullptr, c->s.err, kf ? 1 : 0,
+                                        c->stream));
+    LCC_LAUNCH(c, 6, launch_decode_px(c->g, db, 1, c->s.err, c->stream));
+    return copy_valid(c, d_bits, nbytes, d_valid);
+}
+
+lcc_status lcc_decode_sequence(lcc_ctx *c, int32_t nframes, int32_t key_index, const double *poses,
+                               const uint8_t *const *d_bits, const uint64_t *nbytes, float *const *d_range,
+                               float *const *d_xyz4, uint32_t *const *d_valid) {
+    if (!c || !poses || !d_bits || !nbytes || nframes < 1 || nframes > c->slots || key_index < 0 ||
+        key_index >= nframes)
+        return LCC_ERR_INVALID_ARG;
+    for (int f = 0; f < nframes; f++) {
+        if (!d_bits[f] || !aligned16(d_bits[f])) return LCC_ERR_INVALID_ARG;
+        if (d_xyz4 && d_xyz4[f] && !aligned16(d_xyz4[f])) return LCC_ERR_INVALID_ARG;
     }
+    DecBatch dk, dp;
+    memset(&dk, 0, sizeof(dk));
+    memset(&dp, 0, sizeof(dp));
+    Poses pk, pp;
+    memset(&pk, 0, sizeof(pk));
+    memset(&pp, 0, sizeof(pp));
+    dk.bits[0] = d_bits[key_index];
+    dk.nbytes[0] = nbytes[key_index];
+    dk.dt[0] = dec_slot(c, key_index);
+    dk.range[0] = d_range ? d_range[key_index] : nullptr;
+    dk.xyz[0] = d_xyz4 ? reinterpret_cast<float4 *>(d_xyz4[key_index]) : nullptr;
+    int np = 0;
+    for (int f = 0; f < nframes; f++) {
+        if (f == key_index) continue;
+        dp.bits[np] = d_bits[f];
+        dp.nbytes[np] = nbytes[f];
+        dp.dt[np] = dec_slot(c, f);
+        dp.range[np] = d_range ? d_range[f] : nullptr;
+        dp.xyz[np] = d_xyz4 ? reinterpret_cast<float4 *>(d_xyz4[f]) : nullptr;
+        memcpy(pp.m[np], poses + 16 * (size_t)f, 16 * sizeof(double));
+        np++;
+    }
+    // the key frame's stream gives its coding planes, then all P streams are resolved against them
+    // in one launch (a CTA per stream) and reconstructed in one launch
+    LCC_LAUNCH(c, 5, launch_decode_prep(c->g, dk, 1, nullptr, pk, c->d_kplanes, c->s.err, 0, c->stream));
+    LCC_LAUNCH(c, 6, launch_decode_px(c->g, dk, 1, c->s.err, c->stream));
+    LCC_LAUNCH(c, 5, launch_decode_prep(c->g, dp, np, c->d_kplanes, pp, nullptr, c->s.err, 1, c->stream));
+    LCC_LAUNCH(c, 6, launch_decode_px(c->g, dp, np, c->s.err, c->stream));
+    if (d_valid)
+        for (int f = 0; f < nframes; f++)
+            if (d_valid[f]) {
+                const lcc_status st = copy_valid(c, d_bits[f], nbytes[f], d_valid[f]);
+                if (st != LCC_OK) return st;
+            }
     return LCC_OK;
 }
 

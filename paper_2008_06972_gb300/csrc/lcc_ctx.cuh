@@ -51,7 +51,8 @@ struct lcc_ctx {
     lcc::Scratch s{};
     void *d_tables = nullptr;
     void *d_scratch = nullptr;
-    lcc::DecTile *d_dec = nullptr;
+    lcc::DecTile *d_dec = nullptr;      // decoder state: per slot NT DecTiles, then a DecState
+    float4 *d_kplanes = nullptr;        // key-frame coding planes of lcc_decode_sequence
     std::vector<float> h_tables;  // ce, se, ct, st, rbc, rbs, cbc, cbs
     int slots = 0;
     int num_sms = 0;   // SMs of the context's device
@@ -73,6 +74,9 @@ struct lcc_ctx {
     unsigned long long *d_stage_bytes = nullptr;
     unsigned long long *h_pinned = nullptr;   // page-locked: stream sizes (kMaxBatch) + error word
 };
+
+// Decoder state of batch slot f (NT DecTiles, then the slot's DecState).
+inline lcc::DecTile *dec_slot(lcc_ctx *c, int f) { return c->d_dec + (size_t)f * ((size_t)c->g.NT + 4); }
 
 namespace lcc {
 namespace api {

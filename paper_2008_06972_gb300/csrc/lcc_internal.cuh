@@ -400,11 +400,18 @@ inline int queued_round_kernels(const Geometry &g, const Batch &b) {
 cudaError_t launch_merge(const Geometry &g, const Scratch &s, const Batch &b, cudaStream_t st);
 size_t merge_smem_bytes(int TC);
 cudaError_t launch_pack(const Geometry &g, const Scratch &s, const Batch &b, cudaStream_t st);
-cudaError_t launch_decode_prep(const Geometry &g, const uint8_t *bits, unsigned long long nbytes,
-                               const float4 *kf, const double *pose, DecTile *dt, float4 *kf_out,
-                               uint32_t *err, int expect_kind, const Poses *poses, cudaStream_t st);
+// Streams decoded by one launch (frame f = blockIdx.y): its bytes, its per-tile decoder state
+// (NT DecTiles, then its DecState) and its outputs (range and xyz may be NULL).
+struct DecBatch {
+    const uint8_t *bits[kMaxBatch];
+    unsigned long long nbytes[kMaxBatch];
+    DecTile *dt[kMaxBatch];
+    float *range[kMaxBatch];
+    float4 *xyz[kMaxBatch];
+};
+cudaError_t launch_decode_prep(const Geometry &g, const DecBatch &db, int nframes, const float4 *kf,
+                               const Poses &poses, float4 *kf_out, uint32_t *err, int expect_kind, cudaStream_t st);
 cudaError_t launch_maxdiff(const float *a, const float *b, long long n, uint32_t *out, cudaStream_t st);
-cudaError_t launch_decode_px(const Geometry &g, const uint8_t *bits, const DecTile *dt, float *range,
-                             float4 *xyz, uint32_t *err, cudaStream_t st);
+cudaError_t launch_decode_px(const Geometry &g, const DecBatch &db, int nframes, uint32_t *err, cudaStream_t st);
 
 }  // namespace lcc

@@ -107,6 +107,7 @@ def load(path: str = LIB_PATH):
         "lcc_encode_sequence_host": (i32, [vp, i32, i32, vp, vp, vp, vp, vp, vp]),
         "lcc_keyframe_from_stream": (i32, [vp, vp, u64, vp]),
         "lcc_decode": (i32, [vp, vp, u64, vp, vp, vp, vp, vp]),
+        "lcc_decode_sequence": (i32, [vp, i32, i32, vp, vp, vp, vp, vp, vp]),
         "lcc_sync": (i32, [vp]),
         "lcc_last_stats": (i32, [vp, i32, vp]),
         "lcc_tile_records": (i32, [vp, i32, vp, i64]),
@@ -150,7 +151,7 @@ def exported_symbols() -> list[str]:
     return ["lcc_status_string", "lcc_default_params", "lcc_create", "lcc_destroy", "lcc_max_encoded_bytes",
             "lcc_num_tiles", "lcc_tables", "lcc_range_image", "lcc_keyframe_create", "lcc_keyframe_free",
             "lcc_encode_keyframe", "lcc_encode_keyframe_seeded", "lcc_encode_keyframes", "lcc_encode_pframe", "lcc_encode_pframes", "lcc_encode_sequence",
-            "lcc_encode_sequence_host", "lcc_keyframe_from_stream", "lcc_decode", "lcc_sync", "lcc_last_stats",
+            "lcc_encode_sequence_host", "lcc_keyframe_from_stream", "lcc_decode", "lcc_decode_sequence", "lcc_sync", "lcc_last_stats",
             "lcc_tile_records", "lcc_set_profiling", "lcc_kernel_times", "lcc_kernel_timeline", "lcc_range_image_static", "lcc_net_num_params", "lcc_net_create", "lcc_net_destroy",
             "lcc_net_get_params", "lcc_net_set_params", "lcc_net_tile_inputs", "lcc_net_tile_inputs_batch", "lcc_net_forward", "lcc_net_sync", "lcc_net_gradient",
             "lcc_net_train_step", "lcc_selftest_bounded_wait", "lcc_plan_create", "lcc_plan_update",
@@ -334,6 +335,20 @@ class Context:
             pose_p = pose.ctypes.data
         _check(self.lib.lcc_decode(self.h, _ptr(d_bits), nbytes, kf.h if kf else None, pose_p, _ptr(d_range),
                                    _ptr(d_xyz4), _ptr(d_valid)), "lcc_decode")
+
+    def lcc_decode_sequence(self, key_index: int, poses, d_bits, nbytes, d_range=None, d_xyz4=None, d_valid=None):
+        """Decode the frames of one sequence (device buffers; optional lists of outputs)."""
+        n = len(d_bits)
+        P = ctypes.c_void_p * n
+        pz = np.ascontiguousarray(np.asarray(poses, dtype=np.float64).reshape(n, 16))
+        nb = np.ascontiguousarray(np.asarray(nbytes, dtype=np.uint64))
+
+        def arr(xs):
+            return None if xs is None else P(*[_ptr(x) for x in xs])
+
+        bits_a, rng_a, xyz_a, val_a = arr(d_bits), arr(d_range), arr(d_xyz4), arr(d_valid)
+        _check(self.lib.lcc_decode_sequence(self.h, n, key_index, pz.ctypes.data, bits_a, nb.ctypes.data, rng_a,
+                                            xyz_a, val_a), "lcc_decode_sequence")
 
     def lcc_sync(self) -> int:
         return int(self.lib.lcc_sync(self.h))

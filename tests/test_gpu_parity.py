@@ -481,3 +481,40 @@ def test_profiler_counts_every_kernel_and_orders_the_timeline(cfg2_seq):
         it = names.index("temporal")
         assert names[it + 1:] == ["merge", "pack"]
         assert chunk[it + 1][1] >= chunk[it][2] - 1e-3 and chunk[it + 2][1] >= chunk[it + 1][2] - 1e-3
+
+
+def test_sequence_decode_matches_per_frame_decode(cfg2_seq):
+    """lcc_decode_sequence (key stream first, all P streams in one launch) gives the ranges, points
+    and occupancy of the per-frame decoder bit for bit; a corrupt P stream in the batch is
+    reported."""
+    from paper_2008_06972_gb300 import lcc
+    seq = cfg2_seq
+    n = len(seq.frames)
+    c = H.ctx(seq.sensor, max_batch=16)
+    ds = [H.to_dev(p) for p in seq.frames]
+    outs = [H.out_buf(c) for _ in range(n)]
+    nb = torch.zeros(n, dtype=torch.int64, device="cuda")
+    c.lcc_encode_sequence(seq.key_index, seq.poses, ds, [len(p) for p in seq.frames], outs,
+                          [o.numel() for o in outs], nb, None)
+    assert c.lcc_sync() == 0
+    sizes = [int(x) for x in nb.cpu().numpy()]
+    npx = seq.sensor.rows * seq.sensor.cols
+    new = lambda *shape, dt=torch.float32: [torch.full(shape, -1, dtype=dt, device="cuda") for _ in range(n)]
+    r1, x1, v1 = new(npx), new(npx * 4), new((npx + 31) // 32, dt=torch.int32)
+    kf = lcc.Keyframe(c)
+    c.lcc_keyframe_from_stream(outs[seq.key_index], sizes[seq.key_index], kf)
+    for f in range(n):
+        isk = f == seq.key_index
+        c.lcc_decode(outs[f], sizes[f], None if isk else kf, None if isk else seq.poses[f], r1[f], x1[f], v1[f])
+    assert c.lcc_sync() == 0
+    r2, x2, v2 = new(npx), new(npx * 4), new((npx + 31) // 32, dt=torch.int32)
+    c.lcc_decode_sequence(seq.key_index, seq.poses, outs, sizes, r2, x2, v2)
+    assert c.lcc_sync() == 0
+    for f in range(n):
+        assert torch.equal(r1[f], r2[f]) and torch.equal(x1[f], x2[f]) and torch.equal(v1[f], v2[f]), f
+    bad = outs[(seq.key_index + 1) % n].clone()
+    bad[:4] = 0   # magic number
+    outs2 = list(outs)
+    outs2[(seq.key_index + 1) % n] = bad
+    c.lcc_decode_sequence(seq.key_index, seq.poses, outs2, sizes, r2, None, None)
+    assert c.lcc_sync() == lcc.ERR_CORRUPT
