@@ -235,20 +235,62 @@ __device__ __forceinline__ Moments moments_zero() {
     return m;
 }
 
-// Adds the point p = r u, shifted by the anchor a, to m.
-__device__ __forceinline__ void moments_point(Moments &m, float rr, float ux, float uy, float uz, float ax, float ay,
-                                              float az) {
+// Running moment sums of one pixel chunk: per moment a sum hi of the terms' leading parts,
+// whose rounding errors are caught exactly (TwoSum), and a plain sum lo of those errors and of
+// the terms' own low parts (exact product errors, cross terms).  Cheaper than float-float
+// addition per term; finished into normalised float-float by moments_finish.
+struct MomentAcc {
+    float h[9], l[9];
+};
+
+__device__ __forceinline__ MomentAcc macc_zero() {
+    MomentAcc a;
+#pragma unroll
+    for (int i = 0; i < 9; i++) a.h[i] = a.l[i] = 0.f;
+    return a;
+}
+
+// h + l += p + e, the rounding error of h + p kept exactly (Knuth's TwoSum)
+__device__ __forceinline__ void macc_add(float &h, float &l, float p, float e) {
+    const float s = __fadd_rn(h, p);
+    const float bb = __fsub_rn(s, h);
+    const float err = __fadd_rn(__fsub_rn(h, __fsub_rn(s, bb)), __fsub_rn(p, bb));
+    h = s;
+    l = __fadd_rn(l, __fadd_rn(err, e));
+}
+
+// Adds the point p = r u, shifted by the anchor a (q = p - a exactly, as hi + lo), to m:
+// q, and q_i q_j as p = fl(hi_i hi_j) plus its exact error and the cross terms by fma.
+__device__ __forceinline__ void moments_point(MomentAcc &m, float rr, float ux, float uy, float uz, float ax,
+                                              float ay, float az) {
     const ff qx = two_sum(__fmul_rn(rr, ux), -ax), qy = two_sum(__fmul_rn(rr, uy), -ay),
              qz = two_sum(__fmul_rn(rr, uz), -az);
-    m.s1x = ff_add(m.s1x, qx);
-    m.s1y = ff_add(m.s1y, qy);
-    m.s1z = ff_add(m.s1z, qz);
-    m.sxx = ff_add(m.sxx, ff_mul(qx, qx));
-    m.sxy = ff_add(m.sxy, ff_mul(qx, qy));
-    m.sxz = ff_add(m.sxz, ff_mul(qx, qz));
-    m.syy = ff_add(m.syy, ff_mul(qy, qy));
-    m.syz = ff_add(m.syz, ff_mul(qy, qz));
-    m.szz = ff_add(m.szz, ff_mul(qz, qz));
+    macc_add(m.h[0], m.l[0], qx.hi, qx.lo);
+    macc_add(m.h[1], m.l[1], qy.hi, qy.lo);
+    macc_add(m.h[2], m.l[2], qz.hi, qz.lo);
+    const ff *q[3] = {&qx, &qy, &qz};
+    int k = 3;
+#pragma unroll
+    for (int i = 0; i < 3; i++)
+#pragma unroll
+        for (int j = i; j < 3; j++, k++) {
+            const float a = q[i]->hi, al = q[i]->lo, b = q[j]->hi, bl = q[j]->lo;
+            const float p = __fmul_rn(a, b);
+            const float e = fmaf(a, bl, fmaf(al, b, fmaf(a, b, -p)));
+            macc_add(m.h[k], m.l[k], p, e);
+        }
+}
+
+// The chunk's sums as normalised float-float moments.
+__device__ __forceinline__ Moments moments_finish(const MomentAcc &a) {
+    ff v[9];
+#pragma unroll
+    for (int i = 0; i < 9; i++) v[i] = two_sum(a.h[i], a.l[i]);   // exact whatever the magnitudes
+    Moments m;
+    m.s1x = v[0]; m.s1y = v[1]; m.s1z = v[2];
+    m.sxx = v[3]; m.sxy = v[4]; m.sxz = v[5];
+    m.syy = v[6]; m.syz = v[7]; m.szz = v[8];
+    return m;
 }
 
 __device__ __forceinline__ Moments moments_add(const Moments &a, const Moments &b) {
@@ -393,14 +435,15 @@ struct TileView {
         Moments m = moments_zero();
 #pragma unroll 1
         for (int c = 0; c < L; c++) {
-            Moments part = moments_zero();
+            MomentAcc acc = macc_zero();
 #pragma unroll 2
             for (int k = c * CH; k < (c + 1) * CH; k++) {
                 if (!S.get(k)) continue;
                 float ux, uy, uz;
                 u(k, ux, uy, uz);
-                moments_point(part, r(k), ux, uy, uz, ax, ay, az);
+                moments_point(acc, r(k), ux, uy, uz, ax, ay, az);
             }
+            const Moments part = moments_finish(acc);
             m = c == 0 ? part : moments_add(m, part);
         }
         return solve_moments(m, nS, ax, ay, az, g.solver, &pl, &ratio);
@@ -478,14 +521,15 @@ struct TileLanes {
         return __popcll(I.w0) + __popcll(I.w1);
     }
     __device__ __forceinline__ bool fit(const Mask &S, int nS, float4 &pl, float &ratio) const {
-        Moments part = moments_zero();
+        MomentAcc acc = macc_zero();
 #pragma unroll 2
         for (int k = l * CH; k < (l + 1) * CH; k++) {
             if (!S.get(k)) continue;
             float ux, uy, uz;
             u(k, ux, uy, uz);
-            moments_point(part, r(k), ux, uy, uz, ax, ay, az);
+            moments_point(acc, r(k), ux, uy, uz, ax, ay, az);
         }
+        const Moments part = moments_finish(acc);
         Moments m = moments_shfl(gmask, part, g0);
 #pragma unroll
         for (int c = 1; c < L; c++) m = moments_add(m, moments_shfl(gmask, part, g0 + c));
