@@ -636,7 +636,7 @@ static void section_offsets(const header_t *h, uint64_t off[8]) {
     off[3] = off[2] + 4ull * h->n_runs;
     off[4] = off[3] + 2ull * h->n_temporal;
     off[5] = off[4] + words_for(h->n_cand);
-    off[6] = off[5] + words_for((uint64_t)h->n_fitted * h->w_res);
+    off[6] = off[5] + ((h->flags & 2u) ? 0 : words_for((uint64_t)h->n_fitted * h->w_res));   /* no deltas */
     off[7] = off[6] + words_for((uint64_t)h->n_raw * h->w_raw);
 }
 
@@ -692,7 +692,7 @@ static int header_read(const uint8_t *b, uint64_t nbytes, header_t *h) {
     h->n_raw = rd32(b + 48);
     h->k_max = (int32_t)rd32(b + 52);
     h->total_bytes = rd32(b + 56);
-    if (h->kind > 1 || h->tile_h == 0 || h->tile_w == 0 || h->w_res == 0 || h->w_res > 16 ||
+    if (h->kind > 1 || (h->flags & ~3u) || h->tile_h == 0 || h->tile_w == 0 || h->w_res == 0 || h->w_res > 16 ||
         h->w_raw == 0 || h->w_raw > 24 || !(h->q > 0))
         return ORC_ERR_CORRUPT;
     uint64_t off[8];
@@ -775,7 +775,7 @@ int64_t orc_pack(const orc_sensor *s, const orc_params *prm, int kind, const flo
 
     /* 2. counts */
     h.kind = kind;
-    h.flags = prm->merge_runs ? 1 : 0;
+    h.flags = (prm->merge_runs ? 1u : 0u) | (prm->no_delta ? 2u : 0u);
     h.rows = s->rows;
     h.cols = s->cols;
     h.tile_h = prm->tile_h;
@@ -841,7 +841,9 @@ int64_t orc_pack(const orc_sensor *s, const orc_params *prm, int kind, const flo
                 int in = coded && residual(&cp[4 * t], tp->u[k], tp->r[k], prm->fit_thr_m, &e);
                 if (coded) put_bits(w + off[4], ic++, (uint32_t)in, 1);
                 if (in) {
-                    put_bits(w + off[5], ifit * w_res, (uint32_t)(quant_res(e, prm->quant_m) + k_max), w_res);
+                    /* with deltas the residual code follows; without, the point is the plane's */
+                    if (!prm->no_delta)
+                        put_bits(w + off[5], ifit * w_res, (uint32_t)(quant_res(e, prm->quant_m) + k_max), w_res);
                     ifit++;
                 } else {
                     put_bits(w + off[6], iraw * w_raw, (uint32_t)quant_raw(tp->r[k], prm->quant_m), w_raw);
@@ -1046,7 +1048,8 @@ int orc_decode(const orc_sensor *s, const uint8_t *bits, uint64_t nbytes, const 
                 }
                 if (fitted) {
                     if (ifit >= st.h.n_fitted) { r = ORC_ERR_CORRUPT; break; }
-                    int k = (int)get_bits(st.w + st.off[5], ifit * st.h.w_res, st.h.w_res) - st.h.k_max;
+                    int k = (st.h.flags & 2u) ? 0
+                            : (int)get_bits(st.w + st.off[5], ifit * st.h.w_res, st.h.w_res) - st.h.k_max;
                     ifit++;
                     const float *pl = &cp[4 * t];
                     float dot = fmaf(pl[0], u[0], fmaf(pl[1], u[1], pl[2] * u[2]));

@@ -40,6 +40,8 @@ typedef struct {
     int32_t max_refits;          /* R: refit rounds after the first fit */
     float min_inlier_frac;       /* f_min: inlier share a plane needs (1.0 = all points) */
     int32_t merge_runs;          /* 1: grow runs of tiles horizontally (Sec. III-C) */
+    int32_t no_delta;            /* 1: plane-coded points carry no residual code (Sec. III-C:
+                                    the deltas are dropped, decode error <= threshold) */
 } orc_params;
 
 /* tile codes of the bitstream */

@@ -3,8 +3,9 @@
 Layout (little-endian): a 64-byte header, then 32-bit-word sections in this
 order: occupancy bitmap (rows*cols bits, raster), tile codes (4 bits per tile),
 run planes (4 fp32 words each), temporal records (u32 K-tile index, fp32 c'),
-fitted bits (one per candidate pixel), residual codes (w_res bits, k + k_max),
-raw codes (w_raw bits).  Bits are LSB-first within words.
+fitted bits (one per candidate pixel), residual codes (w_res bits, k + k_max;
+none when flags bit 1, the no-delta mode, is set), raw codes (w_raw bits).  Bits
+are LSB-first within words.
 """
 import numpy as np
 
@@ -30,7 +31,8 @@ def sections(bits) -> dict:
     h = header(bits)
     sizes = [("bitmap", _words(h["rows"] * h["cols"])), ("tiles", _words(4 * h["n_tiles"])),
              ("runs", 4 * h["n_runs"]), ("temporal", 2 * h["n_temporal"]), ("fitted", _words(h["n_cand"])),
-             ("res", _words(h["n_fitted"] * h["w_res"])), ("raw", _words(h["n_raw"] * h["w_raw"]))]
+             ("res", 0 if h["flags"] & 2 else _words(h["n_fitted"] * h["w_res"])),
+             ("raw", _words(h["n_raw"] * h["w_raw"]))]
     w = np.frombuffer(np.asarray(bits, np.uint8)[64:h["total_bytes"]].tobytes(), "<u4")
     out, o = {}, 0
     for name, n in sizes:

@@ -517,3 +517,56 @@ def test_seeded_fit_skip_and_fallbacks():
     far = _prop_for(s, p, rng_img, n, d)
     far[:, 4] += 5.0
     assert O.fit_tiles_seeded(s, p, rng_img, far, -2.944).tobytes() == plain.tobytes()
+
+
+# ------------------------------------------------------------- no-delta mode --
+
+def _no_delta_pair(s, p_kw, pts):
+    pd = O.params(**p_kw)
+    pn = O.params(no_delta=1, **p_kw)
+    bd, kd, fd, md = O.encode_keyframe(s, pd, pts)
+    bn, kn, fn, mn = O.encode_keyframe(s, pn, pts)
+    return bd, bn, kd, kn, md, mn
+
+
+@pytest.mark.parametrize("tile,thr", [((4, 4), 0.05), ((8, 8), 0.02)])
+def test_no_delta_stream_is_the_delta_stream_without_residual_codes(cfg1, tile, thr):
+    """Sec. III-C drops the deltas of plane-coded points: the no-delta stream holds every section
+    of the delta stream except the residual codes, flags bit 1 set, and the same planes."""
+    sen, pts = cfg1
+    s = O.sensor(sen)
+    bd, bn, kd, kn, md, mn = _no_delta_pair(s, dict(tile_h=tile[0], tile_w=tile[1], fit_thr_m=thr), pts)
+    sd, sn = streamfmt.sections(bd), streamfmt.sections(bn)
+    hd, hn = sd["header"], sn["header"]
+    assert hn["flags"] == hd["flags"] | 2 and hd["flags"] & 2 == 0
+    for k in ("n_tiles", "n_valid", "n_runs", "n_temporal", "n_cand", "n_fitted", "n_raw", "w_res", "w_raw", "k_max"):
+        assert hn[k] == hd[k], k
+    for name in ("bitmap", "tiles", "runs", "temporal", "fitted", "raw"):
+        assert np.array_equal(sn[name], sd[name]), name
+    assert len(sn["res"]) == 0 and len(sd["res"]) > 0
+    assert hn["total_bytes"] == hd["total_bytes"] - 4 * len(sd["res"]) == len(bn)
+    assert np.array_equal(kn, kd) and np.array_equal(mn, md)
+
+
+def test_no_delta_decode_lies_on_the_plane_within_the_threshold(cfg1):
+    """Decoded without deltas, a plane-coded point is the plane's intersection with its ray: it
+    differs from the delta decode by exactly its residual code times q, so it is within the
+    threshold of the input range; raw points decode as with deltas."""
+    sen, pts = cfg1
+    s = O.sensor(sen)
+    thr = 0.05
+    bd, bn, *_ = _no_delta_pair(s, dict(fit_thr_m=thr), pts)
+    rng, _, _ = O.range_image(s, pts)
+    dd, xd, _ = O.decode(s, bd)
+    dn, xn, _ = O.decode(s, bn)
+    m = rng > 0
+    assert ((dn > 0) == m).all()
+    assert np.abs(dn[m] - rng[m]).max() <= thr + 1e-5
+    # the pixels whose decode differs are plane-coded; the difference is k q with |k| <= k_max
+    k = streamfmt.residual_codes(bd)
+    diff = (dd - dn)[m]
+    q = np.float32(0.02)
+    assert np.abs(diff).max() <= (np.abs(k).max() + 0.5) * q + 1e-5
+    assert np.count_nonzero(diff) <= np.count_nonzero(k)
+    u = O.beams(s)
+    assert np.abs(xn[..., :3] - dn[..., None] * u).max() == 0
