@@ -365,8 +365,9 @@ def run_batched(args, stream, hbm):
 
 def run_sweep(args, stream, seq, d_pts, flush):
     """The HDL-64E sequence under the swept parameters (tiles 4x4 and 8x8, fit thresholds 0.02,
-    0.05 and 0.10 m, q 0.02 m): device throughput (CUDA events, L2 flushed between steps),
-    compression ratio, tile modes and the max decode error of every frame."""
+    0.05 and 0.10 m, q 0.02 m; and the no-delta mode at 0.02 m): device throughput (CUDA events,
+    L2 flushed between steps), compression ratio, tile modes and the max decode error of every
+    frame."""
     import torch
     from paper_2008_06972_gb300 import lcc
     n_frames = len(seq.frames)
@@ -375,9 +376,11 @@ def run_sweep(args, stream, seq, d_pts, flush):
     H, W = seq.sensor.rows, seq.sensor.cols
     steps = max(10, min(args.steps, 50))
     rows = []
-    for th, tw in ((4, 4), (8, 8)):
-        for thr in (0.02, 0.05, 0.10):
-            ctx = lcc.Context(seq.sensor, lcc.default_params(tile_h=th, tile_w=tw, fit_thr_m=thr,
+    points = [(th, tw, thr, 0) for th, tw in ((4, 4), (8, 8)) for thr in (0.02, 0.05, 0.10)]
+    points += [(4, 4, 0.02, 1), (8, 8, 0.02, 1)]   # the paper's no-delta mode at a 2 cm threshold
+    for th, tw, thr, nd in points:
+        if True:
+            ctx = lcc.Context(seq.sensor, lcc.default_params(tile_h=th, tile_w=tw, fit_thr_m=thr, no_delta=nd,
                                                             max_batch=max(16, n_frames)), stream=stream)
             cap = ctx.max_encoded_bytes
             outs = [torch.zeros(cap, dtype=torch.uint8, device="cuda") for _ in range(n_frames)]
@@ -420,7 +423,7 @@ def run_sweep(args, stream, seq, d_pts, flush):
                 m = ref > 0
                 if bool(m.any()):
                     err = max(err, float((dec[m] - ref[m]).abs().max().item()))
-            rows.append({"tile": f"{th}x{tw}", "thr_m": thr, "mpts_per_s": round(pts / (ms * 1e-3) / 1e6, 1),
+            rows.append({"tile": f"{th}x{tw}", "thr_m": thr, "no_delta": nd, "mpts_per_s": round(pts / (ms * 1e-3) / 1e6, 1),
                          "ms_per_step": round(ms, 4), "compression_ratio": round(12.0 * pts / float(sizes.sum()), 3),
                          "max_decode_error_m": err, "tile_modes": modes})
             del kf, kfd, ctx

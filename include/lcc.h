@@ -65,6 +65,9 @@ typedef struct {
                                  dense warps, one kernel per round; 3: one round per thread, then the
                                  queued tiles' remaining rounds in one dense kernel (same results for
                                  every value) */
+    int32_t no_delta;         /* 1: plane-coded points carry no residual code, the paper's default
+                                 (Sec. III-C drops the deltas): they decode onto their plane, decode
+                                 error <= fit_thr_m; 0 (default here): residual codes, error <= q/2 */
 } lcc_params;
 
 /* Per-frame statistics of the last encode (Fig. 11's categories and more). */

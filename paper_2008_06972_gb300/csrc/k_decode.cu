@@ -18,6 +18,7 @@ struct DecState {
     uint32_t sec[8];
     float q;
     int32_t k_max, w_res, w_raw;
+    int32_t no_delta;   // plane-coded points carry no residual code
 };
 
 __device__ __forceinline__ uint32_t rd_u32(const uint8_t *p) {
@@ -99,8 +100,8 @@ __global__ void __launch_bounds__(kPrepThreads) k_decode_prep(Geometry g, DecBat
         int bad = nbytes < (unsigned long long)kHeaderBytes;
         if (!bad) {
             for (int q = 0; q < 16; q++) s_h[q] = rd_u32(bits + 4 * q);
-            const uint32_t kind = (s_h[1] >> 16) & 0xff;
-            bad |= s_h[0] != kMagic || (s_h[1] & 0xffff) != (uint32_t)kVersion;
+            const uint32_t kind = (s_h[1] >> 16) & 0xff, flags = s_h[1] >> 24;
+            bad |= s_h[0] != kMagic || (s_h[1] & 0xffff) != (uint32_t)kVersion || (flags & ~3u);
             bad |= (int)(s_h[2] & 0xffff) != g.H || (int)(s_h[2] >> 16) != g.W;
             bad |= (int)(s_h[3] & 0xff) != g.th || (int)((s_h[3] >> 8) & 0xff) != g.tw;
             const uint32_t w_res = (s_h[3] >> 16) & 0xff, w_raw = s_h[3] >> 24;
@@ -114,7 +115,7 @@ __global__ void __launch_bounds__(kPrepThreads) k_decode_prep(Geometry g, DecBat
             s_sec[3] = s_sec[2] + 4u * s_h[8];
             s_sec[4] = s_sec[3] + 2u * s_h[9];
             s_sec[5] = s_sec[4] + dwords(s_h[10]);
-            s_sec[6] = s_sec[5] + dwords((uint64_t)s_h[11] * w_res);
+            s_sec[6] = s_sec[5] + ((flags & 2u) ? 0u : dwords((uint64_t)s_h[11] * w_res));   // no deltas: none
             s_sec[7] = s_sec[6] + dwords((uint64_t)s_h[12] * w_raw);
             const unsigned long long total = (unsigned long long)kHeaderBytes + 4ull * s_sec[7];
             bad |= total != s_h[14] || total > nbytes || s_h[8] > (uint32_t)g.NT || s_h[9] > (uint32_t)g.NT ||
@@ -261,6 +262,7 @@ __global__ void __launch_bounds__(kPrepThreads) k_decode_prep(Geometry g, DecBat
         st.k_max = (int32_t)s_h[13];
         st.w_res = (int32_t)((s_h[3] >> 16) & 0xff);
         st.w_raw = (int32_t)(s_h[3] >> 24);
+        st.no_delta = (int32_t)((s_h[1] >> 25) & 1u);
         *state = st;
         if (bad) atomicOr(err, E_CORRUPT);
     }
@@ -326,7 +328,9 @@ __global__ void __launch_bounds__(kDecWarps * 32) k_decode_px(Geometry g, DecBat
         beam(g, ii[m], jj[m], ux, uy, uz);
         if (v[m]) {
             if (fb[m]) {
-                const int k = (int)get_bits(w + st.sec[5], (uint64_t)(d.off_fit + frank) * st.w_res, st.w_res) - st.k_max;
+                const int k = st.no_delta ? 0
+                              : (int)get_bits(w + st.sec[5], (uint64_t)(d.off_fit + frank) * st.w_res, st.w_res) -
+                                    st.k_max;
                 const float dot = fmaf(d.plane.x, ux, fmaf(d.plane.y, uy, __fmul_rn(d.plane.z, uz)));
                 if (!(dot > 1e-3f)) bad = true;
                 r = fmaf((float)k, st.q, __fdiv_rn(d.plane.w, dot));

@@ -209,14 +209,17 @@ __global__ void __launch_bounds__(kPackWarps * 32) k_pack(Geometry g, Scratch s,
         val[m] = fit[m] ? 1u : 0u;
     }
     stage_codes<LPT, PPL>(buf, S::SW, words + L.sec[4], L.sec[5] - L.sec[4], off.cand, coded ? vacc : 0, 1, has, rank, val, sl);
-    // residual codes of plane-coded pixels
+    // residual codes of plane-coded pixels (none in the no-delta mode)
+    if (!g.no_delta) {
 #pragma unroll
-    for (int m = 0; m < PPL; m++) {
-        has[m] = fit[m];
-        rank[m] = frank[m];
-        val[m] = kc[m];
+        for (int m = 0; m < PPL; m++) {
+            has[m] = fit[m];
+            rank[m] = frank[m];
+            val[m] = kc[m];
+        }
+        stage_codes<LPT, PPL>(buf, S::SW, words + L.sec[5], L.sec[6] - L.sec[5], off.fitted, facc, g.w_res, has, rank,
+                              val, sl);
     }
-    stage_codes<LPT, PPL>(buf, S::SW, words + L.sec[5], L.sec[6] - L.sec[5], off.fitted, facc, g.w_res, has, rank, val, sl);
     // raw codes of the remaining valid pixels
 #pragma unroll
     for (int m = 0; m < PPL; m++) {

@@ -82,7 +82,7 @@ __device__ __forceinline__ void scan_frame(const Geometry &g, const Scratch &s, 
         L.sec[3] = L.sec[2] + 4u * runs;
         L.sec[4] = L.sec[3] + 2u * temporal;
         L.sec[5] = L.sec[4] + words_for(cand);
-        L.sec[6] = L.sec[5] + words_for((uint64_t)fitted * g.w_res);
+        L.sec[6] = L.sec[5] + (g.no_delta ? 0u : words_for((uint64_t)fitted * g.w_res));   // no deltas: none
         L.sec[7] = L.sec[6] + words_for((uint64_t)raw * g.w_raw);
         const unsigned long long total = (unsigned long long)kHeaderBytes + 4ull * L.sec[7];
         L.total_bytes = (uint32_t)total;
@@ -98,7 +98,8 @@ __device__ __forceinline__ void scan_frame(const Geometry &g, const Scratch &s, 
         if (L.ok) {
             uint32_t hw[16];
             hw[0] = kMagic;
-            hw[1] = (uint32_t)kVersion | ((uint32_t)b.kind << 16) | ((uint32_t)(g.merge ? 1 : 0) << 24);
+            hw[1] = (uint32_t)kVersion | ((uint32_t)b.kind << 16) | ((uint32_t)(g.merge ? 1 : 0) << 24) |
+                    ((uint32_t)(g.no_delta ? 1 : 0) << 25);
             hw[2] = (uint32_t)g.H | ((uint32_t)g.W << 16);
             hw[3] = (uint32_t)g.th | ((uint32_t)g.tw << 8) | ((uint32_t)g.w_res << 16) | ((uint32_t)g.w_raw << 24);
             hw[4] = __float_as_uint(g.thr);

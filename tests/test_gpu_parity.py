@@ -31,8 +31,8 @@ def _cuda():
     lcc.load()
 
 
-def _oparams(tile=(4, 4), thr=0.05, q=0.02, R=3, fmin=0.75, merge=1):
-    return O.params(tile[0], tile[1], thr, q, R, fmin, merge)
+def _oparams(tile=(4, 4), thr=0.05, q=0.02, R=3, fmin=0.75, merge=1, no_delta=0):
+    return O.params(tile[0], tile[1], thr, q, R, fmin, merge, no_delta)
 
 
 def _gparams(tile=(4, 4), thr=0.05, q=0.02, R=3, fmin=0.75, merge=1, solver=0, **kw):
@@ -71,7 +71,7 @@ def _compare_spatial(s, p, rng, recs, ofits, thr, skip=None):
     return compared, border
 
 
-def _check_decode(c, s, bits, rng, q, kf_gpu=None, kft=None, pose=None):
+def _check_decode(c, s, bits, rng, q, kf_gpu=None, kft=None, pose=None, bound=None):
     st, drng, dxyz, dvalid = H.decode(c, bits, kf_gpu, pose)
     assert st == 0
     orng, oxyz, ovalid = O.decode(s, bits, kft, pose)
@@ -81,7 +81,7 @@ def _check_decode(c, s, bits, rng, q, kf_gpu=None, kft=None, pose=None):
     m = rng > 0
     assert ((drng > 0) == m).all()
     err = np.abs(drng[m] - rng[m]).max() if m.any() else 0.0
-    assert err <= q / 2 + 1e-5
+    assert err <= (q / 2 if bound is None else bound) + 1e-5
     return err
 
 
@@ -106,7 +106,7 @@ def _keyframe_case(sensor_, pts, **kw):
         np.array_equal(ok, (ofits["status"] == O.FIT_OK).astype(np.uint8))
     if same_planes:
         assert obits.tobytes() == gbits.tobytes()
-    err = _check_decode(c, s, gbits, rng, p.quant_m)
+    err = _check_decode(c, s, gbits, rng, p.quant_m, bound=p.fit_thr_m if p.no_delta else None)
     return dict(bytes=len(gbits), border=border, compared=compared, err=err, same_planes=same_planes, ctx=c,
                 recs=recs, bits=gbits)
 
@@ -518,3 +518,43 @@ def test_sequence_decode_matches_per_frame_decode(cfg2_seq):
     outs2[(seq.key_index + 1) % n] = bad
     c.lcc_decode_sequence(seq.key_index, seq.poses, outs2, sizes, r2, None, None)
     assert c.lcc_sync() == lcc.ERR_CORRUPT
+
+
+@pytest.mark.parametrize("tile,thr", [((4, 4), 0.05), ((8, 8), 0.02)])
+def test_no_delta_keyframe_parity(cfg2_seq, tile, thr):
+    """The no-delta mode (Sec. III-C drops the deltas): the GPU stream is the oracle's on the GPU's
+    planes, both decoders agree bit for bit, and the decode error stays within the threshold."""
+    seq = cfg2_seq
+    r = _keyframe_case(seq.sensor, seq.frames[seq.key_index], tile=tile, thr=thr, no_delta=1)
+    h = streamfmt.header(r["bits"])
+    assert h["flags"] & 2 and r["err"] <= thr + 1e-5
+    d = _keyframe_case(seq.sensor, seq.frames[seq.key_index], tile=tile, thr=thr)
+    assert r["bytes"] < d["bytes"]
+
+
+def test_no_delta_sequence_decodes_within_threshold(cfg2_seq):
+    """A whole sequence in the no-delta mode: every frame decodes with the oracle's decoder to the
+    GPU decoder's ranges, within the threshold of its range image."""
+    from paper_2008_06972_gb300 import lcc
+    seq = cfg2_seq
+    n = len(seq.frames)
+    thr = 0.05
+    c = H.ctx(seq.sensor, max_batch=16, no_delta=1, fit_thr_m=thr)
+    ds = [H.to_dev(p) for p in seq.frames]
+    outs = [H.out_buf(c) for _ in range(n)]
+    nb = torch.zeros(n, dtype=torch.int64, device="cuda")
+    kf = lcc.Keyframe(c)
+    c.lcc_encode_sequence(seq.key_index, seq.poses, ds, [len(p) for p in seq.frames], outs,
+                          [o.numel() for o in outs], nb, kf)
+    assert c.lcc_sync() == 0
+    sizes = [int(x) for x in nb.cpu().numpy()]
+    s = O.sensor(seq.sensor)
+    bits = [outs[f][:sizes[f]].cpu().numpy() for f in range(n)]
+    kft = O.kf_table_from_stream(s, bits[seq.key_index], c.num_tiles)
+    kfd = lcc.Keyframe(c)
+    c.lcc_keyframe_from_stream(outs[seq.key_index], sizes[seq.key_index], kfd)
+    for f in range(n):
+        isk = f == seq.key_index
+        rng, _, _ = O.range_image(s, seq.frames[f])
+        _check_decode(c, s, bits[f], rng, 0.02, None if isk else kfd, None if isk else kft,
+                      None if isk else seq.poses[f], bound=thr)
