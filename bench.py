@@ -53,6 +53,7 @@ def parse():
     ap.add_argument("--no-batched", action="store_true", help="skip the uneven multi-sequence batch")
     ap.add_argument("--no-learned", action="store_true", help="skip the learned-proposal section")
     ap.add_argument("--no-sweep", action="store_true", help="skip the tile / threshold sweep")
+    ap.add_argument("--no-imu", action="store_true", help="skip the IMU-pose section")
     ap.add_argument("--train-steps", type=int, default=300)
     ap.add_argument("--train-seqs", type=int, default=6)
     return ap.parse_args()
@@ -429,6 +430,95 @@ def run_sweep(args, stream, seq, d_pts, flush):
             del kf, kfd, ctx
     return {"workload": WORKLOAD.split(",")[0] + ", swept tiles and thresholds, q 0.02 m", "steps": steps,
             "rows": rows}
+
+
+IMU_LEVELS = (
+    # name, acc white sigma (m/s^2), gyro white sigma (deg/s), acc bias (m/s^2), gyro bias (deg/s)
+    ("ideal", 0.0, 0.0, 0.0, 0.0),
+    ("navigation grade", 0.01, 0.005, 0.002, 0.001),
+    ("automotive MEMS", 0.05, 0.05, 0.02, 0.05),
+    ("low-cost MEMS", 0.2, 0.3, 0.1, 0.5),
+)
+
+
+def run_imu(args, stream, flush):
+    """Frame poses from IMU samples (Sec. III-D): the HDL-64E scene driven on a 10 m/s, 5 deg/s arc,
+    10 frames at 10 Hz, key frame the middle one; 100 Hz samples (clock offset from the frames) at
+    four noise levels, integrated by lcc_imu_pose into every P frame's pose, then the sequence encoded
+    and decoded with those poses.  Rows: pose error against the exact arc, temporal tiles, bytes,
+    device time of the encode and the max decode error."""
+    import torch
+    import synth
+    from paper_2008_06972_gb300 import lcc
+    seq = synth.sequence_arc(0, 10)
+    n_frames = len(seq.frames)
+    n = [len(f) for f in seq.frames]
+    pts = sum(n)
+    H, W = seq.sensor.rows, seq.sensor.cols
+    t_key = seq.key_index * synth.FRAME_DT
+    d_pts = [torch.from_numpy(f).cuda() for f in seq.frames]
+    ctx = lcc.Context(seq.sensor, lcc.default_params(max_batch=max(16, n_frames)), stream=stream)
+    cap = ctx.max_encoded_bytes
+    outs = [torch.zeros(cap, dtype=torch.uint8, device="cuda") for _ in range(n_frames)]
+    nb = torch.zeros(n_frames, dtype=torch.int64, device="cuda")
+    kf = lcc.Keyframe(ctx)
+    kfd = lcc.Keyframe(ctx)
+    ref = torch.empty(H * W, dtype=torch.float32, device="cuda")
+    dec = torch.empty(H * W, dtype=torch.float32, device="cuda")
+    steps = max(5, min(args.steps, 30))
+    rows = []
+    for name, sa, sg, ba, bg in (("exact",) + IMU_LEVELS[0][1:],) + IMU_LEVELS:
+        if name == "exact":
+            poses, pose_us = seq.poses, 0.0
+        else:
+            smp = synth.imu_samples(0.0, (n_frames - 1) * synth.FRAME_DT, 10.0, math.radians(5.0), t_key,
+                                    acc_sigma=sa, gyro_sigma=math.radians(sg), acc_bias=(ba, -ba, ba),
+                                    gyro_bias=(math.radians(bg),) * 3, seed=17)
+            t0 = time.perf_counter()
+            poses = np.stack([lcc.imu_pose(smp.t, smp.acc, smp.gyro, smp.v_key, t_key, f * synth.FRAME_DT)
+                              for f in range(n_frames)])
+            pose_us = (time.perf_counter() - t0) / n_frames * 1e6
+        et = max(float(np.abs(poses[f][:3, 3] - seq.poses[f][:3, 3]).max()) for f in range(n_frames))
+        er = max(math.degrees(math.acos(min(1.0, (np.trace(poses[f][:3, :3].T @ seq.poses[f][:3, :3]) - 1) / 2)))
+                 for f in range(n_frames))
+
+        def step():
+            ctx.lcc_encode_sequence(seq.key_index, poses, d_pts, n, outs, [cap] * n_frames, nb, kf)
+
+        for _ in range(3):
+            step()
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        torch.cuda.synchronize()
+        for k in range(steps):
+            flush.zero_()
+            evs[k][0].record(stream)
+            step()
+            evs[k][1].record(stream)
+        torch.cuda.synchronize()
+        assert ctx.lcc_sync() == lcc.OK
+        ms = float(np.mean([a.elapsed_time(b) for a, b in evs]))
+        sizes = nb.cpu().numpy()
+        temporal = sum(ctx.lcc_last_stats(f)["tiles_temporal"] for f in range(n_frames))
+        ctx.lcc_keyframe_from_stream(outs[seq.key_index], int(sizes[seq.key_index]), kfd)
+        err = 0.0
+        for f in range(n_frames):
+            ctx.lcc_range_image(d_pts[f], n[f], ref, None)
+            isk = f == seq.key_index
+            ctx.lcc_decode(outs[f], int(sizes[f]), None if isk else kfd, None if isk else poses[f], dec, None, None)
+            assert ctx.lcc_sync() == lcc.OK
+            m = ref > 0
+            if bool(m.any()):
+                err = max(err, float((dec[m] - ref[m]).abs().max().item()))
+        assert err <= 0.02, err
+        rows.append({"poses": name, "acc_sigma": sa, "gyro_sigma_dps": sg, "acc_bias": ba, "gyro_bias_dps": bg,
+                     "max_pose_err_m": et, "max_pose_err_deg": er, "pose_us_per_frame": round(pose_us, 2),
+                     "tiles_temporal": temporal, "bytes": int(sizes.sum()),
+                     "compression_ratio": round(12.0 * pts / float(sizes.sum()), 3),
+                     "ms_per_step": round(ms, 4), "mpts_per_s": round(pts / (ms * 1e-3) / 1e6, 1),
+                     "max_decode_error_m": err})
+    del kf, kfd, ctx
+    return {"workload": "64x2048 HDL-64E-shaped frames, 10 per sequence on a 10 m/s, 5 deg/s arc, "
+                        "4x4 tiles, thr 0.05 m, q 0.02 m; 100 Hz IMU samples", "steps": steps, "rows": rows}
 
 
 def run_learned(args, stream):
@@ -816,6 +906,7 @@ def main():
                      "frac": path_bytes / (ms_step * 1e-3) / 1e9 / hbm}}
 
     sweep = None if args.no_sweep or world > 1 else run_sweep(args, stream, seq, d_pts, flush)
+    imu_rows = None if args.no_imu or world > 1 else run_imu(args, stream, flush)
     batched = None if args.no_batched else run_batched(args, stream, hbm)
     learned = None if args.no_learned else run_learned(args, stream)
 
@@ -845,6 +936,7 @@ def main():
             "roofline": roof,
             "decode": decode,
             "sweep": sweep,
+            "imu": imu_rows,
             "batched": batched,
             "learned": learned,
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(16 * pts_step),

@@ -228,6 +228,21 @@ lcc_status lcc_decode_sequence(lcc_ctx *ctx, int32_t nframes, int32_t key_index,
                                const uint8_t *const *d_bits, const uint64_t *nbytes, float *const *d_range,
                                float *const *d_xyz4, uint32_t *const *d_valid);
 
+/* Pose of a P frame from IMU samples (Sec. III-D, the equations of T and R before
+ * Eq. 6): the 4x4 row-major M with p_K = R p_P + T for the frame taken at t_p,
+ * the key frame taken at t_key.  Samples k = 0..n-1 at strictly increasing times
+ * t[k] give the acceleration acc[3k..3k+2] (m/s^2, gravity removed) and rotation
+ * rate gyro[3k..3k+2] (rad/s, about x, y, z), in the key frame's sensor axes;
+ * each holds until the next sample.  v_key is the velocity at t_key.
+ * Integration is first-order (explicit Euler) from t_key to t_p, forward or
+ * backward, one step per (partial) sample interval, position before velocity;
+ * T = the position reached, R = Rz(alpha) Ry(beta) Rx(gamma) in the paper's
+ * printed form with (alpha, beta, gamma) = -(angle about z, y, x).  Host code,
+ * synchronous; LCC_ERR_INVALID_ARG on NULL pointers, n < 1, non-increasing
+ * times or non-finite t_key / t_p. */
+lcc_status lcc_imu_pose(const double *t, const double *acc, const double *gyro, int32_t n, const double v_key[3],
+                        double t_key, double t_p, double pose[16]);
+
 /* Wait for the context's stream and return (then clear) any latched device error. */
 lcc_status lcc_sync(lcc_ctx *ctx);
 

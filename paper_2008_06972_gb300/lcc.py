@@ -108,6 +108,7 @@ def load(path: str = LIB_PATH):
         "lcc_keyframe_from_stream": (i32, [vp, vp, u64, vp]),
         "lcc_decode": (i32, [vp, vp, u64, vp, vp, vp, vp, vp]),
         "lcc_decode_sequence": (i32, [vp, i32, i32, vp, vp, vp, vp, vp, vp]),
+        "lcc_imu_pose": (i32, [vp, vp, vp, i32, vp, ctypes.c_double, ctypes.c_double, vp]),
         "lcc_sync": (i32, [vp]),
         "lcc_last_stats": (i32, [vp, i32, vp]),
         "lcc_tile_records": (i32, [vp, i32, vp, i64]),
@@ -151,7 +152,7 @@ def exported_symbols() -> list[str]:
     return ["lcc_status_string", "lcc_default_params", "lcc_create", "lcc_destroy", "lcc_max_encoded_bytes",
             "lcc_num_tiles", "lcc_tables", "lcc_range_image", "lcc_keyframe_create", "lcc_keyframe_free",
             "lcc_encode_keyframe", "lcc_encode_keyframe_seeded", "lcc_encode_keyframes", "lcc_encode_pframe", "lcc_encode_pframes", "lcc_encode_sequence",
-            "lcc_encode_sequence_host", "lcc_keyframe_from_stream", "lcc_decode", "lcc_decode_sequence", "lcc_sync", "lcc_last_stats",
+            "lcc_encode_sequence_host", "lcc_keyframe_from_stream", "lcc_decode", "lcc_decode_sequence", "lcc_imu_pose", "lcc_sync", "lcc_last_stats",
             "lcc_tile_records", "lcc_set_profiling", "lcc_kernel_times", "lcc_kernel_timeline", "lcc_range_image_static", "lcc_net_num_params", "lcc_net_create", "lcc_net_destroy",
             "lcc_net_get_params", "lcc_net_set_params", "lcc_net_tile_inputs", "lcc_net_tile_inputs_batch", "lcc_net_forward", "lcc_net_sync", "lcc_net_gradient",
             "lcc_net_train_step", "lcc_selftest_bounded_wait", "lcc_plan_create", "lcc_plan_update",
@@ -194,6 +195,18 @@ def default_params(**kw) -> lcc_params:
     for k, v in kw.items():
         setattr(p, k, v)
     return p
+
+
+def imu_pose(t, acc, gyro, v_key, t_key: float, t_p: float) -> np.ndarray:
+    """4x4 pose of the frame taken at t_p in the key frame's coordinates (lcc_imu_pose)."""
+    t = np.ascontiguousarray(t, dtype=np.float64)
+    acc = np.ascontiguousarray(acc, dtype=np.float64).reshape(-1, 3)
+    gyro = np.ascontiguousarray(gyro, dtype=np.float64).reshape(-1, 3)
+    v = np.ascontiguousarray(v_key, dtype=np.float64).reshape(3)
+    out = np.zeros(16, np.float64)
+    _check(load().lcc_imu_pose(t.ctypes.data, acc.ctypes.data, gyro.ctypes.data, len(t), v.ctypes.data,
+                               float(t_key), float(t_p), out.ctypes.data), "lcc_imu_pose")
+    return out.reshape(4, 4)
 
 
 def sensor(s) -> lcc_sensor:

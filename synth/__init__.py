@@ -140,6 +140,55 @@ def ego_poses(n_frames: int, step_m: float, yaw_deg_per_frame: float):
     return poses
 
 
+FRAME_DT = 0.1   # a 10 Hz spinning sensor
+
+
+def arc_poses(n_frames: int, speed: float, yaw_rate: float, frame_dt: float = FRAME_DT):
+    """World poses (R, t) at times f * frame_dt of a sensor that drives at a constant speed (m/s)
+    along its heading while yawing at a constant rate (rad/s): frame 0 at the origin, heading +x."""
+    poses = []
+    for f in range(n_frames):
+        tau = f * frame_dt
+        psi = yaw_rate * tau
+        if yaw_rate == 0.0:
+            pos = np.array([speed * tau, 0.0, 0.0])
+        else:
+            r = speed / yaw_rate
+            pos = np.array([r * math.sin(psi), r * (1.0 - math.cos(psi)), 0.0])
+        poses.append((yaw_matrix(psi), pos))
+    return poses
+
+
+@dataclass
+class ImuSamples:
+    t: np.ndarray        # (n,) sample times, s
+    acc: np.ndarray      # (n, 3) acceleration, m/s^2, gravity removed, key frame's axes
+    gyro: np.ndarray     # (n, 3) rotation rate about x, y, z, rad/s
+    v_key: np.ndarray    # (3,) velocity at the key frame's time, key frame's axes
+
+
+def imu_samples(t0: float, t1: float, speed: float, yaw_rate: float, t_key: float, rate_hz: float = 100.0,
+                offset: float = 0.0037, acc_sigma: float = 0.0, gyro_sigma: float = 0.0,
+                acc_bias=(0.0, 0.0, 0.0), gyro_bias=(0.0, 0.0, 0.0), seed: int = 0) -> ImuSamples:
+    """IMU samples of the arc_poses motion on [t0 - 1/rate, t1 + 1/rate], expressed in the axes of the
+    frame taken at t_key: velocity speed * (cos phi, sin phi, 0) with phi = yaw_rate * (t - t_key), so
+    acceleration speed * yaw_rate * (-sin phi, cos phi, 0) and rate (0, 0, yaw_rate).  The sample
+    clock is offset from the frame clock; white noise (per-sample sigma) and a constant bias model
+    the sensor."""
+    h = 1.0 / rate_hz
+    k0 = math.floor((t0 - offset) / h) - 1
+    k1 = math.ceil((t1 - offset) / h) + 1
+    t = offset + np.arange(k0, k1 + 1) * h
+    phi = yaw_rate * (t - t_key)
+    acc = speed * yaw_rate * np.stack([-np.sin(phi), np.cos(phi), np.zeros_like(phi)], axis=1)
+    gyro = np.zeros((len(t), 3))
+    gyro[:, 2] = yaw_rate
+    rng = np.random.default_rng(seed)
+    acc = acc + rng.normal(0.0, 1.0, acc.shape) * acc_sigma + np.asarray(acc_bias, dtype=np.float64)
+    gyro = gyro + rng.normal(0.0, 1.0, gyro.shape) * gyro_sigma + np.asarray(gyro_bias, dtype=np.float64)
+    return ImuSamples(t, acc, gyro, np.array([speed, 0.0, 0.0]))
+
+
 def relative_pose(pose_f, pose_k) -> np.ndarray:
     """4x4 row-major matrix M with p_K = R p_f + T (frame f coordinates to frame k)."""
     Rf, tf = pose_f
@@ -184,9 +233,10 @@ class Sequence:
 
 def sequence(sensor: Sensor, n_frames: int, seed: int, n_walls: int, n_boxes: int, n_poles: int,
              step_m: float, yaw_deg: float, sigma: float = 0.02, dropout: float = 0.0,
-             clutter: float = 0.0, pose_noise=None, key_index=None) -> Sequence:
-    """A sequence in one scene; the key frame is the middle one (floor(n/2))."""
-    world = ego_poses(n_frames, step_m, yaw_deg)
+             clutter: float = 0.0, pose_noise=None, key_index=None, world=None) -> Sequence:
+    """A sequence in one scene; the key frame is the middle one (floor(n/2)).  The sensor moves by
+    ego_poses(step_m, yaw_deg) unless world poses are given."""
+    world = ego_poses(n_frames, step_m, yaw_deg) if world is None else world
     path_len = step_m * max(n_frames - 1, 0)
     scene = Scene(seed, n_walls, n_boxes, n_poles, path_len=path_len)
     k = n_frames // 2 if key_index is None else key_index
@@ -207,6 +257,16 @@ def sequence_cfg2(sequence_id: int = 0, n_frames: int = 10) -> Sequence:
     seed = config_seed(2, sequence_id, 0)
     return sequence(HDL64_SENSOR, n_frames, seed, n_walls=20, n_boxes=40, n_poles=60,
                     step_m=1.0, yaw_deg=0.5, sigma=0.02, dropout=0.0, clutter=0.02)
+
+
+def sequence_arc(sequence_id: int = 0, n_frames: int = 10, speed: float = 10.0,
+                 yaw_rate: float = math.radians(5.0)) -> Sequence:
+    """The HDL-64E urban scene driven on a constant-speed, constant-yaw-rate arc (10 m/s and
+    5 deg/s: 1 m and 0.5 deg per 10 Hz frame), exact poses; the IMU workload."""
+    seed = config_seed(2, sequence_id, 0)
+    return sequence(HDL64_SENSOR, n_frames, seed, n_walls=20, n_boxes=40, n_poles=60, step_m=speed * FRAME_DT,
+                    yaw_deg=0.0, sigma=0.02, dropout=0.0, clutter=0.02,
+                    world=arc_poses(n_frames, speed, yaw_rate))
 
 
 CFG5_SENSOR = Sensor(128, 4096, -15.0, 15.0, 80.0)

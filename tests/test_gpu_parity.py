@@ -558,3 +558,46 @@ def test_no_delta_sequence_decodes_within_threshold(cfg2_seq):
         rng, _, _ = O.range_image(s, seq.frames[f])
         _check_decode(c, s, bits[f], rng, 0.02, None if isk else kfd, None if isk else kft,
                       None if isk else seq.poses[f], bound=thr)
+
+
+def test_imu_poses_parity_and_decode():
+    """P frames moved into the key frame's coordinates by poses integrated from 100 Hz IMU samples
+    (Sec. III-D; automotive-grade noise and bias): the C-ABI poses agree with the oracle's within
+    1e-12, the P frames encoded with the oracle's IMU poses match the oracle tile by tile, and the
+    whole sequence encoded with the C-ABI's poses decodes (GPU decoder) within the quantisation
+    bound of the oracle's range images."""
+    from paper_2008_06972_gb300 import lcc
+    from oracle import imu
+    seq = synth.sequence_arc(0, 5)
+    t_key = seq.key_index * synth.FRAME_DT
+    smp = synth.imu_samples(0.0, 0.4, 10.0, math.radians(5.0), t_key, acc_sigma=0.05, gyro_sigma=math.radians(0.05),
+                            acc_bias=(0.02, -0.02, 0.02), gyro_bias=(math.radians(0.05),) * 3, seed=17)
+    n = len(seq.frames)
+    pc = np.stack([lcc.imu_pose(smp.t, smp.acc, smp.gyro, smp.v_key, t_key, f * synth.FRAME_DT) for f in range(n)])
+    po = np.stack([imu.pose_from_imu(smp.t, smp.acc, smp.gyro, smp.v_key, t_key, f * synth.FRAME_DT)
+                   for f in range(n)])
+    assert np.abs(pc - po).max() <= 1e-12
+    assert np.abs(po[:, :3, 3] - seq.poses[:, :3, 3]).max() < 0.01   # the IMU pose is close to the arc
+    frames = [f for f in range(n) if f != seq.key_index]
+    border = _pframe_case(seq, frames, poses=[po[f] for f in frames])
+    assert border <= 20
+    c = H.ctx(seq.sensor, max_batch=16)
+    ds = [H.to_dev(p) for p in seq.frames]
+    outs = [H.out_buf(c) for _ in range(n)]
+    nb = torch.zeros(n, dtype=torch.int64, device="cuda")
+    kf = lcc.Keyframe(c)
+    c.lcc_encode_sequence(seq.key_index, pc, ds, [len(p) for p in seq.frames], outs, [o.numel() for o in outs], nb, kf)
+    assert c.lcc_sync() == 0
+    assert sum(c.lcc_last_stats(f)["tiles_temporal"] for f in frames) > 0
+    sizes = [int(x) for x in nb.cpu().numpy()]
+    s = O.sensor(seq.sensor)
+    kfd = lcc.Keyframe(c)
+    c.lcc_keyframe_from_stream(outs[seq.key_index], sizes[seq.key_index], kfd)
+    for f in range(n):
+        isk = f == seq.key_index
+        rng, _, _ = O.range_image(s, seq.frames[f])
+        st, drng, _, _ = H.decode(c, outs[f][:sizes[f]].cpu().numpy(), None if isk else kfd, None if isk else pc[f])
+        assert st == 0
+        m = rng > 0
+        assert ((drng > 0) == m).all()
+        assert np.abs(drng[m] - rng[m]).max() <= 0.01 + 1e-5
