@@ -54,6 +54,7 @@ def parse():
     ap.add_argument("--no-learned", action="store_true", help="skip the learned-proposal section")
     ap.add_argument("--no-sweep", action="store_true", help="skip the tile / threshold sweep")
     ap.add_argument("--no-imu", action="store_true", help="skip the IMU-pose section")
+    ap.add_argument("--no-entropy", action="store_true", help="skip the entropy-stage section")
     ap.add_argument("--train-steps", type=int, default=300)
     ap.add_argument("--train-seqs", type=int, default=6)
     return ap.parse_args()
@@ -430,6 +431,89 @@ def run_sweep(args, stream, seq, d_pts, flush):
             del kf, kfd, ctx
     return {"workload": WORKLOAD.split(",")[0] + ", swept tiles and thresholds, q 0.02 m", "steps": steps,
             "rows": rows}
+
+
+def run_entropy(args, stream, ctx, d_out, sizes, pts_step, flush, hbm):
+    """The lossless entropy stage (Sec. III-A) on the step's 10 fixed-width streams: one
+    lcc_entropy_encode call and one lcc_entropy_decode call, each timed with CUDA events (L2
+    flushed between steps); sizes per section; the round trip checked byte for byte."""
+    import torch
+    from paper_2008_06972_gb300 import lcc
+    n = len(d_out)
+    cap = ctx.max_encoded_bytes + 4096
+    ent = [torch.zeros(cap, dtype=torch.uint8, device="cuda") for _ in range(n)]
+    enb = torch.zeros(n, dtype=torch.int64, device="cuda")
+    back = [torch.zeros(ctx.max_encoded_bytes, dtype=torch.uint8, device="cuda") for _ in range(n)]
+    bnb = torch.zeros(n, dtype=torch.int64, device="cuda")
+    in_size = [o.numel() for o in d_out]
+
+    def enc():
+        ctx.lcc_entropy_encode(d_out, in_size, ent, [cap] * n, enb)
+
+    enc()
+    assert ctx.lcc_sync() == lcc.OK
+    ent_sizes = [int(x) for x in enb.cpu().numpy()]
+
+    def dec():
+        ctx.lcc_entropy_decode(ent, ent_sizes, back, [b.numel() for b in back], bnb)
+
+    def timed(fn):
+        for _ in range(3):
+            fn()
+        assert ctx.lcc_sync() == lcc.OK
+        k_steps = max(5, min(args.steps, 50))
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(k_steps)]
+        for k in range(k_steps):
+            flush.zero_()
+            evs[k][0].record(stream)
+            fn()
+            evs[k][1].record(stream)
+        torch.cuda.synchronize()
+        assert ctx.lcc_sync() == lcc.OK
+        return float(np.mean([a.elapsed_time(b) for a, b in evs])), k_steps
+
+    enc_ms, k_steps = timed(enc)
+    dec_ms, _ = timed(dec)
+    assert [int(x) for x in bnb.cpu().numpy()] == list(sizes)
+    for f in range(n):
+        assert torch.equal(back[f][:sizes[f]], d_out[f][:sizes[f]]), f"frame {f}: entropy round trip differs"
+    ctx.lcc_set_profiling(True)
+    enc()
+    dec()
+    kt = ctx.lcc_kernel_times()
+    ctx.lcc_set_profiling(False)
+    names = ("bitmap", "tiles", "runs", "temporal", "fitted", "res", "raw")
+    fixed_w = {k: 0 for k in names}
+    ent_w = {k: 0 for k in names}
+    coded = {k: 0 for k in names}
+    for f in range(n):
+        h = ent[f][:184].cpu().numpy().view("<u4")
+        fx = d_out[f][:64].cpu().numpy().view("<u4")
+        for s_, k in enumerate(names):
+            mode, count, alph, words = (int(x) for x in h[18 + 4 * s_:22 + 4 * s_])
+            ent_w[k] += words
+            coded[k] += mode & 1
+        # fixed-width section sizes from the fixed header
+        rows, cols = int(fx[2] & 0xFFFF), int(fx[2] >> 16)
+        w_res, w_raw, flags = int((fx[3] >> 16) & 0xFF), int(fx[3] >> 24), int(fx[1] >> 24)
+        nt, nr, ntm, nc, nf, nraw = (int(fx[i]) for i in (6, 8, 9, 10, 11, 12))
+        wd = lambda b: (b + 31) // 32
+        for k, v in zip(names, (wd(rows * cols), wd(4 * nt), 4 * nr, 2 * ntm, wd(nc),
+                                0 if flags & 2 else wd(nf * w_res), wd(nraw * w_raw))):
+            fixed_w[k] += v
+    fixed_bytes, ent_bytes = int(sum(sizes)), int(sum(ent_sizes))
+    alg = fixed_bytes + ent_bytes
+    return {"workload": "the step's 10 fixed-width streams through one lcc_entropy_encode and one "
+                        "lcc_entropy_decode call (canonical Huffman per section, 1024-symbol chunks)",
+            "steps": k_steps, "fixed_bytes": fixed_bytes, "entropy_bytes": ent_bytes,
+            "compression_ratio_fixed": 12.0 * pts_step / fixed_bytes,
+            "compression_ratio_entropy": 12.0 * pts_step / ent_bytes,
+            "encode_ms": enc_ms, "encode_mpts_per_s": pts_step / (enc_ms * 1e-3) / 1e6,
+            "decode_ms": dec_ms, "decode_mpts_per_s": pts_step / (dec_ms * 1e-3) / 1e6,
+            "encode_hbm_frac": alg / (enc_ms * 1e-3) / 1e9 / hbm,
+            "kernel_ms": {k: v[1] for k, v in kt.items()},
+            "section_bytes": {k: {"fixed": 4 * fixed_w[k], "entropy": 4 * ent_w[k], "frames_coded": coded[k]}
+                              for k in names}}
 
 
 IMU_LEVELS = (
@@ -851,6 +935,9 @@ def main():
               "steps": dec_steps, "ms_per_step": dec_ms, "mpts_per_s": pts_step / (dec_ms * 1e-3) / 1e6,
               "per_frame_calls": {"ms_per_step": dec1_ms, "mpts_per_s": pts_step / (dec1_ms * 1e-3) / 1e6}}
 
+    hbm_peak, _ = peaks()
+    entropy = None if args.no_entropy else run_entropy(args, stream, ctx, d_out, sizes, pts_step, flush, hbm_peak)
+
     # ---- end to end through the C ABI with HOST buffers (pinned) ----
     h_pts = [torch.from_numpy(f).pin_memory() for f in seq.frames]
     h_out = [torch.zeros(cap, dtype=torch.uint8).pin_memory() for _ in range(n_frames)]
@@ -935,6 +1022,7 @@ def main():
             "kernel_ms_per_step": {k: v[1] / args.steps for k, v in ktimes.items()},
             "roofline": roof,
             "decode": decode,
+            "entropy": entropy,
             "sweep": sweep,
             "imu": imu_rows,
             "batched": batched,

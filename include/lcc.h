@@ -228,6 +228,34 @@ lcc_status lcc_decode_sequence(lcc_ctx *ctx, int32_t nframes, int32_t key_index,
                                const uint8_t *const *d_bits, const uint64_t *nbytes, float *const *d_range,
                                float *const *d_xyz4, uint32_t *const *d_valid);
 
+/* Lossless entropy stage (Sec. III-A, its last paragraph: planes and residual
+ * maps pass through a lossless coder, Huffman coding being the one named).
+ * lcc_entropy_encode turns each fixed-width frame stream d_in[f] (in_size[f]
+ * readable bytes, at least the stream's own size) into an entropy stream at
+ * d_out[f] (out_cap[f] bytes); lcc_entropy_decode gives the fixed-width stream
+ * back, byte for byte.  Entropy stream: the fixed-width stream's 64-byte
+ * header, word 16 "LCE1", word 17 its size in bytes, words 18..45 one
+ * descriptor of 4 words per section (mode | width << 8, count, alphabet,
+ * words), then the sections in stream order.  The bitmap and the fitted bits
+ * are coded as bytes, the tile codes as 4-bit symbols, the residual and raw
+ * codes at their width (at most 12 bits); the run planes and temporal records
+ * are copied.  A symbol section gets its own canonical Huffman code (lengths
+ * <= 15 from Huffman's construction over (count, symbol)-sorted leaves, a leaf
+ * first on equal weights, counts halved until the depth fits; codes in
+ * (length, symbol) order by the DEFLATE rule) when the coded form - a 4-bit
+ * length per symbol of the alphabet, one word offset per 1024-symbol chunk,
+ * then the word-padded chunks, each code's bits most significant first at
+ * increasing LSB-first bit positions - is smaller than the copy.
+ * Device buffers 16-byte aligned; out_bytes is a DEVICE array of nframes sizes
+ * (the needed size on a capacity error).  Asynchronous on the context stream;
+ * up to max_batch frames per call.  Errors latch (lcc_sync): LCC_ERR_CAPACITY,
+ * LCC_ERR_CORRUPT (a stream that is not this sensor's, or a corrupt entropy
+ * stream). */
+lcc_status lcc_entropy_encode(lcc_ctx *ctx, int32_t nframes, const uint8_t *const *d_in, const uint64_t *in_size,
+                              uint8_t *const *d_out, const uint64_t *out_cap, uint64_t *out_bytes);
+lcc_status lcc_entropy_decode(lcc_ctx *ctx, int32_t nframes, const uint8_t *const *d_in, const uint64_t *in_bytes,
+                              uint8_t *const *d_out, const uint64_t *out_cap, uint64_t *out_bytes);
+
 /* Pose of a P frame from IMU samples (Sec. III-D, the equations of T and R before
  * Eq. 6): the 4x4 row-major M with p_K = R p_P + T for the frame taken at t_p,
  * the key frame taken at t_key.  Samples k = 0..n-1 at strictly increasing times

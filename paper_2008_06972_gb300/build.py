@@ -19,7 +19,7 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "liblcc.so")
-SOURCES = ["lcc_api.cu", "lcc_plan.cu", "lcc_tune.cu", "lcc_static.cu", "lcc_imu.cu", "k_bin.cu", "k_fit.cu", "k_merge.cu", "k_pack.cu", "k_decode.cu", "k_net.cu"]
+SOURCES = ["lcc_api.cu", "lcc_plan.cu", "lcc_tune.cu", "lcc_static.cu", "lcc_imu.cu", "k_entropy.cu", "k_bin.cu", "k_fit.cu", "k_merge.cu", "k_pack.cu", "k_decode.cu", "k_net.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -1,0 +1,809 @@
+// Lossless entropy stage (Sec. III-A, its last paragraph): the planes and residual maps left by
+// spatial and temporal coding pass through a lossless coder, Huffman coding being the one named.
+//
+// The stage is a lossless transform of a fixed-width frame stream into an entropy stream and
+// back.  Sections, in stream order: the occupancy bitmap as 8-bit symbols (its bytes), the tile
+// codes as 4-bit symbols, the run planes and temporal records copied, the fitted bits as 8-bit
+// symbols, the residual and raw codes as symbols of their own width.  A symbol section of width
+// <= 12 with at least one symbol gets its own canonical Huffman code when the coded form (4-bit
+// length table, one offset word per 1024-symbol chunk, word-padded chunks of codes) is smaller
+// than the copy.  Code lengths: Huffman's construction over the symbols that occur sorted by
+// (count, symbol), the two lightest nodes joined at each step, a leaf before an internal node of
+// equal weight; lengths above 15 halve every count (rounding up) and the construction runs
+// again.  Canonical codes: consecutive in (length, symbol) order, the first code of each length
+// from the DEFLATE rule.  A code's bits go most significant first to increasing bit positions
+// (LSB-first words).
+//
+// Entropy stream: the fixed-width stream's 64-byte header; word 16 "LCE1"; word 17 the stream's
+// bytes; words 18..45 one descriptor per section (mode | width << 8, count, alphabet, words);
+// then the sections.
+//
+// Kernels.  Encode: k_ent_build (a CTA per frame and symbol section: histogram, sort, Huffman
+// lengths, canonical codes, chunk sizes, the copy-or-code decision), k_ent_layout (a warp per
+// frame: section offsets, capacity, header, length tables, chunk offsets), k_ent_write (a thread
+// per 1024-symbol chunk writes its codes; the copied sections move a block of words per CTA).
+// Decode: k_ent_dec_prep (a CTA per frame and section: validation, canonical decode tables),
+// k_ent_dec (a thread per chunk decodes into the fixed-width section; copies as above).
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <cstring>
+
+#include "lcc_ctx.cuh"
+
+namespace lcc {
+namespace ent {
+
+constexpr uint32_t kEntMagic = 0x3145434Cu;   // "LCE1"
+constexpr int kChunk = 1024;
+constexpr int kMaxLen = 15;
+constexpr int kMaxWidth = 12;
+constexpr int kMaxAlph = 1 << kMaxWidth;
+constexpr int kSecs = 7;
+constexpr int kEntHeaderWords = 16 + 2 + kSecs * 4;
+constexpr int kBuildThreads = 1024;
+constexpr int kWriteThreads = 128;
+constexpr int kCopyWords = 1024;   // words a CTA copies per step of a copied section
+
+struct Layout {            // a fixed-width stream's sections, from its header
+    uint32_t width[kSecs];  // symbol width (0: a section that is always copied)
+    uint32_t count[kSecs];  // symbols
+    uint32_t words[kSecs];  // 32-bit words in the fixed-width stream
+    uint32_t off[kSecs];    // word offset after the 64-byte header
+    uint32_t total;         // bytes
+};
+
+struct Sec {               // one section of one frame in the entropy stream
+    uint32_t mode;          // 0 copy, 1 Huffman
+    uint32_t alph;
+    uint32_t nch;
+    uint32_t words;         // words in the entropy stream
+    uint32_t ent_off;       // word offset in the entropy stream
+    uint32_t per_len[kMaxLen + 1];
+    uint32_t first[kMaxLen + 1];
+    uint32_t index[kMaxLen + 2];
+};
+
+struct Frame {
+    Sec sec[kSecs];
+    Layout L;
+    uint32_t ok;
+};
+
+struct Scratch {
+    Frame *frame;          // [slots]
+    uint8_t *len;          // [slots][7][kMaxAlph]
+    uint16_t *rcode;       // [slots][7][kMaxAlph] codes with their bits reversed (LSB = first bit)
+    uint16_t *sorted;      // [slots][7][kMaxAlph] symbols in (length, symbol) order (decoder)
+    uint32_t *chunk;       // [slots][7][max_chunks] chunk words, then chunk offsets (in place)
+    uint32_t max_chunks;
+};
+
+struct EntBatch {
+    const uint8_t *in[kMaxBatch];
+    uint8_t *out[kMaxBatch];
+    unsigned long long in_size[kMaxBatch];   // bytes readable at in[f]
+    unsigned long long out_cap[kMaxBatch];
+    unsigned long long *out_bytes;            // device, one per frame
+    uint32_t rows, cols;
+};
+
+__device__ __forceinline__ uint32_t words_of_bits(unsigned long long bits) { return (uint32_t)((bits + 31) / 32); }
+
+// Section layout of the fixed-width stream whose header is h (16-byte aligned); false if the
+// header is not one of this sensor's streams or its sizes disagree.
+__device__ bool parse_fixed(const uint8_t *h, unsigned long long avail, uint32_t rows, uint32_t cols, Layout &L) {
+    if (avail < (unsigned long long)kHeaderBytes) return false;
+    const uint32_t *w = reinterpret_cast<const uint32_t *>(h);
+    if (w[0] != kMagic || (w[1] & 0xFFFFu) != (uint32_t)kVersion) return false;
+    const uint32_t flags = w[1] >> 24;
+    if ((w[2] & 0xFFFFu) != rows || (w[2] >> 16) != cols) return false;
+    const uint32_t w_res = (w[3] >> 16) & 0xFFu, w_raw = w[3] >> 24;
+    const uint32_t n_tiles = w[6], n_runs = w[8], n_temp = w[9], n_cand = w[10], n_fit = w[11], n_raw = w[12];
+    const unsigned long long npx = (unsigned long long)rows * cols;
+    if (w_res > 32 || w_raw > 32 || n_tiles > npx || n_runs > n_tiles || n_temp > n_tiles || n_cand > npx ||
+        n_fit > n_cand || n_raw > npx)
+        return false;
+    const uint32_t bw = words_of_bits(npx), fw = words_of_bits(n_cand);
+    const uint32_t res_cnt = (flags & 2u) ? 0u : n_fit;
+    const uint32_t width[kSecs] = {8, 4, 0, 0, 8, w_res, w_raw};
+    const uint32_t count[kSecs] = {4 * bw, n_tiles, 0, 0, 4 * fw, res_cnt, n_raw};
+    const uint32_t words[kSecs] = {bw,
+                                   words_of_bits(4ull * n_tiles),
+                                   4 * n_runs,
+                                   2 * n_temp,
+                                   fw,
+                                   words_of_bits((unsigned long long)res_cnt * w_res),
+                                   words_of_bits((unsigned long long)n_raw * w_raw)};
+    unsigned long long o = 0;
+    for (int s = 0; s < kSecs; s++) {
+        L.width[s] = width[s];
+        L.count[s] = count[s];
+        L.words[s] = words[s];
+        L.off[s] = (uint32_t)o;
+        o += words[s];
+    }
+    const unsigned long long total = (unsigned long long)kHeaderBytes + 4 * o;
+    if (total != w[14] || total > avail) return false;
+    L.total = (uint32_t)total;
+    return true;
+}
+
+__device__ __forceinline__ bool coded_width(uint32_t w) { return w >= 1 && w <= (uint32_t)kMaxWidth; }
+
+// Symbol i of a section of width w (LSB-first in words; the symbol lies inside the section).
+__device__ __forceinline__ uint32_t get_sym(const uint32_t *sec, uint32_t w, uint32_t i) {
+    const unsigned long long p = (unsigned long long)i * w;
+    const uint32_t wi = (uint32_t)(p >> 5), sh = (uint32_t)(p & 31);
+    uint32_t v = sec[wi] >> sh;
+    if (sh + w > 32) v |= sec[wi + 1] << (32 - sh);
+    return v & ((1u << w) - 1u);
+}
+
+__device__ uint32_t block_sum(uint32_t v, uint32_t *red) {
+    for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xFFFFFFFFu, v, o);
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    __syncthreads();
+    if (lane == 0) red[wid] = v;
+    __syncthreads();
+    uint32_t t = 0;
+    for (int k = 0; k < (int)(blockDim.x >> 5); k++) t += red[k];
+    __syncthreads();
+    return t;
+}
+
+__device__ uint32_t block_max(uint32_t v, uint32_t *red) {
+    for (int o = 16; o; o >>= 1) v = max(v, __shfl_xor_sync(0xFFFFFFFFu, v, o));
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    __syncthreads();
+    if (lane == 0) red[wid] = v;
+    __syncthreads();
+    uint32_t t = 0;
+    for (int k = 0; k < (int)(blockDim.x >> 5); k++) t = max(t, red[k]);
+    __syncthreads();
+    return t;
+}
+
+// Exclusive prefix sum over the block (threads in order); *total receives the sum.
+__device__ uint32_t block_excl(uint32_t v, uint32_t *red, uint32_t *total) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    uint32_t x = v;
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, x, o);
+        if (lane >= o) x += y;
+    }
+    __syncthreads();
+    if (lane == 31) red[wid] = x;
+    __syncthreads();
+    uint32_t before = 0, all = 0;
+    for (int k = 0; k < (int)(blockDim.x >> 5); k++) {
+        if (k < wid) before += red[k];
+        all += red[k];
+    }
+    __syncthreads();
+    *total = all;
+    return before + x - v;
+}
+
+// Ascending bitonic sort of keys[0, P), P a power of two (the textbook network).
+__device__ void bitonic_sort(unsigned long long *keys, uint32_t P) {
+    for (uint32_t k = 2; k <= P; k <<= 1)
+        for (uint32_t j = k >> 1; j > 0; j >>= 1) {
+            for (uint32_t i = threadIdx.x; i < P; i += blockDim.x) {
+                const uint32_t l = i ^ j;
+                if (l > i) {
+                    const unsigned long long a = keys[i], b = keys[l];
+                    const bool up = (i & k) == 0;
+                    if ((a > b) == up) {
+                        keys[i] = b;
+                        keys[l] = a;
+                    }
+                }
+            }
+            __syncthreads();
+        }
+}
+
+// Canonical tables of a length table (any thread count): per length the number of codes, the
+// first code and the index of its first symbol in (length, symbol) order.  Thread 0 only.
+__device__ void canonical_tables(const uint32_t *per_len, uint32_t *first, uint32_t *index) {
+    uint32_t code = 0;
+    index[0] = index[1] = 0;
+    first[0] = 0;
+    for (int l = 1; l <= kMaxLen; l++) {
+        code = l > 1 ? (code + per_len[l - 1]) << 1 : 0u;
+        first[l] = code;
+        index[l + 1] = index[l] + per_len[l];
+    }
+}
+
+// (length, symbol) sort of the alphabet's used symbols into keys[0, n) as length << 12 | symbol.
+__device__ uint32_t sort_by_length(const uint8_t *len, uint32_t alph, unsigned long long *keys, uint32_t *red) {
+    // compaction in symbol order: each thread owns a run of consecutive symbols
+    const uint32_t per = (alph + blockDim.x - 1) / blockDim.x;
+    const uint32_t s0 = min(alph, threadIdx.x * per), s1 = min(alph, s0 + per);
+    uint32_t own = 0;
+    for (uint32_t s = s0; s < s1; s++) own += len[s] != 0;
+    uint32_t n = 0;
+    uint32_t pos = block_excl(own, red, &n);
+    for (uint32_t s = s0; s < s1; s++)
+        if (len[s]) keys[pos++] = (unsigned long long)len[s] << 12 | s;
+    uint32_t P = 2;
+    while (P < n) P <<= 1;
+    for (uint32_t i = n + threadIdx.x; i < P; i += blockDim.x) keys[i] = ~0ull;
+    __syncthreads();
+    bitonic_sort(keys, P);
+    return n;
+}
+
+struct BuildSmem {
+    unsigned long long keys[kMaxAlph];
+    uint32_t hist[kMaxAlph];        // counts; then the internal nodes' weights
+    uint16_t leaf_parent[kMaxAlph];
+    uint16_t node_parent[kMaxAlph];
+    uint16_t node_depth[kMaxAlph];
+    uint8_t len[kMaxAlph];
+    uint32_t red[32];
+    uint32_t per_len[kMaxLen + 1];
+    uint32_t first[kMaxLen + 1];
+    uint32_t index[kMaxLen + 2];
+    uint32_t flag;
+};
+
+// grid (5 symbol sections, nframes), kBuildThreads threads
+__global__ void __launch_bounds__(kBuildThreads) k_ent_build(EntBatch b, Scratch sc, unsigned *err) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    BuildSmem &S = *reinterpret_cast<BuildSmem *>(smem_raw);
+    const int sid_of[5] = {0, 1, 4, 5, 6};
+    const int s = sid_of[blockIdx.x], f = blockIdx.y;
+    const int tid = threadIdx.x;
+    Frame &F = sc.frame[f];
+    Layout L;
+    const bool valid = parse_fixed(b.in[f], b.in_size[f], b.rows, b.cols, L);
+    if (!valid) {
+        if (blockIdx.x == 0 && tid == 0) {
+            F.ok = 0;
+            atomicOr(err, E_CORRUPT);
+        }
+        return;
+    }
+    if (blockIdx.x == 0 && tid == 0) {
+        F.L = L;
+        for (int k = 2; k <= 3; k++) {   // the run planes and temporal records are copied
+            F.sec[k].mode = 0;
+            F.sec[k].alph = 0;
+            F.sec[k].nch = 0;
+            F.sec[k].words = L.words[k];
+        }
+    }
+    Sec &out = F.sec[s];
+    const uint32_t w = L.width[s], cnt = L.count[s];
+    if (!coded_width(w) || cnt == 0) {
+        if (tid == 0) {
+            out.mode = 0;
+            out.alph = 0;
+            out.nch = 0;
+            out.words = L.words[s];
+        }
+        return;
+    }
+    const uint32_t *sec = reinterpret_cast<const uint32_t *>(b.in[f] + kHeaderBytes) + L.off[s];
+    // histogram
+    for (int i = tid; i < kMaxAlph; i += blockDim.x) {
+        S.hist[i] = 0;
+        S.len[i] = 0;
+    }
+    __syncthreads();
+    for (uint32_t i = tid; i < cnt; i += blockDim.x) atomicAdd(&S.hist[get_sym(sec, w, i)], 1u);
+    __syncthreads();
+    uint32_t top = 0;
+    for (uint32_t v = tid; v < (1u << w); v += blockDim.x)
+        if (S.hist[v]) top = v + 1;
+    const uint32_t alph = block_max(top, S.red);
+    // used symbols as (count << 12 | symbol), in symbol order
+    const uint32_t per = (alph + blockDim.x - 1) / blockDim.x;
+    const uint32_t s0 = min(alph, tid * per), s1 = min(alph, s0 + per);
+    uint32_t own = 0;
+    for (uint32_t v = s0; v < s1; v++) own += S.hist[v] != 0;
+    uint32_t n = 0;
+    uint32_t pos = block_excl(own, S.red, &n);
+    for (uint32_t v = s0; v < s1; v++)
+        if (S.hist[v]) S.keys[pos++] = (unsigned long long)S.hist[v] << 12 | v;
+    __syncthreads();
+    if (n == 1) {
+        if (tid == 0) S.len[S.keys[0] & 0xFFFu] = 1;
+    } else {
+        uint32_t P = 2;
+        while (P < n) P <<= 1;
+        for (;;) {
+            for (uint32_t i = n + tid; i < P; i += blockDim.x) S.keys[i] = ~0ull;
+            __syncthreads();
+            bitonic_sort(S.keys, P);
+            if (tid == 0) {
+                // two queues: leaves in (count, symbol) order, internal nodes in order of creation
+                uint32_t li = 0, ni = 0;
+                for (uint32_t k = 0; k + 1 < n; k++) {
+                    uint32_t wsum = 0;
+                    for (int pick = 0; pick < 2; pick++) {
+                        const bool leaf = li < n && (ni >= k || (uint32_t)(S.keys[li] >> 12) <= S.hist[ni]);
+                        if (leaf) {
+                            wsum += (uint32_t)(S.keys[li] >> 12);
+                            S.leaf_parent[li++] = (uint16_t)k;
+                        } else {
+                            wsum += S.hist[ni];
+                            S.node_parent[ni++] = (uint16_t)k;
+                        }
+                    }
+                    S.hist[k] = wsum;
+                }
+                // the root is the last node made; children are made before their parents
+                S.node_depth[n - 2] = 0;
+                for (int k = (int)n - 3; k >= 0; k--) S.node_depth[k] = S.node_depth[S.node_parent[k]] + 1;
+                uint32_t deepest = 0;
+                for (uint32_t i = 0; i < n; i++) deepest = max(deepest, (uint32_t)S.node_depth[S.leaf_parent[i]] + 1);
+                S.flag = deepest > (uint32_t)kMaxLen;
+            }
+            __syncthreads();
+            if (!S.flag) break;
+            // too deep: halve every count (rounding up) and build again
+            for (uint32_t i = tid; i < n; i += blockDim.x) {
+                const unsigned long long c = S.keys[i] >> 12;
+                S.keys[i] = ((c + 1) >> 1) << 12 | (S.keys[i] & 0xFFFu);
+            }
+            __syncthreads();
+        }
+        for (uint32_t i = tid; i < n; i += blockDim.x)
+            S.len[S.keys[i] & 0xFFFu] = (uint8_t)(S.node_depth[S.leaf_parent[i]] + 1);
+    }
+    __syncthreads();
+    // canonical codes: rank in (length, symbol) order
+    if (tid <= kMaxLen) S.per_len[tid] = 0;
+    __syncthreads();
+    for (uint32_t v = tid; v < alph; v += blockDim.x)
+        if (S.len[v]) atomicAdd(&S.per_len[S.len[v]], 1u);
+    __syncthreads();
+    if (tid == 0) canonical_tables(S.per_len, S.first, S.index);
+    __syncthreads();
+    const uint32_t nused = sort_by_length(S.len, alph, S.keys, S.red);
+    const size_t tab = ((size_t)f * kSecs + s) * kMaxAlph;
+    for (uint32_t i = tid; i < nused; i += blockDim.x) {
+        const uint32_t l = (uint32_t)(S.keys[i] >> 12), v = (uint32_t)(S.keys[i] & 0xFFFu);
+        const uint32_t code = S.first[l] + (i - S.index[l]);
+        sc.rcode[tab + v] = (uint16_t)(__brev(code) >> (32 - l));
+    }
+    for (uint32_t v = tid; v < alph; v += blockDim.x) sc.len[tab + v] = S.len[v];
+    // chunk sizes
+    const uint32_t nch = (cnt + kChunk - 1) / kChunk;
+    uint32_t *cw = sc.chunk + ((size_t)f * kSecs + s) * sc.max_chunks;
+    uint32_t mine = 0;
+    for (uint32_t c = tid; c < nch; c += blockDim.x) {
+        const uint32_t e = min(cnt, (c + 1) * kChunk);
+        uint32_t bits = 0;
+        for (uint32_t i = c * kChunk; i < e; i++) bits += S.len[get_sym(sec, w, i)];
+        cw[c] = (bits + 31) / 32;
+        mine += (bits + 31) / 32;
+    }
+    const uint32_t payload = block_sum(mine, S.red);
+    if (tid == 0) {
+        const uint32_t coded = (alph + 7) / 8 + nch + payload;
+        out.mode = coded < L.words[s] ? 1u : 0u;
+        out.alph = out.mode ? alph : 0u;
+        out.nch = out.mode ? nch : 0u;
+        out.words = out.mode ? coded : L.words[s];
+    }
+}
+
+// grid nframes, 32 threads
+__global__ void k_ent_layout(EntBatch b, Scratch sc, unsigned *err, int nframes) {
+    const int f = blockIdx.x, lane = threadIdx.x;
+    if (f >= nframes) return;
+    Frame &F = sc.frame[f];
+    Layout L;
+    if (!parse_fixed(b.in[f], b.in_size[f], b.rows, b.cols, L)) {
+        if (lane == 0) b.out_bytes[f] = 0;
+        return;
+    }
+    uint32_t eo[kSecs];   // every lane computes the section offsets
+    uint32_t off = kEntHeaderWords;
+    for (int s = 0; s < kSecs; s++) {
+        eo[s] = off;
+        off += F.sec[s].words;
+    }
+    if (lane < kSecs) F.sec[lane].ent_off = eo[lane];
+    const unsigned long long total = 4ull * off;
+    if (total > b.out_cap[f]) {
+        if (lane == 0) {
+            F.ok = 0;
+            b.out_bytes[f] = total;
+            atomicOr(err, E_CAPACITY);
+        }
+        return;
+    }
+    uint32_t *o = reinterpret_cast<uint32_t *>(b.out[f]);
+    const uint32_t *h = reinterpret_cast<const uint32_t *>(b.in[f]);
+    if (lane < 16) o[lane] = h[lane];
+    if (lane == 16) o[16] = kEntMagic;
+    if (lane == 17) o[17] = (uint32_t)total;
+    if (lane < kSecs) {
+        const Sec &S = F.sec[lane];
+        o[18 + 4 * lane] = S.mode ? (1u | L.width[lane] << 8) : 0u;
+        o[19 + 4 * lane] = S.mode ? L.count[lane] : L.words[lane];
+        o[20 + 4 * lane] = S.alph;
+        o[21 + 4 * lane] = S.words;
+    }
+    for (int s = 0; s < kSecs; s++) {
+        const Sec &S = F.sec[s];
+        if (!S.mode) continue;
+        uint32_t *dst = o + eo[s];
+        const uint8_t *len = sc.len + ((size_t)f * kSecs + s) * kMaxAlph;
+        const uint32_t tw = (S.alph + 7) / 8;
+        for (uint32_t j = lane; j < tw; j += 32) {
+            uint32_t v = 0;
+            for (uint32_t k = 0; k < 8 && 8 * j + k < S.alph; k++) v |= (uint32_t)len[8 * j + k] << (4 * k);
+            dst[j] = v;
+        }
+        // chunk offsets: exclusive prefix of the chunk sizes, kept in place for the writer
+        uint32_t *cw = sc.chunk + ((size_t)f * kSecs + s) * sc.max_chunks;
+        uint32_t carry = 0;
+        for (uint32_t c0 = 0; c0 < S.nch; c0 += 32) {
+            const uint32_t c = c0 + lane;
+            const uint32_t v = c < S.nch ? cw[c] : 0u;
+            uint32_t x = v;
+            for (int d = 1; d < 32; d <<= 1) {
+                const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, x, d);
+                if (lane >= d) x += y;
+            }
+            if (c < S.nch) {
+                cw[c] = carry + x - v;
+                dst[tw + c] = carry + x - v;
+            }
+            carry += __shfl_sync(0xFFFFFFFFu, x, 31);
+        }
+    }
+    if (lane == 0) {
+        F.ok = 1;
+        b.out_bytes[f] = total;
+    }
+}
+
+// grid (G, 7 sections, nframes), kWriteThreads threads: chunks and copied words with stride G
+__global__ void __launch_bounds__(kWriteThreads) k_ent_write(EntBatch b, Scratch sc) {
+    const int s = blockIdx.y, f = blockIdx.z;
+    const Frame &F = sc.frame[f];
+    if (!F.ok) return;
+    const Sec &S = F.sec[s];
+    const Layout &L = F.L;
+    const uint32_t *sec = reinterpret_cast<const uint32_t *>(b.in[f] + kHeaderBytes) + L.off[s];
+    uint32_t *dst = reinterpret_cast<uint32_t *>(b.out[f]) + S.ent_off;
+    if (!S.mode) {
+        for (uint32_t base = blockIdx.x * kCopyWords; base < L.words[s]; base += gridDim.x * kCopyWords) {
+            const uint32_t e = min(L.words[s], base + kCopyWords);
+            for (uint32_t i = base + threadIdx.x; i < e; i += blockDim.x) dst[i] = sec[i];
+        }
+        return;
+    }
+    const size_t tab = ((size_t)f * kSecs + s) * kMaxAlph;
+    const uint8_t *len = sc.len + tab;
+    const uint16_t *rcode = sc.rcode + tab;
+    const uint32_t *coff = sc.chunk + ((size_t)f * kSecs + s) * sc.max_chunks;
+    const uint32_t w = L.width[s], cnt = L.count[s];
+    uint32_t *pay = dst + (S.alph + 7) / 8 + S.nch;
+    for (uint32_t c = blockIdx.x * blockDim.x + threadIdx.x; c < S.nch; c += gridDim.x * blockDim.x) {
+        uint32_t *o = pay + coff[c];
+        unsigned long long acc = 0;
+        uint32_t nb = 0;
+        const uint32_t e = min(cnt, (c + 1) * kChunk);
+        for (uint32_t i = c * kChunk; i < e; i++) {
+            const uint32_t v = get_sym(sec, w, i);
+            acc |= (unsigned long long)rcode[v] << nb;
+            nb += len[v];
+            if (nb >= 32) {
+                *o++ = (uint32_t)acc;
+                acc >>= 32;
+                nb -= 32;
+            }
+        }
+        if (nb) *o = (uint32_t)acc;
+    }
+}
+
+// ---- decoder ----
+
+struct DecSmem {
+    uint8_t len[kMaxAlph];
+    uint32_t red[32];
+    uint32_t per_len[kMaxLen + 1];
+    uint32_t first[kMaxLen + 1];
+    uint32_t index[kMaxLen + 2];
+    unsigned long long keys[kMaxAlph];
+    uint32_t bad;
+};
+
+// Descriptor words of section s and the section's word offset; false if they cannot be this
+// frame's (layout L, stream of ent_words words).
+__device__ bool read_desc(const uint32_t *e, uint32_t ent_words, const Layout &L, int s, uint32_t &mode,
+                          uint32_t &alph, uint32_t &words, uint32_t &off) {
+    uint32_t o = kEntHeaderWords;
+    for (int k = 0; k < s; k++) o += e[21 + 4 * k];
+    const uint32_t mw = e[18 + 4 * s], count = e[19 + 4 * s];
+    alph = e[20 + 4 * s];
+    words = e[21 + 4 * s];
+    off = o;
+    if ((unsigned long long)o + words > ent_words) return false;
+    if (mw == 0) {
+        mode = 0;
+        return count == L.words[s] && words == L.words[s] && alph == 0;
+    }
+    mode = 1;
+    if (mw != (1u | L.width[s] << 8) || !coded_width(L.width[s]) || count != L.count[s] || alph < 1 ||
+        alph > (1u << L.width[s]))
+        return false;
+    const uint32_t nch = (count + kChunk - 1) / kChunk;
+    return (unsigned long long)(alph + 7) / 8 + nch <= words;
+}
+
+// grid (7 sections, nframes), 256 threads
+__global__ void __launch_bounds__(256) k_ent_dec_prep(EntBatch b, Scratch sc, unsigned *err) {
+    __shared__ DecSmem S;
+    const int s = blockIdx.x, f = blockIdx.y, tid = threadIdx.x;
+    Frame &F = sc.frame[f];
+    const uint32_t *e = reinterpret_cast<const uint32_t *>(b.in[f]);
+    if (tid == 0) S.bad = 0;
+    __syncthreads();
+    // header checks (every block repeats them; all read the same words)
+    Layout L;
+    bool ok = b.in_size[f] >= 4ull * kEntHeaderWords && e[16] == kEntMagic && e[17] % 4 == 0 &&
+              e[17] >= 4u * kEntHeaderWords && e[17] <= b.in_size[f];
+    if (ok) {
+        // the fixed-width header with a body of the size it states
+        ok = parse_fixed(b.in[f], ~0ull, b.rows, b.cols, L) && L.total <= b.out_cap[f];
+    }
+    uint32_t mode = 0, alph = 0, words = 0, off = 0;
+    if (ok) {
+        const uint32_t ew = e[17] / 4;
+        unsigned long long sum = kEntHeaderWords;
+        for (int k = 0; k < kSecs; k++) sum += e[21 + 4 * k];
+        ok = sum == ew && read_desc(e, ew, L, s, mode, alph, words, off);
+    }
+    if (!ok) {
+        if (tid == 0) {
+            atomicOr(&F.ok, 2u);   // bit 1: corrupt
+            atomicOr(err, E_CORRUPT);
+        }
+        return;
+    }
+    Sec &D = F.sec[s];
+    if (tid == 0) {
+        D.mode = mode;
+        D.alph = alph;
+        D.words = words;
+        D.ent_off = off;
+        D.nch = mode ? (L.count[s] + kChunk - 1) / kChunk : 0u;
+        if (s == 0) F.L = L;
+    }
+    if (s == 0 && tid < 16) reinterpret_cast<uint32_t *>(b.out[f])[tid] = e[tid];
+    if (s == 0 && tid == 0) b.out_bytes[f] = L.total;
+    if (!mode) return;
+    // length table, Kraft sum, canonical tables, symbols in (length, symbol) order
+    const uint32_t *sec = e + off;
+    for (uint32_t v = tid; v < alph; v += blockDim.x) S.len[v] = (sec[v / 8] >> (4 * (v % 8))) & 15u;
+    if (tid <= kMaxLen) S.per_len[tid] = 0;
+    __syncthreads();
+    uint32_t kraft = 0;
+    for (uint32_t v = tid; v < alph; v += blockDim.x)
+        if (S.len[v]) {
+            atomicAdd(&S.per_len[S.len[v]], 1u);
+            kraft += 1u << (kMaxLen - S.len[v]);
+        }
+    kraft = block_sum(kraft, S.red);
+    if (kraft == 0 || kraft > (1u << kMaxLen)) {
+        if (tid == 0) {
+            atomicOr(&F.ok, 2u);
+            atomicOr(err, E_CORRUPT);
+        }
+        return;
+    }
+    if (tid == 0) {
+        canonical_tables(S.per_len, S.first, S.index);
+        for (int l = 0; l <= kMaxLen; l++) {
+            D.per_len[l] = S.per_len[l];
+            D.first[l] = S.first[l];
+        }
+        for (int l = 0; l <= kMaxLen + 1; l++) D.index[l] = S.index[l];
+    }
+    const uint32_t n = sort_by_length(S.len, alph, S.keys, S.red);
+    uint16_t *sorted = sc.sorted + ((size_t)f * kSecs + s) * kMaxAlph;
+    for (uint32_t i = tid; i < n; i += blockDim.x) sorted[i] = (uint16_t)(S.keys[i] & 0xFFFu);
+    // chunk offsets non-decreasing, inside the payload
+    const uint32_t nch = (L.count[s] + kChunk - 1) / kChunk, tw = (alph + 7) / 8;
+    const uint32_t pay = words - tw - nch;
+    const uint32_t *co = sec + tw;
+    uint32_t badc = 0;
+    for (uint32_t c = tid; c < nch; c += blockDim.x) {
+        const uint32_t hi = c + 1 < nch ? co[c + 1] : pay;
+        if (co[c] > hi || hi > pay) badc = 1;
+    }
+    if (block_sum(badc, S.red) && tid == 0) {
+        atomicOr(&F.ok, 2u);
+        atomicOr(err, E_CORRUPT);
+    }
+}
+
+// grid (G, 7 sections, nframes), kWriteThreads threads
+__global__ void __launch_bounds__(kWriteThreads) k_ent_dec(EntBatch b, Scratch sc, unsigned *err) {
+    __shared__ uint32_t s_first[kMaxLen + 1], s_cnt[kMaxLen + 1], s_index[kMaxLen + 2];
+    const int s = blockIdx.y, f = blockIdx.z;
+    const Frame &F = sc.frame[f];
+    if (F.ok & 2u) return;
+    const Sec &D = F.sec[s];
+    const Layout &L = F.L;
+    const uint32_t *src = reinterpret_cast<const uint32_t *>(b.in[f]) + D.ent_off;
+    uint32_t *dst = reinterpret_cast<uint32_t *>(b.out[f] + kHeaderBytes) + L.off[s];
+    if (!D.mode) {
+        for (uint32_t base = blockIdx.x * kCopyWords; base < L.words[s]; base += gridDim.x * kCopyWords) {
+            const uint32_t e = min(L.words[s], base + kCopyWords);
+            for (uint32_t i = base + threadIdx.x; i < e; i += blockDim.x) dst[i] = src[i];
+        }
+        return;
+    }
+    if (threadIdx.x <= kMaxLen) {
+        s_first[threadIdx.x] = D.first[threadIdx.x];
+        s_cnt[threadIdx.x] = D.per_len[threadIdx.x];
+    }
+    if (threadIdx.x <= kMaxLen + 1) s_index[threadIdx.x] = D.index[threadIdx.x];
+    __syncthreads();
+    const uint16_t *sorted = sc.sorted + ((size_t)f * kSecs + s) * kMaxAlph;
+    const uint32_t w = L.width[s], cnt = L.count[s];
+    const uint32_t tw = (D.alph + 7) / 8, nch = D.nch;
+    const uint32_t *co = src + tw;
+    const uint32_t *pay = co + nch;
+    const uint32_t pay_words = D.words - tw - nch;
+    for (uint32_t c = blockIdx.x * blockDim.x + threadIdx.x; c < nch; c += gridDim.x * blockDim.x) {
+        const uint32_t beg = co[c], end = c + 1 < nch ? co[c + 1] : pay_words;   // validated by the prep
+        const unsigned long long end_bit = 32ull * end;
+        unsigned long long p = 32ull * beg;
+        uint32_t *o = dst + (size_t)c * kChunk * w / 32;   // 1024 symbols of w bits fill whole words
+        unsigned long long acc = 0;
+        uint32_t nb = 0;
+        const uint32_t m = min(cnt - c * kChunk, (uint32_t)kChunk);
+        bool bad = false;
+        for (uint32_t i = 0; i < m && !bad; i++) {
+            uint32_t code = 0, sym = 0;
+            int l = 1;
+            for (;; l++) {
+                if (l > kMaxLen || p >= end_bit) {
+                    bad = true;
+                    break;
+                }
+                code = code << 1 | ((pay[p >> 5] >> (p & 31)) & 1u);
+                p++;
+                if (code - s_first[l] < s_cnt[l]) {
+                    sym = sorted[s_index[l] + code - s_first[l]];
+                    break;
+                }
+            }
+            if (bad) break;
+            acc |= (unsigned long long)sym << nb;
+            nb += w;
+            if (nb >= 32) {
+                *o++ = (uint32_t)acc;
+                acc >>= 32;
+                nb -= 32;
+            }
+        }
+        if (bad) {
+            atomicOr(err, E_CORRUPT);
+            continue;
+        }
+        if (nb) *o = (uint32_t)acc;
+    }
+}
+
+}  // namespace ent
+}  // namespace lcc
+
+// ---- host side ----
+
+namespace {
+
+using namespace lcc;
+using namespace lcc::api;
+
+lcc_status ent_scratch(lcc_ctx *c, ent::Scratch &sc) {
+    const uint64_t npx = (uint64_t)c->g.H * c->g.W;
+    const uint32_t max_chunks = (uint32_t)((npx + 64 + ent::kChunk - 1) / ent::kChunk);
+    const size_t slots = (size_t)c->slots;
+    const size_t per = (size_t)ent::kSecs * ent::kMaxAlph;
+    const size_t bytes = align256(slots * sizeof(ent::Frame)) + align256(slots * per) +
+                         2 * align256(slots * per * 2) + align256(slots * ent::kSecs * max_chunks * 4);
+    if (!c->d_ent) {
+        if (cudaMalloc(&c->d_ent, bytes) != cudaSuccess) {
+            c->d_ent = nullptr;
+            return LCC_ERR_CUDA;
+        }
+    }
+    unsigned char *p = static_cast<unsigned char *>(c->d_ent);
+    sc.frame = reinterpret_cast<ent::Frame *>(p);
+    p += align256(slots * sizeof(ent::Frame));
+    sc.len = p;
+    p += align256(slots * per);
+    sc.rcode = reinterpret_cast<uint16_t *>(p);
+    p += align256(slots * per * 2);
+    sc.sorted = reinterpret_cast<uint16_t *>(p);
+    p += align256(slots * per * 2);
+    sc.chunk = reinterpret_cast<uint32_t *>(p);
+    sc.max_chunks = max_chunks;
+    return LCC_OK;
+}
+
+int grid_x(lcc_ctx *c, const ent::Scratch &sc) {
+    const uint64_t words = c->max_bytes / 4;
+    const uint64_t by_copy = (words + ent::kCopyWords - 1) / ent::kCopyWords;
+    const uint64_t by_chunk = (sc.max_chunks + ent::kWriteThreads - 1) / ent::kWriteThreads;
+    uint64_t g = by_copy > by_chunk ? by_copy : by_chunk;
+    return (int)(g < 1 ? 1 : (g > 64 ? 64 : g));
+}
+
+lcc_status fill_batch(lcc_ctx *c, ent::EntBatch &b, int nframes, const uint8_t *const *d_in, const uint64_t *in_size,
+                      uint8_t *const *d_out, const uint64_t *out_cap, uint64_t *d_out_bytes) {
+    memset(&b, 0, sizeof(b));
+    for (int f = 0; f < nframes; f++) {
+        if (!d_in[f] || !d_out[f] || !aligned16(d_in[f]) || !aligned16(d_out[f])) return LCC_ERR_INVALID_ARG;
+        b.in[f] = d_in[f];
+        b.out[f] = d_out[f];
+        b.in_size[f] = in_size[f];
+        b.out_cap[f] = out_cap[f];
+    }
+    b.out_bytes = reinterpret_cast<unsigned long long *>(d_out_bytes);
+    b.rows = (uint32_t)c->g.H;
+    b.cols = (uint32_t)c->g.W;
+    return LCC_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+lcc_status lcc_entropy_encode(lcc_ctx *c, int32_t nframes, const uint8_t *const *d_in, const uint64_t *in_size,
+                              uint8_t *const *d_out, const uint64_t *out_cap, uint64_t *d_out_bytes) {
+    if (!c || !d_in || !in_size || !d_out || !out_cap || !d_out_bytes || nframes < 1 || nframes > c->slots ||
+        !aligned16(d_out_bytes))
+        return LCC_ERR_INVALID_ARG;
+    ent::EntBatch b;
+    lcc_status st = fill_batch(c, b, nframes, d_in, in_size, d_out, out_cap, d_out_bytes);
+    if (st != LCC_OK) return st;
+    ent::Scratch sc;
+    if ((st = ent_scratch(c, sc)) != LCC_OK) return st;
+    const size_t smem = sizeof(ent::BuildSmem);
+    LCC_CUDA(cudaFuncSetAttribute(ent::k_ent_build, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    LCC_LAUNCH(c, 10, (ent::k_ent_build<<<dim3(5, nframes), ent::kBuildThreads, smem, c->stream>>>(b, sc, c->s.err),
+                       cudaGetLastError()));
+    LCC_LAUNCH(c, 11, (ent::k_ent_layout<<<nframes, 32, 0, c->stream>>>(b, sc, c->s.err, nframes), cudaGetLastError()));
+    LCC_LAUNCH(c, 12, (ent::k_ent_write<<<dim3(grid_x(c, sc), ent::kSecs, nframes), ent::kWriteThreads, 0, c->stream>>>(
+                           b, sc),
+                       cudaGetLastError()));
+    return LCC_OK;
+}
+
+lcc_status lcc_entropy_decode(lcc_ctx *c, int32_t nframes, const uint8_t *const *d_in, const uint64_t *in_bytes,
+                              uint8_t *const *d_out, const uint64_t *out_cap, uint64_t *d_out_bytes) {
+    if (!c || !d_in || !in_bytes || !d_out || !out_cap || !d_out_bytes || nframes < 1 || nframes > c->slots ||
+        !aligned16(d_out_bytes))
+        return LCC_ERR_INVALID_ARG;
+    ent::EntBatch b;
+    lcc_status st = fill_batch(c, b, nframes, d_in, in_bytes, d_out, out_cap, d_out_bytes);
+    if (st != LCC_OK) return st;
+    ent::Scratch sc;
+    if ((st = ent_scratch(c, sc)) != LCC_OK) return st;
+    // clear the frames' state words (bit 1 marks a corrupt frame)
+    for (int f = 0; f < nframes; f++)
+        LCC_CUDA(cudaMemsetAsync(&sc.frame[f].ok, 0, sizeof(uint32_t), c->stream));
+    LCC_LAUNCH(c, 13, (ent::k_ent_dec_prep<<<dim3(ent::kSecs, nframes), 256, 0, c->stream>>>(b, sc, c->s.err),
+                       cudaGetLastError()));
+    LCC_LAUNCH(c, 13, (ent::k_ent_dec<<<dim3(grid_x(c, sc), ent::kSecs, nframes), ent::kWriteThreads, 0, c->stream>>>(
+                           b, sc, c->s.err),
+                       cudaGetLastError()));
+    return LCC_OK;
+}
+
+}  // extern "C"

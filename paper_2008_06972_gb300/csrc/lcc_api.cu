@@ -18,8 +18,9 @@ using namespace lcc;
 namespace lcc {
 namespace api {
 
-const char *kKernelNames[] = {"bin",          "fit",   "merge", "rounds",  "pack", "decode_prep",
-                              "decode_px",    "range_export",   "lookbehind",   "temporal"};
+const char *kKernelNames[] = {"bin",        "fit",          "merge",      "rounds",    "pack",
+                              "decode_prep", "decode_px",    "range_export", "lookbehind", "temporal",
+                              "ent_build",  "ent_layout",   "ent_write",  "ent_decode"};
 
 cudaEvent_t get_event(lcc_ctx *c) {
     if (!c->pool.empty()) {
@@ -424,6 +425,7 @@ lcc_status lcc_destroy(lcc_ctx *c) {
     if (c->ev_kdone) cudaEventDestroy(c->ev_kdone);
     cudaFree(c->d_tables);
     cudaFree(c->d_scratch);
+    cudaFree(c->d_ent);
     cudaFree(c->d_stage_pts);
     cudaFree(c->d_stage_out);
     cudaFree(c->d_stage_bytes);

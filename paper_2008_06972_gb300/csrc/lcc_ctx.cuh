@@ -26,7 +26,7 @@ struct TimelineRec {
 };
 constexpr size_t kMaxTimeline = 65536;
 
-constexpr int kNumKernels = 10;
+constexpr int kNumKernels = 14;
 extern const char *kKernelNames[];
 
 inline size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
@@ -53,6 +53,7 @@ struct lcc_ctx {
     void *d_scratch = nullptr;
     lcc::DecTile *d_dec = nullptr;      // decoder state: per slot NT DecTiles, then a DecState
     float4 *d_kplanes = nullptr;        // key-frame coding planes of lcc_decode_sequence
+    void *d_ent = nullptr;              // entropy-stage scratch (allocated on first use)
     std::vector<float> h_tables;  // ce, se, ct, st, rbc, rbs, cbc, cbs
     int slots = 0;
     int num_sms = 0;   // SMs of the context's device

@@ -75,7 +75,7 @@ assert TILE_INFO_DTYPE.itemsize == 64
 
 _lib = None
 KERNEL_NAMES = ("bin", "fit", "merge", "rounds", "pack", "decode_prep", "decode_px", "range_export", "lookbehind",
-                "temporal")
+                "temporal", "ent_build", "ent_layout", "ent_write", "ent_decode")
 
 
 def load(path: str = LIB_PATH):
@@ -109,6 +109,8 @@ def load(path: str = LIB_PATH):
         "lcc_decode": (i32, [vp, vp, u64, vp, vp, vp, vp, vp]),
         "lcc_decode_sequence": (i32, [vp, i32, i32, vp, vp, vp, vp, vp, vp]),
         "lcc_imu_pose": (i32, [vp, vp, vp, i32, vp, ctypes.c_double, ctypes.c_double, vp]),
+        "lcc_entropy_encode": (i32, [vp, i32, vp, vp, vp, vp, vp]),
+        "lcc_entropy_decode": (i32, [vp, i32, vp, vp, vp, vp, vp]),
         "lcc_sync": (i32, [vp]),
         "lcc_last_stats": (i32, [vp, i32, vp]),
         "lcc_tile_records": (i32, [vp, i32, vp, i64]),
@@ -152,7 +154,7 @@ def exported_symbols() -> list[str]:
     return ["lcc_status_string", "lcc_default_params", "lcc_create", "lcc_destroy", "lcc_max_encoded_bytes",
             "lcc_num_tiles", "lcc_tables", "lcc_range_image", "lcc_keyframe_create", "lcc_keyframe_free",
             "lcc_encode_keyframe", "lcc_encode_keyframe_seeded", "lcc_encode_keyframes", "lcc_encode_pframe", "lcc_encode_pframes", "lcc_encode_sequence",
-            "lcc_encode_sequence_host", "lcc_keyframe_from_stream", "lcc_decode", "lcc_decode_sequence", "lcc_imu_pose", "lcc_sync", "lcc_last_stats",
+            "lcc_encode_sequence_host", "lcc_keyframe_from_stream", "lcc_decode", "lcc_decode_sequence", "lcc_imu_pose", "lcc_entropy_encode", "lcc_entropy_decode", "lcc_sync", "lcc_last_stats",
             "lcc_tile_records", "lcc_set_profiling", "lcc_kernel_times", "lcc_kernel_timeline", "lcc_range_image_static", "lcc_net_num_params", "lcc_net_create", "lcc_net_destroy",
             "lcc_net_get_params", "lcc_net_set_params", "lcc_net_tile_inputs", "lcc_net_tile_inputs_batch", "lcc_net_forward", "lcc_net_sync", "lcc_net_gradient",
             "lcc_net_train_step", "lcc_selftest_bounded_wait", "lcc_plan_create", "lcc_plan_update",
@@ -362,6 +364,22 @@ class Context:
         bits_a, rng_a, xyz_a, val_a = arr(d_bits), arr(d_range), arr(d_xyz4), arr(d_valid)
         _check(self.lib.lcc_decode_sequence(self.h, n, key_index, pz.ctypes.data, bits_a, nb.ctypes.data, rng_a,
                                             xyz_a, val_a), "lcc_decode_sequence")
+
+    def _entropy(self, fn, name, d_in, in_size, d_out, out_cap, out_bytes):
+        n = len(d_in)
+        P = ctypes.c_void_p * n
+        isz = np.ascontiguousarray(np.asarray(in_size, dtype=np.uint64))
+        cap = np.ascontiguousarray(np.asarray(out_cap, dtype=np.uint64))
+        _check(fn(self.h, n, P(*[_ptr(x) for x in d_in]), isz.ctypes.data, P(*[_ptr(x) for x in d_out]),
+                  cap.ctypes.data, _ptr(out_bytes)), name)
+
+    def lcc_entropy_encode(self, d_in, in_size, d_out, out_cap, out_bytes):
+        """Entropy streams of fixed-width streams (device buffers; out_bytes a device uint64/int64 array)."""
+        self._entropy(self.lib.lcc_entropy_encode, "lcc_entropy_encode", d_in, in_size, d_out, out_cap, out_bytes)
+
+    def lcc_entropy_decode(self, d_in, in_bytes, d_out, out_cap, out_bytes):
+        """Fixed-width streams back from entropy streams (device buffers)."""
+        self._entropy(self.lib.lcc_entropy_decode, "lcc_entropy_decode", d_in, in_bytes, d_out, out_cap, out_bytes)
 
     def lcc_sync(self) -> int:
         return int(self.lib.lcc_sync(self.h))
