@@ -242,12 +242,12 @@ struct BuildSmem {
     uint16_t leaf_parent[kMaxAlph];
     uint16_t node_parent[kMaxAlph];
     uint16_t node_depth[kMaxAlph];
+    uint32_t lw[kMaxAlph];          // leaf weights in queue order
     uint8_t len[kMaxAlph];
     uint32_t red[32];
     uint32_t per_len[kMaxLen + 1];
     uint32_t first[kMaxLen + 1];
     uint32_t index[kMaxLen + 2];
-    uint32_t flag;
 };
 
 // grid (5 symbol sections, nframes), kBuildThreads threads
@@ -319,32 +319,59 @@ __global__ void __launch_bounds__(kBuildThreads) k_ent_build(EntBatch b, Scratch
             for (uint32_t i = n + tid; i < P; i += blockDim.x) S.keys[i] = ~0ull;
             __syncthreads();
             bitonic_sort(S.keys, P);
+            for (uint32_t i = tid; i < n; i += blockDim.x) S.lw[i] = (uint32_t)(S.keys[i] >> 12);
+            __syncthreads();
             if (tid == 0) {
-                // two queues: leaves in (count, symbol) order, internal nodes in order of creation
-                uint32_t li = 0, ni = 0;
+                // two queues: leaves in (count, symbol) order, internal nodes in order of creation;
+                // each queue's front weight is kept in a register (~0u: empty), a leaf goes first
+                // on equal weights
+                uint32_t li = 0, ni = 0, wl = S.lw[0], wn = ~0u;
                 for (uint32_t k = 0; k + 1 < n; k++) {
                     uint32_t wsum = 0;
+#pragma unroll
                     for (int pick = 0; pick < 2; pick++) {
-                        const bool leaf = li < n && (ni >= k || (uint32_t)(S.keys[li] >> 12) <= S.hist[ni]);
-                        if (leaf) {
-                            wsum += (uint32_t)(S.keys[li] >> 12);
+                        if (wl <= wn) {
+                            wsum += wl;
                             S.leaf_parent[li++] = (uint16_t)k;
+                            wl = li < n ? S.lw[li] : ~0u;
                         } else {
-                            wsum += S.hist[ni];
+                            wsum += wn;
                             S.node_parent[ni++] = (uint16_t)k;
+                            wn = ni < k ? S.hist[ni] : ~0u;
                         }
                     }
                     S.hist[k] = wsum;
+                    if (ni == k) wn = wsum;
                 }
-                // the root is the last node made; children are made before their parents
-                S.node_depth[n - 2] = 0;
-                for (int k = (int)n - 3; k >= 0; k--) S.node_depth[k] = S.node_depth[S.node_parent[k]] + 1;
-                uint32_t deepest = 0;
-                for (uint32_t i = 0; i < n; i++) deepest = max(deepest, (uint32_t)S.node_depth[S.leaf_parent[i]] + 1);
-                S.flag = deepest > (uint32_t)kMaxLen;
             }
             __syncthreads();
-            if (!S.flag) break;
+            // node depths by pointer jumping (children are made before parents, the root last):
+            // node_parent becomes an ancestor pointer and node_depth the edges up to it
+            for (uint32_t k = tid; k + 1 < n; k += blockDim.x) {
+                const bool root = k + 2 == n;
+                if (root) S.node_parent[k] = (uint16_t)k;
+                S.node_depth[k] = root ? 0 : 1;
+            }
+            __syncthreads();
+            for (int r = 0; r < kMaxWidth; r++) {   // 2^12 >= the 4095 nodes a tree can have
+                uint16_t na[kMaxAlph / kBuildThreads], nd[kMaxAlph / kBuildThreads];
+                int q = 0;
+                for (uint32_t k = tid; k + 1 < n; k += blockDim.x, q++) {
+                    const uint16_t a = S.node_parent[k];
+                    na[q] = S.node_parent[a];
+                    nd[q] = S.node_depth[k] + S.node_depth[a];
+                }
+                __syncthreads();
+                q = 0;
+                for (uint32_t k = tid; k + 1 < n; k += blockDim.x, q++) {
+                    S.node_parent[k] = na[q];
+                    S.node_depth[k] = nd[q];
+                }
+                __syncthreads();
+            }
+            uint32_t deep = 0;
+            for (uint32_t i = tid; i < n; i += blockDim.x) deep = max(deep, (uint32_t)S.node_depth[S.leaf_parent[i]] + 1);
+            if (block_max(deep, S.red) <= (uint32_t)kMaxLen) break;
             // too deep: halve every count (rounding up) and build again
             for (uint32_t i = tid; i < n; i += blockDim.x) {
                 const unsigned long long c = S.keys[i] >> 12;
@@ -482,9 +509,13 @@ __global__ void __launch_bounds__(kWriteThreads) k_ent_write(EntBatch b, Scratch
         }
         return;
     }
+    if (blockIdx.x * blockDim.x >= S.nch) return;
+    // the section's codes in shared memory: reversed code | length << 16
+    __shared__ uint32_t s_code[kMaxAlph];
     const size_t tab = ((size_t)f * kSecs + s) * kMaxAlph;
-    const uint8_t *len = sc.len + tab;
-    const uint16_t *rcode = sc.rcode + tab;
+    for (uint32_t v = threadIdx.x; v < S.alph; v += blockDim.x)
+        s_code[v] = (uint32_t)sc.rcode[tab + v] | (uint32_t)sc.len[tab + v] << 16;
+    __syncthreads();
     const uint32_t *coff = sc.chunk + ((size_t)f * kSecs + s) * sc.max_chunks;
     const uint32_t w = L.width[s], cnt = L.count[s];
     uint32_t *pay = dst + (S.alph + 7) / 8 + S.nch;
@@ -494,9 +525,9 @@ __global__ void __launch_bounds__(kWriteThreads) k_ent_write(EntBatch b, Scratch
         uint32_t nb = 0;
         const uint32_t e = min(cnt, (c + 1) * kChunk);
         for (uint32_t i = c * kChunk; i < e; i++) {
-            const uint32_t v = get_sym(sec, w, i);
-            acc |= (unsigned long long)rcode[v] << nb;
-            nb += len[v];
+            const uint32_t cl = s_code[get_sym(sec, w, i)];
+            acc |= (unsigned long long)(cl & 0xFFFFu) << nb;
+            nb += cl >> 16;
             if (nb >= 32) {
                 *o++ = (uint32_t)acc;
                 acc >>= 32;
@@ -629,9 +660,13 @@ __global__ void __launch_bounds__(256) k_ent_dec_prep(EntBatch b, Scratch sc, un
     }
 }
 
+constexpr int kPeek = 9;   // codes up to this length resolve in one table lookup
+
 // grid (G, 7 sections, nframes), kWriteThreads threads
 __global__ void __launch_bounds__(kWriteThreads) k_ent_dec(EntBatch b, Scratch sc, unsigned *err) {
-    __shared__ uint32_t s_first[kMaxLen + 1], s_cnt[kMaxLen + 1], s_index[kMaxLen + 2];
+    __shared__ uint16_t s_sym[kMaxAlph];          // symbols in (length, symbol) order
+    __shared__ uint32_t s_peek[1 << kPeek];       // first kPeek bits -> symbol | length << 16 (0: longer)
+    __shared__ uint32_t s_lim[kMaxLen + 1], s_first[kMaxLen + 1], s_index[kMaxLen + 2];
     const int s = blockIdx.y, f = blockIdx.z;
     const Frame &F = sc.frame[f];
     if (F.ok & 2u) return;
@@ -646,13 +681,28 @@ __global__ void __launch_bounds__(kWriteThreads) k_ent_dec(EntBatch b, Scratch s
         }
         return;
     }
-    if (threadIdx.x <= kMaxLen) {
-        s_first[threadIdx.x] = D.first[threadIdx.x];
-        s_cnt[threadIdx.x] = D.per_len[threadIdx.x];
+    if (blockIdx.x * blockDim.x >= D.nch) return;
+    // canonical decode tables: per length the left-justified limit (codes of length l are the
+    // 15-bit windows in [limit(l - 1), limit(l))), and a direct table for the short codes
+    if (threadIdx.x == 0) {
+        for (int l = 1; l <= kMaxLen; l++) s_lim[l] = (D.first[l] + D.per_len[l]) << (kMaxLen - l);
     }
+    if (threadIdx.x <= kMaxLen) s_first[threadIdx.x] = D.first[threadIdx.x];
     if (threadIdx.x <= kMaxLen + 1) s_index[threadIdx.x] = D.index[threadIdx.x];
-    __syncthreads();
+    const uint32_t nused = D.index[kMaxLen + 1];
     const uint16_t *sorted = sc.sorted + ((size_t)f * kSecs + s) * kMaxAlph;
+    for (uint32_t i = threadIdx.x; i < nused; i += blockDim.x) s_sym[i] = sorted[i];
+    for (uint32_t i = threadIdx.x; i < (1u << kPeek); i += blockDim.x) s_peek[i] = 0;
+    __syncthreads();
+    for (uint32_t i = threadIdx.x; i < nused; i += blockDim.x) {
+        int l = 1;
+        while (l < kMaxLen && s_index[l + 1] <= i) l++;
+        if (l > kPeek) continue;
+        const uint32_t code = s_first[l] + (i - s_index[l]);
+        const uint32_t lo = code << (kPeek - l), hi = (code + 1) << (kPeek - l);
+        for (uint32_t x = lo; x < hi; x++) s_peek[x] = (uint32_t)s_sym[i] | (uint32_t)l << 16;
+    }
+    __syncthreads();
     const uint32_t w = L.width[s], cnt = L.count[s];
     const uint32_t tw = (D.alph + 7) / 8, nch = D.nch;
     const uint32_t *co = src + tw;
@@ -660,42 +710,54 @@ __global__ void __launch_bounds__(kWriteThreads) k_ent_dec(EntBatch b, Scratch s
     const uint32_t pay_words = D.words - tw - nch;
     for (uint32_t c = blockIdx.x * blockDim.x + threadIdx.x; c < nch; c += gridDim.x * blockDim.x) {
         const uint32_t beg = co[c], end = c + 1 < nch ? co[c + 1] : pay_words;   // validated by the prep
-        const unsigned long long end_bit = 32ull * end;
-        unsigned long long p = 32ull * beg;
+        uint32_t wp = beg;
+        unsigned long long buf = 0;   // stream bits, the next one in bit 0
+        int nb = 0;
         uint32_t *o = dst + (size_t)c * kChunk * w / 32;   // 1024 symbols of w bits fill whole words
         unsigned long long acc = 0;
-        uint32_t nb = 0;
+        uint32_t na = 0;
         const uint32_t m = min(cnt - c * kChunk, (uint32_t)kChunk);
         bool bad = false;
-        for (uint32_t i = 0; i < m && !bad; i++) {
-            uint32_t code = 0, sym = 0;
-            int l = 1;
-            for (;; l++) {
-                if (l > kMaxLen || p >= end_bit) {
+        for (uint32_t i = 0; i < m; i++) {
+            if (nb < 32 && wp < end) {
+                buf |= (unsigned long long)pay[wp++] << nb;
+                nb += 32;
+            }
+            // the next 15 stream bits, first bit most significant
+            const uint32_t v = __brev((uint32_t)buf & 0x7FFFu) >> (32 - kMaxLen);
+            uint32_t sym, l;
+            const uint32_t pk = s_peek[v >> (kMaxLen - kPeek)];
+            if (pk) {
+                sym = pk & 0xFFFFu;
+                l = pk >> 16;
+            } else {
+                l = kPeek + 1;
+                while (l <= (uint32_t)kMaxLen && v >= s_lim[l]) l++;
+                if (l > (uint32_t)kMaxLen) {
                     bad = true;
                     break;
                 }
-                code = code << 1 | ((pay[p >> 5] >> (p & 31)) & 1u);
-                p++;
-                if (code - s_first[l] < s_cnt[l]) {
-                    sym = sorted[s_index[l] + code - s_first[l]];
-                    break;
-                }
+                sym = s_sym[s_index[l] + (v >> (kMaxLen - l)) - s_first[l]];
             }
-            if (bad) break;
-            acc |= (unsigned long long)sym << nb;
-            nb += w;
-            if (nb >= 32) {
+            if ((int)l > nb) {
+                bad = true;
+                break;
+            }
+            buf >>= l;
+            nb -= (int)l;
+            acc |= (unsigned long long)sym << na;
+            na += w;
+            if (na >= 32) {
                 *o++ = (uint32_t)acc;
                 acc >>= 32;
-                nb -= 32;
+                na -= 32;
             }
         }
         if (bad) {
             atomicOr(err, E_CORRUPT);
             continue;
         }
-        if (nb) *o = (uint32_t)acc;
+        if (na) *o = (uint32_t)acc;
     }
 }
 
