@@ -68,6 +68,9 @@ typedef struct {
     int32_t no_delta;         /* 1: plane-coded points carry no residual code, the paper's default
                                  (Sec. III-C drops the deltas): they decode onto their plane, decode
                                  error <= fit_thr_m; 0 (default here): residual codes, error <= q/2 */
+    int32_t raw_exact;        /* 1: raw (unfit) pixels carry their fp32 range bits instead of a
+                                 q-quantised code, so they decode exactly (header flags bit 2, 32-bit
+                                 raw codes); 0 (default): raw codes m = round(r / q) */
 } lcc_params;
 
 /* Per-frame statistics of the last encode (Fig. 11's categories and more). */

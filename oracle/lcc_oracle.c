@@ -592,7 +592,7 @@ static void code_widths(const orc_sensor *s, const orc_params *prm, int *k_max, 
     int m_max = (int)floorf((float)s->max_range_m / prm->quant_m + 0.5f) + 1;
     w = 1;
     while ((1 << w) < m_max + 1) w++;
-    *w_raw = w;
+    *w_raw = prm->raw_exact ? 32 : w;   /* lossless raw pixels: the range's fp32 bits */
 }
 
 static int quant_res(float e, float q) {
@@ -692,8 +692,8 @@ static int header_read(const uint8_t *b, uint64_t nbytes, header_t *h) {
     h->n_raw = rd32(b + 48);
     h->k_max = (int32_t)rd32(b + 52);
     h->total_bytes = rd32(b + 56);
-    if (h->kind > 1 || (h->flags & ~3u) || h->tile_h == 0 || h->tile_w == 0 || h->w_res == 0 || h->w_res > 16 ||
-        h->w_raw == 0 || h->w_raw > 24 || !(h->q > 0))
+    if (h->kind > 1 || (h->flags & ~7u) || h->tile_h == 0 || h->tile_w == 0 || h->w_res == 0 || h->w_res > 16 ||
+        h->w_raw == 0 || ((h->flags & 4u) ? h->w_raw != 32 : h->w_raw > 24) || !(h->q > 0))
         return ORC_ERR_CORRUPT;
     uint64_t off[8];
     section_offsets(h, off);
@@ -775,7 +775,7 @@ int64_t orc_pack(const orc_sensor *s, const orc_params *prm, int kind, const flo
 
     /* 2. counts */
     h.kind = kind;
-    h.flags = (prm->merge_runs ? 1u : 0u) | (prm->no_delta ? 2u : 0u);
+    h.flags = (prm->merge_runs ? 1u : 0u) | (prm->no_delta ? 2u : 0u) | (prm->raw_exact ? 4u : 0u);
     h.rows = s->rows;
     h.cols = s->cols;
     h.tile_h = prm->tile_h;
@@ -846,7 +846,8 @@ int64_t orc_pack(const orc_sensor *s, const orc_params *prm, int kind, const flo
                         put_bits(w + off[5], ifit * w_res, (uint32_t)(quant_res(e, prm->quant_m) + k_max), w_res);
                     ifit++;
                 } else {
-                    put_bits(w + off[6], iraw * w_raw, (uint32_t)quant_raw(tp->r[k], prm->quant_m), w_raw);
+                    put_bits(w + off[6], iraw * w_raw,
+                             prm->raw_exact ? f2u(tp->r[k]) : (uint32_t)quant_raw(tp->r[k], prm->quant_m), w_raw);
                     iraw++;
                 }
             }
@@ -1059,7 +1060,7 @@ int orc_decode(const orc_sensor *s, const uint8_t *bits, uint64_t nbytes, const 
                     if (iraw >= st.h.n_raw) { r = ORC_ERR_CORRUPT; break; }
                     uint32_t m = get_bits(st.w + st.off[6], iraw * st.h.w_raw, st.h.w_raw);
                     iraw++;
-                    rr = (float)m * st.h.q;
+                    rr = (st.h.flags & 4u) ? u2f(m) : (float)m * st.h.q;
                 }
                 range[p] = rr;
                 if (xyz4) {

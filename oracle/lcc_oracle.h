@@ -42,6 +42,8 @@ typedef struct {
     int32_t merge_runs;          /* 1: grow runs of tiles horizontally (Sec. III-C) */
     int32_t no_delta;            /* 1: plane-coded points carry no residual code (Sec. III-C:
                                     the deltas are dropped, decode error <= threshold) */
+    int32_t raw_exact;           /* 1: raw pixels carry their fp32 range bits, so unfit points
+                                    are kept losslessly (header flags bit 2, 32-bit raw codes) */
 } orc_params;
 
 /* tile codes of the bitstream */

@@ -19,6 +19,7 @@ struct DecState {
     float q;
     int32_t k_max, w_res, w_raw;
     int32_t no_delta;   // plane-coded points carry no residual code
+    int32_t raw_exact;  // raw codes are the fp32 range bits
 };
 
 __device__ __forceinline__ uint32_t rd_u32(const uint8_t *p) {
@@ -101,11 +102,11 @@ __global__ void __launch_bounds__(kPrepThreads) k_decode_prep(Geometry g, DecBat
         if (!bad) {
             for (int q = 0; q < 16; q++) s_h[q] = rd_u32(bits + 4 * q);
             const uint32_t kind = (s_h[1] >> 16) & 0xff, flags = s_h[1] >> 24;
-            bad |= s_h[0] != kMagic || (s_h[1] & 0xffff) != (uint32_t)kVersion || (flags & ~3u);
+            bad |= s_h[0] != kMagic || (s_h[1] & 0xffff) != (uint32_t)kVersion || (flags & ~7u);
             bad |= (int)(s_h[2] & 0xffff) != g.H || (int)(s_h[2] >> 16) != g.W;
             bad |= (int)(s_h[3] & 0xff) != g.th || (int)((s_h[3] >> 8) & 0xff) != g.tw;
             const uint32_t w_res = (s_h[3] >> 16) & 0xff, w_raw = s_h[3] >> 24;
-            bad |= w_res == 0 || w_res > 16 || w_raw == 0 || w_raw > 24;
+            bad |= w_res == 0 || w_res > 16 || w_raw == 0 || ((flags & 4u) ? w_raw != 32 : w_raw > 24);
             bad |= s_h[6] != (uint32_t)g.NT || kind > 1 || (expect_kind >= 0 && kind != (uint32_t)expect_kind);
             bad |= !(__uint_as_float(s_h[5]) > 0.0f);
             if (kind == 1 && kf == nullptr) bad = 1;
@@ -263,6 +264,7 @@ __global__ void __launch_bounds__(kPrepThreads) k_decode_prep(Geometry g, DecBat
         st.w_res = (int32_t)((s_h[3] >> 16) & 0xff);
         st.w_raw = (int32_t)(s_h[3] >> 24);
         st.no_delta = (int32_t)((s_h[1] >> 25) & 1u);
+        st.raw_exact = (int32_t)((s_h[1] >> 26) & 1u);
         *state = st;
         if (bad) atomicOr(err, E_CORRUPT);
     }
@@ -337,7 +339,7 @@ __global__ void __launch_bounds__(kDecWarps * 32) k_decode_px(Geometry g, DecBat
             } else {
                 const int rrank = vrank[m] - frank;
                 const uint32_t mm = get_bits(w + st.sec[6], (uint64_t)(d.off_raw + rrank) * st.w_raw, st.w_raw);
-                r = __fmul_rn((float)mm, st.q);
+                r = st.raw_exact ? __uint_as_float(mm) : __fmul_rn((float)mm, st.q);
             }
         }
         if (range) range[p] = r;

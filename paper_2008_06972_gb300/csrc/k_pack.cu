@@ -135,7 +135,7 @@ __global__ void __launch_bounds__(kPackWarps * 32) k_pack(Geometry g, Scratch s,
             float e = 0.f;
             fit[m] = coded && residual(pl, ux[m], uy[m], uz[m], r, g.thr, e);
             if (fit[m]) kc[m] = (uint32_t)(quant_res(e, g.q) + g.k_max);
-            else mc[m] = quant_raw(r, g.q);
+            else mc[m] = g.raw_exact ? __float_as_uint(r) : quant_raw(r, g.q);
         }
     }
     if (!L.ok) return;

@@ -256,6 +256,7 @@ void lcc_default_params(lcc_params *p) {
     p->solver = 0;
     p->fit_schedule = 3;
     p->no_delta = 0;
+    p->raw_exact = 0;
 }
 
 lcc_status lcc_create(lcc_ctx **out, const lcc_sensor *sensor, const lcc_params *params, void *cuda_stream) {
@@ -271,7 +272,7 @@ lcc_status lcc_create(lcc_ctx **out, const lcc_sensor *sensor, const lcc_params 
     if (!(p.fit_thr_m >= 0) || !(p.quant_m > 0) || p.max_refits < 0 || p.max_refits > 6 ||
         !(p.min_inlier_frac >= 0) || p.max_batch < 1 || p.max_batch > kMaxBatch || p.lookahead < 0 ||
         p.lookahead > 32 || p.solver < 0 || p.solver > 1 || p.fit_schedule < 0 ||
-        p.fit_schedule > 3 || p.no_delta < 0 || p.no_delta > 1)
+        p.fit_schedule > 3 || p.no_delta < 0 || p.no_delta > 1 || p.raw_exact < 0 || p.raw_exact > 1)
         return LCC_ERR_INVALID_ARG;
     int dev = 0;
     cudaDeviceProp prop;
@@ -304,16 +305,17 @@ lcc_status lcc_create(lcc_ctx **out, const lcc_sensor *sensor, const lcc_params 
     g.solver = p.solver;
     g.schedule = p.fit_schedule;
     g.no_delta = p.no_delta;
+    g.raw_exact = p.raw_exact;
     g.first_rounds = std::min(p.fit_schedule == 3 ? 1 : p.fit_schedule, p.max_refits + 1);
     g.k_max = (int)floorf(p.fit_thr_m / p.quant_m + 0.5f) + 1;
     g.w_res = bits_for(2 * g.k_max);
     const int m_max = (int)floorf((float)s.max_range_m / p.quant_m + 0.5f) + 1;
-    g.w_raw = bits_for(m_max);
+    g.w_raw = p.raw_exact ? 32 : bits_for(m_max);   // lossless raw pixels: the range's fp32 bits
     g.elev_max_rad = (float)(s.elev_max_deg * (M_PI / 180.0));
     g.inv_d_el = (float)(s.rows / ((s.elev_max_deg - s.elev_min_deg) * (M_PI / 180.0)));
     g.inv_d_az = (float)(s.cols / (2.0 * M_PI));
     // the run walker keeps one tile row in shared memory
-    if (g.w_res > 16 || g.w_raw > 24 || merge_smem_bytes(g.TC) > 200 * 1024 || g.TC > 65535) {
+    if (g.w_res > 16 || (g.w_raw > 24 && !g.raw_exact) || merge_smem_bytes(g.TC) > 200 * 1024 || g.TC > 65535) {
         delete c;
         return LCC_ERR_UNSUPPORTED;
     }

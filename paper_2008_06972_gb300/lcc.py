@@ -35,7 +35,8 @@ class lcc_params(ctypes.Structure):
     _fields_ = [("tile_h", ctypes.c_int32), ("tile_w", ctypes.c_int32), ("fit_thr_m", ctypes.c_float),
                 ("quant_m", ctypes.c_float), ("max_refits", ctypes.c_int32), ("min_inlier_frac", ctypes.c_float),
                 ("merge_runs", ctypes.c_int32), ("max_batch", ctypes.c_int32), ("lookahead", ctypes.c_int32),
-                ("solver", ctypes.c_int32), ("fit_schedule", ctypes.c_int32), ("no_delta", ctypes.c_int32)]
+                ("solver", ctypes.c_int32), ("fit_schedule", ctypes.c_int32), ("no_delta", ctypes.c_int32),
+                ("raw_exact", ctypes.c_int32)]
 
 
 class lcc_stats(ctypes.Structure):

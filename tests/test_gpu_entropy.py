@@ -61,6 +61,8 @@ def oracle_streams(cfg2_seq):
         out.append(pb.tobytes())
     nd, _, _, _ = O.encode_keyframe(s, O.params(no_delta=1, fit_thr_m=0.02), seq.frames[seq.key_index])
     out.append(nd.tobytes())
+    re_, _, _, _ = O.encode_keyframe(s, O.params(raw_exact=1), seq.frames[seq.key_index])
+    out.append(re_.tobytes())   # 32-bit raw codes: a copied section
     return out
 
 

@@ -31,8 +31,8 @@ def _cuda():
     lcc.load()
 
 
-def _oparams(tile=(4, 4), thr=0.05, q=0.02, R=3, fmin=0.75, merge=1, no_delta=0):
-    return O.params(tile[0], tile[1], thr, q, R, fmin, merge, no_delta)
+def _oparams(tile=(4, 4), thr=0.05, q=0.02, R=3, fmin=0.75, merge=1, no_delta=0, raw_exact=0):
+    return O.params(tile[0], tile[1], thr, q, R, fmin, merge, no_delta, raw_exact)
 
 
 def _gparams(tile=(4, 4), thr=0.05, q=0.02, R=3, fmin=0.75, merge=1, solver=0, **kw):
@@ -601,3 +601,48 @@ def test_imu_poses_parity_and_decode():
         m = rng > 0
         assert ((drng > 0) == m).all()
         assert np.abs(drng[m] - rng[m]).max() <= 0.01 + 1e-5
+
+
+@pytest.mark.parametrize("tile", [(4, 4), (8, 8)])
+def test_raw_exact_keyframe_parity(cfg2_seq, tile):
+    """The lossless raw option: the GPU stream is the oracle's on the GPU's planes, both decoders
+    agree bit for bit, raw pixels decode to their range exactly and the raw section holds 32 bits
+    per raw pixel."""
+    seq = cfg2_seq
+    r = _keyframe_case(seq.sensor, seq.frames[seq.key_index], tile=tile, raw_exact=1)
+    h = streamfmt.header(r["bits"])
+    assert h["flags"] & 4 and h["w_raw"] == 32 and h["n_raw"] > 0
+    raw = streamfmt.raw_codes(r["bits"]).astype(np.uint32).view(np.float32)
+    s = O.sensor(seq.sensor)
+    rng, _, _ = O.range_image(s, seq.frames[seq.key_index])
+    assert np.isin(raw, rng[rng > 0]).all()
+
+
+def test_raw_exact_sequence_round_trip(cfg2_seq):
+    """A whole sequence with raw_exact: every frame decodes (GPU) within q/2 and at least the raw
+    pixels' count of pixels decode to their range bit for bit."""
+    from paper_2008_06972_gb300 import lcc
+    seq = cfg2_seq
+    n = len(seq.frames)
+    c = H.ctx(seq.sensor, max_batch=16, raw_exact=1)
+    ds = [H.to_dev(p) for p in seq.frames]
+    outs = [H.out_buf(c) for _ in range(n)]
+    nb = torch.zeros(n, dtype=torch.int64, device="cuda")
+    kf = lcc.Keyframe(c)
+    c.lcc_encode_sequence(seq.key_index, seq.poses, ds, [len(p) for p in seq.frames], outs,
+                          [o.numel() for o in outs], nb, kf)
+    assert c.lcc_sync() == 0
+    sizes = [int(x) for x in nb.cpu().numpy()]
+    s = O.sensor(seq.sensor)
+    kfd = lcc.Keyframe(c)
+    c.lcc_keyframe_from_stream(outs[seq.key_index], sizes[seq.key_index], kfd)
+    for f in (seq.key_index, 0, n - 1):
+        isk = f == seq.key_index
+        bits = outs[f][:sizes[f]].cpu().numpy()
+        rng, _, _ = O.range_image(s, seq.frames[f])
+        st, drng, _, _ = H.decode(c, bits, None if isk else kfd, None if isk else seq.poses[f])
+        assert st == 0
+        m = rng > 0
+        assert np.abs(drng[m] - rng[m]).max() <= 0.01 + 1e-5
+        exact = (drng.view(np.uint32) == rng.view(np.uint32)) & m
+        assert exact.sum() >= streamfmt.header(bits)["n_raw"]

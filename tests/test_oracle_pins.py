@@ -570,3 +570,50 @@ def test_no_delta_decode_lies_on_the_plane_within_the_threshold(cfg1):
     assert np.count_nonzero(diff) <= np.count_nonzero(k)
     u = O.beams(s)
     assert np.abs(xn[..., :3] - dn[..., None] * u).max() == 0
+
+
+@pytest.mark.parametrize("tile", [(4, 4), (8, 8)])
+def test_raw_exact_keeps_raw_points_losslessly(cfg1, tile):
+    """The lossless raw option: header flags bit 2 and 32-bit raw codes holding each raw pixel's
+    fp32 range; every other section equals the quantised mode's, the raw codes quantise to the
+    quantised mode's raw codes in the same order, and raw pixels decode to their range exactly."""
+    sensor, pts = cfg1
+    s = O.sensor(sensor)
+    pq, pe = O.params(*tile), O.params(*tile, raw_exact=1)
+    bq, _, _, _ = O.encode_keyframe(s, pq, pts)
+    be, _, _, _ = O.encode_keyframe(s, pe, pts)
+    hq, he = streamfmt.header(bq), streamfmt.header(be)
+    assert he["flags"] & 4 and not hq["flags"] & 4 and he["w_raw"] == 32 and hq["w_raw"] < 32
+    assert he["n_raw"] == hq["n_raw"] > 0
+    sq, se = streamfmt.sections(bq), streamfmt.sections(be)
+    for k in ("bitmap", "tiles", "runs", "temporal", "fitted", "res"):
+        assert np.array_equal(sq[k], se[k]), k
+    assert len(se["raw"]) == he["n_raw"]
+    raw_e = streamfmt.raw_codes(be).astype(np.uint32).view(np.float32)
+    q = np.float32(pq.quant_m)
+    assert np.array_equal(np.floor(raw_e / q + np.float32(0.5)).astype(np.int64), streamfmt.raw_codes(bq))
+    rng, _, _ = O.range_image(s, pts)
+    drng, dxyz, _ = O.decode(s, be)
+    m = rng > 0
+    exact = m & (drng.view(np.uint32) == rng.view(np.uint32))
+    assert exact.sum() >= he["n_raw"]
+    assert np.isin(raw_e, rng[m]).all()
+    assert np.abs(drng[m] - rng[m]).max() <= q / 2 + 1e-5
+    # the raw pixels of the quantised mode are the exact ones here
+    dq, _, _ = O.decode(s, bq)
+    raw_px = m & (np.abs(dq - rng) > 0) & ~np.isclose(dq, drng, rtol=0, atol=0)
+    assert (drng[raw_px] == rng[raw_px]).all()
+
+
+def test_raw_exact_flag_needs_32_bit_raw_codes(cfg1):
+    sensor, pts = cfg1
+    s = O.sensor(sensor)
+    b, _, _, _ = O.encode_keyframe(s, O.params(raw_exact=1), pts)
+    bad = b.copy()
+    bad[15] = 12   # w_raw
+    with pytest.raises(ValueError):
+        O.decode(s, bad)
+    bad = b.copy()
+    bad[7] |= 8    # an unknown flag
+    with pytest.raises(ValueError):
+        O.decode(s, bad)
