@@ -140,6 +140,37 @@ __device__ __forceinline__ uint32_t get_sym(const uint32_t *sec, uint32_t w, uin
     return v & ((1u << w) - 1u);
 }
 
+// The symbols of chunk c of a section of width w, in order: the chunk starts on a word (1024
+// symbols of w bits fill whole words), words are read one ahead of their use.
+struct SymReader {
+    const uint32_t *in;
+    uint32_t words, ip, nxt, w, m;
+    unsigned long long buf;
+    int nb;
+    __device__ SymReader(const uint32_t *sec, uint32_t w_, uint32_t c, uint32_t m_) {
+        w = w_;
+        m = m_;
+        in = sec + (size_t)c * kChunk * w / 32;
+        words = (uint32_t)(((unsigned long long)m * w + 31) / 32);
+        ip = 0;
+        nxt = words ? in[0] : 0u;
+        buf = 0;
+        nb = 0;
+    }
+    __device__ __forceinline__ uint32_t next() {
+        if (nb < (int)w) {
+            buf |= (unsigned long long)nxt << nb;
+            nb += 32;
+            ip++;
+            nxt = ip < words ? in[ip] : 0u;
+        }
+        const uint32_t v = (uint32_t)buf & ((1u << w) - 1u);
+        buf >>= w;
+        nb -= (int)w;
+        return v;
+    }
+};
+
 __device__ uint32_t block_sum(uint32_t v, uint32_t *red) {
     for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xFFFFFFFFu, v, o);
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -325,7 +356,9 @@ __global__ void __launch_bounds__(kBuildThreads) k_ent_build(EntBatch b, Scratch
                 // two queues: leaves in (count, symbol) order, internal nodes in order of creation;
                 // each queue's front weight is kept in a register (~0u: empty), a leaf goes first
                 // on equal weights
-                uint32_t li = 0, ni = 0, wl = S.lw[0], wn = ~0u;
+                // (wl, wl2: the first two leaves left; wn, wn2: the first two nodes made and not
+                // yet joined; the second of each is loaded one join ahead)
+                uint32_t li = 0, ni = 0, wl = S.lw[0], wl2 = n > 1 ? S.lw[1] : ~0u, wn = ~0u, wn2 = ~0u;
                 for (uint32_t k = 0; k + 1 < n; k++) {
                     uint32_t wsum = 0;
 #pragma unroll
@@ -333,15 +366,18 @@ __global__ void __launch_bounds__(kBuildThreads) k_ent_build(EntBatch b, Scratch
                         if (wl <= wn) {
                             wsum += wl;
                             S.leaf_parent[li++] = (uint16_t)k;
-                            wl = li < n ? S.lw[li] : ~0u;
+                            wl = wl2;
+                            wl2 = li + 1 < n ? S.lw[li + 1] : ~0u;
                         } else {
                             wsum += wn;
                             S.node_parent[ni++] = (uint16_t)k;
-                            wn = ni < k ? S.hist[ni] : ~0u;
+                            wn = wn2;
+                            wn2 = ni + 1 < k ? S.hist[ni + 1] : ~0u;
                         }
                     }
                     S.hist[k] = wsum;
                     if (ni == k) wn = wsum;
+                    else if (ni + 1 == k) wn2 = wsum;
                 }
             }
             __syncthreads();
@@ -404,9 +440,9 @@ __global__ void __launch_bounds__(kBuildThreads) k_ent_build(EntBatch b, Scratch
     uint32_t *cw = sc.chunk + ((size_t)f * kSecs + s) * sc.max_chunks;
     uint32_t mine = 0;
     for (uint32_t c = tid; c < nch; c += blockDim.x) {
-        const uint32_t e = min(cnt, (c + 1) * kChunk);
+        SymReader rd(sec, w, c, min(cnt - c * kChunk, (uint32_t)kChunk));
         uint32_t bits = 0;
-        for (uint32_t i = c * kChunk; i < e; i++) bits += S.len[get_sym(sec, w, i)];
+        for (uint32_t i = 0; i < rd.m; i++) bits += S.len[rd.next()];
         cw[c] = (bits + 31) / 32;
         mine += (bits + 31) / 32;
     }
@@ -523,9 +559,9 @@ __global__ void __launch_bounds__(kWriteThreads) k_ent_write(EntBatch b, Scratch
         uint32_t *o = pay + coff[c];
         unsigned long long acc = 0;
         uint32_t nb = 0;
-        const uint32_t e = min(cnt, (c + 1) * kChunk);
-        for (uint32_t i = c * kChunk; i < e; i++) {
-            const uint32_t cl = s_code[get_sym(sec, w, i)];
+        SymReader rd(sec, w, c, min(cnt - c * kChunk, (uint32_t)kChunk));
+        for (uint32_t i = 0; i < rd.m; i++) {
+            const uint32_t cl = s_code[rd.next()];
             acc |= (unsigned long long)(cl & 0xFFFFu) << nb;
             nb += cl >> 16;
             if (nb >= 32) {
@@ -711,6 +747,7 @@ __global__ void __launch_bounds__(kWriteThreads) k_ent_dec(EntBatch b, Scratch s
     for (uint32_t c = blockIdx.x * blockDim.x + threadIdx.x; c < nch; c += gridDim.x * blockDim.x) {
         const uint32_t beg = co[c], end = c + 1 < nch ? co[c + 1] : pay_words;   // validated by the prep
         uint32_t wp = beg;
+        uint32_t nxt = wp < end ? pay[wp] : 0u;   // the next payload word, loaded one refill ahead
         unsigned long long buf = 0;   // stream bits, the next one in bit 0
         int nb = 0;
         uint32_t *o = dst + (size_t)c * kChunk * w / 32;   // 1024 symbols of w bits fill whole words
@@ -720,8 +757,10 @@ __global__ void __launch_bounds__(kWriteThreads) k_ent_dec(EntBatch b, Scratch s
         bool bad = false;
         for (uint32_t i = 0; i < m; i++) {
             if (nb < 32 && wp < end) {
-                buf |= (unsigned long long)pay[wp++] << nb;
+                buf |= (unsigned long long)nxt << nb;
                 nb += 32;
+                wp++;
+                nxt = wp < end ? pay[wp] : 0u;
             }
             // the next 15 stream bits, first bit most significant
             const uint32_t v = __brev((uint32_t)buf & 0x7FFFu) >> (32 - kMaxLen);
