@@ -325,7 +325,13 @@ __global__ void __launch_bounds__(kBuildThreads) k_ent_build(EntBatch b, Scratch
         S.len[i] = 0;
     }
     __syncthreads();
-    for (uint32_t i = tid; i < cnt; i += blockDim.x) atomicAdd(&S.hist[get_sym(sec, w, i)], 1u);
+    // lanes holding the same symbol add once (small alphabets would serialise on a few counters)
+    for (uint32_t base = 0; base < cnt; base += blockDim.x) {
+        const uint32_t i = base + tid;
+        const uint32_t v = i < cnt ? get_sym(sec, w, i) : 0xFFFFFFFFu;
+        const unsigned same = __match_any_sync(0xFFFFFFFFu, v);
+        if (i < cnt && (tid & 31) == __ffs(same) - 1) atomicAdd(&S.hist[v], (uint32_t)__popc(same));
+    }
     __syncthreads();
     uint32_t top = 0;
     for (uint32_t v = tid; v < (1u << w); v += blockDim.x)
