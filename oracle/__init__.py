@@ -35,7 +35,8 @@ class Params(ctypes.Structure):
     _fields_ = [("tile_h", ctypes.c_int32), ("tile_w", ctypes.c_int32),
                 ("fit_thr_m", ctypes.c_float), ("quant_m", ctypes.c_float),
                 ("max_refits", ctypes.c_int32), ("min_inlier_frac", ctypes.c_float),
-                ("merge_runs", ctypes.c_int32), ("no_delta", ctypes.c_int32), ("raw_exact", ctypes.c_int32)]
+                ("merge_runs", ctypes.c_int32), ("no_delta", ctypes.c_int32), ("raw_exact", ctypes.c_int32),
+                ("temporal_candidates", ctypes.c_int32)]
 
 
 class TileFit(ctypes.Structure):
@@ -113,8 +114,9 @@ def sensor(s) -> Sensor:
 
 
 def params(tile_h=4, tile_w=4, fit_thr_m=0.05, quant_m=0.02, max_refits=3, min_inlier_frac=0.75,
-           merge_runs=1, no_delta=0, raw_exact=0) -> Params:
-    return Params(tile_h, tile_w, fit_thr_m, quant_m, max_refits, min_inlier_frac, merge_runs, no_delta, raw_exact)
+           merge_runs=1, no_delta=0, raw_exact=0, temporal_candidates=1) -> Params:
+    return Params(tile_h, tile_w, fit_thr_m, quant_m, max_refits, min_inlier_frac, merge_runs, no_delta, raw_exact,
+                  temporal_candidates)
 
 
 def n_tiles(s: Sensor, p: Params) -> int:

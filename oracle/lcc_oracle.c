@@ -452,7 +452,8 @@ static void fit_one_seeded(const orc_params *prm, const tile_px_t *tp, const flo
 static int params_ok(const orc_sensor *s, const orc_params *p) {
     return sensor_ok(s) && p && p->tile_h >= 1 && p->tile_w >= 1 &&
            p->tile_h * p->tile_w <= MAX_TILE_PX && p->tile_h <= 255 && p->tile_w <= 255 &&
-           p->fit_thr_m >= 0 && p->quant_m > 0 && p->max_refits >= 0 && p->min_inlier_frac >= 0;
+           p->fit_thr_m >= 0 && p->quant_m > 0 && p->max_refits >= 0 && p->min_inlier_frac >= 0 &&
+           p->temporal_candidates >= 0 && p->temporal_candidates <= 4;
 }
 
 int orc_fit_tiles(const orc_sensor *s, const orc_params *prm, const float *range, orc_tile_fit *out) {
@@ -519,7 +520,11 @@ static void transform_point(const double M[16], const float p[3], float out[3]) 
  * The K tile is the one the tile's anchor (first valid pixel in raster order)
  * falls in after Eq. 6 and Eq. 1-2.  The normal n' is held fixed and only the
  * offset c' is refit as the mean of n'.p over the current set, with the same
- * drop-and-refit rounds and acceptance rule as the spatial fit.
+ * drop-and-refit rounds and acceptance rule as the spatial fit.  With several
+ * candidates the test runs against the distinct K tiles the tile's valid
+ * pixels fall in, in raster order from the anchor's (K tiles without a plane
+ * are skipped), until one passes; the record holds the passing test, or the
+ * last one run, with the borderline flag of all of them.
  */
 int orc_temporal_tiles(const orc_sensor *s, const orc_params *prm, const float *range,
                        const float *kf_table, const double pose[16], orc_tile_temporal *out) {
@@ -539,39 +544,64 @@ int orc_temporal_tiles(const orc_sensor *s, const orc_params *prm, const float *
         if (tp->n_valid == 0) continue;
         int a = 0;
         while (!tp->valid[a]) a++;
-        float aK[3];
-        transform_point(pose, tp->p[a], aK);
-        float rK;
-        int pixK;
-        if (bin_point(s, &T, aK[0], aK[1], aK[2], &rK, &pixK) != 0) continue;
-        int kt = (pixK / s->cols / prm->tile_h) * TW + (pixK % s->cols) / prm->tile_w;
-        const float *kp = &kf_table[4 * kt];
-        if (kp[0] == 0.0f && kp[1] == 0.0f && kp[2] == 0.0f) continue;
-        o->kref = kt;
-        o->status = 1;
-        rotate_normal(pose, kp, o->plane);
-        for (int k = 0; k < tp->n; k++) S[k] = tp->valid[k];
-        int nS = tp->n_valid, nI = 0;
-        for (;;) {
-            double sum = 0.0;
-            for (int k = 0; k < tp->n; k++) {
-                if (!S[k]) continue;
-                double dp = (double)o->plane[0] * (double)tp->p[k][0];
-                dp = fma((double)o->plane[1], (double)tp->p[k][1], dp);
-                dp = fma((double)o->plane[2], (double)tp->p[k][2], dp);
-                sum += dp;
+        /* candidate K tiles: those of the valid pixels (Eq. 6, then Eq. 1-2), distinct, in raster
+         * order from the anchor's; none if the anchor falls outside the key frame's image */
+        const int ncand_max = prm->temporal_candidates > 1 ? prm->temporal_candidates : 1;
+        int cand[4], ncand = 0, tested = 0, border = 0;
+        for (int k = a; k < tp->n && ncand < ncand_max; k++) {
+            if (!tp->valid[k]) continue;
+            float aK[3];
+            transform_point(pose, tp->p[k], aK);
+            float rK;
+            int pixK;
+            if (bin_point(s, &T, aK[0], aK[1], aK[2], &rK, &pixK) != 0) {
+                if (k == a) break;
+                continue;
             }
-            o->plane[3] = (float)(sum / nS);
-            o->rounds++;
-            nI = inliers(tp, o->plane, prm->fit_thr_m, I, &o->borderline);
-            int same = (nI == nS);
-            for (int k = 0; k < tp->n && same; k++) same = (I[k] == S[k]);
-            if (same || o->rounds == prm->max_refits + 1 || nI < 3) break;
-            memcpy(S, I, sizeof(int) * tp->n);
-            nS = nI;
+            const int kt = (pixK / s->cols / prm->tile_h) * TW + (pixK % s->cols) / prm->tile_w;
+            int seen = 0;
+            for (int q = 0; q < ncand; q++) seen |= cand[q] == kt;
+            if (seen) continue;
+            cand[ncand++] = kt;
+            const float *kp = &kf_table[4 * kt];
+            if (kp[0] == 0.0f && kp[1] == 0.0f && kp[2] == 0.0f) continue;
+            /* the relaxed-plane test against this K tile; the record keeps the last one tested,
+             * or the first that passes */
+            tested = 1;
+            o->kref = kt;
+            o->status = 1;
+            o->rounds = 0;
+            o->borderline = 0;
+            rotate_normal(pose, kp, o->plane);
+            for (int q = 0; q < tp->n; q++) S[q] = tp->valid[q];
+            int nS = tp->n_valid, nI = 0;
+            for (;;) {
+                double sum = 0.0;
+                for (int q = 0; q < tp->n; q++) {
+                    if (!S[q]) continue;
+                    double dp = (double)o->plane[0] * (double)tp->p[q][0];
+                    dp = fma((double)o->plane[1], (double)tp->p[q][1], dp);
+                    dp = fma((double)o->plane[2], (double)tp->p[q][2], dp);
+                    sum += dp;
+                }
+                o->plane[3] = (float)(sum / nS);
+                o->rounds++;
+                nI = inliers(tp, o->plane, prm->fit_thr_m, I, &o->borderline);
+                int same = (nI == nS);
+                for (int q = 0; q < tp->n && same; q++) same = (I[q] == S[q]);
+                if (same || o->rounds == prm->max_refits + 1 || nI < 3) break;
+                memcpy(S, I, sizeof(int) * tp->n);
+                nS = nI;
+            }
+            border |= o->borderline;
+            o->n_inlier = nI;
+            if (tp->n_valid >= 3 && nI >= need_inliers(prm, tp->n_valid)) {
+                o->status = 2;
+                break;
+            }
         }
-        o->n_inlier = nI;
-        if (tp->n_valid >= 3 && nI >= need_inliers(prm, tp->n_valid)) o->status = 2;
+        (void)tested;
+        o->borderline = border;
     }
     free(tp);
     tables_free(&T);

@@ -44,6 +44,9 @@ typedef struct {
                                     the deltas are dropped, decode error <= threshold) */
     int32_t raw_exact;           /* 1: raw pixels carry their fp32 range bits, so unfit points
                                     are kept losslessly (header flags bit 2, 32-bit raw codes) */
+    int32_t temporal_candidates; /* K tiles a P tile's relaxed-plane test may try (1..4): the
+                                    distinct K tiles its valid pixels fall in, raster order from
+                                    the anchor's; 1 (or 0) = the anchor's K tile only */
 } orc_params;
 
 /* tile codes of the bitstream */

@@ -617,3 +617,40 @@ def test_raw_exact_flag_needs_32_bit_raw_codes(cfg1):
     bad[7] |= 8    # an unknown flag
     with pytest.raises(ValueError):
         O.decode(s, bad)
+
+
+def test_temporal_candidates_extend_the_anchor_test():
+    """Several candidate K tiles: every tile that passes against its anchor's K tile keeps the
+    same record; the other passes name a K tile that one of the tile's own valid pixels falls in
+    after Eq. 6 (binned here through the range-image conversion of the moved points)."""
+    seq = synth.sequence_cfg2(0, 10)
+    s = O.sensor(seq.sensor)
+    k, f = seq.key_index, 0
+    p1, p4 = O.params(), O.params(temporal_candidates=4)
+    _, kft, _, _ = O.encode_keyframe(s, p1, seq.frames[k])
+    rng, _, _ = O.range_image(s, seq.frames[f])
+    t1 = O.temporal_tiles(s, p1, rng, kft, seq.poses[f])
+    t4 = O.temporal_tiles(s, p4, rng, kft, seq.poses[f])
+    pass1, pass4 = t1["status"] == 2, t4["status"] == 2
+    assert (pass4 >= pass1).all() and pass4.sum() > pass1.sum()
+    for name in ("kref", "plane", "n_inlier", "rounds"):
+        assert np.array_equal(t1[name][pass1], t4[name][pass1]), name
+    # tiles untouched by the extra candidates: no anchor bin, or the anchor's K tile only
+    H, W, th, tw = seq.sensor.rows, seq.sensor.cols, p1.tile_h, p1.tile_w
+    TC = (W + tw - 1) // tw
+    beams = O.beams(s).reshape(H, W, 3)
+    M = seq.poses[f]
+    new = np.nonzero(pass4 & ~pass1)[0]
+    assert len(new) > 0
+    for t in new[:200]:
+        i0, j0 = (t // TC) * th, (t % TC) * tw
+        r = rng[i0:i0 + th, j0:j0 + tw]
+        u = beams[i0:i0 + th, j0:j0 + tw]
+        m = r > 0
+        pts = (r[m][:, None] * u[m]).astype(np.float32)
+        moved = (pts.astype(np.float64) @ M[:3, :3].T + M[:3, 3]).astype(np.float32)
+        img, _, _ = O.range_image(s, np.concatenate([moved, np.zeros((len(moved), 1), np.float32)], 1))
+        hit = np.argwhere(img > 0)
+        ktiles = {(a // th) * TC + b // tw for a, b in hit}
+        assert int(t4["kref"][t]) in ktiles
+        assert int(t4["kref"][t]) != int(t1["kref"][t])
