@@ -71,6 +71,10 @@ typedef struct {
     int32_t raw_exact;        /* 1: raw (unfit) pixels carry their fp32 range bits instead of a
                                  q-quantised code, so they decode exactly (header flags bit 2, 32-bit
                                  raw codes); 0 (default): raw codes m = round(r / q) */
+    int32_t temporal_candidates; /* K tiles a P tile's relaxed-plane test (Sec. III-D) may try, 1..4:
+                                 the distinct K tiles its valid pixels fall in after Eq. 6, in raster
+                                 order from the anchor's, the first that passes kept; 1 (default):
+                                 the anchor's K tile only */
 } lcc_params;
 
 /* Per-frame statistics of the last encode (Fig. 11's categories and more). */

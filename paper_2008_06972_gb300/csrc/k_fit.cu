@@ -692,39 +692,69 @@ template <int TH_, int TW_>
 __device__ __forceinline__ void temporal_test(const TileView<TH_, TW_> &tv, const double *M, const float4 *kf,
                                               RecOut &o) {
     const Geometry &g = tv.g;
-    float aK[3];
-    transform_point(M, tv.ax, tv.ay, tv.az, aK);
-    float rK;
-    int pixK;
-    if (bin_point(g, aK[0], aK[1], aK[2], rK, pixK) != 0) return;
-    const int kti = (pixK / g.W / g.th) * g.TC + (pixK % g.W) / g.tw;
-    const float4 kp = __ldg(kf + kti);
-    if (kp.x == 0.f && kp.y == 0.f && kp.z == 0.f) return;
-    float n[3];
-    rotate_normal(M, kp.x, kp.y, kp.z, n);
-    o.kref = (uint32_t)kti;
-    Mask S = tv.V, I;
-    int nS = tv.nv, nI = 0;
-    float c = 0.f;
-    bool border = false;
-    for (;;) {
-        const ff acc = class_tree_sum<TH_, TW_>(tv, S, n);
-        c = ffm::mul({acc.hi, acc.lo}, ffm::rcp(ffm::mk((float)nS))).hi;   // mean of n'.p
-        o.t_rounds++;
-        nI = tv.inliers(make_float4(n[0], n[1], n[2], c), I, border);
-        if ((nI == nS && I == S) || o.t_rounds == g.R + 1 || nI < 3) break;
-        S = I;
-        nS = nI;
+    // candidate K tiles: those the valid pixels fall in, distinct, raster order from the
+    // anchor's (one candidate: the anchor's K tile only); the first that passes is kept
+    const int ncand_max = g.tcand > 1 ? g.tcand : 1;
+    int cand[4];
+    int ncand = 0;
+    bool tested = false, border_all = false;
+    for (int k = tv.first; k < TileView<TH_, TW_>::PX && ncand < ncand_max; k++) {
+        if (!tv.V.get(k)) continue;
+        float px = tv.ax, py = tv.ay, pz = tv.az;
+        if (k != tv.first) {
+            float ux, uy, uz;
+            tv.u(k, ux, uy, uz);
+            const float rr = tv.r(k);
+            px = __fmul_rn(rr, ux);
+            py = __fmul_rn(rr, uy);
+            pz = __fmul_rn(rr, uz);
+        }
+        float aK[3];
+        transform_point(M, px, py, pz, aK);
+        float rK;
+        int pixK;
+        if (bin_point(g, aK[0], aK[1], aK[2], rK, pixK) != 0) {
+            if (k == tv.first) break;
+            continue;
+        }
+        const int kti = (pixK / g.W / g.th) * g.TC + (pixK % g.W) / g.tw;
+        bool seen = false;
+        for (int q = 0; q < ncand; q++) seen |= cand[q] == kti;
+        if (seen) continue;
+        cand[ncand++] = kti;
+        const float4 kp = __ldg(kf + kti);
+        if (kp.x == 0.f && kp.y == 0.f && kp.z == 0.f) continue;
+        float n[3];
+        rotate_normal(M, kp.x, kp.y, kp.z, n);
+        o.kref = (uint32_t)kti;
+        o.t_rounds = 0;
+        Mask S = tv.V, I;
+        int nS = tv.nv, nI = 0;
+        float c = 0.f;
+        bool border = false;
+        for (;;) {
+            const ff acc = class_tree_sum<TH_, TW_>(tv, S, n);
+            c = ffm::mul({acc.hi, acc.lo}, ffm::rcp(ffm::mk((float)nS))).hi;   // mean of n'.p
+            o.t_rounds++;
+            nI = tv.inliers(make_float4(n[0], n[1], n[2], c), I, border);
+            if ((nI == nS && I == S) || o.t_rounds == g.R + 1 || nI < 3) break;
+            S = I;
+            nS = nI;
+        }
+        tested = true;
+        border_all |= border;
+        o.tplane = make_float4(n[0], n[1], n[2], c);
+        o.t_inl = (uint8_t)nI;
+        o.t_status = (tv.nv >= 3 && nI >= need_inliers(g.fmin, tv.nv)) ? 2 : 1;
+        if (o.t_status == 2) break;
     }
-    if (border) o.flags |= 1;
+    if (!tested) return;
+    if (border_all) o.flags |= 1;
     o.flags |= 4;
-    o.tplane = make_float4(n[0], n[1], n[2], c);
-    o.t_inl = (uint8_t)nI;
-    o.t_status = (tv.nv >= 3 && nI >= need_inliers(g.fmin, tv.nv)) ? 2 : 1;
     if (o.t_status == 2) {
         o.status = S_TEMPORAL;
         o.plane = o.tplane;
-        o.n_inl = (uint8_t)nI;
+        o.n_inl = o.t_inl;
     }
 }
 
@@ -807,7 +837,8 @@ __global__ void __launch_bounds__(kFitThreads) k_fit_round(Geometry g, Scratch s
 // registers; sums and inlier sets are combined by xor-butterflies inside the
 // group.  A tile that passes becomes temporal; otherwise only the temporal
 // fields and flags of its record change (its spatial fit and run pre-test stay).
-template <int TH_, int TW_>
+// kCand bounds the candidate K tiles (1: the anchor's only, the default path's registers).
+template <int TH_, int TW_, int kCand>
 __global__ void __launch_bounds__(kFitThreads) k_temporal(Geometry g, Scratch s, Batch b, Poses ps) {
     constexpr int PX = TH_ * TW_, L = TLanes<TH_, TW_>::L, PPL = TLanes<TH_, TW_>::PPL;
     static_assert(PX % L == 0 && kFitThreads % L == 0 && 32 % L == 0, "lane groups");
@@ -860,72 +891,128 @@ __global__ void __launch_bounds__(kFitThreads) k_temporal(Geometry g, Scratch s,
         o.amask = src[2].y;
         o.acnt[0] = q3.x; o.acnt[1] = q3.y; o.acnt[2] = q3.z; o.acnt[3] = q3.w;
     }
-    // anchor in key-frame coordinates, key tile, rotated normal: the FP64 products of
-    // transform_point and rotate_normal (same operations, same order), one output coordinate
-    // per lane (GB300's FP64 rate is low), gathered by shuffles
+    // candidate K tiles (the distinct K tiles the valid pixels fall in, raster order from the
+    // anchor's; the first that passes is kept).  Per candidate pixel: its point in key-frame
+    // coordinates, K tile and rotated normal, the FP64 products of transform_point and
+    // rotate_normal (same operations, same order) one output coordinate per lane (GB300's FP64
+    // rate is low), gathered by shuffles
     const double *M = ps.m[f];
     const int cl = l < 3 ? l : 2, g0 = lane - l;
-    float aK[3];
-    {
-        double tt = __dmul_rn(M[cl * 4 + 0], (double)ax);
-        tt = fma(M[cl * 4 + 1], (double)ay, tt);
-        tt = fma(M[cl * 4 + 2], (double)az, tt);
+    int kti = 0, nI = 0;
+    bool tested = false, border = false, pass = false;
+    float n[3] = {0.f, 0.f, 0.f}, c = 0.f;
+    uint8_t t_rounds = 0;
+    // the K tile a point falls in after Eq. 6 (-1 outside the key frame's image)
+    auto key_tile = [&](float px, float py, float pz) -> int {
+        float aK[3];
+        double tt = __dmul_rn(M[cl * 4 + 0], (double)px);
+        tt = fma(M[cl * 4 + 1], (double)py, tt);
+        tt = fma(M[cl * 4 + 2], (double)pz, tt);
         const float v = (float)__dadd_rn(tt, M[cl * 4 + 3]);
 #pragma unroll
         for (int q = 0; q < 3; q++) aK[q] = __shfl_sync(gmask, v, g0 + q);
-    }
-    float rK;
-    int pixK;
-    if (bin_point(g, aK[0], aK[1], aK[2], rK, pixK) != 0) return;
-    const int kti = (pixK / g.W / g.th) * g.TC + (pixK % g.W) / g.tw;
-    const float4 kp = __ldg(b.kf[f] + kti);
-    if (kp.x == 0.f && kp.y == 0.f && kp.z == 0.f) return;
-    float n[3];
-    {
+        float rK;
+        int pixK;
+        if (bin_point(g, aK[0], aK[1], aK[2], rK, pixK) != 0) return -1;
+        return (pixK / g.W / g.th) * g.TC + (pixK % g.W) / g.tw;
+    };
+    // the relaxed-plane test against K plane kp (rotated normal, offset refit rounds)
+    auto relaxed = [&](const float4 kp) {
         double tt = __dmul_rn(M[0 * 4 + cl], (double)kp.x);
         tt = fma(M[1 * 4 + cl], (double)kp.y, tt);
         tt = fma(M[2 * 4 + cl], (double)kp.z, tt);
         const float v = (float)tt;
 #pragma unroll
         for (int q = 0; q < 3; q++) n[q] = __shfl_sync(gmask, v, g0 + q);
-    }
-    Mask S = V, I;
-    int nS = nv, nI = 0;
-    float c = 0.f;
-    bool border = false;
-    uint8_t t_rounds = 0;
-    for (;;) {
-        ff acc = {0.f, 0.f};
+        Mask S = V, I;
+        int nS = nv;
+        t_rounds = 0;
+        for (;;) {
+            ff acc = {0.f, 0.f};
 #pragma unroll
-        for (int m = 0; m < PPL; m++)
-            if (S.get(l + L * m)) acc = ff_add(acc, dot_term(n, pr[m], pux[m], puy[m], puz[m]));
+            for (int m = 0; m < PPL; m++)
+                if (S.get(l + L * m)) acc = ff_add(acc, dot_term(n, pr[m], pux[m], puy[m], puz[m]));
 #pragma unroll
-        for (int off = 1; off < L; off <<= 1) acc = ff_add(acc, shfl_xor_ff_m(gmask, acc, off));
-        c = ffm::mul({acc.hi, acc.lo}, ffm::rcp(ffm::mk((float)nS))).hi;   // mean of n'.p
-        t_rounds++;
-        const float4 pl = make_float4(n[0], n[1], n[2], c);
-        I.w0 = I.w1 = 0ull;
+            for (int off = 1; off < L; off <<= 1) acc = ff_add(acc, shfl_xor_ff_m(gmask, acc, off));
+            c = ffm::mul({acc.hi, acc.lo}, ffm::rcp(ffm::mk((float)nS))).hi;   // mean of n'.p
+            t_rounds++;
+            const float4 pl = make_float4(n[0], n[1], n[2], c);
+            I.w0 = I.w1 = 0ull;
 #pragma unroll
-        for (int m = 0; m < PPL; m++)
-            if (pr[m] > 0.0f && inlier_screened(pl, pux[m], puy[m], puz[m], pr[m], g.thr, border)) I.set(l + L * m);
+            for (int m = 0; m < PPL; m++)
+                if (pr[m] > 0.0f && inlier_screened(pl, pux[m], puy[m], puz[m], pr[m], g.thr, border))
+                    I.set(l + L * m);
 #pragma unroll
-        for (int off = 1; off < L; off <<= 1) {
-            I.w0 |= __shfl_xor_sync(gmask, I.w0, off);
-            I.w1 |= __shfl_xor_sync(gmask, I.w1, off);
+            for (int off = 1; off < L; off <<= 1) {
+                I.w0 |= __shfl_xor_sync(gmask, I.w0, off);
+                I.w1 |= __shfl_xor_sync(gmask, I.w1, off);
+            }
+            nI = __popcll(I.w0) + __popcll(I.w1);
+            if ((nI == nS && I == S) || t_rounds == g.R + 1 || nI < 3) break;
+            S = I;
+            nS = nI;
         }
-        nI = __popcll(I.w0) + __popcll(I.w1);
-        if ((nI == nS && I == S) || t_rounds == g.R + 1 || nI < 3) break;
-        S = I;
-        nS = nI;
+        tested = true;
+        pass = nv >= 3 && nI >= need_inliers(g.fmin, nv);
+    };
+    if constexpr (kCand == 1) {
+        kti = key_tile(ax, ay, az);
+        if (kti < 0) return;
+        const float4 kp = __ldg(b.kf[f] + kti);
+        if (kp.x == 0.f && kp.y == 0.f && kp.z == 0.f) return;
+        relaxed(kp);
+    } else {
+        const int ncand_max = min(kCand, g.tcand > 1 ? g.tcand : 1);
+        int cand[kCand];
+        int ncand = 0;
+        for (int k = first; k < PX && ncand < ncand_max; k++) {   // group-uniform
+            if (!V.get(k)) continue;
+            float px = ax, py = ay, pz = az;
+            if (k != first) {   // pixel k's point, from the lane that holds it
+                const int mk = k / L;
+                float rr = 0.f, ux = 0.f, uy = 0.f, uz = 0.f;
+#pragma unroll
+                for (int m = 0; m < PPL; m++)
+                    if (m == mk) {
+                        rr = pr[m];
+                        ux = pux[m];
+                        uy = puy[m];
+                        uz = puz[m];
+                    }
+                const int src = g0 + k % L;
+                rr = __shfl_sync(gmask, rr, src);
+                ux = __shfl_sync(gmask, ux, src);
+                uy = __shfl_sync(gmask, uy, src);
+                uz = __shfl_sync(gmask, uz, src);
+                px = __fmul_rn(rr, ux);
+                py = __fmul_rn(rr, uy);
+                pz = __fmul_rn(rr, uz);
+            }
+            const int kt = key_tile(px, py, pz);
+            if (kt < 0) {
+                if (k == first) break;
+                continue;
+            }
+            bool seen = false;
+            for (int q = 0; q < ncand; q++) seen |= cand[q] == kt;
+            if (seen) continue;
+            cand[ncand++] = kt;
+            const float4 kp = __ldg(b.kf[f] + kt);
+            if (kp.x == 0.f && kp.y == 0.f && kp.z == 0.f) continue;
+            kti = kt;
+            relaxed(kp);
+            if (pass) break;
+        }
     }
-    border = __any_sync(gmask, border);
+    if (!tested) return;
+    border = __any_sync(gmask, border);   // any lane, any candidate tested
     if (l != 0) return;
     o.kref = (uint32_t)kti;
     const uint8_t tflags = (uint8_t)((border ? 1 : 0) | 4);
     o.tplane = make_float4(n[0], n[1], n[2], c);
     o.t_rounds = t_rounds;
     o.t_inl = (uint8_t)nI;
-    o.t_status = (nv >= 3 && nI >= need_inliers(g.fmin, nv)) ? 2 : 1;
+    o.t_status = pass ? 2 : 1;
     if (o.t_status == 2) {
         o.status = S_TEMPORAL;
         o.plane = o.tplane;
@@ -1061,7 +1148,10 @@ template <int TH_, int TW_>
 static cudaError_t launch_temporal_t(const Geometry &g, const Scratch &s, const Batch &b, const Poses &p,
                                      cudaStream_t st) {
     constexpr int TPB = kFitThreads / TLanes<TH_, TW_>::L;   // tiles per block
-    k_temporal<TH_, TW_><<<dim3((g.NT + TPB - 1) / TPB, b.nframes), kFitThreads, 0, st>>>(g, s, b, p);
+    if (g.tcand > 1)
+        k_temporal<TH_, TW_, 4><<<dim3((g.NT + TPB - 1) / TPB, b.nframes), kFitThreads, 0, st>>>(g, s, b, p);
+    else
+        k_temporal<TH_, TW_, 1><<<dim3((g.NT + TPB - 1) / TPB, b.nframes), kFitThreads, 0, st>>>(g, s, b, p);
     return cudaGetLastError();
 }
 

@@ -257,6 +257,7 @@ void lcc_default_params(lcc_params *p) {
     p->fit_schedule = 3;
     p->no_delta = 0;
     p->raw_exact = 0;
+    p->temporal_candidates = 1;
 }
 
 lcc_status lcc_create(lcc_ctx **out, const lcc_sensor *sensor, const lcc_params *params, void *cuda_stream) {
@@ -272,7 +273,8 @@ lcc_status lcc_create(lcc_ctx **out, const lcc_sensor *sensor, const lcc_params 
     if (!(p.fit_thr_m >= 0) || !(p.quant_m > 0) || p.max_refits < 0 || p.max_refits > 6 ||
         !(p.min_inlier_frac >= 0) || p.max_batch < 1 || p.max_batch > kMaxBatch || p.lookahead < 0 ||
         p.lookahead > 32 || p.solver < 0 || p.solver > 1 || p.fit_schedule < 0 ||
-        p.fit_schedule > 3 || p.no_delta < 0 || p.no_delta > 1 || p.raw_exact < 0 || p.raw_exact > 1)
+        p.fit_schedule > 3 || p.no_delta < 0 || p.no_delta > 1 || p.raw_exact < 0 || p.raw_exact > 1 ||
+        p.temporal_candidates < 0 || p.temporal_candidates > 4)
         return LCC_ERR_INVALID_ARG;
     int dev = 0;
     cudaDeviceProp prop;
@@ -306,6 +308,7 @@ lcc_status lcc_create(lcc_ctx **out, const lcc_sensor *sensor, const lcc_params 
     g.schedule = p.fit_schedule;
     g.no_delta = p.no_delta;
     g.raw_exact = p.raw_exact;
+    g.tcand = p.temporal_candidates;
     g.first_rounds = std::min(p.fit_schedule == 3 ? 1 : p.fit_schedule, p.max_refits + 1);
     g.k_max = (int)floorf(p.fit_thr_m / p.quant_m + 0.5f) + 1;
     g.w_res = bits_for(2 * g.k_max);

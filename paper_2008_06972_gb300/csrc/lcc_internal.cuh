@@ -112,6 +112,7 @@ struct Geometry {
     int first_rounds;    // fit rounds of the first pass under a queued schedule
     int no_delta;        // 1: plane-coded points carry no residual code (no residual section)
     int raw_exact;       // 1: raw pixels carry their fp32 range bits (32-bit raw codes)
+    int tcand;           // K tiles a P tile's relaxed-plane test may try (1..4)
     int k_max, w_res, w_raw;
     float elev_max_rad, inv_d_el, inv_d_az;   // first guesses only (1/row and 1/column pitch, rad); the tables decide
     const float *ce, *se, *ct, *st;       // beam tables

@@ -36,7 +36,7 @@ class lcc_params(ctypes.Structure):
                 ("quant_m", ctypes.c_float), ("max_refits", ctypes.c_int32), ("min_inlier_frac", ctypes.c_float),
                 ("merge_runs", ctypes.c_int32), ("max_batch", ctypes.c_int32), ("lookahead", ctypes.c_int32),
                 ("solver", ctypes.c_int32), ("fit_schedule", ctypes.c_int32), ("no_delta", ctypes.c_int32),
-                ("raw_exact", ctypes.c_int32)]
+                ("raw_exact", ctypes.c_int32), ("temporal_candidates", ctypes.c_int32)]
 
 
 class lcc_stats(ctypes.Structure):

@@ -31,8 +31,8 @@ def _cuda():
     lcc.load()
 
 
-def _oparams(tile=(4, 4), thr=0.05, q=0.02, R=3, fmin=0.75, merge=1, no_delta=0, raw_exact=0):
-    return O.params(tile[0], tile[1], thr, q, R, fmin, merge, no_delta, raw_exact)
+def _oparams(tile=(4, 4), thr=0.05, q=0.02, R=3, fmin=0.75, merge=1, no_delta=0, raw_exact=0, tcand=1):
+    return O.params(tile[0], tile[1], thr, q, R, fmin, merge, no_delta, raw_exact, tcand)
 
 
 def _gparams(tile=(4, 4), thr=0.05, q=0.02, R=3, fmin=0.75, merge=1, solver=0, **kw):
@@ -221,11 +221,12 @@ def test_schedule_invariance_and_determinism(cfg1):
 
 # ------------------------------------------------------------------- P frames --
 
-def _pframe_case(seq, frames, tile=(4, 4), thr=0.05, poses=None, schedule=0):
+def _pframe_case(seq, frames, tile=(4, 4), thr=0.05, poses=None, schedule=0, tcand=1):
     from paper_2008_06972_gb300 import lcc
     s = O.sensor(seq.sensor)
-    p = _oparams(tile=tile, thr=thr)
-    c = H.ctx(seq.sensor, **_gparams(tile=tile, thr=thr, max_batch=max(16, len(frames)), fit_schedule=schedule))
+    p = _oparams(tile=tile, thr=thr, tcand=tcand)
+    c = H.ctx(seq.sensor, **_gparams(tile=tile, thr=thr, max_batch=max(16, len(frames)), fit_schedule=schedule,
+                                     temporal_candidates=tcand))
     kf = lcc.Keyframe(c)
     kbits, krecs = H.encode_keyframe(c, seq.frames[seq.key_index], kf)
     okft = O.kf_table_from_stream(s, kbits, c.num_tiles)
@@ -240,15 +241,21 @@ def _pframe_case(seq, frames, tile=(4, 4), thr=0.05, poses=None, schedule=0):
         rng, _, _ = O.range_image(s, pts)
         recs = precs[i]
         otmp = O.temporal_tiles(s, p, rng, okft, poses[i])
-        # the K tile of every anchor is found identically (FP64 transform + exact binning)
+        # the K tile of every anchor is found identically (FP64 transform + exact binning); with
+        # several candidates the K tile tested last depends on the earlier tests' outcomes, so it
+        # may differ only where a test was borderline
         found = otmp["status"] > 0
         assert np.array_equal(recs["t_status"] > 0, found)
-        assert np.array_equal(recs["kref"][found].astype(np.int64), otmp["kref"][found].astype(np.int64))
-        assert np.array_equal(recs["tplane"][found][:, :3].view(np.uint32),
-                              otmp["plane"][found][:, :3].view(np.uint32))
+        same_k = recs["kref"].astype(np.int64) == otmp["kref"].astype(np.int64)
+        excused = (otmp["borderline"] != 0) | ((recs["flags"] & 1) != 0) if tcand > 1 else np.zeros_like(found)
+        assert (same_k | ~found | excused).all()
+        keep = found & same_k
+        assert np.array_equal(recs["tplane"][keep][:, :3].view(np.uint32),
+                              otmp["plane"][keep][:, :3].view(np.uint32))
         border = 0
         for t in np.nonzero(found)[0]:
-            same = recs["t_status"][t] == otmp["status"][t] and recs["t_inlier"][t] == otmp["n_inlier"][t]
+            same = recs["t_status"][t] == otmp["status"][t] and recs["t_inlier"][t] == otmp["n_inlier"][t] and \
+                same_k[t]
             cg, co = float(recs["tplane"][t][3]), float(otmp["plane"][t][3])
             close = abs(cg - co) <= H.PLANE_TOL * max(abs(co), 1.0)
             if same and close:
@@ -646,3 +653,40 @@ def test_raw_exact_sequence_round_trip(cfg2_seq):
         assert np.abs(drng[m] - rng[m]).max() <= 0.01 + 1e-5
         exact = (drng.view(np.uint32) == rng.view(np.uint32)) & m
         assert exact.sum() >= streamfmt.header(bits)["n_raw"]
+
+
+@pytest.mark.parametrize("tile,tcand", [((4, 4), 4), ((8, 8), 3)])
+def test_temporal_candidates_parity(cfg2_seq, tile, tcand):
+    """Several candidate K tiles per P tile: the K tile each test settled on, its rotated normal and
+    the packed stream match the oracle's; more tiles pass than with the anchor's K tile alone."""
+    seq = cfg2_seq
+    border = _pframe_case(seq, [0, seq.key_index + 1], tile=tile, tcand=tcand)
+    assert border <= 20
+
+
+def test_temporal_candidates_sequence_matches_separate_calls(cfg2_seq):
+    """The sequence call's lane-group temporal test with 4 candidates gives the fused per-thread
+    test's streams, and passes more tiles than one candidate."""
+    from paper_2008_06972_gb300 import lcc
+    seq = cfg2_seq
+    n = len(seq.frames)
+    ds = [H.to_dev(p) for p in seq.frames]
+    nb = torch.zeros(n, dtype=torch.int64, device="cuda")
+    temporal = {}
+    for tc in (1, 4):
+        c = H.ctx(seq.sensor, max_batch=16, temporal_candidates=tc)
+        outs = [H.out_buf(c) for _ in range(n)]
+        c.lcc_encode_sequence(seq.key_index, seq.poses, ds, [len(p) for p in seq.frames], outs,
+                              [o.numel() for o in outs], nb, None)
+        assert c.lcc_sync() == 0
+        nbs = nb.cpu().numpy()
+        seq_bits = [outs[i][:nbs[i]].cpu().numpy() for i in range(n)]
+        temporal[tc] = sum(c.lcc_last_stats(f)["tiles_temporal"] for f in range(n))
+        c2 = H.ctx(seq.sensor, max_batch=16, temporal_candidates=tc)
+        kf2 = lcc.Keyframe(c2)
+        H.encode_keyframe(c2, seq.frames[seq.key_index], kf2)
+        others = [f for f in range(n) if f != seq.key_index]
+        pb, _ = H.encode_pframes(c2, kf2, [seq.poses[f] for f in others], [seq.frames[f] for f in others])
+        for i, f in enumerate(others):
+            assert pb[i].tobytes() == seq_bits[f].tobytes(), (tc, f)
+    assert temporal[4] > temporal[1]
