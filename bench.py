@@ -378,13 +378,15 @@ def run_sweep(args, stream, seq, d_pts, flush):
     H, W = seq.sensor.rows, seq.sensor.cols
     steps = max(10, min(args.steps, 50))
     rows = []
-    points = [(th, tw, thr, 0, 0) for th, tw in ((4, 4), (8, 8)) for thr in (0.02, 0.05, 0.10)]
-    points += [(4, 4, 0.02, 1, 0), (8, 8, 0.02, 1, 0)]   # the paper's no-delta mode at a 2 cm threshold
-    points += [(4, 4, 0.05, 0, 1)]                      # raw pixels kept losslessly (fp32 raw codes)
-    for th, tw, thr, nd, rx in points:
+    points = [(th, tw, thr, 0, 0, 1) for th, tw in ((4, 4), (8, 8)) for thr in (0.02, 0.05, 0.10)]
+    points += [(4, 4, 0.02, 1, 0, 1), (8, 8, 0.02, 1, 0, 1)]   # the paper's no-delta mode at a 2 cm threshold
+    points += [(4, 4, 0.05, 0, 1, 1)]                         # raw pixels kept losslessly (fp32 raw codes)
+    points += [(4, 4, 0.05, 0, 0, 4)]                         # up to 4 candidate K tiles per P tile
+    for th, tw, thr, nd, rx, tc in points:
         if True:
             ctx = lcc.Context(seq.sensor, lcc.default_params(tile_h=th, tile_w=tw, fit_thr_m=thr, no_delta=nd,
-                                                            raw_exact=rx, max_batch=max(16, n_frames)), stream=stream)
+                                                            raw_exact=rx, temporal_candidates=tc,
+                                                            max_batch=max(16, n_frames)), stream=stream)
             cap = ctx.max_encoded_bytes
             outs = [torch.zeros(cap, dtype=torch.uint8, device="cuda") for _ in range(n_frames)]
             nb = torch.zeros(n_frames, dtype=torch.int64, device="cuda")
@@ -426,7 +428,8 @@ def run_sweep(args, stream, seq, d_pts, flush):
                 m = ref > 0
                 if bool(m.any()):
                     err = max(err, float((dec[m] - ref[m]).abs().max().item()))
-            rows.append({"tile": f"{th}x{tw}", "thr_m": thr, "no_delta": nd, "raw_exact": rx, "mpts_per_s": round(pts / (ms * 1e-3) / 1e6, 1),
+            rows.append({"tile": f"{th}x{tw}", "thr_m": thr, "no_delta": nd, "raw_exact": rx,
+                         "temporal_candidates": tc, "mpts_per_s": round(pts / (ms * 1e-3) / 1e6, 1),
                          "ms_per_step": round(ms, 4), "compression_ratio": round(12.0 * pts / float(sizes.sum()), 3),
                          "max_decode_error_m": err, "tile_modes": modes})
             del kf, kfd, ctx
