@@ -55,6 +55,8 @@ def parse():
     ap.add_argument("--no-sweep", action="store_true", help="skip the tile / threshold sweep")
     ap.add_argument("--no-imu", action="store_true", help="skip the IMU-pose section")
     ap.add_argument("--no-entropy", action="store_true", help="skip the entropy-stage section")
+    ap.add_argument("--clocks-csv", default="", help="where the SM-clock samples of the timed region go "
+                    "({rank} is replaced by the rank); default: a file under /tmp")
     ap.add_argument("--train-steps", type=int, default=300)
     ap.add_argument("--train-seqs", type=int, default=6)
     return ap.parse_args()
@@ -834,8 +836,8 @@ def main():
     assert ctx.lcc_sync() == lcc.OK
     # ---- timed region: K steps, each bracketed by CUDA events on the context stream ----
     evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-    clocks = Clocks(os.path.join(ROOT, "gpurun_out", f"clocks_rank{rank}.csv") if os.path.isdir(
-        os.path.join(ROOT, "gpurun_out")) else f"/tmp/lcc_clocks_{os.getpid()}.csv")
+    clocks = Clocks(args.clocks_csv.replace("{rank}", str(rank)) if args.clocks_csv
+                    else f"/tmp/lcc_clocks_{os.getpid()}_rank{rank}.csv")
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
