@@ -95,6 +95,9 @@ def test_ties_take_the_leaf_first():
     # weight 2; taking the leaves first joins them together (all lengths 2), taking the node first
     # would give 3, 3, 2, 1 (the same 12 bits: ties change the lengths, not the cost)
     assert E.code_lengths([1, 1, 2, 2]) == [2, 2, 2, 2]
+    # equal counts queue in symbol order: symbols 0 and 1 join first, so symbol 2 gets the 1-bit code
+    assert E.code_lengths([1, 1, 1]) == [2, 2, 1]
+    assert E.code_lengths([3, 0, 3, 3, 0]) == [2, 0, 2, 1, 0]
 
 
 @pytest.fixture(scope="module")
