@@ -140,17 +140,18 @@ __device__ __forceinline__ uint32_t get_sym(const uint32_t *sec, uint32_t w, uin
     return v & ((1u << w) - 1u);
 }
 
-// The symbols of chunk c of a section of width w, in order: the chunk starts on a word (1024
-// symbols of w bits fill whole words), words are read one ahead of their use.
+// m symbols of a section of width w from symbol `first` on, in order: first is a multiple of 32,
+// so the run starts on a word (32 symbols of w bits fill w words); words are read one ahead of
+// their use.
 struct SymReader {
     const uint32_t *in;
     uint32_t words, ip, nxt, w, m;
     unsigned long long buf;
     int nb;
-    __device__ SymReader(const uint32_t *sec, uint32_t w_, uint32_t c, uint32_t m_) {
+    __device__ SymReader(const uint32_t *sec, uint32_t w_, uint32_t first, uint32_t m_) {
         w = w_;
         m = m_;
-        in = sec + (size_t)c * kChunk * w / 32;
+        in = sec + (size_t)first * w / 32;
         words = (uint32_t)(((unsigned long long)m * w + 31) / 32);
         ip = 0;
         nxt = words ? in[0] : 0u;
@@ -445,12 +446,16 @@ __global__ void __launch_bounds__(kBuildThreads) k_ent_build(EntBatch b, Scratch
     const uint32_t nch = (cnt + kChunk - 1) / kChunk;
     uint32_t *cw = sc.chunk + ((size_t)f * kSecs + s) * sc.max_chunks;
     uint32_t mine = 0;
-    for (uint32_t c = tid; c < nch; c += blockDim.x) {
-        SymReader rd(sec, w, c, min(cnt - c * kChunk, (uint32_t)kChunk));
+    for (uint32_t c = tid >> 5; c < nch; c += blockDim.x >> 5) {   // a warp per chunk, 32 symbols a lane
+        const uint32_t c0 = c * kChunk, m = min(cnt - c0, (uint32_t)kChunk), s0 = 32 * (tid & 31);
+        SymReader rd(sec, w, c0 + s0, s0 < m ? min(m - s0, 32u) : 0u);
         uint32_t bits = 0;
         for (uint32_t i = 0; i < rd.m; i++) bits += S.len[rd.next()];
-        cw[c] = (bits + 31) / 32;
-        mine += (bits + 31) / 32;
+        for (int o = 16; o; o >>= 1) bits += __shfl_xor_sync(0xFFFFFFFFu, bits, o);
+        if ((tid & 31) == 0) {
+            cw[c] = (bits + 31) / 32;
+            mine += (bits + 31) / 32;
+        }
     }
     const uint32_t payload = block_sum(mine, S.red);
     if (tid == 0) {
@@ -551,9 +556,11 @@ __global__ void __launch_bounds__(kWriteThreads) k_ent_write(EntBatch b, Scratch
         }
         return;
     }
-    if (blockIdx.x * blockDim.x >= S.nch) return;
-    // the section's codes in shared memory: reversed code | length << 16
+    constexpr int kWarps = kWriteThreads / 32;
+    if (blockIdx.x * kWarps >= S.nch) return;
+    // the section's codes in shared memory: reversed code | length << 16; a chunk buffer per warp
     __shared__ uint32_t s_code[kMaxAlph];
+    __shared__ uint32_t s_buf[kWarps][kChunk * kMaxLen / 32];
     const size_t tab = ((size_t)f * kSecs + s) * kMaxAlph;
     for (uint32_t v = threadIdx.x; v < S.alph; v += blockDim.x)
         s_code[v] = (uint32_t)sc.rcode[tab + v] | (uint32_t)sc.len[tab + v] << 16;
@@ -561,22 +568,41 @@ __global__ void __launch_bounds__(kWriteThreads) k_ent_write(EntBatch b, Scratch
     const uint32_t *coff = sc.chunk + ((size_t)f * kSecs + s) * sc.max_chunks;
     const uint32_t w = L.width[s], cnt = L.count[s];
     uint32_t *pay = dst + (S.alph + 7) / 8 + S.nch;
-    for (uint32_t c = blockIdx.x * blockDim.x + threadIdx.x; c < S.nch; c += gridDim.x * blockDim.x) {
-        uint32_t *o = pay + coff[c];
-        unsigned long long acc = 0;
-        uint32_t nb = 0;
-        SymReader rd(sec, w, c, min(cnt - c * kChunk, (uint32_t)kChunk));
-        for (uint32_t i = 0; i < rd.m; i++) {
-            const uint32_t cl = s_code[rd.next()];
-            acc |= (unsigned long long)(cl & 0xFFFFu) << nb;
-            nb += cl >> 16;
-            if (nb >= 32) {
-                *o++ = (uint32_t)acc;
-                acc >>= 32;
-                nb -= 32;
+    // a warp per chunk: each lane sizes its 32 symbols, an exclusive scan gives its first bit,
+    // the lanes place their codes in the warp's buffer, the warp stores the chunk's words
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    uint32_t *buf = s_buf[warp];
+    for (uint32_t c = blockIdx.x * kWarps + warp; c < S.nch; c += gridDim.x * kWarps) {
+        const uint32_t c0 = c * kChunk, m = min(cnt - c0, (uint32_t)kChunk), s0 = 32 * lane;
+        const uint32_t ml = s0 < m ? min(m - s0, 32u) : 0u;
+        uint32_t bits = 0;
+        {
+            SymReader rd(sec, w, c0 + s0, ml);
+            for (uint32_t i = 0; i < ml; i++) bits += s_code[rd.next()] >> 16;
+        }
+        uint32_t x = bits;
+        for (int d = 1; d < 32; d <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, x, d);
+            if (lane >= d) x += y;
+        }
+        const uint32_t total = __shfl_sync(0xFFFFFFFFu, x, 31), nwords = (total + 31) / 32;
+        for (uint32_t j = lane; j < nwords; j += 32) buf[j] = 0u;
+        __syncwarp();
+        {
+            SymReader rd(sec, w, c0 + s0, ml);
+            uint32_t p = x - bits;
+            for (uint32_t i = 0; i < ml; i++) {
+                const uint32_t cl = s_code[rd.next()], code = cl & 0xFFFFu, len = cl >> 16;
+                const uint32_t wi = p >> 5, sh = p & 31;
+                atomicOr(&buf[wi], code << sh);
+                if (sh + len > 32) atomicOr(&buf[wi + 1], code >> (32 - sh));
+                p += len;
             }
         }
-        if (nb) *o = (uint32_t)acc;
+        __syncwarp();
+        uint32_t *o = pay + coff[c];
+        for (uint32_t j = lane; j < nwords; j += 32) o[j] = buf[j];
+        __syncwarp();
     }
 }
 
