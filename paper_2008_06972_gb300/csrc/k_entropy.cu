@@ -731,7 +731,7 @@ __global__ void __launch_bounds__(256) k_ent_dec_prep(EntBatch b, Scratch sc, un
 constexpr int kPeek = 9;   // codes up to this length resolve in one table lookup
 
 // grid (G, 7 sections, nframes), kWriteThreads threads
-__global__ void __launch_bounds__(kWriteThreads) k_ent_dec(EntBatch b, Scratch sc, unsigned *err) {
+__global__ void __launch_bounds__(kWriteThreads) k_ent_dec(EntBatch b, Scratch sc, unsigned *err_word) {
     __shared__ uint16_t s_sym[kMaxAlph];          // symbols in (length, symbol) order
     __shared__ uint32_t s_peek[1 << kPeek];       // first kPeek bits -> symbol | length << 16 (0: longer)
     __shared__ uint32_t s_lim[kMaxLen + 1], s_first[kMaxLen + 1], s_index[kMaxLen + 2];
@@ -749,7 +749,7 @@ __global__ void __launch_bounds__(kWriteThreads) k_ent_dec(EntBatch b, Scratch s
         }
         return;
     }
-    if (blockIdx.x * blockDim.x >= D.nch) return;
+    if (blockIdx.x * (kWriteThreads / 32) >= D.nch) return;
     // canonical decode tables: per length the left-justified limit (codes of length l are the
     // 15-bit windows in [limit(l - 1), limit(l))), and a direct table for the short codes
     if (threadIdx.x == 0) {
@@ -776,59 +776,89 @@ __global__ void __launch_bounds__(kWriteThreads) k_ent_dec(EntBatch b, Scratch s
     const uint32_t *co = src + tw;
     const uint32_t *pay = co + nch;
     const uint32_t pay_words = D.words - tw - nch;
-    for (uint32_t c = blockIdx.x * blockDim.x + threadIdx.x; c < nch; c += gridDim.x * blockDim.x) {
+    constexpr int kWarps = kWriteThreads / 32;
+    __shared__ uint32_t s_out[kWarps][kChunk * kMaxWidth / 32];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    uint32_t *obuf = s_out[warp];
+    // a warp per chunk.  Lane j decodes the codes that start in its 1/32 of the chunk's bits.
+    // Its true first bit is where lane j - 1's codes end, found by rounds of speculative decode:
+    // lane 0 starts exactly, each round every lane decodes from its current start and the next
+    // lane takes its end; once no start changes every start is a code boundary (at most 32
+    // rounds; Huffman codes resynchronise within a few codes, so usually two or three).
+    for (uint32_t c = blockIdx.x * kWarps + warp; c < nch; c += gridDim.x * kWarps) {
         const uint32_t beg = co[c], end = c + 1 < nch ? co[c + 1] : pay_words;   // validated by the prep
-        uint32_t wp = beg;
-        uint32_t nxt = wp < end ? pay[wp] : 0u;   // the next payload word, loaded one refill ahead
-        unsigned long long buf = 0;   // stream bits, the next one in bit 0
-        int nb = 0;
-        uint32_t *o = dst + (size_t)c * kChunk * w / 32;   // 1024 symbols of w bits fill whole words
-        unsigned long long acc = 0;
-        uint32_t na = 0;
+        const uint32_t *cw = pay + beg;
+        const uint32_t cwords = end - beg, nbits = 32 * cwords;
         const uint32_t m = min(cnt - c * kChunk, (uint32_t)kChunk);
-        bool bad = false;
-        for (uint32_t i = 0; i < m; i++) {
-            if (nb < 32 && wp < end) {
-                buf |= (unsigned long long)nxt << nb;
-                nb += 32;
-                wp++;
-                nxt = wp < end ? pay[wp] : 0u;
-            }
-            // the next 15 stream bits, first bit most significant
-            const uint32_t v = __brev((uint32_t)buf & 0x7FFFu) >> (32 - kMaxLen);
-            uint32_t sym, l;
+        const uint32_t span = (nbits + 31) / 32;
+        const uint32_t limit = lane == 31 ? nbits : min(nbits, (lane + 1) * span);   // codes starting below
+        // one code at bit p of the chunk: symbol | length << 16, 0 if no code starts there
+        auto code_at = [&](uint32_t p) -> uint32_t {
+            const uint32_t wi = p >> 5, sh = p & 31;
+            const unsigned long long lo = wi < cwords ? cw[wi] : 0u, hi = wi + 1 < cwords ? cw[wi + 1] : 0u;
+            const uint32_t v = __brev((uint32_t)((lo | hi << 32) >> sh) & 0x7FFFu) >> (32 - kMaxLen);
             const uint32_t pk = s_peek[v >> (kMaxLen - kPeek)];
-            if (pk) {
-                sym = pk & 0xFFFFu;
-                l = pk >> 16;
-            } else {
-                l = kPeek + 1;
-                while (l <= (uint32_t)kMaxLen && v >= s_lim[l]) l++;
-                if (l > (uint32_t)kMaxLen) {
+            if (pk) return pk;
+            uint32_t l = kPeek + 1;
+            while (l <= (uint32_t)kMaxLen && v >= s_lim[l]) l++;
+            if (l > (uint32_t)kMaxLen) return 0u;
+            return (uint32_t)s_sym[s_index[l] + (v >> (kMaxLen - l)) - s_first[l]] | l << 16;
+        };
+        uint32_t start = lane == 0 ? 0u : min(nbits, lane * span), n = 0;
+        bool bad = false;
+        for (int round = 0; round < 32; round++) {
+            uint32_t p = start;
+            n = 0;
+            bad = false;
+            while (p < limit) {
+                const uint32_t sl = code_at(p);
+                if (!sl || n == (uint32_t)kChunk) {
                     bad = true;
                     break;
                 }
-                sym = s_sym[s_index[l] + (v >> (kMaxLen - l)) - s_first[l]];
+                p += sl >> 16;
+                n++;
             }
-            if ((int)l > nb) {
-                bad = true;
+            uint32_t next = __shfl_up_sync(0xFFFFFFFFu, p, 1);
+            if (lane == 0) next = 0u;
+            const bool moved = next != start;
+            start = next;
+            if (!__any_sync(0xFFFFFFFFu, moved)) break;
+        }
+        // symbols before each lane's first one; the chunk's word padding may decode into codes
+        // past the m-th symbol, which are dropped
+        uint32_t x = n;
+        for (int d = 1; d < 32; d <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, x, d);
+            if (lane >= d) x += y;
+        }
+        const uint32_t before = x - n, total = __shfl_sync(0xFFFFFFFFu, x, 31);
+        const uint32_t mine = before >= m ? 0u : min(n, m - before);
+        bool err = total < m || (bad && before + n < m);
+        const uint32_t owords = (m * w + 31) / 32;
+        for (uint32_t j = lane; j < owords; j += 32) obuf[j] = 0u;
+        __syncwarp();
+        uint32_t p = start;
+        for (uint32_t i = 0; i < mine && !err; i++) {
+            const uint32_t sl = code_at(p);
+            if (!sl || p + (sl >> 16) > nbits) {   // no code, or one that runs past the chunk
+                err = true;
                 break;
             }
-            buf >>= l;
-            nb -= (int)l;
-            acc |= (unsigned long long)sym << na;
-            na += w;
-            if (na >= 32) {
-                *o++ = (uint32_t)acc;
-                acc >>= 32;
-                na -= 32;
-            }
+            p += sl >> 16;
+            const uint32_t bit = (before + i) * w, wi = bit >> 5, sh = bit & 31, sym = sl & 0xFFFFu;
+            atomicOr(&obuf[wi], sym << sh);
+            if (sh + w > 32) atomicOr(&obuf[wi + 1], sym >> (32 - sh));
         }
-        if (bad) {
-            atomicOr(err, E_CORRUPT);
+        if (__any_sync(0xFFFFFFFFu, err)) {
+            if (lane == 0) atomicOr(err_word, E_CORRUPT);
+            __syncwarp();
             continue;
         }
-        if (na) *o = (uint32_t)acc;
+        __syncwarp();
+        uint32_t *o = dst + (size_t)c * kChunk * w / 32;   // 1024 symbols of w bits fill whole words
+        for (uint32_t j = lane; j < owords; j += 32) o[j] = obuf[j];
+        __syncwarp();
     }
 }
 
