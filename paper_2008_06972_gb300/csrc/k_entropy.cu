@@ -249,23 +249,45 @@ __device__ void canonical_tables(const uint32_t *per_len, uint32_t *first, uint3
     }
 }
 
-// (length, symbol) sort of the alphabet's used symbols into keys[0, n) as length << 12 | symbol.
-__device__ uint32_t sort_by_length(const uint8_t *len, uint32_t alph, unsigned long long *keys, uint32_t *red) {
-    // compaction in symbol order: each thread owns a run of consecutive symbols
-    const uint32_t per = (alph + blockDim.x - 1) / blockDim.x;
-    const uint32_t s0 = min(alph, threadIdx.x * per), s1 = min(alph, s0 + per);
-    uint32_t own = 0;
-    for (uint32_t s = s0; s < s1; s++) own += len[s] != 0;
-    uint32_t n = 0;
-    uint32_t pos = block_excl(own, red, &n);
-    for (uint32_t s = s0; s < s1; s++)
-        if (len[s]) keys[pos++] = (unsigned long long)len[s] << 12 | s;
-    uint32_t P = 2;
-    while (P < n) P <<= 1;
-    for (uint32_t i = n + threadIdx.x; i < P; i += blockDim.x) keys[i] = ~0ull;
+// Every used symbol's position in (length, symbol) order, handed to place(symbol, length,
+// position): a count per length and thread (cnt, kMaxLen rows of blockDim entries), an exclusive
+// prefix of each row over the threads (a warp per row), then each thread places its run of
+// consecutive symbols.  index[l] is the position of the first symbol of length l.
+template <class F>
+__device__ void place_by_length(const uint8_t *len, uint32_t alph, const uint32_t *index, uint16_t *cnt,
+                                F &&place) {
+    const uint32_t T = blockDim.x, t = threadIdx.x, lane = t & 31, warp = t >> 5, nw = T >> 5;
+    const uint32_t per = (alph + T - 1) / T, s0 = min(alph, t * per), s1 = min(alph, s0 + per);
+    for (int l = 0; l < kMaxLen; l++) cnt[l * T + t] = 0;
+    for (uint32_t v = s0; v < s1; v++)
+        if (len[v]) cnt[(len[v] - 1) * T + t]++;
     __syncthreads();
-    bitonic_sort(keys, P);
-    return n;
+    const uint32_t per_lane = T / 32;
+    for (uint32_t row = warp; row < (uint32_t)kMaxLen; row += nw) {
+        uint16_t *r = cnt + row * T + lane * per_lane;
+        uint32_t sum = 0;
+        for (uint32_t k = 0; k < per_lane; k++) sum += r[k];
+        uint32_t x = sum;
+        for (int d = 1; d < 32; d <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, x, d);
+            if ((int)lane >= d) x += y;
+        }
+        uint32_t base = x - sum;
+        for (uint32_t k = 0; k < per_lane; k++) {
+            const uint32_t c = r[k];
+            r[k] = (uint16_t)base;
+            base += c;
+        }
+    }
+    __syncthreads();
+    for (uint32_t v = s0; v < s1; v++) {
+        const uint32_t l = len[v];
+        if (!l) continue;
+        uint16_t &c = cnt[(l - 1) * T + t];
+        place(v, l, index[l] + c);
+        c++;
+    }
+    __syncthreads();
 }
 
 struct BuildSmem {
@@ -434,13 +456,11 @@ __global__ void __launch_bounds__(kBuildThreads) k_ent_build(EntBatch b, Scratch
     __syncthreads();
     if (tid == 0) canonical_tables(S.per_len, S.first, S.index);
     __syncthreads();
-    const uint32_t nused = sort_by_length(S.len, alph, S.keys, S.red);
     const size_t tab = ((size_t)f * kSecs + s) * kMaxAlph;
-    for (uint32_t i = tid; i < nused; i += blockDim.x) {
-        const uint32_t l = (uint32_t)(S.keys[i] >> 12), v = (uint32_t)(S.keys[i] & 0xFFFu);
-        const uint32_t code = S.first[l] + (i - S.index[l]);
+    place_by_length(S.len, alph, S.index, reinterpret_cast<uint16_t *>(S.keys), [&](uint32_t v, uint32_t l, uint32_t pos) {
+        const uint32_t code = S.first[l] + (pos - S.index[l]);
         sc.rcode[tab + v] = (uint16_t)(__brev(code) >> (32 - l));
-    }
+    });
     for (uint32_t v = tid; v < alph; v += blockDim.x) sc.len[tab + v] = S.len[v];
     // chunk sizes
     const uint32_t nch = (cnt + kChunk - 1) / kChunk;
@@ -614,7 +634,7 @@ struct DecSmem {
     uint32_t per_len[kMaxLen + 1];
     uint32_t first[kMaxLen + 1];
     uint32_t index[kMaxLen + 2];
-    unsigned long long keys[kMaxAlph];
+    uint16_t cnt[kMaxLen * 256];   // place_by_length counters (256 threads)
     uint32_t bad;
 };
 
@@ -710,9 +730,9 @@ __global__ void __launch_bounds__(256) k_ent_dec_prep(EntBatch b, Scratch sc, un
         }
         for (int l = 0; l <= kMaxLen + 1; l++) D.index[l] = S.index[l];
     }
-    const uint32_t n = sort_by_length(S.len, alph, S.keys, S.red);
     uint16_t *sorted = sc.sorted + ((size_t)f * kSecs + s) * kMaxAlph;
-    for (uint32_t i = tid; i < n; i += blockDim.x) sorted[i] = (uint16_t)(S.keys[i] & 0xFFFu);
+    place_by_length(S.len, alph, S.index, S.cnt,
+                    [&](uint32_t v, uint32_t, uint32_t pos) { sorted[pos] = (uint16_t)v; });
     // chunk offsets non-decreasing, inside the payload
     const uint32_t nch = (L.count[s] + kChunk - 1) / kChunk, tw = (alph + 7) / 8;
     const uint32_t pay = words - tw - nch;
