@@ -364,14 +364,14 @@ lcc_status lcc_selftest_bounded_wait(int64_t limit, void *cuda_stream);
 /* ---- Range image without a context or any allocation ----
  *
  * The paper has no counterpart: this is an implementation entry point.  It
- * computes what lcc_range_image computes (Sec. III-B, Eq. 1-2: one pixel per
- * point by exact boundary sign tests, nearest point per pixel) for callers
- * that must not allocate device memory: a process whose device memory is
- * fully reserved up front by its own pool, or a latency-critical thread that
- * cannot take the implicit device-wide synchronisation of cudaFree or the
- * cost of a first allocation.  It makes no cudaMalloc, cudaFree or other
- * allocating call; its scratch is one fixed device array of about 1.2 MB
- * (range image, boundary tables, counters) in the library.
+ * writes the same outputs as lcc_range_image, bit for bit, for callers that
+ * must not allocate device memory: a process whose device memory is fully
+ * reserved up front by its own pool, or a latency-critical thread that cannot
+ * take the implicit device-wide synchronisation of cudaFree or the cost of a
+ * first allocation.  It makes no cudaMalloc, cudaFree or other allocating
+ * call; its scratch is one fixed device array of about 1.2 MB (range image,
+ * boundary tables, counters) in the library, which every GPU that loads the
+ * library keeps until the process exits.
  *
  * Limits: rows <= 512, cols <= 8192, rows * cols <= 262144 (e.g. 128 x 2048);
  * larger sensors return LCC_ERR_UNSUPPORTED.  Invalid sensor or pointers
@@ -380,13 +380,17 @@ lcc_status lcc_selftest_bounded_wait(int64_t limit, void *cuda_stream);
  * d_pts: n device float4 (x, y, z, unused), 16-byte aligned (may be NULL when
  * n = 0).  Outputs (either may be NULL): d_range [rows*cols] fp32 (0 =
  * empty), d_valid occupancy bitmap of ceil(rows*cols/32) words, bit p of word
- * p/32 set when pixel p holds a point.  Asynchronous on cuda_stream (the
- * boundary tables are copied from a small host stack buffer by pageable
- * cudaMemcpyAsync, which returns once each chunk is staged).
+ * p/32 set when pixel p holds a point.  The clearing and binning work runs
+ * asynchronously on cuda_stream.  The sensor's boundary tables stay in the
+ * array between calls: a call whose sensor differs from the previous call's on
+ * the device (and the first call) copies them from host memory with pageable
+ * cudaMemcpyAsync, and such a copy first waits for the work already queued on
+ * cuda_stream, so that call returns only after that work has finished.
  *
  * Set-up: the first call on each device, with that device current, resolves
- * the array's address with cudaGetSymbolAddress (checked) and caches it;
- * make that first call before any stream capture on that device.
+ * the array's address with cudaGetSymbolAddress (checked) and keeps it; a
+ * cudaDeviceReset ends the context the address belongs to, and the next call
+ * in the new context repeats the set-up (and the table copy).
  * The array is shared by every call on a device: calls that overlap in time
  * (other streams, other threads) race on it and must be serialised by the
  * caller.  Each call clears what must start cleared (range image to empty,
@@ -438,6 +442,7 @@ typedef struct lcc_plan_info {
     int64_t launches;         /* kernel launches of one encode (after the first encode or capture) */
     int64_t graph_nodes;      /* nodes of the captured graph (0 before capture) */
     int32_t classes, captured;
+    int64_t seeded_key_frames;/* key frames whose fits the attached proposal net seeds */
 } lcc_plan_info;
 
 /* Validates the table and allocates the key-frame plane tables (synchronous).
@@ -448,6 +453,20 @@ lcc_status lcc_plan_create(lcc_plan **out, int32_t nctx, lcc_ctx *const *ctxs, i
  * key_interval) must be unchanged.  A captured plan is re-recorded and its
  * executable graph updated in place. */
 lcc_status lcc_plan_update(lcc_plan *plan, int32_t nseq, const lcc_seq_desc *seqs);
+/* Learned proposals for the plan's key frames (not in the paper; the net is the one of
+ * lcc_net_* below).  With net != NULL, every chunk of key frames of a class whose context has
+ * 8x8 tiles is, after its binning, turned into net inputs (lcc_net_tile_inputs_batch's kernel,
+ * the range images kept) and run through the tcgen05 inference, and its tile fits are seeded by
+ * the proposals as in lcc_encode_keyframes (skip_logit as there), all on the class's stream and
+ * inside the captured graph.  P frames keep the plain fit for the tiles their temporal test
+ * leaves.  Streams are those lcc_encode_keyframes(..., proposals, skip_logit, ...) writes for
+ * the same key frames, followed by the plain P-frame path.  Classes with other tile shapes stay
+ * plain; LCC_ERR_UNSUPPORTED if no class has 8x8 tiles.  net == NULL detaches the net.  The plan
+ * allocates the inputs and proposals of one chunk per class (about 550 B per tile of max_batch
+ * frames) and does not own the net, which must outlive the plan's use.  A captured plan is
+ * re-recorded and its executable graph updated in place.  A bounded wait of the inference that
+ * ran out is reported by lcc_plan_sync (LCC_ERR_TIMEOUT). */
+lcc_status lcc_plan_set_proposals(lcc_plan *plan, lcc_net *net, float skip_logit);
 /* Enqueues one encode of the whole table (asynchronous, no graph). */
 lcc_status lcc_plan_encode(lcc_plan *plan);
 /* Records one encode of the table as a CUDA graph (nothing runs).  Not allowed while
@@ -457,6 +476,16 @@ lcc_status lcc_plan_capture(lcc_plan *plan);
 lcc_status lcc_plan_replay(lcc_plan *plan);
 /* Waits for the stream, then returns (and clears) the first error latched by any context. */
 lcc_status lcc_plan_sync(lcc_plan *plan);
+/* End-to-end encode with HOST outputs: one encode of the table (the captured graph if there is
+ * one, else eager launches), then every frame's stream is copied by one kernel into h_out[f] (a
+ * host array of `frames` pointers in table order: sequence by sequence, frame by frame; each a
+ * page-locked, device-mapped, 16-byte aligned host buffer of at least that frame's cap bytes),
+ * and every stream size into h_nbytes (host array of `frames` entries, table order; the needed
+ * size where a capacity error latched).  Synchronous: returns lcc_plan_sync's status.  The plan's
+ * input points may be page-locked host memory mapped into the device (read in place by the
+ * binning kernel over the host link).  LCC_ERR_INVALID_ARG for an output that is not
+ * page-locked host memory. */
+lcc_status lcc_plan_encode_host(lcc_plan *plan, uint8_t *const *h_out, uint64_t *h_nbytes);
 lcc_status lcc_plan_get_info(const lcc_plan *plan, lcc_plan_info *out);
 void lcc_plan_destroy(lcc_plan *plan);
 
@@ -465,17 +494,18 @@ void lcc_plan_destroy(lcc_plan *plan);
  * Not in the paper (its tile size is a fixed parameter).  Encodes a sample
  * sequence (nframes <= 64 device frames, key frame key_index, poses as in
  * lcc_encode_sequence) with every candidate of tile shape {4x4, 4x8, 8x8,
- * 8x16} x run-test horizon {8, 16, 32} (only 0 when base->merge_runs is 0) x
- * fit schedule {0, 3}, each on a context of its own, `reps` timed encodes per
- * candidate (CUDA events on cuda_stream).  Every frame is then decoded and
- * compared with its binned input: candidates whose max range error exceeds
- * max_err_m are rejected.  Of the rest, those whose total stream size is at
- * most (1 + bytes_slack) x the smallest are eligible, and the fastest of
- * them is written to *best (base with tile_h, tile_w, lookahead and
- * fit_schedule replaced).  results (cap entries, may be NULL when cap is 0)
- * receives every candidate, *nresults their number.  Synchronous; allocates
- * and frees its own buffers.  LCC_ERR_UNSUPPORTED when no candidate is
- * eligible. */
+ * 8x16} (those whose bit is set in `shapes`: bit 0 4x4, bit 1 4x8, bit 2 8x8,
+ * bit 3 8x16; 0 = all four) x run-test horizon {8, 16, 32} (only 0 when
+ * base->merge_runs is 0) x fit schedule {0, 3}, each on a context of its own,
+ * `reps` timed encodes per candidate (CUDA events on cuda_stream).  Every
+ * frame is then decoded and compared with its binned input: candidates whose
+ * max range error exceeds max_err_m are rejected.  Of the rest, those whose
+ * total stream size is at most (1 + bytes_slack) x the smallest are eligible,
+ * and the fastest of them is written to *best (base with tile_h, tile_w,
+ * lookahead and fit_schedule replaced).  results (cap entries, may be NULL
+ * when cap is 0) receives every candidate, *nresults their number.
+ * Synchronous; allocates and frees its own buffers.  LCC_ERR_UNSUPPORTED when
+ * no candidate is eligible. */
 typedef struct lcc_tune_result {
     int32_t tile_h, tile_w, lookahead, fit_schedule;
     int32_t status;           /* LCC_OK, or why the candidate could not be measured */
@@ -489,8 +519,8 @@ typedef struct lcc_tune_result {
 
 lcc_status lcc_autotune(const lcc_sensor *sensor, const lcc_params *base, int32_t nframes, int32_t key_index,
                         const double *poses, const float *const *d_pts, const int64_t *n, int32_t reps,
-                        float max_err_m, float bytes_slack, void *cuda_stream, lcc_tune_result *results,
-                        int32_t cap, int32_t *nresults, lcc_params *best);
+                        float max_err_m, float bytes_slack, uint32_t shapes, void *cuda_stream,
+                        lcc_tune_result *results, int32_t cap, int32_t *nresults, lcc_params *best);
 
 #ifdef __cplusplus
 }

@@ -1,12 +1,12 @@
-// lcc_range_image_static: the range-image conversion of Sec. III-B (Eq. 1-2,
-// nearest point per pixel) for callers that may not allocate: no context, no
-// cudaMalloc/cudaFree, no allocating library call.  Its scratch (the range
-// image being built, the boundary tables, the binning counters) is one
-// fixed device array of this file.
+// lcc_range_image_static: the same range image as lcc_range_image, for callers
+// that may not allocate: no context, no cudaMalloc/cudaFree, no allocating
+// library call.  Its scratch (the range image being built, the boundary
+// tables, the binning counters) is one fixed device array of this file.  The
+// paper has no counterpart: this is an implementation entry point.
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
-#include <atomic>
 #include <cmath>
 #include <cstring>
 
@@ -31,16 +31,56 @@ static_assert(sizeof(DevStats) <= 256, "binning counters fit their slot");
 static __device__ __align__(256) unsigned char g_static_scratch[kStaticBytes];
 
 constexpr int kMaxDevices = 64;
-std::atomic<unsigned char *> g_base[kMaxDevices];
 
-// Address of the scratch array on the current device: resolved once per device by
-// cudaGetSymbolAddress (with the device current), after checking that it is an sm_103 part.
-lcc_status scratch_base(unsigned char **out) {
+// Per device: the context the scratch address was looked up in (its unique id, 0 = none), the
+// address, and the sensor whose boundary tables the array holds (valid while `have_tables`).
+struct DevState {
+    unsigned long long ctx_id = 0;
+    unsigned char *base = nullptr;
+    bool have_tables = false;
+    lcc_sensor tables_of{};
+};
+DevState g_dev[kMaxDevices];
+
+using PfnCtxGetCurrent = CUresult (*)(CUcontext *);
+using PfnCtxGetId = CUresult (*)(CUcontext, unsigned long long *);
+
+// Unique id of the calling thread's current context (0 if there is none yet or the driver
+// cannot tell): a cudaDeviceReset ends a device's context, and the next one gets a new id.
+unsigned long long current_ctx_id() {
+    static PfnCtxGetCurrent get_current = [] {
+        void *fn = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &fn, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+            q != cudaDriverEntryPointSuccess)
+            fn = nullptr;
+        return reinterpret_cast<PfnCtxGetCurrent>(fn);
+    }();
+    static PfnCtxGetId get_id = [] {
+        void *fn = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &fn, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+            q != cudaDriverEntryPointSuccess)
+            fn = nullptr;
+        return reinterpret_cast<PfnCtxGetId>(fn);
+    }();
+    CUcontext c = nullptr;
+    unsigned long long id = 0;
+    if (!get_current || !get_id || get_current(&c) != CUDA_SUCCESS || !c || get_id(c, &id) != CUDA_SUCCESS)
+        return 0;
+    return id;
+}
+
+// Address of the scratch array on the current device.  Set-up (with the device current): check
+// that it is an sm_103 part and look the address up with cudaGetSymbolAddress; done on the first
+// call on a device and again whenever the device's context is not the one of the last set-up.
+lcc_status scratch_base(DevState **out) {
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return LCC_ERR_NO_DEVICE;
     if (dev < 0 || dev >= kMaxDevices) return LCC_ERR_UNSUPPORTED;
-    unsigned char *p = g_base[dev].load(std::memory_order_acquire);
-    if (!p) {
+    DevState &d = g_dev[dev];
+    const unsigned long long id = current_ctx_id();
+    if (!d.base || id == 0 || id != d.ctx_id) {
         int major = 0, minor = 0;
         if (cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, dev) != cudaSuccess ||
             cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, dev) != cudaSuccess)
@@ -48,11 +88,17 @@ lcc_status scratch_base(unsigned char **out) {
         if (!(major == 10 && minor == 3)) return LCC_ERR_NO_DEVICE;
         void *sym = nullptr;
         if (cudaGetSymbolAddress(&sym, g_static_scratch) != cudaSuccess || !sym) return LCC_ERR_CUDA;
-        p = static_cast<unsigned char *>(sym);
-        g_base[dev].store(p, std::memory_order_release);
+        d.base = static_cast<unsigned char *>(sym);
+        d.ctx_id = current_ctx_id();   // the lookup above made the device's context current
+        d.have_tables = false;         // a new context's array holds no tables yet
     }
-    *out = p;
+    *out = &d;
     return LCC_OK;
+}
+
+bool same_sensor(const lcc_sensor &a, const lcc_sensor &b) {
+    return a.rows == b.rows && a.cols == b.cols && a.elev_min_deg == b.elev_min_deg &&
+           a.elev_max_deg == b.elev_max_deg && a.max_range_m == b.max_range_m;
 }
 
 // Boundary tables rbc, rbs (rows + 1 each), cbc, cbs (cols each), packed in that order, uploaded
@@ -94,13 +140,21 @@ extern "C" lcc_status lcc_range_image_static(const lcc_sensor *sensor, const flo
         return LCC_ERR_INVALID_ARG;
     if (s.rows > kStaticMaxRows || s.cols > kStaticMaxCols || (int64_t)s.rows * s.cols > kStaticMaxPixels)
         return LCC_ERR_UNSUPPORTED;
-    unsigned char *base = nullptr;
-    lcc_status st = scratch_base(&base);
+    DevState *dev = nullptr;
+    lcc_status st = scratch_base(&dev);
     if (st != LCC_OK) return st;
+    unsigned char *base = dev->base;
     cudaStream_t stream = (cudaStream_t)cuda_stream;
     const int H = s.rows, W = s.cols;
     float *tab = reinterpret_cast<float *>(base + kTableOff);
-    if ((st = upload_tables(s, tab, stream)) != LCC_OK) return st;
+    // the tables stay in the array between calls: upload them only for a sensor other than the
+    // previous call's on this device (calls are serialised by the caller)
+    if (!dev->have_tables || !same_sensor(dev->tables_of, s)) {
+        dev->have_tables = false;
+        if ((st = upload_tables(s, tab, stream)) != LCC_OK) return st;
+        dev->tables_of = s;
+        dev->have_tables = true;
+    }
 
     Geometry g{};
     g.H = H;
