@@ -177,8 +177,11 @@ __global__ void k_net_prep(NetDev nd) {
 
 // ------------------------------------------------------------------ inputs --
 
-// Net input of every 8x8 tile of the frame binned into slot 0; the range image
-// is reset to empty afterwards.  One warp per tile, two pixels per lane.
+// Net input of every 8x8 tile of the frames binned into slots 0.. (frame = blockIdx.y).  With
+// kReset the range image is reset to empty afterwards (the standalone input call); without it the
+// image stays for the encode that follows (the plan's seeded key frames, whose pack resets it).
+// One warp per tile, two pixels per lane.
+template <bool kReset>
 __global__ void k_net_inputs(Geometry g, uint32_t *rimg0, bf16 *x0, float4 *anchor0) {
     const int lane = threadIdx.x & 31;
     const int tile = blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5);
@@ -205,7 +208,7 @@ __global__ void k_net_inputs(Geometry g, uint32_t *rimg0, bf16 *x0, float4 *anch
             p[h][1] = __fmul_rn(r[h], uy);
             p[h][2] = __fmul_rn(r[h], uz);
         }
-        if (in) rimg[(size_t)i * g.W + j] = kEmptyBits;
+        if (kReset && in) rimg[(size_t)i * g.W + j] = kEmptyBits;
     }
     const unsigned b0 = __ballot_sync(0xffffffffu, v[0]), b1 = __ballot_sync(0xffffffffu, v[1]);
     float ra = 0.f, pa0 = 0.f, pa1 = 0.f, pa2 = 0.f;
@@ -953,6 +956,37 @@ lcc_status backward(lcc_net *net, const uint16_t *d_x, const float *d_labels, in
 
 }  // namespace
 
+namespace lcc {
+namespace api {
+
+lcc_status net_inputs_slots(lcc_ctx *c, int nframes, uint16_t *d_x, float4 *d_anchor) {
+    if (c->g.th != 8 || c->g.tw != 8 || nframes < 1 || nframes > c->slots) return LCC_ERR_UNSUPPORTED;
+    const int wpb = 8;
+    k_net_inputs<false><<<dim3((c->g.NT + wpb - 1) / wpb, nframes), wpb * 32, 0, c->stream>>>(
+        c->g, c->s.rimg, reinterpret_cast<bf16 *>(d_x), d_anchor);
+    return cudaGetLastError() == cudaSuccess ? LCC_OK : LCC_ERR_CUDA;
+}
+
+lcc_status net_forward_on(lcc_net *net, const uint16_t *d_x, int64_t ntiles, float *d_out, cudaStream_t st) {
+    if (ntiles <= 0) return LCC_OK;
+    cudaStream_t own = net->stream;
+    net->stream = st;
+    const lcc_status s = forward_tc(net, d_x, ntiles, d_out, false);
+    net->stream = own;
+    return s;
+}
+
+lcc_status net_latched(lcc_net *net) {
+    int e = 0;
+    if (cudaMemcpy(&e, net->err, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return LCC_ERR_CUDA;
+    if (!e) return LCC_OK;
+    cudaMemset(net->err, 0, sizeof(int));
+    return LCC_ERR_TIMEOUT;
+}
+
+}  // namespace api
+}  // namespace lcc
+
 extern "C" {
 
 lcc_status lcc_net_create(lcc_net **out, const float *h_params, int64_t max_tiles, void *cuda_stream) {
@@ -1064,7 +1098,7 @@ lcc_status lcc_net_tile_inputs_batch(lcc_ctx *c, int32_t nframes, const float *c
     lcc_status st = bin_frames(c, nframes, slots, d_pts, n);
     if (st != LCC_OK) return st;
     const int wpb = 8;
-    k_net_inputs<<<dim3((c->g.NT + wpb - 1) / wpb, nframes), wpb * 32, 0, c->stream>>>(
+    k_net_inputs<true><<<dim3((c->g.NT + wpb - 1) / wpb, nframes), wpb * 32, 0, c->stream>>>(
         c->g, c->s.rimg, reinterpret_cast<bf16 *>(d_x), reinterpret_cast<float4 *>(d_anchor));
     return cudaGetLastError() == cudaSuccess ? LCC_OK : LCC_ERR_CUDA;
 }

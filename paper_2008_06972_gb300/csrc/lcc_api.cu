@@ -20,7 +20,7 @@ namespace api {
 
 const char *kKernelNames[] = {"bin",        "fit",          "merge",      "rounds",    "pack",
                               "decode_prep", "decode_px",    "range_export", "lookbehind", "temporal",
-                              "ent_build",  "ent_layout",   "ent_write",  "ent_decode"};
+                              "ent_build",  "ent_layout",   "ent_write",  "ent_decode", "net_inputs", "net_fwd"};
 
 cudaEvent_t get_event(lcc_ctx *c) {
     if (!c->pool.empty()) {

@@ -26,7 +26,7 @@ struct TimelineRec {
 };
 constexpr size_t kMaxTimeline = 65536;
 
-constexpr int kNumKernels = 14;
+constexpr int kNumKernels = 16;
 extern const char *kKernelNames[];
 
 inline size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
@@ -100,6 +100,13 @@ lcc_status encode_batch(lcc_ctx *c, int kind, int nframes, const int *slots, uin
                         float skip_logit = 0.f);
 lcc_status check_frames(lcc_ctx *c, int nframes, const float *const *d_pts, const int64_t *n,
                         uint8_t *const *d_out, const uint64_t *cap);
+// Net inputs (8x8 tiles) of the frames binned into slots 0..nframes-1 of c, on c's stream; the
+// range images are kept for the encode that follows.  Frame f's tiles are rows f*NT.. of d_x.
+lcc_status net_inputs_slots(lcc_ctx *c, int nframes, uint16_t *d_x, float4 *d_anchor);
+// Proposal-net inference on stream st instead of the net's own stream.
+lcc_status net_forward_on(lcc_net *net, const uint16_t *d_x, int64_t ntiles, float *d_out, cudaStream_t st);
+// Reads and clears the net's bounded-wait error flag (synchronous): LCC_ERR_TIMEOUT if it was set.
+lcc_status net_latched(lcc_net *net);
 
 }  // namespace api
 }  // namespace lcc

@@ -1,7 +1,9 @@
 // Batched encode of a table of sequences (lcc_plan_*): key-frame grouping,
 // chunking of frames into the contexts' slots, fork/join of resolution
 // classes onto side streams, and capture of the whole enqueue as one CUDA
-// graph that is replayed.
+// graph that is replayed.  With a proposal net attached, every chunk of key
+// frames of an 8x8-tile class runs the net's input and tcgen05 inference
+// kernels between its binning and its (seeded) fit, inside the same graph.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -38,6 +40,11 @@ struct PlanClass {
     float4 *tables = nullptr;        // ngroups x NT key-frame planes
     int ngroups = 0;
     std::vector<PlanFrame> keys, pframes;
+    // learned proposals of the key frames (8x8-tile classes with a net attached)
+    bool seeded = false;
+    uint16_t *x = nullptr;           // net inputs of one chunk: slots x NT x 64 pixels x 4 bf16
+    float4 *anchor = nullptr;        // slots x NT tile anchors
+    float *prop = nullptr;           // slots x NT x 5 proposals
 };
 
 }  // namespace
@@ -53,9 +60,44 @@ struct lcc_plan {
     int64_t launches = 0;            // kernel launches of one encode
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
+    lcc_net *net = nullptr;          // proposal net of the seeded key frames (not owned)
+    float skip_logit = 0.f;
+    // host-output path (lcc_plan_encode_host): one copy item per frame, in table order
+    struct CopyItem *d_items = nullptr;
+    unsigned long long *d_sizes = nullptr, *h_sizes = nullptr;   // h_sizes page-locked
+    int64_t items = 0;
+};
+
+// One frame of the host-output copy: its device stream and size, and the host buffer.
+struct CopyItem {
+    const uint8_t *src;
+    uint8_t *dst;
+    unsigned long long cap;
+    const unsigned long long *nbytes;
 };
 
 namespace {
+
+// Every frame's stream (its size read on the device) from its device buffer into the caller's
+// page-locked host buffer, 16-byte stores over the host link; frame f = blockIdx.y + 65535 *
+// blockIdx.z.  The sizes are gathered into `sizes` (table order) for one copy back.
+__global__ void __launch_bounds__(256) k_plan_copy_out(const CopyItem *items, long long nitems,
+                                                     unsigned long long *sizes) {
+    const long long f = blockIdx.y + 65535ll * blockIdx.z;
+    if (f >= nitems) return;
+    const CopyItem it = items[f];
+    const unsigned long long raw = *it.nbytes;
+    const unsigned long long nb = raw <= it.cap ? raw : 0ull;
+    if (blockIdx.x == 0 && threadIdx.x == 0) sizes[f] = raw;
+    const uint4 *src = reinterpret_cast<const uint4 *>(it.src);
+    uint4 *dst = reinterpret_cast<uint4 *>(it.dst);
+    const unsigned long long n16 = nb / 16;
+    for (unsigned long long i = blockIdx.x * 256ull + threadIdx.x; i < n16; i += gridDim.x * 256ull) dst[i] = src[i];
+    const unsigned long long tail = nb - n16 * 16;   // streams are whole 32-bit words
+    if (blockIdx.x == 0 && threadIdx.x < tail / 4)
+        reinterpret_cast<uint32_t *>(it.dst + n16 * 16)[threadIdx.x] =
+            reinterpret_cast<const uint32_t *>(it.src + n16 * 16)[threadIdx.x];
+}
 
 // Group g of a sequence covers frames [g*I, min((g+1)*I, nframes)); its key frame is the
 // group's middle frame start + floor(len/2) (Sec. III-C: K is the middle frame of the group).
@@ -117,12 +159,14 @@ lcc_status fill(lcc_plan *p, int32_t nseq, const lcc_seq_desc *seqs, bool check_
 }
 
 // Enqueue one class: its key frames chunk by chunk, then its P frames, each chunk binned into
-// slots 0..m-1 of the class context and encoded as one batch.
-lcc_status enqueue_class(PlanClass &pc, int64_t *launches) {
+// slots 0..m-1 of the class context and encoded as one batch.  Seeded key-frame chunks run the
+// net's input kernel on the binned slots and its inference between the binning and the fit.
+lcc_status enqueue_class(PlanClass &pc, lcc_net *net, float skip_logit, int64_t *launches) {
     lcc_ctx *c = pc.ctx;
     const int NT = c->g.NT;
     for (int kind = 0; kind < 2; kind++) {
         const std::vector<PlanFrame> &list = kind == 0 ? pc.keys : pc.pframes;
+        const bool seeded = kind == 0 && pc.seeded && net;
         for (size_t base = 0; base < list.size(); base += (size_t)c->slots) {
             const int m = (int)std::min<size_t>((size_t)c->slots, list.size() - base);
             int slots[kMaxBatch];
@@ -133,6 +177,7 @@ lcc_status enqueue_class(PlanClass &pc, int64_t *launches) {
             const float4 *kf[kMaxBatch];
             float4 *kfo[kMaxBatch];
             unsigned long long *nb[kMaxBatch];
+            const float *props[kMaxBatch];
             std::vector<double> poses((size_t)m * 16);
             for (int f = 0; f < m; f++) {
                 const PlanFrame &pf = list[base + f];
@@ -145,12 +190,24 @@ lcc_status enqueue_class(PlanClass &pc, int64_t *launches) {
                 kf[f] = tab;
                 kfo[f] = tab;
                 nb[f] = pf.nbytes;
+                props[f] = seeded ? pc.prop + (size_t)f * NT * 5 : nullptr;
                 memcpy(poses.data() + 16 * (size_t)f, pf.pose, sizeof(pf.pose));
             }
             lcc_status st = bin_frames(c, m, slots, pts, n);
             if (st != LCC_OK) return st;
+            if (seeded) {
+                int pi = prof_begin(c, 14);
+                st = net_inputs_slots(c, m, pc.x, pc.anchor);
+                prof_end(c, pi);
+                if (st != LCC_OK) return st;
+                pi = prof_begin(c, 15);
+                st = net_forward_on(net, pc.x, (int64_t)m * NT, pc.prop, c->stream);
+                prof_end(c, pi);
+                if (st != LCC_OK) return st;
+                *launches += 2;
+            }
             st = encode_batch(c, kind, m, slots, out, cap, kind ? poses.data() : nullptr, kind ? kf : nullptr,
-                              kind ? nullptr : kfo, nb);
+                              kind ? nullptr : kfo, nb, seeded ? props : nullptr, skip_logit);
             if (st != LCC_OK) return st;
             c->last_nframes = m;
             *launches += 1 + 3 + (c->g.lookahead > 0 ? 1 : 0) +
@@ -172,7 +229,7 @@ lcc_status enqueue(lcc_plan *p, cudaStream_t main) {
     for (auto &pc : p->cls) {
         if (forked && cudaStreamWaitEvent(pc.side, p->fork, 0) != cudaSuccess) return LCC_ERR_CUDA;
         pc.ctx->stream = forked ? pc.side : main;
-        st = enqueue_class(pc, &launches);
+        st = enqueue_class(pc, p->net, p->skip_logit, &launches);
         pc.ctx->stream = p->stream;
         if (forked && (cudaEventRecord(pc.done, pc.side) != cudaSuccess ||
                        cudaStreamWaitEvent(main, pc.done, 0) != cudaSuccess))
@@ -190,9 +247,15 @@ void release(lcc_plan *p) {
         if (pc.side) cudaStreamDestroy(pc.side);
         if (pc.done) cudaEventDestroy(pc.done);
         cudaFree(pc.tables);
+        cudaFree(pc.x);
+        cudaFree(pc.anchor);
+        cudaFree(pc.prop);
     }
     if (p->fork) cudaEventDestroy(p->fork);
     if (p->cap) cudaStreamDestroy(p->cap);
+    cudaFree(p->d_items);
+    cudaFree(p->d_sizes);
+    if (p->h_sizes) cudaFreeHost(p->h_sizes);
     delete p;
 }
 
@@ -253,6 +316,38 @@ lcc_status lcc_plan_update(lcc_plan *p, int32_t nseq, const lcc_seq_desc *seqs) 
     return lcc_plan_capture(p);
 }
 
+lcc_status lcc_plan_set_proposals(lcc_plan *p, lcc_net *net, float skip_logit) {
+    if (!p || (net && !(skip_logit == skip_logit))) return LCC_ERR_INVALID_ARG;
+    if (net) {
+        bool any = false;
+        for (const auto &pc : p->cls) any = any || (pc.ctx->g.th == 8 && pc.ctx->g.tw == 8);
+        if (!any) return LCC_ERR_UNSUPPORTED;
+        for (auto &pc : p->cls) {
+            if (pc.ctx->g.th != 8 || pc.ctx->g.tw != 8) continue;
+            if (!pc.x) {
+                const size_t tiles = (size_t)pc.ctx->slots * pc.ctx->g.NT;
+                if (cudaMalloc(&pc.x, tiles * 64 * 4 * sizeof(uint16_t)) != cudaSuccess ||
+                    cudaMalloc(&pc.anchor, tiles * sizeof(float4)) != cudaSuccess ||
+                    cudaMalloc(&pc.prop, tiles * 5 * sizeof(float)) != cudaSuccess) {
+                    cudaFree(pc.x);
+                    cudaFree(pc.anchor);
+                    cudaFree(pc.prop);
+                    pc.x = nullptr;
+                    pc.anchor = nullptr;
+                    pc.prop = nullptr;
+                    return LCC_ERR_CUDA;
+                }
+            }
+        }
+    }
+    for (auto &pc : p->cls) pc.seeded = net && pc.ctx->g.th == 8 && pc.ctx->g.tw == 8;
+    p->net = net;
+    p->skip_logit = skip_logit;
+    if (!p->exec) return LCC_OK;
+    // the captured graph no longer matches: re-record it and update the executable in place
+    return lcc_plan_capture(p);
+}
+
 lcc_status lcc_plan_encode(lcc_plan *p) {
     if (!p) return LCC_ERR_INVALID_ARG;
     return enqueue(p, p->stream);
@@ -301,7 +396,64 @@ lcc_status lcc_plan_sync(lcc_plan *p) {
         const lcc_status st = latched(pc.ctx);
         if (first == LCC_OK) first = st;
     }
+    if (p->net) {
+        const lcc_status st = net_latched(p->net);
+        if (first == LCC_OK) first = st;
+    }
     return first;
+}
+
+lcc_status lcc_plan_encode_host(lcc_plan *p, uint8_t *const *h_out, uint64_t *h_nbytes) {
+    if (!p || !h_out || !h_nbytes) return LCC_ERR_INVALID_ARG;
+    // copy items in table order (sequence by sequence, frame by frame)
+    std::vector<CopyItem> items;
+    items.reserve((size_t)p->frames);
+    std::vector<const PlanFrame *> order((size_t)p->frames, nullptr);
+    {
+        std::vector<int64_t> base(p->shape.size() + 1, 0);
+        for (size_t s = 0; s < p->shape.size(); s++) base[s + 1] = base[s] + p->shape[s].nframes;
+        for (const auto &pc : p->cls)
+            for (const auto *list : {&pc.keys, &pc.pframes})
+                for (const auto &pf : *list) order[(size_t)(base[pf.seq] + pf.frame)] = &pf;
+    }
+    for (int64_t f = 0; f < p->frames; f++) {
+        const PlanFrame *pf = order[(size_t)f];
+        if (!pf || !h_out[f]) return LCC_ERR_INVALID_ARG;
+        cudaPointerAttributes a;
+        if (cudaPointerGetAttributes(&a, h_out[f]) != cudaSuccess) {
+            cudaGetLastError();
+            return LCC_ERR_INVALID_ARG;
+        }
+        if (a.type != cudaMemoryTypeHost || !a.devicePointer || !aligned16(a.devicePointer))
+            return LCC_ERR_INVALID_ARG;   // page-locked, device-mapped, 16-byte aligned host memory only
+        items.push_back(CopyItem{pf->out, (uint8_t *)a.devicePointer, pf->cap, pf->nbytes});
+    }
+    if (p->items != p->frames) {
+        cudaFree(p->d_items);
+        cudaFree(p->d_sizes);
+        if (p->h_sizes) cudaFreeHost(p->h_sizes);
+        p->d_items = nullptr;
+        p->d_sizes = p->h_sizes = nullptr;
+        p->items = 0;
+        LCC_CUDA(cudaMalloc(&p->d_items, sizeof(CopyItem) * (size_t)p->frames));
+        LCC_CUDA(cudaMalloc(&p->d_sizes, sizeof(unsigned long long) * (size_t)p->frames));
+        LCC_CUDA(cudaMallocHost(&p->h_sizes, sizeof(unsigned long long) * (size_t)p->frames));
+        p->items = p->frames;
+    }
+    // the table is small (32 B per frame); it rides on the stream ahead of the encode
+    LCC_CUDA(cudaMemcpyAsync(p->d_items, items.data(), sizeof(CopyItem) * items.size(), cudaMemcpyHostToDevice,
+                             p->stream));
+    lcc_status st = p->exec ? lcc_plan_replay(p) : lcc_plan_encode(p);
+    if (st != LCC_OK) return st;
+    const long long nf = (long long)p->frames;
+    k_plan_copy_out<<<dim3(8, (unsigned)std::min<long long>(nf, 65535), (unsigned)((nf + 65534) / 65535)), 256, 0,
+                      p->stream>>>(p->d_items, nf, p->d_sizes);
+    LCC_CUDA(cudaGetLastError());
+    LCC_CUDA(cudaMemcpyAsync(p->h_sizes, p->d_sizes, sizeof(unsigned long long) * (size_t)nf,
+                             cudaMemcpyDeviceToHost, p->stream));
+    st = lcc_plan_sync(p);
+    memcpy(h_nbytes, p->h_sizes, sizeof(uint64_t) * (size_t)nf);
+    return st;
 }
 
 lcc_status lcc_plan_get_info(const lcc_plan *p, lcc_plan_info *out) {
@@ -313,6 +465,8 @@ lcc_status lcc_plan_get_info(const lcc_plan *p, lcc_plan_info *out) {
     out->launches = p->launches;
     out->classes = (int32_t)p->cls.size();
     out->captured = p->exec ? 1 : 0;
+    for (const auto &pc : p->cls)
+        if (pc.seeded && p->net) out->seeded_key_frames += (int64_t)pc.keys.size();
     size_t nodes = 0;
     if (p->graph && cudaGraphGetNodes(p->graph, nullptr, &nodes) != cudaSuccess) nodes = 0;
     out->graph_nodes = (int64_t)nodes;

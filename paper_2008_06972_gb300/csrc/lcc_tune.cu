@@ -104,18 +104,21 @@ extern "C" {
 
 lcc_status lcc_autotune(const lcc_sensor *sensor, const lcc_params *base, int32_t nframes, int32_t key_index,
                         const double *poses, const float *const *d_pts, const int64_t *n, int32_t reps,
-                        float max_err_m, float bytes_slack, void *cuda_stream, lcc_tune_result *results,
-                        int32_t cap, int32_t *nresults, lcc_params *best) {
+                        float max_err_m, float bytes_slack, uint32_t shapes, void *cuda_stream,
+                        lcc_tune_result *results, int32_t cap, int32_t *nresults, lcc_params *best) {
     if (!sensor || !base || !poses || !d_pts || !n || !best || nframes < 1 || nframes > kMaxBatch ||
         key_index < 0 || key_index >= nframes || reps < 1 || !(max_err_m > 0) || !(bytes_slack >= 0) ||
-        (cap > 0 && !results))
+        (cap > 0 && !results) || shapes > 15u)
         return LCC_ERR_INVALID_ARG;
     static const int kTiles[4][2] = {{4, 4}, {4, 8}, {8, 8}, {8, 16}};
     static const int kHorizon[3] = {8, 16, 32};
+    if (!shapes) shapes = 15u;
     std::vector<lcc_tune_result> all;
-    for (const auto &t : kTiles)
+    for (int ti = 0; ti < 4; ti++)
         for (int sched : {0, 3})
             for (int h = 0; h < (base->merge_runs ? 3 : 1); h++) {
+                if (!((shapes >> ti) & 1u)) continue;
+                const int *t = kTiles[ti];
                 lcc_params prm = *base;
                 prm.tile_h = t[0];
                 prm.tile_w = t[1];

@@ -58,7 +58,7 @@ class lcc_seq_desc(ctypes.Structure):
 class lcc_plan_info(ctypes.Structure):
     _fields_ = [("frames", ctypes.c_int64), ("key_frames", ctypes.c_int64), ("points", ctypes.c_int64),
                 ("launches", ctypes.c_int64), ("graph_nodes", ctypes.c_int64), ("classes", ctypes.c_int32),
-                ("captured", ctypes.c_int32)]
+                ("captured", ctypes.c_int32), ("seeded_key_frames", ctypes.c_int64)]
 
 
 class lcc_tune_result(ctypes.Structure):
@@ -76,7 +76,7 @@ assert TILE_INFO_DTYPE.itemsize == 64
 
 _lib = None
 KERNEL_NAMES = ("bin", "fit", "merge", "rounds", "pack", "decode_prep", "decode_px", "range_export", "lookbehind",
-                "temporal", "ent_build", "ent_layout", "ent_write", "ent_decode")
+                "temporal", "ent_build", "ent_layout", "ent_write", "ent_decode", "net_inputs", "net_fwd")
 
 
 def load(path: str = LIB_PATH):
@@ -133,14 +133,16 @@ def load(path: str = LIB_PATH):
         "lcc_net_train_step": (i32, [vp, vp, vp, i64, ctypes.c_float, i32, vp]),
         "lcc_plan_create": (i32, [vp, i32, vp, i32, vp]),
         "lcc_plan_update": (i32, [vp, i32, vp]),
+        "lcc_plan_set_proposals": (i32, [vp, vp, ctypes.c_float]),
         "lcc_plan_encode": (i32, [vp]),
         "lcc_plan_capture": (i32, [vp]),
         "lcc_plan_replay": (i32, [vp]),
         "lcc_plan_sync": (i32, [vp]),
+        "lcc_plan_encode_host": (i32, [vp, vp, vp]),
         "lcc_plan_get_info": (i32, [vp, vp]),
         "lcc_plan_destroy": (None, [vp]),
-        "lcc_autotune": (i32, [vp, vp, i32, i32, vp, vp, vp, i32, ctypes.c_float, ctypes.c_float, vp, vp, i32,
-                               vp, vp]),
+        "lcc_autotune": (i32, [vp, vp, i32, i32, vp, vp, vp, i32, ctypes.c_float, ctypes.c_float, ctypes.c_uint32,
+                               vp, vp, i32, vp, vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
@@ -159,7 +161,7 @@ def exported_symbols() -> list[str]:
             "lcc_tile_records", "lcc_set_profiling", "lcc_kernel_times", "lcc_kernel_timeline", "lcc_range_image_static", "lcc_net_num_params", "lcc_net_create", "lcc_net_destroy",
             "lcc_net_get_params", "lcc_net_set_params", "lcc_net_tile_inputs", "lcc_net_tile_inputs_batch", "lcc_net_forward", "lcc_net_sync", "lcc_net_gradient",
             "lcc_net_train_step", "lcc_selftest_bounded_wait", "lcc_plan_create", "lcc_plan_update",
-            "lcc_plan_encode", "lcc_plan_capture", "lcc_plan_replay", "lcc_plan_sync", "lcc_plan_get_info",
+            "lcc_plan_set_proposals", "lcc_plan_encode", "lcc_plan_capture", "lcc_plan_replay", "lcc_plan_sync", "lcc_plan_encode_host", "lcc_plan_get_info",
             "lcc_plan_destroy", "lcc_autotune"]
 
 
@@ -470,6 +472,12 @@ class Plan:
     def update(self, seqs: list):
         _check(self.lib.lcc_plan_update(self.h, len(seqs), self._descs(seqs)), "lcc_plan_update")
 
+    def set_proposals(self, net: "Net | None", skip_logit: float = 0.0):
+        """Seed the key frames of 8x8-tile classes with the net's proposals (None: plain)."""
+        self.net = net
+        _check(self.lib.lcc_plan_set_proposals(self.h, net.h if net is not None else None, skip_logit),
+               "lcc_plan_set_proposals")
+
     def encode(self):
         _check(self.lib.lcc_plan_encode(self.h), "lcc_plan_encode")
 
@@ -481,6 +489,15 @@ class Plan:
 
     def sync(self) -> int:
         return int(self.lib.lcc_plan_sync(self.h))
+
+    def encode_host(self, h_out) -> np.ndarray:
+        """lcc_plan_encode_host: h_out is a list of page-locked host buffers (numpy arrays or CPU
+        tensors), one per frame in table order; returns the stream sizes.  Synchronous."""
+        n = len(h_out)
+        sizes = np.zeros(n, np.uint64)
+        ptrs = _arr(ctypes.c_void_p, [_host_ptr(a) for a in h_out])
+        _check(self.lib.lcc_plan_encode_host(self.h, ptrs, sizes.ctypes.data), "lcc_plan_encode_host")
+        return sizes
 
     def info(self) -> dict:
         i = lcc_plan_info()
@@ -499,9 +516,13 @@ class Plan:
             pass
 
 
+TUNE_SHAPES = ((4, 4), (4, 8), (8, 8), (8, 16))
+
+
 def autotune(sensor_, base: lcc_params, key_index: int, poses, d_pts: list, n: list, reps: int = 3,
-             max_err_m: float = 0.02, bytes_slack: float = 0.05, stream=None):
-    """lcc_autotune: returns (best lcc_params, list of candidate dicts)."""
+             max_err_m: float = 0.02, bytes_slack: float = 0.05, stream=None, shapes=None):
+    """lcc_autotune: returns (best lcc_params, list of candidate dicts).  shapes: the tile shapes
+    to search (a subset of TUNE_SHAPES; None = all)."""
     lib = load()
     sn = sensor(sensor_) if not isinstance(sensor_, lcc_sensor) else sensor_
     poses = np.ascontiguousarray(poses, dtype=np.float64).reshape(-1)
@@ -509,9 +530,10 @@ def autotune(sensor_, base: lcc_params, key_index: int, poses, d_pts: list, n: l
     nres = ctypes.c_int32()
     best = lcc_params()
     sp = stream.cuda_stream if stream is not None and hasattr(stream, "cuda_stream") else stream
+    mask = 0 if shapes is None else sum(1 << TUNE_SHAPES.index(tuple(t)) for t in shapes)
     st = lib.lcc_autotune(ctypes.byref(sn), ctypes.byref(base), len(d_pts), key_index, poses.ctypes.data,
                           _arr(ctypes.c_void_p, [_ptr(x) for x in d_pts]), _arr(ctypes.c_int64, n), reps,
-                          max_err_m, bytes_slack, sp, res, 64, ctypes.byref(nres), ctypes.byref(best))
+                          max_err_m, bytes_slack, mask, sp, res, 64, ctypes.byref(nres), ctypes.byref(best))
     _check(st, "lcc_autotune")
     rows = [{k: getattr(res[i], k) for k, _ in lcc_tune_result._fields_ if k != "reserved"}
             for i in range(min(nres.value, 64))]

@@ -17,6 +17,9 @@ sequence.  Workload presets mirror the five benchmark configurations:
   resolutions 16x1024, 32x1024, 64x2048, 128x2048 (elevation -15..+15 deg),
   the frame-1 scene family and noise, the cfg2 ego motion, key-frame groups of
   10 frames with the key frame in the middle of each group.
+* ``batch_cfg5``  32 sequences of 100 frames of 128x4096 with the
+  ``sequence_cfg5`` scene family, motion and pose noise, key-frame groups of
+  10 frames; frames are rendered straight into one caller-owned buffer.
 
 Seeds follow ``seed = 1000003*config + 1009*sequence + frame``.
 """
@@ -121,6 +124,26 @@ class Scene:
         if n < 0:
             raise RuntimeError("render failed")
         return out[:n].copy()
+
+    def render_into(self, sensor: Sensor, out: np.ndarray, R=None, t=None, sigma=0.02, dropout=0.0, clutter=0.0,
+                    seed=0) -> int:
+        """The same frame as render(), written into out (float32, C-contiguous, at least
+        rows*cols x 4); returns the number of points."""
+        lib = _load()
+        R = np.eye(3) if R is None else np.asarray(R, dtype=np.float64)
+        t = np.zeros(3) if t is None else np.asarray(t, dtype=np.float64)
+        R = np.ascontiguousarray(R, dtype=np.float64).reshape(9)
+        t = np.ascontiguousarray(t, dtype=np.float64).reshape(3)
+        cap = sensor.rows * sensor.cols
+        if out.dtype != np.float32 or not out.flags.c_contiguous or out.size < 4 * cap:
+            raise ValueError("out must be a contiguous float32 array of at least rows*cols x 4")
+        n = lib.syn_render(ctypes.cast(self._objs, ctypes.c_void_p), self.n, sensor.rows, sensor.cols,
+                           sensor.elev_min_deg, sensor.elev_max_deg, sensor.max_range_m,
+                           R.ctypes.data, t.ctypes.data, sigma, dropout, clutter, seed,
+                           out.ctypes.data, cap)
+        if n < 0:
+            raise RuntimeError("render failed")
+        return int(n)
 
 
 def yaw_matrix(psi: float) -> np.ndarray:
@@ -316,18 +339,31 @@ class GroupedSequence:
 
 def grouped_sequence(sensor: Sensor, sensor_class: int, n_frames: int, seed: int, key_interval: int,
                      n_walls=4, n_boxes=6, n_poles=10, step_m=1.0, yaw_deg=0.5, sigma=0.02, dropout=0.05,
-                     clutter=0.0, pool=None) -> GroupedSequence:
+                     clutter=0.0, pool=None, enclose=True, pose_noise=None, out=None) -> GroupedSequence:
+    """A sequence in key-frame groups of key_interval frames (key = each group's middle frame).
+    pose_noise (sigma_t m, sigma_rot deg) perturbs every P frame's pose as perturb_pose does.
+    With `out` (float32, n_frames x rows*cols x 4) frame f is rendered into out[f] and the
+    sequence's frames are views of it."""
     world = ego_poses(n_frames, step_m, yaw_deg)
-    scene = Scene(seed, n_walls, n_boxes, n_poles, path_len=step_m * max(n_frames - 1, 0), enclose=True)
+    scene = Scene(seed, n_walls, n_boxes, n_poles, path_len=step_m * max(n_frames - 1, 0), enclose=enclose)
 
     def one(f):
         Rw, tw = world[f]
-        return scene.render(sensor, Rw, tw, sigma=sigma, dropout=dropout, clutter=clutter, seed=seed * 131 + f)
+        if out is None:
+            return scene.render(sensor, Rw, tw, sigma=sigma, dropout=dropout, clutter=clutter, seed=seed * 131 + f)
+        n = scene.render_into(sensor, out[f], Rw, tw, sigma=sigma, dropout=dropout, clutter=clutter,
+                              seed=seed * 131 + f)
+        return out[f, :n]
 
     frames = list(pool.map(one, range(n_frames))) if pool else [one(f) for f in range(n_frames)]
-    poses = np.stack([relative_pose(world[f], world[group_key(f, n_frames, key_interval)])
-                      for f in range(n_frames)])
-    return GroupedSequence(sensor, sensor_class, frames, key_interval, poses)
+    poses = []
+    for f in range(n_frames):
+        k = group_key(f, n_frames, key_interval)
+        M = relative_pose(world[f], world[k])
+        if pose_noise is not None and f != k:
+            M = perturb_pose(M, pose_noise[0], pose_noise[1], seed * 7 + f)
+        poses.append(M)
+    return GroupedSequence(sensor, sensor_class, frames, key_interval, np.stack(poses))
 
 
 def batch_cfg3(n_seq: int = 64, min_len: int = 5, max_len: int = 40, key_interval: int = 10,
@@ -345,3 +381,31 @@ def batch_cfg3(n_seq: int = 64, min_len: int = 5, max_len: int = 40, key_interva
     with cf.ThreadPoolExecutor(threads) as pool:
         return [grouped_sequence(CFG3_SENSORS[int(c)], int(c), int(L), config_seed(3, i, 0), key_interval,
                                  pool=pool) for i, (L, c) in enumerate(zip(lens, cls))]
+
+
+CFG5_FRAMES, CFG5_SEQUENCES, CFG5_KEY_INTERVAL = 100, 32, 10
+
+
+def sequence_cfg5_grouped(sequence_id: int, n_frames: int = CFG5_FRAMES, key_interval: int = CFG5_KEY_INTERVAL,
+                          out=None, pool=None) -> GroupedSequence:
+    """One sequence of the large batched workload: 128x4096 frames, the sequence_cfg5 scene family
+    (8 walls, 12 boxes, 20 poles along the path, 5% clutter, sigma 2 cm), 1.5 m and 1 deg per frame,
+    poses perturbed by 1 cm / 0.05 deg, key-frame groups of key_interval frames."""
+    return grouped_sequence(CFG5_SENSOR, 0, n_frames, config_seed(5, sequence_id, 0), key_interval, n_walls=8,
+                            n_boxes=12, n_poles=20, step_m=1.5, yaw_deg=1.0, sigma=0.02, dropout=0.0, clutter=0.05,
+                            pool=pool, enclose=False, pose_noise=(0.01, 0.05), out=out)
+
+
+def batch_cfg5(out: np.ndarray, n_seq: int = CFG5_SEQUENCES, n_frames: int = CFG5_FRAMES,
+               key_interval: int = CFG5_KEY_INTERVAL, first: int = 0, threads: int = 0) -> list:
+    """The large batched workload: n_seq sequences (ids first..first+n_seq-1) of n_frames 128x4096
+    frames each, rendered in parallel threads into out, a float32 array of shape
+    (n_seq * n_frames, 128 * 4096, 4) (sequence i's frame f in out[i * n_frames + f])."""
+    import concurrent.futures as cf
+    npx = CFG5_SENSOR.rows * CFG5_SENSOR.cols
+    if out.shape != (n_seq * n_frames, npx, 4) or out.dtype != np.float32:
+        raise ValueError("out must be float32 of shape (n_seq * n_frames, rows * cols, 4)")
+    threads = threads or min(32, os.cpu_count() or 4)
+    with cf.ThreadPoolExecutor(threads) as pool:
+        return [sequence_cfg5_grouped(first + i, n_frames, key_interval, out=out[i * n_frames:(i + 1) * n_frames],
+                                      pool=pool) for i in range(n_seq)]
