@@ -428,9 +428,10 @@ typedef struct lcc_seq_desc {
     int32_t key_interval;     /* frames per key-frame group, >= 1 */
     int32_t reserved;
     const double *poses;      /* host, nframes x 16 */
-    const float *const *d_pts;/* host array of nframes device pointers to float4 (x, y, z, unused), 16-B aligned */
+    const float *const *d_pts;/* host array of nframes pointers to float4 (x, y, z, unused), 16-B aligned: device
+                                 memory, or page-locked host memory (read in place over the host link) */
     const int64_t *n;         /* host array: points per frame */
-    uint8_t *const *d_out;    /* host array of nframes device output buffers, 16-B aligned */
+    uint8_t *const *d_out;    /* host array of nframes device output buffers (device memory), 16-B aligned */
     const uint64_t *cap;      /* host array: capacity of each output buffer (bytes) */
     uint64_t *d_nbytes;       /* DEVICE array of nframes: stream size of each frame, written by the encode */
 } lcc_seq_desc;
@@ -487,6 +488,10 @@ lcc_status lcc_plan_sync(lcc_plan *plan);
  * page-locked host memory. */
 lcc_status lcc_plan_encode_host(lcc_plan *plan, uint8_t *const *h_out, uint64_t *h_nbytes);
 lcc_status lcc_plan_get_info(const lcc_plan *plan, lcc_plan_info *out);
+/* Statistics of frame `frame` of sequence `seq` of the last encode or replay, or (seq = -1) their
+ * sum over every frame of the table (counts add up; bytes is the total stream size).  Waits for
+ * the stream.  Synchronous. */
+lcc_status lcc_plan_stats(lcc_plan *plan, int32_t seq, int32_t frame, lcc_stats *out);
 void lcc_plan_destroy(lcc_plan *plan);
 
 /* ---- Autotuner ----

@@ -113,6 +113,25 @@ int bits_for(int max_value) {
 
 bool aligned16(const void *p) { return ((uintptr_t)p & 15u) == 0; }
 
+void public_stats(const DevStats &d, lcc_stats *out) {
+    out->points_in = (int64_t)d.points_in;
+    out->points_invalid = (int64_t)d.invalid;
+    out->points_fov = (int64_t)d.fov;
+    out->points_binned = (int64_t)d.binned;
+    out->pixels_valid = (int64_t)d.valid;
+    out->tiles_empty = (int64_t)d.empty;
+    out->tiles_raw = (int64_t)d.raw_tiles;
+    out->tiles_run_start = (int64_t)d.run_start;
+    out->tiles_run_cont = (int64_t)d.run_cont;
+    out->tiles_temporal = (int64_t)d.temporal;
+    for (int q = 0; q < 8; q++) out->fit_rounds[q] = (int64_t)d.rounds[q];
+    out->tiles_borderline = (int64_t)d.borderline;
+    out->cand = (int64_t)d.cand;
+    out->fitted = (int64_t)d.fitted;
+    out->raw = (int64_t)d.raw;
+    out->bytes = d.bytes;
+}
+
 lcc_status latched(lcc_ctx *c) {
     uint32_t e = 0;
     if (cudaMemcpy(&e, c->s.err, 4, cudaMemcpyDeviceToHost) != cudaSuccess) return LCC_ERR_CUDA;
@@ -929,22 +948,7 @@ lcc_status lcc_last_stats(lcc_ctx *c, int32_t frame, lcc_stats *out) {
     if (cudaStreamSynchronize(c->stream) != cudaSuccess) return LCC_ERR_CUDA;
     DevStats d;
     LCC_CUDA(cudaMemcpy(&d, c->s.stats + frame, sizeof(d), cudaMemcpyDeviceToHost));
-    out->points_in = (int64_t)d.points_in;
-    out->points_invalid = (int64_t)d.invalid;
-    out->points_fov = (int64_t)d.fov;
-    out->points_binned = (int64_t)d.binned;
-    out->pixels_valid = (int64_t)d.valid;
-    out->tiles_empty = (int64_t)d.empty;
-    out->tiles_raw = (int64_t)d.raw_tiles;
-    out->tiles_run_start = (int64_t)d.run_start;
-    out->tiles_run_cont = (int64_t)d.run_cont;
-    out->tiles_temporal = (int64_t)d.temporal;
-    for (int q = 0; q < 8; q++) out->fit_rounds[q] = (int64_t)d.rounds[q];
-    out->tiles_borderline = (int64_t)d.borderline;
-    out->cand = (int64_t)d.cand;
-    out->fitted = (int64_t)d.fitted;
-    out->raw = (int64_t)d.raw;
-    out->bytes = d.bytes;
+    public_stats(d, out);
     return LCC_OK;
 }
 

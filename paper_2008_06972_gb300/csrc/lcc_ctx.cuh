@@ -85,6 +85,8 @@ namespace api {
 int prof_begin(lcc_ctx *c, int name, int count = 1);
 void prof_end(lcc_ctx *c, int idx);
 bool aligned16(const void *p);
+// The device counters of one frame as the public statistics record.
+void public_stats(const DevStats &d, lcc_stats *out);
 // Reads and clears the device error word (synchronous).
 lcc_status latched(lcc_ctx *c);
 // Bin frames d_pts[f] into slots[f] (their stats are reset first).

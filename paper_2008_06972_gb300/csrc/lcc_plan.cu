@@ -45,6 +45,7 @@ struct PlanClass {
     uint16_t *x = nullptr;           // net inputs of one chunk: slots x NT x 64 pixels x 4 bf16
     float4 *anchor = nullptr;        // slots x NT tile anchors
     float *prop = nullptr;           // slots x NT x 5 proposals
+    DevStats *stats = nullptr;       // per frame of the last encode, in enqueue order (keys, then P frames)
 };
 
 }  // namespace
@@ -108,6 +109,30 @@ int key_of(int frame, int nframes, int interval, int *group) {
     return start + len / 2;
 }
 
+// Address the device reads a frame's points at: device (or managed) memory as given, page-locked
+// host memory through its device view (read in place over the host link); NULL for host memory
+// the device cannot address.
+const float *points_view(const float *p) {
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    if (a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged) return p;
+    if (a.type == cudaMemoryTypeHost && a.devicePointer) return static_cast<const float *>(a.devicePointer);
+    return nullptr;
+}
+
+// Output buffers are written with device atomics: device memory only.
+bool device_memory(const void *p) {
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice;
+}
+
 // Builds the frame lists of every class from the sequence table; the plan is left untouched
 // unless the whole table is valid (and, for check_only, has the plan's group structure).
 lcc_status fill(lcc_plan *p, int32_t nseq, const lcc_seq_desc *seqs, bool check_only) {
@@ -122,8 +147,10 @@ lcc_status fill(lcc_plan *p, int32_t nseq, const lcc_seq_desc *seqs, bool check_
             return LCC_ERR_INVALID_ARG;
         for (int f = 0; f < d.nframes; f++) {
             if (d.n[f] < 0 || d.n[f] > (int64_t)1 << 31) return LCC_ERR_INVALID_ARG;
-            if (d.n[f] > 0 && (!d.d_pts[f] || !aligned16(d.d_pts[f]))) return LCC_ERR_INVALID_ARG;
-            if (!d.d_out[f] || !aligned16(d.d_out[f]) || d.cap[f] < (uint64_t)kHeaderBytes)
+            const float *pts = d.n[f] > 0 && d.d_pts[f] ? points_view(d.d_pts[f]) : nullptr;
+            if (d.n[f] > 0 && (!pts || !aligned16(pts))) return LCC_ERR_INVALID_ARG;
+            if (!d.d_out[f] || !aligned16(d.d_out[f]) || d.cap[f] < (uint64_t)kHeaderBytes ||
+                !device_memory(d.d_out[f]))
                 return LCC_ERR_INVALID_ARG;
             int grp = 0;
             const int k = key_of(f, d.nframes, d.key_interval, &grp);
@@ -131,7 +158,7 @@ lcc_status fill(lcc_plan *p, int32_t nseq, const lcc_seq_desc *seqs, bool check_
             pf.seq = s;
             pf.frame = f;
             pf.table = group_base[d.ctx] + grp;
-            pf.pts = d.d_pts[f];
+            pf.pts = pts;
             pf.n = d.n[f];
             pf.out = d.d_out[f];
             pf.cap = d.cap[f];
@@ -209,6 +236,9 @@ lcc_status enqueue_class(PlanClass &pc, lcc_net *net, float skip_logit, int64_t 
             st = encode_batch(c, kind, m, slots, out, cap, kind ? poses.data() : nullptr, kind ? kf : nullptr,
                               kind ? nullptr : kfo, nb, seeded ? props : nullptr, skip_logit);
             if (st != LCC_OK) return st;
+            // the chunk's counters (reset by the next chunk's binning) into the plan's per-frame record
+            LCC_CUDA(cudaMemcpyAsync(pc.stats + (kind ? pc.keys.size() : 0) + base, c->s.stats, sizeof(DevStats) * m,
+                                     cudaMemcpyDeviceToDevice, c->stream));
             c->last_nframes = m;
             *launches += 1 + 3 + (c->g.lookahead > 0 ? 1 : 0) +
                          (c->g.schedule == 3 ? 1
@@ -250,6 +280,7 @@ void release(lcc_plan *p) {
         cudaFree(pc.x);
         cudaFree(pc.anchor);
         cudaFree(pc.prop);
+        cudaFree(pc.stats);
     }
     if (p->fork) cudaEventDestroy(p->fork);
     if (p->cap) cudaStreamDestroy(p->cap);
@@ -290,6 +321,9 @@ lcc_status lcc_plan_create(lcc_plan **out, int32_t nctx, lcc_ctx *const *ctxs, i
                        cudaSuccess;
         ok = ok && cudaMemset(pc.tables, 0, sizeof(float4) * (size_t)std::max(pc.ngroups, 1) * pc.ctx->g.NT) ==
                        cudaSuccess;
+        const size_t nfr = std::max<size_t>(pc.keys.size() + pc.pframes.size(), 1);
+        ok = ok && cudaMalloc(&pc.stats, sizeof(DevStats) * nfr) == cudaSuccess &&
+             cudaMemset(pc.stats, 0, sizeof(DevStats) * nfr) == cudaSuccess;
         if (nctx > 1) {
             ok = ok && cudaStreamCreateWithFlags(&pc.side, cudaStreamNonBlocking) == cudaSuccess;
             ok = ok && cudaEventCreateWithFlags(&pc.done, cudaEventDisableTiming) == cudaSuccess;
@@ -454,6 +488,32 @@ lcc_status lcc_plan_encode_host(lcc_plan *p, uint8_t *const *h_out, uint64_t *h_
     st = lcc_plan_sync(p);
     memcpy(h_nbytes, p->h_sizes, sizeof(uint64_t) * (size_t)nf);
     return st;
+}
+
+lcc_status lcc_plan_stats(lcc_plan *p, int32_t seq, int32_t frame, lcc_stats *out) {
+    if (!p || !out || seq >= (int32_t)p->shape.size() || (seq >= 0 && (frame < 0 || frame >= p->shape[seq].nframes)))
+        return LCC_ERR_INVALID_ARG;
+    LCC_CUDA(cudaStreamSynchronize(p->stream));
+    DevStats sum;
+    memset(&sum, 0, sizeof(sum));
+    bool found = false;
+    for (const auto &pc : p->cls) {
+        const size_t nk = pc.keys.size(), n = nk + pc.pframes.size();
+        if (!n) continue;
+        std::vector<DevStats> h(n);
+        LCC_CUDA(cudaMemcpy(h.data(), pc.stats, sizeof(DevStats) * n, cudaMemcpyDeviceToHost));
+        for (size_t i = 0; i < n; i++) {
+            const PlanFrame &pf = i < nk ? pc.keys[i] : pc.pframes[i - nk];
+            if (seq >= 0 && (pf.seq != seq || pf.frame != frame)) continue;
+            const unsigned long long *a = reinterpret_cast<const unsigned long long *>(&h[i]);
+            unsigned long long *b = reinterpret_cast<unsigned long long *>(&sum);
+            for (size_t w = 0; w < sizeof(DevStats) / sizeof(unsigned long long); w++) b[w] += a[w];
+            found = true;
+        }
+    }
+    if (!found && seq >= 0) return LCC_ERR_INVALID_ARG;
+    public_stats(sum, out);
+    return LCC_OK;
 }
 
 lcc_status lcc_plan_get_info(const lcc_plan *p, lcc_plan_info *out) {

@@ -140,6 +140,7 @@ def load(path: str = LIB_PATH):
         "lcc_plan_sync": (i32, [vp]),
         "lcc_plan_encode_host": (i32, [vp, vp, vp]),
         "lcc_plan_get_info": (i32, [vp, vp]),
+        "lcc_plan_stats": (i32, [vp, i32, i32, vp]),
         "lcc_plan_destroy": (None, [vp]),
         "lcc_autotune": (i32, [vp, vp, i32, i32, vp, vp, vp, i32, ctypes.c_float, ctypes.c_float, ctypes.c_uint32,
                                vp, vp, i32, vp, vp]),
@@ -161,7 +162,7 @@ def exported_symbols() -> list[str]:
             "lcc_tile_records", "lcc_set_profiling", "lcc_kernel_times", "lcc_kernel_timeline", "lcc_range_image_static", "lcc_net_num_params", "lcc_net_create", "lcc_net_destroy",
             "lcc_net_get_params", "lcc_net_set_params", "lcc_net_tile_inputs", "lcc_net_tile_inputs_batch", "lcc_net_forward", "lcc_net_sync", "lcc_net_gradient",
             "lcc_net_train_step", "lcc_selftest_bounded_wait", "lcc_plan_create", "lcc_plan_update",
-            "lcc_plan_set_proposals", "lcc_plan_encode", "lcc_plan_capture", "lcc_plan_replay", "lcc_plan_sync", "lcc_plan_encode_host", "lcc_plan_get_info",
+            "lcc_plan_set_proposals", "lcc_plan_encode", "lcc_plan_capture", "lcc_plan_replay", "lcc_plan_sync", "lcc_plan_encode_host", "lcc_plan_get_info", "lcc_plan_stats",
             "lcc_plan_destroy", "lcc_autotune"]
 
 
@@ -503,6 +504,14 @@ class Plan:
         i = lcc_plan_info()
         _check(self.lib.lcc_plan_get_info(self.h, ctypes.byref(i)), "lcc_plan_get_info")
         return {n: getattr(i, n) for n, _ in lcc_plan_info._fields_}
+
+    def stats(self, seq: int = -1, frame: int = 0) -> dict:
+        """lcc_plan_stats: one frame's statistics of the last encode, or (seq=-1) their sum."""
+        st = lcc_stats()
+        _check(self.lib.lcc_plan_stats(self.h, seq, frame, ctypes.byref(st)), "lcc_plan_stats")
+        out = {n: getattr(st, n) for n, _ in lcc_stats._fields_}
+        out["fit_rounds"] = list(st.fit_rounds)
+        return out
 
     def close(self):
         if getattr(self, "h", None):

@@ -339,16 +339,19 @@ class GroupedSequence:
 
 def grouped_sequence(sensor: Sensor, sensor_class: int, n_frames: int, seed: int, key_interval: int,
                      n_walls=4, n_boxes=6, n_poles=10, step_m=1.0, yaw_deg=0.5, sigma=0.02, dropout=0.05,
-                     clutter=0.0, pool=None, enclose=True, pose_noise=None, out=None) -> GroupedSequence:
+                     clutter=0.0, pool=None, enclose=True, pose_noise=None, out=None, only=None) -> GroupedSequence:
     """A sequence in key-frame groups of key_interval frames (key = each group's middle frame).
     pose_noise (sigma_t m, sigma_rot deg) perturbs every P frame's pose as perturb_pose does.
     With `out` (float32, n_frames x rows*cols x 4) frame f is rendered into out[f] and the
-    sequence's frames are views of it."""
+    sequence's frames are views of it.  With `only` (frame indices) just those frames are
+    rendered (the others are empty); poses are given for every frame."""
     world = ego_poses(n_frames, step_m, yaw_deg)
     scene = Scene(seed, n_walls, n_boxes, n_poles, path_len=step_m * max(n_frames - 1, 0), enclose=enclose)
 
     def one(f):
         Rw, tw = world[f]
+        if only is not None and f not in only:
+            return np.zeros((0, 4), np.float32)
         if out is None:
             return scene.render(sensor, Rw, tw, sigma=sigma, dropout=dropout, clutter=clutter, seed=seed * 131 + f)
         n = scene.render_into(sensor, out[f], Rw, tw, sigma=sigma, dropout=dropout, clutter=clutter,
@@ -387,13 +390,13 @@ CFG5_FRAMES, CFG5_SEQUENCES, CFG5_KEY_INTERVAL = 100, 32, 10
 
 
 def sequence_cfg5_grouped(sequence_id: int, n_frames: int = CFG5_FRAMES, key_interval: int = CFG5_KEY_INTERVAL,
-                          out=None, pool=None) -> GroupedSequence:
+                          out=None, pool=None, only=None) -> GroupedSequence:
     """One sequence of the large batched workload: 128x4096 frames, the sequence_cfg5 scene family
     (8 walls, 12 boxes, 20 poles along the path, 5% clutter, sigma 2 cm), 1.5 m and 1 deg per frame,
     poses perturbed by 1 cm / 0.05 deg, key-frame groups of key_interval frames."""
     return grouped_sequence(CFG5_SENSOR, 0, n_frames, config_seed(5, sequence_id, 0), key_interval, n_walls=8,
                             n_boxes=12, n_poles=20, step_m=1.5, yaw_deg=1.0, sigma=0.02, dropout=0.0, clutter=0.05,
-                            pool=pool, enclose=False, pose_noise=(0.01, 0.05), out=out)
+                            pool=pool, enclose=False, pose_noise=(0.01, 0.05), out=out, only=only)
 
 
 def batch_cfg5(out: np.ndarray, n_seq: int = CFG5_SEQUENCES, n_frames: int = CFG5_FRAMES,
