@@ -1,20 +1,23 @@
-"""Throughput of the spatio-temporal LiDAR encoder on one synthetic HDL-64E sequence.
+"""Throughput of the spatio-temporal LiDAR encoder on the large batched workload.
 
-Workload (one step): a 10-frame sequence of 64x2048 range images (about 1.3 M
-points), the middle frame spatially encoded as the key frame and the nine
-others temporally + spatially encoded against it (Sec. III), tiles 4x4,
-threshold 0.05 m, quantisation 0.02 m (max decode error 0.01 m <= 2 cm).
-Inputs are resident in HBM; L2 is flushed (256 MiB write) between timed steps
-and the flush is outside the per-step CUDA-event timing.
+Headline workload (one step): 32 sequences of 100 frames of 128x4096 range images (about 1.07 G
+points, 17 GB of float4 input resident in HBM), key-frame groups of 10 frames with the middle
+frame as key frame (Sec. III-D), 1.5 m and 1 deg of ego motion per frame, poses perturbed by
+1 cm / 0.05 deg, twice the frame-1 scene density with 5% clutter.  One batched plan over the whole
+table is recorded as a CUDA graph and replayed once per step; its tiles are autotuned among the
+shapes the proposal net takes (8x8), and the net (trained on the GPU beforehand on frames of other
+sequences, labelled by the plain encoder) seeds the key frames' fits.  The plain plan (tiles
+autotuned over every shape, no net) is timed on the same inputs in the same run.  Threshold
+0.05 m, quantisation 0.02 m: max decode error 0.01 m <= 2 cm, checked on every frame.
 
-Prints one JSON line.  Besides the headline sequence it carries two sections:
-"batched" (64 uneven sequences of four resolutions in one plan replayed as a
-CUDA graph, against one call per key-frame group) and "learned" (the proposal
-net trained on the GPU, then the seeded encode against the plain one on
-held-out 64x2048 frames with 8x8 tiles).  --impl reference times the CPU
-oracle (plain C, one core) on a bounded sample of the headline workload.
-Multi-GPU: one process per GPU (torchrun); each rank encodes its own sequence
-(no data-path collective; weak scaling); timing is the max over ranks.
+The JSON line also carries: the oracle on the host cores over a sample of the same workload
+(cpu_baseline), the end-to-end figure through lcc_plan_encode_host (page-locked host inputs read
+in place, streams copied to page-locked host buffers), the dominant kernel's roofline, and
+sections: "hdl64_sequence" (one 10-frame 64x2048 sequence per call, with decode, entropy, sweep
+and IMU rows), "batched" (64 uneven sequences of four resolutions), "learned" (the proposal net on
+64x2048 key frames).  --impl reference times the oracle on the headline workload.
+Multi-GPU: one process per GPU (torchrun); each rank encodes its own 32 sequences (no data-path
+collective; weak scaling); timing is the max over ranks.
 """
 from __future__ import annotations
 
@@ -33,7 +36,16 @@ sys.path.insert(0, ROOT)
 
 METRIC = "Mpoints/s encoded at ≤2 cm max error: plain vs batched+learned, % HBM roofline"
 WORKLOAD = "HDL-64E sequence: 10 frames of 64x2048 (1 key frame + 9 P-frames), tiles 4x4, thr 0.05 m, q 0.02 m"
+CFG5_WORKLOAD = ("large batched + learned: 32 sequences x 100 frames of 128x4096, key-frame groups of 10, "
+                 "1.5 m + 1 deg/frame, poses perturbed 1 cm / 0.05 deg, 2x frame-1 scene density, 5% clutter; "
+                 "one plan replayed as a CUDA graph, tiles autotuned among 8x8 + learned proposal on the key frames")
 UNIT = "Mpoints/s"
+
+
+def cfg5_config(args) -> dict:
+    return {"workload": CFG5_WORKLOAD, "sequences": args.cfg5_seqs, "frames_per_sequence": args.cfg5_frames,
+            "key_interval": 10, "sensor": "128x4096, elevation -15..+15 deg, 80 m", "thr_m": args.thr, "q_m": 0.02,
+            "l2": "inputs (about 17 GB) larger than L2: no flush"}
 
 
 def parse():
@@ -59,6 +71,13 @@ def parse():
                     "({rank} is replaced by the rank); default: a file under /tmp")
     ap.add_argument("--train-steps", type=int, default=300)
     ap.add_argument("--train-seqs", type=int, default=6)
+    ap.add_argument("--cfg5-seqs", type=int, default=32, help="sequences of the headline workload (per rank)")
+    ap.add_argument("--cfg5-frames", type=int, default=100, help="frames per sequence of the headline workload")
+    ap.add_argument("--cfg5-train-frames", type=int, default=64,
+                    help="128x4096 frames (of other sequences) the headline's net is trained on")
+    ap.add_argument("--cfg5-train-steps", type=int, default=600)
+    ap.add_argument("--cpu-steps", type=int, default=10, help="oracle frames per core for cpu_baseline")
+    ap.add_argument("--no-hdl64", action="store_true", help="skip the single-sequence HDL-64E section")
     return ap.parse_args()
 
 
@@ -122,9 +141,28 @@ def oracle_all_cores(seq, th, tw, thr, seconds, pool=None):
     return pts * nseq / wall / 1e6, nseq, wall, cores
 
 
+TRAFFIC_FILE_CFG5 = os.path.join(ROOT, "profiles", "dram_traffic_cfg5_plan.txt")
+
+
+def measured_traffic_cfg5(kernel: str):
+    """DRAM bytes per launch of a headline-plan kernel from the committed ncu summary (scaled to a
+    full launch as that file states), or None when the kernel's sources changed since."""
+    if kernel not in KERNEL_SOURCES:
+        return None
+    try:
+        for line in open(TRAFFIC_FILE_CFG5):
+            f = line.split()
+            if len(f) == 3 and f[0] == kernel and not line.startswith("#"):
+                return float(f[1]) if f[2] == source_digest(kernel) else None
+    except OSError:
+        pass
+    return None
+
+
 KERNEL_SOURCES = {"bin": ("k_bin.cu",), "fit": ("k_fit.cu",), "rounds": ("k_fit.cu",), "lookbehind": ("k_fit.cu",),
                   "temporal": ("k_fit.cu",),
-                  "merge": ("k_merge.cu", "scan_frame.cuh"), "pack": ("k_pack.cu",)}
+                  "merge": ("k_merge.cu", "scan_frame.cuh"), "pack": ("k_pack.cu",), "net_inputs": ("k_net.cu",),
+                  "net_fwd": ("k_net.cu",)}
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "dram_traffic_hdl64_sequence.txt")
 
 
@@ -211,32 +249,142 @@ class Clocks:
                 "reasons": reasons, "samples": len(rows)}
 
 
+def _oracle_core(conn, seq_id, learned, thr, n_frames, key_interval):
+    """One host core: the oracle (as it stands) encodes the frames of its own key-frame groups of
+    the large batched workload (sequence seq_id), one frame per request, key frame first.  The key
+    frame takes the learned path when `learned` (the oracle net's forward on every 8x8 tile, with
+    its own seeded initial weights, then the seeded fit) and the plain fit otherwise; P frames are
+    encoded against it.  Replies (points, seconds of oracle work, stream bytes).  Rendering the
+    next group happens between requests and is not part of the reported seconds."""
+    import oracle as O
+    from oracle import net as N
+    import synth
+    O.build()
+    s = O.sensor(synth.CFG5_SENSOR)
+    p = O.params(8, 8, thr, 0.02)
+    theta = N.init_params(7)
+    beams = O.beams(s)
+    skip = math.log(0.05 / 0.95)
+    ngroups = (n_frames + key_interval - 1) // key_interval
+
+    def load(g):
+        f0 = g * key_interval
+        f1 = min(f0 + key_interval, n_frames)
+        q = synth.sequence_cfg5_grouped(seq_id, n_frames, key_interval, only=set(range(f0, f1)))
+        k = synth.group_key(f0, n_frames, key_interval)
+        return q, [k] + [f for f in range(f0, f1) if f != k]
+
+    g, j = 0, 0
+    q, order = load(0)
+    kft = None
+    while True:
+        msg = conn.recv()
+        if msg is None:
+            break
+        f = order[j]
+        pts = q.frames[f]
+        t0 = time.perf_counter()
+        if j == 0:
+            rng, _, _ = O.range_image(s, pts)
+            if learned:
+                X, _, _ = N.tile_inputs(rng, beams)
+                prop = np.concatenate([N.forward(theta, X[a:a + 1024])[0] for a in range(0, len(X), 1024)])
+                fits = O.fit_tiles_seeded(s, p, rng, prop.astype(np.float32), skip)
+            else:
+                fits = O.fit_tiles(s, p, rng)
+            bits, kft, _ = O.pack(s, p, 0, rng, fits["plane"], (fits["status"] == O.FIT_OK).astype(np.uint8))
+        else:
+            bits = O.encode_pframe(s, p, kft, q.poses[f], pts)[0]
+        conn.send((len(pts), time.perf_counter() - t0, len(bits)))
+        j += 1
+        if j == len(order):
+            g = (g + 1) % ngroups
+            q, order = load(g)
+            j = 0
+
+
+class OracleCores:
+    """One spawned process per host core (_oracle_core), each on its own sequence of the large
+    batched workload; step() has every core encode its next frame (the cores work side by side)
+    and returns (points, seconds: the slowest core's oracle time, stream bytes)."""
+
+    def __init__(self, cores, learned=True, thr=0.05, first_seq=0, n_frames=100, key_interval=10):
+        import multiprocessing as mp
+        ctx = mp.get_context("spawn")
+        self.cores = cores
+        self.conns, self.procs = [], []
+        for c in range(cores):
+            a, b = ctx.Pipe()
+            pr = ctx.Process(target=_oracle_core, args=(b, first_seq + c, learned, thr, n_frames, key_interval),
+                             daemon=True)
+            pr.start()
+            self.conns.append(a)
+            self.procs.append(pr)
+
+    def step(self):
+        for c in self.conns:
+            c.send(1)
+        res = [c.recv() for c in self.conns]
+        return sum(r[0] for r in res), max(r[1] for r in res), sum(r[2] for r in res)
+
+    def close(self):
+        for c in self.conns:
+            try:
+                c.send(None)
+            except Exception:
+                pass
+        for pr in self.procs:
+            pr.join(timeout=10)
+            if pr.is_alive():
+                pr.terminate()
+
+
+def oracle_cfg5(steps, thr=0.05, cores=None, warmup=0):
+    """The oracle on all host cores over `steps` frames per core (one key-frame group = 10
+    steps, key frame first): Mpoints/s over the summed step times, and what was sampled."""
+    cores = cores or os.cpu_count() or 1
+    oc = OracleCores(cores, learned=True, thr=thr)
+    try:
+        for _ in range(warmup):
+            oc.step()
+        pts = sec = 0.0
+        for _ in range(steps):
+            a, b, _ = oc.step()
+            pts += a
+            sec += b
+    finally:
+        oc.close()
+    return pts / sec / 1e6, pts, sec, cores
+
+
 def run_reference(args, rank, world):
-    th, tw = (int(x) for x in args.tile.split("x"))
+    """The reference arm: the oracle (plain C and numpy, as it stands) on the headline workload,
+    one process per host core, each step every core encoding the next frame of its own key-frame
+    group (key frame first: the oracle net's forward on every tile, then the seeded fit)."""
     if world > 1 and rank != 0:
         return
-    import multiprocessing as mp
-    seq = make_workload(0)
-    pts = sum(len(f) for f in seq.frames)
-    # each step: every host core encodes whole sequences for a bounded time (one pool for the run)
-    per_step = min(max(args.cpu_seconds / max(args.steps + args.warmup, 1), 0.3), 4.0)
     cores = os.cpu_count() or 1
-    vals, nseqs = [], 0
-    with mp.get_context("spawn").Pool(cores) as pool:
+    oc = OracleCores(cores, learned=True, thr=args.thr)
+    try:
         for _ in range(args.warmup):
-            oracle_all_cores(seq, th, tw, args.thr, 0.0, pool)
+            oc.step()
+        pts = sec = 0.0
         for _ in range(args.steps):
-            v, nseq, el, cores = oracle_all_cores(seq, th, tw, args.thr, per_step, pool)
-            vals.append(v)
-            nseqs += nseq
-    value = float(np.mean(vals))
+            a, b, _ = oc.step()
+            pts += a
+            sec += b
+    finally:
+        oc.close()
+    value = pts / sec / 1e6
+    groups = args.steps / 10.0
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * pts / (value * 1e6),
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sec / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "points_per_step": pts, "tile": args.tile, "thr_m": args.thr},
+            "config": cfg5_config(args),
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
-                             "sample": f"{nseqs} whole sequences (10 frames each) over {args.steps} steps, one "
-                                       f"process per host core, >= {per_step:.1f} s each per step"},
+                             "sample": f"{args.steps} steps of one frame per core ({groups:g} key-frame groups of "
+                                       f"10 frames of 128x4096 per core, key frame first: oracle net forward on "
+                                       f"every 8x8 tile + seeded fit; P frames plain), {pts / 1e6:.1f} M points"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -793,26 +941,328 @@ def run_learned(args, stream):
     }
 
 
-def main():
-    args = parse()
-    rank = int(os.environ.get("RANK", "0"))
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    if args.impl == "reference":
-        run_reference(args, rank, world)
-        return
-    th, tw = (int(x) for x in args.tile.split("x"))
-    seq = make_workload(rank)
-    import torch
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    torch.cuda.set_device(local)
-    dist = None
-    if world > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl")
-    from paper_2008_06972_gb300 import build as B
-    B.build()
-    from paper_2008_06972_gb300 import lcc
+# Algorithmic bytes (or FLOPs) of each kernel per unit, the figures the roofline uses:
+#   bin:        20 B per input point (16 B float4 read + 4 B atomic into the range image)
+#   fit:        4 B per pixel (range image) + 64 B per tile record written
+#   rounds:     128 B per queued tile (its record read and written) + 4 B per pixel per further round
+#   lookbehind: 4 B per pixel + 96 B per tile (record read, look-behind counts written)
+#   temporal:   (P frames) 4 B per pixel + 128 B per tile (record read and written)
+#   merge:      128 B per tile (record read, code and offsets written) + the stream bytes zeroed
+#   pack:       8 B per pixel (range read and reset) + the stream bytes written
+#   net_inputs: (seeded key frames) 4 B per pixel read + 8 B per pixel of BF16 input + 16 B anchor per tile
+#   net_fwd:    7.2 MFLOP per 8x8 tile on the tensor cores
+NET_FLOPS_PER_TILE = 7.2e6
 
+
+def kernel_units(st: dict, frames: int, p_frames: int, key_seeded: int, npx: int, nt: int, tpx: int) -> dict:
+    """Per-kernel algorithmic bytes of one encode of `frames` frames from its statistics."""
+    hist = st["fit_rounds"]
+    queued = sum(hist[r] for r in range(2, 8))
+    extra = sum((r - 1) * hist[r] for r in range(2, 8))
+    return {
+        "bin": 20.0 * st["points_in"],
+        "fit": frames * (4.0 * npx + 64.0 * nt),
+        "rounds": 128.0 * queued + 4.0 * tpx * extra,
+        "lookbehind": frames * (4.0 * npx + 96.0 * nt),
+        "temporal": p_frames * (4.0 * npx + 128.0 * nt),
+        "merge": frames * 128.0 * nt + st["bytes"],
+        "pack": frames * 8.0 * npx + st["bytes"],
+        "net_inputs": key_seeded * (12.0 * npx + 16.0 * nt),
+        "net_fwd": key_seeded * nt * NET_FLOPS_PER_TILE,
+    }
+
+
+def bf16_peak():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            d = json.load(fh)
+        return float(d["bf16_tflops_sustained"]), "measured (sustained)"
+    except Exception:
+        return 1700.0, "fallback (sustained)"
+
+
+def run_cfg5(args, stream, rank, world, dist):
+    """The headline: the large batched workload encoded by one plan with the learned proposal
+    (value) and by the plain plan on the same inputs, plus e2e, roofline and the CPU baseline."""
+    import concurrent.futures as cf
+    import torch
+    import synth
+    from paper_2008_06972_gb300 import lcc
+    from paper_2008_06972_gb300 import multi
+    from paper_2008_06972_gb300 import train as TR
+    S = synth.CFG5_SENSOR
+    npx = S.rows * S.cols
+    nseq, nfr, ki = args.cfg5_seqs, args.cfg5_frames, synth.CFG5_KEY_INTERVAL
+    nf = nseq * nfr
+    setup = {}
+    t0 = time.perf_counter()
+    host = np.empty((nf, npx, 4), np.float32)
+    seqs = synth.batch_cfg5(host, n_seq=nseq, n_frames=nfr, first=rank * nseq)
+    setup["generate_s"] = time.perf_counter() - t0
+    npts = [[len(f) for f in q.frames] for q in seqs]
+    total_pts = sum(sum(n) for n in npts)
+    t0 = time.perf_counter()
+    cudart = torch.cuda.cudart()
+    # page-lock the inputs: the end-to-end plan reads them in place, and the copy into HBM is one DMA
+    assert int(cudart.cudaHostRegister(host.ctypes.data, host.nbytes, 0)) == 0, "cudaHostRegister failed"
+    dev = torch.empty((nf, npx, 4), dtype=torch.float32, device="cuda")
+    hostt = torch.from_numpy(host)
+    for a in range(0, nf, 64):
+        dev[a:a + 64].copy_(hostt[a:a + 64], non_blocking=True)
+    torch.cuda.synchronize()
+    setup["to_device_s"] = time.perf_counter() - t0
+
+    def pts_dev(i, f):
+        return dev[i * nfr + f].data_ptr()
+
+    # ---- the proposal net: trained on the GPU on frames of other sequences of the same family ----
+    t0 = time.perf_counter()
+    ctx_tr = lcc.Context(S, lcc.default_params(tile_h=8, tile_w=8, fit_thr_m=args.thr), stream=stream)
+    per_seq = 8
+    tr_ids = [100000 + rank * 1000 + i for i in range(max(1, args.cfg5_train_frames // per_seq))]
+    with cf.ThreadPoolExecutor(min(32, os.cpu_count() or 4)) as pool:
+        tr_seqs = list(pool.map(lambda sid: synth.sequence_cfg5_grouped(sid, n_frames=per_seq), tr_ids))
+    X, Y = [], []
+    for q in tr_seqs:
+        for f in q.frames:
+            x, _, y, _ = TR.frame_examples(ctx_tr, torch.from_numpy(f).cuda(), len(f))
+            X.append(x)
+            Y.append(y)
+    X, Y = torch.cat(X), torch.cat(Y)
+    setup["train_data_s"] = time.perf_counter() - t0
+    batch = 4096
+    net = lcc.Net(TR.he_uniform_params(4), max_tiles=batch, stream=stream)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    losses = TR.train(net, X, Y, args.cfg5_train_steps, batch, 2e-3, seed=1, lr_final=2e-4)
+    torch.cuda.synchronize()
+    train = {"frames": len(tr_ids) * per_seq, "tiles": int(X.shape[0]), "steps": args.cfg5_train_steps,
+             "batch_tiles": batch, "seconds": time.perf_counter() - t0, "loss_first": float(losses[0]),
+             "loss_last": float(np.mean(losses[-10:]))}
+    assert net.sync() == lcc.OK
+    del X, Y
+
+    # ---- autotune: the plain plan over every tile shape, the learned plan among 8x8 ----
+    t0 = time.perf_counter()
+    k0 = synth.group_key(0, nfr, ki)
+    m0 = min(ki, nfr)
+    samp = [pts_dev(0, f) for f in range(m0)]
+    tuned = {}
+    for name, shapes in (("plain", None), ("learned", [(8, 8)])):
+        best, rows = lcc.autotune(S, lcc.default_params(max_batch=64, fit_thr_m=args.thr), k0, seqs[0].poses[:m0],
+                                  samp, npts[0][:m0], reps=3, stream=stream, shapes=shapes)
+        ch = next(r for r in rows if r["chosen"])
+        tuned[name] = (best, {"tile": f"{ch['tile_h']}x{ch['tile_w']}", "lookahead": ch["lookahead"],
+                              "fit_schedule": ch["fit_schedule"], "sample_mpts_s": round(ch["mpts_per_s"], 1),
+                              "candidates": len(rows)})
+    setup["autotune_s"] = time.perf_counter() - t0
+
+    ctxs = {k: lcc.Context(S, tuned[k][0], stream=stream) for k in tuned}
+    cap = (max(c.max_encoded_bytes for c in ctxs.values()) + 255) // 256 * 256
+    outs = {k: torch.empty((nf, cap), dtype=torch.uint8, device="cuda") for k in ctxs}
+    nbytes = {k: torch.zeros(nf, dtype=torch.int64, device="cuda") for k in ctxs}
+
+    def descs(kind, pts_of):
+        return [dict(ctx=0, key_interval=ki, poses=q.poses, d_pts=[pts_of(i, f) for f in range(nfr)], n=npts[i],
+                     d_out=[outs[kind][i * nfr + f].data_ptr() for f in range(nfr)], cap=[cap] * nfr,
+                     d_nbytes=nbytes[kind][i * nfr:(i + 1) * nfr]) for i, q in enumerate(seqs)]
+
+    plans = {k: lcc.Plan([ctxs[k]], descs(k, pts_dev)) for k in ctxs}
+    plans["learned"].set_proposals(net, TR.SKIP_LOGIT)
+    for k in plans:
+        plans[k].capture()
+        for _ in range(max(args.warmup, 3)):
+            plans[k].replay()
+        st = plans[k].sync()
+        assert st == lcc.OK, lcc.status_string(st)
+
+    def timed(plan, steps, clocks=None):
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+        t_wall = time.perf_counter()
+        if clocks:
+            clocks.__enter__()
+        try:
+            for k in range(steps):
+                evs[k][0].record(stream)
+                plan.replay()
+                evs[k][1].record(stream)
+            torch.cuda.synchronize()
+        finally:
+            if clocks:
+                clocks.__exit__()
+        t_wall = time.perf_counter() - t_wall
+        if dist:
+            dist.barrier()
+        st = plan.sync()
+        assert st == lcc.OK, lcc.status_string(st)
+        return float(np.mean([a.elapsed_time(b) for a, b in evs])), t_wall
+
+    # ---- timed region: K replays of the learned plan (the headline), then the plain plan ----
+    clocks = Clocks(args.clocks_csv.replace("{rank}", str(rank)) if args.clocks_csv
+                    else f"/tmp/lcc_clocks_{os.getpid()}_rank{rank}.csv")
+    ms_l, wall_l = timed(plans["learned"], args.steps, clocks)
+    value, sec_step, _ = multi.job_value(total_pts, ms_l * 1e-3, dist, "cuda")
+    plain_steps = max(3, min(args.steps, 10))
+    ms_p, _ = timed(plans["plain"], plain_steps)
+    value_p, _, _ = multi.job_value(total_pts, ms_p * 1e-3, dist, "cuda")
+
+    # ---- correctness of what was timed: every frame decoded, max error against its range image ----
+    def check(kind):
+        c = ctxs[kind]
+        nb = nbytes[kind].cpu().numpy()
+        ref = torch.empty(npx, dtype=torch.float32, device="cuda")
+        dec = [torch.empty(npx, dtype=torch.float32, device="cuda") for _ in range(ki)]
+        err = torch.zeros((), dtype=torch.float32, device="cuda")
+        bad = torch.zeros((), dtype=torch.int64, device="cuda")
+        for i, q in enumerate(seqs):
+            for g0 in range(0, nfr, ki):
+                fr = list(range(g0, min(g0 + ki, nfr)))
+                k = synth.group_key(g0, nfr, ki)
+                c.lcc_decode_sequence(k - g0, q.poses[g0:g0 + len(fr)], [outs[kind][i * nfr + f] for f in fr],
+                                      [int(nb[i * nfr + f]) for f in fr], dec[:len(fr)], None, None)
+                for j, f in enumerate(fr):
+                    c.lcc_range_image(pts_dev(i, f), npts[i][f], ref, None)
+                    m = ref > 0
+                    bad += ((dec[j] > 0) != m).sum()
+                    err = torch.maximum(err, torch.where(m, (dec[j] - ref).abs(), 0.0).max())
+        assert c.lcc_sync() == lcc.OK
+        return float(err.item()), int(bad.item()), int(nb.sum())
+
+    err_l, bad_l, bytes_l = check("learned")
+    err_p, bad_p, bytes_p = check("plain")
+    assert err_l <= 0.02 and err_p <= 0.02 and bad_l == 0 and bad_p == 0, (err_l, err_p, bad_l, bad_p)
+
+    # ---- per-kernel times: one eager encode of each plan with a CUDA event pair around every launch ----
+    hbm, src = peaks()
+    tpeak, tsrc = bf16_peak()
+    kernels, stats = {}, {}
+    for kind in ("learned", "plain"):
+        c = ctxs[kind]
+        c.lcc_set_profiling(True)
+        plans[kind].encode()
+        assert plans[kind].sync() == lcc.OK
+        kt = c.lcc_kernel_times()
+        c.lcc_set_profiling(False)
+        st = plans[kind].stats()
+        info = plans[kind].info()
+        p_ = tuned[kind][0]
+        nt = ctxs[kind].num_tiles
+        units = kernel_units(st, nf, nf - info["key_frames"], info["seeded_key_frames"], npx, nt,
+                             p_.tile_h * p_.tile_w)
+        tot = sum(v[1] for v in kt.values())
+        rows = {}
+        for name, (launches, ms_k) in kt.items():
+            if launches == 0:
+                continue
+            per_launch = ms_k / launches
+            if name == "net_fwd":
+                ach = units[name] / launches / (per_launch * 1e-3) / 1e12
+                rows[name] = {"launches": launches, "ms": ms_k, "share": ms_k / tot, "bound": "tensor",
+                              "achieved": ach, "unit": "TFLOP/s", "frac": ach / tpeak,
+                              "alg_per_launch": units[name] / launches}
+            else:
+                ach = units.get(name, 0.0) / launches / (per_launch * 1e-3) / 1e9
+                rows[name] = {"launches": launches, "ms": ms_k, "share": ms_k / tot, "bound": "hbm",
+                              "achieved": ach, "unit": "GB/s", "frac": ach / hbm,
+                              "alg_per_launch": units.get(name, 0.0) / launches}
+        kernels[kind] = rows
+        stats[kind] = st
+    dname = max(kernels["learned"].items(), key=lambda kv: kv[1]["ms"])[0]
+    d = kernels["learned"][dname]
+    roof = {"bound": d["bound"], "kernel": dname, "achieved": d["achieved"],
+            "peak": tpeak if d["bound"] == "tensor" else hbm, "unit": d["unit"], "frac": d["frac"],
+            "traffic": measured_traffic_cfg5(dname), "alg_per_launch": d["alg_per_launch"],
+            "peak_source": tsrc if d["bound"] == "tensor" else src,
+            "path": {"alg_bytes_per_step": 16.0 * total_pts + bytes_l,
+                     "achieved": (16.0 * total_pts + bytes_l) / (ms_l * 1e-3) / 1e9,
+                     "frac": (16.0 * total_pts + bytes_l) / (ms_l * 1e-3) / 1e9 / hbm}}
+
+    # ---- end to end through lcc_plan_encode_host: page-locked host points read in place, every
+    #      stream copied into page-locked host buffers, sizes back: one host round trip per step ----
+    h_out = np.empty((nf, cap), np.uint8)
+    assert int(cudart.cudaHostRegister(h_out.ctypes.data, h_out.nbytes, 0)) == 0, "cudaHostRegister failed"
+    plan_e = lcc.Plan([ctxs["learned"]], descs("learned", lambda i, f: host[i * nfr + f].ctypes.data))
+    plan_e.set_proposals(net, TR.SKIP_LOGIT)
+    plan_e.capture()
+    h_rows = [h_out[f] for f in range(nf)]
+    for _ in range(2):
+        sizes = plan_e.encode_host(h_rows)
+    assert np.array_equal(sizes.astype(np.int64), nbytes["learned"].cpu().numpy())
+    e2e_steps = max(3, min(args.steps, 10))
+    if dist:
+        dist.barrier()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        sizes = plan_e.encode_host(h_rows)
+    e2e_s = (time.perf_counter() - t0) / e2e_steps
+    e2e_value, _, _ = multi.job_value(total_pts, e2e_s, dist, "cuda")
+    plan_e.close()
+
+    info_l = plans["learned"].info()
+    for k in plans:
+        plans[k].close()
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        v, pts_c, sec_c, cores = oracle_cfg5(args.cpu_steps, args.thr)
+        cpu = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
+               "sample": f"{args.cpu_steps} frames per core of the same workload ({args.cpu_steps / 10:g} key-frame "
+                         f"groups of 10 per core, key frame first: oracle net forward on every 8x8 tile + seeded "
+                         f"fit; P frames plain), {pts_c / 1e6:.1f} M points in {sec_c:.1f} s of oracle time"}
+
+    def summary(kind, ms, val, err, nbytes_):
+        st = stats[kind]
+        return {"value": val, "unit": UNIT, "ms_per_step": ms, "params": tuned[kind][1],
+                "compression_ratio": 12.0 * total_pts / nbytes_, "bytes_per_step": nbytes_,
+                "max_decode_error_m": err,
+                "tile_modes": {"empty": st["tiles_empty"], "raw": st["tiles_raw"], "run_start": st["tiles_run_start"],
+                               "run_cont": st["tiles_run_cont"], "temporal": st["tiles_temporal"]},
+                "fit_rounds_hist": st["fit_rounds"], "fit_rounds": sum(r * c for r, c in enumerate(st["fit_rounds"])),
+                "tiles_borderline": st["tiles_borderline"],
+                "hbm_path_frac": (16.0 * total_pts + nbytes_) / (ms * 1e-3) / 1e9 / hbm,
+                "kernels": kernels[kind]}
+
+    learned = summary("learned", ms_l, value, err_l, bytes_l)
+    plain = summary("plain", ms_p, value_p, err_p, bytes_p)
+    return {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": sec_step * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {**cfg5_config(args), "points_per_step": total_pts, "frames": nf,
+                   "key_frames": info_l["key_frames"], "seeded_key_frames": info_l["seeded_key_frames"],
+                   "parallelism": f"replicas x{world}", "tile": tuned["learned"][1]["tile"]},
+        "max_decode_error_m": max(err_l, err_p),
+        "roofline": roof,
+        "cpu_baseline": cpu,
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(16 * total_pts),
+                "d2h_bytes_per_step": int(bytes_l + 8 * nf), "steps": e2e_steps,
+                "how": "lcc_plan_encode_host: page-locked host points read in place by the binning kernels, "
+                       "streams copied to page-locked host buffers by one kernel, sizes back"},
+        "gpu_launches": int(info_l["launches"] * args.steps),
+        "graph_nodes": info_l["graph_nodes"],
+        "clocks": clocks.summary(),
+        "wall_s_timed": wall_l,
+        "learned_vs_plain": {"throughput_ratio": value / value_p, "bytes_ratio": bytes_l / bytes_p,
+                             "fit_rounds_saved_frac": 1.0 - learned["fit_rounds"] / max(plain["fit_rounds"], 1)},
+        "batched_learned": learned,
+        "batched_plain": plain,
+        "net_training": train,
+        "setup_s": setup,
+    }
+
+
+def run_hdl64(args, stream):
+    """One synthetic HDL-64E sequence (10 frames of 64x2048, the middle one the key frame) encoded
+    per call by lcc_encode_sequence: throughput (L2 flushed between steps), kernel times, decode,
+    the entropy stage, the end-to-end host-buffer call, the dominant kernel's roofline, and the
+    tile / threshold sweep and IMU rows."""
+    import torch
+    from paper_2008_06972_gb300 import lcc
+    th, tw = (int(x) for x in args.tile.split("x"))
+    seq = make_workload(0)
     n_frames = len(seq.frames)
     stream = torch.cuda.current_stream()
     params = lcc.default_params(tile_h=th, tile_w=tw, fit_thr_m=args.thr, max_batch=max(16, n_frames),
@@ -836,10 +1286,7 @@ def main():
     assert ctx.lcc_sync() == lcc.OK
     # ---- timed region: K steps, each bracketed by CUDA events on the context stream ----
     evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-    clocks = Clocks(args.clocks_csv.replace("{rank}", str(rank)) if args.clocks_csv
-                    else f"/tmp/lcc_clocks_{os.getpid()}_rank{rank}.csv")
-    if dist:
-        dist.barrier()
+    clocks = Clocks(f"/tmp/lcc_clocks_{os.getpid()}_hdl64.csv")
     torch.cuda.synchronize()
     with clocks:
         t_wall = time.perf_counter()
@@ -850,15 +1297,11 @@ def main():
             evs[k][1].record(stream)
         torch.cuda.synchronize()
         t_wall = time.perf_counter() - t_wall
-    if dist:
-        dist.barrier()
     st = ctx.lcc_sync()
     assert st == lcc.OK, lcc.status_string(st)
     ms = np.array([a.elapsed_time(b) for a, b in evs])
-    from paper_2008_06972_gb300 import multi
-    # whole job: all ranks' points over the slowest rank's mean step time
-    value, sec_step, pts_job = multi.job_value(pts_step, float(ms.mean()) * 1e-3, dist, "cuda")
-    ms_step = sec_step * 1e3
+    value = pts_step / (float(ms.mean()) * 1e-3) / 1e6
+    ms_step = float(ms.mean())
 
     # ---- per-kernel times (same workload, profiling events around each launch) ----
     ctx.lcc_set_profiling(True)
@@ -955,7 +1398,7 @@ def main():
     for _ in range(e2e_steps):
         nb = ctx.lcc_encode_sequence_host(seq.key_index, seq.poses, h_pts, h_out, [cap] * n_frames)
     e2e_s = (time.perf_counter() - t0) / e2e_steps
-    e2e_value, e2e_s, _ = multi.job_value(pts_step, e2e_s, dist, "cuda")
+    e2e_value = pts_step / e2e_s / 1e6
 
     # ---- roofline of the dominant kernel ----
     hbm, src = peaks()
@@ -998,49 +1441,49 @@ def main():
             "path": {"alg_bytes_per_step": path_bytes, "achieved": path_bytes / (ms_step * 1e-3) / 1e9,
                      "frac": path_bytes / (ms_step * 1e-3) / 1e9 / hbm}}
 
-    sweep = None if args.no_sweep or world > 1 else run_sweep(args, stream, seq, d_pts, flush)
-    imu_rows = None if args.no_imu or world > 1 else run_imu(args, stream, flush)
-    batched = None if args.no_batched else run_batched(args, stream, hbm)
-    learned = None if args.no_learned else run_learned(args, stream)
+    sweep = None if args.no_sweep else run_sweep(args, stream, seq, d_pts, flush)
+    imu_rows = None if args.no_imu else run_imu(args, stream, flush)
+    assert max_err <= 0.02, max_err
+    return {
+        "workload": WORKLOAD, "value": value, "unit": UNIT, "ms_per_step": ms_step, "steps": args.steps,
+        "config": {"frames": n_frames, "points_per_step": pts_step, "tile": args.tile, "thr_m": args.thr, "q_m": 0.02,
+                   "lookahead": args.lookahead, "max_refits": args.refits,
+                   "plane_solver": "float-float" if args.solver == "ff" else "fp64", "fit_schedule": args.schedule,
+                   "l2": "flushed between steps (256 MiB write, untimed)"},
+        "max_decode_error_m": max_err, "tile_modes": modes, "fit_rounds_hist": rounds_hist,
+        "tiles_borderline": border, "compression_ratio": 12.0 * pts_step / total_bytes,
+        "bytes_per_step": total_bytes, "kernel_ms_per_step": {k: v[1] / args.steps for k, v in ktimes.items()},
+        "gpu_launches_per_step": launches_per_step, "roofline": roof, "decode": decode, "entropy": entropy,
+        "sweep": sweep, "imu": imu_rows, "clocks": clocks.summary(),
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(16 * pts_step),
+                "d2h_bytes_per_step": int(total_bytes + 8 * n_frames)},
+    }
 
-    cpu = None
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        v1, nseq1, el1 = oracle_sample(seq, th, tw, args.thr, args.cpu_seconds / 2)
-        v, nseq, el, cores = oracle_all_cores(seq, th, tw, args.thr, args.cpu_seconds / 2)
-        cpu = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
-               "sample": f"{nseq} whole sequences (10 frames each) in {el:.1f} s, one process per host core",
-               "single_core": {"value": v1, "sample": f"{nseq1} whole sequences in {el1:.1f} s on one core"}}
 
+def main():
+    args = parse()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+    import torch
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    from paper_2008_06972_gb300 import build as B
+    B.build()
+    stream = torch.cuda.current_stream()
+    hbm, _ = peaks()
+    line = run_cfg5(args, stream, rank, world, dist)
+    if world == 1:
+        line["hdl64_sequence"] = None if args.no_hdl64 else run_hdl64(args, stream)
+        line["batched"] = None if args.no_batched else run_batched(args, stream, hbm)
+        line["learned"] = None if args.no_learned else run_learned(args, stream)
     if rank == 0:
-        line = {
-            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "frames": n_frames, "points_per_step": pts_step, "tile": args.tile,
-                       "thr_m": args.thr, "q_m": 0.02, "lookahead": args.lookahead, "max_refits": args.refits,
-                       "plane_solver": "float-float" if args.solver == "ff" else "fp64",
-                       "fit_schedule": args.schedule, "l2": "flushed between steps (256 MiB write, untimed)",
-                       "parallelism": f"replicas x{world}"},
-            "max_decode_error_m": max_err,
-            "tile_modes": modes, "fit_rounds_hist": rounds_hist, "tiles_borderline": border,
-            "compression_ratio": 12.0 * pts_step / total_bytes,
-            "bytes_per_step": total_bytes,
-            "kernel_ms_per_step": {k: v[1] / args.steps for k, v in ktimes.items()},
-            "roofline": roof,
-            "decode": decode,
-            "entropy": entropy,
-            "sweep": sweep,
-            "imu": imu_rows,
-            "batched": batched,
-            "learned": learned,
-            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(16 * pts_step),
-                    "d2h_bytes_per_step": int(total_bytes + 8 * n_frames)},
-            "gpu_launches": int(round(launches_per_step * args.steps)),
-            "cpu_baseline": cpu,
-            "clocks": clocks.summary(),
-            "wall_s_timed": t_wall,
-        }
-        assert max_err <= 0.02, max_err
         print(json.dumps(line), flush=True)
     if dist:
         dist.barrier()
