@@ -63,8 +63,11 @@ typedef struct {
     int32_t fit_schedule;     /* 0: a thread runs all refit rounds of its tile; 1 or 2: a thread runs that
                                  many rounds, tiles needing another round are queued and re-run in
                                  dense warps, one kernel per round; 3: one round per thread, then the
-                                 queued tiles' remaining rounds in one dense kernel (same results for
-                                 every value) */
+                                 queued tiles' remaining rounds in one dense kernel; 4: as 3, and P
+                                 frames encoded in batches (lcc_encode_pframes, plans) run their spatial
+                                 fits first and the temporal test after them (one lane group per tile),
+                                 the order lcc_encode_sequence always uses, which pays when few P tiles
+                                 pass the temporal test (same results for every value) */
     int32_t no_delta;         /* 1: plane-coded points carry no residual code, the paper's default
                                  (Sec. III-C drops the deltas): they decode onto their plane, decode
                                  error <= fit_thr_m; 0 (default here): residual codes, error <= q/2 */
@@ -497,11 +500,13 @@ void lcc_plan_destroy(lcc_plan *plan);
 /* ---- Autotuner ----
  *
  * Not in the paper (its tile size is a fixed parameter).  Encodes a sample
- * sequence (nframes <= 64 device frames, key frame key_index, poses as in
- * lcc_encode_sequence) with every candidate of tile shape {4x4, 4x8, 8x8,
+ * key-frame group (nframes <= 64 device frames, key frame key_index, poses as
+ * in lcc_encode_sequence) the way a plan encodes its chunks (the key frame by
+ * lcc_encode_keyframe, then the P frames in one lcc_encode_pframes call
+ * against its planes) with every candidate of tile shape {4x4, 4x8, 8x8,
  * 8x16} (those whose bit is set in `shapes`: bit 0 4x4, bit 1 4x8, bit 2 8x8,
  * bit 3 8x16; 0 = all four) x run-test horizon {8, 16, 32} (only 0 when
- * base->merge_runs is 0) x fit schedule {0, 3}, each on a context of its own,
+ * base->merge_runs is 0) x fit schedule {0, 3, 4}, each on a context of its own,
  * `reps` timed encodes per candidate (CUDA events on cuda_stream).  Every
  * frame is then decoded and compared with its binned input: candidates whose
  * max range error exceeds max_err_m are rejected.  Of the rest, those whose

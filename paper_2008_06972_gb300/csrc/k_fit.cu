@@ -1131,7 +1131,7 @@ static cudaError_t launch_queued_rounds_t(const Geometry &g, const Scratch &s, c
         const long long worst = (long long)g.NT * b.nframes;
         constexpr int L = FitLanes<TH_, TW_>::L;   // lanes per queued tile
         const int blocks = (int)std::min<long long>((worst * L + kFitThreads - 1) / kFitThreads, 152 * 8);
-        if (g.schedule == 3) {   // the queued tiles run all their remaining rounds in one dense launch
+        if (g.schedule >= 3) {   // the queued tiles run all their remaining rounds in one dense launch
             k_fit_round<TH_, TW_><<<blocks, kFitThreads, 0, st>>>(g, s, b, 0, 1, rounds_left);
             return cudaGetLastError();
         }

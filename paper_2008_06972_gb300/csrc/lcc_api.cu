@@ -183,6 +183,22 @@ lcc_status encode_batch(lcc_ctx *c, int kind, int nframes, const int *slots, uin
     Batch b;
     Poses p;
     prepare_batch(b, p, kind, nframes, slots, d_out, cap, poses, kf, kf_out, nbytes_out, prop, skip_logit);
+    if (kind == 1 && kf && c->g.schedule == 4) {
+        // P frames, spatial fits first: every tile's first round in the first pass (one thread per
+        // tile, no temporal test), the queued tiles' remaining rounds and the run pre-test, then the
+        // temporal test with a lane group per tile (a tile that passes becomes temporal exactly as
+        // if its spatial fit had never run), merge and pack: the order of lcc_encode_sequence's P
+        // frames, the same streams as the temporal-first order
+        Batch bs = b;
+        for (int f = 0; f < nframes; f++) bs.kf[f] = nullptr;
+        LCC_LAUNCH(c, 1, launch_fit(c->g, c->s, bs, p, c->stream));
+        LCC_LAUNCH_N(c, 3, queued_round_kernels(c->g, bs), launch_queued_rounds(c->g, c->s, bs, c->stream));
+        if (c->g.merge && c->g.lookahead > 0) LCC_LAUNCH(c, 8, launch_lookbehind(c->g, c->s, b, c->stream));
+        LCC_LAUNCH(c, 9, launch_temporal(c->g, c->s, b, p, c->stream));
+        LCC_LAUNCH(c, 2, launch_merge(c->g, c->s, b, c->stream));
+        LCC_LAUNCH(c, 4, launch_pack(c->g, c->s, b, c->stream));
+        return LCC_OK;
+    }
     LCC_LAUNCH(c, 1, launch_fit(c->g, c->s, b, p, c->stream));
     return encode_tail(c, b);
 }
@@ -292,7 +308,7 @@ lcc_status lcc_create(lcc_ctx **out, const lcc_sensor *sensor, const lcc_params 
     if (!(p.fit_thr_m >= 0) || !(p.quant_m > 0) || p.max_refits < 0 || p.max_refits > 6 ||
         !(p.min_inlier_frac >= 0) || p.max_batch < 1 || p.max_batch > kMaxBatch || p.lookahead < 0 ||
         p.lookahead > 32 || p.solver < 0 || p.solver > 1 || p.fit_schedule < 0 ||
-        p.fit_schedule > 3 || p.no_delta < 0 || p.no_delta > 1 || p.raw_exact < 0 || p.raw_exact > 1 ||
+        p.fit_schedule > 4 || p.no_delta < 0 || p.no_delta > 1 || p.raw_exact < 0 || p.raw_exact > 1 ||
         p.temporal_candidates < 0 || p.temporal_candidates > 4)
         return LCC_ERR_INVALID_ARG;
     int dev = 0;
@@ -328,7 +344,7 @@ lcc_status lcc_create(lcc_ctx **out, const lcc_sensor *sensor, const lcc_params 
     g.no_delta = p.no_delta;
     g.raw_exact = p.raw_exact;
     g.tcand = p.temporal_candidates;
-    g.first_rounds = std::min(p.fit_schedule == 3 ? 1 : p.fit_schedule, p.max_refits + 1);
+    g.first_rounds = std::min(p.fit_schedule >= 3 ? 1 : p.fit_schedule, p.max_refits + 1);
     g.k_max = (int)floorf(p.fit_thr_m / p.quant_m + 0.5f) + 1;
     g.w_res = bits_for(2 * g.k_max);
     const int m_max = (int)floorf((float)s.max_range_m / p.quant_m + 0.5f) + 1;

@@ -108,7 +108,9 @@ struct Geometry {
     int R;               // refit rounds after the first fit
     int merge, lookahead;
     int solver;          // 0 float-float plane solve, 1 FP64
-    int schedule;        // 0 per-thread fit rounds; 1, 2: that many rounds per thread, the rest queued
+    int schedule;        // 0 per-thread fit rounds; 1, 2: that many rounds per thread, the rest queued;
+                         // 3: one round per thread, the rest in one dense launch; 4: as 3, and batched
+                         // P frames fit spatially first and run the temporal test after
     int first_rounds;    // fit rounds of the first pass under a queued schedule
     int no_delta;        // 1: plane-coded points carry no residual code (no residual section)
     int raw_exact;       // 1: raw pixels carry their fp32 range bits (32-bit raw codes)
@@ -398,7 +400,7 @@ inline int queued_rounds_left(const Geometry &g, const Batch &b) {
 // Kernels launch_queued_rounds launches for a batch (one per round, or one under schedule 3).
 inline int queued_round_kernels(const Geometry &g, const Batch &b) {
     if (g.schedule < 1 || b.nframes <= 0) return 0;
-    return g.schedule == 3 ? 1 : queued_rounds_left(g, b);
+    return g.schedule >= 3 ? 1 : queued_rounds_left(g, b);
 }
 cudaError_t launch_merge(const Geometry &g, const Scratch &s, const Batch &b, cudaStream_t st);
 size_t merge_smem_bytes(int TC);

@@ -1,7 +1,9 @@
-// Autotuner (lcc_autotune): encodes a sample sequence with every candidate
-// schedule (tile shape x run-test horizon x fit schedule), times it with CUDA
-// events, decodes it to check the error bound, and picks the fastest
-// candidate whose stream is within a slack of the smallest one.
+// Autotuner (lcc_autotune): encodes a sample key-frame group with every
+// candidate schedule (tile shape x run-test horizon x fit schedule) the way a
+// plan encodes its chunks (the key frame, then the P frames in one batched
+// call against its planes), times it with CUDA events, decodes it to check the
+// error bound, and picks the fastest candidate whose stream is within a slack
+// of the smallest one.
 #include <cuda_runtime.h>
 
 #include <cstring>
@@ -47,9 +49,26 @@ lcc_status measure(const lcc_sensor *sensor, const lcc_params &prm, int nframes,
     std::vector<uint8_t *> outs(nframes);
     std::vector<uint64_t> caps(nframes, cap);
     for (int f = 0; f < nframes; f++) outs[f] = (uint8_t *)out.p + cap * f;
+    // the P frames in one batch, in frame order
+    std::vector<const float *> pp;
+    std::vector<int64_t> pn;
+    std::vector<uint8_t *> po;
+    std::vector<uint64_t> pc;
+    std::vector<double> pposes;
+    for (int f = 0; f < nframes; f++) {
+        if (f == key_index) continue;
+        pp.push_back(d_pts[f]);
+        pn.push_back(n[f]);
+        po.push_back(outs[f]);
+        pc.push_back(cap);
+        pposes.insert(pposes.end(), poses + 16 * (size_t)f, poses + 16 * (size_t)f + 16);
+    }
+    uint64_t *nb_dev = (uint64_t *)nbytes.p;   // key frame's size first, then the P frames'
     auto encode = [&]() {
-        return lcc_encode_sequence(c, nframes, key_index, poses, d_pts, n, outs.data(), caps.data(),
-                                   (uint64_t *)nbytes.p, guard.k);
+        lcc_status e = lcc_encode_keyframe(c, d_pts[key_index], n[key_index], guard.k, outs[key_index], cap, nb_dev);
+        if (e != LCC_OK || pp.empty()) return e;
+        return lcc_encode_pframes(c, guard.k, (int32_t)pp.size(), pposes.data(), pp.data(), pn.data(), po.data(),
+                                  pc.data(), nb_dev + 1);
     };
     if ((st = encode()) != LCC_OK || (st = lcc_sync(c)) != LCC_OK) return st;
     cudaEvent_t a, b;
@@ -68,8 +87,9 @@ lcc_status measure(const lcc_sensor *sensor, const lcc_params &prm, int nframes,
     if (st != LCC_OK) return st;
     if (!timed) return LCC_ERR_CUDA;
     if ((st = lcc_sync(c)) != LCC_OK) return st;
-    std::vector<uint64_t> nb(nframes);
-    LCC_CUDA(cudaMemcpy(nb.data(), nbytes.p, 8 * (size_t)nframes, cudaMemcpyDeviceToHost));
+    std::vector<uint64_t> nbk(nframes), nb(nframes);
+    LCC_CUDA(cudaMemcpy(nbk.data(), nbytes.p, 8 * (size_t)nframes, cudaMemcpyDeviceToHost));
+    for (int f = 0, q = 1; f < nframes; f++) nb[f] = f == key_index ? nbk[0] : nbk[q++];
     uint64_t total = 0;
     int64_t pts = 0;
     for (int f = 0; f < nframes; f++) {
@@ -115,7 +135,7 @@ lcc_status lcc_autotune(const lcc_sensor *sensor, const lcc_params *base, int32_
     if (!shapes) shapes = 15u;
     std::vector<lcc_tune_result> all;
     for (int ti = 0; ti < 4; ti++)
-        for (int sched : {0, 3})
+        for (int sched : {0, 3, 4})
             for (int h = 0; h < (base->merge_runs ? 3 : 1); h++) {
                 if (!((shapes >> ti) & 1u)) continue;
                 const int *t = kTiles[ti];

@@ -163,6 +163,22 @@ def test_plan_graph_replay_and_update(batch):
     plan.close()
 
 
+def test_plan_spatial_first_schedule_matches_per_sequence_encode(batch):
+    """Fit schedule 4 (P frames fitted spatially first, temporal test after) writes the streams
+    of the per-sequence encode."""
+    from paper_2008_06972_gb300 import lcc
+    stream = torch.cuda.current_stream()
+    classes = sorted({s.sensor_class for s in batch})
+    ctxs = [H.ctx(synth.CFG3_SENSORS[c], stream=stream, fit_schedule=4, **PARAMS[c]) for c in classes]
+    _, _, _, descs = _setup(batch)
+    plan = lcc.Plan(ctxs, descs)
+    plan.capture()
+    plan.replay()
+    assert plan.sync() == lcc.OK
+    _assert_same(_streams(descs), _reference(batch))
+    plan.close()
+
+
 def test_plan_rejects_bad_tables(batch):
     from paper_2008_06972_gb300 import lcc
     lcc_, classes, ctxs, descs = _setup(batch[:2])
@@ -196,7 +212,7 @@ def test_autotune_picks_fastest_within_byte_slack():
     base = lcc.default_params(max_batch=8)
     best, rows = lcc.autotune(s.sensor, base, k, s.poses, ds, [len(f) for f in s.frames], reps=2,
                               stream=torch.cuda.current_stream())
-    assert len(rows) == 4 * 3 * 2
+    assert len(rows) == 4 * 3 * 3
     ok = [r for r in rows if r["status"] == lcc.OK]
     assert len(ok) == len(rows)
     assert all(r["max_err_m"] <= 0.01 + 1e-5 for r in ok)

@@ -205,7 +205,7 @@ def test_schedule_invariance_and_determinism(cfg1):
     sen, pts = cfg1
     ref = None
     ref_recs = None
-    for la, sched in ((0, 0), (1, 0), (8, 0), (16, 0), (32, 0), (16, 1), (16, 2), (0, 2), (16, 3)):
+    for la, sched in ((0, 0), (1, 0), (8, 0), (16, 0), (32, 0), (16, 1), (16, 2), (0, 2), (16, 3), (16, 4)):
         c = H.ctx(sen, lookahead=la, fit_schedule=sched)
         b1, r1 = H.encode_keyframe(c, pts)
         b2, _ = H.encode_keyframe(c, pts)
@@ -292,9 +292,11 @@ def test_pframe_parity_tiles(cfg2_seq, tile, thr):
     _pframe_case(seq, [0, seq.key_index + 1], tile=tile, thr=thr)
 
 
-def test_pframe_parity_queued_schedule(cfg2_seq):
+@pytest.mark.parametrize("schedule", [1, 4])
+def test_pframe_parity_queued_schedule(cfg2_seq, schedule):
+    """Queued rounds (1); spatial fits first and the temporal test after them (4)."""
     seq = cfg2_seq
-    _pframe_case(seq, [1, 7], schedule=1)
+    _pframe_case(seq, [1, 7], schedule=schedule)
 
 
 def test_pframe_noisy_pose(cfg2_seq):
