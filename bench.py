@@ -78,6 +78,11 @@ def parse():
     ap.add_argument("--cfg5-train-steps", type=int, default=600)
     ap.add_argument("--cpu-steps", type=int, default=10, help="oracle frames per core for cpu_baseline")
     ap.add_argument("--no-hdl64", action="store_true", help="skip the single-sequence HDL-64E section")
+    ap.add_argument("--profile-plan", action="store_true",
+                    help="profiling case: --cfg5-seqs x --cfg5-frames of the headline workload encoded --steps times "
+                         "by one eager plan with fixed parameters (--tile, --lookahead, --schedule, --max-batch), "
+                         "no autotuning, training or other sections (for ncu)")
+    ap.add_argument("--max-batch", type=int, default=64, help="frames per launch of the profiling case")
     return ap.parse_args()
 
 
@@ -1057,20 +1062,54 @@ def run_cfg5(args, stream, rank, world, dist):
                               "candidates": len(rows)})
     setup["autotune_s"] = time.perf_counter() - t0
 
-    ctxs = {k: lcc.Context(S, tuned[k][0], stream=stream) for k in tuned}
-    cap = (max(c.max_encoded_bytes for c in ctxs.values()) + 255) // 256 * 256
-    outs = {k: torch.empty((nf, cap), dtype=torch.uint8, device="cuda") for k in ctxs}
-    nbytes = {k: torch.zeros(nf, dtype=torch.int64, device="cuda") for k in ctxs}
+    cap = (max(lcc.Context(S, tuned[k][0], stream=stream).max_encoded_bytes for k in tuned) + 255) // 256 * 256
+    outs = {k: torch.empty((nf, cap), dtype=torch.uint8, device="cuda") for k in tuned}
+    nbytes = {k: torch.zeros(nf, dtype=torch.int64, device="cuda") for k in tuned}
 
     def descs(kind, pts_of):
         return [dict(ctx=0, key_interval=ki, poses=q.poses, d_pts=[pts_of(i, f) for f in range(nfr)], n=npts[i],
                      d_out=[outs[kind][i * nfr + f].data_ptr() for f in range(nfr)], cap=[cap] * nfr,
                      d_nbytes=nbytes[kind][i * nfr:(i + 1) * nfr]) for i, q in enumerate(seqs)]
 
-    plans = {k: lcc.Plan([ctxs[k]], descs(k, pts_dev)) for k in ctxs}
-    plans["learned"].set_proposals(net, TR.SKIP_LOGIT)
+    def build_plan(kind, frames_per_launch):
+        prm = lcc.lcc_params.from_buffer_copy(tuned[kind][0])
+        prm.max_batch = frames_per_launch
+        ctx = lcc.Context(S, prm, stream=stream)
+        plan = lcc.Plan([ctx], descs(kind, pts_dev))
+        if kind == "learned":
+            plan.set_proposals(net, TR.SKIP_LOGIT)
+        plan.capture()
+        return ctx, plan
+
+    # frames per launch (the plan's chunk size; the chunk's range images should stay in L2): one
+    # timed replay of the whole table at 16, 32 and 64, the fastest kept
+    t0 = time.perf_counter()
+    ctxs, plans = {}, {}
+    for kind in tuned:
+        rows = {}
+        best = None
+        for fpl in (16, 32, 64):
+            ctx, plan = build_plan(kind, fpl)
+            plan.replay()
+            assert plan.sync() == lcc.OK
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            plan.replay()
+            b.record(stream)
+            assert plan.sync() == lcc.OK
+            ms = a.elapsed_time(b)
+            rows[fpl] = round(total_pts / (ms * 1e-3) / 1e6, 1)
+            if best is None or ms < best[0]:
+                if best is not None:
+                    best[3].close()
+                best = (ms, fpl, ctx, plan)
+            else:
+                plan.close()
+        ctxs[kind], plans[kind] = best[2], best[3]
+        tuned[kind][1]["frames_per_launch"] = best[1]
+        tuned[kind][1]["frames_per_launch_mpts_s"] = rows
+    setup["frames_per_launch_s"] = time.perf_counter() - t0
     for k in plans:
-        plans[k].capture()
         for _ in range(max(args.warmup, 3)):
             plans[k].replay()
         st = plans[k].sync()
@@ -1252,6 +1291,47 @@ def run_cfg5(args, stream, rank, world, dist):
         "net_training": train,
         "setup_s": setup,
     }
+
+
+def run_profile_plan(args, stream):
+    """A fixed-parameter plan over a subsample of the headline workload, encoded eagerly --steps
+    times after one warm-up encode: the case the ncu summaries under profiles/ are taken on."""
+    import torch
+    import synth
+    from paper_2008_06972_gb300 import lcc
+    S = synth.CFG5_SENSOR
+    npx = S.rows * S.cols
+    nseq, nfr = args.cfg5_seqs, args.cfg5_frames
+    host = np.empty((nseq * nfr, npx, 4), np.float32)
+    seqs = synth.batch_cfg5(host, n_seq=nseq, n_frames=nfr)
+    dev = torch.from_numpy(host).cuda()
+    th, tw = (int(x) for x in args.tile.split("x"))
+    prm = lcc.default_params(tile_h=th, tile_w=tw, fit_thr_m=args.thr, max_batch=args.max_batch,
+                             lookahead=args.lookahead, fit_schedule=args.schedule,
+                             solver=0 if args.solver == "ff" else 1)
+    ctx = lcc.Context(S, prm, stream=stream)
+    cap = (ctx.max_encoded_bytes + 255) // 256 * 256
+    outs = torch.empty((nseq * nfr, cap), dtype=torch.uint8, device="cuda")
+    nb = torch.zeros(nseq * nfr, dtype=torch.int64, device="cuda")
+    descs = [dict(ctx=0, key_interval=synth.CFG5_KEY_INTERVAL, poses=q.poses,
+                  d_pts=[dev[i * nfr + f].data_ptr() for f in range(nfr)], n=[len(f) for f in q.frames],
+                  d_out=[outs[i * nfr + f].data_ptr() for f in range(nfr)], cap=[cap] * nfr,
+                  d_nbytes=nb[i * nfr:(i + 1) * nfr]) for i, q in enumerate(seqs)]
+    plan = lcc.Plan([ctx], descs)
+    plan.encode()
+    assert plan.sync() == lcc.OK
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        plan.encode()
+    assert plan.sync() == lcc.OK
+    el = time.perf_counter() - t0
+    pts = sum(len(f) for q in seqs for f in q.frames)
+    info = plan.info()
+    plan.close()
+    return {"profile_plan": True, "frames": nseq * nfr, "points": pts, "tile": args.tile,
+            "schedule": args.schedule, "max_batch": args.max_batch, "launches_per_encode": info["launches"],
+            "mpts_per_s_wall": pts * args.steps / el / 1e6, "bytes": int(nb.sum().item())}
 
 
 def run_hdl64(args, stream):
@@ -1478,6 +1558,9 @@ def main():
     B.build()
     stream = torch.cuda.current_stream()
     hbm, _ = peaks()
+    if args.profile_plan:
+        print(json.dumps(run_profile_plan(args, stream)), flush=True)
+        return
     line = run_cfg5(args, stream, rank, world, dist)
     if world == 1:
         line["hdl64_sequence"] = None if args.no_hdl64 else run_hdl64(args, stream)

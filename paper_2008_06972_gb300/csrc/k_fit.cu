@@ -1031,67 +1031,76 @@ __global__ void __launch_bounds__(kFitThreads) k_temporal(Geometry g, Scratch s,
 // whether tile t would join a run started at tile t-1-j, i.e. passes that
 // plane under the acceptance rule (Sec. III-C run growth).
 //
-// LPT lanes per tile (16 for horizons up to 16, else 32): the lanes stage the
-// tile's pixels (unit ray and range) in shared memory, one pixel each, then
-// lane j tests all of them against the plane of tile t-1-j.  The tests of
-// one tile run side by side instead of one after the other, which is what a
-// single key frame (8192 tiles at 64x2048) needs to fill the GPU.
+// LPT lanes per tile (16 for horizons up to 16, else 32).  Lane l holds the
+// tile's pixels k = l, l + LPT, ... (range and unit ray in registers).  The
+// group first marks which of the tiles to its left were fitted (lane j reads
+// the status of tile t-1-j, a ballot gathers them), then tests the fitted
+// planes one after another, every lane its own pixels, and adds the inlier
+// counts by shuffles: every lane of the group works on every test, whatever
+// share of the candidate tiles holds a plane.
 template <int TH_, int TW_, int LPT>
 __global__ void __launch_bounds__(kFitThreads) k_lookbehind(Geometry g, Scratch s, Batch b) {
     constexpr int PX = TH_ * TW_;
+    constexpr int PPL = (PX + LPT - 1) / LPT;
     constexpr int TPB = kFitThreads / LPT;
-    __shared__ float4 s_px[TPB][PX + 1];   // +1: tiles of one warp start in different banks
     const unsigned FULL = 0xffffffffu;
     const int f = blockIdx.y;
-    const int lt = threadIdx.x / LPT, j = threadIdx.x % LPT;
+    const int lt = threadIdx.x / LPT, l = threadIdx.x % LPT;
+    const int lane = threadIdx.x & 31;
+    const int gbase = lane & ~(LPT - 1);
+    const unsigned gmask = LPT == 32 ? FULL : (((1u << LPT) - 1u) << gbase);
     const int t = blockIdx.x * TPB + lt;
     const bool live = t < g.NT;
     const uint32_t *rimg = s.rimg + (size_t)b.slot[f] * g.H * g.W;
     TileRec *recs = s.tiles + (size_t)b.slot[f] * g.NT;
     const int tc = live ? t % g.TC : 0;
     const int i0 = live ? (t / g.TC) * TH_ : 0, j0 = tc * TW_;
+    float pr[PPL], pux[PPL], puy[PPL], puz[PPL];
     int nv = 0;
-    for (int k = j; k < PX; k += LPT) {
-        float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+    for (int m = 0; m < PPL; m++) {
+        const int k = l + LPT * m;
         const int i = i0 + k / TW_, jj = j0 + k % TW_;
-        const bool in = live && i < g.H && jj < g.W;
+        const bool in = live && k < PX && i < g.H && jj < g.W;
         const uint32_t bits = in ? __ldg(rimg + (size_t)i * g.W + jj) : kEmptyBits;
-        beam(g, in ? i : 0, in ? jj : 0, v.x, v.y, v.z);   // issued beside the range load
-        if (bits_valid(bits)) {
-            v.w = __uint_as_float(bits);
-            nv++;
-        } else {
-            v = make_float4(0.f, 0.f, 0.f, 0.f);
-        }
-        s_px[lt][k] = v;
+        beam(g, in ? i : 0, in ? jj : 0, pux[m], puy[m], puz[m]);   // issued beside the range load
+        pr[m] = bits_valid(bits) ? __uint_as_float(bits) : 0.0f;
+        nv += bits_valid(bits) ? 1 : 0;
     }
 #pragma unroll
-    for (int off = LPT / 2; off; off >>= 1) nv += __shfl_xor_sync(FULL, nv, off);
-    __syncwarp();
-    int nin = 0;
-    bool pass = false, border = false;
-    if (live && nv >= 3 && j < min(g.lookahead, tc)) {
-        const TileRec *src = recs + (t - 1 - j);
+    for (int off = LPT / 2; off; off >>= 1) nv += __shfl_xor_sync(gmask, nv, off);
+    // the fitted tiles among the candidates (group-uniform mask, bit j = tile t-1-j)
+    const int ncand = live && nv >= 3 ? min(g.lookahead, tc) : 0;
+    bool fitted = false;
+    if (l < ncand) {
+        const TileRec *src = recs + (t - 1 - l);
         const uint32_t w0 = *reinterpret_cast<const uint32_t *>(reinterpret_cast<const uint8_t *>(src) + 40);
-        if ((w0 & 0xff) == S_FIT) {
-            const float4 pl = src->plane;
-#pragma unroll 4
-            for (int k = 0; k < PX; k++) {
-                const float4 v = s_px[lt][k];
-                if (v.w > 0.0f) nin += inlier_screened(pl, v.x, v.y, v.z, v.w, g.thr, border) ? 1 : 0;
-            }
-            pass = nin >= need_inliers(g.fmin, nv);
-        }
+        fitted = (w0 & 0xff) == S_FIT;
     }
-    const uint32_t bal = __ballot_sync(FULL, pass);
-    const uint32_t bmask = LPT == 32 ? bal : (bal >> ((threadIdx.x & 31) & ~(LPT - 1))) & ((1u << LPT) - 1u);
+    const unsigned fmask = (__ballot_sync(gmask, fitted) & gmask) >> gbase;
+    const int need = need_inliers(g.fmin, nv);
+    int my_nin = 0;
+    uint32_t pass_mask = 0;
+    bool border = false;
+    for (unsigned m = fmask; m; m &= m - 1) {
+        const int j = __ffs(m) - 1;
+        const float4 pl = recs[t - 1 - j].plane;
+        int c = 0;
+#pragma unroll
+        for (int q = 0; q < PPL; q++)
+            if (pr[q] > 0.0f) c += inlier_screened(pl, pux[q], puy[q], puz[q], pr[q], g.thr, border) ? 1 : 0;
+#pragma unroll
+        for (int off = LPT / 2; off; off >>= 1) c += __shfl_xor_sync(gmask, c, off);
+        if (l == j) my_nin = c;
+        if (c >= need) pass_mask |= 1u << j;
+    }
     if (live) {
         uint8_t *lb = s.lbcnt + ((size_t)b.slot[f] * g.NT + t) * 32;
-        lb[j] = (uint8_t)nin;
-        if (LPT == 16) lb[j + 16] = 0;
+        lb[l] = (uint8_t)my_nin;
+        if (LPT == 16) lb[l + 16] = 0;
         uint8_t *base = reinterpret_cast<uint8_t *>(recs + t);
-        if (j < 16) base[48 + j] = (uint8_t)nin;
-        if (j == 0) *reinterpret_cast<uint32_t *>(base + 36) = bmask;
+        if (l < 16) base[48 + l] = (uint8_t)my_nin;
+        if (l == 0) *reinterpret_cast<uint32_t *>(base + 36) = pass_mask;
     }
 }
 
