@@ -69,8 +69,10 @@ def parse():
     ap.add_argument("--no-entropy", action="store_true", help="skip the entropy-stage section")
     ap.add_argument("--clocks-csv", default="", help="where the SM-clock samples of the timed region go "
                     "({rank} is replaced by the rank); default: a file under /tmp")
-    ap.add_argument("--train-steps", type=int, default=300)
-    ap.add_argument("--train-seqs", type=int, default=6)
+    ap.add_argument("--train-steps", type=int, default=0, help="training steps of the learned section "
+                    "(0: one epoch over the training tiles, at least 300)")
+    ap.add_argument("--train-frames", type=int, default=512, help="64x2048 frames the learned section trains on "
+                    "(the configuration's full scale is 20000)")
     ap.add_argument("--cfg5-seqs", type=int, default=32, help="sequences of the headline workload (per rank)")
     ap.add_argument("--cfg5-frames", type=int, default=100, help="frames per sequence of the headline workload")
     ap.add_argument("--cfg5-train-frames", type=int, default=64,
@@ -568,7 +570,7 @@ def run_sweep(args, stream, seq, d_pts, flush):
                 st_f = ctx.lcc_last_stats(f)
                 modes["raw"] += st_f["tiles_raw"]
                 modes["run"] += st_f["tiles_run_start"] + st_f["tiles_run_cont"]
-                modes["temporal"] += st_f["tiles_temporal"]
+                modes["temporal"] += st_f["tiles_temporal"] + st_f["tiles_temporal_cont"]
             ref = torch.empty(H * W, dtype=torch.float32, device="cuda")
             dec = torch.empty(H * W, dtype=torch.float32, device="cuda")
             kfd = lcc.Keyframe(ctx)
@@ -775,30 +777,44 @@ def run_learned(args, stream):
     from paper_2008_06972_gb300 import train as TR
     sensor = synth.HDL64_SENSOR
 
-    def frames(ids, n):
-        out = []
-        for i in ids:
-            q = synth.sequence(sensor, n, synth.config_seed(4, i, 0), n_walls=20, n_boxes=40, n_poles=60,
-                               step_m=1.0, yaw_deg=0.5, sigma=0.02, clutter=0.02)
-            out += q.frames
-        return out
+    import concurrent.futures as cf
 
-    t0 = time.perf_counter()
-    train_f = frames(range(args.train_seqs), 8)
-    eval_f = frames(range(1000, 1002), 8)
-    gen_s = time.perf_counter() - t0
+    def seq_frames(i, n):
+        return synth.sequence(sensor, n, synth.config_seed(4, i, 0), n_walls=20, n_boxes=40, n_poles=60,
+                              step_m=1.0, yaw_deg=0.5, sigma=0.02, clutter=0.02).frames
+
+    def frames(ids, n, pool):
+        return [f for fr in pool.map(lambda i: seq_frames(i, n), ids) for f in fr]
+
+    # training data: sequences of 8 frames (seeds of sequences 0.., disjoint from the evaluation's
+    # 1000..), rendered in parallel threads chunk by chunk; only the BF16 tile inputs and the labels
+    # of the plain GPU encoder stay (on the device)
     ctx = lcc.Context(sensor, lcc.default_params(tile_h=8, tile_w=8, fit_thr_m=0.05), stream=stream)
+    n_train_seq = max(1, args.train_frames // 8)
     X, Y = [], []
-    for f in train_f:
-        x, _, y, _ = TR.frame_examples(ctx, torch.from_numpy(f).cuda(), len(f))
-        X.append(x)
-        Y.append(y)
+    gen_s = label_s = 0.0
+    with cf.ThreadPoolExecutor(min(32, os.cpu_count() or 4)) as pool:
+        for a in range(0, n_train_seq, 32):
+            t0 = time.perf_counter()
+            chunk = frames(range(a, min(a + 32, n_train_seq)), 8, pool)
+            gen_s += time.perf_counter() - t0
+            t0 = time.perf_counter()
+            for f in chunk:
+                x, _, y, _ = TR.frame_examples(ctx, torch.from_numpy(f).cuda(), len(f))
+                X.append(x)
+                Y.append(y)
+            label_s += time.perf_counter() - t0
+        t0 = time.perf_counter()
+        eval_f = frames(range(1000, 1002), 8, pool)
+        gen_s += time.perf_counter() - t0
+    train_f_count = 8 * n_train_seq
     X, Y = torch.cat(X), torch.cat(Y)
     batch = 4096
     net = lcc.Net(TR.he_uniform_params(4), max_tiles=batch, stream=stream)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    losses = TR.train(net, X, Y, args.train_steps, batch, 2e-3, seed=1, lr_final=2e-4)
+    train_steps = args.train_steps if args.train_steps > 0 else max(300, int(X.shape[0]) // batch)   # one epoch
+    losses = TR.train(net, X, Y, train_steps, batch, 2e-3, seed=1, lr_final=2e-4)
     torch.cuda.synchronize()
     train_s = time.perf_counter() - t0
     nt = ctx.num_tiles
@@ -931,18 +947,18 @@ def run_learned(args, stream):
                  "frac": 7.2e6 * big / (inf_ms * 1e-3) / 1e12 / bf16_peak, "kernel": "k_net_fwd_tc (tcgen05)"}
     return {
         "workload": "HDL-64E key frames 64x2048, tiles 8x8, thr 0.05 m; net trained on "
-                    f"{len(train_f)} frames ({X.shape[0]} tiles) of the same scene family, evaluated on "
+                    f"{train_f_count} frames ({X.shape[0]} tiles) of the same scene family, evaluated on "
                     f"{len(eval_f)} held-out frames",
-        "train": {"steps": args.train_steps, "batch_tiles": batch, "seconds": train_s,
-                  "loss_first": float(losses[0]), "loss_last": float(np.mean(losses[-10:])),
-                  "tflops": 3 * 7.2e6 * batch * args.train_steps / train_s / 1e12},
+        "train": {"frames": train_f_count, "tiles": int(X.shape[0]), "steps": train_steps, "batch_tiles": batch,
+                  "seconds": train_s, "loss_first": float(losses[0]), "loss_last": float(np.mean(losses[-10:])),
+                  "tflops": 3 * 7.2e6 * batch * train_steps / train_s / 1e12},
         "net_flops_per_tile": 7.2e6,
         "inference": inference,
         "plain": stats["plain"], "learned": stats["learned"],
         "batched_16_frames": batched,
         "rounds_saved_frac": 1.0 - stats["learned"]["rounds"] / max(stats["plain"]["rounds"], 1),
         "bytes_ratio_learned_vs_plain": stats["learned"]["bytes"] / max(stats["plain"]["bytes"], 1),
-        "setup_s": {"generate": gen_s},
+        "setup_s": {"generate": gen_s, "label": label_s},
     }
 
 
@@ -1258,7 +1274,8 @@ def run_cfg5(args, stream, rank, world, dist):
                 "compression_ratio": 12.0 * total_pts / nbytes_, "bytes_per_step": nbytes_,
                 "max_decode_error_m": err,
                 "tile_modes": {"empty": st["tiles_empty"], "raw": st["tiles_raw"], "run_start": st["tiles_run_start"],
-                               "run_cont": st["tiles_run_cont"], "temporal": st["tiles_temporal"]},
+                               "run_cont": st["tiles_run_cont"], "temporal": st["tiles_temporal"],
+                               "temporal_cont": st["tiles_temporal_cont"]},
                 "fit_rounds_hist": st["fit_rounds"], "fit_rounds": sum(r * c for r, c in enumerate(st["fit_rounds"])),
                 "tiles_borderline": st["tiles_borderline"],
                 "hbm_path_frac": (16.0 * total_pts + nbytes_) / (ms * 1e-3) / 1e9 / hbm,
@@ -1392,7 +1409,7 @@ def run_hdl64(args, stream):
     ctx.lcc_set_profiling(False)
     launches_per_step = sum(v[0] for v in ktimes.values()) / args.steps
     # tile-mode split and fit rounds of the last step (library statistics, all frames)
-    modes = {"empty": 0, "raw": 0, "run_start": 0, "run_cont": 0, "temporal": 0}
+    modes = {"empty": 0, "raw": 0, "run_start": 0, "run_cont": 0, "temporal": 0, "temporal_cont": 0}
     rounds_hist = [0] * 8
     border = 0
     for f in range(n_frames):
@@ -1402,6 +1419,7 @@ def run_hdl64(args, stream):
         modes["run_start"] += st_f["tiles_run_start"]
         modes["run_cont"] += st_f["tiles_run_cont"]
         modes["temporal"] += st_f["tiles_temporal"]
+        modes["temporal_cont"] += st_f["tiles_temporal_cont"]
         rounds_hist = [a + b for a, b in zip(rounds_hist, st_f["fit_rounds"])]
         border += st_f["tiles_borderline"]
 

@@ -78,6 +78,13 @@ typedef struct {
                                  the distinct K tiles its valid pixels fall in after Eq. 6, in raster
                                  order from the anchor's, the first that passes kept; 1 (default):
                                  the anchor's K tile only */
+    int32_t temporal_runs;    /* 1 (default): P tiles that passed the relaxed-plane test grow runs to the
+                                 right like spatial runs (Sec. III-D applies the same horizontal growing
+                                 strategy): a following tile that passes the acceptance rule against
+                                 the run start's relaxed plane (n', c') joins the run (tile code
+                                 TEMPORAL_CONT = 5, no record of its own; header flags bit 3); spatial
+                                 runs stop at temporal tiles.  Needs merge_runs.  0: each temporal
+                                 tile carries its own record */
 } lcc_params;
 
 /* Per-frame statistics of the last encode (Fig. 11's categories and more). */
@@ -92,6 +99,7 @@ typedef struct {
     int64_t tiles_borderline; /* tiles with a residual within 1e-6 m of the threshold in some round */
     int64_t cand, fitted, raw;/* candidate, plane-coded and raw-coded pixels */
     uint64_t bytes;           /* stream size */
+    int64_t tiles_temporal_cont; /* tiles inside a temporal run (after its first tile) */
 } lcc_stats;
 
 /* Per-tile record (debug and parity checks): the tile's own fit results. */
@@ -122,8 +130,9 @@ typedef struct lcc_keyframe lcc_keyframe;
 const char *lcc_status_string(lcc_status s);
 
 /* Default parameters: 4x4 tiles, thr 0.05 m, q 0.02 m, 3 refits, f_min 0.75,
- * runs on, max_batch 16, lookahead 16, float-float solver, fit schedule 3 (one
- * round per thread, the few tiles needing more finish in one dense launch). */
+ * runs on (spatial and temporal), max_batch 16, lookahead 16, float-float
+ * solver, fit schedule 3 (one round per thread, the few tiles needing more
+ * finish in one dense launch). */
 void lcc_default_params(lcc_params *p);
 
 /* Create a context on the current device bound to cuda_stream (a

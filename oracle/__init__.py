@@ -20,7 +20,7 @@ _LIB_PATH = os.path.join(_HERE, "liblcc_oracle.so")
 _lock = threading.Lock()
 _lib = None
 
-T_EMPTY, T_RAW, T_RUN_START, T_RUN_CONT, T_TEMPORAL = range(5)
+T_EMPTY, T_RAW, T_RUN_START, T_RUN_CONT, T_TEMPORAL, T_TEMPORAL_CONT = range(6)
 FIT_EMPTY, FIT_FAIL, FIT_OK = range(3)
 OK, ERR_ARG, ERR_CORRUPT, ERR_CAPACITY, ERR_INCONSISTENT = 0, -1, -2, -3, -4
 
@@ -36,7 +36,7 @@ class Params(ctypes.Structure):
                 ("fit_thr_m", ctypes.c_float), ("quant_m", ctypes.c_float),
                 ("max_refits", ctypes.c_int32), ("min_inlier_frac", ctypes.c_float),
                 ("merge_runs", ctypes.c_int32), ("no_delta", ctypes.c_int32), ("raw_exact", ctypes.c_int32),
-                ("temporal_candidates", ctypes.c_int32)]
+                ("temporal_candidates", ctypes.c_int32), ("temporal_runs", ctypes.c_int32)]
 
 
 class TileFit(ctypes.Structure):
@@ -114,9 +114,9 @@ def sensor(s) -> Sensor:
 
 
 def params(tile_h=4, tile_w=4, fit_thr_m=0.05, quant_m=0.02, max_refits=3, min_inlier_frac=0.75,
-           merge_runs=1, no_delta=0, raw_exact=0, temporal_candidates=1) -> Params:
+           merge_runs=1, no_delta=0, raw_exact=0, temporal_candidates=1, temporal_runs=1) -> Params:
     return Params(tile_h, tile_w, fit_thr_m, quant_m, max_refits, min_inlier_frac, merge_runs, no_delta, raw_exact,
-                  temporal_candidates)
+                  temporal_candidates, temporal_runs)
 
 
 def n_tiles(s: Sensor, p: Params) -> int:

@@ -453,7 +453,8 @@ static int params_ok(const orc_sensor *s, const orc_params *p) {
     return sensor_ok(s) && p && p->tile_h >= 1 && p->tile_w >= 1 &&
            p->tile_h * p->tile_w <= MAX_TILE_PX && p->tile_h <= 255 && p->tile_w <= 255 &&
            p->fit_thr_m >= 0 && p->quant_m > 0 && p->max_refits >= 0 && p->min_inlier_frac >= 0 &&
-           p->temporal_candidates >= 0 && p->temporal_candidates <= 4;
+           p->temporal_candidates >= 0 && p->temporal_candidates <= 4 && p->temporal_runs >= 0 &&
+           p->temporal_runs <= 1;
 }
 
 int orc_fit_tiles(const orc_sensor *s, const orc_params *prm, const float *range, orc_tile_fit *out) {
@@ -722,7 +723,7 @@ static int header_read(const uint8_t *b, uint64_t nbytes, header_t *h) {
     h->n_raw = rd32(b + 48);
     h->k_max = (int32_t)rd32(b + 52);
     h->total_bytes = rd32(b + 56);
-    if (h->kind > 1 || (h->flags & ~7u) || h->tile_h == 0 || h->tile_w == 0 || h->w_res == 0 || h->w_res > 16 ||
+    if (h->kind > 1 || (h->flags & ~15u) || ((h->flags & 8u) && h->kind != 1) || h->tile_h == 0 || h->tile_w == 0 || h->w_res == 0 || h->w_res > 16 ||
         h->w_raw == 0 || ((h->flags & 4u) ? h->w_raw != 32 : h->w_raw > 24) || !(h->q > 0))
         return ORC_ERR_CORRUPT;
     uint64_t off[8];
@@ -742,11 +743,16 @@ static int tile_passes(const orc_params *prm, const tile_px_t *tp, const float p
  * Greedy horizontal run growth (Sec. III-C): a run starts at a tile whose own
  * fit succeeded and takes that plane; the next tile to the right joins while it
  * passes the acceptance rule against the run's plane (the plane "fit so far" is
- * not refit); on failure the process restarts at the failing tile.  Temporal
- * tiles of a P frame are already coded and end a run (Sec. III-D).  Then each
- * valid pixel, in canonical order (tiles row-major, raster inside a tile), is
- * coded against its tile's plane: fitted bit + residual code if it passes the
- * threshold, raw range code otherwise; pixels of raw tiles get raw codes.
+ * not refit); on failure the process restarts at the failing tile.  In a P
+ * frame the tiles that passed the relaxed-plane test are coded first
+ * (Sec. III-D): each ends any spatial run before it, and with temporal_runs it
+ * starts a temporal run that grows to the right by the same rule against its
+ * relaxed plane (n', c'), over any tile that passes it; the tiles left over are
+ * then coded spatially.  One left-to-right walk gives both: temporal runs take
+ * every tile they reach, and spatial runs never cross a temporal tile.  Then
+ * each valid pixel, in canonical order (tiles row-major, raster inside a tile),
+ * is coded against its tile's plane: fitted bit + residual code if it passes
+ * the threshold, raw range code otherwise; pixels of raw tiles get raw codes.
  */
 int64_t orc_pack(const orc_sensor *s, const orc_params *prm, int kind, const float *range,
                  const float *fit_plane, const uint8_t *fit_ok,
@@ -777,7 +783,16 @@ int64_t orc_pack(const orc_sensor *s, const orc_params *prm, int kind, const flo
                 mode[t] = ORC_T_TEMPORAL;
                 memcpy(&cp[4 * t], &temporal_plane[4 * t], 16);
                 if (!tile_passes(prm, tp, &cp[4 * t])) ret = ORC_ERR_INCONSISTENT;
-                j++;
+                int k = j + 1;
+                while (prm->merge_runs && prm->temporal_runs && k < TW) {
+                    int t2 = tr * TW + k;
+                    tile_gather(s, prm, &T, range, t2, tp);
+                    if (!tile_passes(prm, tp, &cp[4 * t])) break;
+                    mode[t2] = ORC_T_TEMPORAL_CONT;
+                    memcpy(&cp[4 * t2], &cp[4 * t], 16);
+                    k++;
+                }
+                j = k;
                 continue;
             }
             if (!fit_ok[t]) {
@@ -805,7 +820,8 @@ int64_t orc_pack(const orc_sensor *s, const orc_params *prm, int kind, const flo
 
     /* 2. counts */
     h.kind = kind;
-    h.flags = (prm->merge_runs ? 1u : 0u) | (prm->no_delta ? 2u : 0u) | (prm->raw_exact ? 4u : 0u);
+    h.flags = (prm->merge_runs ? 1u : 0u) | (prm->no_delta ? 2u : 0u) | (prm->raw_exact ? 4u : 0u) |
+              (kind == 1 && prm->merge_runs && prm->temporal_runs ? 8u : 0u);
     h.rows = s->rows;
     h.cols = s->cols;
     h.tile_h = prm->tile_h;
@@ -999,6 +1015,13 @@ static int stream_planes(const orc_sensor *s, const stream_t *st, const float *k
             break;
         case ORC_T_RUN_CONT:
             if (t % TW == 0 || (mode[t - 1] != ORC_T_RUN_START && mode[t - 1] != ORC_T_RUN_CONT))
+                return ORC_ERR_CORRUPT;
+            memcpy(&cp[4 * t], &cp[4 * (t - 1)], 16);
+            break;
+        case ORC_T_TEMPORAL_CONT:
+            /* continues the temporal run to its left (flags bit 3): the run start's plane */
+            if (!(st->h.flags & 8u) || t % TW == 0 ||
+                (mode[t - 1] != ORC_T_TEMPORAL && mode[t - 1] != ORC_T_TEMPORAL_CONT))
                 return ORC_ERR_CORRUPT;
             memcpy(&cp[4 * t], &cp[4 * (t - 1)], 16);
             break;

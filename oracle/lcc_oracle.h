@@ -16,7 +16,8 @@
  *                                 plane), planted outliers (rounds, inlier set).
  *   orc_temporal_tiles            pinned: pure translation (c' = d - n.T), P == K.
  *   orc_pack / orc_decode         pinned: decode error <= q/2, raw round trip,
- *                                 greedy-run invariants, re-encode identity.
+ *                                 greedy-run invariants (spatial and temporal runs),
+ *                                 re-encode identity.
  */
 #ifndef LCC_ORACLE_H
 #define LCC_ORACLE_H
@@ -47,10 +48,16 @@ typedef struct {
     int32_t temporal_candidates; /* K tiles a P tile's relaxed-plane test may try (1..4): the
                                     distinct K tiles its valid pixels fall in, raster order from
                                     the anchor's; 1 (or 0) = the anchor's K tile only */
+    int32_t temporal_runs;       /* 1: temporally coded tiles grow runs like spatial ones
+                                    (Sec. III-D: the same horizontal growing strategy): a tile
+                                    that passes the acceptance rule against the relaxed plane of
+                                    the temporal tile to its left joins that tile's run (tile code
+                                    TEMPORAL_CONT, no record of its own; header flags bit 3) */
 } orc_params;
 
 /* tile codes of the bitstream */
-enum { ORC_T_EMPTY = 0, ORC_T_RAW = 1, ORC_T_RUN_START = 2, ORC_T_RUN_CONT = 3, ORC_T_TEMPORAL = 4 };
+enum { ORC_T_EMPTY = 0, ORC_T_RAW = 1, ORC_T_RUN_START = 2, ORC_T_RUN_CONT = 3, ORC_T_TEMPORAL = 4,
+       ORC_T_TEMPORAL_CONT = 5 };
 /* own-fit status */
 enum { ORC_FIT_EMPTY = 0, ORC_FIT_FAIL = 1, ORC_FIT_OK = 2 };
 /* errors */

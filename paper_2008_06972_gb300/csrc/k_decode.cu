@@ -102,7 +102,8 @@ __global__ void __launch_bounds__(kPrepThreads) k_decode_prep(Geometry g, DecBat
         if (!bad) {
             for (int q = 0; q < 16; q++) s_h[q] = rd_u32(bits + 4 * q);
             const uint32_t kind = (s_h[1] >> 16) & 0xff, flags = s_h[1] >> 24;
-            bad |= s_h[0] != kMagic || (s_h[1] & 0xffff) != (uint32_t)kVersion || (flags & ~7u);
+            bad |= s_h[0] != kMagic || (s_h[1] & 0xffff) != (uint32_t)kVersion || (flags & ~15u) ||
+                   ((flags & 8u) && kind != 1);
             bad |= (int)(s_h[2] & 0xffff) != g.H || (int)(s_h[2] >> 16) != g.W;
             bad |= (int)(s_h[3] & 0xff) != g.th || (int)((s_h[3] >> 8) & 0xff) != g.tw;
             const uint32_t w_res = (s_h[3] >> 16) & 0xff, w_raw = s_h[3] >> 24;
@@ -138,7 +139,7 @@ __global__ void __launch_bounds__(kPrepThreads) k_decode_prep(Geometry g, DecBat
     const uint32_t *bm = w + s_sec[0], *tcw = w + s_sec[1], *runw = w + s_sec[2], *tmpw = w + s_sec[3],
                    *fitw = w + s_sec[4];
     const uint32_t n_runs = s_h[8], n_temp = s_h[9], n_cand = s_h[10];
-    const uint32_t kind = (s_h[1] >> 16) & 0xff;
+    const uint32_t kind = (s_h[1] >> 16) & 0xff, hflags = s_h[1] >> 24;
     int bad = 0;
     for (int base = 0; base < g.NT; base += kPrepThreads) {
         const int t = base + tid;
@@ -152,14 +153,16 @@ __global__ void __launch_bounds__(kPrepThreads) k_decode_prep(Geometry g, DecBat
                 if (i >= g.H) break;
                 nv += popc_range(bm, (uint64_t)i * g.W + j0, (uint32_t)wdt);
             }
-            if (mode > T_TEMPORAL) bad = 1;
+            if (mode > T_TEMPORAL_CONT) bad = 1;
             if (mode == T_EMPTY && nv) bad = 1;
-            if (mode == T_RUN_CONT) {
+            if (mode == T_RUN_CONT || mode == T_TEMPORAL_CONT) {   // continues the run to its left
                 const uint32_t pm = tc ? (tcw[(t - 1) >> 3] >> (4 * ((t - 1) & 7))) & 15u : 0u;
-                if (tc == 0 || (pm != T_RUN_START && pm != T_RUN_CONT)) bad = 1;
+                const bool ok = mode == T_RUN_CONT ? (pm == T_RUN_START || pm == T_RUN_CONT)
+                                                   : ((hflags & 8u) && (pm == T_TEMPORAL || pm == T_TEMPORAL_CONT));
+                if (tc == 0 || !ok) bad = 1;
             }
         }
-        const bool coded = mode >= T_RUN_START && mode <= T_TEMPORAL;
+        const bool coded = mode >= T_RUN_START && mode <= T_TEMPORAL_CONT;
         uint32_t v5[5] = {coded ? nv : 0u, mode == T_RUN_START ? 1u : 0u, mode == T_TEMPORAL ? 1u : 0u,
                           mode == T_RAW ? nv : 0u, nv};
         uint32_t e5[5], t5[5];
@@ -213,10 +216,11 @@ __global__ void __launch_bounds__(kPrepThreads) k_decode_prep(Geometry g, DecBat
             dt[t] = d;
         }
         __syncthreads();
-        // run continuations take the plane of the last run start at or before them
+        // run continuations (spatial or temporal) take the plane of the last run start at or before
+        // them: a continuation follows its own kind of start with only continuations between
         {
             __shared__ int s_ms[32];
-            int x = (t < g.NT && mode == T_RUN_START) ? t : -1;
+            int x = (t < g.NT && (mode == T_RUN_START || mode == T_TEMPORAL)) ? t : -1;
             const int lane = tid & 31, wp = tid >> 5;
 #pragma unroll
             for (int off = 1; off < 32; off <<= 1) {
@@ -236,7 +240,7 @@ __global__ void __launch_bounds__(kPrepThreads) k_decode_prep(Geometry g, DecBat
             }
             __syncthreads();
             const int start = max(max(x, wp ? s_ms[wp - 1] : -1), s_last_start);
-            if (t < g.NT && mode == T_RUN_CONT) {
+            if (t < g.NT && (mode == T_RUN_CONT || mode == T_TEMPORAL_CONT)) {
                 if (start < 0) bad = 1;
                 else dt[t].plane = dt[start].plane;
             }

@@ -1027,7 +1027,8 @@ __global__ void __launch_bounds__(kFitThreads) k_temporal(Geometry g, Scratch s,
 
 // Run pre-test, after every tile's own fit is final: tile t tests its own
 // pixels against the planes of the (up to `lookahead`) tiles to its left in
-// the row whose fit succeeded.  Bit j of the result (and count byte j) says
+// the row whose fit succeeded (and, with temporal runs, that passed the
+// temporal test: their plane is the relaxed one).  Bit j of the result (and count byte j) says
 // whether tile t would join a run started at tile t-1-j, i.e. passes that
 // plane under the acceptance rule (Sec. III-C run growth).
 //
@@ -1075,7 +1076,7 @@ __global__ void __launch_bounds__(kFitThreads) k_lookbehind(Geometry g, Scratch 
     if (l < ncand) {
         const TileRec *src = recs + (t - 1 - l);
         const uint32_t w0 = *reinterpret_cast<const uint32_t *>(reinterpret_cast<const uint8_t *>(src) + 40);
-        fitted = (w0 & 0xff) == S_FIT;
+        fitted = (w0 & 0xff) == S_FIT || (g.truns && (w0 & 0xff) == S_TEMPORAL);
     }
     const unsigned fmask = (__ballot_sync(gmask, fitted) & gmask) >> gbase;
     const int need = need_inliers(g.fmin, nv);

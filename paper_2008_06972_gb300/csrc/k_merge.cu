@@ -6,8 +6,10 @@
 // along a row, so everything around it is parallel: the followers'
 // look-behind bits (from the fit stage) decide the first `lookahead` joins of
 // a run in one ballot, and the walk itself is a pointer chase in shared
-// memory.  Temporal tiles of P frames are already coded (Sec. III-D) and end
-// a run.
+// memory.  Temporal tiles of P frames are coded first (Sec. III-D): each ends
+// the spatial run before it and starts a run of its own, which with temporal
+// runs grows to the right by the same rule against its relaxed plane, over any
+// tile that passes it (TEMPORAL_CONT); the walk treats both kinds of start alike.
 //
 // Output per tile: its stream mode, the tile whose plane codes it, its counts
 // of candidate / plane-coded / raw-coded pixels and their offsets within the
@@ -78,8 +80,8 @@ __global__ void __launch_bounds__(kMergeThreads) k_merge(Geometry g, Scratch s, 
     constexpr int kStepTiles = kMergeThreads / kEL;    // tiles tested per extension step
     const int TC = g.TC;
     RowRec *row = reinterpret_cast<RowRec *>(smem);
-    uint16_t *nextfit = reinterpret_cast<uint16_t *>(row + TC);   // TC + 1 entries
-    uint16_t *runend = nextfit + (TC + 1);                         // end of the run started at c, 0 if none
+    uint16_t *nextstart = reinterpret_cast<uint16_t *>(row + TC); // next run start (fitted or temporal tile), TC + 1 entries
+    uint16_t *runend = nextstart + (TC + 1);                         // end of the run started at c, 0 if none
     uint16_t *reach = runend + TC;                                 // look-behind reach of a fitted tile
     uint16_t *jmp = reach + TC;                                    // walk successor of a fitted tile (below)
     uint8_t *extcnt = reinterpret_cast<uint8_t *>(jmp + TC);       // counts of explicitly tested joins
@@ -126,19 +128,22 @@ __global__ void __launch_bounds__(kMergeThreads) k_merge(Geometry g, Scratch s, 
     }
     if (tid < 6) s_carry[tid] = 0;
     __syncthreads();
-    // (B) reach of every fitted tile: 1 + the number of its followers, from the next one on,
-    // whose look-behind bit for it is set (and that are not temporal); next fitted tile at or
-    // after c
+    // (B) reach of every run start (a fitted tile, or a temporal one): 1 + the number of its
+    // followers, from the next one on, whose look-behind bit for it is set (for a spatial start:
+    // and that are not temporal; a temporal start without temporal runs keeps to itself); next
+    // start at or after c
     for (int c = tid; c < TC; c += kMergeThreads) {
         int k = c + 1;
-        if (row[c].status == S_FIT) {
+        const uint8_t sc = row[c].status;
+        if (sc == S_FIT || (sc == S_TEMPORAL && g.truns)) {
+            const bool temp = sc == S_TEMPORAL;
             const int hz = min(hzmax, TC - 1 - c);
             uint32_t m = 0u;
 #pragma unroll 4
             for (int j = 0; j < hz; j++) {
                 // amask and the status byte of follower c + 1 + j in one 8-byte load
                 const uint2 w = *reinterpret_cast<const uint2 *>(&row[c + 1 + j].amask);
-                if (((w.x >> j) & 1u) && (w.y & 0xffu) != S_TEMPORAL) m |= 1u << j;
+                if (((w.x >> j) & 1u) && (temp || (w.y & 0xffu) != S_TEMPORAL)) m |= 1u << j;
             }
             k += (m == 0xFFFFFFFFu) ? 32 : __ffs(~m) - 1;   // consecutive joins from j = 0
         }
@@ -146,17 +151,17 @@ __global__ void __launch_bounds__(kMergeThreads) k_merge(Geometry g, Scratch s, 
     }
     if (warp == 0) {
         uint32_t carry = (uint32_t)TC;
-        if (lane == 0) nextfit[TC] = (uint16_t)TC;
+        if (lane == 0) nextstart[TC] = (uint16_t)TC;
         for (int base = ((TC - 1) / 32) * 32; base >= 0; base -= 32) {
             const int c = base + lane;
-            uint32_t v = (c < TC && row[c].status == S_FIT) ? (uint32_t)c : 0xFFFFu;
+            uint32_t v = (c < TC && (row[c].status == S_FIT || row[c].status == S_TEMPORAL)) ? (uint32_t)c : 0xFFFFu;
 #pragma unroll
             for (int off = 1; off < 32; off <<= 1) {
                 const uint32_t y = __shfl_down_sync(FULL, v, off);
                 if (lane + off < 32) v = min(v, y);
             }
             v = min(v, carry);
-            if (c < TC) nextfit[c] = (uint16_t)v;
+            if (c < TC) nextstart[c] = (uint16_t)v;
             carry = __shfl_sync(FULL, v, 0);
         }
     }
@@ -166,10 +171,11 @@ __global__ void __launch_bounds__(kMergeThreads) k_merge(Geometry g, Scratch s, 
     // row end), or the reach itself with bit 15 set when the run reaches past the horizon and
     // must be extended by explicit tests (TC < 32768: the row records fit in shared memory)
     for (int c = tid; c < TC; c += kMergeThreads) {
-        if (row[c].status != S_FIT) continue;
+        const uint8_t sc = row[c].status;
+        if (sc != S_FIT && sc != S_TEMPORAL) continue;
         const int k = reach[c];
-        const bool open = g.merge && k < TC && k - c - 1 >= hzmax;
-        jmp[c] = open ? (uint16_t)(0x8000 | k) : (uint16_t)(k < TC ? nextfit[k] : TC);
+        const bool open = g.merge && k < TC && k - c - 1 >= hzmax && (sc == S_FIT || g.truns);
+        jmp[c] = open ? (uint16_t)(0x8000 | k) : (uint16_t)(k < TC ? nextstart[k] : TC);
     }
     __syncthreads();
     // (C) the greedy walk.  Warp 0 follows the chain through the runs that end inside the
@@ -180,7 +186,7 @@ __global__ void __launch_bounds__(kMergeThreads) k_merge(Geometry g, Scratch s, 
         __shared__ uint32_t s_fail[kMergeThreads / 32];
         __shared__ int s_walk;   // walk position handed from warp 0 to the block
         bool staged = false;
-        int st = nextfit[0];
+        int st = nextstart[0];
         for (;;) {
             if (warp == 0) {
                 while (st < TC) {
@@ -247,9 +253,10 @@ __global__ void __launch_bounds__(kMergeThreads) k_merge(Geometry g, Scratch s, 
             }
             {
                 const float4 pl = row[st].plane;
+                const bool trun = row[st].status == S_TEMPORAL;   // a temporal run joins any tile
                 while (open) {
                     const int c2 = k + tid / kEL, l = tid % kEL;
-                    const bool cand = c2 < TC && row[c2].status != S_TEMPORAL;
+                    const bool cand = c2 < TC && (trun || row[c2].status != S_TEMPORAL);
                     int nin = 0;
                     if (cand) {
                         bool border = false;
@@ -291,13 +298,13 @@ __global__ void __launch_bounds__(kMergeThreads) k_merge(Geometry g, Scratch s, 
                 }
             }
             if (tid == 0) runend[st] = (uint16_t)k;
-            st = k < TC ? nextfit[k] : TC;
+            st = k < TC ? nextstart[k] : TC;
             __syncthreads();   // every thread has read s_walk before warp 0 writes it again
         }
     }
     __syncthreads();
     // (D) codes, counts and intra-row offsets (block scan in chunks of the block size)
-    uint32_t hist[5] = {0u, 0u, 0u, 0u, 0u}, rhist[8] = {0u, 0u, 0u, 0u, 0u, 0u, 0u, 0u}, border = 0;
+    uint32_t hist[6] = {0u, 0u, 0u, 0u, 0u, 0u}, rhist[8] = {0u, 0u, 0u, 0u, 0u, 0u, 0u, 0u}, border = 0;
     __shared__ int s_wmax[kMergeThreads / 32];
     __shared__ int s_last;
     if (tid == 0) s_last = -1;
@@ -324,30 +331,26 @@ __global__ void __launch_bounds__(kMergeThreads) k_merge(Geometry g, Scratch s, 
             if (!isstart && (stc < 0 || c >= (int)runend[stc])) stc = -1;
             uint32_t cand = 0, fit = 0, raw = 0, ptile = (uint32_t)(row0 + c);
             uint8_t mode;
-            if (isstart) {
-                mode = T_RUN_START;
+            if (isstart) {   // a run start: its own spatial plane, or its relaxed plane (temporal)
+                mode = h.status == S_TEMPORAL ? T_TEMPORAL : T_RUN_START;
                 cand = h.n_valid;
                 fit = h.n_inlier;
             } else if (stc >= 0) {
-                mode = T_RUN_CONT;
+                mode = row[stc].status == S_TEMPORAL ? T_TEMPORAL_CONT : T_RUN_CONT;
                 const int j = c - stc - 1;
                 cand = h.n_valid;
                 fit = j < hzmax ? (uint32_t)s.lbcnt[(slot * g.NT + row0 + c) * 32 + j] : extcnt[c];
                 ptile = (uint32_t)(row0 + stc);
-            } else if (h.status == S_TEMPORAL) {
-                mode = T_TEMPORAL;
-                cand = h.n_valid;
-                fit = h.n_inlier;
             } else {
                 mode = h.n_valid ? T_RAW : T_EMPTY;
                 raw = h.n_valid;
             }
             if (mode >= T_RUN_START) raw = cand - fit;
-            const float4 cpl = (mode == T_RUN_START || mode == T_RUN_CONT) ? row[stc].plane
-                               : (mode == T_TEMPORAL ? h.plane : make_float4(0.f, 0.f, 0.f, 0.f));
+            const float4 cpl = mode >= T_RUN_START ? row[stc].plane : make_float4(0.f, 0.f, 0.f, 0.f);
             put_code(codes, row0 + c, mode, (int)cand, (int)fit, (int)raw, ptile, h.kref, cpl);
-            if (kfo) kfo[row0 + c] = mode == T_TEMPORAL ? make_float4(0.f, 0.f, 0.f, 0.f) : cpl;
-            v[0] = cand; v[1] = fit; v[2] = raw; v[3] = isstart; v[4] = mode == T_TEMPORAL; v[5] = h.n_valid;
+            if (kfo) kfo[row0 + c] = (mode == T_RUN_START || mode == T_RUN_CONT) ? cpl : make_float4(0.f, 0.f, 0.f, 0.f);
+            v[0] = cand; v[1] = fit; v[2] = raw; v[3] = mode == T_RUN_START; v[4] = mode == T_TEMPORAL;
+            v[5] = h.n_valid;
             hist[mode]++;
             rhist[min((uint32_t)h.rounds, 7u)]++;
             border += h.flags & 1u;
@@ -388,14 +391,14 @@ __global__ void __launch_bounds__(kMergeThreads) k_merge(Geometry g, Scratch s, 
 #pragma unroll
     for (int off = 16; off; off >>= 1) {
 #pragma unroll
-        for (int q = 0; q < 5; q++) hist[q] += __shfl_xor_sync(FULL, hist[q], off);
+        for (int q = 0; q < 6; q++) hist[q] += __shfl_xor_sync(FULL, hist[q], off);
 #pragma unroll
         for (int q = 0; q < 8; q++) rhist[q] += __shfl_xor_sync(FULL, rhist[q], off);
         border += __shfl_xor_sync(FULL, border, off);
     }
     if (lane == 0) {
         DevStats *stt = s.stats + slot;
-        for (int q = 0; q < 5; q++)
+        for (int q = 0; q < 6; q++)   // empty, raw, run start, run continuation, temporal, temporal continuation
             if (hist[q]) atomicAdd(&(&stt->empty)[q], (unsigned long long)hist[q]);
         for (int q = 0; q < 8; q++)
             if (rhist[q]) atomicAdd(&stt->rounds[q], (unsigned long long)rhist[q]);

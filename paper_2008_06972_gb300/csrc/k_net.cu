@@ -239,7 +239,7 @@ __global__ void k_net_inputs(Geometry g, uint32_t *rimg0, bf16 *x0, float4 *anch
 
 // ------------------------------------------------------------------ forward on tcgen05 --
 //
-// Two tiles per step: M = 128 GEMM rows ordered (tile row y, tile, pixel x),
+// Two tiles per MMA: M = 128 GEMM rows ordered (tile row y, tile, pixel x),
 // so that every 8-row core matrix of A is 8 consecutive pixels of one row of
 // one tile.  Activations live in shared memory as [channel/8][y 0..9][tile][x
 // 0..9][8 channels] with a zero border, i.e. K-major core matrices whose
@@ -247,20 +247,23 @@ __global__ void k_net_inputs(Geometry g, uint32_t *rimg0, bf16 *x0, float4 *anch
 // descriptor started (ky*20 + kx)*16 bytes further, so the nine taps of a
 // convolution are nine accumulating MMAs per 16 input channels, with no im2col.
 // One thread issues tcgen05.mma into a 128-lane x 64-column fp32 TMEM
-// accumulator; the four warps read their 32 lanes back (tcgen05.ld) for the
+// accumulator; epilogue warps read their 32 lanes back (tcgen05.ld) for the
 // bias/ReLU/BF16 epilogue into the next layer's copy.
 
 constexpr int TPOS = 10 * 2 * 10;              // padded positions per 8-channel chunk
 constexpr int TCHUNK = TPOS * 16;              // bytes per chunk (3200)
 constexpr int TW1 = 9 * 2 * C1 * 16, TW2 = 9 * (C1 / 8) * C2 * 16, TW3 = 9 * (C2 / 8) * C3 * 16;
-constexpr int TX = 2 * TCHUNK, TA1 = (C1 / 8) * TCHUNK, TA2 = (C2 / 8) * TCHUNK;
-constexpr int TSLOT = TX + TA1 + TA2;           // activation copies of one pair of tiles
-constexpr int kTcWarps = 8;                     // two warps per TMEM lane quadrant (column halves)
+// One activation buffer per pair slot, shared by the layer input (2 chunks: 4 channels and
+// zeros), the first activations (4 chunks) and the second (8 chunks): each is dead once the
+// convolution reading it has committed, which is before the next one is written.
+constexpr int TACT = (C2 / 8) * TCHUNK;
+constexpr int kTcSlots = 3;                     // pairs of tiles in flight per CTA
 constexpr int TGP = 4 * 2 * C3 * 4, TG = 2 * C3 * 4;
 constexpr int TPAR = (C1 + C2 + C3 + HID * C3 + HID + NOUT * HID + NOUT + 3) / 4 * 16;   // biases, head (fp32)
-constexpr size_t kTcSmem = (size_t)TW1 + TW2 + TW3 + 2 * (size_t)(TSLOT + TGP + TG) + TPAR + 64;   // + 5 barriers
-constexpr uint32_t kTmemCols = 128;             // two 64-column accumulators, one per pair in flight
+constexpr size_t kTcSmem = (size_t)TW1 + TW2 + TW3 + kTcSlots * (size_t)(TACT + TGP + TG) + TPAR + 128;   // + barriers
+constexpr uint32_t kTmemCols = 256;             // one 64-column accumulator per pair slot (3 x 64, rounded up)
 constexpr long long kSpinLimit = 1ll << 22;
+static_assert(kTcSmem <= 227 * 1024, "shared memory of the tcgen05 forward");
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -315,6 +318,15 @@ __device__ __forceinline__ void tc_ld16(uint32_t taddr, float (&v)[16]) {
     for (int i = 0; i < 16; i++) v[i] = __uint_as_float(r[i]);
 }
 
+__device__ __forceinline__ void tc_ld8(uint32_t taddr, float (&v)[8]) {
+    uint32_t r[8];
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];\n"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+                 : "r"(taddr));
+#pragma unroll
+    for (int i = 0; i < 8; i++) v[i] = __uint_as_float(r[i]);
+}
+
 __device__ __forceinline__ void tc_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory"); }
 __device__ __forceinline__ void tc_before_sync() { asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory"); }
 __device__ __forceinline__ void tc_after_sync() { asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory"); }
@@ -350,51 +362,61 @@ __device__ __forceinline__ void bulk_g2s(uint32_t dst, const void *src, uint32_t
                  : "memory");
 }
 
-// Warp-specialised: eight epilogue warps (two per TMEM lane quadrant, a column half each)
-// and one MMA warp.  Two pairs of tiles are in flight in separate activation copies and TMEM
-// accumulators; for each pair slot, an mbarrier armed by tcgen05.commit hands a finished
-// layer to the epilogue warps, and an mbarrier the epilogue warps arrive on hands the
-// next layer's input (and the emptied accumulator) back to the MMA warp.  No CTA-wide
-// barrier sits between layers, so the tensor cores run one pair's layer while the epilogue
-// warps finish the other's.
-constexpr int kTcParts = 2;                       // epilogue warps per TMEM lane quadrant (column parts)
-constexpr int kTcEpiWarps = 4 * kTcParts;
+// Warp-specialised: kTcSlots pair slots, each with its own group of four epilogue warps (one
+// per TMEM lane quadrant), its activation buffer and its 64 TMEM columns, and one MMA warp.
+// A group runs its own pairs of tiles (the CTA's pairs s, s + 3, s + 6, ...) through input,
+// three convolutions, pooling and head; an mbarrier the group arrives on hands a layer's input
+// (and the emptied accumulator) to the MMA warp, and an mbarrier armed by tcgen05.commit hands
+// the finished layer back.  The MMA warp serves whichever slot is ready, so one pair's
+// epilogue, pooling and head overlap the other pairs' convolutions.
+constexpr int kTcEpiWarps = 4 * kTcSlots;
 constexpr int kTcThreads = (kTcEpiWarps + 1) * 32;
 
 __device__ __forceinline__ void mbar_arrive(uint32_t mbar) {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(mbar) : "memory");
 }
-__device__ __forceinline__ void epi_sync() { asm volatile("bar.sync 1, %0;\n" ::"n"(kTcEpiWarps * 32) : "memory"); }
+__device__ __forceinline__ bool mbar_try(uint32_t mbar, uint32_t parity) {
+    uint32_t done;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}\n"
+        : "=r"(done)
+        : "r"(mbar), "r"(parity)
+        : "memory");
+    return done != 0;
+}
+// barrier of one slot's four epilogue warps (ids 1..kTcSlots; 0 is __syncthreads)
+__device__ __forceinline__ void group_sync(int slot) {
+    asm volatile("bar.sync %0, 128;\n" ::"r"(slot + 1) : "memory");
+}
 
 template <bool kTrain>
 __global__ void __launch_bounds__(kTcThreads, 1) k_net_fwd_tc(NetDev nd, const bf16 *x, long long T, float *out,
                                                               int *err, NetAct act) {
     extern __shared__ __align__(1024) uint8_t sm[];
     uint8_t *sW1 = sm, *sW2 = sW1 + TW1, *sW3 = sW2 + TW2;
-    uint8_t *sSlot = sW3 + TW3;                                        // [2][TSLOT]
-    float *sGP = reinterpret_cast<float *>(sSlot + 2 * TSLOT);         // [2][quadrant][tile][64]
-    float *sG = sGP + 2 * 4 * 2 * C3;                                  // [2][tile][64]
-    float *sPar = sG + 2 * 2 * C3;                                     // b1 b2 b3 F1b c1 F2b c2
+    uint8_t *sAct = sW3 + TW3;                                         // [slot][TACT]
+    float *sGP = reinterpret_cast<float *>(sAct + kTcSlots * TACT);    // [slot][quadrant][tile][64]
+    float *sG = sGP + kTcSlots * 4 * 2 * C3;                           // [slot][tile][64]
+    float *sPar = sG + kTcSlots * 2 * C3;                              // b1 b2 b3 F1b c1 F2b c2
     float *sB1 = sPar, *sB2 = sB1 + C1, *sB3 = sB2 + C2, *sF1 = sB3 + C3, *sC1 = sF1 + HID * C3;
     float *sF2 = sC1 + HID, *sC2 = sF2 + NOUT * HID;
-    // barriers: [0] weights, [1 + s] layer done (tcgen05.commit), [3 + s] layer input ready (epilogue)
+    // barriers: [0] weights, [1 + s] layer done (tcgen05.commit), [1 + kTcSlots + s] layer input ready
     uint64_t *bar = reinterpret_cast<uint64_t *>(reinterpret_cast<uint8_t *>(sPar) + TPAR);
-    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bar + 5);
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bar + 1 + 2 * kTcSlots);
     int *s_fail = reinterpret_cast<int *>(tmem_slot + 1);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const float *th = nd.theta;
     if (tid == 0) {
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(bar)) : "memory");
-        for (int i = 1; i < 3; i++)
+        for (int i = 0; i < 1 + kTcSlots; i++)
             asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(bar + i)) : "memory");
-        for (int i = 3; i < 5; i++)
-            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_u32(bar + i)), "n"(kTcEpiWarps)
-                         : "memory");
+        for (int i = 1 + kTcSlots; i < 1 + 2 * kTcSlots; i++)
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 4;\n" ::"r"(smem_u32(bar + i)) : "memory");
         *s_fail = 0;
     }
     {
-        uint4 *z = reinterpret_cast<uint4 *>(sSlot);
-        for (int i = tid; i < 2 * TSLOT / 16; i += blockDim.x) z[i] = make_uint4(0u, 0u, 0u, 0u);
+        uint4 *z = reinterpret_cast<uint4 *>(sAct);
+        for (int i = tid; i < kTcSlots * TACT / 16; i += blockDim.x) z[i] = make_uint4(0u, 0u, 0u, 0u);
         for (int i = tid; i < C1; i += blockDim.x) sB1[i] = th[OB1 + i];
         for (int i = tid; i < C2; i += blockDim.x) sB2[i] = th[OB2 + i];
         for (int i = tid; i < C3; i += blockDim.x) sB3[i] = th[OB3 + i];
@@ -427,142 +449,141 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_net_fwd_tc(NetDev nd, const b
     __syncthreads();
     tc_after_sync();
     const uint32_t tmem = *tmem_slot;
-    auto slot_x = [&](int sl) { return sSlot + sl * TSLOT; };
-    // a bounded wait that gives up at once after any earlier wait expired
-    auto wait = [&](uint32_t mbar, uint32_t parity) {
-        if (*(volatile int *)s_fail) return;
-        if (!mbar_wait(mbar, parity)) {
-            atomicExch(s_fail, 1);
-            if (err) atomicExch(err, 1);
-        }
-    };
     const long long G = gridDim.x;
     if (warp == kTcEpiWarps) {
-        // ---- MMA warp: one lane issues every convolution of both pair slots ----
-        uint32_t ph = 0u;   // bit s: parity of slot s's next wait (no per-thread arrays: no local memory)
-        const uint32_t aW1 = smem_u32(sW1), aW2 = smem_u32(sW2), aW3 = smem_u32(sW3);
-        for (long long pa = blockIdx.x; pa * 2 < T; pa += 2 * G) {
-            const bool hasB = (pa + G) * 2 < T;
-#pragma unroll 1
-            for (int layer = 0; layer < 3; layer++) {
-#pragma unroll 1
-                for (int sl = 0; sl < (hasB ? 2 : 1); sl++) {
-                    if (lane == 0) {
-                        wait(smem_u32(bar + 3 + sl), (ph >> sl) & 1u);
-                        tc_after_sync();
-                        const uint32_t base = smem_u32(slot_x(sl));
-                        const uint32_t d = tmem + (uint32_t)(sl * 64);
-                        if (layer == 0) tc_conv<C0, C1>(d, base, aW1);
-                        else if (layer == 1) tc_conv<C1, C2>(d, base + TX, aW2);
-                        else tc_conv<C2, C3>(d, base + TX + TA1, aW3);
-                        tc_commit(smem_u32(bar + 1 + sl));
-                    }
+        // ---- MMA warp: one lane issues the convolutions of every slot, whichever is ready ----
+        if (lane == 0) {
+            const uint32_t aW1 = smem_u32(sW1), aW2 = smem_u32(sW2), aW3 = smem_u32(sW3);
+            long long pa[kTcSlots];
+            int layer[kTcSlots];
+            uint32_t ph = 0u;   // bit s: parity of slot s's next input-ready wait
+            int live = 0;
+#pragma unroll
+            for (int sl = 0; sl < kTcSlots; sl++) {
+                pa[sl] = blockIdx.x + sl * G;
+                layer[sl] = 0;
+                live += pa[sl] * 2 < T ? 1 : 0;
+            }
+            long long idle = 0;
+            while (live > 0 && !*(volatile int *)s_fail) {
+                bool progressed = false;
+#pragma unroll
+                for (int sl = 0; sl < kTcSlots; sl++) {
+                    if (pa[sl] * 2 >= T || !mbar_try(smem_u32(bar + 1 + kTcSlots + sl), (ph >> sl) & 1u)) continue;
                     ph ^= 1u << sl;
-                    __syncwarp();
+                    tc_after_sync();
+                    const uint32_t base = smem_u32(sAct + sl * TACT);
+                    const uint32_t d = tmem + (uint32_t)(sl * 64);
+                    if (layer[sl] == 0) tc_conv<C0, C1>(d, base, aW1);
+                    else if (layer[sl] == 1) tc_conv<C1, C2>(d, base, aW2);
+                    else tc_conv<C2, C3>(d, base, aW3);
+                    tc_commit(smem_u32(bar + 1 + sl));
+                    if (++layer[sl] == 3) {
+                        layer[sl] = 0;
+                        pa[sl] += kTcSlots * G;
+                        if (pa[sl] * 2 >= T) live--;
+                    }
+                    progressed = true;
+                }
+                idle = progressed ? 0 : idle + 1;
+                if (idle > kSpinLimit) {   // nothing became ready for too long: give up, report
+                    atomicExch(s_fail, 1);
+                    if (err) atomicExch(err, 1);
                 }
             }
         }
+        __syncwarp();
     } else {
-        // ---- epilogue warps: row = 32 (warp % 4) + lane -> (y, tile, x); column part = warp / 4 ----
-        const int quad = warp & 3, part = warp >> 2;
+        // ---- epilogue group of slot sl: row = 32 quad + lane -> (y, tile, x) ----
+        const int sl = warp >> 2, quad = warp & 3;
         const int row = quad * 32 + lane, grp = row >> 3, px = row & 7, py = grp >> 1, tl = grp & 1;
+        const int gt = tid - sl * 128;   // thread index within the group
+        uint8_t *buf = sAct + sl * TACT;
+        const uint32_t bar_done = smem_u32(bar + 1 + sl), bar_in = smem_u32(bar + 1 + kTcSlots + sl);
         uint32_t ph = 0u;
-        auto handoff = [&](int sl) {   // this warp's part of slot sl is written: hand it to the MMA warp
+        auto wait = [&](uint32_t mbar, uint32_t parity) {   // bounded; gives up at once after any expiry
+            if (*(volatile int *)s_fail) return;
+            if (!mbar_wait(mbar, parity)) {
+                atomicExch(s_fail, 1);
+                if (err) atomicExch(err, 1);
+            }
+        };
+        auto handoff = [&]() {   // this warp's rows of the slot's next input are written
             proxy_fence();
             tc_before_sync();
             __syncwarp();
-            if (lane == 0) mbar_arrive(smem_u32(bar + 3 + sl));
+            if (lane == 0) mbar_arrive(bar_in);
         };
-        for (long long pa = blockIdx.x; pa * 2 < T; pa += 2 * G) {
-            const bool hasB = (pa + G) * 2 < T;
-            if (part < 2 && (part == 0 || hasB)) {   // inputs (4 channels + 4 zero): part p fills slot p
-                const long long tile = (pa + part * G) * 2 + tl;
+        const uint32_t trow = tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(sl * 64);
+        float *gp = sGP + sl * 4 * 2 * C3;
+        float *gs = sG + sl * 2 * C3;
+        for (long long pa = blockIdx.x + sl * G; pa * 2 < T; pa += kTcSlots * G) {
+            {   // input: 4 channels and 4 zeros in chunk 0, zeros in chunk 1 (the 16 channels of a k-step)
+                const long long tile = pa * 2 + tl;
                 uint2 v = make_uint2(0u, 0u);
                 if (tile < T) v = *reinterpret_cast<const uint2 *>(x + ((size_t)tile * kPX + py * 8 + px) * C0);
-                *reinterpret_cast<uint4 *>(slot_x(part) + tpos(0, py + 1, tl, px + 1)) = make_uint4(v.x, v.y, 0u, 0u);
+                *reinterpret_cast<uint4 *>(buf + tpos(0, py + 1, tl, px + 1)) = make_uint4(v.x, v.y, 0u, 0u);
+                *reinterpret_cast<uint4 *>(buf + tpos(1, py + 1, tl, px + 1)) = make_uint4(0u, 0u, 0u, 0u);
             }
-            for (int sl = 0; sl < (hasB ? 2 : 1); sl++) handoff(sl);
+            handoff();
+            const long long tile = pa * 2 + tl;
 #pragma unroll 1
             for (int layer = 0; layer < 3; layer++) {
+                wait(bar_done, ph);
+                ph ^= 1u;
+                tc_after_sync();
+                const int cout = layer == 0 ? C1 : C2;
+                const float *bias = layer == 0 ? sB1 : layer == 1 ? sB2 : sB3;
 #pragma unroll 1
-                for (int sl = 0; sl < (hasB ? 2 : 1); sl++) {
-                    wait(smem_u32(bar + 1 + sl), (ph >> sl) & 1u);
-                    ph ^= 1u << sl;
-                    tc_after_sync();
-                    const int cout = layer == 0 ? C1 : C2;
-                    const float *bias = layer == 0 ? sB1 : layer == 1 ? sB2 : sB3;
-                    uint8_t *dst = slot_x(sl) + (layer == 0 ? TX : TX + TA1);
-                    const uint32_t trow = tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(sl * 64);
-                    float *gp = sGP + sl * 4 * 2 * C3;
-                    const int cw = cout / kTcParts < 16 ? 16 : cout / kTcParts;   // 16-column loads
-                    const int cbeg = part * cw, cend = cbeg + cw < cout ? cbeg + cw : cout;
-#pragma unroll 1
-                    for (int c0 = cbeg; c0 < cend; c0 += 16) {
-                        float v[16];
-                        tc_ld16(trow + (uint32_t)c0, v);
-                        tc_wait_ld();
+                for (int c0 = 0; c0 < cout; c0 += 8) {   // 8 columns per load: 13 warps need <= 128 registers
+                    float v[8];
+                    tc_ld8(trow + (uint32_t)c0, v);
+                    tc_wait_ld();
 #pragma unroll
-                        for (int i = 0; i < 16; i++) v[i] = fmaxf(v[i] + bias[c0 + i], 0.f);
-                        const long long tile = (pa + sl * G) * 2 + tl;
-                        if (kTrain && tile < T) {   // activations for the backward pass: [tile][pixel][channel]
-                            bf16 *ao = layer == 0 ? act.a1 + ((size_t)tile * kPX + py * 8 + px) * C1
-                                                  : (layer == 1 ? act.a2 : act.a3) + ((size_t)tile * kPX + py * 8 + px) * C2;
-                            uint32_t w[8];
+                    for (int i = 0; i < 8; i++) v[i] = fmaxf(v[i] + bias[c0 + i], 0.f);
+                    uint32_t w[4];
 #pragma unroll
-                            for (int q = 0; q < 8; q++) {
-                                const __nv_bfloat162 b2 = __floats2bfloat162_rn(v[2 * q], v[2 * q + 1]);
-                                w[q] = *reinterpret_cast<const uint32_t *>(&b2);
-                            }
-                            *reinterpret_cast<uint4 *>(ao + c0) = make_uint4(w[0], w[1], w[2], w[3]);
-                            *reinterpret_cast<uint4 *>(ao + c0 + 8) = make_uint4(w[4], w[5], w[6], w[7]);
-                        }
-                        if (layer < 2) {
+                    for (int q = 0; q < 4; q++) {
+                        const __nv_bfloat162 b2 = __floats2bfloat162_rn(v[2 * q], v[2 * q + 1]);
+                        w[q] = *reinterpret_cast<const uint32_t *>(&b2);
+                    }
+                    if (kTrain && tile < T) {   // activations for the backward pass: [tile][pixel][channel]
+                        bf16 *ao = layer == 0 ? act.a1 + ((size_t)tile * kPX + py * 8 + px) * C1
+                                              : (layer == 1 ? act.a2 : act.a3) + ((size_t)tile * kPX + py * 8 + px) * C2;
+                        *reinterpret_cast<uint4 *>(ao + c0) = make_uint4(w[0], w[1], w[2], w[3]);
+                    }
+                    if (layer < 2) {   // the next layer's input, in place of this layer's (already read)
+                        *reinterpret_cast<uint4 *>(buf + tpos(c0 / 8, py + 1, tl, px + 1)) = make_uint4(w[0], w[1], w[2], w[3]);
+                    } else {   // pooling: the 16 pixels of a tile in this quadrant, per channel
 #pragma unroll
-                            for (int h = 0; h < 2; h++) {
-                                uint32_t w[4];
-#pragma unroll
-                                for (int q = 0; q < 4; q++) {
-                                    const __nv_bfloat162 b2 =
-                                        __floats2bfloat162_rn(v[8 * h + 2 * q], v[8 * h + 2 * q + 1]);
-                                    w[q] = *reinterpret_cast<const uint32_t *>(&b2);
-                                }
-                                *reinterpret_cast<uint4 *>(dst + tpos(c0 / 8 + h, py + 1, tl, px + 1)) =
-                                    make_uint4(w[0], w[1], w[2], w[3]);
-                            }
-                        } else {
-#pragma unroll
-                            for (int i = 0; i < 16; i++) {
-                                float s2 = bfround(v[i]);
-                                s2 += __shfl_xor_sync(0xffffffffu, s2, 1);
-                                s2 += __shfl_xor_sync(0xffffffffu, s2, 2);
-                                s2 += __shfl_xor_sync(0xffffffffu, s2, 4);
-                                s2 += __shfl_xor_sync(0xffffffffu, s2, 16);
-                                if (lane == 0 || lane == 8) gp[(quad * 2 + tl) * C3 + c0 + i] = s2;
-                            }
+                        for (int i = 0; i < 8; i++) {
+                            float s2 = bfround(v[i]);
+                            s2 += __shfl_xor_sync(0xffffffffu, s2, 1);
+                            s2 += __shfl_xor_sync(0xffffffffu, s2, 2);
+                            s2 += __shfl_xor_sync(0xffffffffu, s2, 4);
+                            s2 += __shfl_xor_sync(0xffffffffu, s2, 16);
+                            if (lane == 0 || lane == 8) gp[(quad * 2 + tl) * C3 + c0 + i] = s2;
                         }
                     }
-                    if (layer < 2) handoff(sl);   // the next layer's input is in place, the accumulator is read
-                    else tc_before_sync();
                 }
+                if (layer < 2) handoff();   // the next layer's input is in place, the accumulator is read
+                else tc_before_sync();
             }
-            epi_sync();
-            if (tid < 256) {   // pooled vectors (fixed order over the lane quadrants): thread -> (slot, tile, channel)
-                const int sl = tid >> 7, t2 = (tid >> 6) & 1, c = tid & 63;
-                if (sl == 0 || hasB) {
-                    const float *gp = sGP + sl * 4 * 2 * C3;
-                    float s2 = 0.f;
-                    for (int w = 0; w < 4; w++) s2 += gp[(w * 2 + t2) * C3 + c];
-                    sG[(sl * 2 + t2) * C3 + c] = bfround(s2 * (1.0f / kPX));
-                }
+            group_sync(sl);
+            {   // pooled vectors (fixed order over the lane quadrants): thread -> (tile, channel)
+                const int t2 = gt >> 6, c = gt & 63;
+                float s2 = 0.f;
+                for (int w = 0; w < 4; w++) s2 += gp[(w * 2 + t2) * C3 + c];
+                gs[t2 * C3 + c] = bfround(s2 * (1.0f / kPX));
             }
-            epi_sync();
-            if (warp < 4) {   // head: warp w < 4 takes tile (w & 1) of pair slot (w >> 1)
-                const int sl = warp >> 1, t2 = warp & 1;
-                const long long tile = (pa + sl * G) * 2 + t2;
-                if ((sl == 0 || hasB) && tile < T) {
-                    const float *gs = sG + (sl * 2 + t2) * C3;
+            group_sync(sl);
+            if (quad < 2) {   // head: warp quad < 2 of the group takes tile quad of the pair
+                const int t2 = quad;
+                const long long ht = pa * 2 + t2;
+                if (ht < T) {
+                    const float *g2 = gs + t2 * C3;
                     float yv = sC1[lane];
-                    for (int c = 0; c < C3; c++) yv = fmaf(sF1[lane * C3 + c], gs[c], yv);
+                    for (int c = 0; c < C3; c++) yv = fmaf(sF1[lane * C3 + c], g2[c], yv);
                     const float hj = bfround(fmaxf(yv, 0.f));
                     float o[NOUT];
 #pragma unroll
@@ -572,12 +593,12 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_net_fwd_tc(NetDev nd, const b
                         for (int off = 16; off; off >>= 1) sacc += __shfl_xor_sync(0xffffffffu, sacc, off);
                         o[i] = sacc + sC2[i];
                     }
-                    if (lane < NOUT) out[(size_t)tile * NOUT + lane] = o[lane];
+                    if (lane < NOUT) out[(size_t)ht * NOUT + lane] = o[lane];
                     if (kTrain) {
-                        act.h[(size_t)tile * HID + lane] = hj;
-                        act.g[(size_t)tile * C3 + lane] = gs[lane];
-                        act.g[(size_t)tile * C3 + lane + 32] = gs[lane + 32];
-                        if (lane < NOUT) act.o[(size_t)tile * NOUT + lane] = o[lane];
+                        act.h[(size_t)ht * HID + lane] = hj;
+                        act.g[(size_t)ht * C3 + lane] = g2[lane];
+                        act.g[(size_t)ht * C3 + lane + 32] = g2[lane + 32];
+                        if (lane < NOUT) act.o[(size_t)ht * NOUT + lane] = o[lane];
                     }
                 }
             }

@@ -16,19 +16,23 @@
 namespace lcc {
 
 constexpr int kPackWarps = 8;
-constexpr int kStageWords = 128;   // shared staging words per warp
 
-// Lanes per tile: an eighth of the tile's pixels (at least 4 lanes, at most a warp), so every
-// lane codes several pixels whose loads are in flight together: the kernel waits on memory,
-// and more pixels per warp keep more loads in flight per resident warp (measured on 128x4096
-// frames: 2, 4 and 8 pixels per lane gave 8.9, 11.0 and 11.7 Gpoints/s for the whole plan).
+// Lanes per tile: an eighth of the tile's pixels (at least 4 lanes and a tile row, at most a
+// warp), so every lane codes several pixels whose loads are in flight together: the kernel waits
+// on memory, and more pixels per warp keep more loads in flight per resident warp (measured on
+// 128x4096 frames: 2, 4 and 8 pixels per lane gave 8.9, 11.0 and 11.7 Gpoints/s for the whole
+// plan).  A tile row's pixels must lie in one lane segment (the occupancy-bitmap step takes a
+// row from one ballot).  Each segment stages its codes in SW shared words: one section of the
+// tile's codes at up to 32 bits each (raw_exact) plus the partial words at both ends.
 template <int TH_, int TW_>
 struct PShape {
     static constexpr int PX = TH_ * TW_;
-    static constexpr int LPT = PX / 8 < 4 ? 4 : (PX / 8 < 32 ? PX / 8 : 32);
+    static constexpr int LPT0 = PX / 8 < 4 ? 4 : (PX / 8 < 32 ? PX / 8 : 32);
+    static constexpr int LPT = LPT0 < TW_ ? TW_ : LPT0;
     static constexpr int PPL = PX / LPT;
     static constexpr int TPW = 32 / LPT;
-    static constexpr int SW = kStageWords / TPW;   // staging words per segment
+    static constexpr int SW = (PX + 2 + 3) / 4 * 4;   // staging words per segment
+    static_assert(LPT <= 32 && PX % LPT == 0 && LPT % TW_ == 0, "lane segments");
 };
 
 // Write `count` codes of `width` bits, code index base0 + rank, into `sec`.
@@ -68,7 +72,7 @@ template <int TH_, int TW_>
 __global__ void __launch_bounds__(kPackWarps * 32) k_pack(Geometry g, Scratch s, Batch b) {
     using S = PShape<TH_, TW_>;
     constexpr int LPT = S::LPT, PPL = S::PPL, TPW = S::TPW;
-    __shared__ uint32_t s_stage[kPackWarps][kStageWords];
+    __shared__ uint32_t s_stage[kPackWarps][TPW * S::SW];
     const unsigned FULL = 0xffffffffu;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int seg = lane / LPT, sl = lane % LPT;

@@ -130,6 +130,7 @@ void public_stats(const DevStats &d, lcc_stats *out) {
     out->fitted = (int64_t)d.fitted;
     out->raw = (int64_t)d.raw;
     out->bytes = d.bytes;
+    out->tiles_temporal_cont = (int64_t)d.temporal_cont;
 }
 
 lcc_status latched(lcc_ctx *c) {
@@ -193,8 +194,11 @@ lcc_status encode_batch(lcc_ctx *c, int kind, int nframes, const int *slots, uin
         for (int f = 0; f < nframes; f++) bs.kf[f] = nullptr;
         LCC_LAUNCH(c, 1, launch_fit(c->g, c->s, bs, p, c->stream));
         LCC_LAUNCH_N(c, 3, queued_round_kernels(c->g, bs), launch_queued_rounds(c->g, c->s, bs, c->stream));
-        if (c->g.merge && c->g.lookahead > 0) LCC_LAUNCH(c, 8, launch_lookbehind(c->g, c->s, b, c->stream));
+        const bool pretest = c->g.merge && c->g.lookahead > 0;
+        // with temporal runs the pre-test also tests against temporal tiles' planes: after the test
+        if (pretest && !c->g.truns) LCC_LAUNCH(c, 8, launch_lookbehind(c->g, c->s, b, c->stream));
         LCC_LAUNCH(c, 9, launch_temporal(c->g, c->s, b, p, c->stream));
+        if (pretest && c->g.truns) LCC_LAUNCH(c, 8, launch_lookbehind(c->g, c->s, b, c->stream));
         LCC_LAUNCH(c, 2, launch_merge(c->g, c->s, b, c->stream));
         LCC_LAUNCH(c, 4, launch_pack(c->g, c->s, b, c->stream));
         return LCC_OK;
@@ -293,6 +297,7 @@ void lcc_default_params(lcc_params *p) {
     p->no_delta = 0;
     p->raw_exact = 0;
     p->temporal_candidates = 1;
+    p->temporal_runs = 1;
 }
 
 lcc_status lcc_create(lcc_ctx **out, const lcc_sensor *sensor, const lcc_params *params, void *cuda_stream) {
@@ -309,7 +314,7 @@ lcc_status lcc_create(lcc_ctx **out, const lcc_sensor *sensor, const lcc_params 
         !(p.min_inlier_frac >= 0) || p.max_batch < 1 || p.max_batch > kMaxBatch || p.lookahead < 0 ||
         p.lookahead > 32 || p.solver < 0 || p.solver > 1 || p.fit_schedule < 0 ||
         p.fit_schedule > 4 || p.no_delta < 0 || p.no_delta > 1 || p.raw_exact < 0 || p.raw_exact > 1 ||
-        p.temporal_candidates < 0 || p.temporal_candidates > 4)
+        p.temporal_candidates < 0 || p.temporal_candidates > 4 || p.temporal_runs < 0 || p.temporal_runs > 1)
         return LCC_ERR_INVALID_ARG;
     int dev = 0;
     cudaDeviceProp prop;
@@ -344,6 +349,7 @@ lcc_status lcc_create(lcc_ctx **out, const lcc_sensor *sensor, const lcc_params 
     g.no_delta = p.no_delta;
     g.raw_exact = p.raw_exact;
     g.tcand = p.temporal_candidates;
+    g.truns = p.temporal_runs && p.merge_runs ? 1 : 0;
     g.first_rounds = std::min(p.fit_schedule >= 3 ? 1 : p.fit_schedule, p.max_refits + 1);
     g.k_max = (int)floorf(p.fit_thr_m / p.quant_m + 0.5f) + 1;
     g.w_res = bits_for(2 * g.k_max);
@@ -701,7 +707,8 @@ lcc_status encode_sequence(lcc_ctx *c, int32_t nframes, int32_t key_index, const
         LCC_LAUNCH(c, 1, launch_fit(c->g, c->s, bp, pp, c->stream));
         if (c->g.schedule >= 1)
             LCC_LAUNCH_N(c, 3, queued_round_kernels(c->g, bp), launch_queued_rounds(c->g, c->s, bp, c->stream));
-        if (c->g.merge && c->g.lookahead > 0) LCC_LAUNCH(c, 8, launch_lookbehind(c->g, c->s, bp, c->stream));
+        const bool ppretest = c->g.merge && c->g.lookahead > 0;
+        if (ppretest && !c->g.truns) LCC_LAUNCH(c, 8, launch_lookbehind(c->g, c->s, bp, c->stream));
         // key frame: the rest of its rounds and its pre-test, merge (its coding planes), pack
         c->stream = c->kstream;
         if (c->g.schedule >= 1)
@@ -716,6 +723,8 @@ lcc_status encode_sequence(lcc_ctx *c, int32_t nframes, int32_t key_index, const
         LCC_CUDA(cudaStreamWaitEvent(c->side, c->ev_kplanes, 0));
         for (int f = 0; f < np; f++) bp.kf[f] = k->planes;
         LCC_LAUNCH(c, 9, launch_temporal(c->g, c->s, bp, pp, c->stream));
+        // with temporal runs the P frames' pre-test needs the temporal tiles' planes: after the test
+        if (ppretest && c->g.truns) LCC_LAUNCH(c, 8, launch_lookbehind(c->g, c->s, bp, c->stream));
         LCC_LAUNCH(c, 2, launch_merge(c->g, c->s, bp, c->stream));
         LCC_LAUNCH(c, 4, launch_pack(c->g, c->s, bp, c->stream));
         LCC_CUDA(cudaEventRecord(c->ev_join, c->side));

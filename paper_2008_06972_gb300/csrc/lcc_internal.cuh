@@ -40,7 +40,7 @@ constexpr int kVersion = 1;
 constexpr int kMaxTilePx = 128;
 
 // tile codes in the stream
-enum : uint8_t { T_EMPTY = 0, T_RAW = 1, T_RUN_START = 2, T_RUN_CONT = 3, T_TEMPORAL = 4 };
+enum : uint8_t { T_EMPTY = 0, T_RAW = 1, T_RUN_START = 2, T_RUN_CONT = 3, T_TEMPORAL = 4, T_TEMPORAL_CONT = 5 };
 // own-fit status of a tile
 enum : uint8_t { S_EMPTY = 0, S_FAIL = 1, S_FIT = 2, S_TEMPORAL = 3 };
 // latched device error bits
@@ -86,7 +86,7 @@ struct FrameLayout {
 // Per-frame device counters (atomics).
 struct DevStats {
     unsigned long long points_in, invalid, fov, binned, valid;
-    unsigned long long empty, raw_tiles, run_start, run_cont, temporal;
+    unsigned long long empty, raw_tiles, run_start, run_cont, temporal, temporal_cont;
     unsigned long long rounds[8];
     unsigned long long borderline, cand, fitted, raw;
     unsigned long long bytes;
@@ -115,6 +115,7 @@ struct Geometry {
     int no_delta;        // 1: plane-coded points carry no residual code (no residual section)
     int raw_exact;       // 1: raw pixels carry their fp32 range bits (32-bit raw codes)
     int tcand;           // K tiles a P tile's relaxed-plane test may try (1..4)
+    int truns;           // 1: temporal tiles of P frames grow runs (TEMPORAL_CONT tiles)
     int k_max, w_res, w_raw;
     float elev_max_rad, inv_d_el, inv_d_az;   // first guesses only (1/row and 1/column pitch, rad); the tables decide
     const float *ce, *se, *ct, *st;       // beam tables

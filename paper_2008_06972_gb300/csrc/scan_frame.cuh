@@ -99,7 +99,8 @@ __device__ __forceinline__ void scan_frame(const Geometry &g, const Scratch &s, 
             uint32_t hw[16];
             hw[0] = kMagic;
             hw[1] = (uint32_t)kVersion | ((uint32_t)b.kind << 16) | ((uint32_t)(g.merge ? 1 : 0) << 24) |
-                    ((uint32_t)(g.no_delta ? 1 : 0) << 25) | ((uint32_t)(g.raw_exact ? 1 : 0) << 26);
+                    ((uint32_t)(g.no_delta ? 1 : 0) << 25) | ((uint32_t)(g.raw_exact ? 1 : 0) << 26) |
+                    ((uint32_t)(g.truns && b.kind == 1 ? 1 : 0) << 27);
             hw[2] = (uint32_t)g.H | ((uint32_t)g.W << 16);
             hw[3] = (uint32_t)g.th | ((uint32_t)g.tw << 8) | ((uint32_t)g.w_res << 16) | ((uint32_t)g.w_raw << 24);
             hw[4] = __float_as_uint(g.thr);

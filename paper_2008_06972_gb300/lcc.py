@@ -16,7 +16,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "liblcc.so")
 
 OK, ERR_INVALID_ARG, ERR_CAPACITY, ERR_CUDA, ERR_TIMEOUT, ERR_CORRUPT, ERR_UNSUPPORTED, ERR_NO_DEVICE = range(8)
-T_EMPTY, T_RAW, T_RUN_START, T_RUN_CONT, T_TEMPORAL = range(5)
+T_EMPTY, T_RAW, T_RUN_START, T_RUN_CONT, T_TEMPORAL, T_TEMPORAL_CONT = range(6)
 S_EMPTY, S_FAIL, S_FIT, S_TEMPORAL = range(4)
 
 
@@ -36,7 +36,8 @@ class lcc_params(ctypes.Structure):
                 ("quant_m", ctypes.c_float), ("max_refits", ctypes.c_int32), ("min_inlier_frac", ctypes.c_float),
                 ("merge_runs", ctypes.c_int32), ("max_batch", ctypes.c_int32), ("lookahead", ctypes.c_int32),
                 ("solver", ctypes.c_int32), ("fit_schedule", ctypes.c_int32), ("no_delta", ctypes.c_int32),
-                ("raw_exact", ctypes.c_int32), ("temporal_candidates", ctypes.c_int32)]
+                ("raw_exact", ctypes.c_int32), ("temporal_candidates", ctypes.c_int32),
+                ("temporal_runs", ctypes.c_int32)]
 
 
 class lcc_stats(ctypes.Structure):
@@ -45,7 +46,7 @@ class lcc_stats(ctypes.Structure):
                                                "tiles_run_cont", "tiles_temporal")] + \
                [("fit_rounds", ctypes.c_int64 * 8), ("tiles_borderline", ctypes.c_int64),
                 ("cand", ctypes.c_int64), ("fitted", ctypes.c_int64), ("raw", ctypes.c_int64),
-                ("bytes", ctypes.c_uint64)]
+                ("bytes", ctypes.c_uint64), ("tiles_temporal_cont", ctypes.c_int64)]
 
 
 class lcc_seq_desc(ctypes.Structure):

@@ -125,15 +125,19 @@ def _labels(nt, seed):
 
 
 def test_gradient_matches_oracle(frame):
+    """Parameter gradients of the mean loss over 1024 tiles against the oracle's (BF16 rounding
+    points, FP64 sums): per parameter block the relative norm of the difference is at most 2e-2,
+    and the worst element of each block, relative to that block's largest gradient, is reported
+    (a BF16 activation that rounds to its other neighbour moves single elements, not the block)."""
     from paper_2008_06972_gb300 import lcc
     sensor, pts = frame
     _, x, _ = _gpu_inputs(sensor, pts)
     s = O.sensor(sensor)
     rng, _, _ = O.range_image(s, pts)
     _, _, nv = N.tile_inputs(rng, O.beams(s))
-    idx = _sample(nv, 64, 2)
+    idx = _sample(nv, 1024, 2)
     theta = _params(33)
-    net = lcc.Net(theta, max_tiles=64)
+    net = lcc.Net(theta, max_tiles=1024)
     xs = x[torch.from_numpy(idx).cuda()].contiguous()
     y = _labels(len(idx), 5)
     yd = torch.from_numpy(y).cuda()
@@ -146,18 +150,25 @@ def test_gradient_matches_oracle(frame):
                                 rounding=True)
     assert abs(float(loss.item()) - lo) <= 1e-3 * max(1.0, abs(lo))
     o = 0
+    report = {}
     for name, shp in N.SHAPES:
         n = int(np.prod(shp))
         a, b = gg[o:o + n], go[o:o + n]
         rel = np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-12)
-        assert rel <= 3e-2, (name, rel)
+        worst = np.abs(a - b).max() / max(np.abs(b).max(), 1e-12)
+        report[name] = (round(float(rel), 5), round(float(worst), 5))
         o += n
-    # an Adam step from that gradient (step 1: theta - lr * g / (|g| + eps))
-    net.train_step(xs, yd, len(idx), 1e-3, 1)
+    print("gradient relative error per block (norm, worst element / block max):", report)
+    for name, (rel, worst) in report.items():
+        assert rel <= 2e-2, (name, rel, report)
+        assert worst <= 0.1, (name, worst, report)
+    # an Adam step from a gradient over 64 of the tiles (step 1: theta - lr * g / (|g| + eps))
+    xs, yd = xs[:64].contiguous(), yd[:64].contiguous()
+    net.train_step(xs, yd, 64, 1e-3, 1)
     t1 = net.params().astype(np.float64)
     net.set_params(theta)
     grad2 = torch.zeros_like(grad)
-    net.gradient(xs, yd, len(idx), grad2, None)
+    net.gradient(xs, yd, 64, grad2, None)
     torch.cuda.synchronize()
     g2 = grad2.cpu().numpy().astype(np.float64)
     ref, _, _ = N.adam(theta.astype(np.float64), g2, np.zeros_like(g2), np.zeros_like(g2), 1, 1e-3)

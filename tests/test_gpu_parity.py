@@ -274,7 +274,9 @@ def _pframe_case(seq, frames, tile=(4, 4), thr=0.05, poses=None, schedule=0, tca
         tplanes, kref = H.gpu_temporal(recs)
         cbits, _, _ = O.pack(s, p, 1, rng, planes, ok, tplanes, kref)
         assert cbits.tobytes() == pbits[i].tobytes(), f"frame {f}: stream differs from the oracle's packing"
-        assert (streamfmt.tile_codes(pbits[i]) == 4).sum() == temporal.sum()
+        codes = streamfmt.tile_codes(pbits[i])
+        assert np.isin(codes[temporal], [4, 5]).all()            # temporal run start or continuation
+        assert (codes == 4).sum() == streamfmt.header(pbits[i])["n_temporal"] <= temporal.sum()
         _check_decode(c, s, pbits[i], rng, p.quant_m, kf_gpu=kf2, kft=okft, pose=poses[i])
     return total_border
 
@@ -481,15 +483,17 @@ def test_profiler_counts_every_kernel_and_orders_the_timeline(cfg2_seq):
     assert {k: v[0] for k, v in times.items()} == {k: 3 * v for k, v in per_call.items()}
     assert len(tl) == 3 * sum(per_call.values())
     assert all(t1 >= t0 >= 0.0 for _, t0, t1 in tl)
-    # in issue order per call; the P frames' merge and pack follow their temporal test on one stream
+    # in issue order per call; the P frames' run pre-test (which, with temporal runs, also tests
+    # against the temporal tiles' planes), merge and pack follow their temporal test on one stream
     k = sum(per_call.values())
     for i in range(3):
         chunk = tl[i * k:(i + 1) * k]
         names = [nm for nm, _, _ in chunk]
         assert names[0] == "bin" and names.count("temporal") == 1
         it = names.index("temporal")
-        assert names[it + 1:] == ["merge", "pack"]
-        assert chunk[it + 1][1] >= chunk[it][2] - 1e-3 and chunk[it + 2][1] >= chunk[it + 1][2] - 1e-3
+        assert names[it + 1:] == ["lookbehind", "merge", "pack"]
+        for q in range(it, it + 3):
+            assert chunk[q + 1][1] >= chunk[q][2] - 1e-3
 
 
 def test_sequence_decode_matches_per_frame_decode(cfg2_seq):
@@ -612,7 +616,7 @@ def test_imu_poses_parity_and_decode():
         assert np.abs(drng[m] - rng[m]).max() <= 0.01 + 1e-5
 
 
-@pytest.mark.parametrize("tile", [(4, 4), (8, 8)])
+@pytest.mark.parametrize("tile", [(4, 4), (4, 8), (8, 8), (8, 16)])
 def test_raw_exact_keyframe_parity(cfg2_seq, tile):
     """The lossless raw option: the GPU stream is the oracle's on the GPU's planes, both decoders
     agree bit for bit, raw pixels decode to their range exactly and the raw section holds 32 bits

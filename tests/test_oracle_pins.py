@@ -413,7 +413,7 @@ def test_temporal_offset_is_exact_under_known_motion(R):
     assert (tmp["status"][found & (tmp["n_valid"] >= 3)] == 2).all()
     assert found.sum() > 0.9 * (tmp["n_valid"] > 0).sum()
     sel = tmp["status"] == 2
-    assert (modes[sel] == O.T_TEMPORAL).all()
+    assert np.isin(modes[sel], [O.T_TEMPORAL, O.T_TEMPORAL_CONT]).all()   # a temporal run start or continuation
     n = np.array([0, 0, -1.0])
     assert np.abs(tmp["plane"][sel][:, :3] - (R.T @ n).astype(np.float32)).max() < 1e-6
     assert np.abs(tmp["plane"][sel][:, 3] - (1.7 - n @ T)).max() < 2e-5
@@ -432,7 +432,7 @@ def test_identity_pose_makes_every_plane_tile_temporal():
     bits, fits, tmp, modes = O.encode_pframe(s, p, kft, np.eye(4), pts)
     plane = (kmodes == O.T_RUN_START) | (kmodes == O.T_RUN_CONT)
     assert (tmp["kref"][plane] == np.nonzero(plane)[0]).all()
-    assert (modes[plane] == O.T_TEMPORAL).mean() > 0.99
+    assert np.isin(modes[plane], [O.T_TEMPORAL, O.T_TEMPORAL_CONT]).mean() > 0.99
 
 
 def test_pframe_decode_error_and_kf_table_from_stream(cfg2_seq):
@@ -444,7 +444,7 @@ def test_pframe_decode_error_and_kf_table_from_stream(cfg2_seq):
     assert (kft2 == kft).all()
     for f in (0, seq.key_index + 1, len(seq.frames) - 1):
         bits, fits, tmp, modes = O.encode_pframe(s, p, kft, seq.poses[f], seq.frames[f])
-        assert (modes == O.T_TEMPORAL).sum() > 1000
+        assert np.isin(modes, [O.T_TEMPORAL, O.T_TEMPORAL_CONT]).sum() > 1000
         rng, _, _ = O.range_image(s, seq.frames[f])
         dec, _, _ = O.decode(s, bits, kft2, seq.poses[f])
         m = rng > 0
@@ -654,3 +654,120 @@ def test_temporal_candidates_extend_the_anchor_test():
         ktiles = {(a // th) * TC + b // tw for a, b in hit}
         assert int(t4["kref"][t]) in ktiles
         assert int(t4["kref"][t]) != int(t1["kref"][t])
+
+
+# ----------------------------------------------------- temporal run growth (Sec. III-D) --
+
+def _tile_passes(s, p, rng, u, t, plane):
+    """fp64 acceptance rule of a tile against a plane (independent of the oracle's fp32 test);
+    returns (passes, near the threshold)."""
+    TW = (s.cols + p.tile_w - 1) // p.tile_w
+    tr, tc = divmod(t, TW)
+    r = rng[tr * p.tile_h:(tr + 1) * p.tile_h, tc * p.tile_w:(tc + 1) * p.tile_w].astype(np.float64).reshape(-1)
+    uu = u[tr * p.tile_h:(tr + 1) * p.tile_h, tc * p.tile_w:(tc + 1) * p.tile_w].reshape(-1, 3)
+    v = r > 0
+    if v.sum() < 3:
+        return False, False
+    dot = uu[v] @ plane[:3].astype(np.float64)
+    e = np.where(dot > 1e-3, r[v] - plane[3] / np.where(dot > 1e-3, dot, 1), np.inf)
+    near = bool(np.any(np.abs(np.abs(e) - p.fit_thr_m) < 1e-4))
+    need = max(3, math.ceil(p.min_inlier_frac * v.sum()))
+    return bool((np.abs(e) <= p.fit_thr_m).sum() >= need), near
+
+
+@pytest.mark.parametrize("tile", [(4, 4), (8, 8)])
+def test_temporal_run_invariants(cfg2_seq, tile):
+    """Temporal runs: a run starts at a tile that passed the relaxed-plane test; every tile coded
+    TEMPORAL_CONT passes the acceptance rule against the run start's relaxed plane (n', c'), and the
+    tile after a run fails it (or the row ends); every tile that passed its own relaxed-plane test is
+    coded temporally (a run start or inside a temporal run: spatial runs never cross it); spatial
+    runs keep their rule.  The stream carries one temporal record per temporal run."""
+    seq = cfg2_seq
+    s = O.sensor(seq.sensor)
+    p = O.params(tile[0], tile[1], temporal_runs=1)
+    _, kft, _, _ = O.encode_keyframe(s, p, seq.frames[seq.key_index])
+    u = O.beams(s).astype(np.float64)
+    TW = (s.cols + p.tile_w - 1) // p.tile_w
+    checked = conts = 0
+    for f in (seq.key_index - 1, seq.key_index + 2):
+        bits, fits, tmp, modes = O.encode_pframe(s, p, kft, seq.poses[f], seq.frames[f])
+        rng, _, _ = O.range_image(s, seq.frames[f])
+        passed = tmp["status"] == 2
+        temporal = (modes == O.T_TEMPORAL) | (modes == O.T_TEMPORAL_CONT)
+        assert ((modes == O.T_TEMPORAL) <= passed).all()
+        assert (passed <= temporal).all()
+        h = streamfmt.header(bits)
+        assert h["flags"] & 8 and h["n_temporal"] == int((modes == O.T_TEMPORAL).sum())
+        for t in np.nonzero(modes == O.T_TEMPORAL)[0]:
+            plane = tmp["plane"][t]
+            k = t + 1
+            while k % TW and modes[k] == O.T_TEMPORAL_CONT:
+                good, near = _tile_passes(s, p, rng, u, k, plane)
+                assert good or near
+                conts += 1
+                k += 1
+            if k % TW:
+                good, near = _tile_passes(s, p, rng, u, k, plane)
+                assert (not good) or near
+                checked += 1
+        # spatial runs: a continuation follows a run start or continuation, never a temporal tile
+        cont = np.nonzero(modes == O.T_RUN_CONT)[0]
+        assert (cont % TW > 0).all()
+        assert np.isin(modes[cont - 1], [O.T_RUN_START, O.T_RUN_CONT]).all()
+        tc = np.nonzero(modes == O.T_TEMPORAL_CONT)[0]
+        assert (tc % TW > 0).all()
+        assert np.isin(modes[tc - 1], [O.T_TEMPORAL, O.T_TEMPORAL_CONT]).all()
+    assert conts > 100 and checked > 100
+
+
+def test_temporal_runs_cut_records_and_decode_within_half_step(cfg2_seq):
+    """Growing temporal runs codes the same tiles with fewer records than one record per temporal
+    tile (the reading without growth), every pixel still decodes within q/2, and without growth no
+    stream holds a TEMPORAL_CONT tile or flags bit 3."""
+    seq = cfg2_seq
+    s = O.sensor(seq.sensor)
+    f = seq.key_index + 1
+    rng, _, _ = O.range_image(s, seq.frames[f])
+    m = rng > 0
+    out = {}
+    for tr in (0, 1):
+        p = O.params(temporal_runs=tr)
+        kbits, kft, _, _ = O.encode_keyframe(s, p, seq.frames[seq.key_index])
+        bits, _, tmp, modes = O.encode_pframe(s, p, kft, seq.poses[f], seq.frames[f])
+        kft2 = O.kf_table_from_stream(s, kbits, O.n_tiles(s, p))
+        drng, _, _ = O.decode(s, bits, kft2, seq.poses[f])
+        assert ((drng > 0) == m).all()
+        assert np.abs(drng[m] - rng[m]).max() <= p.quant_m / 2 + 1e-5
+        out[tr] = (bits, tmp, modes)
+    (b0, t0, m0), (b1, t1, m1) = out[0], out[1]
+    assert not (m0 == O.T_TEMPORAL_CONT).any() and not (streamfmt.header(b0)["flags"] & 8)
+    assert (m0 == O.T_TEMPORAL).sum() == (t0["status"] == 2).sum()
+    h0, h1 = streamfmt.header(b0), streamfmt.header(b1)
+    assert h1["n_temporal"] < h0["n_temporal"]
+    assert ((m1 == O.T_TEMPORAL) | (m1 == O.T_TEMPORAL_CONT)).sum() >= (m0 == O.T_TEMPORAL).sum()
+    assert len(b1) < len(b0)
+
+
+def test_temporal_cont_without_flag_or_after_a_spatial_tile_is_corrupt(cfg2_seq):
+    """The decoder accepts a TEMPORAL_CONT tile only in a stream flagged for temporal runs and only
+    right after a temporal tile of the same row."""
+    seq = cfg2_seq
+    s = O.sensor(seq.sensor)
+    p = O.params(temporal_runs=1)
+    f = seq.key_index + 1
+    kbits, kft, _, _ = O.encode_keyframe(s, p, seq.frames[seq.key_index])
+    bits, _, _, modes = O.encode_pframe(s, p, kft, seq.poses[f], seq.frames[f])
+    assert O.decode_status(s, bits, kft, seq.poses[f]) == O.OK
+    bad = bits.copy()
+    bad[7] &= ~np.uint8(8)                       # clear flags bit 3
+    assert O.decode_status(s, bad, kft, seq.poses[f]) == O.ERR_CORRUPT
+    # turn the first spatial continuation into a temporal continuation
+    t = int(np.nonzero(modes == O.T_RUN_CONT)[0][0])
+    sec = streamfmt.sections(bits)
+    off = 64 + 4 * (len(sec["bitmap"]))
+    word = off + 4 * (t // 8)
+    v = int.from_bytes(bits[word:word + 4].tobytes(), "little")
+    v = (v & ~(0xF << (4 * (t % 8)))) | (O.T_TEMPORAL_CONT << (4 * (t % 8)))
+    bad = bits.copy()
+    bad[word:word + 4] = np.frombuffer(v.to_bytes(4, "little"), np.uint8)
+    assert O.decode_status(s, bad, kft, seq.poses[f]) == O.ERR_CORRUPT
