@@ -85,6 +85,13 @@ typedef struct {
                                  TEMPORAL_CONT = 5, no record of its own; header flags bit 3); spatial
                                  runs stop at temporal tiles.  Needs merge_runs.  0: each temporal
                                  tile carries its own record */
+    int32_t plane3;           /* 1: planes in Eq. 3's three-coefficient form (Sec. III-C prints x + a y + b z
+                                 = c, which misses planes with n_x = 0; here divided by the dominant
+                                 component): every fitted plane becomes the unit-normal plane of its
+                                 coefficients a = n_i/n_k, b = n_j/n_k, c = d/n_k (k the axis of the
+                                 largest |n_k|, i, j the next axes), run records carry the 3
+                                 coefficients (header flags bit 4) and a run start's tile code is
+                                 6 + k.  0 (default): unit normal and offset, 4 words a run */
 } lcc_params;
 
 /* Per-frame statistics of the last encode (Fig. 11's categories and more). */
@@ -299,6 +306,12 @@ lcc_status lcc_last_stats(lcc_ctx *ctx, int32_t frame, lcc_stats *out);
 /* Per-tile records of frame `frame` of the last encode call (host array of
  * at least lcc_num_tiles entries).  Synchronous. */
 lcc_status lcc_tile_records(lcc_ctx *ctx, int32_t frame, lcc_tile_info *h_out, int64_t cap);
+
+/* With plane3: the three-coefficient form (a, b, c, axis as a float) of each tile's last spatial
+ * fit in frame `frame` of the last encode call (h_out: at least lcc_num_tiles x 4 floats; the
+ * plane in the tile record is the unit-normal plane of these coefficients).  Synchronous;
+ * LCC_ERR_UNSUPPORTED for a context without plane3. */
+lcc_status lcc_tile_coefficients(lcc_ctx *ctx, int32_t frame, float *h_out, int64_t cap);
 
 /* Kernel timing: when enabled, every kernel launch is bracketed by CUDA events
  * on the stream it runs on.  lcc_kernel_times returns, per kernel name, the

@@ -21,6 +21,7 @@ _lock = threading.Lock()
 _lib = None
 
 T_EMPTY, T_RAW, T_RUN_START, T_RUN_CONT, T_TEMPORAL, T_TEMPORAL_CONT = range(6)
+T_RUN_START3 = 6   # .. 8: a three-coefficient run start along axis x, y, z
 FIT_EMPTY, FIT_FAIL, FIT_OK = range(3)
 OK, ERR_ARG, ERR_CORRUPT, ERR_CAPACITY, ERR_INCONSISTENT = 0, -1, -2, -3, -4
 
@@ -36,13 +37,15 @@ class Params(ctypes.Structure):
                 ("fit_thr_m", ctypes.c_float), ("quant_m", ctypes.c_float),
                 ("max_refits", ctypes.c_int32), ("min_inlier_frac", ctypes.c_float),
                 ("merge_runs", ctypes.c_int32), ("no_delta", ctypes.c_int32), ("raw_exact", ctypes.c_int32),
-                ("temporal_candidates", ctypes.c_int32), ("temporal_runs", ctypes.c_int32)]
+                ("temporal_candidates", ctypes.c_int32), ("temporal_runs", ctypes.c_int32),
+                ("plane3", ctypes.c_int32)]
 
 
 class TileFit(ctypes.Structure):
     _fields_ = [("status", ctypes.c_int32), ("n_valid", ctypes.c_int32), ("n_inlier", ctypes.c_int32),
                 ("rounds", ctypes.c_int32), ("borderline", ctypes.c_int32), ("degenerate", ctypes.c_int32),
-                ("plane", ctypes.c_float * 4), ("plane64", ctypes.c_double * 4), ("lam", ctypes.c_double * 3)]
+                ("plane", ctypes.c_float * 4), ("plane64", ctypes.c_double * 4), ("lam", ctypes.c_double * 3),
+                ("coef", ctypes.c_float * 3), ("axis", ctypes.c_int32)]
 
 
 class TileTemporal(ctypes.Structure):
@@ -53,7 +56,7 @@ class TileTemporal(ctypes.Structure):
 
 FIT_DTYPE = np.dtype([("status", "<i4"), ("n_valid", "<i4"), ("n_inlier", "<i4"), ("rounds", "<i4"),
                       ("borderline", "<i4"), ("degenerate", "<i4"), ("plane", "<f4", 4),
-                      ("plane64", "<f8", 4), ("lam", "<f8", 3)], align=True)
+                      ("plane64", "<f8", 4), ("lam", "<f8", 3), ("coef", "<f4", 3), ("axis", "<i4")], align=True)
 TEMPORAL_DTYPE = np.dtype([("status", "<i4"), ("kref", "<i4"), ("n_valid", "<i4"), ("n_inlier", "<i4"),
                            ("rounds", "<i4"), ("borderline", "<i4"), ("plane", "<f4", 4)], align=True)
 assert FIT_DTYPE.itemsize == ctypes.sizeof(TileFit)
@@ -94,6 +97,12 @@ def lib():
             L.orc_fit_tiles_seeded.argtypes = [vp, vp, vp, vp, ctypes.c_float, vp]
             L.orc_temporal_tiles.restype = i32
             L.orc_temporal_tiles.argtypes = [vp, vp, vp, vp, vp, vp]
+            L.orc_pack3.restype = i64
+            L.orc_pack3.argtypes = [vp, vp, i32, vp, vp, vp, vp, vp, vp, vp, u64, vp, vp]
+            L.orc_plane_to3.restype = None
+            L.orc_plane_to3.argtypes = [vp, vp, vp]
+            L.orc_plane_from3.restype = None
+            L.orc_plane_from3.argtypes = [i32, vp, vp]
             L.orc_pack.restype = i64
             L.orc_pack.argtypes = [vp, vp, i32, vp, vp, vp, vp, vp, vp, u64, vp, vp]
             L.orc_encode_keyframe.restype = i64
@@ -114,9 +123,9 @@ def sensor(s) -> Sensor:
 
 
 def params(tile_h=4, tile_w=4, fit_thr_m=0.05, quant_m=0.02, max_refits=3, min_inlier_frac=0.75,
-           merge_runs=1, no_delta=0, raw_exact=0, temporal_candidates=1, temporal_runs=1) -> Params:
+           merge_runs=1, no_delta=0, raw_exact=0, temporal_candidates=1, temporal_runs=1, plane3=0) -> Params:
     return Params(tile_h, tile_w, fit_thr_m, quant_m, max_refits, min_inlier_frac, merge_runs, no_delta, raw_exact,
-                  temporal_candidates, temporal_runs)
+                  temporal_candidates, temporal_runs, plane3)
 
 
 def n_tiles(s: Sensor, p: Params) -> int:
@@ -201,8 +210,10 @@ def max_stream_bytes(s: Sensor, p: Params) -> int:
     return 64 + 4 * (npx // 32 + 1 + nt // 8 + 1 + 4 * nt + 2 * nt + npx // 32 + 1) + 4 * (npx * 40 // 32 + 2)
 
 
-def pack(s: Sensor, p: Params, kind: int, rng, fit_plane, fit_ok, temporal_plane=None, temporal_kref=None):
-    """Merge + code + pack given per-tile results.  Returns (bytes, kf_table, modes)."""
+def pack(s: Sensor, p: Params, kind: int, rng, fit_plane, fit_ok, temporal_plane=None, temporal_kref=None,
+         fit_coef=None):
+    """Merge + code + pack given per-tile results (fit_coef: (T, 4) a, b, c, axis for plane3
+    streams).  Returns (bytes, kf_table, modes)."""
     rng = np.ascontiguousarray(rng, dtype=np.float32)
     fit_plane = np.ascontiguousarray(fit_plane, dtype=np.float32)
     fit_ok = np.ascontiguousarray(fit_ok, dtype=np.uint8)
@@ -214,8 +225,10 @@ def pack(s: Sensor, p: Params, kind: int, rng, fit_plane, fit_ok, temporal_plane
     out = np.zeros(cap, np.uint8)
     kft = np.zeros((nt, 4), np.float32)
     modes = np.zeros(nt, np.uint8)
-    n = lib().orc_pack(ctypes.byref(s), ctypes.byref(p), kind, _p(rng), _p(fit_plane), _p(fit_ok),
-                       _p(temporal_plane), _p(temporal_kref), _p(out), cap, _p(kft), _p(modes))
+    if fit_coef is not None:
+        fit_coef = np.ascontiguousarray(fit_coef, dtype=np.float32)
+    n = lib().orc_pack3(ctypes.byref(s), ctypes.byref(p), kind, _p(rng), _p(fit_plane), _p(fit_coef), _p(fit_ok),
+                        _p(temporal_plane), _p(temporal_kref), _p(out), cap, _p(kft), _p(modes))
     if n < 0:
         raise ValueError(f"orc_pack: {n}")
     if n > cap:
@@ -290,3 +303,19 @@ def kf_table_from_stream(s: Sensor, bits: np.ndarray, n_tiles_: int) -> np.ndarr
     if rc != OK:
         raise ValueError(f"orc_kf_table_from_stream: {rc}")
     return kft
+
+
+def plane_to3(pl) -> tuple:
+    """(axis, (a, b, c)) of a unit-normal fp32 plane (Eq. 3's form with the dominant axis)."""
+    pl = np.ascontiguousarray(pl, dtype=np.float32)
+    axis = ctypes.c_int32()
+    abc = np.zeros(3, np.float32)
+    lib().orc_plane_to3(_p(pl), ctypes.byref(axis), _p(abc))
+    return int(axis.value), abc
+
+
+def plane_from3(axis: int, abc) -> np.ndarray:
+    abc = np.ascontiguousarray(abc, dtype=np.float32)
+    pl = np.zeros(4, np.float32)
+    lib().orc_plane_from3(int(axis), _p(abc), _p(pl))
+    return pl

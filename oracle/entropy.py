@@ -68,7 +68,8 @@ def fixed_layout(fixed: bytes):
 
     bw, fw = words(rows * cols), words(n_cand)
     res_w = 0 if flags & 2 else words(n_fit * w_res)
-    secs = [("bitmap", 8, 4 * bw, bw), ("tiles", 4, n_tiles, words(4 * n_tiles)), ("runs", 0, 0, 4 * n_runs),
+    run_words = (3 if flags & 16 else 4) * n_runs   # three-coefficient planes (flags bit 4): 3 words a run
+    secs = [("bitmap", 8, 4 * bw, bw), ("tiles", 4, n_tiles, words(4 * n_tiles)), ("runs", 0, 0, run_words),
             ("temporal", 0, 0, 2 * n_temp), ("fitted", 8, 4 * fw, fw),
             ("res", w_res, 0 if flags & 2 else n_fit, res_w), ("raw", w_raw, n_raw, words(n_raw * w_raw))]
     if 64 + 4 * sum(s[3] for s in secs) != total or total > len(b):

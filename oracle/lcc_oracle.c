@@ -291,6 +291,35 @@ static int residual(const float pl[4], const float u[3], float r, float thr, flo
     return fabsf(e) <= thr;
 }
 
+/*
+ * Eq. 3 writes a plane as x + a y + b z = c, which cannot hold planes with n_x = 0.  Its
+ * three-coefficient form is kept by dividing by the dominant component instead: with k the axis of
+ * the largest |n_k| (the lowest index on ties) and i, j the next two axes in cyclic order,
+ * a = n_i / n_k, b = n_j / n_k, c = d / n_k (IEEE fp32 divisions).  The plane a decoder gets back
+ * is the unit-normal one: n_k = 1 / sqrt(a^2 + b^2 + 1), n_i = a n_k, n_j = b n_k, d = c n_k,
+ * negated when d < 0 (a plane through the origin, |d| < 1e-9, keeps n_k > 0).
+ */
+void orc_plane_to3(const float pl[4], int *axis, float abc[3]) {
+    int k = 0;
+    float m = fabsf(pl[0]);
+    if (fabsf(pl[1]) > m) { k = 1; m = fabsf(pl[1]); }
+    if (fabsf(pl[2]) > m) k = 2;
+    abc[0] = pl[(k + 1) % 3] / pl[k];
+    abc[1] = pl[(k + 2) % 3] / pl[k];
+    abc[2] = pl[3] / pl[k];
+    *axis = k;
+}
+
+void orc_plane_from3(int axis, const float abc[3], float pl[4]) {
+    const float inv = 1.0f / sqrtf(fmaf(abc[0], abc[0], fmaf(abc[1], abc[1], 1.0f)));
+    pl[axis] = inv;
+    pl[(axis + 1) % 3] = abc[0] * inv;
+    pl[(axis + 2) % 3] = abc[1] * inv;
+    pl[3] = abc[2] * inv;
+    if (!(fabsf(pl[3]) < 1e-9f) && pl[3] < 0.0f)
+        for (int a = 0; a < 4; a++) pl[a] = -pl[a];
+}
+
 typedef struct {
     int n;               /* pixels of the tile inside the image */
     int pix[MAX_TILE_PX];/* image pixel index, raster order within the tile */
@@ -373,6 +402,10 @@ static void fit_one(const orc_params *prm, const tile_px_t *tp, orc_tile_fit *f)
         f->plane64[0] = nrm[0]; f->plane64[1] = nrm[1]; f->plane64[2] = nrm[2]; f->plane64[3] = d;
         for (int a = 0; a < 3; a++) f->plane[a] = (float)nrm[a];
         f->plane[3] = (float)d;
+        if (prm->plane3) {   /* the fitted plane as Eq. 3's coefficients store it */
+            orc_plane_to3(f->plane, &f->axis, f->coef);
+            orc_plane_from3(f->axis, f->coef, f->plane);
+        }
         if (lam[1] >= 0.999e-12 * lam[2] && lam[1] <= 1.001e-12 * lam[2]) f->borderline = 1;
         if (!(lam[1] > 1e-12 * lam[2])) { f->degenerate = 1; nI = 0; break; }
         nI = inliers(tp, f->plane, prm->fit_thr_m, I, &f->borderline);
@@ -436,6 +469,10 @@ static void fit_one_seeded(const orc_params *prm, const tile_px_t *tp, const flo
         f->plane64[0] = nrm[0]; f->plane64[1] = nrm[1]; f->plane64[2] = nrm[2]; f->plane64[3] = d;
         for (int a = 0; a < 3; a++) f->plane[a] = (float)nrm[a];
         f->plane[3] = (float)d;
+        if (prm->plane3) {   /* the fitted plane as Eq. 3's coefficients store it */
+            orc_plane_to3(f->plane, &f->axis, f->coef);
+            orc_plane_from3(f->axis, f->coef, f->plane);
+        }
         if (lam[1] >= 0.999e-12 * lam[2] && lam[1] <= 1.001e-12 * lam[2]) f->borderline = 1;
         if (!(lam[1] > 1e-12 * lam[2])) { f->degenerate = 1; nI = 0; break; }
         nI = inliers(tp, f->plane, prm->fit_thr_m, I, &f->borderline);
@@ -454,7 +491,7 @@ static int params_ok(const orc_sensor *s, const orc_params *p) {
            p->tile_h * p->tile_w <= MAX_TILE_PX && p->tile_h <= 255 && p->tile_w <= 255 &&
            p->fit_thr_m >= 0 && p->quant_m > 0 && p->max_refits >= 0 && p->min_inlier_frac >= 0 &&
            p->temporal_candidates >= 0 && p->temporal_candidates <= 4 && p->temporal_runs >= 0 &&
-           p->temporal_runs <= 1;
+           p->temporal_runs <= 1 && p->plane3 >= 0 && p->plane3 <= 1;
 }
 
 int orc_fit_tiles(const orc_sensor *s, const orc_params *prm, const float *range, orc_tile_fit *out) {
@@ -664,7 +701,7 @@ static void section_offsets(const header_t *h, uint64_t off[8]) {
     off[0] = 0;
     off[1] = off[0] + words_for((uint64_t)h->rows * h->cols);
     off[2] = off[1] + words_for((uint64_t)h->n_tiles * 4);
-    off[3] = off[2] + 4ull * h->n_runs;
+    off[3] = off[2] + ((h->flags & 16u) ? 3ull : 4ull) * h->n_runs;
     off[4] = off[3] + 2ull * h->n_temporal;
     off[5] = off[4] + words_for(h->n_cand);
     off[6] = off[5] + ((h->flags & 2u) ? 0 : words_for((uint64_t)h->n_fitted * h->w_res));   /* no deltas */
@@ -723,7 +760,7 @@ static int header_read(const uint8_t *b, uint64_t nbytes, header_t *h) {
     h->n_raw = rd32(b + 48);
     h->k_max = (int32_t)rd32(b + 52);
     h->total_bytes = rd32(b + 56);
-    if (h->kind > 1 || (h->flags & ~15u) || ((h->flags & 8u) && h->kind != 1) || h->tile_h == 0 || h->tile_w == 0 || h->w_res == 0 || h->w_res > 16 ||
+    if (h->kind > 1 || (h->flags & ~31u) || ((h->flags & 8u) && h->kind != 1) || h->tile_h == 0 || h->tile_w == 0 || h->w_res == 0 || h->w_res > 16 ||
         h->w_raw == 0 || ((h->flags & 4u) ? h->w_raw != 32 : h->w_raw > 24) || !(h->q > 0))
         return ORC_ERR_CORRUPT;
     uint64_t off[8];
@@ -758,7 +795,15 @@ int64_t orc_pack(const orc_sensor *s, const orc_params *prm, int kind, const flo
                  const float *fit_plane, const uint8_t *fit_ok,
                  const float *temporal_plane, const int32_t *temporal_kref,
                  uint8_t *out, uint64_t cap, float *kf_table_out, uint8_t *modes_out) {
-    if (!params_ok(s, prm) || (kind != 0 && kind != 1)) return ORC_ERR_ARG;
+    return orc_pack3(s, prm, kind, range, fit_plane, NULL, fit_ok, temporal_plane, temporal_kref, out, cap,
+                     kf_table_out, modes_out);
+}
+
+int64_t orc_pack3(const orc_sensor *s, const orc_params *prm, int kind, const float *range,
+                  const float *fit_plane, const float *fit_coef, const uint8_t *fit_ok,
+                  const float *temporal_plane, const int32_t *temporal_kref,
+                  uint8_t *out, uint64_t cap, float *kf_table_out, uint8_t *modes_out) {
+    if (!params_ok(s, prm) || (kind != 0 && kind != 1) || (prm->plane3 && !fit_coef)) return ORC_ERR_ARG;
     tables_t T;
     tables_make(s, &T);
     const int TW = (s->cols + prm->tile_w - 1) / prm->tile_w;
@@ -803,6 +848,12 @@ int64_t orc_pack(const orc_sensor *s, const orc_params *prm, int kind, const flo
             mode[t] = ORC_T_RUN_START;
             memcpy(&cp[4 * t], &fit_plane[4 * t], 16);
             if (!tile_passes(prm, tp, &cp[4 * t])) ret = ORC_ERR_INCONSISTENT;
+            if (prm->plane3) {   /* the run record holds the coefficients: they must give this plane */
+                float back[4];
+                orc_plane_from3((int)fit_coef[4 * t + 3], &fit_coef[4 * t], back);
+                if (memcmp(back, &cp[4 * t], 16) != 0 || fit_coef[4 * t + 3] < 0.0f || fit_coef[4 * t + 3] > 2.0f)
+                    ret = ORC_ERR_INCONSISTENT;
+            }
             int k = j + 1;
             while (prm->merge_runs && k < TW) {
                 int t2 = tr * TW + k;
@@ -821,7 +872,7 @@ int64_t orc_pack(const orc_sensor *s, const orc_params *prm, int kind, const flo
     /* 2. counts */
     h.kind = kind;
     h.flags = (prm->merge_runs ? 1u : 0u) | (prm->no_delta ? 2u : 0u) | (prm->raw_exact ? 4u : 0u) |
-              (kind == 1 && prm->merge_runs && prm->temporal_runs ? 8u : 0u);
+              (kind == 1 && prm->merge_runs && prm->temporal_runs ? 8u : 0u) | (prm->plane3 ? 16u : 0u);
     h.rows = s->rows;
     h.cols = s->cols;
     h.tile_h = prm->tile_h;
@@ -867,11 +918,19 @@ int64_t orc_pack(const orc_sensor *s, const orc_params *prm, int kind, const flo
         uint32_t *w = calloc(off[7] + 1, sizeof(uint32_t));
         for (int64_t p = 0; p < (int64_t)s->rows * s->cols; p++)
             if (range[p] > 0.0f) put_bits(w + off[0], (uint64_t)p, 1, 1);
-        for (int t = 0; t < NT; t++) put_bits(w + off[1], (uint64_t)t * 4, mode[t], 4);
+        for (int t = 0; t < NT; t++) {   /* plane3: a run start's code names its dominant axis */
+            const uint32_t code = (prm->plane3 && mode[t] == ORC_T_RUN_START)
+                                      ? ORC_T_RUN_START3 + (uint32_t)fit_coef[4 * t + 3] : mode[t];
+            put_bits(w + off[1], (uint64_t)t * 4, code, 4);
+        }
         uint64_t ir = 0, itp = 0, ic = 0, ifit = 0, iraw = 0;
         for (int t = 0; t < NT; t++) {
             if (mode[t] == ORC_T_RUN_START) {
-                for (int a = 0; a < 4; a++) w[off[2] + 4 * ir + a] = f2u(cp[4 * t + a]);
+                if (prm->plane3) {   /* Eq. 3's coefficients; the axis is in the tile code */
+                    for (int a = 0; a < 3; a++) w[off[2] + 3 * ir + a] = f2u(fit_coef[4 * t + a]);
+                } else {
+                    for (int a = 0; a < 4; a++) w[off[2] + 4 * ir + a] = f2u(cp[4 * t + a]);
+                }
                 ir++;
             }
             if (mode[t] == ORC_T_TEMPORAL) {
@@ -925,13 +984,17 @@ int64_t orc_encode_keyframe(const orc_sensor *s, const orc_params *prm, const fl
     orc_tile_fit *fits = malloc(sizeof(orc_tile_fit) * NT);
     float *planes = malloc(sizeof(float) * 4 * NT);
     uint8_t *ok = malloc(NT);
+    float *coef = malloc(sizeof(float) * 4 * NT);
     orc_range_image(s, pts, n, range, NULL, NULL);
     orc_fit_tiles(s, prm, range, fits);
     for (int t = 0; t < NT; t++) {
         memcpy(&planes[4 * t], fits[t].plane, 16);
+        memcpy(&coef[4 * t], fits[t].coef, 12);
+        coef[4 * t + 3] = (float)fits[t].axis;
         ok[t] = fits[t].status == ORC_FIT_OK;
     }
-    int64_t r = orc_pack(s, prm, 0, range, planes, ok, NULL, NULL, out, cap, kf_table_out, modes_out);
+    int64_t r = orc_pack3(s, prm, 0, range, planes, coef, ok, NULL, NULL, out, cap, kf_table_out, modes_out);
+    free(coef);
     if (fits_out) memcpy(fits_out, fits, sizeof(orc_tile_fit) * NT);
     free(range); free(fits); free(planes); free(ok);
     return r;
@@ -954,16 +1017,20 @@ int64_t orc_encode_pframe(const orc_sensor *s, const orc_params *prm, const floa
     float *tplanes = malloc(sizeof(float) * 4 * NT);
     int32_t *kref = malloc(sizeof(int32_t) * NT);
     uint8_t *ok = malloc(NT);
+    float *coef = malloc(sizeof(float) * 4 * NT);
     orc_range_image(s, pts, n, range, NULL, NULL);
     orc_temporal_tiles(s, prm, range, kf_table, pose, tmp);
     orc_fit_tiles(s, prm, range, fits);
     for (int t = 0; t < NT; t++) {
         memcpy(&planes[4 * t], fits[t].plane, 16);
+        memcpy(&coef[4 * t], fits[t].coef, 12);
+        coef[4 * t + 3] = (float)fits[t].axis;
         memcpy(&tplanes[4 * t], tmp[t].plane, 16);
         kref[t] = (tmp[t].status == 2) ? tmp[t].kref : -1;
         ok[t] = fits[t].status == ORC_FIT_OK;
     }
-    int64_t r = orc_pack(s, prm, 1, range, planes, ok, tplanes, kref, out, cap, NULL, modes_out);
+    int64_t r = orc_pack3(s, prm, 1, range, planes, coef, ok, tplanes, kref, out, cap, NULL, modes_out);
+    free(coef);
     if (fits_out) memcpy(fits_out, fits, sizeof(orc_tile_fit) * NT);
     if (temporal_out) memcpy(temporal_out, tmp, sizeof(orc_tile_temporal) * NT);
     free(range); free(fits); free(tmp); free(planes); free(tplanes); free(kref); free(ok);
@@ -1004,13 +1071,27 @@ static int stream_planes(const orc_sensor *s, const stream_t *st, const float *k
     uint64_t ir = 0, itp = 0;
     for (int t = 0; t < NT; t++) {
         mode[t] = (uint8_t)get_bits(st->w + st->off[1], (uint64_t)t * 4, 4);
+        int axis = -1;
+        if (mode[t] >= ORC_T_RUN_START3 && mode[t] < ORC_T_RUN_START3 + 3) {
+            if (!(st->h.flags & 16u)) return ORC_ERR_CORRUPT;
+            axis = mode[t] - ORC_T_RUN_START3;
+            mode[t] = ORC_T_RUN_START;
+        } else if (mode[t] == ORC_T_RUN_START && (st->h.flags & 16u)) {
+            return ORC_ERR_CORRUPT;   /* a 3-coefficient stream names every run start's axis */
+        }
         switch (mode[t]) {
         case ORC_T_EMPTY:
         case ORC_T_RAW:
             break;
         case ORC_T_RUN_START:
             if (ir >= st->h.n_runs) return ORC_ERR_CORRUPT;
-            for (int a = 0; a < 4; a++) cp[4 * t + a] = u2f(st->w[st->off[2] + 4 * ir + a]);
+            if (st->h.flags & 16u) {   /* Eq. 3's coefficients along the tile code's axis */
+                float abc[3];
+                for (int a = 0; a < 3; a++) abc[a] = u2f(st->w[st->off[2] + 3 * ir + a]);
+                orc_plane_from3(axis, abc, &cp[4 * t]);
+            } else {
+                for (int a = 0; a < 4; a++) cp[4 * t + a] = u2f(st->w[st->off[2] + 4 * ir + a]);
+            }
             ir++;
             break;
         case ORC_T_RUN_CONT:

@@ -53,11 +53,17 @@ typedef struct {
                                     that passes the acceptance rule against the relaxed plane of
                                     the temporal tile to its left joins that tile's run (tile code
                                     TEMPORAL_CONT, no record of its own; header flags bit 3) */
+    int32_t plane3;              /* 1: planes in Eq. 3's three-coefficient form (dominant axis):
+                                    every fitted plane is replaced by the unit-normal plane of its
+                                    coefficients a = n_i/n_k, b = n_j/n_k, c = d/n_k (k the axis of
+                                    the largest |n_k|), and run records carry the coefficients (3
+                                    words; header flags bit 4) with the axis in the run start's tile
+                                    code (6 + k) */
 } orc_params;
 
 /* tile codes of the bitstream */
 enum { ORC_T_EMPTY = 0, ORC_T_RAW = 1, ORC_T_RUN_START = 2, ORC_T_RUN_CONT = 3, ORC_T_TEMPORAL = 4,
-       ORC_T_TEMPORAL_CONT = 5 };
+       ORC_T_TEMPORAL_CONT = 5, ORC_T_RUN_START3 = 6 /* .. 8: plane3 run start, dominant axis x, y, z */ };
 /* own-fit status */
 enum { ORC_FIT_EMPTY = 0, ORC_FIT_FAIL = 1, ORC_FIT_OK = 2 };
 /* errors */
@@ -73,6 +79,8 @@ typedef struct {
     float plane[4];              /* stored fp32 plane n.x, n.y, n.z, d (n.p = d) */
     double plane64[4];           /* the fp64 plane before rounding */
     double lam[3];               /* eigenvalues of the last fit, ascending */
+    float coef[3];               /* plane3: the plane's coefficients a, b, c */
+    int32_t axis;                /* plane3: its dominant axis k (0 x, 1 y, 2 z) */
 } orc_tile_fit;
 
 typedef struct {
@@ -119,6 +127,18 @@ int64_t orc_pack(const orc_sensor *s, const orc_params *prm, int kind, const flo
                  const float *fit_plane, const uint8_t *fit_ok,
                  const float *temporal_plane, const int32_t *temporal_kref,
                  uint8_t *out, uint64_t cap, float *kf_table_out, uint8_t *modes_out);
+
+/* orc_pack for plane3 streams: fit_coef (ntiles x 4: a, b, c, axis as a float) gives each
+ * fitted tile's coefficients, whose unit-normal plane must equal fit_plane bit for bit. */
+int64_t orc_pack3(const orc_sensor *s, const orc_params *prm, int kind, const float *range,
+                  const float *fit_plane, const float *fit_coef, const uint8_t *fit_ok,
+                  const float *temporal_plane, const int32_t *temporal_kref,
+                  uint8_t *out, uint64_t cap, float *kf_table_out, uint8_t *modes_out);
+
+/* Eq. 3 generalised to any dominant axis: the coefficients (a, b, c) and axis k of a unit-normal
+ * plane, and the unit-normal plane of coefficients (both fp32, fixed operation order). */
+void orc_plane_to3(const float pl[4], int *axis, float abc[3]);
+void orc_plane_from3(int axis, const float abc[3], float pl[4]);
 
 /* Full key-frame encode: bin, fit, merge, code, pack. */
 int64_t orc_encode_keyframe(const orc_sensor *s, const orc_params *prm, const float *pts, int64_t n,

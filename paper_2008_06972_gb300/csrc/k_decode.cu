@@ -102,7 +102,7 @@ __global__ void __launch_bounds__(kPrepThreads) k_decode_prep(Geometry g, DecBat
         if (!bad) {
             for (int q = 0; q < 16; q++) s_h[q] = rd_u32(bits + 4 * q);
             const uint32_t kind = (s_h[1] >> 16) & 0xff, flags = s_h[1] >> 24;
-            bad |= s_h[0] != kMagic || (s_h[1] & 0xffff) != (uint32_t)kVersion || (flags & ~15u) ||
+            bad |= s_h[0] != kMagic || (s_h[1] & 0xffff) != (uint32_t)kVersion || (flags & ~31u) ||
                    ((flags & 8u) && kind != 1);
             bad |= (int)(s_h[2] & 0xffff) != g.H || (int)(s_h[2] >> 16) != g.W;
             bad |= (int)(s_h[3] & 0xff) != g.th || (int)((s_h[3] >> 8) & 0xff) != g.tw;
@@ -114,7 +114,7 @@ __global__ void __launch_bounds__(kPrepThreads) k_decode_prep(Geometry g, DecBat
             s_sec[0] = 0;
             s_sec[1] = s_sec[0] + dwords((uint64_t)g.H * g.W);
             s_sec[2] = s_sec[1] + dwords((uint64_t)g.NT * 4);
-            s_sec[3] = s_sec[2] + 4u * s_h[8];
+            s_sec[3] = s_sec[2] + ((flags & 16u) ? 3u : 4u) * s_h[8];   // three-coefficient planes: 3 words
             s_sec[4] = s_sec[3] + 2u * s_h[9];
             s_sec[5] = s_sec[4] + dwords(s_h[10]);
             s_sec[6] = s_sec[5] + ((flags & 2u) ? 0u : dwords((uint64_t)s_h[11] * w_res));   // no deltas: none
@@ -144,9 +144,17 @@ __global__ void __launch_bounds__(kPrepThreads) k_decode_prep(Geometry g, DecBat
     for (int base = 0; base < g.NT; base += kPrepThreads) {
         const int t = base + tid;
         uint32_t mode = 0, nv = 0;
+        int axis = -1;   // three-coefficient run start: its dominant axis (tile code 6 + axis)
         const int tr = t / g.TC, tc = t % g.TC;
         if (t < g.NT) {
             mode = (tcw[t >> 3] >> (4 * (t & 7))) & 15u;
+            if (mode >= T_RUN_START3 && mode < T_RUN_START3 + 3u) {
+                if (!(hflags & 16u)) bad = 1;
+                axis = (int)(mode - T_RUN_START3);
+                mode = T_RUN_START;
+            } else if (mode == T_RUN_START && (hflags & 16u)) {
+                bad = 1;
+            }
             const int j0 = tc * g.tw, wdt = min(g.tw, g.W - j0);
             for (int rr = 0; rr < g.th; rr++) {
                 const int i = tr * g.th + rr;
@@ -156,7 +164,8 @@ __global__ void __launch_bounds__(kPrepThreads) k_decode_prep(Geometry g, DecBat
             if (mode > T_TEMPORAL_CONT) bad = 1;
             if (mode == T_EMPTY && nv) bad = 1;
             if (mode == T_RUN_CONT || mode == T_TEMPORAL_CONT) {   // continues the run to its left
-                const uint32_t pm = tc ? (tcw[(t - 1) >> 3] >> (4 * ((t - 1) & 7))) & 15u : 0u;
+                uint32_t pm = tc ? (tcw[(t - 1) >> 3] >> (4 * ((t - 1) & 7))) & 15u : 0u;
+                if (pm >= T_RUN_START3 && pm < T_RUN_START3 + 3u) pm = T_RUN_START;
                 const bool ok = mode == T_RUN_CONT ? (pm == T_RUN_START || pm == T_RUN_CONT)
                                                    : ((hflags & 8u) && (pm == T_TEMPORAL || pm == T_TEMPORAL_CONT));
                 if (tc == 0 || !ok) bad = 1;
@@ -186,6 +195,9 @@ __global__ void __launch_bounds__(kPrepThreads) k_decode_prep(Geometry g, DecBat
         if (t < g.NT) {
             if (mode == T_RUN_START) {
                 if (run_idx >= n_runs) bad = 1;
+                else if (hflags & 16u)
+                    pl = plane_from3(make_float4(__uint_as_float(runw[3 * run_idx]), __uint_as_float(runw[3 * run_idx + 1]),
+                                                 __uint_as_float(runw[3 * run_idx + 2]), (float)(axis < 0 ? 0 : axis)));
                 else pl = make_float4(__uint_as_float(runw[4 * run_idx]), __uint_as_float(runw[4 * run_idx + 1]),
                                       __uint_as_float(runw[4 * run_idx + 2]), __uint_as_float(runw[4 * run_idx + 3]));
             } else if (mode == T_TEMPORAL) {

@@ -110,7 +110,7 @@ __device__ bool parse_fixed(const uint8_t *h, unsigned long long avail, uint32_t
     const uint32_t count[kSecs] = {4 * bw, n_tiles, 0, 0, 4 * fw, res_cnt, n_raw};
     const uint32_t words[kSecs] = {bw,
                                    words_of_bits(4ull * n_tiles),
-                                   4 * n_runs,
+                                   ((flags & 16u) ? 3u : 4u) * n_runs,   // three-coefficient planes: 3 words
                                    2 * n_temp,
                                    fw,
                                    words_of_bits((unsigned long long)res_cnt * w_res),

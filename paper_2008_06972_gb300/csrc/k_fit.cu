@@ -332,11 +332,9 @@ struct FitLanes {
     static constexpr int CH = PX / L;
 };
 
-// One plane solve; a single out-of-line copy keeps the instruction footprint
-// of the kernels small (the kernels run few warps per SM, so cold instruction
-// fetches, not arithmetic, bound them when code is duplicated).
-__device__ __noinline__ bool solve_moments(const Moments m, int n, float ax, float ay, float az, int solver,
-                                           float4 *pl, float *ratio) {
+// The plane solve of the moments (FP64 or float-float).
+__device__ __forceinline__ bool solve_moments_raw(const Moments m, int n, float ax, float ay, float az, int solver,
+                                                  float4 *pl, float *ratio) {
     if (solver == 1) {
         const double m1[3] = {ff_to_d(m.s1x), ff_to_d(m.s1y), ff_to_d(m.s1z)};
         const double m2[6] = {ff_to_d(m.sxx), ff_to_d(m.sxy), ff_to_d(m.sxz),
@@ -349,6 +347,20 @@ __device__ __noinline__ bool solve_moments(const Moments m, int n, float ax, flo
     float o4[4];
     const bool dg = ffm::solve_plane_ff(f1, f2m, n, ax, ay, az, o4, ratio);
     *pl = make_float4(o4[0], o4[1], o4[2], o4[3]);
+    return dg;
+}
+
+// One plane solve; a single out-of-line copy keeps the instruction footprint
+// of the kernels small (the kernels run few warps per SM, so cold instruction
+// fetches, not arithmetic, bound them when code is duplicated).
+__device__ __noinline__ bool solve_moments(const Moments m, int n, float ax, float ay, float az, int solver,
+                                           int plane3, float4 *pl, float4 *coef, float *ratio) {
+    const bool dg = solve_moments_raw(m, n, ax, ay, az, solver, pl, ratio);
+    // three-coefficient planes: the fitted plane is the one its stored coefficients give back
+    if (plane3 && (pl->x != 0.0f || pl->y != 0.0f || pl->z != 0.0f)) {
+        *coef = plane_to3(*pl);
+        *pl = plane_from3(*coef);
+    }
     return dg;
 }
 
@@ -430,7 +442,7 @@ struct TileView {
     }
     // one total-least-squares fit over the set S (float-float moments, in the chunk order
     // of FitLanes)
-    __device__ __forceinline__ bool fit(const Mask &S, int nS, float4 &pl, float &ratio) const {
+    __device__ __forceinline__ bool fit(const Mask &S, int nS, float4 &pl, float4 &coef, float &ratio) const {
         constexpr int L = FitLanes<TH_, TW_>::L, CH = FitLanes<TH_, TW_>::CH;
         Moments m = moments_zero();
 #pragma unroll 1
@@ -446,7 +458,7 @@ struct TileView {
             const Moments part = moments_finish(acc);
             m = c == 0 ? part : moments_add(m, part);
         }
-        return solve_moments(m, nS, ax, ay, az, g.solver, &pl, &ratio);
+        return solve_moments(m, nS, ax, ay, az, g.solver, g.plane3, &pl, &coef, &ratio);
     }
 };
 
@@ -520,7 +532,7 @@ struct TileLanes {
         if (__any_sync(gmask, bd)) border = true;
         return __popcll(I.w0) + __popcll(I.w1);
     }
-    __device__ __forceinline__ bool fit(const Mask &S, int nS, float4 &pl, float &ratio) const {
+    __device__ __forceinline__ bool fit(const Mask &S, int nS, float4 &pl, float4 &coef, float &ratio) const {
         MomentAcc acc = macc_zero();
 #pragma unroll 2
         for (int k = l * CH; k < (l + 1) * CH; k++) {
@@ -533,12 +545,13 @@ struct TileLanes {
         Moments m = moments_shfl(gmask, part, g0);
 #pragma unroll
         for (int c = 1; c < L; c++) m = moments_add(m, moments_shfl(gmask, part, g0 + c));
-        return solve_moments(m, nS, ax, ay, az, g.solver, &pl, &ratio);
+        return solve_moments(m, nS, ax, ay, az, g.solver, g.plane3, &pl, &coef, &ratio);
     }
 };
 
 struct RecOut {
     float4 plane, tplane;
+    float4 coef;          // plane3: the coefficients of the last spatial fit (kept in Scratch::coef)
     uint32_t kref, amask;
     uint8_t status, rounds, flags, nv, n_inl, t_rounds, t_inl, t_status;
     uint32_t acnt[4];
@@ -568,6 +581,7 @@ __device__ __forceinline__ RecOut read_rec(const TileRec *src_rec) {
     o.status = q2.z & 0xff; o.rounds = (q2.z >> 8) & 0xff; o.flags = (q2.z >> 16) & 0xff; o.nv = q2.z >> 24;
     o.n_inl = q2.w & 0xff; o.t_rounds = (q2.w >> 8) & 0xff; o.t_inl = (q2.w >> 16) & 0xff; o.t_status = q2.w >> 24;
     o.acnt[0] = o.acnt[1] = o.acnt[2] = o.acnt[3] = 0;
+    o.coef = make_float4(0.f, 0.f, 0.f, 0.f);
     return o;
 }
 
@@ -626,7 +640,7 @@ __device__ __forceinline__ bool spatial_rounds(const TV &tv, RecOut &o, int max_
     bool done = false;
     for (int r = 0; r < max_rounds; r++) {
         float ratio = 0.f;
-        const bool degen = tv.fit(S, nS, o.plane, ratio);
+        const bool degen = tv.fit(S, nS, o.plane, o.coef, ratio);
         if (ratio >= 0.999e-12f && ratio <= 1.001e-12f) o.flags |= 1;
         o.rounds++;
         const int nI = degen ? 0 : tv.inliers(o.plane, I, border);
@@ -774,7 +788,7 @@ __global__ void __launch_bounds__(kFitThreads) k_fit_first(Geometry g, Scratch s
     TileRec *recs = s.tiles + (size_t)b.slot[f] * g.NT;
     const TV tv(g, rimg, t);
     RecOut o;
-    o.plane = o.tplane = make_float4(0.f, 0.f, 0.f, 0.f);
+    o.plane = o.tplane = o.coef = make_float4(0.f, 0.f, 0.f, 0.f);
     o.kref = 0xFFFFFFFFu;
     o.amask = 0;
     o.acnt[0] = o.acnt[1] = o.acnt[2] = o.acnt[3] = 0;
@@ -797,6 +811,7 @@ __global__ void __launch_bounds__(kFitThreads) k_fit_first(Geometry g, Scratch s
         queue_push(queued, ((uint32_t)f << 26) | (uint32_t)t, s.queue + (size_t)b.qset * 2 * s.qcap,
                    s.qcount + 8 * b.qset);
     write_rec(recs + t, o);
+    if (g.plane3) s.coef[(size_t)b.slot[f] * g.NT + t] = o.coef;
 }
 
 // Further spatial rounds (at most max_rounds) for every queued tile, a group of
@@ -827,6 +842,7 @@ __global__ void __launch_bounds__(kFitThreads) k_fit_round(Geometry g, Scratch s
         const bool leader = tv.l == 0;
         queue_push(!done && leader, item, qout, qcount + out_q);
         if (leader) write_rec(recs + t, o);
+        if (leader && g.plane3) s.coef[(size_t)b.slot[f] * g.NT + t] = o.coef;
     }
 }
 
@@ -1037,9 +1053,14 @@ __global__ void __launch_bounds__(kFitThreads) k_temporal(Geometry g, Scratch s,
 // group first marks which of the tiles to its left were fitted (lane j reads
 // the status of tile t-1-j, a ballot gathers them), then tests the fitted
 // planes one after another, every lane its own pixels, and adds the inlier
-// counts by shuffles: every lane of the group works on every test, whatever
+// counts by ballots: every lane of the group works on every test, whatever
 // share of the candidate tiles holds a plane.
-template <int TH_, int TW_, int LPT>
+//
+// kTOnly: the update after the temporal test of P frames whose spatial fits
+// (and full pre-test) ran first: only the candidates that became temporal are
+// tested, against their relaxed planes, and only their bits and counts are
+// rewritten; a tile with no temporal candidate does nothing.
+template <int TH_, int TW_, int LPT, bool kTOnly>
 __global__ void __launch_bounds__(kFitThreads) k_lookbehind(Geometry g, Scratch s, Batch b) {
     constexpr int PX = TH_ * TW_;
     constexpr int PPL = (PX + LPT - 1) / LPT;
@@ -1076,9 +1097,11 @@ __global__ void __launch_bounds__(kFitThreads) k_lookbehind(Geometry g, Scratch 
     if (l < ncand) {
         const TileRec *src = recs + (t - 1 - l);
         const uint32_t w0 = *reinterpret_cast<const uint32_t *>(reinterpret_cast<const uint8_t *>(src) + 40);
-        fitted = (w0 & 0xff) == S_FIT || (g.truns && (w0 & 0xff) == S_TEMPORAL);
+        fitted = kTOnly ? (w0 & 0xff) == S_TEMPORAL
+                        : ((w0 & 0xff) == S_FIT || (g.truns && (w0 & 0xff) == S_TEMPORAL));
     }
     const unsigned fmask = (__ballot_sync(gmask, fitted) & gmask) >> gbase;
+    if (kTOnly && !fmask) return;   // group-uniform: no candidate became temporal
     const int need = need_inliers(g.fmin, nv);
     int my_nin = 0;
     uint32_t pass_mask = 0;
@@ -1088,20 +1111,25 @@ __global__ void __launch_bounds__(kFitThreads) k_lookbehind(Geometry g, Scratch 
         const float4 pl = recs[t - 1 - j].plane;
         int c = 0;
 #pragma unroll
-        for (int q = 0; q < PPL; q++)
-            if (pr[q] > 0.0f) c += inlier_screened(pl, pux[q], puy[q], puz[q], pr[q], g.thr, border) ? 1 : 0;
-#pragma unroll
-        for (int off = LPT / 2; off; off >>= 1) c += __shfl_xor_sync(gmask, c, off);
+        for (int q = 0; q < PPL; q++) {
+            const bool in = pr[q] > 0.0f && inlier_screened(pl, pux[q], puy[q], puz[q], pr[q], g.thr, border);
+            c += __popc(__ballot_sync(gmask, in) & gmask);
+        }
         if (l == j) my_nin = c;
         if (c >= need) pass_mask |= 1u << j;
     }
     if (live) {
         uint8_t *lb = s.lbcnt + ((size_t)b.slot[f] * g.NT + t) * 32;
-        lb[l] = (uint8_t)my_nin;
-        if (LPT == 16) lb[l + 16] = 0;
         uint8_t *base = reinterpret_cast<uint8_t *>(recs + t);
-        if (l < 16) base[48 + l] = (uint8_t)my_nin;
-        if (l == 0) *reinterpret_cast<uint32_t *>(base + 36) = pass_mask;
+        if (!kTOnly || ((fmask >> l) & 1u)) {
+            lb[l] = (uint8_t)my_nin;
+            if (l < 16) base[48 + l] = (uint8_t)my_nin;
+        }
+        if (!kTOnly && LPT == 16) lb[l + 16] = 0;
+        if (l == 0) {
+            uint32_t *mw = reinterpret_cast<uint32_t *>(base + 36);
+            *mw = kTOnly ? ((*mw & ~fmask) | pass_mask) : pass_mask;
+        }
     }
 }
 
@@ -1119,15 +1147,15 @@ static cudaError_t launch_fit_first_t(const Geometry &g, const Scratch &s, const
     return cudaGetLastError();
 }
 
-template <int TH_, int TW_>
+template <int TH_, int TW_, bool kTOnly>
 static cudaError_t launch_lookbehind_t(const Geometry &g, const Scratch &s, const Batch &b, cudaStream_t st) {
     if (!g.merge || g.lookahead <= 0) return cudaSuccess;
     if (g.lookahead <= 16) {
         constexpr int TPB = kFitThreads / 16;
-        k_lookbehind<TH_, TW_, 16><<<dim3((g.NT + TPB - 1) / TPB, b.nframes), kFitThreads, 0, st>>>(g, s, b);
+        k_lookbehind<TH_, TW_, 16, kTOnly><<<dim3((g.NT + TPB - 1) / TPB, b.nframes), kFitThreads, 0, st>>>(g, s, b);
     } else {
         constexpr int TPB = kFitThreads / 32;
-        k_lookbehind<TH_, TW_, 32><<<dim3((g.NT + TPB - 1) / TPB, b.nframes), kFitThreads, 0, st>>>(g, s, b);
+        k_lookbehind<TH_, TW_, 32, kTOnly><<<dim3((g.NT + TPB - 1) / TPB, b.nframes), kFitThreads, 0, st>>>(g, s, b);
     }
     return cudaGetLastError();
 }
@@ -1192,12 +1220,19 @@ cudaError_t launch_queued_rounds(const Geometry &g, const Scratch &s, const Batc
     return cudaErrorInvalidValue;
 }
 
-cudaError_t launch_lookbehind(const Geometry &g, const Scratch &s, const Batch &b, cudaStream_t st) {
+cudaError_t launch_lookbehind(const Geometry &g, const Scratch &s, const Batch &b, cudaStream_t st, bool temporal_only) {
     if (b.nframes <= 0) return cudaSuccess;
-    if (g.th == 4 && g.tw == 4) return launch_lookbehind_t<4, 4>(g, s, b, st);
-    if (g.th == 4 && g.tw == 8) return launch_lookbehind_t<4, 8>(g, s, b, st);
-    if (g.th == 8 && g.tw == 8) return launch_lookbehind_t<8, 8>(g, s, b, st);
-    if (g.th == 8 && g.tw == 16) return launch_lookbehind_t<8, 16>(g, s, b, st);
+    if (temporal_only) {
+        if (g.th == 4 && g.tw == 4) return launch_lookbehind_t<4, 4, true>(g, s, b, st);
+        if (g.th == 4 && g.tw == 8) return launch_lookbehind_t<4, 8, true>(g, s, b, st);
+        if (g.th == 8 && g.tw == 8) return launch_lookbehind_t<8, 8, true>(g, s, b, st);
+        if (g.th == 8 && g.tw == 16) return launch_lookbehind_t<8, 16, true>(g, s, b, st);
+        return cudaErrorInvalidValue;
+    }
+    if (g.th == 4 && g.tw == 4) return launch_lookbehind_t<4, 4, false>(g, s, b, st);
+    if (g.th == 4 && g.tw == 8) return launch_lookbehind_t<4, 8, false>(g, s, b, st);
+    if (g.th == 8 && g.tw == 8) return launch_lookbehind_t<8, 8, false>(g, s, b, st);
+    if (g.th == 8 && g.tw == 16) return launch_lookbehind_t<8, 16, false>(g, s, b, st);
     return cudaErrorInvalidValue;
 }
 

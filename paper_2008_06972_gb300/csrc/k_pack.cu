@@ -188,13 +188,24 @@ __global__ void __launch_bounds__(kPackWarps * 32) k_pack(Geometry g, Scratch s,
             atomicOr(words + L.sec[0] + (pos >> 5), piece << sh);
             if (sh + TW_ > 32) atomicOr(words + L.sec[0] + (pos >> 5) + 1, piece >> (32 - sh));
         }
-        if (mode) atomicOr(words + L.sec[1] + (t >> 3), (uint32_t)mode << (4 * (t & 7)));
+        // three-coefficient planes: a run start's record is its fit's coefficients and its tile code
+        // names the dominant axis
+        const float4 cf = (g.plane3 && mode == T_RUN_START) ? s.coef[slot * g.NT + t] : make_float4(0.f, 0.f, 0.f, 0.f);
+        const uint32_t code = (g.plane3 && mode == T_RUN_START) ? (uint32_t)T_RUN_START3 + (uint32_t)cf.w : mode;
+        if (code) atomicOr(words + L.sec[1] + (t >> 3), code << (4 * (t & 7)));
         if (mode == T_RUN_START) {
-            uint32_t *d = words + L.sec[2] + 4u * off.run;
-            d[0] = __float_as_uint(pl.x);
-            d[1] = __float_as_uint(pl.y);
-            d[2] = __float_as_uint(pl.z);
-            d[3] = __float_as_uint(pl.w);
+            if (g.plane3) {
+                uint32_t *d = words + L.sec[2] + 3u * off.run;
+                d[0] = __float_as_uint(cf.x);
+                d[1] = __float_as_uint(cf.y);
+                d[2] = __float_as_uint(cf.z);
+            } else {
+                uint32_t *d = words + L.sec[2] + 4u * off.run;
+                d[0] = __float_as_uint(pl.x);
+                d[1] = __float_as_uint(pl.y);
+                d[2] = __float_as_uint(pl.z);
+                d[3] = __float_as_uint(pl.w);
+            }
         }
         if (mode == T_TEMPORAL) {
             uint32_t *d = words + L.sec[3] + 2u * off.temporal;

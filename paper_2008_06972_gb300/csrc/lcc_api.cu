@@ -195,10 +195,11 @@ lcc_status encode_batch(lcc_ctx *c, int kind, int nframes, const int *slots, uin
         LCC_LAUNCH(c, 1, launch_fit(c->g, c->s, bs, p, c->stream));
         LCC_LAUNCH_N(c, 3, queued_round_kernels(c->g, bs), launch_queued_rounds(c->g, c->s, bs, c->stream));
         const bool pretest = c->g.merge && c->g.lookahead > 0;
-        // with temporal runs the pre-test also tests against temporal tiles' planes: after the test
-        if (pretest && !c->g.truns) LCC_LAUNCH(c, 8, launch_lookbehind(c->g, c->s, b, c->stream));
+        if (pretest) LCC_LAUNCH(c, 8, launch_lookbehind(c->g, c->s, b, c->stream));
         LCC_LAUNCH(c, 9, launch_temporal(c->g, c->s, b, p, c->stream));
-        if (pretest && c->g.truns) LCC_LAUNCH(c, 8, launch_lookbehind(c->g, c->s, b, c->stream));
+        // with temporal runs, the candidates that became temporal are tested again against their
+        // relaxed planes
+        if (pretest && c->g.truns) LCC_LAUNCH(c, 8, launch_lookbehind(c->g, c->s, b, c->stream, true));
         LCC_LAUNCH(c, 2, launch_merge(c->g, c->s, b, c->stream));
         LCC_LAUNCH(c, 4, launch_pack(c->g, c->s, b, c->stream));
         return LCC_OK;
@@ -298,6 +299,7 @@ void lcc_default_params(lcc_params *p) {
     p->raw_exact = 0;
     p->temporal_candidates = 1;
     p->temporal_runs = 1;
+    p->plane3 = 0;
 }
 
 lcc_status lcc_create(lcc_ctx **out, const lcc_sensor *sensor, const lcc_params *params, void *cuda_stream) {
@@ -314,7 +316,8 @@ lcc_status lcc_create(lcc_ctx **out, const lcc_sensor *sensor, const lcc_params 
         !(p.min_inlier_frac >= 0) || p.max_batch < 1 || p.max_batch > kMaxBatch || p.lookahead < 0 ||
         p.lookahead > 32 || p.solver < 0 || p.solver > 1 || p.fit_schedule < 0 ||
         p.fit_schedule > 4 || p.no_delta < 0 || p.no_delta > 1 || p.raw_exact < 0 || p.raw_exact > 1 ||
-        p.temporal_candidates < 0 || p.temporal_candidates > 4 || p.temporal_runs < 0 || p.temporal_runs > 1)
+        p.temporal_candidates < 0 || p.temporal_candidates > 4 || p.temporal_runs < 0 || p.temporal_runs > 1 ||
+        p.plane3 < 0 || p.plane3 > 1)
         return LCC_ERR_INVALID_ARG;
     int dev = 0;
     cudaDeviceProp prop;
@@ -350,6 +353,7 @@ lcc_status lcc_create(lcc_ctx **out, const lcc_sensor *sensor, const lcc_params 
     g.raw_exact = p.raw_exact;
     g.tcand = p.temporal_candidates;
     g.truns = p.temporal_runs && p.merge_runs ? 1 : 0;
+    g.plane3 = p.plane3 ? 1 : 0;
     g.first_rounds = std::min(p.fit_schedule >= 3 ? 1 : p.fit_schedule, p.max_refits + 1);
     g.k_max = (int)floorf(p.fit_thr_m / p.quant_m + 0.5f) + 1;
     g.w_res = bits_for(2 * g.k_max);
@@ -398,7 +402,8 @@ lcc_status lcc_create(lcc_ctx **out, const lcc_sensor *sensor, const lcc_params 
     const size_t o_qcount = o_queue + align256(4 * sl * nt * 4);
     const size_t o_rowdone = o_qcount + 256;
     const size_t o_kplanes = o_rowdone + align256(sl * 4);
-    const size_t total = o_kplanes + align256(nt * sizeof(float4));
+    const size_t o_coef = o_kplanes + align256(nt * sizeof(float4));
+    const size_t total = o_coef + (p.plane3 ? align256(sl * nt * sizeof(float4)) : 0);
     if (cudaMalloc(&c->d_scratch, total) != cudaSuccess) {
         cudaFree(c->d_tables);
         delete c;
@@ -421,6 +426,7 @@ lcc_status lcc_create(lcc_ctx **out, const lcc_sensor *sensor, const lcc_params 
     c->s.qcount = (uint32_t *)(base + o_qcount);
     c->s.rowdone = (uint32_t *)(base + o_rowdone);
     c->d_kplanes = (float4 *)(base + o_kplanes);
+    c->s.coef = p.plane3 ? (float4 *)(base + o_coef) : nullptr;
     c->s.qcap = (uint32_t)(sl * nt);
     cudaMemset(c->d_scratch, 0, total);
     cudaMemset(c->s.rimg, 0xFF, sl * npx * 4);
@@ -708,7 +714,7 @@ lcc_status encode_sequence(lcc_ctx *c, int32_t nframes, int32_t key_index, const
         if (c->g.schedule >= 1)
             LCC_LAUNCH_N(c, 3, queued_round_kernels(c->g, bp), launch_queued_rounds(c->g, c->s, bp, c->stream));
         const bool ppretest = c->g.merge && c->g.lookahead > 0;
-        if (ppretest && !c->g.truns) LCC_LAUNCH(c, 8, launch_lookbehind(c->g, c->s, bp, c->stream));
+        if (ppretest) LCC_LAUNCH(c, 8, launch_lookbehind(c->g, c->s, bp, c->stream));
         // key frame: the rest of its rounds and its pre-test, merge (its coding planes), pack
         c->stream = c->kstream;
         if (c->g.schedule >= 1)
@@ -723,8 +729,9 @@ lcc_status encode_sequence(lcc_ctx *c, int32_t nframes, int32_t key_index, const
         LCC_CUDA(cudaStreamWaitEvent(c->side, c->ev_kplanes, 0));
         for (int f = 0; f < np; f++) bp.kf[f] = k->planes;
         LCC_LAUNCH(c, 9, launch_temporal(c->g, c->s, bp, pp, c->stream));
-        // with temporal runs the P frames' pre-test needs the temporal tiles' planes: after the test
-        if (ppretest && c->g.truns) LCC_LAUNCH(c, 8, launch_lookbehind(c->g, c->s, bp, c->stream));
+        // with temporal runs, the P tiles' candidates that became temporal are tested again against
+        // their relaxed planes (a pass that skips every tile without such a candidate)
+        if (ppretest && c->g.truns) LCC_LAUNCH(c, 8, launch_lookbehind(c->g, c->s, bp, c->stream, true));
         LCC_LAUNCH(c, 2, launch_merge(c->g, c->s, bp, c->stream));
         LCC_LAUNCH(c, 4, launch_pack(c->g, c->s, bp, c->stream));
         LCC_CUDA(cudaEventRecord(c->ev_join, c->side));
@@ -982,6 +989,14 @@ lcc_status lcc_tile_records(lcc_ctx *c, int32_t frame, lcc_tile_info *h_out, int
     if (cudaStreamSynchronize(c->stream) != cudaSuccess) return LCC_ERR_CUDA;
     LCC_CUDA(cudaMemcpy(h_out, c->s.tiles + (size_t)frame * c->g.NT, sizeof(TileRec) * c->g.NT,
                         cudaMemcpyDeviceToHost));
+    return LCC_OK;
+}
+
+lcc_status lcc_tile_coefficients(lcc_ctx *c, int32_t frame, float *h_out, int64_t cap) {
+    if (!c || !h_out || frame < 0 || frame >= c->last_nframes || cap < c->g.NT) return LCC_ERR_INVALID_ARG;
+    if (!c->s.coef) return LCC_ERR_UNSUPPORTED;
+    if (cudaStreamSynchronize(c->stream) != cudaSuccess) return LCC_ERR_CUDA;
+    LCC_CUDA(cudaMemcpy(h_out, c->s.coef + (size_t)frame * c->g.NT, sizeof(float4) * c->g.NT, cudaMemcpyDeviceToHost));
     return LCC_OK;
 }
 

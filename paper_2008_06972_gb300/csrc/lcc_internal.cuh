@@ -40,7 +40,8 @@ constexpr int kVersion = 1;
 constexpr int kMaxTilePx = 128;
 
 // tile codes in the stream
-enum : uint8_t { T_EMPTY = 0, T_RAW = 1, T_RUN_START = 2, T_RUN_CONT = 3, T_TEMPORAL = 4, T_TEMPORAL_CONT = 5 };
+enum : uint8_t { T_EMPTY = 0, T_RAW = 1, T_RUN_START = 2, T_RUN_CONT = 3, T_TEMPORAL = 4, T_TEMPORAL_CONT = 5,
+                 T_RUN_START3 = 6 /* .. 8: a three-coefficient run start, dominant axis x, y, z */ };
 // own-fit status of a tile
 enum : uint8_t { S_EMPTY = 0, S_FAIL = 1, S_FIT = 2, S_TEMPORAL = 3 };
 // latched device error bits
@@ -116,6 +117,7 @@ struct Geometry {
     int raw_exact;       // 1: raw pixels carry their fp32 range bits (32-bit raw codes)
     int tcand;           // K tiles a P tile's relaxed-plane test may try (1..4)
     int truns;           // 1: temporal tiles of P frames grow runs (TEMPORAL_CONT tiles)
+    int plane3;          // 1: planes in Eq. 3's three-coefficient form (dominant axis)
     int k_max, w_res, w_raw;
     float elev_max_rad, inv_d_el, inv_d_az;   // first guesses only (1/row and 1/column pitch, rad); the tables decide
     const float *ce, *se, *ct, *st;       // beam tables
@@ -139,6 +141,7 @@ struct Scratch {
     uint32_t *qcount;    // [2 sets][8] items pushed per fit round
     uint32_t *rowdone;   // [slots] tile rows of the frame merged so far (0 between launches)
     uint32_t qcap;       // entries per queue (slots * tiles)
+    float4 *coef;        // [slots][NT] plane3: a tile's plane coefficients (a, b, c, axis) of its last fit
 };
 
 // One batched launch over up to kMaxBatch frames of the same sensor.
@@ -297,6 +300,34 @@ __device__ __forceinline__ int bin_point(const Geometry &g, float x, float y, fl
     return 0;
 }
 
+// Eq. 3 generalised to the dominant axis k of a unit-normal plane (largest |n_k|, lowest index on
+// ties; i, j the next axes in cyclic order): a = n_i / n_k, b = n_j / n_k, c = d / n_k, and back:
+// n_k = 1 / sqrt(a^2 + b^2 + 1), n_i = a n_k, n_j = b n_k, d = c n_k, negated when d < 0 (|d| <
+// 1e-9 keeps n_k > 0).  IEEE fp32 operations in a fixed order, so encoder and decoder agree.
+__device__ __forceinline__ float4 plane_to3(float4 pl) {
+    const float n[3] = {pl.x, pl.y, pl.z};
+    int k = 0;
+    float m = fabsf(n[0]);
+    if (fabsf(n[1]) > m) { k = 1; m = fabsf(n[1]); }
+    if (fabsf(n[2]) > m) k = 2;
+    const float nk = n[k];
+    return make_float4(__fdiv_rn(n[(k + 1) % 3], nk), __fdiv_rn(n[(k + 2) % 3], nk), __fdiv_rn(pl.w, nk), (float)k);
+}
+
+__device__ __forceinline__ float4 plane_from3(float4 c) {
+    const int k = (int)c.w;
+    const float inv = __fdiv_rn(1.0f, __fsqrt_rn(fmaf(c.x, c.x, fmaf(c.y, c.y, 1.0f))));
+    float n[3];
+    n[k] = inv;
+    n[(k + 1) % 3] = __fmul_rn(c.x, inv);
+    n[(k + 2) % 3] = __fmul_rn(c.y, inv);
+    float d = __fmul_rn(c.z, inv);
+    if (!(fabsf(d) < 1e-9f) && d < 0.0f) {
+        n[0] = -n[0]; n[1] = -n[1]; n[2] = -n[2]; d = -d;
+    }
+    return make_float4(n[0], n[1], n[2], d);
+}
+
 // n' = R^T n in fp64 with a fixed operation order, rounded to fp32.
 __device__ __forceinline__ void rotate_normal(const double *M, float nx, float ny, float nz, float *o) {
 #pragma unroll
@@ -389,7 +420,10 @@ cudaError_t launch_range_image(const Geometry &g, const uint32_t *rimg, float *r
                                cudaStream_t st);
 cudaError_t launch_fit(const Geometry &g, const Scratch &s, const Batch &b, const Poses &p, cudaStream_t st);
 cudaError_t launch_temporal(const Geometry &g, const Scratch &s, const Batch &b, const Poses &p, cudaStream_t st);
-cudaError_t launch_lookbehind(const Geometry &g, const Scratch &s, const Batch &b, cudaStream_t st);
+// temporal_only: after the temporal test of P frames whose full pre-test ran before it, rewrite the
+// bits and counts of the candidates that became temporal (tested against their relaxed planes)
+cudaError_t launch_lookbehind(const Geometry &g, const Scratch &s, const Batch &b, cudaStream_t st,
+                              bool temporal_only = false);
 cudaError_t launch_queued_rounds(const Geometry &g, const Scratch &s, const Batch &b, cudaStream_t st);
 
 // Spatial rounds still to run after a batch's first fit pass under a queued schedule: all of

@@ -79,7 +79,7 @@ __device__ __forceinline__ void scan_frame(const Geometry &g, const Scratch &s, 
         L.sec[0] = 0;
         L.sec[1] = L.sec[0] + words_for((uint64_t)g.H * g.W);
         L.sec[2] = L.sec[1] + words_for((uint64_t)g.NT * 4);
-        L.sec[3] = L.sec[2] + 4u * runs;
+        L.sec[3] = L.sec[2] + (g.plane3 ? 3u : 4u) * runs;   // three-coefficient planes: 3 words a run
         L.sec[4] = L.sec[3] + 2u * temporal;
         L.sec[5] = L.sec[4] + words_for(cand);
         L.sec[6] = L.sec[5] + (g.no_delta ? 0u : words_for((uint64_t)fitted * g.w_res));   // no deltas: none
@@ -100,7 +100,7 @@ __device__ __forceinline__ void scan_frame(const Geometry &g, const Scratch &s, 
             hw[0] = kMagic;
             hw[1] = (uint32_t)kVersion | ((uint32_t)b.kind << 16) | ((uint32_t)(g.merge ? 1 : 0) << 24) |
                     ((uint32_t)(g.no_delta ? 1 : 0) << 25) | ((uint32_t)(g.raw_exact ? 1 : 0) << 26) |
-                    ((uint32_t)(g.truns && b.kind == 1 ? 1 : 0) << 27);
+                    ((uint32_t)(g.truns && b.kind == 1 ? 1 : 0) << 27) | ((uint32_t)(g.plane3 ? 1 : 0) << 28);
             hw[2] = (uint32_t)g.H | ((uint32_t)g.W << 16);
             hw[3] = (uint32_t)g.th | ((uint32_t)g.tw << 8) | ((uint32_t)g.w_res << 16) | ((uint32_t)g.w_raw << 24);
             hw[4] = __float_as_uint(g.thr);

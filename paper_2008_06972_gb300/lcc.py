@@ -17,6 +17,7 @@ LIB_PATH = os.path.join(_HERE, "liblcc.so")
 
 OK, ERR_INVALID_ARG, ERR_CAPACITY, ERR_CUDA, ERR_TIMEOUT, ERR_CORRUPT, ERR_UNSUPPORTED, ERR_NO_DEVICE = range(8)
 T_EMPTY, T_RAW, T_RUN_START, T_RUN_CONT, T_TEMPORAL, T_TEMPORAL_CONT = range(6)
+T_RUN_START3 = 6   # .. 8: a three-coefficient run start along axis x, y, z
 S_EMPTY, S_FAIL, S_FIT, S_TEMPORAL = range(4)
 
 
@@ -37,7 +38,7 @@ class lcc_params(ctypes.Structure):
                 ("merge_runs", ctypes.c_int32), ("max_batch", ctypes.c_int32), ("lookahead", ctypes.c_int32),
                 ("solver", ctypes.c_int32), ("fit_schedule", ctypes.c_int32), ("no_delta", ctypes.c_int32),
                 ("raw_exact", ctypes.c_int32), ("temporal_candidates", ctypes.c_int32),
-                ("temporal_runs", ctypes.c_int32)]
+                ("temporal_runs", ctypes.c_int32), ("plane3", ctypes.c_int32)]
 
 
 class lcc_stats(ctypes.Structure):
@@ -116,6 +117,7 @@ def load(path: str = LIB_PATH):
         "lcc_sync": (i32, [vp]),
         "lcc_last_stats": (i32, [vp, i32, vp]),
         "lcc_tile_records": (i32, [vp, i32, vp, i64]),
+        "lcc_tile_coefficients": (i32, [vp, i32, vp, i64]),
         "lcc_set_profiling": (i32, [vp, i32]),
         "lcc_kernel_times": (i32, [vp, vp, vp, vp, i32]),
         "lcc_kernel_timeline": (i32, [vp, vp, vp, vp, i32]),
@@ -160,7 +162,7 @@ def exported_symbols() -> list[str]:
             "lcc_num_tiles", "lcc_tables", "lcc_range_image", "lcc_keyframe_create", "lcc_keyframe_free",
             "lcc_encode_keyframe", "lcc_encode_keyframe_seeded", "lcc_encode_keyframes", "lcc_encode_pframe", "lcc_encode_pframes", "lcc_encode_sequence",
             "lcc_encode_sequence_host", "lcc_keyframe_from_stream", "lcc_decode", "lcc_decode_sequence", "lcc_imu_pose", "lcc_entropy_encode", "lcc_entropy_decode", "lcc_sync", "lcc_last_stats",
-            "lcc_tile_records", "lcc_set_profiling", "lcc_kernel_times", "lcc_kernel_timeline", "lcc_range_image_static", "lcc_net_num_params", "lcc_net_create", "lcc_net_destroy",
+            "lcc_tile_records", "lcc_tile_coefficients", "lcc_set_profiling", "lcc_kernel_times", "lcc_kernel_timeline", "lcc_range_image_static", "lcc_net_num_params", "lcc_net_create", "lcc_net_destroy",
             "lcc_net_get_params", "lcc_net_set_params", "lcc_net_tile_inputs", "lcc_net_tile_inputs_batch", "lcc_net_forward", "lcc_net_sync", "lcc_net_gradient",
             "lcc_net_train_step", "lcc_selftest_bounded_wait", "lcc_plan_create", "lcc_plan_update",
             "lcc_plan_set_proposals", "lcc_plan_encode", "lcc_plan_capture", "lcc_plan_replay", "lcc_plan_sync", "lcc_plan_encode_host", "lcc_plan_get_info", "lcc_plan_stats",
@@ -399,6 +401,12 @@ class Context:
     def lcc_tile_records(self, frame: int = 0) -> np.ndarray:
         out = np.zeros(self.num_tiles, TILE_INFO_DTYPE)
         _check(self.lib.lcc_tile_records(self.h, frame, out.ctypes.data, len(out)), "lcc_tile_records")
+        return out
+
+    def lcc_tile_coefficients(self, frame: int = 0) -> np.ndarray:
+        """(T, 4) float32: a, b, c and the axis of each tile's last fit (plane3 contexts)."""
+        out = np.zeros((self.num_tiles, 4), np.float32)
+        _check(self.lib.lcc_tile_coefficients(self.h, frame, out.ctypes.data, self.num_tiles), "lcc_tile_coefficients")
         return out
 
     def lcc_set_profiling(self, enable: bool):

@@ -2,7 +2,8 @@
 
 Layout (little-endian): a 64-byte header, then 32-bit-word sections in this
 order: occupancy bitmap (rows*cols bits, raster), tile codes (4 bits per tile),
-run planes (4 fp32 words each), temporal records (u32 K-tile index, fp32 c'),
+run planes (4 fp32 words each; with flags bit 4, Eq. 3's three coefficients each, the run start's
+tile code 6 + axis naming the dominant axis), temporal records (u32 K-tile index, fp32 c'),
 fitted bits (one per candidate pixel), residual codes (w_res bits, k + k_max;
 none when flags bit 1, the no-delta mode, is set), raw codes (w_raw bits).  Bits
 are LSB-first within words.
@@ -30,7 +31,8 @@ def _words(n_bits):
 def sections(bits) -> dict:
     h = header(bits)
     sizes = [("bitmap", _words(h["rows"] * h["cols"])), ("tiles", _words(4 * h["n_tiles"])),
-             ("runs", 4 * h["n_runs"]), ("temporal", 2 * h["n_temporal"]), ("fitted", _words(h["n_cand"])),
+             ("runs", (3 if h["flags"] & 16 else 4) * h["n_runs"]),
+             ("temporal", 2 * h["n_temporal"]), ("fitted", _words(h["n_cand"])),
              ("res", 0 if h["flags"] & 2 else _words(h["n_fitted"] * h["w_res"])),
              ("raw", _words(h["n_raw"] * h["w_raw"]))]
     w = np.frombuffer(np.asarray(bits, np.uint8)[64:h["total_bytes"]].tobytes(), "<u4")

@@ -31,8 +31,8 @@ def _cuda():
     lcc.load()
 
 
-def _oparams(tile=(4, 4), thr=0.05, q=0.02, R=3, fmin=0.75, merge=1, no_delta=0, raw_exact=0, tcand=1):
-    return O.params(tile[0], tile[1], thr, q, R, fmin, merge, no_delta, raw_exact, tcand)
+def _oparams(tile=(4, 4), thr=0.05, q=0.02, R=3, fmin=0.75, merge=1, no_delta=0, raw_exact=0, tcand=1, plane3=0):
+    return O.params(tile[0], tile[1], thr, q, R, fmin, merge, no_delta, raw_exact, tcand, plane3=plane3)
 
 
 def _gparams(tile=(4, 4), thr=0.05, q=0.02, R=3, fmin=0.75, merge=1, solver=0, **kw):
@@ -97,7 +97,8 @@ def _keyframe_case(sensor_, pts, **kw):
     assert border <= max(2, 0.005 * compared), f"{border} borderline tiles of {compared}"
     # Layer 1: the oracle's merge + code + pack on the GPU's planes reproduces the GPU stream
     planes, ok = H.gpu_planes(recs)
-    cbits, _, _ = O.pack(s, p, 0, rng, planes, ok)
+    coef = c.lcc_tile_coefficients(0) if p.plane3 else None
+    cbits, _, _ = O.pack(s, p, 0, rng, planes, ok, fit_coef=coef)
     assert cbits.tobytes() == gbits.tobytes()
     # with identical planes the streams are identical outright
     obits, _, _, _ = O.encode_keyframe(s, p, pts)
@@ -221,12 +222,12 @@ def test_schedule_invariance_and_determinism(cfg1):
 
 # ------------------------------------------------------------------- P frames --
 
-def _pframe_case(seq, frames, tile=(4, 4), thr=0.05, poses=None, schedule=0, tcand=1):
+def _pframe_case(seq, frames, tile=(4, 4), thr=0.05, poses=None, schedule=0, tcand=1, plane3=0):
     from paper_2008_06972_gb300 import lcc
     s = O.sensor(seq.sensor)
-    p = _oparams(tile=tile, thr=thr, tcand=tcand)
+    p = _oparams(tile=tile, thr=thr, tcand=tcand, plane3=plane3)
     c = H.ctx(seq.sensor, **_gparams(tile=tile, thr=thr, max_batch=max(16, len(frames)), fit_schedule=schedule,
-                                     temporal_candidates=tcand))
+                                     temporal_candidates=tcand, plane3=plane3))
     kf = lcc.Keyframe(c)
     kbits, krecs = H.encode_keyframe(c, seq.frames[seq.key_index], kf)
     okft = O.kf_table_from_stream(s, kbits, c.num_tiles)
@@ -272,7 +273,8 @@ def _pframe_case(seq, frames, tile=(4, 4), thr=0.05, poses=None, schedule=0, tca
         total_border += border + b2
         planes, ok = H.gpu_planes(recs)
         tplanes, kref = H.gpu_temporal(recs)
-        cbits, _, _ = O.pack(s, p, 1, rng, planes, ok, tplanes, kref)
+        coef = c.lcc_tile_coefficients(i) if plane3 else None
+        cbits, _, _ = O.pack(s, p, 1, rng, planes, ok, tplanes, kref, fit_coef=coef)
         assert cbits.tobytes() == pbits[i].tobytes(), f"frame {f}: stream differs from the oracle's packing"
         codes = streamfmt.tile_codes(pbits[i])
         assert np.isin(codes[temporal], [4, 5]).all()            # temporal run start or continuation
@@ -459,7 +461,7 @@ def test_largest_resolution_sequence_with_noisy_poses():
 def test_profiler_counts_every_kernel_and_orders_the_timeline(cfg2_seq):
     """The profiler's launch counts (what bench.py reports as gpu_launches) are the kernels a
     sequence call launches: per call, two binnings, two first fit passes, two queued-round
-    launches (fit schedule 3), two run pre-tests, two merges, two packs and one temporal test;
+    launches (fit schedule 3), three run pre-tests, two merges, two packs and one temporal test;
     the timeline lists the same launches, each ending after it starts."""
     from paper_2008_06972_gb300 import lcc
     seq = cfg2_seq
@@ -479,7 +481,9 @@ def test_profiler_counts_every_kernel_and_orders_the_timeline(cfg2_seq):
     times = c.lcc_kernel_times()
     tl = c.lcc_kernel_timeline()
     c.lcc_set_profiling(False)
-    per_call = {"bin": 2, "fit": 2, "rounds": 2, "lookbehind": 2, "merge": 2, "pack": 2, "temporal": 1}
+    # run pre-tests: the key frame's, the P frames' beside it, and (temporal runs) the P frames' update
+    # against the tiles that became temporal
+    per_call = {"bin": 2, "fit": 2, "rounds": 2, "lookbehind": 3, "merge": 2, "pack": 2, "temporal": 1}
     assert {k: v[0] for k, v in times.items()} == {k: 3 * v for k, v in per_call.items()}
     assert len(tl) == 3 * sum(per_call.values())
     assert all(t1 >= t0 >= 0.0 for _, t0, t1 in tl)
@@ -696,3 +700,31 @@ def test_temporal_candidates_sequence_matches_separate_calls(cfg2_seq):
         for i, f in enumerate(others):
             assert pb[i].tobytes() == seq_bits[f].tobytes(), (tc, f)
     assert temporal[4] > temporal[1]
+
+
+# --------------------------------------------- Eq. 3's three-coefficient plane form (plane3) --
+
+@pytest.mark.parametrize("tile", [(4, 4), (8, 16)])
+def test_plane3_keyframe_parity(cfg2_seq, tile):
+    """Three-coefficient planes: the GPU's planes are the unit-normal planes of its coefficients (the
+    oracle's conversion, bit for bit), its stream is the oracle's packing of its planes and
+    coefficients, the fits agree with the oracle's plane3 fits (Layer 2), both decoders agree and
+    every pixel decodes within q/2."""
+    seq = cfg2_seq
+    r = _keyframe_case(seq.sensor, seq.frames[seq.key_index], tile=tile, plane3=1)
+    assert streamfmt.header(r["bits"])["flags"] & 16
+    coef = r["ctx"].lcc_tile_coefficients(0)
+    ok = r["recs"]["status"] == 2
+    for t in np.nonzero(ok)[0]:
+        back = O.plane_from3(int(coef[t, 3]), coef[t, :3])
+        assert np.array_equal(back.view(np.uint32), r["recs"]["plane"][t].view(np.uint32))
+    codes = streamfmt.tile_codes(r["bits"])
+    assert not (codes == 2).any() and np.isin(codes, [6, 7, 8]).sum() == streamfmt.header(r["bits"])["n_runs"]
+
+
+def test_plane3_pframe_parity(cfg2_seq):
+    """P frames of a three-coefficient key frame: temporal test against its reconstructed planes,
+    spatial fallback in the three-coefficient form, streams equal to the oracle's packing."""
+    seq = cfg2_seq
+    border = _pframe_case(seq, [1, seq.key_index + 2], plane3=1)
+    assert border <= 20

@@ -771,3 +771,84 @@ def test_temporal_cont_without_flag_or_after_a_spatial_tile_is_corrupt(cfg2_seq)
     bad = bits.copy()
     bad[word:word + 4] = np.frombuffer(v.to_bytes(4, "little"), np.uint8)
     assert O.decode_status(s, bad, kft, seq.poses[f]) == O.ERR_CORRUPT
+
+
+# ------------------------------------------------- Eq. 3's three-coefficient plane form --
+
+def test_three_coefficient_form_closed_forms():
+    """The dominant-axis form of Eq. 3: axis-aligned planes (the ground z = -1.7 m, walls x = 12 m,
+    y = -30 m), which x + a y + b z = c cannot hold when n_x = 0, convert and come back exactly;
+    a general plane's coefficients satisfy Eq. 3 along its dominant axis for points on it, and it
+    comes back within fp32 rounding with the canonical sign (d >= 0)."""
+    for pl, axis, abc in (((0.0, 0.0, -1.0, 1.7), 2, (0.0, 0.0, -1.7)), ((1.0, 0.0, 0.0, 12.0), 0, (0.0, 0.0, 12.0)),
+                          ((0.0, -1.0, 0.0, 30.0), 1, (0.0, 0.0, -30.0))):
+        k, c = O.plane_to3(np.array(pl, np.float32))
+        assert k == axis and np.array_equal(c, np.array(abc, np.float32))
+        assert np.array_equal(O.plane_from3(k, c), np.array(pl, np.float32))
+    rng = np.random.default_rng(3)
+    for _ in range(200):
+        n = rng.normal(size=3)
+        n /= np.linalg.norm(n)
+        d = rng.uniform(0.5, 60.0)
+        pl = np.array([*n, d], np.float32)
+        k, abc = O.plane_to3(pl)
+        assert k == int(np.argmax(np.abs(pl[:3])))
+        i, j = (k + 1) % 3, (k + 2) % 3
+        # Eq. 3 along axis k: p_k + a p_i + b p_j = c for a point on the plane (fp64)
+        p = d * n.astype(np.float64) + np.cross(n, rng.normal(size=3))
+        lhs = p[k] + float(abc[0]) * p[i] + float(abc[1]) * p[j]
+        assert abs(lhs - float(abc[2])) <= 1e-5 * max(1.0, abs(float(abc[2])))
+        back = O.plane_from3(k, abc)
+        assert back[3] >= 0 and np.abs(back - pl).max() <= 2e-6 * max(1.0, d)
+
+
+@pytest.mark.parametrize("tile", [(4, 4), (8, 8)])
+def test_three_coefficient_streams(cfg2_seq, tile):
+    """With plane3 every fitted plane is the plane of its stored coefficients (bit for bit), fits
+    agree with the unit-normal ones except near the threshold, each run record shrinks from 4 words
+    to 3 (the axis in the run start's tile code), and key and P streams decode within q/2 (the P frames' temporal test
+    against the key frame's reconstructed planes)."""
+    seq = cfg2_seq
+    s = O.sensor(seq.sensor)
+    p3 = O.params(tile[0], tile[1], plane3=1)
+    p4 = O.params(tile[0], tile[1])
+    kpts = seq.frames[seq.key_index]
+    b3, kft3, f3, m3 = O.encode_keyframe(s, p3, kpts)
+    b4, kft4, f4, m4 = O.encode_keyframe(s, p4, kpts)
+    ok = f3["status"] == O.FIT_OK
+    for t in np.nonzero(ok)[0]:
+        assert np.array_equal(O.plane_from3(int(f3["axis"][t]), f3["coef"][t]), f3["plane"][t])
+    same = (f3["status"] == f4["status"])
+    assert same.mean() > 0.995
+    both = ok & (f4["status"] == O.FIT_OK)
+    assert np.abs(f3["plane"][both] - f4["plane"][both]).max() < 1e-4
+    h3, h4 = streamfmt.header(b3), streamfmt.header(b4)
+    assert h3["flags"] & 16 and not (h4["flags"] & 16)
+    runs = h3["n_runs"]
+    assert len(streamfmt.sections(b3)["runs"]) == 3 * runs
+    codes = streamfmt.tile_codes(b3)
+    assert not (codes == O.T_RUN_START).any()
+    starts = np.nonzero(m3 == O.T_RUN_START)[0]
+    assert np.array_equal(codes[starts], O.T_RUN_START3 + f3["axis"][starts])
+    assert len(b4) - len(b3) == 4 * runs
+    rng, _, _ = O.range_image(s, kpts)
+    m = rng > 0
+    dec, _, _ = O.decode(s, b3)
+    assert np.abs(dec[m] - rng[m]).max() <= p3.quant_m / 2 + 1e-5
+    assert np.array_equal(O.kf_table_from_stream(s, b3, len(kft3)), kft3)
+    for f in (seq.key_index - 2, seq.key_index + 1):
+        bits, _, _, _ = O.encode_pframe(s, p3, kft3, seq.poses[f], seq.frames[f])
+        rng, _, _ = O.range_image(s, seq.frames[f])
+        m = rng > 0
+        dec, _, _ = O.decode(s, bits, kft3, seq.poses[f])
+        assert streamfmt.header(bits)["flags"] & 16
+        assert np.abs(dec[m] - rng[m]).max() <= p3.quant_m / 2 + 1e-5
+    # a unit-normal run start code in a three-coefficient stream is corrupt
+    sec = streamfmt.sections(b3)
+    t = int(starts[0])
+    word = 64 + 4 * (len(sec["bitmap"]) + t // 8)
+    v = int.from_bytes(b3[word:word + 4].tobytes(), "little")
+    v = (v & ~(0xF << (4 * (t % 8)))) | (O.T_RUN_START << (4 * (t % 8)))
+    bad = b3.copy()
+    bad[word:word + 4] = np.frombuffer(v.to_bytes(4, "little"), np.uint8)
+    assert O.decode_status(s, bad) == O.ERR_CORRUPT
