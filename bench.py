@@ -524,9 +524,10 @@ def run_batched(args, stream, hbm):
 
 def run_sweep(args, stream, seq, d_pts, flush):
     """The HDL-64E sequence under the swept parameters (tiles 4x4 and 8x8, fit thresholds 0.02,
-    0.05 and 0.10 m, q 0.02 m; and the no-delta mode at 0.02 m): device throughput (CUDA events,
-    L2 flushed between steps), compression ratio, tile modes and the max decode error of every
-    frame."""
+    0.05 and 0.10 m, q 0.02 m; the no-delta mode at 0.02 m; lossless raw codes; four temporal
+    candidates; temporal run growth off; three-coefficient planes; the FP64 plane solver): device
+    throughput (CUDA events, L2 flushed between steps), compression ratio, tile modes and the max
+    decode error of every frame."""
     import torch
     from paper_2008_06972_gb300 import lcc
     n_frames = len(seq.frames)
@@ -535,14 +536,18 @@ def run_sweep(args, stream, seq, d_pts, flush):
     H, W = seq.sensor.rows, seq.sensor.cols
     steps = max(10, min(args.steps, 50))
     rows = []
-    points = [(th, tw, thr, 0, 0, 1) for th, tw in ((4, 4), (8, 8)) for thr in (0.02, 0.05, 0.10)]
-    points += [(4, 4, 0.02, 1, 0, 1), (8, 8, 0.02, 1, 0, 1)]   # the paper's no-delta mode at a 2 cm threshold
-    points += [(4, 4, 0.05, 0, 1, 1)]                         # raw pixels kept losslessly (fp32 raw codes)
-    points += [(4, 4, 0.05, 0, 0, 4)]                         # up to 4 candidate K tiles per P tile
-    for th, tw, thr, nd, rx, tc in points:
+    points = [(th, tw, thr, 0, 0, 1, 1, 0, 0) for th, tw in ((4, 4), (8, 8)) for thr in (0.02, 0.05, 0.10)]
+    points += [(4, 4, 0.02, 1, 0, 1, 1, 0, 0), (8, 8, 0.02, 1, 0, 1, 1, 0, 0)]   # the paper's no-delta mode at 2 cm
+    points += [(4, 4, 0.05, 0, 1, 1, 1, 0, 0)]                      # raw pixels kept losslessly (fp32 raw codes)
+    points += [(4, 4, 0.05, 0, 0, 4, 1, 0, 0)]                      # up to 4 candidate K tiles per P tile
+    points += [(4, 4, 0.05, 0, 0, 1, 0, 0, 0)]                      # temporal tiles never grow runs
+    points += [(4, 4, 0.05, 0, 0, 1, 1, 1, 0), (8, 8, 0.05, 0, 0, 1, 1, 1, 0)]   # Eq. 3's three-coefficient planes
+    points += [(4, 4, 0.05, 0, 0, 1, 1, 0, 1), (8, 8, 0.05, 0, 0, 1, 1, 0, 1)]   # FP64 plane solver
+    for th, tw, thr, nd, rx, tc, tr, p3, sv in points:
         if True:
             ctx = lcc.Context(seq.sensor, lcc.default_params(tile_h=th, tile_w=tw, fit_thr_m=thr, no_delta=nd,
                                                             raw_exact=rx, temporal_candidates=tc,
+                                                            temporal_runs=tr, plane3=p3, solver=sv,
                                                             max_batch=max(16, n_frames)), stream=stream)
             cap = ctx.max_encoded_bytes
             outs = [torch.zeros(cap, dtype=torch.uint8, device="cuda") for _ in range(n_frames)]
@@ -586,7 +591,9 @@ def run_sweep(args, stream, seq, d_pts, flush):
                 if bool(m.any()):
                     err = max(err, float((dec[m] - ref[m]).abs().max().item()))
             rows.append({"tile": f"{th}x{tw}", "thr_m": thr, "no_delta": nd, "raw_exact": rx,
-                         "temporal_candidates": tc, "mpts_per_s": round(pts / (ms * 1e-3) / 1e6, 1),
+                         "temporal_candidates": tc, "temporal_runs": tr, "plane3": p3,
+                         "solver": "fp64" if sv else "float-float",
+                         "bytes": int(sizes.sum()), "mpts_per_s": round(pts / (ms * 1e-3) / 1e6, 1),
                          "ms_per_step": round(ms, 4), "compression_ratio": round(12.0 * pts / float(sizes.sum()), 3),
                          "max_decode_error_m": err, "tile_modes": modes})
             del kf, kfd, ctx

@@ -297,12 +297,111 @@ struct BuildSmem {
     uint16_t node_parent[kMaxAlph];
     uint16_t node_depth[kMaxAlph];
     uint32_t lw[kMaxAlph];          // leaf weights in queue order
+    uint32_t tw[kMaxAlph];          // a batch's items in pick order (their weights)
     uint8_t len[kMaxAlph];
     uint32_t red[32];
+    uint32_t last_leaf;
     uint32_t per_len[kMaxLen + 1];
     uint32_t first[kMaxLen + 1];
     uint32_t index[kMaxLen + 2];
 };
+
+// Huffman's two-queue construction over the n >= 2 leaf weights S.lw (sorted by (count,
+// symbol)): node k's weight goes to S.hist[k], every leaf's and node's parent to S.leaf_parent /
+// S.node_parent.  Picks follow the two-queue rule (the lighter front; a leaf first on equal
+// weights), and they are taken a batch at a time: with m the weight of the next node to be made
+// (its two picks), every remaining node made so far (node weights never decrease, so they are
+// all <= m) and every remaining leaf of weight <= m is picked before any node made from here on
+// (a later node weighs >= m; a leaf wins ties and older nodes are ahead in their queue).  Those
+// items, in pick order (a merge of the two sorted queue segments, ranks by binary search),
+// pair up into the next nodes; an odd last item stays at its queue's front.  The smallest pair
+// grows at least like a Fibonacci sequence from batch to batch, so the batches number
+// O(log of the total count); after kMaxBatches one thread makes the remaining joins one by one.
+// All threads of the block call this.
+constexpr int kMaxBatches = 48;
+
+__device__ __forceinline__ uint32_t upper_bound_u32(const uint32_t *a, uint32_t lo, uint32_t hi, uint32_t v) {
+    while (lo < hi) {
+        const uint32_t mid = (lo + hi) >> 1;
+        if (a[mid] <= v) lo = mid + 1;
+        else hi = mid;
+    }
+    return lo;
+}
+
+__device__ __forceinline__ uint32_t lower_bound_u32(const uint32_t *a, uint32_t lo, uint32_t hi, uint32_t v) {
+    while (lo < hi) {
+        const uint32_t mid = (lo + hi) >> 1;
+        if (a[mid] < v) lo = mid + 1;
+        else hi = mid;
+    }
+    return lo;
+}
+
+template <class Smem>
+__device__ void huffman_joins(Smem &S, uint32_t n) {
+    const uint32_t tid = threadIdx.x;
+    constexpr uint32_t kNone = 0xFFFFFFFFu;
+    uint32_t li = 0, ni = 0, nk = 0;   // leaf front, node front, nodes made (the same in every thread)
+    for (int batch = 0; batch < kMaxBatches && nk + 1 < n; batch++) {
+        const uint32_t l0 = li < n ? S.lw[li] : kNone, l1 = li + 1 < n ? S.lw[li + 1] : kNone;
+        const uint32_t n0 = ni < nk ? S.hist[ni] : kNone, n1 = ni + 1 < nk ? S.hist[ni + 1] : kNone;
+        const uint32_t m = l0 <= n0 ? l0 + (l1 <= n0 ? l1 : n0) : n0 + (l0 <= n1 ? l0 : n1);
+        const uint32_t a = upper_bound_u32(S.lw, li, n, m) - li, b = nk - ni;
+        const uint32_t T = a + b, P = T >> 1;
+        for (uint32_t e = tid; e < T; e += blockDim.x) {
+            uint32_t w, r;
+            if (e < a) {   // a leaf goes after the nodes strictly lighter than it
+                w = S.lw[li + e];
+                r = e + (lower_bound_u32(S.hist, ni, nk, w) - ni);
+            } else {       // a node goes after the leaves no heavier than it
+                w = S.hist[ni + e - a];
+                r = (e - a) + (upper_bound_u32(S.lw, li, li + a, w) - li);
+            }
+            S.tw[r] = w;
+            if (r < 2 * P) {
+                if (e < a) S.leaf_parent[li + e] = (uint16_t)(nk + (r >> 1));
+                else S.node_parent[ni + e - a] = (uint16_t)(nk + (r >> 1));
+            } else {       // the odd last item
+                S.last_leaf = e < a ? 1u : 0u;
+            }
+        }
+        __syncthreads();
+        const bool leaf_left = (T & 1) && S.last_leaf;   // read before the next batch can write it
+        for (uint32_t q = tid; q < P; q += blockDim.x) S.hist[nk + q] = S.tw[2 * q] + S.tw[2 * q + 1];
+        __syncthreads();
+        li += (T & 1) && leaf_left ? a - 1 : a;
+        ni += (T & 1) && !leaf_left ? b - 1 : b;
+        nk += P;
+    }
+    if (tid == 0 && nk + 1 < n) {
+        // the two-queue rule one join at a time; each queue's front weight is kept in a register
+        // (kNone: empty) and the second one loaded a join ahead
+        uint32_t wl = li < n ? S.lw[li] : kNone, wl2 = li + 1 < n ? S.lw[li + 1] : kNone;
+        uint32_t wn = ni < nk ? S.hist[ni] : kNone, wn2 = ni + 1 < nk ? S.hist[ni + 1] : kNone;
+        for (uint32_t k = nk; k + 1 < n; k++) {
+            uint32_t wsum = 0;
+#pragma unroll
+            for (int pick = 0; pick < 2; pick++) {
+                if (wl <= wn) {
+                    wsum += wl;
+                    S.leaf_parent[li++] = (uint16_t)k;
+                    wl = wl2;
+                    wl2 = li + 1 < n ? S.lw[li + 1] : kNone;
+                } else {
+                    wsum += wn;
+                    S.node_parent[ni++] = (uint16_t)k;
+                    wn = wn2;
+                    wn2 = ni + 1 < k ? S.hist[ni + 1] : kNone;
+                }
+            }
+            S.hist[k] = wsum;
+            if (ni == k) wn = wsum;
+            else if (ni + 1 == k) wn2 = wsum;
+        }
+    }
+    __syncthreads();
+}
 
 // grid (5 symbol sections, nframes), kBuildThreads threads
 __global__ void __launch_bounds__(kBuildThreads) k_ent_build(EntBatch b, Scratch sc, unsigned *err) {
@@ -342,20 +441,43 @@ __global__ void __launch_bounds__(kBuildThreads) k_ent_build(EntBatch b, Scratch
         return;
     }
     const uint32_t *sec = reinterpret_cast<const uint32_t *>(b.in[f] + kHeaderBytes) + L.off[s];
-    // histogram
+    // histogram: lanes holding the same symbol add once; alphabets of up to 256 symbols count into
+    // one copy per warp (the sorting keys' space, not in use yet), summed afterwards, so that the
+    // warps do not queue on a few shared counters; four symbols a thread are loaded at once
+    constexpr uint32_t kPrivAlph = 256, kNone = 0xFFFFFFFFu;
+    static_assert(sizeof(S.keys) >= 32 * kPrivAlph * sizeof(uint32_t), "per-warp histograms");
+    const bool priv = w <= 8;
+    uint32_t *wh = reinterpret_cast<uint32_t *>(S.keys);
     for (int i = tid; i < kMaxAlph; i += blockDim.x) {
         S.hist[i] = 0;
         S.len[i] = 0;
     }
+    if (priv)
+        for (int i = tid; i < 32 * (int)kPrivAlph; i += blockDim.x) wh[i] = 0;
     __syncthreads();
-    // lanes holding the same symbol add once (small alphabets would serialise on a few counters)
-    for (uint32_t base = 0; base < cnt; base += blockDim.x) {
-        const uint32_t i = base + tid;
-        const uint32_t v = i < cnt ? get_sym(sec, w, i) : 0xFFFFFFFFu;
-        const unsigned same = __match_any_sync(0xFFFFFFFFu, v);
-        if (i < cnt && (tid & 31) == __ffs(same) - 1) atomicAdd(&S.hist[v], (uint32_t)__popc(same));
+    uint32_t *hh = priv ? wh + (tid >> 5) * kPrivAlph : S.hist;
+    for (uint32_t base = 0; base < cnt; base += 4 * blockDim.x) {
+        uint32_t v[4];
+#pragma unroll
+        for (int u = 0; u < 4; u++) {
+            const uint32_t i = base + u * blockDim.x + tid;
+            v[u] = i < cnt ? get_sym(sec, w, i) : kNone;
+        }
+#pragma unroll
+        for (int u = 0; u < 4; u++) {
+            const unsigned same = __match_any_sync(0xFFFFFFFFu, v[u]);
+            if (v[u] != kNone && (tid & 31) == __ffs(same) - 1) atomicAdd(&hh[v[u]], (uint32_t)__popc(same));
+        }
     }
     __syncthreads();
+    if (priv) {
+        for (uint32_t v = tid; v < kPrivAlph; v += blockDim.x) {
+            uint32_t t = 0;
+            for (int k = 0; k < 32; k++) t += wh[k * kPrivAlph + v];
+            S.hist[v] = t;
+        }
+        __syncthreads();
+    }
     uint32_t top = 0;
     for (uint32_t v = tid; v < (1u << w); v += blockDim.x)
         if (S.hist[v]) top = v + 1;
@@ -381,35 +503,7 @@ __global__ void __launch_bounds__(kBuildThreads) k_ent_build(EntBatch b, Scratch
             bitonic_sort(S.keys, P);
             for (uint32_t i = tid; i < n; i += blockDim.x) S.lw[i] = (uint32_t)(S.keys[i] >> 12);
             __syncthreads();
-            if (tid == 0) {
-                // two queues: leaves in (count, symbol) order, internal nodes in order of creation;
-                // each queue's front weight is kept in a register (~0u: empty), a leaf goes first
-                // on equal weights
-                // (wl, wl2: the first two leaves left; wn, wn2: the first two nodes made and not
-                // yet joined; the second of each is loaded one join ahead)
-                uint32_t li = 0, ni = 0, wl = S.lw[0], wl2 = n > 1 ? S.lw[1] : ~0u, wn = ~0u, wn2 = ~0u;
-                for (uint32_t k = 0; k + 1 < n; k++) {
-                    uint32_t wsum = 0;
-#pragma unroll
-                    for (int pick = 0; pick < 2; pick++) {
-                        if (wl <= wn) {
-                            wsum += wl;
-                            S.leaf_parent[li++] = (uint16_t)k;
-                            wl = wl2;
-                            wl2 = li + 1 < n ? S.lw[li + 1] : ~0u;
-                        } else {
-                            wsum += wn;
-                            S.node_parent[ni++] = (uint16_t)k;
-                            wn = wn2;
-                            wn2 = ni + 1 < k ? S.hist[ni + 1] : ~0u;
-                        }
-                    }
-                    S.hist[k] = wsum;
-                    if (ni == k) wn = wsum;
-                    else if (ni + 1 == k) wn2 = wsum;
-                }
-            }
-            __syncthreads();
+            huffman_joins(S, n);
             // node depths by pointer jumping (children are made before parents, the root last):
             // node_parent becomes an ancestor pointer and node_depth the edges up to it
             for (uint32_t k = tid; k + 1 < n; k += blockDim.x) {
@@ -419,18 +513,25 @@ __global__ void __launch_bounds__(kBuildThreads) k_ent_build(EntBatch b, Scratch
             }
             __syncthreads();
             for (int r = 0; r < kMaxWidth; r++) {   // 2^12 >= the 4095 nodes a tree can have
-                uint16_t na[kMaxAlph / kBuildThreads], nd[kMaxAlph / kBuildThreads];
-                int q = 0;
-                for (uint32_t k = tid; k + 1 < n; k += blockDim.x, q++) {
-                    const uint16_t a = S.node_parent[k];
-                    na[q] = S.node_parent[a];
-                    nd[q] = S.node_depth[k] + S.node_depth[a];
+                constexpr int kPer = kMaxAlph / kBuildThreads;   // nodes a thread holds (registers)
+                uint16_t na[kPer], nd[kPer];
+#pragma unroll
+                for (int q = 0; q < kPer; q++) {
+                    const uint32_t k = tid + q * kBuildThreads;
+                    if (k + 1 < n) {
+                        const uint16_t a = S.node_parent[k];
+                        na[q] = S.node_parent[a];
+                        nd[q] = S.node_depth[k] + S.node_depth[a];
+                    }
                 }
                 __syncthreads();
-                q = 0;
-                for (uint32_t k = tid; k + 1 < n; k += blockDim.x, q++) {
-                    S.node_parent[k] = na[q];
-                    S.node_depth[k] = nd[q];
+#pragma unroll
+                for (int q = 0; q < kPer; q++) {
+                    const uint32_t k = tid + q * kBuildThreads;
+                    if (k + 1 < n) {
+                        S.node_parent[k] = na[q];
+                        S.node_depth[k] = nd[q];
+                    }
                 }
                 __syncthreads();
             }
@@ -631,6 +732,7 @@ __global__ void __launch_bounds__(kWriteThreads) k_ent_write(EntBatch b, Scratch
 struct DecSmem {
     uint8_t len[kMaxAlph];
     uint32_t red[32];
+    uint32_t last_leaf;
     uint32_t per_len[kMaxLen + 1];
     uint32_t first[kMaxLen + 1];
     uint32_t index[kMaxLen + 2];

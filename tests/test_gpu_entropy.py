@@ -63,6 +63,11 @@ def oracle_streams(cfg2_seq):
     out.append(nd.tobytes())
     re_, _, _, _ = O.encode_keyframe(s, O.params(raw_exact=1), seq.frames[seq.key_index])
     out.append(re_.tobytes())   # 32-bit raw codes: a copied section
+    p3 = O.params(plane3=1)
+    k3, kft3, _, _ = O.encode_keyframe(s, p3, seq.frames[seq.key_index])
+    out.append(k3.tobytes())    # three-coefficient run records
+    pb3, _, _, _ = O.encode_pframe(s, p3, kft3, seq.poses[3], seq.frames[3])
+    out.append(pb3.tobytes())
     return out
 
 

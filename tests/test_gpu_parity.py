@@ -500,14 +500,15 @@ def test_profiler_counts_every_kernel_and_orders_the_timeline(cfg2_seq):
             assert chunk[q + 1][1] >= chunk[q][2] - 1e-3
 
 
-def test_sequence_decode_matches_per_frame_decode(cfg2_seq):
+@pytest.mark.parametrize("plane3", [0, 1])
+def test_sequence_decode_matches_per_frame_decode(cfg2_seq, plane3):
     """lcc_decode_sequence (key stream first, all P streams in one launch) gives the ranges, points
-    and occupancy of the per-frame decoder bit for bit; a corrupt P stream in the batch is
-    reported."""
+    and occupancy of the per-frame decoder bit for bit, with four-word and with three-coefficient
+    run records; a corrupt P stream in the batch is reported."""
     from paper_2008_06972_gb300 import lcc
     seq = cfg2_seq
     n = len(seq.frames)
-    c = H.ctx(seq.sensor, max_batch=16)
+    c = H.ctx(seq.sensor, max_batch=16, plane3=plane3)
     ds = [H.to_dev(p) for p in seq.frames]
     outs = [H.out_buf(c) for _ in range(n)]
     nb = torch.zeros(n, dtype=torch.int64, device="cuda")
