@@ -17,8 +17,10 @@
 
 #ifdef __CUDACC__
 #define FF_FN __host__ __device__ __forceinline__
+#define FF_OUTLINE __host__ __device__ __noinline__
 #else
 #define FF_FN inline
+#define FF_OUTLINE inline
 #endif
 
 namespace lcc {
@@ -102,6 +104,32 @@ FF_FN float fabs_hi(f2 a) { return fabsf(a.hi); }
 // Dot product of two float-float 3-vectors.
 FF_FN f2 dot3(f2 ax, f2 ay, f2 az, f2 bx, f2 by, f2 bz) { return add(add(mul(ax, bx), mul(ay, by)), mul(az, bz)); }
 
+// Out-of-line pieces of the solve: one copy each, called several times, so the solve's code
+// stays small (the fit kernels run few warps per SM and stall on instruction fetch otherwise).
+FF_OUTLINE f2 dot3o(f2 ax, f2 ay, f2 az, f2 bx, f2 by, f2 bz) { return dot3(ax, ay, az, bx, by, bz); }
+
+// r x s of two 3-vectors (each component a*b - c*d by msub)
+FF_OUTLINE void cross3(f2 rx, f2 ry, f2 rz, f2 sx, f2 sy, f2 sz, f2 &x, f2 &y, f2 &z) {
+    x = msub(ry, sz, rz, sy);
+    y = msub(rz, sx, rx, sz);
+    z = msub(rx, sy, ry, sx);
+}
+
+// C v for the symmetric C = (xx, xy, xz, yy, yz, zz)
+FF_OUTLINE void symmv(f2 cxx, f2 cxy, f2 cxz, f2 cyy, f2 cyz, f2 czz, f2 vx, f2 vy, f2 vz, f2 &ox, f2 &oy, f2 &oz) {
+    ox = dot3(cxx, cxy, cxz, vx, vy, vz);
+    oy = dot3(cxy, cyy, cyz, vx, vy, vz);
+    oz = dot3(cxz, cyz, czz, vx, vy, vz);
+}
+
+// v / |v| (one Newton-refined reciprocal square root)
+FF_OUTLINE void normalize3(f2 &x, f2 &y, f2 &z) {
+    const f2 in = rsqrt(dot3(x, y, z, x, y, z));
+    x = mul(x, in);
+    y = mul(y, in);
+    z = mul(z, in);
+}
+
 // Plane of the moments of a point set: s1 = sum of q, s2 = sum of q q^T
 // (xx, xy, xz, yy, yz, zz) with q = p - a for the anchor a, over n points.
 // Writes the fp32 plane (unit normal, offset; n.p = d, canonical sign) and
@@ -144,6 +172,7 @@ FF_FN bool solve_plane_ff(const f2 s1[3], const f2 s2[6], int n, float ax, float
     // Newton on f(l) = det(C - l I) from above lambda_max: f is concave and
     // decreasing there, so the iterates fall onto the root.
     f2 lam = add(mk(seed), mk(3e-5f * spread));
+#pragma unroll 1
     for (int it = 0; it < 3; it++) {
         const f2 a = sub(cxx, lam), b = sub(cyy, lam), c = sub(czz, lam);
         const f2 myz = msub(b, c, cyz, cyz), mxz = msub(a, c, cxz, cxz), mxy = msub(a, b, cxy, cxy);
@@ -155,9 +184,10 @@ FF_FN bool solve_plane_ff(const f2 s1[3], const f2 s2[6], int n, float ax, float
     f2 vx, vy, vz;
     {
         const f2 a = sub(cxx, lam), b = sub(cyy, lam), c = sub(czz, lam);
-        const f2 x0 = msub(cxy, cyz, b, cxz), y0 = msub(cxz, cxy, cyz, a), z0 = msub(b, a, cxy, cxy);   // r0 x r1
-        const f2 x1 = msub(cxy, c, cxz, cyz), y1 = msub(cxz, cxz, a, c), z1 = msub(a, cyz, cxy, cxz);   // r0 x r2
-        const f2 x2 = msub(b, c, cyz, cyz), y2 = msub(cyz, cxz, cxy, c), z2 = msub(cxy, cyz, b, cxz);   // r1 x r2
+        f2 x0, y0, z0, x1, y1, z1, x2, y2, z2;
+        cross3(a, cxy, cxz, cxy, b, cyz, x0, y0, z0);     // r0 x r1
+        cross3(a, cxy, cxz, cxz, cyz, c, x1, y1, z1);     // r0 x r2
+        cross3(cxy, b, cyz, cxz, cyz, c, x2, y2, z2);     // r1 x r2
         const float n0 = x0.hi * x0.hi + y0.hi * y0.hi + z0.hi * z0.hi;
         const float n1 = x1.hi * x1.hi + y1.hi * y1.hi + z1.hi * z1.hi;
         const float n2 = x2.hi * x2.hi + y2.hi * y2.hi + z2.hi * z2.hi;
@@ -184,8 +214,7 @@ FF_FN bool solve_plane_ff(const f2 s1[3], const f2 s2[6], int n, float ax, float
         if (!(m > 1e-30f)) return true;
         const float sc = 1.0f / m;   // any scale works before normalising
         vx = mulf(vx, sc); vy = mulf(vy, sc); vz = mulf(vz, sc);
-        const f2 in = rsqrt(dot3(vx, vy, vz, vx, vy, vz));
-        vx = mul(vx, in); vy = mul(vy, in); vz = mul(vz, in);
+        normalize3(vx, vy, vz);
     }
     // orthonormal basis (u, w) of the plane orthogonal to v
     f2 ux, uy, uz;
@@ -194,18 +223,17 @@ FF_FN bool solve_plane_ff(const f2 s1[3], const f2 s2[6], int n, float ax, float
         if (a2 <= b2 && a2 <= c2) { ux = mk(0.0f); uy = vz; uz = neg(vy); }
         else if (b2 <= c2) { ux = neg(vz); uy = mk(0.0f); uz = vx; }
         else { ux = vy; uy = neg(vx); uz = mk(0.0f); }
-        const f2 in = rsqrt(dot3(ux, uy, uz, ux, uy, uz));   // in [1/2, 1]
-        ux = mul(ux, in); uy = mul(uy, in); uz = mul(uz, in);
+        normalize3(ux, uy, uz);   // the scale is in [1/2, 1]
     }
-    const f2 wx = msub(vy, uz, vz, uy), wy = msub(vz, ux, vx, uz), wz = msub(vx, uy, vy, ux);
+    f2 wx, wy, wz;
+    cross3(vx, vy, vz, ux, uy, uz, wx, wy, wz);
     // B = [u w]^T C [u w]
-    const f2 cux = dot3(cxx, cxy, cxz, ux, uy, uz), cuy = dot3(cxy, cyy, cyz, ux, uy, uz),
-             cuz = dot3(cxz, cyz, czz, ux, uy, uz);
-    const f2 cwx = dot3(cxx, cxy, cxz, wx, wy, wz), cwy = dot3(cxy, cyy, cyz, wx, wy, wz),
-             cwz = dot3(cxz, cyz, czz, wx, wy, wz);
-    const f2 b00 = dot3(ux, uy, uz, cux, cuy, cuz);
-    const f2 b01 = dot3(ux, uy, uz, cwx, cwy, cwz);
-    const f2 b11 = dot3(wx, wy, wz, cwx, cwy, cwz);
+    f2 cux, cuy, cuz, cwx, cwy, cwz;
+    symmv(cxx, cxy, cxz, cyy, cyz, czz, ux, uy, uz, cux, cuy, cuz);
+    symmv(cxx, cxy, cxz, cyy, cyz, czz, wx, wy, wz, cwx, cwy, cwz);
+    const f2 b00 = dot3o(ux, uy, uz, cux, cuy, cuz);
+    const f2 b01 = dot3o(ux, uy, uz, cwx, cwy, cwz);
+    const f2 b11 = dot3o(wx, wy, wz, cwx, cwy, cwz);
     // one Jacobi rotation diagonalises the 2x2 block
     f2 e0 = b00, e1 = b11, c0 = mk(1.0f), s0 = mk(0.0f);
     if (fabs_hi(b01) > 1e-30f * tr.hi) {
@@ -237,10 +265,7 @@ FF_FN bool solve_plane_ff(const f2 s1[3], const f2 s2[6], int n, float ax, float
     }
     const bool degenerate = !(lmid.hi > 1e-12f * lam.hi);
     *ratio = lam.hi > 0.0f ? lmid.hi / lam.hi : 0.0f;
-    {
-        const f2 in = rsqrt(dot3(nx, ny, nz, nx, ny, nz));   // ~1 already
-        nx = mul(nx, in); ny = mul(ny, in); nz = mul(nz, in);
-    }
+    normalize3(nx, ny, nz);   // ~1 already
     const f2 d = dot3(nx, ny, nz, add(mk(ax), mx), add(mk(ay), my), add(mk(az), mz));
     bool flip;
     if (fabsf(d.hi) < 1e-9f) {

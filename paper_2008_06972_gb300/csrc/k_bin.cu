@@ -18,6 +18,7 @@ constexpr int kBinPerThread = 4;
 // blockIdx.x + gridDim.x, ... so that a capped grid covers them all.
 __global__ void __launch_bounds__(kBinThreads) k_bin(Geometry g, Scratch s, Batch b, long long chunks) {
     __shared__ int s_frame;
+    __shared__ unsigned s_cnt[kBinThreads / 32][3];
     for (long long cb = blockIdx.x; cb < chunks; cb += gridDim.x) {
         __syncthreads();   // s_frame of the previous chunk has been read by every thread
         if (threadIdx.x == 0) {
@@ -56,13 +57,22 @@ __global__ void __launch_bounds__(kBinThreads) k_bin(Geometry g, Scratch s, Batc
             fov += __shfl_xor_sync(0xffffffffu, fov, off);
             binned += __shfl_xor_sync(0xffffffffu, binned, off);
         }
-        DevStats *st = s.stats + b.slot[f];
-        if ((threadIdx.x & 31) == 0 && (invalid | fov | binned)) {
-            if (invalid) atomicAdd(&st->invalid, (unsigned long long)invalid);
-            if (fov) atomicAdd(&st->fov, (unsigned long long)fov);
-            if (binned) atomicAdd(&st->binned, (unsigned long long)binned);
+        // one set of counter updates per chunk: the frame's counters are shared by all its chunks
+        if ((threadIdx.x & 31) == 0) {
+            s_cnt[threadIdx.x >> 5][0] = invalid;
+            s_cnt[threadIdx.x >> 5][1] = fov;
+            s_cnt[threadIdx.x >> 5][2] = binned;
         }
-        if (threadIdx.x == 0 && base == 0) atomicAdd(&st->points_in, (unsigned long long)n);
+        __syncthreads();
+        if (threadIdx.x < 3) {
+            unsigned long long v = 0;
+#pragma unroll
+            for (int w = 0; w < kBinThreads / 32; w++) v += s_cnt[w][threadIdx.x];
+            DevStats *st = s.stats + b.slot[f];
+            unsigned long long *dst = threadIdx.x == 0 ? &st->invalid : (threadIdx.x == 1 ? &st->fov : &st->binned);
+            if (v) atomicAdd(dst, v);
+            if (threadIdx.x == 0 && base == 0) atomicAdd(&st->points_in, (unsigned long long)n);
+        }
     }
 }
 

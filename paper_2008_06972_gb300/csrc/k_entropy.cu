@@ -217,23 +217,74 @@ __device__ uint32_t block_excl(uint32_t v, uint32_t *red, uint32_t *total) {
     return before + x - v;
 }
 
-// Ascending bitonic sort of keys[0, P), P a power of two (the textbook network).
+// Ascending bitonic sort of keys[0, P), P a power of two up to 4 blockDim (the textbook
+// network, every compare-exchange of it).  Each thread holds E = max(1, P / blockDim) consecutive
+// keys in registers, so a warp holds 32 E consecutive keys: the steps whose partner distance j is
+// below 32 E exchange in registers and by shuffles; only the longer ones go through shared memory
+// with a barrier.  keys must be in shared memory and complete (barrier before the call); they are
+// sorted in place and complete after it.
 __device__ void bitonic_sort(unsigned long long *keys, uint32_t P) {
-    for (uint32_t k = 2; k <= P; k <<= 1)
-        for (uint32_t j = k >> 1; j > 0; j >>= 1) {
-            for (uint32_t i = threadIdx.x; i < P; i += blockDim.x) {
-                const uint32_t l = i ^ j;
-                if (l > i) {
-                    const unsigned long long a = keys[i], b = keys[l];
-                    const bool up = (i & k) == 0;
-                    if ((a > b) == up) {
-                        keys[i] = b;
-                        keys[l] = a;
+    const uint32_t T = blockDim.x, t = threadIdx.x;
+    const uint32_t E = P > T ? P / T : 1u;      // 1, 2 or 4
+    const uint32_t base = t * E, WR = 32u * E;   // first key of the thread, keys per warp
+    unsigned long long r[4];
+#pragma unroll
+    for (int e = 0; e < 4; e++) r[e] = (uint32_t)e < E && base + e < P ? keys[base + e] : ~0ull;
+    // one compare-exchange in registers: lo keeps the smaller key when up
+    auto cx = [](unsigned long long &lo, unsigned long long &hi, bool up) {
+        if ((lo > hi) == up) {
+            const unsigned long long x = lo;
+            lo = hi;
+            hi = x;
+        }
+    };
+    for (uint32_t k = 2; k <= P; k <<= 1) {
+        uint32_t j = k >> 1;
+        if (j >= WR) {
+#pragma unroll
+            for (int e = 0; e < 4; e++)
+                if ((uint32_t)e < E && base + e < P) keys[base + e] = r[e];
+            __syncthreads();
+            for (; j >= WR; j >>= 1) {
+                for (uint32_t i = t; i < P; i += T) {
+                    const uint32_t l = i ^ j;
+                    if (l > i) {
+                        const unsigned long long a = keys[i], b = keys[l];
+                        const bool up = (i & k) == 0;
+                        if ((a > b) == up) {
+                            keys[i] = b;
+                            keys[l] = a;
+                        }
                     }
                 }
+                __syncthreads();
             }
-            __syncthreads();
+#pragma unroll
+            for (int e = 0; e < 4; e++) r[e] = (uint32_t)e < E && base + e < P ? keys[base + e] : ~0ull;
         }
+        for (; j > 0; j >>= 1) {
+            if (j >= E) {   // partner: the same slot of lane ^ (j / E)
+#pragma unroll
+                for (int e = 0; e < 4; e++) {
+                    if ((uint32_t)e >= E) break;
+                    const uint32_t i = base + e;
+                    const unsigned long long o = __shfl_xor_sync(0xFFFFFFFFu, r[e], j / E);
+                    const bool up = (i & k) == 0, lower = (i & j) == 0;
+                    r[e] = up == lower ? (r[e] < o ? r[e] : o) : (r[e] > o ? r[e] : o);
+                }
+            } else if (j == 2) {   // E == 4: slots (0, 2) and (1, 3)
+                cx(r[0], r[2], (base & k) == 0);
+                cx(r[1], r[3], ((base + 1) & k) == 0);
+            } else {               // j == 1, E >= 2: slots (0, 1) and (2, 3)
+                cx(r[0], r[1], (base & k) == 0);
+                if (E == 4) cx(r[2], r[3], ((base + 2) & k) == 0);
+            }
+        }
+    }
+#pragma unroll
+    for (int e = 0; e < 4; e++)
+        if ((uint32_t)e < E && base + e < P) keys[base + e] = r[e];
+    __syncthreads();
 }
 
 // Canonical tables of a length table (any thread count): per length the number of codes, the
@@ -250,44 +301,48 @@ __device__ void canonical_tables(const uint32_t *per_len, uint32_t *first, uint3
 }
 
 // Every used symbol's position in (length, symbol) order, handed to place(symbol, length,
-// position): a count per length and thread (cnt, kMaxLen rows of blockDim entries), an exclusive
-// prefix of each row over the threads (a warp per row), then each thread places its run of
-// consecutive symbols.  index[l] is the position of the first symbol of length l.
+// position).  A thread takes a run of consecutive symbols; for each length that has symbols, a
+// block-wide exclusive scan of the threads' counts of that length gives each thread its first
+// position (index[l] is the position of the first symbol of length l).  red: 32 words.  Called
+// by every thread of the block; it starts with a barrier, so len and index may have been written
+// by any thread just before the call.
 template <class F>
-__device__ void place_by_length(const uint8_t *len, uint32_t alph, const uint32_t *index, uint16_t *cnt,
+__device__ void place_by_length(const uint8_t *len, uint32_t alph, const uint32_t *index, uint32_t *red,
                                 F &&place) {
-    const uint32_t T = blockDim.x, t = threadIdx.x, lane = t & 31, warp = t >> 5, nw = T >> 5;
+    __syncthreads();
+    const uint32_t T = blockDim.x, t = threadIdx.x;
     const uint32_t per = (alph + T - 1) / T, s0 = min(alph, t * per), s1 = min(alph, s0 + per);
-    for (int l = 0; l < kMaxLen; l++) cnt[l * T + t] = 0;
-    for (uint32_t v = s0; v < s1; v++)
-        if (len[v]) cnt[(len[v] - 1) * T + t]++;
-    __syncthreads();
-    const uint32_t per_lane = T / 32;
-    for (uint32_t row = warp; row < (uint32_t)kMaxLen; row += nw) {
-        uint16_t *r = cnt + row * T + lane * per_lane;
-        uint32_t sum = 0;
-        for (uint32_t k = 0; k < per_lane; k++) sum += r[k];
-        uint32_t x = sum;
-        for (int d = 1; d < 32; d <<= 1) {
-            const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, x, d);
-            if ((int)lane >= d) x += y;
-        }
-        uint32_t base = x - sum;
-        for (uint32_t k = 0; k < per_lane; k++) {
-            const uint32_t c = r[k];
-            r[k] = (uint16_t)base;
-            base += c;
-        }
+    for (uint32_t l = 1; l <= (uint32_t)kMaxLen; l++) {
+        if (index[l + 1] == index[l]) continue;   // no symbol of this length (the same in every thread)
+        uint32_t own = 0;
+        for (uint32_t v = s0; v < s1; v++) own += len[v] == l ? 1u : 0u;
+        uint32_t total;
+        uint32_t pos = index[l] + block_excl(own, red, &total);
+        for (uint32_t v = s0; v < s1; v++)
+            if (len[v] == l) place(v, l, pos++);
     }
     __syncthreads();
-    for (uint32_t v = s0; v < s1; v++) {
-        const uint32_t l = len[v];
-        if (!l) continue;
-        uint16_t &c = cnt[(l - 1) * T + t];
-        place(v, l, index[l] + c);
-        c++;
+}
+
+// One warp copies the words holding symbols [b0, b0 + m) of a section of width w (b0 a multiple
+// of 32, so its first symbol starts a word; m <= 1024) into buf, all of its loads in flight at
+// once; the words are in buf for every lane after the call.
+__device__ __forceinline__ void stage_symbols(const uint32_t *sec, uint32_t w, uint32_t b0, uint32_t m, uint32_t *buf) {
+    const uint32_t lane = threadIdx.x & 31;
+    const uint32_t nw = (uint32_t)(((unsigned long long)m * w + 31) / 32);
+    const uint32_t *src = sec + (size_t)b0 / 32 * w;
+    uint32_t v[kMaxWidth];
+#pragma unroll
+    for (int k = 0; k < kMaxWidth; k++) {
+        const uint32_t i = lane + 32u * k;
+        v[k] = i < nw ? src[i] : 0u;
     }
-    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < kMaxWidth; k++) {
+        const uint32_t i = lane + 32u * k;
+        if (i < nw) buf[i] = v[k];
+    }
+    __syncwarp();
 }
 
 struct BuildSmem {
@@ -298,6 +353,7 @@ struct BuildSmem {
     uint16_t node_depth[kMaxAlph];
     uint32_t lw[kMaxAlph];          // leaf weights in queue order
     uint32_t tw[kMaxAlph];          // a batch's items in pick order (their weights)
+    uint32_t stage[kBuildThreads / 32][32 * kMaxWidth];   // per warp: the words of 1024 symbols
     uint8_t len[kMaxAlph];
     uint32_t red[32];
     uint32_t last_leaf;
@@ -441,13 +497,18 @@ __global__ void __launch_bounds__(kBuildThreads) k_ent_build(EntBatch b, Scratch
         return;
     }
     const uint32_t *sec = reinterpret_cast<const uint32_t *>(b.in[f] + kHeaderBytes) + L.off[s];
-    // histogram: lanes holding the same symbol add once; alphabets of up to 256 symbols count into
-    // one copy per warp (the sorting keys' space, not in use yet), summed afterwards, so that the
-    // warps do not queue on a few shared counters; four symbols a thread are loaded at once
+    // histogram, a warp per block of 1024 symbols staged in shared memory.  Widths up to 4: each
+    // lane counts its 32 consecutive symbols in registers (16-bit fields; a lane sees at most
+    // 32 symbols per block, so the fields cannot overflow below 2^21 blocks); widths 5..8: lanes
+    // holding the same symbol add once (__match_any) into the warp's own copy of the histogram
+    // (the sorting keys' space, not in use yet); wider: one shared atomic per symbol (large
+    // alphabets rarely collide)
     constexpr uint32_t kPrivAlph = 256, kNone = 0xFFFFFFFFu;
     static_assert(sizeof(S.keys) >= 32 * kPrivAlph * sizeof(uint32_t), "per-warp histograms");
-    const bool priv = w <= 8;
+    const uint32_t lane = tid & 31, warp = tid >> 5, nwarp = blockDim.x >> 5;
+    const bool regc = w <= 4, priv = w > 4 && w <= 8;
     uint32_t *wh = reinterpret_cast<uint32_t *>(S.keys);
+    uint32_t *wbuf = S.stage[warp];
     for (int i = tid; i < kMaxAlph; i += blockDim.x) {
         S.hist[i] = 0;
         S.len[i] = 0;
@@ -455,18 +516,47 @@ __global__ void __launch_bounds__(kBuildThreads) k_ent_build(EntBatch b, Scratch
     if (priv)
         for (int i = tid; i < 32 * (int)kPrivAlph; i += blockDim.x) wh[i] = 0;
     __syncthreads();
-    uint32_t *hh = priv ? wh + (tid >> 5) * kPrivAlph : S.hist;
-    for (uint32_t base = 0; base < cnt; base += 4 * blockDim.x) {
-        uint32_t v[4];
+    uint32_t *hh = priv ? wh + warp * kPrivAlph : S.hist;
+    uint32_t c2[8] = {0u, 0u, 0u, 0u, 0u, 0u, 0u, 0u};   // symbol 2k in the low half of c2[k], 2k + 1 in the high
+    const uint32_t nblk = (cnt + kChunk - 1) / kChunk;
+    for (uint32_t blk = warp; blk < nblk; blk += nwarp) {
+        const uint32_t b0 = blk * kChunk, m = min(cnt - b0, (uint32_t)kChunk);
+        stage_symbols(sec, w, b0, m, wbuf);
+        if (regc) {
+            const uint32_t s0 = 32 * lane;
+            SymReader rd(wbuf, w, s0, s0 < m ? min(m - s0, 32u) : 0u);
+            for (uint32_t i = 0; i < rd.m; i++) {
+                const uint32_t v = rd.next(), q = v >> 1, inc = 1u << ((v & 1u) << 4);
 #pragma unroll
-        for (int u = 0; u < 4; u++) {
-            const uint32_t i = base + u * blockDim.x + tid;
-            v[u] = i < cnt ? get_sym(sec, w, i) : kNone;
+                for (int k = 0; k < 8; k++) c2[k] += q == (uint32_t)k ? inc : 0u;
+            }
+        } else {
+            for (uint32_t k = 0; k < 32; k++) {
+                const uint32_t i = 32 * k + lane;
+                const uint32_t v = i < m ? get_sym(wbuf, w, i) : kNone;
+                if (priv) {
+                    const unsigned same = __match_any_sync(0xFFFFFFFFu, v);
+                    if (v != kNone && lane == (uint32_t)__ffs(same) - 1) atomicAdd(&hh[v], (uint32_t)__popc(same));
+                } else if (v != kNone) {
+                    atomicAdd(&hh[v], 1u);
+                }
+            }
         }
+        __syncwarp();   // the staged words are read before the next block overwrites them
+    }
+    if (regc) {
 #pragma unroll
-        for (int u = 0; u < 4; u++) {
-            const unsigned same = __match_any_sync(0xFFFFFFFFu, v[u]);
-            if (v[u] != kNone && (tid & 31) == __ffs(same) - 1) atomicAdd(&hh[v[u]], (uint32_t)__popc(same));
+        for (int k = 0; k < 8; k++) {
+            uint32_t lo = c2[k] & 0xFFFFu, hi = c2[k] >> 16;
+#pragma unroll
+            for (int o = 16; o; o >>= 1) {
+                lo += __shfl_xor_sync(0xFFFFFFFFu, lo, o);
+                hi += __shfl_xor_sync(0xFFFFFFFFu, hi, o);
+            }
+            if (lane == 0) {
+                if (lo) atomicAdd(&S.hist[2 * k], lo);
+                if (hi) atomicAdd(&S.hist[2 * k + 1], hi);
+            }
         }
     }
     __syncthreads();
@@ -512,9 +602,11 @@ __global__ void __launch_bounds__(kBuildThreads) k_ent_build(EntBatch b, Scratch
                 S.node_depth[k] = root ? 0 : 1;
             }
             __syncthreads();
-            for (int r = 0; r < kMaxWidth; r++) {   // 2^12 >= the 4095 nodes a tree can have
+            // (2^12 >= the 4095 nodes a tree can have; the rounds stop once every pointer is the root)
+            for (int r = 0; r < kMaxWidth; r++) {
                 constexpr int kPer = kMaxAlph / kBuildThreads;   // nodes a thread holds (registers)
                 uint16_t na[kPer], nd[kPer];
+                int moved = 0;
 #pragma unroll
                 for (int q = 0; q < kPer; q++) {
                     const uint32_t k = tid + q * kBuildThreads;
@@ -522,6 +614,7 @@ __global__ void __launch_bounds__(kBuildThreads) k_ent_build(EntBatch b, Scratch
                         const uint16_t a = S.node_parent[k];
                         na[q] = S.node_parent[a];
                         nd[q] = S.node_depth[k] + S.node_depth[a];
+                        moved |= na[q] != a;
                     }
                 }
                 __syncthreads();
@@ -533,7 +626,7 @@ __global__ void __launch_bounds__(kBuildThreads) k_ent_build(EntBatch b, Scratch
                         S.node_depth[k] = nd[q];
                     }
                 }
-                __syncthreads();
+                if (!__syncthreads_or(moved)) break;
             }
             uint32_t deep = 0;
             for (uint32_t i = tid; i < n; i += blockDim.x) deep = max(deep, (uint32_t)S.node_depth[S.leaf_parent[i]] + 1);
@@ -558,7 +651,7 @@ __global__ void __launch_bounds__(kBuildThreads) k_ent_build(EntBatch b, Scratch
     if (tid == 0) canonical_tables(S.per_len, S.first, S.index);
     __syncthreads();
     const size_t tab = ((size_t)f * kSecs + s) * kMaxAlph;
-    place_by_length(S.len, alph, S.index, reinterpret_cast<uint16_t *>(S.keys), [&](uint32_t v, uint32_t l, uint32_t pos) {
+    place_by_length(S.len, alph, S.index, S.red, [&](uint32_t v, uint32_t l, uint32_t pos) {
         const uint32_t code = S.first[l] + (pos - S.index[l]);
         sc.rcode[tab + v] = (uint16_t)(__brev(code) >> (32 - l));
     });
@@ -567,16 +660,18 @@ __global__ void __launch_bounds__(kBuildThreads) k_ent_build(EntBatch b, Scratch
     const uint32_t nch = (cnt + kChunk - 1) / kChunk;
     uint32_t *cw = sc.chunk + ((size_t)f * kSecs + s) * sc.max_chunks;
     uint32_t mine = 0;
-    for (uint32_t c = tid >> 5; c < nch; c += blockDim.x >> 5) {   // a warp per chunk, 32 symbols a lane
-        const uint32_t c0 = c * kChunk, m = min(cnt - c0, (uint32_t)kChunk), s0 = 32 * (tid & 31);
-        SymReader rd(sec, w, c0 + s0, s0 < m ? min(m - s0, 32u) : 0u);
+    for (uint32_t c = warp; c < nch; c += nwarp) {   // a warp per chunk (staged), 32 symbols a lane
+        const uint32_t c0 = c * kChunk, m = min(cnt - c0, (uint32_t)kChunk), s0 = 32 * lane;
+        stage_symbols(sec, w, c0, m, wbuf);
+        SymReader rd(wbuf, w, s0, s0 < m ? min(m - s0, 32u) : 0u);
         uint32_t bits = 0;
         for (uint32_t i = 0; i < rd.m; i++) bits += S.len[rd.next()];
         for (int o = 16; o; o >>= 1) bits += __shfl_xor_sync(0xFFFFFFFFu, bits, o);
-        if ((tid & 31) == 0) {
+        if (lane == 0) {
             cw[c] = (bits + 31) / 32;
             mine += (bits + 31) / 32;
         }
+        __syncwarp();
     }
     const uint32_t payload = block_sum(mine, S.red);
     if (tid == 0) {
@@ -588,26 +683,26 @@ __global__ void __launch_bounds__(kBuildThreads) k_ent_build(EntBatch b, Scratch
     }
 }
 
-// grid nframes, 32 threads
-__global__ void k_ent_layout(EntBatch b, Scratch sc, unsigned *err, int nframes) {
-    const int f = blockIdx.x, lane = threadIdx.x;
+// grid nframes, 32 * kSecs threads: every warp derives the section offsets; warp 0 writes the
+// header and descriptors, warp s the length table and chunk offsets of section s
+__global__ void __launch_bounds__(32 * kSecs) k_ent_layout(EntBatch b, Scratch sc, unsigned *err, int nframes) {
+    const int f = blockIdx.x, lane = threadIdx.x & 31, s = threadIdx.x >> 5;
     if (f >= nframes) return;
     Frame &F = sc.frame[f];
     Layout L;
     if (!parse_fixed(b.in[f], b.in_size[f], b.rows, b.cols, L)) {
-        if (lane == 0) b.out_bytes[f] = 0;
+        if (threadIdx.x == 0) b.out_bytes[f] = 0;
         return;
     }
-    uint32_t eo[kSecs];   // every lane computes the section offsets
+    uint32_t eo[kSecs];
     uint32_t off = kEntHeaderWords;
-    for (int s = 0; s < kSecs; s++) {
-        eo[s] = off;
-        off += F.sec[s].words;
+    for (int k = 0; k < kSecs; k++) {
+        eo[k] = off;
+        off += F.sec[k].words;
     }
-    if (lane < kSecs) F.sec[lane].ent_off = eo[lane];
     const unsigned long long total = 4ull * off;
     if (total > b.out_cap[f]) {
-        if (lane == 0) {
+        if (threadIdx.x == 0) {
             F.ok = 0;
             b.out_bytes[f] = total;
             atomicOr(err, E_CAPACITY);
@@ -615,49 +710,50 @@ __global__ void k_ent_layout(EntBatch b, Scratch sc, unsigned *err, int nframes)
         return;
     }
     uint32_t *o = reinterpret_cast<uint32_t *>(b.out[f]);
-    const uint32_t *h = reinterpret_cast<const uint32_t *>(b.in[f]);
-    if (lane < 16) o[lane] = h[lane];
-    if (lane == 16) o[16] = kEntMagic;
-    if (lane == 17) o[17] = (uint32_t)total;
-    if (lane < kSecs) {
-        const Sec &S = F.sec[lane];
-        o[18 + 4 * lane] = S.mode ? (1u | L.width[lane] << 8) : 0u;
-        o[19 + 4 * lane] = S.mode ? L.count[lane] : L.words[lane];
-        o[20 + 4 * lane] = S.alph;
-        o[21 + 4 * lane] = S.words;
-    }
-    for (int s = 0; s < kSecs; s++) {
-        const Sec &S = F.sec[s];
-        if (!S.mode) continue;
-        uint32_t *dst = o + eo[s];
-        const uint8_t *len = sc.len + ((size_t)f * kSecs + s) * kMaxAlph;
-        const uint32_t tw = (S.alph + 7) / 8;
-        for (uint32_t j = lane; j < tw; j += 32) {
-            uint32_t v = 0;
-            for (uint32_t k = 0; k < 8 && 8 * j + k < S.alph; k++) v |= (uint32_t)len[8 * j + k] << (4 * k);
-            dst[j] = v;
+    if (s == 0) {
+        const uint32_t *h = reinterpret_cast<const uint32_t *>(b.in[f]);
+        if (lane < 16) o[lane] = h[lane];
+        if (lane == 16) o[16] = kEntMagic;
+        if (lane == 17) o[17] = (uint32_t)total;
+        if (lane < kSecs) {
+            F.sec[lane].ent_off = eo[lane];
+            const Sec &D = F.sec[lane];
+            o[18 + 4 * lane] = D.mode ? (1u | L.width[lane] << 8) : 0u;
+            o[19 + 4 * lane] = D.mode ? L.count[lane] : L.words[lane];
+            o[20 + 4 * lane] = D.alph;
+            o[21 + 4 * lane] = D.words;
         }
-        // chunk offsets: exclusive prefix of the chunk sizes, kept in place for the writer
-        uint32_t *cw = sc.chunk + ((size_t)f * kSecs + s) * sc.max_chunks;
-        uint32_t carry = 0;
-        for (uint32_t c0 = 0; c0 < S.nch; c0 += 32) {
-            const uint32_t c = c0 + lane;
-            const uint32_t v = c < S.nch ? cw[c] : 0u;
-            uint32_t x = v;
-            for (int d = 1; d < 32; d <<= 1) {
-                const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, x, d);
-                if (lane >= d) x += y;
-            }
-            if (c < S.nch) {
-                cw[c] = carry + x - v;
-                dst[tw + c] = carry + x - v;
-            }
-            carry += __shfl_sync(0xFFFFFFFFu, x, 31);
+        if (lane == 0) {
+            F.ok = 1;
+            b.out_bytes[f] = total;
         }
     }
-    if (lane == 0) {
-        F.ok = 1;
-        b.out_bytes[f] = total;
+    const Sec &S = F.sec[s];
+    if (!S.mode) return;
+    uint32_t *dst = o + eo[s];
+    const uint8_t *len = sc.len + ((size_t)f * kSecs + s) * kMaxAlph;
+    const uint32_t tw = (S.alph + 7) / 8;
+    for (uint32_t j = lane; j < tw; j += 32) {
+        uint32_t v = 0;
+        for (uint32_t k = 0; k < 8 && 8 * j + k < S.alph; k++) v |= (uint32_t)len[8 * j + k] << (4 * k);
+        dst[j] = v;
+    }
+    // chunk offsets: exclusive prefix of the chunk sizes, kept in place for the writer
+    uint32_t *cw = sc.chunk + ((size_t)f * kSecs + s) * sc.max_chunks;
+    uint32_t carry = 0;
+    for (uint32_t c0 = 0; c0 < S.nch; c0 += 32) {
+        const uint32_t c = c0 + lane;
+        const uint32_t v = c < S.nch ? cw[c] : 0u;
+        uint32_t x = v;
+        for (int d = 1; d < 32; d <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, x, d);
+            if (lane >= d) x += y;
+        }
+        if (c < S.nch) {
+            cw[c] = carry + x - v;
+            dst[tw + c] = carry + x - v;
+        }
+        carry += __shfl_sync(0xFFFFFFFFu, x, 31);
     }
 }
 
@@ -682,6 +778,7 @@ __global__ void __launch_bounds__(kWriteThreads) k_ent_write(EntBatch b, Scratch
     // the section's codes in shared memory: reversed code | length << 16; a chunk buffer per warp
     __shared__ uint32_t s_code[kMaxAlph];
     __shared__ uint32_t s_buf[kWarps][kChunk * kMaxLen / 32];
+    __shared__ uint32_t s_sym[kWarps][32 * kMaxWidth];   // the chunk's fixed-width words (staged once)
     const size_t tab = ((size_t)f * kSecs + s) * kMaxAlph;
     for (uint32_t v = threadIdx.x; v < S.alph; v += blockDim.x)
         s_code[v] = (uint32_t)sc.rcode[tab + v] | (uint32_t)sc.len[tab + v] << 16;
@@ -696,9 +793,10 @@ __global__ void __launch_bounds__(kWriteThreads) k_ent_write(EntBatch b, Scratch
     for (uint32_t c = blockIdx.x * kWarps + warp; c < S.nch; c += gridDim.x * kWarps) {
         const uint32_t c0 = c * kChunk, m = min(cnt - c0, (uint32_t)kChunk), s0 = 32 * lane;
         const uint32_t ml = s0 < m ? min(m - s0, 32u) : 0u;
+        stage_symbols(sec, w, c0, m, s_sym[warp]);
         uint32_t bits = 0;
         {
-            SymReader rd(sec, w, c0 + s0, ml);
+            SymReader rd(s_sym[warp], w, s0, ml);
             for (uint32_t i = 0; i < ml; i++) bits += s_code[rd.next()] >> 16;
         }
         uint32_t x = bits;
@@ -710,7 +808,7 @@ __global__ void __launch_bounds__(kWriteThreads) k_ent_write(EntBatch b, Scratch
         for (uint32_t j = lane; j < nwords; j += 32) buf[j] = 0u;
         __syncwarp();
         {
-            SymReader rd(sec, w, c0 + s0, ml);
+            SymReader rd(s_sym[warp], w, s0, ml);
             uint32_t p = x - bits;
             for (uint32_t i = 0; i < ml; i++) {
                 const uint32_t cl = s_code[rd.next()], code = cl & 0xFFFFu, len = cl >> 16;
@@ -736,7 +834,6 @@ struct DecSmem {
     uint32_t per_len[kMaxLen + 1];
     uint32_t first[kMaxLen + 1];
     uint32_t index[kMaxLen + 2];
-    uint16_t cnt[kMaxLen * 256];   // place_by_length counters (256 threads)
     uint32_t bad;
 };
 
@@ -833,7 +930,7 @@ __global__ void __launch_bounds__(256) k_ent_dec_prep(EntBatch b, Scratch sc, un
         for (int l = 0; l <= kMaxLen + 1; l++) D.index[l] = S.index[l];
     }
     uint16_t *sorted = sc.sorted + ((size_t)f * kSecs + s) * kMaxAlph;
-    place_by_length(S.len, alph, S.index, S.cnt,
+    place_by_length(S.len, alph, S.index, S.red,
                     [&](uint32_t v, uint32_t, uint32_t pos) { sorted[pos] = (uint16_t)v; });
     // chunk offsets non-decreasing, inside the payload
     const uint32_t nch = (L.count[s] + kChunk - 1) / kChunk, tw = (alph + 7) / 8;
@@ -1063,7 +1160,7 @@ lcc_status lcc_entropy_encode(lcc_ctx *c, int32_t nframes, const uint8_t *const 
     LCC_CUDA(cudaFuncSetAttribute(ent::k_ent_build, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     LCC_LAUNCH(c, 10, (ent::k_ent_build<<<dim3(5, nframes), ent::kBuildThreads, smem, c->stream>>>(b, sc, c->s.err),
                        cudaGetLastError()));
-    LCC_LAUNCH(c, 11, (ent::k_ent_layout<<<nframes, 32, 0, c->stream>>>(b, sc, c->s.err, nframes), cudaGetLastError()));
+    LCC_LAUNCH(c, 11, (ent::k_ent_layout<<<nframes, 32 * ent::kSecs, 0, c->stream>>>(b, sc, c->s.err, nframes), cudaGetLastError()));
     LCC_LAUNCH(c, 12, (ent::k_ent_write<<<dim3(grid_x(c, sc), ent::kSecs, nframes), ent::kWriteThreads, 0, c->stream>>>(
                            b, sc),
                        cudaGetLastError()));

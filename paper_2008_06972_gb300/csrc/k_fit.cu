@@ -259,12 +259,15 @@ __device__ __forceinline__ void macc_add(float &h, float &l, float p, float e) {
     l = __fadd_rn(l, __fadd_rn(err, e));
 }
 
-// Adds the point p = r u, shifted by the anchor a (q = p - a exactly, as hi + lo), to m:
-// q, and q_i q_j as p = fl(hi_i hi_j) plus its exact error and the cross terms by fma.
-__device__ __forceinline__ void moments_point(MomentAcc &m, float rr, float ux, float uy, float uz, float ax,
-                                              float ay, float az) {
-    const ff qx = two_sum(__fmul_rn(rr, ux), -ax), qy = two_sum(__fmul_rn(rr, uy), -ay),
-             qz = two_sum(__fmul_rn(rr, uz), -az);
+// Adds the point p = r u, shifted by the anchor a (q = p - a exactly, as hi + lo), to m when it
+// is in the set: q, and q_i q_j as p = fl(hi_i hi_j) plus its exact error and the cross terms by
+// fma.  A pixel outside the set adds exact zeros, which leave every running sum and error term as
+// it was, so the pixel loops need no branch.
+__device__ __forceinline__ void moments_point(MomentAcc &m, bool in, float rr, float ux, float uy, float uz,
+                                                 float ax, float ay, float az) {
+    ff qx = two_sum(__fmul_rn(rr, ux), -ax), qy = two_sum(__fmul_rn(rr, uy), -ay),
+       qz = two_sum(__fmul_rn(rr, uz), -az);
+    if (!in) qx = qy = qz = {0.f, 0.f};
     macc_add(m.h[0], m.l[0], qx.hi, qx.lo);
     macc_add(m.h[1], m.l[1], qy.hi, qy.lo);
     macc_add(m.h[2], m.l[2], qz.hi, qz.lo);
@@ -450,10 +453,9 @@ struct TileView {
             MomentAcc acc = macc_zero();
 #pragma unroll 2
             for (int k = c * CH; k < (c + 1) * CH; k++) {
-                if (!S.get(k)) continue;
                 float ux, uy, uz;
                 u(k, ux, uy, uz);
-                moments_point(acc, r(k), ux, uy, uz, ax, ay, az);
+                moments_point(acc, S.get(k), r(k), ux, uy, uz, ax, ay, az);
             }
             const Moments part = moments_finish(acc);
             m = c == 0 ? part : moments_add(m, part);
@@ -536,10 +538,9 @@ struct TileLanes {
         MomentAcc acc = macc_zero();
 #pragma unroll 2
         for (int k = l * CH; k < (l + 1) * CH; k++) {
-            if (!S.get(k)) continue;
             float ux, uy, uz;
             u(k, ux, uy, uz);
-            moments_point(acc, r(k), ux, uy, uz, ax, ay, az);
+            moments_point(acc, S.get(k), r(k), ux, uy, uz, ax, ay, az);
         }
         const Moments part = moments_finish(acc);
         Moments m = moments_shfl(gmask, part, g0);

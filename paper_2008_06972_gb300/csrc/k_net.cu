@@ -420,7 +420,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_net_fwd_tc(NetDev nd, const b
         for (int i = tid; i < C1; i += blockDim.x) sB1[i] = th[OB1 + i];
         for (int i = tid; i < C2; i += blockDim.x) sB2[i] = th[OB2 + i];
         for (int i = tid; i < C3; i += blockDim.x) sB3[i] = th[OB3 + i];
-        for (int i = tid; i < HID * C3; i += blockDim.x) sF1[i] = nd.F1b[i];
+        for (int i = tid; i < HID * C3; i += blockDim.x) sF1[(i % C3) * HID + i / C3] = nd.F1b[i];   // [c][j]
         for (int i = tid; i < HID; i += blockDim.x) sC1[i] = th[OC1 + i];
         for (int i = tid; i < NOUT * HID; i += blockDim.x) sF2[i] = nd.F2b[i];
         for (int i = tid; i < NOUT; i += blockDim.x) sC2[i] = th[OC2 + i];
@@ -517,15 +517,22 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_net_fwd_tc(NetDev nd, const b
         const uint32_t trow = tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(sl * 64);
         float *gp = sGP + sl * 4 * 2 * C3;
         float *gs = sG + sl * 2 * C3;
+        // this thread's input pixel of pair pa (loaded one pair ahead, so that the global load's
+        // latency overlaps the previous pair's layers)
+        auto load_in = [&](long long pa) {
+            const long long tile = pa * 2 + tl;
+            uint2 v = make_uint2(0u, 0u);
+            if (pa * 2 < T && tile < T) v = *reinterpret_cast<const uint2 *>(x + ((size_t)tile * kPX + py * 8 + px) * C0);
+            return v;
+        };
+        uint2 vin = load_in(blockIdx.x + sl * G);
         for (long long pa = blockIdx.x + sl * G; pa * 2 < T; pa += kTcSlots * G) {
             {   // input: 4 channels and 4 zeros in chunk 0, zeros in chunk 1 (the 16 channels of a k-step)
-                const long long tile = pa * 2 + tl;
-                uint2 v = make_uint2(0u, 0u);
-                if (tile < T) v = *reinterpret_cast<const uint2 *>(x + ((size_t)tile * kPX + py * 8 + px) * C0);
-                *reinterpret_cast<uint4 *>(buf + tpos(0, py + 1, tl, px + 1)) = make_uint4(v.x, v.y, 0u, 0u);
+                *reinterpret_cast<uint4 *>(buf + tpos(0, py + 1, tl, px + 1)) = make_uint4(vin.x, vin.y, 0u, 0u);
                 *reinterpret_cast<uint4 *>(buf + tpos(1, py + 1, tl, px + 1)) = make_uint4(0u, 0u, 0u, 0u);
             }
             handoff();
+            vin = load_in(pa + kTcSlots * G);
             const long long tile = pa * 2 + tl;
 #pragma unroll 1
             for (int layer = 0; layer < 3; layer++) {
@@ -583,7 +590,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_net_fwd_tc(NetDev nd, const b
                 if (ht < T) {
                     const float *g2 = gs + t2 * C3;
                     float yv = sC1[lane];
-                    for (int c = 0; c < C3; c++) yv = fmaf(sF1[lane * C3 + c], g2[c], yv);
+                    for (int c = 0; c < C3; c++) yv = fmaf(sF1[c * HID + lane], g2[c], yv);   // lanes on consecutive banks
                     const float hj = bfround(fmaxf(yv, 0.f));
                     float o[NOUT];
 #pragma unroll
