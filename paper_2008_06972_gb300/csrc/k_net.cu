@@ -40,6 +40,7 @@ typedef __nv_bfloat16 bf16;
 constexpr int kPX = 64;                       // pixels of an 8x8 tile
 constexpr int C0 = 4, C1 = 32, C2 = 64, C3 = 64, HID = 32, NOUT = 5;
 constexpr int XS = 8;                         // padded channel stride of the input copy
+constexpr int K1 = 48;                        // conv1 on tcgen05 as one contraction: 9 taps x 4 channels, 3 k-steps
 constexpr int A1S = C1 + 8, A2S = C2 + 8;     // padded channel strides (bank spread)
 constexpr int BTS = 9 * 64 + 8;               // input-gradient weight rows (9 taps x 64 channels + bank pad)
 constexpr int kNetWarps = 4;
@@ -153,14 +154,16 @@ __global__ void k_net_prep(NetDev nd) {
         j -= HID * C3;
         nd.F2b[j] = bfround(th[OF2 + j]);
     }
-    // tcgen05 layouts: element (tap, c8, co, e) = W[co][ci = 8 c8 + e][tap] (conv1: ci >= 4 is zero)
-    const int m1 = 9 * 2 * C1 * 8, m2 = 9 * (C1 / 8) * C2 * 8, m3 = 9 * (C2 / 8) * C3 * 8;
+    // tcgen05 layouts: conv2/conv3 element (tap, c8, co, e) = W[co][ci = 8 c8 + e][tap]; conv1 is
+    // one contraction over k = tap * 4 + ci (im2col, 36 of K1 = 48 used): element (c8, co, e) =
+    // W1[co][ci][tap] for k = 8 c8 + e
+    const int m1 = (K1 / 8) * C1 * 8, m2 = 9 * (C1 / 8) * C2 * 8, m3 = 9 * (C2 / 8) * C3 * 8;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < m1 + m2 + m3; i += gridDim.x * blockDim.x) {
         int j = i;
         if (j < m1) {
-            const int e = j % 8, co = (j / 8) % C1, c8 = (j / (8 * C1)) % 2, tap = j / (8 * C1 * 2);
-            const int ci = 8 * c8 + e;
-            nd.T1[j] = __float2bfloat16_rn(ci < C0 ? th[OW1 + co * C0 * 9 + ci * 9 + tap] : 0.f);
+            const int e = j % 8, co = (j / 8) % C1, c8 = j / (8 * C1);
+            const int k = 8 * c8 + e, tap = k / C0, ci = k % C0;
+            nd.T1[j] = __float2bfloat16_rn(k < 9 * C0 ? th[OW1 + co * C0 * 9 + ci * 9 + tap] : 0.f);
             continue;
         }
         j -= m1;
@@ -252,15 +255,15 @@ __global__ void k_net_inputs(Geometry g, uint32_t *rimg0, bf16 *x0, float4 *anch
 
 constexpr int TPOS = 10 * 2 * 10;              // padded positions per 8-channel chunk
 constexpr int TCHUNK = TPOS * 16;              // bytes per chunk (3200)
-constexpr int TW1 = 9 * 2 * C1 * 16, TW2 = 9 * (C1 / 8) * C2 * 16, TW3 = 9 * (C2 / 8) * C3 * 16;
+constexpr int TW1 = (K1 / 8) * C1 * 16, TW2 = 9 * (C1 / 8) * C2 * 16, TW3 = 9 * (C2 / 8) * C3 * 16;
 // One activation buffer per pair slot, shared by the layer input (2 chunks: 4 channels and
 // zeros), the first activations (4 chunks) and the second (8 chunks): each is dead once the
 // convolution reading it has committed, which is before the next one is written.
 constexpr int TACT = (C2 / 8) * TCHUNK;
 constexpr int kTcSlots = 3;                     // pairs of tiles in flight per CTA
-constexpr int TGP = 4 * 2 * C3 * 4, TG = 2 * C3 * 4;
+constexpr int TG = 2 * C3 * 4;
 constexpr int TPAR = (C1 + C2 + C3 + HID * C3 + HID + NOUT * HID + NOUT + 3) / 4 * 16;   // biases, head (fp32)
-constexpr size_t kTcSmem = (size_t)TW1 + TW2 + TW3 + kTcSlots * (size_t)(TACT + TGP + TG) + TPAR + 128;   // + barriers
+constexpr size_t kTcSmem = (size_t)TW1 + TW2 + TW3 + kTcSlots * (size_t)(TACT + TG) + TPAR + 128;   // + barriers
 constexpr uint32_t kTmemCols = 256;             // one 64-column accumulator per pair slot (3 x 64, rounded up)
 constexpr long long kSpinLimit = 1ll << 22;
 static_assert(kTcSmem <= 227 * 1024, "shared memory of the tcgen05 forward");
@@ -355,6 +358,18 @@ __device__ __forceinline__ void tc_conv(uint32_t tmem, uint32_t act, uint32_t wt
     }
 }
 
+// Conv1 as one contraction over the im2col rows (k = tap * 4 + ci, written by the epilogue at
+// each pixel's own position): three k-steps of M=128, N=32 MMAs.
+__device__ __forceinline__ void tc_conv1(uint32_t tmem, uint32_t act, uint32_t wts) {
+    constexpr uint32_t idesc = mma_idesc(128, C1);
+    const uint64_t a0 = smem_desc(act, TCHUNK, 160) + (uint64_t)(((1 * 20 + 1) * 16) >> 4);
+    const uint64_t b0 = smem_desc(wts, C1 * 16, 128);
+#pragma unroll
+    for (int ks = 0; ks < K1 / 16; ks++)
+        tc_mma(tmem, a0 + (uint64_t)((2 * ks * TCHUNK) >> 4), b0 + (uint64_t)((2 * ks * C1 * 16) >> 4), idesc,
+               ks ? 1u : 0u);
+}
+
 // bulk copy global -> shared (TMA engine), completion counted on an mbarrier
 __device__ __forceinline__ void bulk_g2s(uint32_t dst, const void *src, uint32_t bytes, uint32_t mbar) {
     asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(dst),
@@ -375,10 +390,12 @@ constexpr int kTcThreads = (kTcEpiWarps + 1) * 32;
 __device__ __forceinline__ void mbar_arrive(uint32_t mbar) {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(mbar) : "memory");
 }
+// non-blocking test of an mbarrier phase (the MMA warp polls several barriers in turn, so it must
+// not be suspended on one that is not ready)
 __device__ __forceinline__ bool mbar_try(uint32_t mbar, uint32_t parity) {
     uint32_t done;
     asm volatile(
-        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "{\n\t.reg .pred p;\n\tmbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
         "selp.u32 %0, 1, 0, p;\n\t}\n"
         : "=r"(done)
         : "r"(mbar), "r"(parity)
@@ -396,8 +413,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_net_fwd_tc(NetDev nd, const b
     extern __shared__ __align__(1024) uint8_t sm[];
     uint8_t *sW1 = sm, *sW2 = sW1 + TW1, *sW3 = sW2 + TW2;
     uint8_t *sAct = sW3 + TW3;                                         // [slot][TACT]
-    float *sGP = reinterpret_cast<float *>(sAct + kTcSlots * TACT);    // [slot][quadrant][tile][64]
-    float *sG = sGP + kTcSlots * 4 * 2 * C3;                           // [slot][tile][64]
+    float *sG = reinterpret_cast<float *>(sAct + kTcSlots * TACT);     // [slot][tile][64] pooled vectors
     float *sPar = sG + kTcSlots * 2 * C3;                              // b1 b2 b3 F1b c1 F2b c2
     float *sB1 = sPar, *sB2 = sB1 + C1, *sB3 = sB2 + C2, *sF1 = sB3 + C3, *sC1 = sF1 + HID * C3;
     float *sF2 = sC1 + HID, *sC2 = sF2 + NOUT * HID;
@@ -474,7 +490,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_net_fwd_tc(NetDev nd, const b
                     tc_after_sync();
                     const uint32_t base = smem_u32(sAct + sl * TACT);
                     const uint32_t d = tmem + (uint32_t)(sl * 64);
-                    if (layer[sl] == 0) tc_conv<C0, C1>(d, base, aW1);
+                    if (layer[sl] == 0) tc_conv1(d, base, aW1);
                     else if (layer[sl] == 1) tc_conv<C1, C2>(d, base, aW2);
                     else tc_conv<C2, C3>(d, base, aW3);
                     tc_commit(smem_u32(bar + 1 + sl));
@@ -485,6 +501,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_net_fwd_tc(NetDev nd, const b
                     }
                     progressed = true;
                 }
+                if (!progressed) __nanosleep(20);   // leave the issue slots to the epilogue warps meanwhile
                 idle = progressed ? 0 : idle + 1;
                 if (idle > kSpinLimit) {   // nothing became ready for too long: give up, report
                     atomicExch(s_fail, 1);
@@ -515,7 +532,6 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_net_fwd_tc(NetDev nd, const b
             if (lane == 0) mbar_arrive(bar_in);
         };
         const uint32_t trow = tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(sl * 64);
-        float *gp = sGP + sl * 4 * 2 * C3;
         float *gs = sG + sl * 2 * C3;
         // this thread's input pixel of pair pa (loaded one pair ahead, so that the global load's
         // latency overlaps the previous pair's layers)
@@ -525,14 +541,31 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_net_fwd_tc(NetDev nd, const b
             if (pa * 2 < T && tile < T) v = *reinterpret_cast<const uint2 *>(x + ((size_t)tile * kPX + py * 8 + px) * C0);
             return v;
         };
-        uint2 vin = load_in(blockIdx.x + sl * G);
-        for (long long pa = blockIdx.x + sl * G; pa * 2 < T; pa += kTcSlots * G) {
-            {   // input: 4 channels and 4 zeros in chunk 0, zeros in chunk 1 (the 16 channels of a k-step)
-                *reinterpret_cast<uint4 *>(buf + tpos(0, py + 1, tl, px + 1)) = make_uint4(vin.x, vin.y, 0u, 0u);
-                *reinterpret_cast<uint4 *>(buf + tpos(1, py + 1, tl, px + 1)) = make_uint4(0u, 0u, 0u, 0u);
+        // the pair's input: the pixel's 4 channels into chunk 6 (zero border), then conv1's im2col
+        // row (k = tap * 4 + ci, 36 values and 12 zeros) into chunks 0..5 at the pixel's position,
+        // handed to the MMA warp; chunk 6 is free until the second layer's output is written
+        auto put_input = [&](uint2 v) {
+            *reinterpret_cast<uint4 *>(buf + tpos(6, py + 1, tl, px + 1)) = make_uint4(v.x, v.y, 0u, 0u);
+            group_sync(sl);
+#pragma unroll
+            for (int c8 = 0; c8 < K1 / 8; c8++) {
+                uint2 t0 = make_uint2(0u, 0u), t1 = make_uint2(0u, 0u);
+                if (2 * c8 < 9) {
+                    const int tap = 2 * c8;
+                    t0 = *reinterpret_cast<const uint2 *>(buf + tpos(6, py + tap / 3, tl, px + tap % 3));
+                }
+                if (2 * c8 + 1 < 9) {
+                    const int tap = 2 * c8 + 1;
+                    t1 = *reinterpret_cast<const uint2 *>(buf + tpos(6, py + tap / 3, tl, px + tap % 3));
+                }
+                *reinterpret_cast<uint4 *>(buf + tpos(c8, py + 1, tl, px + 1)) = make_uint4(t0.x, t0.y, t1.x, t1.y);
             }
             handoff();
-            vin = load_in(pa + kTcSlots * G);
+        };
+        const long long pa0 = blockIdx.x + sl * G;
+        if (pa0 * 2 < T) put_input(load_in(pa0));
+        uint2 vin = load_in(pa0 + kTcSlots * G);
+        for (long long pa = pa0; pa * 2 < T; pa += kTcSlots * G) {
             const long long tile = pa * 2 + tl;
 #pragma unroll 1
             for (int layer = 0; layer < 3; layer++) {
@@ -559,38 +592,62 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_net_fwd_tc(NetDev nd, const b
                                               : (layer == 1 ? act.a2 : act.a3) + ((size_t)tile * kPX + py * 8 + px) * C2;
                         *reinterpret_cast<uint4 *>(ao + c0) = make_uint4(w[0], w[1], w[2], w[3]);
                     }
-                    if (layer < 2) {   // the next layer's input, in place of this layer's (already read)
-                        *reinterpret_cast<uint4 *>(buf + tpos(c0 / 8, py + 1, tl, px + 1)) = make_uint4(w[0], w[1], w[2], w[3]);
-                    } else {   // pooling: the 16 pixels of a tile in this quadrant, per channel
-#pragma unroll
-                        for (int i = 0; i < 8; i++) {
-                            float s2 = bfround(v[i]);
-                            s2 += __shfl_xor_sync(0xffffffffu, s2, 1);
-                            s2 += __shfl_xor_sync(0xffffffffu, s2, 2);
-                            s2 += __shfl_xor_sync(0xffffffffu, s2, 4);
-                            s2 += __shfl_xor_sync(0xffffffffu, s2, 16);
-                            if (lane == 0 || lane == 8) gp[(quad * 2 + tl) * C3 + c0 + i] = s2;
-                        }
-                    }
+                    // the next layer's input (or, after the last layer, the activations to pool) in
+                    // place of this layer's input (already read by the MMAs)
+                    *reinterpret_cast<uint4 *>(buf + tpos(c0 / 8, py + 1, tl, px + 1)) = make_uint4(w[0], w[1], w[2], w[3]);
                 }
                 if (layer < 2) handoff();   // the next layer's input is in place, the accumulator is read
                 else tc_before_sync();
             }
             group_sync(sl);
-            {   // pooled vectors (fixed order over the lane quadrants): thread -> (tile, channel)
-                const int t2 = gt >> 6, c = gt & 63;
-                float s2 = 0.f;
-                for (int w = 0; w < 4; w++) s2 += gp[(w * 2 + t2) * C3 + c];
-                gs[t2 * C3 + c] = bfround(s2 * (1.0f / kPX));
+            {   // pooling: thread (tile t2, channel chunk c8, column x) sums its column's 8 pixels of
+                // 8 channels (16-byte loads, 8 lanes on consecutive positions), then a reduce-scatter
+                // over the 8 columns leaves lane x with channel 8 c8 + x
+                const int t2 = gt >> 6, c8 = (gt >> 3) & 7, x = gt & 7;
+                float a[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+                for (int y = 0; y < 8; y++) {
+                    const uint4 q = *reinterpret_cast<const uint4 *>(buf + tpos(c8, y + 1, t2, x + 1));
+                    const uint32_t u[4] = {q.x, q.y, q.z, q.w};
+#pragma unroll
+                    for (int k = 0; k < 4; k++) {
+                        a[2 * k] += __uint_as_float(u[k] << 16);
+                        a[2 * k + 1] += __uint_as_float(u[k] & 0xFFFF0000u);
+                    }
+                }
+                const bool h4 = x & 4, h2 = x & 2, h1 = x & 1;
+                float b4[4], b2[2];
+#pragma unroll
+                for (int i = 0; i < 4; i++) {
+                    const float send = h4 ? a[i] : a[i + 4];
+                    b4[i] = (h4 ? a[i + 4] : a[i]) + __shfl_xor_sync(0xffffffffu, send, 4);
+                }
+#pragma unroll
+                for (int i = 0; i < 2; i++) {
+                    const float send = h2 ? b4[i] : b4[i + 2];
+                    b2[i] = (h2 ? b4[i + 2] : b4[i]) + __shfl_xor_sync(0xffffffffu, send, 2);
+                }
+                const float b1 = (h1 ? b2[1] : b2[0]) + __shfl_xor_sync(0xffffffffu, h1 ? b2[0] : b2[1], 1);
+                gs[t2 * C3 + 8 * c8 + x] = bfround(b1 * (1.0f / kPX));
             }
-            group_sync(sl);
+            group_sync(sl);   // pooled vectors complete; the activations are read, so the buffer is free
+            if ((pa + kTcSlots * G) * 2 < T) {   // the next pair's input goes to the MMA warp before this head
+                put_input(vin);
+                vin = load_in(pa + 2 * kTcSlots * G);
+            }
             if (quad < 2) {   // head: warp quad < 2 of the group takes tile quad of the pair
                 const int t2 = quad;
                 const long long ht = pa * 2 + t2;
                 if (ht < T) {
                     const float *g2 = gs + t2 * C3;
-                    float yv = sC1[lane];
-                    for (int c = 0; c < C3; c++) yv = fmaf(sF1[c * HID + lane], g2[c], yv);   // lanes on consecutive banks
+                    // four interleaved partial sums (a quarter of the dependent chain); lanes read
+                    // consecutive banks
+                    float y4[4] = {sC1[lane], 0.f, 0.f, 0.f};
+#pragma unroll 4
+                    for (int c = 0; c < C3; c += 4)
+#pragma unroll
+                        for (int q = 0; q < 4; q++) y4[q] = fmaf(sF1[(c + q) * HID + lane], g2[c + q], y4[q]);
+                    const float yv = (y4[0] + y4[1]) + (y4[2] + y4[3]);
                     const float hj = bfround(fmaxf(yv, 0.f));
                     float o[NOUT];
 #pragma unroll
