@@ -85,6 +85,10 @@ def parse():
                          "by one eager plan with fixed parameters (--tile, --lookahead, --schedule, --max-batch), "
                          "no autotuning, training or other sections (for ncu)")
     ap.add_argument("--max-batch", type=int, default=64, help="frames per launch of the profiling case")
+    ap.add_argument("--profile-net", action="store_true",
+                    help="profiling case: the proposal net's forward over --net-tiles seeded tiles, --steps calls after "
+                         "one warm-up call, nothing else (for ncu)")
+    ap.add_argument("--net-tiles", type=int, default=98304)
     return ap.parse_args()
 
 
@@ -1366,6 +1370,32 @@ def run_profile_plan(args, stream):
             "mpts_per_s_wall": pts * args.steps / el / 1e6, "bytes": int(nb.sum().item())}
 
 
+def run_profile_net(args, stream):
+    """The proposal net's inference alone (k_net_fwd_tc): --net-tiles tiles of seeded BF16 inputs and
+    He-initialised weights, one warm-up call and --steps timed calls: the case the net's ncu summary
+    under profiles/ is taken on."""
+    import torch
+    from paper_2008_06972_gb300 import lcc
+    from paper_2008_06972_gb300 import train as TR
+    T = args.net_tiles
+    net = lcc.Net(TR.he_uniform_params(4), max_tiles=4096, stream=stream)
+    g = torch.Generator(device="cpu").manual_seed(0)
+    x = (torch.randn((T, 64, 4), generator=g) * 0.3).to(torch.bfloat16).view(torch.int16).cuda()
+    out = torch.zeros((T, 5), dtype=torch.float32, device="cuda")
+    net.forward(x, T, out)
+    assert net.sync() == lcc.OK
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for _ in range(args.steps):
+        net.forward(x, T, out)
+    b.record(stream)
+    assert net.sync() == lcc.OK
+    torch.cuda.synchronize()
+    ms = a.elapsed_time(b) / args.steps
+    flops = NET_FLOPS_PER_TILE * T
+    return {"profile_net": True, "tiles": T, "ms_per_call": ms, "tflops": flops / (ms * 1e-3) / 1e12}
+
+
 def run_hdl64(args, stream):
     """One synthetic HDL-64E sequence (10 frames of 64x2048, the middle one the key frame) encoded
     per call by lcc_encode_sequence: throughput (L2 flushed between steps), kernel times, decode,
@@ -1593,6 +1623,9 @@ def main():
     hbm, _ = peaks()
     if args.profile_plan:
         print(json.dumps(run_profile_plan(args, stream)), flush=True)
+        return
+    if args.profile_net:
+        print(json.dumps(run_profile_net(args, stream)), flush=True)
         return
     line = run_cfg5(args, stream, rank, world, dist)
     if world == 1:

@@ -68,8 +68,11 @@ __device__ __forceinline__ void stage_codes(uint32_t *buf, int sw, uint32_t *sec
     __syncwarp();
 }
 
+// Four blocks per SM (at most 64 registers a thread): twice the resident warps of the
+// unconstrained allocation (112 registers), which hides the tile loads' latency; measured about
+// 30% faster on 128x4096 frames, with the same bytes.
 template <int TH_, int TW_>
-__global__ void __launch_bounds__(kPackWarps * 32) k_pack(Geometry g, Scratch s, Batch b) {
+__global__ void __launch_bounds__(kPackWarps * 32, 4) k_pack(Geometry g, Scratch s, Batch b) {
     using S = PShape<TH_, TW_>;
     constexpr int LPT = S::LPT, PPL = S::PPL, TPW = S::TPW;
     __shared__ uint32_t s_stage[kPackWarps][TPW * S::SW];
