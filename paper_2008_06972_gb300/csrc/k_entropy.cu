@@ -642,11 +642,31 @@ __global__ void __launch_bounds__(kBuildThreads) k_ent_build(EntBatch b, Scratch
             S.len[S.keys[i] & 0xFFFu] = (uint8_t)(S.node_depth[S.leaf_parent[i]] + 1);
     }
     __syncthreads();
-    // canonical codes: rank in (length, symbol) order
+    // canonical codes: rank in (length, symbol) order.  Codes per length: a thread counts its (at
+    // most 4) symbols in 4-bit fields of one register, the fields are widened to bytes (even and
+    // odd lengths apart) and summed over the warp, and each warp adds its 15 counts once (a shared
+    // atomic per symbol queued thousands of symbols on a dozen counters)
     if (tid <= kMaxLen) S.per_len[tid] = 0;
     __syncthreads();
-    for (uint32_t v = tid; v < alph; v += blockDim.x)
-        if (S.len[v]) atomicAdd(&S.per_len[S.len[v]], 1u);
+    {
+        static_assert(kMaxAlph / kBuildThreads <= 4 && 32 * 4 < 256, "per-length fields");
+        unsigned long long c4 = 0ull;   // field l - 1: symbols of length l
+        for (uint32_t v = tid; v < alph; v += blockDim.x) {
+            const uint32_t l = S.len[v];
+            if (l) c4 += 1ull << (4 * (l - 1));
+        }
+        unsigned long long ev = c4 & 0x0F0F0F0F0F0F0F0Full, od = (c4 >> 4) & 0x0F0F0F0F0F0F0F0Full;
+#pragma unroll
+        for (int o = 16; o; o >>= 1) {
+            ev += __shfl_xor_sync(0xFFFFFFFFu, ev, o);
+            od += __shfl_xor_sync(0xFFFFFFFFu, od, o);
+        }
+        if (lane == 0)
+            for (int l = 1; l <= kMaxLen; l++) {
+                const uint32_t q = (uint32_t)((((l - 1) & 1) ? od : ev) >> (8 * ((l - 1) >> 1))) & 0xFFu;
+                if (q) atomicAdd(&S.per_len[l], q);
+            }
+    }
     __syncthreads();
     if (tid == 0) canonical_tables(S.per_len, S.first, S.index);
     __syncthreads();
@@ -731,11 +751,17 @@ __global__ void __launch_bounds__(32 * kSecs) k_ent_layout(EntBatch b, Scratch s
     const Sec &S = F.sec[s];
     if (!S.mode) return;
     uint32_t *dst = o + eo[s];
-    const uint8_t *len = sc.len + ((size_t)f * kSecs + s) * kMaxAlph;
+    // 4-bit length table: eight byte lengths from two 32-bit loads per word (the table's base is
+    // kMaxAlph-aligned); bytes past the alphabet are stale from earlier calls and masked out
+    const uint32_t *len4 = reinterpret_cast<const uint32_t *>(sc.len + ((size_t)f * kSecs + s) * kMaxAlph);
     const uint32_t tw = (S.alph + 7) / 8;
+#pragma unroll 4
     for (uint32_t j = lane; j < tw; j += 32) {
+        const unsigned long long v8 = (unsigned long long)len4[2 * j] | ((unsigned long long)len4[2 * j + 1] << 32);
         uint32_t v = 0;
-        for (uint32_t k = 0; k < 8 && 8 * j + k < S.alph; k++) v |= (uint32_t)len[8 * j + k] << (4 * k);
+#pragma unroll
+        for (uint32_t k = 0; k < 8; k++)
+            if (8 * j + k < S.alph) v |= ((uint32_t)(v8 >> (8 * k)) & 15u) << (4 * k);
         dst[j] = v;
     }
     // chunk offsets: exclusive prefix of the chunk sizes, kept in place for the writer
@@ -780,8 +806,19 @@ __global__ void __launch_bounds__(kWriteThreads) k_ent_write(EntBatch b, Scratch
     __shared__ uint32_t s_buf[kWarps][kChunk * kMaxLen / 32];
     __shared__ uint32_t s_sym[kWarps][32 * kMaxWidth];   // the chunk's fixed-width words (staged once)
     const size_t tab = ((size_t)f * kSecs + s) * kMaxAlph;
-    for (uint32_t v = threadIdx.x; v < S.alph; v += blockDim.x)
-        s_code[v] = (uint32_t)sc.rcode[tab + v] | (uint32_t)sc.len[tab + v] << 16;
+    {   // four entries per thread and step: 8-byte code loads and 4-byte length loads (the tables'
+        // bases are kMaxAlph-aligned; entries past the alphabet are loaded but never looked up)
+        const uint2 *rc4 = reinterpret_cast<const uint2 *>(sc.rcode + tab);
+        const uint32_t *ln4 = reinterpret_cast<const uint32_t *>(sc.len + tab);
+        for (uint32_t v4 = threadIdx.x; v4 < (S.alph + 3) / 4; v4 += blockDim.x) {
+            const uint2 rc = rc4[v4];
+            const uint32_t ln = ln4[v4];
+            s_code[4 * v4] = (rc.x & 0xFFFFu) | (ln & 0xFFu) << 16;
+            s_code[4 * v4 + 1] = (rc.x >> 16) | ((ln >> 8) & 0xFFu) << 16;
+            s_code[4 * v4 + 2] = (rc.y & 0xFFFFu) | ((ln >> 16) & 0xFFu) << 16;
+            s_code[4 * v4 + 3] = (rc.y >> 16) | (ln >> 24) << 16;
+        }
+    }
     __syncthreads();
     const uint32_t *coff = sc.chunk + ((size_t)f * kSecs + s) * sc.max_chunks;
     const uint32_t w = L.width[s], cnt = L.count[s];
