@@ -177,3 +177,79 @@ def test_corrupt_entropy_streams_are_rejected(streams):
         bad[i] = 0x11
     with pytest.raises(ValueError):
         E.decode(bytes(bad))
+
+
+def _batched_depths(used, weight):
+    """Leaf depths of Huffman's two-queue construction taken a batch of joins at a time (the GPU
+    builder's schedule, restated here to check that it is exact): with m the weight of the next
+    node to be made, every remaining node made so far and every remaining leaf of weight <= m
+    is picked before any node made later, so those items, in pick order, pair up at once; an odd
+    last item stays at the front of its queue."""
+    import bisect
+    leaves = sorted(used, key=lambda s: (weight[s], s))
+    n = len(leaves)
+    lw = [weight[s] for s in leaves]
+    nw = [0] * (n - 1)
+    leaf_parent, node_parent = [None] * n, [None] * (n - 1)
+    li = ni = nk = 0
+    big = 1 << 62
+    while nk + 1 < n:
+        l0 = lw[li] if li < n else big
+        l1 = lw[li + 1] if li + 1 < n else big
+        n0 = nw[ni] if ni < nk else big
+        n1 = nw[ni + 1] if ni + 1 < nk else big
+        m = l0 + (l1 if l1 <= n0 else n0) if l0 <= n0 else n0 + (l0 if l0 <= n1 else n1)
+        a = bisect.bisect_right(lw, m, li, n) - li
+        b = nk - ni
+        T, P = a + b, (a + b) // 2
+        picked = [None] * T
+        for e in range(T):
+            if e < a:   # a leaf goes after the nodes strictly lighter than it
+                r = e + bisect.bisect_left(nw, lw[li + e], ni, nk) - ni
+            else:       # a node goes after the leaves no heavier than it
+                r = (e - a) + bisect.bisect_right(lw, nw[ni + e - a], li, li + a) - li
+            picked[r] = e
+        for r in range(2 * P):
+            e = picked[r]
+            if e < a:
+                leaf_parent[li + e] = nk + r // 2
+            else:
+                node_parent[ni + e - a] = nk + r // 2
+        for q in range(P):
+            w = [lw[li + picked[2 * q + k]] if picked[2 * q + k] < a else nw[ni + picked[2 * q + k] - a] for k in (0, 1)]
+            nw[nk + q] = w[0] + w[1]
+        if T % 2 and picked[T - 1] < a:
+            li, ni = li + a - 1, ni + b
+        elif T % 2:
+            li, ni = li + a, ni + b - 1
+        else:
+            li, ni = li + a, ni + b
+        nk += P
+    depth = [0] * (n - 1)
+    for k in range(n - 3, -1, -1):
+        depth[k] = depth[node_parent[k]] + 1
+    return {s: depth[leaf_parent[i]] + 1 for i, s in enumerate(leaves)}
+
+
+def test_batched_construction_is_the_two_queue_construction():
+    """Taking the joins a batch at a time gives every leaf the depth of the one-at-a-time
+    two-queue construction (ties included): uniform, geometric, Fibonacci and random count
+    tables up to 4096 symbols."""
+    rng = np.random.default_rng(11)
+    tables = [[1] * 100, [2 ** k for k in range(20)], [1, 1, 2, 3, 5, 8, 13, 21, 34, 55, 89, 144]]
+    for _ in range(300):
+        n = int(rng.choice([2, 3, 5, 17, 300, 4096]))
+        kind = rng.integers(4)
+        if kind == 0:
+            c = rng.integers(1, 10, n)
+        elif kind == 1:
+            c = rng.exponential(100.0, n).astype(int) + 1
+        elif kind == 2:
+            c = (1000 * 2.0 ** -np.abs(rng.normal(0, 3, n))).astype(int) + 1
+        else:
+            c = rng.choice([1, 2, 3, 5, 8], n)
+        tables.append([int(x) for x in c])
+    for c in tables:
+        used = list(range(len(c)))
+        weight = {s: c[s] for s in used}
+        assert _batched_depths(used, weight) == E._huffman_depths(used, weight)
