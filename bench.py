@@ -1000,7 +1000,9 @@ def kernel_units(st: dict, frames: int, p_frames: int, key_seeded: int, npx: int
         "merge": frames * 128.0 * nt + st["bytes"],
         "pack": frames * 8.0 * npx + st["bytes"],
         "net_inputs": key_seeded * (12.0 * npx + 16.0 * nt),
-        "net_fwd": key_seeded * nt * NET_FLOPS_PER_TILE,
+        # the net runs on pairs of tiles that hold a tile with the 3 valid pixels a fit needs; the
+        # work counted is those tiles' alone (st["tiles_net"]), not their pair partners'
+        "net_fwd": st.get("tiles_net", key_seeded * nt) * NET_FLOPS_PER_TILE,
     }
 
 

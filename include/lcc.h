@@ -107,6 +107,8 @@ typedef struct {
     int64_t cand, fitted, raw;/* candidate, plane-coded and raw-coded pixels */
     uint64_t bytes;           /* stream size */
     int64_t tiles_temporal_cont; /* tiles inside a temporal run (after its first tile) */
+    int64_t tiles_net;        /* plans with a proposal net: key-frame tiles with the 3 valid pixels a
+                                 fit needs, the tiles whose proposals the net computes */
 } lcc_stats;
 
 /* Per-tile record (debug and parity checks): the tile's own fit results. */

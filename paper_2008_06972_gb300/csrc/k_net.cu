@@ -184,11 +184,11 @@ __global__ void k_net_prep(NetDev nd) {
 // kReset the range image is reset to empty afterwards (the standalone input call); without it the
 // image stays for the encode that follows (the plan's seeded key frames, whose pack resets it).
 // One warp per tile, two pixels per lane.
+// The inputs of one tile (one warp, two pixels per lane); returns whether the tile has the 3
+// valid pixels a fit needs (the same on every lane).
 template <bool kReset>
-__global__ void k_net_inputs(Geometry g, uint32_t *rimg0, bf16 *x0, float4 *anchor0) {
-    const int lane = threadIdx.x & 31;
-    const int tile = blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5);
-    if (tile >= g.NT) return;
+__device__ __forceinline__ bool net_inputs_tile(const Geometry &g, uint32_t *rimg0, bf16 *x0, float4 *anchor0, int tile,
+                                                int lane) {
     // frame blockIdx.y: its range image is slot blockIdx.y, its tiles follow the previous frames'
     uint32_t *rimg = rimg0 + (size_t)blockIdx.y * g.H * g.W;
     bf16 *x = x0 + (size_t)blockIdx.y * g.NT * kPX * C0;
@@ -238,6 +238,63 @@ __global__ void k_net_inputs(Geometry g, uint32_t *rimg0, bf16 *x0, float4 *anch
         *reinterpret_cast<uint2 *>(x + ((size_t)tile * kPX + q) * C0) = make_uint2(pack2(c[0], c[1]), pack2(c[2], c[3]));
     }
     if (lane == 0) anchor[tile] = make_float4(pa0, pa1, pa2, ra);
+    // with need0: whether the tile can be fitted at all (3 valid pixels), the only tiles whose
+    // proposals the seeded fit reads
+    return __popc(b0) + __popc(b1) >= 3;
+}
+
+template <bool kReset>
+__global__ void k_net_inputs(Geometry g, uint32_t *rimg0, bf16 *x0, float4 *anchor0, uint8_t *need0 = nullptr,
+                             DevStats *stats0 = nullptr) {
+    const int lane = threadIdx.x & 31;
+    const int tile = blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5);
+    const bool live = tile < g.NT;
+    const bool needed = live && net_inputs_tile<kReset>(g, rimg0, x0, anchor0, tile, lane);
+    // with need0: whether the tile can be fitted at all, the only tiles whose proposals the
+    // seeded fit reads; with stats0 the frame's count of them (frame blockIdx.y is slot blockIdx.y)
+    if (need0 && live && lane == 0) need0[(size_t)blockIdx.y * g.NT + tile] = needed ? 1 : 0;
+    if (need0 && stats0) {   // block-uniform condition: every thread reaches the barrier
+        const int cnt = __syncthreads_count(needed && lane == 0);
+        if (threadIdx.x == 0 && cnt) atomicAdd(&stats0[blockIdx.y].net_tiles, (unsigned long long)cnt);
+    }
+}
+
+// The pairs of tiles (2p, 2p + 1) of which at least one is needed, appended to pairs; *npairs
+// (zero before the launch) ends as their number.  A thread takes kPairsPer consecutive pairs;
+// a block scan orders a block's pairs, and one atomic per block places the block's run (runs
+// land in any order: a pair's outputs do not depend on where in the list it is).
+constexpr int kPairsThreads = 256, kPairsPer = 8;
+__global__ void __launch_bounds__(kPairsThreads) k_net_pairs(const uint8_t *need, long long T, uint32_t *pairs,
+                                                             uint32_t *npairs) {
+    __shared__ uint32_t s_warp[kPairsThreads / 32];
+    __shared__ uint32_t s_base;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const long long P = (T + 1) / 2;
+    const long long p0 = ((long long)blockIdx.x * kPairsThreads + tid) * kPairsPer;
+    uint32_t mask = 0;
+#pragma unroll
+    for (int k = 0; k < kPairsPer; k++) {
+        const long long p = p0 + k;
+        if (p < P && (need[2 * p] || (2 * p + 1 < T && need[2 * p + 1]))) mask |= 1u << k;
+    }
+    const uint32_t own = __popc(mask);
+    uint32_t x = own;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) s_warp[warp] = x;
+    __syncthreads();
+    uint32_t before = 0, total = 0;
+    for (int w = 0; w < kPairsThreads / 32; w++) {
+        before += w < warp ? s_warp[w] : 0u;
+        total += s_warp[w];
+    }
+    if (tid == 0) s_base = total ? atomicAdd(npairs, total) : 0u;
+    __syncthreads();
+    uint32_t pos = s_base + before + x - own;
+    for (uint32_t m = mask; m; m &= m - 1) pairs[pos++] = (uint32_t)(p0 + __ffs(m) - 1);
 }
 
 // ------------------------------------------------------------------ forward on tcgen05 --
@@ -409,7 +466,8 @@ __device__ __forceinline__ void group_sync(int slot) {
 
 template <bool kTrain>
 __global__ void __launch_bounds__(kTcThreads, 1) k_net_fwd_tc(NetDev nd, const bf16 *x, long long T, float *out,
-                                                              int *err, NetAct act) {
+                                                              int *err, NetAct act, const uint32_t *pairs = nullptr,
+                                                              const uint32_t *npairs = nullptr) {
     extern __shared__ __align__(1024) uint8_t sm[];
     uint8_t *sW1 = sm, *sW2 = sW1 + TW1, *sW3 = sW2 + TW2;
     uint8_t *sAct = sW3 + TW3;                                         // [slot][TACT]
@@ -466,6 +524,9 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_net_fwd_tc(NetDev nd, const b
     tc_after_sync();
     const uint32_t tmem = *tmem_slot;
     const long long G = gridDim.x;
+    // pair slots i = 0..NP-1: pair i itself, or with a pair list the pair pairs[i] (its count
+    // written by the kernel before this one)
+    const long long NP = pairs ? (long long)*npairs : (T + 1) / 2;
     if (warp == kTcEpiWarps) {
         // ---- MMA warp: one lane issues the convolutions of every slot, whichever is ready ----
         if (lane == 0) {
@@ -478,14 +539,14 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_net_fwd_tc(NetDev nd, const b
             for (int sl = 0; sl < kTcSlots; sl++) {
                 pa[sl] = blockIdx.x + sl * G;
                 layer[sl] = 0;
-                live += pa[sl] * 2 < T ? 1 : 0;
+                live += pa[sl] < NP ? 1 : 0;
             }
             long long idle = 0;
             while (live > 0 && !*(volatile int *)s_fail) {
                 bool progressed = false;
 #pragma unroll
                 for (int sl = 0; sl < kTcSlots; sl++) {
-                    if (pa[sl] * 2 >= T || !mbar_try(smem_u32(bar + 1 + kTcSlots + sl), (ph >> sl) & 1u)) continue;
+                    if (pa[sl] >= NP || !mbar_try(smem_u32(bar + 1 + kTcSlots + sl), (ph >> sl) & 1u)) continue;
                     ph ^= 1u << sl;
                     tc_after_sync();
                     const uint32_t base = smem_u32(sAct + sl * TACT);
@@ -497,7 +558,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_net_fwd_tc(NetDev nd, const b
                     if (++layer[sl] == 3) {
                         layer[sl] = 0;
                         pa[sl] += kTcSlots * G;
-                        if (pa[sl] * 2 >= T) live--;
+                        if (pa[sl] >= NP) live--;
                     }
                     progressed = true;
                 }
@@ -535,10 +596,13 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_net_fwd_tc(NetDev nd, const b
         float *gs = sG + sl * 2 * C3;
         // this thread's input pixel of pair pa (loaded one pair ahead, so that the global load's
         // latency overlaps the previous pair's layers)
-        auto load_in = [&](long long pa) {
-            const long long tile = pa * 2 + tl;
+        auto pair_of = [&](long long i) { return pairs ? (long long)pairs[i] : i; };
+        auto load_in = [&](long long i) {   // this thread's input pixel of pair slot i
             uint2 v = make_uint2(0u, 0u);
-            if (pa * 2 < T && tile < T) v = *reinterpret_cast<const uint2 *>(x + ((size_t)tile * kPX + py * 8 + px) * C0);
+            if (i < NP) {
+                const long long tile = pair_of(i) * 2 + tl;
+                if (tile < T) v = *reinterpret_cast<const uint2 *>(x + ((size_t)tile * kPX + py * 8 + px) * C0);
+            }
             return v;
         };
         // the pair's input: the pixel's 4 channels into chunk 6 (zero border), then conv1's im2col
@@ -562,10 +626,11 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_net_fwd_tc(NetDev nd, const b
             }
             handoff();
         };
-        const long long pa0 = blockIdx.x + sl * G;
-        if (pa0 * 2 < T) put_input(load_in(pa0));
-        uint2 vin = load_in(pa0 + kTcSlots * G);
-        for (long long pa = pa0; pa * 2 < T; pa += kTcSlots * G) {
+        const long long i0 = blockIdx.x + sl * G;
+        if (i0 < NP) put_input(load_in(i0));
+        uint2 vin = load_in(i0 + kTcSlots * G);
+        for (long long i = i0; i < NP; i += kTcSlots * G) {
+            const long long pa = pair_of(i);
             const long long tile = pa * 2 + tl;
 #pragma unroll 1
             for (int layer = 0; layer < 3; layer++) {
@@ -631,9 +696,9 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_net_fwd_tc(NetDev nd, const b
                 gs[t2 * C3 + 8 * c8 + x] = bfround(b1 * (1.0f / kPX));
             }
             group_sync(sl);   // pooled vectors complete; the activations are read, so the buffer is free
-            if ((pa + kTcSlots * G) * 2 < T) {   // the next pair's input goes to the MMA warp before this head
+            if (i + kTcSlots * G < NP) {   // the next pair's input goes to the MMA warp before this head
                 put_input(vin);
-                vin = load_in(pa + 2 * kTcSlots * G);
+                vin = load_in(i + 2 * kTcSlots * G);
             }
             if (quad < 2) {   // head: warp quad < 2 of the group takes tile quad of the pair
                 const int t2 = quad;
@@ -1009,14 +1074,19 @@ int grid_for(const lcc_net *net, int64_t tiles) {
 }
 
 // tcgen05 forward; with `train` it also keeps the activations the backward pass reads
-lcc_status forward_tc(lcc_net *net, const uint16_t *d_x, int64_t ntiles, float *d_out, bool train) {
+// With a pair list (pair_list, its count at *npairs on the device) only the listed pairs of
+// tiles are run; the grid is sized for all (ntiles + 1) / 2 pairs.
+lcc_status forward_tc(lcc_net *net, const uint16_t *d_x, int64_t ntiles, float *d_out, bool train,
+                      const uint32_t *pair_list = nullptr, const uint32_t *npairs = nullptr) {
     const int64_t pairs = (ntiles + 1) / 2;
     const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(pairs, net->sms));
     const bf16 *x = reinterpret_cast<const bf16 *>(d_x);
     if (train)
-        k_net_fwd_tc<true><<<grid, kTcThreads, kTcSmem, net->stream>>>(net->nd, x, ntiles, d_out, net->err, net->act);
+        k_net_fwd_tc<true><<<grid, kTcThreads, kTcSmem, net->stream>>>(net->nd, x, ntiles, d_out, net->err, net->act,
+                                                                        pair_list, npairs);
     else
-        k_net_fwd_tc<false><<<grid, kTcThreads, kTcSmem, net->stream>>>(net->nd, x, ntiles, d_out, net->err, net->act);
+        k_net_fwd_tc<false><<<grid, kTcThreads, kTcSmem, net->stream>>>(net->nd, x, ntiles, d_out, net->err, net->act,
+                                                                         pair_list, npairs);
     return cudaGetLastError() == cudaSuccess ? LCC_OK : LCC_ERR_CUDA;
 }
 
@@ -1044,19 +1114,29 @@ lcc_status backward(lcc_net *net, const uint16_t *d_x, const float *d_labels, in
 namespace lcc {
 namespace api {
 
-lcc_status net_inputs_slots(lcc_ctx *c, int nframes, uint16_t *d_x, float4 *d_anchor) {
+lcc_status net_inputs_slots(lcc_ctx *c, int nframes, uint16_t *d_x, float4 *d_anchor, uint8_t *d_need) {
     if (c->g.th != 8 || c->g.tw != 8 || nframes < 1 || nframes > c->slots) return LCC_ERR_UNSUPPORTED;
     const int wpb = 8;
     k_net_inputs<false><<<dim3((c->g.NT + wpb - 1) / wpb, nframes), wpb * 32, 0, c->stream>>>(
-        c->g, c->s.rimg, reinterpret_cast<bf16 *>(d_x), d_anchor);
+        c->g, c->s.rimg, reinterpret_cast<bf16 *>(d_x), d_anchor, d_need, c->s.stats);
     return cudaGetLastError() == cudaSuccess ? LCC_OK : LCC_ERR_CUDA;
 }
 
-lcc_status net_forward_on(lcc_net *net, const uint16_t *d_x, int64_t ntiles, float *d_out, cudaStream_t st) {
+lcc_status net_pairs(const uint8_t *d_need, int64_t ntiles, uint32_t *d_pairs, uint32_t *d_npairs, cudaStream_t st) {
+    if (ntiles <= 0) return LCC_OK;
+    LCC_CUDA(cudaMemsetAsync(d_npairs, 0, sizeof(uint32_t), st));
+    const int64_t per_block = (int64_t)kPairsThreads * kPairsPer, pairs = (ntiles + 1) / 2;
+    k_net_pairs<<<(unsigned)((pairs + per_block - 1) / per_block), kPairsThreads, 0, st>>>(d_need, ntiles, d_pairs,
+                                                                                            d_npairs);
+    return cudaGetLastError() == cudaSuccess ? LCC_OK : LCC_ERR_CUDA;
+}
+
+lcc_status net_forward_on(lcc_net *net, const uint16_t *d_x, int64_t ntiles, float *d_out, cudaStream_t st,
+                          const uint32_t *d_pairs, const uint32_t *d_npairs) {
     if (ntiles <= 0) return LCC_OK;
     cudaStream_t own = net->stream;
     net->stream = st;
-    const lcc_status s = forward_tc(net, d_x, ntiles, d_out, false);
+    const lcc_status s = forward_tc(net, d_x, ntiles, d_out, false, d_pairs, d_npairs);
     net->stream = own;
     return s;
 }

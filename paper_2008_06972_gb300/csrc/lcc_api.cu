@@ -131,6 +131,7 @@ void public_stats(const DevStats &d, lcc_stats *out) {
     out->raw = (int64_t)d.raw;
     out->bytes = d.bytes;
     out->tiles_temporal_cont = (int64_t)d.temporal_cont;
+    out->tiles_net = (int64_t)d.net_tiles;
 }
 
 lcc_status latched(lcc_ctx *c) {

@@ -104,9 +104,15 @@ lcc_status check_frames(lcc_ctx *c, int nframes, const float *const *d_pts, cons
                         uint8_t *const *d_out, const uint64_t *cap);
 // Net inputs (8x8 tiles) of the frames binned into slots 0..nframes-1 of c, on c's stream; the
 // range images are kept for the encode that follows.  Frame f's tiles are rows f*NT.. of d_x.
-lcc_status net_inputs_slots(lcc_ctx *c, int nframes, uint16_t *d_x, float4 *d_anchor);
-// Proposal-net inference on stream st instead of the net's own stream.
-lcc_status net_forward_on(lcc_net *net, const uint16_t *d_x, int64_t ntiles, float *d_out, cudaStream_t st);
+// d_need (may be NULL): per tile, 1 if it has the 3 valid pixels a fit needs.
+lcc_status net_inputs_slots(lcc_ctx *c, int nframes, uint16_t *d_x, float4 *d_anchor, uint8_t *d_need = nullptr);
+// The pairs of tiles with a needed tile (d_pairs, (ntiles + 1) / 2 entries; their count at
+// *d_npairs), on stream st.
+lcc_status net_pairs(const uint8_t *d_need, int64_t ntiles, uint32_t *d_pairs, uint32_t *d_npairs, cudaStream_t st);
+// Proposal-net inference on stream st instead of the net's own stream; with a pair list only the
+// listed pairs' outputs are written.
+lcc_status net_forward_on(lcc_net *net, const uint16_t *d_x, int64_t ntiles, float *d_out, cudaStream_t st,
+                          const uint32_t *d_pairs = nullptr, const uint32_t *d_npairs = nullptr);
 // Reads and clears the net's bounded-wait error flag (synchronous): LCC_ERR_TIMEOUT if it was set.
 lcc_status net_latched(lcc_net *net);
 

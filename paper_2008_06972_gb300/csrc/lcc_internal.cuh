@@ -91,6 +91,7 @@ struct DevStats {
     unsigned long long rounds[8];
     unsigned long long borderline, cand, fitted, raw;
     unsigned long long bytes;
+    unsigned long long net_tiles;   // tiles the proposal net must cover (3 valid pixels)
 };
 
 // Decoder per-tile state.

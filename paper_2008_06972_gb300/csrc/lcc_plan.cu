@@ -44,7 +44,10 @@ struct PlanClass {
     bool seeded = false;
     uint16_t *x = nullptr;           // net inputs of one chunk: slots x NT x 64 pixels x 4 bf16
     float4 *anchor = nullptr;        // slots x NT tile anchors
-    float *prop = nullptr;           // slots x NT x 5 proposals
+    float *prop = nullptr;           // slots x NT x 5 proposals (written for the listed pairs only)
+    uint8_t *need = nullptr;         // slots x NT: the tile has the 3 valid pixels a fit needs
+    uint32_t *pairs = nullptr;       // pairs of tiles with a needed tile, and their count
+    uint32_t *npairs = nullptr;
     DevStats *stats = nullptr;       // per frame of the last encode, in enqueue order (keys, then P frames)
 };
 
@@ -223,15 +226,18 @@ lcc_status enqueue_class(PlanClass &pc, lcc_net *net, float skip_logit, int64_t 
             lcc_status st = bin_frames(c, m, slots, pts, n);
             if (st != LCC_OK) return st;
             if (seeded) {
+                // the net runs only on pairs of tiles with a tile that can be fitted: the seeded fit
+                // reads no other tile's proposal (empty sky and sparse tiles are often half a frame)
                 int pi = prof_begin(c, 14);
-                st = net_inputs_slots(c, m, pc.x, pc.anchor);
+                st = net_inputs_slots(c, m, pc.x, pc.anchor, pc.need);
+                if (st == LCC_OK) st = net_pairs(pc.need, (int64_t)m * NT, pc.pairs, pc.npairs, c->stream);
                 prof_end(c, pi);
                 if (st != LCC_OK) return st;
                 pi = prof_begin(c, 15);
-                st = net_forward_on(net, pc.x, (int64_t)m * NT, pc.prop, c->stream);
+                st = net_forward_on(net, pc.x, (int64_t)m * NT, pc.prop, c->stream, pc.pairs, pc.npairs);
                 prof_end(c, pi);
                 if (st != LCC_OK) return st;
-                *launches += 2;
+                *launches += 3;
             }
             st = encode_batch(c, kind, m, slots, out, cap, kind ? poses.data() : nullptr, kind ? kf : nullptr,
                               kind ? nullptr : kfo, nb, seeded ? props : nullptr, skip_logit);
@@ -281,6 +287,9 @@ void release(lcc_plan *p) {
         cudaFree(pc.x);
         cudaFree(pc.anchor);
         cudaFree(pc.prop);
+        cudaFree(pc.need);
+        cudaFree(pc.pairs);
+        cudaFree(pc.npairs);
         cudaFree(pc.stats);
     }
     if (p->fork) cudaEventDestroy(p->fork);
@@ -363,13 +372,22 @@ lcc_status lcc_plan_set_proposals(lcc_plan *p, lcc_net *net, float skip_logit) {
                 const size_t tiles = (size_t)pc.ctx->slots * pc.ctx->g.NT;
                 if (cudaMalloc(&pc.x, tiles * 64 * 4 * sizeof(uint16_t)) != cudaSuccess ||
                     cudaMalloc(&pc.anchor, tiles * sizeof(float4)) != cudaSuccess ||
-                    cudaMalloc(&pc.prop, tiles * 5 * sizeof(float)) != cudaSuccess) {
+                    cudaMalloc(&pc.prop, tiles * 5 * sizeof(float)) != cudaSuccess ||
+                    cudaMalloc(&pc.need, tiles) != cudaSuccess ||
+                    cudaMalloc(&pc.pairs, (tiles + 1) / 2 * sizeof(uint32_t)) != cudaSuccess ||
+                    cudaMalloc(&pc.npairs, sizeof(uint32_t)) != cudaSuccess) {
                     cudaFree(pc.x);
                     cudaFree(pc.anchor);
                     cudaFree(pc.prop);
+                    cudaFree(pc.need);
+                    cudaFree(pc.pairs);
+                    cudaFree(pc.npairs);
                     pc.x = nullptr;
                     pc.anchor = nullptr;
                     pc.prop = nullptr;
+                    pc.need = nullptr;
+                    pc.pairs = nullptr;
+                    pc.npairs = nullptr;
                     return LCC_ERR_CUDA;
                 }
             }

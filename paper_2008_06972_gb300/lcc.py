@@ -47,7 +47,7 @@ class lcc_stats(ctypes.Structure):
                                                "tiles_run_cont", "tiles_temporal")] + \
                [("fit_rounds", ctypes.c_int64 * 8), ("tiles_borderline", ctypes.c_int64),
                 ("cand", ctypes.c_int64), ("fitted", ctypes.c_int64), ("raw", ctypes.c_int64),
-                ("bytes", ctypes.c_uint64), ("tiles_temporal_cont", ctypes.c_int64)]
+                ("bytes", ctypes.c_uint64), ("tiles_temporal_cont", ctypes.c_int64), ("tiles_net", ctypes.c_int64)]
 
 
 class lcc_seq_desc(ctypes.Structure):
