@@ -89,6 +89,9 @@ def parse():
                     help="profiling case: the proposal net's forward over --net-tiles seeded tiles, --steps calls after "
                          "one warm-up call, nothing else (for ncu)")
     ap.add_argument("--net-tiles", type=int, default=98304)
+    ap.add_argument("--profile-train", action="store_true",
+                    help="profiling case: --steps training steps of the proposal net on 4096 seeded tiles after one "
+                         "warm-up step, nothing else (for ncu)")
     return ap.parse_args()
 
 
@@ -1398,6 +1401,35 @@ def run_profile_net(args, stream):
     return {"profile_net": True, "tiles": T, "ms_per_call": ms, "tflops": flops / (ms * 1e-3) / 1e12}
 
 
+def run_profile_train(args, stream):
+    """Training steps of the proposal net alone (tcgen05 forward with saved activations, head
+    backward, input gradients, weight gradients, Adam) on 4096 seeded tiles with random labels:
+    one warm-up step and --steps timed steps, the case the training summary under profiles/ is
+    taken on."""
+    import torch
+    from paper_2008_06972_gb300 import lcc
+    from paper_2008_06972_gb300 import train as TR
+    T = 4096
+    net = lcc.Net(TR.he_uniform_params(4), max_tiles=T, stream=stream)
+    g = torch.Generator(device="cpu").manual_seed(1)
+    x = (torch.randn((T, 64, 4), generator=g) * 0.3).to(torch.bfloat16).view(torch.int16).cuda()
+    y = torch.zeros((T, 5), dtype=torch.float32)
+    y[:, 0] = (torch.rand(T, generator=g) < 0.5).float()
+    n = torch.randn((T, 3), generator=g)
+    y[:, 1:4] = n / n.norm(dim=1, keepdim=True) * y[:, :1]
+    y = y.cuda()
+    net.train_step(x, y, T, 1e-3, 1)
+    assert net.sync() == lcc.OK
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for k in range(args.steps):
+        net.train_step(x, y, T, 1e-3, k + 2)
+    b.record(stream)
+    assert net.sync() == lcc.OK
+    torch.cuda.synchronize()
+    return {"profile_train": True, "tiles": T, "ms_per_step": a.elapsed_time(b) / args.steps}
+
+
 def run_hdl64(args, stream):
     """One synthetic HDL-64E sequence (10 frames of 64x2048, the middle one the key frame) encoded
     per call by lcc_encode_sequence: throughput (L2 flushed between steps), kernel times, decode,
@@ -1628,6 +1660,9 @@ def main():
         return
     if args.profile_net:
         print(json.dumps(run_profile_net(args, stream)), flush=True)
+        return
+    if args.profile_train:
+        print(json.dumps(run_profile_train(args, stream)), flush=True)
         return
     line = run_cfg5(args, stream, rank, world, dist)
     if world == 1:

@@ -42,7 +42,6 @@ constexpr int C0 = 4, C1 = 32, C2 = 64, C3 = 64, HID = 32, NOUT = 5;
 constexpr int XS = 8;                         // padded channel stride of the input copy
 constexpr int K1 = 48;                        // conv1 on tcgen05 as one contraction: 9 taps x 4 channels, 3 k-steps
 constexpr int A1S = C1 + 8, A2S = C2 + 8;     // padded channel strides (bank spread)
-constexpr int BTS = 9 * 64 + 8;               // input-gradient weight rows (9 taps x 64 channels + bank pad)
 constexpr int kNetWarps = 4;
 
 // offsets of the flat parameter vector: W1[32,4,3,3] b1 W2[64,32,3,3] b2 W3[64,64,3,3] b3 F1[32,64] c1 F2[5,32] c2
@@ -54,9 +53,9 @@ static_assert(NPARAM == 58853, "parameter count");
 // device copies of the weights in the layouts the kernels read
 struct NetDev {
     const float *theta;                      // fp32 master parameters
-    bf16 *B2t, *B3t;                         // input-gradient GEMM B: [ci][k = tap*cout + co]
     float *F1b, *F2b;                        // head weights rounded to bf16 values
     bf16 *T1, *T2, *T3;                      // tcgen05 B operands: [tap][ci/8][cout][8], core-matrix order
+    bf16 *TB3, *TB2;                         // tcgen05 B operands of the input gradients: [tap][co/8][ci][8]
 };
 
 struct NetAct {                              // per-tile training activations
@@ -67,10 +66,6 @@ struct NetAct {                              // per-tile training activations
 };
 
 __device__ __forceinline__ uint32_t ld32(const bf16 *p) { return *reinterpret_cast<const uint32_t *>(p); }
-__device__ __forceinline__ void st32(bf16 *p, float a, float b) {
-    __nv_bfloat162 v = __floats2bfloat162_rn(a, b);
-    *reinterpret_cast<__nv_bfloat162 *>(p) = v;
-}
 __device__ __forceinline__ float bfround(float x) { return __bfloat162float(__float2bfloat16_rn(x)); }
 __device__ __forceinline__ uint32_t pack2(bf16 lo, bf16 hi) {
     return (uint32_t)__bfloat16_as_ushort(lo) | ((uint32_t)__bfloat16_as_ushort(hi) << 16);
@@ -85,68 +80,13 @@ __device__ __forceinline__ void mma_bf16(float c[4], uint32_t a0, uint32_t a1, u
         : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
 }
 
-// One warp: acc[m][n] (+)= conv of the padded tile `ap` (stride AS) with B rows
-// [COUT][9*CIN (+pad)] (stride BS).  Row block m covers pixels 16m..16m+15,
-// i.e. tile rows 2m and 2m+1; lane (g, t) holds rows g and g+8 of each block.
-// MIRROR reads tap (ky, kx) at offset (2-ky, 2-kx): the input-gradient form.
-template <int CIN, int COUT, int AS, int BS, bool MIRROR>
-__device__ __forceinline__ void conv_tile(const bf16 *ap, const bf16 *B, float (&acc)[4][COUT / 8][4]) {
-    const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
-#pragma unroll 1
-    for (int tap = 0; tap < 9; tap++) {
-        const int ky = tap / 3, kx = tap % 3;
-        const int oy = MIRROR ? 2 - ky : ky, ox = MIRROR ? 2 - kx : kx;
-#pragma unroll 1
-        for (int c0 = 0; c0 < CIN; c0 += 16) {
-            uint32_t a[4][4];
-#pragma unroll
-            for (int m = 0; m < 4; m++) {
-                const bf16 *r0 = ap + ((2 * m + oy) * 10 + g + ox) * AS + c0 + 2 * t;
-                const bf16 *r1 = r0 + 10 * AS;
-                a[m][0] = ld32(r0);
-                a[m][1] = ld32(r1);
-                a[m][2] = ld32(r0 + 8);
-                a[m][3] = ld32(r1 + 8);
-            }
-#pragma unroll
-            for (int n = 0; n < COUT / 8; n++) {
-                const bf16 *bp = B + (n * 8 + g) * BS + tap * CIN + c0 + 2 * t;
-                const uint32_t b0 = ld32(bp), b1 = ld32(bp + 8);
-#pragma unroll
-                for (int m = 0; m < 4; m++) mma_bf16(acc[m][n], a[m][0], a[m][1], a[m][2], a[m][3], b0, b1);
-            }
-        }
-    }
-}
-
-template <int COUT>
-__device__ __forceinline__ void zero_acc(float (&acc)[4][COUT / 8][4]) {
-#pragma unroll
-    for (int m = 0; m < 4; m++)
-#pragma unroll
-        for (int n = 0; n < COUT / 8; n++) acc[m][n][0] = acc[m][n][1] = acc[m][n][2] = acc[m][n][3] = 0.f;
-}
-
 // ------------------------------------------------------------------ weights --
 
 __global__ void k_net_prep(NetDev nd) {
     const float *th = nd.theta;
-    const int n2t = C1 * BTS, n3t = C2 * BTS;
-    const int total = n2t + n3t + HID * C3 + NOUT * HID;
+    const int total = HID * C3 + NOUT * HID;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < total; i += gridDim.x * blockDim.x) {
         int j = i;
-        if (j < n2t) {   // conv2 input gradient: rows ci (32), k = tap*64 + co
-            const int ci = j / BTS, k = j % BTS;
-            nd.B2t[j] = __float2bfloat16_rn(k < 9 * C2 ? th[OW2 + (k % C2) * 9 * C1 + ci * 9 + k / C2] : 0.f);
-            continue;
-        }
-        j -= n2t;
-        if (j < n3t) {   // conv3 input gradient: rows ci (64), k = tap*64 + co
-            const int ci = j / BTS, k = j % BTS;
-            nd.B3t[j] = __float2bfloat16_rn(k < 9 * C3 ? th[OW3 + (k % C3) * 9 * C2 + ci * 9 + k / C3] : 0.f);
-            continue;
-        }
-        j -= n3t;
         if (j < HID * C3) {
             nd.F1b[j] = bfround(th[OF1 + j]);
             continue;
@@ -157,8 +97,10 @@ __global__ void k_net_prep(NetDev nd) {
     // tcgen05 layouts: conv2/conv3 element (tap, c8, co, e) = W[co][ci = 8 c8 + e][tap]; conv1 is
     // one contraction over k = tap * 4 + ci (im2col, 36 of K1 = 48 used): element (c8, co, e) =
     // W1[co][ci][tap] for k = 8 c8 + e
+    // the input gradients' B operands: element (tap, c8, ci, e) = W[co = 8 c8 + e][ci][8 - tap]
     const int m1 = (K1 / 8) * C1 * 8, m2 = 9 * (C1 / 8) * C2 * 8, m3 = 9 * (C2 / 8) * C3 * 8;
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < m1 + m2 + m3; i += gridDim.x * blockDim.x) {
+    const int m4 = 9 * (C3 / 8) * C2 * 8, m5 = 9 * (C2 / 8) * C1 * 8;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < m1 + m2 + m3 + m4 + m5; i += gridDim.x * blockDim.x) {
         int j = i;
         if (j < m1) {
             const int e = j % 8, co = (j / 8) % C1, c8 = j / (8 * C1);
@@ -173,8 +115,20 @@ __global__ void k_net_prep(NetDev nd) {
             continue;
         }
         j -= m2;
-        const int e = j % 8, co = (j / 8) % C3, c8 = (j / (8 * C3)) % (C2 / 8), tap = j / (8 * C3 * (C2 / 8));
-        nd.T3[j] = __float2bfloat16_rn(th[OW3 + co * C2 * 9 + (8 * c8 + e) * 9 + tap]);
+        if (j < m3) {
+            const int e = j % 8, co = (j / 8) % C3, c8 = (j / (8 * C3)) % (C2 / 8), tap = j / (8 * C3 * (C2 / 8));
+            nd.T3[j] = __float2bfloat16_rn(th[OW3 + co * C2 * 9 + (8 * c8 + e) * 9 + tap]);
+            continue;
+        }
+        j -= m3;
+        if (j < m4) {
+            const int e = j % 8, ci = (j / 8) % C2, c8 = (j / (8 * C2)) % (C3 / 8), tap = j / (8 * C2 * (C3 / 8));
+            nd.TB3[j] = __float2bfloat16_rn(th[OW3 + (8 * c8 + e) * C2 * 9 + ci * 9 + (8 - tap)]);
+            continue;
+        }
+        j -= m4;
+        const int e = j % 8, ci = (j / 8) % C1, c8 = (j / (8 * C1)) % (C2 / 8), tap = j / (8 * C1 * (C2 / 8));
+        nd.TB2[j] = __float2bfloat16_rn(th[OW2 + (8 * c8 + e) * C1 * 9 + ci * 9 + (8 - tap)]);
     }
 }
 
@@ -365,17 +319,6 @@ __device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity, long l
         if (done) return true;
     }
     return false;
-}
-
-__device__ __forceinline__ void tc_ld16(uint32_t taddr, float (&v)[16]) {
-    uint32_t r[16];
-    asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];\n"
-        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
-        : "r"(taddr));
-#pragma unroll
-    for (int i = 0; i < 16; i++) v[i] = __uint_as_float(r[i]);
 }
 
 __device__ __forceinline__ void tc_ld8(uint32_t taddr, float (&v)[8]) {
@@ -820,129 +763,227 @@ __global__ void __launch_bounds__(kNetWarps * 32) k_net_head_bwd(NetDev nd, cons
     if (lane == 0 && lsum != 0.f) atomicAdd(loss, lsum * invT);
 }
 
-// ------------------------------------------------------------------ backward: convolution inputs --
+// ------------------------------------------------------------------ backward: input gradients on tcgen05 --
+//
+// The input gradient of a 3x3 convolution is a 3x3 convolution of its output gradient with the
+// taps mirrored and the channel roles swapped: da[p][ci] = sum over taps and co of
+// dz[p + off(tap)][co] * W[co][ci][8 - tap].  So it runs on the forward's machinery: per pair of
+// tiles the output gradient dz3 (the pooled gradient through the last ReLU) is written into the
+// padded copy, conv3' (B: [tap][co/8][ci][8] = W3[co][ci][8 - tap]) accumulates da2 in TMEM,
+// the epilogue applies conv2's ReLU mask into dz2 (the next input, and its pixel-contiguous global
+// copy for the weight gradients), conv2' gives da1 and the epilogue dz1.  Bias gradients are the
+// column sums of dz3, dz2 and dz1, reduced over each warp's rows by shuffles into shared sums.
+constexpr int TWB3 = 9 * (C3 / 8) * C2 * 16, TWB2 = 9 * (C2 / 8) * C1 * 16;
+constexpr int NDB = C3 + C2 + C1;   // bias-gradient sums per slot: db3, db2, db1
+constexpr size_t kTcBwdSmem = (size_t)TWB3 + TWB2 + kTcSlots * (size_t)TACT + kTcSlots * NDB * 4 + 128;
+static_assert(kTcBwdSmem <= 227 * 1024, "shared memory of the tcgen05 input-gradient kernel");
 
-constexpr size_t kBwdWeightBytes = sizeof(bf16) * (size_t)(C3 * BTS + C1 * BTS);
-constexpr size_t kBwdWarpBytes = sizeof(bf16) * (size_t)(100 * A2S);
-constexpr size_t kBwdSmem = kBwdWeightBytes + kNetWarps * kBwdWarpBytes;
+// Sum over the warp's 32 rows of 8 channel values (one per lane and channel): a reduce-scatter
+// leaves the full sum of channel 4 [lane & 16] + 2 [lane & 8] + [lane & 4] on lanes whose two low
+// bits are zero, which add it to sums[c0 + that channel].
+__device__ __forceinline__ void colsum8(const float (&v)[8], float *sums, int c0, int lane) {
+    const bool h16 = lane & 16, h8 = lane & 8, h4 = lane & 4;
+    float b4[4], b2[2];
+#pragma unroll
+    for (int i = 0; i < 4; i++)
+        b4[i] = (h16 ? v[i + 4] : v[i]) + __shfl_xor_sync(0xffffffffu, h16 ? v[i] : v[i + 4], 16);
+#pragma unroll
+    for (int i = 0; i < 2; i++)
+        b2[i] = (h8 ? b4[i + 2] : b4[i]) + __shfl_xor_sync(0xffffffffu, h8 ? b4[i] : b4[i + 2], 8);
+    float b1 = (h4 ? b2[1] : b2[0]) + __shfl_xor_sync(0xffffffffu, h4 ? b2[0] : b2[1], 4);
+    b1 += __shfl_xor_sync(0xffffffffu, b1, 2);
+    b1 += __shfl_xor_sync(0xffffffffu, b1, 1);
+    if ((lane & 3) == 0) atomicAdd(sums + c0 + (h16 ? 4 : 0) + (h8 ? 2 : 0) + (h4 ? 1 : 0), b1);
+}
 
-// column sums over the 64 pixel rows of an accumulator set (bias gradients);
-// lanes with g == 0 end up holding the sums of channels 8n + 2t + {0, 1}
-template <int COUT>
-__device__ __forceinline__ void colsum_add(const float (&v)[4][COUT / 8][4], float (&bsum)[COUT / 8][2]) {
-#pragma unroll
-    for (int n = 0; n < COUT / 8; n++) {
-        float s0 = 0.f, s1 = 0.f;
-#pragma unroll
-        for (int m = 0; m < 4; m++) {
-            s0 += v[m][n][0] + v[m][n][2];
-            s1 += v[m][n][1] + v[m][n][3];
-        }
-#pragma unroll
-        for (int off = 4; off < 32; off <<= 1) {
-            s0 += __shfl_xor_sync(0xffffffffu, s0, off);
-            s1 += __shfl_xor_sync(0xffffffffu, s1, off);
-        }
-        bsum[n][0] += s0;
-        bsum[n][1] += s1;
+__global__ void __launch_bounds__(kTcThreads, 1) k_net_bwd_tc(NetDev nd, long long T, NetAct act, float *grad, int *err) {
+    extern __shared__ __align__(1024) uint8_t sm[];
+    uint8_t *sWB3 = sm, *sWB2 = sWB3 + TWB3;
+    uint8_t *sAct = sWB2 + TWB2;                                       // [slot][TACT]
+    float *sDB = reinterpret_cast<float *>(sAct + kTcSlots * TACT);    // [slot][NDB]
+    // barriers: [0] weights, [1 + s] layer done (tcgen05.commit), [1 + kTcSlots + s] layer input ready
+    uint64_t *bar = reinterpret_cast<uint64_t *>(sDB + kTcSlots * NDB);
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bar + 1 + 2 * kTcSlots);
+    int *s_fail = reinterpret_cast<int *>(tmem_slot + 1);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    if (tid == 0) {
+        for (int i = 0; i < 1 + kTcSlots; i++)
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(bar + i)) : "memory");
+        for (int i = 1 + kTcSlots; i < 1 + 2 * kTcSlots; i++)
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 4;\n" ::"r"(smem_u32(bar + i)) : "memory");
+        *s_fail = 0;
     }
-}
-
-// dz = bf16(da * [a > 0]) from an accumulator set: into the padded copy (for the next
-// input-gradient convolution), the pixel-contiguous global copy, and back into acc.
-template <int C, bool kPad>
-__device__ __forceinline__ void relu_grad(float (&acc)[4][C / 8][4], const bf16 *a, bf16 *pad, bf16 *dzt) {
-    const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
-#pragma unroll
-    for (int m = 0; m < 4; m++)
-#pragma unroll
-        for (int n = 0; n < C / 8; n++) {
-            const int c = n * 8 + 2 * t;
-#pragma unroll
-            for (int h = 0; h < 2; h++) {
-                const int p = (2 * m + h) * 8 + g;
-                const __nv_bfloat162 av = *reinterpret_cast<const __nv_bfloat162 *>(a + p * C + c);
-                const float d0 = bfround(__bfloat162float(av.x) > 0.f ? acc[m][n][2 * h] : 0.f);
-                const float d1 = bfround(__bfloat162float(av.y) > 0.f ? acc[m][n][2 * h + 1] : 0.f);
-                acc[m][n][2 * h] = d0;
-                acc[m][n][2 * h + 1] = d1;
-                if (kPad) st32(pad + ((2 * m + h + 1) * 10 + g + 1) * A2S + c, d0, d1);
-                dzt[c * kPX + p] = __float2bfloat16_rn(d0);
-                dzt[(c + 1) * kPX + p] = __float2bfloat16_rn(d1);
-            }
-        }
-}
-
-__global__ void __launch_bounds__(kNetWarps * 32, 1) k_net_conv_bwd(NetDev nd, long long T, NetAct act, float *grad) {
-    extern __shared__ __align__(16) uint8_t sm[];
-    bf16 *sB3t = reinterpret_cast<bf16 *>(sm);
-    bf16 *sB2t = sB3t + C3 * BTS;
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    bf16 *dp = reinterpret_cast<bf16 *>(sm + kBwdWeightBytes + warp * kBwdWarpBytes);
     {
-        const uint4 *s3 = reinterpret_cast<const uint4 *>(nd.B3t), *s2 = reinterpret_cast<const uint4 *>(nd.B2t);
-        uint4 *d3 = reinterpret_cast<uint4 *>(sB3t), *d2 = reinterpret_cast<uint4 *>(sB2t);
-        for (int i = threadIdx.x; i < C3 * BTS / 8; i += blockDim.x) d3[i] = s3[i];
-        for (int i = threadIdx.x; i < C1 * BTS / 8; i += blockDim.x) d2[i] = s2[i];
-        uint32_t *z = reinterpret_cast<uint32_t *>(dp);
-        for (int i = lane; i < (int)(kBwdWarpBytes / 4); i += 32) z[i] = 0u;
+        uint4 *z = reinterpret_cast<uint4 *>(sAct);
+        for (int i = tid; i < kTcSlots * TACT / 16; i += blockDim.x) z[i] = make_uint4(0u, 0u, 0u, 0u);
+        for (int i = tid; i < kTcSlots * NDB; i += blockDim.x) sDB[i] = 0.f;
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(smem_u32(tmem_slot)),
+                     "r"(kTmemCols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::: "memory");
     }
     __syncthreads();
-    float db3[C3 / 8][2], db2[C2 / 8][2], db1[C1 / 8][2];
-#pragma unroll
-    for (int n = 0; n < C3 / 8; n++) db3[n][0] = db3[n][1] = db2[n][0] = db2[n][1] = 0.f;
-#pragma unroll
-    for (int n = 0; n < C1 / 8; n++) db1[n][0] = db1[n][1] = 0.f;
-    const int g = lane >> 2, t = lane & 3;
-    for (long long tile = (long long)blockIdx.x * kNetWarps + warp; tile < T; tile += (long long)gridDim.x * kNetWarps) {
-        const bf16 *a1 = act.a1 + (size_t)tile * kPX * C1;
-        const bf16 *a2 = act.a2 + (size_t)tile * kPX * C2;
-        const bf16 *a3 = act.a3 + (size_t)tile * kPX * C3;
-        const float *da3 = act.da3c + (size_t)tile * C3;
-        {   // dz3 from the pooled gradient and the ReLU mask
-            float acc[4][C3 / 8][4];
-#pragma unroll
-            for (int m = 0; m < 4; m++)
-#pragma unroll
-                for (int n = 0; n < C3 / 8; n++) {
-                    const int c = n * 8 + 2 * t;
-                    acc[m][n][0] = acc[m][n][2] = da3[c];
-                    acc[m][n][1] = acc[m][n][3] = da3[c + 1];
-                }
-            relu_grad<C3, true>(acc, a3, dp, act.dz3t + (size_t)tile * C3 * kPX);
-            colsum_add<C3>(acc, db3);
-        }
-        __syncwarp();
-        {   // da2 = conv3 input gradient; dz2
-            float acc[4][C2 / 8][4];
-            zero_acc<C2>(acc);
-            conv_tile<C3, C2, A2S, BTS, true>(dp, sB3t, acc);
-            __syncwarp();
-            relu_grad<C2, true>(acc, a2, dp, act.dz2t + (size_t)tile * C2 * kPX);
-            colsum_add<C2>(acc, db2);
-        }
-        __syncwarp();
-        {   // da1 = conv2 input gradient; dz1
-            float acc[4][C1 / 8][4];
-            zero_acc<C1>(acc);
-            conv_tile<C2, C1, A2S, BTS, true>(dp, sB2t, acc);
-            relu_grad<C1, false>(acc, a1, nullptr, act.dz1t + (size_t)tile * C1 * kPX);
-            colsum_add<C1>(acc, db1);
-        }
-        __syncwarp();
+    if (tid == 0) {   // weights by the TMA engine, counted on barrier 0
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_u32(bar)),
+                     "r"((uint32_t)(TWB3 + TWB2))
+                     : "memory");
+        bulk_g2s(smem_u32(sWB3), nd.TB3, TWB3, smem_u32(bar));
+        bulk_g2s(smem_u32(sWB2), nd.TB2, TWB2, smem_u32(bar));
     }
-    if (g == 0) {
+    if (!mbar_wait(smem_u32(bar), 0)) {
+        atomicExch(s_fail, 1);
+        if (err) atomicExch(err, 1);
+    }
+    proxy_fence();
+    tc_before_sync();
+    __syncthreads();
+    tc_after_sync();
+    const uint32_t tmem = *tmem_slot;
+    const long long G = gridDim.x, NP = (T + 1) / 2;
+    if (warp == kTcEpiWarps) {
+        // ---- MMA warp: conv3' then conv2' for every slot, whichever is ready ----
+        if (lane == 0) {
+            const uint32_t aWB3 = smem_u32(sWB3), aWB2 = smem_u32(sWB2);
+            long long pa[kTcSlots];
+            int layer[kTcSlots];
+            uint32_t ph = 0u;
+            int live = 0;
 #pragma unroll
-        for (int n = 0; n < C3 / 8; n++)
-#pragma unroll
-            for (int j = 0; j < 2; j++) {
-                atomicAdd(grad + OB3 + n * 8 + 2 * t + j, db3[n][j]);
-                atomicAdd(grad + OB2 + n * 8 + 2 * t + j, db2[n][j]);
+            for (int sl = 0; sl < kTcSlots; sl++) {
+                pa[sl] = blockIdx.x + sl * G;
+                layer[sl] = 0;
+                live += pa[sl] < NP ? 1 : 0;
             }
+            long long idle = 0;
+            while (live > 0 && !*(volatile int *)s_fail) {
+                bool progressed = false;
 #pragma unroll
-        for (int n = 0; n < C1 / 8; n++)
+                for (int sl = 0; sl < kTcSlots; sl++) {
+                    if (pa[sl] >= NP || !mbar_try(smem_u32(bar + 1 + kTcSlots + sl), (ph >> sl) & 1u)) continue;
+                    ph ^= 1u << sl;
+                    tc_after_sync();
+                    const uint32_t base = smem_u32(sAct + sl * TACT);
+                    const uint32_t d = tmem + (uint32_t)(sl * 64);
+                    if (layer[sl] == 0) tc_conv<C3, C2>(d, base, aWB3);
+                    else tc_conv<C2, C1>(d, base, aWB2);
+                    tc_commit(smem_u32(bar + 1 + sl));
+                    if (++layer[sl] == 2) {
+                        layer[sl] = 0;
+                        pa[sl] += kTcSlots * G;
+                        if (pa[sl] >= NP) live--;
+                    }
+                    progressed = true;
+                }
+                if (!progressed) __nanosleep(20);
+                idle = progressed ? 0 : idle + 1;
+                if (idle > kSpinLimit) {
+                    atomicExch(s_fail, 1);
+                    if (err) atomicExch(err, 1);
+                }
+            }
+        }
+        __syncwarp();
+    } else {
+        // ---- epilogue group of slot sl: row = 32 quad + lane -> (y, tile, x) ----
+        const int sl = warp >> 2, quad = warp & 3;
+        const int row = quad * 32 + lane, grp = row >> 3, px = row & 7, py = grp >> 1, tl = grp & 1;
+        const int pix = py * 8 + px;
+        uint8_t *buf = sAct + sl * TACT;
+        float *db = sDB + sl * NDB;
+        const uint32_t bar_done = smem_u32(bar + 1 + sl), bar_in = smem_u32(bar + 1 + kTcSlots + sl);
+        uint32_t ph = 0u;
+        auto wait = [&](uint32_t mbar, uint32_t parity) {
+            if (*(volatile int *)s_fail) return;
+            if (!mbar_wait(mbar, parity)) {
+                atomicExch(s_fail, 1);
+                if (err) atomicExch(err, 1);
+            }
+        };
+        auto handoff = [&]() {
+            proxy_fence();
+            tc_before_sync();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(bar_in);
+        };
+        const uint32_t trow = tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(sl * 64);
+        // dz = bf16(da * [a > 0]) for 8 channels of this pixel: into the padded copy (when the next
+        // convolution reads it), the pixel-contiguous global copy, and the bias sums
+        auto emit = [&](const float (&da)[8], const bf16 *a, int C, int c0, bool in, bool pad, bf16 *dzt, float *sums) {
+            uint4 av = make_uint4(0u, 0u, 0u, 0u);
+            if (in) av = *reinterpret_cast<const uint4 *>(a + c0);
+            const uint32_t aw[4] = {av.x, av.y, av.z, av.w};
+            float d[8];
+            uint32_t w[4];
 #pragma unroll
-            for (int j = 0; j < 2; j++) atomicAdd(grad + OB1 + n * 8 + 2 * t + j, db1[n][j]);
+            for (int q = 0; q < 4; q++) {
+                const float lo = __uint_as_float(aw[q] << 16), hi = __uint_as_float(aw[q] & 0xFFFF0000u);
+                d[2 * q] = bfround(in && lo > 0.f ? da[2 * q] : 0.f);
+                d[2 * q + 1] = bfround(in && hi > 0.f ? da[2 * q + 1] : 0.f);
+                const __nv_bfloat162 b2 = __floats2bfloat162_rn(d[2 * q], d[2 * q + 1]);
+                w[q] = *reinterpret_cast<const uint32_t *>(&b2);
+            }
+            if (pad) *reinterpret_cast<uint4 *>(buf + tpos(c0 / 8, py + 1, tl, px + 1)) = make_uint4(w[0], w[1], w[2], w[3]);
+            if (in)
+#pragma unroll
+                for (int i = 0; i < 8; i++) dzt[(size_t)(c0 + i) * kPX + pix] = __float2bfloat16_rn(d[i]);
+            colsum8(d, sums, c0, lane);
+            (void)C;
+        };
+        for (long long pa = blockIdx.x + sl * G; pa < NP; pa += kTcSlots * G) {
+            const long long tile = pa * 2 + tl;
+            const bool in = tile < T;
+            const size_t tp = (size_t)(in ? tile : 0);
+            {   // dz3: the pooled gradient of every pixel through the last ReLU
+                const float *da3 = act.da3c + tp * C3;
+                const bf16 *a3 = act.a3 + (tp * kPX + pix) * C3;
+                bf16 *dzt = act.dz3t + tp * C3 * kPX;
+#pragma unroll 1
+                for (int c0 = 0; c0 < C3; c0 += 8) {
+                    float da[8];
+                    if (in) {
+                        const float4 u = *reinterpret_cast<const float4 *>(da3 + c0), v = *reinterpret_cast<const float4 *>(da3 + c0 + 4);
+                        da[0] = u.x; da[1] = u.y; da[2] = u.z; da[3] = u.w; da[4] = v.x; da[5] = v.y; da[6] = v.z; da[7] = v.w;
+                    } else {
+#pragma unroll
+                        for (int i = 0; i < 8; i++) da[i] = 0.f;
+                    }
+                    emit(da, a3, C3, c0, in, true, dzt, db);
+                }
+            }
+            handoff();
+#pragma unroll 1
+            for (int layer = 0; layer < 2; layer++) {
+                wait(bar_done, ph);
+                ph ^= 1u;
+                tc_after_sync();
+                const int C = layer == 0 ? C2 : C1;
+                const bf16 *a = (layer == 0 ? act.a2 : act.a1) + (tp * kPX + pix) * C;
+                bf16 *dzt = (layer == 0 ? act.dz2t : act.dz1t) + tp * C * kPX;
+                float *sums = db + (layer == 0 ? C3 : C3 + C2);
+#pragma unroll 1
+                for (int c0 = 0; c0 < C; c0 += 8) {
+                    float v[8];
+                    tc_ld8(trow + (uint32_t)c0, v);
+                    tc_wait_ld();
+                    emit(v, a, C, c0, in, layer == 0, dzt, sums);
+                }
+                if (layer == 0) handoff();   // dz2 is in place and the accumulator is read
+                else tc_before_sync();
+            }
+        }
+    }
+    tc_before_sync();
+    __syncthreads();
+    tc_after_sync();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(kTmemCols) : "memory");
+    for (int c = tid; c < NDB; c += blockDim.x) {   // the slots' bias sums into the gradient
+        float v = 0.f;
+        for (int sl2 = 0; sl2 < kTcSlots; sl2++) v += sDB[sl2 * NDB + c];
+        const int off = c < C3 ? OB3 + c : (c < C3 + C2 ? OB2 + (c - C3) : OB1 + (c - C3 - C2));
+        if (v != 0.f) atomicAdd(grad + off, v);
     }
 }
 
@@ -1098,7 +1139,11 @@ lcc_status backward(lcc_net *net, const uint16_t *d_x, const float *d_labels, in
     if (s != LCC_OK) return s;
     k_net_head_bwd<<<grid_for(net, ntiles), kNetWarps * 32, 0, st>>>(net->nd, d_labels, ntiles, net->act, net->grad,
                                                                      net->loss);
-    k_net_conv_bwd<<<grid_for(net, ntiles), kNetWarps * 32, kBwdSmem, st>>>(net->nd, ntiles, net->act, net->grad);
+    {   // input gradients on tcgen05: one CTA per SM over pairs of tiles
+        const int64_t pairs = (ntiles + 1) / 2;
+        const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(pairs, net->sms));
+        k_net_bwd_tc<<<grid, kTcThreads, kTcBwdSmem, st>>>(net->nd, ntiles, net->act, net->grad, net->err);
+    }
     const int slices = (int)std::max<int64_t>(1, std::min<int64_t>((ntiles + kNetWarps - 1) / kNetWarps, 64));
     k_net_wgrad<C2, C3, 64, A2S><<<dim3(9 * C2 / 64, slices), kNetWarps * 32, wgrad_smem(A2S), st>>>(
         net->act.a2, net->act.dz3t, ntiles, net->grad, OW3);
@@ -1168,7 +1213,7 @@ lcc_status lcc_net_create(lcc_net **out, const float *h_params, int64_t max_tile
     net->max_tiles = max_tiles;
     net->sms = prop.multiProcessorCount;
     const size_t wb[] = {sizeof(float) * NPARAM * 4 + 256,   // theta, grad, m, v
-                         sizeof(bf16) * (C1 * BTS + C3 * BTS) + TW1 + TW2 + TW3,
+                         (size_t)TW1 + TW2 + TW3 + TWB3 + TWB2,
                          sizeof(float) * (HID * C3 + NOUT * HID), 256};
     size_t wtotal = 0;
     for (size_t b : wb) wtotal += align256(b);
@@ -1190,11 +1235,11 @@ lcc_status lcc_net_create(lcc_net **out, const float *h_params, int64_t max_tile
     net->v = net->m + NPARAM;
     w += align256(wb[0]);
     net->nd.theta = net->theta;
-    net->nd.B2t = (bf16 *)w;
-    net->nd.B3t = net->nd.B2t + C1 * BTS;
-    net->nd.T1 = net->nd.B3t + C3 * BTS;
+    net->nd.T1 = (bf16 *)w;
     net->nd.T2 = net->nd.T1 + TW1 / 2;
     net->nd.T3 = net->nd.T2 + TW2 / 2;
+    net->nd.TB3 = net->nd.T3 + TW3 / 2;
+    net->nd.TB2 = net->nd.TB3 + TWB3 / 2;
     w += align256(wb[1]);
     net->nd.F1b = (float *)w;
     net->nd.F2b = net->nd.F1b + HID * C3;
@@ -1209,7 +1254,8 @@ lcc_status lcc_net_create(lcc_net **out, const float *h_params, int64_t max_tile
         *slots[i] = a;
         a += align256(ab[i]);
     }
-    if (smem_attr(k_net_conv_bwd, kBwdSmem) != LCC_OK || smem_attr(k_net_fwd_tc<false>, kTcSmem) != LCC_OK ||
+    if (smem_attr(k_net_bwd_tc, kTcBwdSmem) != LCC_OK ||
+        smem_attr(k_net_fwd_tc<false>, kTcSmem) != LCC_OK ||
         smem_attr(k_net_fwd_tc<true>, kTcSmem) != LCC_OK ||
         smem_attr(k_net_wgrad<C2, C3, 64, A2S>, wgrad_smem(A2S)) != LCC_OK ||
         cudaMemcpy(net->theta, h_params, sizeof(float) * NPARAM, cudaMemcpyHostToDevice) != cudaSuccess ||
