@@ -1104,9 +1104,11 @@ def run_cfg5(args, stream, rank, world, dist):
                      d_out=[outs[kind][i * nfr + f].data_ptr() for f in range(nfr)], cap=[cap] * nfr,
                      d_nbytes=nbytes[kind][i * nfr:(i + 1) * nfr]) for i, q in enumerate(seqs)]
 
-    def build_plan(kind, frames_per_launch):
+    def build_plan(kind, frames_per_launch, lookahead=None):
         prm = lcc.lcc_params.from_buffer_copy(tuned[kind][0])
         prm.max_batch = frames_per_launch
+        if lookahead is not None:
+            prm.lookahead = lookahead
         ctx = lcc.Context(S, prm, stream=stream)
         plan = lcc.Plan([ctx], descs(kind, pts_dev))
         if kind == "learned":
@@ -1114,15 +1116,17 @@ def run_cfg5(args, stream, rank, world, dist):
         plan.capture()
         return ctx, plan
 
-    # frames per launch (the plan's chunk size; the chunk's range images should stay in L2): one
-    # timed replay of the whole table at 16, 32 and 64, the fastest kept
+    # frames per launch (the plan's chunk size) and run-test horizon, on the whole table: the
+    # autotuner timed one key-frame group with the per-group calls, while a plan's launches hold up
+    # to 64 frames, so both speed knobs are settled here (neither changes a stream byte): one timed
+    # replay at 16, 32 and 64 frames per launch and horizons 16 and 32, the fastest kept
     t0 = time.perf_counter()
     ctxs, plans = {}, {}
     for kind in tuned:
         rows = {}
         best = None
-        for fpl in (16, 32, 64):
-            ctx, plan = build_plan(kind, fpl)
+        for fpl, la in [(f, h) for f in (16, 32, 64) for h in (16, 32)]:
+            ctx, plan = build_plan(kind, fpl, la)
             plan.replay()
             assert plan.sync() == lcc.OK
             a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -1131,16 +1135,17 @@ def run_cfg5(args, stream, rank, world, dist):
             b.record(stream)
             assert plan.sync() == lcc.OK
             ms = a.elapsed_time(b)
-            rows[fpl] = round(total_pts / (ms * 1e-3) / 1e6, 1)
+            rows[f"{fpl}/{la}"] = round(total_pts / (ms * 1e-3) / 1e6, 1)
             if best is None or ms < best[0]:
                 if best is not None:
                     best[3].close()
-                best = (ms, fpl, ctx, plan)
+                best = (ms, (fpl, la), ctx, plan)
             else:
                 plan.close()
         ctxs[kind], plans[kind] = best[2], best[3]
-        tuned[kind][1]["frames_per_launch"] = best[1]
-        tuned[kind][1]["frames_per_launch_mpts_s"] = rows
+        tuned[kind][1]["frames_per_launch"] = best[1][0]
+        tuned[kind][1]["lookahead"] = best[1][1]
+        tuned[kind][1]["frames_per_launch_mpts_s"] = rows   # keys: frames per launch / horizon
     setup["frames_per_launch_s"] = time.perf_counter() - t0
     for k in plans:
         for _ in range(max(args.warmup, 3)):
