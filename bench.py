@@ -89,6 +89,9 @@ def parse():
                     help="profiling case: the proposal net's forward over --net-tiles seeded tiles, --steps calls after "
                          "one warm-up call, nothing else (for ncu)")
     ap.add_argument("--net-tiles", type=int, default=98304)
+    ap.add_argument("--profile-sequence", action="store_true",
+                    help="profiling case: the HDL-64E sequence encoded by lcc_encode_sequence --steps times after one "
+                         "warm-up call (--tile, --thr, --lookahead, --schedule), nothing else (for ncu)")
     ap.add_argument("--profile-train", action="store_true",
                     help="profiling case: --steps training steps of the proposal net on 4096 seeded tiles after one "
                          "warm-up step, nothing else (for ncu)")
@@ -1406,6 +1409,36 @@ def run_profile_net(args, stream):
     return {"profile_net": True, "tiles": T, "ms_per_call": ms, "tflops": flops / (ms * 1e-3) / 1e12}
 
 
+def run_profile_sequence(args, stream):
+    """The HDL-64E sequence alone: one warm-up lcc_encode_sequence call and --steps timed calls
+    (the case the DRAM traffic of the sequence's kernels is captured on)."""
+    import torch
+    from paper_2008_06972_gb300 import lcc
+    th, tw = (int(v) for v in args.tile.split("x"))
+    seq = make_workload(0)
+    n = [len(f) for f in seq.frames]
+    prm = lcc.default_params(tile_h=th, tile_w=tw, fit_thr_m=args.thr, max_batch=max(16, len(n)),
+                             lookahead=args.lookahead, fit_schedule=args.schedule)
+    ctx = lcc.Context(seq.sensor, prm, stream=stream)
+    kf = lcc.Keyframe(ctx)
+    d_pts = [torch.from_numpy(f).cuda() for f in seq.frames]
+    cap = ctx.max_encoded_bytes
+    outs = [torch.zeros(cap, dtype=torch.uint8, device="cuda") for _ in n]
+    nb = torch.zeros(len(n), dtype=torch.int64, device="cuda")
+    step = lambda: ctx.lcc_encode_sequence(seq.key_index, seq.poses, d_pts, n, outs, [cap] * len(n), nb, kf)
+    step()
+    assert ctx.lcc_sync() == lcc.OK
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for _ in range(args.steps):
+        step()
+    b.record(stream)
+    assert ctx.lcc_sync() == lcc.OK
+    torch.cuda.synchronize()
+    return {"profile_sequence": True, "points": sum(n), "ms_per_step": a.elapsed_time(b) / args.steps,
+            "bytes": int(nb.sum().item())}
+
+
 def run_profile_train(args, stream):
     """Training steps of the proposal net alone (tcgen05 forward with saved activations, head
     backward, input gradients, weight gradients, Adam) on 4096 seeded tiles with random labels:
@@ -1668,6 +1701,9 @@ def main():
         return
     if args.profile_train:
         print(json.dumps(run_profile_train(args, stream)), flush=True)
+        return
+    if args.profile_sequence:
+        print(json.dumps(run_profile_sequence(args, stream)), flush=True)
         return
     line = run_cfg5(args, stream, rank, world, dist)
     if world == 1:

@@ -415,9 +415,10 @@ lcc_status lcc_selftest_bounded_wait(int64_t limit, void *cuda_stream);
  * cuda_stream, so that call returns only after that work has finished.
  *
  * Set-up: the first call on each device, with that device current, resolves
- * the array's address with cudaGetSymbolAddress (checked) and keeps it; a
- * cudaDeviceReset ends the context the address belongs to, and the next call
- * in the new context repeats the set-up (and the table copy).
+ * the array's address with cudaGetSymbolAddress (checked) and keeps it; make
+ * that first call before any stream capture begins.  A cudaDeviceReset ends
+ * the context the address belongs to, and the next call in the new context
+ * repeats the set-up (and the table copy).
  * The array is shared by every call on a device: calls that overlap in time
  * (other streams, other threads) race on it and must be serialised by the
  * caller.  Each call clears what must start cleared (range image to empty,
