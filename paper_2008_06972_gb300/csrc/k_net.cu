@@ -16,9 +16,11 @@
 // straight from a zero-bordered 10x10 copy of the tile in shared memory (no
 // im2col buffer).  The forward pass (inference and training) runs on tcgen05
 // with TMEM accumulators, two tiles per 128-row MMA.  The backward pass runs
-// on the warp-level mma.sync m16n8k16 instruction: the input-gradient
-// convolution is the same GEMM with the taps mirrored and the weights
-// transposed, the weight gradient a GEMM over (tile, pixel) split across CTAs.
+// on tcgen05 as well: the input-gradient convolution is the same GEMM with the
+// taps mirrored and the channel roles swapped; the weight gradient is a GEMM
+// whose reduction runs over the pixels of all tiles (one accumulator per CTA,
+// summed across CTAs in a fixed order), the taps' shifts taken from where the
+// staged operands start.
 #include <cuda_bf16.h>
 
 #include <algorithm>
@@ -39,10 +41,7 @@ typedef __nv_bfloat16 bf16;
 
 constexpr int kPX = 64;                       // pixels of an 8x8 tile
 constexpr int C0 = 4, C1 = 32, C2 = 64, C3 = 64, HID = 32, NOUT = 5;
-constexpr int XS = 8;                         // padded channel stride of the input copy
 constexpr int K1 = 48;                        // conv1 on tcgen05 as one contraction: 9 taps x 4 channels, 3 k-steps
-constexpr int A1S = C1 + 8, A2S = C2 + 8;     // padded channel strides (bank spread)
-constexpr int kNetWarps = 4;
 
 // offsets of the flat parameter vector: W1[32,4,3,3] b1 W2[64,32,3,3] b2 W3[64,64,3,3] b3 F1[32,64] c1 F2[5,32] c2
 constexpr int OW1 = 0, OB1 = OW1 + C1 * C0 * 9, OW2 = OB1 + C1, OB2 = OW2 + C2 * C1 * 9, OW3 = OB2 + C2,
@@ -62,22 +61,13 @@ struct NetAct {                              // per-tile training activations
     bf16 *a1, *a2, *a3;                      // [T][64][C]
     float *g, *h, *o;                        // [T][64], [T][32], [T][5]
     float *da3c;                             // [T][64]  dL/d(pooled input) / 64
+    float *hdy, *hdo, *hlt;                  // [T][32], [T][8], [T]: head gradient terms and loss per tile
     bf16 *dz1t, *dz2t, *dz3t;                // [T][C][64] pre-activation gradients, pixel-contiguous
 };
 
-__device__ __forceinline__ uint32_t ld32(const bf16 *p) { return *reinterpret_cast<const uint32_t *>(p); }
 __device__ __forceinline__ float bfround(float x) { return __bfloat162float(__float2bfloat16_rn(x)); }
 __device__ __forceinline__ uint32_t pack2(bf16 lo, bf16 hi) {
     return (uint32_t)__bfloat16_as_ushort(lo) | ((uint32_t)__bfloat16_as_ushort(hi) << 16);
-}
-
-__device__ __forceinline__ void mma_bf16(float c[4], uint32_t a0, uint32_t a1, uint32_t a2, uint32_t a3, uint32_t b0,
-                                         uint32_t b1) {
-    asm volatile(
-        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
-        "{%0,%1,%2,%3};\n"
-        : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
-        : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
 }
 
 // ------------------------------------------------------------------ weights --
@@ -697,70 +687,122 @@ __global__ void k_bounded_wait_selftest(long long limit, int *err) {
 
 constexpr float kBeta = 0.02f, kNormEps = 1e-12f;
 
-// One warp per tile (persistent): loss terms, head gradients (accumulated per
-// warp, one atomic per value at the end), and dL/d(pooled) / 64 per channel.
-__global__ void __launch_bounds__(kNetWarps * 32) k_net_head_bwd(NetDev nd, const float *labels, long long T,
-                                                                  NetAct act, float *grad, float *loss) {
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+// One warp per tile: the loss term, dL/d(output) (dout, scaled by 1/T), the hidden layer's
+// gradient dy = F2b^T dout through its ReLU, and dL/d(pooled) / 64 per channel; the per-tile
+// terms go to global memory and k_net_head_sums forms the head's weight gradients from them.
+constexpr int kHeadWarps = 8;
+constexpr int HDO = 8;   // dout row stride (5 used)
+
+__global__ void __launch_bounds__(kHeadWarps * 32) k_net_head_bwd(NetDev nd, const float *labels, long long T,
+                                                                   NetAct act) {
+    const int lane = threadIdx.x & 31;
+    const long long tile = (long long)blockIdx.x * kHeadWarps + (threadIdx.x >> 5);
+    if (tile >= T) return;
     const float invT = 1.0f / (float)T;
-    float dF1[C3], dF2[NOUT], dc1 = 0.f, dc2 = 0.f, lsum = 0.f;
+    const float *o = act.o + (size_t)tile * NOUT;
+    const float *y = labels + (size_t)tile * NOUT;
+    const float lg = o[0], v0 = o[1], v1 = o[2], v2 = o[3], dd = o[4];
+    const float fit = y[0], n0 = y[1], n1 = y[2], n2 = y[3], drel = y[4];
+    const float s = sqrtf(v0 * v0 + v1 * v1 + v2 * v2 + kNormEps);
+    const float vn = v0 * n0 + v1 * n1 + v2 * n2;
+    const float cs = vn / s;
+    const float xd = dd - drel, ax = fabsf(xd);
+    const float sl1 = ax < kBeta ? 0.5f * xd * xd / kBeta : ax - 0.5f * kBeta;
+    const float bce = fmaxf(lg, 0.f) - fit * lg + log1pf(expf(-fabsf(lg)));
+    float dout[NOUT];
+    dout[0] = (1.f / (1.f + expf(-lg)) - fit) * invT;
+    const float sg = cs > 0.f ? 1.f : (cs < 0.f ? -1.f : 0.f);
+    const float k3 = vn / (s * s * s);
+    dout[1] = -fit * sg * (n0 / s - k3 * v0) * invT;
+    dout[2] = -fit * sg * (n1 / s - k3 * v1) * invT;
+    dout[3] = -fit * sg * (n2 / s - k3 * v2) * invT;
+    dout[4] = fit * fminf(fmaxf(xd / kBeta, -1.f), 1.f) * invT;
+    const float hj = act.h[(size_t)tile * HID + lane];
+    float dh = 0.f;
 #pragma unroll
-    for (int c = 0; c < C3; c++) dF1[c] = 0.f;
-#pragma unroll
-    for (int i = 0; i < NOUT; i++) dF2[i] = 0.f;
-    for (long long tile = (long long)blockIdx.x * kNetWarps + warp; tile < T; tile += (long long)gridDim.x * kNetWarps) {
-        const float *o = act.o + (size_t)tile * NOUT;
-        const float *y = labels + (size_t)tile * NOUT;
-        const float lg = o[0], v0 = o[1], v1 = o[2], v2 = o[3], dd = o[4];
-        const float fit = y[0], n0 = y[1], n1 = y[2], n2 = y[3], drel = y[4];
-        const float s = sqrtf(v0 * v0 + v1 * v1 + v2 * v2 + kNormEps);
-        const float vn = v0 * n0 + v1 * n1 + v2 * n2;
-        const float cs = vn / s;
-        const float xd = dd - drel, ax = fabsf(xd);
-        const float sl1 = ax < kBeta ? 0.5f * xd * xd / kBeta : ax - 0.5f * kBeta;
-        const float bce = fmaxf(lg, 0.f) - fit * lg + log1pf(expf(-fabsf(lg)));
-        lsum += bce + fit * (1.f - fabsf(cs)) + fit * sl1;
-        float dout[NOUT];
-        dout[0] = (1.f / (1.f + expf(-lg)) - fit) * invT;
-        const float sg = cs > 0.f ? 1.f : (cs < 0.f ? -1.f : 0.f);
-        const float k3 = vn / (s * s * s);
-        dout[1] = -fit * sg * (n0 / s - k3 * v0) * invT;
-        dout[2] = -fit * sg * (n1 / s - k3 * v1) * invT;
-        dout[3] = -fit * sg * (n2 / s - k3 * v2) * invT;
-        dout[4] = fit * fminf(fmaxf(xd / kBeta, -1.f), 1.f) * invT;
-        const float hj = act.h[(size_t)tile * HID + lane];
-        float dh = 0.f;
-#pragma unroll
-        for (int i = 0; i < NOUT; i++) {
-            dF2[i] = fmaf(dout[i], hj, dF2[i]);
-            dh = fmaf(__ldg(nd.F2b + i * HID + lane), dout[i], dh);
-        }
-        if (lane < NOUT) dc2 += dout[lane];
-        const float dy = hj > 0.f ? dh : 0.f;
-        dc1 += dy;
-        const float *gv = act.g + (size_t)tile * C3;
-#pragma unroll
-        for (int c = 0; c < C3; c++) dF1[c] = fmaf(dy, gv[c], dF1[c]);
-        // dg[c] = sum_j F1b[j][c] dy_j: lane c and c + 32 gather the 32 hidden units
-        float dg0 = 0.f, dg1 = 0.f;
-        for (int j = 0; j < HID; j++) {
-            const float dyj = __shfl_sync(0xffffffffu, dy, j);
-            dg0 = fmaf(__ldg(nd.F1b + j * C3 + lane), dyj, dg0);
-            dg1 = fmaf(__ldg(nd.F1b + j * C3 + lane + 32), dyj, dg1);
-        }
-        act.da3c[(size_t)tile * C3 + lane] = dg0 * (1.0f / kPX);
-        act.da3c[(size_t)tile * C3 + lane + 32] = dg1 * (1.0f / kPX);
+    for (int i = 0; i < NOUT; i++) dh = fmaf(__ldg(nd.F2b + i * HID + lane), dout[i], dh);
+    const float dy = hj > 0.f ? dh : 0.f;
+    act.hdy[(size_t)tile * HID + lane] = dy;
+    if (lane < NOUT) act.hdo[(size_t)tile * HDO + lane] = dout[lane];
+    if (lane == 0) act.hlt[tile] = bce + fit * (1.f - fabsf(cs)) + fit * sl1;
+    // dg[c] = sum_j F1b[j][c] dy_j: lane c and c + 32 gather the 32 hidden units
+    float dg0 = 0.f, dg1 = 0.f;
+#pragma unroll 8
+    for (int j = 0; j < HID; j++) {
+        const float dyj = __shfl_sync(0xffffffffu, dy, j);
+        dg0 = fmaf(__ldg(nd.F1b + j * C3 + lane), dyj, dg0);
+        dg1 = fmaf(__ldg(nd.F1b + j * C3 + lane + 32), dyj, dg1);
     }
+    act.da3c[(size_t)tile * C3 + lane] = dg0 * (1.0f / kPX);
+    act.da3c[(size_t)tile * C3 + lane + 32] = dg1 * (1.0f / kPX);
+}
+
+// The head's weight gradients and the loss as sums over tiles: dF1[j][c] = sum dy[j] g[c],
+// dc1[j] = sum dy[j], dF2[i][j] = sum dout[i] h[j], dc2[i] = sum dout[i], loss = sum of the terms.
+// Each block sums its chunks of kHeadChunk tiles (staged in shared memory) in tile order and
+// stores its partial sums; k_net_head_reduce adds the blocks' partials in block order.
+constexpr int kHeadChunk = 64, kHeadSumThreads = 256;
+constexpr int HS_F1 = 0, HS_C1 = HS_F1 + HID * C3, HS_F2 = HS_C1 + HID, HS_C2 = HS_F2 + NOUT * HID,
+              HS_LOSS = HS_C2 + NOUT, HS_N = HS_LOSS + 1;
+
+__global__ void __launch_bounds__(kHeadSumThreads) k_net_head_sums(long long T, NetAct act, float *part) {
+    __shared__ float sdy[kHeadChunk][HID], sg[kHeadChunk][C3], sh[kHeadChunk][HID], sdo[kHeadChunk][HDO],
+        slt[kHeadChunk];
+    const int tid = threadIdx.x, c = tid % C3, j0 = tid / C3;   // dF1 rows j0, j0 + 4, ..., column c
+    float f1[HID / 4];
 #pragma unroll
-    for (int c = 0; c < C3; c++)
-        if (dF1[c] != 0.f) atomicAdd(grad + OF1 + lane * C3 + c, dF1[c]);
+    for (int k = 0; k < HID / 4; k++) f1[k] = 0.f;
+    float ex = 0.f;   // the one other sum of this thread (dc1, dF2, dc2 or the loss), if any
+    for (long long t0 = (long long)blockIdx.x * kHeadChunk; t0 < T; t0 += (long long)gridDim.x * kHeadChunk) {
+        const int nt = T - t0 < kHeadChunk ? (int)(T - t0) : kHeadChunk;
+        __syncthreads();
+        for (int i = tid; i < kHeadChunk * C3; i += kHeadSumThreads) {
+            const int t = i / C3;
+            sg[t][i % C3] = t < nt ? act.g[(size_t)(t0 + t) * C3 + i % C3] : 0.f;
+        }
+        for (int i = tid; i < kHeadChunk * HID; i += kHeadSumThreads) {
+            const int t = i / HID;
+            sdy[t][i % HID] = t < nt ? act.hdy[(size_t)(t0 + t) * HID + i % HID] : 0.f;
+            sh[t][i % HID] = t < nt ? act.h[(size_t)(t0 + t) * HID + i % HID] : 0.f;
+        }
+        for (int i = tid; i < kHeadChunk * HDO; i += kHeadSumThreads) {
+            const int t = i / HDO;
+            sdo[t][i % HDO] = t < nt && i % HDO < NOUT ? act.hdo[(size_t)(t0 + t) * HDO + i % HDO] : 0.f;
+        }
+        if (tid < kHeadChunk) slt[tid] = tid < nt ? act.hlt[t0 + tid] : 0.f;
+        __syncthreads();
+        for (int t = 0; t < nt; t++) {
+            const float gc = sg[t][c];
 #pragma unroll
-    for (int i = 0; i < NOUT; i++)
-        if (dF2[i] != 0.f) atomicAdd(grad + OF2 + i * HID + lane, dF2[i]);
-    if (dc1 != 0.f) atomicAdd(grad + OC1 + lane, dc1);
-    if (lane < NOUT && dc2 != 0.f) atomicAdd(grad + OC2 + lane, dc2);
-    // every lane of a warp evaluated the same tiles' loss: count it once
-    if (lane == 0 && lsum != 0.f) atomicAdd(loss, lsum * invT);
+            for (int k = 0; k < HID / 4; k++) f1[k] = fmaf(sdy[t][j0 + 4 * k], gc, f1[k]);
+        }
+        if (tid < HID) {
+            for (int t = 0; t < nt; t++) ex += sdy[t][tid];
+        } else if (tid < HID + NOUT * HID) {
+            const int i = (tid - HID) / HID, jj = (tid - HID) % HID;
+            for (int t = 0; t < nt; t++) ex = fmaf(sdo[t][i], sh[t][jj], ex);
+        } else if (tid < HID + NOUT * HID + NOUT) {
+            for (int t = 0; t < nt; t++) ex += sdo[t][tid - HID - NOUT * HID];
+        } else if (tid == HID + NOUT * HID + NOUT) {
+            for (int t = 0; t < nt; t++) ex += slt[t];
+        }
+    }
+    float *dst = part + (size_t)blockIdx.x * HS_N;
+#pragma unroll
+    for (int k = 0; k < HID / 4; k++) dst[HS_F1 + (j0 + 4 * k) * C3 + c] = f1[k];
+    if (tid < HS_N - HS_C1) dst[HS_C1 + tid] = ex;   // dc1, dF2, dc2 and the loss follow dF1 in this order
+}
+
+__global__ void k_net_head_reduce(const float *part, int nparts, float invT, float *grad, float *loss) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= HS_N) return;
+    float s = 0.f;
+    for (int b = 0; b < nparts; b++) s += part[(size_t)b * HS_N + k];
+    if (k < HS_C1) grad[OF1 + k] += s;
+    else if (k < HS_F2) grad[OC1 + (k - HS_C1)] += s;
+    else if (k < HS_C2) grad[OF2 + (k - HS_F2)] += s;
+    else if (k < HS_LOSS) grad[OC2 + (k - HS_C2)] += s;
+    else *loss += s * invT;
 }
 
 // ------------------------------------------------------------------ backward: input gradients on tcgen05 --
@@ -987,81 +1029,242 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_net_bwd_tc(NetDev nd, long lo
     }
 }
 
-// ------------------------------------------------------------------ backward: weight gradients --
+// ------------------------------------------------------------------ backward: weight gradients on tcgen05 --
+//
+// dW[co][ci][ky][kx] = sum over tiles and pixels p = (y, x) of dz[co][p] * a[ci][y + ky - 1][x + kx - 1]
+// (zero outside the tile): a GEMM whose reduction runs over pixels.  Both operands are staged in
+// shared memory K-major with the pixels as K; a "core" is one 8-pixel row of the tile (one core
+// matrix wide in K):
+//   P: rows (dx, ci), dx = -1, 0, +1: the input activations of channel ci shifted by dx along
+//      each row (zero fill), cores 0..9 (8 and 9 stay zero);
+//   Z: rows co, the pre-activation gradient, cores -1..9 (-1, 8 and 9 stay zero).
+// Within a core the 8-row groups are kWgSbo = 144 bytes apart (128 + 16, so that the 16-byte
+// stores of a quarter-warp fall in different banks) and the next core starts where the core's
+// last group ends: an operand with more rows than a core holds continues into the next core, one
+// tile row further down.  So the row shift dy comes from the core an operand starts at and the
+// column shift dx from P's row blocks:
+//   conv2, conv3 (A = P, B = Z, N = 3 CO): B starts one core early, its three row blocks are dz
+//   one row above, level with and below A's rows (ky = 2, 1, 0); A starts at group 0 (and for
+//   conv3's 192 rows at group 16 as well), so one or two M = 128 MMAs per k-step cover all dx;
+//   conv1 (A = Z, B = P, M = 128, N = 32): A's row blocks are dz at ky = 2, 1, 0 (and an unused
+//   fourth), B's rows are (dx, ci) with ci padded to 8.
+// Rows and columns that hold no tap (the operand's spill into the next core, padding channels)
+// are computed and ignored.  Every CTA accumulates its tiles in TMEM and stores the accumulator
+// (lanes contiguous); k_net_wgrad_reduce adds the CTAs' copies in CTA order into the gradient.
+constexpr int kWgSbo = 144;
+constexpr int kWgTeams = 4, kWgTeamWarps = 2;                   // a team of warps fills one slot
+constexpr int kWgProdWarps = kWgTeams * kWgTeamWarps;
+constexpr int kWgThreads = (kWgProdWarps + 1) * 32;             // + the MMA warp
 
-// dW[co][k = tap*CIN + ci] = sum over tiles and pixels of dz[co][p] * a_pad[p + tap][ci].
-// CTA (x: a chunk of KCH reduction columns, y: a slice of tiles); each warp runs its
-// own tiles of the slice with the tile's input staged in a padded shared copy.
-template <int CIN, int COUT, int KCH, int AS>
-__global__ void __launch_bounds__(kNetWarps * 32) k_net_wgrad(const bf16 *a, const bf16 *dzt, long long T, float *grad,
-                                                               int wofs) {
-    extern __shared__ __align__(16) uint8_t sm[];
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
-    bf16 *ap = reinterpret_cast<bf16 *>(sm) + warp * 100 * AS;
-    for (int i = lane; i < 100 * AS / 2; i += 32) reinterpret_cast<uint32_t *>(ap)[i] = 0u;
-    __syncwarp();
-    const int k0 = blockIdx.x * KCH;
-    constexpr int MT = COUT / 16, NT = KCH / 8;
-    float acc[MT][NT][4];
-#pragma unroll
-    for (int m = 0; m < MT; m++)
-#pragma unroll
-        for (int n = 0; n < NT; n++) acc[m][n][0] = acc[m][n][1] = acc[m][n][2] = acc[m][n][3] = 0.f;
-    // column k -> (tap, ci) of the padded copy, per lane for its two B columns
-    int koff[NT];
-#pragma unroll
-    for (int n = 0; n < NT; n++) {
-        const int k = k0 + n * 8 + g;
-        koff[n] = k < 9 * CIN ? ((k / CIN) / 3 * 10 + (k / CIN) % 3) * AS + k % CIN : -1;
+template <int CI, int CO>
+struct Wg {
+    static constexpr int CIP = CI < 8 ? 8 : CI;
+    static constexpr int RP = 3 * CIP, GP = RP / 8, GZ = CO / 8;   // P rows; 8-row groups per core
+    static constexpr int LBP = GP * kWgSbo, LBZ = GZ * kWgSbo;     // bytes per core
+    static constexpr int PB = 10 * LBP, ZB = 11 * LBZ, SLOT = PB + ZB;
+    static constexpr bool kAP = CI >= 16;                          // A = P; else A = Z
+    static constexpr int N = kAP ? 3 * CO : 32;
+    static constexpr int NM = kAP ? (RP + 127) / 128 : 1;          // MMAs per k-step
+    static constexpr int DCOLS = NM * N, DSZ = 128 * DCOLS;        // accumulator columns, floats
+    static constexpr uint32_t TCOLS = DCOLS <= 32 ? 32 : DCOLS <= 64 ? 64 : DCOLS <= 128 ? 128 : DCOLS <= 256 ? 256 : 512;
+    static constexpr size_t SMEM = (size_t)kWgTeams * SLOT + (2 * kWgTeams + 1) * 8 + 16;
+    static_assert(kAP ? (CI % 8 == 0 && CO % 8 == 0 && N <= 256) : (CI <= 8 && CO == 32), "operand shapes");
+    static_assert(DCOLS <= 512 && SMEM <= 227 * 1024, "accumulator and staging fit");
+};
+
+__device__ __forceinline__ void st16(uint8_t *p, uint32_t a, uint32_t b, uint32_t c, uint32_t d) {
+    *reinterpret_cast<uint4 *>(p) = make_uint4(a, b, c, d);
+}
+
+// The three shifted copies (dx = -1, 0, +1) of one row of 8 pixels (w: 4 words, 2 pixels each)
+// at p, p + step and p + 2 step.
+__device__ __forceinline__ void put_shifts(uint8_t *p, int step, const uint32_t (&w)[4]) {
+    const uint32_t s1 = __byte_perm(w[0], w[1], 0x5432), s2 = __byte_perm(w[1], w[2], 0x5432),
+                   s3 = __byte_perm(w[2], w[3], 0x5432);
+    st16(p, w[0] << 16, s1, s2, s3);            // value at x is a[x - 1]
+    st16(p + step, w[0], w[1], w[2], w[3]);
+    st16(p + 2 * step, s1, s2, s3, w[3] >> 16); // value at x is a[x + 1]
+}
+
+template <int CI, int CO>
+__global__ void __launch_bounds__(kWgThreads, 1) k_net_wgrad_tc(const bf16 *a, const bf16 *dzt, long long T, float *part,
+                                                                 int *err) {
+    using C = Wg<CI, CO>;
+    extern __shared__ __align__(1024) uint8_t sm[];
+    // barriers: [t] slot t filled (its team's warps), [kWgTeams + t] slot t read (tcgen05.commit),
+    // [2 kWgTeams] all MMAs done
+    uint64_t *bar = reinterpret_cast<uint64_t *>(sm + kWgTeams * C::SLOT);
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bar + 2 * kWgTeams + 1);
+    int *s_fail = reinterpret_cast<int *>(tmem_slot + 1);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    if (tid == 0) {
+        for (int i = 0; i < kWgTeams; i++)
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_u32(bar + i)), "r"(kWgTeamWarps) : "memory");
+        for (int i = kWgTeams; i < 2 * kWgTeams + 1; i++)
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(bar + i)) : "memory");
+        *s_fail = 0;
     }
-    for (long long tile = (long long)blockIdx.y * kNetWarps + warp; tile < T; tile += (long long)gridDim.y * kNetWarps) {
-        const bf16 *at = a + (size_t)tile * kPX * CIN;
-        for (int i = lane; i < kPX * CIN / 2; i += 32) {
-            const int p = (2 * i) / CIN, c = (2 * i) % CIN;
-            *reinterpret_cast<uint32_t *>(ap + ((p / 8 + 1) * 10 + p % 8 + 1) * AS + c) =
-                reinterpret_cast<const uint32_t *>(at)[i];
-        }
-        __syncwarp();
-        const bf16 *dz = dzt + (size_t)tile * COUT * kPX;
+    {   // zero cores and padding rows stay as written here
+        uint4 *z = reinterpret_cast<uint4 *>(sm);
+        for (int i = tid; i < kWgTeams * C::SLOT / 16; i += blockDim.x) z[i] = make_uint4(0u, 0u, 0u, 0u);
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(smem_u32(tmem_slot)),
+                     "r"(C::TCOLS)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::: "memory");
+    }
+    proxy_fence();
+    tc_before_sync();
+    __syncthreads();
+    tc_after_sync();
+    const uint32_t tmem = *tmem_slot;
+    const long long G = gridDim.x;
+    const long long ntl = (T - blockIdx.x + G - 1) / G;   // this CTA's tiles blockIdx.x + j G (>= 1: grid <= T)
+    auto fail = [&]() {
+        atomicExch(s_fail, 1);
+        if (err) atomicExch(err, 1);
+    };
+    const uint32_t bar_done = smem_u32(bar + 2 * kWgTeams);
+    if (warp == kWgProdWarps) {
+        // ---- MMA warp: the tiles in order, slot j % kWgTeams ----
+        if (lane == 0) {
+            constexpr uint32_t idesc = mma_idesc(128, C::N);
+            for (long long j = 0; j < ntl && !*(volatile int *)s_fail; j++) {
+                const int s = (int)(j % kWgTeams);
+                if (!mbar_wait(smem_u32(bar + s), (uint32_t)((j / kWgTeams) & 1))) {
+                    fail();
+                    break;
+                }
+                tc_after_sync();
+                const uint32_t P = smem_u32(sm + s * C::SLOT), Z = P + C::PB;
 #pragma unroll
-        for (int ks = 0; ks < kPX / 16; ks++) {
-            const int p0 = ks * 16 + 2 * t;     // this lane's pixel pairs: p0, p0+1 and p0+8, p0+9
-            uint32_t b[NT][2];
+                for (int ks = 0; ks < 4; ks++) {
+                    const int kc = 2 * ks;   // first core of the k-step; Z's position kc is core kc - 1
 #pragma unroll
-            for (int n = 0; n < NT; n++) {
-#pragma unroll
-                for (int hh = 0; hh < 2; hh++) {
-                    const int pa = p0 + 8 * hh;
-                    if (koff[n] < 0) {
-                        b[n][hh] = 0u;
-                    } else {
-                        const bf16 lo = ap[koff[n] + ((pa / 8) * 10 + pa % 8) * AS];
-                        const bf16 hi = ap[koff[n] + (((pa + 1) / 8) * 10 + (pa + 1) % 8) * AS];
-                        b[n][hh] = pack2(lo, hi);
+                    for (int jm = 0; jm < C::NM; jm++) {
+                        const uint64_t ad = C::kAP ? smem_desc(P + kc * C::LBP + jm * 16 * kWgSbo, C::LBP, kWgSbo)
+                                                   : smem_desc(Z + kc * C::LBZ, C::LBZ, kWgSbo);
+                        const uint64_t bd = C::kAP ? smem_desc(Z + kc * C::LBZ, C::LBZ, kWgSbo)
+                                                   : smem_desc(P + kc * C::LBP, C::LBP, kWgSbo);
+                        tc_mma(tmem + (uint32_t)(jm * C::N), ad, bd, idesc, (j | ks) ? 1u : 0u);
                     }
                 }
+                tc_commit(smem_u32(bar + kWgTeams + s));
             }
-#pragma unroll
-            for (int m = 0; m < MT; m++) {
-                const bf16 *r0 = dz + (m * 16 + g) * kPX + p0;
-                const bf16 *r1 = r0 + 8 * kPX;
-                const uint32_t a0 = ld32(r0), a1 = ld32(r1), a2 = ld32(r0 + 8), a3 = ld32(r1 + 8);
-#pragma unroll
-                for (int n = 0; n < NT; n++) mma_bf16(acc[m][n], a0, a1, a2, a3, b[n][0], b[n][1]);
-            }
+            tc_commit(bar_done);
         }
         __syncwarp();
-    }
-#pragma unroll
-    for (int m = 0; m < MT; m++)
-#pragma unroll
-        for (int n = 0; n < NT; n++)
-#pragma unroll
-            for (int q = 0; q < 4; q++) {
-                const int co = m * 16 + g + (q >> 1) * 8, k = k0 + n * 8 + 2 * t + (q & 1);
-                if (k < 9 * CIN && acc[m][n][q] != 0.f)
-                    atomicAdd(grad + wofs + co * 9 * CIN + (k % CIN) * 9 + k / CIN, acc[m][n][q]);
+    } else {
+        // ---- team t = warp / kWgTeamWarps fills slot t with the tiles j = t, t + kWgTeams, ... ----
+        const int team = warp / kWgTeamWarps, tt = tid % (kWgTeamWarps * 32), tw = warp % kWgTeamWarps;
+        uint8_t *P = sm + team * C::SLOT, *Z = P + C::PB;
+        for (long long j = team; j < ntl; j += kWgTeams) {
+            if (*(volatile int *)s_fail) break;
+            if (j >= kWgTeams && !mbar_wait(smem_u32(bar + kWgTeams + team), (uint32_t)((j / kWgTeams - 1) & 1))) {
+                fail();
+                break;
             }
+            const long long tile = blockIdx.x + j * G;
+            if constexpr (C::kAP) {
+                constexpr int NC8 = CI / 8;
+                for (int it = tt; it < 8 * NC8; it += kWgTeamWarps * 32) {
+                    const int c8 = it % NC8, y = it / NC8;
+                    const uint4 *src = reinterpret_cast<const uint4 *>(a + ((size_t)tile * kPX + y * 8) * CI) + c8;
+                    uint32_t r[8][4];
+#pragma unroll
+                    for (int x = 0; x < 8; x++) {
+                        const uint4 v = __ldg(src + x * NC8);
+                        r[x][0] = v.x; r[x][1] = v.y; r[x][2] = v.z; r[x][3] = v.w;
+                    }
+                    uint8_t *row = P + y * C::LBP + c8 * kWgSbo;
+#pragma unroll
+                    for (int q = 0; q < 4; q++) {   // channels 2q and 2q + 1 of the group
+                        uint32_t lo[4], hi[4];
+#pragma unroll
+                        for (int m = 0; m < 4; m++) {
+                            lo[m] = __byte_perm(r[2 * m][q], r[2 * m + 1][q], 0x5410);
+                            hi[m] = __byte_perm(r[2 * m][q], r[2 * m + 1][q], 0x7632);
+                        }
+                        put_shifts(row + (2 * q) * 16, NC8 * kWgSbo, lo);
+                        put_shifts(row + (2 * q + 1) * 16, NC8 * kWgSbo, hi);
+                    }
+                }
+            } else {
+                if (tt < 8 * CI) {   // one channel of one row of 8 pixels per thread
+                    const int ci = tt % CI, y = tt / CI;
+                    const unsigned short *src =
+                        reinterpret_cast<const unsigned short *>(a) + ((size_t)tile * kPX + y * 8) * CI + ci;
+                    uint32_t w[4];
+#pragma unroll
+                    for (int m = 0; m < 4; m++)
+                        w[m] = (uint32_t)__ldg(src + (2 * m) * CI) | ((uint32_t)__ldg(src + (2 * m + 1) * CI) << 16);
+                    put_shifts(P + y * C::LBP + ci * 16, kWgSbo, w);
+                }
+            }
+            {   // dz rows: a block of 8 channels x 4 rows per warp instruction (64 contiguous bytes per channel)
+                constexpr int NBLK = (CO / 8) * 2;
+                for (int b = tw; b < NBLK; b += kWgTeamWarps) {
+                    const int chi = b % (CO / 8), y = (b / (CO / 8)) * 4 + (lane >> 3), co = chi * 8 + (lane & 7);
+                    const uint4 v = __ldg(reinterpret_cast<const uint4 *>(dzt + ((size_t)tile * CO + co) * kPX + y * 8));
+                    *reinterpret_cast<uint4 *>(Z + (y + 1) * C::LBZ + chi * kWgSbo + (lane & 7) * 16) = v;
+                }
+            }
+            proxy_fence();
+            tc_before_sync();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(smem_u32(bar + team));
+        }
+        // ---- epilogue: warp w reads TMEM lanes 32 (w % 4).. and every other 8-column chunk ----
+        if (!*(volatile int *)s_fail && !mbar_wait(bar_done, 0)) fail();
+        tc_after_sync();
+        if (!*(volatile int *)s_fail) {
+            const int quad = warp & 3, half = warp >> 2;
+            float *dst = part + (size_t)blockIdx.x * C::DSZ + quad * 32 + lane;
+            const uint32_t trow = tmem + ((uint32_t)(quad * 32) << 16);
+            for (int c0 = half * 8; c0 < C::DCOLS; c0 += 16) {
+                float v[8];
+                tc_ld8(trow + (uint32_t)c0, v);
+                tc_wait_ld();
+#pragma unroll
+                for (int i = 0; i < 8; i++) dst[(size_t)(c0 + i) * 128] = v[i];
+            }
+        }
+    }
+    tc_before_sync();
+    __syncthreads();
+    tc_after_sync();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(C::TCOLS) : "memory");
+}
+
+// The CTAs' accumulators summed in CTA order into the gradient: element (MMA jm, column n, row m)
+// maps back to (co, ci, ky, kx) through the staging above; the elements that hold no tap are
+// skipped, every tap is held by exactly one element.
+template <int CI, int CO>
+__global__ void k_net_wgrad_reduce(const float *part, int nparts, float *grad, int wofs) {
+    using C = Wg<CI, CO>;
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= C::DSZ) return;
+    const int m = e % 128, col = e / 128, jm = col / C::N, n = col % C::N;
+    int co, ci, ky, kx;
+    if (C::kAP) {
+        const int r = jm * 128 + m;   // P row (dx + 1) CI + ci of the k-step's first core
+        if (r >= C::RP) return;
+        kx = r / CI;
+        ci = r % CI;
+        ky = 2 - n / CO;
+        co = n % CO;
+    } else {
+        if (m >= 3 * CO || n >= 24 || n % 8 >= CI) return;
+        ky = 2 - m / CO;
+        co = m % CO;
+        kx = n / 8;
+        ci = n % 8;
+    }
+    float s = 0.f;
+    for (int c = 0; c < nparts; c++) s += part[(size_t)c * C::DSZ + e];
+    grad[wofs + (co * CI + ci) * 9 + ky * 3 + kx] += s;
 }
 
 // ------------------------------------------------------------------ optimiser --
@@ -1088,6 +1291,7 @@ struct lcc_net {
     int sms = 0;
     float *theta = nullptr, *grad = nullptr, *m = nullptr, *v = nullptr, *loss = nullptr;
     int *err = nullptr;                      // set by a kernel whose bounded wait ran out
+    float *wpart = nullptr;                  // per-CTA weight-gradient accumulators [sms][Wg::DSZ]
     NetDev nd{};
     NetAct act{};
     void *wbuf = nullptr, *abuf = nullptr;
@@ -1107,11 +1311,12 @@ lcc_status smem_attr(K kernel, size_t bytes) {
                : LCC_ERR_CUDA;
 }
 
-constexpr size_t wgrad_smem(int as) { return sizeof(bf16) * (size_t)kNetWarps * 100 * as; }
-
-int grid_for(const lcc_net *net, int64_t tiles) {
-    const int64_t want = (tiles + kNetWarps - 1) / kNetWarps;
-    return (int)std::max<int64_t>(1, std::min<int64_t>(want, net->sms));
+template <int CI, int CO>
+lcc_status wgrad_tc(lcc_net *net, const bf16 *a, const bf16 *dzt, int64_t ntiles, int grid, int wofs) {
+    using C = Wg<CI, CO>;
+    k_net_wgrad_tc<CI, CO><<<grid, kWgThreads, C::SMEM, net->stream>>>(a, dzt, ntiles, net->wpart, net->err);
+    k_net_wgrad_reduce<CI, CO><<<(C::DSZ + 255) / 256, 256, 0, net->stream>>>(net->wpart, grid, net->grad, wofs);
+    return cudaGetLastError() == cudaSuccess ? LCC_OK : LCC_ERR_CUDA;
 }
 
 // tcgen05 forward; with `train` it also keeps the activations the backward pass reads
@@ -1137,20 +1342,26 @@ lcc_status backward(lcc_net *net, const uint16_t *d_x, const float *d_labels, in
     LCC_CUDA(cudaMemsetAsync(net->loss, 0, sizeof(float), st));
     lcc_status s = forward_tc(net, d_x, ntiles, net->act.o, true);
     if (s != LCC_OK) return s;
-    k_net_head_bwd<<<grid_for(net, ntiles), kNetWarps * 32, 0, st>>>(net->nd, d_labels, ntiles, net->act, net->grad,
-                                                                     net->loss);
+    k_net_head_bwd<<<(unsigned)((ntiles + kHeadWarps - 1) / kHeadWarps), kHeadWarps * 32, 0, st>>>(net->nd, d_labels,
+                                                                                                  ntiles, net->act);
+    {   // the head's weight gradients and the loss, summed per block and then across blocks in order
+        const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>((ntiles + kHeadChunk - 1) / kHeadChunk, net->sms));
+        k_net_head_sums<<<blocks, kHeadSumThreads, 0, st>>>(ntiles, net->act, net->wpart);
+        k_net_head_reduce<<<(HS_N + 255) / 256, 256, 0, st>>>(net->wpart, blocks, 1.0f / (float)ntiles, net->grad,
+                                                            net->loss);
+    }
     {   // input gradients on tcgen05: one CTA per SM over pairs of tiles
         const int64_t pairs = (ntiles + 1) / 2;
         const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(pairs, net->sms));
         k_net_bwd_tc<<<grid, kTcThreads, kTcBwdSmem, st>>>(net->nd, ntiles, net->act, net->grad, net->err);
     }
-    const int slices = (int)std::max<int64_t>(1, std::min<int64_t>((ntiles + kNetWarps - 1) / kNetWarps, 64));
-    k_net_wgrad<C2, C3, 64, A2S><<<dim3(9 * C2 / 64, slices), kNetWarps * 32, wgrad_smem(A2S), st>>>(
-        net->act.a2, net->act.dz3t, ntiles, net->grad, OW3);
-    k_net_wgrad<C1, C2, 32, A1S><<<dim3(9 * C1 / 32, slices), kNetWarps * 32, wgrad_smem(A1S), st>>>(
-        net->act.a1, net->act.dz2t, ntiles, net->grad, OW2);
-    k_net_wgrad<C0, C1, 40, XS><<<dim3(1, slices), kNetWarps * 32, wgrad_smem(XS), st>>>(
-        reinterpret_cast<const bf16 *>(d_x), net->act.dz1t, ntiles, net->grad, OW1);
+    {   // weight gradients on tcgen05, then the CTAs' accumulators summed (one buffer, reused in order)
+        const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(ntiles, net->sms));
+        s = wgrad_tc<C2, C3>(net, net->act.a2, net->act.dz3t, ntiles, grid, OW3);
+        if (s == LCC_OK) s = wgrad_tc<C1, C2>(net, net->act.a1, net->act.dz2t, ntiles, grid, OW2);
+        if (s == LCC_OK) s = wgrad_tc<C0, C1>(net, reinterpret_cast<const bf16 *>(d_x), net->act.dz1t, ntiles, grid, OW1);
+        if (s != LCC_OK) return s;
+    }
     return cudaGetLastError() == cudaSuccess ? LCC_OK : LCC_ERR_CUDA;
 }
 
@@ -1221,7 +1432,8 @@ lcc_status lcc_net_create(lcc_net **out, const float *h_params, int64_t max_tile
     const size_t ab[] = {sizeof(bf16) * T * kPX * C1, sizeof(bf16) * T * kPX * C2, sizeof(bf16) * T * kPX * C3,
                          sizeof(float) * T * C3,      sizeof(float) * T * HID,      sizeof(float) * T * NOUT,
                          sizeof(float) * T * C3,      sizeof(bf16) * T * C1 * kPX,  sizeof(bf16) * T * C2 * kPX,
-                         sizeof(bf16) * T * C3 * kPX};
+                         sizeof(bf16) * T * C3 * kPX, sizeof(float) * (size_t)net->sms * Wg<C2, C3>::DSZ,
+                         sizeof(float) * T * HID,     sizeof(float) * T * HDO,      sizeof(float) * T};
     size_t atotal = 0;
     for (size_t b : ab) atotal += align256(b);
     if (cudaMalloc(&net->wbuf, wtotal) != cudaSuccess || cudaMalloc(&net->abuf, atotal) != cudaSuccess) {
@@ -1249,15 +1461,18 @@ lcc_status lcc_net_create(lcc_net **out, const float *h_params, int64_t max_tile
     char *a = (char *)net->abuf;
     void **slots[] = {(void **)&net->act.a1, (void **)&net->act.a2, (void **)&net->act.a3, (void **)&net->act.g,
                       (void **)&net->act.h,  (void **)&net->act.o,  (void **)&net->act.da3c, (void **)&net->act.dz1t,
-                      (void **)&net->act.dz2t, (void **)&net->act.dz3t};
-    for (int i = 0; i < 10; i++) {
+                      (void **)&net->act.dz2t, (void **)&net->act.dz3t, (void **)&net->wpart,
+                      (void **)&net->act.hdy, (void **)&net->act.hdo, (void **)&net->act.hlt};
+    for (int i = 0; i < 14; i++) {
         *slots[i] = a;
         a += align256(ab[i]);
     }
     if (smem_attr(k_net_bwd_tc, kTcBwdSmem) != LCC_OK ||
         smem_attr(k_net_fwd_tc<false>, kTcSmem) != LCC_OK ||
         smem_attr(k_net_fwd_tc<true>, kTcSmem) != LCC_OK ||
-        smem_attr(k_net_wgrad<C2, C3, 64, A2S>, wgrad_smem(A2S)) != LCC_OK ||
+        smem_attr(k_net_wgrad_tc<C2, C3>, Wg<C2, C3>::SMEM) != LCC_OK ||
+        smem_attr(k_net_wgrad_tc<C1, C2>, Wg<C1, C2>::SMEM) != LCC_OK ||
+        smem_attr(k_net_wgrad_tc<C0, C1>, Wg<C0, C1>::SMEM) != LCC_OK ||
         cudaMemcpy(net->theta, h_params, sizeof(float) * NPARAM, cudaMemcpyHostToDevice) != cudaSuccess ||
         cudaMemset(net->m, 0, sizeof(float) * 2 * NPARAM) != cudaSuccess ||
         cudaMemset(net->err, 0, sizeof(int)) != cudaSuccess || net_prep(net) != LCC_OK ||

@@ -176,6 +176,44 @@ def test_gradient_matches_oracle(frame):
     assert np.abs(t1 - ref)[big].max() <= 1e-6
 
 
+@pytest.mark.parametrize("nt", [1, 5, 37, 333])
+def test_weight_gradients_any_tile_count(frame, nt):
+    """The convolutions' weight gradients (tcgen05, one accumulator per CTA over its tiles, the
+    CTAs' copies summed in a fixed order) against the oracle's for tile counts below one tile per
+    SM, a few and an uneven number per CTA: per block a relative norm of at most 2e-2, and two runs
+    give the same bits (no atomics in the weights' sums); the head's gradients, summed per block of
+    tiles and then across blocks in order, as well."""
+    from paper_2008_06972_gb300 import lcc
+    sensor, pts = frame
+    _, x, _ = _gpu_inputs(sensor, pts)
+    s = O.sensor(sensor)
+    rng, _, _ = O.range_image(s, pts)
+    _, _, nv = N.tile_inputs(rng, O.beams(s))
+    idx = _sample(nv, nt, 7) if nt >= 8 else np.flatnonzero(nv >= 3)[:nt]
+    theta = _params(41)
+    net = lcc.Net(theta, max_tiles=nt)
+    xs = x[torch.from_numpy(idx).cuda()].contiguous()
+    y = _labels(len(idx), 9)
+    yd = torch.from_numpy(y).cuda()
+    runs = []
+    for _ in range(2):
+        grad = torch.zeros(N.N_PARAMS, dtype=torch.float32, device="cuda")
+        net.gradient(xs, yd, len(idx), grad, None)
+        torch.cuda.synchronize()
+        runs.append(grad.cpu().numpy())
+    _, go, _ = N.loss_and_grad(theta.astype(np.float64), _oracle_x(xs.cpu().numpy()), y.astype(np.float64),
+                               rounding=True)
+    o = 0
+    for name, shp in N.SHAPES:
+        n = int(np.prod(shp))
+        if name in ("W1", "W2", "W3", "F1", "c1", "F2", "c2"):
+            a, b = runs[0][o:o + n].astype(np.float64), go[o:o + n]
+            rel = np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-12)
+            assert rel <= 2e-2, (name, nt, rel)
+            assert np.array_equal(runs[0][o:o + n], runs[1][o:o + n]), name
+        o += n
+
+
 def test_training_lowers_the_loss(frame):
     """Labels from the plain GPU encoder (fit flag and plane per 8x8 tile); Adam on one frame."""
     from paper_2008_06972_gb300 import lcc
