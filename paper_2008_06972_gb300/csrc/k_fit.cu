@@ -804,6 +804,10 @@ __global__ void __launch_bounds__(kFitThreads) k_fit_first(Geometry g, Scratch s
             spatial_rounds(tv, o, g.R + 1, prop, b.skip_logit);
         } else if (b.kind == 1 && b.kf[f]) {
             queued = true;   // P-frame spatial fallback after its temporal test: from its first round, dense
+        } else if (g.first_rounds == 0) {
+            // every round on a lane group (schedule 5): only the proposal's skip is decided here
+            if (prop && prop[0] < b.skip_logit) o.flags |= 8;
+            else queued = true;
         } else {
             queued = !spatial_rounds(tv, o, g.first_rounds, prop, b.skip_logit);
         }
@@ -818,7 +822,8 @@ __global__ void __launch_bounds__(kFitThreads) k_fit_first(Geometry g, Scratch s
 // Further spatial rounds (at most max_rounds) for every queued tile, a group of
 // FitLanes::L lanes per tile (the few tiles that need them are latency-bound:
 // the group splits each round's pixel work); tiles that still need a round are
-// pushed onto the next queue.
+// pushed onto the next queue.  Under schedule 5 every tile that can be fitted
+// arrives here before its first round: a lane group per tile for all rounds.
 template <int TH_, int TW_>
 __global__ void __launch_bounds__(kFitThreads) k_fit_round(Geometry g, Scratch s, Batch b, int in_q, int out_q,
                                                              int max_rounds) {
@@ -839,7 +844,9 @@ __global__ void __launch_bounds__(kFitThreads) k_fit_round(Geometry g, Scratch s
         TileRec *recs = s.tiles + (size_t)b.slot[f] * g.NT;
         const TV tv(g, rimg, t, lane);
         RecOut o = read_rec(recs + t);
-        const bool done = spatial_rounds(tv, o, max_rounds);
+        // a tile queued before its first round starts from its proposal's inliers, as in the first pass
+        const float *prop = o.rounds == 0 && b.prop[f] ? b.prop[f] + 5 * (size_t)t : nullptr;
+        const bool done = spatial_rounds(tv, o, max_rounds, prop, b.skip_logit);
         const bool leader = tv.l == 0;
         queue_push(!done && leader, item, qout, qcount + out_q);
         if (leader) write_rec(recs + t, o);

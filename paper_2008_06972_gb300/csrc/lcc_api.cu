@@ -185,7 +185,7 @@ lcc_status encode_batch(lcc_ctx *c, int kind, int nframes, const int *slots, uin
     Batch b;
     Poses p;
     prepare_batch(b, p, kind, nframes, slots, d_out, cap, poses, kf, kf_out, nbytes_out, prop, skip_logit);
-    if (kind == 1 && kf && c->g.schedule == 4) {
+    if (kind == 1 && kf && c->g.schedule >= 4) {
         // P frames, spatial fits first: every tile's first round in the first pass (one thread per
         // tile, no temporal test), the queued tiles' remaining rounds and the run pre-test, then the
         // temporal test with a lane group per tile (a tile that passes becomes temporal exactly as
@@ -316,7 +316,7 @@ lcc_status lcc_create(lcc_ctx **out, const lcc_sensor *sensor, const lcc_params 
     if (!(p.fit_thr_m >= 0) || !(p.quant_m > 0) || p.max_refits < 0 || p.max_refits > 6 ||
         !(p.min_inlier_frac >= 0) || p.max_batch < 1 || p.max_batch > kMaxBatch || p.lookahead < 0 ||
         p.lookahead > 32 || p.solver < 0 || p.solver > 1 || p.fit_schedule < 0 ||
-        p.fit_schedule > 4 || p.no_delta < 0 || p.no_delta > 1 || p.raw_exact < 0 || p.raw_exact > 1 ||
+        p.fit_schedule > 5 || p.no_delta < 0 || p.no_delta > 1 || p.raw_exact < 0 || p.raw_exact > 1 ||
         p.temporal_candidates < 0 || p.temporal_candidates > 4 || p.temporal_runs < 0 || p.temporal_runs > 1 ||
         p.plane3 < 0 || p.plane3 > 1)
         return LCC_ERR_INVALID_ARG;
@@ -355,7 +355,7 @@ lcc_status lcc_create(lcc_ctx **out, const lcc_sensor *sensor, const lcc_params 
     g.tcand = p.temporal_candidates;
     g.truns = p.temporal_runs && p.merge_runs ? 1 : 0;
     g.plane3 = p.plane3 ? 1 : 0;
-    g.first_rounds = std::min(p.fit_schedule >= 3 ? 1 : p.fit_schedule, p.max_refits + 1);
+    g.first_rounds = p.fit_schedule == 5 ? 0 : std::min(p.fit_schedule >= 3 ? 1 : p.fit_schedule, p.max_refits + 1);
     g.k_max = (int)floorf(p.fit_thr_m / p.quant_m + 0.5f) + 1;
     g.w_res = bits_for(2 * g.k_max);
     const int m_max = (int)floorf((float)s.max_range_m / p.quant_m + 0.5f) + 1;

@@ -112,8 +112,9 @@ struct Geometry {
     int solver;          // 0 float-float plane solve, 1 FP64
     int schedule;        // 0 per-thread fit rounds; 1, 2: that many rounds per thread, the rest queued;
                          // 3: one round per thread, the rest in one dense launch; 4: as 3, and batched
-                         // P frames fit spatially first and run the temporal test after
-    int first_rounds;    // fit rounds of the first pass under a queued schedule
+                         // P frames fit spatially first and run the temporal test after; 5: as 4 with
+                         // every round on a lane group per tile (the first pass only queues)
+    int first_rounds;    // fit rounds of the first pass under a queued schedule (0 under schedule 5)
     int no_delta;        // 1: plane-coded points carry no residual code (no residual section)
     int raw_exact;       // 1: raw pixels carry their fp32 range bits (32-bit raw codes)
     int tcand;           // K tiles a P tile's relaxed-plane test may try (1..4)

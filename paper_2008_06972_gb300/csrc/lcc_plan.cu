@@ -246,8 +246,8 @@ lcc_status enqueue_class(PlanClass &pc, lcc_net *net, float skip_logit, int64_t 
             LCC_CUDA(cudaMemcpyAsync(pc.stats + (kind ? pc.keys.size() : 0) + base, c->s.stats, sizeof(DevStats) * m,
                                      cudaMemcpyDeviceToDevice, c->stream));
             c->last_nframes = m;
-            *launches += 1 + 3 + (c->g.lookahead > 0 ? 1 : 0) + (kind == 1 && c->g.schedule == 4 ? 1 : 0) +
-                         (kind == 1 && c->g.schedule == 4 && c->g.truns && c->g.lookahead > 0 ? 1 : 0) +
+            *launches += 1 + 3 + (c->g.lookahead > 0 ? 1 : 0) + (kind == 1 && c->g.schedule >= 4 ? 1 : 0) +
+                         (kind == 1 && c->g.schedule >= 4 && c->g.truns && c->g.lookahead > 0 ? 1 : 0) +
                          (c->g.schedule >= 3 ? 1
                           : c->g.schedule >= 1 ? c->g.R + 1 - (kind == 1 ? 0 : c->g.first_rounds) : 0);
         }

@@ -212,7 +212,11 @@ def test_autotune_picks_fastest_within_byte_slack():
     base = lcc.default_params(max_batch=8)
     best, rows = lcc.autotune(s.sensor, base, k, s.poses, ds, [len(f) for f in s.frames], reps=2,
                               stream=torch.cuda.current_stream())
-    assert len(rows) == 4 * 3 * 3
+    assert len(rows) == 4 * 3 * 4   # tile shapes x horizons x fit schedules {0, 3, 4, 5}
+    assert sorted({r["fit_schedule"] for r in rows}) == [0, 3, 4, 5]
+    # every schedule fits the same planes: per tile shape and horizon one stream size
+    for th, tw, la in {(r["tile_h"], r["tile_w"], r["lookahead"]) for r in rows}:
+        assert len({r["bytes"] for r in rows if (r["tile_h"], r["tile_w"], r["lookahead"]) == (th, tw, la)}) == 1
     ok = [r for r in rows if r["status"] == lcc.OK]
     assert len(ok) == len(rows)
     assert all(r["max_err_m"] <= 0.01 + 1e-5 for r in ok)

@@ -28,7 +28,7 @@ k = synth.group_key(0, 5, 10)
 d = [torch.from_numpy(f).cuda() for f in s.frames]
 n = [len(f) for f in s.frames]
 for th, tw in ((4, 4), (4, 8), (8, 8), (8, 16)):
-    for sched in (0, 3):
+    for sched in (0, 3, 5):
         c = lcc.Context(sen, lcc.default_params(max_batch=5, tile_h=th, tile_w=tw, fit_schedule=sched))
         cap = c.max_encoded_bytes
         outs = [torch.zeros(cap, dtype=torch.uint8, device="cuda") for _ in range(5)]

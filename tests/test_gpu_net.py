@@ -275,6 +275,16 @@ def test_seeded_keyframe_parity(frame):
     assert st == lcc.OK
     m = rng > 0
     assert np.abs(drng[m] - rng[m]).max() <= 0.01 + 1e-5
+    # fit schedule 5 (every round, the seeded first included, on a lane group per tile): the same
+    # tile records and stream
+    c5 = H.ctx(sensor, tile_h=8, tile_w=8, fit_schedule=5)
+    out5 = H.out_buf(c5)
+    c5.lcc_encode_keyframe_seeded(H.to_dev(pts), len(pts), d_prop, SKIP_LOGIT, None, out5, out5.numel(), nb)
+    assert c5.lcc_sync() == lcc.OK
+    assert out5[:int(nb.item())].cpu().numpy().tobytes() == gbits.tobytes()
+    r5 = c5.lcc_tile_records(0)
+    for k in ("plane", "status", "rounds", "n_inlier", "flags"):
+        assert np.array_equal(r5[k], grecs[k]), k
 
 
 def test_trained_net_saves_fit_rounds_on_held_out_frames():
