@@ -438,7 +438,11 @@ lcc_status lcc_range_image_static(const lcc_sensor *sensor, const float *d_pts, 
  * all key frames are encoded first, then all P frames, in chunks of the
  * context's max_batch frames, each chunk one batched launch set.  With more
  * than one class, each class runs on its own stream between a fork and a
- * join, so the classes overlap on the GPU.
+ * join, so the classes overlap on the GPU; each class after the first starts
+ * once the one before it has binned its first chunk, so that one class's
+ * binning (over the host link for host points) meets the others' fits and
+ * packs.  Sequences of one sensor may be spread over several contexts of the
+ * same parameters to have their chunks overlap in this way.
  *
  * Key-frame groups: group g of a sequence covers frames [g*I, min((g+1)*I, n))
  * with I = key_interval; its key frame is the group's frame start + floor(len/2).
@@ -498,6 +502,17 @@ lcc_status lcc_plan_update(lcc_plan *plan, int32_t nseq, const lcc_seq_desc *seq
  * re-recorded and its executable graph updated in place.  A bounded wait of the inference that
  * ran out is reported by lcc_plan_sync (LCC_ERR_TIMEOUT). */
 lcc_status lcc_plan_set_proposals(lcc_plan *plan, lcc_net *net, float skip_logit);
+/* Staging of host points (not in the paper; an I/O choice).  enable = 1: the points of frames
+ * that are page-locked host memory are copied by the copy engines, one cudaMemcpyAsync per
+ * frame on a copy stream of the class, into one of two device buffers of a chunk (the class
+ * context's max_batch frames, each the size of the class's largest such frame) ahead of that
+ * chunk's binning, so that the copies of one chunk run while the previous chunk is encoded
+ * and the binning reads device memory; a buffer is refilled only after the chunk that used it
+ * is binned.  enable = 0 (the default): the binning kernels read such points in place over the
+ * host link.  The streams are the same either way.  Allocates 2 x max_batch x (largest host
+ * frame) x 16 bytes per class (grown by lcc_plan_update if a frame grows); device points are not
+ * copied.  A captured plan is re-recorded.  LCC_ERR_INVALID_ARG for enable outside 0..1. */
+lcc_status lcc_plan_set_staging(lcc_plan *plan, int32_t enable);
 /* Enqueues one encode of the whole table (asynchronous, no graph). */
 lcc_status lcc_plan_encode(lcc_plan *plan);
 /* Records one encode of the table as a CUDA graph (nothing runs).  Not allowed while

@@ -25,7 +25,9 @@ constexpr int kMaxPlanContexts = 8;
 struct PlanFrame {
     int seq, frame;       // position in the caller's table
     int table;            // key-frame plane table (index into the context's tables)
-    const float *pts;
+    const float *pts;     // where the device reads the points (device memory, or host memory's device view)
+    const float *src;     // the caller's pointer
+    bool host;            // the points are page-locked host memory
     int64_t n;
     uint8_t *out;
     uint64_t cap;
@@ -37,6 +39,7 @@ struct PlanClass {
     lcc_ctx *ctx = nullptr;
     cudaStream_t side = nullptr;     // side stream when the plan has several classes
     cudaEvent_t done = nullptr;
+    cudaEvent_t first_bin = nullptr; // the class's first chunk is binned (the next class starts after it)
     float4 *tables = nullptr;        // ngroups x NT key-frame planes
     int ngroups = 0;
     std::vector<PlanFrame> keys, pframes;
@@ -49,6 +52,13 @@ struct PlanClass {
     uint32_t *pairs = nullptr;       // pairs of tiles with a needed tile, and their count
     uint32_t *npairs = nullptr;
     DevStats *stats = nullptr;       // per frame of the last encode, in enqueue order (keys, then P frames)
+    // staging of host points by the copy engines (lcc_plan_set_staging): two device buffers of a
+    // chunk each (slots x stage_n points), filled on the class's copy stream
+    bool staged = false;
+    cudaStream_t cstream = nullptr;
+    cudaEvent_t copied[2] = {nullptr, nullptr}, consumed[2] = {nullptr, nullptr};
+    float4 *stage = nullptr;
+    int64_t stage_n = 0;
 };
 
 }  // namespace
@@ -65,6 +75,7 @@ struct lcc_plan {
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
     lcc_net *net = nullptr;          // proposal net of the seeded key frames (not owned)
+    bool staging = false;            // host points copied by the copy engines ahead of each chunk
     float skip_logit = 0.f;
     // host-output path (lcc_plan_encode_host): one copy item per frame, in table order
     struct CopyItem *d_items = nullptr;
@@ -115,13 +126,15 @@ int key_of(int frame, int nframes, int interval, int *group) {
 // Address the device reads a frame's points at: device (or managed) memory as given, page-locked
 // host memory through its device view (read in place over the host link); NULL for host memory
 // the device cannot address.
-const float *points_view(const float *p) {
+const float *points_view(const float *p, bool *host) {
+    *host = false;
     cudaPointerAttributes a;
     if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
         cudaGetLastError();
         return nullptr;
     }
     if (a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged) return p;
+    *host = a.type == cudaMemoryTypeHost;
     if (a.type == cudaMemoryTypeHost && a.devicePointer) return static_cast<const float *>(a.devicePointer);
     return nullptr;
 }
@@ -150,7 +163,8 @@ lcc_status fill(lcc_plan *p, int32_t nseq, const lcc_seq_desc *seqs, bool check_
             return LCC_ERR_INVALID_ARG;
         for (int f = 0; f < d.nframes; f++) {
             if (d.n[f] < 0 || d.n[f] > (int64_t)1 << 31) return LCC_ERR_INVALID_ARG;
-            const float *pts = d.n[f] > 0 && d.d_pts[f] ? points_view(d.d_pts[f]) : nullptr;
+            bool host = false;
+            const float *pts = d.n[f] > 0 && d.d_pts[f] ? points_view(d.d_pts[f], &host) : nullptr;
             if (d.n[f] > 0 && (!pts || !aligned16(pts))) return LCC_ERR_INVALID_ARG;
             if (!d.d_out[f] || !aligned16(d.d_out[f]) || d.cap[f] < (uint64_t)kHeaderBytes ||
                 !device_memory(d.d_out[f]))
@@ -162,6 +176,8 @@ lcc_status fill(lcc_plan *p, int32_t nseq, const lcc_seq_desc *seqs, bool check_
             pf.frame = f;
             pf.table = group_base[d.ctx] + grp;
             pf.pts = pts;
+            pf.src = d.d_pts[f];
+            pf.host = host;
             pf.n = d.n[f];
             pf.out = d.d_out[f];
             pf.cap = d.cap[f];
@@ -194,6 +210,8 @@ lcc_status fill(lcc_plan *p, int32_t nseq, const lcc_seq_desc *seqs, bool check_
 lcc_status enqueue_class(PlanClass &pc, lcc_net *net, float skip_logit, int64_t *launches) {
     lcc_ctx *c = pc.ctx;
     const int NT = c->g.NT;
+    int chunk = 0;                      // chunks of the class so far: staging buffer chunk % 2
+    bool used[2] = {false, false};      // staging buffer b was filled for an earlier chunk of this encode
     for (int kind = 0; kind < 2; kind++) {
         const std::vector<PlanFrame> &list = kind == 0 ? pc.keys : pc.pframes;
         const bool seeded = kind == 0 && pc.seeded && net;
@@ -223,8 +241,29 @@ lcc_status enqueue_class(PlanClass &pc, lcc_net *net, float skip_logit, int64_t 
                 props[f] = seeded ? pc.prop + (size_t)f * NT * 5 : nullptr;
                 memcpy(poses.data() + 16 * (size_t)f, pf.pose, sizeof(pf.pose));
             }
+            // staged class: the chunk's host points are copied (one copy per frame, copy stream) into
+            // buffer b once the chunk two before it, which used b, is binned; the binning waits for them
+            const int b = chunk++ & 1;
+            bool staged = false;
+            for (int f = 0; f < m; f++) staged = staged || (pc.staged && list[base + f].host && n[f] > 0);
+            if (staged) {
+                if (used[b]) LCC_CUDA(cudaStreamWaitEvent(pc.cstream, pc.consumed[b], 0));
+                for (int f = 0; f < m; f++) {
+                    const PlanFrame &pf = list[base + f];
+                    if (!pf.host || pf.n <= 0) continue;
+                    float4 *dst = pc.stage + ((size_t)b * c->slots + f) * (size_t)pc.stage_n;
+                    LCC_CUDA(cudaMemcpyAsync(dst, pf.src, sizeof(float4) * (size_t)pf.n, cudaMemcpyHostToDevice,
+                                             pc.cstream));
+                    pts[f] = reinterpret_cast<const float *>(dst);
+                }
+                LCC_CUDA(cudaEventRecord(pc.copied[b], pc.cstream));
+                LCC_CUDA(cudaStreamWaitEvent(c->stream, pc.copied[b], 0));
+            }
             lcc_status st = bin_frames(c, m, slots, pts, n);
             if (st != LCC_OK) return st;
+            if (staged) LCC_CUDA(cudaEventRecord(pc.consumed[b], c->stream));
+            used[b] = staged;
+            if (kind == 0 && base == 0 && pc.first_bin) LCC_CUDA(cudaEventRecord(pc.first_bin, c->stream));
             if (seeded) {
                 // the net runs only on pairs of tiles with a tile that can be fitted: the seeded fit
                 // reads no other tile's proposal (empty sky and sparse tiles are often half a frame)
@@ -257,14 +296,24 @@ lcc_status enqueue_class(PlanClass &pc, lcc_net *net, float skip_logit, int64_t 
 
 // Every launch of the plan, ordered after earlier work on `main`.  With several classes each
 // class runs on its own side stream between a fork and a join event, so classes overlap on the
-// GPU.  The contexts' launches go to the chosen stream for the duration of the call.
+// GPU; each class after the first starts once the class before it has binned its first chunk,
+// so that the classes' binning (over the host link when the points are in host memory) falls
+// beside the other classes' fits and packs rather than beside their binning.  The contexts'
+// launches go to the chosen stream for the duration of the call.
 lcc_status enqueue(lcc_plan *p, cudaStream_t main) {
     int64_t launches = 0;
     const bool forked = p->cls.size() > 1;
-    if (forked) LCC_CUDA(cudaEventRecord(p->fork, main));
+    bool any_staged = false;
+    for (const auto &pc : p->cls) any_staged = any_staged || pc.staged;
+    if (forked || any_staged) LCC_CUDA(cudaEventRecord(p->fork, main));
     lcc_status st = LCC_OK;
+    const PlanClass *prev = nullptr;
     for (auto &pc : p->cls) {
         if (forked && cudaStreamWaitEvent(pc.side, p->fork, 0) != cudaSuccess) return LCC_ERR_CUDA;
+        if (pc.staged && cudaStreamWaitEvent(pc.cstream, p->fork, 0) != cudaSuccess) return LCC_ERR_CUDA;
+        if (forked && prev && !prev->keys.empty() && cudaStreamWaitEvent(pc.side, prev->first_bin, 0) != cudaSuccess)
+            return LCC_ERR_CUDA;
+        prev = &pc;
         pc.ctx->stream = forked ? pc.side : main;
         st = enqueue_class(pc, p->net, p->skip_logit, &launches);
         pc.ctx->stream = p->stream;
@@ -283,6 +332,13 @@ void release(lcc_plan *p) {
     for (auto &pc : p->cls) {
         if (pc.side) cudaStreamDestroy(pc.side);
         if (pc.done) cudaEventDestroy(pc.done);
+        if (pc.first_bin) cudaEventDestroy(pc.first_bin);
+        if (pc.cstream) cudaStreamDestroy(pc.cstream);
+        for (int b = 0; b < 2; b++) {
+            if (pc.copied[b]) cudaEventDestroy(pc.copied[b]);
+            if (pc.consumed[b]) cudaEventDestroy(pc.consumed[b]);
+        }
+        cudaFree(pc.stage);
         cudaFree(pc.tables);
         cudaFree(pc.x);
         cudaFree(pc.anchor);
@@ -298,6 +354,35 @@ void release(lcc_plan *p) {
     cudaFree(p->d_sizes);
     if (p->h_sizes) cudaFreeHost(p->h_sizes);
     delete p;
+}
+
+// Staging buffers and copy streams of the classes with host points (when staging is on): two
+// chunks of the context's slots at the class's largest host frame; grown when an update needs it.
+lcc_status ensure_staging(lcc_plan *p) {
+    for (auto &pc : p->cls) {
+        int64_t need = 0;
+        for (const auto *list : {&pc.keys, &pc.pframes})
+            for (const auto &pf : *list)
+                if (pf.host) need = std::max(need, pf.n);
+        pc.staged = p->staging && need > 0;
+        if (!pc.staged) continue;
+        if (!pc.cstream) {
+            if (cudaStreamCreateWithFlags(&pc.cstream, cudaStreamNonBlocking) != cudaSuccess) return LCC_ERR_CUDA;
+            for (int b = 0; b < 2; b++)
+                if (cudaEventCreateWithFlags(&pc.copied[b], cudaEventDisableTiming) != cudaSuccess ||
+                    cudaEventCreateWithFlags(&pc.consumed[b], cudaEventDisableTiming) != cudaSuccess)
+                    return LCC_ERR_CUDA;
+        }
+        if (need > pc.stage_n) {
+            LCC_CUDA(cudaStreamSynchronize(p->stream));   // a replay may still read the old buffers
+            cudaFree(pc.stage);
+            pc.stage = nullptr;
+            pc.stage_n = 0;
+            LCC_CUDA(cudaMalloc(&pc.stage, sizeof(float4) * 2 * (size_t)pc.ctx->slots * (size_t)need));
+            pc.stage_n = need;
+        }
+    }
+    return LCC_OK;
 }
 
 }  // namespace
@@ -337,6 +422,7 @@ lcc_status lcc_plan_create(lcc_plan **out, int32_t nctx, lcc_ctx *const *ctxs, i
         if (nctx > 1) {
             ok = ok && cudaStreamCreateWithFlags(&pc.side, cudaStreamNonBlocking) == cudaSuccess;
             ok = ok && cudaEventCreateWithFlags(&pc.done, cudaEventDisableTiming) == cudaSuccess;
+            ok = ok && cudaEventCreateWithFlags(&pc.first_bin, cudaEventDisableTiming) == cudaSuccess;
         }
     }
     if (!ok || cudaDeviceSynchronize() != cudaSuccess) {
@@ -355,6 +441,7 @@ lcc_status lcc_plan_update(lcc_plan *p, int32_t nseq, const lcc_seq_desc *seqs) 
             return LCC_ERR_INVALID_ARG;
     lcc_status st = fill(p, nseq, seqs, true);
     if (st != LCC_OK) return st;
+    if ((st = ensure_staging(p)) != LCC_OK) return st;
     if (!p->exec) return LCC_OK;
     // re-record with the new pointers, counts and poses and update the executable graph in place
     return lcc_plan_capture(p);
@@ -398,6 +485,15 @@ lcc_status lcc_plan_set_proposals(lcc_plan *p, lcc_net *net, float skip_logit) {
     p->skip_logit = skip_logit;
     if (!p->exec) return LCC_OK;
     // the captured graph no longer matches: re-record it and update the executable in place
+    return lcc_plan_capture(p);
+}
+
+lcc_status lcc_plan_set_staging(lcc_plan *p, int32_t enable) {
+    if (!p || enable < 0 || enable > 1) return LCC_ERR_INVALID_ARG;
+    p->staging = enable != 0;
+    const lcc_status st = ensure_staging(p);
+    if (st != LCC_OK) return st;
+    if (!p->exec) return LCC_OK;
     return lcc_plan_capture(p);
 }
 

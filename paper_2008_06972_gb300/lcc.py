@@ -137,6 +137,7 @@ def load(path: str = LIB_PATH):
         "lcc_plan_create": (i32, [vp, i32, vp, i32, vp]),
         "lcc_plan_update": (i32, [vp, i32, vp]),
         "lcc_plan_set_proposals": (i32, [vp, vp, ctypes.c_float]),
+        "lcc_plan_set_staging": (i32, [vp, i32]),
         "lcc_plan_encode": (i32, [vp]),
         "lcc_plan_capture": (i32, [vp]),
         "lcc_plan_replay": (i32, [vp]),
@@ -165,7 +166,7 @@ def exported_symbols() -> list[str]:
             "lcc_tile_records", "lcc_tile_coefficients", "lcc_set_profiling", "lcc_kernel_times", "lcc_kernel_timeline", "lcc_range_image_static", "lcc_net_num_params", "lcc_net_create", "lcc_net_destroy",
             "lcc_net_get_params", "lcc_net_set_params", "lcc_net_tile_inputs", "lcc_net_tile_inputs_batch", "lcc_net_forward", "lcc_net_sync", "lcc_net_gradient",
             "lcc_net_train_step", "lcc_selftest_bounded_wait", "lcc_plan_create", "lcc_plan_update",
-            "lcc_plan_set_proposals", "lcc_plan_encode", "lcc_plan_capture", "lcc_plan_replay", "lcc_plan_sync", "lcc_plan_encode_host", "lcc_plan_get_info", "lcc_plan_stats",
+            "lcc_plan_set_proposals", "lcc_plan_set_staging", "lcc_plan_encode", "lcc_plan_capture", "lcc_plan_replay", "lcc_plan_sync", "lcc_plan_encode_host", "lcc_plan_get_info", "lcc_plan_stats",
             "lcc_plan_destroy", "lcc_autotune"]
 
 
@@ -487,6 +488,10 @@ class Plan:
         self.net = net
         _check(self.lib.lcc_plan_set_proposals(self.h, net.h if net is not None else None, skip_logit),
                "lcc_plan_set_proposals")
+
+    def set_staging(self, enable: bool):
+        """Host points copied by the copy engines ahead of each chunk (lcc_plan_set_staging)."""
+        _check(self.lib.lcc_plan_set_staging(self.h, int(enable)), "lcc_plan_set_staging")
 
     def encode(self):
         _check(self.lib.lcc_plan_encode(self.h), "lcc_plan_encode")

@@ -70,7 +70,7 @@ def test_seeded_plan_matches_oracle_on_large_frames(trained_net, batch):
     k0 = synth.group_key(0, NFR, 10)
     best, rows = lcc.autotune(sensor, lcc.default_params(max_batch=10), k0, seqs[0].poses[:10], d_pts[0][:10],
                               [len(f) for f in seqs[0].frames[:10]], reps=1, stream=stream, shapes=[(8, 8)])
-    assert (best.tile_h, best.tile_w) == (8, 8) and len(rows) == 3 * 3
+    assert (best.tile_h, best.tile_w) == (8, 8) and len(rows) == 3 * 4   # horizons x fit schedules
     best.max_batch = 3            # several chunks of key and P frames
     ctx = lcc.Context(sensor, best, stream=stream)
     descs = []
@@ -174,8 +174,9 @@ def test_seeded_plan_matches_oracle_on_large_frames(trained_net, batch):
 
 
 def test_plan_host_outputs_match_device_outputs(batch):
-    """lcc_plan_encode_host (page-locked points read in place, streams copied to page-locked host
-    buffers by one kernel) writes the streams the device-buffer plan writes."""
+    """lcc_plan_encode_host (page-locked points read in place or staged by the copy engines,
+    streams copied to page-locked host buffers by one kernel) writes the streams the device-buffer
+    plan writes."""
     from paper_2008_06972_gb300 import lcc
     seqs, host = batch
     stream = torch.cuda.current_stream()
@@ -206,8 +207,32 @@ def test_plan_host_outputs_match_device_outputs(batch):
             assert int(sizes[i * NFR + f]) == int(nb[f])
             assert h_out[i * NFR + f][:int(nb[f])].numpy().tobytes() == \
                 d["d_out"][f][:int(nb[f])].cpu().numpy().tobytes(), f"seq {i} frame {f}"
+    # the points staged by the copy engines (two chunk buffers, one copy per frame) instead of read
+    # in place: the same streams; then spread over two contexts of the same parameters, whose
+    # classes run on two streams, each with its own staging
+    p_host.set_staging(True)
+    for ho in h_out:
+        ho.zero_()
+    sizes = p_host.encode_host(h_out)
+    ctx2 = H.ctx(synth.CFG5_SENSOR, tile_h=8, tile_w=16, max_batch=4, stream=stream)
+    for k, d in enumerate(host_descs):
+        d["ctx"] = k % 2
+    p_two = lcc.Plan([ctx, ctx2], host_descs)
+    p_two.set_staging(True)
+    p_two.capture()
+    sizes2 = p_two.encode_host(h_out)
+    assert np.array_equal(sizes, sizes2)
+    for i, d in enumerate(dev_descs):
+        nb = d["d_nbytes"].cpu().numpy()
+        for f in range(NFR):
+            assert int(sizes[i * NFR + f]) == int(nb[f])
+            assert h_out[i * NFR + f][:int(nb[f])].numpy().tobytes() == \
+                d["d_out"][f][:int(nb[f])].cpu().numpy().tobytes(), f"staged: seq {i} frame {f}"
+    p_two.close()
     # pageable host outputs are rejected before anything runs
     with pytest.raises(lcc.LccError):
         p_host.encode_host([np.zeros(cap, np.uint8) for _ in range(NSEQ * NFR)])
+    with pytest.raises(lcc.LccError):
+        p_host.set_staging(2)
     p_dev.close()
     p_host.close()
