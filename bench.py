@@ -162,8 +162,8 @@ TRAFFIC_FILE_CFG5 = os.path.join(ROOT, "profiles", "dram_traffic_cfg5_plan.txt")
 
 
 def measured_traffic_cfg5(kernel: str):
-    """DRAM bytes per launch of a headline-plan kernel from the committed ncu summary (scaled to a
-    full launch as that file states), or None when the kernel's sources changed since."""
+    """DRAM bytes per frame of a headline-plan kernel from the committed ncu summary (to be scaled
+    by the frames of a launch), or None when the kernel's sources changed since."""
     if kernel not in KERNEL_SOURCES:
         return None
     try:
@@ -1228,7 +1228,7 @@ def run_cfg5(args, stream, rank, world, dist):
     # ---- per-kernel times: one eager encode of each plan with a CUDA event pair around every launch ----
     hbm, src = peaks()
     tpeak, tsrc = bf16_peak()
-    kernels, stats = {}, {}
+    kernels, stats, stats_info = {}, {}, {}
     for kind in ("learned", "plain", "plain_8x8"):
         # one lane, so that no other launch shares the GPU while a launch is timed
         (c,), pplan = build_plan(kind, tuned[kind][1]["frames_per_launch"], tuned[kind][1]["lookahead"], 1,
@@ -1241,6 +1241,7 @@ def run_cfg5(args, stream, rank, world, dist):
         st = pplan.stats()
         pplan.close()
         info = plans[kind].info()
+        stats_info[kind] = info
         p_ = tuned[kind][0]
         nt = c.num_tiles
         units = kernel_units(st, nf, nf - info["key_frames"], info["seeded_key_frames"], npx, nt,
@@ -1265,9 +1266,14 @@ def run_cfg5(args, stream, rank, world, dist):
         stats[kind] = st
     dname = max(kernels["learned"].items(), key=lambda kv: kv[1]["ms"])[0]
     d = kernels["learned"][dname]
+    # measured DRAM bytes per frame x the frames one launch of that kernel processed
+    per_frame = measured_traffic_cfg5(dname)
+    nfp = nf - stats_info["learned"]["key_frames"]
+    frames_done = {"temporal": nfp, "lookbehind": nf + nfp}.get(dname, nf)
+    traffic_per_launch = per_frame * frames_done / d["launches"] if per_frame is not None else None
     roof = {"bound": d["bound"], "kernel": dname, "achieved": d["achieved"],
             "peak": tpeak if d["bound"] == "tensor" else hbm, "unit": d["unit"], "frac": d["frac"],
-            "traffic": measured_traffic_cfg5(dname), "alg_per_launch": d["alg_per_launch"],
+            "traffic": traffic_per_launch, "alg_per_launch": d["alg_per_launch"],
             "peak_source": tsrc if d["bound"] == "tensor" else src,
             "path": {"alg_bytes_per_step": 16.0 * total_pts + bytes_l,
                      "achieved": (16.0 * total_pts + bytes_l) / (ms_l * 1e-3) / 1e9,

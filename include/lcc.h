@@ -438,11 +438,11 @@ lcc_status lcc_range_image_static(const lcc_sensor *sensor, const float *d_pts, 
  * all key frames are encoded first, then all P frames, in chunks of the
  * context's max_batch frames, each chunk one batched launch set.  With more
  * than one class, each class runs on its own stream between a fork and a
- * join, so the classes overlap on the GPU; each class after the first starts
- * once the one before it has binned its first chunk, so that one class's
- * binning (over the host link for host points) meets the others' fits and
- * packs.  Sequences of one sensor may be spread over several contexts of the
- * same parameters to have their chunks overlap in this way.
+ * join, so the classes overlap on the GPU; when a class's points are in host
+ * memory the next class starts once it has binned its first chunk, so that
+ * one class's binning (over the host link) meets the others' fits and packs.
+ * Sequences of one sensor may be spread over several contexts of the same
+ * parameters to have their chunks overlap in this way.
  *
  * Key-frame groups: group g of a sequence covers frames [g*I, min((g+1)*I, n))
  * with I = key_interval; its key frame is the group's frame start + floor(len/2).

@@ -296,8 +296,8 @@ lcc_status enqueue_class(PlanClass &pc, lcc_net *net, float skip_logit, int64_t 
 
 // Every launch of the plan, ordered after earlier work on `main`.  With several classes each
 // class runs on its own side stream between a fork and a join event, so classes overlap on the
-// GPU; each class after the first starts once the class before it has binned its first chunk,
-// so that the classes' binning (over the host link when the points are in host memory) falls
+// GPU.  When a class's points are in host memory, the next class starts once it has binned its
+// first chunk, so that the classes' binning (over the host link, or their staged copies) falls
 // beside the other classes' fits and packs rather than beside their binning.  The contexts'
 // launches go to the chosen stream for the duration of the call.
 lcc_status enqueue(lcc_plan *p, cudaStream_t main) {
@@ -311,7 +311,8 @@ lcc_status enqueue(lcc_plan *p, cudaStream_t main) {
     for (auto &pc : p->cls) {
         if (forked && cudaStreamWaitEvent(pc.side, p->fork, 0) != cudaSuccess) return LCC_ERR_CUDA;
         if (pc.staged && cudaStreamWaitEvent(pc.cstream, p->fork, 0) != cudaSuccess) return LCC_ERR_CUDA;
-        if (forked && prev && !prev->keys.empty() && cudaStreamWaitEvent(pc.side, prev->first_bin, 0) != cudaSuccess)
+        if (forked && prev && !prev->keys.empty() && prev->keys.front().host &&
+            cudaStreamWaitEvent(pc.side, prev->first_bin, 0) != cudaSuccess)
             return LCC_ERR_CUDA;
         prev = &pc;
         pc.ctx->stream = forked ? pc.side : main;
