@@ -268,6 +268,7 @@ constexpr size_t kTcSmem = (size_t)TW1 + TW2 + TW3 + kTcSlots * (size_t)(TACT + 
 constexpr uint32_t kTmemCols = 256;             // one 64-column accumulator per pair slot (3 x 64, rounded up)
 constexpr long long kSpinLimit = 1ll << 22;
 static_assert(kTcSmem <= 227 * 1024, "shared memory of the tcgen05 forward");
+static_assert((1 + 4 * kTcSlots) * 8 + 8 <= 128, "the forward's barriers, TMEM address and failure flag fit");
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -375,7 +376,8 @@ __device__ __forceinline__ void bulk_g2s(uint32_t dst, const void *src, uint32_t
 // the finished layer back.  The MMA warp serves whichever slot is ready, so one pair's
 // epilogue, pooling and head overlap the other pairs' convolutions.
 constexpr int kTcEpiWarps = 4 * kTcSlots;
-constexpr int kTcThreads = (kTcEpiWarps + 1) * 32;
+constexpr int kTcThreads = (kTcEpiWarps + 1) * 32;    // the input-gradient kernel: + the MMA warp
+constexpr int kFwdThreads = (kTcEpiWarps + 2) * 32;   // the forward: + the MMA warp and the head warp
 
 __device__ __forceinline__ void mbar_arrive(uint32_t mbar) {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(mbar) : "memory");
@@ -398,7 +400,7 @@ __device__ __forceinline__ void group_sync(int slot) {
 }
 
 template <bool kTrain>
-__global__ void __launch_bounds__(kTcThreads, 1) k_net_fwd_tc(NetDev nd, const bf16 *x, long long T, float *out,
+__global__ void __launch_bounds__(kFwdThreads, 1) k_net_fwd_tc(NetDev nd, const bf16 *x, long long T, float *out,
                                                               int *err, NetAct act, const uint32_t *pairs = nullptr,
                                                               const uint32_t *npairs = nullptr) {
     extern __shared__ __align__(1024) uint8_t sm[];
@@ -408,17 +410,21 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_net_fwd_tc(NetDev nd, const b
     float *sPar = sG + kTcSlots * 2 * C3;                              // b1 b2 b3 F1b c1 F2b c2
     float *sB1 = sPar, *sB2 = sB1 + C1, *sB3 = sB2 + C2, *sF1 = sB3 + C3, *sC1 = sF1 + HID * C3;
     float *sF2 = sC1 + HID, *sC2 = sF2 + NOUT * HID;
-    // barriers: [0] weights, [1 + s] layer done (tcgen05.commit), [1 + kTcSlots + s] layer input ready
+    // barriers: [0] weights, [1 + s] layer done (tcgen05.commit), [1 + kTcSlots + s] layer input ready,
+    // [1 + 2 kTcSlots + s] pooled vectors ready (the slot's four warps), [1 + 3 kTcSlots + s] pooled
+    // vectors read (the head warp)
     uint64_t *bar = reinterpret_cast<uint64_t *>(reinterpret_cast<uint8_t *>(sPar) + TPAR);
-    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bar + 1 + 2 * kTcSlots);
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bar + 1 + 4 * kTcSlots);
     int *s_fail = reinterpret_cast<int *>(tmem_slot + 1);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const float *th = nd.theta;
     if (tid == 0) {
         for (int i = 0; i < 1 + kTcSlots; i++)
             asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(bar + i)) : "memory");
-        for (int i = 1 + kTcSlots; i < 1 + 2 * kTcSlots; i++)
+        for (int i = 1 + kTcSlots; i < 1 + 3 * kTcSlots; i++)
             asm volatile("mbarrier.init.shared::cta.b64 [%0], 4;\n" ::"r"(smem_u32(bar + i)) : "memory");
+        for (int i = 1 + 3 * kTcSlots; i < 1 + 4 * kTcSlots; i++)
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(bar + i)) : "memory");
         *s_fail = 0;
     }
     {
@@ -504,6 +510,67 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_net_fwd_tc(NetDev nd, const b
             }
         }
         __syncwarp();
+    } else if (warp == kTcEpiWarps + 1) {
+        // ---- head warp: the pairs in the CTA's order (pair k in slot k mod kTcSlots); lane j holds
+        //      hidden unit j's F1 row in registers ----
+        float f1[C3];
+#pragma unroll
+        for (int c = 0; c < C3; c++) f1[c] = sF1[c * HID + lane];
+        float f2[NOUT];
+#pragma unroll
+        for (int i = 0; i < NOUT; i++) f2[i] = sF2[i * HID + lane];
+        const float c1 = sC1[lane];
+        uint32_t ph = 0u;   // bit s: parity of slot s's next pooled-ready wait
+        long long k = 0;
+        for (long long i = blockIdx.x; i < NP; i += G, k++) {
+            const int sl = (int)(k % kTcSlots);
+            if (*(volatile int *)s_fail) break;
+            if (!mbar_wait(smem_u32(bar + 1 + 2 * kTcSlots + sl), (ph >> sl) & 1u)) {
+                atomicExch(s_fail, 1);
+                if (err) atomicExch(err, 1);
+                break;
+            }
+            ph ^= 1u << sl;
+            const long long pa = pairs ? (long long)pairs[i] : i;
+            const float *gsl = sG + sl * 2 * C3;
+#pragma unroll 1
+            for (int t2 = 0; t2 < 2; t2++) {
+                const long long ht = pa * 2 + t2;
+                if (ht >= T) continue;
+                const float *g2 = gsl + t2 * C3;
+                // four interleaved partial sums (a quarter of the dependent chain); g2 read as
+                // broadcast 16-byte loads
+                float y4[4] = {c1, 0.f, 0.f, 0.f};
+#pragma unroll
+                for (int c = 0; c < C3; c += 4) {
+                    const float4 gv = *reinterpret_cast<const float4 *>(g2 + c);
+                    y4[0] = fmaf(f1[c], gv.x, y4[0]);
+                    y4[1] = fmaf(f1[c + 1], gv.y, y4[1]);
+                    y4[2] = fmaf(f1[c + 2], gv.z, y4[2]);
+                    y4[3] = fmaf(f1[c + 3], gv.w, y4[3]);
+                }
+                const float yv = (y4[0] + y4[1]) + (y4[2] + y4[3]);
+                const float hj = bfround(fmaxf(yv, 0.f));
+                float o[NOUT];
+#pragma unroll
+                for (int q = 0; q < NOUT; q++) {
+                    float sacc = f2[q] * hj;
+#pragma unroll
+                    for (int off = 16; off; off >>= 1) sacc += __shfl_xor_sync(0xffffffffu, sacc, off);
+                    o[q] = sacc + sC2[q];
+                }
+                if (lane < NOUT) out[(size_t)ht * NOUT + lane] = o[lane];
+                if (kTrain) {
+                    act.h[(size_t)ht * HID + lane] = hj;
+                    act.g[(size_t)ht * C3 + lane] = g2[lane];
+                    act.g[(size_t)ht * C3 + lane + 32] = g2[lane + 32];
+                    if (lane < NOUT) act.o[(size_t)ht * NOUT + lane] = o[lane];
+                }
+            }
+            __syncwarp();
+            if (lane == 0) mbar_arrive(smem_u32(bar + 1 + 3 * kTcSlots + sl));   // the slot's vectors are read
+        }
+        __syncwarp();
     } else {
         // ---- epilogue group of slot sl: row = 32 quad + lane -> (y, tile, x) ----
         const int sl = warp >> 2, quad = warp & 3;
@@ -511,7 +578,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_net_fwd_tc(NetDev nd, const b
         const int gt = tid - sl * 128;   // thread index within the group
         uint8_t *buf = sAct + sl * TACT;
         const uint32_t bar_done = smem_u32(bar + 1 + sl), bar_in = smem_u32(bar + 1 + kTcSlots + sl);
-        uint32_t ph = 0u;
+        const uint32_t bar_pooled = smem_u32(bar + 1 + 2 * kTcSlots + sl), bar_headdone = smem_u32(bar + 1 + 3 * kTcSlots + sl);
+        uint32_t ph = 0u, hph = 0u;
         auto wait = [&](uint32_t mbar, uint32_t parity) {   // bounded; gives up at once after any expiry
             if (*(volatile int *)s_fail) return;
             if (!mbar_wait(mbar, parity)) {
@@ -563,8 +631,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_net_fwd_tc(NetDev nd, const b
         if (i0 < NP) put_input(load_in(i0));
         uint2 vin = load_in(i0 + kTcSlots * G);
         for (long long i = i0; i < NP; i += kTcSlots * G) {
-            const long long pa = pair_of(i);
-            const long long tile = pa * 2 + tl;
+            const long long tile = pair_of(i) * 2 + tl;
 #pragma unroll 1
             for (int layer = 0; layer < 3; layer++) {
                 wait(bar_done, ph);
@@ -573,7 +640,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_net_fwd_tc(NetDev nd, const b
                 const int cout = layer == 0 ? C1 : C2;
                 const float *bias = layer == 0 ? sB1 : layer == 1 ? sB2 : sB3;
 #pragma unroll 1
-                for (int c0 = 0; c0 < cout; c0 += 8) {   // 8 columns per load: 13 warps need <= 128 registers
+                for (int c0 = 0; c0 < cout; c0 += 8) {   // 8 columns per load: 14 warps need <= 128 registers
                     float v[8];
                     tc_ld8(trow + (uint32_t)c0, v);
                     tc_wait_ld();
@@ -598,6 +665,10 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_net_fwd_tc(NetDev nd, const b
                 else tc_before_sync();
             }
             group_sync(sl);
+            if (i != i0) {   // the head warp has read this slot's previous pooled vectors
+                wait(bar_headdone, hph);
+                hph ^= 1u;
+            }
             {   // pooling: thread (tile t2, channel chunk c8, column x) sums its column's 8 pixels of
                 // 8 channels (16-byte loads, 8 lanes on consecutive positions), then a reduce-scatter
                 // over the 8 columns leaves lane x with channel 8 c8 + x
@@ -629,40 +700,11 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_net_fwd_tc(NetDev nd, const b
                 gs[t2 * C3 + 8 * c8 + x] = bfround(b1 * (1.0f / kPX));
             }
             group_sync(sl);   // pooled vectors complete; the activations are read, so the buffer is free
-            if (i + kTcSlots * G < NP) {   // the next pair's input goes to the MMA warp before this head
+            __syncwarp();
+            if (lane == 0) mbar_arrive(bar_pooled);   // the head warp takes the pair's pooled vectors
+            if (i + kTcSlots * G < NP) {   // the next pair's input goes to the MMA warp
                 put_input(vin);
                 vin = load_in(i + 2 * kTcSlots * G);
-            }
-            if (quad < 2) {   // head: warp quad < 2 of the group takes tile quad of the pair
-                const int t2 = quad;
-                const long long ht = pa * 2 + t2;
-                if (ht < T) {
-                    const float *g2 = gs + t2 * C3;
-                    // four interleaved partial sums (a quarter of the dependent chain); lanes read
-                    // consecutive banks
-                    float y4[4] = {sC1[lane], 0.f, 0.f, 0.f};
-#pragma unroll 4
-                    for (int c = 0; c < C3; c += 4)
-#pragma unroll
-                        for (int q = 0; q < 4; q++) y4[q] = fmaf(sF1[(c + q) * HID + lane], g2[c + q], y4[q]);
-                    const float yv = (y4[0] + y4[1]) + (y4[2] + y4[3]);
-                    const float hj = bfround(fmaxf(yv, 0.f));
-                    float o[NOUT];
-#pragma unroll
-                    for (int i = 0; i < NOUT; i++) {
-                        float sacc = sF2[i * HID + lane] * hj;
-#pragma unroll
-                        for (int off = 16; off; off >>= 1) sacc += __shfl_xor_sync(0xffffffffu, sacc, off);
-                        o[i] = sacc + sC2[i];
-                    }
-                    if (lane < NOUT) out[(size_t)ht * NOUT + lane] = o[lane];
-                    if (kTrain) {
-                        act.h[(size_t)ht * HID + lane] = hj;
-                        act.g[(size_t)ht * C3 + lane] = g2[lane];
-                        act.g[(size_t)ht * C3 + lane + 32] = g2[lane + 32];
-                        if (lane < NOUT) act.o[(size_t)ht * NOUT + lane] = o[lane];
-                    }
-                }
             }
         }
     }
@@ -1328,10 +1370,10 @@ lcc_status forward_tc(lcc_net *net, const uint16_t *d_x, int64_t ntiles, float *
     const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(pairs, net->sms));
     const bf16 *x = reinterpret_cast<const bf16 *>(d_x);
     if (train)
-        k_net_fwd_tc<true><<<grid, kTcThreads, kTcSmem, net->stream>>>(net->nd, x, ntiles, d_out, net->err, net->act,
+        k_net_fwd_tc<true><<<grid, kFwdThreads, kTcSmem, net->stream>>>(net->nd, x, ntiles, d_out, net->err, net->act,
                                                                         pair_list, npairs);
     else
-        k_net_fwd_tc<false><<<grid, kTcThreads, kTcSmem, net->stream>>>(net->nd, x, ntiles, d_out, net->err, net->act,
+        k_net_fwd_tc<false><<<grid, kFwdThreads, kTcSmem, net->stream>>>(net->nd, x, ntiles, d_out, net->err, net->act,
                                                                          pair_list, npairs);
     return cudaGetLastError() == cudaSuccess ? LCC_OK : LCC_ERR_CUDA;
 }
