@@ -643,9 +643,13 @@ __global__ void __launch_bounds__(kFwdThreads, 1) k_net_fwd_tc(NetDev nd, const 
                 for (int c0 = 0; c0 < cout; c0 += 8) {   // 8 columns per load: 14 warps need <= 128 registers
                     float v[8];
                     tc_ld8(trow + (uint32_t)c0, v);
+                    // the 8 biases as two broadcast 16-byte loads (bias arrays are 16-byte aligned)
+                    const float4 bl = *reinterpret_cast<const float4 *>(bias + c0),
+                                 bh = *reinterpret_cast<const float4 *>(bias + c0 + 4);
+                    const float bv[8] = {bl.x, bl.y, bl.z, bl.w, bh.x, bh.y, bh.z, bh.w};
                     tc_wait_ld();
 #pragma unroll
-                    for (int i = 0; i < 8; i++) v[i] = fmaxf(v[i] + bias[c0 + i], 0.f);
+                    for (int i = 0; i < 8; i++) v[i] = fmaxf(v[i] + bv[i], 0.f);
                     uint32_t w[4];
 #pragma unroll
                     for (int q = 0; q < 4; q++) {
