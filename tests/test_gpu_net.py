@@ -106,6 +106,14 @@ def test_forward_matches_oracle(frame):
     err = np.abs(og - oo)
     assert (err <= 1e-2 * (1.0 + np.abs(oo))).all(), err.max()
     assert np.median(err) <= 1e-3
+    # per output (logit, normal x/y/z, offset) over the tiles: relative norm of the difference at
+    # most 1e-2 (the relative bound without an absolute floor), worst element against the
+    # output's largest magnitude reported
+    rel = np.linalg.norm(og - oo, axis=0) / np.maximum(np.linalg.norm(oo, axis=0), 1e-12)
+    worst = err.max(axis=0) / np.maximum(np.abs(oo).max(axis=0), 1e-12)
+    print("forward relative error per output (norm, worst element / output max):",
+          np.round(rel, 6).tolist(), np.round(worst, 6).tolist())
+    assert (rel <= 1e-2).all(), rel
     # the full frame runs too (persistent kernel over 2048 tiles)
     full = torch.zeros((c.num_tiles, 5), dtype=torch.float32, device="cuda")
     net.forward(x, c.num_tiles, full)
