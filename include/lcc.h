@@ -368,6 +368,13 @@ lcc_status lcc_net_tile_inputs(lcc_ctx *ctx, const float *d_pts, int64_t n, uint
  * tiles are rows [f*num_tiles, (f+1)*num_tiles) of d_x and d_anchor. */
 lcc_status lcc_net_tile_inputs_batch(lcc_ctx *ctx, int32_t nframes, const float *const *d_pts, const int64_t *n,
                                      uint16_t *d_x, float *d_anchor);
+/* Training labels of frame `frame` of the context's last encode: d_labels [num_tiles][5] fp32
+ * (fit flag 1 or 0, the plane's unit normal n[3], its offset relative to the tile's anchor
+ * d - n.anchor formed in FP64 and rounded once; zeros for a tile whose status is not FIT), from
+ * the tile records and d_anchor [num_tiles] float4 as lcc_net_tile_inputs writes it (16-byte
+ * aligned).  Asynchronous on the context's stream.  LCC_ERR_INVALID_ARG for a frame outside the
+ * last encode. */
+lcc_status lcc_net_tile_labels(lcc_ctx *ctx, int32_t frame, const float *d_anchor, float *d_labels);
 /* Outputs d_out [ntiles][5] fp32 (logit, v[3], d_rel), on the net's stream.
  * Inference runs on tcgen05 (TMEM accumulators, two tiles per MMA); its
  * waits are bounded, and one that ran out is reported by lcc_net_sync. */

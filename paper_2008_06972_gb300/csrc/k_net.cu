@@ -207,6 +207,26 @@ __global__ void k_net_inputs(Geometry g, uint32_t *rimg0, bf16 *x0, float4 *anch
 // (zero before the launch) ends as their number.  A thread takes kPairsPer consecutive pairs;
 // a block scan orders a block's pairs, and one atomic per block places the block's run (runs
 // land in any order: a pair's outputs do not depend on where in the list it is).
+// Training labels of one encoded frame, a thread per tile: (fit flag, unit normal, offset of the
+// plane relative to the tile's anchor, d - n.a), zeros for tiles that did not fit.  The offset is
+// formed in FP64 with separately rounded products and sums, n_x a_x + n_y a_y + n_z a_z added left
+// to right, then rounded to fp32 once.
+__global__ void k_net_labels(const TileRec *recs, const float4 *anchor, int NT, float *labels) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= NT) return;
+    const TileRec &r = recs[t];
+    const bool fit = r.status == S_FIT;
+    const float4 pl = r.plane, a = anchor[t];
+    const double s = __dadd_rn(__dadd_rn(__dmul_rn((double)pl.x, (double)a.x), __dmul_rn((double)pl.y, (double)a.y)),
+                               __dmul_rn((double)pl.z, (double)a.z));
+    float *y = labels + (size_t)t * NOUT;
+    y[0] = fit ? 1.0f : 0.0f;
+    y[1] = fit ? pl.x : 0.0f;
+    y[2] = fit ? pl.y : 0.0f;
+    y[3] = fit ? pl.z : 0.0f;
+    y[4] = fit ? (float)__dsub_rn((double)pl.w, s) : 0.0f;
+}
+
 constexpr int kPairsThreads = 256, kPairsPer = 8;
 __global__ void __launch_bounds__(kPairsThreads) k_net_pairs(const uint8_t *need, long long T, uint32_t *pairs,
                                                              uint32_t *npairs) {
@@ -1577,6 +1597,15 @@ lcc_status lcc_net_tile_inputs_batch(lcc_ctx *c, int32_t nframes, const float *c
 
 lcc_status lcc_net_tile_inputs(lcc_ctx *c, const float *d_pts, int64_t n, uint16_t *d_x, float *d_anchor) {
     return lcc_net_tile_inputs_batch(c, 1, &d_pts, &n, d_x, d_anchor);
+}
+
+lcc_status lcc_net_tile_labels(lcc_ctx *c, int32_t frame, const float *d_anchor, float *d_labels) {
+    if (!c || !d_anchor || !d_labels || frame < 0 || frame >= c->last_nframes || ((uintptr_t)d_anchor & 15u))
+        return LCC_ERR_INVALID_ARG;
+    const int NT = c->g.NT;
+    k_net_labels<<<(NT + 255) / 256, 256, 0, c->stream>>>(c->s.tiles + (size_t)frame * NT,
+                                                          reinterpret_cast<const float4 *>(d_anchor), NT, d_labels);
+    return cudaGetLastError() == cudaSuccess ? LCC_OK : LCC_ERR_CUDA;
 }
 
 lcc_status lcc_net_forward(lcc_net *net, const uint16_t *d_x, int64_t ntiles, float *d_out) {

@@ -129,6 +129,7 @@ def load(path: str = LIB_PATH):
         "lcc_net_set_params": (i32, [vp, vp]),
         "lcc_net_tile_inputs": (i32, [vp, vp, i64, vp, vp]),
         "lcc_net_tile_inputs_batch": (i32, [vp, i32, vp, vp, vp, vp]),
+        "lcc_net_tile_labels": (i32, [vp, i32, vp, vp]),
         "lcc_net_forward": (i32, [vp, vp, i64, vp]),
         "lcc_net_sync": (i32, [vp]),
         "lcc_selftest_bounded_wait": (i32, [i64, vp]),
@@ -164,7 +165,7 @@ def exported_symbols() -> list[str]:
             "lcc_encode_keyframe", "lcc_encode_keyframe_seeded", "lcc_encode_keyframes", "lcc_encode_pframe", "lcc_encode_pframes", "lcc_encode_sequence",
             "lcc_encode_sequence_host", "lcc_keyframe_from_stream", "lcc_decode", "lcc_decode_sequence", "lcc_imu_pose", "lcc_entropy_encode", "lcc_entropy_decode", "lcc_sync", "lcc_last_stats",
             "lcc_tile_records", "lcc_tile_coefficients", "lcc_set_profiling", "lcc_kernel_times", "lcc_kernel_timeline", "lcc_range_image_static", "lcc_net_num_params", "lcc_net_create", "lcc_net_destroy",
-            "lcc_net_get_params", "lcc_net_set_params", "lcc_net_tile_inputs", "lcc_net_tile_inputs_batch", "lcc_net_forward", "lcc_net_sync", "lcc_net_gradient",
+            "lcc_net_get_params", "lcc_net_set_params", "lcc_net_tile_inputs", "lcc_net_tile_inputs_batch", "lcc_net_tile_labels", "lcc_net_forward", "lcc_net_sync", "lcc_net_gradient",
             "lcc_net_train_step", "lcc_selftest_bounded_wait", "lcc_plan_create", "lcc_plan_update",
             "lcc_plan_set_proposals", "lcc_plan_set_staging", "lcc_plan_encode", "lcc_plan_capture", "lcc_plan_replay", "lcc_plan_sync", "lcc_plan_encode_host", "lcc_plan_get_info", "lcc_plan_stats",
             "lcc_plan_destroy", "lcc_autotune"]
@@ -617,6 +618,11 @@ class Net:
 
 def net_tile_inputs(ctx: "Context", d_pts, n: int, d_x, d_anchor):
     _check(load().lcc_net_tile_inputs(ctx.h, _ptr(d_pts), n, _ptr(d_x), _ptr(d_anchor)), "lcc_net_tile_inputs")
+
+
+def net_tile_labels(ctx: "Context", frame: int, d_anchor, d_labels):
+    """Training labels (fit, n, d - n.anchor) of frame `frame` of the context's last encode."""
+    _check(load().lcc_net_tile_labels(ctx.h, frame, _ptr(d_anchor), _ptr(d_labels)), "lcc_net_tile_labels")
 
 
 def net_tile_inputs_batch(ctx: "Context", d_pts: list, n: list, d_x, d_anchor):

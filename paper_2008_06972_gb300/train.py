@@ -2,8 +2,9 @@
 
 Labels come from the plain encoder itself: for every 8x8 tile of a key frame, the fit flag
 of its own iterative fit and its plane, with the offset expressed relative to the tile's
-anchor (the first valid pixel's point).  Every forward, backward and optimiser step runs
-in the library's CUDA kernels; this module only gathers tiles into batches.
+anchor (the first valid pixel's point), formed on the device (lcc_net_tile_labels).  Every
+forward, backward and optimiser step runs in the library's CUDA kernels; this module only
+gathers tiles into batches.
 """
 from __future__ import annotations
 
@@ -34,19 +35,6 @@ def he_uniform_params(seed: int) -> np.ndarray:
     return out
 
 
-def tile_labels(recs: np.ndarray, anchors: np.ndarray) -> np.ndarray:
-    """(T, 5) float32 targets from the plain encoder's tile records: fit flag, unit normal,
-    offset relative to the anchor (zeros for tiles that did not fit)."""
-    fit = recs["status"] == lcc.S_FIT
-    n = recs["plane"][:, :3].astype(np.float64)
-    y = np.zeros((len(recs), 5), np.float64)
-    y[:, 0] = fit
-    y[:, 1:4] = n
-    y[:, 4] = recs["plane"][:, 3].astype(np.float64) - (n * anchors[:, :3].astype(np.float64)).sum(axis=1)
-    y[~fit, 1:] = 0.0
-    return y.astype(np.float32)
-
-
 def frame_examples(ctx: "lcc.Context", pts_dev, n: int):
     """Net inputs (T, 64, 4) bf16-as-int16 device tensor, anchors and labels of one frame."""
     import torch
@@ -60,9 +48,10 @@ def frame_examples(ctx: "lcc.Context", pts_dev, n: int):
     st = ctx.lcc_sync()
     if st != lcc.OK:
         raise lcc.LccError(st, "frame_examples")
+    y = torch.empty((nt, 5), dtype=torch.float32, device="cuda")
+    lcc.net_tile_labels(ctx, 0, anc, y)
     recs = ctx.lcc_tile_records(0)
-    y = tile_labels(recs, anc.cpu().numpy())
-    return x, anc, torch.from_numpy(y).cuda(), recs
+    return x, anc, y, recs
 
 
 def train(net: "lcc.Net", x, y, steps: int, batch: int, lr: float, seed: int = 0, lr_final: float | None = None):

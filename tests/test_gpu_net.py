@@ -222,6 +222,24 @@ def test_weight_gradients_any_tile_count(frame, nt):
         o += n
 
 
+def test_tile_labels_on_device_match_oracle(frame):
+    """lcc_net_tile_labels (fit flag, normal, d - n.anchor in FP64 rounded once) equals the
+    oracle's labels of the same records and anchors, bit for bit."""
+    from paper_2008_06972_gb300 import lcc
+    sensor, pts = frame
+    c, x, anc = _gpu_inputs(sensor, pts)
+    _, recs = H.encode_keyframe(c, pts)
+    planes, ok = H.gpu_planes(recs)
+    y = N.labels(ok, planes, anc.cpu().numpy()[:, :3]).astype(np.float32)
+    yg = torch.full((c.num_tiles, 5), float("nan"), dtype=torch.float32, device="cuda")
+    lcc.net_tile_labels(c, 0, anc, yg)
+    assert c.lcc_sync() == lcc.OK
+    assert np.array_equal(yg.cpu().numpy().view(np.uint32), y.view(np.uint32))
+    assert (ok == 1).sum() > 100 and (ok == 0).sum() > 100
+    with pytest.raises(lcc.LccError):
+        lcc.net_tile_labels(c, 1, anc, yg)   # one frame was encoded
+
+
 def test_training_lowers_the_loss(frame):
     """Labels from the plain GPU encoder (fit flag and plane per 8x8 tile); Adam on one frame."""
     from paper_2008_06972_gb300 import lcc
