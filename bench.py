@@ -1320,6 +1320,10 @@ def run_cfg5(args, stream, rank, world, dist):
                "sample": f"{args.cpu_steps} frames per core of the same workload ({args.cpu_steps / 10:g} key-frame "
                          f"groups of 10 per core, key frame first: oracle net forward on every 8x8 tile + seeded "
                          f"fit; P frames plain), {pts_c / 1e6:.1f} M points in {sec_c:.1f} s of oracle time"}
+        # the same sample on one core (the oracle's single-thread rate)
+        v1, pts1, sec1, _ = oracle_cfg5(args.cpu_steps, args.thr, cores=1)
+        cpu["single_core"] = {"value": v1, "unit": UNIT, "cores": 1,
+                              "sample": f"{args.cpu_steps} frames, {pts1 / 1e6:.1f} M points in {sec1:.1f} s"}
 
     def summary(kind, ms, val, err, nbytes_):
         st = stats[kind]
