@@ -365,8 +365,9 @@ lcc_status ensure_staging(lcc_plan *p) {
         for (const auto *list : {&pc.keys, &pc.pframes})
             for (const auto &pf : *list)
                 if (pf.host) need = std::max(need, pf.n);
-        pc.staged = p->staging && need > 0;
-        if (!pc.staged) continue;
+        // the class reads its host points in place unless everything below is in place
+        pc.staged = false;
+        if (!p->staging || need == 0) continue;
         if (!pc.cstream) {
             if (cudaStreamCreateWithFlags(&pc.cstream, cudaStreamNonBlocking) != cudaSuccess) return LCC_ERR_CUDA;
             for (int b = 0; b < 2; b++)
@@ -382,6 +383,7 @@ lcc_status ensure_staging(lcc_plan *p) {
             LCC_CUDA(cudaMalloc(&pc.stage, sizeof(float4) * 2 * (size_t)pc.ctx->slots * (size_t)need));
             pc.stage_n = need;
         }
+        pc.staged = true;
     }
     return LCC_OK;
 }
