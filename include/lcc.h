@@ -69,7 +69,9 @@ typedef struct {
                                  the order lcc_encode_sequence always uses, which pays when few P tiles
                                  pass the temporal test; 5: as 4 with every round of every tile run by
                                  a group of lanes (a warp quarter for 8x8 tiles) splitting its pixels,
-                                 the first pass only queueing the tiles (same results for every value) */
+                                 the first pass only queueing the tiles; 6: as 4 with the queued tiles'
+                                 remaining rounds run by one thread per tile (same results for every
+                                 value) */
     int32_t no_delta;         /* 1: plane-coded points carry no residual code, the paper's default
                                  (Sec. III-C drops the deltas): they decode onto their plane, decode
                                  error <= fit_thr_m; 0 (default here): residual codes, error <= q/2 */
@@ -555,7 +557,7 @@ void lcc_plan_destroy(lcc_plan *plan);
  * against its planes) with every candidate of tile shape {4x4, 4x8, 8x8,
  * 8x16} (those whose bit is set in `shapes`: bit 0 4x4, bit 1 4x8, bit 2 8x8,
  * bit 3 8x16; 0 = all four) x run-test horizon {8, 16, 32} (only 0 when
- * base->merge_runs is 0) x fit schedule {0, 3, 4, 5}, each on a context of its own,
+ * base->merge_runs is 0) x fit schedule {0, 3, 4, 5, 6}, each on a context of its own,
  * `reps` timed encodes per candidate (CUDA events on cuda_stream).  Every
  * frame is then decoded and compared with its binned input: candidates whose
  * max range error exceeds max_err_m are rejected.  Of the rest, those whose

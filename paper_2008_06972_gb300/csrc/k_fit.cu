@@ -854,6 +854,33 @@ __global__ void __launch_bounds__(kFitThreads) k_fit_round(Geometry g, Scratch s
     }
 }
 
+// The same rounds for the queued tiles with one thread per tile (schedule 6): the per-thread fit
+// of the first pass, so each round's solve runs once per tile instead of on every lane of a group.
+template <int TH_, int TW_>
+__global__ void __launch_bounds__(kFitThreads) k_fit_round_thr(Geometry g, Scratch s, Batch b, int in_q, int out_q,
+                                                                 int max_rounds) {
+    using TV = TileView<TH_, TW_>;
+    uint32_t *queue = s.queue + (size_t)b.qset * 2 * s.qcap;
+    uint32_t *qcount = s.qcount + 8 * b.qset;
+    const uint32_t n_in = qcount[in_q];
+    const uint32_t *qin = queue + (size_t)(in_q & 1) * s.qcap;
+    uint32_t *qout = queue + (size_t)(out_q & 1) * s.qcap;
+    const uint32_t stride = gridDim.x * kFitThreads;
+    for (uint32_t idx = blockIdx.x * kFitThreads + threadIdx.x; idx < n_in; idx += stride) {
+        const uint32_t item = qin[idx];
+        const int f = (int)(item >> 26), t = (int)(item & 0x3FFFFFFu);
+        const uint32_t *rimg = s.rimg + (size_t)b.slot[f] * g.H * g.W;
+        TileRec *recs = s.tiles + (size_t)b.slot[f] * g.NT;
+        const TV tv(g, rimg, t);
+        RecOut o = read_rec(recs + t);
+        const float *prop = o.rounds == 0 && b.prop[f] ? b.prop[f] + 5 * (size_t)t : nullptr;
+        const bool done = spatial_rounds(tv, o, max_rounds, prop, b.skip_logit);
+        queue_push(!done, item, qout, qcount + out_q);
+        write_rec(recs + t, o);
+        if (g.plane3) s.coef[(size_t)b.slot[f] * g.NT + t] = o.coef;
+    }
+}
+
 // Temporal test of the P frames after their spatial fits (lcc_encode_sequence), with the
 // same per-tile decision as the fused pass (a tile that passes becomes temporal exactly as
 // if its spatial fit had never run):
@@ -1178,6 +1205,11 @@ static cudaError_t launch_queued_rounds_t(const Geometry &g, const Scratch &s, c
         const long long worst = (long long)g.NT * b.nframes;
         constexpr int L = FitLanes<TH_, TW_>::L;   // lanes per queued tile
         const int blocks = (int)std::min<long long>((worst * L + kFitThreads - 1) / kFitThreads, 152 * 8);
+        if (g.schedule == 6) {   // one dense launch, a thread per queued tile
+            const int tblocks = (int)std::min<long long>((worst + kFitThreads - 1) / kFitThreads, 152 * 8);
+            k_fit_round_thr<TH_, TW_><<<tblocks, kFitThreads, 0, st>>>(g, s, b, 0, 1, rounds_left);
+            return cudaGetLastError();
+        }
         if (g.schedule >= 3) {   // the queued tiles run all their remaining rounds in one dense launch
             k_fit_round<TH_, TW_><<<blocks, kFitThreads, 0, st>>>(g, s, b, 0, 1, rounds_left);
             return cudaGetLastError();

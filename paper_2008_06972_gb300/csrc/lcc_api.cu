@@ -316,7 +316,7 @@ lcc_status lcc_create(lcc_ctx **out, const lcc_sensor *sensor, const lcc_params 
     if (!(p.fit_thr_m >= 0) || !(p.quant_m > 0) || p.max_refits < 0 || p.max_refits > 6 ||
         !(p.min_inlier_frac >= 0) || p.max_batch < 1 || p.max_batch > kMaxBatch || p.lookahead < 0 ||
         p.lookahead > 32 || p.solver < 0 || p.solver > 1 || p.fit_schedule < 0 ||
-        p.fit_schedule > 5 || p.no_delta < 0 || p.no_delta > 1 || p.raw_exact < 0 || p.raw_exact > 1 ||
+        p.fit_schedule > 6 || p.no_delta < 0 || p.no_delta > 1 || p.raw_exact < 0 || p.raw_exact > 1 ||
         p.temporal_candidates < 0 || p.temporal_candidates > 4 || p.temporal_runs < 0 || p.temporal_runs > 1 ||
         p.plane3 < 0 || p.plane3 > 1)
         return LCC_ERR_INVALID_ARG;

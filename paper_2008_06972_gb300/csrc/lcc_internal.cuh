@@ -113,7 +113,8 @@ struct Geometry {
     int schedule;        // 0 per-thread fit rounds; 1, 2: that many rounds per thread, the rest queued;
                          // 3: one round per thread, the rest in one dense launch; 4: as 3, and batched
                          // P frames fit spatially first and run the temporal test after; 5: as 4 with
-                         // every round on a lane group per tile (the first pass only queues)
+                         // every round on a lane group per tile (the first pass only queues); 6: as 4
+                         // with the queued rounds on a thread per tile
     int first_rounds;    // fit rounds of the first pass under a queued schedule (0 under schedule 5)
     int no_delta;        // 1: plane-coded points carry no residual code (no residual section)
     int raw_exact;       // 1: raw pixels carry their fp32 range bits (32-bit raw codes)

@@ -135,7 +135,7 @@ lcc_status lcc_autotune(const lcc_sensor *sensor, const lcc_params *base, int32_
     if (!shapes) shapes = 15u;
     std::vector<lcc_tune_result> all;
     for (int ti = 0; ti < 4; ti++)
-        for (int sched : {0, 3, 4, 5})
+        for (int sched : {0, 3, 4, 5, 6})
             for (int h = 0; h < (base->merge_runs ? 3 : 1); h++) {
                 if (!((shapes >> ti) & 1u)) continue;
                 const int *t = kTiles[ti];

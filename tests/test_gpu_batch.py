@@ -212,8 +212,8 @@ def test_autotune_picks_fastest_within_byte_slack():
     base = lcc.default_params(max_batch=8)
     best, rows = lcc.autotune(s.sensor, base, k, s.poses, ds, [len(f) for f in s.frames], reps=2,
                               stream=torch.cuda.current_stream())
-    assert len(rows) == 4 * 3 * 4   # tile shapes x horizons x fit schedules {0, 3, 4, 5}
-    assert sorted({r["fit_schedule"] for r in rows}) == [0, 3, 4, 5]
+    assert len(rows) == 4 * 3 * 5   # tile shapes x horizons x fit schedules {0, 3, 4, 5, 6}
+    assert sorted({r["fit_schedule"] for r in rows}) == [0, 3, 4, 5, 6]
     # every schedule fits the same planes: per tile shape and horizon one stream size
     for th, tw, la in {(r["tile_h"], r["tile_w"], r["lookahead"]) for r in rows}:
         assert len({r["bytes"] for r in rows if (r["tile_h"], r["tile_w"], r["lookahead"]) == (th, tw, la)}) == 1

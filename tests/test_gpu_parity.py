@@ -207,7 +207,7 @@ def test_schedule_invariance_and_determinism(cfg1):
     ref = None
     ref_recs = None
     for la, sched in ((0, 0), (1, 0), (8, 0), (16, 0), (32, 0), (16, 1), (16, 2), (0, 2), (16, 3), (16, 4),
-                      (16, 5), (0, 5)):
+                      (16, 5), (0, 5), (16, 6)):
         c = H.ctx(sen, lookahead=la, fit_schedule=sched)
         b1, r1 = H.encode_keyframe(c, pts)
         b2, _ = H.encode_keyframe(c, pts)
@@ -297,7 +297,7 @@ def test_pframe_parity_tiles(cfg2_seq, tile, thr):
     _pframe_case(seq, [0, seq.key_index + 1], tile=tile, thr=thr)
 
 
-@pytest.mark.parametrize("schedule", [1, 4, 5])
+@pytest.mark.parametrize("schedule", [1, 4, 5, 6])
 def test_pframe_parity_queued_schedule(cfg2_seq, schedule):
     """Queued rounds (1); spatial fits first and the temporal test after them (4)."""
     seq = cfg2_seq
@@ -359,7 +359,7 @@ def test_sequence_call_matches_separate_calls(cfg2_seq):
         assert _canonical_ahead(precs[i], tc).tobytes() == _canonical_ahead(seq_recs[f], tc).tobytes(), \
             f"frame {f}: tile records differ"
     # the same with the queued fit schedules (their P rounds also run beside the key frame)
-    for sched in (1, 2, 3, 5):
+    for sched in (1, 2, 3, 5, 6):
         cq = H.ctx(seq.sensor, max_batch=16, fit_schedule=sched)
         outs_q = [H.out_buf(cq) for _ in range(n)]
         cq.lcc_encode_sequence(seq.key_index, seq.poses, ds, [len(p) for p in seq.frames], outs_q,

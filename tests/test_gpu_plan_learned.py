@@ -70,7 +70,7 @@ def test_seeded_plan_matches_oracle_on_large_frames(trained_net, batch):
     k0 = synth.group_key(0, NFR, 10)
     best, rows = lcc.autotune(sensor, lcc.default_params(max_batch=10), k0, seqs[0].poses[:10], d_pts[0][:10],
                               [len(f) for f in seqs[0].frames[:10]], reps=1, stream=stream, shapes=[(8, 8)])
-    assert (best.tile_h, best.tile_w) == (8, 8) and len(rows) == 3 * 4   # horizons x fit schedules
+    assert (best.tile_h, best.tile_w) == (8, 8) and len(rows) == 3 * 5   # horizons x fit schedules
     best.max_batch = 3            # several chunks of key and P frames
     ctx = lcc.Context(sensor, best, stream=stream)
     descs = []
